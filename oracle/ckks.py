@@ -1,0 +1,632 @@
+"""Python layer of the CPU oracle: ctypes bindings to liboracle.so, the exact big-integer CRT step of
+decoding, and the composite schedules (sum, dot, vector x plain matrix, im2col convolution, the
+MNIST-shaped CNN) written in the order their definitions state.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, the package smoke check and the benchmark's
+CPU-baseline leg; never by the GPU library. Shares no code with it.
+
+The paper (TenSEAL) describes the operations at the level of its tensor API (§2-§3, Table 3); the
+RNS-CKKS definitions each function follows are stated in its docstring.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .build import build
+
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_dblp = ctypes.POINTER(ctypes.c_double)
+_lib = None
+
+
+def lib():
+    """Load (building first if needed) the oracle's shared library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    L = ctypes.CDLL(build())
+    u64, u32, i64, vp, i32 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
+    sig = {
+        "orc_is_prime": (i32, [u64]),
+        "orc_gen_primes": (i32, [u32, _u32p, u32, _u64p]),
+        "orc_min_psi": (u64, [u64, u32]),
+        "orc_bit_reverse": (u32, [u32, u32]),
+        "orc_philox4x64": (None, [_u64p, _u64p, _u64p]),
+        "orc_ntt_naive": (None, [_u64p, _u64p, u32, u64, u64]),
+        "orc_ntt": (None, [_u64p, u32, u64, u64]),
+        "orc_intt": (None, [_u64p, u32, u64, u64]),
+        "orc_ctx_new": (vp, [u32, _u64p, u32]),
+        "orc_ctx_free": (None, [vp]),
+        "orc_ctx_psi": (u64, [vp, u32]),
+        "orc_ntt_limb": (None, [vp, _u64p, u32]),
+        "orc_intt_limb": (None, [vp, _u64p, u32]),
+        "orc_galois_elt": (u32, [vp, i64]),
+        "orc_automorphism_ntt": (None, [vp, _u64p, u32, u32, _u64p]),
+        "orc_automorphism_coeff": (None, [vp, _u64p, u64, u32, _u64p]),
+        "orc_keygen_secret": (None, [vp, u64, _u64p]),
+        "orc_keygen_public": (None, [vp, u64, _u64p, _u64p]),
+        "orc_keygen_switch": (None, [vp, u64, u64, _u64p, _u64p, u32, _u64p]),
+        "orc_keygen_relin": (None, [vp, u64, _u64p, u32, _u64p]),
+        "orc_keygen_galois": (None, [vp, u64, _u64p, u32, u32, _u64p]),
+        "orc_encode": (i32, [vp, _dblp, u32, ctypes.c_double, u32, _dblp, _u64p]),
+        "orc_decode_sum": (None, [vp, _dblp, ctypes.c_double, u32, _dblp]),
+        "orc_encrypt": (None, [vp, _u64p, _u64p, u32, u64, _u64p]),
+        "orc_decrypt": (None, [vp, _u64p, _u64p, u32, _u64p]),
+        "orc_add": (None, [vp, _u64p, _u64p, u32, u32, _u64p]),
+        "orc_sub": (None, [vp, _u64p, _u64p, u32, u32, _u64p]),
+        "orc_negate": (None, [vp, _u64p, u32, u32, _u64p]),
+        "orc_add_plain": (None, [vp, _u64p, _u64p, u32, _u64p]),
+        "orc_sub_plain": (None, [vp, _u64p, _u64p, u32, _u64p]),
+        "orc_mul_plain": (None, [vp, _u64p, _u64p, u32, _u64p]),
+        "orc_tensor": (None, [vp, _u64p, _u64p, u32, _u64p]),
+        "orc_rescale": (None, [vp, _u64p, u32, _u64p]),
+        "orc_modup": (None, [vp, _u64p, u32, _u64p]),
+        "orc_keyswitch_digits": (None, [vp, _u64p, u32, _u64p, u32, u32, _u64p]),
+        "orc_keyswitch": (None, [vp, _u64p, u32, _u64p, u32, _u64p]),
+        "orc_relinearize": (None, [vp, _u64p, u32, _u64p, u32, _u64p]),
+        "orc_rotate": (None, [vp, _u64p, u32, u32, _u64p, u32, _u64p]),
+        "orc_rotate_from_digits": (None, [vp, _u64p, _u64p, u32, u32, _u64p, u32, _u64p]),
+        "orc_max_threads": (i32, []),
+        "orc_set_threads": (None, [i32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def P(a: np.ndarray):
+    """Pointer to a C-contiguous uint64 / uint32 / float64 numpy array."""
+    assert a.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+    if a.dtype == np.uint64:
+        return a.ctypes.data_as(_u64p)
+    if a.dtype == np.uint32:
+        return a.ctypes.data_as(_u32p)
+    if a.dtype == np.float64:
+        return a.ctypes.data_as(_dblp)
+    raise TypeError(a.dtype)
+
+
+# ------------------------------------------------------------------------------ free functions --
+
+def is_prime(n: int) -> bool:
+    return bool(lib().orc_is_prime(n))
+
+
+def gen_primes(log_n: int, bits) -> list[int]:
+    b = np.ascontiguousarray(bits, dtype=np.uint32)
+    out = np.zeros(len(bits), dtype=np.uint64)
+    if lib().orc_gen_primes(log_n, P(b), len(bits), P(out)) != 0:
+        raise ValueError(f"no NTT-friendly primes for bits={list(bits)} at N=2^{log_n}")
+    return [int(x) for x in out]
+
+
+def min_psi(q: int, log_n: int) -> int:
+    return int(lib().orc_min_psi(q, log_n))
+
+
+def philox4x64(ctr, key) -> list[int]:
+    c = np.array(ctr, dtype=np.uint64)
+    k = np.array(key, dtype=np.uint64)
+    o = np.zeros(4, dtype=np.uint64)
+    lib().orc_philox4x64(P(c), P(k), P(o))
+    return [int(x) for x in o]
+
+
+def ntt_naive(a, q: int, psi: int) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    out = np.zeros_like(a)
+    lib().orc_ntt_naive(P(a), P(out), int(len(a)).bit_length() - 1, q, psi)
+    return out
+
+
+def ntt(a, q: int, psi: int) -> np.ndarray:
+    a = np.array(a, dtype=np.uint64)
+    lib().orc_ntt(P(a), int(len(a)).bit_length() - 1, q, psi)
+    return a
+
+
+def intt(a, q: int, psi: int) -> np.ndarray:
+    a = np.array(a, dtype=np.uint64)
+    lib().orc_intt(P(a), int(len(a)).bit_length() - 1, q, psi)
+    return a
+
+
+# ------------------------------------------------------------------------ ciphertext records --
+
+@dataclass
+class Ct:
+    """A CKKSVector ciphertext: data [2][level][N] (NTT form), its level and its scale."""
+    data: np.ndarray
+    level: int
+    scale: float
+
+
+@dataclass
+class Pt:
+    """An encoded plaintext: data [level][N] (NTT form), its level and its scale."""
+    data: np.ndarray
+    level: int
+    scale: float
+
+
+@dataclass
+class SwitchKey:
+    """A switching key [K][2][K+1][N] of level K (limb K is the special prime)."""
+    data: np.ndarray
+    level: int
+
+
+class OracleCKKS:
+    """RNS-CKKS over the chain q_0..q_{L-1} (data primes) and P (special prime).
+
+    Mirrors the TenSEAL context of §2.1: it owns the secret, public, relinearization and Galois keys,
+    and the context-wide default scale.
+    """
+
+    def __init__(self, log_n: int, bits, scale: float, key_seed: int = 0x7E5EA1, primes=None):
+        self.log_n = log_n
+        self.N = 1 << log_n
+        self.slots = self.N // 2
+        self.primes = list(primes) if primes is not None else gen_primes(log_n, bits)
+        self.q = self.primes
+        self.L = len(self.primes) - 1
+        self.Pspecial = self.primes[-1]
+        self.scale = float(scale)
+        self.key_seed = key_seed
+        arr = np.array(self.primes, dtype=np.uint64)
+        self._ctx = lib().orc_ctx_new(log_n, P(arr), len(self.primes))
+        if not self._ctx:
+            raise ValueError("a prime of the chain has no primitive 2N-th root")
+        self.s = None
+        self.pk = None
+        self.rlk = None
+        self.galois = {}
+
+    def __del__(self):
+        if getattr(self, "_ctx", None):
+            lib().orc_ctx_free(self._ctx)
+            self._ctx = None
+
+    # ------------------------------------------------------------------------------- keys ----
+    def keygen(self, relin_level: int | None = None):
+        """Secret, public and relinearization keys from the context seed (§2.1)."""
+        N, L = self.N, self.L
+        self.s = np.zeros((L + 1, N), dtype=np.uint64)
+        lib().orc_keygen_secret(self._ctx, self.key_seed, P(self.s))
+        self.pk = np.zeros((2, L, N), dtype=np.uint64)
+        lib().orc_keygen_public(self._ctx, self.key_seed, P(self.s), P(self.pk))
+        K = L if relin_level is None else relin_level
+        rlk = np.zeros((K, 2, K + 1, N), dtype=np.uint64)
+        lib().orc_keygen_relin(self._ctx, self.key_seed, P(self.s), K, P(rlk))
+        self.rlk = SwitchKey(rlk, K)
+        return self
+
+    def galois_elt(self, step: int) -> int:
+        return int(lib().orc_galois_elt(self._ctx, step))
+
+    def gen_galois_key(self, step: int, key_level: int | None = None) -> SwitchKey:
+        """Galois key for a left rotation by `step` slots, trimmed to `key_level` (default L)."""
+        K = self.L if key_level is None else key_level
+        g = self.galois_elt(step)
+        gk = np.zeros((K, 2, K + 1, self.N), dtype=np.uint64)
+        lib().orc_keygen_galois(self._ctx, self.key_seed, P(self.s), g, K, P(gk))
+        self.galois[step % self.slots] = SwitchKey(gk, K)
+        return self.galois[step % self.slots]
+
+    def gen_galois_keys(self, steps, key_level: int | None = None):
+        for st in steps:
+            self.gen_galois_key(st, key_level)
+
+    # -------------------------------------------------------------------- encode / decode ----
+    def encode(self, z, scale: float | None = None, level: int | None = None, want_pre: bool = False):
+        """Encode real slot values (O9); returns Pt (and the pre-rounding scale*m_i if asked)."""
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        scale = self.scale if scale is None else float(scale)
+        level = self.L if level is None else level
+        pt = np.zeros((level, self.N), dtype=np.uint64)
+        pre = np.zeros(self.N, dtype=np.float64)
+        st = lib().orc_encode(self._ctx, P(z), len(z), scale, level, P(pre), P(pt))
+        if st == -1:
+            raise ValueError("encode: bad size or level")
+        if st == -2:
+            raise OverflowError("encode: |scale * m_i| >= 2^62")
+        out = Pt(pt, level, scale)
+        return (out, pre) if want_pre else out
+
+    def intt_limbs(self, limbs: np.ndarray, level: int) -> np.ndarray:
+        out = np.array(limbs, dtype=np.uint64, copy=True).reshape(level, self.N)
+        for l in range(level):
+            row = np.ascontiguousarray(out[l])
+            lib().orc_intt_limb(self._ctx, P(row), l)
+            out[l] = row
+        return out
+
+    def crt_compose(self, coeffs: np.ndarray, level: int) -> list[int]:
+        """Exact CRT of coefficient-domain residues [level][N] to centred integers in (-Q/2, Q/2]."""
+        qs = self.q[:level]
+        Q = math.prod(qs)
+        terms = []
+        for l, ql in enumerate(qs):
+            Ql = Q // ql
+            terms.append((ql, pow(Ql % ql, -1, ql), Ql))
+        rows = [[int(v) for v in coeffs[l]] for l in range(level)]
+        out = []
+        half = Q // 2
+        for i in range(self.N):
+            x = 0
+            for l, (ql, inv, Ql) in enumerate(terms):
+                x += (rows[l][i] * inv % ql) * Ql
+            x %= Q
+            if x > half:
+                x -= Q
+            out.append(x)
+        return out
+
+    def decode(self, pt: Pt, n: int | None = None) -> np.ndarray:
+        """Decode (O10): INTT, exact CRT to centred integers, round to double, canonical embedding."""
+        n = self.slots if n is None else n
+        coeffs = self.intt_limbs(pt.data, pt.level)
+        ints = self.crt_compose(coeffs, pt.level)
+        p = np.array([float(x) for x in ints], dtype=np.float64)
+        z = np.zeros(n, dtype=np.float64)
+        lib().orc_decode_sum(self._ctx, P(p), pt.scale, n, P(z))
+        return z
+
+    # ------------------------------------------------------------------ encrypt / decrypt ----
+    def encrypt(self, pt: Pt, seed: int) -> Ct:
+        """Public-key encryption at the plaintext's level (O11)."""
+        ct = np.zeros((2, pt.level, self.N), dtype=np.uint64)
+        data = np.ascontiguousarray(pt.data)
+        lib().orc_encrypt(self._ctx, P(self.pk), P(data), pt.level, seed, P(ct))
+        return Ct(ct, pt.level, pt.scale)
+
+    def decrypt(self, ct: Ct) -> Pt:
+        pt = np.zeros((ct.level, self.N), dtype=np.uint64)
+        lib().orc_decrypt(self._ctx, P(self.s), P(np.ascontiguousarray(ct.data)), ct.level, P(pt))
+        return Pt(pt, ct.level, ct.scale)
+
+    def encrypt_values(self, z, seed: int, level: int | None = None) -> Ct:
+        return self.encrypt(self.encode(z, level=level), seed)
+
+    def decrypt_values(self, ct: Ct, n: int | None = None) -> np.ndarray:
+        return self.decode(self.decrypt(ct), n)
+
+    # ------------------------------------------------------------------- element-wise ops ----
+    @staticmethod
+    def _check_pair(a: Ct, b: Ct):
+        if a.level != b.level:
+            raise ValueError("level mismatch")
+        if a.scale != b.scale:
+            raise ValueError("scale mismatch")
+
+    def add(self, a: Ct, b: Ct) -> Ct:
+        self._check_pair(a, b)
+        out = np.zeros_like(a.data)
+        lib().orc_add(self._ctx, P(a.data), P(b.data), a.level, 2, P(out))
+        return Ct(out, a.level, a.scale)
+
+    def sub(self, a: Ct, b: Ct) -> Ct:
+        self._check_pair(a, b)
+        out = np.zeros_like(a.data)
+        lib().orc_sub(self._ctx, P(a.data), P(b.data), a.level, 2, P(out))
+        return Ct(out, a.level, a.scale)
+
+    def negate(self, a: Ct) -> Ct:
+        out = np.zeros_like(a.data)
+        lib().orc_negate(self._ctx, P(a.data), a.level, 2, P(out))
+        return Ct(out, a.level, a.scale)
+
+    def _plain_for(self, ct: Ct, pt: Pt) -> np.ndarray:
+        if pt.level < ct.level:
+            raise ValueError("plaintext level below ciphertext level")
+        return np.ascontiguousarray(pt.data[: ct.level])
+
+    def add_plain(self, ct: Ct, pt: Pt) -> Ct:
+        if pt.scale != ct.scale:
+            raise ValueError("scale mismatch")
+        out = np.zeros_like(ct.data)
+        lib().orc_add_plain(self._ctx, P(ct.data), P(self._plain_for(ct, pt)), ct.level, P(out))
+        return Ct(out, ct.level, ct.scale)
+
+    def sub_plain(self, ct: Ct, pt: Pt) -> Ct:
+        if pt.scale != ct.scale:
+            raise ValueError("scale mismatch")
+        out = np.zeros_like(ct.data)
+        lib().orc_sub_plain(self._ctx, P(ct.data), P(self._plain_for(ct, pt)), ct.level, P(out))
+        return Ct(out, ct.level, ct.scale)
+
+    def mul_plain(self, ct: Ct, pt: Pt) -> Ct:
+        out = np.zeros_like(ct.data)
+        lib().orc_mul_plain(self._ctx, P(ct.data), P(self._plain_for(ct, pt)), ct.level, P(out))
+        return Ct(out, ct.level, ct.scale * pt.scale)
+
+    def tensor(self, a: Ct, b: Ct) -> tuple[np.ndarray, int, float]:
+        """(d0, d1, d2) of O13 as [3][level][N], with scale a.scale * b.scale."""
+        if a.level != b.level:
+            raise ValueError("level mismatch")
+        out = np.zeros((3, a.level, self.N), dtype=np.uint64)
+        lib().orc_tensor(self._ctx, P(a.data), P(b.data), a.level, P(out))
+        return out, a.level, a.scale * b.scale
+
+    def relinearize(self, d3: np.ndarray, level: int, scale: float) -> Ct:
+        out = np.zeros((2, level, self.N), dtype=np.uint64)
+        lib().orc_relinearize(self._ctx, P(np.ascontiguousarray(d3)), level, P(self.rlk.data), self.rlk.level, P(out))
+        return Ct(out, level, scale)
+
+    def rescale(self, ct: Ct) -> Ct:
+        """Divide by the last prime with rounding (O14)."""
+        if ct.level < 2:
+            raise ValueError("level exhausted")
+        out = np.zeros((2, ct.level - 1, self.N), dtype=np.uint64)
+        lib().orc_rescale(self._ctx, P(np.ascontiguousarray(ct.data)), ct.level, P(out))
+        return Ct(out, ct.level - 1, ct.scale / float(self.q[ct.level - 1]))
+
+    def mod_switch(self, ct: Ct, level: int) -> Ct:
+        """Drop limbs level..ell-1; the scale is unchanged (O19)."""
+        return Ct(np.ascontiguousarray(ct.data[:, :level]), level, ct.scale)
+
+    def mul(self, a: Ct, b: Ct, relin: bool = True, rescale: bool = True) -> Ct:
+        """enc x enc multiply with the context's auto relinearize / rescale policy (§2.1)."""
+        d3, level, scale = self.tensor(a, b)
+        ct = self.relinearize(d3, level, scale)
+        return self.rescale(ct) if rescale else ct
+
+    def square(self, a: Ct) -> Ct:
+        return self.mul(a, a)
+
+    # ----------------------------------------------------------------------------- rotate ----
+    def _key(self, step: int) -> SwitchKey:
+        k = step % self.slots
+        if k not in self.galois:
+            raise KeyError(f"no Galois key for step {step}")
+        return self.galois[k]
+
+    def rotate(self, ct: Ct, step: int) -> Ct:
+        """Left rotation by `step` slots (O18): automorphism then key switch."""
+        if step % self.slots == 0:
+            return Ct(ct.data.copy(), ct.level, ct.scale)
+        key = self._key(step)
+        out = np.zeros_like(ct.data)
+        lib().orc_rotate(self._ctx, P(ct.data), ct.level, self.galois_elt(step), P(key.data), key.level, P(out))
+        return Ct(out, ct.level, ct.scale)
+
+    def modup(self, ct: Ct) -> np.ndarray:
+        """Digits of c1 for hoisted rotations: [level][level+1][N]."""
+        d = np.zeros((ct.level, ct.level + 1, self.N), dtype=np.uint64)
+        c1 = np.ascontiguousarray(ct.data[1])
+        lib().orc_modup(self._ctx, P(c1), ct.level, P(d))
+        return d
+
+    def rotate_from_digits(self, ct: Ct, digits: np.ndarray, step: int) -> Ct:
+        if step % self.slots == 0:
+            return Ct(ct.data.copy(), ct.level, ct.scale)
+        key = self._key(step)
+        out = np.zeros_like(ct.data)
+        lib().orc_rotate_from_digits(self._ctx, P(ct.data), P(digits), ct.level, self.galois_elt(step),
+                                     P(key.data), key.level, P(out))
+        return Ct(out, ct.level, ct.scale)
+
+    def rotate_hoisted(self, ct: Ct, steps) -> list[Ct]:
+        """Several rotations of one ciphertext sharing one ModUp of c1 (O18)."""
+        digits = self.modup(ct)
+        return [self.rotate_from_digits(ct, digits, s) for s in steps]
+
+    def keyswitch(self, x: np.ndarray, level: int, key: SwitchKey) -> np.ndarray:
+        out = np.zeros((2, level, self.N), dtype=np.uint64)
+        lib().orc_keyswitch(self._ctx, P(np.ascontiguousarray(x)), level, P(key.data), key.level, P(out))
+        return out
+
+    # ---------------------------------------------------------------- composite schedules ----
+    def sum_steps(self) -> list[int]:
+        return [1 << m for m in range(self.log_n - 1)]
+
+    def sum(self, ct: Ct, n: int) -> Ct:
+        """Rotate-and-add over all N/2 slots (O20); slots >= n must be zero. Every slot ends up with
+        the total."""
+        if n > self.slots:
+            raise ValueError("n exceeds the slot count")
+        for m in range(self.log_n - 1):
+            ct = self.add(ct, self.rotate(ct, 1 << m))
+        return ct
+
+    def dot(self, a: Ct, b: Ct, n: int) -> Ct:
+        """enc . enc dot product (§3.1): sum(rescale(relin(a x b)), n)."""
+        return self.sum(self.mul(a, b), n)
+
+    def dot_plain(self, a: Ct, w, n: int) -> Ct:
+        """enc . plain dot product (§3.1): sum(rescale(a * enc(w)), n)."""
+        pt = self.encode(w, level=a.level)
+        return self.sum(self.rescale(self.mul_plain(a, pt)), n)
+
+    def replicate_steps(self, n: int) -> list[int]:
+        """Left-rotation steps that replicate an n-vector over all N/2 slots (§3.1)."""
+        reps = self.slots // n
+        return [self.slots - n * (1 << m) for m in range(int(math.log2(reps)))]
+
+    def matrix_diagonals(self, M: np.ndarray) -> list[np.ndarray]:
+        """Generalised diagonals d_k[s] = M[(s+k) mod n][s] for s < m, 0 elsewhere (O21)."""
+        n, m = M.shape
+        out = []
+        for k in range(n):
+            d = np.zeros(self.slots, dtype=np.float64)
+            for s in range(m):
+                d[s] = M[(s + k) % n][s]
+            out.append(d)
+        return out
+
+    def encode_matrix(self, M: np.ndarray, level: int) -> list[Pt]:
+        return [self.encode(d, level=level) for d in self.matrix_diagonals(np.asarray(M, dtype=np.float64))]
+
+    def vecmat_steps(self, n: int) -> list[int]:
+        steps = self.replicate_steps(n) if n < self.slots else []
+        return steps + list(range(1, n))
+
+    def vecmat(self, ct: Ct, diags: list[Pt], n: int, m: int) -> Ct:
+        """Encrypted vector (slots [0, n), zeros elsewhere) times a plain n x m matrix given as
+        pre-encoded diagonals (§3.1, the diagonal method with left rotations only and a replicated
+        input): replicate, then y = sum_k rot(ct, k) * d_k with hoisted rotations, then rescale."""
+        if len(diags) != n or m > n:
+            raise ValueError("bad matrix shape")
+        if n < self.slots:
+            for st in self.replicate_steps(n):
+                ct = self.add(ct, self.rotate(ct, st))
+        digits = self.modup(ct)
+        acc = None
+        for k in range(n):
+            r = ct if k == 0 else self.rotate_from_digits(ct, digits, k)
+            t = self.mul_plain(r, diags[k])
+            acc = t if acc is None else self.add(acc, t)
+        return self.rescale(acc)
+
+    @staticmethod
+    def im2col(img: np.ndarray, kh: int, kw: int, stride: int, slots: int):
+        """Client-side im2col (§3.2): windows as rows (row-major windows, row-major taps), flattened
+        by a vertical scan: slot t*W + w holds tap t of window w. Returns (slot vector, W)."""
+        H, Wd = img.shape
+        oh = (H - kh) // stride + 1
+        ow = (Wd - kw) // stride + 1
+        windows = oh * ow
+        taps = kh * kw
+        if taps * windows > slots:
+            raise ValueError("image does not fit the slots")
+        v = np.zeros(slots, dtype=np.float64)
+        for r in range(oh):
+            for c in range(ow):
+                w = r * ow + c
+                for t in range(taps):
+                    v[t * windows + w] = img[stride * r + t // kw][stride * c + t % kw]
+        return v, windows
+
+    def conv_steps(self, taps: int, windows: int) -> list[int]:
+        return [windows * (1 << m) for m in range(int(math.ceil(math.log2(taps))))]
+
+    def conv2d_im2col_pt(self, ct: Ct, kernel_pt: Pt, taps: int, windows: int) -> Ct:
+        """One kernel of the im2col convolution (§3.2): one multiplication by the replicated kernel,
+        rescale, then log2(taps) left rotate-and-adds by windows * 2^m. Block-w of every 'windows'
+        slots then holds the output for window w."""
+        out = self.rescale(self.mul_plain(ct, kernel_pt))
+        for st in self.conv_steps(taps, windows):
+            out = self.add(out, self.rotate(out, st))
+        return out
+
+    def kernel_slots(self, kernel: np.ndarray, windows: int) -> np.ndarray:
+        """Plain kernel laid out to match the vertical scan: slot t*W + w holds kernel tap t."""
+        k = np.asarray(kernel, dtype=np.float64).reshape(-1)
+        v = np.zeros(self.slots, dtype=np.float64)
+        for t in range(len(k)):
+            v[t * windows: (t + 1) * windows] = k[t]
+        return v
+
+    def conv2d_im2col(self, ct: Ct, kernel, windows: int) -> Ct:
+        k = np.asarray(kernel, dtype=np.float64).reshape(-1)
+        pt = self.encode(self.kernel_slots(k, windows), level=ct.level)
+        return self.conv2d_im2col_pt(ct, pt, len(k), windows)
+
+
+@dataclass
+class CNNWeights:
+    """Weights of the MNIST-shaped network of §4: conv 4x7x7 stride 3, square, FC 256->64, square,
+    FC 64->10."""
+    conv_w: np.ndarray  # [4][49]
+    conv_b: np.ndarray  # [4]
+    fc1_w: np.ndarray   # [64][256]
+    fc1_b: np.ndarray   # [64]
+    fc2_w: np.ndarray   # [10][64]
+    fc2_b: np.ndarray   # [10]
+
+
+@dataclass
+class EncodedCNN:
+    """Plaintexts of the CNN schedule, encoded at the levels the schedule uses them."""
+    conv: list = field(default_factory=list)   # per kernel, level L
+    masks: list = field(default_factory=list)  # per kernel, level L-1
+    fc1: list = field(default_factory=list)    # 256 diagonals, level L-3
+    fc2: list = field(default_factory=list)    # 64 diagonals, level L-5
+    windows: int = 64
+    taps: int = 49
+
+
+def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64):
+    """Galois steps of the CNN schedule with the level each is used at (key trimming)."""
+    L = o.L
+    need = {}
+
+    def use(steps, level):
+        for s in steps:
+            s %= o.slots
+            if s:
+                need[s] = max(need.get(s, 0), level)
+
+    use(o.conv_steps(taps, windows), L - 1)
+    use(o.vecmat_steps(n1), L - 3)
+    use(o.vecmat_steps(n2), L - 5)
+    return need
+
+
+def cnn_encode(o: OracleCKKS, w: CNNWeights, windows=64) -> EncodedCNN:
+    L = o.L
+    e = EncodedCNN(windows=windows, taps=w.conv_w.shape[1])
+    for k in range(w.conv_w.shape[0]):
+        e.conv.append(o.encode(o.kernel_slots(w.conv_w[k], windows), level=L))
+        mask = np.zeros(o.slots)
+        mask[k * windows: (k + 1) * windows] = 1.0
+        e.masks.append(o.encode(mask, level=L - 1))
+    e.fc1 = o.encode_matrix(w.fc1_w.T, L - 3)
+    e.fc2 = o.encode_matrix(w.fc2_w.T, L - 5)
+    return e
+
+
+def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN) -> Ct:
+    """The encrypted CNN schedule (§4): conv (im2col, one multiplication per kernel) -> pack the
+    four channel outputs with masks -> square -> FC1 (vector x plain matrix) -> square -> FC2.
+    Six multiplicative levels; biases are added as plaintexts at the ciphertext's scale and level."""
+    W = enc.windows
+    K = len(enc.conv)
+    chans = [o.conv2d_im2col_pt(ct, enc.conv[k], enc.taps, W) for k in range(K)]
+    v = None
+    for k in range(K):
+        t = o.rescale(o.mul_plain(chans[k], enc.masks[k]))
+        v = t if v is None else o.add(v, t)
+    bias = np.zeros(o.slots)
+    for k in range(K):
+        bias[k * W: (k + 1) * W] = w.conv_b[k]
+    v = o.add_plain(v, o.encode(bias, scale=v.scale, level=v.level))
+    v = o.square(v)
+    n1, m1 = w.fc1_w.shape[1], w.fc1_w.shape[0]
+    v = o.vecmat(v, enc.fc1, n1, m1)
+    b1 = np.zeros(o.slots)
+    b1[:m1] = w.fc1_b
+    v = o.add_plain(v, o.encode(b1, scale=v.scale, level=v.level))
+    v = o.square(v)
+    n2, m2 = w.fc2_w.shape[1], w.fc2_w.shape[0]
+    v = o.vecmat(v, enc.fc2, n2, m2)
+    b2 = np.zeros(o.slots)
+    b2[:m2] = w.fc2_b
+    v = o.add_plain(v, o.encode(b2, scale=v.scale, level=v.level))
+    return v
+
+
+def cnn_plain(img: np.ndarray, w: CNNWeights, stride=3) -> np.ndarray:
+    """The same network evaluated directly in FP64 (the accuracy reference)."""
+    kh = kw = int(round(math.sqrt(w.conv_w.shape[1])))
+    H, Wd = img.shape
+    oh = (H - kh) // stride + 1
+    ow = (Wd - kw) // stride + 1
+    conv = np.zeros((w.conv_w.shape[0], oh, ow))
+    for k in range(w.conv_w.shape[0]):
+        ker = w.conv_w[k].reshape(kh, kw)
+        for r in range(oh):
+            for c in range(ow):
+                conv[k, r, c] = np.sum(img[stride * r: stride * r + kh, stride * c: stride * c + kw] * ker) + w.conv_b[k]
+    x = conv.reshape(-1) ** 2
+    x = w.fc1_w @ x + w.fc1_b
+    x = x ** 2
+    return w.fc2_w @ x + w.fc2_b

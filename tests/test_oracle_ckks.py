@@ -1,0 +1,327 @@
+"""Pins of the oracle's CKKS layer (encoding, keys, homomorphic ops, schedules).
+
+Independent references used here: a numpy-FFT derivation of the canonical embedding, the closed form
+of encoding a constant, a big-integer (non-RNS) re-derivation of every exact op for tiny N
+(tests/tiny_ckks.py), exact algebraic invariants of automorphisms, a worst-case key-switch noise
+bound, and decrypt(op(Enc(x))) against FP64 arithmetic on the same values.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import OracleCKKS
+from paper_2104_03152_gb300 import inputs
+from tiny_ckks import TinyCKKS, primitive_2n_roots
+
+
+@pytest.fixture(scope="module")
+def c1():
+    """Config C1 chain: N=4096, [36,36,36 | 37], scale 2^30."""
+    o = OracleCKKS(12, [36, 36, 36, 37], 2.0 ** 30).keygen()
+    o.gen_galois_keys([1, 2, 5, 100, 2047] + o.sum_steps())
+    return o
+
+
+def fft_encode(z, n, scale):
+    """Canonical-embedding inverse via numpy: slot j sits at index t_j = (5^j mod 2N - 1)/4 of a size
+    N/2 transform (zeta^(5^j) = zeta * omega^t_j, omega = zeta^4); w_k zeta^k = (1/n) sum_t y_t
+    omega^(-tk) (numpy's forward FFT / n); m_k = Re w_k, m_{k+N/2} = Im w_k."""
+    half = n // 2
+    y = np.zeros(half, dtype=np.complex128)
+    g = 1
+    for j in range(half):
+        y[(g - 1) // 4] = z[j] if j < len(z) else 0.0
+        g = g * 5 % (2 * n)
+    wz = np.fft.fft(y) / half
+    k = np.arange(half)
+    w = wz * np.exp(-1j * np.pi * k / n)
+    return scale * np.concatenate([w.real, w.imag])
+
+
+def fft_decode(p, n, scale, n_out):
+    half = n // 2
+    w = (p[:half] + 1j * p[half:]) / scale
+    k = np.arange(half)
+    out = np.fft.ifft(w * np.exp(1j * np.pi * k / n)) * half  # sum_k (w_k zeta^k) omega^(+tk)
+    z = np.zeros(n_out)
+    g = 1
+    for j in range(n_out):
+        z[j] = out[(g - 1) // 4].real
+        g = g * 5 % (2 * n)
+    return z
+
+
+# ------------------------------------------------------------------------------ encoding ----
+
+def test_encode_constant_closed_form(c1):
+    """P6: a constant vector encodes to coefficient 0 = round(scale * c), every other coefficient 0."""
+    for c in (0.5, -1.25, 3.0):
+        pt, pre = c1.encode(np.full(c1.slots, c), want_pre=True)
+        coeffs = c1.crt_compose(c1.intt_limbs(pt.data, pt.level), pt.level)
+        assert coeffs[0] == round(c * 2 ** 30)
+        assert all(x == 0 for x in coeffs[1:])
+
+
+def test_encode_matches_fft_derivation(c1):
+    z = inputs.uniform_slots(c1.slots, 1)
+    pt, pre = c1.encode(z, want_pre=True)
+    ref = fft_encode(z, c1.N, 2.0 ** 30)
+    assert np.max(np.abs(pre - ref)) / 2 ** 30 < 1e-12
+    # a short, zero-padded input
+    z2 = inputs.uniform_slots(37, 2)
+    _, pre2 = c1.encode(z2, want_pre=True)
+    assert np.max(np.abs(pre2 - fft_encode(z2, c1.N, 2.0 ** 30))) / 2 ** 30 < 1e-12
+
+
+def test_decode_matches_fft_and_roundtrip(c1):
+    z = inputs.uniform_slots(c1.slots, 3)
+    pt = c1.encode(z)
+    dec = c1.decode(pt)
+    coeffs = np.array(c1.crt_compose(c1.intt_limbs(pt.data, pt.level), pt.level), dtype=np.float64)
+    assert np.max(np.abs(dec - fft_decode(coeffs, c1.N, 2.0 ** 30, c1.slots))) < 1e-12
+    # rounding each coefficient moves a slot by at most N/2 * 0.5 / scale
+    assert np.max(np.abs(dec - z)) < c1.N / 4 / 2 ** 30
+
+
+def test_encode_overflow_and_sizes(c1):
+    with pytest.raises(OverflowError):
+        c1.encode(np.full(4, 1e10), scale=2.0 ** 40)
+    with pytest.raises(ValueError):
+        c1.encode(np.zeros(c1.slots + 1))
+
+
+# -------------------------------------------------------------------------- keys / sampler ----
+
+def test_sampler_distributions(c1):
+    """s ternary, pk and key 'a' parts uniform, errors CBD(21): checked through the keys themselves."""
+    s_coeff = c1.intt_limbs(c1.s[:1], 1)[0]
+    q0 = c1.q[0]
+    vals = np.array([int(v) if int(v) <= q0 // 2 else int(v) - q0 for v in s_coeff])
+    assert set(np.unique(vals)) <= {-1, 0, 1}
+    frac = [np.mean(vals == t) for t in (-1, 0, 1)]
+    assert all(abs(f - 1 / 3) < 0.04 for f in frac)
+    # pk0 + pk1 * s = e (CBD, |e| <= 21, variance 10.5)
+    d = c1.decrypt(oracle.Ct(c1.pk[:, :1].copy(), 1, 1.0))
+    e = c1.crt_compose(c1.intt_limbs(d.data, 1), 1)
+    e = np.array(e)
+    assert np.max(np.abs(e)) <= 21
+    assert abs(np.var(e) - 10.5) < 1.5
+    a = c1.pk[1, 0].astype(np.float64)
+    assert abs(np.mean(a) / q0 - 0.5) < 0.02
+
+
+def test_key_trimming_is_subset():
+    o = OracleCKKS(10, [30, 30, 30, 30, 31], 2.0 ** 25).keygen()
+    full = o.gen_galois_key(3, 4).data.copy()
+    trim = o.gen_galois_key(3, 2).data
+    # trimmed key = digits j < 2, limbs q_0, q_1 and P of the full key
+    assert np.array_equal(trim[:, :, :2], full[:2, :, :2])
+    assert np.array_equal(trim[:, :, 2], full[:2, :, 4])
+
+
+# ------------------------------------------------------------- big-integer re-derivation ----
+
+@pytest.fixture(scope="module")
+def tiny():
+    o = OracleCKKS(4, [24, 24, 24, 26], 2.0 ** 10).keygen()
+    o.gen_galois_keys([1, 3])
+    # roots found independently of the oracle (smallest of all primitive 2N-th roots)
+    t = TinyCKKS(o.N, o.q, [primitive_2n_roots(q, o.N)[0] for q in o.q])
+    return o, t
+
+
+def _rand_ct(o, level, seed):
+    lim = inputs.random_limbs(o.q[:level], o.N, seed, polys=2)
+    return oracle.Ct(np.ascontiguousarray(lim), level, 1.0)
+
+
+def test_tiny_tensor_relin_rescale(tiny):
+    """P4/P5: tensor product, relinearization and rescale equal the big-integer definitions."""
+    o, t = tiny
+    lvl = 3
+    a, b = _rand_ct(o, lvl, 1), _rand_ct(o, lvl, 2)
+    idx = list(range(lvl))
+    Q = math.prod(o.q[:lvl])
+    A = [t.to_int(a.data[p], idx) for p in range(2)]
+    B = [t.to_int(b.data[p], idx) for p in range(2)]
+    d3, _, _ = o.tensor(a, b)
+    from tiny_ckks import negacyclic_mul
+    d0 = negacyclic_mul(A[0], B[0], Q)
+    d1 = [(x + y) % Q for x, y in zip(negacyclic_mul(A[0], B[1], Q), negacyclic_mul(A[1], B[0], Q))]
+    d2 = negacyclic_mul(A[1], B[1], Q)
+    for p, ref in enumerate((d0, d1, d2)):
+        assert t.to_int(d3[p], idx) == ref
+    rel = o.relinearize(d3, lvl, 1.0)
+    k0, k1 = t.keyswitch(d2, lvl, o.rlk.data, o.rlk.level)
+    assert t.to_int(rel.data[0], idx) == [(x + y) % Q for x, y in zip(d0, k0)]
+    assert t.to_int(rel.data[1], idx) == [(x + y) % Q for x, y in zip(d1, k1)]
+    rs = o.rescale(rel)
+    for p in range(2):
+        assert t.to_int(rs.data[p], idx[:-1]) == t.rescale(t.to_int(rel.data[p], idx), lvl)
+
+
+def test_tiny_rotation(tiny):
+    """P5: rotation = coefficient automorphism, then key switch, in big integers."""
+    o, t = tiny
+    lvl = 2
+    a = _rand_ct(o, lvl, 5)
+    idx = list(range(lvl))
+    Q = math.prod(o.q[:lvl])
+    for step in (1, 3):
+        g = o.galois_elt(step)
+        A = [t.automorphism(t.to_int(a.data[p], idx), g, Q) for p in range(2)]
+        k0, k1 = t.keyswitch(A[1], lvl, o.galois[step].data, o.galois[step].level)
+        r = o.rotate(a, step)
+        assert t.to_int(r.data[0], idx) == [(x + y) % Q for x, y in zip(A[0], k0)]
+        assert t.to_int(r.data[1], idx) == k1
+
+
+# --------------------------------------------------------------------- exact invariants ----
+
+def test_automorphism_ntt_equals_coefficient_map(c1):
+    """P7: the NTT-domain permutation equals the coefficient map a(X) -> a(X^g)."""
+    L = oracle.lib()
+    q = c1.q[0]
+    a = inputs.random_limbs([q], c1.N, 9)[0, 0].copy()
+    fa = a.copy()
+    L.orc_ntt_limb(c1._ctx, oracle.ckks.P(fa), 0)
+    for step in (1, 5, 2047):
+        g = c1.galois_elt(step)
+        ca = np.zeros_like(a)
+        L.orc_automorphism_coeff(c1._ctx, oracle.ckks.P(a), q, g, oracle.ckks.P(ca))
+        L.orc_ntt_limb(c1._ctx, oracle.ckks.P(ca), 0)
+        na = np.zeros_like(fa)
+        L.orc_automorphism_ntt(c1._ctx, oracle.ckks.P(fa), 1, g, oracle.ckks.P(na))
+        assert np.array_equal(ca, na)
+
+
+def test_automorphism_composition_and_rotation(c1):
+    """P7: tau_a(tau_b(x)) = tau_(ab)(x) exactly, and tau_(5^k) rotates slots left by k."""
+    L = oracle.lib()
+    z = inputs.uniform_slots(c1.slots, 4)
+    pt = c1.encode(z, level=1)
+    ga, gb = c1.galois_elt(2), c1.galois_elt(5)
+    t1 = np.zeros_like(pt.data)
+    t2 = np.zeros_like(pt.data)
+    L.orc_automorphism_ntt(c1._ctx, oracle.ckks.P(pt.data), 1, gb, oracle.ckks.P(t1))
+    L.orc_automorphism_ntt(c1._ctx, oracle.ckks.P(t1), 1, ga, oracle.ckks.P(t2))
+    t3 = np.zeros_like(pt.data)
+    L.orc_automorphism_ntt(c1._ctx, oracle.ckks.P(pt.data), 1, ga * gb % (2 * c1.N), oracle.ckks.P(t3))
+    assert np.array_equal(t2, t3)
+    assert ga * gb % (2 * c1.N) == c1.galois_elt(7)
+    dec = c1.decode(oracle.Pt(t1, 1, pt.scale))
+    assert np.max(np.abs(dec - np.roll(z, -5))) < 1e-6
+
+
+def test_hoisted_equals_plain_rotation(c1):
+    """P9: rotating from hoisted (balanced) digits is bit-identical to the plain rotation."""
+    ct = c1.encrypt_values(inputs.uniform_slots(c1.slots, 1), seed=11)
+    outs = c1.rotate_hoisted(ct, [1, 2, 100])
+    for st, h in zip([1, 2, 100], outs):
+        assert np.array_equal(h.data, c1.rotate(ct, st).data)
+
+
+def test_keyswitch_noise_bound(c1):
+    """P10: decrypt(KS_{s'->s}(x)) - x*s' has infinity norm at most
+    level*N*21*max(q_j)/(2P) + (N + 1)/2 (digits |D_j| <= q_j/2, |e| <= 21, ModDown rounding <= 1/2,
+    s ternary)."""
+    lvl = 3
+    x = inputs.random_limbs(c1.q[:lvl], c1.N, 12)[0]
+    ks = c1.keyswitch(x, lvl, c1.rlk)
+    s2 = np.array([[int(v) * int(v) % c1.q[l] for v in c1.s[l]] for l in range(lvl)], dtype=np.uint64)
+    dec = c1.decrypt(oracle.Ct(np.ascontiguousarray(ks), lvl, 1.0)).data
+    diff = np.array([[(int(dec[l, i]) - int(x[l, i]) * int(s2[l, i])) % c1.q[l] for i in range(c1.N)]
+                     for l in range(lvl)], dtype=np.uint64)
+    err = c1.crt_compose(c1.intt_limbs(diff, lvl), lvl)
+    bound = lvl * c1.N * 21 * max(c1.q[:lvl]) / (2 * c1.Pspecial) + (c1.N + 1) / 2
+    assert max(abs(e) for e in err) <= bound
+    assert max(abs(e) for e in err) > 0
+
+
+# ------------------------------------------------------------- decrypt(op(Enc x)) ~ op(x) ----
+
+def test_ops_against_fp64(c1):
+    """P11 on C1's chain (scale 2^30): every element-wise op decrypts to the FP64 result."""
+    x = inputs.uniform_slots(c1.slots, 1)
+    y = inputs.uniform_slots(c1.slots, 2)
+    cx, cy = c1.encrypt_values(x, seed=21), c1.encrypt_values(y, seed=22)
+    tol = 2e-4  # fresh-encryption noise: ~sqrt(N) * 300 / 2^30 per slot
+    dec = lambda ct: c1.decrypt_values(ct)
+    assert np.max(np.abs(dec(c1.add(cx, cy)) - (x + y))) < tol
+    assert np.max(np.abs(dec(c1.sub(cx, cy)) - (x - y))) < tol
+    assert np.max(np.abs(dec(c1.negate(cx)) + x)) < tol
+    assert np.max(np.abs(dec(c1.add_plain(cx, c1.encode(y))) - (x + y))) < tol
+    assert np.max(np.abs(dec(c1.sub_plain(cx, c1.encode(y))) - (x - y))) < tol
+    assert np.max(np.abs(dec(c1.rescale(c1.mul_plain(cx, c1.encode(y)))) - x * y)) < 1e-3
+    m = c1.mul(cx, cy)
+    assert m.level == 2
+    assert np.max(np.abs(dec(m) - x * y)) < 1e-3
+    assert np.max(np.abs(dec(c1.square(cx)) - x * x)) < 1e-3
+    assert np.max(np.abs(dec(c1.rotate(cx, 1)) - np.roll(x, -1))) < tol
+    assert np.max(np.abs(dec(c1.rotate(c1.rotate(cx, 1), 5)) - np.roll(x, -6))) < tol  # P8 (composition)
+    assert np.max(np.abs(dec(c1.mod_switch(cx, 1)) - x)) < tol
+
+
+def test_sum_dot():
+    """sum / dot / dot_plain (§3.1) on a chain whose rescale keeps the scale at 2^40 (with C1's
+    36-bit primes the scale drops to 2^24 after one rescale, and summing N/2 slots multiplies the
+    per-slot noise by about sqrt(N/2))."""
+    o = OracleCKKS(12, [55, 40, 40, 56], 2.0 ** 40).keygen()
+    o.gen_galois_keys(o.sum_steps())
+    n = 300
+    x = np.zeros(o.slots)
+    y = np.zeros(o.slots)
+    x[:n] = inputs.uniform_slots(n, 5)
+    y[:n] = inputs.uniform_slots(n, 6)
+    cx, cy = o.encrypt_values(x, 31), o.encrypt_values(y, 32)
+    s = o.decrypt_values(o.sum(cx, n))
+    assert np.max(np.abs(s - x.sum())) < 1e-6
+    d = o.decrypt_values(o.dot(cx, cy, n))
+    assert np.max(np.abs(d - x @ y)) < 1e-6
+    dp = o.decrypt_values(o.dot_plain(cx, y[:n], n))
+    assert np.max(np.abs(dp - x @ y)) < 1e-6
+
+
+def test_vecmat_identity_permutation_and_random():
+    """P14 and P11: vector x plain matrix with identity, permutation and random matrices."""
+    o = OracleCKKS(12, [36, 36, 36, 37], 2.0 ** 30).keygen()
+    n, m = 16, 8
+    o.gen_galois_keys(o.vecmat_steps(n))
+    v = np.zeros(o.slots)
+    v[:n] = inputs.uniform_slots(n, 7)
+    ct = o.encrypt_values(v, 41)
+    perm = np.random.default_rng(0).permutation(n)
+    Mp = np.zeros((n, m))
+    for s in range(m):
+        Mp[perm[s], s] = 1.0
+    Mr = inputs.random_matrix(n, m, 8, 0.5)
+    for M in (np.eye(n)[:, :m], Mp, Mr):
+        out = o.decrypt_values(o.vecmat(ct, o.encode_matrix(M, ct.level), n, m))
+        # C1's chain: the result scale after the rescale is 2^60 / q_2 ~ 2^24
+        assert np.max(np.abs(out[:m] - v[:n] @ M)) < 1e-3
+        assert np.max(np.abs(out[m:])) < 1e-3
+
+
+def test_im2col_layout_and_delta_conv():
+    """§3.2 geometry pins (28x28, 7x7, stride 3 -> 64 windows x 49 taps = 3136 slots) and P14: a
+    delta kernel reproduces the selected pixel of every window."""
+    img = inputs.mnist_like_image(3)
+    v, W = OracleCKKS.im2col(img, 7, 7, 3, 4096)
+    assert W == 64 and (28 - 7) // 3 + 1 == 8
+    assert np.all(v[49 * 64:] == 0)
+    assert v[10 * 64 + 9] == img[3 * 1 + 10 // 7][3 * 1 + 10 % 7]
+    o = OracleCKKS(13, [40, 30, 30, 41], 2.0 ** 30).keygen()
+    o.gen_galois_keys(o.conv_steps(49, W))
+    ct = o.encrypt_values(v, 51)
+    ker = np.zeros(49)
+    ker[24] = 1.0  # centre tap
+    out = o.decrypt_values(o.conv2d_im2col(ct, ker, W))
+    ref = np.array([img[3 * (w // 8) + 3][3 * (w % 8) + 3] for w in range(64)])
+    assert np.max(np.abs(out[:64] - ref)) < 1e-3  # noise of the 64 summed blocks
+    ker2 = inputs.cnn_weights(4)["conv_w"][0]
+    out2 = o.decrypt_values(o.conv2d_im2col(ct, ker2, W))
+    ref2 = np.array([np.sum(img[3 * (w // 8):3 * (w // 8) + 7, 3 * (w % 8):3 * (w % 8) + 7] * ker2.reshape(7, 7))
+                     for w in range(64)])
+    assert np.max(np.abs(out2[:64] - ref2)) < 1e-3
