@@ -1,0 +1,250 @@
+/*
+ * tcks.h — C ABI of a GB300 (sm_103a) RNS-CKKS library for encrypted vectors.
+ *
+ * What it computes: the CKKSVector operations of TenSEAL (arXiv 2104.03152, §2-§3 and Table 3) —
+ * a context holding secret, public, relinearization and Galois keys with automatic
+ * relinearization / rescaling (§2.1), encode / encrypt / decrypt / decode of up to N/2 real slots
+ * per ciphertext (§3), element-wise add / sub / negate / multiply with encrypted or plain operands,
+ * rotation, sum, dot products and the vector x plain-matrix product (§3.1), and the im2col
+ * convolution (§3.2) — down to the polynomial layer (negacyclic NTT, RNS key switching, Galois
+ * automorphisms, rescaling). The CKKS scheme itself (Cheon et al. 2017, which the paper builds on)
+ * is implemented in its RNS form with one special prime P and one key-switching digit per prime.
+ *
+ * Conventions
+ *   Handles are opaque. Every `**out` argument receives a newly created object owned by the caller,
+ *   released with the matching *_free call. Inputs are never modified unless the call says
+ *   "in place". Every call returns a tcks_status (0 = OK, < 0 = error) and never throws; on error no
+ *   output is produced and tcks_last_error_detail() (thread-local) explains it.
+ *   Levels count data primes: a ciphertext at level l has limbs q_0..q_{l-1}.
+ *   Device layouts: a ciphertext is u64 [2][level][N] (NTT form, canonical residues in [0, q_i)),
+ *   a plaintext u64 [level][N]. Host buffers use the same row-major layouts.
+ *   Concurrency: all work of a context runs asynchronously on the context's CUDA stream, in call
+ *   order. Calls that return host data (decode, decrypt-to-host, *_export) synchronise that stream.
+ *   A context must not be used from two host threads at once.
+ *   Scales are doubles carried with each object: multiplication multiplies them, rescale divides by
+ *   the dropped prime (as a double); add / sub require bitwise-equal scales and equal levels.
+ */
+#ifndef TCKS_H
+#define TCKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tcks_status;
+enum {
+  TCKS_OK = 0,
+  TCKS_ERR_INVALID_ARG = -1,     /* null pointer, size out of range, bad layout */
+  TCKS_ERR_BAD_PARAMS = -2,      /* N not a power of two in [2^3, 2^16], or no NTT-friendly prime */
+  TCKS_ERR_NO_GALOIS_KEY = -3,   /* rotation step without a generated Galois key */
+  TCKS_ERR_LEVEL_EXHAUSTED = -4, /* rescale at level 1, or a key trimmed below the needed level */
+  TCKS_ERR_SCALE_MISMATCH = -5,  /* add / sub of operands whose scales differ */
+  TCKS_ERR_LEVEL_MISMATCH = -6,  /* binary op on operands at different levels */
+  TCKS_ERR_OUT_OF_MEMORY = -7,   /* device allocation failed */
+  TCKS_ERR_BUDGET_EXCEEDED = -8, /* serving admission: HBM budget would be exceeded */
+  TCKS_ERR_CUDA = -9,            /* a CUDA runtime call failed (detail has the CUDA message) */
+  TCKS_ERR_TIMEOUT = -10,        /* a bounded device wait ran out */
+  TCKS_ERR_VALUE_OVERFLOW = -11, /* encode: |scale * m_i| >= 2^62 */
+  TCKS_ERR_UNSUPPORTED = -12     /* valid request this build does not implement (detail says what) */
+};
+
+const char* tcks_status_string(tcks_status s);
+/* Thread-local text of the last error raised on this thread ("" if none). */
+const char* tcks_last_error_detail(void);
+
+typedef struct tcks_params tcks_params;
+typedef struct tcks_ctx tcks_ctx;
+typedef struct tcks_ct tcks_ct;
+typedef struct tcks_pt tcks_pt;
+typedef struct tcks_matrix tcks_matrix;
+
+/* Optional device allocator (e.g. PyTorch's caching allocator bound by the Python layer). Both
+ * callbacks are stream-ordered on `stream`. NULL selects the library's own stream-ordered pool. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* user);
+  void (*free)(void* ptr, void* stream, void* user);
+  void* user;
+} tcks_allocator;
+
+/* ---------------------------------------------------------------------------- parameters ---- */
+/* Coefficient-modulus chain (the CKKS parameters of §4 / Tables 4-5: poly degree N = 2^log_n and
+ * the bit sizes of the coefficient modulus, last entry = the special prime P). For each bit size
+ * in order the prime is the largest c < 2^b, c > 2^(b-1), c == 1 (mod 2N), not chosen before.
+ * n_primes >= 2 (at least one data prime plus P), every size in [20, 61]. `scale` is the default
+ * encoding scale. */
+tcks_status tcks_params_create(uint32_t log_n, const uint32_t* bit_sizes, uint32_t n_primes, double scale,
+                               tcks_params** out);
+void tcks_params_free(tcks_params* p);
+/* Writes the n_primes chosen primes (data primes, then P) to host `primes`. */
+tcks_status tcks_params_primes(const tcks_params* p, uint64_t* primes, uint32_t capacity);
+
+/* ------------------------------------------------------------------------------- context ---- */
+/* TenSEAL context (§2.1): generates the secret key (ternary), the public key and the
+ * relinearization key from `seed` with the library's counter-based sampler (Philox4x64-10), on
+ * the device. flags: TCKS_AUTO_RELIN | TCKS_AUTO_RESCALE (the context's automatic policies).
+ * cuda_stream: a cudaStream_t the context works on (NULL = a stream the context creates).
+ * The context copies `params`. */
+enum { TCKS_AUTO_RELIN = 1u, TCKS_AUTO_RESCALE = 2u };
+tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32_t flags,
+                                const tcks_allocator* allocator, void* cuda_stream, tcks_ctx** out);
+void tcks_ctx_free(tcks_ctx* ctx);
+tcks_status tcks_ctx_info(const tcks_ctx* ctx, uint32_t* log_n, uint32_t* n_data_primes, double* scale);
+/* Device bytes held by the context's keys and tables. */
+tcks_status tcks_ctx_key_bytes(const tcks_ctx* ctx, uint64_t* bytes);
+/* Wait for all work queued on the context's stream. */
+tcks_status tcks_ctx_synchronize(tcks_ctx* ctx);
+
+/* Galois keys for left rotations by `steps` (§2.1, used by rotate / sum / dot / matmul_plain /
+ * conv2d_im2col). A step is taken modulo N/2; step 0 needs no key. max_level in [1, L] trims each
+ * key to the digits and limbs needed by ciphertexts at levels <= max_level (0 = L). Regenerating a
+ * step replaces its key. */
+tcks_status tcks_gen_galois_keys(tcks_ctx* ctx, const int32_t* steps, uint32_t n_steps, uint32_t max_level);
+tcks_status tcks_has_galois_key(const tcks_ctx* ctx, int32_t step, uint32_t* key_level);
+
+/* Key export / import as raw u64 limbs (host). kinds and layouts:
+ *   TCKS_KEY_SECRET [L+1][N]; TCKS_KEY_PUBLIC [2][L][N]; TCKS_KEY_RELIN [L][2][L+1][N];
+ *   TCKS_KEY_GALOIS [K][2][K+1][N] for the key of `step` (K = its level; limb K is P).
+ * n_words must equal the layout size. Import replaces the context's key (for Galois keys, the key
+ * of `step` at level `key_level`). */
+enum { TCKS_KEY_SECRET = 0, TCKS_KEY_PUBLIC = 1, TCKS_KEY_RELIN = 2, TCKS_KEY_GALOIS = 3 };
+tcks_status tcks_export_key(tcks_ctx* ctx, uint32_t kind, int32_t step, uint64_t* host, size_t n_words);
+tcks_status tcks_import_key(tcks_ctx* ctx, uint32_t kind, int32_t step, uint32_t key_level, const uint64_t* host,
+                            size_t n_words);
+
+/* ---------------------------------------------------------------- encode / encrypt (§3) ---- */
+/* Encode n <= N/2 real values (zero-padded) at `scale` (<= 0: the context scale) on limbs
+ * q_0..q_{level-1} (level 0 = L): inverse canonical embedding with slot j at zeta^(5^j), FP64 FFT on
+ * the device, rounding half away from zero, RNS reduction, NTT. VALUE_OVERFLOW if some
+ * |scale * m_i| >= 2^62. v is a host array. */
+tcks_status tcks_encode(tcks_ctx* ctx, const double* v, size_t n, double scale, uint32_t level, tcks_pt** out);
+/* The same from a device array of n doubles. */
+tcks_status tcks_encode_device(tcks_ctx* ctx, const double* d_v, size_t n, double scale, uint32_t level,
+                               tcks_pt** out);
+/* Decode the first n slots into host `out` (exact CRT to the centred integer, rounded to double,
+ * FP64 FFT). Synchronises. */
+tcks_status tcks_decode(tcks_ctx* ctx, const tcks_pt* pt, double* out, size_t n);
+/* Public-key encryption at the plaintext's level: c0 = u*pk0 + e0 + m, c1 = u*pk1 + e1 with u
+ * ternary and e0, e1 centred-binomial, all drawn from `seed`. */
+tcks_status tcks_encrypt(tcks_ctx* ctx, const tcks_pt* pt, uint64_t seed, tcks_ct** out);
+/* m = c0 + c1*s. */
+tcks_status tcks_decrypt(tcks_ctx* ctx, const tcks_ct* ct, tcks_pt** out);
+
+/* Raw import / export (host u64, layouts above). Import copies host -> device (asynchronously,
+ * then synchronises so `limbs` may be reused). Export synchronises. */
+tcks_status tcks_ct_import(tcks_ctx* ctx, const uint64_t* limbs, uint32_t level, double scale, tcks_ct** out);
+tcks_status tcks_ct_export(const tcks_ct* ct, uint64_t* limbs, size_t n_words);
+tcks_status tcks_pt_import(tcks_ctx* ctx, const uint64_t* limbs, uint32_t level, double scale, tcks_pt** out);
+tcks_status tcks_pt_export(const tcks_pt* pt, uint64_t* limbs, size_t n_words);
+tcks_status tcks_ct_info(const tcks_ct* ct, uint32_t* level, double* scale);
+tcks_status tcks_pt_info(const tcks_pt* pt, uint32_t* level, double* scale);
+/* Device pointer of the [2][level][N] limbs (valid until the ciphertext is freed). */
+tcks_status tcks_ct_device_ptr(const tcks_ct* ct, uint64_t** d_limbs);
+void tcks_ct_free(tcks_ct* ct);
+void tcks_pt_free(tcks_pt* pt);
+
+/* --------------------------------------------------------- element-wise ops (§3, Table 3) ---- */
+tcks_status tcks_add(const tcks_ct* a, const tcks_ct* b, tcks_ct** out);
+tcks_status tcks_sub(const tcks_ct* a, const tcks_ct* b, tcks_ct** out);
+tcks_status tcks_negate(const tcks_ct* a, tcks_ct** out);
+/* Plain operand: its first level(ct) limbs are used; add / sub need the plaintext at the
+ * ciphertext's scale. mul_plain multiplies the scales. */
+tcks_status tcks_add_plain(const tcks_ct* a, const tcks_pt* p, tcks_ct** out);
+tcks_status tcks_sub_plain(const tcks_ct* a, const tcks_pt* p, tcks_ct** out);
+tcks_status tcks_mul_plain(const tcks_ct* a, const tcks_pt* p, tcks_ct** out);
+/* enc x enc: tensor product (d0, d1, d2) = (a0b0, a0b1 + a1b0, a1b1), then relinearize and
+ * rescale as the context's AUTO flags say. Without AUTO_RELIN the result cannot be returned as a
+ * 2-component ciphertext and the call fails with UNSUPPORTED. */
+tcks_status tcks_mul(const tcks_ct* a, const tcks_ct* b, tcks_ct** out);
+tcks_status tcks_square(const tcks_ct* a, tcks_ct** out);
+/* Rescale in place: divide by the last prime with rounding (level - 1, scale / q_last). */
+tcks_status tcks_rescale(tcks_ct* ct);
+/* Drop limbs level..ell-1 in place (scale unchanged). */
+tcks_status tcks_mod_switch(tcks_ct* ct, uint32_t level);
+
+/* Negacyclic NTT (inverse = 0) or INTT (inverse = 1), in place, of `polys` polynomials of `level`
+ * limbs laid out [polys][level][N] in device memory: limb l of every polynomial is transformed
+ * modulo q_l. Forward: natural order in, bit-reversed order out, out_j = sum_i a_i
+ * psi_l^((2 brv(j) + 1) i) with psi_l the smallest primitive 2N-th root of unity mod q_l; the
+ * inverse undoes it exactly. Inputs must be canonical residues. Asynchronous on the context stream.
+ * (The transform CKKS uses for every polynomial product, implied by §2's CKKS backend.) */
+tcks_status tcks_ntt_inplace(tcks_ctx* ctx, uint64_t* d_limbs, uint32_t polys, uint32_t level, int32_t inverse);
+
+/* ------------------------------------------------------------------------------ rotations ---- */
+/* Left rotation of the N/2 slots by `step` (Galois automorphism 5^step mod 2N + key switch). */
+tcks_status tcks_rotate(const tcks_ct* a, int32_t step, tcks_ct** out);
+/* Several rotations of one ciphertext sharing one decomposition of c1 (hoisting). outs[i] receives
+ * the rotation by steps[i]; results are bit-identical to tcks_rotate. */
+tcks_status tcks_rotate_hoisted(const tcks_ct* a, const int32_t* steps, uint32_t n_steps, tcks_ct** outs);
+
+/* ----------------------------------------------------------------- composite ops (§3.1) ---- */
+/* Rotate-and-add over all N/2 slots (slots >= n must be zero): every slot receives the total.
+ * Needs Galois keys for steps 1, 2, 4, ..., N/4. */
+tcks_status tcks_sum(const tcks_ct* a, uint32_t n, tcks_ct** out);
+/* dot(a, b) = sum(mul(a, b)); dot_plain(a, w) = sum(rescale(a * encode(w))) with w (host, n values)
+ * encoded at the context scale and a's level. */
+tcks_status tcks_dot(const tcks_ct* a, const tcks_ct* b, uint32_t n, tcks_ct** out);
+tcks_status tcks_dot_plain(const tcks_ct* a, const double* w, uint32_t n, tcks_ct** out);
+
+/* Plain matrix for the vector x matrix product y = v M (M is rows x cols, rows = n inputs,
+ * cols = m outputs, m <= n, n a power of two dividing N/2), stored as its n generalised diagonals
+ * d_k[s] = M[(s+k) mod n][s] (s < m), each encoded at `level` and the context scale.
+ * From host doubles (row-major M) or from pre-encoded host limbs [n][level][N]. */
+tcks_status tcks_matrix_encode(tcks_ctx* ctx, const double* M, uint32_t rows, uint32_t cols, uint32_t level,
+                               tcks_matrix** out);
+tcks_status tcks_matrix_import(tcks_ctx* ctx, const uint64_t* diag_limbs, uint32_t rows, uint32_t cols,
+                               uint32_t level, double scale, tcks_matrix** out);
+void tcks_matrix_free(tcks_matrix* m);
+/* Encrypted vector (slots [0, n), zeros elsewhere) times plain matrix (§3.1): replicate the input
+ * over the N/2 slots with left rotations (if n < N/2), y = sum_k rot(ct, k) * d_k with hoisted
+ * rotations, then rescale. Result: y in slots [0, m), zeros elsewhere. Needs Galois keys for the
+ * replication steps N/2 - n*2^i and for steps 1..n-1. */
+tcks_status tcks_vecmat_plain(const tcks_ct* a, const tcks_matrix* M, tcks_ct** out);
+
+/* Client-side im2col (§3.2, host only, no context): windows of a kh x kw kernel sliding with
+ * `stride` over an H x W image (row-major), windows ordered row-major, taps row-major; slot
+ * t*n_windows + w receives tap t of window w (the vertical scan of the windows-as-rows matrix).
+ * Fills out_slots[0..cap) (zeros after the last tap). */
+tcks_status tcks_im2col_encode(const double* img, uint32_t H, uint32_t W, uint32_t kh, uint32_t kw, uint32_t stride,
+                               double* out_slots, size_t cap, uint32_t* n_windows);
+/* Encrypted im2col input times one plain kernel (§3.2): one multiplication by the kernel laid out
+ * as the input (slot t*windows + w = kernel[t]), rescale, then ceil(log2(taps)) left rotate-and-adds
+ * by windows*2^i. Every block of `windows` slots then holds the convolution output. */
+tcks_status tcks_conv2d_im2col(const tcks_ct* a, const double* kernel, uint32_t taps, uint32_t windows,
+                               tcks_ct** out);
+/* The same with the laid-out kernel already encoded (at the input's level). */
+tcks_status tcks_conv2d_im2col_pt(const tcks_ct* a, const tcks_pt* kernel, uint32_t taps, uint32_t windows,
+                                  tcks_ct** out);
+
+/* ------------------------------------------------------------- the encrypted CNN (§4) ---- */
+/* The MNIST-shaped network of the paper's evaluation (§4, Table 2): im2col conv with `kernels`
+ * kernels of `taps` taps over `windows` windows (§3.2), square, FC (kernels*windows) -> hidden
+ * (§3.1), square, FC hidden -> classes. Weights are host doubles: conv_w [kernels][taps], conv_b
+ * [kernels], fc1_w [hidden][kernels*windows], fc1_b [hidden], fc2_w [classes][hidden], fc2_b
+ * [classes]. All plaintexts are encoded on the device at creation: kernels at level L, channel
+ * masks at L-1, FC1 diagonals at L-3, FC2 diagonals at L-5, biases at the scales the schedule
+ * reaches from an input at the context scale. Needs L >= 7 data primes (six levels are consumed:
+ * the paper's "6 multiplications"), power-of-two FC sizes, classes <= hidden <= kernels*windows. */
+typedef struct tcks_cnn tcks_cnn;
+tcks_status tcks_cnn_create(tcks_ctx* ctx, const double* conv_w, const double* conv_b, uint32_t kernels,
+                            uint32_t taps, uint32_t windows, const double* fc1_w, const double* fc1_b, uint32_t hidden,
+                            const double* fc2_w, const double* fc2_b, uint32_t classes, tcks_cnn** out);
+void tcks_cnn_free(tcks_cnn* m);
+/* Rotation steps the forward pass uses and the level each key must cover: (steps[i], levels[i]),
+ * i < *count. With steps == NULL only *count is written. */
+tcks_status tcks_cnn_galois_steps(const tcks_cnn* m, int32_t* steps, uint32_t* levels, uint32_t cap,
+                                  uint32_t* count);
+/* One encrypted inference: input = the im2col-encoded image encrypted at level L and the context
+ * scale; output at level L-6 with the logits in slots [0, classes). */
+tcks_status tcks_cnn_forward(const tcks_cnn* m, const tcks_ct* in, tcks_ct** out);
+/* Export one of the model's encoded plaintexts (kind 0 conv kernel, 1 channel mask, 2 bias
+ * (index 0..2), 3 FC1 diagonal, 4 FC2 diagonal) to host [level][N]; level / scale are reported. */
+tcks_status tcks_cnn_export_plaintext(const tcks_cnn* m, uint32_t kind, uint32_t index, uint64_t* host,
+                                      size_t n_words, uint32_t* level, double* scale);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TCKS_H */

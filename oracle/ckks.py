@@ -584,7 +584,7 @@ def cnn_encode(o: OracleCKKS, w: CNNWeights, windows=64) -> EncodedCNN:
     return e
 
 
-def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN) -> Ct:
+def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: dict | None = None) -> Ct:
     """The encrypted CNN schedule (§4): conv (im2col, one multiplication per kernel) -> pack the
     four channel outputs with masks -> square -> FC1 (vector x plain matrix) -> square -> FC2.
     Six multiplicative levels; biases are added as plaintexts at the ciphertext's scale and level."""
@@ -598,18 +598,24 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN) -> Ct:
     bias = np.zeros(o.slots)
     for k in range(K):
         bias[k * W: (k + 1) * W] = w.conv_b[k]
+    if trace is not None:
+        trace["bias_scales"] = [v.scale]
     v = o.add_plain(v, o.encode(bias, scale=v.scale, level=v.level))
     v = o.square(v)
     n1, m1 = w.fc1_w.shape[1], w.fc1_w.shape[0]
     v = o.vecmat(v, enc.fc1, n1, m1)
     b1 = np.zeros(o.slots)
     b1[:m1] = w.fc1_b
+    if trace is not None:
+        trace["bias_scales"].append(v.scale)
     v = o.add_plain(v, o.encode(b1, scale=v.scale, level=v.level))
     v = o.square(v)
     n2, m2 = w.fc2_w.shape[1], w.fc2_w.shape[0]
     v = o.vecmat(v, enc.fc2, n2, m2)
     b2 = np.zeros(o.slots)
     b2[:m2] = w.fc2_b
+    if trace is not None:
+        trace["bias_scales"].append(v.scale)
     v = o.add_plain(v, o.encode(b2, scale=v.scale, level=v.level))
     return v
 

@@ -1,0 +1,505 @@
+"""Python binding of libtcks (include/tcks.h): RNS-CKKS encrypted-vector arithmetic on one GB300.
+
+Argument marshalling only: every step of every operation runs in the CUDA library. Each C function
+is reachable under its own name through `lib()` (e.g. `lib().tcks_add`), and the classes below wrap
+the handles (Params, Context, Ciphertext, Plaintext, Matrix) with the same operation names. There is
+no CPU fallback: if the compiled library is missing, importing the classes works but any call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libtcks.so")
+
+TCKS_AUTO_RELIN = 1
+TCKS_AUTO_RESCALE = 2
+KEY_SECRET, KEY_PUBLIC, KEY_RELIN, KEY_GALOIS = 0, 1, 2, 3
+
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_dblp = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+_vpp = ctypes.POINTER(ctypes.c_void_p)
+
+
+class TcksError(RuntimeError):
+    def __init__(self, status: int, name: str, detail: str):
+        super().__init__(f"{name} ({status}): {detail}")
+        self.status = status
+        self.name = name
+        self.detail = detail
+
+
+class _Allocator(ctypes.Structure):
+    _fields_ = [("alloc", ctypes.CFUNCTYPE(_vp, ctypes.c_size_t, _vp, _vp)),
+                ("free", ctypes.CFUNCTYPE(None, _vp, _vp, _vp)),
+                ("user", _vp)]
+
+
+# name -> (restype, argtypes); status-returning functions use c_int32
+_SIGS = {
+    "tcks_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
+    "tcks_last_error_detail": (ctypes.c_char_p, []),
+    "tcks_params_create": (ctypes.c_int32, [ctypes.c_uint32, _u32p, ctypes.c_uint32, ctypes.c_double, _vpp]),
+    "tcks_params_free": (None, [_vp]),
+    "tcks_params_primes": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32]),
+    "tcks_context_create": (ctypes.c_int32, [_vp, ctypes.c_uint64, ctypes.c_uint32, _vp, _vp, _vpp]),
+    "tcks_ctx_free": (None, [_vp]),
+    "tcks_ctx_info": (ctypes.c_int32, [_vp, _u32p, _u32p, _dblp]),
+    "tcks_ctx_key_bytes": (ctypes.c_int32, [_vp, _u64p]),
+    "tcks_ctx_synchronize": (ctypes.c_int32, [_vp]),
+    "tcks_gen_galois_keys": (ctypes.c_int32, [_vp, _i32p, ctypes.c_uint32, ctypes.c_uint32]),
+    "tcks_has_galois_key": (ctypes.c_int32, [_vp, ctypes.c_int32, _u32p]),
+    "tcks_export_key": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_int32, _u64p, ctypes.c_size_t]),
+    "tcks_import_key": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint32, _u64p,
+                                          ctypes.c_size_t]),
+    "tcks_encode": (ctypes.c_int32, [_vp, _dblp, ctypes.c_size_t, ctypes.c_double, ctypes.c_uint32, _vpp]),
+    "tcks_encode_device": (ctypes.c_int32, [_vp, _vp, ctypes.c_size_t, ctypes.c_double, ctypes.c_uint32, _vpp]),
+    "tcks_decode": (ctypes.c_int32, [_vp, _vp, _dblp, ctypes.c_size_t]),
+    "tcks_encrypt": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint64, _vpp]),
+    "tcks_decrypt": (ctypes.c_int32, [_vp, _vp, _vpp]),
+    "tcks_ct_import": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, ctypes.c_double, _vpp]),
+    "tcks_ct_export": (ctypes.c_int32, [_vp, _u64p, ctypes.c_size_t]),
+    "tcks_pt_import": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, ctypes.c_double, _vpp]),
+    "tcks_pt_export": (ctypes.c_int32, [_vp, _u64p, ctypes.c_size_t]),
+    "tcks_ct_info": (ctypes.c_int32, [_vp, _u32p, _dblp]),
+    "tcks_pt_info": (ctypes.c_int32, [_vp, _u32p, _dblp]),
+    "tcks_ct_device_ptr": (ctypes.c_int32, [_vp, ctypes.POINTER(_u64p)]),
+    "tcks_ct_free": (None, [_vp]),
+    "tcks_pt_free": (None, [_vp]),
+    "tcks_add": (ctypes.c_int32, [_vp, _vp, _vpp]),
+    "tcks_sub": (ctypes.c_int32, [_vp, _vp, _vpp]),
+    "tcks_negate": (ctypes.c_int32, [_vp, _vpp]),
+    "tcks_add_plain": (ctypes.c_int32, [_vp, _vp, _vpp]),
+    "tcks_sub_plain": (ctypes.c_int32, [_vp, _vp, _vpp]),
+    "tcks_mul_plain": (ctypes.c_int32, [_vp, _vp, _vpp]),
+    "tcks_mul": (ctypes.c_int32, [_vp, _vp, _vpp]),
+    "tcks_square": (ctypes.c_int32, [_vp, _vpp]),
+    "tcks_rescale": (ctypes.c_int32, [_vp]),
+    "tcks_mod_switch": (ctypes.c_int32, [_vp, ctypes.c_uint32]),
+    "tcks_rotate": (ctypes.c_int32, [_vp, ctypes.c_int32, _vpp]),
+    "tcks_rotate_hoisted": (ctypes.c_int32, [_vp, _i32p, ctypes.c_uint32, _vpp]),
+    "tcks_ntt_inplace": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int32]),
+    "tcks_sum": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vpp]),
+    "tcks_dot": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, _vpp]),
+    "tcks_dot_plain": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32, _vpp]),
+    "tcks_matrix_encode": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
+    "tcks_matrix_import": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                             ctypes.c_double, _vpp]),
+    "tcks_matrix_free": (None, [_vp]),
+    "tcks_vecmat_plain": (ctypes.c_int32, [_vp, _vp, _vpp]),
+    "tcks_im2col_encode": (ctypes.c_int32, [_dblp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                             ctypes.c_uint32, ctypes.c_uint32, _dblp, ctypes.c_size_t, _u32p]),
+    "tcks_conv2d_im2col": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
+    "tcks_conv2d_im2col_pt": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
+    "tcks_cnn_create": (ctypes.c_int32, [_vp, _dblp, _dblp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                          _dblp, _dblp, ctypes.c_uint32, _dblp, _dblp, ctypes.c_uint32, _vpp]),
+    "tcks_cnn_free": (None, [_vp]),
+    "tcks_cnn_galois_steps": (ctypes.c_int32, [_vp, _i32p, _u32p, ctypes.c_uint32, _u32p]),
+    "tcks_cnn_forward": (ctypes.c_int32, [_vp, _vp, _vpp]),
+    "tcks_cnn_export_plaintext": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, _u64p, ctypes.c_size_t,
+                                                    _u32p, _dblp]),
+}
+
+_lib = None
+
+
+def lib(build_if_missing: bool = False):
+    """The loaded CUDA library. Raises if it has not been built (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        if build_if_missing:
+            from .build import build
+            build()
+        else:
+            raise RuntimeError(f"libtcks.so is not built ({LIB_PATH}); run paper_2104_03152_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def check(status: int):
+    if status != 0:
+        L = lib()
+        raise TcksError(status, L.tcks_status_string(status).decode(), L.tcks_last_error_detail().decode())
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as({np.dtype(np.uint64): _u64p, np.dtype(np.float64): _dblp,
+                             np.dtype(np.uint32): _u32p, np.dtype(np.int32): _i32p}[a.dtype])
+
+
+class Params:
+    def __init__(self, log_n: int, bits, scale: float):
+        b = np.ascontiguousarray(bits, dtype=np.uint32)
+        h = _vp()
+        check(lib().tcks_params_create(log_n, _p(b), len(b), float(scale), ctypes.byref(h)))
+        self.h = h
+        self.log_n = log_n
+        self.N = 1 << log_n
+        self.bits = list(bits)
+        self.scale = float(scale)
+        q = np.zeros(len(b), dtype=np.uint64)
+        check(lib().tcks_params_primes(h, _p(q), len(q)))
+        self.primes = [int(x) for x in q]
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().tcks_params_free(self.h)
+            self.h = None
+
+
+def _torch_allocator():
+    """tcks_allocator backed by PyTorch's caching allocator (stream-ordered)."""
+    import torch
+
+    @ctypes.CFUNCTYPE(_vp, ctypes.c_size_t, _vp, _vp)
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=stream or 0)
+        except Exception:  # out of memory -> NULL, reported by the library as OUT_OF_MEMORY
+            return None
+
+    @ctypes.CFUNCTYPE(None, _vp, _vp, _vp)
+    def _free(ptr, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = _Allocator(_alloc, _free, None)
+    return a, (_alloc, _free)
+
+
+class Context:
+    """TenSEAL context (§2.1): keys on the device, auto relinearize / rescale flags."""
+
+    def __init__(self, params: Params, seed: int = 0x7E5EA1, flags: int = TCKS_AUTO_RELIN | TCKS_AUTO_RESCALE,
+                 stream: int | None = None, allocator: str = "pool"):
+        self.params = params
+        self.N = params.N
+        self.slots = params.N // 2
+        self.primes = params.primes
+        self.L = len(params.primes) - 1
+        self._alloc_keep = None
+        aptr = None
+        if allocator == "torch":
+            a, keep = _torch_allocator()
+            self._alloc_keep = (a, keep)
+            aptr = ctypes.cast(ctypes.pointer(a), _vp)
+        h = _vp()
+        check(lib().tcks_context_create(params.h, seed, flags, aptr, _vp(stream) if stream else None,
+                                        ctypes.byref(h)))
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().tcks_ctx_free(self.h)
+            self.h = None
+
+    def synchronize(self):
+        check(lib().tcks_ctx_synchronize(self.h))
+
+    def key_bytes(self) -> int:
+        v = ctypes.c_uint64()
+        check(lib().tcks_ctx_key_bytes(self.h, ctypes.byref(v)))
+        return v.value
+
+    def gen_galois_keys(self, steps, max_level: int = 0):
+        s = np.ascontiguousarray(list(steps), dtype=np.int32)
+        check(lib().tcks_gen_galois_keys(self.h, _p(s), len(s), max_level))
+
+    def galois_key_level(self, step: int) -> int | None:
+        v = ctypes.c_uint32()
+        st = lib().tcks_has_galois_key(self.h, step, ctypes.byref(v))
+        return v.value if st == 0 else None
+
+    def _key_shape(self, kind: int, step: int):
+        N, L = self.N, self.L
+        if kind == KEY_SECRET:
+            return (L + 1, N)
+        if kind == KEY_PUBLIC:
+            return (2, L, N)
+        if kind == KEY_RELIN:
+            return (L, 2, L + 1, N)
+        K = self.galois_key_level(step)
+        if K is None:
+            raise KeyError(step)
+        return (K, 2, K + 1, N)
+
+    def export_key(self, kind: int, step: int = 0) -> np.ndarray:
+        a = np.zeros(self._key_shape(kind, step), dtype=np.uint64)
+        check(lib().tcks_export_key(self.h, kind, step, _p(a), a.size))
+        return a
+
+    def import_key(self, kind: int, data: np.ndarray, step: int = 0, key_level: int = 0):
+        a = np.ascontiguousarray(data, dtype=np.uint64)
+        check(lib().tcks_import_key(self.h, kind, step, key_level, _p(a), a.size))
+
+    # encode / encrypt
+    def encode(self, v, scale: float = 0.0, level: int = 0) -> "Plaintext":
+        a = np.ascontiguousarray(v, dtype=np.float64)
+        h = _vp()
+        check(lib().tcks_encode(self.h, _p(a), len(a), float(scale), level, ctypes.byref(h)))
+        return Plaintext(self, h)
+
+    def decode(self, pt: "Plaintext", n: int | None = None) -> np.ndarray:
+        n = self.slots if n is None else n
+        out = np.zeros(n, dtype=np.float64)
+        check(lib().tcks_decode(self.h, pt.h, _p(out), n))
+        return out
+
+    def encrypt(self, pt: "Plaintext", seed: int) -> "Ciphertext":
+        h = _vp()
+        check(lib().tcks_encrypt(self.h, pt.h, seed, ctypes.byref(h)))
+        return Ciphertext(self, h)
+
+    def decrypt(self, ct: "Ciphertext") -> "Plaintext":
+        h = _vp()
+        check(lib().tcks_decrypt(self.h, ct.h, ctypes.byref(h)))
+        return Plaintext(self, h)
+
+    def encrypt_values(self, v, seed: int, level: int = 0) -> "Ciphertext":
+        return self.encrypt(self.encode(v, level=level), seed)
+
+    def decrypt_values(self, ct: "Ciphertext", n: int | None = None) -> np.ndarray:
+        return self.decode(self.decrypt(ct), n)
+
+    def ct_import(self, limbs: np.ndarray, scale: float) -> "Ciphertext":
+        a = np.ascontiguousarray(limbs, dtype=np.uint64)
+        level = a.shape[1]
+        h = _vp()
+        check(lib().tcks_ct_import(self.h, _p(a), level, float(scale), ctypes.byref(h)))
+        return Ciphertext(self, h)
+
+    def pt_import(self, limbs: np.ndarray, scale: float) -> "Plaintext":
+        a = np.ascontiguousarray(limbs, dtype=np.uint64)
+        h = _vp()
+        check(lib().tcks_pt_import(self.h, _p(a), a.shape[0], float(scale), ctypes.byref(h)))
+        return Plaintext(self, h)
+
+    def ntt_inplace(self, d_ptr: int, polys: int, level: int, inverse: bool):
+        check(lib().tcks_ntt_inplace(self.h, _vp(d_ptr), polys, level, 1 if inverse else 0))
+
+    def matrix_encode(self, M: np.ndarray, level: int = 0) -> "Matrix":
+        a = np.ascontiguousarray(M, dtype=np.float64)
+        h = _vp()
+        check(lib().tcks_matrix_encode(self.h, _p(a), a.shape[0], a.shape[1], level, ctypes.byref(h)))
+        return Matrix(self, h, a.shape[0], a.shape[1])
+
+    def matrix_import(self, diag_limbs: np.ndarray, rows: int, cols: int, scale: float) -> "Matrix":
+        a = np.ascontiguousarray(diag_limbs, dtype=np.uint64)
+        h = _vp()
+        check(lib().tcks_matrix_import(self.h, _p(a), rows, cols, a.shape[1], float(scale), ctypes.byref(h)))
+        return Matrix(self, h, rows, cols)
+
+
+def im2col_encode(img: np.ndarray, kh: int, kw: int, stride: int, cap: int):
+    """Client-side im2col (§3.2): (slot vector of length cap, number of windows)."""
+    a = np.ascontiguousarray(img, dtype=np.float64)
+    out = np.zeros(cap, dtype=np.float64)
+    w = ctypes.c_uint32()
+    check(lib().tcks_im2col_encode(_p(a), a.shape[0], a.shape[1], kh, kw, stride, _p(out), cap, ctypes.byref(w)))
+    return out, w.value
+
+
+class Plaintext:
+    def __init__(self, ctx: Context, h):
+        self.ctx = ctx
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().tcks_pt_free(self.h)
+            self.h = None
+
+    def info(self):
+        lv, sc = ctypes.c_uint32(), ctypes.c_double()
+        check(lib().tcks_pt_info(self.h, ctypes.byref(lv), ctypes.byref(sc)))
+        return lv.value, sc.value
+
+    @property
+    def level(self) -> int:
+        return self.info()[0]
+
+    @property
+    def scale(self) -> float:
+        return self.info()[1]
+
+    def export(self) -> np.ndarray:
+        a = np.zeros((self.level, self.ctx.N), dtype=np.uint64)
+        check(lib().tcks_pt_export(self.h, _p(a), a.size))
+        return a
+
+
+class Matrix:
+    def __init__(self, ctx: Context, h, rows: int, cols: int):
+        self.ctx = ctx
+        self.h = h
+        self.rows = rows
+        self.cols = cols
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().tcks_matrix_free(self.h)
+            self.h = None
+
+
+class Ciphertext:
+    """A CKKSVector: up to N/2 encrypted real slots in one ciphertext (§2.3)."""
+
+    def __init__(self, ctx: Context, h):
+        self.ctx = ctx
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().tcks_ct_free(self.h)
+            self.h = None
+
+    def info(self):
+        lv, sc = ctypes.c_uint32(), ctypes.c_double()
+        check(lib().tcks_ct_info(self.h, ctypes.byref(lv), ctypes.byref(sc)))
+        return lv.value, sc.value
+
+    @property
+    def level(self) -> int:
+        return self.info()[0]
+
+    @property
+    def scale(self) -> float:
+        return self.info()[1]
+
+    def export(self) -> np.ndarray:
+        a = np.zeros((2, self.level, self.ctx.N), dtype=np.uint64)
+        check(lib().tcks_ct_export(self.h, _p(a), a.size))
+        return a
+
+    def device_ptr(self) -> int:
+        p = _u64p()
+        check(lib().tcks_ct_device_ptr(self.h, ctypes.byref(p)))
+        return ctypes.cast(p, _vp).value
+
+    def _unary(self, fn, *args) -> "Ciphertext":
+        h = _vp()
+        check(fn(self.h, *args, ctypes.byref(h)))
+        return Ciphertext(self.ctx, h)
+
+    def add(self, o: "Ciphertext"):
+        return self._unary(lib().tcks_add, o.h)
+
+    def sub(self, o: "Ciphertext"):
+        return self._unary(lib().tcks_sub, o.h)
+
+    def negate(self):
+        return self._unary(lib().tcks_negate)
+
+    def add_plain(self, p: Plaintext):
+        return self._unary(lib().tcks_add_plain, p.h)
+
+    def sub_plain(self, p: Plaintext):
+        return self._unary(lib().tcks_sub_plain, p.h)
+
+    def mul_plain(self, p: Plaintext):
+        return self._unary(lib().tcks_mul_plain, p.h)
+
+    def mul(self, o: "Ciphertext"):
+        return self._unary(lib().tcks_mul, o.h)
+
+    def square(self):
+        return self._unary(lib().tcks_square)
+
+    def rescale_(self):
+        check(lib().tcks_rescale(self.h))
+        return self
+
+    def mod_switch_(self, level: int):
+        check(lib().tcks_mod_switch(self.h, level))
+        return self
+
+    def rotate(self, step: int):
+        return self._unary(lib().tcks_rotate, step)
+
+    def rotate_hoisted(self, steps) -> list:
+        s = np.ascontiguousarray(list(steps), dtype=np.int32)
+        outs = (_vp * len(s))()
+        check(lib().tcks_rotate_hoisted(self.h, _p(s), len(s), outs))
+        return [Ciphertext(self.ctx, _vp(outs[i])) for i in range(len(s))]
+
+    def sum(self, n: int):
+        return self._unary(lib().tcks_sum, n)
+
+    def dot(self, o: "Ciphertext", n: int):
+        return self._unary(lib().tcks_dot, o.h, n)
+
+    def dot_plain(self, w, n: int | None = None):
+        a = np.ascontiguousarray(w, dtype=np.float64)
+        return self._unary(lib().tcks_dot_plain, _p(a), len(a) if n is None else n)
+
+    def vecmat_plain(self, M: Matrix):
+        return self._unary(lib().tcks_vecmat_plain, M.h)
+
+    def conv2d_im2col(self, kernel, windows: int):
+        k = np.ascontiguousarray(kernel, dtype=np.float64).reshape(-1)
+        return self._unary(lib().tcks_conv2d_im2col, _p(k), len(k), windows)
+
+    def conv2d_im2col_pt(self, kernel: Plaintext, taps: int, windows: int):
+        return self._unary(lib().tcks_conv2d_im2col_pt, kernel.h, taps, windows)
+
+
+class CNN:
+    """The encrypted MNIST-shaped network of §4 (conv -> square -> FC -> square -> FC)."""
+
+    def __init__(self, ctx: Context, conv_w, conv_b, fc1_w, fc1_b, fc2_w, fc2_b, windows: int = 64):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (conv_w, conv_b, fc1_w, fc1_b, fc2_w, fc2_b)]
+        self._keep = arrs
+        cw, cb, w1, b1, w2, b2 = arrs
+        h = _vp()
+        check(lib().tcks_cnn_create(ctx.h, _p(cw), _p(cb), cw.shape[0], cw.shape[1], windows, _p(w1), _p(b1),
+                                    w1.shape[0], _p(w2), _p(b2), w2.shape[0], ctypes.byref(h)))
+        self.ctx = ctx
+        self.h = h
+        self.classes = w2.shape[0]
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().tcks_cnn_free(self.h)
+            self.h = None
+
+    def galois_steps(self) -> dict:
+        n = ctypes.c_uint32()
+        check(lib().tcks_cnn_galois_steps(self.h, None, None, 0, ctypes.byref(n)))
+        st = np.zeros(n.value, dtype=np.int32)
+        lv = np.zeros(n.value, dtype=np.uint32)
+        check(lib().tcks_cnn_galois_steps(self.h, _p(st), _p(lv), n.value, ctypes.byref(n)))
+        return {int(s): int(l) for s, l in zip(st, lv)}
+
+    def gen_keys(self):
+        """Galois keys for every step, each trimmed to the level it is used at."""
+        by_level = {}
+        for s, l in self.galois_steps().items():
+            by_level.setdefault(l, []).append(s)
+        for l, steps in sorted(by_level.items()):
+            self.ctx.gen_galois_keys(steps, l)
+
+    def forward(self, ct: Ciphertext) -> Ciphertext:
+        h = _vp()
+        check(lib().tcks_cnn_forward(self.h, ct.h, ctypes.byref(h)))
+        return Ciphertext(self.ctx, h)
+
+    def export_plaintext(self, kind: int, index: int):
+        lv = {0: self.ctx.L, 1: self.ctx.L - 1, 2: self.ctx.L - 2 - 2 * index, 3: self.ctx.L - 3,
+              4: self.ctx.L - 5}[kind]
+        a = np.zeros((lv, self.ctx.N), dtype=np.uint64)
+        l, sc = ctypes.c_uint32(), ctypes.c_double()
+        check(lib().tcks_cnn_export_plaintext(self.h, kind, index, _p(a), a.size, ctypes.byref(l), ctypes.byref(sc)))
+        return a, sc.value

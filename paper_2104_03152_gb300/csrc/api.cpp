@@ -1,0 +1,930 @@
+// C ABI of the library (include/tcks.h): handle management, argument checks, and the composition of
+// kernels into the CKKSVector operations of TenSEAL (§2-§3).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "context.h"
+
+using namespace tcks;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+tcks_status record(tcks_status code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+}  // namespace
+
+#define TCKS_API_BEGIN try {
+#define TCKS_API_END                                                   \
+  }                                                                    \
+  catch (const tcks::Error& e) {                                       \
+    return record(e.code, e.msg);                                      \
+  }                                                                    \
+  catch (const std::bad_alloc&) {                                      \
+    return record(TCKS_ERR_OUT_OF_MEMORY, "host allocation failed");   \
+  }                                                                    \
+  catch (const std::exception& e) {                                    \
+    return record(TCKS_ERR_INVALID_ARG, e.what());                     \
+  }                                                                    \
+  g_last_error.clear();                                                \
+  return TCKS_OK;
+
+namespace tcks {
+
+[[noreturn]] void fail(tcks_status code, const std::string& msg) { throw Error{code, msg}; }
+
+tcks_status abi_record(tcks_status code, const std::string& msg) { return record(code, msg); }
+void abi_clear() { g_last_error.clear(); }
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) fail(TCKS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void check_launch(const char* what) { check_cuda(cudaGetLastError(), what); }
+
+tcks_ct* new_ct(tcks_ctx* c, u32 level, double scale) {
+  DevBuf b(c, ct_words(c, level));
+  tcks_ct* ct = new tcks_ct{c, b.release(), level, scale};
+  return ct;
+}
+
+tcks_pt* new_pt(tcks_ctx* c, u32 level, double scale) {
+  DevBuf b(c, pt_words(c, level));
+  return new tcks_pt{c, b.release(), level, scale};
+}
+
+void free_ct(tcks_ct* ct) {
+  if (!ct) return;
+  if (ct->d) ct->ctx->dev_free(ct->d);
+  delete ct;
+}
+
+u32 step_mod(const tcks_ctx* c, int64_t step) {
+  const int64_t half = (int64_t)c->N / 2;
+  int64_t k = step % half;
+  if (k < 0) k += half;
+  return (u32)k;
+}
+
+const GaloisKey& galois_key_for(tcks_ctx* c, int64_t step, u32 ell) {
+  const u32 k = step_mod(c, step);
+  auto it = c->galois.find(k);
+  if (it == c->galois.end()) fail(TCKS_ERR_NO_GALOIS_KEY, "no Galois key for rotation step " + std::to_string(k));
+  if (it->second.K < ell)
+    fail(TCKS_ERR_LEVEL_EXHAUSTED, "Galois key for step " + std::to_string(k) + " is trimmed to level " +
+                                       std::to_string(it->second.K) + " < " + std::to_string(ell));
+  return it->second;
+}
+
+void op_rescale(tcks_ctx* c, const u64* in, u32 ell, u64* out) {
+  if (ell < 2) fail(TCKS_ERR_LEVEL_EXHAUSTED, "rescale needs level >= 2");
+  DevBuf top(c, (size_t)2 * c->N);
+  launch_rescale(c->T, in, ell, top.p, out, c->stream);
+  check_launch("rescale");
+}
+
+void op_relinearize(tcks_ctx* c, const u64* d3, u32 ell, u64* out) {
+  const size_t n = c->N;
+  DevBuf coef(c, (size_t)ell * n), digits(c, (size_t)ell * (ell + 1) * n), top(c, 2 * n);
+  launch_modup(c->T, d3 + (size_t)2 * ell * n, ell, coef.p, digits.p, c->stream);
+  KsBatch b{};
+  b.count = 1;
+  b.job[0] = KsJob{digits.p, c->rlk, out, top.p, d3, d3 + (size_t)ell * n, c->L, 1u, 0u, 0u};
+  launch_keyswitch(c->T, ell, b, c->stream);
+  check_launch("relinearize");
+}
+
+void op_rotate_hoisted(tcks_ctx* c, const u64* ct, u32 ell, const int32_t* steps, u32 n_steps, u64* const* outs) {
+  const size_t n = c->N;
+  // validate every step before launching anything
+  std::vector<const GaloisKey*> keys(n_steps, nullptr);
+  bool any = false;
+  for (u32 i = 0; i < n_steps; ++i) {
+    if (step_mod(c, steps[i]) == 0) continue;
+    keys[i] = &galois_key_for(c, steps[i], ell);
+    any = true;
+  }
+  for (u32 i = 0; i < n_steps; ++i)
+    if (!keys[i]) check_cuda(cudaMemcpyAsync(outs[i], ct, ct_words(c, ell) * 8, cudaMemcpyDeviceToDevice, c->stream),
+                             "rotate by 0");
+  if (!any) return;
+  DevBuf coef(c, (size_t)ell * n), digits(c, (size_t)ell * (ell + 1) * n);
+  DevBuf top(c, (size_t)KS_BATCH_MAX * 2 * n);
+  launch_modup(c->T, ct + (size_t)ell * n, ell, coef.p, digits.p, c->stream);
+  KsBatch b{};
+  for (u32 i = 0; i < n_steps; ++i) {
+    if (!keys[i]) continue;
+    const u32 g = (u32)galois_element(c->params.log_n, steps[i]);
+    b.job[b.count] =
+        KsJob{digits.p, keys[i]->d, outs[i], top.p + (size_t)b.count * 2 * n, ct, nullptr, keys[i]->K, g, 1u, 0u};
+    if (++b.count == KS_BATCH_MAX) {
+      launch_keyswitch(c->T, ell, b, c->stream);
+      b.count = 0;
+    }
+  }
+  launch_keyswitch(c->T, ell, b, c->stream);
+  check_launch("rotate");
+}
+
+void encode_into(tcks_ctx* c, const double* d_v, size_t n, double scale, u32 level, u64* pt_out) {
+  if (c->params.log_n > 14) fail(TCKS_ERR_UNSUPPORTED, "encoding is implemented for N <= 2^14");
+  DevBuf coeffs(c, c->N);
+  check_cuda(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "encode status");
+  launch_encode_coeffs(c->T, c->F, d_v, (u32)n, scale, (i64*)coeffs.p, c->d_status, c->stream);
+  launch_coeffs_to_ntt(c->T, (const i64*)coeffs.p, level, pt_out, c->stream);
+  check_launch("encode");
+  int status = 0;
+  check_cuda(cudaMemcpyAsync(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "encode status");
+  check_cuda(cudaStreamSynchronize(c->stream), "encode");
+  if (status) fail(TCKS_ERR_VALUE_OVERFLOW, "encode: |scale * m_i| >= 2^62");
+}
+
+}  // namespace tcks
+
+void* tcks_ctx::dev_alloc(size_t bytes) {
+  if (bytes == 0) bytes = 8;
+  void* p = nullptr;
+  if (has_alloc) {
+    p = alloc.alloc(bytes, (void*)stream, alloc.user);
+    if (!p) fail(TCKS_ERR_OUT_OF_MEMORY, "allocator callback returned NULL for " + std::to_string(bytes) + " bytes");
+    return p;
+  }
+  const cudaError_t e = cudaMallocAsync(&p, bytes, stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(TCKS_ERR_OUT_OF_MEMORY, "device allocation of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  return p;
+}
+
+void tcks_ctx::dev_free(void* p) {
+  if (!p) return;
+  if (has_alloc)
+    alloc.free(p, (void*)stream, alloc.user);
+  else
+    cudaFreeAsync(p, stream);
+}
+
+tcks::u64 tcks_ctx::key_bytes() const {
+  u64 b = 0;
+  const u64 n = N;
+  b += (u64)(L + 1) * n * 8 + (u64)2 * L * n * 8 + (u64)L * 2 * (L + 1) * n * 8;
+  for (const auto& kv : galois) b += (u64)kv.second.K * 2 * (kv.second.K + 1) * n * 8;
+  return b;
+}
+
+// =============================================================================================
+extern "C" {
+
+const char* tcks_status_string(tcks_status s) {
+  switch (s) {
+    case TCKS_OK: return "OK";
+    case TCKS_ERR_INVALID_ARG: return "INVALID_ARG";
+    case TCKS_ERR_BAD_PARAMS: return "BAD_PARAMS";
+    case TCKS_ERR_NO_GALOIS_KEY: return "NO_GALOIS_KEY";
+    case TCKS_ERR_LEVEL_EXHAUSTED: return "LEVEL_EXHAUSTED";
+    case TCKS_ERR_SCALE_MISMATCH: return "SCALE_MISMATCH";
+    case TCKS_ERR_LEVEL_MISMATCH: return "LEVEL_MISMATCH";
+    case TCKS_ERR_OUT_OF_MEMORY: return "OUT_OF_MEMORY";
+    case TCKS_ERR_BUDGET_EXCEEDED: return "BUDGET_EXCEEDED";
+    case TCKS_ERR_CUDA: return "CUDA_ERROR";
+    case TCKS_ERR_TIMEOUT: return "TIMEOUT";
+    case TCKS_ERR_VALUE_OVERFLOW: return "VALUE_OVERFLOW";
+    case TCKS_ERR_UNSUPPORTED: return "UNSUPPORTED";
+    default: return "UNKNOWN";
+  }
+}
+
+const char* tcks_last_error_detail(void) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------------------------ parameters ---
+tcks_status tcks_params_create(uint32_t log_n, const uint32_t* bit_sizes, uint32_t n_primes, double scale,
+                               tcks_params** out) {
+  TCKS_API_BEGIN
+  if (!out || !bit_sizes) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (log_n < 3 || log_n > 16) fail(TCKS_ERR_BAD_PARAMS, "log_n must be in [3, 16]");
+  if (n_primes < 2 || n_primes > CRT_MAXW - 1) fail(TCKS_ERR_BAD_PARAMS, "need 2..33 primes (data primes + P)");
+  if (!(scale > 0) || !std::isfinite(scale)) fail(TCKS_ERR_BAD_PARAMS, "scale must be positive");
+  std::vector<u64> chain;
+  if (!find_chain(log_n, bit_sizes, n_primes, chain))
+    fail(TCKS_ERR_BAD_PARAMS, "no NTT-friendly prime for some bit size (sizes must be in [20, 61])");
+  tcks_params* p = new tcks_params{log_n, std::vector<u32>(bit_sizes, bit_sizes + n_primes), chain, scale};
+  *out = p;
+  TCKS_API_END
+}
+
+void tcks_params_free(tcks_params* p) { delete p; }
+
+tcks_status tcks_params_primes(const tcks_params* p, uint64_t* primes, uint32_t capacity) {
+  TCKS_API_BEGIN
+  if (!p || !primes) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  if (capacity < p->chain.size()) fail(TCKS_ERR_INVALID_ARG, "capacity too small");
+  for (size_t i = 0; i < p->chain.size(); ++i) primes[i] = p->chain[i];
+  TCKS_API_END
+}
+
+// --------------------------------------------------------------------------------- context ---
+tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32_t flags,
+                                const tcks_allocator* allocator, void* cuda_stream, tcks_ctx** out) {
+  tcks_ctx* c = nullptr;
+  TCKS_API_BEGIN
+  if (!params || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  c = new tcks_ctx();
+  c->params = *params;
+  c->N = 1u << params->log_n;
+  c->L = (u32)params->chain.size() - 1;
+  c->flags = flags;
+  c->seed = seed;
+  check_cuda(cudaGetDevice(&c->device), "cudaGetDevice");
+  if (allocator && allocator->alloc && allocator->free) {
+    c->alloc = *allocator;
+    c->has_alloc = true;
+  }
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    check_cuda(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+    c->own_stream = true;
+  }
+  if (!c->has_alloc) {
+    // keep freed blocks in the device pool instead of returning them to the driver
+    cudaMemPool_t pool;
+    check_cuda(cudaDeviceGetDefaultMemPool(&pool, c->device), "default mem pool");
+    u64 threshold = ~0ull;
+    check_cuda(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold), "mem pool threshold");
+  }
+  if (!build_tables(params->log_n, params->chain, c->host)) fail(TCKS_ERR_BAD_PARAMS, "a prime has no 2N-th root");
+  const u32 nm = c->L + 1, n = c->N;
+  const HostTables& H = c->host;
+  c->d_mods = c->dev_alloc(sizeof(ModConst) * nm);
+  c->d_pairs = c->dev_alloc(sizeof(PairConst) * nm * nm);
+  c->d_tw = (u64*)c->dev_alloc(sizeof(u64) * H.tw.size());
+  c->d_slot = (u32*)c->dev_alloc(sizeof(u32) * H.slot_index.size());
+  c->d_zeta = (double*)c->dev_alloc(sizeof(double) * H.zeta.size());
+  c->d_status = (int*)c->dev_alloc(sizeof(int) * 4);
+  // CRT words per level: Q_l and (Q_l - 1)/2
+  std::vector<u64> qw((size_t)2 * c->L * CRT_MAXW, 0);
+  for (u32 l = 1; l <= c->L; ++l) {
+    std::vector<u64> Q(CRT_MAXW, 0);
+    Q[0] = 1;
+    for (u32 i = 0; i < l; ++i) {
+      unsigned __int128 carry = 0;
+      for (u32 w = 0; w < CRT_MAXW; ++w) {
+        const unsigned __int128 t = (unsigned __int128)Q[w] * H.chain[i] + carry;
+        Q[w] = (u64)t;
+        carry = t >> 64;
+      }
+    }
+    for (u32 w = 0; w < CRT_MAXW; ++w) {
+      qw[(size_t)(l - 1) * CRT_MAXW + w] = Q[w];
+      const u64 hi = (w + 1 < CRT_MAXW) ? Q[w + 1] : 0;
+      qw[((size_t)c->L + l - 1) * CRT_MAXW + w] = (Q[w] >> 1) | (hi << 63);  // Q odd: (Q-1)/2 = Q >> 1
+    }
+  }
+  c->d_qwords = (u64*)c->dev_alloc(sizeof(u64) * qw.size());
+  cudaStream_t s = c->stream;
+  check_cuda(cudaMemcpyAsync(c->d_mods, H.mods.data(), sizeof(ModConst) * nm, cudaMemcpyHostToDevice, s), "H2D");
+  check_cuda(cudaMemcpyAsync(c->d_pairs, H.pairs.data(), sizeof(PairConst) * nm * nm, cudaMemcpyHostToDevice, s), "H2D");
+  check_cuda(cudaMemcpyAsync(c->d_tw, H.tw.data(), sizeof(u64) * H.tw.size(), cudaMemcpyHostToDevice, s), "H2D");
+  check_cuda(cudaMemcpyAsync(c->d_slot, H.slot_index.data(), sizeof(u32) * H.slot_index.size(), cudaMemcpyHostToDevice, s), "H2D");
+  check_cuda(cudaMemcpyAsync(c->d_zeta, H.zeta.data(), sizeof(double) * H.zeta.size(), cudaMemcpyHostToDevice, s), "H2D");
+  check_cuda(cudaMemcpyAsync(c->d_qwords, qw.data(), sizeof(u64) * qw.size(), cudaMemcpyHostToDevice, s), "H2D");
+  c->table_bytes = sizeof(ModConst) * nm + sizeof(PairConst) * nm * nm + 8 * H.tw.size() + 4 * H.slot_index.size() +
+                   8 * H.zeta.size() + 8 * qw.size();
+  c->T.mods = (const ModConst*)c->d_mods;
+  c->T.pairs = (const PairConst*)c->d_pairs;
+  c->T.tw = c->d_tw;
+  c->T.log_n = params->log_n;
+  c->T.n_mods = nm;
+  c->T.L = c->L;
+  c->F.slot_index = c->d_slot;
+  c->F.zeta = c->d_zeta;
+  // keys (§2.1): secret, public, relinearization
+  c->sk = (u64*)c->dev_alloc(sizeof(u64) * (size_t)nm * n);
+  c->pk = (u64*)c->dev_alloc(sizeof(u64) * (size_t)2 * c->L * n);
+  c->rlk = (u64*)c->dev_alloc(sizeof(u64) * (size_t)c->L * 2 * nm * n);
+  launch_keygen_secret(c->T, seed, c->sk, s);
+  launch_keygen_public(c->T, seed, c->sk, c->pk, s);
+  launch_keygen_switch(c->T, seed, 0, c->sk, c->L, c->rlk, s);
+  check_launch("keygen");
+  check_cuda(cudaStreamSynchronize(s), "context create");
+  *out = c;
+  c = nullptr;
+  TCKS_API_END
+}
+
+void tcks_ctx_free(tcks_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->galois) c->dev_free(kv.second.d);
+  void* bufs[] = {c->d_mods, c->d_pairs, c->d_tw, c->d_slot, c->d_zeta, c->d_qwords, c->d_status, c->sk, c->pk, c->rlk};
+  for (void* b : bufs) c->dev_free(b);
+  cudaStreamSynchronize(c->stream);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+tcks_status tcks_ctx_info(const tcks_ctx* c, uint32_t* log_n, uint32_t* n_data_primes, double* scale) {
+  TCKS_API_BEGIN
+  if (!c) fail(TCKS_ERR_INVALID_ARG, "null context");
+  if (log_n) *log_n = c->params.log_n;
+  if (n_data_primes) *n_data_primes = c->L;
+  if (scale) *scale = c->params.scale;
+  TCKS_API_END
+}
+
+tcks_status tcks_ctx_key_bytes(const tcks_ctx* c, uint64_t* bytes) {
+  TCKS_API_BEGIN
+  if (!c || !bytes) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *bytes = c->key_bytes() + c->table_bytes;
+  TCKS_API_END
+}
+
+tcks_status tcks_ctx_synchronize(tcks_ctx* c) {
+  TCKS_API_BEGIN
+  if (!c) fail(TCKS_ERR_INVALID_ARG, "null context");
+  check_cuda(cudaStreamSynchronize(c->stream), "synchronize");
+  TCKS_API_END
+}
+
+tcks_status tcks_gen_galois_keys(tcks_ctx* c, const int32_t* steps, uint32_t n_steps, uint32_t max_level) {
+  TCKS_API_BEGIN
+  if (!c || (n_steps && !steps)) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  const u32 K = max_level == 0 ? c->L : max_level;
+  if (K > c->L) fail(TCKS_ERR_INVALID_ARG, "max_level exceeds the number of data primes");
+  for (u32 i = 0; i < n_steps; ++i) {
+    const u32 k = step_mod(c, steps[i]);
+    if (k == 0) continue;
+    auto it = c->galois.find(k);
+    if (it != c->galois.end()) {
+      c->dev_free(it->second.d);
+      c->galois.erase(it);
+    }
+    GaloisKey gk;
+    gk.K = K;
+    gk.d = (u64*)c->dev_alloc(sizeof(u64) * (size_t)K * 2 * (K + 1) * c->N);
+    launch_keygen_switch(c->T, c->seed, (u32)galois_element(c->params.log_n, k), c->sk, K, gk.d, c->stream);
+    check_launch("galois keygen");
+    c->galois[k] = gk;
+  }
+  TCKS_API_END
+}
+
+tcks_status tcks_has_galois_key(const tcks_ctx* c, int32_t step, uint32_t* key_level) {
+  TCKS_API_BEGIN
+  if (!c) fail(TCKS_ERR_INVALID_ARG, "null context");
+  auto it = c->galois.find(step_mod(c, step));
+  if (it == c->galois.end()) fail(TCKS_ERR_NO_GALOIS_KEY, "no key");
+  if (key_level) *key_level = it->second.K;
+  TCKS_API_END
+}
+
+static u64* key_slot(tcks_ctx* c, uint32_t kind, int32_t step, size_t* words, u32* K_out) {
+  const size_t n = c->N;
+  const u32 L = c->L;
+  switch (kind) {
+    case TCKS_KEY_SECRET: *words = (size_t)(L + 1) * n; return c->sk;
+    case TCKS_KEY_PUBLIC: *words = (size_t)2 * L * n; return c->pk;
+    case TCKS_KEY_RELIN: *words = (size_t)L * 2 * (L + 1) * n; return c->rlk;
+    case TCKS_KEY_GALOIS: {
+      auto it = c->galois.find(step_mod(c, step));
+      if (it == c->galois.end()) fail(TCKS_ERR_NO_GALOIS_KEY, "no Galois key for this step");
+      const u32 K = it->second.K;
+      *words = (size_t)K * 2 * (K + 1) * n;
+      if (K_out) *K_out = K;
+      return it->second.d;
+    }
+    default: fail(TCKS_ERR_INVALID_ARG, "unknown key kind");
+  }
+}
+
+tcks_status tcks_export_key(tcks_ctx* c, uint32_t kind, int32_t step, uint64_t* host, size_t n_words) {
+  TCKS_API_BEGIN
+  if (!c || !host) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  size_t words = 0;
+  u64* d = key_slot(c, kind, step, &words, nullptr);
+  if (n_words != words) fail(TCKS_ERR_INVALID_ARG, "n_words does not match the key layout");
+  check_cuda(cudaMemcpyAsync(host, d, words * 8, cudaMemcpyDeviceToHost, c->stream), "export key");
+  check_cuda(cudaStreamSynchronize(c->stream), "export key");
+  TCKS_API_END
+}
+
+tcks_status tcks_import_key(tcks_ctx* c, uint32_t kind, int32_t step, uint32_t key_level, const uint64_t* host,
+                            size_t n_words) {
+  TCKS_API_BEGIN
+  if (!c || !host) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  if (kind == TCKS_KEY_GALOIS) {
+    const u32 k = step_mod(c, step);
+    if (k == 0) fail(TCKS_ERR_INVALID_ARG, "step 0 has no key");
+    const u32 K = key_level == 0 ? c->L : key_level;
+    if (K > c->L) fail(TCKS_ERR_INVALID_ARG, "key_level exceeds L");
+    const size_t words = (size_t)K * 2 * (K + 1) * c->N;
+    if (n_words != words) fail(TCKS_ERR_INVALID_ARG, "n_words does not match the key layout");
+    auto it = c->galois.find(k);
+    if (it != c->galois.end()) {
+      c->dev_free(it->second.d);
+      c->galois.erase(it);
+    }
+    GaloisKey gk;
+    gk.K = K;
+    gk.d = (u64*)c->dev_alloc(words * 8);
+    check_cuda(cudaMemcpyAsync(gk.d, host, words * 8, cudaMemcpyHostToDevice, c->stream), "import key");
+    c->galois[k] = gk;
+  } else {
+    size_t words = 0;
+    u64* d = key_slot(c, kind, step, &words, nullptr);
+    if (n_words != words) fail(TCKS_ERR_INVALID_ARG, "n_words does not match the key layout");
+    check_cuda(cudaMemcpyAsync(d, host, words * 8, cudaMemcpyHostToDevice, c->stream), "import key");
+  }
+  check_cuda(cudaStreamSynchronize(c->stream), "import key");
+  TCKS_API_END
+}
+
+// ----------------------------------------------------------------------- encode / encrypt ----
+tcks_status tcks_encode_device(tcks_ctx* c, const double* d_v, size_t n, double scale, uint32_t level,
+                               tcks_pt** out) {
+  TCKS_API_BEGIN
+  if (!c || !out || (n && !d_v)) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (n > c->N / 2) fail(TCKS_ERR_INVALID_ARG, "more values than slots");
+  const u32 l = level == 0 ? c->L : level;
+  if (l > c->L) fail(TCKS_ERR_INVALID_ARG, "level exceeds L");
+  const double sc = scale > 0 ? scale : c->params.scale;
+  tcks_pt* pt = new_pt(c, l, sc);
+  try {
+    encode_into(c, d_v, n, sc, l, pt->d);
+  } catch (...) {
+    c->dev_free(pt->d);
+    delete pt;
+    throw;
+  }
+  *out = pt;
+  TCKS_API_END
+}
+
+tcks_status tcks_encode(tcks_ctx* c, const double* v, size_t n, double scale, uint32_t level, tcks_pt** out) {
+  TCKS_API_BEGIN
+  if (!c || !out || (n && !v)) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (n > c->N / 2) fail(TCKS_ERR_INVALID_ARG, "more values than slots");
+  DevBuf dv(c, n ? n : 1);
+  if (n) check_cuda(cudaMemcpyAsync(dv.p, v, n * 8, cudaMemcpyHostToDevice, c->stream), "encode H2D");
+  const tcks_status s = tcks_encode_device(c, (const double*)dv.p, n, scale, level, out);
+  if (s != TCKS_OK) return s;
+  TCKS_API_END
+}
+
+tcks_status tcks_decode(tcks_ctx* c, const tcks_pt* pt, double* out, size_t n) {
+  TCKS_API_BEGIN
+  if (!c || !pt || (n && !out)) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  if (n > c->N / 2) fail(TCKS_ERR_INVALID_ARG, "more values than slots");
+  if (c->params.log_n > 14) fail(TCKS_ERR_UNSUPPORTED, "decoding is implemented for N <= 2^14");
+  const size_t N = c->N;
+  DevBuf coef(c, (size_t)pt->level * N), p(c, N), z(c, n ? n : 1);
+  launch_ntt(c->T, true, pt->d, N, coef.p, N, pt->level, 0, pt->level, c->stream);
+  launch_crt_compose(c->T, coef.p, pt->level, c->d_qwords, (double*)p.p, c->stream);
+  launch_decode_slots(c->T, c->F, (const double*)p.p, pt->scale, (u32)n, (double*)z.p, c->stream);
+  check_launch("decode");
+  if (n) check_cuda(cudaMemcpyAsync(out, z.p, n * 8, cudaMemcpyDeviceToHost, c->stream), "decode D2H");
+  check_cuda(cudaStreamSynchronize(c->stream), "decode");
+  TCKS_API_END
+}
+
+tcks_status tcks_encrypt(tcks_ctx* c, const tcks_pt* pt, uint64_t seed, tcks_ct** out) {
+  TCKS_API_BEGIN
+  if (!c || !pt || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  tcks_ct* ct = new_ct(c, pt->level, pt->scale);
+  launch_encrypt(c->T, seed, c->pk, pt->d, pt->level, ct->d, c->stream);
+  check_launch("encrypt");
+  *out = ct;
+  TCKS_API_END
+}
+
+tcks_status tcks_decrypt(tcks_ctx* c, const tcks_ct* ct, tcks_pt** out) {
+  TCKS_API_BEGIN
+  if (!c || !ct || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  tcks_pt* pt = new_pt(c, ct->level, ct->scale);
+  launch_decrypt(c->T, ct->d, c->sk, pt->d, ct->level, c->stream);
+  check_launch("decrypt");
+  *out = pt;
+  TCKS_API_END
+}
+
+tcks_status tcks_ct_import(tcks_ctx* c, const uint64_t* limbs, uint32_t level, double scale, tcks_ct** out) {
+  TCKS_API_BEGIN
+  if (!c || !limbs || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (level < 1 || level > c->L) fail(TCKS_ERR_INVALID_ARG, "level out of range");
+  tcks_ct* ct = new_ct(c, level, scale);
+  check_cuda(cudaMemcpyAsync(ct->d, limbs, ct_words(c, level) * 8, cudaMemcpyHostToDevice, c->stream), "ct import");
+  check_cuda(cudaStreamSynchronize(c->stream), "ct import");
+  *out = ct;
+  TCKS_API_END
+}
+
+tcks_status tcks_ct_export(const tcks_ct* ct, uint64_t* limbs, size_t n_words) {
+  TCKS_API_BEGIN
+  if (!ct || !limbs) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  if (n_words != ct_words(ct->ctx, ct->level)) fail(TCKS_ERR_INVALID_ARG, "n_words does not match [2][level][N]");
+  check_cuda(cudaMemcpyAsync(limbs, ct->d, n_words * 8, cudaMemcpyDeviceToHost, ct->ctx->stream), "ct export");
+  check_cuda(cudaStreamSynchronize(ct->ctx->stream), "ct export");
+  TCKS_API_END
+}
+
+tcks_status tcks_pt_import(tcks_ctx* c, const uint64_t* limbs, uint32_t level, double scale, tcks_pt** out) {
+  TCKS_API_BEGIN
+  if (!c || !limbs || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (level < 1 || level > c->L) fail(TCKS_ERR_INVALID_ARG, "level out of range");
+  tcks_pt* pt = new_pt(c, level, scale);
+  check_cuda(cudaMemcpyAsync(pt->d, limbs, pt_words(c, level) * 8, cudaMemcpyHostToDevice, c->stream), "pt import");
+  check_cuda(cudaStreamSynchronize(c->stream), "pt import");
+  *out = pt;
+  TCKS_API_END
+}
+
+tcks_status tcks_pt_export(const tcks_pt* pt, uint64_t* limbs, size_t n_words) {
+  TCKS_API_BEGIN
+  if (!pt || !limbs) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  if (n_words != pt_words(pt->ctx, pt->level)) fail(TCKS_ERR_INVALID_ARG, "n_words does not match [level][N]");
+  check_cuda(cudaMemcpyAsync(limbs, pt->d, n_words * 8, cudaMemcpyDeviceToHost, pt->ctx->stream), "pt export");
+  check_cuda(cudaStreamSynchronize(pt->ctx->stream), "pt export");
+  TCKS_API_END
+}
+
+tcks_status tcks_ct_info(const tcks_ct* ct, uint32_t* level, double* scale) {
+  TCKS_API_BEGIN
+  if (!ct) fail(TCKS_ERR_INVALID_ARG, "null ciphertext");
+  if (level) *level = ct->level;
+  if (scale) *scale = ct->scale;
+  TCKS_API_END
+}
+
+tcks_status tcks_pt_info(const tcks_pt* pt, uint32_t* level, double* scale) {
+  TCKS_API_BEGIN
+  if (!pt) fail(TCKS_ERR_INVALID_ARG, "null plaintext");
+  if (level) *level = pt->level;
+  if (scale) *scale = pt->scale;
+  TCKS_API_END
+}
+
+tcks_status tcks_ct_device_ptr(const tcks_ct* ct, uint64_t** d_limbs) {
+  TCKS_API_BEGIN
+  if (!ct || !d_limbs) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *d_limbs = ct->d;
+  TCKS_API_END
+}
+
+void tcks_ct_free(tcks_ct* ct) { free_ct(ct); }
+
+void tcks_pt_free(tcks_pt* pt) {
+  if (!pt) return;
+  if (pt->d) pt->ctx->dev_free(pt->d);
+  delete pt;
+}
+
+// ------------------------------------------------------------------------ element-wise ops ----
+static void check_pair(const tcks_ct* a, const tcks_ct* b, bool need_scale) {
+  if (!a || !b) fail(TCKS_ERR_INVALID_ARG, "null ciphertext");
+  if (a->ctx != b->ctx) fail(TCKS_ERR_INVALID_ARG, "operands belong to different contexts");
+  if (a->level != b->level) fail(TCKS_ERR_LEVEL_MISMATCH, "operands at different levels");
+  if (need_scale && a->scale != b->scale) fail(TCKS_ERR_SCALE_MISMATCH, "operands at different scales");
+}
+
+static tcks_status binary_ct(const tcks_ct* a, const tcks_ct* b, u32 op, tcks_ct** out) {
+  TCKS_API_BEGIN
+  if (!out) fail(TCKS_ERR_INVALID_ARG, "null output");
+  *out = nullptr;
+  check_pair(a, b, true);
+  tcks_ctx* c = a->ctx;
+  tcks_ct* r = new_ct(c, a->level, a->scale);
+  launch_elementwise(c->T, op, a->d, b->d, r->d, a->level, 2, c->stream);
+  check_launch("elementwise");
+  *out = r;
+  TCKS_API_END
+}
+
+tcks_status tcks_add(const tcks_ct* a, const tcks_ct* b, tcks_ct** out) { return binary_ct(a, b, OP_ADD, out); }
+tcks_status tcks_sub(const tcks_ct* a, const tcks_ct* b, tcks_ct** out) { return binary_ct(a, b, OP_SUB, out); }
+
+tcks_status tcks_negate(const tcks_ct* a, tcks_ct** out) {
+  TCKS_API_BEGIN
+  if (!a || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  tcks_ct* r = new_ct(a->ctx, a->level, a->scale);
+  launch_elementwise(a->ctx->T, OP_NEG, a->d, nullptr, r->d, a->level, 2, a->ctx->stream);
+  check_launch("negate");
+  *out = r;
+  TCKS_API_END
+}
+
+static tcks_status plain_op(const tcks_ct* a, const tcks_pt* p, u32 op, tcks_ct** out) {
+  TCKS_API_BEGIN
+  if (!a || !p || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (a->ctx != p->ctx) fail(TCKS_ERR_INVALID_ARG, "operands belong to different contexts");
+  if (p->level < a->level) fail(TCKS_ERR_LEVEL_MISMATCH, "plaintext level below the ciphertext level");
+  if (op != OP_MUL_PLAIN && p->scale != a->scale) fail(TCKS_ERR_SCALE_MISMATCH, "plaintext scale differs");
+  tcks_ct* r = new_ct(a->ctx, a->level, op == OP_MUL_PLAIN ? a->scale * p->scale : a->scale);
+  launch_elementwise(a->ctx->T, op, a->d, p->d, r->d, a->level, 2, a->ctx->stream);
+  check_launch("plain op");
+  *out = r;
+  TCKS_API_END
+}
+
+tcks_status tcks_add_plain(const tcks_ct* a, const tcks_pt* p, tcks_ct** out) { return plain_op(a, p, OP_ADD_PLAIN, out); }
+tcks_status tcks_sub_plain(const tcks_ct* a, const tcks_pt* p, tcks_ct** out) { return plain_op(a, p, OP_SUB_PLAIN, out); }
+tcks_status tcks_mul_plain(const tcks_ct* a, const tcks_pt* p, tcks_ct** out) { return plain_op(a, p, OP_MUL_PLAIN, out); }
+
+tcks_status tcks_mul(const tcks_ct* a, const tcks_ct* b, tcks_ct** out) {
+  TCKS_API_BEGIN
+  if (!out) fail(TCKS_ERR_INVALID_ARG, "null output");
+  *out = nullptr;
+  check_pair(a, b, false);
+  tcks_ctx* c = a->ctx;
+  if (!(c->flags & TCKS_AUTO_RELIN))
+    fail(TCKS_ERR_UNSUPPORTED, "enc x enc without automatic relinearization has no 2-component result");
+  const u32 ell = a->level;
+  const bool rescale = (c->flags & TCKS_AUTO_RESCALE) != 0;
+  if (rescale && ell < 2) fail(TCKS_ERR_LEVEL_EXHAUSTED, "multiply with auto-rescale needs level >= 2");
+  DevBuf d3(c, (size_t)3 * ell * c->N);
+  launch_tensor(c->T, a->d, b->d, d3.p, ell, c->stream);
+  check_launch("tensor");
+  const double sc = a->scale * b->scale;
+  if (!rescale) {
+    tcks_ct* r = new_ct(c, ell, sc);
+    op_relinearize(c, d3.p, ell, r->d);
+    *out = r;
+  } else {
+    DevBuf rel(c, ct_words(c, ell));
+    op_relinearize(c, d3.p, ell, rel.p);
+    tcks_ct* r = new_ct(c, ell - 1, sc / (double)c->host.chain[ell - 1]);
+    op_rescale(c, rel.p, ell, r->d);
+    *out = r;
+  }
+  TCKS_API_END
+}
+
+tcks_status tcks_square(const tcks_ct* a, tcks_ct** out) { return tcks_mul(a, a, out); }
+
+tcks_status tcks_rescale(tcks_ct* ct) {
+  TCKS_API_BEGIN
+  if (!ct) fail(TCKS_ERR_INVALID_ARG, "null ciphertext");
+  tcks_ctx* c = ct->ctx;
+  if (ct->level < 2) fail(TCKS_ERR_LEVEL_EXHAUSTED, "rescale needs level >= 2");
+  DevBuf nb(c, ct_words(c, ct->level - 1));
+  op_rescale(c, ct->d, ct->level, nb.p);
+  c->dev_free(ct->d);
+  ct->d = nb.release();
+  ct->scale = ct->scale / (double)c->host.chain[ct->level - 1];
+  ct->level -= 1;
+  TCKS_API_END
+}
+
+tcks_status tcks_mod_switch(tcks_ct* ct, uint32_t level) {
+  TCKS_API_BEGIN
+  if (!ct) fail(TCKS_ERR_INVALID_ARG, "null ciphertext");
+  if (level < 1 || level > ct->level) fail(TCKS_ERR_INVALID_ARG, "target level out of range");
+  if (level == ct->level) return TCKS_OK;
+  tcks_ctx* c = ct->ctx;
+  DevBuf nb(c, ct_words(c, level));
+  const size_t n = c->N;
+  check_cuda(cudaMemcpy2DAsync(nb.p, (size_t)level * n * 8, ct->d, (size_t)ct->level * n * 8, (size_t)level * n * 8, 2,
+                               cudaMemcpyDeviceToDevice, c->stream),
+             "mod switch");
+  c->dev_free(ct->d);
+  ct->d = nb.release();
+  ct->level = level;
+  TCKS_API_END
+}
+
+tcks_status tcks_ntt_inplace(tcks_ctx* c, uint64_t* d_limbs, uint32_t polys, uint32_t level, int32_t inverse) {
+  TCKS_API_BEGIN
+  if (!c || !d_limbs) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  if (level < 1 || level > c->L + 1) fail(TCKS_ERR_INVALID_ARG, "level out of range");
+  if (c->params.log_n > 14) fail(TCKS_ERR_UNSUPPORTED, "single-pass transforms are implemented for N <= 2^14");
+  const u64 n = c->N;
+  launch_ntt(c->T, inverse != 0, d_limbs, n, d_limbs, n, polys * level, 0, level, c->stream);
+  check_launch("ntt");
+  TCKS_API_END
+}
+
+// ------------------------------------------------------------------------------- rotations ----
+tcks_status tcks_rotate(const tcks_ct* a, int32_t step, tcks_ct** out) { return tcks_rotate_hoisted(a, &step, 1, out); }
+
+tcks_status tcks_rotate_hoisted(const tcks_ct* a, const int32_t* steps, uint32_t n_steps, tcks_ct** outs) {
+  std::vector<tcks_ct*> made;
+  TCKS_API_BEGIN
+  if (!a || !outs || (n_steps && !steps)) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  for (u32 i = 0; i < n_steps; ++i) outs[i] = nullptr;
+  tcks_ctx* c = a->ctx;
+  for (u32 i = 0; i < n_steps; ++i)
+    if (step_mod(c, steps[i])) galois_key_for(c, steps[i], a->level);  // validate first
+  std::vector<u64*> ptrs(n_steps);
+  for (u32 i = 0; i < n_steps; ++i) {
+    made.push_back(new_ct(c, a->level, a->scale));
+    ptrs[i] = made.back()->d;
+  }
+  op_rotate_hoisted(c, a->d, a->level, steps, n_steps, ptrs.data());
+  for (u32 i = 0; i < n_steps; ++i) outs[i] = made[i];
+  made.clear();
+  return TCKS_OK;
+  }
+  catch (const tcks::Error& e) {
+    for (tcks_ct* m : made) free_ct(m);
+    return record(e.code, e.msg);
+  }
+  catch (const std::bad_alloc&) {
+    for (tcks_ct* m : made) free_ct(m);
+    return record(TCKS_ERR_OUT_OF_MEMORY, "host allocation failed");
+  }
+}
+
+// --------------------------------------------------------------------------- composites ----
+tcks_status tcks_sum(const tcks_ct* a, uint32_t n, tcks_ct** out) {
+  TCKS_API_BEGIN
+  if (!a || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  tcks_ctx* c = a->ctx;
+  if (n > c->N / 2) fail(TCKS_ERR_INVALID_ARG, "n exceeds the slot count");
+  for (u32 m = 0; m + 1 < c->params.log_n; ++m) galois_key_for(c, (int32_t)(1u << m), a->level);
+  tcks_ct* r = new_ct(c, a->level, a->scale);
+  check_cuda(cudaMemcpyAsync(r->d, a->d, ct_words(c, a->level) * 8, cudaMemcpyDeviceToDevice, c->stream), "sum copy");
+  try {
+    op_sum(c, r->d, r->level);
+  } catch (...) {
+    free_ct(r);
+    throw;
+  }
+  *out = r;
+  TCKS_API_END
+}
+
+tcks_status tcks_dot(const tcks_ct* a, const tcks_ct* b, uint32_t n, tcks_ct** out) {
+  TCKS_API_BEGIN
+  if (!out) fail(TCKS_ERR_INVALID_ARG, "null output");
+  *out = nullptr;
+  tcks_ct* prod = nullptr;
+  tcks_status s = tcks_mul(a, b, &prod);
+  if (s != TCKS_OK) return s;
+  s = tcks_sum(prod, n, out);
+  free_ct(prod);
+  if (s != TCKS_OK) return s;
+  TCKS_API_END
+}
+
+tcks_status tcks_dot_plain(const tcks_ct* a, const double* w, uint32_t n, tcks_ct** out) {
+  TCKS_API_BEGIN
+  if (!a || !w || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  tcks_pt* p = nullptr;
+  tcks_status s = tcks_encode(a->ctx, w, n, 0.0, a->level, &p);
+  if (s != TCKS_OK) return s;
+  tcks_ct* prod = nullptr;
+  s = tcks_mul_plain(a, p, &prod);
+  tcks_pt_free(p);
+  if (s != TCKS_OK) return s;
+  s = tcks_rescale(prod);
+  if (s == TCKS_OK) s = tcks_sum(prod, n, out);
+  free_ct(prod);
+  if (s != TCKS_OK) return s;
+  TCKS_API_END
+}
+
+tcks_status tcks_matrix_encode(tcks_ctx* c, const double* M, uint32_t rows, uint32_t cols, uint32_t level,
+                               tcks_matrix** out) {
+  TCKS_API_BEGIN
+  if (!c || !M || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  const u32 slots = c->N / 2;
+  if (rows == 0 || cols == 0 || cols > rows || rows > slots || (rows & (rows - 1)) || slots % rows)
+    fail(TCKS_ERR_INVALID_ARG, "need cols <= rows, rows a power of two dividing N/2");
+  const u32 l = level == 0 ? c->L : level;
+  if (l < 2 || l > c->L) fail(TCKS_ERR_INVALID_ARG, "level out of range (needs >= 2 for the rescale)");
+  DevBuf d(c, (size_t)rows * l * c->N);
+  DevBuf dv(c, slots);
+  std::vector<double> diag(slots);
+  for (u32 k = 0; k < rows; ++k) {
+    std::fill(diag.begin(), diag.end(), 0.0);
+    for (u32 s2 = 0; s2 < cols; ++s2) diag[s2] = M[(size_t)((s2 + k) % rows) * cols + s2];
+    check_cuda(cudaMemcpyAsync(dv.p, diag.data(), (size_t)slots * 8, cudaMemcpyHostToDevice, c->stream), "diag H2D");
+    encode_into(c, (const double*)dv.p, slots, c->params.scale, l, d.p + (size_t)k * l * c->N);
+  }
+  *out = new tcks_matrix{c, rows, cols, l, c->params.scale, d.release()};
+  TCKS_API_END
+}
+
+tcks_status tcks_matrix_import(tcks_ctx* c, const uint64_t* diag_limbs, uint32_t rows, uint32_t cols, uint32_t level,
+                               double scale, tcks_matrix** out) {
+  TCKS_API_BEGIN
+  if (!c || !diag_limbs || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  const u32 slots = c->N / 2;
+  if (rows == 0 || cols == 0 || cols > rows || rows > slots || (rows & (rows - 1)) || slots % rows)
+    fail(TCKS_ERR_INVALID_ARG, "need cols <= rows, rows a power of two dividing N/2");
+  if (level < 2 || level > c->L) fail(TCKS_ERR_INVALID_ARG, "level out of range");
+  const size_t words = (size_t)rows * level * c->N;
+  DevBuf d(c, words);
+  check_cuda(cudaMemcpyAsync(d.p, diag_limbs, words * 8, cudaMemcpyHostToDevice, c->stream), "matrix import");
+  check_cuda(cudaStreamSynchronize(c->stream), "matrix import");
+  *out = new tcks_matrix{c, rows, cols, level, scale, d.release()};
+  TCKS_API_END
+}
+
+void tcks_matrix_free(tcks_matrix* m) {
+  if (!m) return;
+  m->ctx->dev_free(m->d);
+  delete m;
+}
+
+tcks_status tcks_vecmat_plain(const tcks_ct* a, const tcks_matrix* M, tcks_ct** out) {
+  TCKS_API_BEGIN
+  if (!a || !M || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  tcks_ctx* c = a->ctx;
+  if (M->ctx != c) fail(TCKS_ERR_INVALID_ARG, "matrix belongs to another context");
+  if (M->level < a->level) fail(TCKS_ERR_LEVEL_MISMATCH, "matrix encoded below the ciphertext level");
+  if (a->level < 2) fail(TCKS_ERR_LEVEL_EXHAUSTED, "vecmat needs level >= 2");
+  tcks_ct* r = new_ct(c, a->level - 1, a->scale * M->scale / (double)c->host.chain[a->level - 1]);
+  try {
+    op_vecmat(c, a->d, a->level, M, r->d);
+  } catch (...) {
+    free_ct(r);
+    throw;
+  }
+  *out = r;
+  TCKS_API_END
+}
+
+tcks_status tcks_im2col_encode(const double* img, uint32_t H, uint32_t W, uint32_t kh, uint32_t kw, uint32_t stride,
+                               double* out_slots, size_t cap, uint32_t* n_windows) {
+  TCKS_API_BEGIN
+  if (!img || !out_slots || !n_windows) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  if (kh == 0 || kw == 0 || stride == 0 || kh > H || kw > W) fail(TCKS_ERR_INVALID_ARG, "bad kernel geometry");
+  const u32 oh = (H - kh) / stride + 1, ow = (W - kw) / stride + 1;
+  const u64 windows = (u64)oh * ow, taps = (u64)kh * kw;
+  if (windows * taps > cap) fail(TCKS_ERR_INVALID_ARG, "output capacity too small for windows * taps");
+  for (size_t i = 0; i < cap; ++i) out_slots[i] = 0.0;
+  for (u32 r = 0; r < oh; ++r)
+    for (u32 cc = 0; cc < ow; ++cc) {
+      const u64 w = (u64)r * ow + cc;
+      for (u64 t = 0; t < taps; ++t)
+        out_slots[t * windows + w] = img[(size_t)(stride * r + t / kw) * W + (stride * cc + t % kw)];
+    }
+  *n_windows = (uint32_t)windows;
+  TCKS_API_END
+}
+
+tcks_status tcks_conv2d_im2col_pt(const tcks_ct* a, const tcks_pt* kernel, uint32_t taps, uint32_t windows,
+                                  tcks_ct** out) {
+  TCKS_API_BEGIN
+  if (!a || !kernel || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  tcks_ctx* c = a->ctx;
+  if (kernel->ctx != c) fail(TCKS_ERR_INVALID_ARG, "kernel belongs to another context");
+  if (kernel->level < a->level) fail(TCKS_ERR_LEVEL_MISMATCH, "kernel encoded below the ciphertext level");
+  if (a->level < 2) fail(TCKS_ERR_LEVEL_EXHAUSTED, "conv needs level >= 2");
+  if (taps == 0 || windows == 0 || (u64)windows * taps > c->N / 2) fail(TCKS_ERR_INVALID_ARG, "bad conv geometry");
+  tcks_ct* r = new_ct(c, a->level - 1, a->scale * kernel->scale / (double)c->host.chain[a->level - 1]);
+  try {
+    op_conv(c, a->d, a->level, kernel->d, taps, windows, r->d);
+  } catch (...) {
+    free_ct(r);
+    throw;
+  }
+  *out = r;
+  TCKS_API_END
+}
+
+tcks_status tcks_conv2d_im2col(const tcks_ct* a, const double* kernel, uint32_t taps, uint32_t windows,
+                               tcks_ct** out) {
+  TCKS_API_BEGIN
+  if (!a || !kernel || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  tcks_ctx* c = a->ctx;
+  const u32 slots = c->N / 2;
+  if (taps == 0 || windows == 0 || (u64)windows * taps > slots) fail(TCKS_ERR_INVALID_ARG, "bad conv geometry");
+  std::vector<double> lay(slots, 0.0);
+  for (u32 t = 0; t < taps; ++t)
+    for (u32 w = 0; w < windows; ++w) lay[(size_t)t * windows + w] = kernel[t];
+  tcks_pt* p = nullptr;
+  tcks_status s = tcks_encode(c, lay.data(), slots, 0.0, a->level, &p);
+  if (s != TCKS_OK) return s;
+  s = tcks_conv2d_im2col_pt(a, p, taps, windows, out);
+  tcks_pt_free(p);
+  if (s != TCKS_OK) return s;
+  TCKS_API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,343 @@
+// The encrypted MNIST-shaped CNN of the paper's evaluation (§4, Table 2): conv (4 kernels 7x7,
+// stride 3, im2col, §3.2) -> square -> FC 256->64 (§3.1) -> square -> FC 64->10, six multiplicative
+// levels, on one CKKSVector.
+//
+// Schedule (levels in brackets, L = input level):
+//   conv: per kernel k, rescale(ct * kernel_k) [L-1], then log2(taps) left rotate-and-adds by
+//         windows * 2^i — the four channels rotate together, one key-switch launch per step;
+//   pack: v = sum_k rescale(conv_k * mask_k) [L-2], mask_k = 1 on slots [k*W, (k+1)*W); + conv bias;
+//   square: rescale(relin(v * v)) [L-3];
+//   FC1: vector x plain matrix (replicate, hoisted diagonal method, rescale) [L-4]; + bias;
+//   square [L-5]; FC2 [L-6]; + bias. Logits sit in slots [0, classes).
+// Biases are encoded once, at the scales the schedule reaches from an input at the context scale
+// (the same double operations the forward pass performs), so the forward pass needs no encoding.
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "context.h"
+
+using namespace tcks;
+
+struct tcks_cnn {
+  tcks_ctx* ctx;
+  u32 kernels, taps, windows, hidden, classes;
+  u32 L;                     // input level
+  double in_scale;           // expected input scale
+  std::vector<u64*> conv;    // per kernel, [L][N]
+  std::vector<u64*> masks;   // per kernel, [L-1][N]
+  u64* bias[3];              // [L-2], [L-4], [L-6]
+  double bias_scale[3];
+  tcks_matrix* fc1;          // level L-3
+  tcks_matrix* fc2;          // level L-5
+  double out_scale;
+};
+
+namespace tcks {
+
+// ct_i <- ct_i + rot(ct_i, step) for `count` ciphertexts at once: one ModUp per ciphertext, one
+// key-switch launch for all of them.
+static void rotate_add_many(tcks_ctx* c, u64* const* cts, u32 count, u32 ell, int32_t step) {
+  const size_t n = c->N;
+  const GaloisKey& gk = galois_key_for(c, step, ell);
+  const u32 g = (u32)galois_element(c->params.log_n, step);
+  DevBuf coef(c, (size_t)ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
+  DevBuf tmp(c, (size_t)count * ct_words(c, ell)), top(c, (size_t)count * 2 * n);
+  KsBatch b{};
+  for (u32 i = 0; i < count; ++i) {
+    u64* d = digits.p + (size_t)i * ell * (ell + 1) * n;
+    launch_modup(c->T, cts[i] + (size_t)ell * n, ell, coef.p, d, c->stream);
+    b.job[b.count++] = KsJob{d, gk.d, tmp.p + (size_t)i * ct_words(c, ell), top.p + (size_t)i * 2 * n, cts[i],
+                             nullptr, gk.K, g, 1u, 0u};
+  }
+  launch_keyswitch(c->T, ell, b, c->stream);
+  for (u32 i = 0; i < count; ++i)
+    launch_elementwise(c->T, OP_ADD, cts[i], tmp.p + (size_t)i * ct_words(c, ell), cts[i], ell, 2, c->stream);
+  check_launch("rotate-add batch");
+}
+
+static int ceil_log2(u32 x) {
+  int r = 0;
+  while ((1u << r) < x) ++r;
+  return r;
+}
+
+// Scale after each stage, from the input scale (identical double operations to the forward pass).
+static void schedule_scales(const tcks_cnn* m, double s_in, double delta, double* s_pack, double* s_fc1,
+                            double* s_fc2) {
+  const std::vector<u64>& q = m->ctx->host.chain;
+  const u32 L = m->L;
+  double s = s_in * delta / (double)q[L - 1];  // conv: mul_plain + rescale
+  s = s * delta / (double)q[L - 2];             // pack: mul_plain(mask) + rescale
+  *s_pack = s;
+  s = s * s / (double)q[L - 3];                 // square
+  s = s * m->fc1->scale / (double)q[L - 4];     // FC1
+  *s_fc1 = s;
+  s = s * s / (double)q[L - 5];                 // square
+  s = s * m->fc2->scale / (double)q[L - 6];     // FC2
+  *s_fc2 = s;
+}
+
+static void cnn_forward_dev(const tcks_cnn* m, const u64* in, u64* out) {
+  tcks_ctx* c = m->ctx;
+  const size_t n = c->N;
+  const u32 L = m->L, K = m->kernels;
+  // conv [L-1]
+  std::vector<DevBuf> chans;
+  std::vector<u64*> cp;
+  {
+    DevBuf prod(c, ct_words(c, L));
+    for (u32 k = 0; k < K; ++k) {
+      chans.emplace_back(c, ct_words(c, L - 1));
+      launch_elementwise(c->T, OP_MUL_PLAIN, in, m->conv[k], prod.p, L, 2, c->stream);
+      op_rescale(c, prod.p, L, chans.back().p);
+      cp.push_back(chans.back().p);
+    }
+  }
+  const int rsteps = ceil_log2(m->taps);
+  for (int i = 0; i < rsteps; ++i) rotate_add_many(c, cp.data(), K, L - 1, (int32_t)(m->windows << i));
+  // pack [L-2] + bias
+  DevBuf v(c, ct_words(c, L - 2));
+  {
+    DevBuf prod(c, ct_words(c, L - 1)), t(c, ct_words(c, L - 2));
+    for (u32 k = 0; k < K; ++k) {
+      launch_elementwise(c->T, OP_MUL_PLAIN, cp[k], m->masks[k], prod.p, L - 1, 2, c->stream);
+      op_rescale(c, prod.p, L - 1, k == 0 ? v.p : t.p);
+      if (k) launch_elementwise(c->T, OP_ADD, v.p, t.p, v.p, L - 2, 2, c->stream);
+    }
+    launch_elementwise(c->T, OP_ADD_PLAIN, v.p, m->bias[0], v.p, L - 2, 2, c->stream);
+  }
+  chans.clear();
+  // square [L-3]
+  DevBuf sq1(c, ct_words(c, L - 3));
+  {
+    DevBuf d3(c, (size_t)3 * (L - 2) * n), rel(c, ct_words(c, L - 2));
+    launch_tensor(c->T, v.p, v.p, d3.p, L - 2, c->stream);
+    op_relinearize(c, d3.p, L - 2, rel.p);
+    op_rescale(c, rel.p, L - 2, sq1.p);
+  }
+  // FC1 [L-4] + bias
+  DevBuf f1(c, ct_words(c, L - 4));
+  op_vecmat(c, sq1.p, L - 3, m->fc1, f1.p);
+  launch_elementwise(c->T, OP_ADD_PLAIN, f1.p, m->bias[1], f1.p, L - 4, 2, c->stream);
+  // square [L-5]
+  DevBuf sq2(c, ct_words(c, L - 5));
+  {
+    DevBuf d3(c, (size_t)3 * (L - 4) * n), rel(c, ct_words(c, L - 4));
+    launch_tensor(c->T, f1.p, f1.p, d3.p, L - 4, c->stream);
+    op_relinearize(c, d3.p, L - 4, rel.p);
+    op_rescale(c, rel.p, L - 4, sq2.p);
+  }
+  // FC2 [L-6] + bias
+  op_vecmat(c, sq2.p, L - 5, m->fc2, out);
+  launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[2], out, L - 6, 2, c->stream);
+  check_launch("cnn forward");
+}
+
+}  // namespace tcks
+
+// The ABI wrappers share api.cpp's error channel through these two helpers.
+namespace tcks {
+tcks_status abi_record(tcks_status code, const std::string& msg);
+void abi_clear();
+}  // namespace tcks
+
+#define CNN_BEGIN try {
+#define CNN_END                                                       \
+  }                                                                   \
+  catch (const tcks::Error& e) {                                      \
+    return tcks::abi_record(e.code, e.msg);                           \
+  }                                                                   \
+  catch (const std::bad_alloc&) {                                     \
+    return tcks::abi_record(TCKS_ERR_OUT_OF_MEMORY, "host allocation failed"); \
+  }                                                                   \
+  tcks::abi_clear();                                                  \
+  return TCKS_OK;
+
+extern "C" {
+
+void tcks_cnn_free(tcks_cnn* m) {
+  if (!m) return;
+  tcks_ctx* c = m->ctx;
+  for (u64* p : m->conv) c->dev_free(p);
+  for (u64* p : m->masks) c->dev_free(p);
+  for (u64* p : m->bias) c->dev_free(p);
+  tcks_matrix_free(m->fc1);
+  tcks_matrix_free(m->fc2);
+  delete m;
+}
+
+tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* conv_b, uint32_t kernels, uint32_t taps,
+                            uint32_t windows, const double* fc1_w, const double* fc1_b, uint32_t hidden,
+                            const double* fc2_w, const double* fc2_b, uint32_t classes, tcks_cnn** out) {
+  struct Guard {  // frees a partly built model when creation fails
+    tcks_cnn* m = nullptr;
+    ~Guard() { tcks_cnn_free(m); }
+  } guard;
+  tcks_cnn*& m = guard.m;
+  CNN_BEGIN
+  if (!c || !conv_w || !conv_b || !fc1_w || !fc1_b || !fc2_w || !fc2_b || !out)
+    fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  const u32 slots = c->N / 2, L = c->L;
+  if (L < 7) fail(TCKS_ERR_BAD_PARAMS, "the network needs at least 7 data primes (6 levels + 1)");
+  if (!kernels || !taps || !windows || (u64)taps * windows > slots || (u64)kernels * windows > slots)
+    fail(TCKS_ERR_INVALID_ARG, "bad conv geometry");
+  const u32 n1 = kernels * windows;
+  if ((n1 & (n1 - 1)) || (hidden & (hidden - 1)) || hidden > n1 || classes > hidden || slots % n1)
+    fail(TCKS_ERR_INVALID_ARG, "FC sizes must be powers of two with classes <= hidden <= kernels*windows");
+  m = new tcks_cnn();
+  m->ctx = c;
+  m->kernels = kernels;
+  m->taps = taps;
+  m->windows = windows;
+  m->hidden = hidden;
+  m->classes = classes;
+  m->L = L;
+  m->in_scale = c->params.scale;
+  m->bias[0] = m->bias[1] = m->bias[2] = nullptr;
+  m->fc1 = m->fc2 = nullptr;
+  const double delta = c->params.scale;
+  std::vector<double> lay(slots);
+  DevBuf dv(c, slots);
+  auto encode_host = [&](const std::vector<double>& v, double scale, u32 level) -> u64* {
+    DevBuf p(c, (size_t)level * c->N);
+    check_cuda(cudaMemcpyAsync(dv.p, v.data(), (size_t)slots * 8, cudaMemcpyHostToDevice, c->stream), "H2D");
+    encode_into(c, (const double*)dv.p, slots, scale, level, p.p);
+    return p.release();
+  };
+  for (u32 k = 0; k < kernels; ++k) {
+    std::fill(lay.begin(), lay.end(), 0.0);
+    for (u32 t = 0; t < taps; ++t)
+      for (u32 w = 0; w < windows; ++w) lay[(size_t)t * windows + w] = conv_w[(size_t)k * taps + t];
+    m->conv.push_back(encode_host(lay, delta, L));
+    std::fill(lay.begin(), lay.end(), 0.0);
+    for (u32 w = 0; w < windows; ++w) lay[(size_t)k * windows + w] = 1.0;
+    m->masks.push_back(encode_host(lay, delta, L - 1));
+  }
+  // FC weights W [out][in] act as M = W^T [in][out]
+  std::vector<double> M1((size_t)n1 * hidden), M2((size_t)hidden * classes);
+  for (u32 i = 0; i < n1; ++i)
+    for (u32 o = 0; o < hidden; ++o) M1[(size_t)i * hidden + o] = fc1_w[(size_t)o * n1 + i];
+  for (u32 i = 0; i < hidden; ++i)
+    for (u32 o = 0; o < classes; ++o) M2[(size_t)i * classes + o] = fc2_w[(size_t)o * hidden + i];
+  tcks_status st = tcks_matrix_encode(c, M1.data(), n1, hidden, L - 3, &m->fc1);
+  if (st != TCKS_OK) fail(st, tcks_last_error_detail());
+  st = tcks_matrix_encode(c, M2.data(), hidden, classes, L - 5, &m->fc2);
+  if (st != TCKS_OK) fail(st, tcks_last_error_detail());
+  double s_pack, s_fc1, s_fc2;
+  schedule_scales(m, m->in_scale, delta, &s_pack, &s_fc1, &s_fc2);
+  m->bias_scale[0] = s_pack;
+  m->bias_scale[1] = s_fc1;
+  m->bias_scale[2] = s_fc2;
+  m->out_scale = s_fc2;
+  std::fill(lay.begin(), lay.end(), 0.0);
+  for (u32 k = 0; k < kernels; ++k)
+    for (u32 w = 0; w < windows; ++w) lay[(size_t)k * windows + w] = conv_b[k];
+  m->bias[0] = encode_host(lay, s_pack, L - 2);
+  std::fill(lay.begin(), lay.end(), 0.0);
+  for (u32 o = 0; o < hidden; ++o) lay[o] = fc1_b[o];
+  m->bias[1] = encode_host(lay, s_fc1, L - 4);
+  std::fill(lay.begin(), lay.end(), 0.0);
+  for (u32 o = 0; o < classes; ++o) lay[o] = fc2_b[o];
+  m->bias[2] = encode_host(lay, s_fc2, L - 6);
+  *out = m;
+  m = nullptr;
+  CNN_END
+}
+
+// Galois steps the forward pass needs, with the level each must reach (for key trimming):
+// writes up to `cap` (step, level) pairs and the count.
+tcks_status tcks_cnn_galois_steps(const tcks_cnn* m, int32_t* steps, uint32_t* levels, uint32_t cap,
+                                  uint32_t* count) {
+  CNN_BEGIN
+  if (!m || !count) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  const u32 slots = m->ctx->N / 2, L = m->L;
+  std::vector<std::pair<u32, u32>> need;  // (step, level)
+  auto use = [&](u32 s, u32 lv) {
+    s %= slots;
+    if (!s) return;
+    for (auto& p : need)
+      if (p.first == s) {
+        if (lv > p.second) p.second = lv;
+        return;
+      }
+    need.push_back({s, lv});
+  };
+  for (int i = 0; i < ceil_log2(m->taps); ++i) use(m->windows << i, L - 1);
+  const u32 n1 = m->kernels * m->windows, n2 = m->hidden;
+  for (u32 r = 0; ((u64)n1 << r) < slots; ++r) use(slots - (n1 << r), L - 3);
+  for (u32 k = 1; k < n1; ++k) use(k, L - 3);
+  for (u32 r = 0; ((u64)n2 << r) < slots; ++r) use(slots - (n2 << r), L - 5);
+  for (u32 k = 1; k < n2; ++k) use(k, L - 5);
+  *count = (u32)need.size();
+  if (steps && levels) {
+    if (cap < need.size()) fail(TCKS_ERR_INVALID_ARG, "capacity too small");
+    for (size_t i = 0; i < need.size(); ++i) {
+      steps[i] = (int32_t)need[i].first;
+      levels[i] = need[i].second;
+    }
+  }
+  CNN_END
+}
+
+tcks_status tcks_cnn_forward(const tcks_cnn* m, const tcks_ct* in, tcks_ct** out) {
+  CNN_BEGIN
+  if (!m || !in || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  tcks_ctx* c = m->ctx;
+  if (in->ctx != c) fail(TCKS_ERR_INVALID_ARG, "ciphertext belongs to another context");
+  if (in->level != m->L) fail(TCKS_ERR_LEVEL_MISMATCH, "the network takes a ciphertext at the top level");
+  if (in->scale != m->in_scale) fail(TCKS_ERR_SCALE_MISMATCH, "the network takes a ciphertext at the context scale");
+  tcks_ct* r = new_ct(c, m->L - 6, m->out_scale);
+  try {
+    cnn_forward_dev(m, in->d, r->d);
+  } catch (...) {
+    free_ct(r);
+    throw;
+  }
+  *out = r;
+  CNN_END
+}
+
+// Plaintexts of the model for inspection: kind 0 conv kernel, 1 mask (index = kernel), 2 bias
+// (index 0..2), 3 FC1 diagonal, 4 FC2 diagonal (index = diagonal); host [level][N].
+tcks_status tcks_cnn_export_plaintext(const tcks_cnn* m, uint32_t kind, uint32_t index, uint64_t* host,
+                                      size_t n_words, uint32_t* level, double* scale) {
+  CNN_BEGIN
+  if (!m || !host) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  tcks_ctx* c = m->ctx;
+  const u64* src = nullptr;
+  u32 lv = 0;
+  double sc = 0;
+  switch (kind) {
+    case 0:
+      if (index >= m->kernels) fail(TCKS_ERR_INVALID_ARG, "index");
+      src = m->conv[index], lv = m->L, sc = c->params.scale;
+      break;
+    case 1:
+      if (index >= m->kernels) fail(TCKS_ERR_INVALID_ARG, "index");
+      src = m->masks[index], lv = m->L - 1, sc = c->params.scale;
+      break;
+    case 2:
+      if (index >= 3) fail(TCKS_ERR_INVALID_ARG, "index");
+      src = m->bias[index], lv = m->L - 2 - 2 * index, sc = m->bias_scale[index];
+      break;
+    case 3:
+    case 4: {
+      const tcks_matrix* M = kind == 3 ? m->fc1 : m->fc2;
+      if (index >= M->rows) fail(TCKS_ERR_INVALID_ARG, "index");
+      src = M->d + (size_t)index * M->level * c->N, lv = M->level, sc = M->scale;
+      break;
+    }
+    default: fail(TCKS_ERR_INVALID_ARG, "kind");
+  }
+  if (n_words != (size_t)lv * c->N) fail(TCKS_ERR_INVALID_ARG, "n_words does not match [level][N]");
+  check_cuda(cudaMemcpyAsync(host, src, n_words * 8, cudaMemcpyDeviceToHost, c->stream), "export");
+  check_cuda(cudaStreamSynchronize(c->stream), "export");
+  if (level) *level = lv;
+  if (scale) *scale = sc;
+  CNN_END
+}
+
+}  // extern "C"

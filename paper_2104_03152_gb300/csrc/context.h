@@ -1,0 +1,136 @@
+// Internal definitions of the ABI's opaque handles and shared host helpers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/tcks.h"
+#include "kernels.h"
+#include "params.h"
+
+struct tcks_params {
+  tcks::u32 log_n;
+  std::vector<tcks::u32> bits;
+  std::vector<tcks::u64> chain;  // data primes then P
+  double scale;
+};
+
+namespace tcks {
+
+struct GaloisKey {
+  u64* d = nullptr;
+  u32 K = 0;
+};
+
+// Status with message, raised by internal helpers and turned into a return code at the ABI.
+struct Error {
+  tcks_status code;
+  std::string msg;
+};
+
+}  // namespace tcks
+
+struct tcks_ctx {
+  tcks_params params;
+  tcks::HostTables host;
+  tcks::DevTables T{};
+  tcks::FftTables F{};
+  tcks::u32 N = 0, L = 0;
+  // device tables
+  void* d_mods = nullptr;
+  void* d_pairs = nullptr;
+  tcks::u64* d_tw = nullptr;
+  tcks::u32* d_slot = nullptr;
+  double* d_zeta = nullptr;
+  tcks::u64* d_qwords = nullptr;
+  int* d_status = nullptr;
+  // execution
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  tcks_allocator alloc{};
+  bool has_alloc = false;
+  tcks::u32 flags = 0;
+  tcks::u64 seed = 0;
+  int device = 0;
+  // keys
+  tcks::u64* sk = nullptr;   // [L+1][N]
+  tcks::u64* pk = nullptr;   // [2][L][N]
+  tcks::u64* rlk = nullptr;  // [L][2][L+1][N]
+  std::map<tcks::u32, tcks::GaloisKey> galois;  // step mod N/2 -> key
+  tcks::u64 table_bytes = 0;
+
+  void* dev_alloc(size_t bytes);
+  void dev_free(void* p);
+  tcks::u64 key_bytes() const;
+};
+
+struct tcks_ct {
+  tcks_ctx* ctx;
+  tcks::u64* d;  // [2][level][N]
+  tcks::u32 level;
+  double scale;
+};
+
+struct tcks_pt {
+  tcks_ctx* ctx;
+  tcks::u64* d;  // [level][N]
+  tcks::u32 level;
+  double scale;
+};
+
+struct tcks_matrix {
+  tcks_ctx* ctx;
+  tcks::u32 rows, cols, level;
+  double scale;
+  tcks::u64* d;  // [rows][level][N] encoded diagonals
+};
+
+namespace tcks {
+
+// Device buffer owned by a context, released (stream-ordered) when it goes out of scope.
+struct DevBuf {
+  tcks_ctx* ctx = nullptr;
+  u64* p = nullptr;
+  DevBuf() = default;
+  DevBuf(tcks_ctx* c, size_t words) : ctx(c), p((u64*)c->dev_alloc(words * sizeof(u64))) {}
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : ctx(o.ctx), p(o.p) { o.p = nullptr; }
+  ~DevBuf() {
+    if (p) ctx->dev_free(p);
+  }
+  u64* release() {
+    u64* r = p;
+    p = nullptr;
+    return r;
+  }
+};
+
+void check_cuda(cudaError_t e, const char* what);
+void check_launch(const char* what);
+[[noreturn]] void fail(tcks_status code, const std::string& msg);
+
+inline size_t ct_words(const tcks_ctx* c, u32 level) { return (size_t)2 * level * c->N; }
+inline size_t pt_words(const tcks_ctx* c, u32 level) { return (size_t)level * c->N; }
+
+tcks_ct* new_ct(tcks_ctx* c, u32 level, double scale);  // uninitialised limbs
+tcks_pt* new_pt(tcks_ctx* c, u32 level, double scale);
+void free_ct(tcks_ct* ct);
+
+// Internal ops on device buffers (results written to caller-provided buffers).
+void op_rescale(tcks_ctx* c, const u64* in, u32 ell, u64* out);
+// Relinearize [3][ell][N] -> [2][ell][N].
+void op_relinearize(tcks_ctx* c, const u64* d3, u32 ell, u64* out);
+// Rotations of one ciphertext from shared digits: outs[i] = rot(ct, steps[i]) (each [2][ell][N]).
+void op_rotate_hoisted(tcks_ctx* c, const u64* ct, u32 ell, const int32_t* steps, u32 n, u64* const* outs);
+const GaloisKey& galois_key_for(tcks_ctx* c, int64_t step, u32 ell);
+u32 step_mod(const tcks_ctx* c, int64_t step);
+void encode_into(tcks_ctx* c, const double* d_v, size_t n, double scale, u32 level, u64* pt_out);
+// composite.cpp
+void op_sum(tcks_ctx* c, u64* ct, u32 ell);  // in place
+void op_vecmat(tcks_ctx* c, const u64* ct, u32 ell, const tcks_matrix* M, u64* out);  // out at ell - 1
+void op_conv(tcks_ctx* c, const u64* ct, u32 ell, const u64* kernel_pt, u32 taps, u32 windows, u64* out);
+
+}  // namespace tcks

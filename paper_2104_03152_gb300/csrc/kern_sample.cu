@@ -1,0 +1,187 @@
+// Key generation and public-key encryption on the device, driven by a counter-based generator so
+// that every coefficient is drawn independently of launch shape: Philox4x64-10 (Salmon et al.,
+// SC'11) with key = (seed, stream tag) and counter = (coefficient index, chain index of the limb,
+// 0, 0). Draws: uniform residue = (w1:w0) mod q, ternary = (w0 mod 3) - 1, centred binomial
+// error (eta = 21) = popcount(w0 & (2^21-1)) - popcount((w0 >> 21) & (2^21-1)).
+// Stream tags: 1 s, 2 pk.a, 3 pk.e, 4 enc.u, 5 enc.e0, 6 enc.e1; switching key of kind `kind`
+// (0 = relinearization, else the Galois element) digit j: a -> (kind<<32)|0x80000000|2j,
+// e -> the same | 1.
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+#include "ntt.cuh"
+
+namespace tcks {
+
+namespace {
+
+struct Philox4 {
+  u64 w[4];
+};
+
+__device__ __forceinline__ Philox4 philox(u64 seed, u64 tag, u64 index, u64 limb) {
+  u64 c0 = index, c1 = limb, c2 = 0, c3 = 0;
+  u64 k0 = seed, k1 = tag;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const u64 lo0 = 0xD2E7470EE14C6C93ull * c0, hi0 = __umul64hi(0xD2E7470EE14C6C93ull, c0);
+    const u64 lo1 = 0xCA5A826395121157ull * c2, hi1 = __umul64hi(0xCA5A826395121157ull, c2);
+    const u64 n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B97F4A7C15ull;
+    k1 += 0xBB67AE8584CAA73Bull;
+  }
+  Philox4 o;
+  o.w[0] = c0;
+  o.w[1] = c1;
+  o.w[2] = c2;
+  o.w[3] = c3;
+  return o;
+}
+
+__device__ __forceinline__ u64 draw_uniform(u64 seed, u64 tag, u64 index, u64 limb, const ModConst& m) {
+  const Philox4 r = philox(seed, tag, index, limb);
+  return reduce128(r.w[1], r.w[0], m);
+}
+
+__device__ __forceinline__ int draw_ternary(u64 seed, u64 tag, u64 index) {
+  return (int)(philox(seed, tag, index, 0).w[0] % 3ull) - 1;
+}
+
+__device__ __forceinline__ int draw_cbd(u64 seed, u64 tag, u64 index) {
+  const u64 w = philox(seed, tag, index, 0).w[0];
+  return __popcll(w & 0x1FFFFFull) - __popcll((w >> 21) & 0x1FFFFFull);
+}
+
+__device__ __forceinline__ u64 small_to_residue(int v, u64 q) { return v >= 0 ? (u64)v : q - (u64)(-v); }
+
+enum : u32 { SMALL_TERNARY = 0, SMALL_CBD = 1 };
+
+// Fill s[] with a small polynomial (ternary / CBD) reduced mod the chain prime, NTT it in place;
+// on return s holds values in [0, 4q).
+__device__ __forceinline__ void small_ntt(u64* s, const DevTables& T, u32 mod, u32 kind, u64 seed, u64 tag) {
+  const u32 n = 1u << T.log_n;
+  const u64 q = T.mods[mod].q;
+  for (u32 k = threadIdx.x; k < n; k += blockDim.x) {
+    const int v = kind == SMALL_TERNARY ? draw_ternary(seed, tag, k) : draw_cbd(seed, tag, k);
+    s[k] = small_to_residue(v, q);
+  }
+  __syncthreads();
+  ntt_fwd_smem(s, T, mod);
+}
+
+// Limb slot -> chain index when a layout holds `count` data limbs followed by P.
+__device__ __forceinline__ u32 slot_chain(u32 slot, u32 count, u32 L) { return slot < count ? slot : L; }
+
+}  // namespace
+
+// s: [L+1][N], one CTA per limb.
+__global__ void k_keygen_secret(DevTables T, u64 seed, u64* __restrict__ s_out) {
+  extern __shared__ u64 s[];
+  const u32 n = 1u << T.log_n;
+  const u32 mod = blockIdx.x;  // 0..L (L is P)
+  small_ntt(s, T, mod, SMALL_TERNARY, seed, 1);
+  const u64 q = T.mods[mod].q;
+  for (u32 k = threadIdx.x; k < n; k += blockDim.x) s_out[(u64)mod * n + k] = fwd_final(s[k], q);
+}
+
+// pk: [2][L][N]; pk0 = -a*s + e, pk1 = a.
+__global__ void k_keygen_public(DevTables T, u64 seed, const u64* __restrict__ sk, u64* __restrict__ pk) {
+  extern __shared__ u64 s[];
+  const u32 n = 1u << T.log_n;
+  const u32 l = blockIdx.x;
+  const ModConst m = T.mods[l];
+  small_ntt(s, T, l, SMALL_CBD, seed, 3);
+  for (u32 k = threadIdx.x; k < n; k += blockDim.x) {
+    const u64 a = draw_uniform(seed, 2, k, l, m);
+    const u64 e = fwd_final(s[k], m.q);
+    pk[(u64)l * n + k] = add_mod(neg_mod(mul_mod(a, sk[(u64)l * n + k], m), m.q), e, m.q);
+    pk[((u64)T.L + l) * n + k] = a;
+  }
+}
+
+// Switching key of level K: [K][2][K+1][N]; CTA per (digit j, slot).
+//   b_j[slot] = -a*s + e + [chain(slot) == j] * (P mod q_j) * s'
+__global__ void k_keygen_switch(DevTables T, u64 seed, u32 kind, const u64* __restrict__ sk, u32 K,
+                                u64* __restrict__ ksk) {
+  extern __shared__ u64 s[];
+  const u32 log_n = T.log_n, n = 1u << log_n;
+  const u32 j = blockIdx.x / (K + 1), slot = blockIdx.x % (K + 1);
+  const u32 l = slot_chain(slot, K, T.L);
+  const ModConst m = T.mods[l];
+  const u64 tag_a = ((u64)kind << 32) | 0x80000000ull | (2ull * j);
+  const u64 tag_e = tag_a | 1ull;
+  small_ntt(s, T, l, SMALL_CBD, seed, tag_e);
+  const u64 gadget = (l == j) ? T.pairs[(u64)T.L * T.n_mods + l].qa_mod_b : 0;  // P mod q_j
+  const u64* s_l = sk + (u64)l * n;
+  u64* b0 = ksk + (((u64)j * 2 + 0) * (K + 1) + slot) * n;
+  u64* b1 = ksk + (((u64)j * 2 + 1) * (K + 1) + slot) * n;
+  for (u32 k = threadIdx.x; k < n; k += blockDim.x) {
+    const u64 a = draw_uniform(seed, tag_a, k, l, m);
+    u64 v = add_mod(neg_mod(mul_mod(a, s_l[k], m), m.q), fwd_final(s[k], m.q), m.q);
+    if (gadget) {
+      const u64 sp = kind == 0 ? mul_mod(s_l[k], s_l[k], m) : s_l[galois_src(k, kind, log_n)];
+      v = add_mod(v, mul_mod(gadget, sp, m), m.q);
+    }
+    b0[k] = v;
+    b1[k] = a;
+  }
+}
+
+// Encryption at level ell, CTA per limb: c0 = u*pk0 + e0 + m, c1 = u*pk1 + e1.
+__global__ void k_encrypt(DevTables T, u64 seed, const u64* __restrict__ pk, const u64* __restrict__ pt, u32 ell,
+                          u64* __restrict__ out) {
+  extern __shared__ u64 s[];
+  const u32 n = 1u << T.log_n;
+  const u32 l = blockIdx.x;
+  const ModConst m = T.mods[l];
+  u64* c0 = out + (u64)l * n;
+  u64* c1 = out + ((u64)ell + l) * n;
+  small_ntt(s, T, l, SMALL_TERNARY, seed, 4);
+  for (u32 k = threadIdx.x; k < n; k += blockDim.x) {
+    const u64 u = fwd_final(s[k], m.q);
+    c0[k] = add_mod(mul_mod(u, pk[(u64)l * n + k], m), pt[(u64)l * n + k], m.q);
+    c1[k] = mul_mod(u, pk[((u64)T.L + l) * n + k], m);
+  }
+  __syncthreads();
+  small_ntt(s, T, l, SMALL_CBD, seed, 5);
+  for (u32 k = threadIdx.x; k < n; k += blockDim.x) c0[k] = add_mod(c0[k], fwd_final(s[k], m.q), m.q);
+  __syncthreads();
+  small_ntt(s, T, l, SMALL_CBD, seed, 6);
+  for (u32 k = threadIdx.x; k < n; k += blockDim.x) c1[k] = add_mod(c1[k], fwd_final(s[k], m.q), m.q);
+}
+
+static size_t smem_bytes(u32 log_n) { return ((size_t)8) << log_n; }
+template <typename K>
+static void allow_smem(K kernel, size_t bytes) {
+  ensure_smem((const void*)kernel, bytes);
+}
+
+void launch_keygen_secret(const DevTables& T, u64 seed, u64* s, cudaStream_t st) {
+  const size_t sm = smem_bytes(T.log_n);
+  allow_smem(k_keygen_secret, sm);
+  k_keygen_secret<<<T.L + 1, ntt_threads(T.log_n), sm, st>>>(T, seed, s);
+}
+
+void launch_keygen_public(const DevTables& T, u64 seed, const u64* s, u64* pk, cudaStream_t st) {
+  const size_t sm = smem_bytes(T.log_n);
+  allow_smem(k_keygen_public, sm);
+  k_keygen_public<<<T.L, ntt_threads(T.log_n), sm, st>>>(T, seed, s, pk);
+}
+
+void launch_keygen_switch(const DevTables& T, u64 seed, u32 kind, const u64* s, u32 K, u64* ksk, cudaStream_t st) {
+  const size_t sm = smem_bytes(T.log_n);
+  allow_smem(k_keygen_switch, sm);
+  k_keygen_switch<<<K * (K + 1), ntt_threads(T.log_n), sm, st>>>(T, seed, kind, s, K, ksk);
+}
+
+void launch_encrypt(const DevTables& T, u64 seed, const u64* pk, const u64* pt, u32 ell, u64* out, cudaStream_t st) {
+  const size_t sm = smem_bytes(T.log_n);
+  allow_smem(k_encrypt, sm);
+  k_encrypt<<<ell, ntt_threads(T.log_n), sm, st>>>(T, seed, pk, pt, ell, out);
+}
+
+}  // namespace tcks

@@ -1,0 +1,83 @@
+// Host-side launch wrappers of the library's kernels (one translation unit per kernel family).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "tcks_types.h"
+
+namespace tcks {
+
+// ---- kern_core.cu
+u32 ntt_threads(u32 log_n);
+// Raise a kernel's dynamic shared-memory limit to `bytes` (no-op at or below 48 KB).
+void ensure_smem(const void* kernel, size_t bytes);
+// count jobs: src + b*src_stride -> dst + b*dst_stride (may alias for in place), prime
+// mod_base + b % mod_period.
+void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_stride, u64* dst, u64 dst_stride,
+                u32 count, u32 mod_base, u32 mod_period, cudaStream_t st);
+enum : u32 { OP_ADD = 0, OP_SUB = 1, OP_NEG = 2, OP_MUL_PLAIN = 3, OP_ADD_PLAIN = 4, OP_SUB_PLAIN = 5 };
+void launch_elementwise(const DevTables& T, u32 op, const u64* a, const u64* b, u64* out, u32 ell, u32 polys,
+                        cudaStream_t st);
+void launch_tensor(const DevTables& T, const u64* a, const u64* b, u64* out, u32 ell, cudaStream_t st);
+void launch_decrypt(const DevTables& T, const u64* ct, const u64* s, u64* pt, u32 ell, cudaStream_t st);
+// ct [2][ell][N] -> out [2][ell-1][N]; top_tmp: [2][N] scratch.
+void launch_rescale(const DevTables& T, const u64* ct, u32 ell, u64* top_tmp, u64* out, cudaStream_t st);
+// x_ntt [ell][N] -> digits [ell][ell+1][N]; x_coef_tmp: [ell][N] scratch.
+void launch_modup(const DevTables& T, const u64* x_ntt, u32 ell, u64* x_coef_tmp, u64* digits, cudaStream_t st);
+
+// One key switch of hoisted digits: automorphism g (1 = none), key of level K, output [2][ell][N],
+// scratch top [2][N], optional addends per output component (read through the automorphism when
+// add_perm is set).
+struct KsJob {
+  const u64* digits;  // [ell][ell+1][N]
+  const u64* key;
+  u64* out;
+  u64* top;
+  const u64* add0;
+  const u64* add1;
+  u32 K;
+  u32 g;
+  u32 add_perm;
+  u32 pad;
+};
+constexpr u32 KS_BATCH_MAX = 64;
+struct KsBatch {
+  KsJob job[KS_BATCH_MAX];
+  u32 count;
+};
+void launch_keyswitch(const DevTables& T, u32 ell, const KsBatch& jobs, cudaStream_t st);
+// acc[2][ell][N] += sum_c rots[c] * diag[c] (c < count), rots[c] = rots + c * rot_stride,
+// diag[c] = diag + c * diag_stride (each diag has >= ell limbs).
+void launch_mulacc(const DevTables& T, u64* acc, const u64* rots, u64 rot_stride, const u64* diag, u64 diag_stride,
+                   u32 count, u32 ell, cudaStream_t st);
+
+// ---- kern_sample.cu (Philox4x64-10 sampler; key = (seed, tag), counter = (index, limb, 0, 0))
+// Secret key: ternary, NTT form over the data primes and P: out [L+1][N].
+void launch_keygen_secret(const DevTables& T, u64 seed, u64* s, cudaStream_t st);
+// Public key (-a*s + e, a) over the L data primes: out [2][L][N].
+void launch_keygen_public(const DevTables& T, u64 seed, const u64* s, u64* pk, cudaStream_t st);
+// Switching key of level K from s' to s: kind 0 = relinearization (s' = s^2), otherwise the Galois
+// element g (s' = tau_g(s)); out [K][2][K+1][N].
+void launch_keygen_switch(const DevTables& T, u64 seed, u32 kind, const u64* s, u32 K, u64* ksk, cudaStream_t st);
+// Public-key encryption at level ell: out [2][ell][N]; scratch none.
+void launch_encrypt(const DevTables& T, u64 seed, const u64* pk, const u64* pt, u32 ell, u64* out, cudaStream_t st);
+
+// ---- kern_fft.cu (FP64 canonical embedding)
+struct FftTables {
+  const u32* slot_index;  // [N/2]
+  const double* zeta;     // [2N][2]
+};
+// n_in device doubles -> integer coefficients (int64 [N]) at `scale`; *d_status = 1 on overflow.
+void launch_encode_coeffs(const DevTables& T, const FftTables& F, const double* d_z, u32 n_in, double scale,
+                          i64* d_coeffs, int* d_status, cudaStream_t st);
+// int64 coefficients -> NTT-form plaintext [ell][N].
+void launch_coeffs_to_ntt(const DevTables& T, const i64* d_coeffs, u32 ell, u64* pt, cudaStream_t st);
+// Coefficient-domain residues [ell][N] -> centred integers as doubles [N] (exact CRT, correctly
+// rounded); q_words: [L][MAXW] products Q_l and [L][MAXW] (Q_l - 1)/2 per level.
+constexpr u32 CRT_MAXW = 34;
+void launch_crt_compose(const DevTables& T, const u64* coef, u32 ell, const u64* d_qwords, double* out,
+                        cudaStream_t st);
+// p [N] doubles -> slot values [n_out].
+void launch_decode_slots(const DevTables& T, const FftTables& F, const double* p, double scale, u32 n_out,
+                         double* out, cudaStream_t st);
+
+}  // namespace tcks

@@ -1,0 +1,200 @@
+// Host parameter layer of the GPU library: the modulus chain, roots of unity and the constant
+// tables the kernels read. Independent of the CPU oracle (no shared source).
+//
+// Prime chain: for each requested bit size b in order, the largest prime q < 2^b with
+// q == 1 (mod 2N), q > 2^(b-1), not already in the chain (so that a 2N-th root of unity exists
+// and the negacyclic NTT of size N is defined modulo q). Root: the smallest primitive 2N-th root.
+#include "params.h"
+
+#include <cmath>
+#include <cstring>
+
+namespace tcks {
+
+namespace {
+
+typedef unsigned __int128 u128;
+
+inline u64 mulmod_h(u64 a, u64 b, u64 m) { return (u64)((u128)a * b % m); }
+
+u64 powmod_h(u64 base, u64 exp, u64 m) {
+  u64 result = 1 % m, x = base % m;
+  for (; exp; exp >>= 1, x = mulmod_h(x, x, m))
+    if (exp & 1) result = mulmod_h(result, x, m);
+  return result;
+}
+
+// Strong-probable-prime test to base a (n odd, n > a).
+bool sprp(u64 n, u64 a) {
+  u64 d = n - 1;
+  unsigned r = 0;
+  while (!(d & 1)) {
+    d >>= 1;
+    ++r;
+  }
+  u64 y = powmod_h(a, d, n);
+  if (y == 1 || y == n - 1) return true;
+  while (--r) {
+    y = mulmod_h(y, y, n);
+    if (y == n - 1) return true;
+    if (y == 1) return false;
+  }
+  return false;
+}
+
+u32 reverse_bits(u32 v, u32 width) {
+  u32 out = 0;
+  for (u32 b = 0; b < width; ++b, v >>= 1) out = (out << 1) | (v & 1u);
+  return out;
+}
+
+}  // namespace
+
+bool is_prime_u64(u64 n) {
+  const u64 small[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+  if (n < 2) return false;
+  for (u64 p : small) {
+    if (n == p) return true;
+    if (n % p == 0) return false;
+  }
+  for (u64 a : small)
+    if (!sprp(n, a)) return false;
+  return true;  // the twelve bases are deterministic below 3.3e24
+}
+
+bool find_chain(u32 log_n, const u32* bits, u32 count, std::vector<u64>& chain) {
+  chain.clear();
+  const u64 step = 2ull << log_n;
+  for (u32 k = 0; k < count; ++k) {
+    const u32 b = bits[k];
+    if (b < 20 || b > 61) return false;
+    const u64 hi = 1ull << b, lo = 1ull << (b - 1);
+    // candidates are 1 + step * t below 2^b, scanned downward
+    u64 t = (hi - 2) / step;
+    bool ok = false;
+    for (; t > 0; --t) {
+      const u64 c = 1 + step * t;
+      if (c <= lo) break;
+      bool dup = false;
+      for (u64 x : chain) dup |= (x == c);
+      if (!dup && is_prime_u64(c)) {
+        chain.push_back(c);
+        ok = true;
+        break;
+      }
+    }
+    if (!ok) return false;
+  }
+  return true;
+}
+
+u64 smallest_psi(u64 q, u32 log_n) {
+  const u64 n = 1ull << log_n, order = 2 * n;
+  if ((q - 1) % order) return 0;
+  // A primitive 2N-th root: g^((q-1)/2N) for a g whose power has order exactly 2N (its N-th power is -1).
+  u64 root = 0;
+  for (u64 g = 2; g < q && !root; ++g) {
+    const u64 c = powmod_h(g, (q - 1) / order, q);
+    if (powmod_h(c, n, q) == q - 1) root = c;
+  }
+  if (!root) return 0;
+  // The primitive 2N-th roots are exactly root^k for odd k < 2N; take the least of them.
+  const u64 r2 = mulmod_h(root, root, q);
+  u64 best = root;
+  u64 v = root;
+  for (u64 k = 1; k < n; ++k) {
+    v = mulmod_h(v, r2, q);
+    best = v < best ? v : best;
+  }
+  return best;
+}
+
+u64 invmod_h(u64 a, u64 q) { return powmod_h(a, q - 2, q); }
+
+u64 shoup_of(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+
+bool build_tables(u32 log_n, const std::vector<u64>& chain, HostTables& out) {
+  const u32 nm = (u32)chain.size();
+  const u64 n = 1ull << log_n;
+  out.log_n = log_n;
+  out.chain = chain;
+  out.psi.resize(nm);
+  out.mods.resize(nm);
+  out.pairs.resize((size_t)nm * nm);
+  out.tw.assign((size_t)nm * 4 * n, 0);
+  for (u32 i = 0; i < nm; ++i) {
+    const u64 q = chain[i];
+    const u64 psi = smallest_psi(q, log_n);
+    if (!psi) return false;
+    out.psi[i] = psi;
+    ModConst& m = out.mods[i];
+    std::memset(&m, 0, sizeof(m));
+    m.q = q;
+    m.mu64 = (u64)(~(u128)0 >> 64) / q;  // floor((2^64 - 1) / q) = floor(2^64 / q) for odd q > 1
+    const u128 mu = (~(u128)0) / q;       // floor((2^128 - 1) / q) = floor(2^128 / q)
+    m.mu_hi = (u64)(mu >> 64);
+    m.mu_lo = (u64)mu;
+    m.ninv = invmod_h(n % q, q);
+    m.ninv_sh = shoup_of(m.ninv, q);
+    m.half = (q - 1) / 2;
+    // twiddles: psi^brv(k) and psi^-brv(k) with Shoup companions
+    u64* t0 = &out.tw[((size_t)i * 4 + 0) * n];
+    u64* t1 = &out.tw[((size_t)i * 4 + 1) * n];
+    u64* t2 = &out.tw[((size_t)i * 4 + 2) * n];
+    u64* t3 = &out.tw[((size_t)i * 4 + 3) * n];
+    const u64 ipsi = invmod_h(psi, q);
+    std::vector<u64> pw(n), ipw(n);
+    pw[0] = 1;
+    ipw[0] = 1;
+    for (u64 k = 1; k < n; ++k) {
+      pw[k] = mulmod_h(pw[k - 1], psi, q);
+      ipw[k] = mulmod_h(ipw[k - 1], ipsi, q);
+    }
+    for (u64 k = 0; k < n; ++k) {
+      const u32 r = reverse_bits((u32)k, log_n);
+      t0[k] = pw[r];
+      t1[k] = shoup_of(pw[r], q);
+      t2[k] = ipw[r];
+      t3[k] = shoup_of(ipw[r], q);
+    }
+  }
+  for (u32 a = 0; a < nm; ++a)
+    for (u32 b = 0; b < nm; ++b) {
+      PairConst& p = out.pairs[(size_t)a * nm + b];
+      std::memset(&p, 0, sizeof(p));
+      p.qa_mod_b = chain[a] % chain[b];
+      if (a != b) {
+        p.inv_qa = invmod_h(p.qa_mod_b, chain[b]);
+        p.inv_qa_sh = shoup_of(p.inv_qa, chain[b]);
+      }
+    }
+  // rotation group: slot j sits at DFT index (5^j mod 2N - 1) / 4 of the size-N/2 transform
+  const u64 slots = n / 2;
+  out.slot_index.resize(slots);
+  u64 g = 1;
+  for (u64 j = 0; j < slots; ++j) {
+    out.slot_index[j] = (u32)((g - 1) / 4);
+    g = (g * 5) & (2 * n - 1);
+  }
+  // zeta^k = exp(i pi k / N), k < 2N (FP64), as interleaved (re, im)
+  out.zeta.resize(4 * n);
+  for (u64 k = 0; k < 2 * n; ++k) {
+    const double ang = M_PI * (double)k / (double)n;
+    out.zeta[2 * k] = std::cos(ang);
+    out.zeta[2 * k + 1] = std::sin(ang);
+  }
+  return true;
+}
+
+u64 galois_element(u32 log_n, int64_t step) {
+  const int64_t half = (int64_t)1 << (log_n - 1);
+  int64_t k = step % half;
+  if (k < 0) k += half;
+  const u64 mask = (2ull << log_n) - 1;
+  u64 g = 1, base = 5;
+  for (u64 e = (u64)k; e; e >>= 1, base = (base * base) & mask)
+    if (e & 1) g = (g * base) & mask;
+  return g;
+}
+
+}  // namespace tcks

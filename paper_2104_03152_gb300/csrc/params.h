@@ -1,0 +1,30 @@
+// Host parameter layer: modulus chain, roots, constant tables (see params.cpp).
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "tcks_types.h"
+
+namespace tcks {
+
+struct HostTables {
+  u32 log_n = 0;
+  std::vector<u64> chain;        // data primes then P
+  std::vector<u64> psi;          // smallest primitive 2N-th root per prime
+  std::vector<ModConst> mods;    // per prime
+  std::vector<PairConst> pairs;  // [a][b]
+  std::vector<u64> tw;           // [prime][4][N]
+  std::vector<u32> slot_index;   // slot j -> (5^j mod 2N - 1)/4, j < N/2
+  std::vector<double> zeta;      // exp(i pi k / N), k < 2N, interleaved (re, im)
+};
+
+bool is_prime_u64(u64 n);
+bool find_chain(u32 log_n, const u32* bits, u32 count, std::vector<u64>& chain);
+u64 smallest_psi(u64 q, u32 log_n);
+u64 invmod_h(u64 a, u64 q);
+u64 shoup_of(u64 w, u64 q);
+bool build_tables(u32 log_n, const std::vector<u64>& chain, HostTables& out);
+// 5^step mod 2N with step taken modulo N/2 (left rotation by `step` slots).
+u64 galois_element(u32 log_n, int64_t step);
+
+}  // namespace tcks

@@ -1,0 +1,41 @@
+// Types shared by the library's host code and its kernels.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+namespace tcks {
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+typedef int64_t i64;
+
+// Per-prime constants (device copy indexed by chain position; P sits at index L).
+struct ModConst {
+  u64 q;
+  u64 mu64;          // floor(2^64 / q)
+  u64 mu_hi, mu_lo;  // floor(2^128 / q)
+  u64 ninv, ninv_sh; // N^-1 mod q and its Shoup companion
+  u64 half;          // (q - 1) / 2
+  u64 pad;
+};
+
+// Pairwise constants for prime a (source) and prime b (target): [a][b].
+struct PairConst {
+  u64 qa_mod_b;      // q_a mod q_b
+  u64 inv_qa;        // q_a^-1 mod q_b (0 when a == b)
+  u64 inv_qa_sh;     // Shoup companion of inv_qa
+  u64 pad;
+};
+
+// Everything a kernel needs about the modulus chain, passed by value.
+struct DevTables {
+  const ModConst* mods;    // [n_mods]
+  const PairConst* pairs;  // [n_mods][n_mods]
+  const u64* tw;           // [n_mods][4][N]: psi^brv(k), Shoup, psi^-brv(k), Shoup
+  u32 log_n;
+  u32 n_mods;  // L + 1
+  u32 L;       // number of data primes; P is chain index L
+  u32 pad;
+};
+
+}  // namespace tcks

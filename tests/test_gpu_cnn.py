@@ -1,0 +1,67 @@
+"""The encrypted MNIST-shaped CNN of §4 (config C2: N=8192, [31,26x6|31], scale 2^26) on the GPU versus
+the oracle: identical encoded weights, identical Galois steps, bit-identical output ciphertext, and
+the decrypted logits against the FP64 network."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2104_03152_gb300 as tk
+from gpu_common import SEED, assert_ct_equal
+from paper_2104_03152_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+BITS = [31, 26, 26, 26, 26, 26, 26, 31]
+
+
+@pytest.fixture(scope="module")
+def setup():
+    o = oracle.OracleCKKS(13, BITS, 2.0 ** 26, key_seed=SEED).keygen()
+    need = oracle.cnn_galois_steps(o)
+    for st, lv in need.items():
+        o.gen_galois_key(st, lv)
+    w = oracle.CNNWeights(**inputs.cnn_weights(4))
+    enc = oracle.cnn_encode(o, w)
+    ctx = tk.Context(tk.Params(13, BITS, 2.0 ** 26), seed=SEED)
+    model = tk.CNN(ctx, w.conv_w, w.conv_b, w.fc1_w, w.fc1_b, w.fc2_w, w.fc2_b, windows=64)
+    model.gen_keys()
+    return o, w, enc, ctx, model, need
+
+
+def test_cnn_steps_and_keys(setup):
+    o, w, enc, ctx, model, need = setup
+    assert model.galois_steps() == need
+    assert len(need) == 264  # 1..255, 256, 512, 1024, 2048, 3072, 3584, 3840, 3968, 4032
+    for st in (1, 255, 256, 4032):
+        assert np.array_equal(ctx.export_key(tk.KEY_GALOIS, st), o.galois[st].data)
+
+
+def test_cnn_plaintexts_match_oracle(setup):
+    o, w, enc, ctx, model, need = setup
+    for k in range(4):
+        assert np.array_equal(model.export_plaintext(0, k)[0], enc.conv[k].data)
+        assert np.array_equal(model.export_plaintext(1, k)[0], enc.masks[k].data)
+    for i in range(0, 256, 17):
+        assert np.array_equal(model.export_plaintext(3, i)[0], enc.fc1[i].data)
+    for i in range(0, 64, 7):
+        assert np.array_equal(model.export_plaintext(4, i)[0], enc.fc2[i].data)
+
+
+def test_cnn_forward_parity(setup):
+    o, w, enc, ctx, model, need = setup
+    img = inputs.mnist_like_image(3)
+    v, W = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+    ct = o.encrypt_values(v, 77)
+    trace = {}
+    ref = oracle.cnn_forward(o, ct, w, enc, trace)
+    # the model's biases sit at the scales the oracle's schedule reaches
+    for i, sc in enumerate(trace["bias_scales"]):
+        data, gsc = model.export_plaintext(2, i)
+        assert gsc == sc
+    got = model.forward(ctx.ct_import(ct.data, ct.scale))
+    assert_ct_equal(got, ref, "cnn forward")
+    logits = ctx.decrypt_values(got, 10)
+    plain = oracle.cnn_plain(img, w)
+    err = float(np.max(np.abs(logits - plain)))
+    print(f"C2 CNN max |decrypted - FP64| = {err:.3e}")
+    assert err < 5e-3  # scale 2^26 (below the 2^30 of the 1e-3 clause): reported, bounded loosely

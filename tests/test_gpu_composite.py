@@ -1,0 +1,78 @@
+"""Composite operations on the GPU versus the oracle: sum, dot, dot_plain (§3.1), vector x plain
+matrix (§3.1), im2col convolution (§3.2). Bit-exact where both sides hold identical plaintexts."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2104_03152_gb300 as tk
+from gpu_common import Pair, assert_ct_equal
+from paper_2104_03152_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def p40():
+    """N=4096 with 40-bit primes and scale 2^40 (rescale keeps the scale near 2^40)."""
+    p = Pair(12, [55, 40, 40, 56], 2.0 ** 40)
+    p.add_galois(p.o.sum_steps())
+    return p
+
+
+def test_sum_dot_parity(p40):
+    o, g = p40.o, p40.g
+    n = 300
+    x = np.zeros(o.slots)
+    y = np.zeros(o.slots)
+    x[:n], y[:n] = inputs.uniform_slots(n, 5), inputs.uniform_slots(n, 6)
+    cx, cy = o.encrypt_values(x, 31), o.encrypt_values(y, 32)
+    gx, gy = p40.import_ct(cx), p40.import_ct(cy)
+    assert_ct_equal(gx.sum(n), o.sum(cx, n), "sum")
+    assert_ct_equal(gx.dot(gy, n), o.dot(cx, cy, n), "dot")
+    w = y[:n]
+    # dot_plain encodes w on each side: bit-exact when the two encodings agree (checked first)
+    assert np.array_equal(g.encode(w, level=cx.level).export(), o.encode(w, level=cx.level).data)
+    got = gx.dot_plain(w)
+    assert_ct_equal(got, o.dot_plain(cx, w, n), "dot_plain")
+    assert np.max(np.abs(g.decrypt_values(got) - x @ y)) < 1e-6
+
+
+@pytest.mark.parametrize("n,m", [(16, 8), (64, 10), (256, 64)])
+def test_vecmat_parity(n, m):
+    p = Pair(12, [55, 40, 40, 56], 2.0 ** 40)
+    o, g = p.o, p.g
+    p.add_galois(o.vecmat_steps(n))
+    v = np.zeros(o.slots)
+    v[:n] = inputs.uniform_slots(n, 7)
+    ct = o.encrypt_values(v, 41)
+    M = inputs.random_matrix(n, m, 8, 0.5)
+    diags = o.encode_matrix(M, ct.level)
+    ref = o.vecmat(ct, diags, n, m)
+    limbs = np.ascontiguousarray(np.stack([d.data for d in diags]))
+    gm = g.matrix_import(limbs, n, m, diags[0].scale)
+    got = p.import_ct(ct).vecmat_plain(gm)
+    assert_ct_equal(got, ref, "vecmat")
+    # the GPU's own encoding of the diagonals matches the oracle's
+    gm2 = g.matrix_encode(M, level=ct.level)
+    assert_ct_equal(p.import_ct(ct).vecmat_plain(gm2), ref, "vecmat (GPU-encoded matrix)")
+    out = g.decrypt_values(got)
+    assert np.max(np.abs(out[:m] - v[:n] @ M)) < 1e-5
+    assert np.max(np.abs(out[m:])) < 1e-5
+
+
+def test_conv_parity():
+    p = Pair(13, [40, 30, 30, 41], 2.0 ** 30)
+    o, g = p.o, p.g
+    img = inputs.mnist_like_image(3)
+    v, W = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+    p.add_galois(o.conv_steps(49, W))
+    ct = o.encrypt_values(v, 51)
+    ker = inputs.cnn_weights(4)["conv_w"][1]
+    kpt = o.encode(o.kernel_slots(ker, W), level=ct.level)
+    ref = o.conv2d_im2col_pt(ct, kpt, 49, W)
+    assert_ct_equal(p.import_ct(ct).conv2d_im2col_pt(p.import_pt(kpt), 49, W), ref, "conv (imported kernel)")
+    assert_ct_equal(p.import_ct(ct).conv2d_im2col(ker, W), ref, "conv (GPU-encoded kernel)")
+    out = g.decrypt_values(p.import_ct(ct).conv2d_im2col(ker, W))
+    want = np.array([np.sum(img[3 * (w // 8):3 * (w // 8) + 7, 3 * (w % 8):3 * (w % 8) + 7] * ker.reshape(7, 7))
+                     for w in range(64)])
+    assert np.max(np.abs(out[:64] - want)) < 1e-3
