@@ -1,0 +1,351 @@
+"""Benchmark: encrypted MNIST-shaped CNN inferences/s on one GB300 (and N replicas under torchrun).
+
+Workload (the paper's evaluation network, §4 / Table 2, with the chain N=8192, primes
+[31,26,26,26,26,26,26,31], scale 2^26): 28x28 seeded uniform image, im2col-encoded and encrypted;
+conv 4x7x7 stride 3 -> square -> FC 256->64 -> square -> FC 64->10 on seeded N(0, 0.1) weights.
+A step is one encrypted inference of one request through the whole hot path (conv rotations, pack,
+relinearized squares, two hoisted vector x matrix products), with the input ciphertext resident in
+HBM. Per step the kernels stream ~0.75 GB of Galois keys, more than the 129 MB L2, so no L2 flush is
+added. `e2e` times the same step through the C ABI with host buffers: the input ciphertext is
+imported from pinned host memory and the output exported back to it inside the timed region.
+
+--impl reference times the CPU oracle (the plain CKKS written from the definitions) on the host
+cores, one inference per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encrypted-CNN inferences/s + p99 latency (served vs plain); NTT/keyswitch GB/s"
+LOG_N, BITS, SCALE = 13, [31, 26, 26, 26, 26, 26, 26, 31], 2.0 ** 26
+SEED_IMG, SEED_W, SEED_ENC = 3, 4, 77
+WORKLOAD = ("encrypted MNIST-shaped CNN (conv 4x7x7/3 -> sq -> FC256->64 -> sq -> FC64->10), CKKS N=8192, "
+            "primes [31,26x6|31], scale 2^26, 264 trimmed Galois keys, batch 1 request per step")
+
+
+# ----------------------------------------------------------------------------- distributed --
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world, local):
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if dist.is_nccl_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return torch
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------ clocks --
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 10:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        load = [r for r in rows if (num(r[4]) or 0) >= 50] or rows
+        sm = [num(r[1]) for r in load if num(r[1]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[6:10]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": num(rows[0][2]), "reasons": sorted(reasons),
+                "samples": len(rows), "samples_under_load": len(load),
+                "power_w_max": max((num(r[3]) or 0) for r in rows)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def ncu_traffic(kernel: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    ent = d.get("kernels", {}).get(kernel)
+    if not ent or ent.get("src_sha") != source_digest():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def source_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    src = os.path.join(ROOT, "paper_2104_03152_gb300", "csrc")
+    for f in sorted(os.listdir(src)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(f.encode())
+            h.update(open(os.path.join(src, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------------- GPU arm --
+def gpu_setup(torch):
+    import paper_2104_03152_gb300 as tk
+    from paper_2104_03152_gb300 import inputs
+
+    tk.lib(build_if_missing=True)
+    stream = torch.cuda.Stream()
+    ctx = tk.Context(tk.Params(LOG_N, BITS, SCALE), seed=inputs.SEED_KEYS, stream=stream.cuda_stream)
+    w = inputs.cnn_weights(SEED_W)
+    model = tk.CNN(ctx, w["conv_w"], w["conv_b"], w["fc1_w"], w["fc1_b"], w["fc2_w"], w["fc2_b"], windows=64)
+    model.gen_keys()
+    img = inputs.mnist_like_image(SEED_IMG)
+    v, _ = tk.im2col_encode(img, 7, 7, 3, ctx.slots)
+    ct = ctx.encrypt_values(v, SEED_ENC)
+    ctx.synchronize()
+    return tk, ctx, model, ct, stream, img, w
+
+
+def run_gpu(args, world, rank, local):
+    torch = dist_init(world, local)
+    tk, ctx, model, ct, stream, img, w = gpu_setup(torch)
+    # correctness guard: the decrypted logits must match the FP64 network
+    out = model.forward(ct)
+    logits = ctx.decrypt_values(out, 10)
+    ref = plain_cnn(img, w)
+    max_err = float(np.max(np.abs(logits - ref)))
+    for _ in range(args.warmup):
+        out = model.forward(ct)
+    ctx.synchronize()
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    n0 = tk.launch_count()
+    tk.profile_start()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.nvtx.range_push("timed")
+    with torch.cuda.stream(stream):
+        evs[0].record(stream)
+        for k in range(args.steps):
+            out = model.forward(ct)
+            evs[k + 1].record(stream)
+    stream.synchronize()
+    torch.cuda.nvtx.range_pop()
+    tk.profile_stop()
+    launches = tk.launch_count() - n0
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    total_ms = reduce_max(world, total_ms)
+    prof = tk.profile_read()
+    # e2e through the C ABI with pinned host buffers
+    host_in = torch.empty(ct.export().size, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    host_in[:] = ct.export().reshape(-1)
+    host_in = host_in.reshape(2, ct.level, ctx.N)
+    out_words = 2 * out.level * ctx.N
+    host_out = torch.empty(out_words, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cin = ctx.ct_import(host_in, ct.scale)
+        cout = model.forward(cin)
+        tk.check(tk.lib().tcks_ct_export(cout.h, tk._p(host_out), out_words))
+    torch.cuda.synchronize()
+    e2e_s = reduce_max(world, time.perf_counter() - t0)
+    return dict(total_ms=total_ms, per_step=per_step, prof=prof, launches=launches, clocks=clk, e2e_s=e2e_s,
+                h2d=host_in.nbytes, d2h=host_out.nbytes, max_err=max_err)
+
+
+def plain_cnn(img, w):
+    stride, kh = 3, 7
+    conv = np.zeros((4, 8, 8))
+    for k in range(4):
+        ker = w["conv_w"][k].reshape(kh, kh)
+        for r in range(8):
+            for c in range(8):
+                conv[k, r, c] = np.sum(img[stride * r:stride * r + kh, stride * c:stride * c + kh] * ker) + w["conv_b"][k]
+    x = conv.reshape(-1) ** 2
+    x = (w["fc1_w"] @ x + w["fc1_b"]) ** 2
+    return w["fc2_w"] @ x + w["fc2_b"]
+
+
+# ------------------------------------------------------------------------------ CPU oracle --
+def oracle_setup():
+    import oracle
+    from paper_2104_03152_gb300 import inputs
+
+    o = oracle.OracleCKKS(LOG_N, BITS, SCALE, key_seed=inputs.SEED_KEYS).keygen()
+    for st, lv in oracle.cnn_galois_steps(o).items():
+        o.gen_galois_key(st, lv)
+    w = oracle.CNNWeights(**inputs.cnn_weights(SEED_W))
+    enc = oracle.cnn_encode(o, w)
+    img = inputs.mnist_like_image(SEED_IMG)
+    v, _ = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+    ct = o.encrypt_values(v, SEED_ENC)
+    return oracle, o, w, enc, ct
+
+
+def time_oracle(n_steps: int, warmup: int):
+    oracle, o, w, enc, ct = oracle_setup()
+    for _ in range(warmup):
+        oracle.cnn_forward(o, ct, w, enc)
+    times = []
+    for _ in range(n_steps):
+        t0 = time.perf_counter()
+        oracle.cnn_forward(o, ct, w, enc)
+        times.append(time.perf_counter() - t0)
+    return times, oracle.lib().orc_max_threads()
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    steps, warmup = args.steps, args.warmup
+    # bound the run: at most ~3 minutes of oracle inferences
+    times, cores = time_oracle(steps, warmup)
+    total = sum(times)
+    value = steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": args.gpus,
+            "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * total / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "cpu oracle"},
+            "cpu_baseline": {"value": value, "unit": "inferences/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{steps} full inferences (forward only; keys and weights prepared outside)"},
+            "e2e": {"value": value, "unit": "inferences/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------ main --
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=2, help="oracle inferences timed for cpu_baseline")
+    args = ap.parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    r = run_gpu(args, world, rank, local)
+    if rank != 0:
+        return
+    peaks = measured_peaks()
+    ms_per_step = r["total_ms"] / args.steps
+    value = world * args.steps / (r["total_ms"] / 1e3)
+    # dominant kernel family by device time
+    prof = r["prof"]
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (nl, ms, by) = dom
+    achieved = by / (ms / 1e3) / 1e9
+    traffic = ncu_traffic(name)
+    roofline = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
+                "traffic": traffic, "launches": nl, "algo_bytes_per_launch": by / nl, "avg_launch_us": 1e3 * ms / nl}
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / sum(x[1] for x in prof.values()), 4),
+                   "gbs": round(v[2] / (v[1] / 1e3) / 1e9, 1)} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    per = sorted(r["per_step"])
+    # CPU baseline: the oracle on the host cores, bounded sample
+    if args.cpu_sample > 0:
+        times, cores = time_oracle(args.cpu_sample, 0)
+        cpu_val = len(times) / sum(times)
+    else:
+        times, cores, cpu_val = [], 0, None
+    line = {
+        "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (Galois keys ~0.75 GB streamed per step)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "latency_ms": {"p50": per[len(per) // 2], "p99": per[min(len(per) - 1, int(0.99 * len(per)))],
+                       "mode": "plain (one request at a time)"},
+        "accuracy": {"max_abs_err_vs_fp64": r["max_err"], "scale": "2^26"},
+        "roofline": roofline, "kernels": kernels,
+        "cpu_baseline": {"value": cpu_val, "unit": "inferences/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{len(times)} full CNN inferences of this workload (forward only)"},
+        "e2e": {"value": world * args.steps / r["e2e_s"], "unit": "inferences/s", "h2d_bytes_per_step": r["h2d"],
+                "d2h_bytes_per_step": r["d2h"]},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -218,6 +218,18 @@ tcks_status tcks_conv2d_im2col(const tcks_ct* a, const double* kernel, uint32_t 
 tcks_status tcks_conv2d_im2col_pt(const tcks_ct* a, const tcks_pt* kernel, uint32_t taps, uint32_t windows,
                                   tcks_ct** out);
 
+/* ------------------------------------------------------------------ launch accounting ---- */
+/* Number of kernel launches the library has issued since it was loaded. */
+uint64_t tcks_launch_count(void);
+/* Kernel profiler: while on, every launch is bracketed by CUDA events on its stream and carries its
+ * algorithmic bytes (each operand read once, each result written once, each distinct key once).
+ * start clears earlier records. read() reports, for kernel family idx < tcks_profile_count(), its
+ * name, launches, summed device milliseconds and summed algorithmic bytes (waits for the events). */
+tcks_status tcks_profile_start(void);
+tcks_status tcks_profile_stop(void);
+uint32_t tcks_profile_count(void);
+tcks_status tcks_profile_read(uint32_t idx, const char** name, uint64_t* launches, double* ms, double* algo_bytes);
+
 /* ------------------------------------------------------------- the encrypted CNN (§4) ---- */
 /* The MNIST-shaped network of the paper's evaluation (§4, Table 2): im2col conv with `kernels`
  * kernels of `taps` taps over `windows` windows (§3.2), square, FC (kernels*windows) -> hidden

@@ -97,6 +97,12 @@ _SIGS = {
                                              ctypes.c_uint32, ctypes.c_uint32, _dblp, ctypes.c_size_t, _u32p]),
     "tcks_conv2d_im2col": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
     "tcks_conv2d_im2col_pt": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
+    "tcks_launch_count": (ctypes.c_uint64, []),
+    "tcks_profile_start": (ctypes.c_int32, []),
+    "tcks_profile_stop": (ctypes.c_int32, []),
+    "tcks_profile_count": (ctypes.c_uint32, []),
+    "tcks_profile_read": (ctypes.c_int32, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_char_p),
+                                            ctypes.POINTER(ctypes.c_uint64), _dblp, _dblp]),
     "tcks_cnn_create": (ctypes.c_int32, [_vp, _dblp, _dblp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                           _dblp, _dblp, ctypes.c_uint32, _dblp, _dblp, ctypes.c_uint32, _vpp]),
     "tcks_cnn_free": (None, [_vp]),
@@ -133,6 +139,30 @@ def check(status: int):
     if status != 0:
         L = lib()
         raise TcksError(status, L.tcks_status_string(status).decode(), L.tcks_last_error_detail().decode())
+
+
+def launch_count() -> int:
+    return int(lib().tcks_launch_count())
+
+
+def profile_start():
+    check(lib().tcks_profile_start())
+
+
+def profile_stop():
+    check(lib().tcks_profile_stop())
+
+
+def profile_read() -> dict:
+    """{kernel family: (launches, device ms, algorithmic bytes)} of the records since profile_start."""
+    L = lib()
+    out = {}
+    for i in range(L.tcks_profile_count()):
+        name, n, ms, by = ctypes.c_char_p(), ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double()
+        check(L.tcks_profile_read(i, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
+        if n.value:
+            out[name.value.decode()] = (n.value, ms.value, by.value)
+    return out
 
 
 def _p(a: np.ndarray):

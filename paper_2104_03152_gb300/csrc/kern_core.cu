@@ -71,6 +71,7 @@ void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_stride
                 u32 count, u32 mod_base, u32 mod_period, cudaStream_t st) {
   if (!count) return;
   const size_t sm = smem_bytes(T.log_n);
+  Launch L(inverse ? K_NTT_INV : K_NTT_FWD, st, 16.0 * count * (1u << T.log_n));
   if (inverse) {
     allow_smem(k_ntt<true>, sm);
     k_ntt<true><<<count, ntt_threads(T.log_n), sm, st>>>(T, src, src_stride, dst, dst_stride, mod_base, mod_period);
@@ -149,6 +150,11 @@ static u32 ew_blocks(u64 elems2) {
 void launch_elementwise(const DevTables& T, u32 op, const u64* a, const u64* b, u64* out, u32 ell, u32 polys,
                         cudaStream_t st) {
   const u64 e2 = ((u64)polys * ell << T.log_n) >> 1;
+  const double limb = 8.0 * ell * (1u << T.log_n);  // bytes of one [ell][N] polynomial
+  const double by = op == OP_NEG ? 2.0 * polys * limb
+                    : (op == OP_ADD || op == OP_SUB) ? 3.0 * polys * limb
+                                                     : (2.0 * polys + 1.0) * limb;  // plaintext operand
+  Launch L(K_ELEMENTWISE, st, by);
   k_elementwise<<<ew_blocks(e2), 256, 0, st>>>(T, op, a, b, out, ell, polys);
 }
 
@@ -172,6 +178,7 @@ __global__ void k_tensor(DevTables T, const u64* __restrict__ a, const u64* __re
 
 void launch_tensor(const DevTables& T, const u64* a, const u64* b, u64* out, u32 ell, cudaStream_t st) {
   const u64 e = (u64)ell << T.log_n;
+  Launch L(K_TENSOR, st, 7.0 * 8.0 * e);
   k_tensor<<<ew_blocks(e / 2 + 1), 256, 0, st>>>(T, a, b, out, ell);
 }
 
@@ -188,6 +195,7 @@ __global__ void k_decrypt(DevTables T, const u64* __restrict__ ct, const u64* __
 
 void launch_decrypt(const DevTables& T, const u64* ct, const u64* s, u64* pt, u32 ell, cudaStream_t st) {
   const u64 e = (u64)ell << T.log_n;
+  Launch L(K_DECRYPT, st, 4.0 * 8.0 * e);
   k_decrypt<<<ew_blocks(e / 2 + 1), 256, 0, st>>>(T, ct, s, pt, ell);
 }
 
@@ -221,6 +229,7 @@ void launch_rescale(const DevTables& T, const u64* ct, u32 ell, u64* top_tmp, u6
   launch_ntt(T, true, ct + (u64)(ell - 1) * n, (u64)ell * n, top_tmp, n, 2, ell - 1, 1, st);
   const size_t sm = smem_bytes(T.log_n);
   allow_smem(k_drop_combine, sm);
+  Launch L(K_DROP, st, 8.0 * (1u << T.log_n) * (4.0 * (ell - 1) + 2.0));
   k_drop_combine<<<2 * (ell - 1), ntt_threads(T.log_n), sm, st>>>(T, ct, (u64)ell * n, top_tmp, ell - 1, ell - 1,
                                                                    out);
 }
@@ -255,6 +264,7 @@ void launch_modup(const DevTables& T, const u64* x_ntt, u32 ell, u64* x_coef_tmp
   launch_ntt(T, true, x_ntt, n, x_coef_tmp, n, ell, 0, ell, st);
   const size_t sm = smem_bytes(T.log_n);
   allow_smem(k_modup, sm);
+  Launch L(K_MODUP, st, 8.0 * (1u << T.log_n) * (2.0 * ell + (double)ell * (ell + 1)));
   k_modup<<<ell * (ell + 1), ntt_threads(T.log_n), sm, st>>>(T, x_ntt, x_coef_tmp, ell, digits);
 }
 
@@ -321,8 +331,29 @@ void launch_keyswitch(const DevTables& T, u32 ell, const KsBatch& jobs, cudaStre
   const size_t sm = smem_bytes(T.log_n);
   allow_smem(k_ks_inner_p, sm);
   allow_smem(k_ks_moddown, sm);
-  k_ks_inner_p<<<dim3(2, jobs.count), ntt_threads(T.log_n), sm, st>>>(T, ell, jobs);
-  k_ks_moddown<<<dim3(2 * ell, jobs.count), ntt_threads(T.log_n), sm, st>>>(T, ell, jobs);
+  // algorithmic bytes: distinct digit sets and keys once, scratch and outputs once
+  const double n = (double)(1u << T.log_n);
+  double digits = 0, keys_p = 0, keys_q = 0, adds = 0;
+  for (u32 j = 0; j < jobs.count; ++j) {
+    bool new_digits = true, new_key = true, new_add = true;
+    for (u32 i = 0; i < j; ++i) {
+      new_digits &= jobs.job[i].digits != jobs.job[j].digits;
+      new_key &= jobs.job[i].key != jobs.job[j].key;
+      new_add &= jobs.job[i].add0 != jobs.job[j].add0;
+    }
+    if (new_digits) digits += 1;
+    if (new_key) keys_p += 2.0 * ell, keys_q += 2.0 * ell * ell;
+    if (new_add && jobs.job[j].add0) adds += jobs.job[j].add1 ? 2.0 * ell : ell;
+  }
+  {
+    Launch L(K_KS_P, st, 8.0 * n * (digits * ell + keys_p + 2.0 * jobs.count));
+    k_ks_inner_p<<<dim3(2, jobs.count), ntt_threads(T.log_n), sm, st>>>(T, ell, jobs);
+  }
+  {
+    Launch L(K_KS_MODDOWN, st,
+             8.0 * n * (digits * ell * ell + keys_q + 2.0 * jobs.count + adds + 2.0 * ell * jobs.count));
+    k_ks_moddown<<<dim3(2 * ell, jobs.count), ntt_threads(T.log_n), sm, st>>>(T, ell, jobs);
+  }
 }
 
 // acc += sum_c rots[c] * diag[c]: one pass over acc, lazy 128-bit accumulation (count <= 64 keeps
@@ -345,6 +376,7 @@ void launch_mulacc(const DevTables& T, u64* acc, const u64* rots, u64 rot_stride
                    u32 count, u32 ell, cudaStream_t st) {
   if (!count) return;
   const u64 e = (u64)2 * ell << T.log_n;
+  Launch L(K_MULACC, st, 8.0 * ((double)e * (2.0 + count) + (double)count * ell * (1u << T.log_n)));
   k_mulacc<<<ew_blocks(e / 2 + 1), 256, 0, st>>>(T, acc, rots, rot_stride, diag, diag_stride, count, ell);
 }
 

@@ -196,18 +196,21 @@ void launch_encode_coeffs(const DevTables& T, const FftTables& F, const double* 
                           i64* d_coeffs, int* d_status, cudaStream_t st) {
   const size_t sm = (size_t)16 << (T.log_n - 1);
   allow((const void*)k_encode_coeffs, sm);
+  Launch L(K_ENCODE, st, 8.0 * n_in + 8.0 * (1u << T.log_n));
   k_encode_coeffs<<<1, 1024, sm, st>>>(T, F, d_z, n_in, scale, d_coeffs, d_status);
 }
 
 void launch_coeffs_to_ntt(const DevTables& T, const i64* d_coeffs, u32 ell, u64* pt, cudaStream_t st) {
   const size_t sm = (size_t)8 << T.log_n;
   allow((const void*)k_coeffs_to_ntt, sm);
+  Launch L(K_ENCODE, st, 8.0 * (1.0 + ell) * (1u << T.log_n));
   k_coeffs_to_ntt<<<ell, ntt_threads(T.log_n), sm, st>>>(T, d_coeffs, pt);
 }
 
 void launch_crt_compose(const DevTables& T, const u64* coef, u32 ell, const u64* d_qwords, double* out,
                         cudaStream_t st) {
   const u32 n = 1u << T.log_n;
+  Launch L(K_DECODE, st, 8.0 * (ell + 1.0) * (1u << T.log_n));
   k_crt_compose<<<(n + 127) / 128, 128, 0, st>>>(T, coef, ell, d_qwords, out);
 }
 
@@ -215,6 +218,7 @@ void launch_decode_slots(const DevTables& T, const FftTables& F, const double* p
                          double* out, cudaStream_t st) {
   const size_t sm = (size_t)16 << (T.log_n - 1);
   allow((const void*)k_decode_slots, sm);
+  Launch L(K_DECODE, st, 8.0 * (1u << T.log_n) + 8.0 * n_out);
   k_decode_slots<<<1, 1024, sm, st>>>(T, F, p, scale, n_out, out);
 }
 

@@ -163,24 +163,28 @@ static void allow_smem(K kernel, size_t bytes) {
 void launch_keygen_secret(const DevTables& T, u64 seed, u64* s, cudaStream_t st) {
   const size_t sm = smem_bytes(T.log_n);
   allow_smem(k_keygen_secret, sm);
+  Launch L(K_KEYGEN, st, 8.0 * (T.L + 1) * (1u << T.log_n));
   k_keygen_secret<<<T.L + 1, ntt_threads(T.log_n), sm, st>>>(T, seed, s);
 }
 
 void launch_keygen_public(const DevTables& T, u64 seed, const u64* s, u64* pk, cudaStream_t st) {
   const size_t sm = smem_bytes(T.log_n);
   allow_smem(k_keygen_public, sm);
+  Launch L(K_KEYGEN, st, 8.0 * 3 * T.L * (1u << T.log_n));
   k_keygen_public<<<T.L, ntt_threads(T.log_n), sm, st>>>(T, seed, s, pk);
 }
 
 void launch_keygen_switch(const DevTables& T, u64 seed, u32 kind, const u64* s, u32 K, u64* ksk, cudaStream_t st) {
   const size_t sm = smem_bytes(T.log_n);
   allow_smem(k_keygen_switch, sm);
+  Launch L(K_KEYGEN, st, 8.0 * 2 * K * (K + 1) * (1u << T.log_n));
   k_keygen_switch<<<K * (K + 1), ntt_threads(T.log_n), sm, st>>>(T, seed, kind, s, K, ksk);
 }
 
 void launch_encrypt(const DevTables& T, u64 seed, const u64* pk, const u64* pt, u32 ell, u64* out, cudaStream_t st) {
   const size_t sm = smem_bytes(T.log_n);
   allow_smem(k_encrypt, sm);
+  Launch L(K_ENCRYPT, st, 8.0 * 5 * ell * (1u << T.log_n));
   k_encrypt<<<ell, ntt_threads(T.log_n), sm, st>>>(T, seed, pk, pt, ell, out);
 }
 

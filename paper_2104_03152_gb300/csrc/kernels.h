@@ -6,6 +6,28 @@
 
 namespace tcks {
 
+// Kernel families for launch accounting and the profiler (profiler.cpp).
+enum KernelId : u32 {
+  K_NTT_FWD = 0, K_NTT_INV, K_ELEMENTWISE, K_TENSOR, K_DROP, K_MODUP, K_KS_P, K_KS_MODDOWN, K_MULACC, K_KEYGEN,
+  K_ENCRYPT, K_ENCODE, K_DECODE, K_BATCH_NTT, K_DECRYPT, K_COUNT
+};
+// Scope around one kernel launch: counts it and, while profiling is on, records CUDA events on the
+// launching stream before and after it together with its algorithmic bytes.
+class Launch {
+ public:
+  Launch(KernelId id, cudaStream_t st, double algo_bytes);
+  ~Launch();
+  Launch(const Launch&) = delete;
+  Launch& operator=(const Launch&) = delete;
+
+ private:
+  KernelId id_;
+  cudaStream_t st_;
+  double bytes_;
+  void* a_ = nullptr;
+  bool active_ = false;
+};
+
 // ---- kern_core.cu
 u32 ntt_threads(u32 log_n);
 // Raise a kernel's dynamic shared-memory limit to `bytes` (no-op at or below 48 KB).
