@@ -163,6 +163,22 @@ tcks_status tcks_square(const tcks_ct* a, tcks_ct** out);
 tcks_status tcks_rescale(tcks_ct* ct);
 /* Drop limbs level..ell-1 in place (scale unchanged). */
 tcks_status tcks_mod_switch(tcks_ct* ct, uint32_t level);
+/* Rescale that allocates no memory, for callers that must not allocate at all while they run: for
+ * example a serving loop that reserves all of its device memory when it starts and admits work
+ * against that fixed budget, so a library call that grows the allocator's pool (or blocks inside
+ * it) would break its accounting. The paper has no counterpart; this is a variant of tcks_rescale
+ * with the same result, bit for bit.
+ * d_in: device [2][level][N] ciphertext limbs (NTT form) of `ctx`; d_out: device [2][level-1][N],
+ * not overlapping d_in; both owned by the caller. The output's scale is the input's divided by
+ * q_{level-1}, which the caller tracks. Its only scratch (two limbs) is a static device array of
+ * 2 x 2^14 u64 words (256 KB), which every GPU that loads the library holds until the process
+ * exits; N above 2^14 is rejected with TCKS_ERR_INVALID_ARG. The first call on a device looks up
+ * that array's address (and raises the two kernels' shared-memory limit), so make one call on
+ * each device before any stream capture. All calls share the one array: calls that can overlap on
+ * the GPU (different streams, or different contexts on the same device) race on it and must be
+ * serialised by the caller. Nothing in the array needs to start at zero. Asynchronous on the
+ * context's stream; errors: INVALID_ARG, LEVEL_EXHAUSTED (level < 2), CUDA_ERROR. */
+tcks_status tcks_rescale_noalloc(tcks_ctx* ctx, const uint64_t* d_in, uint32_t level, uint64_t* d_out);
 
 /* Negacyclic NTT (inverse = 0) or INTT (inverse = 1), in place, of `polys` polynomials of `level`
  * limbs laid out [polys][level][N] in device memory: limb l of every polynomial is transformed

@@ -82,6 +82,7 @@ _SIGS = {
     "tcks_square": (ctypes.c_int32, [_vp, _vpp]),
     "tcks_rescale": (ctypes.c_int32, [_vp]),
     "tcks_mod_switch": (ctypes.c_int32, [_vp, ctypes.c_uint32]),
+    "tcks_rescale_noalloc": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, _vp]),
     "tcks_rotate": (ctypes.c_int32, [_vp, ctypes.c_int32, _vpp]),
     "tcks_rotate_hoisted": (ctypes.c_int32, [_vp, _i32p, ctypes.c_uint32, _vpp]),
     "tcks_ntt_inplace": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int32]),
@@ -316,6 +317,10 @@ class Context:
         h = _vp()
         check(lib().tcks_pt_import(self.h, _p(a), a.shape[0], float(scale), ctypes.byref(h)))
         return Plaintext(self, h)
+
+    def rescale_noalloc(self, d_in: int, level: int, d_out: int):
+        """Allocation-free rescale of device limbs [2][level][N] into [2][level-1][N] (see tcks.h)."""
+        check(lib().tcks_rescale_noalloc(self.h, _vp(d_in), level, _vp(d_out)))
 
     def ntt_inplace(self, d_ptr: int, polys: int, level: int, inverse: bool):
         check(lib().tcks_ntt_inplace(self.h, _vp(d_ptr), polys, level, 1 if inverse else 0))

@@ -9,7 +9,9 @@
 
 #include <map>
 #include <mutex>
+#include <string>
 
+#include "context.h"
 #include "kernels.h"
 #include "ntt.cuh"
 
@@ -381,3 +383,83 @@ void launch_mulacc(const DevTables& T, u64* acc, const u64* rots, u64 rot_stride
 }
 
 }  // namespace tcks
+
+// ------------------------------------------------------------- allocation-free rescale ----
+// A variant of the rescale for callers that cannot allocate device memory. Its only scratch (the
+// coefficient-domain top limb of both components, [2][N] words) lives in the static array below,
+// which every GPU that loads the library holds until the process exits.
+namespace tcks {
+tcks_status abi_record(tcks_status code, const std::string& msg);
+void abi_clear();
+void count_launch();
+
+namespace {
+constexpr u32 kNoAllocMaxLogN = 14;                           // N <= 16384
+constexpr size_t kNoAllocWords = (size_t)2 << kNoAllocMaxLogN;  // 256 KB
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) u64 g_rescale_scratch[kNoAllocWords];
+u64* g_scratch_ptr[kNoAllocMaxDevices];  // device address of g_rescale_scratch per device, set up once
+bool g_scratch_ready[kNoAllocMaxDevices];
+std::mutex g_scratch_mu;
+
+// Once per device, with that device current: resolve the scratch array's device address and raise
+// the shared-memory limit of the two kernels the rescale launches. Returns nullptr on failure.
+u64* noalloc_setup(int device, std::string* why) {
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (g_scratch_ready[device]) return g_scratch_ptr[device];
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) {
+    *why = "cudaGetDevice failed";
+    return nullptr;
+  }
+  if (prev != device && cudaSetDevice(device) != cudaSuccess) {
+    *why = "cudaSetDevice failed";
+    return nullptr;
+  }
+  u64* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_rescale_scratch);
+  const int bytes = (int)(((size_t)8) << kNoAllocMaxLogN);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_drop_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (prev != device) cudaSetDevice(prev);
+  if (e != cudaSuccess) {
+    *why = std::string("scratch set-up failed: ") + cudaGetErrorString(e);
+    return nullptr;
+  }
+  g_scratch_ptr[device] = ptr;
+  g_scratch_ready[device] = true;
+  return ptr;
+}
+}  // namespace
+}  // namespace tcks
+
+extern "C" tcks_status tcks_rescale_noalloc(tcks_ctx* ctx, const uint64_t* d_in, uint32_t level, uint64_t* d_out) {
+  using namespace tcks;
+  if (!ctx || !d_in || !d_out) return abi_record(TCKS_ERR_INVALID_ARG, "rescale_noalloc: null argument");
+  if (level < 2) return abi_record(TCKS_ERR_LEVEL_EXHAUSTED, "rescale_noalloc: needs level >= 2");
+  if (level > ctx->L) return abi_record(TCKS_ERR_INVALID_ARG, "rescale_noalloc: level exceeds the chain");
+  const u32 log_n = ctx->params.log_n;
+  if (log_n > kNoAllocMaxLogN)
+    return abi_record(TCKS_ERR_INVALID_ARG,
+                      "rescale_noalloc: N = 2^" + std::to_string(log_n) +
+                          " exceeds the static scratch, which holds two limbs of at most N = 2^14");
+  if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
+    return abi_record(TCKS_ERR_INVALID_ARG, "rescale_noalloc: device index out of range");
+  std::string why;
+  u64* scratch = noalloc_setup(ctx->device, &why);
+  if (!scratch) return abi_record(TCKS_ERR_CUDA, "rescale_noalloc: " + why);
+  const DevTables& T = ctx->T;
+  const u64 n = 1ull << log_n;
+  const size_t sm = ((size_t)8) << log_n;
+  // the two launches of launch_rescale, without its allocating bookkeeping
+  count_launch();
+  k_ntt<true><<<2, ntt_threads(log_n), sm, ctx->stream>>>(T, d_in + (u64)(level - 1) * n, (u64)level * n, scratch, n,
+                                                           level - 1, 1);
+  count_launch();
+  k_drop_combine<<<2 * (level - 1), ntt_threads(log_n), sm, ctx->stream>>>(T, d_in, (u64)level * n, scratch,
+                                                                             level - 1, level - 1, d_out);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return abi_record(TCKS_ERR_CUDA, std::string("rescale_noalloc: ") + cudaGetErrorString(e));
+  abi_clear();
+  return TCKS_OK;
+}
