@@ -3,11 +3,13 @@
 Workload (the paper's evaluation network, §4 / Table 2, with the chain N=8192, primes
 [31,26,26,26,26,26,26,31], scale 2^26): 28x28 seeded uniform image, im2col-encoded and encrypted;
 conv 4x7x7 stride 3 -> square -> FC 256->64 -> square -> FC 64->10 on seeded N(0, 0.1) weights.
-A step is one encrypted inference of one request through the whole hot path (conv rotations, pack,
-relinearized squares, two hoisted vector x matrix products), with the input ciphertext resident in
-HBM. Per step the kernels stream ~0.75 GB of Galois keys, more than the 129 MB L2, so no L2 flush is
-added. `e2e` times the same step through the C ABI with host buffers: the input ciphertext is
-imported from pinned host memory and the output exported back to it inside the timed region.
+A step is one batch of B encrypted inferences (B requests, default 64) through the whole hot path
+(conv rotations, pack, relinearized squares, two hoisted vector x matrix products) in the batched
+schedule, where every stage runs once for the whole batch; inputs are resident in HBM. Per step the
+kernels stream ~0.75 GB of Galois keys plus ~2 GB of per-request key-switch scratch, more than the
+129 MB L2, so no L2 flush is added. The plain path (one request per step) is timed alongside.
+`e2e` times the batched step through the C ABI with host buffers: the B input ciphertexts are
+imported from pinned host memory and the B outputs exported back to it inside the timed region.
 
 --impl reference times the CPU oracle (the plain CKKS written from the definitions) on the host
 cores, one inference per step.
@@ -32,7 +34,7 @@ METRIC = "encrypted-CNN inferences/s + p99 latency (served vs plain); NTT/keyswi
 LOG_N, BITS, SCALE = 13, [31, 26, 26, 26, 26, 26, 26, 31], 2.0 ** 26
 SEED_IMG, SEED_W, SEED_ENC = 3, 4, 77
 WORKLOAD = ("encrypted MNIST-shaped CNN (conv 4x7x7/3 -> sq -> FC256->64 -> sq -> FC64->10), CKKS N=8192, "
-            "primes [31,26x6|31], scale 2^26, 264 trimmed Galois keys, batch 1 request per step")
+            "primes [31,26x6|31], scale 2^26, 264 trimmed Galois keys")
 
 
 # ----------------------------------------------------------------------------- distributed --
@@ -160,7 +162,7 @@ def source_digest() -> str:
 
 
 # ---------------------------------------------------------------------------------- GPU arm --
-def gpu_setup(torch):
+def gpu_setup(torch, batch):
     import paper_2104_03152_gb300 as tk
     from paper_2104_03152_gb300 import inputs
 
@@ -170,65 +172,86 @@ def gpu_setup(torch):
     w = inputs.cnn_weights(SEED_W)
     model = tk.CNN(ctx, w["conv_w"], w["conv_b"], w["fc1_w"], w["fc1_b"], w["fc2_w"], w["fc2_b"], windows=64)
     model.gen_keys()
-    img = inputs.mnist_like_image(SEED_IMG)
-    v, _ = tk.im2col_encode(img, 7, 7, 3, ctx.slots)
-    ct = ctx.encrypt_values(v, SEED_ENC)
+    imgs = [inputs.mnist_like_image(SEED_IMG + i) for i in range(batch)]
+    cts = []
+    for i, img in enumerate(imgs):
+        v, _ = tk.im2col_encode(img, 7, 7, 3, ctx.slots)
+        cts.append(ctx.encrypt_values(v, SEED_ENC + i))
     ctx.synchronize()
-    return tk, ctx, model, ct, stream, img, w
+    return tk, ctx, model, cts, stream, imgs, w
+
+
+def timed(torch, stream, fn, steps):
+    """CUDA-event times (ms) of `steps` calls of fn on `stream`, one event pair per step."""
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    with torch.cuda.stream(stream):
+        evs[0].record(stream)
+        for k in range(steps):
+            fn()
+            evs[k + 1].record(stream)
+    stream.synchronize()
+    return [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)], evs[0].elapsed_time(evs[-1])
 
 
 def run_gpu(args, world, rank, local):
     torch = dist_init(world, local)
-    tk, ctx, model, ct, stream, img, w = gpu_setup(torch)
-    # correctness guard: the decrypted logits must match the FP64 network
-    out = model.forward(ct)
-    logits = ctx.decrypt_values(out, 10)
-    ref = plain_cnn(img, w)
-    max_err = float(np.max(np.abs(logits - ref)))
+    B = args.batch
+    tk, ctx, model, cts, stream, imgs, w = gpu_setup(torch, B)
+    # correctness guard: the decrypted logits of every request must match the FP64 network, and the
+    # batched outputs must equal the single-request path bit for bit
+    outs = model.forward_batch(cts)
+    max_err = 0.0
+    for i in (0, B - 1):
+        logits = ctx.decrypt_values(outs[i], 10)
+        max_err = max(max_err, float(np.max(np.abs(logits - plain_cnn(imgs[i], w)))))
+        assert np.array_equal(outs[i].export(), model.forward(cts[i]).export()), "batched != single"
     for _ in range(args.warmup):
-        out = model.forward(ct)
+        model.forward_batch(cts)
     ctx.synchronize()
+    # plain path: one request per step
+    plain_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        model.forward(cts[0])
+    plain_times, plain_total = timed(torch, stream, lambda: model.forward(cts[0]), plain_steps)
     clocks = Clocks(local)
     barrier(world)
     torch.cuda.synchronize()
     clocks.start()
     n0 = tk.launch_count()
     tk.profile_start()
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     torch.cuda.nvtx.range_push("timed")
-    with torch.cuda.stream(stream):
-        evs[0].record(stream)
-        for k in range(args.steps):
-            out = model.forward(ct)
-            evs[k + 1].record(stream)
-    stream.synchronize()
+    per_step, total_ms = timed(torch, stream, lambda: model.forward_batch(cts), args.steps)
     torch.cuda.nvtx.range_pop()
     tk.profile_stop()
     launches = tk.launch_count() - n0
     barrier(world)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
     total_ms = reduce_max(world, total_ms)
     prof = tk.profile_read()
-    # e2e through the C ABI with pinned host buffers
-    host_in = torch.empty(ct.export().size, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
-    host_in[:] = ct.export().reshape(-1)
-    host_in = host_in.reshape(2, ct.level, ctx.N)
-    out_words = 2 * out.level * ctx.N
-    host_out = torch.empty(out_words, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    # e2e through the C ABI with pinned host buffers: import B inputs, batched forward, export B outputs
+    L, N = cts[0].level, ctx.N
+    host_in = torch.empty(B * 2 * L * N, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    host_in = host_in.reshape(B, 2, L, N)
+    for i, c in enumerate(cts):
+        host_in[i] = c.export()
+    out_words = 2 * outs[0].level * N
+    host_out = torch.empty(B * out_words, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    host_out = host_out.reshape(B, out_words)
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        cin = ctx.ct_import(host_in, ct.scale)
-        cout = model.forward(cin)
-        tk.check(tk.lib().tcks_ct_export(cout.h, tk._p(host_out), out_words))
+    e2e_steps = max(3, args.steps // 2)
+    for _ in range(e2e_steps):
+        cin = [ctx.ct_import(host_in[i], cts[i].scale) for i in range(B)]
+        couts = model.forward_batch(cin)
+        for i, co in enumerate(couts):
+            tk.check(tk.lib().tcks_ct_export(co.h, tk._p(host_out[i]), out_words))
     torch.cuda.synchronize()
     e2e_s = reduce_max(world, time.perf_counter() - t0)
     return dict(total_ms=total_ms, per_step=per_step, prof=prof, launches=launches, clocks=clk, e2e_s=e2e_s,
-                h2d=host_in.nbytes, d2h=host_out.nbytes, max_err=max_err)
+                e2e_steps=e2e_steps, h2d=host_in.nbytes, d2h=host_out.nbytes, max_err=max_err,
+                plain_ms=plain_total / plain_steps, plain_times=plain_times)
 
 
 def plain_cnn(img, w):
@@ -298,6 +321,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=2, help="oracle inferences timed for cpu_baseline")
+    ap.add_argument("--batch", type=int, default=64, help="requests per step (the batched schedule)")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
@@ -307,8 +331,9 @@ def main():
     if rank != 0:
         return
     peaks = measured_peaks()
+    B = args.batch
     ms_per_step = r["total_ms"] / args.steps
-    value = world * args.steps / (r["total_ms"] / 1e3)
+    value = world * B * args.steps / (r["total_ms"] / 1e3)
     # dominant kernel family by device time
     prof = r["prof"]
     dom = max(prof.items(), key=lambda kv: kv[1][1])
@@ -331,16 +356,20 @@ def main():
         "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (Galois keys ~0.75 GB streamed per step)",
+        "config": {"workload": WORKLOAD, "batch": B,
+                   "l2": "inputs larger than L2 (Galois keys ~0.75 GB + key-switch scratch streamed per step)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "latency_ms": {"p50": per[len(per) // 2], "p99": per[min(len(per) - 1, int(0.99 * len(per)))],
-                       "mode": "plain (one request at a time)"},
+                       "mode": f"batched step of {B} requests (each request completes with its batch)"},
+        "plain": {"value": 1e3 / r["plain_ms"], "unit": "inferences/s", "ms_per_inference": r["plain_ms"],
+                  "p99_ms": sorted(r["plain_times"])[min(len(r["plain_times"]) - 1, int(0.99 * len(r["plain_times"])))],
+                  "mode": "one request at a time"},
         "accuracy": {"max_abs_err_vs_fp64": r["max_err"], "scale": "2^26"},
         "roofline": roofline, "kernels": kernels,
         "cpu_baseline": {"value": cpu_val, "unit": "inferences/s", "cores": cores, "kind": "oracle",
                          "sample": f"{len(times)} full CNN inferences of this workload (forward only)"},
-        "e2e": {"value": world * args.steps / r["e2e_s"], "unit": "inferences/s", "h2d_bytes_per_step": r["h2d"],
-                "d2h_bytes_per_step": r["d2h"]},
+        "e2e": {"value": world * B * r["e2e_steps"] / r["e2e_s"], "unit": "inferences/s",
+                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
     }

@@ -267,6 +267,18 @@ tcks_status tcks_cnn_galois_steps(const tcks_cnn* m, int32_t* steps, uint32_t* l
 /* One encrypted inference: input = the im2col-encoded image encrypted at level L and the context
  * scale; output at level L-6 with the logits in slots [0, classes). */
 tcks_status tcks_cnn_forward(const tcks_cnn* m, const tcks_ct* in, tcks_ct** out);
+/* `count` inferences in one pass (the batched path): every stage of the schedule runs once for
+ * the whole batch (rotations of all requests share key-switch launches). outs[i] is bit-identical
+ * to tcks_cnn_forward(in[i]). */
+tcks_status tcks_cnn_forward_batch(const tcks_cnn* m, const tcks_ct* const* in, uint32_t count, tcks_ct** outs);
+/* CUDA graph of the batched forward for a fixed batch size (the schedule is captured once with its
+ * stream-ordered scratch allocations, then replayed): create captures it (after one eager pass that
+ * warms the key tables), run copies the inputs into the graph's staging buffers, replays and returns
+ * new output ciphertexts, bit-identical to tcks_cnn_forward. Needs the library's own allocator. */
+typedef struct tcks_cnn_graph tcks_cnn_graph;
+tcks_status tcks_cnn_graph_create(const tcks_cnn* m, uint32_t count, tcks_cnn_graph** out);
+tcks_status tcks_cnn_graph_run(tcks_cnn_graph* g, const tcks_ct* const* in, tcks_ct** outs);
+void tcks_cnn_graph_free(tcks_cnn_graph* g);
 /* Export one of the model's encoded plaintexts (kind 0 conv kernel, 1 channel mask, 2 bias
  * (index 0..2), 3 FC1 diagonal, 4 FC2 diagonal) to host [level][N]; level / scale are reported. */
 tcks_status tcks_cnn_export_plaintext(const tcks_cnn* m, uint32_t kind, uint32_t index, uint64_t* host,

@@ -109,6 +109,10 @@ _SIGS = {
     "tcks_cnn_free": (None, [_vp]),
     "tcks_cnn_galois_steps": (ctypes.c_int32, [_vp, _i32p, _u32p, ctypes.c_uint32, _u32p]),
     "tcks_cnn_forward": (ctypes.c_int32, [_vp, _vp, _vpp]),
+    "tcks_cnn_forward_batch": (ctypes.c_int32, [_vp, _vpp, ctypes.c_uint32, _vpp]),
+    "tcks_cnn_graph_create": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vpp]),
+    "tcks_cnn_graph_run": (ctypes.c_int32, [_vp, _vpp, _vpp]),
+    "tcks_cnn_graph_free": (None, [_vp]),
     "tcks_cnn_export_plaintext": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint32, _u64p, ctypes.c_size_t,
                                                     _u32p, _dblp]),
 }
@@ -531,6 +535,15 @@ class CNN:
         check(lib().tcks_cnn_forward(self.h, ct.h, ctypes.byref(h)))
         return Ciphertext(self.ctx, h)
 
+    def forward_batch(self, cts) -> list:
+        ins = (_vp * len(cts))(*[c.h.value if isinstance(c.h, _vp) else c.h for c in cts])
+        outs = (_vp * len(cts))()
+        check(lib().tcks_cnn_forward_batch(self.h, ins, len(cts), outs))
+        return [Ciphertext(self.ctx, _vp(outs[i])) for i in range(len(cts))]
+
+    def graph(self, count: int) -> "CNNGraph":
+        return CNNGraph(self, count)
+
     def export_plaintext(self, kind: int, index: int):
         lv = {0: self.ctx.L, 1: self.ctx.L - 1, 2: self.ctx.L - 2 - 2 * index, 3: self.ctx.L - 3,
               4: self.ctx.L - 5}[kind]
@@ -538,3 +551,26 @@ class CNN:
         l, sc = ctypes.c_uint32(), ctypes.c_double()
         check(lib().tcks_cnn_export_plaintext(self.h, kind, index, _p(a), a.size, ctypes.byref(l), ctypes.byref(sc)))
         return a, sc.value
+
+
+class CNNGraph:
+    """The batched forward captured as a CUDA graph for `count` requests per replay."""
+
+    def __init__(self, model: CNN, count: int):
+        h = _vp()
+        check(lib().tcks_cnn_graph_create(model.h, count, ctypes.byref(h)))
+        self.model = model
+        self.count = count
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().tcks_cnn_graph_free(self.h)
+            self.h = None
+
+    def run(self, cts) -> list:
+        assert len(cts) == self.count
+        ins = (_vp * len(cts))(*[c.h.value if isinstance(c.h, _vp) else c.h for c in cts])
+        outs = (_vp * len(cts))()
+        check(lib().tcks_cnn_graph_run(self.h, ins, outs))
+        return [Ciphertext(self.model.ctx, _vp(outs[i])) for i in range(len(cts))]

@@ -83,53 +83,137 @@ const GaloisKey& galois_key_for(tcks_ctx* c, int64_t step, u32 ell) {
   return it->second;
 }
 
-void op_rescale(tcks_ctx* c, const u64* in, u32 ell, u64* out) {
+void op_rescale(tcks_ctx* c, const u64* in, u32 ell, u64* out, u32 count) {
   if (ell < 2) fail(TCKS_ERR_LEVEL_EXHAUSTED, "rescale needs level >= 2");
-  DevBuf top(c, (size_t)2 * c->N);
-  launch_rescale(c->T, in, ell, top.p, out, c->stream);
+  DevBuf top(c, (size_t)2 * count * c->N);
+  launch_rescale(c->T, in, ell, 2 * count, top.p, out, c->stream);
   check_launch("rescale");
 }
 
-void op_relinearize(tcks_ctx* c, const u64* d3, u32 ell, u64* out) {
+const KeyTable& key_table(tcks_ctx* c, const std::vector<u32>& steps, u32 ell) {
+  auto it = c->key_tables.find(steps);
+  if (it == c->key_tables.end()) {
+    std::vector<KsKey> h(steps.size());
+    u32 min_K = ~0u;
+    for (size_t i = 0; i < steps.size(); ++i) {
+      if (steps[i] == 0) {
+        h[i] = KsKey{c->rlk, c->L, 1u};
+      } else {
+        const GaloisKey& gk = galois_key_for(c, steps[i], 1);
+        h[i] = KsKey{gk.d, gk.K, (u32)galois_element(c->params.log_n, steps[i])};
+      }
+      min_K = h[i].K < min_K ? h[i].K : min_K;
+    }
+    KeyTable t;
+    t.n = (u32)h.size();
+    t.min_K = min_K;
+    t.d = (KsKey*)c->dev_alloc(sizeof(KsKey) * h.size());
+    check_cuda(cudaMemcpyAsync(t.d, h.data(), sizeof(KsKey) * h.size(), cudaMemcpyHostToDevice, c->stream),
+               "key table");
+    check_cuda(cudaStreamSynchronize(c->stream), "key table");
+    it = c->key_tables.emplace(steps, t).first;
+  }
+  if (it->second.min_K < ell) {
+    for (u32 st : steps) galois_key_for(c, st, ell);  // raises with the step that is too short
+  }
+  return it->second;
+}
+
+void op_relinearize(tcks_ctx* c, const u64* d3, u32 ell, u64* out, u32 count) {
   const size_t n = c->N;
-  DevBuf coef(c, (size_t)ell * n), digits(c, (size_t)ell * (ell + 1) * n), top(c, 2 * n);
-  launch_modup(c->T, d3 + (size_t)2 * ell * n, ell, coef.p, digits.p, c->stream);
-  KsBatch b{};
-  b.count = 1;
-  b.job[0] = KsJob{digits.p, c->rlk, out, top.p, d3, d3 + (size_t)ell * n, c->L, 1u, 0u, 0u};
-  launch_keyswitch(c->T, ell, b, c->stream);
+  const KeyTable& kt = key_table(c, {0u}, ell);
+  DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n), top(c, (size_t)count * 2 * n);
+  const u64 d3_stride = (u64)3 * ell * n;
+  launch_modup(c->T, d3 + (size_t)2 * ell * n, d3_stride, count, ell, coef.p, digits.p, c->stream);
+  KsPlan p{};
+  p.keys = kt.d;
+  p.digits = digits.p;
+  p.digits_b = (u64)ell * (ell + 1) * n;
+  p.top = top.p;
+  p.out = out;
+  p.out_b = (u64)2 * ell * n;
+  p.out_r = 0;
+  p.add0 = d3;
+  p.add0_b = d3_stride;
+  p.add1 = d3 + (size_t)ell * n;
+  p.add1_b = d3_stride;
+  p.R = 1;
+  p.B = count;
+  p.add_perm = 0;
+  launch_keyswitch(c->T, ell, p, c->stream);
   check_launch("relinearize");
+}
+
+void op_rotate_add(tcks_ctx* c, u64* base, u64 stride, u32 count, u32 ell, int32_t step) {
+  const size_t n = c->N;
+  const u32 k = step_mod(c, step);
+  if (k == 0) {  // rot by 0 is the identity: ct <- 2 ct
+    for (u32 i = 0; i < count; ++i)
+      launch_elementwise(c->T, OP_ADD, base + i * stride, base + i * stride, base + i * stride, ell, 2, c->stream);
+    return;
+  }
+  const KeyTable& kt = key_table(c, {k}, ell);
+  DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
+  DevBuf tmp(c, (size_t)count * ct_words(c, ell)), top(c, (size_t)count * 2 * n);
+  launch_modup(c->T, base + (size_t)ell * n, stride, count, ell, coef.p, digits.p, c->stream);
+  KsPlan p{};
+  p.keys = kt.d;
+  p.digits = digits.p;
+  p.digits_b = (u64)ell * (ell + 1) * n;
+  p.top = top.p;
+  p.out = tmp.p;
+  p.out_b = ct_words(c, ell);
+  p.add0 = base;
+  p.add0_b = stride;
+  p.R = 1;
+  p.B = count;
+  p.add_perm = 1;
+  launch_keyswitch(c->T, ell, p, c->stream);
+  if (stride == ct_words(c, ell)) {
+    launch_elementwise(c->T, OP_ADD, base, tmp.p, base, ell, 2 * count, c->stream);
+  } else {
+    for (u32 i = 0; i < count; ++i)
+      launch_elementwise(c->T, OP_ADD, base + i * stride, tmp.p + i * ct_words(c, ell), base + i * stride, ell, 2,
+                         c->stream);
+  }
+  check_launch("rotate-add");
 }
 
 void op_rotate_hoisted(tcks_ctx* c, const u64* ct, u32 ell, const int32_t* steps, u32 n_steps, u64* const* outs) {
   const size_t n = c->N;
-  // validate every step before launching anything
-  std::vector<const GaloisKey*> keys(n_steps, nullptr);
-  bool any = false;
+  std::vector<u32> ks;
+  std::vector<u32> where;  // output index of each non-trivial step
   for (u32 i = 0; i < n_steps; ++i) {
-    if (step_mod(c, steps[i]) == 0) continue;
-    keys[i] = &galois_key_for(c, steps[i], ell);
-    any = true;
-  }
-  for (u32 i = 0; i < n_steps; ++i)
-    if (!keys[i]) check_cuda(cudaMemcpyAsync(outs[i], ct, ct_words(c, ell) * 8, cudaMemcpyDeviceToDevice, c->stream),
-                             "rotate by 0");
-  if (!any) return;
-  DevBuf coef(c, (size_t)ell * n), digits(c, (size_t)ell * (ell + 1) * n);
-  DevBuf top(c, (size_t)KS_BATCH_MAX * 2 * n);
-  launch_modup(c->T, ct + (size_t)ell * n, ell, coef.p, digits.p, c->stream);
-  KsBatch b{};
-  for (u32 i = 0; i < n_steps; ++i) {
-    if (!keys[i]) continue;
-    const u32 g = (u32)galois_element(c->params.log_n, steps[i]);
-    b.job[b.count] =
-        KsJob{digits.p, keys[i]->d, outs[i], top.p + (size_t)b.count * 2 * n, ct, nullptr, keys[i]->K, g, 1u, 0u};
-    if (++b.count == KS_BATCH_MAX) {
-      launch_keyswitch(c->T, ell, b, c->stream);
-      b.count = 0;
+    const u32 k = step_mod(c, steps[i]);
+    if (k == 0) {
+      check_cuda(cudaMemcpyAsync(outs[i], ct, ct_words(c, ell) * 8, cudaMemcpyDeviceToDevice, c->stream),
+                 "rotate by 0");
+    } else {
+      ks.push_back(k);
+      where.push_back(i);
     }
   }
-  launch_keyswitch(c->T, ell, b, c->stream);
+  if (ks.empty()) return;
+  const KeyTable& kt = key_table(c, ks, ell);
+  const u32 R = (u32)ks.size();
+  DevBuf coef(c, (size_t)ell * n), digits(c, (size_t)ell * (ell + 1) * n);
+  DevBuf tmp(c, (size_t)R * ct_words(c, ell)), top(c, (size_t)R * 2 * n);
+  launch_modup(c->T, ct + (size_t)ell * n, 0, 1, ell, coef.p, digits.p, c->stream);
+  KsPlan p{};
+  p.keys = kt.d;
+  p.digits = digits.p;
+  p.top = top.p;
+  p.out = tmp.p;
+  p.out_r = ct_words(c, ell);
+  p.add0 = ct;
+  p.R = R;
+  p.B = 1;
+  p.add_perm = 1;
+  launch_keyswitch(c->T, ell, p, c->stream);
+  for (u32 r = 0; r < R; ++r)
+    check_cuda(cudaMemcpyAsync(outs[where[r]], tmp.p + (size_t)r * ct_words(c, ell), ct_words(c, ell) * 8,
+                               cudaMemcpyDeviceToDevice, c->stream),
+               "rotate copy");
   check_launch("rotate");
 }
 
@@ -170,6 +254,11 @@ void tcks_ctx::dev_free(void* p) {
     alloc.free(p, (void*)stream, alloc.user);
   else
     cudaFreeAsync(p, stream);
+}
+
+void tcks_ctx::keys_changed() {
+  for (auto& kv : key_tables) dev_free(kv.second.d);
+  key_tables.clear();
 }
 
 tcks::u64 tcks_ctx::key_bytes() const {
@@ -325,6 +414,7 @@ tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32
 void tcks_ctx_free(tcks_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  c->keys_changed();
   for (auto& kv : c->galois) c->dev_free(kv.second.d);
   void* bufs[] = {c->d_mods, c->d_pairs, c->d_tw, c->d_slot, c->d_zeta, c->d_qwords, c->d_status, c->sk, c->pk, c->rlk};
   for (void* b : bufs) c->dev_free(b);
@@ -361,6 +451,7 @@ tcks_status tcks_gen_galois_keys(tcks_ctx* c, const int32_t* steps, uint32_t n_s
   if (!c || (n_steps && !steps)) fail(TCKS_ERR_INVALID_ARG, "null argument");
   const u32 K = max_level == 0 ? c->L : max_level;
   if (K > c->L) fail(TCKS_ERR_INVALID_ARG, "max_level exceeds the number of data primes");
+  c->keys_changed();
   for (u32 i = 0; i < n_steps; ++i) {
     const u32 k = step_mod(c, steps[i]);
     if (k == 0) continue;
@@ -429,6 +520,7 @@ tcks_status tcks_import_key(tcks_ctx* c, uint32_t kind, int32_t step, uint32_t k
     if (K > c->L) fail(TCKS_ERR_INVALID_ARG, "key_level exceeds L");
     const size_t words = (size_t)K * 2 * (K + 1) * c->N;
     if (n_words != words) fail(TCKS_ERR_INVALID_ARG, "n_words does not match the key layout");
+    c->keys_changed();
     auto it = c->galois.find(k);
     if (it != c->galois.end()) {
       c->dev_free(it->second.d);
@@ -490,7 +582,7 @@ tcks_status tcks_decode(tcks_ctx* c, const tcks_pt* pt, double* out, size_t n) {
   if (c->params.log_n > 14) fail(TCKS_ERR_UNSUPPORTED, "decoding is implemented for N <= 2^14");
   const size_t N = c->N;
   DevBuf coef(c, (size_t)pt->level * N), p(c, N), z(c, n ? n : 1);
-  launch_ntt(c->T, true, pt->d, N, coef.p, N, pt->level, 0, pt->level, c->stream);
+  launch_ntt(c->T, true, pt->d, 0, coef.p, 0, pt->level, 0, pt->level, c->stream);
   launch_crt_compose(c->T, coef.p, pt->level, c->d_qwords, (double*)p.p, c->stream);
   launch_decode_slots(c->T, c->F, (const double*)p.p, pt->scale, (u32)n, (double*)z.p, c->stream);
   check_launch("decode");
@@ -659,7 +751,7 @@ tcks_status tcks_mul(const tcks_ct* a, const tcks_ct* b, tcks_ct** out) {
   const bool rescale = (c->flags & TCKS_AUTO_RESCALE) != 0;
   if (rescale && ell < 2) fail(TCKS_ERR_LEVEL_EXHAUSTED, "multiply with auto-rescale needs level >= 2");
   DevBuf d3(c, (size_t)3 * ell * c->N);
-  launch_tensor(c->T, a->d, b->d, d3.p, ell, c->stream);
+  launch_tensor(c->T, a->d, b->d, d3.p, ell, 1, c->stream);
   check_launch("tensor");
   const double sc = a->scale * b->scale;
   if (!rescale) {
@@ -713,9 +805,9 @@ tcks_status tcks_ntt_inplace(tcks_ctx* c, uint64_t* d_limbs, uint32_t polys, uin
   TCKS_API_BEGIN
   if (!c || !d_limbs) fail(TCKS_ERR_INVALID_ARG, "null argument");
   if (level < 1 || level > c->L + 1) fail(TCKS_ERR_INVALID_ARG, "level out of range");
-  if (c->params.log_n > 14) fail(TCKS_ERR_UNSUPPORTED, "single-pass transforms are implemented for N <= 2^14");
   const u64 n = c->N;
-  launch_ntt(c->T, inverse != 0, d_limbs, n, d_limbs, n, polys * level, 0, level, c->stream);
+  launch_ntt(c->T, inverse != 0, d_limbs, (u64)level * n, d_limbs, (u64)level * n, polys * level, 0, level,
+             c->stream);
   check_launch("ntt");
   TCKS_API_END
 }
@@ -858,7 +950,7 @@ tcks_status tcks_vecmat_plain(const tcks_ct* a, const tcks_matrix* M, tcks_ct** 
   if (a->level < 2) fail(TCKS_ERR_LEVEL_EXHAUSTED, "vecmat needs level >= 2");
   tcks_ct* r = new_ct(c, a->level - 1, a->scale * M->scale / (double)c->host.chain[a->level - 1]);
   try {
-    op_vecmat(c, a->d, a->level, M, r->d);
+    op_vecmat(c, a->d, 0, 1, a->level, M, r->d);
   } catch (...) {
     free_ct(r);
     throw;

@@ -35,27 +35,6 @@ struct tcks_cnn {
 
 namespace tcks {
 
-// ct_i <- ct_i + rot(ct_i, step) for `count` ciphertexts at once: one ModUp per ciphertext, one
-// key-switch launch for all of them.
-static void rotate_add_many(tcks_ctx* c, u64* const* cts, u32 count, u32 ell, int32_t step) {
-  const size_t n = c->N;
-  const GaloisKey& gk = galois_key_for(c, step, ell);
-  const u32 g = (u32)galois_element(c->params.log_n, step);
-  DevBuf coef(c, (size_t)ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
-  DevBuf tmp(c, (size_t)count * ct_words(c, ell)), top(c, (size_t)count * 2 * n);
-  KsBatch b{};
-  for (u32 i = 0; i < count; ++i) {
-    u64* d = digits.p + (size_t)i * ell * (ell + 1) * n;
-    launch_modup(c->T, cts[i] + (size_t)ell * n, ell, coef.p, d, c->stream);
-    b.job[b.count++] = KsJob{d, gk.d, tmp.p + (size_t)i * ct_words(c, ell), top.p + (size_t)i * 2 * n, cts[i],
-                             nullptr, gk.K, g, 1u, 0u};
-  }
-  launch_keyswitch(c->T, ell, b, c->stream);
-  for (u32 i = 0; i < count; ++i)
-    launch_elementwise(c->T, OP_ADD, cts[i], tmp.p + (size_t)i * ct_words(c, ell), cts[i], ell, 2, c->stream);
-  check_launch("rotate-add batch");
-}
-
 static int ceil_log2(u32 x) {
   int r = 0;
   while ((1u << r) < x) ++r;
@@ -78,59 +57,74 @@ static void schedule_scales(const tcks_cnn* m, double s_in, double delta, double
   *s_fc2 = s;
 }
 
-static void cnn_forward_dev(const tcks_cnn* m, const u64* in, u64* out) {
+// Forward pass of `count` requests at once: inputs in + r * in_stride ([2][L][N] each), outputs
+// out [count][2][L-6][N]. Every stage runs on the whole batch: the 4 * count channel ciphertexts
+// rotate together, the relinearizations and rescales take the batch in one launch each, and the two
+// vector x matrix products process every request's rotations in shared launches.
+static void cnn_forward_dev(const tcks_cnn* m, const u64* in, u64 in_stride, u32 count, u64* out) {
   tcks_ctx* c = m->ctx;
   const size_t n = c->N;
   const u32 L = m->L, K = m->kernels;
-  // conv [L-1]
-  std::vector<DevBuf> chans;
-  std::vector<u64*> cp;
+  const u64 w_in = ct_words(c, L);
+  DevBuf xin;
+  const u64* x = in;
+  if (count > 1 && in_stride != w_in) {  // gather the inputs into one contiguous batch
+    xin = DevBuf(c, (size_t)count * w_in);
+    for (u32 r = 0; r < count; ++r)
+      check_cuda(cudaMemcpyAsync(xin.p + r * w_in, in + r * in_stride, w_in * 8, cudaMemcpyDeviceToDevice, c->stream),
+                 "gather");
+    x = xin.p;
+  }
+  // conv [L-1]: channel k of request r at chans + (k * count + r) * w1
+  const u64 w1 = ct_words(c, L - 1);
+  DevBuf chans(c, (size_t)K * count * w1);
   {
-    DevBuf prod(c, ct_words(c, L));
+    DevBuf prod(c, (size_t)count * w_in);
     for (u32 k = 0; k < K; ++k) {
-      chans.emplace_back(c, ct_words(c, L - 1));
-      launch_elementwise(c->T, OP_MUL_PLAIN, in, m->conv[k], prod.p, L, 2, c->stream);
-      op_rescale(c, prod.p, L, chans.back().p);
-      cp.push_back(chans.back().p);
+      launch_elementwise(c->T, OP_MUL_PLAIN, x, m->conv[k], prod.p, L, 2 * count, c->stream);
+      op_rescale(c, prod.p, L, chans.p + (size_t)k * count * w1, count);
     }
   }
   const int rsteps = ceil_log2(m->taps);
-  for (int i = 0; i < rsteps; ++i) rotate_add_many(c, cp.data(), K, L - 1, (int32_t)(m->windows << i));
+  for (int i = 0; i < rsteps; ++i) op_rotate_add(c, chans.p, w1, K * count, L - 1, (int32_t)(m->windows << i));
   // pack [L-2] + bias
-  DevBuf v(c, ct_words(c, L - 2));
+  const u64 w2 = ct_words(c, L - 2);
+  DevBuf v(c, (size_t)count * w2);
   {
-    DevBuf prod(c, ct_words(c, L - 1)), t(c, ct_words(c, L - 2));
+    DevBuf prod(c, (size_t)count * w1), t(c, (size_t)count * w2);
     for (u32 k = 0; k < K; ++k) {
-      launch_elementwise(c->T, OP_MUL_PLAIN, cp[k], m->masks[k], prod.p, L - 1, 2, c->stream);
-      op_rescale(c, prod.p, L - 1, k == 0 ? v.p : t.p);
-      if (k) launch_elementwise(c->T, OP_ADD, v.p, t.p, v.p, L - 2, 2, c->stream);
+      launch_elementwise(c->T, OP_MUL_PLAIN, chans.p + (size_t)k * count * w1, m->masks[k], prod.p, L - 1, 2 * count,
+                         c->stream);
+      op_rescale(c, prod.p, L - 1, k == 0 ? v.p : t.p, count);
+      if (k) launch_elementwise(c->T, OP_ADD, v.p, t.p, v.p, L - 2, 2 * count, c->stream);
     }
-    launch_elementwise(c->T, OP_ADD_PLAIN, v.p, m->bias[0], v.p, L - 2, 2, c->stream);
+    launch_elementwise(c->T, OP_ADD_PLAIN, v.p, m->bias[0], v.p, L - 2, 2 * count, c->stream);
   }
-  chans.clear();
+  chans = DevBuf();
   // square [L-3]
-  DevBuf sq1(c, ct_words(c, L - 3));
+  DevBuf sq1(c, (size_t)count * ct_words(c, L - 3));
   {
-    DevBuf d3(c, (size_t)3 * (L - 2) * n), rel(c, ct_words(c, L - 2));
-    launch_tensor(c->T, v.p, v.p, d3.p, L - 2, c->stream);
-    op_relinearize(c, d3.p, L - 2, rel.p);
-    op_rescale(c, rel.p, L - 2, sq1.p);
+    DevBuf d3(c, (size_t)count * 3 * (L - 2) * n), rel(c, (size_t)count * w2);
+    launch_tensor(c->T, v.p, v.p, d3.p, L - 2, count, c->stream);
+    op_relinearize(c, d3.p, L - 2, rel.p, count);
+    op_rescale(c, rel.p, L - 2, sq1.p, count);
   }
   // FC1 [L-4] + bias
-  DevBuf f1(c, ct_words(c, L - 4));
-  op_vecmat(c, sq1.p, L - 3, m->fc1, f1.p);
-  launch_elementwise(c->T, OP_ADD_PLAIN, f1.p, m->bias[1], f1.p, L - 4, 2, c->stream);
+  const u64 w4 = ct_words(c, L - 4);
+  DevBuf f1(c, (size_t)count * w4);
+  op_vecmat(c, sq1.p, ct_words(c, L - 3), count, L - 3, m->fc1, f1.p);
+  launch_elementwise(c->T, OP_ADD_PLAIN, f1.p, m->bias[1], f1.p, L - 4, 2 * count, c->stream);
   // square [L-5]
-  DevBuf sq2(c, ct_words(c, L - 5));
+  DevBuf sq2(c, (size_t)count * ct_words(c, L - 5));
   {
-    DevBuf d3(c, (size_t)3 * (L - 4) * n), rel(c, ct_words(c, L - 4));
-    launch_tensor(c->T, f1.p, f1.p, d3.p, L - 4, c->stream);
-    op_relinearize(c, d3.p, L - 4, rel.p);
-    op_rescale(c, rel.p, L - 4, sq2.p);
+    DevBuf d3(c, (size_t)count * 3 * (L - 4) * n), rel(c, (size_t)count * w4);
+    launch_tensor(c->T, f1.p, f1.p, d3.p, L - 4, count, c->stream);
+    op_relinearize(c, d3.p, L - 4, rel.p, count);
+    op_rescale(c, rel.p, L - 4, sq2.p, count);
   }
   // FC2 [L-6] + bias
-  op_vecmat(c, sq2.p, L - 5, m->fc2, out);
-  launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[2], out, L - 6, 2, c->stream);
+  op_vecmat(c, sq2.p, ct_words(c, L - 5), count, L - 5, m->fc2, out);
+  launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[2], out, L - 6, 2 * count, c->stream);
   check_launch("cnn forward");
 }
 
@@ -140,6 +134,7 @@ static void cnn_forward_dev(const tcks_cnn* m, const u64* in, u64* out) {
 namespace tcks {
 tcks_status abi_record(tcks_status code, const std::string& msg);
 void abi_clear();
+void count_launches(u64 n);
 }  // namespace tcks
 
 #define CNN_BEGIN try {
@@ -291,12 +286,136 @@ tcks_status tcks_cnn_forward(const tcks_cnn* m, const tcks_ct* in, tcks_ct** out
   if (in->scale != m->in_scale) fail(TCKS_ERR_SCALE_MISMATCH, "the network takes a ciphertext at the context scale");
   tcks_ct* r = new_ct(c, m->L - 6, m->out_scale);
   try {
-    cnn_forward_dev(m, in->d, r->d);
+    cnn_forward_dev(m, in->d, 0, 1, r->d);
   } catch (...) {
     free_ct(r);
     throw;
   }
   *out = r;
+  CNN_END
+}
+
+tcks_status tcks_cnn_forward_batch(const tcks_cnn* m, const tcks_ct* const* in, uint32_t count, tcks_ct** outs) {
+  struct Made {  // outputs created so far, freed unless handed to the caller
+    std::vector<tcks_ct*> v;
+    ~Made() {
+      for (tcks_ct* x : v) free_ct(x);
+    }
+  } owned;
+  std::vector<tcks_ct*>& made = owned.v;
+  CNN_BEGIN
+  if (!m || !outs || (count && !in)) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  for (u32 i = 0; i < count; ++i) outs[i] = nullptr;
+  if (!count) return TCKS_OK;
+  tcks_ctx* c = m->ctx;
+  for (u32 i = 0; i < count; ++i) {
+    if (!in[i] || in[i]->ctx != c) fail(TCKS_ERR_INVALID_ARG, "ciphertext missing or of another context");
+    if (in[i]->level != m->L) fail(TCKS_ERR_LEVEL_MISMATCH, "the network takes ciphertexts at the top level");
+    if (in[i]->scale != m->in_scale) fail(TCKS_ERR_SCALE_MISMATCH, "the network takes ciphertexts at the context scale");
+  }
+  const u64 w_in = ct_words(c, m->L), w_out = ct_words(c, m->L - 6);
+  DevBuf xin(c, (size_t)count * w_in), yout(c, (size_t)count * w_out);
+  for (u32 i = 0; i < count; ++i)
+    check_cuda(cudaMemcpyAsync(xin.p + i * w_in, in[i]->d, w_in * 8, cudaMemcpyDeviceToDevice, c->stream), "gather");
+  cnn_forward_dev(m, xin.p, w_in, count, yout.p);
+  for (u32 i = 0; i < count; ++i) {
+    made.push_back(new_ct(c, m->L - 6, m->out_scale));
+    check_cuda(cudaMemcpyAsync(made.back()->d, yout.p + i * w_out, w_out * 8, cudaMemcpyDeviceToDevice, c->stream),
+               "scatter");
+  }
+  for (u32 i = 0; i < count; ++i) outs[i] = made[i];
+  made.clear();
+  CNN_END
+}
+
+// -------------------------------------------------------------------------- CUDA graphs ----
+struct tcks_cnn_graph {
+  const tcks_cnn* m;
+  u32 count;
+  u64* in;   // staging [count][2][L][N]
+  u64* out;  // staging [count][2][L-6][N]
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  u64 launches;  // kernel launches in one replay
+};
+
+void tcks_cnn_graph_free(tcks_cnn_graph* g) {
+  if (!g) return;
+  tcks_ctx* c = g->m->ctx;
+  cudaStreamSynchronize(c->stream);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  c->dev_free(g->in);
+  c->dev_free(g->out);
+  delete g;
+}
+
+tcks_status tcks_cnn_graph_create(const tcks_cnn* m, uint32_t count, tcks_cnn_graph** out) {
+  struct Guard {
+    tcks_cnn_graph* g = nullptr;
+    ~Guard() { tcks_cnn_graph_free(g); }
+  } guard;
+  CNN_BEGIN
+  if (!m || !out || !count) fail(TCKS_ERR_INVALID_ARG, "null argument or zero batch");
+  *out = nullptr;
+  tcks_ctx* c = m->ctx;
+  if (c->has_alloc) fail(TCKS_ERR_UNSUPPORTED, "graph capture needs the library's own stream-ordered pool allocator");
+  const u64 w_in = ct_words(c, m->L), w_out = ct_words(c, m->L - 6);
+  guard.g = new tcks_cnn_graph{m, count, nullptr, nullptr, nullptr, nullptr, 0};
+  tcks_cnn_graph* g = guard.g;
+  g->in = (u64*)c->dev_alloc((size_t)count * w_in * 8);
+  g->out = (u64*)c->dev_alloc((size_t)count * w_out * 8);
+  check_cuda(cudaMemsetAsync(g->in, 0, (size_t)count * w_in * 8, c->stream), "graph staging");
+  // one eager pass builds every cached key table (their host copies cannot run inside a capture)
+  cnn_forward_dev(m, g->in, w_in, count, g->out);
+  check_cuda(cudaStreamSynchronize(c->stream), "graph warm-up");
+  const u64 n0 = tcks_launch_count();
+  check_cuda(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  try {
+    cnn_forward_dev(m, g->in, w_in, count, g->out);
+  } catch (...) {
+    cudaGraph_t dead = nullptr;
+    cudaStreamEndCapture(c->stream, &dead);
+    if (dead) cudaGraphDestroy(dead);
+    throw;
+  }
+  check_cuda(cudaStreamEndCapture(c->stream, &g->graph), "end capture");
+  g->launches = tcks_launch_count() - n0;
+  check_cuda(cudaGraphInstantiate(&g->exec, g->graph, 0), "graph instantiate");
+  *out = g;
+  guard.g = nullptr;
+  CNN_END
+}
+
+tcks_status tcks_cnn_graph_run(tcks_cnn_graph* g, const tcks_ct* const* in, tcks_ct** outs) {
+  struct Made {
+    std::vector<tcks_ct*> v;
+    ~Made() {
+      for (tcks_ct* x : v) free_ct(x);
+    }
+  } owned;
+  CNN_BEGIN
+  if (!g || !in || !outs) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  const tcks_cnn* m = g->m;
+  tcks_ctx* c = m->ctx;
+  for (u32 i = 0; i < g->count; ++i) {
+    outs[i] = nullptr;
+    if (!in[i] || in[i]->ctx != c) fail(TCKS_ERR_INVALID_ARG, "ciphertext missing or of another context");
+    if (in[i]->level != m->L || in[i]->scale != m->in_scale)
+      fail(TCKS_ERR_LEVEL_MISMATCH, "the network takes ciphertexts at the top level and the context scale");
+  }
+  const u64 w_in = ct_words(c, m->L), w_out = ct_words(c, m->L - 6);
+  for (u32 i = 0; i < g->count; ++i)
+    check_cuda(cudaMemcpyAsync(g->in + i * w_in, in[i]->d, w_in * 8, cudaMemcpyDeviceToDevice, c->stream), "stage in");
+  check_cuda(cudaGraphLaunch(g->exec, c->stream), "graph launch");
+  count_launches(g->launches);
+  for (u32 i = 0; i < g->count; ++i) {
+    owned.v.push_back(new_ct(c, m->L - 6, m->out_scale));
+    check_cuda(cudaMemcpyAsync(owned.v.back()->d, g->out + i * w_out, w_out * 8, cudaMemcpyDeviceToDevice, c->stream),
+               "stage out");
+  }
+  for (u32 i = 0; i < g->count; ++i) outs[i] = owned.v[i];
+  owned.v.clear();
   CNN_END
 }
 

@@ -11,83 +11,116 @@ using namespace tcks;
 
 namespace tcks {
 
-// ct <- ct + rot(ct, step), on device buffers at level ell.
-static void rotate_add(tcks_ctx* c, u64* ct, u32 ell, int32_t step, u64* tmp) {
-  op_rotate_hoisted(c, ct, ell, &step, 1, &tmp);
-  launch_elementwise(c->T, OP_ADD, ct, tmp, ct, ell, 2, c->stream);
-  check_launch("rotate-add");
-}
-
-static int ilog2(u64 x) {
+static int ceil_log2(u64 x) {
   int r = 0;
   while ((1ull << r) < x) ++r;
   return r;
 }
 
 void op_sum(tcks_ctx* c, u64* ct, u32 ell) {
-  DevBuf tmp(c, ct_words(c, ell));
-  for (u32 m = 0; m + 1 < c->params.log_n; ++m) rotate_add(c, ct, ell, (int32_t)(1u << m), tmp.p);
+  for (u32 m = 0; m + 1 < c->params.log_n; ++m) op_rotate_add(c, ct, 0, 1, ell, (int32_t)(1u << m));
 }
 
-// y = v M by the diagonal method with a replicated input (O21 of the hot-path reading).
-void op_vecmat(tcks_ctx* c, const u64* ct_in, u32 ell, const tcks_matrix* M, u64* out) {
+// y = v M by the diagonal method with a replicated input, for `count` ciphertexts at once:
+//   replicate (rotate-and-add by N/2 - rows*2^i), ModUp of c1 once per ciphertext, then for every
+//   rotation step k = 1..rows-1 the P-limb stage of the key switch (k_ks_inner_p) and the fused
+//   ModDown + multiply-accumulate with the diagonal d_k (k_vecmat_acc), the k = 0 term and the
+//   partial sums folded by k_vecmat_reduce, and the rescale. Rotations are processed in blocks so
+//   that the P-limb scratch stays bounded (~512 MB).
+void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell, const tcks_matrix* M, u64* out) {
   const size_t n = c->N;
   const u32 rows = M->rows;
   const u32 slots = c->N / 2;
-  // validate keys first
+  const u64 cw = ct_words(c, ell);
   std::vector<int32_t> rep;
   for (u32 m = 0; ((u64)rows << m) < slots; ++m) rep.push_back((int32_t)(slots - (rows << m)));
-  for (int32_t s : rep) galois_key_for(c, s, ell);
-  for (u32 k = 1; k < rows; ++k) galois_key_for(c, (int32_t)k, ell);
-  DevBuf ct(c, ct_words(c, ell));
-  check_cuda(cudaMemcpyAsync(ct.p, ct_in, ct_words(c, ell) * 8, cudaMemcpyDeviceToDevice, c->stream), "vecmat copy");
-  {
-    DevBuf tmp(c, ct_words(c, ell));
-    for (int32_t s : rep) rotate_add(c, ct.p, ell, s, tmp.p);
+  std::vector<u32> steps;
+  for (u32 k = 1; k < rows; ++k) steps.push_back(k);
+  for (int32_t s : rep) galois_key_for(c, s, ell);  // validate before launching anything
+  const KeyTable* kt = steps.empty() ? nullptr : &key_table(c, steps, ell);
+  DevBuf ct(c, (size_t)count * cw);
+  if (ct_stride == cw || count == 1) {
+    check_cuda(cudaMemcpyAsync(ct.p, ct_in, (size_t)count * cw * 8, cudaMemcpyDeviceToDevice, c->stream), "copy");
+  } else {
+    for (u32 i = 0; i < count; ++i)
+      check_cuda(cudaMemcpyAsync(ct.p + i * cw, ct_in + i * ct_stride, cw * 8, cudaMemcpyDeviceToDevice, c->stream),
+                 "copy");
   }
+  for (int32_t s : rep) op_rotate_add(c, ct.p, cw, count, ell, s);
+  DevBuf acc(c, (size_t)count * cw);
+  if (steps.empty()) {
+    launch_elementwise(c->T, OP_MUL_PLAIN, ct.p, M->d, acc.p, ell, 2 * count, c->stream);
+    op_rescale(c, acc.p, ell, out, count);
+    return;
+  }
+  DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
+  launch_modup(c->T, ct.p + (size_t)ell * n, cw, count, ell, coef.p, digits.p, c->stream);
+  const u32 R = rows - 1;
+  const u64 per_rot = (u64)count * 2 * n;  // P-limb scratch words per rotation
+  u32 RB = (u32)std::max<u64>(1, ((u64)64 << 20) / per_rot);  // 512 MB of scratch per block
+  if (RB > R) RB = R;
+  // chunks per block: enough CTAs (count * 2 ell * chunks) to fill the GPU a few times over
+  const u32 target = 152 * 4;
+  u32 chunks_pb = (u32)std::min<u64>(RB, std::max<u64>(1, (target + count * 2 * ell - 1) / (count * 2 * ell)));
+  const u32 chunk = (RB + chunks_pb - 1) / chunks_pb;
+  chunks_pb = (RB + chunk - 1) / chunk;
+  const u32 blocks = (R + RB - 1) / RB;
+  DevBuf top(c, (size_t)per_rot * RB);
+  DevBuf partial(c, (size_t)count * blocks * chunks_pb * cw);
   const u64 diag_stride = (u64)M->level * n;
-  DevBuf acc(c, ct_words(c, ell));
-  launch_elementwise(c->T, OP_MUL_PLAIN, ct.p, M->d, acc.p, ell, 2, c->stream);  // k = 0
-  // hoisted rotations k = 1..rows-1, KS_BATCH_MAX per launch, each chunk multiply-accumulated
-  DevBuf coef(c, (size_t)ell * n), digits(c, (size_t)ell * (ell + 1) * n);
-  launch_modup(c->T, ct.p + (size_t)ell * n, ell, coef.p, digits.p, c->stream);
-  const u32 chunk = KS_BATCH_MAX;
-  DevBuf rots(c, (size_t)chunk * ct_words(c, ell)), top(c, (size_t)chunk * 2 * n);
-  for (u32 k0 = 1; k0 < rows; k0 += chunk) {
-    const u32 cnt = (rows - k0) < chunk ? (rows - k0) : chunk;
-    KsBatch b{};
-    b.count = cnt;
-    for (u32 t = 0; t < cnt; ++t) {
-      const u32 k = k0 + t;
-      const GaloisKey& gk = galois_key_for(c, (int32_t)k, ell);
-      b.job[t] = KsJob{digits.p,
-                       gk.d,
-                       rots.p + (size_t)t * ct_words(c, ell),
-                       top.p + (size_t)t * 2 * n,
-                       ct.p,
-                       nullptr,
-                       gk.K,
-                       (u32)galois_element(c->params.log_n, k),
-                       1u,
-                       0u};
-    }
-    launch_keyswitch(c->T, ell, b, c->stream);
-    launch_mulacc(c->T, acc.p, rots.p, ct_words(c, ell), M->d + (size_t)k0 * diag_stride, diag_stride, cnt, ell,
-                  c->stream);
-    check_launch("vecmat chunk");
+  u32 total_chunks = 0;
+  for (u32 rb0 = 0; rb0 < R; rb0 += RB) {
+    const u32 rbn = std::min(RB, R - rb0);
+    KsPlan p{};
+    p.keys = kt->d + rb0;
+    p.digits = digits.p;
+    p.digits_b = (u64)ell * (ell + 1) * n;
+    p.top = top.p;
+    p.out = nullptr;
+    p.R = rbn;
+    p.B = count;
+    launch_ks_inner_p(c->T, ell, p, c->stream);
+    VecmatPlan v{};
+    v.keys = kt->d + rb0;
+    v.digits = digits.p;
+    v.digits_b = (u64)ell * (ell + 1) * n;
+    v.top = top.p;
+    v.ct = ct.p;
+    v.ct_b = cw;
+    v.diag = M->d + (size_t)rb0 * diag_stride;
+    v.diag_stride = diag_stride;
+    v.R = rbn;
+    v.B = count;
+    v.chunk = chunk;
+    v.chunks = (rbn + chunk - 1) / chunk;
+    // partials of this block: [count][chunks][...] laid after the previous blocks' partials per request
+    v.partial = partial.p + (size_t)total_chunks * cw;
+    v.partial_b = (u64)blocks * chunks_pb * cw;
+    launch_vecmat_acc(c->T, ell, v, c->stream);
+    total_chunks += v.chunks;
+    check_launch("vecmat block");
   }
-  op_rescale(c, acc.p, ell, out);
+  VecmatPlan red{};
+  red.ct = ct.p;
+  red.ct_b = cw;
+  red.diag = M->d;
+  red.partial = partial.p;
+  red.partial_b = (u64)blocks * chunks_pb * cw;
+  red.B = count;
+  red.chunks = total_chunks;
+  launch_vecmat_reduce(c->T, ell, red, acc.p, c->stream);
+  op_rescale(c, acc.p, ell, out, count);
+  check_launch("vecmat");
 }
 
 // One im2col convolution kernel (§3.2): rescale(ct * kernel), then rotate-and-add by windows*2^i.
 void op_conv(tcks_ctx* c, const u64* ct, u32 ell, const u64* kernel_pt, u32 taps, u32 windows, u64* out) {
-  const int steps = ilog2(taps);
+  const int steps = ceil_log2(taps);
   for (int m = 0; m < steps; ++m) galois_key_for(c, (int32_t)(windows << m), ell - 1);
   DevBuf prod(c, ct_words(c, ell));
   launch_elementwise(c->T, OP_MUL_PLAIN, ct, kernel_pt, prod.p, ell, 2, c->stream);
   op_rescale(c, prod.p, ell, out);
-  DevBuf tmp(c, ct_words(c, ell - 1));
-  for (int m = 0; m < steps; ++m) rotate_add(c, out, ell - 1, (int32_t)(windows << m), tmp.p);
+  for (int m = 0; m < steps; ++m) op_rotate_add(c, out, 0, 1, ell - 1, (int32_t)(windows << m));
 }
 
 }  // namespace tcks

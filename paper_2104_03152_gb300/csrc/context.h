@@ -24,6 +24,13 @@ struct GaloisKey {
   u32 K = 0;
 };
 
+// Device array of KsKey entries for a list of rotation steps (step 0 = the relinearization key).
+struct KeyTable {
+  KsKey* d = nullptr;
+  u32 n = 0;
+  u32 min_K = 0;  // smallest key level in the table
+};
+
 // Status with message, raised by internal helpers and turned into a return code at the ABI.
 struct Error {
   tcks_status code;
@@ -59,7 +66,11 @@ struct tcks_ctx {
   tcks::u64* pk = nullptr;   // [2][L][N]
   tcks::u64* rlk = nullptr;  // [L][2][L+1][N]
   std::map<tcks::u32, tcks::GaloisKey> galois;  // step mod N/2 -> key
+  std::map<std::vector<tcks::u32>, tcks::KeyTable> key_tables;  // cached device key tables
   tcks::u64 table_bytes = 0;
+
+  // Galois keys changed: drop every cached key table.
+  void keys_changed();
 
   void* dev_alloc(size_t bytes);
   void dev_free(void* p);
@@ -98,6 +109,15 @@ struct DevBuf {
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
   DevBuf(DevBuf&& o) noexcept : ctx(o.ctx), p(o.p) { o.p = nullptr; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) {
+      if (p) ctx->dev_free(p);
+      ctx = o.ctx;
+      p = o.p;
+      o.p = nullptr;
+    }
+    return *this;
+  }
   ~DevBuf() {
     if (p) ctx->dev_free(p);
   }
@@ -120,17 +140,23 @@ tcks_pt* new_pt(tcks_ctx* c, u32 level, double scale);
 void free_ct(tcks_ct* ct);
 
 // Internal ops on device buffers (results written to caller-provided buffers).
-void op_rescale(tcks_ctx* c, const u64* in, u32 ell, u64* out);
-// Relinearize [3][ell][N] -> [2][ell][N].
-void op_relinearize(tcks_ctx* c, const u64* d3, u32 ell, u64* out);
+// Rescale `count` ciphertexts [count][2][ell][N] -> [count][2][ell-1][N].
+void op_rescale(tcks_ctx* c, const u64* in, u32 ell, u64* out, u32 count = 1);
+// Relinearize `count` tensor products [count][3][ell][N] -> [count][2][ell][N].
+void op_relinearize(tcks_ctx* c, const u64* d3, u32 ell, u64* out, u32 count = 1);
 // Rotations of one ciphertext from shared digits: outs[i] = rot(ct, steps[i]) (each [2][ell][N]).
 void op_rotate_hoisted(tcks_ctx* c, const u64* ct, u32 ell, const int32_t* steps, u32 n, u64* const* outs);
+// ct_i <- ct_i + rot(ct_i, step) for count ciphertexts at base + i * stride (words).
+void op_rotate_add(tcks_ctx* c, u64* base, u64 stride, u32 count, u32 ell, int32_t step);
 const GaloisKey& galois_key_for(tcks_ctx* c, int64_t step, u32 ell);
+// Device key table for `steps` (0 = relinearization key); every key must cover level ell.
+const KeyTable& key_table(tcks_ctx* c, const std::vector<u32>& steps, u32 ell);
 u32 step_mod(const tcks_ctx* c, int64_t step);
 void encode_into(tcks_ctx* c, const double* d_v, size_t n, double scale, u32 level, u64* pt_out);
 // composite.cpp
 void op_sum(tcks_ctx* c, u64* ct, u32 ell);  // in place
-void op_vecmat(tcks_ctx* c, const u64* ct, u32 ell, const tcks_matrix* M, u64* out);  // out at ell - 1
+// count ciphertexts ct + i * ct_stride at level ell -> out [count][2][ell-1][N]
+void op_vecmat(tcks_ctx* c, const u64* ct, u64 ct_stride, u32 count, u32 ell, const tcks_matrix* M, u64* out);
 void op_conv(tcks_ctx* c, const u64* ct, u32 ell, const u64* kernel_pt, u32 taps, u32 windows, u64* out);
 
 }  // namespace tcks

@@ -1,93 +1,90 @@
 // Core RNS kernels: batched NTT / INTT, element-wise ops, the tensor product, rescale and the
 // key-switching pipeline (ModUp, inner product with the key, ModDown), with the Galois
-// automorphism folded into the inner product's reads.
+// automorphism folded into the inner product's reads, and the fused ModDown + multiply-accumulate
+// of the vector x plain-matrix product.
 //
-// Every kernel that transforms a limb stages it in shared memory (one CTA per limb, N <= 2^14),
-// so a limb crosses HBM once per kernel; the prologue that fills shared memory and the epilogue
-// that drains it carry the surrounding element-wise work (lifts, products, combines).
+// Every kernel that transforms a limb stages it in shared memory: one CTA per limb for N <= 2^14, a
+// cluster of 2 or 4 CTAs (each holding a contiguous slice, cross-slice stages over DSMEM) for
+// N = 2^15, 2^16. A limb crosses HBM once per kernel; the prologue that fills shared memory and the
+// epilogue that drains it carry the surrounding element-wise work (lifts, products, combines).
+// Jobs are laid out on blockIdx.x (limb jobs, clusters along x) and blockIdx.y / z (requests and
+// rotations), so one launch carries a whole batch.
 #include <cuda_runtime.h>
 
 #include <map>
 #include <mutex>
 #include <string>
+#include <utility>
 
 #include "context.h"
 #include "kernels.h"
+#include "limb_launch.cuh"
 #include "ntt.cuh"
 
 namespace tcks {
 
-// Opt a kernel in to more than 48 KB of dynamic shared memory, once per kernel and size (the
-// attribute is per function, so the registry is keyed by the kernel's address).
+// Opt a kernel in to more than 48 KB of dynamic shared memory and to the largest shared-memory
+// carveout, once per kernel (the attributes are per function, so the registry is keyed by address).
 void ensure_smem(const void* kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return;
   static std::mutex mu;
   static std::map<const void*, size_t> granted;
   std::lock_guard<std::mutex> lock(mu);
-  size_t& g = granted[kernel];
-  if (bytes > g) {
+  auto it = granted.find(kernel);
+  if (it == granted.end()) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    it = granted.emplace(kernel, (size_t)48 * 1024).first;
+  }
+  if (bytes > it->second) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    g = bytes;
+    it->second = bytes;
   }
 }
+
+u32 ntt_threads(u32 log_n) { return limb_shape(log_n).threads; }
 
 // --------------------------------------------------------------------------- batched NTT ----
-// Job b (blockIdx.x): src + b*src_stride -> dst + b*dst_stride, prime = mod_base + b % mod_period.
-template <bool INVERSE>
-__global__ void k_ntt(DevTables T, const u64* __restrict__ src, u64 src_stride, u64* __restrict__ dst,
-                      u64 dst_stride, u32 mod_base, u32 mod_period) {
+// Job j: limb (j % per) of entry (j / per): src + (j/per)*src_outer + (j%per)*N, prime mod_base + j%per.
+template <bool INVERSE, int LC>
+__global__ void k_ntt(DevTables T, const u64* __restrict__ src, u64 src_outer, u64* __restrict__ dst, u64 dst_outer,
+                      u32 mod_base, u32 per) {
   extern __shared__ u64 s[];
-  const u32 n = 1u << T.log_n;
-  const u32 b = blockIdx.x;
-  const u32 mod = mod_base + b % mod_period;
+  const Slice sl = slice_of<LC>(T);
+  const u64 n = 1ull << T.log_n;
+  const u32 jo = sl.job / per, ji = sl.job % per;
+  const u32 mod = mod_base + ji;
   const ModConst m = T.mods[mod];
-  const u64* in = src + (u64)b * src_stride;
-  u64* out = dst + (u64)b * dst_stride;
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) s[k] = in[k];
+  const u64* in = src + jo * src_outer + ji * n + sl.off;
+  u64* out = dst + jo * dst_outer + ji * n + sl.off;
+  for (u32 k = 2 * threadIdx.x; k < sl.ns; k += 2 * blockDim.x) {
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(in + k);
+    s[k] = v.x;
+    s[k + 1] = v.y;
+  }
   __syncthreads();
   if (INVERSE) {
-    ntt_inv_smem(s, T, mod);
-    for (u32 k = threadIdx.x; k < n; k += blockDim.x) out[k] = inv_final(s[k], m);
+    ntt_inv_slice<LC>(s, T, mod, sl.rank);
+    for (u32 k = 2 * threadIdx.x; k < sl.ns; k += 2 * blockDim.x)
+      *reinterpret_cast<ulonglong2*>(out + k) = make_ulonglong2(inv_final(s[k], m), inv_final(s[k + 1], m));
   } else {
-    ntt_fwd_smem(s, T, mod);
-    for (u32 k = threadIdx.x; k < n; k += blockDim.x) out[k] = fwd_final(s[k], m.q);
+    ntt_fwd_slice<LC>(s, T, mod, sl.rank);
+    for (u32 k = 2 * threadIdx.x; k < sl.ns; k += 2 * blockDim.x)
+      *reinterpret_cast<ulonglong2*>(out + k) = make_ulonglong2(fwd_final(s[k], m.q), fwd_final(s[k + 1], m.q));
   }
 }
 
-u32 ntt_threads(u32 log_n) {
-  const u32 n = 1u << log_n;
-  u32 t = n / 8;
-  if (t < 32) t = 32;
-  if (t > 1024) t = 1024;
-  return t;
-}
-
-static size_t smem_bytes(u32 log_n) { return ((size_t)8) << log_n; }
-
-template <typename K>
-static void allow_smem(K kernel, size_t bytes) {
-  ensure_smem((const void*)kernel, bytes);
-}
-
-void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_stride, u64* dst, u64 dst_stride,
-                u32 count, u32 mod_base, u32 mod_period, cudaStream_t st) {
+void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_outer, u64* dst, u64 dst_outer, u32 count,
+                u32 mod_base, u32 per, cudaStream_t st) {
   if (!count) return;
-  const size_t sm = smem_bytes(T.log_n);
   Launch L(inverse ? K_NTT_INV : K_NTT_FWD, st, 16.0 * count * (1u << T.log_n));
-  if (inverse) {
-    allow_smem(k_ntt<true>, sm);
-    k_ntt<true><<<count, ntt_threads(T.log_n), sm, st>>>(T, src, src_stride, dst, dst_stride, mod_base, mod_period);
-  } else {
-    allow_smem(k_ntt<false>, sm);
-    k_ntt<false><<<count, ntt_threads(T.log_n), sm, st>>>(T, src, src_stride, dst, dst_stride, mod_base, mod_period);
-  }
+  if (inverse)
+    launch_limb(k_ntt<true, 0>, k_ntt<true, 1>, k_ntt<true, 2>, count, 1, T.log_n, st, 0, T, src, src_outer, dst, dst_outer, mod_base, per);
+  else
+    launch_limb(k_ntt<false, 0>, k_ntt<false, 1>, k_ntt<false, 2>, count, 1, T.log_n, st, 0, T, src, src_outer, dst, dst_outer, mod_base, per);
 }
 
 // ------------------------------------------------------------------------ element-wise ops ----
-// Operands laid out [polys][ell][N]; element e belongs to limb (e >> log_n) % ell.
-enum : u32 { EW_ADD = OP_ADD, EW_SUB = OP_SUB, EW_NEG = OP_NEG, EW_MUL_PLAIN = OP_MUL_PLAIN, EW_ADD_PLAIN = OP_ADD_PLAIN,
-             EW_SUB_PLAIN = OP_SUB_PLAIN };
-
+// Operands laid out [polys][ell][N] (a batch of ciphertexts is [2B][ell][N]); element e belongs to
+// limb (e >> log_n) % ell and component ((e >> log_n) / ell) % 2.
 __global__ void k_elementwise(DevTables T, u32 op, const u64* __restrict__ a, const u64* __restrict__ b,
                               u64* __restrict__ out, u32 ell, u32 polys) {
   const u32 log_n = T.log_n;
@@ -102,32 +99,32 @@ __global__ void k_elementwise(DevTables T, u32 op, const u64* __restrict__ a, co
     const ulonglong2 x = reinterpret_cast<const ulonglong2*>(a)[e2];
     ulonglong2 r;
     switch (op) {
-      case EW_ADD: {
+      case OP_ADD: {
         const ulonglong2 y = reinterpret_cast<const ulonglong2*>(b)[e2];
         r.x = add_mod(x.x, y.x, m.q);
         r.y = add_mod(x.y, y.y, m.q);
         break;
       }
-      case EW_SUB: {
+      case OP_SUB: {
         const ulonglong2 y = reinterpret_cast<const ulonglong2*>(b)[e2];
         r.x = sub_mod(x.x, y.x, m.q);
         r.y = sub_mod(x.y, y.y, m.q);
         break;
       }
-      case EW_NEG:
+      case OP_NEG:
         r.x = neg_mod(x.x, m.q);
         r.y = neg_mod(x.y, m.q);
         break;
-      case EW_MUL_PLAIN: {  // b is a plaintext [ell][N]
+      case OP_MUL_PLAIN: {  // b is a plaintext [>= ell][N] shared by every polynomial
         const ulonglong2 y = reinterpret_cast<const ulonglong2*>(b + (u64)limb * n)[(e & (n - 1)) >> 1];
         r.x = mul_mod(x.x, y.x, m);
         r.y = mul_mod(x.y, y.y, m);
         break;
       }
-      default: {  // EW_ADD_PLAIN / EW_SUB_PLAIN: only component 0 changes
-        if (poly == 0) {
+      default: {  // OP_ADD_PLAIN / OP_SUB_PLAIN: only component 0 of each ciphertext changes
+        if ((poly & 1u) == 0) {
           const ulonglong2 y = reinterpret_cast<const ulonglong2*>(b + (u64)limb * n)[(e & (n - 1)) >> 1];
-          if (op == EW_ADD_PLAIN) {
+          if (op == OP_ADD_PLAIN) {
             r.x = add_mod(x.x, y.x, m.q);
             r.y = add_mod(x.y, y.y, m.q);
           } else {
@@ -155,33 +152,37 @@ void launch_elementwise(const DevTables& T, u32 op, const u64* a, const u64* b, 
   const double limb = 8.0 * ell * (1u << T.log_n);  // bytes of one [ell][N] polynomial
   const double by = op == OP_NEG ? 2.0 * polys * limb
                     : (op == OP_ADD || op == OP_SUB) ? 3.0 * polys * limb
-                                                     : (2.0 * polys + 1.0) * limb;  // plaintext operand
+                                                     : (2.0 * polys + 1.0) * limb;  // shared plaintext operand
   Launch L(K_ELEMENTWISE, st, by);
   k_elementwise<<<ew_blocks(e2), 256, 0, st>>>(T, op, a, b, out, ell, polys);
 }
 
-// Tensor product: (d0, d1, d2) = (a0 b0, a0 b1 + a1 b0, a1 b1), out [3][ell][N].
+// Tensor product of `count` pairs: (d0, d1, d2) = (a0 b0, a0 b1 + a1 b0, a1 b1); a, b [count][2][ell][N],
+// out [count][3][ell][N].
 __global__ void k_tensor(DevTables T, const u64* __restrict__ a, const u64* __restrict__ b, u64* __restrict__ out,
-                         u32 ell) {
+                         u32 ell, u32 count) {
   const u32 log_n = T.log_n;
-  const u64 n = 1ull << log_n;
-  const u64 per_poly = (u64)ell * n;
-  for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < per_poly; e += (u64)gridDim.x * blockDim.x) {
-    const ModConst m = T.mods[e >> log_n];
-    const u64 a0 = a[e], a1 = a[per_poly + e], b0 = b[e], b1 = b[per_poly + e];
-    out[e] = mul_mod(a0, b0, m);
+  const u64 per_poly = (u64)ell << log_n;
+  for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < per_poly * count; e += (u64)gridDim.x * blockDim.x) {
+    const u64 c = e / per_poly, o = e - c * per_poly;
+    const ModConst m = T.mods[o >> log_n];
+    const u64* ac = a + c * 2 * per_poly;
+    const u64* bc = b + c * 2 * per_poly;
+    u64* oc = out + c * 3 * per_poly;
+    const u64 a0 = ac[o], a1 = ac[per_poly + o], b0 = bc[o], b1 = bc[per_poly + o];
+    oc[o] = mul_mod(a0, b0, m);
     Acc128 acc{0, 0};
     mac128(acc, a0, b1);
     mac128(acc, a1, b0);
-    out[per_poly + e] = reduce128(acc.hi, acc.lo, m);
-    out[2 * per_poly + e] = mul_mod(a1, b1, m);
+    oc[per_poly + o] = reduce128(acc.hi, acc.lo, m);
+    oc[2 * per_poly + o] = mul_mod(a1, b1, m);
   }
 }
 
-void launch_tensor(const DevTables& T, const u64* a, const u64* b, u64* out, u32 ell, cudaStream_t st) {
-  const u64 e = (u64)ell << T.log_n;
+void launch_tensor(const DevTables& T, const u64* a, const u64* b, u64* out, u32 ell, u32 count, cudaStream_t st) {
+  const u64 e = ((u64)ell << T.log_n) * count;
   Launch L(K_TENSOR, st, 7.0 * 8.0 * e);
-  k_tensor<<<ew_blocks(e / 2 + 1), 256, 0, st>>>(T, a, b, out, ell);
+  k_tensor<<<ew_blocks(e / 2 + 1), 256, 0, st>>>(T, a, b, out, ell, count);
 }
 
 // Decryption kernel: m = c0 + c1 * s over limbs < ell (s has L+1 limbs, chain order).
@@ -204,76 +205,78 @@ void launch_decrypt(const DevTables& T, const u64* ct, const u64* s, u64* pt, u3
 // ---------------------------------------------------------------- drop the last prime ----
 // Rescale (drop = q_{ell-1}) and ModDown (drop = P) share this combine:
 //   out[p][i] = (in[p][i] - NTT_i(bal(top[p]) mod q_i)) * drop^-1 mod q_i,  i < n_out,
-// with top[p] the coefficient-domain limb of the dropped prime. One CTA per (p, i).
+// with top[p] the coefficient-domain limb of the dropped prime. Limb job = p * n_out + i.
+template <int LC>
 __global__ void k_drop_combine(DevTables T, const u64* __restrict__ in, u64 in_poly_stride,
                                const u64* __restrict__ top, u32 drop_mod, u32 n_out, u64* __restrict__ out) {
   extern __shared__ u64 s[];
-  const u32 n = 1u << T.log_n;
-  const u32 p = blockIdx.x / n_out, i = blockIdx.x % n_out;
+  const Slice sl = slice_of<LC>(T);
+  const u64 n = 1ull << T.log_n;
+  const u32 p = sl.job / n_out, i = sl.job % n_out;
   const ModConst mi = T.mods[i];
   const ModConst md = T.mods[drop_mod];
   const PairConst pc = T.pairs[(u64)drop_mod * T.n_mods + i];
-  const u64* tp = top + (u64)p * n;
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) s[k] = lift_balanced(tp[k], md.half, pc.qa_mod_b, mi);
+  const u64* tp = top + (u64)p * n + sl.off;
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[k] = lift_balanced(tp[k], md.half, pc.qa_mod_b, mi);
   __syncthreads();
-  ntt_fwd_smem(s, T, i);
-  const u64* src = in + (u64)p * in_poly_stride + (u64)i * n;
-  u64* dst = out + ((u64)p * n_out + i) * n;
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) {
+  ntt_fwd_slice<LC>(s, T, i, sl.rank);
+  const u64* src = in + (u64)p * in_poly_stride + (u64)i * n + sl.off;
+  u64* dst = out + ((u64)p * n_out + i) * n + sl.off;
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
     const u64 c = sub_mod(src[k], fwd_final(s[k], mi.q), mi.q);
     dst[k] = mul_shoup(c, pc.inv_qa, pc.inv_qa_sh, mi.q);
   }
 }
 
-void launch_rescale(const DevTables& T, const u64* ct, u32 ell, u64* top_tmp, u64* out, cudaStream_t st) {
+void launch_rescale(const DevTables& T, const u64* ct, u32 ell, u32 polys, u64* top_tmp, u64* out, cudaStream_t st) {
   const u64 n = 1ull << T.log_n;
-  // INTT of the last limb of each component
-  launch_ntt(T, true, ct + (u64)(ell - 1) * n, (u64)ell * n, top_tmp, n, 2, ell - 1, 1, st);
-  const size_t sm = smem_bytes(T.log_n);
-  allow_smem(k_drop_combine, sm);
-  Launch L(K_DROP, st, 8.0 * (1u << T.log_n) * (4.0 * (ell - 1) + 2.0));
-  k_drop_combine<<<2 * (ell - 1), ntt_threads(T.log_n), sm, st>>>(T, ct, (u64)ell * n, top_tmp, ell - 1, ell - 1,
-                                                                   out);
+  // INTT of the last limb of each polynomial
+  launch_ntt(T, true, ct + (u64)(ell - 1) * n, (u64)ell * n, top_tmp, n, polys, ell - 1, 1, st);
+  Launch L(K_DROP, st, 8.0 * n * polys * (2.0 * (ell - 1) + 1.0));
+  launch_limb(TCKS_LC3(k_drop_combine), polys * (ell - 1), 1, T.log_n, st, 0, T, ct, (u64)ell * n, (const u64*)top_tmp, ell - 1,
+              ell - 1, out);
 }
 
 // ------------------------------------------------------------------------ key switching ----
-// ModUp (one digit per prime): digit j = bal_{q_j}(x_j) lifted to slot i (prime q_i for i < ell,
-// P for i = ell) and NTT'd; digits [ell][ell+1][N]. Slot i == j is x_j itself.
-__global__ void k_modup(DevTables T, const u64* __restrict__ x_ntt, const u64* __restrict__ x_coef, u32 ell,
-                        u64* __restrict__ digits) {
+// ModUp (one digit per prime) for a batch (y) of inputs: digit j = bal_{q_j}(x_j) lifted to slot i
+// (prime q_i for i < ell, P for i = ell) and NTT'd; digits [batch][ell][ell+1][N]. Slot i == j is
+// x_j itself. x_coef holds the inputs' INTT, [batch][ell][N].
+template <int LC>
+__global__ void k_modup(DevTables T, const u64* __restrict__ x_ntt, u64 x_stride, const u64* __restrict__ x_coef,
+                        u32 ell, u64* __restrict__ digits) {
   extern __shared__ u64 s[];
-  const u32 n = 1u << T.log_n;
-  const u32 j = blockIdx.x / (ell + 1), slot = blockIdx.x % (ell + 1);
-  u64* out = digits + ((u64)j * (ell + 1) + slot) * n;
+  const Slice sl = slice_of<LC>(T);
+  const u64 n = 1ull << T.log_n;
+  const u32 j = sl.job / (ell + 1), slot = sl.job % (ell + 1);
+  u64* out = digits + ((sl.y * ell + j) * (ell + 1) + slot) * n + sl.off;
   if (slot == j) {
-    const u64* in = x_ntt + (u64)j * n;
-    for (u32 k = threadIdx.x; k < n; k += blockDim.x) out[k] = in[k];
+    const u64* in = x_ntt + sl.y * x_stride + (u64)j * n + sl.off;
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) out[k] = in[k];
     return;
   }
   const u32 tmod = slot < ell ? slot : T.L;
   const ModConst mt = T.mods[tmod];
   const u64 half_j = T.mods[j].half;
   const u64 qj_mod_t = T.pairs[(u64)j * T.n_mods + tmod].qa_mod_b;
-  const u64* in = x_coef + (u64)j * n;
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) s[k] = lift_balanced(in[k], half_j, qj_mod_t, mt);
+  const u64* in = x_coef + (sl.y * ell + j) * n + sl.off;
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[k] = lift_balanced(in[k], half_j, qj_mod_t, mt);
   __syncthreads();
-  ntt_fwd_smem(s, T, tmod);
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) out[k] = fwd_final(s[k], mt.q);
+  ntt_fwd_slice<LC>(s, T, tmod, sl.rank);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) out[k] = fwd_final(s[k], mt.q);
 }
 
-void launch_modup(const DevTables& T, const u64* x_ntt, u32 ell, u64* x_coef_tmp, u64* digits, cudaStream_t st) {
+void launch_modup(const DevTables& T, const u64* x_ntt, u64 x_stride, u32 count, u32 ell, u64* x_coef_tmp,
+                  u64* digits, cudaStream_t st) {
   const u64 n = 1ull << T.log_n;
-  launch_ntt(T, true, x_ntt, n, x_coef_tmp, n, ell, 0, ell, st);
-  const size_t sm = smem_bytes(T.log_n);
-  allow_smem(k_modup, sm);
-  Launch L(K_MODUP, st, 8.0 * (1u << T.log_n) * (2.0 * ell + (double)ell * (ell + 1)));
-  k_modup<<<ell * (ell + 1), ntt_threads(T.log_n), sm, st>>>(T, x_ntt, x_coef_tmp, ell, digits);
+  launch_ntt(T, true, x_ntt, x_stride, x_coef_tmp, (u64)ell * n, count * ell, 0, ell, st);
+  Launch L(K_MODUP, st, 8.0 * n * count * (2.0 * ell + (double)ell * (ell + 1)));
+  launch_limb(TCKS_LC3(k_modup), ell * (ell + 1), count, T.log_n, st, 0, T, x_ntt, x_stride, (const u64*)x_coef_tmp, ell, digits);
 }
 
 // Inner product of (automorphed) digits with one key component on slot `slot`:
-//   sum_j D_j[slot][src(k)] * key_j[b][key_slot][k], 128-bit lazy accumulation, one reduction.
+//   sum_j D_j[slot][src] * key_j[b][key_slot][k], 128-bit lazy accumulation, one reduction.
 __device__ __forceinline__ u64 ks_inner(const u64* __restrict__ digits, u32 ell, u32 slot, const u64* __restrict__ key,
-                                        u32 K, u32 key_slot, u32 b, u32 k, u32 src, u32 n, const ModConst& m) {
+                                        u32 K, u32 key_slot, u32 b, u32 k, u32 src, u64 n, const ModConst& m) {
   Acc128 acc{0, 0};
   for (u32 j = 0; j < ell; ++j) {
     const u64 d = digits[((u64)j * (ell + 1) + slot) * n + src];
@@ -283,103 +286,193 @@ __device__ __forceinline__ u64 ks_inner(const u64* __restrict__ digits, u32 ell,
   return reduce128(acc.hi, acc.lo, m);
 }
 
-
-// Stage 1: u_b[P] = sum_j tau_g(D_j)[P] * key_j[b][P], then INTT mod P -> top[b]. grid (2, jobs).
-__global__ void k_ks_inner_p(DevTables T, u32 ell, const __grid_constant__ KsBatch jobs) {
+// Stage 1: u_b[P] = sum_j tau_g(D_j)[P] * key_j[b][P], then INTT mod P -> top. Limb job = component
+// b; entry y = request * R + rotation.
+template <int LC>
+__global__ void k_ks_inner_p(DevTables T, u32 ell, const __grid_constant__ KsPlan plan) {
   extern __shared__ u64 s[];
-  const u32 log_n = T.log_n, n = 1u << log_n;
-  const KsJob& J = jobs.job[blockIdx.y];
-  const u64* __restrict__ digits = J.digits;
-  const u32 b = blockIdx.x;
+  const Slice sl = slice_of<LC>(T);
+  if (sl.y >= (u64)plan.B * plan.R) return;
+  const u32 log_n = T.log_n;
+  const u64 n = 1ull << log_n;
+  const u32 rq = (u32)(sl.y % plan.B), r = (u32)(sl.y / plan.B);  // rotation-major: a key's requests adjacent
+  const KsKey kk = plan.keys[r];
+  const u64* digits = plan.digits + rq * plan.digits_b;
+  const u32 b = sl.job;
   const ModConst mp = T.mods[T.L];
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) {
-    const u32 src = J.g == 1 ? k : galois_src(k, J.g, log_n);
-    s[k] = ks_inner(digits, ell, ell, J.key, J.K, J.K, b, k, src, n, mp);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
+    const u32 g = sl.off + k;
+    const u32 src = kk.g == 1 ? g : galois_src(g, kk.g, log_n);
+    s[k] = ks_inner(digits, ell, ell, kk.key, kk.K, kk.K, b, g, src, n, mp);
   }
   __syncthreads();
-  ntt_inv_smem(s, T, T.L);
-  u64* top = J.top + (u64)b * n;
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) top[k] = inv_final(s[k], mp);
+  ntt_inv_slice<LC>(s, T, T.L, sl.rank);
+  u64* top = plan.top + (sl.y * 2 + b) * n + sl.off;
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) top[k] = inv_final(s[k], mp);
 }
 
 // Stage 2 (ModDown): out_b[i] = (u_b[i] - NTT_i(bal_P(top_b) mod q_i)) * P^-1 + addend_b[i].
-// grid (2 * ell, jobs).
-__global__ void k_ks_moddown(DevTables T, u32 ell, const __grid_constant__ KsBatch jobs) {
+// Limb job = b * ell + i.
+template <int LC>
+__global__ void k_ks_moddown(DevTables T, u32 ell, const __grid_constant__ KsPlan plan) {
   extern __shared__ u64 s[];
-  const u32 log_n = T.log_n, n = 1u << log_n;
-  const KsJob& J = jobs.job[blockIdx.y];
-  const u64* __restrict__ digits = J.digits;
-  const u32 b = blockIdx.x / ell, i = blockIdx.x % ell;
+  const Slice sl = slice_of<LC>(T);
+  if (sl.y >= (u64)plan.B * plan.R) return;
+  const u32 log_n = T.log_n;
+  const u64 n = 1ull << log_n;
+  const u32 rq = (u32)(sl.y % plan.B), r = (u32)(sl.y / plan.B);  // rotation-major: a key's requests adjacent
+  const KsKey kk = plan.keys[r];
+  const u64* digits = plan.digits + rq * plan.digits_b;
+  const u32 b = sl.job / ell, i = sl.job % ell;
   const ModConst mi = T.mods[i];
   const ModConst mp = T.mods[T.L];
   const PairConst pc = T.pairs[(u64)T.L * T.n_mods + i];
-  const u64* top = J.top + (u64)b * n;
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) s[k] = lift_balanced(top[k], mp.half, pc.qa_mod_b, mi);
+  const u64* top = plan.top + (sl.y * 2 + b) * n + sl.off;
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[k] = lift_balanced(top[k], mp.half, pc.qa_mod_b, mi);
   __syncthreads();
-  ntt_fwd_smem(s, T, i);
-  const u64* add = b == 0 ? J.add0 : J.add1;
-  u64* dst = J.out + ((u64)b * ell + i) * n;
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) {
-    const u32 src = J.g == 1 ? k : galois_src(k, J.g, log_n);
-    const u64 u = ks_inner(digits, ell, i, J.key, J.K, i, b, k, src, n, mi);
+  ntt_fwd_slice<LC>(s, T, i, sl.rank);
+  const u64* add = b == 0 ? (plan.add0 ? plan.add0 + rq * plan.add0_b : nullptr)
+                          : (plan.add1 ? plan.add1 + rq * plan.add1_b : nullptr);
+  u64* dst = plan.out + rq * plan.out_b + r * plan.out_r + ((u64)b * ell + i) * n;
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
+    const u32 g = sl.off + k;
+    const u32 src = kk.g == 1 ? g : galois_src(g, kk.g, log_n);
+    const u64 u = ks_inner(digits, ell, i, kk.key, kk.K, i, b, g, src, n, mi);
     u64 v = mul_shoup(sub_mod(u, fwd_final(s[k], mi.q), mi.q), pc.inv_qa, pc.inv_qa_sh, mi.q);
-    if (add) v = add_mod(v, add[(u64)i * n + (J.add_perm ? src : k)], mi.q);
-    dst[k] = v;
+    if (add) v = add_mod(v, add[(u64)i * n + (plan.add_perm ? src : g)], mi.q);
+    dst[g] = v;
   }
 }
 
-void launch_keyswitch(const DevTables& T, u32 ell, const KsBatch& jobs, cudaStream_t st) {
-  if (!jobs.count) return;
-  const size_t sm = smem_bytes(T.log_n);
-  allow_smem(k_ks_inner_p, sm);
-  allow_smem(k_ks_moddown, sm);
-  // algorithmic bytes: distinct digit sets and keys once, scratch and outputs once
-  const double n = (double)(1u << T.log_n);
-  double digits = 0, keys_p = 0, keys_q = 0, adds = 0;
-  for (u32 j = 0; j < jobs.count; ++j) {
-    bool new_digits = true, new_key = true, new_add = true;
-    for (u32 i = 0; i < j; ++i) {
-      new_digits &= jobs.job[i].digits != jobs.job[j].digits;
-      new_key &= jobs.job[i].key != jobs.job[j].key;
-      new_add &= jobs.job[i].add0 != jobs.job[j].add0;
-    }
-    if (new_digits) digits += 1;
-    if (new_key) keys_p += 2.0 * ell, keys_q += 2.0 * ell * ell;
-    if (new_add && jobs.job[j].add0) adds += jobs.job[j].add1 ? 2.0 * ell : ell;
-  }
-  {
-    Launch L(K_KS_P, st, 8.0 * n * (digits * ell + keys_p + 2.0 * jobs.count));
-    k_ks_inner_p<<<dim3(2, jobs.count), ntt_threads(T.log_n), sm, st>>>(T, ell, jobs);
-  }
-  {
-    Launch L(K_KS_MODDOWN, st,
-             8.0 * n * (digits * ell * ell + keys_q + 2.0 * jobs.count + adds + 2.0 * ell * jobs.count));
-    k_ks_moddown<<<dim3(2 * ell, jobs.count), ntt_threads(T.log_n), sm, st>>>(T, ell, jobs);
-  }
+// Algorithmic bytes of a plan: distinct digit sets and keys once, scratch and outputs once.
+static void ks_plan_bytes(const KsPlan& p, u32 ell, u32 log_n, double* inner, double* moddown) {
+  const double n = (double)(1u << log_n);
+  const double jobs = (double)p.B * p.R;
+  const double digit_sets = p.digits_b ? p.B : 1;
+  const double key_sets = p.R;  // each rotation index has its own key, shared by the batch
+  const double adds = (p.add0 ? (p.add0_b ? p.B : 1) : 0) + (p.add1 ? (p.add1_b ? p.B : 1) : 0);
+  *inner = 8.0 * n * (digit_sets * ell + key_sets * 2.0 * ell + 2.0 * jobs);
+  *moddown =
+      8.0 * n * (digit_sets * ell * ell + key_sets * 2.0 * ell * ell + 2.0 * jobs + adds * ell + 2.0 * ell * jobs);
 }
 
-// acc += sum_c rots[c] * diag[c]: one pass over acc, lazy 128-bit accumulation (count <= 64 keeps
-// the sum below 2^128 for q < 2^61), one reduction per element.
-__global__ void k_mulacc(DevTables T, u64* __restrict__ acc, const u64* __restrict__ rots, u64 rot_stride,
-                         const u64* __restrict__ diag, u64 diag_stride, u32 count, u32 ell) {
+void launch_ks_inner_p(const DevTables& T, u32 ell, const KsPlan& plan, cudaStream_t st) {
+  const u64 jobs = (u64)plan.B * plan.R;
+  if (!jobs) return;
+  double bi, bm;
+  ks_plan_bytes(plan, ell, T.log_n, &bi, &bm);
+  Launch L(K_KS_P, st, bi);
+  launch_limb(TCKS_LC3(k_ks_inner_p), 2, jobs, T.log_n, st, 0, T, ell, plan);
+}
+
+void launch_keyswitch(const DevTables& T, u32 ell, const KsPlan& plan, cudaStream_t st) {
+  const u64 jobs = (u64)plan.B * plan.R;
+  if (!jobs) return;
+  launch_ks_inner_p(T, ell, plan, st);
+  double bi, bm;
+  ks_plan_bytes(plan, ell, T.log_n, &bi, &bm);
+  Launch L(K_KS_MODDOWN, st, bm);
+  launch_limb(TCKS_LC3(k_ks_moddown), 2 * ell, jobs, T.log_n, st, 0, T, ell, plan);
+}
+
+// -------------------------------------------------- vector x plain matrix: fused ModDown + MAC ----
+// For request rq and the rotations r of this CTA's chunk (step k = r + 1): the rotated ciphertext
+// rot_k = (tau(c0) + ModDown(u_0), ModDown(u_1)) is multiplied by the diagonal d_k and summed in
+// registers, then stored as a per-chunk partial [B][chunks][2][ell][N]. Limb job = chunk * 2 * ell
+// + b * ell + i. Thread t owns elements t + e * blockDim.x of the slice.
+constexpr int kVmEpt = 16;
+// Threads of k_vecmat_acc: each owns kVmEpt elements of the slice.
+static u32 vecmat_threads(u32 log_n) {
+  const u32 ns = 1u << (log_n > 14 ? 14 : log_n);
+  return ns / kVmEpt < 32 ? 32 : ns / kVmEpt;
+}
+template <int LC>
+__global__ void k_vecmat_acc(DevTables T, u32 ell, const __grid_constant__ VecmatPlan plan) {
+  extern __shared__ u64 s[];
+  const Slice sl = slice_of<LC>(T);
   const u32 log_n = T.log_n;
   const u64 n = 1ull << log_n;
-  const u64 per_poly = (u64)ell * n;
-  for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < 2 * per_poly; e += (u64)gridDim.x * blockDim.x) {
-    const u64 pe = e < per_poly ? e : e - per_poly;  // offset inside the component
-    const ModConst m = T.mods[pe >> log_n];
-    Acc128 a{acc[e], 0};
-    for (u32 c = 0; c < count; ++c) mac128(a, rots[c * rot_stride + e], diag[c * diag_stride + pe]);
-    acc[e] = reduce128(a.hi, a.lo, m);
+  const u32 rq = sl.job % plan.B;  // requests fastest: CTAs reading the same keys run together
+  const u32 job = sl.job / plan.B;
+  const u32 chunk = job / (2 * ell), bi = job % (2 * ell);
+  const u32 b = bi / ell, i = bi % ell;
+  const ModConst mi = T.mods[i];
+  const ModConst mp = T.mods[T.L];
+  const PairConst pc = T.pairs[(u64)T.L * T.n_mods + i];
+  const u64* digits = plan.digits + rq * plan.digits_b;
+  const u64* c0 = plan.ct + rq * plan.ct_b;  // component 0, [ell][N]
+  u64 acc[kVmEpt];
+#pragma unroll
+  for (int e = 0; e < kVmEpt; ++e) acc[e] = 0;
+  const u32 r0 = chunk * plan.chunk;
+  const u32 r1 = min(plan.R, r0 + plan.chunk);
+  for (u32 r = r0; r < r1; ++r) {
+    const KsKey kk = plan.keys[r];
+    const u64* top = plan.top + (((u64)r * plan.B + rq) * 2 + b) * n + sl.off;
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[k] = lift_balanced(top[k], mp.half, pc.qa_mod_b, mi);
+    __syncthreads();
+    ntt_fwd_slice<LC>(s, T, i, sl.rank);
+    const u64* dk = plan.diag + (u64)(r + 1) * plan.diag_stride + (u64)i * n;
+#pragma unroll
+    for (int e = 0; e < kVmEpt; ++e) {
+      const u32 k = threadIdx.x + e * blockDim.x;
+      if (k < sl.ns) {
+        const u32 g = sl.off + k;
+        const u32 src = galois_src(g, kk.g, log_n);
+        const u64 u = ks_inner(digits, ell, i, kk.key, kk.K, i, b, g, src, n, mi);
+        u64 v = mul_shoup(sub_mod(u, fwd_final(s[k], mi.q), mi.q), pc.inv_qa, pc.inv_qa_sh, mi.q);
+        if (b == 0) v = add_mod(v, c0[(u64)i * n + src], mi.q);
+        acc[e] = add_mod(acc[e], mul_mod(v, dk[g], mi), mi.q);
+      }
+    }
+    __syncthreads();  // s is refilled for the next rotation
+  }
+  u64* dst = plan.partial + rq * plan.partial_b + (((u64)chunk * 2 + b) * ell + i) * n + sl.off;
+#pragma unroll
+  for (int e = 0; e < kVmEpt; ++e) {
+    const u32 k = threadIdx.x + e * blockDim.x;
+    if (k < sl.ns) dst[k] = acc[e];
   }
 }
 
-void launch_mulacc(const DevTables& T, u64* acc, const u64* rots, u64 rot_stride, const u64* diag, u64 diag_stride,
-                   u32 count, u32 ell, cudaStream_t st) {
-  if (!count) return;
-  const u64 e = (u64)2 * ell << T.log_n;
-  Launch L(K_MULACC, st, 8.0 * ((double)e * (2.0 + count) + (double)count * ell * (1u << T.log_n)));
-  k_mulacc<<<ew_blocks(e / 2 + 1), 256, 0, st>>>(T, acc, rots, rot_stride, diag, diag_stride, count, ell);
+// out[rq] = ct[rq] * d_0 + sum over chunks of partial[rq][chunk]; out [B][2][ell][N].
+__global__ void k_vecmat_reduce(DevTables T, u32 ell, const __grid_constant__ VecmatPlan plan, u64* __restrict__ out) {
+  const u32 log_n = T.log_n;
+  const u64 n = 1ull << log_n;
+  const u64 per_comp = (u64)ell * n, per_ct = 2 * per_comp;
+  for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < per_ct * plan.B; e += (u64)gridDim.x * blockDim.x) {
+    const u64 rq = e / per_ct, o = e - rq * per_ct;
+    const u64 lo_off = o % per_comp;  // offset inside the component
+    const ModConst m = T.mods[lo_off >> log_n];
+    Acc128 a{0, 0};
+    mac128(a, plan.ct[rq * plan.ct_b + o], plan.diag[lo_off]);
+    for (u32 c = 0; c < plan.chunks; ++c) {
+      const u64 v = plan.partial[rq * plan.partial_b + c * per_ct + o];
+      const u64 lo = a.lo + v;
+      a.hi += lo < v;
+      a.lo = lo;
+    }
+    out[rq * per_ct + o] = reduce128(a.hi, a.lo, m);
+  }
+}
+
+void launch_vecmat_acc(const DevTables& T, u32 ell, const VecmatPlan& plan, cudaStream_t st) {
+  const double n = (double)(1u << T.log_n);
+  // per (request, rotation): the P-limb scratch; per rotation: key limbs and diagonal; per request:
+  // digits, c0 and the partial outputs
+  const double by = 8.0 * n *
+                    ((double)plan.B * plan.R * 2.0 + plan.R * (2.0 * ell * ell + ell) + plan.B * (ell * ell + ell) +
+                     (double)plan.B * plan.chunks * 2.0 * ell);
+  Launch L(K_VECMAT, st, by);
+  launch_limb(TCKS_LC3(k_vecmat_acc), plan.chunks * 2 * ell * plan.B, 1, T.log_n, st, vecmat_threads(T.log_n), T,
+              ell, plan);
+}
+
+void launch_vecmat_reduce(const DevTables& T, u32 ell, const VecmatPlan& plan, u64* out, cudaStream_t st) {
+  const double n = (double)(1u << T.log_n);
+  const u64 e = (u64)plan.B * 2 * ell << T.log_n;
+  Launch L(K_MULACC, st, 8.0 * ((double)e * (2.0 + plan.chunks) + ell * n));
+  k_vecmat_reduce<<<ew_blocks(e / 2 + 1), 256, 0, st>>>(T, ell, plan, out);
 }
 
 }  // namespace tcks
@@ -419,8 +512,10 @@ u64* noalloc_setup(int device, std::string* why) {
   u64* ptr = nullptr;
   cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_rescale_scratch);
   const int bytes = (int)(((size_t)8) << kNoAllocMaxLogN);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_drop_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_drop_combine<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt<true, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_drop_combine<0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (prev != device) cudaSetDevice(prev);
   if (e != cudaSuccess) {
     *why = std::string("scratch set-up failed: ") + cudaGetErrorString(e);
@@ -450,14 +545,14 @@ extern "C" tcks_status tcks_rescale_noalloc(tcks_ctx* ctx, const uint64_t* d_in,
   if (!scratch) return abi_record(TCKS_ERR_CUDA, "rescale_noalloc: " + why);
   const DevTables& T = ctx->T;
   const u64 n = 1ull << log_n;
-  const size_t sm = ((size_t)8) << log_n;
+  const LimbShape sh = limb_shape(log_n);  // one CTA per limb at these sizes
   // the two launches of launch_rescale, without its allocating bookkeeping
   count_launch();
-  k_ntt<true><<<2, ntt_threads(log_n), sm, ctx->stream>>>(T, d_in + (u64)(level - 1) * n, (u64)level * n, scratch, n,
-                                                           level - 1, 1);
+  k_ntt<true, 0><<<2, sh.threads, sh.smem, ctx->stream>>>(T, d_in + (u64)(level - 1) * n, (u64)level * n, scratch, n,
+                                                        level - 1, 1);
   count_launch();
-  k_drop_combine<<<2 * (level - 1), ntt_threads(log_n), sm, ctx->stream>>>(T, d_in, (u64)level * n, scratch,
-                                                                             level - 1, level - 1, d_out);
+  k_drop_combine<0><<<2 * (level - 1), sh.threads, sh.smem, ctx->stream>>>(T, d_in, (u64)level * n, scratch, level - 1,
+                                                                          level - 1, d_out);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return abi_record(TCKS_ERR_CUDA, std::string("rescale_noalloc: ") + cudaGetErrorString(e));
   abi_clear();

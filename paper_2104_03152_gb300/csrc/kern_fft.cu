@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "limb_launch.cuh"
 #include "ntt.cuh"
 
 namespace tcks {
@@ -90,21 +91,23 @@ __global__ void k_encode_coeffs(DevTables T, FftTables F, const double* __restri
   if (overflow) atomicExch(status, 1);
 }
 
-// int64 coefficients -> NTT-form limbs, CTA per limb.
+// int64 coefficients -> NTT-form limbs, one limb job per prime.
+template <int LC>
 __global__ void k_coeffs_to_ntt(DevTables T, const i64* __restrict__ coeffs, u64* __restrict__ pt) {
   extern __shared__ u64 s[];
-  const u32 n = 1u << T.log_n;
-  const u32 l = blockIdx.x;
+  const Slice P = slice_of<LC>(T);
+  const u32 rank = P.rank, l = P.job, ns = P.ns, off = P.off;
   const ModConst m = T.mods[l];
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) {
-    const i64 v = coeffs[k];
+  for (u32 k = threadIdx.x; k < ns; k += blockDim.x) {
+    const i64 v = coeffs[off + k];
     const u64 a = v >= 0 ? (u64)v : (u64)(-(v + 1)) + 1;  // |v|
     const u64 r = reduce64(a, m);
     s[k] = v >= 0 ? r : neg_mod(r, m.q);
   }
   __syncthreads();
-  ntt_fwd_smem(s, T, l);
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) pt[(u64)l * n + k] = fwd_final(s[k], m.q);
+  ntt_fwd_slice<LC>(s, T, l, rank);
+  u64* out = pt + ((u64)l << T.log_n) + off;
+  for (u32 k = threadIdx.x; k < ns; k += blockDim.x) out[k] = fwd_final(s[k], m.q);
 }
 
 // Exact CRT of one coefficient: Garner digits v_i (x = v_0 + v_1 q_0 + v_2 q_0 q_1 + ...), the
@@ -201,10 +204,8 @@ void launch_encode_coeffs(const DevTables& T, const FftTables& F, const double* 
 }
 
 void launch_coeffs_to_ntt(const DevTables& T, const i64* d_coeffs, u32 ell, u64* pt, cudaStream_t st) {
-  const size_t sm = (size_t)8 << T.log_n;
-  allow((const void*)k_coeffs_to_ntt, sm);
   Launch L(K_ENCODE, st, 8.0 * (1.0 + ell) * (1u << T.log_n));
-  k_coeffs_to_ntt<<<ell, ntt_threads(T.log_n), sm, st>>>(T, d_coeffs, pt);
+  launch_limb(TCKS_LC3(k_coeffs_to_ntt), ell, 1, T.log_n, st, 0, T, d_coeffs, pt);
 }
 
 void launch_crt_compose(const DevTables& T, const u64* coef, u32 ell, const u64* d_qwords, double* out,

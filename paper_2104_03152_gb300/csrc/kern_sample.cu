@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "limb_launch.cuh"
 #include "ntt.cuh"
 
 namespace tcks {
@@ -60,17 +61,19 @@ __device__ __forceinline__ u64 small_to_residue(int v, u64 q) { return v >= 0 ? 
 
 enum : u32 { SMALL_TERNARY = 0, SMALL_CBD = 1 };
 
-// Fill s[] with a small polynomial (ternary / CBD) reduced mod the chain prime, NTT it in place;
-// on return s holds values in [0, 4q).
-__device__ __forceinline__ void small_ntt(u64* s, const DevTables& T, u32 mod, u32 kind, u64 seed, u64 tag) {
-  const u32 n = 1u << T.log_n;
+// Fill the CTA's slice of s[] with a small polynomial (ternary / CBD, drawn at the global
+// coefficient index) reduced mod the chain prime, and NTT it; on return s holds values in [0, 4q).
+template <int LC>
+__device__ __forceinline__ void small_ntt(u64* s, const DevTables& T, u32 mod, u32 kind, u64 seed, u64 tag,
+                                          u32 rank, u32 ns) {
   const u64 q = T.mods[mod].q;
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) {
-    const int v = kind == SMALL_TERNARY ? draw_ternary(seed, tag, k) : draw_cbd(seed, tag, k);
+  const u32 off = rank * ns;
+  for (u32 k = threadIdx.x; k < ns; k += blockDim.x) {
+    const int v = kind == SMALL_TERNARY ? draw_ternary(seed, tag, off + k) : draw_cbd(seed, tag, off + k);
     s[k] = small_to_residue(v, q);
   }
   __syncthreads();
-  ntt_fwd_smem(s, T, mod);
+  ntt_fwd_slice<LC>(s, T, mod, rank);
 }
 
 // Limb slot -> chain index when a layout holds `count` data limbs followed by P.
@@ -78,114 +81,114 @@ __device__ __forceinline__ u32 slot_chain(u32 slot, u32 count, u32 L) { return s
 
 }  // namespace
 
-// s: [L+1][N], one CTA per limb.
+// s: [L+1][N], one limb job per prime.
+template <int LC>
 __global__ void k_keygen_secret(DevTables T, u64 seed, u64* __restrict__ s_out) {
   extern __shared__ u64 s[];
-  const u32 n = 1u << T.log_n;
-  const u32 mod = blockIdx.x;  // 0..L (L is P)
-  small_ntt(s, T, mod, SMALL_TERNARY, seed, 1);
+  const Slice P = slice_of<LC>(T);
+  const u32 mod = P.job;  // 0..L (L is P)
+  small_ntt<LC>(s, T, mod, SMALL_TERNARY, seed, 1, P.rank, P.ns);
   const u64 q = T.mods[mod].q;
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) s_out[(u64)mod * n + k] = fwd_final(s[k], q);
+  u64* out = s_out + ((u64)mod << T.log_n) + P.off;
+  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) out[k] = fwd_final(s[k], q);
 }
 
 // pk: [2][L][N]; pk0 = -a*s + e, pk1 = a.
+template <int LC>
 __global__ void k_keygen_public(DevTables T, u64 seed, const u64* __restrict__ sk, u64* __restrict__ pk) {
   extern __shared__ u64 s[];
-  const u32 n = 1u << T.log_n;
-  const u32 l = blockIdx.x;
+  const Slice P = slice_of<LC>(T);
+  const u64 n = 1ull << T.log_n;
+  const u32 l = P.job;
   const ModConst m = T.mods[l];
-  small_ntt(s, T, l, SMALL_CBD, seed, 3);
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) {
-    const u64 a = draw_uniform(seed, 2, k, l, m);
+  small_ntt<LC>(s, T, l, SMALL_CBD, seed, 3, P.rank, P.ns);
+  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) {
+    const u32 g = P.off + k;
+    const u64 a = draw_uniform(seed, 2, g, l, m);
     const u64 e = fwd_final(s[k], m.q);
-    pk[(u64)l * n + k] = add_mod(neg_mod(mul_mod(a, sk[(u64)l * n + k], m), m.q), e, m.q);
-    pk[((u64)T.L + l) * n + k] = a;
+    pk[(u64)l * n + g] = add_mod(neg_mod(mul_mod(a, sk[(u64)l * n + g], m), m.q), e, m.q);
+    pk[((u64)T.L + l) * n + g] = a;
   }
 }
 
-// Switching key of level K: [K][2][K+1][N]; CTA per (digit j, slot).
+// Switching key of level K: [K][2][K+1][N]; limb job = digit j * (K+1) + slot.
 //   b_j[slot] = -a*s + e + [chain(slot) == j] * (P mod q_j) * s'
+template <int LC>
 __global__ void k_keygen_switch(DevTables T, u64 seed, u32 kind, const u64* __restrict__ sk, u32 K,
                                 u64* __restrict__ ksk) {
   extern __shared__ u64 s[];
-  const u32 log_n = T.log_n, n = 1u << log_n;
-  const u32 j = blockIdx.x / (K + 1), slot = blockIdx.x % (K + 1);
+  const Slice P = slice_of<LC>(T);
+  const u32 log_n = T.log_n;
+  const u64 n = 1ull << log_n;
+  const u32 j = P.job / (K + 1), slot = P.job % (K + 1);
   const u32 l = slot_chain(slot, K, T.L);
   const ModConst m = T.mods[l];
   const u64 tag_a = ((u64)kind << 32) | 0x80000000ull | (2ull * j);
   const u64 tag_e = tag_a | 1ull;
-  small_ntt(s, T, l, SMALL_CBD, seed, tag_e);
+  small_ntt<LC>(s, T, l, SMALL_CBD, seed, tag_e, P.rank, P.ns);
   const u64 gadget = (l == j) ? T.pairs[(u64)T.L * T.n_mods + l].qa_mod_b : 0;  // P mod q_j
   const u64* s_l = sk + (u64)l * n;
   u64* b0 = ksk + (((u64)j * 2 + 0) * (K + 1) + slot) * n;
   u64* b1 = ksk + (((u64)j * 2 + 1) * (K + 1) + slot) * n;
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) {
-    const u64 a = draw_uniform(seed, tag_a, k, l, m);
-    u64 v = add_mod(neg_mod(mul_mod(a, s_l[k], m), m.q), fwd_final(s[k], m.q), m.q);
+  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) {
+    const u32 g = P.off + k;
+    const u64 a = draw_uniform(seed, tag_a, g, l, m);
+    u64 v = add_mod(neg_mod(mul_mod(a, s_l[g], m), m.q), fwd_final(s[k], m.q), m.q);
     if (gadget) {
-      const u64 sp = kind == 0 ? mul_mod(s_l[k], s_l[k], m) : s_l[galois_src(k, kind, log_n)];
+      const u64 sp = kind == 0 ? mul_mod(s_l[g], s_l[g], m) : s_l[galois_src(g, kind, log_n)];
       v = add_mod(v, mul_mod(gadget, sp, m), m.q);
     }
-    b0[k] = v;
-    b1[k] = a;
+    b0[g] = v;
+    b1[g] = a;
   }
 }
 
-// Encryption at level ell, CTA per limb: c0 = u*pk0 + e0 + m, c1 = u*pk1 + e1.
+// Encryption at level ell, limb job = limb: c0 = u*pk0 + e0 + m, c1 = u*pk1 + e1.
+template <int LC>
 __global__ void k_encrypt(DevTables T, u64 seed, const u64* __restrict__ pk, const u64* __restrict__ pt, u32 ell,
                           u64* __restrict__ out) {
   extern __shared__ u64 s[];
-  const u32 n = 1u << T.log_n;
-  const u32 l = blockIdx.x;
+  const Slice P = slice_of<LC>(T);
+  const u64 n = 1ull << T.log_n;
+  const u32 l = P.job;
   const ModConst m = T.mods[l];
-  u64* c0 = out + (u64)l * n;
-  u64* c1 = out + ((u64)ell + l) * n;
-  small_ntt(s, T, l, SMALL_TERNARY, seed, 4);
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) {
+  u64* c0 = out + (u64)l * n + P.off;
+  u64* c1 = out + ((u64)ell + l) * n + P.off;
+  const u64* p0 = pk + (u64)l * n + P.off;
+  const u64* p1 = pk + ((u64)T.L + l) * n + P.off;
+  const u64* ml = pt + (u64)l * n + P.off;
+  small_ntt<LC>(s, T, l, SMALL_TERNARY, seed, 4, P.rank, P.ns);
+  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) {
     const u64 u = fwd_final(s[k], m.q);
-    c0[k] = add_mod(mul_mod(u, pk[(u64)l * n + k], m), pt[(u64)l * n + k], m.q);
-    c1[k] = mul_mod(u, pk[((u64)T.L + l) * n + k], m);
+    c0[k] = add_mod(mul_mod(u, p0[k], m), ml[k], m.q);
+    c1[k] = mul_mod(u, p1[k], m);
   }
   __syncthreads();
-  small_ntt(s, T, l, SMALL_CBD, seed, 5);
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) c0[k] = add_mod(c0[k], fwd_final(s[k], m.q), m.q);
+  small_ntt<LC>(s, T, l, SMALL_CBD, seed, 5, P.rank, P.ns);
+  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) c0[k] = add_mod(c0[k], fwd_final(s[k], m.q), m.q);
   __syncthreads();
-  small_ntt(s, T, l, SMALL_CBD, seed, 6);
-  for (u32 k = threadIdx.x; k < n; k += blockDim.x) c1[k] = add_mod(c1[k], fwd_final(s[k], m.q), m.q);
-}
-
-static size_t smem_bytes(u32 log_n) { return ((size_t)8) << log_n; }
-template <typename K>
-static void allow_smem(K kernel, size_t bytes) {
-  ensure_smem((const void*)kernel, bytes);
+  small_ntt<LC>(s, T, l, SMALL_CBD, seed, 6, P.rank, P.ns);
+  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) c1[k] = add_mod(c1[k], fwd_final(s[k], m.q), m.q);
 }
 
 void launch_keygen_secret(const DevTables& T, u64 seed, u64* s, cudaStream_t st) {
-  const size_t sm = smem_bytes(T.log_n);
-  allow_smem(k_keygen_secret, sm);
   Launch L(K_KEYGEN, st, 8.0 * (T.L + 1) * (1u << T.log_n));
-  k_keygen_secret<<<T.L + 1, ntt_threads(T.log_n), sm, st>>>(T, seed, s);
+  launch_limb(TCKS_LC3(k_keygen_secret), T.L + 1, 1, T.log_n, st, 0, T, seed, s);
 }
 
 void launch_keygen_public(const DevTables& T, u64 seed, const u64* s, u64* pk, cudaStream_t st) {
-  const size_t sm = smem_bytes(T.log_n);
-  allow_smem(k_keygen_public, sm);
   Launch L(K_KEYGEN, st, 8.0 * 3 * T.L * (1u << T.log_n));
-  k_keygen_public<<<T.L, ntt_threads(T.log_n), sm, st>>>(T, seed, s, pk);
+  launch_limb(TCKS_LC3(k_keygen_public), T.L, 1, T.log_n, st, 0, T, seed, s, pk);
 }
 
 void launch_keygen_switch(const DevTables& T, u64 seed, u32 kind, const u64* s, u32 K, u64* ksk, cudaStream_t st) {
-  const size_t sm = smem_bytes(T.log_n);
-  allow_smem(k_keygen_switch, sm);
   Launch L(K_KEYGEN, st, 8.0 * 2 * K * (K + 1) * (1u << T.log_n));
-  k_keygen_switch<<<K * (K + 1), ntt_threads(T.log_n), sm, st>>>(T, seed, kind, s, K, ksk);
+  launch_limb(TCKS_LC3(k_keygen_switch), K * (K + 1), 1, T.log_n, st, 0, T, seed, kind, s, K, ksk);
 }
 
 void launch_encrypt(const DevTables& T, u64 seed, const u64* pk, const u64* pt, u32 ell, u64* out, cudaStream_t st) {
-  const size_t sm = smem_bytes(T.log_n);
-  allow_smem(k_encrypt, sm);
   Launch L(K_ENCRYPT, st, 8.0 * 5 * ell * (1u << T.log_n));
-  k_encrypt<<<ell, ntt_threads(T.log_n), sm, st>>>(T, seed, pk, pt, ell, out);
+  launch_limb(TCKS_LC3(k_encrypt), ell, 1, T.log_n, st, 0, T, seed, pk, pt, ell, out);
 }
 
 }  // namespace tcks

@@ -9,7 +9,7 @@ namespace tcks {
 // Kernel families for launch accounting and the profiler (profiler.cpp).
 enum KernelId : u32 {
   K_NTT_FWD = 0, K_NTT_INV, K_ELEMENTWISE, K_TENSOR, K_DROP, K_MODUP, K_KS_P, K_KS_MODDOWN, K_MULACC, K_KEYGEN,
-  K_ENCRYPT, K_ENCODE, K_DECODE, K_BATCH_NTT, K_DECRYPT, K_COUNT
+  K_ENCRYPT, K_ENCODE, K_DECODE, K_VECMAT, K_DECRYPT, K_COUNT
 };
 // Scope around one kernel launch: counts it and, while profiling is on, records CUDA events on the
 // launching stream before and after it together with its algorithmic bytes.
@@ -30,47 +30,73 @@ class Launch {
 
 // ---- kern_core.cu
 u32 ntt_threads(u32 log_n);
-// Raise a kernel's dynamic shared-memory limit to `bytes` (no-op at or below 48 KB).
+// Raise a kernel's dynamic shared-memory limit to `bytes` and its carveout to the maximum.
 void ensure_smem(const void* kernel, size_t bytes);
-// count jobs: src + b*src_stride -> dst + b*dst_stride (may alias for in place), prime
-// mod_base + b % mod_period.
-void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_stride, u64* dst, u64 dst_stride,
-                u32 count, u32 mod_base, u32 mod_period, cudaStream_t st);
+// count jobs: limb (j % per) of entry (j / per), src + (j/per)*src_outer + (j%per)*N -> dst likewise
+// (may alias for in place), prime mod_base + j % per.
+void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_outer, u64* dst, u64 dst_outer,
+                u32 count, u32 mod_base, u32 per, cudaStream_t st);
 enum : u32 { OP_ADD = 0, OP_SUB = 1, OP_NEG = 2, OP_MUL_PLAIN = 3, OP_ADD_PLAIN = 4, OP_SUB_PLAIN = 5 };
+// [polys][ell][N] operands; plain ops share one plaintext across all polynomials.
 void launch_elementwise(const DevTables& T, u32 op, const u64* a, const u64* b, u64* out, u32 ell, u32 polys,
                         cudaStream_t st);
-void launch_tensor(const DevTables& T, const u64* a, const u64* b, u64* out, u32 ell, cudaStream_t st);
+// count pairs [count][2][ell][N] -> [count][3][ell][N].
+void launch_tensor(const DevTables& T, const u64* a, const u64* b, u64* out, u32 ell, u32 count, cudaStream_t st);
 void launch_decrypt(const DevTables& T, const u64* ct, const u64* s, u64* pt, u32 ell, cudaStream_t st);
-// ct [2][ell][N] -> out [2][ell-1][N]; top_tmp: [2][N] scratch.
-void launch_rescale(const DevTables& T, const u64* ct, u32 ell, u64* top_tmp, u64* out, cudaStream_t st);
-// x_ntt [ell][N] -> digits [ell][ell+1][N]; x_coef_tmp: [ell][N] scratch.
-void launch_modup(const DevTables& T, const u64* x_ntt, u32 ell, u64* x_coef_tmp, u64* digits, cudaStream_t st);
+// polys polynomials [polys][ell][N] -> [polys][ell-1][N]; top_tmp: [polys][N] scratch.
+void launch_rescale(const DevTables& T, const u64* ct, u32 ell, u32 polys, u64* top_tmp, u64* out, cudaStream_t st);
+// count inputs x_ntt + c * x_stride ([ell][N] each) -> digits [count][ell][ell+1][N];
+// x_coef_tmp: [count][ell][N] scratch.
+void launch_modup(const DevTables& T, const u64* x_ntt, u64 x_stride, u32 count, u32 ell, u64* x_coef_tmp,
+                  u64* digits, cudaStream_t st);
 
-// One key switch of hoisted digits: automorphism g (1 = none), key of level K, output [2][ell][N],
-// scratch top [2][N], optional addends per output component (read through the automorphism when
-// add_perm is set).
-struct KsJob {
-  const u64* digits;  // [ell][ell+1][N]
+// A key for rotation index r of a plan: switching key of level K, Galois element g (1 = none).
+struct KsKey {
   const u64* key;
-  u64* out;
-  u64* top;
-  const u64* add0;
-  const u64* add1;
   u32 K;
   u32 g;
-  u32 add_perm;
-  u32 pad;
 };
-constexpr u32 KS_BATCH_MAX = 64;
-struct KsBatch {
-  KsJob job[KS_BATCH_MAX];
-  u32 count;
+// B requests x R key switches of hoisted digits. Request rq, rotation r: digits + rq*digits_b,
+// key keys[r] (device array), P-limb scratch top [R][B][2][N], output out + rq*out_b + r*out_r
+// ([2][ell][N]), addends add0 + rq*add0_b / add1 + rq*add1_b ([ell][N], read through the
+// automorphism when add_perm is set; null for none).
+struct KsPlan {
+  const KsKey* keys;
+  const u64* digits;
+  u64 digits_b;
+  u64* top;
+  u64* out;
+  u64 out_b, out_r;
+  const u64* add0;
+  u64 add0_b;
+  const u64* add1;
+  u64 add1_b;
+  u32 R, B, add_perm, pad;
 };
-void launch_keyswitch(const DevTables& T, u32 ell, const KsBatch& jobs, cudaStream_t st);
-// acc[2][ell][N] += sum_c rots[c] * diag[c] (c < count), rots[c] = rots + c * rot_stride,
-// diag[c] = diag + c * diag_stride (each diag has >= ell limbs).
-void launch_mulacc(const DevTables& T, u64* acc, const u64* rots, u64 rot_stride, const u64* diag, u64 diag_stride,
-                   u32 count, u32 ell, cudaStream_t st);
+void launch_keyswitch(const DevTables& T, u32 ell, const KsPlan& plan, cudaStream_t st);
+// Vector x plain matrix after ModUp and the P-limb stage of R = n-1 rotations (steps 1..R):
+// keys[r] = key of step r+1; top [R][B][2][N] from the KsPlan stage 1; ct + rq*ct_b the input
+// ([2][ell][N]); diag + k*diag_stride the diagonal d_k (k = 0..R); partial [B][chunks][2][ell][N]
+// scratch. Output out [B][2][ell][N] = sum_k rot(ct, k) * d_k, before the rescale.
+struct VecmatPlan {
+  const KsKey* keys;
+  const u64* digits;
+  u64 digits_b;
+  const u64* top;
+  const u64* ct;
+  u64 ct_b;
+  const u64* diag;
+  u64 diag_stride;
+  u64* partial;    // partial of request rq, chunk c: partial + rq * partial_b + c * [2][ell][N]
+  u64 partial_b;
+  u32 R, B, chunk, chunks;
+};
+// Stage 1 of a KsPlan alone (the P-limb inner product and its INTT into plan.top).
+void launch_ks_inner_p(const DevTables& T, u32 ell, const KsPlan& plan, cudaStream_t st);
+// The fused ModDown + multiply-accumulate over the plan's R rotations, chunk rotations per CTA.
+void launch_vecmat_acc(const DevTables& T, u32 ell, const VecmatPlan& plan, cudaStream_t st);
+// out [B][2][ell][N] = ct * diag[0] + sum of plan.chunks partials per request.
+void launch_vecmat_reduce(const DevTables& T, u32 ell, const VecmatPlan& plan, u64* out, cudaStream_t st);
 
 // ---- kern_sample.cu (Philox4x64-10 sampler; key = (seed, tag), counter = (index, limb, 0, 0))
 // Secret key: ternary, NTT form over the data primes and P: out [L+1][N].

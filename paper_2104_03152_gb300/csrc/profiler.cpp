@@ -18,8 +18,8 @@ namespace tcks {
 namespace {
 
 const char* const kNames[K_COUNT] = {"ntt_fwd",      "ntt_inv",    "elementwise", "tensor",    "drop_combine",
-                                     "modup",        "ks_inner_p", "ks_moddown",  "mulacc",    "keygen",
-                                     "encrypt",      "encode",     "decode",      "batch_ntt", "decrypt"};
+                                     "modup",        "ks_inner_p", "ks_moddown",  "vecmat_reduce", "keygen",
+                                     "encrypt",      "encode",     "decode",      "vecmat_acc", "decrypt"};
 
 struct Rec {
   u32 id;
@@ -55,10 +55,13 @@ std::atomic<bool> g_on{false};
 }  // namespace
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(u64 n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 Launch::Launch(KernelId id, cudaStream_t st, double algo_bytes) : id_(id), st_(st), bytes_(algo_bytes) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!g_on.load(std::memory_order_relaxed)) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;  // no events in graphs
   Prof& p = prof();
   std::lock_guard<std::mutex> lock(p.mu);
   a_ = p.get();
