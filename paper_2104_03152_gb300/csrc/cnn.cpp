@@ -35,7 +35,7 @@ struct tcks_cnn {
 
 namespace tcks {
 
-static int ceil_log2(u32 x) {
+int ceil_log2(u32 x) {
   int r = 0;
   while ((1u << r) < x) ++r;
   return r;
@@ -57,15 +57,81 @@ static void schedule_scales(const tcks_cnn* m, double s_in, double delta, double
   *s_fc2 = s;
 }
 
+// Stages of the schedule, each on a contiguous batch [count][2][level][N]:
+//   0: conv + pack + conv bias   (L   -> L-2)
+//   1: square                    (L-2 -> L-3)
+//   2: FC1 + bias                (L-3 -> L-4)
+//   3: square                    (L-4 -> L-5)
+//   4: FC2 + bias                (L-5 -> L-6)
+// Every stage runs once for the whole batch: the 4 * count channel ciphertexts rotate together, the
+// relinearizations and rescales take the batch in one launch each, and the vector x matrix products
+// process every request's rotations in shared launches.
+u32 cnn_stage_level(const tcks_cnn* m, u32 stage) {  // input level of a stage (stage 5 = output)
+  static const u32 drop[6] = {0, 2, 3, 4, 5, 6};
+  return m->L - drop[stage];
+}
+
+static void square_stage(tcks_ctx* c, const u64* in, u32 ell, u32 count, u64* out) {
+  const size_t n = c->N;
+  DevBuf d3(c, (size_t)count * 3 * ell * n), rel(c, (size_t)count * ct_words(c, ell));
+  launch_tensor(c->T, in, in, d3.p, ell, count, c->stream);
+  op_relinearize(c, d3.p, ell, rel.p, count);
+  op_rescale(c, rel.p, ell, out, count);
+}
+
+void cnn_stage(const tcks_cnn* m, u32 stage, const u64* x, u32 count, u64* out) {
+  tcks_ctx* c = m->ctx;
+  const u32 L = m->L, K = m->kernels;
+  switch (stage) {
+    case 0: {
+      const u64 w_in = ct_words(c, L), w1 = ct_words(c, L - 1), w2 = ct_words(c, L - 2);
+      // conv [L-1]: channel k of request r at chans + (k * count + r) * w1
+      DevBuf chans(c, (size_t)K * count * w1);
+      {
+        DevBuf prod(c, (size_t)count * w_in);
+        for (u32 k = 0; k < K; ++k) {
+          launch_elementwise(c->T, OP_MUL_PLAIN, x, m->conv[k], prod.p, L, 2 * count, c->stream);
+          op_rescale(c, prod.p, L, chans.p + (size_t)k * count * w1, count);
+        }
+      }
+      const int rsteps = ceil_log2(m->taps);
+      for (int i = 0; i < rsteps; ++i) op_rotate_add(c, chans.p, w1, K * count, L - 1, (int32_t)(m->windows << i));
+      // pack [L-2] + bias
+      DevBuf prod(c, (size_t)count * w1), t(c, (size_t)count * w2);
+      for (u32 k = 0; k < K; ++k) {
+        launch_elementwise(c->T, OP_MUL_PLAIN, chans.p + (size_t)k * count * w1, m->masks[k], prod.p, L - 1,
+                           2 * count, c->stream);
+        op_rescale(c, prod.p, L - 1, k == 0 ? out : t.p, count);
+        if (k) launch_elementwise(c->T, OP_ADD, out, t.p, out, L - 2, 2 * count, c->stream);
+      }
+      launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[0], out, L - 2, 2 * count, c->stream);
+      break;
+    }
+    case 1:
+      square_stage(c, x, L - 2, count, out);
+      break;
+    case 2:
+      op_vecmat(c, x, ct_words(c, L - 3), count, L - 3, m->fc1, out);
+      launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[1], out, L - 4, 2 * count, c->stream);
+      break;
+    case 3:
+      square_stage(c, x, L - 4, count, out);
+      break;
+    case 4:
+      op_vecmat(c, x, ct_words(c, L - 5), count, L - 5, m->fc2, out);
+      launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[2], out, L - 6, 2 * count, c->stream);
+      break;
+    default:
+      fail(TCKS_ERR_INVALID_ARG, "no such stage");
+  }
+  check_launch("cnn stage");
+}
+
 // Forward pass of `count` requests at once: inputs in + r * in_stride ([2][L][N] each), outputs
-// out [count][2][L-6][N]. Every stage runs on the whole batch: the 4 * count channel ciphertexts
-// rotate together, the relinearizations and rescales take the batch in one launch each, and the two
-// vector x matrix products process every request's rotations in shared launches.
+// out [count][2][L-6][N].
 static void cnn_forward_dev(const tcks_cnn* m, const u64* in, u64 in_stride, u32 count, u64* out) {
   tcks_ctx* c = m->ctx;
-  const size_t n = c->N;
-  const u32 L = m->L, K = m->kernels;
-  const u64 w_in = ct_words(c, L);
+  const u64 w_in = ct_words(c, m->L);
   DevBuf xin;
   const u64* x = in;
   if (count > 1 && in_stride != w_in) {  // gather the inputs into one contiguous batch
@@ -75,57 +141,17 @@ static void cnn_forward_dev(const tcks_cnn* m, const u64* in, u64 in_stride, u32
                  "gather");
     x = xin.p;
   }
-  // conv [L-1]: channel k of request r at chans + (k * count + r) * w1
-  const u64 w1 = ct_words(c, L - 1);
-  DevBuf chans(c, (size_t)K * count * w1);
-  {
-    DevBuf prod(c, (size_t)count * w_in);
-    for (u32 k = 0; k < K; ++k) {
-      launch_elementwise(c->T, OP_MUL_PLAIN, x, m->conv[k], prod.p, L, 2 * count, c->stream);
-      op_rescale(c, prod.p, L, chans.p + (size_t)k * count * w1, count);
+  DevBuf cur;
+  for (u32 st = 0; st < 5; ++st) {
+    if (st == 4) {
+      cnn_stage(m, st, x, count, out);
+      break;
     }
+    DevBuf next(c, (size_t)count * ct_words(c, cnn_stage_level(m, st + 1)));
+    cnn_stage(m, st, x, count, next.p);
+    cur = std::move(next);
+    x = cur.p;
   }
-  const int rsteps = ceil_log2(m->taps);
-  for (int i = 0; i < rsteps; ++i) op_rotate_add(c, chans.p, w1, K * count, L - 1, (int32_t)(m->windows << i));
-  // pack [L-2] + bias
-  const u64 w2 = ct_words(c, L - 2);
-  DevBuf v(c, (size_t)count * w2);
-  {
-    DevBuf prod(c, (size_t)count * w1), t(c, (size_t)count * w2);
-    for (u32 k = 0; k < K; ++k) {
-      launch_elementwise(c->T, OP_MUL_PLAIN, chans.p + (size_t)k * count * w1, m->masks[k], prod.p, L - 1, 2 * count,
-                         c->stream);
-      op_rescale(c, prod.p, L - 1, k == 0 ? v.p : t.p, count);
-      if (k) launch_elementwise(c->T, OP_ADD, v.p, t.p, v.p, L - 2, 2 * count, c->stream);
-    }
-    launch_elementwise(c->T, OP_ADD_PLAIN, v.p, m->bias[0], v.p, L - 2, 2 * count, c->stream);
-  }
-  chans = DevBuf();
-  // square [L-3]
-  DevBuf sq1(c, (size_t)count * ct_words(c, L - 3));
-  {
-    DevBuf d3(c, (size_t)count * 3 * (L - 2) * n), rel(c, (size_t)count * w2);
-    launch_tensor(c->T, v.p, v.p, d3.p, L - 2, count, c->stream);
-    op_relinearize(c, d3.p, L - 2, rel.p, count);
-    op_rescale(c, rel.p, L - 2, sq1.p, count);
-  }
-  // FC1 [L-4] + bias
-  const u64 w4 = ct_words(c, L - 4);
-  DevBuf f1(c, (size_t)count * w4);
-  op_vecmat(c, sq1.p, ct_words(c, L - 3), count, L - 3, m->fc1, f1.p);
-  launch_elementwise(c->T, OP_ADD_PLAIN, f1.p, m->bias[1], f1.p, L - 4, 2 * count, c->stream);
-  // square [L-5]
-  DevBuf sq2(c, (size_t)count * ct_words(c, L - 5));
-  {
-    DevBuf d3(c, (size_t)count * 3 * (L - 4) * n), rel(c, (size_t)count * w4);
-    launch_tensor(c->T, f1.p, f1.p, d3.p, L - 4, count, c->stream);
-    op_relinearize(c, d3.p, L - 4, rel.p, count);
-    op_rescale(c, rel.p, L - 4, sq2.p, count);
-  }
-  // FC2 [L-6] + bias
-  op_vecmat(c, sq2.p, ct_words(c, L - 5), count, L - 5, m->fc2, out);
-  launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[2], out, L - 6, 2 * count, c->stream);
-  check_launch("cnn forward");
 }
 
 }  // namespace tcks

@@ -57,18 +57,18 @@ __global__ void k_ntt(DevTables T, const u64* __restrict__ src, u64 src_outer, u
   u64* out = dst + jo * dst_outer + ji * n + sl.off;
   for (u32 k = 2 * threadIdx.x; k < sl.ns; k += 2 * blockDim.x) {
     const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(in + k);
-    s[k] = v.x;
-    s[k + 1] = v.y;
+    s[sw(k)] = v.x;
+    s[sw(k + 1)] = v.y;
   }
   __syncthreads();
   if (INVERSE) {
     ntt_inv_slice<LC>(s, T, mod, sl.rank);
     for (u32 k = 2 * threadIdx.x; k < sl.ns; k += 2 * blockDim.x)
-      *reinterpret_cast<ulonglong2*>(out + k) = make_ulonglong2(inv_final(s[k], m), inv_final(s[k + 1], m));
+      *reinterpret_cast<ulonglong2*>(out + k) = make_ulonglong2(inv_final(s[sw(k)], m), inv_final(s[sw(k + 1)], m));
   } else {
     ntt_fwd_slice<LC>(s, T, mod, sl.rank);
     for (u32 k = 2 * threadIdx.x; k < sl.ns; k += 2 * blockDim.x)
-      *reinterpret_cast<ulonglong2*>(out + k) = make_ulonglong2(fwd_final(s[k], m.q), fwd_final(s[k + 1], m.q));
+      *reinterpret_cast<ulonglong2*>(out + k) = make_ulonglong2(fwd_final(s[sw(k)], m.q), fwd_final(s[sw(k + 1)], m.q));
   }
 }
 
@@ -217,13 +217,13 @@ __global__ void k_drop_combine(DevTables T, const u64* __restrict__ in, u64 in_p
   const ModConst md = T.mods[drop_mod];
   const PairConst pc = T.pairs[(u64)drop_mod * T.n_mods + i];
   const u64* tp = top + (u64)p * n + sl.off;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[k] = lift_balanced(tp[k], md.half, pc.qa_mod_b, mi);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced(tp[k], md.half, pc.qa_mod_b, mi);
   __syncthreads();
   ntt_fwd_slice<LC>(s, T, i, sl.rank);
   const u64* src = in + (u64)p * in_poly_stride + (u64)i * n + sl.off;
   u64* dst = out + ((u64)p * n_out + i) * n + sl.off;
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
-    const u64 c = sub_mod(src[k], fwd_final(s[k], mi.q), mi.q);
+    const u64 c = sub_mod(src[k], fwd_final(s[sw(k)], mi.q), mi.q);
     dst[k] = mul_shoup(c, pc.inv_qa, pc.inv_qa_sh, mi.q);
   }
 }
@@ -259,10 +259,10 @@ __global__ void k_modup(DevTables T, const u64* __restrict__ x_ntt, u64 x_stride
   const u64 half_j = T.mods[j].half;
   const u64 qj_mod_t = T.pairs[(u64)j * T.n_mods + tmod].qa_mod_b;
   const u64* in = x_coef + (sl.y * ell + j) * n + sl.off;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[k] = lift_balanced(in[k], half_j, qj_mod_t, mt);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced(in[k], half_j, qj_mod_t, mt);
   __syncthreads();
   ntt_fwd_slice<LC>(s, T, tmod, sl.rank);
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) out[k] = fwd_final(s[k], mt.q);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) out[k] = fwd_final(s[sw(k)], mt.q);
 }
 
 void launch_modup(const DevTables& T, const u64* x_ntt, u64 x_stride, u32 count, u32 ell, u64* x_coef_tmp,
@@ -303,12 +303,12 @@ __global__ void k_ks_inner_p(DevTables T, u32 ell, const __grid_constant__ KsPla
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
     const u32 g = sl.off + k;
     const u32 src = kk.g == 1 ? g : galois_src(g, kk.g, log_n);
-    s[k] = ks_inner(digits, ell, ell, kk.key, kk.K, kk.K, b, g, src, n, mp);
+    s[sw(k)] = ks_inner(digits, ell, ell, kk.key, kk.K, kk.K, b, g, src, n, mp);
   }
   __syncthreads();
   ntt_inv_slice<LC>(s, T, T.L, sl.rank);
   u64* top = plan.top + (sl.y * 2 + b) * n + sl.off;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) top[k] = inv_final(s[k], mp);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) top[k] = inv_final(s[sw(k)], mp);
 }
 
 // Stage 2 (ModDown): out_b[i] = (u_b[i] - NTT_i(bal_P(top_b) mod q_i)) * P^-1 + addend_b[i].
@@ -328,7 +328,7 @@ __global__ void k_ks_moddown(DevTables T, u32 ell, const __grid_constant__ KsPla
   const ModConst mp = T.mods[T.L];
   const PairConst pc = T.pairs[(u64)T.L * T.n_mods + i];
   const u64* top = plan.top + (sl.y * 2 + b) * n + sl.off;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[k] = lift_balanced(top[k], mp.half, pc.qa_mod_b, mi);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced(top[k], mp.half, pc.qa_mod_b, mi);
   __syncthreads();
   ntt_fwd_slice<LC>(s, T, i, sl.rank);
   const u64* add = b == 0 ? (plan.add0 ? plan.add0 + rq * plan.add0_b : nullptr)
@@ -338,7 +338,7 @@ __global__ void k_ks_moddown(DevTables T, u32 ell, const __grid_constant__ KsPla
     const u32 g = sl.off + k;
     const u32 src = kk.g == 1 ? g : galois_src(g, kk.g, log_n);
     const u64 u = ks_inner(digits, ell, i, kk.key, kk.K, i, b, g, src, n, mi);
-    u64 v = mul_shoup(sub_mod(u, fwd_final(s[k], mi.q), mi.q), pc.inv_qa, pc.inv_qa_sh, mi.q);
+    u64 v = mul_shoup(sub_mod(u, fwd_final(s[sw(k)], mi.q), mi.q), pc.inv_qa, pc.inv_qa_sh, mi.q);
     if (add) v = add_mod(v, add[(u64)i * n + (plan.add_perm ? src : g)], mi.q);
     dst[g] = v;
   }
@@ -409,7 +409,7 @@ __global__ void k_vecmat_acc(DevTables T, u32 ell, const __grid_constant__ Vecma
   for (u32 r = r0; r < r1; ++r) {
     const KsKey kk = plan.keys[r];
     const u64* top = plan.top + (((u64)r * plan.B + rq) * 2 + b) * n + sl.off;
-    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[k] = lift_balanced(top[k], mp.half, pc.qa_mod_b, mi);
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced(top[k], mp.half, pc.qa_mod_b, mi);
     __syncthreads();
     ntt_fwd_slice<LC>(s, T, i, sl.rank);
     const u64* dk = plan.diag + (u64)(r + 1) * plan.diag_stride + (u64)i * n;
@@ -420,7 +420,7 @@ __global__ void k_vecmat_acc(DevTables T, u32 ell, const __grid_constant__ Vecma
         const u32 g = sl.off + k;
         const u32 src = galois_src(g, kk.g, log_n);
         const u64 u = ks_inner(digits, ell, i, kk.key, kk.K, i, b, g, src, n, mi);
-        u64 v = mul_shoup(sub_mod(u, fwd_final(s[k], mi.q), mi.q), pc.inv_qa, pc.inv_qa_sh, mi.q);
+        u64 v = mul_shoup(sub_mod(u, fwd_final(s[sw(k)], mi.q), mi.q), pc.inv_qa, pc.inv_qa_sh, mi.q);
         if (b == 0) v = add_mod(v, c0[(u64)i * n + src], mi.q);
         acc[e] = add_mod(acc[e], mul_mod(v, dk[g], mi), mi.q);
       }

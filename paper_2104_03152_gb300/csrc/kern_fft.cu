@@ -102,12 +102,12 @@ __global__ void k_coeffs_to_ntt(DevTables T, const i64* __restrict__ coeffs, u64
     const i64 v = coeffs[off + k];
     const u64 a = v >= 0 ? (u64)v : (u64)(-(v + 1)) + 1;  // |v|
     const u64 r = reduce64(a, m);
-    s[k] = v >= 0 ? r : neg_mod(r, m.q);
+    s[sw(k)] = v >= 0 ? r : neg_mod(r, m.q);
   }
   __syncthreads();
   ntt_fwd_slice<LC>(s, T, l, rank);
   u64* out = pt + ((u64)l << T.log_n) + off;
-  for (u32 k = threadIdx.x; k < ns; k += blockDim.x) out[k] = fwd_final(s[k], m.q);
+  for (u32 k = threadIdx.x; k < ns; k += blockDim.x) out[k] = fwd_final(s[sw(k)], m.q);
 }
 
 // Exact CRT of one coefficient: Garner digits v_i (x = v_0 + v_1 q_0 + v_2 q_0 q_1 + ...), the

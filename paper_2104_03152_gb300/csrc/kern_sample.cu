@@ -70,7 +70,7 @@ __device__ __forceinline__ void small_ntt(u64* s, const DevTables& T, u32 mod, u
   const u32 off = rank * ns;
   for (u32 k = threadIdx.x; k < ns; k += blockDim.x) {
     const int v = kind == SMALL_TERNARY ? draw_ternary(seed, tag, off + k) : draw_cbd(seed, tag, off + k);
-    s[k] = small_to_residue(v, q);
+    s[sw(k)] = small_to_residue(v, q);
   }
   __syncthreads();
   ntt_fwd_slice<LC>(s, T, mod, rank);
@@ -90,7 +90,7 @@ __global__ void k_keygen_secret(DevTables T, u64 seed, u64* __restrict__ s_out) 
   small_ntt<LC>(s, T, mod, SMALL_TERNARY, seed, 1, P.rank, P.ns);
   const u64 q = T.mods[mod].q;
   u64* out = s_out + ((u64)mod << T.log_n) + P.off;
-  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) out[k] = fwd_final(s[k], q);
+  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) out[k] = fwd_final(s[sw(k)], q);
 }
 
 // pk: [2][L][N]; pk0 = -a*s + e, pk1 = a.
@@ -105,7 +105,7 @@ __global__ void k_keygen_public(DevTables T, u64 seed, const u64* __restrict__ s
   for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) {
     const u32 g = P.off + k;
     const u64 a = draw_uniform(seed, 2, g, l, m);
-    const u64 e = fwd_final(s[k], m.q);
+    const u64 e = fwd_final(s[sw(k)], m.q);
     pk[(u64)l * n + g] = add_mod(neg_mod(mul_mod(a, sk[(u64)l * n + g], m), m.q), e, m.q);
     pk[((u64)T.L + l) * n + g] = a;
   }
@@ -133,7 +133,7 @@ __global__ void k_keygen_switch(DevTables T, u64 seed, u32 kind, const u64* __re
   for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) {
     const u32 g = P.off + k;
     const u64 a = draw_uniform(seed, tag_a, g, l, m);
-    u64 v = add_mod(neg_mod(mul_mod(a, s_l[g], m), m.q), fwd_final(s[k], m.q), m.q);
+    u64 v = add_mod(neg_mod(mul_mod(a, s_l[g], m), m.q), fwd_final(s[sw(k)], m.q), m.q);
     if (gadget) {
       const u64 sp = kind == 0 ? mul_mod(s_l[g], s_l[g], m) : s_l[galois_src(g, kind, log_n)];
       v = add_mod(v, mul_mod(gadget, sp, m), m.q);
@@ -159,16 +159,16 @@ __global__ void k_encrypt(DevTables T, u64 seed, const u64* __restrict__ pk, con
   const u64* ml = pt + (u64)l * n + P.off;
   small_ntt<LC>(s, T, l, SMALL_TERNARY, seed, 4, P.rank, P.ns);
   for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) {
-    const u64 u = fwd_final(s[k], m.q);
+    const u64 u = fwd_final(s[sw(k)], m.q);
     c0[k] = add_mod(mul_mod(u, p0[k], m), ml[k], m.q);
     c1[k] = mul_mod(u, p1[k], m);
   }
   __syncthreads();
   small_ntt<LC>(s, T, l, SMALL_CBD, seed, 5, P.rank, P.ns);
-  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) c0[k] = add_mod(c0[k], fwd_final(s[k], m.q), m.q);
+  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) c0[k] = add_mod(c0[k], fwd_final(s[sw(k)], m.q), m.q);
   __syncthreads();
   small_ntt<LC>(s, T, l, SMALL_CBD, seed, 6, P.rank, P.ns);
-  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) c1[k] = add_mod(c1[k], fwd_final(s[k], m.q), m.q);
+  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) c1[k] = add_mod(c1[k], fwd_final(s[sw(k)], m.q), m.q);
 }
 
 void launch_keygen_secret(const DevTables& T, u64 seed, u64* s, cudaStream_t st) {

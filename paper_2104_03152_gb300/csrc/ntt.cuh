@@ -17,6 +17,11 @@
 
 namespace tcks {
 
+// Shared-memory position of limb element i: the low four bits are XORed with the 16-word row index,
+// so the strided accesses of the small-distance rounds spread over all bank pairs (8-byte words:
+// 16 words span the 32 banks) while each row keeps its 16 words.
+__device__ __forceinline__ u32 sw(u32 i) { return i ^ ((i >> 4) & 15u); }
+
 __device__ __forceinline__ const u64* tw_at(const DevTables& T, u32 mod, u32 which) {
   return T.tw + ((u64)mod * 4 + which) * (1ull << T.log_n);
 }
@@ -89,10 +94,10 @@ __device__ __forceinline__ void fwd_round(u64* s, u32 log_n, u32 log_ns, u32 ran
     const u32 base = (blk << (log_tr + LR)) + j;
     u64 x[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) x[k] = s[base + k * tr];
+    for (int k = 0; k < R; ++k) x[k] = s[sw(base + k * tr)];
     fwd_group<LR>(x, st, gbase + blk, tw, tws, q, two_q);
 #pragma unroll
-    for (int k = 0; k < R; ++k) s[base + k * tr] = x[k];
+    for (int k = 0; k < R; ++k) s[sw(base + k * tr)] = x[k];
   }
   __syncthreads();
 }
@@ -110,10 +115,10 @@ __device__ __forceinline__ void inv_round(u64* s, u32 log_n, u32 log_ns, u32 ran
     const u32 base = (blk << (log_t + LR)) + j;
     u64 x[R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) x[k] = s[base + k * t];
+    for (int k = 0; k < R; ++k) x[k] = s[sw(base + k * t)];
     inv_group<LR>(x, log_n, st, gbase + blk, tw, tws, q, two_q);
 #pragma unroll
-    for (int k = 0; k < R; ++k) s[base + k * t] = x[k];
+    for (int k = 0; k < R; ++k) s[sw(base + k * t)] = x[k];
   }
   __syncthreads();
 }
@@ -141,7 +146,7 @@ __device__ __forceinline__ void fwd_cross(u64* s, u32 log_ns, u32 rank, const u6
       if (j < ns) {
         u64 x[C];
 #pragma unroll
-        for (int r = 0; r < C; ++r) x[r] = rem[r][j];
+        for (int r = 0; r < C; ++r) x[r] = rem[r][sw(j)];
         fwd_group<LC>(x, 0, 0, tw, tws, q, two_q);
         keep[e] = x[0];
 #pragma unroll
@@ -153,7 +158,7 @@ __device__ __forceinline__ void fwd_cross(u64* s, u32 log_ns, u32 rank, const u6
 #pragma unroll
     for (int e = 0; e < PER; ++e) {
       const u32 j = c0 + e * blockDim.x + threadIdx.x;
-      if (j < ns) s[j] = keep[e];
+      if (j < ns) s[sw(j)] = keep[e];
     }
     cl.sync();
   }
@@ -180,7 +185,7 @@ __device__ __forceinline__ void inv_cross(u64* s, u32 log_n, u32 log_ns, u32 ran
       if (j < ns) {
         u64 x[C];
 #pragma unroll
-        for (int r = 0; r < C; ++r) x[r] = rem[r][j];
+        for (int r = 0; r < C; ++r) x[r] = rem[r][sw(j)];
         inv_group<LC>(x, log_n, log_ns, 0, tw, tws, q, two_q);
         keep[e] = x[0];
 #pragma unroll
@@ -192,7 +197,7 @@ __device__ __forceinline__ void inv_cross(u64* s, u32 log_n, u32 log_ns, u32 ran
 #pragma unroll
     for (int e = 0; e < PER; ++e) {
       const u32 j = c0 + e * blockDim.x + threadIdx.x;
-      if (j < ns) s[j] = keep[e];
+      if (j < ns) s[sw(j)] = keep[e];
     }
     cl.sync();
   }
