@@ -249,9 +249,76 @@ def run_gpu(args, world, rank, local):
             tk.check(tk.lib().tcks_ct_export(co.h, tk._p(host_out[i]), out_words))
     torch.cuda.synchronize()
     e2e_s = reduce_max(world, time.perf_counter() - t0)
-    return dict(total_ms=total_ms, per_step=per_step, prof=prof, launches=launches, clocks=clk, e2e_s=e2e_s,
+    serving = None
+    if args.serve_seconds > 0:
+        arr = poisson_arrivals(args.serve_rate, args.serve_seconds, 8)
+        lat_s, thr_s = serve_trace(tk, ctx, model, cts, arr, args.batch)
+        # the plain path saturates far below the offered rate: serve the first second of the trace
+        arr_p = arr[arr < min(1.0, args.serve_seconds)]
+        lat_p, thr_p = plain_trace(tk, ctx, model, cts, arr_p)
+        pct = lambda a, p: float(np.percentile(a, p) * 1e3)
+        serving = {"offered_rate": args.serve_rate, "seconds": args.serve_seconds, "requests": len(arr),
+                   "served": {"throughput": thr_s, "p50_ms": pct(lat_s, 50), "p99_ms": pct(lat_s, 99),
+                              "max_batch_per_stage": args.batch},
+                   "plain": {"throughput": thr_p, "p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
+                             "requests": len(arr_p)},
+                   "latency": "arrival -> result exported to the host"}
+    return dict(serving=serving, total_ms=total_ms, per_step=per_step, prof=prof, launches=launches, clocks=clk, e2e_s=e2e_s,
                 e2e_steps=e2e_steps, h2d=host_in.nbytes, d2h=host_out.nbytes, max_err=max_err,
                 plain_ms=plain_total / plain_steps, plain_times=plain_times)
+
+
+def poisson_arrivals(rate: float, seconds: float, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t >= seconds:
+            return np.array(out)
+        out.append(t)
+
+
+def serve_trace(tk, ctx, model, cts, arrivals, max_batch):
+    """Continuous batching: requests are submitted when their arrival time passes and join the
+    running pipeline at the next step; latency = arrival -> result exported to the host."""
+    srv = tk.Server(hbm_budget_bytes=200 << 30, max_in_flight=1024, max_batch=max_batch)
+    lane = srv.add_cnn(model)
+    host = np.zeros((2, 1, ctx.N), dtype=np.uint64)
+    pending, lat = {}, []
+    i, total = 0, len(arrivals)
+    t0 = time.perf_counter()
+    while len(lat) < total:
+        now = time.perf_counter() - t0
+        while i < total and arrivals[i] <= now:
+            pending[srv.submit(lane, cts[i % len(cts)])] = arrivals[i]
+            i += 1
+        st = srv.stats()
+        if st["queued"] + st["in_flight"] == 0:
+            time.sleep(max(0.0, min(arrivals[i] - now, 0.01)) if i < total else 0.0)
+            continue
+        srv.step()
+        for rid in srv.poll():
+            out = srv.take(rid, ctx)
+            tk.check(tk.lib().tcks_ct_export(out.h, tk._p(host), host.size))
+            lat.append(time.perf_counter() - t0 - pending.pop(rid))
+    span = time.perf_counter() - t0 - arrivals[0]
+    return np.array(lat), total / span
+
+
+def plain_trace(tk, ctx, model, cts, arrivals):
+    """The plain path on the same trace: one request at a time in arrival order."""
+    host = np.zeros((2, 1, ctx.N), dtype=np.uint64)
+    lat = []
+    t0 = time.perf_counter()
+    for i, a in enumerate(arrivals):
+        now = time.perf_counter() - t0
+        if now < a:
+            time.sleep(a - now)
+        out = model.forward(cts[i % len(cts)])
+        tk.check(tk.lib().tcks_ct_export(out.h, tk._p(host), host.size))
+        lat.append(time.perf_counter() - t0 - a)
+    span = time.perf_counter() - t0 - arrivals[0]
+    return np.array(lat), len(arrivals) / span
 
 
 def plain_cnn(img, w):
@@ -322,6 +389,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=2, help="oracle inferences timed for cpu_baseline")
     ap.add_argument("--batch", type=int, default=64, help="requests per step (the batched schedule)")
+    ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of the Poisson serving trace (0: skip)")
+    ap.add_argument("--serve-rate", type=float, default=600.0, help="offered requests/s of the serving trace")
     args = ap.parse_args()
     world, rank, local = dist_env()
     if args.impl == "reference":
@@ -370,6 +439,7 @@ def main():
                          "sample": f"{len(times)} full CNN inferences of this workload (forward only)"},
         "e2e": {"value": world * B * r["e2e_steps"] / r["e2e_s"], "unit": "inferences/s",
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+        "serving": r["serving"],
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
     }

@@ -48,7 +48,8 @@ enum {
   TCKS_ERR_CUDA = -9,            /* a CUDA runtime call failed (detail has the CUDA message) */
   TCKS_ERR_TIMEOUT = -10,        /* a bounded device wait ran out */
   TCKS_ERR_VALUE_OVERFLOW = -11, /* encode: |scale * m_i| >= 2^62 */
-  TCKS_ERR_UNSUPPORTED = -12     /* valid request this build does not implement (detail says what) */
+  TCKS_ERR_UNSUPPORTED = -12,    /* valid request this build does not implement (detail says what) */
+  TCKS_ERR_NOT_READY = -13       /* serving: the request has not completed yet */
 };
 
 const char* tcks_status_string(tcks_status s);
@@ -283,6 +284,33 @@ void tcks_cnn_graph_free(tcks_cnn_graph* g);
  * (index 0..2), 3 FC1 diagonal, 4 FC2 diagonal) to host [level][N]; level / scale are reported. */
 tcks_status tcks_cnn_export_plaintext(const tcks_cnn* m, uint32_t kind, uint32_t index, uint64_t* host,
                                       size_t n_words, uint32_t* level, double* scale);
+
+/* ------------------------------------------------------------------------------ serving ---- */
+/* A serving loop for encrypted inference requests (the paper's client-server setting, §2 and §4,
+ * with requests of several parameter sizes on one GPU). Lanes are models on their contexts: a CNN
+ * (five stages) or a vector x plain matrix (one stage). Requests are queued on submit (the server
+ * keeps a device copy of the input) and admitted in arrival order while the HBM budget (every
+ * lane's resident keys, tables and model plaintexts, plus a per-request allowance of 65 top-level
+ * ciphertexts for the live state and the stage scratch) and the in-flight cap allow. A step groups
+ * admitted requests by (lane, stage), runs each group's stage as one batched pass of up to max_batch
+ * requests (all lanes' work is launched before the step waits), and advances each request by one
+ * stage; requests submitted while a step runs join stage 0 at the next step (continuous batching).
+ * Results are bit-identical to the single-request path. submit fails with BUDGET_EXCEEDED for a
+ * request that could never fit; take returns NOT_READY for a request still queued or running. */
+typedef struct tcks_server tcks_server;
+tcks_status tcks_server_create(uint64_t hbm_budget_bytes, uint32_t max_in_flight, uint32_t max_batch,
+                               tcks_server** out);
+void tcks_server_free(tcks_server* s);
+tcks_status tcks_server_add_cnn(tcks_server* s, const tcks_cnn* m, uint32_t* lane);
+tcks_status tcks_server_add_vecmat(tcks_server* s, const tcks_matrix* M, uint32_t* lane);
+tcks_status tcks_server_submit(tcks_server* s, uint32_t lane, const tcks_ct* in, uint64_t* id);
+/* Runs one step and waits for it; *completed = requests that finished in it. */
+tcks_status tcks_server_step(tcks_server* s, uint32_t* completed);
+/* Ids completed since the last poll (up to cap). */
+tcks_status tcks_server_poll(tcks_server* s, uint64_t* ids, uint32_t cap, uint32_t* n);
+tcks_status tcks_server_take(tcks_server* s, uint64_t id, tcks_ct** out);
+tcks_status tcks_server_stats(const tcks_server* s, uint64_t* queued, uint64_t* in_flight, uint64_t* finished,
+                              uint64_t* bytes_in_use, uint64_t* bytes_resident);
 
 #ifdef __cplusplus
 }

@@ -104,6 +104,15 @@ _SIGS = {
     "tcks_profile_count": (ctypes.c_uint32, []),
     "tcks_profile_read": (ctypes.c_int32, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_char_p),
                                             ctypes.POINTER(ctypes.c_uint64), _dblp, _dblp]),
+    "tcks_server_create": (ctypes.c_int32, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
+    "tcks_server_free": (None, [_vp]),
+    "tcks_server_add_cnn": (ctypes.c_int32, [_vp, _vp, _u32p]),
+    "tcks_server_add_vecmat": (ctypes.c_int32, [_vp, _vp, _u32p]),
+    "tcks_server_submit": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vp, _u64p]),
+    "tcks_server_step": (ctypes.c_int32, [_vp, _u32p]),
+    "tcks_server_poll": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, _u32p]),
+    "tcks_server_take": (ctypes.c_int32, [_vp, ctypes.c_uint64, _vpp]),
+    "tcks_server_stats": (ctypes.c_int32, [_vp, _u64p, _u64p, _u64p, _u64p, _u64p]),
     "tcks_cnn_create": (ctypes.c_int32, [_vp, _dblp, _dblp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                           _dblp, _dblp, ctypes.c_uint32, _dblp, _dblp, ctypes.c_uint32, _vpp]),
     "tcks_cnn_free": (None, [_vp]),
@@ -574,3 +583,56 @@ class CNNGraph:
         outs = (_vp * len(cts))()
         check(lib().tcks_cnn_graph_run(self.h, ins, outs))
         return [Ciphertext(self.model.ctx, _vp(outs[i])) for i in range(len(cts))]
+
+
+class Server:
+    """Continuous-batching serving loop with HBM-budget admission (see tcks_server_* in tcks.h)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_in_flight: int = 1024, max_batch: int = 64):
+        h = _vp()
+        check(lib().tcks_server_create(int(hbm_budget_bytes), max_in_flight, max_batch, ctypes.byref(h)))
+        self.h = h
+        self._keep = []
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().tcks_server_free(self.h)
+            self.h = None
+
+    def add_cnn(self, model: CNN) -> int:
+        lane = ctypes.c_uint32()
+        check(lib().tcks_server_add_cnn(self.h, model.h, ctypes.byref(lane)))
+        self._keep.append(model)
+        return lane.value
+
+    def add_vecmat(self, M: Matrix) -> int:
+        lane = ctypes.c_uint32()
+        check(lib().tcks_server_add_vecmat(self.h, M.h, ctypes.byref(lane)))
+        self._keep.append(M)
+        return lane.value
+
+    def submit(self, lane: int, ct: Ciphertext) -> int:
+        rid = ctypes.c_uint64()
+        check(lib().tcks_server_submit(self.h, lane, ct.h, ctypes.byref(rid)))
+        return rid.value
+
+    def step(self) -> int:
+        n = ctypes.c_uint32()
+        check(lib().tcks_server_step(self.h, ctypes.byref(n)))
+        return n.value
+
+    def poll(self, cap: int = 4096) -> list:
+        ids = np.zeros(cap, dtype=np.uint64)
+        n = ctypes.c_uint32()
+        check(lib().tcks_server_poll(self.h, _p(ids), cap, ctypes.byref(n)))
+        return [int(x) for x in ids[: n.value]]
+
+    def take(self, rid: int, ctx: Context) -> Ciphertext:
+        h = _vp()
+        check(lib().tcks_server_take(self.h, rid, ctypes.byref(h)))
+        return Ciphertext(ctx, h)
+
+    def stats(self) -> dict:
+        v = [ctypes.c_uint64() for _ in range(5)]
+        check(lib().tcks_server_stats(self.h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(["queued", "in_flight", "finished", "bytes_in_use", "bytes_resident"], [x.value for x in v]))

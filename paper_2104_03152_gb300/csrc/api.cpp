@@ -287,6 +287,7 @@ const char* tcks_status_string(tcks_status s) {
     case TCKS_ERR_TIMEOUT: return "TIMEOUT";
     case TCKS_ERR_VALUE_OVERFLOW: return "VALUE_OVERFLOW";
     case TCKS_ERR_UNSUPPORTED: return "UNSUPPORTED";
+    case TCKS_ERR_NOT_READY: return "NOT_READY";
     default: return "UNKNOWN";
   }
 }

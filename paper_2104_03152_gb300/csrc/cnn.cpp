@@ -57,6 +57,33 @@ static void schedule_scales(const tcks_cnn* m, double s_in, double delta, double
   *s_fc2 = s;
 }
 
+u64 cnn_resident_bytes(const tcks_cnn* m) {
+  const tcks_ctx* c = m->ctx;
+  const u64 n = c->N, L = m->L;
+  u64 b = (u64)m->kernels * (L + (L - 1)) * n * 8;          // conv kernels and masks
+  b += ((L - 2) + (L - 4) + (L - 6)) * n * 8;                  // biases
+  b += (u64)m->fc1->rows * m->fc1->level * n * 8 + (u64)m->fc2->rows * m->fc2->level * n * 8;
+  return b;
+}
+
+tcks_ctx* cnn_context(const tcks_cnn* m) { return m->ctx; }
+
+// Scale after stage `stage` for an input scale s (the double operations of the forward pass).
+double cnn_out_scale(const tcks_cnn* m, u32 stage, double s) {
+  const std::vector<u64>& q = m->ctx->host.chain;
+  const u32 L = m->L;
+  const double delta = m->ctx->params.scale;
+  switch (stage) {
+    case 0:
+      s = s * delta / (double)q[L - 1];
+      return s * delta / (double)q[L - 2];
+    case 1: return s * s / (double)q[L - 3];
+    case 2: return s * m->fc1->scale / (double)q[L - 4];
+    case 3: return s * s / (double)q[L - 5];
+    default: return s * m->fc2->scale / (double)q[L - 6];
+  }
+}
+
 // Stages of the schedule, each on a contiguous batch [count][2][level][N]:
 //   0: conv + pack + conv bias   (L   -> L-2)
 //   1: square                    (L-2 -> L-3)
