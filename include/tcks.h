@@ -78,6 +78,11 @@ typedef struct {
  * encoding scale. */
 tcks_status tcks_params_create(uint32_t log_n, const uint32_t* bit_sizes, uint32_t n_primes, double scale,
                                tcks_params** out);
+/* The same chain given explicitly: n_primes primes (data primes, then P), each a prime below 2^61,
+ * == 1 (mod 2N) and distinct. One chain of primes == 1 (mod 2^17) serves every N <= 2^16. Errors:
+ * BAD_PARAMS when a prime fails a condition. */
+tcks_status tcks_params_create_primes(uint32_t log_n, const uint64_t* primes, uint32_t n_primes, double scale,
+                                      tcks_params** out);
 void tcks_params_free(tcks_params* p);
 /* Writes the n_primes chosen primes (data primes, then P) to host `primes`. */
 tcks_status tcks_params_primes(const tcks_params* p, uint64_t* primes, uint32_t capacity);
@@ -234,6 +239,54 @@ tcks_status tcks_conv2d_im2col(const tcks_ct* a, const double* kernel, uint32_t 
 /* The same with the laid-out kernel already encoded (at the input's level). */
 tcks_status tcks_conv2d_im2col_pt(const tcks_ct* a, const tcks_pt* kernel, uint32_t taps, uint32_t windows,
                                   tcks_ct** out);
+
+/* Autotuner: picks the CTA size of the limb kernels (transforms and their fused key-switch,
+ * rescale and ModUp work) for this context's N and word type by timing a batched transform at each
+ * candidate, and applies it to the context. With a cache_path (JSON, keyed by GPU name, log N and
+ * word size) a stored choice is reused and a new one recorded. Results are unchanged (bit-exact);
+ * only the launch shape moves. *chosen_threads may be NULL. */
+tcks_status tcks_autotune(tcks_ctx* ctx, const char* cache_path, uint32_t* chosen_threads);
+
+/* --------------------------------------------------- batched launches (descriptor table) ---- */
+/* A batch of independent jobs over raw device buffers, possibly of several contexts (different N)
+ * and levels, run as one unit: the NTT/INTT jobs of a context go out as ONE launch over a
+ * descriptor table (mixed levels and buffers), the key-switch jobs of a context as one batched
+ * launch sequence per (level, op), and the contexts' streams run concurrently (forked from and
+ * joined back into the first job's context stream). Results are bit-identical to the single
+ * calls (tcks_ntt_inplace, tcks_relinearize, tcks_rotate). The batching of homomorphic work on
+ * the device is this library's replacement for the CPU thread pool of §2; the paper has no
+ * counterpart for the call itself.
+ *   TCKS_JOB_NTT / TCKS_JOB_INTT: count polynomials [count][level][N] from d_in to d_out (equal
+ *     pointers transform in place); canonical residues in, forward output bit-reversed.
+ *   TCKS_JOB_RELIN: count size-3 ciphertexts d_in [count][3][level][N] (NTT form) to d_out
+ *     [count][2][level][N] with the relinearization key.
+ *   TCKS_JOB_ROTATE: count ciphertexts d_in [count][2][level][N] rotated left by `step` slots to
+ *     d_out (same shape; must not overlap d_in); needs the Galois key for `step`.
+ * The jobs are independent: no job reads another's output, and they may run in any order or at
+ * once. Pointers may be NULL when count is 0 (the job is skipped).
+ * Buffers are the caller's; they must stay valid until the work completes. Asynchronous: wait
+ * with tcks_ctx_synchronize on jobs[0].ctx. Errors: INVALID_ARG (null pointer, unknown op, level
+ * out of range), NO_GALOIS_KEY, LEVEL_EXHAUSTED (key trimmed below the level), OUT_OF_MEMORY, CUDA;
+ * nothing is launched when validation fails. */
+enum { TCKS_JOB_NTT = 0, TCKS_JOB_INTT = 1, TCKS_JOB_RELIN = 2, TCKS_JOB_ROTATE = 3 };
+typedef struct {
+  tcks_ctx* ctx;
+  uint32_t op;
+  int32_t step;
+  uint32_t count;
+  uint32_t level;
+  const uint64_t* d_in;
+  uint64_t* d_out;
+} tcks_batch_job;
+tcks_status tcks_batch_run(const tcks_batch_job* jobs, uint32_t n_jobs);
+/* The batch captured once as a CUDA graph (after one eager run that builds the key tables) and
+ * replayed by tcks_batch_graph_run on jobs[0].ctx's stream over the same buffers. Every context
+ * must use the library's own pool allocator (UNSUPPORTED otherwise). launches: kernels per replay. */
+typedef struct tcks_batch_graph tcks_batch_graph;
+tcks_status tcks_batch_graph_create(const tcks_batch_job* jobs, uint32_t n_jobs, tcks_batch_graph** out);
+tcks_status tcks_batch_graph_run(tcks_batch_graph* g);
+tcks_status tcks_batch_graph_launches(const tcks_batch_graph* g, uint64_t* launches);
+void tcks_batch_graph_free(tcks_batch_graph* g);
 
 /* ------------------------------------------------------------------ launch accounting ---- */
 /* Number of kernel launches the library has issued since it was loaded. */

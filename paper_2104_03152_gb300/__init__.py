@@ -46,6 +46,7 @@ _SIGS = {
     "tcks_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
     "tcks_last_error_detail": (ctypes.c_char_p, []),
     "tcks_params_create": (ctypes.c_int32, [ctypes.c_uint32, _u32p, ctypes.c_uint32, ctypes.c_double, _vpp]),
+    "tcks_params_create_primes": (ctypes.c_int32, [ctypes.c_uint32, _u64p, ctypes.c_uint32, ctypes.c_double, _vpp]),
     "tcks_params_free": (None, [_vp]),
     "tcks_params_primes": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32]),
     "tcks_context_create": (ctypes.c_int32, [_vp, ctypes.c_uint64, ctypes.c_uint32, _vp, _vp, _vpp]),
@@ -98,6 +99,7 @@ _SIGS = {
                                              ctypes.c_uint32, ctypes.c_uint32, _dblp, ctypes.c_size_t, _u32p]),
     "tcks_conv2d_im2col": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
     "tcks_conv2d_im2col_pt": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
+    "tcks_autotune": (ctypes.c_int32, [_vp, ctypes.c_char_p, _u32p]),
     "tcks_launch_count": (ctypes.c_uint64, []),
     "tcks_profile_start": (ctypes.c_int32, []),
     "tcks_profile_stop": (ctypes.c_int32, []),
@@ -119,6 +121,11 @@ _SIGS = {
     "tcks_cnn_galois_steps": (ctypes.c_int32, [_vp, _i32p, _u32p, ctypes.c_uint32, _u32p]),
     "tcks_cnn_forward": (ctypes.c_int32, [_vp, _vp, _vpp]),
     "tcks_cnn_forward_batch": (ctypes.c_int32, [_vp, _vpp, ctypes.c_uint32, _vpp]),
+    "tcks_batch_run": (ctypes.c_int32, [_vp, ctypes.c_uint32]),
+    "tcks_batch_graph_create": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vpp]),
+    "tcks_batch_graph_run": (ctypes.c_int32, [_vp]),
+    "tcks_batch_graph_launches": (ctypes.c_int32, [_vp, _u64p]),
+    "tcks_batch_graph_free": (None, [_vp]),
     "tcks_cnn_graph_create": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vpp]),
     "tcks_cnn_graph_run": (ctypes.c_int32, [_vp, _vpp, _vpp]),
     "tcks_cnn_graph_free": (None, [_vp]),
@@ -186,16 +193,24 @@ def _p(a: np.ndarray):
 
 
 class Params:
-    def __init__(self, log_n: int, bits, scale: float):
-        b = np.ascontiguousarray(bits, dtype=np.uint32)
+    """CKKS parameters: N = 2^log_n and the prime chain (data primes, then P), chosen from bit sizes
+    (`bits`) or given explicitly (`primes`)."""
+
+    def __init__(self, log_n: int, bits=None, scale: float = 2.0 ** 40, primes=None):
         h = _vp()
-        check(lib().tcks_params_create(log_n, _p(b), len(b), float(scale), ctypes.byref(h)))
+        if primes is not None:
+            q_in = np.ascontiguousarray([int(x) for x in primes], dtype=np.uint64)
+            check(lib().tcks_params_create_primes(log_n, _p(q_in), len(q_in), float(scale), ctypes.byref(h)))
+            bits = [int(x).bit_length() for x in primes]
+        else:
+            b = np.ascontiguousarray(bits, dtype=np.uint32)
+            check(lib().tcks_params_create(log_n, _p(b), len(b), float(scale), ctypes.byref(h)))
         self.h = h
         self.log_n = log_n
         self.N = 1 << log_n
         self.bits = list(bits)
         self.scale = float(scale)
-        q = np.zeros(len(b), dtype=np.uint64)
+        q = np.zeros(len(self.bits), dtype=np.uint64)
         check(lib().tcks_params_primes(h, _p(q), len(q)))
         self.primes = [int(x) for x in q]
 
@@ -252,6 +267,11 @@ class Context:
 
     def synchronize(self):
         check(lib().tcks_ctx_synchronize(self.h))
+
+    def autotune(self, cache_path: str | None = None) -> int:
+        t = ctypes.c_uint32()
+        check(lib().tcks_autotune(self.h, cache_path.encode() if cache_path else None, ctypes.byref(t)))
+        return t.value
 
     def key_bytes(self) -> int:
         v = ctypes.c_uint64()
@@ -560,6 +580,52 @@ class CNN:
         l, sc = ctypes.c_uint32(), ctypes.c_double()
         check(lib().tcks_cnn_export_plaintext(self.h, kind, index, _p(a), a.size, ctypes.byref(l), ctypes.byref(sc)))
         return a, sc.value
+
+
+JOB_NTT, JOB_INTT, JOB_RELIN, JOB_ROTATE = 0, 1, 2, 3
+
+
+class _BatchJob(ctypes.Structure):
+    _fields_ = [("ctx", _vp), ("op", ctypes.c_uint32), ("step", ctypes.c_int32), ("count", ctypes.c_uint32),
+                ("level", ctypes.c_uint32), ("d_in", _vp), ("d_out", _vp)]
+
+
+def _job_array(jobs):
+    """jobs: (context, op, step, count, level, d_in, d_out) tuples with device pointers as ints."""
+    arr = (_BatchJob * len(jobs))()
+    for i, (ctx, op, step, count, level, d_in, d_out) in enumerate(jobs):
+        arr[i] = _BatchJob(ctx.h, op, step, count, level, _vp(d_in), _vp(d_out))
+    return arr
+
+
+def batch_run(jobs):
+    """Runs a descriptor table of NTT / INTT / relinearize / rotate jobs over raw device buffers,
+    possibly of several contexts and levels, as one batched unit (asynchronous on the first job's
+    context stream)."""
+    arr = _job_array(jobs)
+    check(lib().tcks_batch_run(arr, len(jobs)))
+
+
+class BatchGraph:
+    """A job table captured once as a CUDA graph and replayed over the same buffers."""
+
+    def __init__(self, jobs):
+        self._ctxs = [j[0] for j in jobs]  # the contexts outlive the graph
+        arr = _job_array(jobs)
+        h = _vp()
+        check(lib().tcks_batch_graph_create(arr, len(jobs), ctypes.byref(h)))
+        self.h = h
+        n = np.zeros(1, dtype=np.uint64)
+        check(lib().tcks_batch_graph_launches(h, _p(n)))
+        self.launches = int(n[0])
+
+    def run(self):
+        check(lib().tcks_batch_graph_run(self.h))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().tcks_batch_graph_free(self.h)
+            self.h = None
 
 
 class CNNGraph:

@@ -21,6 +21,8 @@ tcks_status record(tcks_status code, const std::string& msg) {
 
 }  // namespace
 
+static void ctx_destroy(tcks_ctx* c);
+
 #define TCKS_API_BEGIN try {
 #define TCKS_API_END                                                   \
   }                                                                    \
@@ -52,18 +54,29 @@ void check_launch(const char* what) { check_cuda(cudaGetLastError(), what); }
 tcks_ct* new_ct(tcks_ctx* c, u32 level, double scale) {
   DevBuf b(c, ct_words(c, level));
   tcks_ct* ct = new tcks_ct{c, b.release(), level, scale};
+  ctx_retain(c);
   return ct;
 }
 
 tcks_pt* new_pt(tcks_ctx* c, u32 level, double scale) {
   DevBuf b(c, pt_words(c, level));
-  return new tcks_pt{c, b.release(), level, scale};
+  tcks_pt* pt = new tcks_pt{c, b.release(), level, scale};
+  ctx_retain(c);
+  return pt;
 }
 
 void free_ct(tcks_ct* ct) {
   if (!ct) return;
-  if (ct->d) ct->ctx->dev_free(ct->d);
+  tcks_ctx* c = ct->ctx;
+  if (ct->d) c->dev_free(ct->d);
   delete ct;
+  ctx_release(c);
+}
+
+void ctx_retain(tcks_ctx* c) { c->refs.fetch_add(1); }
+
+void ctx_release(tcks_ctx* c) {
+  if (c->refs.fetch_sub(1) == 1) ::ctx_destroy(c);
 }
 
 u32 step_mod(const tcks_ctx* c, int64_t step) {
@@ -311,6 +324,31 @@ tcks_status tcks_params_create(uint32_t log_n, const uint32_t* bit_sizes, uint32
   TCKS_API_END
 }
 
+tcks_status tcks_params_create_primes(uint32_t log_n, const uint64_t* primes, uint32_t n_primes, double scale,
+                                      tcks_params** out) {
+  TCKS_API_BEGIN
+  if (!out || !primes) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (log_n < 3 || log_n > 16) fail(TCKS_ERR_BAD_PARAMS, "log_n must be in [3, 16]");
+  if (n_primes < 2 || n_primes > CRT_MAXW - 1) fail(TCKS_ERR_BAD_PARAMS, "need 2..33 primes (data primes + P)");
+  if (!(scale > 0) || !std::isfinite(scale)) fail(TCKS_ERR_BAD_PARAMS, "scale must be positive");
+  std::vector<u64> chain(primes, primes + n_primes);
+  std::vector<u32> bits;
+  const u64 two_n = 2ull << log_n;
+  for (u32 i = 0; i < n_primes; ++i) {
+    const u64 q = chain[i];
+    if (q >= (1ull << 61) || !is_prime_u64(q) || q % two_n != 1)
+      fail(TCKS_ERR_BAD_PARAMS, "prime " + std::to_string(i) + " is not a prime below 2^61 with q == 1 mod 2N");
+    for (u32 j = 0; j < i; ++j)
+      if (chain[j] == q) fail(TCKS_ERR_BAD_PARAMS, "prime " + std::to_string(i) + " repeats an earlier one");
+    u32 b = 0;
+    while (b < 64 && (q >> b)) ++b;
+    bits.push_back(b);
+  }
+  *out = new tcks_params{log_n, bits, chain, scale};
+  TCKS_API_END
+}
+
 void tcks_params_free(tcks_params* p) { delete p; }
 
 tcks_status tcks_params_primes(const tcks_params* p, uint64_t* primes, uint32_t capacity) {
@@ -358,6 +396,7 @@ tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32
   c->d_mods = c->dev_alloc(sizeof(ModConst) * nm);
   c->d_pairs = c->dev_alloc(sizeof(PairConst) * nm * nm);
   c->d_tw = (u64*)c->dev_alloc(sizeof(u64) * H.tw.size());
+  if (H.narrow) c->d_tw32 = (u32*)c->dev_alloc(sizeof(u32) * H.tw32.size());
   c->d_slot = (u32*)c->dev_alloc(sizeof(u32) * H.slot_index.size());
   c->d_zeta = (double*)c->dev_alloc(sizeof(double) * H.zeta.size());
   c->d_status = (int*)c->dev_alloc(sizeof(int) * 4);
@@ -385,14 +424,19 @@ tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32
   check_cuda(cudaMemcpyAsync(c->d_mods, H.mods.data(), sizeof(ModConst) * nm, cudaMemcpyHostToDevice, s), "H2D");
   check_cuda(cudaMemcpyAsync(c->d_pairs, H.pairs.data(), sizeof(PairConst) * nm * nm, cudaMemcpyHostToDevice, s), "H2D");
   check_cuda(cudaMemcpyAsync(c->d_tw, H.tw.data(), sizeof(u64) * H.tw.size(), cudaMemcpyHostToDevice, s), "H2D");
+  if (H.narrow)
+    check_cuda(cudaMemcpyAsync(c->d_tw32, H.tw32.data(), sizeof(u32) * H.tw32.size(), cudaMemcpyHostToDevice, s),
+               "H2D");
   check_cuda(cudaMemcpyAsync(c->d_slot, H.slot_index.data(), sizeof(u32) * H.slot_index.size(), cudaMemcpyHostToDevice, s), "H2D");
   check_cuda(cudaMemcpyAsync(c->d_zeta, H.zeta.data(), sizeof(double) * H.zeta.size(), cudaMemcpyHostToDevice, s), "H2D");
   check_cuda(cudaMemcpyAsync(c->d_qwords, qw.data(), sizeof(u64) * qw.size(), cudaMemcpyHostToDevice, s), "H2D");
-  c->table_bytes = sizeof(ModConst) * nm + sizeof(PairConst) * nm * nm + 8 * H.tw.size() + 4 * H.slot_index.size() +
-                   8 * H.zeta.size() + 8 * qw.size();
+  c->table_bytes = sizeof(ModConst) * nm + sizeof(PairConst) * nm * nm + 8 * H.tw.size() + 4 * H.tw32.size() +
+                   4 * H.slot_index.size() + 8 * H.zeta.size() + 8 * qw.size();
   c->T.mods = (const ModConst*)c->d_mods;
   c->T.pairs = (const PairConst*)c->d_pairs;
   c->T.tw = c->d_tw;
+  c->T.tw32 = c->d_tw32;
+  c->T.narrow = H.narrow ? 1u : 0u;
   c->T.log_n = params->log_n;
   c->T.n_mods = nm;
   c->T.L = c->L;
@@ -414,15 +458,24 @@ tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32
 
 void tcks_ctx_free(tcks_ctx* c) {
   if (!c) return;
+  ctx_release(c);
+}
+
+}  // extern "C"
+
+static void ctx_destroy(tcks_ctx* c) {
   cudaStreamSynchronize(c->stream);
   c->keys_changed();
   for (auto& kv : c->galois) c->dev_free(kv.second.d);
-  void* bufs[] = {c->d_mods, c->d_pairs, c->d_tw, c->d_slot, c->d_zeta, c->d_qwords, c->d_status, c->sk, c->pk, c->rlk};
+  void* bufs[] = {c->d_mods, c->d_pairs, c->d_tw,  c->d_tw32, c->d_slot, c->d_zeta,
+                  c->d_qwords, c->d_status, c->sk, c->pk,   c->rlk};
   for (void* b : bufs) c->dev_free(b);
   cudaStreamSynchronize(c->stream);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
+
+extern "C" {
 
 tcks_status tcks_ctx_info(const tcks_ctx* c, uint32_t* log_n, uint32_t* n_data_primes, double* scale) {
   TCKS_API_BEGIN
@@ -683,8 +736,10 @@ void tcks_ct_free(tcks_ct* ct) { free_ct(ct); }
 
 void tcks_pt_free(tcks_pt* pt) {
   if (!pt) return;
-  if (pt->d) pt->ctx->dev_free(pt->d);
+  tcks_ctx* c = pt->ctx;
+  if (pt->d) c->dev_free(pt->d);
   delete pt;
+  ctx_release(c);
 }
 
 // ------------------------------------------------------------------------ element-wise ops ----
@@ -915,6 +970,7 @@ tcks_status tcks_matrix_encode(tcks_ctx* c, const double* M, uint32_t rows, uint
     encode_into(c, (const double*)dv.p, slots, c->params.scale, l, d.p + (size_t)k * l * c->N);
   }
   *out = new tcks_matrix{c, rows, cols, l, c->params.scale, d.release()};
+  ctx_retain(c);
   TCKS_API_END
 }
 
@@ -932,13 +988,16 @@ tcks_status tcks_matrix_import(tcks_ctx* c, const uint64_t* diag_limbs, uint32_t
   check_cuda(cudaMemcpyAsync(d.p, diag_limbs, words * 8, cudaMemcpyHostToDevice, c->stream), "matrix import");
   check_cuda(cudaStreamSynchronize(c->stream), "matrix import");
   *out = new tcks_matrix{c, rows, cols, level, scale, d.release()};
+  ctx_retain(c);
   TCKS_API_END
 }
 
 void tcks_matrix_free(tcks_matrix* m) {
   if (!m) return;
-  m->ctx->dev_free(m->d);
+  tcks_ctx* c = m->ctx;
+  c->dev_free(m->d);
   delete m;
+  ctx_release(c);
 }
 
 tcks_status tcks_vecmat_plain(const tcks_ct* a, const tcks_matrix* M, tcks_ct** out) {

@@ -1,0 +1,130 @@
+// Autotuner for the limb kernels' CTA size.
+//
+// Every limb kernel (transforms with their fused prologues and epilogues) strides its work over
+// the CTA's threads, so any multiple of 32 up to the slice size is correct; the best size depends
+// on the GPU, N and the word type. The tuner times a batched forward + inverse transform of 256 limbs
+// for each candidate (N/64, N/32, N/16 threads per slice, clamped to [32, 1024]), keeps the fastest,
+// and records it in a small JSON file keyed by "<GPU name>|<log N>|<word bits>", so a later context
+// with the same key reads the choice instead of measuring again.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <fstream>
+#include <map>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "context.h"
+
+using namespace tcks;
+
+namespace {
+
+// The cache: a flat JSON object {"key": threads, ...}.
+std::map<std::string, u32> read_cache(const std::string& path) {
+  std::map<std::string, u32> out;
+  std::ifstream f(path);
+  if (!f) return out;
+  std::stringstream ss;
+  ss << f.rdbuf();
+  const std::string t = ss.str();
+  size_t i = 0;
+  while ((i = t.find('"', i)) != std::string::npos) {
+    const size_t j = t.find('"', i + 1);
+    if (j == std::string::npos) break;
+    const std::string key = t.substr(i + 1, j - i - 1);
+    size_t k = t.find(':', j);
+    if (k == std::string::npos) break;
+    out[key] = (u32)std::strtoul(t.c_str() + k + 1, nullptr, 10);
+    i = t.find_first_of(",}", k);
+    if (i == std::string::npos) break;
+  }
+  return out;
+}
+
+void write_cache(const std::string& path, const std::map<std::string, u32>& c) {
+  const std::string tmp = path + ".tmp";
+  {
+    std::ofstream f(tmp);
+    f << "{";
+    bool first = true;
+    for (const auto& kv : c) {
+      f << (first ? "\n  " : ",\n  ") << '"' << kv.first << "\": " << kv.second;
+      first = false;
+    }
+    f << "\n}\n";
+  }
+  std::rename(tmp.c_str(), path.c_str());
+}
+
+}  // namespace
+
+extern "C" tcks_status tcks_autotune(tcks_ctx* c, const char* cache_path, uint32_t* chosen_threads) {
+  try {
+    if (!c) fail(TCKS_ERR_INVALID_ARG, "null context");
+    cudaDeviceProp prop;
+    check_cuda(cudaGetDeviceProperties(&prop, c->device), "device properties");
+    const u32 log_n = c->params.log_n;
+    const u32 log_c = log_n > 14 ? log_n - 14 : 0;  // the cluster split of a limb (see ntt.cuh)
+    const u32 ns = 1u << (log_n - log_c);
+    const std::string key =
+        std::string(prop.name) + "|" + std::to_string(log_n) + "|" + (c->T.narrow ? "32" : "64");
+    std::map<std::string, u32> cache;
+    if (cache_path && *cache_path) cache = read_cache(cache_path);
+    u32 best = 0;
+    auto it = cache.find(key);
+    if (it != cache.end() && it->second >= 32 && it->second <= 1024 && it->second % 32 == 0) {
+      best = it->second;
+    } else {
+      std::vector<u32> cand;
+      for (u32 div : {64u, 32u, 16u}) {
+        u32 t = ns / div;
+        t = t < 32 ? 32 : (t > 1024 ? 1024 : t);
+        if (std::find(cand.begin(), cand.end(), t) == cand.end()) cand.push_back(t);
+      }
+      const u32 limbs = 256, lv = c->L + 1;
+      DevBuf buf(c, (size_t)limbs * c->N);
+      check_cuda(cudaMemsetAsync(buf.p, 0, (size_t)limbs * c->N * 8, c->stream), "tune buffer");
+      cudaEvent_t a, b;
+      check_cuda(cudaEventCreate(&a), "event");
+      check_cuda(cudaEventCreate(&b), "event");
+      float best_ms = 1e30f;
+      const u32 saved = c->T.limb_threads;
+      for (u32 t : cand) {
+        c->T.limb_threads = t;
+        for (int rep = 0; rep < 2; ++rep) {  // warm-up, then timed
+          cudaEventRecord(a, c->stream);
+          for (int it2 = 0; it2 < 3; ++it2) {
+            launch_ntt(c->T, false, buf.p, (u64)lv * c->N, buf.p, (u64)lv * c->N, limbs, 0, lv, c->stream);
+            launch_ntt(c->T, true, buf.p, (u64)lv * c->N, buf.p, (u64)lv * c->N, limbs, 0, lv, c->stream);
+          }
+          cudaEventRecord(b, c->stream);
+        }
+        check_cuda(cudaEventSynchronize(b), "tune");
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = t;
+        }
+      }
+      c->T.limb_threads = saved;
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      check_launch("autotune");
+      if (cache_path && *cache_path) {
+        cache[key] = best;
+        write_cache(cache_path, cache);
+      }
+    }
+    c->T.limb_threads = best;
+    if (chosen_threads) *chosen_threads = best;
+  } catch (const tcks::Error& e) {
+    return abi_record(e.code, e.msg);
+  }
+  abi_clear();
+  return TCKS_OK;
+}

@@ -1,0 +1,269 @@
+// Batched launches over a descriptor table of independent jobs (several contexts, N and levels):
+// the device-side replacement for the CPU thread pool that runs TenSEAL's per-ciphertext work.
+//   * NTT / INTT jobs of one context: one launch of k_ntt_desc over all of them (mixed levels and
+//     buffers), split only when the table holds more than kNttDescMax batches;
+//   * relinearize / rotate jobs: the batched key-switch sequence (ModUp, inner product, ModDown)
+//     per job, in sub-batches whose scratch stays under a fixed bound;
+//   * each context's work is queued on its own stream, forked from and joined back into the first
+//     job's context stream, so that different N overlap on the device.
+// The whole batch can be captured once as a CUDA graph and replayed.
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "context.h"
+
+using namespace tcks;
+
+namespace tcks {
+
+namespace {
+
+constexpr u64 kScratchBound = 4ull << 30;  // bytes of key-switch scratch per sub-batch
+
+// Key-switch scratch words per ciphertext at level ell: coefficients, digits [ell][ell+1], P limbs.
+u64 ks_scratch_words(const tcks_ctx* c, u32 ell) { return ((u64)ell + (u64)ell * (ell + 1) + 2) * c->N; }
+
+// log2 of the CTAs per limb of the limb kernels (clusters above N = 2^14)
+u32 cluster_log(const tcks_ctx* c) { return c->params.log_n > 14 ? c->params.log_n - 14 : 0; }
+
+u32 sub_batch(const tcks_ctx* c, u32 ell, u32 count) {
+  const u64 per = ks_scratch_words(c, ell) * 8;
+  return (u32)std::max<u64>(1, std::min<u64>(count, kScratchBound / per));
+}
+
+// Rotation of `count` ciphertexts [count][2][ell][N] by one step: out = tau_g(c0) + ModDown(<digits, gk_0>),
+// ModDown(<digits, gk_1>) with the automorphism folded into the reads.
+void op_rotate_batch(tcks_ctx* c, const u64* in, u32 count, u32 ell, int32_t step, u64* out) {
+  const size_t n = c->N;
+  const u64 cw = ct_words(c, ell);
+  const u32 k = step_mod(c, step);
+  if (k == 0) {
+    check_cuda(cudaMemcpyAsync(out, in, (size_t)count * cw * 8, cudaMemcpyDeviceToDevice, c->stream), "rotate by 0");
+    return;
+  }
+  const KeyTable& kt = key_table(c, {k}, ell);
+  const u32 sb = sub_batch(c, ell, count);
+  DevBuf coef(c, (size_t)sb * ell * n), digits(c, (size_t)sb * ell * (ell + 1) * n), top(c, (size_t)sb * 2 * n);
+  for (u32 b0 = 0; b0 < count; b0 += sb) {
+    const u32 bn = std::min(sb, count - b0);
+    const u64* src = in + (size_t)b0 * cw;
+    launch_modup(c->T, src + (size_t)ell * n, cw, bn, ell, coef.p, digits.p, c->stream);
+    KsPlan p{};
+    p.keys = kt.d;
+    p.digits = digits.p;
+    p.digits_b = (u64)ell * (ell + 1) * n;
+    p.top = top.p;
+    p.out = out + (size_t)b0 * cw;
+    p.out_b = cw;
+    p.add0 = src;
+    p.add0_b = cw;
+    p.R = 1;
+    p.B = bn;
+    p.add_perm = 1;
+    launch_keyswitch(c->T, ell, p, c->stream);
+  }
+  check_launch("rotate batch");
+}
+
+void op_relin_batch(tcks_ctx* c, const u64* in, u32 count, u32 ell, u64* out) {
+  const u32 sb = sub_batch(c, ell, count);
+  const u64 w3 = (u64)3 * ell * c->N, w2 = ct_words(c, ell);
+  for (u32 b0 = 0; b0 < count; b0 += sb)
+    op_relinearize(c, in + (size_t)b0 * w3, ell, out + (size_t)b0 * w2, std::min(sb, count - b0));
+}
+
+void validate(const tcks_batch_job* jobs, u32 n_jobs) {
+  if (!jobs || !n_jobs) fail(TCKS_ERR_INVALID_ARG, "empty job list");
+  for (u32 i = 0; i < n_jobs; ++i) {
+    const tcks_batch_job& j = jobs[i];
+    if (!j.ctx || (j.count && (!j.d_in || !j.d_out)))
+      fail(TCKS_ERR_INVALID_ARG, "job " + std::to_string(i) + ": null pointer");
+    tcks_ctx* c = j.ctx;
+    switch (j.op) {
+      case TCKS_JOB_NTT:
+      case TCKS_JOB_INTT:
+        if (j.level < 1 || j.level > c->L + 1) fail(TCKS_ERR_INVALID_ARG, "job " + std::to_string(i) + ": level out of range");
+        if ((u64)j.count * j.level > 0x7fffffffull >> cluster_log(c))
+          fail(TCKS_ERR_INVALID_ARG, "job " + std::to_string(i) + ": too many limbs for one launch");
+        break;
+      case TCKS_JOB_RELIN:
+        if (j.level < 1 || j.level > c->L) fail(TCKS_ERR_INVALID_ARG, "job " + std::to_string(i) + ": level out of range");
+        key_table(c, {0u}, j.level);
+        break;
+      case TCKS_JOB_ROTATE:
+        if (j.level < 1 || j.level > c->L) fail(TCKS_ERR_INVALID_ARG, "job " + std::to_string(i) + ": level out of range");
+        if (step_mod(c, j.step)) galois_key_for(c, j.step, j.level);
+        if (j.count && j.d_in == j.d_out) fail(TCKS_ERR_INVALID_ARG, "job " + std::to_string(i) + ": rotation output overlaps input");
+        break;
+      default:
+        fail(TCKS_ERR_INVALID_ARG, "job " + std::to_string(i) + ": unknown op");
+    }
+  }
+}
+
+void run_ctx_ntt(tcks_ctx* c, const std::vector<const tcks_batch_job*>& js, bool inverse) {
+  NttDescTable tab{};
+  u32 total = 0;
+  auto flush = [&]() {
+    launch_ntt_desc(c->T, inverse, tab, total, c->stream);
+    tab.n = 0;
+    total = 0;
+  };
+  for (const tcks_batch_job* j : js) {
+    if (!j->count) continue;
+    const u64 limbs = (u64)j->count * j->level;
+    if (tab.n == kNttDescMax || total + limbs > (0x7fffffffull >> cluster_log(c))) flush();
+    tab.d[tab.n++] = NttDesc{j->d_in, j->d_out, total, j->level};
+    total += (u32)limbs;
+  }
+  flush();
+  check_launch("batched NTT");
+}
+
+// Queue every job; contexts other than the first run on their own streams between a fork and a join.
+void run_jobs(const tcks_batch_job* jobs, u32 n_jobs) {
+  std::vector<tcks_ctx*> order;
+  std::map<tcks_ctx*, std::vector<const tcks_batch_job*>> by_ctx;
+  for (u32 i = 0; i < n_jobs; ++i) {
+    if (!by_ctx.count(jobs[i].ctx)) order.push_back(jobs[i].ctx);
+    by_ctx[jobs[i].ctx].push_back(&jobs[i]);
+  }
+  cudaStream_t origin = order[0]->stream;
+  std::vector<cudaEvent_t> events;
+  struct Events {
+    std::vector<cudaEvent_t>& v;
+    ~Events() {
+      for (cudaEvent_t e : v) cudaEventDestroy(e);
+    }
+  } guard{events};
+  auto new_event = [&]() {
+    cudaEvent_t e;
+    check_cuda(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    events.push_back(e);
+    return e;
+  };
+  cudaEvent_t fork = new_event();
+  check_cuda(cudaEventRecord(fork, origin), "fork");
+  for (tcks_ctx* c : order) {
+    if (c->stream != origin) check_cuda(cudaStreamWaitEvent(c->stream, fork, 0), "fork wait");
+    const auto& js = by_ctx[c];
+    std::vector<const tcks_batch_job*> fwd, inv;
+    for (const tcks_batch_job* j : js) {
+      if (j->op == TCKS_JOB_NTT) fwd.push_back(j);
+      if (j->op == TCKS_JOB_INTT) inv.push_back(j);
+    }
+    if (!fwd.empty()) run_ctx_ntt(c, fwd, false);
+    if (!inv.empty()) run_ctx_ntt(c, inv, true);
+    for (const tcks_batch_job* j : js) {
+      if (!j->count) continue;
+      if (j->op == TCKS_JOB_RELIN) op_relin_batch(c, j->d_in, j->count, j->level, j->d_out);
+      if (j->op == TCKS_JOB_ROTATE) op_rotate_batch(c, j->d_in, j->count, j->level, j->step, j->d_out);
+    }
+    if (c->stream != origin) {
+      cudaEvent_t join = new_event();
+      check_cuda(cudaEventRecord(join, c->stream), "join");
+      check_cuda(cudaStreamWaitEvent(origin, join, 0), "join wait");
+    }
+  }
+}
+
+}  // namespace
+
+}  // namespace tcks
+
+struct tcks_batch_graph {
+  std::vector<tcks_ctx*> ctxs;  // retained
+  cudaStream_t origin = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  u64 launches = 0;
+};
+
+#define BATCH_BEGIN try {
+#define BATCH_END                                                    \
+  }                                                                  \
+  catch (const tcks::Error& e) {                                     \
+    return tcks::abi_record(e.code, e.msg);                          \
+  }                                                                  \
+  catch (const std::bad_alloc&) {                                    \
+    return tcks::abi_record(TCKS_ERR_OUT_OF_MEMORY, "host allocation failed"); \
+  }                                                                  \
+  tcks::abi_clear();                                                 \
+  return TCKS_OK;
+
+extern "C" {
+
+tcks_status tcks_batch_run(const tcks_batch_job* jobs, uint32_t n_jobs) {
+  BATCH_BEGIN
+  validate(jobs, n_jobs);
+  run_jobs(jobs, n_jobs);
+  BATCH_END
+}
+
+void tcks_batch_graph_free(tcks_batch_graph* g) {
+  if (!g) return;
+  if (g->origin) cudaStreamSynchronize(g->origin);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  for (tcks_ctx* c : g->ctxs) ctx_release(c);
+  delete g;
+}
+
+tcks_status tcks_batch_graph_create(const tcks_batch_job* jobs, uint32_t n_jobs, tcks_batch_graph** out) {
+  struct Guard {
+    tcks_batch_graph* g = nullptr;
+    ~Guard() { tcks_batch_graph_free(g); }
+  } guard;
+  BATCH_BEGIN
+  if (!out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  validate(jobs, n_jobs);
+  guard.g = new tcks_batch_graph();
+  tcks_batch_graph* g = guard.g;
+  for (u32 i = 0; i < n_jobs; ++i) {
+    tcks_ctx* c = jobs[i].ctx;
+    if (c->has_alloc) fail(TCKS_ERR_UNSUPPORTED, "graph capture needs the library's own stream-ordered pool allocator");
+    if (std::find(g->ctxs.begin(), g->ctxs.end(), c) == g->ctxs.end()) {
+      ctx_retain(c);
+      g->ctxs.push_back(c);
+    }
+  }
+  g->origin = jobs[0].ctx->stream;
+  // one eager pass builds every cached key table (their host copies cannot run inside a capture)
+  run_jobs(jobs, n_jobs);
+  for (tcks_ctx* c : g->ctxs) check_cuda(cudaStreamSynchronize(c->stream), "graph warm-up");
+  const u64 n0 = tcks_launch_count();
+  check_cuda(cudaStreamBeginCapture(g->origin, cudaStreamCaptureModeThreadLocal), "begin capture");
+  try {
+    run_jobs(jobs, n_jobs);
+  } catch (...) {
+    cudaGraph_t dead = nullptr;
+    cudaStreamEndCapture(g->origin, &dead);
+    if (dead) cudaGraphDestroy(dead);
+    throw;
+  }
+  check_cuda(cudaStreamEndCapture(g->origin, &g->graph), "end capture");
+  g->launches = tcks_launch_count() - n0;
+  check_cuda(cudaGraphInstantiate(&g->exec, g->graph, 0), "graph instantiate");
+  *out = g;
+  guard.g = nullptr;
+  BATCH_END
+}
+
+tcks_status tcks_batch_graph_run(tcks_batch_graph* g) {
+  BATCH_BEGIN
+  if (!g) fail(TCKS_ERR_INVALID_ARG, "null graph");
+  check_cuda(cudaGraphLaunch(g->exec, g->origin), "graph launch");
+  count_launches(g->launches);
+  BATCH_END
+}
+
+tcks_status tcks_batch_graph_launches(const tcks_batch_graph* g, uint64_t* launches) {
+  BATCH_BEGIN
+  if (!g || !launches) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *launches = g->launches;
+  BATCH_END
+}
+
+}  // extern "C"

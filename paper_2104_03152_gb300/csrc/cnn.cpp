@@ -183,13 +183,6 @@ static void cnn_forward_dev(const tcks_cnn* m, const u64* in, u64 in_stride, u32
 
 }  // namespace tcks
 
-// The ABI wrappers share api.cpp's error channel through these two helpers.
-namespace tcks {
-tcks_status abi_record(tcks_status code, const std::string& msg);
-void abi_clear();
-void count_launches(u64 n);
-}  // namespace tcks
-
 #define CNN_BEGIN try {
 #define CNN_END                                                       \
   }                                                                   \
@@ -213,6 +206,7 @@ void tcks_cnn_free(tcks_cnn* m) {
   tcks_matrix_free(m->fc1);
   tcks_matrix_free(m->fc2);
   delete m;
+  ctx_release(c);
 }
 
 tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* conv_b, uint32_t kernels, uint32_t taps,
@@ -236,6 +230,7 @@ tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* con
     fail(TCKS_ERR_INVALID_ARG, "FC sizes must be powers of two with classes <= hidden <= kernels*windows");
   m = new tcks_cnn();
   m->ctx = c;
+  ctx_retain(c);
   m->kernels = kernels;
   m->taps = taps;
   m->windows = windows;
@@ -383,6 +378,7 @@ tcks_status tcks_cnn_forward_batch(const tcks_cnn* m, const tcks_ct* const* in, 
 
 // -------------------------------------------------------------------------- CUDA graphs ----
 struct tcks_cnn_graph {
+  tcks_ctx* ctx;  // retained: the graph's buffers belong to it
   const tcks_cnn* m;
   u32 count;
   u64* in;   // staging [count][2][L][N]
@@ -394,13 +390,14 @@ struct tcks_cnn_graph {
 
 void tcks_cnn_graph_free(tcks_cnn_graph* g) {
   if (!g) return;
-  tcks_ctx* c = g->m->ctx;
+  tcks_ctx* c = g->ctx;
   cudaStreamSynchronize(c->stream);
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   c->dev_free(g->in);
   c->dev_free(g->out);
   delete g;
+  ctx_release(c);
 }
 
 tcks_status tcks_cnn_graph_create(const tcks_cnn* m, uint32_t count, tcks_cnn_graph** out) {
@@ -414,7 +411,8 @@ tcks_status tcks_cnn_graph_create(const tcks_cnn* m, uint32_t count, tcks_cnn_gr
   tcks_ctx* c = m->ctx;
   if (c->has_alloc) fail(TCKS_ERR_UNSUPPORTED, "graph capture needs the library's own stream-ordered pool allocator");
   const u64 w_in = ct_words(c, m->L), w_out = ct_words(c, m->L - 6);
-  guard.g = new tcks_cnn_graph{m, count, nullptr, nullptr, nullptr, nullptr, 0};
+  guard.g = new tcks_cnn_graph{c, m, count, nullptr, nullptr, nullptr, nullptr, 0};
+  ctx_retain(c);
   tcks_cnn_graph* g = guard.g;
   g->in = (u64*)c->dev_alloc((size_t)count * w_in * 8);
   g->out = (u64*)c->dev_alloc((size_t)count * w_out * 8);

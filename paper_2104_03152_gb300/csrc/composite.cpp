@@ -64,11 +64,10 @@ void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell,
   u32 chunks_pb = (u32)std::min<u64>(RB, std::max<u64>(1, (target + count * 2 * ell - 1) / (count * 2 * ell)));
   const u32 chunk = (RB + chunks_pb - 1) / chunks_pb;
   chunks_pb = (RB + chunk - 1) / chunk;
-  const u32 blocks = (R + RB - 1) / RB;
   DevBuf top(c, (size_t)per_rot * RB);
-  DevBuf partial(c, (size_t)count * blocks * chunks_pb * cw);
+  // chunk partials per request, reused (accumulated) across the rotation blocks
+  DevBuf partial(c, (size_t)count * chunks_pb * cw);
   const u64 diag_stride = (u64)M->level * n;
-  u32 total_chunks = 0;
   for (u32 rb0 = 0; rb0 < R; rb0 += RB) {
     const u32 rbn = std::min(RB, R - rb0);
     KsPlan p{};
@@ -92,12 +91,11 @@ void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell,
     v.R = rbn;
     v.B = count;
     v.chunk = chunk;
-    v.chunks = (rbn + chunk - 1) / chunk;
-    // partials of this block: [count][chunks][...] laid after the previous blocks' partials per request
-    v.partial = partial.p + (size_t)total_chunks * cw;
-    v.partial_b = (u64)blocks * chunks_pb * cw;
+    v.chunks = chunks_pb;  // a short last block leaves its upper chunks empty (zero rotations)
+    v.partial = partial.p;
+    v.partial_b = (u64)chunks_pb * cw;
+    v.accumulate = rb0 > 0;
     launch_vecmat_acc(c->T, ell, v, c->stream);
-    total_chunks += v.chunks;
     check_launch("vecmat block");
   }
   VecmatPlan red{};
@@ -105,9 +103,9 @@ void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell,
   red.ct_b = cw;
   red.diag = M->d;
   red.partial = partial.p;
-  red.partial_b = (u64)blocks * chunks_pb * cw;
+  red.partial_b = (u64)chunks_pb * cw;
   red.B = count;
-  red.chunks = total_chunks;
+  red.chunks = chunks_pb;
   launch_vecmat_reduce(c->T, ell, red, acc.p, c->stream);
   op_rescale(c, acc.p, ell, out, count);
   check_launch("vecmat");

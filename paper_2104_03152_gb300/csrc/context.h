@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <map>
 #include <string>
 #include <vector>
@@ -49,6 +50,7 @@ struct tcks_ctx {
   void* d_mods = nullptr;
   void* d_pairs = nullptr;
   tcks::u64* d_tw = nullptr;
+  tcks::u32* d_tw32 = nullptr;
   tcks::u32* d_slot = nullptr;
   double* d_zeta = nullptr;
   tcks::u64* d_qwords = nullptr;
@@ -68,6 +70,9 @@ struct tcks_ctx {
   std::map<tcks::u32, tcks::GaloisKey> galois;  // step mod N/2 -> key
   std::map<std::vector<tcks::u32>, tcks::KeyTable> key_tables;  // cached device key tables
   tcks::u64 table_bytes = 0;
+  // References: the caller's handle plus every object made from the context (ciphertexts,
+  // plaintexts, matrices, models, graphs). The context is destroyed when the last one goes.
+  std::atomic<int> refs{1};
 
   // Galois keys changed: drop every cached key table.
   void keys_changed();
@@ -100,6 +105,9 @@ struct tcks_matrix {
 
 namespace tcks {
 
+void ctx_retain(tcks_ctx* c);
+void ctx_release(tcks_ctx* c);
+
 // Device buffer owned by a context, released (stream-ordered) when it goes out of scope.
 struct DevBuf {
   tcks_ctx* ctx = nullptr;
@@ -131,6 +139,10 @@ struct DevBuf {
 void check_cuda(cudaError_t e, const char* what);
 void check_launch(const char* what);
 [[noreturn]] void fail(tcks_status code, const std::string& msg);
+// Record / clear the calling thread's last error for the ABI (api.cpp); count graph-replayed launches.
+tcks_status abi_record(tcks_status code, const std::string& msg);
+void abi_clear();
+void count_launches(u64 n);
 
 inline size_t ct_words(const tcks_ctx* c, u32 level) { return (size_t)2 * level * c->N; }
 inline size_t pt_words(const tcks_ctx* c, u32 level) { return (size_t)level * c->N; }

@@ -44,10 +44,10 @@ u32 ntt_threads(u32 log_n) { return limb_shape(log_n).threads; }
 
 // --------------------------------------------------------------------------- batched NTT ----
 // Job j: limb (j % per) of entry (j / per): src + (j/per)*src_outer + (j%per)*N, prime mod_base + j%per.
-template <bool INVERSE, int LC>
+template <bool INVERSE, typename W, int LC>
 __global__ void k_ntt(DevTables T, const u64* __restrict__ src, u64 src_outer, u64* __restrict__ dst, u64 dst_outer,
                       u32 mod_base, u32 per) {
-  extern __shared__ u64 s[];
+  TCKS_SMEM(W);
   const Slice sl = slice_of<LC>(T);
   const u64 n = 1ull << T.log_n;
   const u32 jo = sl.job / per, ji = sl.job % per;
@@ -57,19 +57,81 @@ __global__ void k_ntt(DevTables T, const u64* __restrict__ src, u64 src_outer, u
   u64* out = dst + jo * dst_outer + ji * n + sl.off;
   for (u32 k = 2 * threadIdx.x; k < sl.ns; k += 2 * blockDim.x) {
     const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(in + k);
-    s[sw(k)] = v.x;
-    s[sw(k + 1)] = v.y;
+    s[sw(k)] = (W)v.x;
+    s[sw(k + 1)] = (W)v.y;
   }
   __syncthreads();
   if (INVERSE) {
-    ntt_inv_slice<LC>(s, T, mod, sl.rank);
+    ntt_inv_slice<W, LC>(s, T, mod, sl.rank);
     for (u32 k = 2 * threadIdx.x; k < sl.ns; k += 2 * blockDim.x)
-      *reinterpret_cast<ulonglong2*>(out + k) = make_ulonglong2(inv_final(s[sw(k)], m), inv_final(s[sw(k + 1)], m));
+      *reinterpret_cast<ulonglong2*>(out + k) = make_ulonglong2(Ar<W>::inv_out(s[sw(k)], m), Ar<W>::inv_out(s[sw(k + 1)], m));
   } else {
-    ntt_fwd_slice<LC>(s, T, mod, sl.rank);
+    ntt_fwd_slice<W, LC>(s, T, mod, sl.rank);
     for (u32 k = 2 * threadIdx.x; k < sl.ns; k += 2 * blockDim.x)
-      *reinterpret_cast<ulonglong2*>(out + k) = make_ulonglong2(fwd_final(s[sw(k)], m.q), fwd_final(s[sw(k + 1)], m.q));
+      *reinterpret_cast<ulonglong2*>(out + k) = make_ulonglong2(Ar<W>::fwd_out(s[sw(k)], m), Ar<W>::fwd_out(s[sw(k + 1)], m));
   }
+}
+
+static void (*const kNttInv[6])(DevTables, const u64*, u64, u64*, u64, u32, u32) = {
+    k_ntt<true, u64, 0>, k_ntt<true, u64, 1>, k_ntt<true, u64, 2>,
+    k_ntt<true, u32, 0>, k_ntt<true, u32, 1>, k_ntt<true, u32, 2>};
+static void (*const kNttFwd[6])(DevTables, const u64*, u64, u64*, u64, u32, u32) = {
+    k_ntt<false, u64, 0>, k_ntt<false, u64, 1>, k_ntt<false, u64, 2>,
+    k_ntt<false, u32, 0>, k_ntt<false, u32, 1>, k_ntt<false, u32, 2>};
+
+// ------------------------------------------------------- NTT over a descriptor table ----
+// One launch over several polynomial batches of the same N and chain but their own levels and
+// buffers: CTA job j belongs to the last descriptor whose first job is <= j, and is limb
+// (j - first) of that batch laid out [polys][level][N] (prime (j - first) % level).
+template <bool INVERSE, typename W, int LC>
+__global__ void k_ntt_desc(DevTables T, const __grid_constant__ NttDescTable tab) {
+  TCKS_SMEM(W);
+  const Slice sl = slice_of<LC>(T);
+  u32 lo = 0, hi = tab.n;
+  while (hi - lo > 1) {
+    const u32 mid = (lo + hi) >> 1;
+    if (tab.d[mid].first <= sl.job)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  const NttDesc& d = tab.d[lo];
+  const u32 local = sl.job - d.first;
+  const u32 mod = local % d.level;
+  const ModConst m = T.mods[mod];
+  const u64* in = d.src + ((u64)local << T.log_n) + sl.off;
+  u64* out = d.dst + ((u64)local << T.log_n) + sl.off;
+  for (u32 k = 2 * threadIdx.x; k < sl.ns; k += 2 * blockDim.x) {
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(in + k);
+    s[sw(k)] = (W)v.x;
+    s[sw(k + 1)] = (W)v.y;
+  }
+  __syncthreads();
+  if (INVERSE) {
+    ntt_inv_slice<W, LC>(s, T, mod, sl.rank);
+    for (u32 k = 2 * threadIdx.x; k < sl.ns; k += 2 * blockDim.x)
+      *reinterpret_cast<ulonglong2*>(out + k) = make_ulonglong2(Ar<W>::inv_out(s[sw(k)], m), Ar<W>::inv_out(s[sw(k + 1)], m));
+  } else {
+    ntt_fwd_slice<W, LC>(s, T, mod, sl.rank);
+    for (u32 k = 2 * threadIdx.x; k < sl.ns; k += 2 * blockDim.x)
+      *reinterpret_cast<ulonglong2*>(out + k) = make_ulonglong2(Ar<W>::fwd_out(s[sw(k)], m), Ar<W>::fwd_out(s[sw(k + 1)], m));
+  }
+}
+
+static void (*const kNttDescInv[6])(DevTables, NttDescTable) = {
+    k_ntt_desc<true, u64, 0>, k_ntt_desc<true, u64, 1>, k_ntt_desc<true, u64, 2>,
+    k_ntt_desc<true, u32, 0>, k_ntt_desc<true, u32, 1>, k_ntt_desc<true, u32, 2>};
+static void (*const kNttDescFwd[6])(DevTables, NttDescTable) = {
+    k_ntt_desc<false, u64, 0>, k_ntt_desc<false, u64, 1>, k_ntt_desc<false, u64, 2>,
+    k_ntt_desc<false, u32, 0>, k_ntt_desc<false, u32, 1>, k_ntt_desc<false, u32, 2>};
+
+void launch_ntt_desc(const DevTables& T, bool inverse, const NttDescTable& tab, u32 total_jobs, cudaStream_t st) {
+  if (!total_jobs || !tab.n) return;
+  Launch L(inverse ? K_NTT_INV : K_NTT_FWD, st, 16.0 * total_jobs * (1u << T.log_n));
+  if (inverse)
+    launch_limb(kNttDescInv, T.narrow, total_jobs, 1, T.log_n, st, T.limb_threads, T, tab);
+  else
+    launch_limb(kNttDescFwd, T.narrow, total_jobs, 1, T.log_n, st, T.limb_threads, T, tab);
 }
 
 void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_outer, u64* dst, u64 dst_outer, u32 count,
@@ -77,9 +139,14 @@ void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_outer,
   if (!count) return;
   Launch L(inverse ? K_NTT_INV : K_NTT_FWD, st, 16.0 * count * (1u << T.log_n));
   if (inverse)
-    launch_limb(k_ntt<true, 0>, k_ntt<true, 1>, k_ntt<true, 2>, count, 1, T.log_n, st, 0, T, src, src_outer, dst, dst_outer, mod_base, per);
+    launch_limb(kNttInv, T.narrow, count, 1, T.log_n, st, T.limb_threads, T, src, src_outer, dst, dst_outer, mod_base, per);
   else
-    launch_limb(k_ntt<false, 0>, k_ntt<false, 1>, k_ntt<false, 2>, count, 1, T.log_n, st, 0, T, src, src_outer, dst, dst_outer, mod_base, per);
+    launch_limb(kNttFwd, T.narrow, count, 1, T.log_n, st, T.limb_threads, T, src, src_outer, dst, dst_outer, mod_base, per);
+}
+
+// a * b mod q: the 64-bit Barrett of the product when every prime is below 2^31, else the 128-bit one
+__device__ __forceinline__ u64 mulq(u64 a, u64 b, const ModConst& m, u32 narrow) {
+  return narrow ? reduce64(a * b, m) : mul_mod(a, b, m);
 }
 
 // ------------------------------------------------------------------------ element-wise ops ----
@@ -117,8 +184,8 @@ __global__ void k_elementwise(DevTables T, u32 op, const u64* __restrict__ a, co
         break;
       case OP_MUL_PLAIN: {  // b is a plaintext [>= ell][N] shared by every polynomial
         const ulonglong2 y = reinterpret_cast<const ulonglong2*>(b + (u64)limb * n)[(e & (n - 1)) >> 1];
-        r.x = mul_mod(x.x, y.x, m);
-        r.y = mul_mod(x.y, y.y, m);
+        r.x = mulq(x.x, y.x, m, T.narrow);
+        r.y = mulq(x.y, y.y, m, T.narrow);
         break;
       }
       default: {  // OP_ADD_PLAIN / OP_SUB_PLAIN: only component 0 of each ciphertext changes
@@ -170,12 +237,12 @@ __global__ void k_tensor(DevTables T, const u64* __restrict__ a, const u64* __re
     const u64* bc = b + c * 2 * per_poly;
     u64* oc = out + c * 3 * per_poly;
     const u64 a0 = ac[o], a1 = ac[per_poly + o], b0 = bc[o], b1 = bc[per_poly + o];
-    oc[o] = mul_mod(a0, b0, m);
+    oc[o] = mulq(a0, b0, m, T.narrow);
     Acc128 acc{0, 0};
     mac128(acc, a0, b1);
     mac128(acc, a1, b0);
     oc[per_poly + o] = reduce128(acc.hi, acc.lo, m);
-    oc[2 * per_poly + o] = mul_mod(a1, b1, m);
+    oc[2 * per_poly + o] = mulq(a1, b1, m, T.narrow);
   }
 }
 
@@ -192,7 +259,7 @@ __global__ void k_decrypt(DevTables T, const u64* __restrict__ ct, const u64* __
   const u64 per_poly = (u64)ell << log_n;
   for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < per_poly; e += (u64)gridDim.x * blockDim.x) {
     const ModConst m = T.mods[e >> log_n];
-    pt[e] = add_mod(ct[e], mul_mod(ct[per_poly + e], s[e], m), m.q);
+    pt[e] = add_mod(ct[e], mulq(ct[per_poly + e], s[e], m, T.narrow), m.q);
   }
 }
 
@@ -206,10 +273,10 @@ void launch_decrypt(const DevTables& T, const u64* ct, const u64* s, u64* pt, u3
 // Rescale (drop = q_{ell-1}) and ModDown (drop = P) share this combine:
 //   out[p][i] = (in[p][i] - NTT_i(bal(top[p]) mod q_i)) * drop^-1 mod q_i,  i < n_out,
 // with top[p] the coefficient-domain limb of the dropped prime. Limb job = p * n_out + i.
-template <int LC>
+template <typename W, int LC>
 __global__ void k_drop_combine(DevTables T, const u64* __restrict__ in, u64 in_poly_stride,
                                const u64* __restrict__ top, u32 drop_mod, u32 n_out, u64* __restrict__ out) {
-  extern __shared__ u64 s[];
+  TCKS_SMEM(W);
   const Slice sl = slice_of<LC>(T);
   const u64 n = 1ull << T.log_n;
   const u32 p = sl.job / n_out, i = sl.job % n_out;
@@ -217,23 +284,25 @@ __global__ void k_drop_combine(DevTables T, const u64* __restrict__ in, u64 in_p
   const ModConst md = T.mods[drop_mod];
   const PairConst pc = T.pairs[(u64)drop_mod * T.n_mods + i];
   const u64* tp = top + (u64)p * n + sl.off;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced(tp[k], md.half, pc.qa_mod_b, mi);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)lift_balanced(tp[k], md.half, pc.qa_mod_b, mi);
   __syncthreads();
-  ntt_fwd_slice<LC>(s, T, i, sl.rank);
+  ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
   const u64* src = in + (u64)p * in_poly_stride + (u64)i * n + sl.off;
   u64* dst = out + ((u64)p * n_out + i) * n + sl.off;
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
-    const u64 c = sub_mod(src[k], fwd_final(s[sw(k)], mi.q), mi.q);
-    dst[k] = mul_shoup(c, pc.inv_qa, pc.inv_qa_sh, mi.q);
+    const u64 c = sub_mod(src[k], Ar<W>::fwd_out(s[sw(k)], mi), mi.q);
+    dst[k] = Ew<W>::shoup_inv(c, pc, mi);
   }
 }
+
+static decltype(&k_drop_combine<u64, 0>) const K6_k_drop_combine[6] = TCKS_K6(k_drop_combine);
 
 void launch_rescale(const DevTables& T, const u64* ct, u32 ell, u32 polys, u64* top_tmp, u64* out, cudaStream_t st) {
   const u64 n = 1ull << T.log_n;
   // INTT of the last limb of each polynomial
   launch_ntt(T, true, ct + (u64)(ell - 1) * n, (u64)ell * n, top_tmp, n, polys, ell - 1, 1, st);
   Launch L(K_DROP, st, 8.0 * n * polys * (2.0 * (ell - 1) + 1.0));
-  launch_limb(TCKS_LC3(k_drop_combine), polys * (ell - 1), 1, T.log_n, st, 0, T, ct, (u64)ell * n, (const u64*)top_tmp, ell - 1,
+  launch_limb(K6_k_drop_combine, T.narrow, polys * (ell - 1), 1, T.log_n, st, T.limb_threads, T, ct, (u64)ell * n, (const u64*)top_tmp, ell - 1,
               ell - 1, out);
 }
 
@@ -241,10 +310,10 @@ void launch_rescale(const DevTables& T, const u64* ct, u32 ell, u32 polys, u64* 
 // ModUp (one digit per prime) for a batch (y) of inputs: digit j = bal_{q_j}(x_j) lifted to slot i
 // (prime q_i for i < ell, P for i = ell) and NTT'd; digits [batch][ell][ell+1][N]. Slot i == j is
 // x_j itself. x_coef holds the inputs' INTT, [batch][ell][N].
-template <int LC>
+template <typename W, int LC>
 __global__ void k_modup(DevTables T, const u64* __restrict__ x_ntt, u64 x_stride, const u64* __restrict__ x_coef,
                         u32 ell, u64* __restrict__ digits) {
-  extern __shared__ u64 s[];
+  TCKS_SMEM(W);
   const Slice sl = slice_of<LC>(T);
   const u64 n = 1ull << T.log_n;
   const u32 j = sl.job / (ell + 1), slot = sl.job % (ell + 1);
@@ -259,38 +328,41 @@ __global__ void k_modup(DevTables T, const u64* __restrict__ x_ntt, u64 x_stride
   const u64 half_j = T.mods[j].half;
   const u64 qj_mod_t = T.pairs[(u64)j * T.n_mods + tmod].qa_mod_b;
   const u64* in = x_coef + (sl.y * ell + j) * n + sl.off;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced(in[k], half_j, qj_mod_t, mt);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)lift_balanced(in[k], half_j, qj_mod_t, mt);
   __syncthreads();
-  ntt_fwd_slice<LC>(s, T, tmod, sl.rank);
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) out[k] = fwd_final(s[sw(k)], mt.q);
+  ntt_fwd_slice<W, LC>(s, T, tmod, sl.rank);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) out[k] = Ar<W>::fwd_out(s[sw(k)], mt);
 }
+
+static decltype(&k_modup<u64, 0>) const K6_k_modup[6] = TCKS_K6(k_modup);
 
 void launch_modup(const DevTables& T, const u64* x_ntt, u64 x_stride, u32 count, u32 ell, u64* x_coef_tmp,
                   u64* digits, cudaStream_t st) {
   const u64 n = 1ull << T.log_n;
   launch_ntt(T, true, x_ntt, x_stride, x_coef_tmp, (u64)ell * n, count * ell, 0, ell, st);
   Launch L(K_MODUP, st, 8.0 * n * count * (2.0 * ell + (double)ell * (ell + 1)));
-  launch_limb(TCKS_LC3(k_modup), ell * (ell + 1), count, T.log_n, st, 0, T, x_ntt, x_stride, (const u64*)x_coef_tmp, ell, digits);
+  launch_limb(K6_k_modup, T.narrow, ell * (ell + 1), count, T.log_n, st, T.limb_threads, T, x_ntt, x_stride, (const u64*)x_coef_tmp, ell, digits);
 }
 
 // Inner product of (automorphed) digits with one key component on slot `slot`:
-//   sum_j D_j[slot][src] * key_j[b][key_slot][k], 128-bit lazy accumulation, one reduction.
+//   sum_j D_j[slot][src] * key_j[b][key_slot][k], lazy accumulation, one reduction.
+template <typename W>
 __device__ __forceinline__ u64 ks_inner(const u64* __restrict__ digits, u32 ell, u32 slot, const u64* __restrict__ key,
                                         u32 K, u32 key_slot, u32 b, u32 k, u32 src, u64 n, const ModConst& m) {
-  Acc128 acc{0, 0};
+  typename Ew<W>::Acc acc;
   for (u32 j = 0; j < ell; ++j) {
     const u64 d = digits[((u64)j * (ell + 1) + slot) * n + src];
     const u64 w = key[(((u64)j * 2 + b) * (K + 1) + key_slot) * n + k];
-    mac128(acc, d, w);
+    acc.mac(d, w);
   }
-  return reduce128(acc.hi, acc.lo, m);
+  return acc.get(m);
 }
 
 // Stage 1: u_b[P] = sum_j tau_g(D_j)[P] * key_j[b][P], then INTT mod P -> top. Limb job = component
 // b; entry y = request * R + rotation.
-template <int LC>
+template <typename W, int LC>
 __global__ void k_ks_inner_p(DevTables T, u32 ell, const __grid_constant__ KsPlan plan) {
-  extern __shared__ u64 s[];
+  TCKS_SMEM(W);
   const Slice sl = slice_of<LC>(T);
   if (sl.y >= (u64)plan.B * plan.R) return;
   const u32 log_n = T.log_n;
@@ -303,19 +375,19 @@ __global__ void k_ks_inner_p(DevTables T, u32 ell, const __grid_constant__ KsPla
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
     const u32 g = sl.off + k;
     const u32 src = kk.g == 1 ? g : galois_src(g, kk.g, log_n);
-    s[sw(k)] = ks_inner(digits, ell, ell, kk.key, kk.K, kk.K, b, g, src, n, mp);
+    s[sw(k)] = (W)ks_inner<W>(digits, ell, ell, kk.key, kk.K, kk.K, b, g, src, n, mp);
   }
   __syncthreads();
-  ntt_inv_slice<LC>(s, T, T.L, sl.rank);
+  ntt_inv_slice<W, LC>(s, T, T.L, sl.rank);
   u64* top = plan.top + (sl.y * 2 + b) * n + sl.off;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) top[k] = inv_final(s[sw(k)], mp);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) top[k] = Ar<W>::inv_out(s[sw(k)], mp);
 }
 
 // Stage 2 (ModDown): out_b[i] = (u_b[i] - NTT_i(bal_P(top_b) mod q_i)) * P^-1 + addend_b[i].
 // Limb job = b * ell + i.
-template <int LC>
+template <typename W, int LC>
 __global__ void k_ks_moddown(DevTables T, u32 ell, const __grid_constant__ KsPlan plan) {
-  extern __shared__ u64 s[];
+  TCKS_SMEM(W);
   const Slice sl = slice_of<LC>(T);
   if (sl.y >= (u64)plan.B * plan.R) return;
   const u32 log_n = T.log_n;
@@ -328,17 +400,17 @@ __global__ void k_ks_moddown(DevTables T, u32 ell, const __grid_constant__ KsPla
   const ModConst mp = T.mods[T.L];
   const PairConst pc = T.pairs[(u64)T.L * T.n_mods + i];
   const u64* top = plan.top + (sl.y * 2 + b) * n + sl.off;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced(top[k], mp.half, pc.qa_mod_b, mi);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)lift_balanced(top[k], mp.half, pc.qa_mod_b, mi);
   __syncthreads();
-  ntt_fwd_slice<LC>(s, T, i, sl.rank);
+  ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
   const u64* add = b == 0 ? (plan.add0 ? plan.add0 + rq * plan.add0_b : nullptr)
                           : (plan.add1 ? plan.add1 + rq * plan.add1_b : nullptr);
   u64* dst = plan.out + rq * plan.out_b + r * plan.out_r + ((u64)b * ell + i) * n;
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
     const u32 g = sl.off + k;
     const u32 src = kk.g == 1 ? g : galois_src(g, kk.g, log_n);
-    const u64 u = ks_inner(digits, ell, i, kk.key, kk.K, i, b, g, src, n, mi);
-    u64 v = mul_shoup(sub_mod(u, fwd_final(s[sw(k)], mi.q), mi.q), pc.inv_qa, pc.inv_qa_sh, mi.q);
+    const u64 u = ks_inner<W>(digits, ell, i, kk.key, kk.K, i, b, g, src, n, mi);
+    u64 v = Ew<W>::shoup_inv(sub_mod(u, Ar<W>::fwd_out(s[sw(k)], mi), mi.q), pc, mi);
     if (add) v = add_mod(v, add[(u64)i * n + (plan.add_perm ? src : g)], mi.q);
     dst[g] = v;
   }
@@ -356,14 +428,18 @@ static void ks_plan_bytes(const KsPlan& p, u32 ell, u32 log_n, double* inner, do
       8.0 * n * (digit_sets * ell * ell + key_sets * 2.0 * ell * ell + 2.0 * jobs + adds * ell + 2.0 * ell * jobs);
 }
 
+static decltype(&k_ks_inner_p<u64, 0>) const K6_k_ks_inner_p[6] = TCKS_K6(k_ks_inner_p);
+
 void launch_ks_inner_p(const DevTables& T, u32 ell, const KsPlan& plan, cudaStream_t st) {
   const u64 jobs = (u64)plan.B * plan.R;
   if (!jobs) return;
   double bi, bm;
   ks_plan_bytes(plan, ell, T.log_n, &bi, &bm);
   Launch L(K_KS_P, st, bi);
-  launch_limb(TCKS_LC3(k_ks_inner_p), 2, jobs, T.log_n, st, 0, T, ell, plan);
+  launch_limb(K6_k_ks_inner_p, T.narrow, 2, jobs, T.log_n, st, T.limb_threads, T, ell, plan);
 }
+
+static decltype(&k_ks_moddown<u64, 0>) const K6_k_ks_moddown[6] = TCKS_K6(k_ks_moddown);
 
 void launch_keyswitch(const DevTables& T, u32 ell, const KsPlan& plan, cudaStream_t st) {
   const u64 jobs = (u64)plan.B * plan.R;
@@ -372,7 +448,7 @@ void launch_keyswitch(const DevTables& T, u32 ell, const KsPlan& plan, cudaStrea
   double bi, bm;
   ks_plan_bytes(plan, ell, T.log_n, &bi, &bm);
   Launch L(K_KS_MODDOWN, st, bm);
-  launch_limb(TCKS_LC3(k_ks_moddown), 2 * ell, jobs, T.log_n, st, 0, T, ell, plan);
+  launch_limb(K6_k_ks_moddown, T.narrow, 2 * ell, jobs, T.log_n, st, T.limb_threads, T, ell, plan);
 }
 
 // -------------------------------------------------- vector x plain matrix: fused ModDown + MAC ----
@@ -386,9 +462,9 @@ static u32 vecmat_threads(u32 log_n) {
   const u32 ns = 1u << (log_n > 14 ? 14 : log_n);
   return ns / kVmEpt < 32 ? 32 : ns / kVmEpt;
 }
-template <int LC>
+template <typename W, int LC>
 __global__ void k_vecmat_acc(DevTables T, u32 ell, const __grid_constant__ VecmatPlan plan) {
-  extern __shared__ u64 s[];
+  TCKS_SMEM(W);
   const Slice sl = slice_of<LC>(T);
   const u32 log_n = T.log_n;
   const u64 n = 1ull << log_n;
@@ -401,7 +477,7 @@ __global__ void k_vecmat_acc(DevTables T, u32 ell, const __grid_constant__ Vecma
   const PairConst pc = T.pairs[(u64)T.L * T.n_mods + i];
   const u64* digits = plan.digits + rq * plan.digits_b;
   const u64* c0 = plan.ct + rq * plan.ct_b;  // component 0, [ell][N]
-  u64 acc[kVmEpt];
+  W acc[kVmEpt];
 #pragma unroll
   for (int e = 0; e < kVmEpt; ++e) acc[e] = 0;
   const u32 r0 = chunk * plan.chunk;
@@ -409,9 +485,9 @@ __global__ void k_vecmat_acc(DevTables T, u32 ell, const __grid_constant__ Vecma
   for (u32 r = r0; r < r1; ++r) {
     const KsKey kk = plan.keys[r];
     const u64* top = plan.top + (((u64)r * plan.B + rq) * 2 + b) * n + sl.off;
-    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced(top[k], mp.half, pc.qa_mod_b, mi);
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)lift_balanced(top[k], mp.half, pc.qa_mod_b, mi);
     __syncthreads();
-    ntt_fwd_slice<LC>(s, T, i, sl.rank);
+    ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
     const u64* dk = plan.diag + (u64)(r + 1) * plan.diag_stride + (u64)i * n;
 #pragma unroll
     for (int e = 0; e < kVmEpt; ++e) {
@@ -419,10 +495,10 @@ __global__ void k_vecmat_acc(DevTables T, u32 ell, const __grid_constant__ Vecma
       if (k < sl.ns) {
         const u32 g = sl.off + k;
         const u32 src = galois_src(g, kk.g, log_n);
-        const u64 u = ks_inner(digits, ell, i, kk.key, kk.K, i, b, g, src, n, mi);
-        u64 v = mul_shoup(sub_mod(u, fwd_final(s[sw(k)], mi.q), mi.q), pc.inv_qa, pc.inv_qa_sh, mi.q);
+        const u64 u = ks_inner<W>(digits, ell, i, kk.key, kk.K, i, b, g, src, n, mi);
+        u64 v = Ew<W>::shoup_inv(sub_mod(u, Ar<W>::fwd_out(s[sw(k)], mi), mi.q), pc, mi);
         if (b == 0) v = add_mod(v, c0[(u64)i * n + src], mi.q);
-        acc[e] = add_mod(acc[e], mul_mod(v, dk[g], mi), mi.q);
+        acc[e] = (W)add_mod(acc[e], Ew<W>::mul(v, dk[g], mi), mi.q);
       }
     }
     __syncthreads();  // s is refilled for the next rotation
@@ -431,7 +507,7 @@ __global__ void k_vecmat_acc(DevTables T, u32 ell, const __grid_constant__ Vecma
 #pragma unroll
   for (int e = 0; e < kVmEpt; ++e) {
     const u32 k = threadIdx.x + e * blockDim.x;
-    if (k < sl.ns) dst[k] = acc[e];
+    if (k < sl.ns) dst[k] = plan.accumulate ? add_mod(dst[k], acc[e], mi.q) : acc[e];
   }
 }
 
@@ -456,15 +532,17 @@ __global__ void k_vecmat_reduce(DevTables T, u32 ell, const __grid_constant__ Ve
   }
 }
 
+static decltype(&k_vecmat_acc<u64, 0>) const K6_k_vecmat_acc[6] = TCKS_K6(k_vecmat_acc);
+
 void launch_vecmat_acc(const DevTables& T, u32 ell, const VecmatPlan& plan, cudaStream_t st) {
   const double n = (double)(1u << T.log_n);
   // per (request, rotation): the P-limb scratch; per rotation: key limbs and diagonal; per request:
   // digits, c0 and the partial outputs
   const double by = 8.0 * n *
                     ((double)plan.B * plan.R * 2.0 + plan.R * (2.0 * ell * ell + ell) + plan.B * (ell * ell + ell) +
-                     (double)plan.B * plan.chunks * 2.0 * ell);
+                     (double)plan.B * plan.chunks * 2.0 * ell * (plan.accumulate ? 2.0 : 1.0));
   Launch L(K_VECMAT, st, by);
-  launch_limb(TCKS_LC3(k_vecmat_acc), plan.chunks * 2 * ell * plan.B, 1, T.log_n, st, vecmat_threads(T.log_n), T,
+  launch_limb(K6_k_vecmat_acc, T.narrow, plan.chunks * 2 * ell * plan.B, 1, T.log_n, st, vecmat_threads(T.log_n), T,
               ell, plan);
 }
 
@@ -512,10 +590,12 @@ u64* noalloc_setup(int device, std::string* why) {
   u64* ptr = nullptr;
   cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_rescale_scratch);
   const int bytes = (int)(((size_t)8) << kNoAllocMaxLogN);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_drop_combine<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ntt<true, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_drop_combine<0>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  const void* fns[4] = {(const void*)k_ntt<true, u64, 0>, (const void*)k_drop_combine<u64, 0>,
+                        (const void*)k_ntt<true, u32, 0>, (const void*)k_drop_combine<u32, 0>};
+  for (const void* f : fns) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  }
   if (prev != device) cudaSetDevice(prev);
   if (e != cudaSuccess) {
     *why = std::string("scratch set-up failed: ") + cudaGetErrorString(e);
@@ -547,12 +627,14 @@ extern "C" tcks_status tcks_rescale_noalloc(tcks_ctx* ctx, const uint64_t* d_in,
   const u64 n = 1ull << log_n;
   const LimbShape sh = limb_shape(log_n);  // one CTA per limb at these sizes
   // the two launches of launch_rescale, without its allocating bookkeeping
+  const size_t smem = T.narrow ? sh.smem / 2 : sh.smem;
+  auto ntt = T.narrow ? k_ntt<true, u32, 0> : k_ntt<true, u64, 0>;
+  auto drop = T.narrow ? k_drop_combine<u32, 0> : k_drop_combine<u64, 0>;
   count_launch();
-  k_ntt<true, 0><<<2, sh.threads, sh.smem, ctx->stream>>>(T, d_in + (u64)(level - 1) * n, (u64)level * n, scratch, n,
-                                                        level - 1, 1);
+  ntt<<<2, sh.threads, smem, ctx->stream>>>(T, d_in + (u64)(level - 1) * n, (u64)level * n, scratch, n, level - 1, 1);
   count_launch();
-  k_drop_combine<0><<<2 * (level - 1), sh.threads, sh.smem, ctx->stream>>>(T, d_in, (u64)level * n, scratch, level - 1,
-                                                                          level - 1, d_out);
+  drop<<<2 * (level - 1), sh.threads, smem, ctx->stream>>>(T, d_in, (u64)level * n, scratch, level - 1, level - 1,
+                                                             d_out);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return abi_record(TCKS_ERR_CUDA, std::string("rescale_noalloc: ") + cudaGetErrorString(e));
   abi_clear();

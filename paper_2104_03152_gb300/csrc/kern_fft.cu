@@ -92,9 +92,9 @@ __global__ void k_encode_coeffs(DevTables T, FftTables F, const double* __restri
 }
 
 // int64 coefficients -> NTT-form limbs, one limb job per prime.
-template <int LC>
+template <typename W, int LC>
 __global__ void k_coeffs_to_ntt(DevTables T, const i64* __restrict__ coeffs, u64* __restrict__ pt) {
-  extern __shared__ u64 s[];
+  TCKS_SMEM(W);
   const Slice P = slice_of<LC>(T);
   const u32 rank = P.rank, l = P.job, ns = P.ns, off = P.off;
   const ModConst m = T.mods[l];
@@ -102,12 +102,12 @@ __global__ void k_coeffs_to_ntt(DevTables T, const i64* __restrict__ coeffs, u64
     const i64 v = coeffs[off + k];
     const u64 a = v >= 0 ? (u64)v : (u64)(-(v + 1)) + 1;  // |v|
     const u64 r = reduce64(a, m);
-    s[sw(k)] = v >= 0 ? r : neg_mod(r, m.q);
+    s[sw(k)] = (W)(v >= 0 ? r : neg_mod(r, m.q));
   }
   __syncthreads();
-  ntt_fwd_slice<LC>(s, T, l, rank);
+  ntt_fwd_slice<W, LC>(s, T, l, rank);
   u64* out = pt + ((u64)l << T.log_n) + off;
-  for (u32 k = threadIdx.x; k < ns; k += blockDim.x) out[k] = fwd_final(s[sw(k)], m.q);
+  for (u32 k = threadIdx.x; k < ns; k += blockDim.x) out[k] = Ar<W>::fwd_out(s[sw(k)], m);
 }
 
 // Exact CRT of one coefficient: Garner digits v_i (x = v_0 + v_1 q_0 + v_2 q_0 q_1 + ...), the
@@ -205,7 +205,8 @@ void launch_encode_coeffs(const DevTables& T, const FftTables& F, const double* 
 
 void launch_coeffs_to_ntt(const DevTables& T, const i64* d_coeffs, u32 ell, u64* pt, cudaStream_t st) {
   Launch L(K_ENCODE, st, 8.0 * (1.0 + ell) * (1u << T.log_n));
-  launch_limb(TCKS_LC3(k_coeffs_to_ntt), ell, 1, T.log_n, st, 0, T, d_coeffs, pt);
+  static decltype(&k_coeffs_to_ntt<u64, 0>) const ks[6] = TCKS_K6(k_coeffs_to_ntt);
+  launch_limb(ks, T.narrow, ell, 1, T.log_n, st, T.limb_threads, T, d_coeffs, pt);
 }
 
 void launch_crt_compose(const DevTables& T, const u64* coef, u32 ell, const u64* d_qwords, double* out,

@@ -63,17 +63,21 @@ enum : u32 { SMALL_TERNARY = 0, SMALL_CBD = 1 };
 
 // Fill the CTA's slice of s[] with a small polynomial (ternary / CBD, drawn at the global
 // coefficient index) reduced mod the chain prime, and NTT it; on return s holds values in [0, 4q).
-template <int LC>
-__device__ __forceinline__ void small_ntt(u64* s, const DevTables& T, u32 mod, u32 kind, u64 seed, u64 tag,
+template <typename W, int LC>
+__device__ __forceinline__ void small_ntt(W* s, const DevTables& T, u32 mod, u32 kind, u64 seed, u64 tag,
                                           u32 rank, u32 ns) {
   const u64 q = T.mods[mod].q;
   const u32 off = rank * ns;
   for (u32 k = threadIdx.x; k < ns; k += blockDim.x) {
     const int v = kind == SMALL_TERNARY ? draw_ternary(seed, tag, off + k) : draw_cbd(seed, tag, off + k);
-    s[sw(k)] = small_to_residue(v, q);
+    s[sw(k)] = (W)small_to_residue(v, q);
   }
   __syncthreads();
-  ntt_fwd_slice<LC>(s, T, mod, rank);
+  ntt_fwd_slice<W, LC>(s, T, mod, rank);
+}
+
+__device__ __forceinline__ u64 mulq_s(u64 a, u64 b, const ModConst& m, u32 narrow) {
+  return narrow ? reduce64(a * b, m) : mul_mod(a, b, m);
 }
 
 // Limb slot -> chain index when a layout holds `count` data limbs followed by P.
@@ -82,41 +86,41 @@ __device__ __forceinline__ u32 slot_chain(u32 slot, u32 count, u32 L) { return s
 }  // namespace
 
 // s: [L+1][N], one limb job per prime.
-template <int LC>
+template <typename W, int LC>
 __global__ void k_keygen_secret(DevTables T, u64 seed, u64* __restrict__ s_out) {
-  extern __shared__ u64 s[];
+  TCKS_SMEM(W);
   const Slice P = slice_of<LC>(T);
   const u32 mod = P.job;  // 0..L (L is P)
-  small_ntt<LC>(s, T, mod, SMALL_TERNARY, seed, 1, P.rank, P.ns);
+  small_ntt<W, LC>(s, T, mod, SMALL_TERNARY, seed, 1, P.rank, P.ns);
   const u64 q = T.mods[mod].q;
   u64* out = s_out + ((u64)mod << T.log_n) + P.off;
-  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) out[k] = fwd_final(s[sw(k)], q);
+  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) out[k] = Ar<W>::fwd_out(s[sw(k)], T.mods[mod]);
 }
 
 // pk: [2][L][N]; pk0 = -a*s + e, pk1 = a.
-template <int LC>
+template <typename W, int LC>
 __global__ void k_keygen_public(DevTables T, u64 seed, const u64* __restrict__ sk, u64* __restrict__ pk) {
-  extern __shared__ u64 s[];
+  TCKS_SMEM(W);
   const Slice P = slice_of<LC>(T);
   const u64 n = 1ull << T.log_n;
   const u32 l = P.job;
   const ModConst m = T.mods[l];
-  small_ntt<LC>(s, T, l, SMALL_CBD, seed, 3, P.rank, P.ns);
+  small_ntt<W, LC>(s, T, l, SMALL_CBD, seed, 3, P.rank, P.ns);
   for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) {
     const u32 g = P.off + k;
     const u64 a = draw_uniform(seed, 2, g, l, m);
-    const u64 e = fwd_final(s[sw(k)], m.q);
-    pk[(u64)l * n + g] = add_mod(neg_mod(mul_mod(a, sk[(u64)l * n + g], m), m.q), e, m.q);
+    const u64 e = Ar<W>::fwd_out(s[sw(k)], m);
+    pk[(u64)l * n + g] = add_mod(neg_mod(mulq_s(a, sk[(u64)l * n + g], m, T.narrow), m.q), e, m.q);
     pk[((u64)T.L + l) * n + g] = a;
   }
 }
 
 // Switching key of level K: [K][2][K+1][N]; limb job = digit j * (K+1) + slot.
 //   b_j[slot] = -a*s + e + [chain(slot) == j] * (P mod q_j) * s'
-template <int LC>
+template <typename W, int LC>
 __global__ void k_keygen_switch(DevTables T, u64 seed, u32 kind, const u64* __restrict__ sk, u32 K,
                                 u64* __restrict__ ksk) {
-  extern __shared__ u64 s[];
+  TCKS_SMEM(W);
   const Slice P = slice_of<LC>(T);
   const u32 log_n = T.log_n;
   const u64 n = 1ull << log_n;
@@ -125,7 +129,7 @@ __global__ void k_keygen_switch(DevTables T, u64 seed, u32 kind, const u64* __re
   const ModConst m = T.mods[l];
   const u64 tag_a = ((u64)kind << 32) | 0x80000000ull | (2ull * j);
   const u64 tag_e = tag_a | 1ull;
-  small_ntt<LC>(s, T, l, SMALL_CBD, seed, tag_e, P.rank, P.ns);
+  small_ntt<W, LC>(s, T, l, SMALL_CBD, seed, tag_e, P.rank, P.ns);
   const u64 gadget = (l == j) ? T.pairs[(u64)T.L * T.n_mods + l].qa_mod_b : 0;  // P mod q_j
   const u64* s_l = sk + (u64)l * n;
   u64* b0 = ksk + (((u64)j * 2 + 0) * (K + 1) + slot) * n;
@@ -133,10 +137,10 @@ __global__ void k_keygen_switch(DevTables T, u64 seed, u32 kind, const u64* __re
   for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) {
     const u32 g = P.off + k;
     const u64 a = draw_uniform(seed, tag_a, g, l, m);
-    u64 v = add_mod(neg_mod(mul_mod(a, s_l[g], m), m.q), fwd_final(s[sw(k)], m.q), m.q);
+    u64 v = add_mod(neg_mod(mulq_s(a, s_l[g], m, T.narrow), m.q), Ar<W>::fwd_out(s[sw(k)], m), m.q);
     if (gadget) {
-      const u64 sp = kind == 0 ? mul_mod(s_l[g], s_l[g], m) : s_l[galois_src(g, kind, log_n)];
-      v = add_mod(v, mul_mod(gadget, sp, m), m.q);
+      const u64 sp = kind == 0 ? mulq_s(s_l[g], s_l[g], m, T.narrow) : s_l[galois_src(g, kind, log_n)];
+      v = add_mod(v, mulq_s(gadget, sp, m, T.narrow), m.q);
     }
     b0[g] = v;
     b1[g] = a;
@@ -144,10 +148,10 @@ __global__ void k_keygen_switch(DevTables T, u64 seed, u32 kind, const u64* __re
 }
 
 // Encryption at level ell, limb job = limb: c0 = u*pk0 + e0 + m, c1 = u*pk1 + e1.
-template <int LC>
+template <typename W, int LC>
 __global__ void k_encrypt(DevTables T, u64 seed, const u64* __restrict__ pk, const u64* __restrict__ pt, u32 ell,
                           u64* __restrict__ out) {
-  extern __shared__ u64 s[];
+  TCKS_SMEM(W);
   const Slice P = slice_of<LC>(T);
   const u64 n = 1ull << T.log_n;
   const u32 l = P.job;
@@ -157,38 +161,42 @@ __global__ void k_encrypt(DevTables T, u64 seed, const u64* __restrict__ pk, con
   const u64* p0 = pk + (u64)l * n + P.off;
   const u64* p1 = pk + ((u64)T.L + l) * n + P.off;
   const u64* ml = pt + (u64)l * n + P.off;
-  small_ntt<LC>(s, T, l, SMALL_TERNARY, seed, 4, P.rank, P.ns);
+  small_ntt<W, LC>(s, T, l, SMALL_TERNARY, seed, 4, P.rank, P.ns);
   for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) {
-    const u64 u = fwd_final(s[sw(k)], m.q);
-    c0[k] = add_mod(mul_mod(u, p0[k], m), ml[k], m.q);
-    c1[k] = mul_mod(u, p1[k], m);
+    const u64 u = Ar<W>::fwd_out(s[sw(k)], m);
+    c0[k] = add_mod(mulq_s(u, p0[k], m, T.narrow), ml[k], m.q);
+    c1[k] = mulq_s(u, p1[k], m, T.narrow);
   }
   __syncthreads();
-  small_ntt<LC>(s, T, l, SMALL_CBD, seed, 5, P.rank, P.ns);
-  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) c0[k] = add_mod(c0[k], fwd_final(s[sw(k)], m.q), m.q);
+  small_ntt<W, LC>(s, T, l, SMALL_CBD, seed, 5, P.rank, P.ns);
+  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) c0[k] = add_mod(c0[k], Ar<W>::fwd_out(s[sw(k)], m), m.q);
   __syncthreads();
-  small_ntt<LC>(s, T, l, SMALL_CBD, seed, 6, P.rank, P.ns);
-  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) c1[k] = add_mod(c1[k], fwd_final(s[sw(k)], m.q), m.q);
+  small_ntt<W, LC>(s, T, l, SMALL_CBD, seed, 6, P.rank, P.ns);
+  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) c1[k] = add_mod(c1[k], Ar<W>::fwd_out(s[sw(k)], m), m.q);
 }
 
 void launch_keygen_secret(const DevTables& T, u64 seed, u64* s, cudaStream_t st) {
   Launch L(K_KEYGEN, st, 8.0 * (T.L + 1) * (1u << T.log_n));
-  launch_limb(TCKS_LC3(k_keygen_secret), T.L + 1, 1, T.log_n, st, 0, T, seed, s);
+  static decltype(&k_keygen_secret<u64, 0>) const ks[6] = TCKS_K6(k_keygen_secret);
+  launch_limb(ks, T.narrow, T.L + 1, 1, T.log_n, st, T.limb_threads, T, seed, s);
 }
 
 void launch_keygen_public(const DevTables& T, u64 seed, const u64* s, u64* pk, cudaStream_t st) {
   Launch L(K_KEYGEN, st, 8.0 * 3 * T.L * (1u << T.log_n));
-  launch_limb(TCKS_LC3(k_keygen_public), T.L, 1, T.log_n, st, 0, T, seed, s, pk);
+  static decltype(&k_keygen_public<u64, 0>) const ks[6] = TCKS_K6(k_keygen_public);
+  launch_limb(ks, T.narrow, T.L, 1, T.log_n, st, T.limb_threads, T, seed, s, pk);
 }
 
 void launch_keygen_switch(const DevTables& T, u64 seed, u32 kind, const u64* s, u32 K, u64* ksk, cudaStream_t st) {
   Launch L(K_KEYGEN, st, 8.0 * 2 * K * (K + 1) * (1u << T.log_n));
-  launch_limb(TCKS_LC3(k_keygen_switch), K * (K + 1), 1, T.log_n, st, 0, T, seed, kind, s, K, ksk);
+  static decltype(&k_keygen_switch<u64, 0>) const ks[6] = TCKS_K6(k_keygen_switch);
+  launch_limb(ks, T.narrow, K * (K + 1), 1, T.log_n, st, T.limb_threads, T, seed, kind, s, K, ksk);
 }
 
 void launch_encrypt(const DevTables& T, u64 seed, const u64* pk, const u64* pt, u32 ell, u64* out, cudaStream_t st) {
   Launch L(K_ENCRYPT, st, 8.0 * 5 * ell * (1u << T.log_n));
-  launch_limb(TCKS_LC3(k_encrypt), ell, 1, T.log_n, st, 0, T, seed, pk, pt, ell, out);
+  static decltype(&k_encrypt<u64, 0>) const ks[6] = TCKS_K6(k_encrypt);
+  launch_limb(ks, T.narrow, ell, 1, T.log_n, st, T.limb_threads, T, seed, pk, pt, ell, out);
 }
 
 }  // namespace tcks

@@ -34,6 +34,20 @@ u32 ntt_threads(u32 log_n);
 void ensure_smem(const void* kernel, size_t bytes);
 // count jobs: limb (j % per) of entry (j / per), src + (j/per)*src_outer + (j%per)*N -> dst likewise
 // (may alias for in place), prime mod_base + j % per.
+// A table of polynomial batches for one NTT launch (same N and chain, their own levels).
+struct NttDesc {
+  const u64* src;  // [polys][level][N]
+  u64* dst;        // [polys][level][N] (may equal src)
+  u32 first;       // index of the batch's first limb job in the launch
+  u32 level;
+};
+constexpr u32 kNttDescMax = 96;
+struct NttDescTable {
+  NttDesc d[kNttDescMax];  // sorted by `first`, d[0].first == 0
+  u32 n;
+  u32 pad;
+};
+void launch_ntt_desc(const DevTables& T, bool inverse, const NttDescTable& tab, u32 total_jobs, cudaStream_t st);
 void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_outer, u64* dst, u64 dst_outer,
                 u32 count, u32 mod_base, u32 per, cudaStream_t st);
 enum : u32 { OP_ADD = 0, OP_SUB = 1, OP_NEG = 2, OP_MUL_PLAIN = 3, OP_ADD_PLAIN = 4, OP_SUB_PLAIN = 5 };
@@ -90,6 +104,8 @@ struct VecmatPlan {
   u64* partial;    // partial of request rq, chunk c: partial + rq * partial_b + c * [2][ell][N]
   u64 partial_b;
   u32 R, B, chunk, chunks;
+  u32 accumulate;  // 0: write the chunk partials; 1: add into them (later rotation blocks)
+  u32 pad;
 };
 // Stage 1 of a KsPlan alone (the P-limb inner product and its INTT into plan.top).
 void launch_ks_inner_p(const DevTables& T, u32 ell, const KsPlan& plan, cudaStream_t st);

@@ -27,28 +27,30 @@ __device__ __forceinline__ Slice slice_of(const DevTables& T) {
   return s;
 }
 
-// Launch a per-limb kernel over jobs_x limb jobs (x; each a cluster of 2^log_c CTAs, using the
-// instantiation for that cluster size) and jobs_y batch entries (split over y and z above the
-// 65535 limit of y; kernels skip the overhang). threads = 0 takes the default for the limb size.
+// Launch a per-limb kernel over jobs_x limb jobs (x; each a cluster of 2^log_c CTAs) and jobs_y
+// batch entries (split over y and z above the 65535 limit of y; kernels skip the overhang), using the
+// instantiation for the chain's word type (u32 when every prime is below 2^31) and the cluster size.
+// threads = 0 takes the default for the limb size.
 template <typename... KArgs, typename... Args>
-inline void launch_limb(void (*k0)(KArgs...), void (*k1)(KArgs...), void (*k2)(KArgs...), u32 jobs_x, u64 jobs_y,
-                        u32 log_n, cudaStream_t st, u32 threads, Args&&... args) {
+inline void launch_limb(void (*const (&ks)[6])(KArgs...), bool narrow, u32 jobs_x, u64 jobs_y, u32 log_n,
+                        cudaStream_t st, u32 threads, Args&&... args) {
   if (!jobs_x || !jobs_y) return;
   const LimbShape sh = limb_shape(log_n);
-  void (*kernel)(KArgs...) = sh.log_c == 0 ? k0 : sh.log_c == 1 ? k1 : k2;
+  void (*kernel)(KArgs...) = ks[(narrow ? 3 : 0) + sh.log_c];
   const u32 nt = threads ? threads : sh.threads;
-  ensure_smem((const void*)kernel, sh.smem);
+  const size_t smem = narrow ? sh.smem / 2 : sh.smem;
+  ensure_smem((const void*)kernel, smem);
   const u32 gy = jobs_y > 65535 ? 65535 : (u32)jobs_y;
   const u32 gz = (u32)((jobs_y + gy - 1) / gy);
   dim3 grid(jobs_x << sh.log_c, gy, gz);
   if (!sh.log_c) {
-    kernel<<<grid, nt, sh.smem, st>>>(std::forward<Args>(args)...);
+    kernel<<<grid, nt, smem, st>>>(std::forward<Args>(args)...);
     return;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = dim3(nt);
-  cfg.dynamicSmemBytes = sh.smem;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -60,7 +62,12 @@ inline void launch_limb(void (*k0)(KArgs...), void (*k1)(KArgs...), void (*k2)(K
   cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
-// The three cluster-size instantiations of a kernel template K<LC>.
-#define TCKS_LC3(K) K<0>, K<1>, K<2>
+// The six instantiations K<W, LC> of a limb kernel template, in launch_limb's order.
+#define TCKS_K6(K) {K<u64, 0>, K<u64, 1>, K<u64, 2>, K<u32, 0>, K<u32, 1>, K<u32, 2>}
+
+// Dynamic shared memory of a limb kernel viewed as W words.
+#define TCKS_SMEM(W)                                   \
+  extern __shared__ __align__(16) unsigned char smem_raw[]; \
+  W* s = reinterpret_cast<W*>(smem_raw)
 
 }  // namespace tcks

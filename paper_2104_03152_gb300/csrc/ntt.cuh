@@ -10,6 +10,10 @@
 // the partner elements from the other CTAs' shared memory (DSMEM) and keep their own result; every
 // other stage is local. Local stages run as radix-8 rounds in registers (three stages per shared
 // memory round trip), with a radix-4 or radix-2 round for the remainder.
+//
+// Word types: W = u64 for any prime below 2^62 (Harvey's lazy butterflies: [0, 4q) forward,
+// [0, 2q) inverse, 64-bit Shoup); W = u32 when every prime of the chain is below 2^31 (fully reduced
+// butterflies with 32-bit Shoup companions, half the shared memory). Both give the canonical result.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -18,34 +22,71 @@
 namespace tcks {
 
 // Shared-memory position of limb element i: the low four bits are XORed with the 16-word row index,
-// so the strided accesses of the small-distance rounds spread over all bank pairs (8-byte words:
-// 16 words span the 32 banks) while each row keeps its 16 words.
+// so the strided accesses of the small-distance rounds spread over the banks while each row keeps
+// its 16 words.
 __device__ __forceinline__ u32 sw(u32 i) { return i ^ ((i >> 4) & 15u); }
 
 __device__ __forceinline__ const u64* tw_at(const DevTables& T, u32 mod, u32 which) {
   return T.tw + ((u64)mod * 4 + which) * (1ull << T.log_n);
 }
 
-// Harvey forward butterfly: X, Y in [0, 4q) -> X + WY, X - WY in [0, 4q).
-__device__ __forceinline__ void ct_bfly(u64& X, u64& Y, u64 W, u64 Wsh, u64 q, u64 two_q) {
-  const u64 x = csub(X, two_q);
-  const u64 t = mul_shoup_lazy(Y, W, Wsh, q);
-  X = x + t;
-  Y = x - t + two_q;
-}
+template <typename W>
+struct Ar;
 
-// Harvey inverse butterfly: X, Y in [0, 2q) -> X + Y, (X - Y) W in [0, 2q).
-__device__ __forceinline__ void gs_bfly(u64& X, u64& Y, u64 W, u64 Wsh, u64 q, u64 two_q) {
-  const u64 u = csub(X + Y, two_q);
-  Y = mul_shoup_lazy(X - Y + two_q, W, Wsh, q);
-  X = u;
-}
+// 64-bit words, Harvey lazy reduction.
+template <>
+struct Ar<u64> {
+  static __device__ __forceinline__ const u64* tw(const DevTables& T, u32 mod, u32 which) { return tw_at(T, mod, which); }
+  // X, Y in [0, 4q) -> X + WY, X - WY in [0, 4q).
+  static __device__ __forceinline__ void ct(u64& X, u64& Y, u64 W, u64 Wsh, u64 q) {
+    const u64 two_q = 2 * q;
+    const u64 x = csub(X, two_q);
+    const u64 t = mul_shoup_lazy(Y, W, Wsh, q);
+    X = x + t;
+    Y = x - t + two_q;
+  }
+  // X, Y in [0, 2q) -> X + Y, (X - Y) W in [0, 2q).
+  static __device__ __forceinline__ void gs(u64& X, u64& Y, u64 W, u64 Wsh, u64 q) {
+    const u64 two_q = 2 * q;
+    const u64 u = csub(X + Y, two_q);
+    Y = mul_shoup_lazy(X - Y + two_q, W, Wsh, q);
+    X = u;
+  }
+  static __device__ __forceinline__ u64 fwd_out(u64 x, const ModConst& m) { return csub(csub(x, 2 * m.q), m.q); }
+  static __device__ __forceinline__ u64 inv_out(u64 x, const ModConst& m) { return mul_shoup(x, m.ninv, m.ninv_sh, m.q); }
+};
 
-// R = 2^LR elements x[q] = element base + q * stride (stride = the round's smallest butterfly distance)
-// through forward stages st .. st+LR-1; gblk = global index of the block of stage st.
-template <int LR>
-__device__ __forceinline__ void fwd_group(u64 (&x)[1 << LR], u32 st, u32 gblk, const u64* tw, const u64* tws, u64 q,
-                                          u64 two_q) {
+// 32-bit words (q < 2^31), every value fully reduced.
+__device__ __forceinline__ u32 csub32(u32 a, u32 q) { return a >= q ? a - q : a; }
+__device__ __forceinline__ u32 shoup32(u32 a, u32 w, u32 wsh, u32 q) {
+  return csub32(a * w - __umulhi(a, wsh) * q, q);
+}
+template <>
+struct Ar<u32> {
+  static __device__ __forceinline__ const u32* tw(const DevTables& T, u32 mod, u32 which) {
+    return T.tw32 + ((u64)mod * 4 + which) * (1ull << T.log_n);
+  }
+  static __device__ __forceinline__ void ct(u32& X, u32& Y, u32 W, u32 Wsh, u32 q) {
+    const u32 t = shoup32(Y, W, Wsh, q);
+    const u32 x = X;
+    X = csub32(x + t, q);
+    Y = x >= t ? x - t : x + q - t;
+  }
+  static __device__ __forceinline__ void gs(u32& X, u32& Y, u32 W, u32 Wsh, u32 q) {
+    const u32 x = X, y = Y;
+    X = csub32(x + y, q);
+    Y = shoup32(x >= y ? x - y : x + q - y, W, Wsh, q);
+  }
+  static __device__ __forceinline__ u64 fwd_out(u32 x, const ModConst&) { return x; }
+  static __device__ __forceinline__ u64 inv_out(u32 x, const ModConst& m) {
+    return shoup32(x, (u32)m.ninv, (u32)m.ninv_sh32, (u32)m.q);
+  }
+};
+
+// R = 2^LR elements x[q] = element base + q * stride (stride = the round's smallest butterfly
+// distance) through forward stages st .. st+LR-1; gblk = global index of the block of stage st.
+template <typename W, int LR>
+__device__ __forceinline__ void fwd_group(W (&x)[1 << LR], u32 st, u32 gblk, const W* tw, const W* tws, W q) {
   constexpr int R = 1 << LR;
 #pragma unroll
   for (int u = 0; u < LR; ++u) {
@@ -53,18 +94,18 @@ __device__ __forceinline__ void fwd_group(u64 (&x)[1 << LR], u32 st, u32 gblk, c
 #pragma unroll
     for (int b = 0; b < (1 << u); ++b) {
       const u32 idx = ((1u << st) << u) + (gblk << u) + b;
-      const u64 w = tw[idx], wsh = tws[idx];
+      const W w = tw[idx], wsh = tws[idx];
 #pragma unroll
-      for (int x0 = 0; x0 < h; ++x0) ct_bfly(x[b * 2 * h + x0], x[b * 2 * h + x0 + h], w, wsh, q, two_q);
+      for (int x0 = 0; x0 < h; ++x0) Ar<W>::ct(x[b * 2 * h + x0], x[b * 2 * h + x0 + h], w, wsh, q);
     }
   }
 }
 
-// Inverse stages st .. st+LR-1 on R elements base + q * 2^st; m0 = N >> (st+1); gblk = global block
-// index (at the round's last sub-stage) of the group.
-template <int LR>
-__device__ __forceinline__ void inv_group(u64 (&x)[1 << LR], u32 log_n, u32 st, u32 gblk, const u64* tw,
-                                          const u64* tws, u64 q, u64 two_q) {
+// Inverse stages st .. st+LR-1 on R elements base + q * 2^st; gblk = global block index (at the
+// round's last sub-stage) of the group.
+template <typename W, int LR>
+__device__ __forceinline__ void inv_group(W (&x)[1 << LR], u32 log_n, u32 st, u32 gblk, const W* tw, const W* tws,
+                                          W q) {
   constexpr int R = 1 << LR;
 #pragma unroll
   for (int u = 0; u < LR; ++u) {
@@ -73,17 +114,17 @@ __device__ __forceinline__ void inv_group(u64 (&x)[1 << LR], u32 log_n, u32 st, 
 #pragma unroll
     for (int b = 0; b < (R >> (u + 1)); ++b) {
       const u32 idx = m + (gblk << (LR - u - 1)) + b;
-      const u64 w = tw[idx], wsh = tws[idx];
+      const W w = tw[idx], wsh = tws[idx];
 #pragma unroll
-      for (int x0 = 0; x0 < h; ++x0) gs_bfly(x[b * 2 * h + x0], x[b * 2 * h + x0 + h], w, wsh, q, two_q);
+      for (int x0 = 0; x0 < h; ++x0) Ar<W>::gs(x[b * 2 * h + x0], x[b * 2 * h + x0 + h], w, wsh, q);
     }
   }
 }
 
 // One local forward round of LR stages starting at stage st over the CTA's slice s[0, ns).
-template <int LR>
-__device__ __forceinline__ void fwd_round(u64* s, u32 log_n, u32 log_ns, u32 rank, u32 st, const u64* tw,
-                                          const u64* tws, u64 q, u64 two_q) {
+template <typename W, int LR>
+__device__ __forceinline__ void fwd_round(W* s, u32 log_n, u32 log_ns, u32 rank, u32 st, const W* tw, const W* tws,
+                                          W q) {
   constexpr int R = 1 << LR;
   const u32 log_tr = log_n - st - LR;  // smallest distance of the round
   const u32 tr = 1u << log_tr;
@@ -92,19 +133,19 @@ __device__ __forceinline__ void fwd_round(u64* s, u32 log_n, u32 log_ns, u32 ran
   for (u32 g = threadIdx.x; g < groups; g += blockDim.x) {
     const u32 blk = g >> log_tr, j = g & (tr - 1);
     const u32 base = (blk << (log_tr + LR)) + j;
-    u64 x[R];
+    W x[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) x[k] = s[sw(base + k * tr)];
-    fwd_group<LR>(x, st, gbase + blk, tw, tws, q, two_q);
+    fwd_group<W, LR>(x, st, gbase + blk, tw, tws, q);
 #pragma unroll
     for (int k = 0; k < R; ++k) s[sw(base + k * tr)] = x[k];
   }
   __syncthreads();
 }
 
-template <int LR>
-__device__ __forceinline__ void inv_round(u64* s, u32 log_n, u32 log_ns, u32 rank, u32 st, const u64* tw,
-                                          const u64* tws, u64 q, u64 two_q) {
+template <typename W, int LR>
+__device__ __forceinline__ void inv_round(W* s, u32 log_n, u32 log_ns, u32 rank, u32 st, const W* tw, const W* tws,
+                                          W q) {
   constexpr int R = 1 << LR;
   const u32 log_t = st;
   const u32 t = 1u << log_t;
@@ -113,80 +154,43 @@ __device__ __forceinline__ void inv_round(u64* s, u32 log_n, u32 log_ns, u32 ran
   for (u32 g = threadIdx.x; g < groups; g += blockDim.x) {
     const u32 blk = g >> log_t, j = g & (t - 1);
     const u32 base = (blk << (log_t + LR)) + j;
-    u64 x[R];
+    W x[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) x[k] = s[sw(base + k * t)];
-    inv_group<LR>(x, log_n, st, gbase + blk, tw, tws, q, two_q);
+    inv_group<W, LR>(x, log_n, st, gbase + blk, tw, tws, q);
 #pragma unroll
     for (int k = 0; k < R; ++k) s[sw(base + k * t)] = x[k];
   }
   __syncthreads();
 }
 
-// Cross-CTA forward stages 0 .. LC-1 (C = 2^LC CTAs): element j of every CTA's slice forms a group
-// of C; each CTA computes the group and keeps its own element. The slice s must be complete in
-// every CTA of the cluster (the caller's prologue), and s is overwritten only after all reads.
-template <int LC>
-__device__ __forceinline__ void fwd_cross(u64* s, u32 log_ns, u32 rank, const u64* tw, const u64* tws, u64 q,
-                                          u64 two_q) {
+// Cross-CTA stages (C = 2^LC CTAs): element j of every CTA's slice forms a group of C; each CTA
+// computes the group and keeps its own element. FWD: the first LC forward stages (the slice must be
+// complete in every CTA); otherwise the last LC inverse stages. s is overwritten only after all reads.
+template <typename W, int LC, bool FWD>
+__device__ __forceinline__ void cross_stages(W* s, u32 log_n, u32 log_ns, u32 rank, const W* tw, const W* tws, W q) {
   namespace cg = cooperative_groups;
   constexpr int C = 1 << LC;
   constexpr int PER = 8;  // elements a thread finishes before the write-back barrier
   cg::cluster_group cl = cg::this_cluster();
   const u32 ns = 1u << log_ns;
-  const u64* rem[C];
+  const W* rem[C];
 #pragma unroll
   for (int r = 0; r < C; ++r) rem[r] = cl.map_shared_rank(s, r);
   cl.sync();
   for (u32 c0 = 0; c0 < ns; c0 += blockDim.x * PER) {
-    u64 keep[PER];
+    W keep[PER];
 #pragma unroll
     for (int e = 0; e < PER; ++e) {
       const u32 j = c0 + e * blockDim.x + threadIdx.x;
       if (j < ns) {
-        u64 x[C];
+        W x[C];
 #pragma unroll
         for (int r = 0; r < C; ++r) x[r] = rem[r][sw(j)];
-        fwd_group<LC>(x, 0, 0, tw, tws, q, two_q);
-        keep[e] = x[0];
-#pragma unroll
-        for (int r = 1; r < C; ++r)
-          if ((u32)r == rank) keep[e] = x[r];
-      }
-    }
-    cl.sync();
-#pragma unroll
-    for (int e = 0; e < PER; ++e) {
-      const u32 j = c0 + e * blockDim.x + threadIdx.x;
-      if (j < ns) s[sw(j)] = keep[e];
-    }
-    cl.sync();
-  }
-}
-
-// Cross-CTA inverse stages (the last LC): after all local stages; results go to s in place.
-template <int LC>
-__device__ __forceinline__ void inv_cross(u64* s, u32 log_n, u32 log_ns, u32 rank, const u64* tw, const u64* tws,
-                                          u64 q, u64 two_q) {
-  namespace cg = cooperative_groups;
-  constexpr int C = 1 << LC;
-  constexpr int PER = 8;
-  cg::cluster_group cl = cg::this_cluster();
-  const u32 ns = 1u << log_ns;
-  const u64* rem[C];
-#pragma unroll
-  for (int r = 0; r < C; ++r) rem[r] = cl.map_shared_rank(s, r);
-  cl.sync();
-  for (u32 c0 = 0; c0 < ns; c0 += blockDim.x * PER) {
-    u64 keep[PER];
-#pragma unroll
-    for (int e = 0; e < PER; ++e) {
-      const u32 j = c0 + e * blockDim.x + threadIdx.x;
-      if (j < ns) {
-        u64 x[C];
-#pragma unroll
-        for (int r = 0; r < C; ++r) x[r] = rem[r][sw(j)];
-        inv_group<LC>(x, log_n, log_ns, 0, tw, tws, q, two_q);
+        if (FWD)
+          fwd_group<W, LC>(x, 0, 0, tw, tws, q);
+        else
+          inv_group<W, LC>(x, log_n, log_ns, 0, tw, tws, q);
         keep[e] = x[0];
 #pragma unroll
         for (int r = 1; r < C; ++r)
@@ -204,51 +208,89 @@ __device__ __forceinline__ void inv_cross(u64* s, u32 log_n, u32 log_ns, u32 ran
 }
 
 // Forward transform of the CTA's slice s[0, N/C) of a limb split over C = 2^LC CTAs (LC = 0: the
-// whole limb). Input in [0, 4q), output in [0, 4q). Ends with a barrier.
-template <int LC>
-__device__ __forceinline__ void ntt_fwd_slice(u64* s, const DevTables& T, u32 mod, u32 rank) {
+// whole limb). Input canonical (or in [0, 4q) for W = u64); output in [0, 4q) (u64) or canonical
+// (u32); Ar<W>::fwd_out gives the canonical value. Ends with a barrier.
+template <typename W, int LC>
+__device__ __forceinline__ void ntt_fwd_slice(W* s, const DevTables& T, u32 mod, u32 rank) {
   const u32 log_n = T.log_n, log_ns = log_n - LC;
-  const u64 q = T.mods[mod].q, two_q = 2 * q;
-  const u64* tw = tw_at(T, mod, 0);
-  const u64* tws = tw_at(T, mod, 1);
-  if constexpr (LC > 0) fwd_cross<LC>(s, log_ns, rank, tw, tws, q, two_q);
+  const W q = (W)T.mods[mod].q;
+  const W* tw = Ar<W>::tw(T, mod, 0);
+  const W* tws = Ar<W>::tw(T, mod, 1);
+  if constexpr (LC > 0) cross_stages<W, LC, true>(s, log_n, log_ns, rank, tw, tws, q);
   u32 st = LC;
   const u32 left = log_n - st;
   // remainder round first (radix-2 or radix-4), then radix-8 rounds
   if (left % 3 == 1) {
-    fwd_round<1>(s, log_n, log_ns, rank, st, tw, tws, q, two_q);
+    fwd_round<W, 1>(s, log_n, log_ns, rank, st, tw, tws, q);
     st += 1;
   } else if (left % 3 == 2) {
-    fwd_round<2>(s, log_n, log_ns, rank, st, tw, tws, q, two_q);
+    fwd_round<W, 2>(s, log_n, log_ns, rank, st, tw, tws, q);
     st += 2;
   }
-  for (; st < log_n; st += 3) fwd_round<3>(s, log_n, log_ns, rank, st, tw, tws, q, two_q);
+  for (; st < log_n; st += 3) fwd_round<W, 3>(s, log_n, log_ns, rank, st, tw, tws, q);
 }
 
-// Inverse transform (without N^-1) of the CTA's slice; input in [0, 2q), output in [0, 2q).
-template <int LC>
-__device__ __forceinline__ void ntt_inv_slice(u64* s, const DevTables& T, u32 mod, u32 rank) {
+// Inverse transform (without N^-1) of the CTA's slice; input canonical, output in [0, 2q) (u64)
+// or canonical (u32); Ar<W>::inv_out applies N^-1 and gives the canonical value.
+template <typename W, int LC>
+__device__ __forceinline__ void ntt_inv_slice(W* s, const DevTables& T, u32 mod, u32 rank) {
   const u32 log_n = T.log_n, log_ns = log_n - LC;
-  const u64 q = T.mods[mod].q, two_q = 2 * q;
-  const u64* tw = tw_at(T, mod, 2);
-  const u64* tws = tw_at(T, mod, 3);
+  const W q = (W)T.mods[mod].q;
+  const W* tw = Ar<W>::tw(T, mod, 2);
+  const W* tws = Ar<W>::tw(T, mod, 3);
   u32 st = 0;
-  for (; st + 3 <= log_ns; st += 3) inv_round<3>(s, log_n, log_ns, rank, st, tw, tws, q, two_q);
-  if (log_ns - st == 2) inv_round<2>(s, log_n, log_ns, rank, st, tw, tws, q, two_q);
-  if (log_ns - st == 1) inv_round<1>(s, log_n, log_ns, rank, st, tw, tws, q, two_q);
-  if constexpr (LC > 0) inv_cross<LC>(s, log_n, log_ns, rank, tw, tws, q, two_q);
+  for (; st + 3 <= log_ns; st += 3) inv_round<W, 3>(s, log_n, log_ns, rank, st, tw, tws, q);
+  if (log_ns - st == 2) inv_round<W, 2>(s, log_n, log_ns, rank, st, tw, tws, q);
+  if (log_ns - st == 1) inv_round<W, 1>(s, log_n, log_ns, rank, st, tw, tws, q);
+  if constexpr (LC > 0) cross_stages<W, LC, false>(s, log_n, log_ns, rank, tw, tws, q);
 }
 
-// Whole-limb wrappers (single CTA).
-__device__ __forceinline__ void ntt_fwd_smem(u64* s, const DevTables& T, u32 mod) { ntt_fwd_slice<0>(s, T, mod, 0); }
-__device__ __forceinline__ void ntt_inv_smem(u64* s, const DevTables& T, u32 mod) { ntt_inv_slice<0>(s, T, mod, 0); }
+// ------------------------------------------------------------ word-typed element arithmetic ----
+// Helpers for the kernels' prologues and epilogues: a W-typed multiply, Shoup multiply by a pair
+// constant, and the key-switch inner product.
+template <typename W>
+struct Ew;
 
-// Canonical value of a forward-transform output in [0, 4q).
-__device__ __forceinline__ u64 fwd_final(u64 x, u64 q) { return csub(csub(x, 2 * q), q); }
-// Canonical value of an inverse-transform output in [0, 2q) times N^-1.
-__device__ __forceinline__ u64 inv_final(u64 x, const ModConst& m) { return mul_shoup(x, m.ninv, m.ninv_sh, m.q); }
+template <>
+struct Ew<u64> {
+  static __device__ __forceinline__ u64 mul(u64 a, u64 b, const ModConst& m) { return mul_mod(a, b, m); }
+  static __device__ __forceinline__ u64 shoup_inv(u64 a, const PairConst& p, const ModConst& m) {
+    return mul_shoup(a, p.inv_qa, p.inv_qa_sh, m.q);
+  }
+  // sum_j d_j * w_j mod q, 128-bit lazy accumulation
+  struct Acc {
+    Acc128 a{0, 0};
+    __device__ __forceinline__ void mac(u64 d, u64 w) { mac128(a, d, w); }
+    __device__ __forceinline__ u64 get(const ModConst& m) const { return reduce128(a.hi, a.lo, m); }
+  };
+};
 
-// Launch geometry of a limb transform: cluster size 2^log_c, threads per CTA, shared memory bytes.
+template <>
+struct Ew<u32> {
+  static __device__ __forceinline__ u64 mul(u64 a, u64 b, const ModConst& m) {
+    return reduce64((u64)(u32)a * (u32)b, m);
+  }
+  static __device__ __forceinline__ u64 shoup_inv(u64 a, const PairConst& p, const ModConst& m) {
+    return shoup32((u32)a, (u32)p.inv_qa, (u32)p.inv_qa_sh32, (u32)m.q);
+  }
+  // products of 31-bit residues are below 2^62; a 64-bit sum with a carry count holds any ell
+  struct Acc {
+    u64 lo = 0;
+    u32 carry = 0;
+    __device__ __forceinline__ void mac(u64 d, u64 w) {
+      const u64 p = (u64)(u32)d * (u32)w;
+      lo += p;
+      carry += lo < p;
+    }
+    __device__ __forceinline__ u64 get(const ModConst& m) const {
+      const u64 v = reduce64(lo, m);
+      return carry ? reduce64(v + (u64)carry * m.r64, m) : v;
+    }
+  };
+};
+
+// Launch geometry of a limb transform: cluster size 2^log_c, threads per CTA, shared memory bytes
+// for 8-byte words (u32 limbs use half).
 struct LimbShape {
   u32 log_c;
   u32 threads;

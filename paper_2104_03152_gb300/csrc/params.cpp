@@ -122,6 +122,9 @@ bool build_tables(u32 log_n, const std::vector<u64>& chain, HostTables& out) {
   out.mods.resize(nm);
   out.pairs.resize((size_t)nm * nm);
   out.tw.assign((size_t)nm * 4 * n, 0);
+  out.narrow = true;
+  for (u64 q : chain) out.narrow = out.narrow && q < (1ull << 31);
+  if (out.narrow) out.tw32.assign((size_t)nm * 4 * n, 0);
   for (u32 i = 0; i < nm; ++i) {
     const u64 q = chain[i];
     const u64 psi = smallest_psi(q, log_n);
@@ -137,6 +140,8 @@ bool build_tables(u32 log_n, const std::vector<u64>& chain, HostTables& out) {
     m.ninv = invmod_h(n % q, q);
     m.ninv_sh = shoup_of(m.ninv, q);
     m.half = (q - 1) / 2;
+    m.r64 = (u64)(((u128)1 << 64) % q);
+    m.ninv_sh32 = (u64)(((u128)m.ninv << 32) / q);
     // twiddles: psi^brv(k) and psi^-brv(k) with Shoup companions
     u64* t0 = &out.tw[((size_t)i * 4 + 0) * n];
     u64* t1 = &out.tw[((size_t)i * 4 + 1) * n];
@@ -156,6 +161,13 @@ bool build_tables(u32 log_n, const std::vector<u64>& chain, HostTables& out) {
       t1[k] = shoup_of(pw[r], q);
       t2[k] = ipw[r];
       t3[k] = shoup_of(ipw[r], q);
+      if (out.narrow) {
+        u32* n32 = &out.tw32[(size_t)i * 4 * n];
+        n32[k] = (u32)pw[r];
+        n32[n + k] = (u32)(((u128)pw[r] << 32) / q);
+        n32[2 * n + k] = (u32)ipw[r];
+        n32[3 * n + k] = (u32)(((u128)ipw[r] << 32) / q);
+      }
     }
   }
   for (u32 a = 0; a < nm; ++a)
@@ -166,6 +178,7 @@ bool build_tables(u32 log_n, const std::vector<u64>& chain, HostTables& out) {
       if (a != b) {
         p.inv_qa = invmod_h(p.qa_mod_b, chain[b]);
         p.inv_qa_sh = shoup_of(p.inv_qa, chain[b]);
+        p.inv_qa_sh32 = (u64)(((u128)p.inv_qa << 32) / chain[b]);
       }
     }
   // rotation group: slot j sits at DFT index (5^j mod 2N - 1) / 4 of the size-N/2 transform

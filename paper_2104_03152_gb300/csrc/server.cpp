@@ -21,8 +21,6 @@
 using namespace tcks;
 
 namespace tcks {
-tcks_status abi_record(tcks_status code, const std::string& msg);
-void abi_clear();
 void cnn_stage(const tcks_cnn* m, u32 stage, const u64* x, u32 count, u64* out);
 u32 cnn_stage_level(const tcks_cnn* m, u32 stage);
 u64 cnn_resident_bytes(const tcks_cnn* m);

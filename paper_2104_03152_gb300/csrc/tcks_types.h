@@ -16,6 +16,8 @@ struct ModConst {
   u64 mu_hi, mu_lo;  // floor(2^128 / q)
   u64 ninv, ninv_sh; // N^-1 mod q and its Shoup companion
   u64 half;          // (q - 1) / 2
+  u64 r64;           // 2^64 mod q
+  u64 ninv_sh32;     // floor(ninv * 2^32 / q) (narrow chains, q < 2^31)
   u64 pad;
 };
 
@@ -24,7 +26,7 @@ struct PairConst {
   u64 qa_mod_b;      // q_a mod q_b
   u64 inv_qa;        // q_a^-1 mod q_b (0 when a == b)
   u64 inv_qa_sh;     // Shoup companion of inv_qa
-  u64 pad;
+  u64 inv_qa_sh32;   // floor(inv_qa * 2^32 / q_b) (narrow chains)
 };
 
 // Everything a kernel needs about the modulus chain, passed by value.
@@ -32,10 +34,13 @@ struct DevTables {
   const ModConst* mods;    // [n_mods]
   const PairConst* pairs;  // [n_mods][n_mods]
   const u64* tw;           // [n_mods][4][N]: psi^brv(k), Shoup, psi^-brv(k), Shoup
+  const u32* tw32;         // the same with 32-bit Shoup companions (narrow chains only)
   u32 log_n;
   u32 n_mods;  // L + 1
   u32 L;       // number of data primes; P is chain index L
-  u32 pad;
+  u32 narrow;  // every prime < 2^31: kernels use 32-bit arithmetic
+  u32 limb_threads;  // threads per CTA of the limb kernels (0 = the default for N), set by the autotuner
+  u32 pad2;
 };
 
 }  // namespace tcks

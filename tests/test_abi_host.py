@@ -68,6 +68,26 @@ def test_bad_params_rejected(built):
         tk.Params(13, [62, 40], 2.0 ** 26)  # prime too large
 
 
+def test_explicit_prime_chain(built):
+    """One chain of primes == 1 (mod 2^17) serves every N <= 2^16; the checks reject what O1 excludes."""
+    chain = oracle.gen_primes(16, [59 - (i % 10) for i in range(32)] + [60])
+    for log_n in (13, 14, 15, 16):
+        assert tk.Params(log_n, primes=chain, scale=2.0 ** 50).primes == chain
+    q = chain[0]
+    bad = {
+        "composite": [(2 ** 14 + 1) * (2 ** 15 + 1), chain[-1]],  # == 1 (mod 2^14), not prime
+        "not 1 mod 2N": [next(p for p in range(2 ** 40 + 1, 2 ** 40 + 10 ** 6, 2) if oracle.is_prime(p)
+                              and p % 2 ** 14 != 1), chain[-1]],
+        "repeated": [q, q],
+        "too wide": [2 ** 61 + 2 ** 17 * 3 + 1, q],
+        "one prime": [q],
+    }
+    for why, primes in bad.items():
+        with pytest.raises(tk.TcksError) as e:
+            tk.Params(13, primes=primes, scale=2.0 ** 40)
+        assert e.value.name == "BAD_PARAMS", why
+
+
 def test_im2col_matches_oracle(built):
     img = inputs.mnist_like_image(3)
     v, w = tk.im2col_encode(img, 7, 7, 3, 4096)

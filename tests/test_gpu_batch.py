@@ -1,0 +1,164 @@
+"""Batched launches over a descriptor table: NTT / INTT / relinearize / rotate jobs of mixed N and
+level in one batch, bit-identical to the single calls and to the oracle, eager and replayed from a
+CUDA graph. The chain is the primitive sweep's: primes == 1 (mod 2^17), data prime i of 59 - (i mod 10)
+bits, P the largest 60-bit one, shared by every N <= 2^16."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2104_03152_gb300 as tk
+from gpu_common import SEED
+from paper_2104_03152_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+L_SMALL, L_LARGE = 32, 8  # data primes of the N = 2^13 and N = 2^15 contexts
+
+
+def _chain():
+    return oracle.gen_primes(16, [59 - (i % 10) for i in range(L_SMALL)] + [60])
+
+
+def _pair(log_n, n_data, steps):
+    full = _chain()
+    primes = full[:n_data] + [full[-1]]
+    o = oracle.OracleCKKS(log_n, None, 2.0 ** 50, key_seed=SEED, primes=primes).keygen()
+    g = tk.Context(tk.Params(log_n, primes=primes, scale=2.0 ** 50), seed=SEED, flags=tk.TCKS_AUTO_RELIN)
+    assert g.primes == primes
+    o.gen_galois_keys(steps)
+    g.gen_galois_keys(steps)
+    return o, g
+
+
+@pytest.fixture(scope="module")
+def ctxs():
+    return {13: _pair(13, L_SMALL, [1]), 15: _pair(15, L_LARGE, [1])}
+
+
+def _dev(a: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
+
+
+def _host(d, shape):
+    return d.cpu().numpy().view(np.uint64).reshape(shape)
+
+
+def _ntt_jobs(ctxs):
+    """(context, op, count, level, seed, in_place) for a mix of N, levels and directions."""
+    (o13, g13), (o15, g15) = ctxs[13], ctxs[15]
+    return [
+        (o13, g13, tk.JOB_NTT, 3, 4, 11, True),
+        (o13, g13, tk.JOB_NTT, 1, 33, 12, False),  # every prime including P
+        (o15, g15, tk.JOB_NTT, 2, 8, 13, True),
+        (o13, g13, tk.JOB_INTT, 2, 16, 14, False),
+        (o13, g13, tk.JOB_NTT, 0, 4, 15, True),  # an empty entry
+        (o15, g15, tk.JOB_INTT, 1, 5, 16, True),
+    ]
+
+
+def test_mixed_ntt_batch_matches_single_calls_and_oracle(ctxs):
+    specs = _ntt_jobs(ctxs)
+    jobs, bufs = [], []
+    for o, g, op, count, level, seed, in_place in specs:
+        x = inputs.random_limbs(o.primes[:level], o.N, seed, polys=max(count, 1))[:count]
+        d_in = _dev(x)
+        d_out = d_in if in_place else torch.empty_like(d_in)
+        bufs.append((x, d_in, d_out))
+        jobs.append((g, op, 0, count, level, d_in.data_ptr(), d_out.data_ptr()))
+    tk.batch_run(jobs)
+    ctxs[13][1].synchronize()
+    for (o, g, op, count, level, seed, in_place), (x, d_in, d_out) in zip(specs, bufs):
+        if count == 0:
+            continue
+        got = _host(d_out, x.shape)
+        single = _dev(x)
+        g.ntt_inplace(single.data_ptr(), count, level, inverse=(op == tk.JOB_INTT))
+        g.synchronize()
+        assert np.array_equal(got, _host(single, x.shape)), (o.log_n, level)
+        for p, l in {(0, 0), (count - 1, level - 1)}:
+            q = o.primes[l]
+            f = oracle.intt if op == tk.JOB_INTT else oracle.ntt
+            assert np.array_equal(got[p, l], f(x[p, l], q, oracle.min_psi(q, o.log_n))), (o.log_n, level, p, l)
+
+
+def _ks_specs(ctxs):
+    """(N, op, count, level, seed) for relinearize / rotate jobs of mixed N and level."""
+    return [(13, tk.JOB_RELIN, 3, 4, 21), (13, tk.JOB_RELIN, 2, 16, 22), (15, tk.JOB_RELIN, 2, 8, 23),
+            (13, tk.JOB_ROTATE, 2, 32, 24), (15, tk.JOB_ROTATE, 1, 4, 25)]
+
+
+def _ks_batch(ctxs):
+    jobs, bufs = [], []
+    for log_n, op, count, level, seed in _ks_specs(ctxs):
+        o, g = ctxs[log_n]
+        polys = 3 if op == tk.JOB_RELIN else 2
+        x = np.stack([inputs.random_limbs(o.primes[:level], o.N, seed * 100 + i, polys=polys) for i in range(count)])
+        d_in = _dev(x)
+        d_out = torch.empty((count, 2, level, o.N), dtype=torch.int64, device="cuda")
+        bufs.append((x, d_in, d_out))
+        jobs.append((g, op, 1, count, level, d_in.data_ptr(), d_out.data_ptr()))
+    return jobs, bufs
+
+
+def _ks_reference(o, op, x, level):
+    if op == tk.JOB_RELIN:
+        return o.relinearize(x, level, 1.0).data
+    return o.rotate(oracle.Ct(np.ascontiguousarray(x), level, 1.0), 1).data
+
+
+def test_mixed_keyswitch_batch_matches_oracle(ctxs):
+    jobs, bufs = _ks_batch(ctxs)
+    tk.batch_run(jobs)
+    ctxs[13][1].synchronize()
+    for (log_n, op, count, level, seed), (x, d_in, d_out) in zip(_ks_specs(ctxs), bufs):
+        o = ctxs[log_n][0]
+        got = _host(d_out, (count, 2, level, o.N))
+        for i in range(count):
+            assert np.array_equal(got[i], _ks_reference(o, op, x[i], level)), (log_n, op, level, i)
+
+
+def test_batch_graph_replay_is_bit_identical(ctxs):
+    jobs, bufs = _ks_batch(ctxs)
+    tk.batch_run(jobs)
+    ctxs[13][1].synchronize()
+    eager = [_host(d_out, tuple(d_out.shape)).copy() for _, _, d_out in bufs]
+    for _, _, d_out in bufs:
+        d_out.zero_()
+    graph = tk.BatchGraph(jobs)
+    assert graph.launches > 0
+    for _ in range(2):
+        for _, _, d_out in bufs:
+            d_out.zero_()
+        torch.cuda.synchronize()
+        before = tk.launch_count()
+        graph.run()
+        ctxs[13][1].synchronize()
+        assert tk.launch_count() - before == graph.launches
+        for ref, (_, _, d_out) in zip(eager, bufs):
+            assert np.array_equal(_host(d_out, ref.shape), ref)
+
+
+def test_batch_validation_launches_nothing(ctxs):
+    o, g = ctxs[13]
+    d = torch.zeros((2, 2, 4, o.N), dtype=torch.int64, device="cuda")
+    e = torch.zeros_like(d)
+    good = (g, tk.JOB_ROTATE, 1, 2, 4, d.data_ptr(), e.data_ptr())
+    cases = {
+        "INVALID_ARG": [good, (g, 7, 0, 1, 4, d.data_ptr(), e.data_ptr())],
+        "NO_GALOIS_KEY": [good, (g, tk.JOB_ROTATE, 5, 1, 4, d.data_ptr(), e.data_ptr())],
+    }
+    cases_level = [good, (g, tk.JOB_RELIN, 0, 1, L_SMALL + 1, d.data_ptr(), e.data_ptr())]
+    torch.cuda.synchronize()
+    before = tk.launch_count()
+    for name, jobs in cases.items():
+        with pytest.raises(tk.TcksError) as err:
+            tk.batch_run(jobs)
+        assert err.value.name == name
+    with pytest.raises(tk.TcksError) as err:
+        tk.batch_run(cases_level)
+    assert err.value.name == "INVALID_ARG"
+    with pytest.raises(tk.TcksError) as err:
+        tk.batch_run([(g, tk.JOB_ROTATE, 1, 1, 4, d.data_ptr(), d.data_ptr())])
+    assert err.value.name == "INVALID_ARG"
+    assert tk.launch_count() == before

@@ -194,3 +194,18 @@ def test_errors(pair):
     with pytest.raises(tk.TcksError) as e:
         g.encode(np.full(4, 1e30))
     assert e.value.name == "VALUE_OVERFLOW"
+
+
+def test_autotune_keeps_results(tmp_path):
+    """The autotuner only moves the launch shape: results stay bit-exact, and its choice is cached."""
+    p = Pair(13, [31, 26, 26, 26, 31], 2.0 ** 26, galois=[1])
+    o = p.o
+    cx = o.encrypt_values(inputs.uniform_slots(o.slots, 1), 3)
+    cache = str(tmp_path / "tune.json")
+    t = p.g.autotune(cache)
+    assert t % 32 == 0 and 32 <= t <= 1024
+    assert p.g.autotune(cache) == t  # read back from the cache
+    assert_ct_equal(p.import_ct(cx).mul(p.import_ct(cx)), o.mul(cx, cx), "mul after tuning")
+    assert_ct_equal(p.import_ct(cx).rotate(1), o.rotate(cx, 1), "rotate after tuning")
+    import json
+    assert any(k.endswith("|13|32") for k in json.load(open(cache)))
