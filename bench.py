@@ -228,7 +228,7 @@ def run_gpu(args, world, rank, local):
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = reduce_max(world, total_ms)
-    prof = tk.profile_read()
+    prof = tk.profile_read(with_ops=True)
     # e2e through the C ABI with pinned host buffers: import B inputs, batched forward, export B outputs
     L, N = cts[0].level, ctx.N
     host_in = torch.empty(B * 2 * L * N, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
@@ -263,7 +263,10 @@ def run_gpu(args, world, rank, local):
                    "plain": {"throughput": thr_p, "p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
                              "requests": len(arr_p)},
                    "latency": "arrival -> result exported to the host"}
-    return dict(serving=serving, total_ms=total_ms, per_step=per_step, prof=prof, launches=launches, clocks=clk, e2e_s=e2e_s,
+    word = 32 if max(ctx.primes) < 2 ** 31 else 64
+    bfly_peak = tk.calibrate_butterflies(word)
+    primitives = primitives_summary(torch, tk) if args.primitives else None
+    return dict(primitives=primitives, bfly_peak=bfly_peak, word=word, serving=serving, total_ms=total_ms, per_step=per_step, prof=prof, launches=launches, clocks=clk, e2e_s=e2e_s,
                 e2e_steps=e2e_steps, h2d=host_in.nbytes, d2h=host_out.nbytes, max_err=max_err,
                 plain_ms=plain_total / plain_steps, plain_times=plain_times)
 
@@ -334,6 +337,154 @@ def plain_cnn(img, w):
     return w["fc2_w"] @ x + w["fc2_b"]
 
 
+# ------------------------------------------------------------------ primitive sweep (C3) --
+# Batched NTT / INTT / relinearize / rotate(1) over N in {2^13..2^16} and L in {4, 8, 16, 32} data
+# primes of one chain (primes == 1 mod 2^17, data prime i of 59 - (i mod 10) bits, P of 60 bits),
+# batches of ciphertexts on seeded uniform limbs, each batch a descriptor-table job list replayed from
+# a CUDA graph. Rates are algorithmic: bytes = each operand read once, each result written once, each
+# distinct key once; integer work = modular butterflies + modular multiply(-accumulate)s.
+SWEEP_BITS = [59 - (i % 10) for i in range(32)] + [60]
+SWEEP_OPS = ("ntt", "intt", "relin", "rotate")
+
+
+def sweep_contexts(torch, tk, log_ns):
+    from paper_2104_03152_gb300 import inputs
+    primes = tk.Params(16, SWEEP_BITS, 2.0 ** 50).primes
+    out = {}
+    for log_n in log_ns:
+        st = torch.cuda.Stream()
+        c = tk.Context(tk.Params(log_n, primes=primes, scale=2.0 ** 50), seed=inputs.SEED_KEYS,
+                       flags=tk.TCKS_AUTO_RELIN, stream=st.cuda_stream)
+        c._torch_stream = st  # keeps the stream alive with the context
+        c.gen_galois_keys([1])
+        c.autotune()
+        out[log_n] = c
+    return out
+
+
+def sweep_work(op, log_n, level, count):
+    """(algorithmic bytes, algorithmic integer ops) of one job."""
+    n, l = 1 << log_n, level
+    bf = 0.5 * n * log_n
+    if op in ("ntt", "intt"):
+        limbs = 2 * count * l  # the ciphertexts' two polynomials
+        return 16.0 * n * limbs, limbs * bf
+    key = 8.0 * n * 2 * l * (l + 1)
+    per_ct_in = (3 if op == "relin" else 2) * l * n * 8.0
+    ops = count * ((l + l * l + 2 + 2 * l) * bf + (2.0 * (l + 1) * l + 2 * l) * n)
+    return count * (per_ct_in + 2 * l * n * 8.0) + key, ops
+
+
+def sweep_buffers(torch, ctx, op, level, count, gen):
+    n = ctx.N
+    polys = {"ntt": 2, "intt": 2, "relin": 3, "rotate": 2}[op]
+    x = torch.empty((count, polys, level, n), dtype=torch.int64, device="cuda")
+    for l in range(level):
+        x[:, :, l, :] = torch.randint(0, int(ctx.primes[l]), (count, polys, n), generator=gen, device="cuda",
+                                      dtype=torch.int64)
+    if op in ("ntt", "intt"):
+        return x, x
+    return x, torch.empty((count, 2, level, n), dtype=torch.int64, device="cuda")
+
+
+def sweep_job(tk, ctx, op, level, count, x, y):
+    code = {"ntt": tk.JOB_NTT, "intt": tk.JOB_INTT, "relin": tk.JOB_RELIN, "rotate": tk.JOB_ROTATE}[op]
+    polys = 2 * count if op in ("ntt", "intt") else count
+    return (ctx, code, 1, polys, level, x.data_ptr(), y.data_ptr())
+
+
+def time_graph(torch, ctx_stream, graph, reps):
+    s = torch.cuda.ExternalStream(ctx_stream)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    graph.run()
+    torch.cuda.synchronize()
+    evs[0].record(s)
+    for k in range(reps):
+        graph.run()
+        evs[k + 1].record(s)
+    torch.cuda.synchronize()
+    return sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(reps))
+
+
+def sweep_point(torch, tk, ctxs, entries, op, peaks, gen, reps=20):
+    """entries: [(log_n, level, count)] forming one batch; returns a result dict."""
+    jobs, keep, by, ops = [], [], 0.0, 0.0
+    for log_n, level, count in entries:
+        c = ctxs[log_n]
+        x, y = sweep_buffers(torch, c, op, level, count, gen)
+        keep += [x, y]
+        jobs.append(sweep_job(tk, c, op, level, count, x, y))
+        b, o = sweep_work(op, log_n, level, count)
+        by, ops = by + b, ops + o
+    graph = tk.BatchGraph(jobs)
+    first = time_graph(torch, jobs[0][0].stream, graph, 1)[0]
+    reps = reps if first < 100 else 5
+    t = time_graph(torch, jobs[0][0].stream, graph, reps)
+    ms = t[len(t) // 2]
+    gbs = by / (ms * 1e-3) / 1e9
+    bfly = ops / (ms * 1e-3)
+    del graph, keep
+    return {"op": op, "ms": round(ms, 4), "reps": reps, "algo_bytes": by, "gbs": round(gbs, 1),
+            "hbm_frac": round(gbs / peaks["hbm_gbs"], 4), "gbfly_s": round(bfly / 1e9, 1),
+            "alu_frac": round(bfly / peaks["bfly64_s"], 4)}
+
+
+def primitive_peaks(tk):
+    p = measured_peaks()
+    return {"hbm_gbs": p["hbm_gbs"], "hbm_source": p["source"], "bfly64_s": tk.calibrate_butterflies(64),
+            "bfly32_s": tk.calibrate_butterflies(32)}
+
+
+def run_sweep(args):
+    import torch
+    import paper_2104_03152_gb300 as tk
+    tk.lib(build_if_missing=True)
+    torch.cuda.set_device(0)
+    peaks = primitive_peaks(tk)
+    print(json.dumps({"sweep_peaks": peaks}), flush=True)
+    log_ns = [13, 14, 15, 16]
+    ctxs = sweep_contexts(torch, tk, log_ns)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    batches = [int(b) for b in args.sweep_batches.split(",")]
+    for log_n in log_ns:
+        for L in (4, 8, 16, 32):
+            for B in batches:
+                for op in SWEEP_OPS:
+                    r = sweep_point(torch, tk, ctxs, [(log_n, L, B)], op, peaks, gen)
+                    r.update({"log_n": log_n, "L": L, "batch": B})
+                    print(json.dumps(r), flush=True)
+                torch.cuda.empty_cache()
+    # mixed batches: every ciphertext draws (N, L) uniformly; one job per (N, L) group, one graph
+    rng = np.random.default_rng(5)
+    for B in [b for b in batches if b > 1]:
+        draws = [(int(rng.choice(log_ns)), int(rng.choice([4, 8, 16, 32]))) for _ in range(B)]
+        groups = {}
+        for d in draws:
+            groups[d] = groups.get(d, 0) + 1
+        entries = [(ln, L, cnt) for (ln, L), cnt in sorted(groups.items())]
+        for op in SWEEP_OPS:
+            r = sweep_point(torch, tk, ctxs, entries, op, peaks, gen)
+            r.update({"mixed": True, "batch": B, "groups": len(entries)})
+            print(json.dumps(r), flush=True)
+        torch.cuda.empty_cache()
+
+
+def primitives_summary(torch, tk):
+    """NTT and key-switch rates at the largest sweep shape (N = 2^16, L = 32, 64 ciphertexts)."""
+    peaks = primitive_peaks(tk)
+    ctxs = sweep_contexts(torch, tk, [16])
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    out = {"shape": "N=2^16, L=32 data primes (50-60-bit), 64 ciphertexts per batch, CUDA-graph replay",
+           "peaks": {"hbm_gbs": peaks["hbm_gbs"], "bfly64_per_s": peaks["bfly64_s"], "bfly32_per_s": peaks["bfly32_s"]}}
+    for op in SWEEP_OPS:
+        out[op] = sweep_point(torch, tk, ctxs, [(16, 32, 64)], op, peaks, gen)
+    del ctxs
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------------------ CPU oracle --
 def oracle_setup():
     import oracle
@@ -391,7 +542,13 @@ def main():
     ap.add_argument("--batch", type=int, default=64, help="requests per step (the batched schedule)")
     ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of the Poisson serving trace (0: skip)")
     ap.add_argument("--serve-rate", type=float, default=600.0, help="offered requests/s of the serving trace")
+    ap.add_argument("--sweep", action="store_true", help="print the batched primitive sweep (JSON lines) and exit")
+    ap.add_argument("--sweep-batches", default="1,8,64,512", help="ciphertexts per batch in the sweep")
+    ap.add_argument("--primitives", type=int, default=1, help="add the NTT / key-switch rates at N=2^16, L=32")
     args = ap.parse_args()
+    if args.sweep:
+        run_sweep(args)
+        return
     world, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -406,14 +563,25 @@ def main():
     # dominant kernel family by device time
     prof = r["prof"]
     dom = max(prof.items(), key=lambda kv: kv[1][1])
-    name, (nl, ms, by) = dom
-    achieved = by / (ms / 1e3) / 1e9
+    name, (nl, ms, by, ops) = dom
+    hbm_ach = by / (ms / 1e3) / 1e9
+    alu_ach = ops / (ms / 1e3) / 1e9
+    alu_peak = r["bfly_peak"] / 1e9
     traffic = ncu_traffic(name)
-    roofline = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "peak_source": peaks["source"],
-                "traffic": traffic, "launches": nl, "algo_bytes_per_launch": by / nl, "avg_launch_us": 1e3 * ms / nl}
+    hbm = {"achieved": hbm_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_ach / peaks["hbm_gbs"],
+           "peak_source": peaks["source"]}
+    alu = {"achieved": alu_ach, "peak": alu_peak, "unit": "Gbfly/s", "frac": alu_ach / alu_peak if alu_peak else None,
+           "peak_source": f"measured: tcks_calibrate_butterflies({r['word']}) on this GPU, registers only"}
+    bound = "alu" if alu["frac"] and alu["frac"] > hbm["frac"] else "hbm"
+    top = alu if bound == "alu" else hbm
+    roofline = {"kernel": name, "bound": bound, "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
+                "frac": top["frac"], "peak_source": top["peak_source"], "traffic": traffic,
+                "hbm": hbm, "alu": alu, "launches": nl, "algo_bytes_per_launch": by / nl,
+                "algo_ops_per_launch": ops / nl, "avg_launch_us": 1e3 * ms / nl,
+                "ops_unit": "modular butterflies + modular multiply(-accumulate)s"}
     kernels = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / sum(x[1] for x in prof.values()), 4),
-                   "gbs": round(v[2] / (v[1] / 1e3) / 1e9, 1)} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+                   "gbs": round(v[2] / (v[1] / 1e3) / 1e9, 1), "gbfly_s": round(v[3] / (v[1] / 1e3) / 1e9, 1)}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
     per = sorted(r["per_step"])
     # CPU baseline: the oracle on the host cores, bounded sample
     if args.cpu_sample > 0:
@@ -440,6 +608,7 @@ def main():
         "e2e": {"value": world * B * r["e2e_steps"] / r["e2e_s"], "unit": "inferences/s",
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
         "serving": r["serving"],
+        "primitives": r["primitives"],
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
     }

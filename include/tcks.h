@@ -289,6 +289,11 @@ tcks_status tcks_batch_graph_launches(const tcks_batch_graph* g, uint64_t* launc
 void tcks_batch_graph_free(tcks_batch_graph* g);
 
 /* ------------------------------------------------------------------ launch accounting ---- */
+/* Integer-pipe ceiling for the roofline of the ALU-bound kernels: modular butterflies per second
+ * (the library's Cooley-Tukey butterfly with a Shoup twiddle product, registers only, every SM
+ * busy) on the current device for 64-bit (q < 2^62) or 32-bit (q < 2^31) words. A measurement aid
+ * with no counterpart in the paper. Synchronous; errors: INVALID_ARG, CUDA. */
+tcks_status tcks_calibrate_butterflies(uint32_t word_bits, double* per_second);
 /* Number of kernel launches the library has issued since it was loaded. */
 uint64_t tcks_launch_count(void);
 /* Kernel profiler: while on, every launch is bracketed by CUDA events on its stream and carries its
@@ -299,6 +304,10 @@ tcks_status tcks_profile_start(void);
 tcks_status tcks_profile_stop(void);
 uint32_t tcks_profile_count(void);
 tcks_status tcks_profile_read(uint32_t idx, const char** name, uint64_t* launches, double* ms, double* algo_bytes);
+/* Algorithmic integer work of family idx over the profiled launches: modular butterflies of its
+ * transforms plus its modular multiplies and multiply-accumulates, one unit each (the unit of
+ * tcks_calibrate_butterflies). */
+tcks_status tcks_profile_read_ops(uint32_t idx, double* algo_ops);
 
 /* ------------------------------------------------------------- the encrypted CNN (§4) ---- */
 /* The MNIST-shaped network of the paper's evaluation (§4, Table 2): im2col conv with `kernels`

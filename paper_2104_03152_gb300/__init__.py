@@ -104,6 +104,8 @@ _SIGS = {
     "tcks_profile_start": (ctypes.c_int32, []),
     "tcks_profile_stop": (ctypes.c_int32, []),
     "tcks_profile_count": (ctypes.c_uint32, []),
+    "tcks_profile_read_ops": (ctypes.c_int32, [ctypes.c_uint32, _dblp]),
+    "tcks_calibrate_butterflies": (ctypes.c_int32, [ctypes.c_uint32, _dblp]),
     "tcks_profile_read": (ctypes.c_int32, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_char_p),
                                             ctypes.POINTER(ctypes.c_uint64), _dblp, _dblp]),
     "tcks_server_create": (ctypes.c_int32, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
@@ -174,16 +176,29 @@ def profile_stop():
     check(lib().tcks_profile_stop())
 
 
-def profile_read() -> dict:
-    """{kernel family: (launches, device ms, algorithmic bytes)} of the records since profile_start."""
+def profile_read(with_ops: bool = False) -> dict:
+    """{kernel family: (launches, device ms, algorithmic bytes[, algorithmic integer ops])} of the
+    records since profile_start; ops are modular butterflies plus modular multiply(-accumulate)s."""
     L = lib()
     out = {}
     for i in range(L.tcks_profile_count()):
         name, n, ms, by = ctypes.c_char_p(), ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double()
         check(L.tcks_profile_read(i, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)))
         if n.value:
-            out[name.value.decode()] = (n.value, ms.value, by.value)
+            rec = (n.value, ms.value, by.value)
+            if with_ops:
+                ops = ctypes.c_double()
+                check(L.tcks_profile_read_ops(i, ctypes.byref(ops)))
+                rec += (ops.value,)
+            out[name.value.decode()] = rec
     return out
+
+
+def calibrate_butterflies(word_bits: int = 64) -> float:
+    """Modular butterflies per second of the integer pipe on the current device (registers only)."""
+    v = ctypes.c_double()
+    check(lib().tcks_calibrate_butterflies(word_bits, ctypes.byref(v)))
+    return v.value
 
 
 def _p(a: np.ndarray):
@@ -249,6 +264,7 @@ class Context:
         self.slots = params.N // 2
         self.primes = params.primes
         self.L = len(params.primes) - 1
+        self.stream = stream  # the cudaStream_t handle given by the caller (None: the context's own)
         self._alloc_keep = None
         aptr = None
         if allocator == "torch":

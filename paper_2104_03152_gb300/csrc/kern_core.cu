@@ -42,6 +42,9 @@ void ensure_smem(const void* kernel, size_t bytes) {
 
 u32 ntt_threads(u32 log_n) { return limb_shape(log_n).threads; }
 
+// Modular butterflies of one length-N transform: (N / 2) log2 N.
+static double bfly_per_limb(u32 log_n) { return 0.5 * (double)(1u << log_n) * log_n; }
+
 // --------------------------------------------------------------------------- batched NTT ----
 // Job j: limb (j % per) of entry (j / per): src + (j/per)*src_outer + (j%per)*N, prime mod_base + j%per.
 template <bool INVERSE, typename W, int LC>
@@ -127,7 +130,7 @@ static void (*const kNttDescFwd[6])(DevTables, NttDescTable) = {
 
 void launch_ntt_desc(const DevTables& T, bool inverse, const NttDescTable& tab, u32 total_jobs, cudaStream_t st) {
   if (!total_jobs || !tab.n) return;
-  Launch L(inverse ? K_NTT_INV : K_NTT_FWD, st, 16.0 * total_jobs * (1u << T.log_n));
+  Launch L(inverse ? K_NTT_INV : K_NTT_FWD, st, 16.0 * total_jobs * (1u << T.log_n), total_jobs * bfly_per_limb(T.log_n));
   if (inverse)
     launch_limb(kNttDescInv, T.narrow, total_jobs, 1, T.log_n, st, T.limb_threads, T, tab);
   else
@@ -137,7 +140,7 @@ void launch_ntt_desc(const DevTables& T, bool inverse, const NttDescTable& tab, 
 void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_outer, u64* dst, u64 dst_outer, u32 count,
                 u32 mod_base, u32 per, cudaStream_t st) {
   if (!count) return;
-  Launch L(inverse ? K_NTT_INV : K_NTT_FWD, st, 16.0 * count * (1u << T.log_n));
+  Launch L(inverse ? K_NTT_INV : K_NTT_FWD, st, 16.0 * count * (1u << T.log_n), count * bfly_per_limb(T.log_n));
   if (inverse)
     launch_limb(kNttInv, T.narrow, count, 1, T.log_n, st, T.limb_threads, T, src, src_outer, dst, dst_outer, mod_base, per);
   else
@@ -248,7 +251,7 @@ __global__ void k_tensor(DevTables T, const u64* __restrict__ a, const u64* __re
 
 void launch_tensor(const DevTables& T, const u64* a, const u64* b, u64* out, u32 ell, u32 count, cudaStream_t st) {
   const u64 e = ((u64)ell << T.log_n) * count;
-  Launch L(K_TENSOR, st, 7.0 * 8.0 * e);
+  Launch L(K_TENSOR, st, 7.0 * 8.0 * e, 4.0 * e);
   k_tensor<<<ew_blocks(e / 2 + 1), 256, 0, st>>>(T, a, b, out, ell, count);
 }
 
@@ -301,7 +304,7 @@ void launch_rescale(const DevTables& T, const u64* ct, u32 ell, u32 polys, u64* 
   const u64 n = 1ull << T.log_n;
   // INTT of the last limb of each polynomial
   launch_ntt(T, true, ct + (u64)(ell - 1) * n, (u64)ell * n, top_tmp, n, polys, ell - 1, 1, st);
-  Launch L(K_DROP, st, 8.0 * n * polys * (2.0 * (ell - 1) + 1.0));
+  Launch L(K_DROP, st, 8.0 * n * polys * (2.0 * (ell - 1) + 1.0), (double)polys * (ell - 1) * (bfly_per_limb(T.log_n) + n));
   launch_limb(K6_k_drop_combine, T.narrow, polys * (ell - 1), 1, T.log_n, st, T.limb_threads, T, ct, (u64)ell * n, (const u64*)top_tmp, ell - 1,
               ell - 1, out);
 }
@@ -340,7 +343,8 @@ void launch_modup(const DevTables& T, const u64* x_ntt, u64 x_stride, u32 count,
                   u64* digits, cudaStream_t st) {
   const u64 n = 1ull << T.log_n;
   launch_ntt(T, true, x_ntt, x_stride, x_coef_tmp, (u64)ell * n, count * ell, 0, ell, st);
-  Launch L(K_MODUP, st, 8.0 * n * count * (2.0 * ell + (double)ell * (ell + 1)));
+  Launch L(K_MODUP, st, 8.0 * n * count * (2.0 * ell + (double)ell * (ell + 1)),
+           (double)count * ell * ell * bfly_per_limb(T.log_n));
   launch_limb(K6_k_modup, T.narrow, ell * (ell + 1), count, T.log_n, st, T.limb_threads, T, x_ntt, x_stride, (const u64*)x_coef_tmp, ell, digits);
 }
 
@@ -435,7 +439,7 @@ void launch_ks_inner_p(const DevTables& T, u32 ell, const KsPlan& plan, cudaStre
   if (!jobs) return;
   double bi, bm;
   ks_plan_bytes(plan, ell, T.log_n, &bi, &bm);
-  Launch L(K_KS_P, st, bi);
+  Launch L(K_KS_P, st, bi, 2.0 * jobs * ((double)ell * (1u << T.log_n) + bfly_per_limb(T.log_n)));
   launch_limb(K6_k_ks_inner_p, T.narrow, 2, jobs, T.log_n, st, T.limb_threads, T, ell, plan);
 }
 
@@ -447,7 +451,8 @@ void launch_keyswitch(const DevTables& T, u32 ell, const KsPlan& plan, cudaStrea
   launch_ks_inner_p(T, ell, plan, st);
   double bi, bm;
   ks_plan_bytes(plan, ell, T.log_n, &bi, &bm);
-  Launch L(K_KS_MODDOWN, st, bm);
+  Launch L(K_KS_MODDOWN, st, bm,
+           2.0 * ell * jobs * ((ell + 1.0) * (1u << T.log_n) + bfly_per_limb(T.log_n)));
   launch_limb(K6_k_ks_moddown, T.narrow, 2 * ell, jobs, T.log_n, st, T.limb_threads, T, ell, plan);
 }
 
@@ -541,7 +546,8 @@ void launch_vecmat_acc(const DevTables& T, u32 ell, const VecmatPlan& plan, cuda
   const double by = 8.0 * n *
                     ((double)plan.B * plan.R * 2.0 + plan.R * (2.0 * ell * ell + ell) + plan.B * (ell * ell + ell) +
                      (double)plan.B * plan.chunks * 2.0 * ell * (plan.accumulate ? 2.0 : 1.0));
-  Launch L(K_VECMAT, st, by);
+  Launch L(K_VECMAT, st, by,
+           (double)plan.B * plan.R * 2.0 * ell * ((ell + 2.0) * n + bfly_per_limb(T.log_n)));
   launch_limb(K6_k_vecmat_acc, T.narrow, plan.chunks * 2 * ell * plan.B, 1, T.log_n, st, vecmat_threads(T.log_n), T,
               ell, plan);
 }

@@ -15,7 +15,8 @@ enum KernelId : u32 {
 // launching stream before and after it together with its algorithmic bytes.
 class Launch {
  public:
-  Launch(KernelId id, cudaStream_t st, double algo_bytes);
+  // algo_ops: modular butterflies plus modular multiplies / multiply-accumulates of the launch
+  Launch(KernelId id, cudaStream_t st, double algo_bytes, double algo_ops = 0.0);
   ~Launch();
   Launch(const Launch&) = delete;
   Launch& operator=(const Launch&) = delete;
@@ -24,6 +25,7 @@ class Launch {
   KernelId id_;
   cudaStream_t st_;
   double bytes_;
+  double ops_;
   void* a_ = nullptr;
   bool active_ = false;
 };

@@ -24,7 +24,7 @@ const char* const kNames[K_COUNT] = {"ntt_fwd",      "ntt_inv",    "elementwise"
 struct Rec {
   u32 id;
   cudaEvent_t a, b;
-  double bytes;
+  double bytes, ops;
 };
 
 struct Prof {
@@ -57,7 +57,8 @@ std::atomic<bool> g_on{false};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_launches(u64 n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-Launch::Launch(KernelId id, cudaStream_t st, double algo_bytes) : id_(id), st_(st), bytes_(algo_bytes) {
+Launch::Launch(KernelId id, cudaStream_t st, double algo_bytes, double algo_ops)
+    : id_(id), st_(st), bytes_(algo_bytes), ops_(algo_ops) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!g_on.load(std::memory_order_relaxed)) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -75,7 +76,7 @@ Launch::~Launch() {
   std::lock_guard<std::mutex> lock(p.mu);
   cudaEvent_t b = p.get();
   cudaEventRecord(b, st_);
-  p.recs.push_back(Rec{(u32)id_, (cudaEvent_t)a_, b, bytes_});
+  p.recs.push_back(Rec{(u32)id_, (cudaEvent_t)a_, b, bytes_, ops_});
 }
 
 }  // namespace tcks
@@ -126,6 +127,17 @@ tcks_status tcks_profile_read(uint32_t idx, const char** name, uint64_t* launche
   if (launches) *launches = n;
   if (ms) *ms = t;
   if (algo_bytes) *algo_bytes = by;
+  return TCKS_OK;
+}
+
+tcks_status tcks_profile_read_ops(uint32_t idx, double* algo_ops) {
+  if (idx >= K_COUNT || !algo_ops) return TCKS_ERR_INVALID_ARG;
+  Prof& p = prof();
+  std::lock_guard<std::mutex> lock(p.mu);
+  double ops = 0;
+  for (const Rec& r : p.recs)
+    if (r.id == idx) ops += r.ops;
+  *algo_ops = ops;
   return TCKS_OK;
 }
 

@@ -162,3 +162,16 @@ def test_batch_validation_launches_nothing(ctxs):
         tk.batch_run([(g, tk.JOB_ROTATE, 1, 1, 4, d.data_ptr(), d.data_ptr())])
     assert err.value.name == "INVALID_ARG"
     assert tk.launch_count() == before
+
+
+def test_profiler_counts_butterflies_and_calibration(ctxs):
+    o, g = ctxs[13]
+    x = _dev(inputs.random_limbs(o.primes[:8], o.N, 31, polys=4))
+    tk.profile_start()
+    tk.batch_run([(g, tk.JOB_NTT, 0, 4, 8, x.data_ptr(), x.data_ptr())])
+    g.synchronize()
+    tk.profile_stop()
+    prof = tk.profile_read(with_ops=True)
+    launches, ms, by, ops = prof["ntt_fwd"]
+    assert launches == 1 and by == 16 * o.N * 32 and ops == 32 * (o.N // 2) * o.log_n
+    assert tk.calibrate_butterflies(64) > 1e10 and tk.calibrate_butterflies(32) > 1e10
