@@ -249,24 +249,43 @@ def run_gpu(args, world, rank, local):
             tk.check(tk.lib().tcks_ct_export(co.h, tk._p(host_out[i]), out_words))
     torch.cuda.synchronize()
     e2e_s = reduce_max(world, time.perf_counter() - t0)
+    c4 = run_c4(torch, tk, args) if args.c4 else None
     serving = None
     if args.serve_seconds > 0:
-        arr = poisson_arrivals(args.serve_rate, args.serve_seconds, 8)
-        lat_s, thr_s = serve_trace(tk, ctx, model, cts, arr, args.batch)
-        # the plain path saturates far below the offered rate: serve the first second of the trace
-        arr_p = arr[arr < min(1.0, args.serve_seconds)]
-        lat_p, thr_p = plain_trace(tk, ctx, model, cts, arr_p)
-        pct = lambda a, p: float(np.percentile(a, p) * 1e3)
-        serving = {"offered_rate": args.serve_rate, "seconds": args.serve_seconds, "requests": len(arr),
-                   "served": {"throughput": thr_s, "p50_ms": pct(lat_s, 50), "p99_ms": pct(lat_s, 99),
-                              "max_batch_per_stage": args.batch},
-                   "plain": {"throughput": thr_p, "p50_ms": pct(lat_p, 50), "p99_ms": pct(lat_p, 99),
-                             "requests": len(arr_p)},
-                   "latency": "arrival -> result exported to the host"}
+        lanes = {"cnn": (ctx, model, cts)}
+        mix = args.serve_mix if c4 else 0.0
+        if c4:
+            lanes["vm"] = (c4["ctx"], c4["mat"], c4["cts"])
+        pct = lambda a, p: float(np.percentile(a, p) * 1e3) if len(a) else None
+
+        def summary(lat, kind, thr):
+            d = {"throughput": thr, "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "requests": len(lat)}
+            for k in ("cnn", "vm"):
+                sel = lat[kind == k]
+                if len(sel):
+                    d[k] = {"requests": len(sel), "p50_ms": pct(sel, 50), "p99_ms": pct(sel, 99)}
+            return d
+        traces = []
+        for rate in [float(x) for x in args.serve_rate.split(",")]:
+            arr = poisson_arrivals(rate, args.serve_seconds, 8)
+            kinds = np.where(np.random.default_rng(9).uniform(size=len(arr)) < mix, "vm", "cnn")
+            lat_s, kind_s, thr_s = serve_trace(tk, lanes, arr, kinds, args.batch)
+            # the plain path saturates below the offered rate: run it on the start of the same trace
+            n_p = int(np.searchsorted(arr, args.plain_trace_seconds))
+            lat_p, kind_p, thr_p = plain_trace(tk, lanes, arr[:n_p], kinds[:n_p])
+            traces.append({"offered_rate": rate, "seconds": args.serve_seconds, "requests": len(arr),
+                           "served": dict(summary(lat_s, kind_s, thr_s), max_batch_per_stage=args.batch,
+                                          max_in_flight=1024, hbm_budget_gb=200),
+                           "plain": dict(summary(lat_p, kind_p, thr_p), trace_seconds=args.plain_trace_seconds)})
+        serving = {"mix": {"cnn": 1.0 - mix, "vm": mix}, "vm_workload": C4_WORKLOAD if c4 else None,
+                   "latency": "arrival -> result exported to the host", "traces": traces}
+    if c4:
+        for k in ("ctx", "mat", "cts"):
+            c4.pop(k)
     word = 32 if max(ctx.primes) < 2 ** 31 else 64
     bfly_peak = tk.calibrate_butterflies(word)
     primitives = primitives_summary(torch, tk) if args.primitives else None
-    return dict(primitives=primitives, bfly_peak=bfly_peak, word=word, serving=serving, total_ms=total_ms, per_step=per_step, prof=prof, launches=launches, clocks=clk, e2e_s=e2e_s,
+    return dict(c4=c4, primitives=primitives, bfly_peak=bfly_peak, word=word, serving=serving, total_ms=total_ms, per_step=per_step, prof=prof, launches=launches, clocks=clk, e2e_s=e2e_s,
                 e2e_steps=e2e_steps, h2d=host_in.nbytes, d2h=host_out.nbytes, max_err=max_err,
                 plain_ms=plain_total / plain_steps, plain_times=plain_times)
 
@@ -281,19 +300,32 @@ def poisson_arrivals(rate: float, seconds: float, seed: int) -> np.ndarray:
         out.append(t)
 
 
-def serve_trace(tk, ctx, model, cts, arrivals, max_batch):
-    """Continuous batching: requests are submitted when their arrival time passes and join the
-    running pipeline at the next step; latency = arrival -> result exported to the host."""
+def _finish(tk, lanes, kind, ct, hosts):
+    """Export a result to the host (the end of a request's latency)."""
+    if kind not in hosts:
+        level = ct.info()[0]
+        hosts[kind] = np.zeros((2, level, lanes[kind][0].N), dtype=np.uint64)
+    h = hosts[kind]
+    tk.check(tk.lib().tcks_ct_export(ct.h, tk._p(h), h.size))
+
+
+def serve_trace(tk, lanes, arrivals, kinds, max_batch):
+    """Continuous batching over the lanes (CNN; vector x matrix): requests are submitted when their
+    arrival time passes and join their lane at its next launch; latency = arrival -> result exported
+    to the host."""
     srv = tk.Server(hbm_budget_bytes=200 << 30, max_in_flight=1024, max_batch=max_batch)
-    lane = srv.add_cnn(model)
-    host = np.zeros((2, 1, ctx.N), dtype=np.uint64)
-    pending, lat = {}, []
+    lane_id = {"cnn": srv.add_cnn(lanes["cnn"][1])}
+    if "vm" in lanes:
+        lane_id["vm"] = srv.add_vecmat(lanes["vm"][1])
+    hosts, pending, lat, lat_kind = {}, {}, [], []
     i, total = 0, len(arrivals)
     t0 = time.perf_counter()
     while len(lat) < total:
         now = time.perf_counter() - t0
         while i < total and arrivals[i] <= now:
-            pending[srv.submit(lane, cts[i % len(cts)])] = arrivals[i]
+            k = kinds[i]
+            pool = lanes[k][2]
+            pending[srv.submit(lane_id[k], pool[i % len(pool)])] = (arrivals[i], k)
             i += 1
         st = srv.stats()
         if st["queued"] + st["in_flight"] == 0:
@@ -301,27 +333,74 @@ def serve_trace(tk, ctx, model, cts, arrivals, max_batch):
             continue
         srv.step()
         for rid in srv.poll():
-            out = srv.take(rid, ctx)
-            tk.check(tk.lib().tcks_ct_export(out.h, tk._p(host), host.size))
-            lat.append(time.perf_counter() - t0 - pending.pop(rid))
+            a, k = pending.pop(rid)
+            _finish(tk, lanes, k, srv.take(rid, lanes[k][0]), hosts)
+            lat.append(time.perf_counter() - t0 - a)
+            lat_kind.append(k)
     span = time.perf_counter() - t0 - arrivals[0]
-    return np.array(lat), total / span
+    return np.array(lat), np.array(lat_kind), total / span
 
 
-def plain_trace(tk, ctx, model, cts, arrivals):
+def plain_trace(tk, lanes, arrivals, kinds):
     """The plain path on the same trace: one request at a time in arrival order."""
-    host = np.zeros((2, 1, ctx.N), dtype=np.uint64)
-    lat = []
+    hosts, lat = {}, []
     t0 = time.perf_counter()
     for i, a in enumerate(arrivals):
         now = time.perf_counter() - t0
         if now < a:
             time.sleep(a - now)
-        out = model.forward(cts[i % len(cts)])
-        tk.check(tk.lib().tcks_ct_export(out.h, tk._p(host), host.size))
+        k = kinds[i]
+        ctx, model, pool = lanes[k]
+        x = pool[i % len(pool)]
+        out = model.forward(x) if k == "cnn" else x.vecmat_plain(model)
+        _finish(tk, lanes, k, out, hosts)
         lat.append(time.perf_counter() - t0 - a)
-    span = time.perf_counter() - t0 - arrivals[0]
-    return np.array(lat), len(arrivals) / span
+    span = time.perf_counter() - t0 - arrivals[0] if len(arrivals) else 1.0
+    return np.array(lat), np.array(kinds), len(arrivals) / span
+
+
+# ------------------------------------------------------ vector x plain matrix at full size --
+C4_ROWS, C4_COLS = 4096, 256
+C4_WORKLOAD = ("encrypted 4096-dim N(0,1) vector x plain 4096x256 N(0,0.05) matrix (diagonal method: 4095 "
+               "hoisted rotations + the replication rotation), CKKS N=16384, primes [60,40,40|60], scale 2^40")
+
+
+def run_c4(torch, tk, args):
+    from paper_2104_03152_gb300 import inputs
+    t0 = time.perf_counter()
+    st = torch.cuda.Stream()
+    ctx = tk.Context(tk.Params(14, [60, 40, 40, 60], 2.0 ** 40), seed=inputs.SEED_KEYS, flags=tk.TCKS_AUTO_RELIN,
+                     stream=st.cuda_stream)
+    ctx._torch_stream = st
+    ctx.gen_galois_keys([ctx.slots - C4_ROWS] + list(range(1, C4_ROWS)))
+    M = inputs.random_matrix(C4_ROWS, C4_COLS, 7, 0.05)
+    mat = ctx.matrix_encode(M, level=3)
+    B = args.c4_batch
+    vs = [inputs.normal_slots(C4_ROWS, 6 + 1000 * i) for i in range(B)]
+    cts = []
+    for i, v in enumerate(vs):
+        z = np.zeros(ctx.slots)
+        z[:C4_ROWS] = v
+        cts.append(ctx.encrypt_values(z, 600 + i))
+    ctx.synchronize()
+    setup_s = time.perf_counter() - t0
+    outs = mat.vecmat_batch(cts)  # warm-up, and the accuracy check
+    err = max(float(np.max(np.abs(ctx.decrypt_values(outs[i])[:C4_COLS] - vs[i] @ M))) for i in (0, B - 1))
+    torch.cuda.synchronize()
+    tk.profile_start()
+    per, total = timed(torch, st, lambda: mat.vecmat_batch(cts), args.c4_steps)
+    tk.profile_stop()
+    prof = tk.profile_read(with_ops=True)
+    peak64 = tk.calibrate_butterflies(64)
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "gbs": round(v[2] / (v[1] / 1e3) / 1e9, 1),
+                   "gbfly_s": round(v[3] / (v[1] / 1e3) / 1e9, 1),
+                   "alu_frac": round(v[3] / (v[1] / 1e3) / peak64, 4)}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    return {"workload": C4_WORKLOAD, "batch": B, "value": B * args.c4_steps / (total / 1e3), "unit": "vectors/s",
+            "ms_per_batch": total / args.c4_steps, "steps": args.c4_steps, "setup_s": setup_s,
+            "galois_keys": C4_ROWS, "key_bytes": ctx.key_bytes(),
+            "max_abs_err_vs_fp64": err, "kernels": kernels, "alu_peak_bfly64_per_s": peak64,
+            "ctx": ctx, "mat": mat, "cts": cts}
 
 
 def plain_cnn(img, w):
@@ -442,28 +521,30 @@ def run_sweep(args):
     torch.cuda.set_device(0)
     peaks = primitive_peaks(tk)
     print(json.dumps({"sweep_peaks": peaks}), flush=True)
-    log_ns = [13, 14, 15, 16]
+    log_ns = [int(x) for x in args.sweep_log_n.split(",")]
     ctxs = sweep_contexts(torch, tk, log_ns)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(5)
     batches = [int(b) for b in args.sweep_batches.split(",")]
+    levels = [int(x) for x in args.sweep_L.split(",")]
+    ops = args.sweep_ops.split(",")
     for log_n in log_ns:
-        for L in (4, 8, 16, 32):
+        for L in levels:
             for B in batches:
-                for op in SWEEP_OPS:
+                for op in ops:
                     r = sweep_point(torch, tk, ctxs, [(log_n, L, B)], op, peaks, gen)
                     r.update({"log_n": log_n, "L": L, "batch": B})
                     print(json.dumps(r), flush=True)
                 torch.cuda.empty_cache()
     # mixed batches: every ciphertext draws (N, L) uniformly; one job per (N, L) group, one graph
     rng = np.random.default_rng(5)
-    for B in [b for b in batches if b > 1]:
-        draws = [(int(rng.choice(log_ns)), int(rng.choice([4, 8, 16, 32]))) for _ in range(B)]
+    for B in [b for b in batches if b > 1 and args.sweep_mixed]:
+        draws = [(int(rng.choice(log_ns)), int(rng.choice(levels))) for _ in range(B)]
         groups = {}
         for d in draws:
             groups[d] = groups.get(d, 0) + 1
         entries = [(ln, L, cnt) for (ln, L), cnt in sorted(groups.items())]
-        for op in SWEEP_OPS:
+        for op in ops:
             r = sweep_point(torch, tk, ctxs, entries, op, peaks, gen)
             r.update({"mixed": True, "batch": B, "groups": len(entries)})
             print(json.dumps(r), flush=True)
@@ -540,11 +621,22 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=2, help="oracle inferences timed for cpu_baseline")
     ap.add_argument("--batch", type=int, default=64, help="requests per step (the batched schedule)")
-    ap.add_argument("--serve-seconds", type=float, default=4.0, help="length of the Poisson serving trace (0: skip)")
-    ap.add_argument("--serve-rate", type=float, default=600.0, help="offered requests/s of the serving trace")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the Poisson serving trace (0: skip)")
+    ap.add_argument("--serve-rate", default="2000,100",
+                    help="offered requests/s of the serving traces (comma-separated; one trace each)")
     ap.add_argument("--sweep", action="store_true", help="print the batched primitive sweep (JSON lines) and exit")
     ap.add_argument("--sweep-batches", default="1,8,64,512", help="ciphertexts per batch in the sweep")
+    ap.add_argument("--sweep-log-n", default="13,14,15,16", help="log2 N values of the sweep")
+    ap.add_argument("--sweep-L", default="4,8,16,32", help="data-prime counts of the sweep")
+    ap.add_argument("--sweep-ops", default=",".join(SWEEP_OPS), help="ops of the sweep")
+    ap.add_argument("--sweep-mixed", type=int, default=1, help="also run the mixed (N, L) batches")
     ap.add_argument("--primitives", type=int, default=1, help="add the NTT / key-switch rates at N=2^16, L=32")
+    ap.add_argument("--c4", type=int, default=1, help="time the 4096x256 vector x matrix workload (64 vectors)")
+    ap.add_argument("--c4-batch", type=int, default=64)
+    ap.add_argument("--c4-steps", type=int, default=3)
+    ap.add_argument("--serve-mix", type=float, default=0.3, help="share of vector x matrix requests in the trace")
+    ap.add_argument("--plain-trace-seconds", type=float, default=0.25,
+                    help="arrivals of the trace's first seconds replayed through the plain path")
     args = ap.parse_args()
     if args.sweep:
         run_sweep(args)
@@ -609,6 +701,7 @@ def main():
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
         "serving": r["serving"],
         "primitives": r["primitives"],
+        "vecmat_4096x256": r["c4"],
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
     }

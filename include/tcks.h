@@ -224,6 +224,10 @@ void tcks_matrix_free(tcks_matrix* m);
  * rotations, then rescale. Result: y in slots [0, m), zeros elsewhere. Needs Galois keys for the
  * replication steps N/2 - n*2^i and for steps 1..n-1. */
 tcks_status tcks_vecmat_plain(const tcks_ct* a, const tcks_matrix* M, tcks_ct** out);
+/* `count` ciphertexts of one level and scale times the same matrix in one batched pass: ModUp
+ * once per ciphertext, every rotation's key read once for the whole batch. outs[i] is
+ * bit-identical to tcks_vecmat_plain(in[i], M). */
+tcks_status tcks_vecmat_plain_batch(const tcks_ct* const* in, uint32_t count, const tcks_matrix* M, tcks_ct** outs);
 
 /* Client-side im2col (§3.2, host only, no context): windows of a kh x kw kernel sliding with
  * `stride` over an H x W image (row-major), windows ordered row-major, taps row-major; slot

@@ -123,6 +123,7 @@ _SIGS = {
     "tcks_cnn_galois_steps": (ctypes.c_int32, [_vp, _i32p, _u32p, ctypes.c_uint32, _u32p]),
     "tcks_cnn_forward": (ctypes.c_int32, [_vp, _vp, _vpp]),
     "tcks_cnn_forward_batch": (ctypes.c_int32, [_vp, _vpp, ctypes.c_uint32, _vpp]),
+    "tcks_vecmat_plain_batch": (ctypes.c_int32, [_vpp, ctypes.c_uint32, _vp, _vpp]),
     "tcks_batch_run": (ctypes.c_int32, [_vp, ctypes.c_uint32]),
     "tcks_batch_graph_create": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vpp]),
     "tcks_batch_graph_run": (ctypes.c_int32, [_vp]),
@@ -235,6 +236,11 @@ class Params:
             self.h = None
 
 
+# Allocator callbacks handed to the library stay referenced for the life of the process: a context
+# outlives its Python wrapper while ciphertexts still hold it, and frees through these callbacks last.
+_CALLBACKS_IN_USE = []
+
+
 def _torch_allocator():
     """tcks_allocator backed by PyTorch's caching allocator (stream-ordered)."""
     import torch
@@ -251,6 +257,7 @@ def _torch_allocator():
         torch.cuda.caching_allocator_delete(ptr)
 
     a = _Allocator(_alloc, _free, None)
+    _CALLBACKS_IN_USE.append((a, _alloc, _free))
     return a, (_alloc, _free)
 
 
@@ -436,6 +443,13 @@ class Matrix:
         if getattr(self, "h", None):
             lib().tcks_matrix_free(self.h)
             self.h = None
+
+    def vecmat_batch(self, cts) -> list:
+        """cts[i] x this matrix for a batch of one level and scale (one batched pass)."""
+        ins = (_vp * len(cts))(*[c.h.value if isinstance(c.h, _vp) else c.h for c in cts])
+        outs = (_vp * len(cts))()
+        check(lib().tcks_vecmat_plain_batch(ins, len(cts), self.h, outs))
+        return [Ciphertext(self.ctx, _vp(outs[i])) for i in range(len(cts))]
 
 
 class Ciphertext:

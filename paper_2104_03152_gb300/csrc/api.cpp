@@ -23,7 +23,9 @@ tcks_status record(tcks_status code, const std::string& msg) {
 
 static void ctx_destroy(tcks_ctx* c);
 
-#define TCKS_API_BEGIN try {
+#define TCKS_API_BEGIN \
+  try {                 \
+    tcks::drop_stale_cuda_error();
 #define TCKS_API_END                                                   \
   }                                                                    \
   catch (const tcks::Error& e) {                                       \
@@ -50,6 +52,7 @@ void check_cuda(cudaError_t e, const char* what) {
 }
 
 void check_launch(const char* what) { check_cuda(cudaGetLastError(), what); }
+void drop_stale_cuda_error() { cudaGetLastError(); }
 
 tcks_ct* new_ct(tcks_ctx* c, u32 level, double scale) {
   DevBuf b(c, ct_words(c, level));
@@ -1016,6 +1019,40 @@ tcks_status tcks_vecmat_plain(const tcks_ct* a, const tcks_matrix* M, tcks_ct** 
     throw;
   }
   *out = r;
+  TCKS_API_END
+}
+
+tcks_status tcks_vecmat_plain_batch(const tcks_ct* const* in, uint32_t count, const tcks_matrix* M, tcks_ct** outs) {
+  std::vector<tcks_ct*> made;
+  TCKS_API_BEGIN
+  if (!M || !outs || (count && !in)) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  for (u32 i = 0; i < count; ++i) outs[i] = nullptr;
+  if (!count) return TCKS_OK;
+  tcks_ctx* c = M->ctx;
+  const u32 ell = in[0] ? in[0]->level : 0;
+  for (u32 i = 0; i < count; ++i) {
+    if (!in[i] || in[i]->ctx != c) fail(TCKS_ERR_INVALID_ARG, "ciphertext missing or of another context");
+    if (in[i]->level != ell) fail(TCKS_ERR_LEVEL_MISMATCH, "the batch must share one level");
+    if (in[i]->scale != in[0]->scale) fail(TCKS_ERR_SCALE_MISMATCH, "the batch must share one scale");
+  }
+  if (M->level < ell) fail(TCKS_ERR_LEVEL_MISMATCH, "matrix encoded below the ciphertext level");
+  if (ell < 2) fail(TCKS_ERR_LEVEL_EXHAUSTED, "vecmat needs level >= 2");
+  const u64 wi = ct_words(c, ell), wo = ct_words(c, ell - 1);
+  DevBuf x(c, (size_t)count * wi), y(c, (size_t)count * wo);
+  for (u32 i = 0; i < count; ++i)
+    check_cuda(cudaMemcpyAsync(x.p + i * wi, in[i]->d, wi * 8, cudaMemcpyDeviceToDevice, c->stream), "gather");
+  op_vecmat(c, x.p, wi, count, ell, M, y.p);
+  const double scale = in[0]->scale * M->scale / (double)c->host.chain[ell - 1];
+  try {
+    for (u32 i = 0; i < count; ++i) {
+      made.push_back(new_ct(c, ell - 1, scale));
+      check_cuda(cudaMemcpyAsync(made.back()->d, y.p + i * wo, wo * 8, cudaMemcpyDeviceToDevice, c->stream), "scatter");
+    }
+  } catch (...) {
+    for (tcks_ct* t : made) free_ct(t);
+    throw;
+  }
+  for (u32 i = 0; i < count; ++i) outs[i] = made[i];
   TCKS_API_END
 }
 

@@ -64,6 +64,7 @@ void write_cache(const std::string& path, const std::map<std::string, u32>& c) {
 
 extern "C" tcks_status tcks_autotune(tcks_ctx* c, const char* cache_path, uint32_t* chosen_threads) {
   try {
+    drop_stale_cuda_error();
     if (!c) fail(TCKS_ERR_INVALID_ARG, "null context");
     cudaDeviceProp prop;
     check_cuda(cudaGetDeviceProperties(&prop, c->device), "device properties");
@@ -74,15 +75,22 @@ extern "C" tcks_status tcks_autotune(tcks_ctx* c, const char* cache_path, uint32
         std::string(prop.name) + "|" + std::to_string(log_n) + "|" + (c->T.narrow ? "32" : "64");
     std::map<std::string, u32> cache;
     if (cache_path && *cache_path) cache = read_cache(cache_path);
+    // every kernel that runs with the tuned CTA size must accept it (registers bound the size)
+    u32 cap = 1024;
+    for (u32 t : {limb_threads_cap_core(c->T.narrow, log_c), limb_threads_cap_sample(c->T.narrow, log_c),
+                  limb_threads_cap_fft(c->T.narrow, log_c)})
+      cap = std::min(cap, t);
+    cap &= ~31u;
+    if (cap < 32) fail(TCKS_ERR_CUDA, "autotune: cannot read the limb kernels' launch limits");
     u32 best = 0;
     auto it = cache.find(key);
-    if (it != cache.end() && it->second >= 32 && it->second <= 1024 && it->second % 32 == 0) {
+    if (it != cache.end() && it->second >= 32 && it->second <= cap && it->second % 32 == 0) {
       best = it->second;
     } else {
       std::vector<u32> cand;
       for (u32 div : {64u, 32u, 16u}) {
         u32 t = ns / div;
-        t = t < 32 ? 32 : (t > 1024 ? 1024 : t);
+        t = t < 32 ? 32 : (t > cap ? cap : t);
         if (std::find(cand.begin(), cand.end(), t) == cand.end()) cand.push_back(t);
       }
       const u32 limbs = 256, lv = c->L + 1;

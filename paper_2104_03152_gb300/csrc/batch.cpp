@@ -180,7 +180,9 @@ struct tcks_batch_graph {
   u64 launches = 0;
 };
 
-#define BATCH_BEGIN try {
+#define BATCH_BEGIN \
+  try {                 \
+    tcks::drop_stale_cuda_error();
 #define BATCH_END                                                    \
   }                                                                  \
   catch (const tcks::Error& e) {                                     \

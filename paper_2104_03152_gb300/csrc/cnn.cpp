@@ -183,7 +183,9 @@ static void cnn_forward_dev(const tcks_cnn* m, const u64* in, u64 in_stride, u32
 
 }  // namespace tcks
 
-#define CNN_BEGIN try {
+#define CNN_BEGIN \
+  try {                 \
+    tcks::drop_stale_cuda_error();
 #define CNN_END                                                       \
   }                                                                   \
   catch (const tcks::Error& e) {                                      \

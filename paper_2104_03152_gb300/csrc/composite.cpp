@@ -59,9 +59,15 @@ void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell,
   const u64 per_rot = (u64)count * 2 * n;  // P-limb scratch words per rotation
   u32 RB = (u32)std::max<u64>(1, ((u64)64 << 20) / per_rot);  // 512 MB of scratch per block
   if (RB > R) RB = R;
-  // chunks per block: enough CTAs (count * 2 ell * chunks) to fill the GPU a few times over
-  const u32 target = 152 * 4;
-  u32 chunks_pb = (u32)std::min<u64>(RB, std::max<u64>(1, (target + count * 2 * ell - 1) / (count * 2 * ell)));
+  // chunks per block: the fewest that give at least two waves of CTAs (count * 2 ell * chunks) with a
+  // full-enough last wave (>= 90% of the slots busy on average), up to 64 chunks
+  const u64 gpu_slots = vecmat_slots(c->T), per_chunk = (u64)count * 2 * ell;
+  u32 chunks_pb = 1;
+  for (u32 k = 1; k <= std::min<u32>(RB, 64); ++k) {
+    chunks_pb = k;
+    const u64 ctas = per_chunk * k, waves = (ctas + gpu_slots - 1) / gpu_slots;
+    if (ctas >= 2 * gpu_slots && (double)ctas / (double)(waves * gpu_slots) >= 0.9) break;
+  }
   const u32 chunk = (RB + chunks_pb - 1) / chunks_pb;
   chunks_pb = (RB + chunk - 1) / chunk;
   DevBuf top(c, (size_t)per_rot * RB);

@@ -143,6 +143,10 @@ void check_launch(const char* what);
 tcks_status abi_record(tcks_status code, const std::string& msg);
 void abi_clear();
 void count_launches(u64 n);
+// Clear a non-sticky CUDA error left in this thread by a call outside the library's checks (another
+// library, or a clean-up call whose status is ignored), so that the next launch check reports only
+// its own launch. Sticky errors stay: the next CUDA call reports them again.
+void drop_stale_cuda_error();
 
 inline size_t ct_words(const tcks_ctx* c, u32 level) { return (size_t)2 * level * c->N; }
 inline size_t pt_words(const tcks_ctx* c, u32 level) { return (size_t)level * c->N; }

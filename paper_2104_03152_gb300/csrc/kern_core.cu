@@ -456,20 +456,55 @@ void launch_keyswitch(const DevTables& T, u32 ell, const KsPlan& plan, cudaStrea
   launch_limb(K6_k_ks_moddown, T.narrow, 2 * ell, jobs, T.log_n, st, T.limb_threads, T, ell, plan);
 }
 
+// ------------------------------------------------------------ launch-shape limits (autotune) ----
+// Largest CTA size every limb kernel of this file accepts for the word type and cluster split.
+template <typename F>
+static u32 max_threads_of(F k) {
+  cudaFuncAttributes a{};
+  if (cudaFuncGetAttributes(&a, (const void*)k) != cudaSuccess) return 0;
+  return (u32)a.maxThreadsPerBlock;
+}
+u32 limb_threads_cap_core(bool narrow, u32 log_c) {
+  const u32 i = (narrow ? 3 : 0) + log_c;
+  u32 cap = 1024;
+  for (u32 t : {max_threads_of(kNttFwd[i]), max_threads_of(kNttInv[i]), max_threads_of(kNttDescFwd[i]),
+                max_threads_of(kNttDescInv[i]), max_threads_of(K6_k_drop_combine[i]), max_threads_of(K6_k_modup[i]),
+                max_threads_of(K6_k_ks_inner_p[i]), max_threads_of(K6_k_ks_moddown[i])})
+    cap = t < cap ? t : cap;
+  return cap;
+}
+
 // -------------------------------------------------- vector x plain matrix: fused ModDown + MAC ----
 // For request rq and the rotations r of this CTA's chunk (step k = r + 1): the rotated ciphertext
-// rot_k = (tau(c0) + ModDown(u_0), ModDown(u_1)) is multiplied by the diagonal d_k and summed in
-// registers, then stored as a per-chunk partial [B][chunks][2][ell][N]. Limb job = chunk * 2 * ell
-// + b * ell + i. Thread t owns elements t + e * blockDim.x of the slice.
+// rot_k = (tau(c0) + ModDown(u_0), ModDown(u_1)) is multiplied by the diagonal d_k and summed into
+// a per-chunk partial [B][chunks][2][ell][N]. Limb job = chunk * 2 * ell + b * ell + i.
+// Two accumulation modes: up to 8192-element slices thread t keeps the sums of elements
+// t + e * blockDim.x (e < 16) in registers and stores them once; for 16384-element slices, whose
+// register accumulators would not fit a CTA's register file with 64-bit words, every rotation adds
+// into the partial in place (each thread owns the same elements throughout, the CTA's partial is
+// L2-resident).
 constexpr int kVmEpt = 16;
-// Threads of k_vecmat_acc: each owns kVmEpt elements of the slice.
+static bool vecmat_in_place(u32 log_n) { return (log_n > 14 ? 14 : log_n) >= 14; }
 static u32 vecmat_threads(u32 log_n) {
   const u32 ns = 1u << (log_n > 14 ? 14 : log_n);
+  if (vecmat_in_place(log_n)) return 512;
   return ns / kVmEpt < 32 ? 32 : ns / kVmEpt;
 }
-template <typename W, int LC>
-__global__ void k_vecmat_acc(DevTables T, u32 ell, const __grid_constant__ VecmatPlan plan) {
-  TCKS_SMEM(W);
+
+// The rotated-and-multiplied element g of rotation r: (tau(c0) + ModDown(u_b))[i][g] * d_k[i][g].
+template <typename W>
+__device__ __forceinline__ u64 vecmat_term(const W* s, u32 k, u32 g, const KsKey& kk, const u64* digits, u32 ell, u32 i,
+                                           u32 b, u64 n, u32 log_n, const u64* c0, const u64* dk, const ModConst& mi,
+                                           const PairConst& pc) {
+  const u32 src = galois_src(g, kk.g, log_n);
+  const u64 u = ks_inner<W>(digits, ell, i, kk.key, kk.K, i, b, g, src, n, mi);
+  u64 v = Ew<W>::shoup_inv(sub_mod(u, Ar<W>::fwd_out(s[sw(k)], mi), mi.q), pc, mi);
+  if (b == 0) v = add_mod(v, c0[(u64)i * n + src], mi.q);
+  return Ew<W>::mul(v, dk[g], mi);
+}
+
+template <typename W, int LC, bool IN_PLACE>
+__device__ __forceinline__ void vecmat_acc_body(W* s, const DevTables& T, u32 ell, const VecmatPlan& plan) {
   const Slice sl = slice_of<LC>(T);
   const u32 log_n = T.log_n;
   const u64 n = 1ull << log_n;
@@ -482,11 +517,16 @@ __global__ void k_vecmat_acc(DevTables T, u32 ell, const __grid_constant__ Vecma
   const PairConst pc = T.pairs[(u64)T.L * T.n_mods + i];
   const u64* digits = plan.digits + rq * plan.digits_b;
   const u64* c0 = plan.ct + rq * plan.ct_b;  // component 0, [ell][N]
-  W acc[kVmEpt];
-#pragma unroll
-  for (int e = 0; e < kVmEpt; ++e) acc[e] = 0;
+  u64* dst = plan.partial + rq * plan.partial_b + (((u64)chunk * 2 + b) * ell + i) * n + sl.off;
   const u32 r0 = chunk * plan.chunk;
   const u32 r1 = min(plan.R, r0 + plan.chunk);
+  W acc[IN_PLACE ? 1 : kVmEpt];
+  if (!IN_PLACE) {
+#pragma unroll
+    for (int e = 0; e < kVmEpt; ++e) acc[e] = 0;
+  } else if (!plan.accumulate && r0 >= r1) {
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) dst[k] = 0;  // an empty chunk still defines its partial
+  }
   for (u32 r = r0; r < r1; ++r) {
     const KsKey kk = plan.keys[r];
     const u64* top = plan.top + (((u64)r * plan.B + rq) * 2 + b) * n + sl.off;
@@ -494,26 +534,44 @@ __global__ void k_vecmat_acc(DevTables T, u32 ell, const __grid_constant__ Vecma
     __syncthreads();
     ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
     const u64* dk = plan.diag + (u64)(r + 1) * plan.diag_stride + (u64)i * n;
+    if (IN_PLACE) {
+      const bool overwrite = r == r0 && !plan.accumulate;
+      for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
+        const u64 t = vecmat_term<W>(s, k, sl.off + k, kk, digits, ell, i, b, n, log_n, c0, dk, mi, pc);
+        dst[k] = overwrite ? t : add_mod(dst[k], t, mi.q);
+      }
+    } else {
 #pragma unroll
-    for (int e = 0; e < kVmEpt; ++e) {
-      const u32 k = threadIdx.x + e * blockDim.x;
-      if (k < sl.ns) {
-        const u32 g = sl.off + k;
-        const u32 src = galois_src(g, kk.g, log_n);
-        const u64 u = ks_inner<W>(digits, ell, i, kk.key, kk.K, i, b, g, src, n, mi);
-        u64 v = Ew<W>::shoup_inv(sub_mod(u, Ar<W>::fwd_out(s[sw(k)], mi), mi.q), pc, mi);
-        if (b == 0) v = add_mod(v, c0[(u64)i * n + src], mi.q);
-        acc[e] = (W)add_mod(acc[e], Ew<W>::mul(v, dk[g], mi), mi.q);
+      for (int e = 0; e < kVmEpt; ++e) {
+        const u32 k = threadIdx.x + e * blockDim.x;
+        if (k < sl.ns)
+          acc[e] = (W)add_mod(acc[e], vecmat_term<W>(s, k, sl.off + k, kk, digits, ell, i, b, n, log_n, c0, dk, mi, pc),
+                              mi.q);
       }
     }
     __syncthreads();  // s is refilled for the next rotation
   }
-  u64* dst = plan.partial + rq * plan.partial_b + (((u64)chunk * 2 + b) * ell + i) * n + sl.off;
+  if (!IN_PLACE) {
 #pragma unroll
-  for (int e = 0; e < kVmEpt; ++e) {
-    const u32 k = threadIdx.x + e * blockDim.x;
-    if (k < sl.ns) dst[k] = plan.accumulate ? add_mod(dst[k], acc[e], mi.q) : acc[e];
+    for (int e = 0; e < kVmEpt; ++e) {
+      const u32 k = threadIdx.x + e * blockDim.x;
+      if (k < sl.ns) dst[k] = plan.accumulate ? add_mod(dst[k], acc[e], mi.q) : acc[e];
+    }
   }
+}
+
+// 32-bit words: two 512-thread CTAs per SM (registers capped at 64) to hide the L2 latency of the
+// digit, key and diagonal reads behind the other CTA's transform.
+template <typename W, int LC>
+__global__ void __launch_bounds__(512, (sizeof(W) == 4 && LC == 0) ? 2 : 1)
+    k_vecmat_acc(DevTables T, u32 ell, const __grid_constant__ VecmatPlan plan) {
+  TCKS_SMEM(W);
+  vecmat_acc_body<W, LC, false>(s, T, ell, plan);
+}
+template <typename W, int LC>
+__global__ void __launch_bounds__(512, 1) k_vecmat_acc_ip(DevTables T, u32 ell, const __grid_constant__ VecmatPlan plan) {
+  TCKS_SMEM(W);
+  vecmat_acc_body<W, LC, true>(s, T, ell, plan);
 }
 
 // out[rq] = ct[rq] * d_0 + sum over chunks of partial[rq][chunk]; out [B][2][ell][N].
@@ -538,6 +596,23 @@ __global__ void k_vecmat_reduce(DevTables T, u32 ell, const __grid_constant__ Ve
 }
 
 static decltype(&k_vecmat_acc<u64, 0>) const K6_k_vecmat_acc[6] = TCKS_K6(k_vecmat_acc);
+static decltype(&k_vecmat_acc_ip<u64, 0>) const K6_k_vecmat_acc_ip[6] = TCKS_K6(k_vecmat_acc_ip);
+
+// CTAs of k_vecmat_acc the whole GPU holds at once (SMs x resident CTAs per SM) for this chain.
+u32 vecmat_slots(const DevTables& T) {
+  const LimbShape sh = limb_shape(T.log_n);
+  const u32 idx = (T.narrow ? 3 : 0) + sh.log_c;
+  const void* k = vecmat_in_place(T.log_n) ? (const void*)K6_k_vecmat_acc_ip[idx] : (const void*)K6_k_vecmat_acc[idx];
+  const size_t smem = T.narrow ? sh.smem / 2 : sh.smem;
+  ensure_smem(k, smem);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, (int)vecmat_threads(T.log_n), smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return (u32)(sms * per_sm) >> sh.log_c;  // clusters of 2^log_c CTAs share the count
+}
 
 void launch_vecmat_acc(const DevTables& T, u32 ell, const VecmatPlan& plan, cudaStream_t st) {
   const double n = (double)(1u << T.log_n);
@@ -548,8 +623,12 @@ void launch_vecmat_acc(const DevTables& T, u32 ell, const VecmatPlan& plan, cuda
                      (double)plan.B * plan.chunks * 2.0 * ell * (plan.accumulate ? 2.0 : 1.0));
   Launch L(K_VECMAT, st, by,
            (double)plan.B * plan.R * 2.0 * ell * ((ell + 2.0) * n + bfly_per_limb(T.log_n)));
-  launch_limb(K6_k_vecmat_acc, T.narrow, plan.chunks * 2 * ell * plan.B, 1, T.log_n, st, vecmat_threads(T.log_n), T,
-              ell, plan);
+  if (vecmat_in_place(T.log_n))
+    launch_limb(K6_k_vecmat_acc_ip, T.narrow, plan.chunks * 2 * ell * plan.B, 1, T.log_n, st, vecmat_threads(T.log_n),
+                T, ell, plan);
+  else
+    launch_limb(K6_k_vecmat_acc, T.narrow, plan.chunks * 2 * ell * plan.B, 1, T.log_n, st, vecmat_threads(T.log_n), T,
+                ell, plan);
 }
 
 void launch_vecmat_reduce(const DevTables& T, u32 ell, const VecmatPlan& plan, u64* out, cudaStream_t st) {

@@ -203,10 +203,18 @@ void launch_encode_coeffs(const DevTables& T, const FftTables& F, const double* 
   k_encode_coeffs<<<1, 1024, sm, st>>>(T, F, d_z, n_in, scale, d_coeffs, d_status);
 }
 
+static decltype(&k_coeffs_to_ntt<u64, 0>) const K6_k_coeffs_to_ntt[6] = TCKS_K6(k_coeffs_to_ntt);
+
+// Largest CTA size the limb kernel of this file accepts for the word type and cluster split.
+u32 limb_threads_cap_fft(bool narrow, u32 log_c) {
+  cudaFuncAttributes a{};
+  if (cudaFuncGetAttributes(&a, (const void*)K6_k_coeffs_to_ntt[(narrow ? 3 : 0) + log_c]) != cudaSuccess) return 0;
+  return (u32)a.maxThreadsPerBlock;
+}
+
 void launch_coeffs_to_ntt(const DevTables& T, const i64* d_coeffs, u32 ell, u64* pt, cudaStream_t st) {
   Launch L(K_ENCODE, st, 8.0 * (1.0 + ell) * (1u << T.log_n));
-  static decltype(&k_coeffs_to_ntt<u64, 0>) const ks[6] = TCKS_K6(k_coeffs_to_ntt);
-  launch_limb(ks, T.narrow, ell, 1, T.log_n, st, T.limb_threads, T, d_coeffs, pt);
+  launch_limb(K6_k_coeffs_to_ntt, T.narrow, ell, 1, T.log_n, st, T.limb_threads, T, d_coeffs, pt);
 }
 
 void launch_crt_compose(const DevTables& T, const u64* coef, u32 ell, const u64* d_qwords, double* out,

@@ -175,28 +175,43 @@ __global__ void k_encrypt(DevTables T, u64 seed, const u64* __restrict__ pk, con
   for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) c1[k] = add_mod(c1[k], Ar<W>::fwd_out(s[sw(k)], m), m.q);
 }
 
+static decltype(&k_keygen_secret<u64, 0>) const K6_k_keygen_secret[6] = TCKS_K6(k_keygen_secret);
+static decltype(&k_keygen_public<u64, 0>) const K6_k_keygen_public[6] = TCKS_K6(k_keygen_public);
+static decltype(&k_keygen_switch<u64, 0>) const K6_k_keygen_switch[6] = TCKS_K6(k_keygen_switch);
+static decltype(&k_encrypt<u64, 0>) const K6_k_encrypt[6] = TCKS_K6(k_encrypt);
+
+// Largest CTA size every limb kernel of this file accepts for the word type and cluster split.
+u32 limb_threads_cap_sample(bool narrow, u32 log_c) {
+  const u32 i = (narrow ? 3 : 0) + log_c;
+  u32 cap = 1024;
+  const void* ks[4] = {(const void*)K6_k_keygen_secret[i], (const void*)K6_k_keygen_public[i],
+                       (const void*)K6_k_keygen_switch[i], (const void*)K6_k_encrypt[i]};
+  for (const void* k : ks) {
+    cudaFuncAttributes a{};
+    if (cudaFuncGetAttributes(&a, k) != cudaSuccess) return 0;
+    cap = (u32)a.maxThreadsPerBlock < cap ? (u32)a.maxThreadsPerBlock : cap;
+  }
+  return cap;
+}
+
 void launch_keygen_secret(const DevTables& T, u64 seed, u64* s, cudaStream_t st) {
   Launch L(K_KEYGEN, st, 8.0 * (T.L + 1) * (1u << T.log_n));
-  static decltype(&k_keygen_secret<u64, 0>) const ks[6] = TCKS_K6(k_keygen_secret);
-  launch_limb(ks, T.narrow, T.L + 1, 1, T.log_n, st, T.limb_threads, T, seed, s);
+  launch_limb(K6_k_keygen_secret, T.narrow, T.L + 1, 1, T.log_n, st, T.limb_threads, T, seed, s);
 }
 
 void launch_keygen_public(const DevTables& T, u64 seed, const u64* s, u64* pk, cudaStream_t st) {
   Launch L(K_KEYGEN, st, 8.0 * 3 * T.L * (1u << T.log_n));
-  static decltype(&k_keygen_public<u64, 0>) const ks[6] = TCKS_K6(k_keygen_public);
-  launch_limb(ks, T.narrow, T.L, 1, T.log_n, st, T.limb_threads, T, seed, s, pk);
+  launch_limb(K6_k_keygen_public, T.narrow, T.L, 1, T.log_n, st, T.limb_threads, T, seed, s, pk);
 }
 
 void launch_keygen_switch(const DevTables& T, u64 seed, u32 kind, const u64* s, u32 K, u64* ksk, cudaStream_t st) {
   Launch L(K_KEYGEN, st, 8.0 * 2 * K * (K + 1) * (1u << T.log_n));
-  static decltype(&k_keygen_switch<u64, 0>) const ks[6] = TCKS_K6(k_keygen_switch);
-  launch_limb(ks, T.narrow, K * (K + 1), 1, T.log_n, st, T.limb_threads, T, seed, kind, s, K, ksk);
+  launch_limb(K6_k_keygen_switch, T.narrow, K * (K + 1), 1, T.log_n, st, T.limb_threads, T, seed, kind, s, K, ksk);
 }
 
 void launch_encrypt(const DevTables& T, u64 seed, const u64* pk, const u64* pt, u32 ell, u64* out, cudaStream_t st) {
   Launch L(K_ENCRYPT, st, 8.0 * 5 * ell * (1u << T.log_n));
-  static decltype(&k_encrypt<u64, 0>) const ks[6] = TCKS_K6(k_encrypt);
-  launch_limb(ks, T.narrow, ell, 1, T.log_n, st, T.limb_threads, T, seed, pk, pt, ell, out);
+  launch_limb(K6_k_encrypt, T.narrow, ell, 1, T.log_n, st, T.limb_threads, T, seed, pk, pt, ell, out);
 }
 
 }  // namespace tcks

@@ -50,6 +50,10 @@ struct NttDescTable {
   u32 pad;
 };
 void launch_ntt_desc(const DevTables& T, bool inverse, const NttDescTable& tab, u32 total_jobs, cudaStream_t st);
+// Largest CTA size the limb kernels of each file accept (0 when the query fails).
+u32 limb_threads_cap_core(bool narrow, u32 log_c);
+u32 limb_threads_cap_sample(bool narrow, u32 log_c);
+u32 limb_threads_cap_fft(bool narrow, u32 log_c);
 void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_outer, u64* dst, u64 dst_outer,
                 u32 count, u32 mod_base, u32 per, cudaStream_t st);
 enum : u32 { OP_ADD = 0, OP_SUB = 1, OP_NEG = 2, OP_MUL_PLAIN = 3, OP_ADD_PLAIN = 4, OP_SUB_PLAIN = 5 };
@@ -112,6 +116,8 @@ struct VecmatPlan {
 // Stage 1 of a KsPlan alone (the P-limb inner product and its INTT into plan.top).
 void launch_ks_inner_p(const DevTables& T, u32 ell, const KsPlan& plan, cudaStream_t st);
 // The fused ModDown + multiply-accumulate over the plan's R rotations, chunk rotations per CTA.
+// CTAs (clusters above N = 2^14) of the fused vector x matrix kernel the GPU runs at once.
+u32 vecmat_slots(const DevTables& T);
 void launch_vecmat_acc(const DevTables& T, u32 ell, const VecmatPlan& plan, cudaStream_t st);
 // out [B][2][ell][N] = ct * diag[0] + sum of plan.chunks partials per request.
 void launch_vecmat_reduce(const DevTables& T, u32 ell, const VecmatPlan& plan, u64* out, cudaStream_t st);

@@ -5,15 +5,20 @@
 // cnn.cpp) or a vector x plain-matrix product (one stage). Requests are queued on submit and
 // admitted in arrival order while the device budget (resident keys and model plaintexts of every
 // lane, plus a per-request allowance for its live ciphertext and the stage scratch) and the in-flight
-// cap allow. Each step groups the admitted requests by (lane, stage), runs every group's stage as one
-// batched pass (up to max_batch requests per group), launching all lanes' work before waiting for
-// any of it, and advances each request one stage. A request that arrives while others are running
-// joins stage 0 at the next step. Results are bit-identical to the single-request path (every stage
-// is exact modular arithmetic and no kernel depends on the batch composition).
+// cap allow. Lanes run asynchronously on their contexts' streams: a step first collects the lanes
+// whose previous launch has completed (a CUDA event per lane), then, on every idle lane, groups its
+// admitted requests by stage and runs each group's stage as one batched pass (up to max_batch
+// requests per group), advancing each request one stage. When no lane could start new work the step
+// waits (bounded) for the first lane to finish. So a slow lane (a 4095-rotation vector x matrix
+// batch) does not hold back a fast one (a CNN stage), and a request that arrives while others are
+// running joins stage 0 at its lane's next launch. Results are bit-identical to the single-request
+// path (every stage is exact modular arithmetic and no kernel depends on the batch composition).
 #include <algorithm>
+#include <chrono>
 #include <deque>
 #include <map>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "context.h"
@@ -37,6 +42,8 @@ struct Lane {
   tcks_ctx* ctx;
   u32 stages;
   u64 req_bytes;  // allowance per in-flight request
+  cudaEvent_t ev;  // recorded after the lane's last launch
+  bool busy;       // a launch is in flight
 };
 
 struct Req {
@@ -45,6 +52,7 @@ struct Req {
   u32 stage;
   tcks_ct* ct;  // current state, owned
   u64 cost;
+  bool running;  // part of its lane's launch in flight
 };
 
 }  // namespace
@@ -63,7 +71,9 @@ struct tcks_server {
   std::vector<tcks_ctx*> ctxs;  // distinct contexts, counted once in `resident`
 };
 
-#define SRV_BEGIN try {
+#define SRV_BEGIN \
+  try {                 \
+    tcks::drop_stale_cuda_error();
 #define SRV_END                                                        \
   }                                                                    \
   catch (const tcks::Error& e) {                                       \
@@ -96,6 +106,9 @@ tcks_status tcks_server_create(uint64_t hbm_budget_bytes, uint32_t max_in_flight
 
 void tcks_server_free(tcks_server* s) {
   if (!s) return;
+  for (tcks_ctx* c : s->ctxs) cudaStreamSynchronize(c->stream);
+  for (Lane& L : s->lanes)
+    if (L.ev) cudaEventDestroy(L.ev);
   for (Req* r : s->queue) {
     free_ct(r->ct);
     delete r;
@@ -120,7 +133,7 @@ tcks_status tcks_server_add_cnn(tcks_server* s, const tcks_cnn* m, uint32_t* lan
   // live ciphertext plus a conservative share of the stage scratch (ModUp digits, rotated
   // partials, tensor products): 64 top-level ciphertexts
   const u64 req = (u64)65 * ct_words(c, cnn_stage_level(m, 0)) * 8;
-  s->lanes.push_back(Lane{true, m, nullptr, c, 5, req});
+  s->lanes.push_back(Lane{true, m, nullptr, c, 5, req, nullptr, false});
   *lane = (u32)s->lanes.size() - 1;
   SRV_END
 }
@@ -132,7 +145,7 @@ tcks_status tcks_server_add_vecmat(tcks_server* s, const tcks_matrix* M, uint32_
   add_context(s, c);
   s->resident += (u64)M->rows * M->level * c->N * 8;
   const u64 req = (u64)65 * ct_words(c, M->level) * 8;
-  s->lanes.push_back(Lane{false, nullptr, M, c, 1, req});
+  s->lanes.push_back(Lane{false, nullptr, M, c, 1, req, nullptr, false});
   *lane = (u32)s->lanes.size() - 1;
   SRV_END
 }
@@ -153,36 +166,53 @@ tcks_status tcks_server_submit(tcks_server* s, uint32_t lane, const tcks_ct* in,
   check_cuda(cudaMemcpyAsync(copy->d, in->d, ct_words(L.ctx, in->level) * 8, cudaMemcpyDeviceToDevice,
                              L.ctx->stream),
              "submit");
-  Req* r = new Req{s->next_id++, lane, 0, copy, L.req_bytes};
+  Req* r = new Req{s->next_id++, lane, 0, copy, L.req_bytes, false};
   s->queue.push_back(r);
   *id = r->id;
   SRV_END
 }
 
-// One scheduling step; *completed = requests finished in this step.
-tcks_status tcks_server_step(tcks_server* s, uint32_t* completed) {
-  SRV_BEGIN
-  if (!s) fail(TCKS_ERR_INVALID_ARG, "null server");
-  // admission in arrival order
-  while (!s->queue.empty() && s->active.size() < s->max_in_flight) {
-    Req* r = s->queue.front();
-    if (s->resident + s->in_use + r->cost > s->budget) break;
-    s->queue.pop_front();
-    s->in_use += r->cost;
-    s->active.push_back(r);
+// Collect the lanes whose launch has completed; their requests that passed the last stage finish.
+static u32 harvest(tcks_server* s) {
+  u32 fin = 0;
+  for (Lane& L : s->lanes) {
+    if (!L.busy) continue;
+    const cudaError_t q = cudaEventQuery(L.ev);
+    if (q == cudaErrorNotReady) continue;
+    check_cuda(q, "server lane");
+    L.busy = false;
   }
-  // group by (lane, stage), oldest first, at most max_batch per group
-  std::map<std::pair<u32, u32>, std::vector<Req*>> groups;
+  for (auto it = s->active.begin(); it != s->active.end();) {
+    Req* r = *it;
+    const Lane& L = s->lanes[r->lane];
+    if (r->running && !L.busy) r->running = false;
+    if (!r->running && r->stage == L.stages) {
+      s->in_use -= r->cost;
+      s->done[r->id] = r;
+      s->completed_ids.push_back(r->id);
+      it = s->active.erase(it);
+      ++fin;
+    } else {
+      ++it;
+    }
+  }
+  return fin;
+}
+
+// Launch every stage group of an idle lane; returns whether anything was launched.
+static bool launch_lane(tcks_server* s, u32 lane) {
+  Lane& L = s->lanes[lane];
+  std::map<u32, std::vector<Req*>> groups;  // by stage, oldest first
   for (Req* r : s->active) {
-    auto& g = groups[{r->lane, r->stage}];
+    if (r->lane != lane || r->running || r->stage == L.stages) continue;
+    auto& g = groups[r->stage];
     if (g.size() < s->max_batch) g.push_back(r);
   }
-  std::vector<Req*> advanced;
+  if (groups.empty()) return false;
+  tcks_ctx* c = L.ctx;
   for (auto& kv : groups) {
-    const Lane& L = s->lanes[kv.first.first];
-    const u32 stage = kv.first.second;
+    const u32 stage = kv.first;
     std::vector<Req*>& g = kv.second;
-    tcks_ctx* c = L.ctx;
     const u32 count = (u32)g.size();
     const u32 lin = g[0]->ct->level;
     const u32 lout = L.is_cnn ? cnn_stage_level(L.cnn, stage + 1) : lin - 1;
@@ -201,25 +231,51 @@ tcks_status tcks_server_step(tcks_server* s, uint32_t* completed) {
     for (u32 i = 0; i < count; ++i) {
       tcks_ct* nx = new_ct(c, lout, sc);
       check_cuda(cudaMemcpyAsync(nx->d, y.p + i * wout, wout * 8, cudaMemcpyDeviceToDevice, c->stream), "scatter");
-      free_ct(g[i]->ct);
+      free_ct(g[i]->ct);  // stream-ordered: released after the gather above has read it
       g[i]->ct = nx;
       g[i]->stage += 1;
-      advanced.push_back(g[i]);
+      g[i]->running = true;
     }
   }
-  for (tcks_ctx* c : s->ctxs) check_cuda(cudaStreamSynchronize(c->stream), "server step");
-  u32 fin = 0;
-  for (auto it = s->active.begin(); it != s->active.end();) {
-    Req* r = *it;
-    if (r->stage == s->lanes[r->lane].stages) {
-      s->in_use -= r->cost;
-      s->done[r->id] = r;
-      s->completed_ids.push_back(r->id);
-      it = s->active.erase(it);
-      ++fin;
-    } else {
-      ++it;
+  if (!L.ev) check_cuda(cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming), "lane event");
+  check_cuda(cudaEventRecord(L.ev, c->stream), "lane event");
+  L.busy = true;
+  return true;
+}
+
+// One scheduling step; *completed = requests finished in this step.
+tcks_status tcks_server_step(tcks_server* s, uint32_t* completed) {
+  SRV_BEGIN
+  if (!s) fail(TCKS_ERR_INVALID_ARG, "null server");
+  u32 fin = harvest(s);
+  // admission in arrival order
+  while (!s->queue.empty() && s->active.size() < s->max_in_flight) {
+    Req* r = s->queue.front();
+    if (s->resident + s->in_use + r->cost > s->budget) break;
+    s->queue.pop_front();
+    s->in_use += r->cost;
+    s->active.push_back(r);
+  }
+  bool launched = false;
+  for (u32 l = 0; l < s->lanes.size(); ++l)
+    if (!s->lanes[l].busy) launched |= launch_lane(s, l);
+  if (!launched) {
+    // nothing new could start: wait (bounded) until some lane finishes
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+      bool any_busy = false, any_done = false;
+      for (Lane& L : s->lanes) {
+        if (!L.busy) continue;
+        any_busy = true;
+        const cudaError_t q = cudaEventQuery(L.ev);
+        if (q != cudaErrorNotReady) any_done = true;
+      }
+      if (!any_busy || any_done) break;
+      if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(300))
+        fail(TCKS_ERR_TIMEOUT, "no server lane finished within 300 s");
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
+    fin += harvest(s);
   }
   if (completed) *completed = fin;
   SRV_END
