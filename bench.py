@@ -271,12 +271,12 @@ def run_gpu(args, world, rank, local):
             kinds = np.where(np.random.default_rng(9).uniform(size=len(arr)) < mix, "vm", "cnn")
             lat_s, kind_s, thr_s = serve_trace(tk, lanes, arr, kinds, args.batch)
             # the plain path saturates below the offered rate: run it on the start of the same trace
-            n_p = int(np.searchsorted(arr, args.plain_trace_seconds))
+            n_p = min(len(arr), args.plain_requests)
             lat_p, kind_p, thr_p = plain_trace(tk, lanes, arr[:n_p], kinds[:n_p])
             traces.append({"offered_rate": rate, "seconds": args.serve_seconds, "requests": len(arr),
                            "served": dict(summary(lat_s, kind_s, thr_s), max_batch_per_stage=args.batch,
                                           max_in_flight=1024, hbm_budget_gb=200),
-                           "plain": dict(summary(lat_p, kind_p, thr_p), trace_seconds=args.plain_trace_seconds)})
+                           "plain": dict(summary(lat_p, kind_p, thr_p), trace_requests=int(n_p))})
         serving = {"mix": {"cnn": 1.0 - mix, "vm": mix}, "vm_workload": C4_WORKLOAD if c4 else None,
                    "latency": "arrival -> result exported to the host", "traces": traces}
     if c4:
@@ -635,8 +635,8 @@ def main():
     ap.add_argument("--c4-batch", type=int, default=64)
     ap.add_argument("--c4-steps", type=int, default=3)
     ap.add_argument("--serve-mix", type=float, default=0.3, help="share of vector x matrix requests in the trace")
-    ap.add_argument("--plain-trace-seconds", type=float, default=0.25,
-                    help="arrivals of the trace's first seconds replayed through the plain path")
+    ap.add_argument("--plain-requests", type=int, default=300,
+                    help="requests at the start of each trace replayed through the plain path")
     args = ap.parse_args()
     if args.sweep:
         run_sweep(args)

@@ -93,9 +93,15 @@ extern "C" tcks_status tcks_autotune(tcks_ctx* c, const char* cache_path, uint32
         t = t < 32 ? 32 : (t > cap ? cap : t);
         if (std::find(cand.begin(), cand.end(), t) == cand.end()) cand.push_back(t);
       }
+      // timed work: batched transforms up to N = 2^13; above that the plain transforms run in two
+      // passes of fixed shape and the tuned size only reaches the fused kernels, so batched rescales
+      // (lift + transform + combine per limb) are timed instead
       const u32 limbs = 256, lv = c->L + 1;
-      DevBuf buf(c, (size_t)limbs * c->N);
+      DevBuf buf(c, (size_t)limbs * c->N), out(c, (size_t)limbs * c->N), top(c, (size_t)limbs * c->N);
       check_cuda(cudaMemsetAsync(buf.p, 0, (size_t)limbs * c->N * 8, c->stream), "tune buffer");
+      const u32 ell = c->L;
+      const bool fused = log_n > 13 && ell >= 2;
+      const u32 polys = fused ? std::max<u32>(1, limbs / ell) : 0;
       cudaEvent_t a, b;
       check_cuda(cudaEventCreate(&a), "event");
       check_cuda(cudaEventCreate(&b), "event");
@@ -106,8 +112,12 @@ extern "C" tcks_status tcks_autotune(tcks_ctx* c, const char* cache_path, uint32
         for (int rep = 0; rep < 2; ++rep) {  // warm-up, then timed
           cudaEventRecord(a, c->stream);
           for (int it2 = 0; it2 < 3; ++it2) {
-            launch_ntt(c->T, false, buf.p, (u64)lv * c->N, buf.p, (u64)lv * c->N, limbs, 0, lv, c->stream);
-            launch_ntt(c->T, true, buf.p, (u64)lv * c->N, buf.p, (u64)lv * c->N, limbs, 0, lv, c->stream);
+            if (fused) {
+              launch_rescale(c->T, buf.p, ell, polys, top.p, out.p, c->stream);
+            } else {
+              launch_ntt(c->T, false, buf.p, (u64)lv * c->N, buf.p, (u64)lv * c->N, limbs, 0, lv, c->stream);
+              launch_ntt(c->T, true, buf.p, (u64)lv * c->N, buf.p, (u64)lv * c->N, limbs, 0, lv, c->stream);
+            }
           }
           cudaEventRecord(b, c->stream);
         }

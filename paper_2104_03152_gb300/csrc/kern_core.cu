@@ -82,6 +82,155 @@ static void (*const kNttFwd[6])(DevTables, const u64*, u64, u64*, u64, u32, u32)
     k_ntt<false, u64, 0>, k_ntt<false, u64, 1>, k_ntt<false, u64, 2>,
     k_ntt<false, u32, 0>, k_ntt<false, u32, 1>, k_ntt<false, u32, 2>};
 
+// ------------------------------------------------------ NTT of N >= 2^14 in two passes ----
+// A limb of N = 2^(13 + k) elements is transformed in two passes over memory instead of one
+// cluster of 2^k CTAs: the first k forward stages pair elements 2^(13) apart and run on columns
+// {j + m 2^13 : m < 2^k} in registers; the other 13 stages run on 2^k independent 8192-element
+// slices in shared memory (three 64 KB CTAs per SM rather than one 128 KB CTA or a cluster). The
+// inverse runs the mirror order, the N^-1 scaling last. Every element meets the same butterflies
+// in the same order as in the one-pass transform, so results are identical. Both passes work in
+// place on the destination. The transform is integer-pipe bound, so the extra pass over HBM is
+// cheaper than the lost occupancy.
+constexpr u32 kSplitLogNs = 13;
+
+// Limb job -> (input, output, prime): the strided batch of launch_ntt ...
+struct NttJobsStrided {
+  const u64* src;
+  u64* dst;
+  u64 src_outer, dst_outer;
+  u32 mod_base, per;
+  __device__ __forceinline__ void locate(u32 job, u32 log_n, const u64*& in, u64*& out, u32& mod) const {
+    const u32 jo = job / per, ji = job % per;
+    mod = mod_base + ji;
+    in = src + jo * src_outer + ((u64)ji << log_n);
+    out = dst + jo * dst_outer + ((u64)ji << log_n);
+  }
+};
+// ... or a descriptor table (see k_ntt_desc).
+struct NttJobsTable {
+  NttDescTable tab;
+  __device__ __forceinline__ void locate(u32 job, u32 log_n, const u64*& in, u64*& out, u32& mod) const {
+    u32 lo = 0, hi = tab.n;
+    while (hi - lo > 1) {
+      const u32 mid = (lo + hi) >> 1;
+      if (tab.d[mid].first <= job)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    const NttDesc& d = tab.d[lo];
+    const u32 local = job - d.first;
+    mod = local % d.level;
+    in = d.src + ((u64)local << log_n);
+    out = d.dst + ((u64)local << log_n);
+  }
+};
+
+// Columns pass: forward stages 0..K-1 (src -> dst), or inverse stages log_n-K..log_n-1 plus N^-1
+// (dst -> dst). Item = (limb job, column j), grid-stride.
+template <bool INVERSE, typename W, int K, typename Jobs>
+__global__ void k_ntt_columns(DevTables T, const __grid_constant__ Jobs jobs, u32 n_jobs) {
+  const u32 log_n = T.log_n, log_cols = log_n - K;
+  const u64 items = (u64)n_jobs << log_cols;
+  for (u64 it = (u64)blockIdx.x * blockDim.x + threadIdx.x; it < items; it += (u64)gridDim.x * blockDim.x) {
+    const u32 job = (u32)(it >> log_cols), j = (u32)(it & ((1u << log_cols) - 1));
+    const u64* in;
+    u64* out;
+    u32 mod;
+    jobs.locate(job, log_n, in, out, mod);
+    const ModConst m = T.mods[mod];
+    const W q = (W)m.q;
+    W x[1 << K];
+    const u64* from = INVERSE ? out : in;
+#pragma unroll
+    for (int c = 0; c < (1 << K); ++c) x[c] = (W)from[j + ((u64)c << log_cols)];
+    if (INVERSE) {
+      inv_group<W, K>(x, log_n, log_cols, 0, Ar<W>::tw(T, mod, 2), Ar<W>::tw(T, mod, 3), q);
+#pragma unroll
+      for (int c = 0; c < (1 << K); ++c) out[j + ((u64)c << log_cols)] = Ar<W>::inv_out(x[c], m);
+    } else {
+      fwd_group<W, K>(x, 0, 0, Ar<W>::tw(T, mod, 0), Ar<W>::tw(T, mod, 1), q);
+#pragma unroll
+      for (int c = 0; c < (1 << K); ++c) out[j + ((u64)c << log_cols)] = (u64)x[c];
+    }
+  }
+}
+
+// Slices pass: CTA = slice `rank` of a limb job; forward stages k..log_n-1 (dst -> dst, canonical
+// out), or inverse stages 0..12 (src -> dst, unscaled).
+template <bool INVERSE, typename W, typename Jobs>
+__global__ void k_ntt_slices(DevTables T, const __grid_constant__ Jobs jobs, u32 log_k) {
+  TCKS_SMEM(W);
+  const u32 log_n = T.log_n, log_ns = log_n - log_k;
+  const u32 rank = blockIdx.x & ((1u << log_k) - 1), job = blockIdx.x >> log_k;
+  const u64* in;
+  u64* out;
+  u32 mod;
+  jobs.locate(job, log_n, in, out, mod);
+  const ModConst m = T.mods[mod];
+  const W q = (W)m.q;
+  const u32 ns = 1u << log_ns;
+  const u64 off = (u64)rank << log_ns;
+  const u64* from = (INVERSE ? in : out) + off;
+  u64* to = out + off;
+  for (u32 k = 2 * threadIdx.x; k < ns; k += 2 * blockDim.x) {
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(from + k);
+    s[sw(k)] = (W)v.x;
+    s[sw(k + 1)] = (W)v.y;
+  }
+  __syncthreads();
+  if (INVERSE) {
+    ntt_inv_local_rounds<W>(s, log_n, log_ns, rank, Ar<W>::tw(T, mod, 2), Ar<W>::tw(T, mod, 3), q);
+    for (u32 k = 2 * threadIdx.x; k < ns; k += 2 * blockDim.x)
+      *reinterpret_cast<ulonglong2*>(to + k) = make_ulonglong2(s[sw(k)], s[sw(k + 1)]);
+  } else {
+    ntt_fwd_local_rounds<W>(s, log_n, log_ns, rank, Ar<W>::tw(T, mod, 0), Ar<W>::tw(T, mod, 1), q);
+    for (u32 k = 2 * threadIdx.x; k < ns; k += 2 * blockDim.x)
+      *reinterpret_cast<ulonglong2*>(to + k) = make_ulonglong2(Ar<W>::fwd_out(s[sw(k)], m), Ar<W>::fwd_out(s[sw(k + 1)], m));
+  }
+}
+
+template <bool INVERSE, typename W, typename Jobs>
+static void launch_columns(const DevTables& T, const Jobs& jobs, u32 n_jobs, u32 k, cudaStream_t st) {
+  const u64 items = (u64)n_jobs << (T.log_n - k);
+  const u32 blocks = (u32)std::min<u64>((items + 255) / 256, 152ull * 16);
+  if (k == 1) k_ntt_columns<INVERSE, W, 1, Jobs><<<blocks, 256, 0, st>>>(T, jobs, n_jobs);
+  if (k == 2) k_ntt_columns<INVERSE, W, 2, Jobs><<<blocks, 256, 0, st>>>(T, jobs, n_jobs);
+  if (k == 3) k_ntt_columns<INVERSE, W, 3, Jobs><<<blocks, 256, 0, st>>>(T, jobs, n_jobs);
+}
+
+template <bool INVERSE, typename W, typename Jobs>
+static void launch_slices(const DevTables& T, const Jobs& jobs, u32 n_jobs, u32 k, cudaStream_t st) {
+  const size_t smem = sizeof(W) << kSplitLogNs;
+  const void* kern = (const void*)k_ntt_slices<INVERSE, W, Jobs>;
+  ensure_smem(kern, smem);
+  k_ntt_slices<INVERSE, W, Jobs><<<n_jobs << k, 256, smem, st>>>(T, jobs, k);
+}
+
+// The two-pass transform of n_jobs limbs; algorithmic bytes and butterflies go to the slices pass.
+template <typename Jobs>
+static void launch_ntt_split(const DevTables& T, bool inverse, const Jobs& jobs, u32 n_jobs, cudaStream_t st) {
+  const u32 k = T.log_n - kSplitLogNs;
+  const double n = (double)(1u << T.log_n);
+  const double cols_ops = n_jobs * 0.5 * n * k, slice_ops = n_jobs * 0.5 * n * kSplitLogNs;
+  const KernelId id = inverse ? K_NTT_INV : K_NTT_FWD;
+  if (!inverse) {
+    {
+      Launch L(id, st, 0.0, cols_ops);
+      if (T.narrow) launch_columns<false, u32>(T, jobs, n_jobs, k, st); else launch_columns<false, u64>(T, jobs, n_jobs, k, st);
+    }
+    Launch L(id, st, 16.0 * n * n_jobs, slice_ops);
+    if (T.narrow) launch_slices<false, u32>(T, jobs, n_jobs, k, st); else launch_slices<false, u64>(T, jobs, n_jobs, k, st);
+  } else {
+    {
+      Launch L(id, st, 16.0 * n * n_jobs, slice_ops);
+      if (T.narrow) launch_slices<true, u32>(T, jobs, n_jobs, k, st); else launch_slices<true, u64>(T, jobs, n_jobs, k, st);
+    }
+    Launch L(id, st, 0.0, cols_ops);
+    if (T.narrow) launch_columns<true, u32>(T, jobs, n_jobs, k, st); else launch_columns<true, u64>(T, jobs, n_jobs, k, st);
+  }
+}
+
 // ------------------------------------------------------- NTT over a descriptor table ----
 // One launch over several polynomial batches of the same N and chain but their own levels and
 // buffers: CTA job j belongs to the last descriptor whose first job is <= j, and is limb
@@ -130,6 +279,12 @@ static void (*const kNttDescFwd[6])(DevTables, NttDescTable) = {
 
 void launch_ntt_desc(const DevTables& T, bool inverse, const NttDescTable& tab, u32 total_jobs, cudaStream_t st) {
   if (!total_jobs || !tab.n) return;
+  if (T.log_n > kSplitLogNs) {
+    NttJobsTable jobs;
+    jobs.tab = tab;
+    launch_ntt_split(T, inverse, jobs, total_jobs, st);
+    return;
+  }
   Launch L(inverse ? K_NTT_INV : K_NTT_FWD, st, 16.0 * total_jobs * (1u << T.log_n), total_jobs * bfly_per_limb(T.log_n));
   if (inverse)
     launch_limb(kNttDescInv, T.narrow, total_jobs, 1, T.log_n, st, T.limb_threads, T, tab);
@@ -140,6 +295,11 @@ void launch_ntt_desc(const DevTables& T, bool inverse, const NttDescTable& tab, 
 void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_outer, u64* dst, u64 dst_outer, u32 count,
                 u32 mod_base, u32 per, cudaStream_t st) {
   if (!count) return;
+  if (T.log_n > kSplitLogNs) {
+    const NttJobsStrided jobs{src, dst, src_outer, dst_outer, mod_base, per};
+    launch_ntt_split(T, inverse, jobs, count, st);
+    return;
+  }
   Launch L(inverse ? K_NTT_INV : K_NTT_FWD, st, 16.0 * count * (1u << T.log_n), count * bfly_per_limb(T.log_n));
   if (inverse)
     launch_limb(kNttInv, T.narrow, count, 1, T.log_n, st, T.limb_threads, T, src, src_outer, dst, dst_outer, mod_base, per);
@@ -362,19 +522,21 @@ __device__ __forceinline__ u64 ks_inner(const u64* __restrict__ digits, u32 ell,
   return acc.get(m);
 }
 
-// Stage 1: u_b[P] = sum_j tau_g(D_j)[P] * key_j[b][P], then INTT mod P -> top. Limb job = component
-// b; entry y = request * R + rotation.
+// Stage 1: u_b[P] = sum_j tau_g(D_j)[P] * key_j[b][P], then INTT mod P -> top. Limb job = b * B +
+// request (requests fastest, so that the CTAs reading one key limb run together and share it through
+// L2), entry y = rotation.
 template <typename W, int LC>
 __global__ void k_ks_inner_p(DevTables T, u32 ell, const __grid_constant__ KsPlan plan) {
   TCKS_SMEM(W);
   const Slice sl = slice_of<LC>(T);
-  if (sl.y >= (u64)plan.B * plan.R) return;
+  if (sl.y >= plan.R) return;
   const u32 log_n = T.log_n;
   const u64 n = 1ull << log_n;
-  const u32 rq = (u32)(sl.y % plan.B), r = (u32)(sl.y / plan.B);  // rotation-major: a key's requests adjacent
+  const u32 rq = sl.job % plan.B, r = (u32)sl.y;
+  const u64 yy = (u64)r * plan.B + rq;  // entry of the P-limb scratch [R][B][2][N]
   const KsKey kk = plan.keys[r];
   const u64* digits = plan.digits + rq * plan.digits_b;
-  const u32 b = sl.job;
+  const u32 b = sl.job / plan.B;
   const ModConst mp = T.mods[T.L];
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
     const u32 g = sl.off + k;
@@ -383,27 +545,28 @@ __global__ void k_ks_inner_p(DevTables T, u32 ell, const __grid_constant__ KsPla
   }
   __syncthreads();
   ntt_inv_slice<W, LC>(s, T, T.L, sl.rank);
-  u64* top = plan.top + (sl.y * 2 + b) * n + sl.off;
+  u64* top = plan.top + (yy * 2 + b) * n + sl.off;
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) top[k] = Ar<W>::inv_out(s[sw(k)], mp);
 }
 
 // Stage 2 (ModDown): out_b[i] = (u_b[i] - NTT_i(bal_P(top_b) mod q_i)) * P^-1 + addend_b[i].
-// Limb job = b * ell + i.
+// Limb job = (b * ell + i) * B + request (requests fastest), entry y = rotation.
 template <typename W, int LC>
 __global__ void k_ks_moddown(DevTables T, u32 ell, const __grid_constant__ KsPlan plan) {
   TCKS_SMEM(W);
   const Slice sl = slice_of<LC>(T);
-  if (sl.y >= (u64)plan.B * plan.R) return;
+  if (sl.y >= plan.R) return;
   const u32 log_n = T.log_n;
   const u64 n = 1ull << log_n;
-  const u32 rq = (u32)(sl.y % plan.B), r = (u32)(sl.y / plan.B);  // rotation-major: a key's requests adjacent
+  const u32 rq = sl.job % plan.B, r = (u32)sl.y;
+  const u64 yy = (u64)r * plan.B + rq;
   const KsKey kk = plan.keys[r];
   const u64* digits = plan.digits + rq * plan.digits_b;
-  const u32 b = sl.job / ell, i = sl.job % ell;
+  const u32 bi = sl.job / plan.B, b = bi / ell, i = bi % ell;
   const ModConst mi = T.mods[i];
   const ModConst mp = T.mods[T.L];
   const PairConst pc = T.pairs[(u64)T.L * T.n_mods + i];
-  const u64* top = plan.top + (sl.y * 2 + b) * n + sl.off;
+  const u64* top = plan.top + (yy * 2 + b) * n + sl.off;
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)lift_balanced(top[k], mp.half, pc.qa_mod_b, mi);
   __syncthreads();
   ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
@@ -440,7 +603,7 @@ void launch_ks_inner_p(const DevTables& T, u32 ell, const KsPlan& plan, cudaStre
   double bi, bm;
   ks_plan_bytes(plan, ell, T.log_n, &bi, &bm);
   Launch L(K_KS_P, st, bi, 2.0 * jobs * ((double)ell * (1u << T.log_n) + bfly_per_limb(T.log_n)));
-  launch_limb(K6_k_ks_inner_p, T.narrow, 2, jobs, T.log_n, st, T.limb_threads, T, ell, plan);
+  launch_limb(K6_k_ks_inner_p, T.narrow, 2 * plan.B, plan.R, T.log_n, st, T.limb_threads, T, ell, plan);
 }
 
 static decltype(&k_ks_moddown<u64, 0>) const K6_k_ks_moddown[6] = TCKS_K6(k_ks_moddown);
@@ -453,7 +616,7 @@ void launch_keyswitch(const DevTables& T, u32 ell, const KsPlan& plan, cudaStrea
   ks_plan_bytes(plan, ell, T.log_n, &bi, &bm);
   Launch L(K_KS_MODDOWN, st, bm,
            2.0 * ell * jobs * ((ell + 1.0) * (1u << T.log_n) + bfly_per_limb(T.log_n)));
-  launch_limb(K6_k_ks_moddown, T.narrow, 2 * ell, jobs, T.log_n, st, T.limb_threads, T, ell, plan);
+  launch_limb(K6_k_ks_moddown, T.narrow, 2 * ell * plan.B, plan.R, T.log_n, st, T.limb_threads, T, ell, plan);
 }
 
 // ------------------------------------------------------------ launch-shape limits (autotune) ----

@@ -207,18 +207,14 @@ __device__ __forceinline__ void cross_stages(W* s, u32 log_n, u32 log_ns, u32 ra
   }
 }
 
-// Forward transform of the CTA's slice s[0, N/C) of a limb split over C = 2^LC CTAs (LC = 0: the
-// whole limb). Input canonical (or in [0, 4q) for W = u64); output in [0, 4q) (u64) or canonical
-// (u32); Ar<W>::fwd_out gives the canonical value. Ends with a barrier.
-template <typename W, int LC>
-__device__ __forceinline__ void ntt_fwd_slice(W* s, const DevTables& T, u32 mod, u32 rank) {
-  const u32 log_n = T.log_n, log_ns = log_n - LC;
-  const W q = (W)T.mods[mod].q;
-  const W* tw = Ar<W>::tw(T, mod, 0);
-  const W* tws = Ar<W>::tw(T, mod, 1);
-  if constexpr (LC > 0) cross_stages<W, LC, true>(s, log_n, log_ns, rank, tw, tws, q);
-  u32 st = LC;
-  const u32 left = log_n - st;
+// The stages a slice of 2^log_ns consecutive elements (slice `rank` of the limb) completes on its
+// own: forward stages log_n - log_ns .. log_n - 1 (the earlier ones pair elements of different
+// slices), or inverse stages 0 .. log_ns - 1. Each ends with a barrier.
+template <typename W>
+__device__ __forceinline__ void ntt_fwd_local_rounds(W* s, u32 log_n, u32 log_ns, u32 rank, const W* tw, const W* tws,
+                                                     W q) {
+  u32 st = log_n - log_ns;
+  const u32 left = log_ns;
   // remainder round first (radix-2 or radix-4), then radix-8 rounds
   if (left % 3 == 1) {
     fwd_round<W, 1>(s, log_n, log_ns, rank, st, tw, tws, q);
@@ -229,6 +225,27 @@ __device__ __forceinline__ void ntt_fwd_slice(W* s, const DevTables& T, u32 mod,
   }
   for (; st < log_n; st += 3) fwd_round<W, 3>(s, log_n, log_ns, rank, st, tw, tws, q);
 }
+template <typename W>
+__device__ __forceinline__ void ntt_inv_local_rounds(W* s, u32 log_n, u32 log_ns, u32 rank, const W* tw, const W* tws,
+                                                     W q) {
+  u32 st = 0;
+  for (; st + 3 <= log_ns; st += 3) inv_round<W, 3>(s, log_n, log_ns, rank, st, tw, tws, q);
+  if (log_ns - st == 2) inv_round<W, 2>(s, log_n, log_ns, rank, st, tw, tws, q);
+  if (log_ns - st == 1) inv_round<W, 1>(s, log_n, log_ns, rank, st, tw, tws, q);
+}
+
+// Forward transform of the CTA's slice s[0, N/C) of a limb split over C = 2^LC CTAs (LC = 0: the
+// whole limb). Input canonical (or in [0, 4q) for W = u64); output in [0, 4q) (u64) or canonical
+// (u32); Ar<W>::fwd_out gives the canonical value. Ends with a barrier.
+template <typename W, int LC>
+__device__ __forceinline__ void ntt_fwd_slice(W* s, const DevTables& T, u32 mod, u32 rank) {
+  const u32 log_n = T.log_n, log_ns = log_n - LC;
+  const W q = (W)T.mods[mod].q;
+  const W* tw = Ar<W>::tw(T, mod, 0);
+  const W* tws = Ar<W>::tw(T, mod, 1);
+  if constexpr (LC > 0) cross_stages<W, LC, true>(s, log_n, log_ns, rank, tw, tws, q);
+  ntt_fwd_local_rounds<W>(s, log_n, log_ns, rank, tw, tws, q);
+}
 
 // Inverse transform (without N^-1) of the CTA's slice; input canonical, output in [0, 2q) (u64)
 // or canonical (u32); Ar<W>::inv_out applies N^-1 and gives the canonical value.
@@ -238,10 +255,7 @@ __device__ __forceinline__ void ntt_inv_slice(W* s, const DevTables& T, u32 mod,
   const W q = (W)T.mods[mod].q;
   const W* tw = Ar<W>::tw(T, mod, 2);
   const W* tws = Ar<W>::tw(T, mod, 3);
-  u32 st = 0;
-  for (; st + 3 <= log_ns; st += 3) inv_round<W, 3>(s, log_n, log_ns, rank, st, tw, tws, q);
-  if (log_ns - st == 2) inv_round<W, 2>(s, log_n, log_ns, rank, st, tw, tws, q);
-  if (log_ns - st == 1) inv_round<W, 1>(s, log_n, log_ns, rank, st, tw, tws, q);
+  ntt_inv_local_rounds<W>(s, log_n, log_ns, rank, tw, tws, q);
   if constexpr (LC > 0) cross_stages<W, LC, false>(s, log_n, log_ns, rank, tw, tws, q);
 }
 

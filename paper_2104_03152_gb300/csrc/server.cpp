@@ -8,8 +8,10 @@
 // cap allow. Lanes run asynchronously on their contexts' streams: a step first collects the lanes
 // whose previous launch has completed (a CUDA event per lane), then, on every idle lane, groups its
 // admitted requests by stage and runs each group's stage as one batched pass (up to max_batch
-// requests per group), advancing each request one stage. When no lane could start new work the step
-// waits (bounded) for the first lane to finish. So a slow lane (a 4095-rotation vector x matrix
+// requests per group). Under load each request advances one stage per lane launch (stage-level
+// pipelining); at light load (no more waiting requests than max_batch) the launch carries them
+// through all remaining stages. When no lane could start new work the step waits (bounded) for the
+// first lane to finish. So a slow lane (a 4095-rotation vector x matrix
 // batch) does not hold back a fast one (a CNN stage), and a request that arrives while others are
 // running joins stage 0 at its lane's next launch. Results are bit-identical to the single-request
 // path (every stage is exact modular arithmetic and no kernel depends on the batch composition).
@@ -199,46 +201,66 @@ static u32 harvest(tcks_server* s) {
   return fin;
 }
 
-// Launch every stage group of an idle lane; returns whether anything was launched.
+// Run one stage for a group of requests of a lane (gather, batched stage, scatter); each request
+// advances one stage.
+static void run_group(tcks_server* s, Lane& L, u32 stage, std::vector<Req*>& g) {
+  tcks_ctx* c = L.ctx;
+  const u32 count = (u32)g.size();
+  const u32 lin = g[0]->ct->level;
+  const u32 lout = L.is_cnn ? cnn_stage_level(L.cnn, stage + 1) : lin - 1;
+  const u64 win = ct_words(c, lin), wout = ct_words(c, lout);
+  DevBuf x(c, (size_t)count * win), y(c, (size_t)count * wout);
+  for (u32 i = 0; i < count; ++i)
+    check_cuda(cudaMemcpyAsync(x.p + i * win, g[i]->ct->d, win * 8, cudaMemcpyDeviceToDevice, c->stream), "gather");
+  double sc;
+  if (L.is_cnn) {
+    cnn_stage(L.cnn, stage, x.p, count, y.p);
+    sc = cnn_out_scale(L.cnn, stage, g[0]->ct->scale);
+  } else {
+    op_vecmat(c, x.p, win, count, lin, L.M, y.p);
+    sc = g[0]->ct->scale * L.M->scale / (double)c->host.chain[lin - 1];
+  }
+  for (u32 i = 0; i < count; ++i) {
+    tcks_ct* nx = new_ct(c, lout, sc);
+    check_cuda(cudaMemcpyAsync(nx->d, y.p + i * wout, wout * 8, cudaMemcpyDeviceToDevice, c->stream), "scatter");
+    free_ct(g[i]->ct);  // stream-ordered: released after the gather above has read it
+    g[i]->ct = nx;
+    g[i]->stage += 1;
+    g[i]->running = true;
+  }
+  (void)s;
+}
+
+// Launch an idle lane's work; returns whether anything was launched. Under load (more waiting
+// requests than max_batch) every stage runs once for up to max_batch requests at that stage, so the
+// stages of different requests overlap (a pipeline); at light load the waiting requests are carried
+// through all their remaining stages in this launch, merging into one group as they reach the same
+// stage, so that a request does not wait one lane cycle per stage.
 static bool launch_lane(tcks_server* s, u32 lane) {
   Lane& L = s->lanes[lane];
-  std::map<u32, std::vector<Req*>> groups;  // by stage, oldest first
-  for (Req* r : s->active) {
-    if (r->lane != lane || r->running || r->stage == L.stages) continue;
-    auto& g = groups[r->stage];
-    if (g.size() < s->max_batch) g.push_back(r);
-  }
-  if (groups.empty()) return false;
-  tcks_ctx* c = L.ctx;
-  for (auto& kv : groups) {
-    const u32 stage = kv.first;
-    std::vector<Req*>& g = kv.second;
-    const u32 count = (u32)g.size();
-    const u32 lin = g[0]->ct->level;
-    const u32 lout = L.is_cnn ? cnn_stage_level(L.cnn, stage + 1) : lin - 1;
-    const u64 win = ct_words(c, lin), wout = ct_words(c, lout);
-    DevBuf x(c, (size_t)count * win), y(c, (size_t)count * wout);
-    for (u32 i = 0; i < count; ++i)
-      check_cuda(cudaMemcpyAsync(x.p + i * win, g[i]->ct->d, win * 8, cudaMemcpyDeviceToDevice, c->stream), "gather");
-    double sc;
-    if (L.is_cnn) {
-      cnn_stage(L.cnn, stage, x.p, count, y.p);
-      sc = cnn_out_scale(L.cnn, stage, g[0]->ct->scale);
-    } else {
-      op_vecmat(c, x.p, win, count, lin, L.M, y.p);
-      sc = g[0]->ct->scale * L.M->scale / (double)c->host.chain[lin - 1];
+  std::vector<Req*> ready;
+  for (Req* r : s->active)
+    if (r->lane == lane && !r->running && r->stage < L.stages) ready.push_back(r);
+  if (ready.empty()) return false;
+  if (ready.size() <= s->max_batch) {
+    u32 first = L.stages;
+    for (Req* r : ready) first = std::min(first, r->stage);
+    for (u32 stage = first; stage < L.stages; ++stage) {
+      std::vector<Req*> g;
+      for (Req* r : ready)
+        if (r->stage == stage) g.push_back(r);  // includes requests advanced from earlier stages here
+      if (!g.empty()) run_group(s, L, stage, g);
     }
-    for (u32 i = 0; i < count; ++i) {
-      tcks_ct* nx = new_ct(c, lout, sc);
-      check_cuda(cudaMemcpyAsync(nx->d, y.p + i * wout, wout * 8, cudaMemcpyDeviceToDevice, c->stream), "scatter");
-      free_ct(g[i]->ct);  // stream-ordered: released after the gather above has read it
-      g[i]->ct = nx;
-      g[i]->stage += 1;
-      g[i]->running = true;
+  } else {
+    std::map<u32, std::vector<Req*>> groups;  // by stage, oldest first
+    for (Req* r : ready) {
+      auto& g = groups[r->stage];
+      if (g.size() < s->max_batch) g.push_back(r);
     }
+    for (auto& kv : groups) run_group(s, L, kv.first, kv.second);
   }
   if (!L.ev) check_cuda(cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming), "lane event");
-  check_cuda(cudaEventRecord(L.ev, c->stream), "lane event");
+  check_cuda(cudaEventRecord(L.ev, L.ctx->stream), "lane event");
   L.busy = true;
   return true;
 }
