@@ -66,6 +66,8 @@ def lib():
         "orc_tensor": (None, [vp, _u64p, _u64p, u32, _u64p]),
         "orc_rescale": (None, [vp, _u64p, u32, _u64p]),
         "orc_modup": (None, [vp, _u64p, u32, _u64p]),
+        "orc_encode_ext": (i32, [vp, _dblp, u32, ctypes.c_double, u32, _u64p]),
+        "orc_vecmat_dh": (None, [vp, _u64p, _u64p, u32, u32, _u64p, ctypes.POINTER(_u64p), _u32p, _u32p, _u64p]),
         "orc_keyswitch_digits": (None, [vp, _u64p, u32, _u64p, u32, u32, _u64p]),
         "orc_keyswitch": (None, [vp, _u64p, u32, _u64p, u32, _u64p]),
         "orc_relinearize": (None, [vp, _u64p, u32, _u64p, u32, _u64p]),
@@ -465,6 +467,20 @@ class OracleCKKS:
     def encode_matrix(self, M: np.ndarray, level: int) -> list[Pt]:
         return [self.encode(d, level=level) for d in self.matrix_diagonals(np.asarray(M, dtype=np.float64))]
 
+    def encode_ext(self, z, level: int, scale: float | None = None) -> np.ndarray:
+        """Encode (O9) over the extended basis: [level+1][N], limbs q_0..q_{level-1} then P."""
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        scale = self.scale if scale is None else float(scale)
+        out = np.zeros((level + 1, self.N), dtype=np.uint64)
+        st = lib().orc_encode_ext(self._ctx, P(z), len(z), scale, level, P(out))
+        if st:
+            raise ValueError(f"encode_ext failed ({st})")
+        return out
+
+    def encode_matrix_ext(self, M: np.ndarray, level: int) -> np.ndarray:
+        """The diagonals over the extended basis: [n][level+1][N]."""
+        return np.stack([self.encode_ext(d, level) for d in self.matrix_diagonals(np.asarray(M, dtype=np.float64))])
+
     def vecmat_steps(self, n: int) -> list[int]:
         steps = self.replicate_steps(n) if n < self.slots else []
         return steps + list(range(1, n))
@@ -485,6 +501,28 @@ class OracleCKKS:
             t = self.mul_plain(r, diags[k])
             acc = t if acc is None else self.add(acc, t)
         return self.rescale(acc)
+
+    def vecmat_dh(self, ct: Ct, diags_ext: np.ndarray, n: int, m: int, scale: float | None = None) -> Ct:
+        """The same product with the ModDown taken once after the sum over rotations (double
+        hoisting): replicate, ModUp(c1) once, then orc_vecmat_dh (steps 1-3 there), then rescale.
+        diags_ext [n][level+1][N] at the ciphertext's level; `scale` is the diagonals' scale."""
+        level = ct.level
+        if diags_ext.shape != (n, level + 1, self.N) or m > n:
+            raise ValueError("bad matrix shape")
+        if n < self.slots:
+            for st in self.replicate_steps(n):
+                ct = self.add(ct, self.rotate(ct, st))
+        digits = self.modup(ct)
+        keys = [self._key(k) for k in range(1, n)]
+        key_arrs = [np.ascontiguousarray(k.data) for k in keys]
+        ptrs = (_u64p * max(1, len(keys)))(*[P(a) for a in key_arrs])
+        lv = np.array([k.level for k in keys] or [0], dtype=np.uint32)
+        ge = np.array([self.galois_elt(k) for k in range(1, n)] or [1], dtype=np.uint32)
+        out = np.zeros((2, level, self.N), dtype=np.uint64)
+        lib().orc_vecmat_dh(self._ctx, P(np.ascontiguousarray(ct.data)), P(digits), level, n,
+                            P(np.ascontiguousarray(diags_ext)), ptrs, P(lv), P(ge), P(out))
+        d_scale = self.scale if scale is None else float(scale)
+        return self.rescale(Ct(out, level, ct.scale * d_scale))
 
     @staticmethod
     def im2col(img: np.ndarray, kh: int, kw: int, stride: int, slots: int):

@@ -518,12 +518,10 @@ void orc_keygen_galois(const OrcCtx* c, u64 seed, const u64* s, u32 g, u32 key_l
 
 // Inverse canonical embedding of n_in real slot values (zero-padded to N/2):
 //   m_i = (2/N) * sum_j z_j * cos(pi * (5^j * i mod 2N) / N),   the real part of z_j * zeta^(-5^j i)
-// then p_i = round-half-away(scale * m_i), reduced into limbs q_0..q_{level-1} and NTT'd.
-// pre (optional, N doubles) receives scale * m_i before rounding. Returns 0, -1 on bad size,
-// -2 when some |scale * m_i| >= 2^62.
-int orc_encode(const OrcCtx* c, const double* z, u32 n_in, double scale, u32 level, double* pre, u64* pt) {
+// then p_i = round-half-away(scale * m_i). pre (optional, N doubles) receives scale * m_i before
+// rounding. Returns 0, or -2 when some |scale * m_i| >= 2^62.
+static int encode_coeffs(const OrcCtx* c, const double* z, u32 n_in, double scale, double* pre, int64_t* p) {
   const u64 n = c->n, m = 2 * n, slots = n / 2;
-  if (n_in > slots || level < 1 || level > c->L) return -1;
   std::vector<double> cosv(m);
   for (u64 k = 0; k < m; ++k) cosv[k] = std::cos(M_PI * (double)k / (double)n);
   std::vector<u64> e(slots);
@@ -532,7 +530,6 @@ int orc_encode(const OrcCtx* c, const double* z, u32 n_in, double scale, u32 lev
     e[j] = g;
     g = (g * 5) % m;
   }
-  std::vector<int64_t> p(n);
   int status = 0;
 #pragma omp parallel for schedule(static)
   for (int64_t ii = 0; ii < (int64_t)n; ++ii) {
@@ -550,8 +547,31 @@ int orc_encode(const OrcCtx* c, const double* z, u32 n_in, double scale, u32 lev
       p[i] = (int64_t)std::llround(x);
     }
   }
+  return status;
+}
+
+// Encode (O9): the coefficients above reduced into limbs q_0..q_{level-1} and NTT'd. Returns 0, -1
+// on bad size, -2 on overflow.
+int orc_encode(const OrcCtx* c, const double* z, u32 n_in, double scale, u32 level, double* pre, u64* pt) {
+  const u64 n = c->n;
+  if (n_in > n / 2 || level < 1 || level > c->L) return -1;
+  std::vector<int64_t> p(n);
+  const int status = encode_coeffs(c, z, n_in, scale, pre, p.data());
   if (status) return status;
   for (u32 l = 0; l < level; ++l) signed_to_ntt(c, p.data(), l, limb(pt, n, l));
+  return 0;
+}
+
+// The same plaintext over the extended basis: limbs q_0..q_{level-1}, then the special prime P
+// (limb `level`) -- the same integer polynomial, as the double-hoisted product needs.
+int orc_encode_ext(const OrcCtx* c, const double* z, u32 n_in, double scale, u32 level, u64* pt) {
+  const u64 n = c->n;
+  if (n_in > n / 2 || level < 1 || level > c->L) return -1;
+  std::vector<int64_t> p(n);
+  const int status = encode_coeffs(c, z, n_in, scale, nullptr, p.data());
+  if (status) return status;
+  for (u32 l = 0; l < level; ++l) signed_to_ntt(c, p.data(), l, limb(pt, n, l));
+  signed_to_ntt(c, p.data(), c->L, limb(pt, n, level));
   return 0;
 }
 
@@ -820,6 +840,74 @@ void orc_rotate_from_digits(const OrcCtx* c, const u64* ct, const u64* digits, u
   orc_automorphism_ntt(c, ct, level, g, c0g.data());
   orc_add(c, c0g.data(), ks.data(), level, 1, out);
   std::memcpy(out + (u64)level * n, ks.data() + (u64)level * n, sizeof(u64) * level * n);
+}
+
+// Vector x plain matrix by the diagonal method with the ModDown taken once, after the sum over
+// rotations ("double hoisting"; the rotation count and the hoisted decomposition are those of the
+// single-hoisted product, only the place of the division by P moves). Inputs: ct [2][level][N] (the
+// replicated input vector), digits = ModUp(c1) [level][level+1][N], the diagonals over the extended
+// basis diag_ext [rows][level+1][N] (the same integer polynomial d_k modulo q_0..q_{level-1} and P),
+// and for k = 1..rows-1 the Galois key of rotation k (keys[k-1], level key_levels[k-1], element
+// g_elts[k-1]). Steps:
+//   1. U_b[i] = sum_{k>=1} (sum_j tau_k(D_j)[i] * gk^(k)_j[b][i]) * d_k[i]   for slots i < level and P;
+//   2. A_0[i] = c0[i] d_0[i] + sum_{k>=1} tau_k(c0)[i] d_k[i],  A_1[i] = c1[i] d_0[i]   (i < level);
+//   3. out_b[i] = A_b[i] + (U_b[i] - (bal_P(U_b[P]) mod q_i)) * P^-1 mod q_i.
+// The caller rescales. out [2][level][N].
+void orc_vecmat_dh(const OrcCtx* c, const u64* ct, const u64* digits, u32 level, u32 rows, const u64* diag_ext,
+                   const u64* const* keys, const u32* key_levels, const u32* g_elts, u64* out) {
+  const u64 n = c->n;
+  const u32 L = c->L, slots = level + 1;
+  const u64 P = c->q[L];
+  std::vector<u64> U((u64)2 * slots * n, 0), A((u64)2 * level * n);
+  // step 2, the k = 0 term
+  for (u32 b = 0; b < 2; ++b)
+    for (u32 i = 0; i < level; ++i)
+      for (u64 e = 0; e < n; ++e)
+        A[((u64)b * level + i) * n + e] =
+            mulm(ct[((u64)b * level + i) * n + e], diag_ext[(u64)i * n + e], c->q[i]);
+  for (u32 k = 1; k < rows; ++k) {
+    const std::vector<u32> src = automorphism_index(c, g_elts[k - 1]);
+    const u64* gk = keys[k - 1];
+    const u32 K = key_levels[k - 1];
+    const u64* dk = diag_ext + (u64)k * slots * n;
+    // step 1
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int b = 0; b < 2; ++b)
+      for (int ii = 0; ii < (int)slots; ++ii) {
+        const u32 i = (u32)ii;
+        const u32 mod_idx = i < level ? i : L;
+        const u32 key_slot = i < level ? i : K;
+        const u64 q = c->q[mod_idx];
+        u64* acc = U.data() + ((u64)b * slots + i) * n;
+        for (u64 e = 0; e < n; ++e) {
+          u64 u = 0;
+          for (u32 j = 0; j < level; ++j)
+            u = addm(u, mulm(digits[((u64)j * slots + i) * n + src[e]],
+                             gk[(((u64)j * 2 + (u64)b) * (K + 1) + key_slot) * n + e], q), q);
+          acc[e] = addm(acc[e], mulm(u, dk[(u64)i * n + e], q), q);
+        }
+      }
+    // step 2
+    for (u32 i = 0; i < level; ++i)
+      for (u64 e = 0; e < n; ++e)
+        A[(u64)i * n + e] = addm(A[(u64)i * n + e], mulm(ct[(u64)i * n + src[e]], dk[(u64)i * n + e], c->q[i]), c->q[i]);
+  }
+  // step 3
+  for (u32 b = 0; b < 2; ++b) {
+    std::vector<u64> top(U.data() + ((u64)b * slots + level) * n, U.data() + ((u64)b * slots + level + 1) * n);
+    intt_mod(c, top.data(), L);
+    for (u32 i = 0; i < level; ++i) {
+      const u64 q = c->q[i];
+      std::vector<u64> t(n);
+      for (u64 e = 0; e < n; ++e) t[e] = from_signed(balanced(top[e], P), q);
+      ntt_mod(c, t.data(), i);
+      const u64 pinv = invm(P % q, q);
+      const u64* ui = U.data() + ((u64)b * slots + i) * n;
+      const u64* ai = A.data() + ((u64)b * level + i) * n;
+      u64* dst = out + ((u64)b * level + i) * n;
+      for (u64 e = 0; e < n; ++e) dst[e] = addm(ai[e], mulm(subm(ui[e], t[e], q), pinv, q), q);
+    }
+  }
 }
 
 int orc_max_threads(void) {

@@ -325,3 +325,85 @@ def test_im2col_layout_and_delta_conv():
     ref2 = np.array([np.sum(img[3 * (w // 8):3 * (w // 8) + 7, 3 * (w % 8):3 * (w % 8) + 7] * ker2.reshape(7, 7))
                      for w in range(64)])
     assert np.max(np.abs(out2[:64] - ref2)) < 1e-3
+
+
+# ------------------------------------------------------------ double-hoisted vector x matrix ----
+
+def _vecmat_dh_raw(o, ct, digits, diags_ext, rows):
+    """orc_vecmat_dh before the rescale (steps 1-3)."""
+    keys = [o._key(k) for k in range(1, rows)]
+    arrs = [np.ascontiguousarray(k.data) for k in keys]
+    ptrs = (oracle.ckks._u64p * len(arrs))(*[a.ctypes.data_as(oracle.ckks._u64p) for a in arrs])
+    lv = np.array([k.level for k in keys], dtype=np.uint32)
+    ge = np.array([o.galois_elt(k) for k in range(1, rows)], dtype=np.uint32)
+    out = np.zeros((2, ct.level, o.N), dtype=np.uint64)
+    P = lambda a: a.ctypes.data_as({np.dtype(np.uint64): oracle.ckks._u64p, np.dtype(np.uint32): oracle.ckks._u32p}[a.dtype])
+    oracle.lib().orc_vecmat_dh(o._ctx, P(np.ascontiguousarray(ct.data)), P(np.ascontiguousarray(digits)), ct.level,
+                               rows, P(np.ascontiguousarray(diags_ext)), ptrs, P(lv), P(ge), P(out))
+    return out
+
+
+def test_vecmat_dh_equals_bigint_definition(tiny):
+    """The double-hoisted product against its big-integer definition on a tiny ring:
+    out_0 = c0 d_0 + sum_k tau_k(c0) d_k + round(U_0 / P),  out_1 = c1 d_0 + round(U_1 / P),
+    U_b = sum_k u_b(tau_k(c1), gk_k) d_k over Q P, with u_b the key-switch inner product before the
+    division by P (TinyCKKS.keyswitch_u, pinned by the relinearization test above)."""
+    o, t = tiny
+    rows, lvl = 4, 3
+    o.gen_galois_keys([1, 2, 3])
+    ct = _rand_ct(o, lvl, 31)
+    idx, idx_ext = list(range(lvl)), t.mods(lvl, with_p=True)
+    Q = math.prod(o.q[:lvl])
+    QP = Q * o.q[-1]
+    rng = np.random.default_rng(5)
+    d_int = [[int(x) for x in rng.integers(-200, 201, size=o.N)] for _ in range(rows)]
+    diags_ext = np.array([t.from_int(d, idx_ext) for d in d_int], dtype=np.uint64)
+    got = _vecmat_dh_raw(o, ct, o.modup(ct), diags_ext, rows)
+    from tiny_ckks import negacyclic_mul
+    C = [t.to_int(ct.data[p], idx) for p in range(2)]
+    A0 = negacyclic_mul(C[0], [x % Q for x in d_int[0]], Q)
+    A1 = negacyclic_mul(C[1], [x % Q for x in d_int[0]], Q)
+    U = [[0] * o.N, [0] * o.N]
+    for k in range(1, rows):
+        g = o.galois_elt(k)
+        c0g = t.automorphism(C[0], g, Q)
+        c1g = t.automorphism(C[1], g, Q)
+        A0 = [(a + b) % Q for a, b in zip(A0, negacyclic_mul(c0g, [x % Q for x in d_int[k]], Q))]
+        u = t.keyswitch_u(c1g, lvl, o.galois[k].data, o.galois[k].level)
+        for b in range(2):
+            U[b] = [(a + x) % QP for a, x in zip(U[b], negacyclic_mul(u[b], [x % QP for x in d_int[k]], QP))]
+    ref0 = [(a + t.round_div(x, o.q[-1])) % Q for a, x in zip(A0, U[0])]
+    ref1 = [(a + t.round_div(x, o.q[-1])) % Q for a, x in zip(A1, U[1])]
+    assert t.to_int(got[0], idx) == ref0
+    assert t.to_int(got[1], idx) == ref1
+
+
+def test_encode_ext_limb_is_the_same_integer_polynomial(c1):
+    """The P limb of an extended encoding is the NTT mod P of the integer coefficients the data limbs
+    carry (recovered by the pinned CRT composition)."""
+    o = c1
+    z = inputs.uniform_slots(o.slots, 3)
+    ext = o.encode_ext(z, 2)
+    base = o.encode(z, level=2)
+    assert np.array_equal(ext[:2], base.data)
+    coef = o.crt_compose(o.intt_limbs(base.data, 2), 2)
+    Pq = o.q[-1]
+    ref = oracle.ntt(np.array([int(c) % Pq for c in coef], dtype=np.uint64), Pq, oracle.min_psi(Pq, o.log_n))
+    assert np.array_equal(ext[2], ref)
+
+
+def test_vecmat_dh_decrypts_to_product_and_tracks_single_hoisting():
+    """decrypt(vecmat_dh(Enc(v))) = v M within the noise bound, and within a much smaller distance of
+    the single-hoisted product (the two differ only in where the division by P is rounded)."""
+    o = OracleCKKS(12, [55, 40, 40, 56], 2.0 ** 40).keygen()
+    n, m = 16, 8
+    o.gen_galois_keys(o.vecmat_steps(n))
+    v = np.zeros(o.slots)
+    v[:n] = inputs.uniform_slots(n, 7)
+    ct = o.encrypt_values(v, 41)
+    M = inputs.random_matrix(n, m, 8, 0.5)
+    dh = o.decrypt_values(o.vecmat_dh(ct, o.encode_matrix_ext(M, ct.level), n, m))
+    sh = o.decrypt_values(o.vecmat(ct, o.encode_matrix(M, ct.level), n, m))
+    assert np.max(np.abs(dh[:m] - v[:n] @ M)) < 1e-6
+    assert np.max(np.abs(dh[m:])) < 1e-6
+    assert np.max(np.abs(dh - sh)) < 1e-7

@@ -121,9 +121,8 @@ class TinyCKKS:
                 out[e - n] = (-c) % mod
         return out
 
-    def keyswitch(self, x: list[int], level: int, key, key_level: int) -> tuple[list[int], list[int]]:
-        """x: coefficients mod Q_level. key: [K][2][K+1][N] NTT-form limbs.
-        u = sum_j bal_{q_j}(x) * ksk_j over Q_level * P, out = round(u / P) mod Q_level."""
+    def keyswitch_u(self, x: list[int], level: int, key, key_level: int) -> list[list[int]]:
+        """u_b = sum_j bal_{q_j}(x) * ksk_j over Q_level * P (before the division by P)."""
         Q = math.prod(self.primes[:level])
         QP = Q * self.P
         key_rows = list(range(level)) + [key_level]
@@ -136,6 +135,13 @@ class TinyCKKS:
                 k = self.to_int([key[j][b][r] for r in key_rows], idx)
                 prod = negacyclic_mul([c % QP for c in d], k, QP)
                 u[b] = [(s + t) % QP for s, t in zip(u[b], prod)]
+        return u
+
+    def keyswitch(self, x: list[int], level: int, key, key_level: int) -> tuple[list[int], list[int]]:
+        """x: coefficients mod Q_level. key: [K][2][K+1][N] NTT-form limbs.
+        u = sum_j bal_{q_j}(x) * ksk_j over Q_level * P, out = round(u / P) mod Q_level."""
+        Q = math.prod(self.primes[:level])
+        u = self.keyswitch_u(x, level, key, key_level)
         return tuple([self.round_div(c, self.P) % Q for c in u[b]] for b in range(2))
 
     def rescale(self, c: list[int], level: int) -> list[int]:
