@@ -162,13 +162,14 @@ def source_digest() -> str:
 
 
 # ---------------------------------------------------------------------------------- GPU arm --
-def gpu_setup(torch, batch):
+def gpu_setup(torch, batch, double_hoist):
     import paper_2104_03152_gb300 as tk
     from paper_2104_03152_gb300 import inputs
 
     tk.lib(build_if_missing=True)
     stream = torch.cuda.Stream()
-    ctx = tk.Context(tk.Params(LOG_N, BITS, SCALE), seed=inputs.SEED_KEYS, stream=stream.cuda_stream)
+    flags = tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | (tk.TCKS_DOUBLE_HOIST if double_hoist else 0)
+    ctx = tk.Context(tk.Params(LOG_N, BITS, SCALE), seed=inputs.SEED_KEYS, flags=flags, stream=stream.cuda_stream)
     w = inputs.cnn_weights(SEED_W)
     model = tk.CNN(ctx, w["conv_w"], w["conv_b"], w["fc1_w"], w["fc1_b"], w["fc2_w"], w["fc2_b"], windows=64)
     model.gen_keys()
@@ -196,7 +197,7 @@ def timed(torch, stream, fn, steps):
 def run_gpu(args, world, rank, local):
     torch = dist_init(world, local)
     B = args.batch
-    tk, ctx, model, cts, stream, imgs, w = gpu_setup(torch, B)
+    tk, ctx, model, cts, stream, imgs, w = gpu_setup(torch, B, args.double_hoist)
     # correctness guard: the decrypted logits of every request must match the FP64 network, and the
     # batched outputs must equal the single-request path bit for bit
     outs = model.forward_batch(cts)
@@ -249,6 +250,16 @@ def run_gpu(args, world, rank, local):
             tk.check(tk.lib().tcks_ct_export(co.h, tk._p(host_out[i]), out_words))
     torch.cuda.synchronize()
     e2e_s = reduce_max(world, time.perf_counter() - t0)
+    # the same batched step with one ModDown per rotation (the schedule bit-identical to rotating
+    # each diagonal's ciphertext separately), for comparison
+    single = None
+    if args.double_hoist:
+        ctx.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE)
+        model.forward_batch(cts)
+        t_single, tot_single = timed(torch, stream, lambda: model.forward_batch(cts), 3)
+        single = {"value": B * 3 / (tot_single / 1e3), "unit": "inferences/s", "ms_per_step": tot_single / 3,
+                  "schedule": "one ModDown per rotation"}
+        ctx.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | tk.TCKS_DOUBLE_HOIST)
     c4 = run_c4(torch, tk, args) if args.c4 else None
     serving = None
     if args.serve_seconds > 0:
@@ -285,7 +296,7 @@ def run_gpu(args, world, rank, local):
     word = 32 if max(ctx.primes) < 2 ** 31 else 64
     bfly_peak = tk.calibrate_butterflies(word)
     primitives = primitives_summary(torch, tk) if args.primitives else None
-    return dict(c4=c4, primitives=primitives, bfly_peak=bfly_peak, word=word, serving=serving, total_ms=total_ms, per_step=per_step, prof=prof, launches=launches, clocks=clk, e2e_s=e2e_s,
+    return dict(single=single, c4=c4, primitives=primitives, bfly_peak=bfly_peak, word=word, serving=serving, total_ms=total_ms, per_step=per_step, prof=prof, launches=launches, clocks=clk, e2e_s=e2e_s,
                 e2e_steps=e2e_steps, h2d=host_in.nbytes, d2h=host_out.nbytes, max_err=max_err,
                 plain_ms=plain_total / plain_steps, plain_times=plain_times)
 
@@ -369,7 +380,8 @@ def run_c4(torch, tk, args):
     from paper_2104_03152_gb300 import inputs
     t0 = time.perf_counter()
     st = torch.cuda.Stream()
-    ctx = tk.Context(tk.Params(14, [60, 40, 40, 60], 2.0 ** 40), seed=inputs.SEED_KEYS, flags=tk.TCKS_AUTO_RELIN,
+    flags = tk.TCKS_AUTO_RELIN | (tk.TCKS_DOUBLE_HOIST if args.double_hoist else 0)
+    ctx = tk.Context(tk.Params(14, [60, 40, 40, 60], 2.0 ** 40), seed=inputs.SEED_KEYS, flags=flags,
                      stream=st.cuda_stream)
     ctx._torch_stream = st
     ctx.gen_galois_keys([ctx.slots - C4_ROWS] + list(range(1, C4_ROWS)))
@@ -392,6 +404,13 @@ def run_c4(torch, tk, args):
     tk.profile_stop()
     prof = tk.profile_read(with_ops=True)
     peak64 = tk.calibrate_butterflies(64)
+    single = None
+    if args.double_hoist:
+        ctx.set_flags(tk.TCKS_AUTO_RELIN)
+        mat.vecmat_batch(cts)
+        _, tot_s = timed(torch, st, lambda: mat.vecmat_batch(cts), 1)
+        single = {"value": B / (tot_s / 1e3), "unit": "vectors/s", "schedule": "one ModDown per rotation"}
+        ctx.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_DOUBLE_HOIST)
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "gbs": round(v[2] / (v[1] / 1e3) / 1e9, 1),
                    "gbfly_s": round(v[3] / (v[1] / 1e3) / 1e9, 1),
                    "alu_frac": round(v[3] / (v[1] / 1e3) / peak64, 4)}
@@ -400,6 +419,8 @@ def run_c4(torch, tk, args):
             "ms_per_batch": total / args.c4_steps, "steps": args.c4_steps, "setup_s": setup_s,
             "galois_keys": C4_ROWS, "key_bytes": ctx.key_bytes(),
             "max_abs_err_vs_fp64": err, "kernels": kernels, "alu_peak_bfly64_per_s": peak64,
+            "schedule": "ModDown once after the rotation sum" if args.double_hoist else "one ModDown per rotation",
+            "single_hoisted": single,
             "ctx": ctx, "mat": mat, "cts": cts}
 
 
@@ -631,6 +652,8 @@ def main():
     ap.add_argument("--sweep-ops", default=",".join(SWEEP_OPS), help="ops of the sweep")
     ap.add_argument("--sweep-mixed", type=int, default=1, help="also run the mixed (N, L) batches")
     ap.add_argument("--primitives", type=int, default=1, help="add the NTT / key-switch rates at N=2^16, L=32")
+    ap.add_argument("--double-hoist", type=int, default=1,
+                    help="vector x matrix products take the ModDown once after the rotation sum (1) or per rotation (0)")
     ap.add_argument("--c4", type=int, default=1, help="time the 4096x256 vector x matrix workload (64 vectors)")
     ap.add_argument("--c4-batch", type=int, default=64)
     ap.add_argument("--c4-steps", type=int, default=3)
@@ -686,6 +709,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "batch": B,
+                   "vecmat_schedule": ("ModDown once after each rotation sum (double hoisting)" if args.double_hoist
+                                       else "one ModDown per rotation"),
                    "l2": "inputs larger than L2 (Galois keys ~0.75 GB + key-switch scratch streamed per step)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "latency_ms": {"p50": per[len(per) // 2], "p99": per[min(len(per) - 1, int(0.99 * len(per)))],
@@ -701,6 +726,7 @@ def main():
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
         "serving": r["serving"],
         "primitives": r["primitives"],
+        "single_hoisted": r["single"],
         "vecmat_4096x256": r["c4"],
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],

@@ -93,7 +93,13 @@ tcks_status tcks_params_primes(const tcks_params* p, uint64_t* primes, uint32_t 
  * the device. flags: TCKS_AUTO_RELIN | TCKS_AUTO_RESCALE (the context's automatic policies).
  * cuda_stream: a cudaStream_t the context works on (NULL = a stream the context creates).
  * The context copies `params`. */
-enum { TCKS_AUTO_RELIN = 1u, TCKS_AUTO_RESCALE = 2u };
+/* TCKS_DOUBLE_HOIST: every vector x plain matrix product of the context (tcks_vecmat_plain,
+ * tcks_vecmat_plain_batch, the CNN's fully connected layers, serving lanes) takes the key switch's
+ * division by P once, after the sum over rotations, instead of once per rotation (the diagonal
+ * method of §3.1 with the same rotations and the same hoisted decomposition; the result decrypts to
+ * the same product with less rounding noise, but its limbs differ from the per-rotation schedule).
+ * The matrix must carry its diagonals modulo P (tcks_matrix_encode does; see tcks_matrix_import_ext). */
+enum { TCKS_AUTO_RELIN = 1u, TCKS_AUTO_RESCALE = 2u, TCKS_DOUBLE_HOIST = 4u };
 tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32_t flags,
                                 const tcks_allocator* allocator, void* cuda_stream, tcks_ctx** out);
 void tcks_ctx_free(tcks_ctx* ctx);
@@ -102,6 +108,9 @@ tcks_status tcks_ctx_info(const tcks_ctx* ctx, uint32_t* log_n, uint32_t* n_data
 tcks_status tcks_ctx_key_bytes(const tcks_ctx* ctx, uint64_t* bytes);
 /* Wait for all work queued on the context's stream. */
 tcks_status tcks_ctx_synchronize(tcks_ctx* ctx);
+/* Replace the context's flags (TCKS_AUTO_RELIN | TCKS_AUTO_RESCALE | TCKS_DOUBLE_HOIST) for the calls
+ * that follow; work already queued or captured in a graph keeps the flags it was issued with. */
+tcks_status tcks_ctx_set_flags(tcks_ctx* ctx, uint32_t flags);
 
 /* Galois keys for left rotations by `steps` (§2.1, used by rotate / sum / dot / matmul_plain /
  * conv2d_im2col). A step is taken modulo N/2; step 0 needs no key. max_level in [1, L] trims each
@@ -213,11 +222,17 @@ tcks_status tcks_dot_plain(const tcks_ct* a, const double* w, uint32_t n, tcks_c
 /* Plain matrix for the vector x matrix product y = v M (M is rows x cols, rows = n inputs,
  * cols = m outputs, m <= n, n a power of two dividing N/2), stored as its n generalised diagonals
  * d_k[s] = M[(s+k) mod n][s] (s < m), each encoded at `level` and the context scale.
- * From host doubles (row-major M) or from pre-encoded host limbs [n][level][N]. */
+ * From host doubles (row-major M; each diagonal is also kept modulo P for the double-hoisted
+ * product) or from pre-encoded host limbs [n][level][N]. */
 tcks_status tcks_matrix_encode(tcks_ctx* ctx, const double* M, uint32_t rows, uint32_t cols, uint32_t level,
                                tcks_matrix** out);
 tcks_status tcks_matrix_import(tcks_ctx* ctx, const uint64_t* diag_limbs, uint32_t rows, uint32_t cols,
                                uint32_t level, double scale, tcks_matrix** out);
+/* The same with each diagonal also given modulo the special prime P: [rows][level+1][N], limb
+ * `level` of each diagonal modulo P (the same integer polynomial as the data limbs). Needed by the
+ * double-hoisted product (TCKS_DOUBLE_HOIST). */
+tcks_status tcks_matrix_import_ext(tcks_ctx* ctx, const uint64_t* diag_limbs, uint32_t rows, uint32_t cols,
+                                   uint32_t level, double scale, tcks_matrix** out);
 void tcks_matrix_free(tcks_matrix* m);
 /* Encrypted vector (slots [0, n), zeros elsewhere) times plain matrix (§3.1): replicate the input
  * over the N/2 slots with left rotations (if n < N/2), y = sum_k rot(ct, k) * d_k with hoisted

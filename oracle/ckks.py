@@ -588,6 +588,8 @@ class EncodedCNN:
     masks: list = field(default_factory=list)  # per kernel, level L-1
     fc1: list = field(default_factory=list)    # 256 diagonals, level L-3
     fc2: list = field(default_factory=list)    # 64 diagonals, level L-5
+    fc1_ext: np.ndarray | None = None          # the same over the extended basis [256][L-2][N]
+    fc2_ext: np.ndarray | None = None          # [64][L-4][N]
     windows: int = 64
     taps: int = 49
 
@@ -619,13 +621,20 @@ def cnn_encode(o: OracleCKKS, w: CNNWeights, windows=64) -> EncodedCNN:
         e.masks.append(o.encode(mask, level=L - 1))
     e.fc1 = o.encode_matrix(w.fc1_w.T, L - 3)
     e.fc2 = o.encode_matrix(w.fc2_w.T, L - 5)
+    e.fc1_ext = o.encode_matrix_ext(w.fc1_w.T, L - 3)
+    e.fc2_ext = o.encode_matrix_ext(w.fc2_w.T, L - 5)
     return e
 
 
-def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: dict | None = None) -> Ct:
+def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: dict | None = None,
+                double_hoist: bool = False) -> Ct:
     """The encrypted CNN schedule (§4): conv (im2col, one multiplication per kernel) -> pack the
     four channel outputs with masks -> square -> FC1 (vector x plain matrix) -> square -> FC2.
-    Six multiplicative levels; biases are added as plaintexts at the ciphertext's scale and level."""
+    Six multiplicative levels; biases are added as plaintexts at the ciphertext's scale and level.
+    double_hoist: the two vector x matrix products take the ModDown once after their rotation sums."""
+    def fc(v, diags, diags_ext, n, m):
+        return o.vecmat_dh(v, diags_ext, n, m) if double_hoist else o.vecmat(v, diags, n, m)
+
     W = enc.windows
     K = len(enc.conv)
     chans = [o.conv2d_im2col_pt(ct, enc.conv[k], enc.taps, W) for k in range(K)]
@@ -641,7 +650,7 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
     v = o.add_plain(v, o.encode(bias, scale=v.scale, level=v.level))
     v = o.square(v)
     n1, m1 = w.fc1_w.shape[1], w.fc1_w.shape[0]
-    v = o.vecmat(v, enc.fc1, n1, m1)
+    v = fc(v, enc.fc1, enc.fc1_ext, n1, m1)
     b1 = np.zeros(o.slots)
     b1[:m1] = w.fc1_b
     if trace is not None:
@@ -649,7 +658,7 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
     v = o.add_plain(v, o.encode(b1, scale=v.scale, level=v.level))
     v = o.square(v)
     n2, m2 = w.fc2_w.shape[1], w.fc2_w.shape[0]
-    v = o.vecmat(v, enc.fc2, n2, m2)
+    v = fc(v, enc.fc2, enc.fc2_ext, n2, m2)
     b2 = np.zeros(o.slots)
     b2[:m2] = w.fc2_b
     if trace is not None:

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libtcks.so")
 
 TCKS_AUTO_RELIN = 1
 TCKS_AUTO_RESCALE = 2
+TCKS_DOUBLE_HOIST = 4
 KEY_SECRET, KEY_PUBLIC, KEY_RELIN, KEY_GALOIS = 0, 1, 2, 3
 
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -91,6 +92,9 @@ _SIGS = {
     "tcks_dot": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, _vpp]),
     "tcks_dot_plain": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32, _vpp]),
     "tcks_matrix_encode": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
+    "tcks_matrix_import_ext": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                                 ctypes.c_double, _vpp]),
+    "tcks_ctx_set_flags": (ctypes.c_int32, [_vp, ctypes.c_uint32]),
     "tcks_matrix_import": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                              ctypes.c_double, _vpp]),
     "tcks_matrix_free": (None, [_vp]),
@@ -392,6 +396,16 @@ class Context:
         h = _vp()
         check(lib().tcks_matrix_import(self.h, _p(a), rows, cols, a.shape[1], float(scale), ctypes.byref(h)))
         return Matrix(self, h, rows, cols)
+
+    def matrix_import_ext(self, diag_limbs: np.ndarray, rows: int, cols: int, scale: float) -> "Matrix":
+        """Diagonals over the extended basis [rows][level+1][N] (limb `level` modulo P)."""
+        a = np.ascontiguousarray(diag_limbs, dtype=np.uint64)
+        h = _vp()
+        check(lib().tcks_matrix_import_ext(self.h, _p(a), rows, cols, a.shape[1] - 1, float(scale), ctypes.byref(h)))
+        return Matrix(self, h, rows, cols)
+
+    def set_flags(self, flags: int):
+        check(lib().tcks_ctx_set_flags(self.h, flags))
 
 
 def im2col_encode(img: np.ndarray, kh: int, kw: int, stride: int, cap: int):

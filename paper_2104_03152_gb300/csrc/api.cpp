@@ -233,12 +233,12 @@ void op_rotate_hoisted(tcks_ctx* c, const u64* ct, u32 ell, const int32_t* steps
   check_launch("rotate");
 }
 
-void encode_into(tcks_ctx* c, const double* d_v, size_t n, double scale, u32 level, u64* pt_out) {
+void encode_into(tcks_ctx* c, const double* d_v, size_t n, double scale, u32 level, u64* pt_out, bool ext) {
   if (c->params.log_n > 14) fail(TCKS_ERR_UNSUPPORTED, "encoding is implemented for N <= 2^14");
   DevBuf coeffs(c, c->N);
   check_cuda(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "encode status");
   launch_encode_coeffs(c->T, c->F, d_v, (u32)n, scale, (i64*)coeffs.p, c->d_status, c->stream);
-  launch_coeffs_to_ntt(c->T, (const i64*)coeffs.p, level, pt_out, c->stream);
+  launch_coeffs_to_ntt(c->T, (const i64*)coeffs.p, level, pt_out, c->stream, ext);
   check_launch("encode");
   int status = 0;
   check_cuda(cudaMemcpyAsync(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "encode status");
@@ -500,6 +500,14 @@ tcks_status tcks_ctx_synchronize(tcks_ctx* c) {
   TCKS_API_BEGIN
   if (!c) fail(TCKS_ERR_INVALID_ARG, "null context");
   check_cuda(cudaStreamSynchronize(c->stream), "synchronize");
+  TCKS_API_END
+}
+
+tcks_status tcks_ctx_set_flags(tcks_ctx* c, uint32_t flags) {
+  TCKS_API_BEGIN
+  if (!c) fail(TCKS_ERR_INVALID_ARG, "null context");
+  if (flags & ~(u32)(TCKS_AUTO_RELIN | TCKS_AUTO_RESCALE | TCKS_DOUBLE_HOIST)) fail(TCKS_ERR_INVALID_ARG, "unknown flag");
+  c->flags = flags;
   TCKS_API_END
 }
 
@@ -963,16 +971,18 @@ tcks_status tcks_matrix_encode(tcks_ctx* c, const double* M, uint32_t rows, uint
     fail(TCKS_ERR_INVALID_ARG, "need cols <= rows, rows a power of two dividing N/2");
   const u32 l = level == 0 ? c->L : level;
   if (l < 2 || l > c->L) fail(TCKS_ERR_INVALID_ARG, "level out of range (needs >= 2 for the rescale)");
-  DevBuf d(c, (size_t)rows * l * c->N);
+  // each diagonal over the extended basis (level limbs, then P): the single-hoisted product reads
+  // the first `level` limbs, the double-hoisted one all of them
+  DevBuf d(c, (size_t)rows * (l + 1) * c->N);
   DevBuf dv(c, slots);
   std::vector<double> diag(slots);
   for (u32 k = 0; k < rows; ++k) {
     std::fill(diag.begin(), diag.end(), 0.0);
     for (u32 s2 = 0; s2 < cols; ++s2) diag[s2] = M[(size_t)((s2 + k) % rows) * cols + s2];
     check_cuda(cudaMemcpyAsync(dv.p, diag.data(), (size_t)slots * 8, cudaMemcpyHostToDevice, c->stream), "diag H2D");
-    encode_into(c, (const double*)dv.p, slots, c->params.scale, l, d.p + (size_t)k * l * c->N);
+    encode_into(c, (const double*)dv.p, slots, c->params.scale, l, d.p + (size_t)k * (l + 1) * c->N, true);
   }
-  *out = new tcks_matrix{c, rows, cols, l, c->params.scale, d.release()};
+  *out = new tcks_matrix{c, rows, cols, l, 1, c->params.scale, d.release()};
   ctx_retain(c);
   TCKS_API_END
 }
@@ -990,7 +1000,25 @@ tcks_status tcks_matrix_import(tcks_ctx* c, const uint64_t* diag_limbs, uint32_t
   DevBuf d(c, words);
   check_cuda(cudaMemcpyAsync(d.p, diag_limbs, words * 8, cudaMemcpyHostToDevice, c->stream), "matrix import");
   check_cuda(cudaStreamSynchronize(c->stream), "matrix import");
-  *out = new tcks_matrix{c, rows, cols, level, scale, d.release()};
+  *out = new tcks_matrix{c, rows, cols, level, 0, scale, d.release()};
+  ctx_retain(c);
+  TCKS_API_END
+}
+
+tcks_status tcks_matrix_import_ext(tcks_ctx* c, const uint64_t* diag_limbs, uint32_t rows, uint32_t cols,
+                                   uint32_t level, double scale, tcks_matrix** out) {
+  TCKS_API_BEGIN
+  if (!c || !diag_limbs || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  const u32 slots = c->N / 2;
+  if (rows == 0 || cols == 0 || cols > rows || rows > slots || (rows & (rows - 1)) || slots % rows)
+    fail(TCKS_ERR_INVALID_ARG, "need cols <= rows, rows a power of two dividing N/2");
+  if (level < 2 || level > c->L) fail(TCKS_ERR_INVALID_ARG, "level out of range");
+  const size_t words = (size_t)rows * (level + 1) * c->N;
+  DevBuf d(c, words);
+  check_cuda(cudaMemcpyAsync(d.p, diag_limbs, words * 8, cudaMemcpyHostToDevice, c->stream), "matrix import");
+  check_cuda(cudaStreamSynchronize(c->stream), "matrix import");
+  *out = new tcks_matrix{c, rows, cols, level, 1, scale, d.release()};
   ctx_retain(c);
   TCKS_API_END
 }

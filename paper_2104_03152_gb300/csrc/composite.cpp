@@ -27,8 +27,55 @@ void op_sum(tcks_ctx* c, u64* ct, u32 ell) {
 //   ModDown + multiply-accumulate with the diagonal d_k (k_vecmat_acc), the k = 0 term and the
 //   partial sums folded by k_vecmat_reduce, and the rescale. Rotations are processed in blocks so
 //   that the P-limb scratch stays bounded (~512 MB).
+// The same product with the ModDown taken once after the sum over rotations (double hoisting):
+// replicate, ModUp once per ciphertext, one element-wise pass over all rotations accumulating the
+// key-switch inner products times the extended-basis diagonals (k_vecmat_dh_acc), the fold of its
+// chunk partials, INTT of the P limbs, one ModDown per (request, component, prime) with the k = 0
+// term and tau(c0) part added (k_vecmat_dh_moddown), and the rescale. No transform runs per rotation.
+static void op_vecmat_dh(tcks_ctx* c, u64* ct, u64 cw, u32 count, u32 ell, const tcks_matrix* M, const KeyTable* kt,
+                         u64* out) {
+  const size_t n = c->N;
+  const u32 R = M->rows - 1;
+  DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
+  launch_modup(c->T, ct + (size_t)ell * n, cw, count, ell, coef.p, digits.p, c->stream);
+  // chunks of rotations: enough CTAs for a few waves of 256-thread CTAs on every SM
+  const u64 base = vecmat_dh_base_ctas(c->params.log_n, ell, count), want = 152ull * 8 * 4;
+  u32 chunks = (u32)std::min<u64>(R, std::max<u64>(1, (want + base - 1) / base));
+  const u32 chunk = (R + chunks - 1) / chunks;
+  chunks = (R + chunk - 1) / chunk;
+  DevBuf partial(c, (size_t)count * chunks * 3 * (ell + 1) * n);
+  VecmatDhPlan p{};
+  p.keys = kt->d;
+  p.digits = digits.p;
+  p.digits_b = (u64)ell * (ell + 1) * n;
+  p.ct = ct;
+  p.ct_b = cw;
+  p.diag = M->d;
+  p.diag_stride = (u64)M->limbs() * n;
+  p.p_limb = M->level;
+  p.partial = partial.p;
+  p.R = R;
+  p.B = count;
+  p.chunk = chunk;
+  p.chunks = chunks;
+  launch_vecmat_dh_acc(c->T, ell, p, c->stream);
+  launch_vecmat_dh_fold(c->T, ell, p, c->stream);
+  DevBuf top(c, (size_t)2 * count * n), acc(c, (size_t)count * cw);
+  const u64 per_rq = (u64)chunks * 3 * (ell + 1) * n;
+  for (u32 b = 0; b < 2; ++b)
+    launch_ntt(c->T, true, partial.p + ((u64)b * (ell + 1) + ell) * n, per_rq, top.p + (u64)b * count * n, n, count,
+               c->L, 1, c->stream);
+  launch_vecmat_dh_moddown(c->T, ell, p, top.p, acc.p, cw, c->stream);
+  op_rescale(c, acc.p, ell, out, count);
+  check_launch("vecmat (double hoisted)");
+}
+
 void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell, const tcks_matrix* M, u64* out) {
   const size_t n = c->N;
+  const bool dh = (c->flags & TCKS_DOUBLE_HOIST) != 0;
+  if (dh && !M->ext)
+    fail(TCKS_ERR_UNSUPPORTED, "double-hoisted vector x matrix needs the diagonals modulo P (tcks_matrix_encode or "
+                               "tcks_matrix_import_ext)");
   const u32 rows = M->rows;
   const u32 slots = c->N / 2;
   const u64 cw = ct_words(c, ell);
@@ -53,6 +100,10 @@ void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell,
     op_rescale(c, acc.p, ell, out, count);
     return;
   }
+  if (dh) {
+    op_vecmat_dh(c, ct.p, cw, count, ell, M, kt, out);
+    return;
+  }
   DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
   launch_modup(c->T, ct.p + (size_t)ell * n, cw, count, ell, coef.p, digits.p, c->stream);
   const u32 R = rows - 1;
@@ -73,7 +124,7 @@ void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell,
   DevBuf top(c, (size_t)per_rot * RB);
   // chunk partials per request, reused (accumulated) across the rotation blocks
   DevBuf partial(c, (size_t)count * chunks_pb * cw);
-  const u64 diag_stride = (u64)M->level * n;
+  const u64 diag_stride = (u64)M->limbs() * n;
   for (u32 rb0 = 0; rb0 < R; rb0 += RB) {
     const u32 rbn = std::min(RB, R - rb0);
     KsPlan p{};

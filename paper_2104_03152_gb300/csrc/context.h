@@ -99,8 +99,10 @@ struct tcks_pt {
 struct tcks_matrix {
   tcks_ctx* ctx;
   tcks::u32 rows, cols, level;
+  tcks::u32 ext;  // 1: every diagonal also carries its limb modulo the special prime P (last)
   double scale;
-  tcks::u64* d;  // [rows][level][N] encoded diagonals
+  tcks::u64* d;  // [rows][level + ext][N] encoded diagonals
+  tcks::u32 limbs() const { return level + ext; }  // limbs per stored diagonal
 };
 
 namespace tcks {
@@ -168,7 +170,7 @@ const GaloisKey& galois_key_for(tcks_ctx* c, int64_t step, u32 ell);
 // Device key table for `steps` (0 = relinearization key); every key must cover level ell.
 const KeyTable& key_table(tcks_ctx* c, const std::vector<u32>& steps, u32 ell);
 u32 step_mod(const tcks_ctx* c, int64_t step);
-void encode_into(tcks_ctx* c, const double* d_v, size_t n, double scale, u32 level, u64* pt_out);
+void encode_into(tcks_ctx* c, const double* d_v, size_t n, double scale, u32 level, u64* pt_out, bool ext = false);
 // composite.cpp
 void op_sum(tcks_ctx* c, u64* ct, u32 ell);  // in place
 // count ciphertexts ct + i * ct_stride at level ell -> out [count][2][ell-1][N]

@@ -91,12 +91,14 @@ __global__ void k_encode_coeffs(DevTables T, FftTables F, const double* __restri
   if (overflow) atomicExch(status, 1);
 }
 
-// int64 coefficients -> NTT-form limbs, one limb job per prime.
+// int64 coefficients -> NTT-form limbs, one limb job per prime: limb j modulo q_j, and limb p_slot
+// (when the launch includes it) modulo the special prime P.
 template <typename W, int LC>
-__global__ void k_coeffs_to_ntt(DevTables T, const i64* __restrict__ coeffs, u64* __restrict__ pt) {
+__global__ void k_coeffs_to_ntt(DevTables T, const i64* __restrict__ coeffs, u32 p_slot, u64* __restrict__ pt) {
   TCKS_SMEM(W);
   const Slice P = slice_of<LC>(T);
-  const u32 rank = P.rank, l = P.job, ns = P.ns, off = P.off;
+  const u32 rank = P.rank, j = P.job, ns = P.ns, off = P.off;
+  const u32 l = j == p_slot ? T.L : j;
   const ModConst m = T.mods[l];
   for (u32 k = threadIdx.x; k < ns; k += blockDim.x) {
     const i64 v = coeffs[off + k];
@@ -106,7 +108,7 @@ __global__ void k_coeffs_to_ntt(DevTables T, const i64* __restrict__ coeffs, u64
   }
   __syncthreads();
   ntt_fwd_slice<W, LC>(s, T, l, rank);
-  u64* out = pt + ((u64)l << T.log_n) + off;
+  u64* out = pt + ((u64)j << T.log_n) + off;
   for (u32 k = threadIdx.x; k < ns; k += blockDim.x) out[k] = Ar<W>::fwd_out(s[sw(k)], m);
 }
 
@@ -212,9 +214,11 @@ u32 limb_threads_cap_fft(bool narrow, u32 log_c) {
   return (u32)a.maxThreadsPerBlock;
 }
 
-void launch_coeffs_to_ntt(const DevTables& T, const i64* d_coeffs, u32 ell, u64* pt, cudaStream_t st) {
-  Launch L(K_ENCODE, st, 8.0 * (1.0 + ell) * (1u << T.log_n));
-  launch_limb(K6_k_coeffs_to_ntt, T.narrow, ell, 1, T.log_n, st, T.limb_threads, T, d_coeffs, pt);
+void launch_coeffs_to_ntt(const DevTables& T, const i64* d_coeffs, u32 ell, u64* pt, cudaStream_t st, bool ext) {
+  const u32 limbs = ell + (ext ? 1 : 0);
+  Launch L(K_ENCODE, st, 8.0 * (1.0 + limbs) * (1u << T.log_n));
+  launch_limb(K6_k_coeffs_to_ntt, T.narrow, limbs, 1, T.log_n, st, T.limb_threads, T, d_coeffs,
+              ext ? ell : 0xffffffffu, pt);
 }
 
 void launch_crt_compose(const DevTables& T, const u64* coef, u32 ell, const u64* d_qwords, double* out,

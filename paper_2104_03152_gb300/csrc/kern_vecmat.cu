@@ -1,0 +1,174 @@
+// Vector x plain matrix with the ModDown taken once, after the sum over rotations (double
+// hoisting), for a batch of B requests at level ell over the rotations k = 1..R of one matrix:
+//
+//   U_b[i] = sum_k (sum_j tau_k(D_j)[i] * gk^(k)_j[b][i]) * d_k[i]      slots i < ell and P
+//   A_0[i] = sum_k tau_k(c0)[i] * d_k[i]                                  i < ell
+//   out_b[i] = A_b[i] + c_b[i] d_0[i] + (U_b[i] - NTT_i(bal_P(INTT_P(U_b[P])))) * P^-1
+//
+// k_vecmat_dh_acc is element-wise (no transform inside the rotation loop): one thread owns a few
+// elements of one (request, slot i) and walks a chunk of rotations, reading the digits through the
+// Galois permutation and each key limb, diagonal and c0 limb once; the grid orders requests fastest
+// so that the CTAs sharing a key limb run together. k_vecmat_dh_fold sums the chunk partials;
+// k_vecmat_dh_moddown finishes (one limb job per request, component and prime).
+#include <cuda_runtime.h>
+
+#include "context.h"
+#include "kernels.h"
+#include "limb_launch.cuh"
+#include "ntt.cuh"
+
+namespace tcks {
+
+namespace {
+
+constexpr u32 kDhThreads = 256;
+constexpr int kDhEpt = 2;  // elements per thread (stride kDhThreads)
+
+// partial layout: [B][chunks][3][ell+1][N] with component 2 = A_0 (slot ell unused)
+__device__ __forceinline__ u64 dh_off(u32 rq, u32 chunk, u32 chunks, u32 comp, u32 slot, u32 ell, u32 log_n) {
+  return ((((u64)rq * chunks + chunk) * 3 + comp) * (ell + 1) + slot) << log_n;
+}
+
+template <typename W>
+__global__ void __launch_bounds__(kDhThreads) k_vecmat_dh_acc(DevTables T, u32 ell, const __grid_constant__ VecmatDhPlan p) {
+  const u32 log_n = T.log_n;
+  const u64 n = 1ull << log_n;
+  const u32 slots = ell + 1;
+  const u32 rq = blockIdx.x % p.B;
+  const u32 rest = blockIdx.x / p.B;
+  const u32 i = rest % slots, eb = rest / slots;
+  const u32 chunk = blockIdx.y;
+  const u32 mod = i < ell ? i : T.L;
+  const ModConst m = T.mods[mod];
+  const u64* digits = p.digits + rq * p.digits_b;  // [ell][ell+1][N]
+  const u64* c0 = p.ct + rq * p.ct_b + (u64)i * n;
+  const u32 base = eb * kDhThreads * kDhEpt + threadIdx.x;
+  W u0[kDhEpt], u1[kDhEpt], a0[kDhEpt];
+#pragma unroll
+  for (int e = 0; e < kDhEpt; ++e) u0[e] = u1[e] = a0[e] = 0;
+  const u32 r0 = chunk * p.chunk, r1 = min(p.R, r0 + p.chunk);
+  for (u32 r = r0; r < r1; ++r) {
+    const KsKey kk = p.keys[r];
+    const u32 key_slot = i < ell ? i : kk.K;
+    const u64* dk = p.diag + (u64)(r + 1) * p.diag_stride + (u64)(i < ell ? i : p.p_limb) * n;
+#pragma unroll
+    for (int e = 0; e < kDhEpt; ++e) {
+      const u32 g = base + e * kDhThreads;
+      if (g < n) {
+        const u32 src = galois_src(g, kk.g, log_n);
+        typename Ew<W>::Acc s0, s1;
+        for (u32 j = 0; j < ell; ++j) {
+          const u64 d = digits[((u64)j * slots + i) * n + src];
+          const u64* kj = kk.key + (((u64)j * 2) * (kk.K + 1) + key_slot) * n;
+          s0.mac(d, kj[g]);
+          s1.mac(d, kj[(u64)(kk.K + 1) * n + g]);
+        }
+        const u64 dv = dk[g];
+        u0[e] = (W)add_mod(u0[e], Ew<W>::mul(s0.get(m), dv, m), m.q);
+        u1[e] = (W)add_mod(u1[e], Ew<W>::mul(s1.get(m), dv, m), m.q);
+        if (i < ell) a0[e] = (W)add_mod(a0[e], Ew<W>::mul(c0[src], dv, m), m.q);
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < kDhEpt; ++e) {
+    const u32 g = base + e * kDhThreads;
+    if (g < n) {
+      p.partial[dh_off(rq, chunk, p.chunks, 0, i, ell, log_n) + g] = u0[e];
+      p.partial[dh_off(rq, chunk, p.chunks, 1, i, ell, log_n) + g] = u1[e];
+      if (i < ell) p.partial[dh_off(rq, chunk, p.chunks, 2, i, ell, log_n) + g] = a0[e];
+    }
+  }
+}
+
+// Sum of the chunk partials into chunk 0 (in place), every (request, component, slot).
+__global__ void k_vecmat_dh_fold(DevTables T, u32 ell, const __grid_constant__ VecmatDhPlan p) {
+  const u32 log_n = T.log_n;
+  const u64 n = 1ull << log_n;
+  const u32 slots = ell + 1;
+  const u64 per_rq = 3ull * slots * n;
+  for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < per_rq * p.B; e += (u64)gridDim.x * blockDim.x) {
+    const u32 rq = (u32)(e / per_rq);
+    const u64 o = e - (u64)rq * per_rq;
+    const u32 slot = (u32)((o >> log_n) % slots);
+    const u64 q = T.mods[slot < ell ? slot : T.L].q;
+    u64* base = p.partial + (u64)rq * p.chunks * per_rq + o;
+    u64 s = base[0];
+    for (u32 c = 1; c < p.chunks; ++c) s = add_mod(s, base[(u64)c * per_rq], q);
+    base[0] = s;
+  }
+}
+
+// out_b[i] = A_b[i] + c_b[i] d_0[i] + (U_b[i] - NTT_i(bal_P(top_b) mod q_i)) * P^-1.
+// Limb job = (b * ell + i) * B + request; top [2][B][N] holds INTT_P(U_b[P]).
+template <typename W, int LC>
+__global__ void k_vecmat_dh_moddown(DevTables T, u32 ell, const __grid_constant__ VecmatDhPlan p, const u64* top,
+                                    u64* out, u64 out_b) {
+  TCKS_SMEM(W);
+  const Slice sl = slice_of<LC>(T);
+  const u32 log_n = T.log_n;
+  const u64 n = 1ull << log_n;
+  const u32 rq = sl.job % p.B, bi = sl.job / p.B, b = bi / ell, i = bi % ell;
+  const ModConst mi = T.mods[i];
+  const ModConst mp = T.mods[T.L];
+  const PairConst pc = T.pairs[(u64)T.L * T.n_mods + i];
+  const u64* t = top + ((u64)b * p.B + rq) * n + sl.off;
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)lift_balanced(t[k], mp.half, pc.qa_mod_b, mi);
+  __syncthreads();
+  ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
+  const u64* U = p.partial + dh_off(rq, 0, p.chunks, b, i, ell, log_n);
+  const u64* A = p.partial + dh_off(rq, 0, p.chunks, 2, i, ell, log_n);
+  const u64* cb = p.ct + rq * p.ct_b + ((u64)b * ell + i) * n;
+  const u64* d0 = p.diag + (u64)i * n;
+  u64* dst = out + rq * out_b + ((u64)b * ell + i) * n;
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
+    const u32 g = sl.off + k;
+    u64 v = Ew<W>::shoup_inv(sub_mod(U[g], Ar<W>::fwd_out(s[sw(k)], mi), mi.q), pc, mi);
+    v = add_mod(v, Ew<W>::mul(cb[g], d0[g], mi), mi.q);
+    if (b == 0) v = add_mod(v, A[g], mi.q);
+    dst[g] = v;
+  }
+}
+
+static decltype(&k_vecmat_dh_moddown<u64, 0>) const K6_k_vecmat_dh_moddown[6] = TCKS_K6(k_vecmat_dh_moddown);
+
+}  // namespace
+
+u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B) {
+  const u64 n = 1ull << log_n;
+  const u64 eblocks = (n + kDhThreads * kDhEpt - 1) / (kDhThreads * kDhEpt);
+  return (u32)(eblocks * (ell + 1) * B);
+}
+
+void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st) {
+  const double n = (double)(1u << T.log_n);
+  const double by = 8.0 * n *
+                    ((double)p.B * (ell * (ell + 1.0) + ell) + (double)p.R * (2.0 * ell * (ell + 1.0) + ell + 1.0) +
+                     (double)p.B * p.chunks * (3.0 * ell + 2.0));
+  const double ops = (double)p.B * p.R * n * ((ell + 1.0) * (2.0 * ell + 4.0) + ell);
+  Launch L(K_VECMAT_DH, st, by, ops);
+  const dim3 grid(vecmat_dh_base_ctas(T.log_n, ell, p.B), p.chunks);
+  if (T.narrow)
+    k_vecmat_dh_acc<u32><<<grid, kDhThreads, 0, st>>>(T, ell, p);
+  else
+    k_vecmat_dh_acc<u64><<<grid, kDhThreads, 0, st>>>(T, ell, p);
+}
+
+void launch_vecmat_dh_fold(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st) {
+  if (p.chunks < 2) return;
+  const u64 e = (u64)p.B * 3 * (ell + 1) << T.log_n;
+  Launch L(K_MULACC, st, 8.0 * (double)e * (p.chunks + 1.0));
+  const u32 blocks = (u32)std::min<u64>((e + 255) / 256, 152ull * 16);
+  k_vecmat_dh_fold<<<blocks, 256, 0, st>>>(T, ell, p);
+}
+
+void launch_vecmat_dh_moddown(const DevTables& T, u32 ell, const VecmatDhPlan& p, const u64* top, u64* out, u64 out_b,
+                              cudaStream_t st) {
+  const double n = (double)(1u << T.log_n);
+  const double jobs = 2.0 * ell * p.B;
+  Launch L(K_KS_MODDOWN, st, 8.0 * n * (jobs * 5.0 + ell), jobs * (0.5 * n * T.log_n + 2.0 * n));
+  launch_limb(K6_k_vecmat_dh_moddown, T.narrow, 2 * ell * p.B, 1, T.log_n, st, T.limb_threads, T, ell, p, top, out,
+              out_b);
+}
+
+}  // namespace tcks

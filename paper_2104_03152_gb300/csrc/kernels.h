@@ -9,7 +9,7 @@ namespace tcks {
 // Kernel families for launch accounting and the profiler (profiler.cpp).
 enum KernelId : u32 {
   K_NTT_FWD = 0, K_NTT_INV, K_ELEMENTWISE, K_TENSOR, K_DROP, K_MODUP, K_KS_P, K_KS_MODDOWN, K_MULACC, K_KEYGEN,
-  K_ENCRYPT, K_ENCODE, K_DECODE, K_VECMAT, K_DECRYPT, K_COUNT
+  K_ENCRYPT, K_ENCODE, K_DECODE, K_VECMAT, K_DECRYPT, K_VECMAT_DH, K_COUNT
 };
 // Scope around one kernel launch: counts it and, while profiling is on, records CUDA events on the
 // launching stream before and after it together with its algorithmic bytes.
@@ -113,6 +113,31 @@ struct VecmatPlan {
   u32 accumulate;  // 0: write the chunk partials; 1: add into them (later rotation blocks)
   u32 pad;
 };
+
+// Double-hoisted vector x matrix over R = rows - 1 rotations for B requests at level ell (see
+// kern_vecmat.cu): keys[r] = the key of rotation r + 1; digits + rq * digits_b the request's ModUp
+// digits [ell][ell+1][N]; ct + rq * ct_b its (replicated) ciphertext [2][ell][N]; diag + k *
+// diag_stride diagonal k over the extended basis (data limbs from 0, the P limb at p_limb, which is
+// the matrix's level and may exceed ell); partial [B][chunks][3][ell+1][N].
+struct VecmatDhPlan {
+  const KsKey* keys;
+  const u64* digits;
+  u64 digits_b;
+  const u64* ct;
+  u64 ct_b;
+  const u64* diag;
+  u64 diag_stride;
+  u64* partial;
+  u32 R, B, chunk, chunks;
+  u32 p_limb, pad;
+};
+// CTAs of one chunk of k_vecmat_dh_acc (element blocks x slots x requests).
+u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B);
+void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st);
+void launch_vecmat_dh_fold(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st);
+// top [2][B][N] = INTT_P of the folded U_b[P]; out + rq * out_b receives [2][ell][N] (before the rescale).
+void launch_vecmat_dh_moddown(const DevTables& T, u32 ell, const VecmatDhPlan& p, const u64* top, u64* out, u64 out_b,
+                              cudaStream_t st);
 // Stage 1 of a KsPlan alone (the P-limb inner product and its INTT into plan.top).
 void launch_ks_inner_p(const DevTables& T, u32 ell, const KsPlan& plan, cudaStream_t st);
 // The fused ModDown + multiply-accumulate over the plan's R rotations, chunk rotations per CTA.
@@ -142,7 +167,9 @@ struct FftTables {
 void launch_encode_coeffs(const DevTables& T, const FftTables& F, const double* d_z, u32 n_in, double scale,
                           i64* d_coeffs, int* d_status, cudaStream_t st);
 // int64 coefficients -> NTT-form plaintext [ell][N].
-void launch_coeffs_to_ntt(const DevTables& T, const i64* d_coeffs, u32 ell, u64* pt, cudaStream_t st);
+// ext: one more limb (index ell) modulo the special prime P, the extended-basis encoding.
+void launch_coeffs_to_ntt(const DevTables& T, const i64* d_coeffs, u32 ell, u64* pt, cudaStream_t st,
+                          bool ext = false);
 // Coefficient-domain residues [ell][N] -> centred integers as doubles [N] (exact CRT, correctly
 // rounded); q_words: [L][MAXW] products Q_l and [L][MAXW] (Q_l - 1)/2 per level.
 constexpr u32 CRT_MAXW = 34;

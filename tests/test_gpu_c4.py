@@ -53,3 +53,18 @@ def test_c4_batch_rejects_mixed_levels(c4):
     with pytest.raises(tk.TcksError) as e:
         mat.vecmat_batch([cts[0], low])
     assert e.value.name == "LEVEL_MISMATCH"
+
+
+def test_c4_double_hoisted(c4):
+    """The same workload with the ModDown once after the rotation sum: batch equals single, and the
+    result decrypts to v M as accurately."""
+    ctx, M, mat, vs, cts = c4
+    ctx.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_DOUBLE_HOIST)
+    try:
+        outs = mat.vecmat_batch(cts)
+        for i in (0, BATCH - 1):
+            assert np.array_equal(outs[i].export(), cts[i].vecmat_plain(mat).export()), i
+        err = max(float(np.max(np.abs(ctx.decrypt_values(outs[i])[:COLS] - vs[i] @ M))) for i in range(0, BATCH, 7))
+        assert err < 1e-3, err
+    finally:
+        ctx.set_flags(tk.TCKS_AUTO_RELIN)

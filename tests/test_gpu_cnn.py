@@ -95,3 +95,32 @@ def test_cnn_graph_equals_single(setup):
     for _ in range(2):
         for s1, b1 in zip(singles, g.run(cts)):
             assert np.array_equal(b1.export(), s1)
+
+
+def test_cnn_double_hoisted_parity(setup):
+    """With TCKS_DOUBLE_HOIST the two fully connected layers take the ModDown once after their
+    rotation sums: bit-identical to the oracle's double-hoisted schedule, batched and graph-captured
+    alike, and the logits still match the FP64 network."""
+    o, w, enc, ctx, model, need = setup
+    ctx.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | tk.TCKS_DOUBLE_HOIST)
+    try:
+        img = inputs.mnist_like_image(3)
+        v, W = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+        ct = o.encrypt_values(v, 77)
+        ref = oracle.cnn_forward(o, ct, w, enc, double_hoist=True)
+        got = model.forward(ctx.ct_import(ct.data, ct.scale))
+        assert_ct_equal(got, ref, "cnn forward (double hoisted)")
+        assert float(np.max(np.abs(ctx.decrypt_values(got, 10) - oracle.cnn_plain(img, w)))) < 5e-3
+        cts = []
+        for seed in range(3):
+            img = inputs.mnist_like_image(300 + seed)
+            v, W = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+            cts.append(ctx.encrypt_values(v, 700 + seed))
+        singles = [model.forward(c).export() for c in cts]
+        for s1, b1 in zip(singles, model.forward_batch(cts)):
+            assert np.array_equal(b1.export(), s1)
+        g = model.graph(3)
+        for s1, b1 in zip(singles, g.run(cts)):
+            assert np.array_equal(b1.export(), s1)
+    finally:
+        ctx.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE)

@@ -60,6 +60,44 @@ def test_vecmat_parity(n, m):
     assert np.max(np.abs(out[m:])) < 1e-5
 
 
+@pytest.mark.parametrize("n,m", [(16, 8), (64, 10), (256, 64)])
+def test_vecmat_double_hoisted_parity(n, m):
+    """TCKS_DOUBLE_HOIST: the ModDown once after the rotation sum, bit-exact against the oracle's
+    double-hoisted product, with the diagonals imported from the oracle or encoded on the GPU, one
+    ciphertext or a batch."""
+    p = Pair(12, [55, 40, 40, 56], 2.0 ** 40)
+    o, g = p.o, p.g
+    p.add_galois(o.vecmat_steps(n))
+    M = inputs.random_matrix(n, m, 8, 0.5)
+    cts = []
+    for i in range(3):
+        v = np.zeros(o.slots)
+        v[:n] = inputs.uniform_slots(n, 70 + i)
+        cts.append((v, o.encrypt_values(v, 410 + i)))
+    level = cts[0][1].level
+    ext = o.encode_matrix_ext(M, level)
+    gm = g.matrix_import_ext(ext, n, m, o.scale)
+    gm2 = g.matrix_encode(M, level=level)
+    plain_only = g.matrix_import(np.ascontiguousarray(ext[:, :level]), n, m, o.scale)
+    g.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | tk.TCKS_DOUBLE_HOIST)
+    try:
+        refs = [o.vecmat_dh(ct, ext, n, m) for _, ct in cts]
+        for (v, ct), ref in zip(cts, refs):
+            got = p.import_ct(ct).vecmat_plain(gm)
+            assert_ct_equal(got, ref, "vecmat (double hoisted)")
+            assert_ct_equal(p.import_ct(ct).vecmat_plain(gm2), ref, "vecmat (double hoisted, GPU-encoded)")
+            out = g.decrypt_values(got)
+            assert np.max(np.abs(out[:m] - v[:n] @ M)) < 1e-5
+        outs = gm.vecmat_batch([p.import_ct(ct) for _, ct in cts])
+        for got, ref in zip(outs, refs):
+            assert_ct_equal(got, ref, "vecmat batch (double hoisted)")
+        with pytest.raises(tk.TcksError) as e:
+            p.import_ct(cts[0][1]).vecmat_plain(plain_only)
+        assert e.value.name == "UNSUPPORTED"
+    finally:
+        g.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE)
+
+
 def test_conv_parity():
     p = Pair(13, [40, 30, 30, 41], 2.0 ** 30)
     o, g = p.o, p.g
