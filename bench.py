@@ -643,7 +643,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=2, help="oracle inferences timed for cpu_baseline")
     ap.add_argument("--batch", type=int, default=64, help="requests per step (the batched schedule)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the Poisson serving trace (0: skip)")
-    ap.add_argument("--serve-rate", default="2000,100",
+    ap.add_argument("--serve-rate", default="2000,300",
                     help="offered requests/s of the serving traces (comma-separated; one trace each)")
     ap.add_argument("--sweep", action="store_true", help="print the batched primitive sweep (JSON lines) and exit")
     ap.add_argument("--sweep-batches", default="1,8,64,512", help="ciphertexts per batch in the sweep")
