@@ -151,6 +151,16 @@ tcks_status tcks_decrypt(tcks_ctx* ctx, const tcks_ct* ct, tcks_pt** out);
  * then synchronises so `limbs` may be reused). Export synchronises. */
 tcks_status tcks_ct_import(tcks_ctx* ctx, const uint64_t* limbs, uint32_t level, double scale, tcks_ct** out);
 tcks_status tcks_ct_export(const tcks_ct* ct, uint64_t* limbs, size_t n_words);
+/* Wire format (the communication of one encrypted inference, §4): a 16-byte header (b"TCKS",
+ * version 1, kind 0, log2 N, level, scale as f64, little-endian) and, for component b = 0, 1 and limb
+ * i < level, the N NTT-form residues packed with exactly bit_length(q_i) bits each (residue k in bits
+ * [k w, (k+1) w) of the limb's ceil(N w / 8)-byte segment, least significant bit first). Packing and
+ * unpacking run on the device. serialize writes *written bytes to host `out` (INVALID_ARG when cap is
+ * too small); deserialize checks the header against the context and every residue against its prime
+ * (INVALID_ARG otherwise). */
+tcks_status tcks_ct_serialized_size(const tcks_ct* ct, uint64_t* bytes);
+tcks_status tcks_ct_serialize(const tcks_ct* ct, uint8_t* out, uint64_t cap, uint64_t* written);
+tcks_status tcks_ct_deserialize(tcks_ctx* ctx, const uint8_t* in, uint64_t size, tcks_ct** out);
 tcks_status tcks_pt_import(tcks_ctx* ctx, const uint64_t* limbs, uint32_t level, double scale, tcks_pt** out);
 tcks_status tcks_pt_export(const tcks_pt* pt, uint64_t* limbs, size_t n_words);
 tcks_status tcks_ct_info(const tcks_ct* ct, uint32_t* level, double* scale);

@@ -128,6 +128,9 @@ _SIGS = {
     "tcks_cnn_forward": (ctypes.c_int32, [_vp, _vp, _vpp]),
     "tcks_cnn_forward_batch": (ctypes.c_int32, [_vp, _vpp, ctypes.c_uint32, _vpp]),
     "tcks_vecmat_plain_batch": (ctypes.c_int32, [_vpp, ctypes.c_uint32, _vp, _vpp]),
+    "tcks_ct_serialized_size": (ctypes.c_int32, [_vp, _u64p]),
+    "tcks_ct_serialize": (ctypes.c_int32, [_vp, ctypes.c_void_p, ctypes.c_uint64, _u64p]),
+    "tcks_ct_deserialize": (ctypes.c_int32, [_vp, ctypes.c_void_p, ctypes.c_uint64, _vpp]),
     "tcks_batch_run": (ctypes.c_int32, [_vp, ctypes.c_uint32]),
     "tcks_batch_graph_create": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vpp]),
     "tcks_batch_graph_run": (ctypes.c_int32, [_vp]),
@@ -372,6 +375,13 @@ class Context:
         check(lib().tcks_ct_import(self.h, _p(a), level, float(scale), ctypes.byref(h)))
         return Ciphertext(self, h)
 
+    def ct_deserialize(self, data: bytes) -> "Ciphertext":
+        """A ciphertext from the bit-packed wire format (see tcks_ct_serialize)."""
+        buf = ctypes.create_string_buffer(bytes(data), len(data))
+        h = _vp()
+        check(lib().tcks_ct_deserialize(self.h, buf, len(data), ctypes.byref(h)))
+        return Ciphertext(self, h)
+
     def pt_import(self, limbs: np.ndarray, scale: float) -> "Plaintext":
         a = np.ascontiguousarray(limbs, dtype=np.uint64)
         h = _vp()
@@ -490,6 +500,15 @@ class Ciphertext:
     @property
     def scale(self) -> float:
         return self.info()[1]
+
+    def serialize(self) -> bytes:
+        """The bit-packed wire format (bit_length(q_i) bits per residue, 16-byte header)."""
+        size = np.zeros(1, dtype=np.uint64)
+        check(lib().tcks_ct_serialized_size(self.h, _p(size)))
+        buf = ctypes.create_string_buffer(int(size[0]))
+        written = np.zeros(1, dtype=np.uint64)
+        check(lib().tcks_ct_serialize(self.h, buf, int(size[0]), _p(written)))
+        return buf.raw[: int(written[0])]
 
     def export(self) -> np.ndarray:
         a = np.zeros((2, self.level, self.ctx.N), dtype=np.uint64)

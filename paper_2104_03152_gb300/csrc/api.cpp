@@ -699,6 +699,70 @@ tcks_status tcks_ct_export(const tcks_ct* ct, uint64_t* limbs, size_t n_words) {
   TCKS_API_END
 }
 
+// ------------------------------------------------------------------------- wire format ----
+static const unsigned char kWireMagic[4] = {'T', 'C', 'K', 'S'};
+static constexpr u64 kWireHeader = 16;
+
+tcks_status tcks_ct_serialized_size(const tcks_ct* ct, uint64_t* bytes) {
+  TCKS_API_BEGIN
+  if (!ct || !bytes) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *bytes = kWireHeader + wire_payload_bytes(ct->ctx->T, ct->ctx->host.chain.data(), ct->level);
+  TCKS_API_END
+}
+
+tcks_status tcks_ct_serialize(const tcks_ct* ct, uint8_t* out, uint64_t cap, uint64_t* written) {
+  TCKS_API_BEGIN
+  if (!ct || !out || !written) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  tcks_ctx* c = ct->ctx;
+  const u64 payload = wire_payload_bytes(c->T, c->host.chain.data(), ct->level);
+  if (cap < kWireHeader + payload) fail(TCKS_ERR_INVALID_ARG, "capacity below the serialized size");
+  DevBuf buf(c, (payload + 7) / 8);
+  launch_pack(c->T, ct->d, ct->level, (unsigned char*)buf.p, c->stream);
+  check_launch("serialize");
+  check_cuda(cudaMemcpyAsync(out + kWireHeader, buf.p, payload, cudaMemcpyDeviceToHost, c->stream), "serialize");
+  std::memcpy(out, kWireMagic, 4);
+  out[4] = 1;  // version
+  out[5] = 0;  // kind: ciphertext
+  out[6] = (uint8_t)c->params.log_n;
+  out[7] = (uint8_t)ct->level;
+  std::memcpy(out + 8, &ct->scale, 8);
+  check_cuda(cudaStreamSynchronize(c->stream), "serialize");
+  *written = kWireHeader + payload;
+  TCKS_API_END
+}
+
+tcks_status tcks_ct_deserialize(tcks_ctx* c, const uint8_t* in, uint64_t size, tcks_ct** out) {
+  TCKS_API_BEGIN
+  if (!c || !in || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (size < kWireHeader || std::memcmp(in, kWireMagic, 4) != 0) fail(TCKS_ERR_INVALID_ARG, "not a serialized ciphertext");
+  if (in[4] != 1 || in[5] != 0) fail(TCKS_ERR_INVALID_ARG, "unsupported version or kind");
+  if (in[6] != c->params.log_n) fail(TCKS_ERR_INVALID_ARG, "ring degree differs from the context's");
+  const u32 level = in[7];
+  if (level < 1 || level > c->L) fail(TCKS_ERR_INVALID_ARG, "level out of range");
+  double scale;
+  std::memcpy(&scale, in + 8, 8);
+  const u64 payload = wire_payload_bytes(c->T, c->host.chain.data(), level);
+  if (size != kWireHeader + payload) fail(TCKS_ERR_INVALID_ARG, "size does not match the header");
+  tcks_ct* r = new_ct(c, level, scale);
+  try {
+    DevBuf buf(c, (payload + 7) / 8);
+    check_cuda(cudaMemcpyAsync(buf.p, in + kWireHeader, payload, cudaMemcpyHostToDevice, c->stream), "deserialize");
+    check_cuda(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "deserialize status");
+    launch_unpack(c->T, (const unsigned char*)buf.p, level, r->d, c->d_status, c->stream);
+    check_launch("deserialize");
+    int status = 0;
+    check_cuda(cudaMemcpyAsync(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "deserialize");
+    check_cuda(cudaStreamSynchronize(c->stream), "deserialize");
+    if (status) fail(TCKS_ERR_INVALID_ARG, "a residue is not below its prime");
+  } catch (...) {
+    free_ct(r);
+    throw;
+  }
+  *out = r;
+  TCKS_API_END
+}
+
 tcks_status tcks_pt_import(tcks_ctx* c, const uint64_t* limbs, uint32_t level, double scale, tcks_pt** out) {
   TCKS_API_BEGIN
   if (!c || !limbs || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");

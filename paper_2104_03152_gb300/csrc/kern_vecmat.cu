@@ -22,64 +22,117 @@ namespace tcks {
 namespace {
 
 constexpr u32 kDhThreads = 256;
-constexpr int kDhEpt = 2;  // elements per thread (stride kDhThreads)
+
+// Lazy sum of products over the whole rotation loop: products of two residues are added without
+// reduction and the sum is reduced once at the end. 32-bit words: products < 2^62 in a 64-bit sum
+// with a carry count; 64-bit words: products < 2^122 in a 128-bit sum with a count of 2^128 carries.
+template <typename W>
+struct DhAcc;
+template <>
+struct DhAcc<u32> {
+  typename Ew<u32>::Acc a;
+  __device__ __forceinline__ void mac(u64 x, u64 y) { a.mac(x, y); }
+  __device__ __forceinline__ u64 get(const ModConst& m) const { return a.get(m); }
+};
+template <>
+struct DhAcc<u64> {
+  u64 lo = 0, hi = 0;
+  u32 top = 0;
+  __device__ __forceinline__ void mac(u64 x, u64 y) {
+    const u64 plo = x * y, phi = __umul64hi(x, y);
+    const u64 l = lo + plo;
+    const u64 h1 = hi + phi;
+    top += h1 < phi;
+    const u64 h2 = h1 + (l < plo);
+    top += h2 < h1;
+    lo = l;
+    hi = h2;
+  }
+  __device__ __forceinline__ u64 get(const ModConst& m) const {
+    u64 r = reduce128(hi, lo, m);
+    if (top) r = add_mod(r, mul_mod(mul_mod(m.r64, m.r64, m), top, m), m.q);  // top * 2^128 mod q
+    return r;
+  }
+};
 
 // partial layout: [B][chunks][3][ell+1][N] with component 2 = A_0 (slot ell unused)
 __device__ __forceinline__ u64 dh_off(u32 rq, u32 chunk, u32 chunks, u32 comp, u32 slot, u32 ell, u32 log_n) {
   return ((((u64)rq * chunks + chunk) * 3 + comp) * (ell + 1) + slot) << log_n;
 }
 
-template <typename W>
+// Thread = EPT elements (stride kDhThreads) x RPT requests of one slot i: the key limbs, the
+// diagonal and the Galois index of a rotation are loaded once for the RPT requests.
+template <typename W, int EPT, int RPT>
 __global__ void __launch_bounds__(kDhThreads) k_vecmat_dh_acc(DevTables T, u32 ell, const __grid_constant__ VecmatDhPlan p) {
   const u32 log_n = T.log_n;
   const u64 n = 1ull << log_n;
   const u32 slots = ell + 1;
-  const u32 rq = blockIdx.x % p.B;
-  const u32 rest = blockIdx.x / p.B;
+  const u32 groups = (p.B + RPT - 1) / RPT;
+  const u32 rg = blockIdx.x % groups;
+  const u32 rest = blockIdx.x / groups;
   const u32 i = rest % slots, eb = rest / slots;
   const u32 chunk = blockIdx.y;
   const u32 mod = i < ell ? i : T.L;
   const ModConst m = T.mods[mod];
-  const u64* digits = p.digits + rq * p.digits_b;  // [ell][ell+1][N]
-  const u64* c0 = p.ct + rq * p.ct_b + (u64)i * n;
-  const u32 base = eb * kDhThreads * kDhEpt + threadIdx.x;
-  W u0[kDhEpt], u1[kDhEpt], a0[kDhEpt];
+  const u64* digits[RPT];
+  const u64* c0[RPT];
 #pragma unroll
-  for (int e = 0; e < kDhEpt; ++e) u0[e] = u1[e] = a0[e] = 0;
+  for (int rr = 0; rr < RPT; ++rr) {
+    const u32 rq = min(rg * RPT + rr, p.B - 1);  // a short last group repeats a request, never stored
+    digits[rr] = p.digits + rq * p.digits_b + (u64)i * n;  // digit j at + j * slots * n
+    c0[rr] = p.ct + rq * p.ct_b + (u64)i * n;
+  }
+  const u32 base = eb * kDhThreads * EPT + threadIdx.x;
+  DhAcc<W> u0[EPT][RPT], u1[EPT][RPT], a0[EPT][RPT];
   const u32 r0 = chunk * p.chunk, r1 = min(p.R, r0 + p.chunk);
   for (u32 r = r0; r < r1; ++r) {
     const KsKey kk = p.keys[r];
     const u32 key_slot = i < ell ? i : kk.K;
     const u64* dk = p.diag + (u64)(r + 1) * p.diag_stride + (u64)(i < ell ? i : p.p_limb) * n;
+    const u64* k0 = kk.key + (u64)key_slot * n;     // digit j's component b at + (2j + b) (K+1) n
+    const u64 kstep = (u64)(kk.K + 1) * n;
 #pragma unroll
-    for (int e = 0; e < kDhEpt; ++e) {
+    for (int e = 0; e < EPT; ++e) {
       const u32 g = base + e * kDhThreads;
       if (g < n) {
         const u32 src = galois_src(g, kk.g, log_n);
-        typename Ew<W>::Acc s0, s1;
+        typename Ew<W>::Acc s0[RPT], s1[RPT];
         for (u32 j = 0; j < ell; ++j) {
-          const u64 d = digits[((u64)j * slots + i) * n + src];
-          const u64* kj = kk.key + (((u64)j * 2) * (kk.K + 1) + key_slot) * n;
-          s0.mac(d, kj[g]);
-          s1.mac(d, kj[(u64)(kk.K + 1) * n + g]);
+          const u64 w0 = k0[2 * j * kstep + g], w1 = k0[(2 * j + 1) * kstep + g];
+#pragma unroll
+          for (int rr = 0; rr < RPT; ++rr) {
+            const u64 d = digits[rr][(u64)j * slots * n + src];
+            s0[rr].mac(d, w0);
+            s1[rr].mac(d, w1);
+          }
         }
         const u64 dv = dk[g];
-        u0[e] = (W)add_mod(u0[e], Ew<W>::mul(s0.get(m), dv, m), m.q);
-        u1[e] = (W)add_mod(u1[e], Ew<W>::mul(s1.get(m), dv, m), m.q);
-        if (i < ell) a0[e] = (W)add_mod(a0[e], Ew<W>::mul(c0[src], dv, m), m.q);
+#pragma unroll
+        for (int rr = 0; rr < RPT; ++rr) {
+          u0[e][rr].mac(s0[rr].get(m), dv);
+          u1[e][rr].mac(s1[rr].get(m), dv);
+          if (i < ell) a0[e][rr].mac(c0[rr][src], dv);
+        }
       }
     }
   }
 #pragma unroll
-  for (int e = 0; e < kDhEpt; ++e) {
+  for (int e = 0; e < EPT; ++e) {
     const u32 g = base + e * kDhThreads;
-    if (g < n) {
-      p.partial[dh_off(rq, chunk, p.chunks, 0, i, ell, log_n) + g] = u0[e];
-      p.partial[dh_off(rq, chunk, p.chunks, 1, i, ell, log_n) + g] = u1[e];
-      if (i < ell) p.partial[dh_off(rq, chunk, p.chunks, 2, i, ell, log_n) + g] = a0[e];
+#pragma unroll
+    for (int rr = 0; rr < RPT; ++rr) {
+      const u32 rq = rg * RPT + rr;
+      if (g < n && rq < p.B) {
+        p.partial[dh_off(rq, chunk, p.chunks, 0, i, ell, log_n) + g] = u0[e][rr].get(m);
+        p.partial[dh_off(rq, chunk, p.chunks, 1, i, ell, log_n) + g] = u1[e][rr].get(m);
+        if (i < ell) p.partial[dh_off(rq, chunk, p.chunks, 2, i, ell, log_n) + g] = a0[e][rr].get(m);
+      }
     }
   }
 }
+
+// Launch shape per word type: elements and requests per thread.
+constexpr int kEpt32 = 1, kRpt32 = 2, kEpt64 = 1, kRpt64 = 1;
 
 // Sum of the chunk partials into chunk 0 (in place), every (request, component, slot).
 __global__ void k_vecmat_dh_fold(DevTables T, u32 ell, const __grid_constant__ VecmatDhPlan p) {
@@ -134,10 +187,11 @@ static decltype(&k_vecmat_dh_moddown<u64, 0>) const K6_k_vecmat_dh_moddown[6] = 
 
 }  // namespace
 
-u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B) {
+u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow) {
   const u64 n = 1ull << log_n;
-  const u64 eblocks = (n + kDhThreads * kDhEpt - 1) / (kDhThreads * kDhEpt);
-  return (u32)(eblocks * (ell + 1) * B);
+  const u32 ept = narrow ? kEpt32 : kEpt64, rpt = narrow ? kRpt32 : kRpt64;
+  const u64 eblocks = (n + kDhThreads * ept - 1) / (kDhThreads * ept);
+  return (u32)(eblocks * (ell + 1) * ((B + rpt - 1) / rpt));
 }
 
 void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st) {
@@ -147,11 +201,11 @@ void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cu
                      (double)p.B * p.chunks * (3.0 * ell + 2.0));
   const double ops = (double)p.B * p.R * n * ((ell + 1.0) * (2.0 * ell + 4.0) + ell);
   Launch L(K_VECMAT_DH, st, by, ops);
-  const dim3 grid(vecmat_dh_base_ctas(T.log_n, ell, p.B), p.chunks);
+  const dim3 grid(vecmat_dh_base_ctas(T.log_n, ell, p.B, T.narrow), p.chunks);
   if (T.narrow)
-    k_vecmat_dh_acc<u32><<<grid, kDhThreads, 0, st>>>(T, ell, p);
+    k_vecmat_dh_acc<u32, kEpt32, kRpt32><<<grid, kDhThreads, 0, st>>>(T, ell, p);
   else
-    k_vecmat_dh_acc<u64><<<grid, kDhThreads, 0, st>>>(T, ell, p);
+    k_vecmat_dh_acc<u64, kEpt64, kRpt64><<<grid, kDhThreads, 0, st>>>(T, ell, p);
 }
 
 void launch_vecmat_dh_fold(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st) {

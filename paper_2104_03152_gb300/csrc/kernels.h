@@ -54,6 +54,11 @@ void launch_ntt_desc(const DevTables& T, bool inverse, const NttDescTable& tab, 
 u32 limb_threads_cap_core(bool narrow, u32 log_c);
 u32 limb_threads_cap_sample(bool narrow, u32 log_c);
 u32 limb_threads_cap_fft(bool narrow, u32 log_c);
+// Bit-packed wire format of a ciphertext [2][level][N] (kern_wire.cu): payload bytes, pack into
+// `out` (device), unpack with a range check (status set to 1 on a residue >= q_i).
+u64 wire_payload_bytes(const DevTables& T, const u64* host_primes, u32 level);
+void launch_pack(const DevTables& T, const u64* ct, u32 level, unsigned char* out, cudaStream_t st);
+void launch_unpack(const DevTables& T, const unsigned char* in, u32 level, u64* ct, int* status, cudaStream_t st);
 void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_outer, u64* dst, u64 dst_outer,
                 u32 count, u32 mod_base, u32 per, cudaStream_t st);
 enum : u32 { OP_ADD = 0, OP_SUB = 1, OP_NEG = 2, OP_MUL_PLAIN = 3, OP_ADD_PLAIN = 4, OP_SUB_PLAIN = 5 };
@@ -132,7 +137,7 @@ struct VecmatDhPlan {
   u32 p_limb, pad;
 };
 // CTAs of one chunk of k_vecmat_dh_acc (element blocks x slots x requests).
-u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B);
+u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow);
 void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st);
 void launch_vecmat_dh_fold(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st);
 // top [2][B][N] = INTT_P of the folded U_b[P]; out + rq * out_b receives [2][ell][N] (before the rescale).

@@ -1,0 +1,46 @@
+"""The bit-packed wire format on the GPU: byte-identical to the oracle's serializer, round trips, the
+range and header checks, and the size of one encrypted CNN inference's traffic (§4)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import wire
+import paper_2104_03152_gb300 as tk
+from gpu_common import SEED
+from paper_2104_03152_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("log_n,bits", [(5, [30, 30, 31]), (12, [36, 36, 36, 37]), (13, [31, 26, 26, 26, 26, 26, 26, 31]),
+                                        (14, [60, 40, 40, 60])])
+def test_serialize_matches_oracle_and_roundtrips(log_n, bits):
+    ctx = tk.Context(tk.Params(log_n, bits, 2.0 ** 26), seed=SEED)
+    for level in (ctx.L, 1):
+        data = np.stack([inputs.random_limbs(ctx.primes[:level], ctx.N, 40 + level + b, polys=1)[0] for b in range(2)])
+        ct = ctx.ct_import(data, 2.0 ** 26)
+        got = ct.serialize()
+        assert got == wire.serialize(data, level, 2.0 ** 26, log_n, ctx.primes)
+        back = ctx.ct_deserialize(got)
+        assert np.array_equal(back.export(), data) and back.info() == (level, 2.0 ** 26)
+
+
+def test_deserialize_rejects_bad_input():
+    ctx = tk.Context(tk.Params(12, [36, 36, 36, 37], 2.0 ** 30), seed=SEED)
+    data = np.stack([inputs.random_limbs(ctx.primes[:3], ctx.N, 7 + b, polys=1)[0] for b in range(2)])
+    buf = ctx.ct_import(data, 1.0).serialize()
+    bad = bytearray(buf)
+    bad[16:24] = b"\xff" * 8  # residues >= q_0
+    for blob in (buf[:-1], bytes(bad), b"XXXX" + buf[4:]):
+        with pytest.raises(tk.TcksError) as e:
+            ctx.ct_deserialize(blob)
+        assert e.value.name == "INVALID_ARG"
+
+
+def test_cnn_inference_traffic():
+    """Encrypted input at level 7 plus encrypted output at level 1 for the C2 chain: 446,496 bytes
+    (436 KiB; the paper's 427 KB is for its 206-bit chain)."""
+    ctx = tk.Context(tk.Params(13, [31, 26, 26, 26, 26, 26, 26, 31], 2.0 ** 26), seed=SEED)
+    x = ctx.encrypt_values(inputs.uniform_slots(8, 1), 3)
+    y = ctx.ct_import(x.export()[:, :1], x.info()[1])
+    assert len(x.serialize()) + len(y.serialize()) == 16 + 382976 + 16 + 63488
