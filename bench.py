@@ -603,16 +603,27 @@ def oracle_setup():
     return oracle, o, w, enc, ct
 
 
-def time_oracle(n_steps: int, warmup: int):
+def time_oracle(n_steps: int, warmup: int, double_hoist: bool = True, single_thread_steps: int = 0):
+    """Oracle CNN inferences on the host cores (same schedule as the GPU arm); optionally also
+    single-threaded ones. Returns (times, cores, single-thread times)."""
     oracle, o, w, enc, ct = oracle_setup()
     for _ in range(warmup):
-        oracle.cnn_forward(o, ct, w, enc)
+        oracle.cnn_forward(o, ct, w, enc, double_hoist=double_hoist)
     times = []
     for _ in range(n_steps):
         t0 = time.perf_counter()
-        oracle.cnn_forward(o, ct, w, enc)
+        oracle.cnn_forward(o, ct, w, enc, double_hoist=double_hoist)
         times.append(time.perf_counter() - t0)
-    return times, oracle.lib().orc_max_threads()
+    cores = oracle.lib().orc_max_threads()
+    single = []
+    if single_thread_steps:
+        oracle.lib().orc_set_threads(1)
+        for _ in range(single_thread_steps):
+            t0 = time.perf_counter()
+            oracle.cnn_forward(o, ct, w, enc, double_hoist=double_hoist)
+            single.append(time.perf_counter() - t0)
+        oracle.lib().orc_set_threads(cores)
+    return times, cores, single
 
 
 def run_reference(args, world, rank):
@@ -620,7 +631,7 @@ def run_reference(args, world, rank):
         return
     steps, warmup = args.steps, args.warmup
     # bound the run: at most ~3 minutes of oracle inferences
-    times, cores = time_oracle(steps, warmup)
+    times, cores, _ = time_oracle(steps, warmup, bool(args.double_hoist))
     total = sum(times)
     value = steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": args.gpus,
@@ -700,10 +711,10 @@ def main():
     per = sorted(r["per_step"])
     # CPU baseline: the oracle on the host cores, bounded sample
     if args.cpu_sample > 0:
-        times, cores = time_oracle(args.cpu_sample, 0)
+        times, cores, single = time_oracle(args.cpu_sample, 0, bool(args.double_hoist), 1)
         cpu_val = len(times) / sum(times)
     else:
-        times, cores, cpu_val = [], 0, None
+        times, cores, cpu_val, single = [], 0, None, []
     line = {
         "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -721,7 +732,10 @@ def main():
         "accuracy": {"max_abs_err_vs_fp64": r["max_err"], "scale": "2^26"},
         "roofline": roofline, "kernels": kernels,
         "cpu_baseline": {"value": cpu_val, "unit": "inferences/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{len(times)} full CNN inferences of this workload (forward only)"},
+                         "sample": f"{len(times)} full CNN inferences of this workload (forward only, same "
+                                   "vector x matrix schedule)",
+                         "single_thread": {"value": len(single) / sum(single) if single else None, "cores": 1,
+                                           "sample": f"{len(single)} inference(s)"}},
         "e2e": {"value": world * B * r["e2e_steps"] / r["e2e_s"], "unit": "inferences/s",
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
         "serving": r["serving"],
