@@ -477,6 +477,87 @@ class OracleCKKS:
             raise ValueError(f"encode_ext failed ({st})")
         return out
 
+    @staticmethod
+    def rect_width(m: int) -> int:
+        """Diagonals of the rectangular form: the smallest power of two >= m."""
+        return 1 << max(0, (m - 1).bit_length())
+
+    def matrix_diagonals_rect(self, M: np.ndarray) -> list[np.ndarray]:
+        """Rectangular (hybrid) diagonals of an n x m matrix, m' = rect_width(m) <= n of them:
+        d_k[t] = M[(t' + k) mod n][t' mod m'] with t' = t mod n, zero where t' mod m' >= m (all N/2
+        slots, period n)."""
+        M = np.asarray(M, dtype=np.float64)
+        n, m = M.shape
+        mw = self.rect_width(m)
+        if mw > n:
+            raise ValueError("more outputs than inputs")
+        t = np.arange(self.slots) % n
+        cols = t % mw
+        out = []
+        for k in range(mw):
+            d = np.zeros(self.slots)
+            ok = cols < m
+            d[ok] = M[(t[ok] + k) % n, cols[ok]]
+            out.append(d)
+        return out
+
+    def encode_matrix_rect(self, M: np.ndarray, level: int) -> list[Pt]:
+        return [self.encode(d, level=level) for d in self.matrix_diagonals_rect(M)]
+
+    def encode_matrix_rect_ext(self, M: np.ndarray, level: int) -> np.ndarray:
+        return np.stack([self.encode_ext(d, level) for d in self.matrix_diagonals_rect(M)])
+
+    def vecmat_rect_steps(self, n: int, m: int) -> list[int]:
+        mw = self.rect_width(m)
+        chain = [mw << j for j in range(int(math.log2(n // mw)))]
+        return (self.replicate_steps(n) if n < self.slots else []) + list(range(1, mw)) + chain
+
+    def vecmat_rect(self, ct: Ct, n: int, m: int, diags: list[Pt] | None = None,
+                    diags_ext: np.ndarray | None = None) -> Ct:
+        """Vector x plain n x m matrix by the rectangular diagonal method: replicate, y' = sum over
+        the m' = rect_width(m) diagonals of rot(ct, k) * d_k (hoisted; with one ModDown per rotation
+        when `diags` is given, or once after the sum when `diags_ext` is), rescale, then
+        log2(n / m') rotate-and-adds by m' 2^j. Slots s < m hold y_s = sum_i v_i M[i][s]; the other
+        slots hold partial sums."""
+        mw = self.rect_width(m)
+        if diags_ext is not None:
+            y = self._vecmat_dh_rows(ct, diags_ext, n, mw)
+        else:
+            y = self._vecmat_rows(ct, diags, n, mw)
+        for j in range(int(math.log2(n // mw))):
+            y = self.add(y, self.rotate(y, mw << j))
+        return y
+
+    def _vecmat_rows(self, ct: Ct, diags: list[Pt], n: int, rows: int) -> Ct:
+        """Replicate an n-vector, then sum_{k < rows} rot(ct, k) * d_k (hoisted), then rescale."""
+        if n < self.slots:
+            for st in self.replicate_steps(n):
+                ct = self.add(ct, self.rotate(ct, st))
+        digits = self.modup(ct)
+        acc = None
+        for k in range(rows):
+            r = ct if k == 0 else self.rotate_from_digits(ct, digits, k)
+            t = self.mul_plain(r, diags[k])
+            acc = t if acc is None else self.add(acc, t)
+        return self.rescale(acc)
+
+    def _vecmat_dh_rows(self, ct: Ct, diags_ext: np.ndarray, n: int, rows: int) -> Ct:
+        """The same with the ModDown once after the sum (orc_vecmat_dh over `rows` diagonals)."""
+        level = ct.level
+        if n < self.slots:
+            for st in self.replicate_steps(n):
+                ct = self.add(ct, self.rotate(ct, st))
+        digits = self.modup(ct)
+        keys = [self._key(k) for k in range(1, rows)]
+        key_arrs = [np.ascontiguousarray(k.data) for k in keys]
+        ptrs = (_u64p * max(1, len(keys)))(*[P(a) for a in key_arrs])
+        lv = np.array([k.level for k in keys] or [0], dtype=np.uint32)
+        ge = np.array([self.galois_elt(k) for k in range(1, rows)] or [1], dtype=np.uint32)
+        out = np.zeros((2, level, self.N), dtype=np.uint64)
+        lib().orc_vecmat_dh(self._ctx, P(np.ascontiguousarray(ct.data)), P(digits), level, rows,
+                            P(np.ascontiguousarray(diags_ext)), ptrs, P(lv), P(ge), P(out))
+        return self.rescale(Ct(out, level, ct.scale * self.scale))
+
     def encode_matrix_ext(self, M: np.ndarray, level: int) -> np.ndarray:
         """The diagonals over the extended basis: [n][level+1][N]."""
         return np.stack([self.encode_ext(d, level) for d in self.matrix_diagonals(np.asarray(M, dtype=np.float64))])
