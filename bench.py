@@ -372,11 +372,14 @@ def plain_trace(tk, lanes, arrivals, kinds):
 
 # ------------------------------------------------------ vector x plain matrix at full size --
 C4_ROWS, C4_COLS = 4096, 256
-C4_WORKLOAD = ("encrypted 4096-dim N(0,1) vector x plain 4096x256 N(0,0.05) matrix (diagonal method: 4095 "
-               "hoisted rotations + the replication rotation), CKKS N=16384, primes [60,40,40|60], scale 2^40")
+C4_WORKLOAD = ("encrypted 4096-dim N(0,1) vector x plain 4096x256 N(0,0.05) matrix (diagonal method, hoisted "
+               "rotations, input replicated by one rotation), CKKS N=16384, primes [60,40,40|60], scale 2^40")
 
 
 def run_c4(torch, tk, args):
+    """The 4096x256 product for a batch of 64 vectors: the form given by --c4-form (rectangular
+    diagonals: 255 hoisted rotations + 4 rotate-and-adds; square: 4095 rotations) and key-switch
+    schedule given by --double-hoist, timed; the other form and schedule timed once beside it."""
     from paper_2104_03152_gb300 import inputs
     t0 = time.perf_counter()
     st = torch.cuda.Stream()
@@ -384,9 +387,13 @@ def run_c4(torch, tk, args):
     ctx = tk.Context(tk.Params(14, [60, 40, 40, 60], 2.0 ** 40), seed=inputs.SEED_KEYS, flags=flags,
                      stream=st.cuda_stream)
     ctx._torch_stream = st
-    ctx.gen_galois_keys([ctx.slots - C4_ROWS] + list(range(1, C4_ROWS)))
+    rect = args.c4_form == "rect"
+    rep = [ctx.slots - C4_ROWS]
+    rect_steps = list(range(1, C4_COLS)) + [C4_COLS << j for j in range(4)]
+    square_steps = list(range(1, C4_ROWS))
+    ctx.gen_galois_keys(rep + (rect_steps if rect else square_steps))
     M = inputs.random_matrix(C4_ROWS, C4_COLS, 7, 0.05)
-    mat = ctx.matrix_encode(M, level=3)
+    mat = ctx.matrix_encode_rect(M, level=3) if rect else ctx.matrix_encode(M, level=3)
     B = args.c4_batch
     vs = [inputs.normal_slots(C4_ROWS, 6 + 1000 * i) for i in range(B)]
     cts = []
@@ -396,6 +403,7 @@ def run_c4(torch, tk, args):
         cts.append(ctx.encrypt_values(z, 600 + i))
     ctx.synchronize()
     setup_s = time.perf_counter() - t0
+    key_bytes = ctx.key_bytes()
     outs = mat.vecmat_batch(cts)  # warm-up, and the accuracy check
     err = max(float(np.max(np.abs(ctx.decrypt_values(outs[i])[:C4_COLS] - vs[i] @ M))) for i in (0, B - 1))
     torch.cuda.synchronize()
@@ -404,23 +412,33 @@ def run_c4(torch, tk, args):
     tk.profile_stop()
     prof = tk.profile_read(with_ops=True)
     peak64 = tk.calibrate_butterflies(64)
-    single = None
+    compare = {}
+
+    def once(m, label):
+        m.vecmat_batch(cts)
+        _, t = timed(torch, st, lambda: m.vecmat_batch(cts), 1)
+        compare[label] = {"value": B / (t / 1e3), "unit": "vectors/s"}
     if args.double_hoist:
         ctx.set_flags(tk.TCKS_AUTO_RELIN)
-        mat.vecmat_batch(cts)
-        _, tot_s = timed(torch, st, lambda: mat.vecmat_batch(cts), 1)
-        single = {"value": B / (tot_s / 1e3), "unit": "vectors/s", "schedule": "one ModDown per rotation"}
-        ctx.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_DOUBLE_HOIST)
+        once(mat, ("rectangular" if rect else "square") + ", one ModDown per rotation")
+        ctx.set_flags(flags)
+    if rect:  # the square form: 4095 rotations
+        ctx.gen_galois_keys(square_steps)
+        sq = ctx.matrix_encode(M, level=3)
+        once(sq, "square" + (", ModDown once after the rotation sum" if args.double_hoist else ", one ModDown per rotation"))
+        del sq
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "gbs": round(v[2] / (v[1] / 1e3) / 1e9, 1),
                    "gbfly_s": round(v[3] / (v[1] / 1e3) / 1e9, 1),
                    "alu_frac": round(v[3] / (v[1] / 1e3) / peak64, 4)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
     return {"workload": C4_WORKLOAD, "batch": B, "value": B * args.c4_steps / (total / 1e3), "unit": "vectors/s",
             "ms_per_batch": total / args.c4_steps, "steps": args.c4_steps, "setup_s": setup_s,
-            "galois_keys": C4_ROWS, "key_bytes": ctx.key_bytes(),
+            "form": ("rectangular diagonals: 255 hoisted rotations + 4 rotate-and-adds" if rect
+                     else "square diagonals: 4095 hoisted rotations"),
+            "galois_keys": len(rep) + len(rect_steps if rect else square_steps), "key_bytes": key_bytes,
             "max_abs_err_vs_fp64": err, "kernels": kernels, "alu_peak_bfly64_per_s": peak64,
             "schedule": "ModDown once after the rotation sum" if args.double_hoist else "one ModDown per rotation",
-            "single_hoisted": single,
+            "compare": compare,
             "ctx": ctx, "mat": mat, "cts": cts}
 
 
@@ -667,6 +685,8 @@ def main():
                     help="vector x matrix products take the ModDown once after the rotation sum (1) or per rotation (0)")
     ap.add_argument("--c4", type=int, default=1, help="time the 4096x256 vector x matrix workload (64 vectors)")
     ap.add_argument("--c4-batch", type=int, default=64)
+    ap.add_argument("--c4-form", default="rect", choices=["rect", "square"],
+                    help="diagonal form of the 4096x256 matrix (rect: 260 rotations, square: 4096)")
     ap.add_argument("--c4-steps", type=int, default=3)
     ap.add_argument("--serve-mix", type=float, default=0.3, help="share of vector x matrix requests in the trace")
     ap.add_argument("--plain-requests", type=int, default=300,

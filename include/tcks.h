@@ -238,6 +238,17 @@ tcks_status tcks_matrix_encode(tcks_ctx* ctx, const double* M, uint32_t rows, ui
                                tcks_matrix** out);
 tcks_status tcks_matrix_import(tcks_ctx* ctx, const uint64_t* diag_limbs, uint32_t rows, uint32_t cols,
                                uint32_t level, double scale, tcks_matrix** out);
+/* Rectangular (hybrid) form of the same rows x cols matrix: m' = the smallest power of two >= cols
+ * diagonals d_k[t] = M[(t' + k) mod rows][t' mod m'] (t' = t mod rows; zero where t' mod m' >= cols),
+ * each over the extended basis. The product then takes m' - 1 hoisted rotations instead of rows - 1,
+ * rescales, and finishes with log2(rows / m') rotate-and-adds by m' 2^j: slots s < cols hold
+ * y_s = sum_i v_i M[i][s], the other slots partial sums (mask them before reusing the ciphertext as a
+ * zero-padded vector). Galois keys needed: steps 1..m'-1, m' 2^j, and the replication steps. */
+tcks_status tcks_matrix_encode_rect(tcks_ctx* ctx, const double* M, uint32_t rows, uint32_t cols, uint32_t level,
+                                    tcks_matrix** out);
+/* A rectangular-form matrix from pre-encoded host limbs over the extended basis: [m'][level+1][N]. */
+tcks_status tcks_matrix_import_rect(tcks_ctx* ctx, const uint64_t* diag_limbs, uint32_t rows, uint32_t cols,
+                                    uint32_t level, double scale, tcks_matrix** out);
 /* The same with each diagonal also given modulo the special prime P: [rows][level+1][N], limb
  * `level` of each diagonal modulo P (the same integer polynomial as the data limbs). Needed by the
  * double-hoisted product (TCKS_DOUBLE_HOIST). */

@@ -513,24 +513,26 @@ class OracleCKKS:
         return (self.replicate_steps(n) if n < self.slots else []) + list(range(1, mw)) + chain
 
     def vecmat_rect(self, ct: Ct, n: int, m: int, diags: list[Pt] | None = None,
-                    diags_ext: np.ndarray | None = None) -> Ct:
+                    diags_ext: np.ndarray | None = None, replicate: bool = True) -> Ct:
         """Vector x plain n x m matrix by the rectangular diagonal method: replicate, y' = sum over
         the m' = rect_width(m) diagonals of rot(ct, k) * d_k (hoisted; with one ModDown per rotation
         when `diags` is given, or once after the sum when `diags_ext` is), rescale, then
-        log2(n / m') rotate-and-adds by m' 2^j. Slots s < m hold y_s = sum_i v_i M[i][s]; the other
-        slots hold partial sums."""
+        log2(n / m') rotate-and-adds by m' 2^j. Slots s < m hold y_s = sum_i v_i M[i][s]; with the
+        input replicated over all slots (period n) every slot s holds the entry s mod m' (zero where
+        s mod m' >= m): the product comes out replicated with period m'. replicate=False: the input is
+        already replicated with period n."""
         mw = self.rect_width(m)
         if diags_ext is not None:
-            y = self._vecmat_dh_rows(ct, diags_ext, n, mw)
+            y = self._vecmat_dh_rows(ct, diags_ext, n, mw, replicate)
         else:
-            y = self._vecmat_rows(ct, diags, n, mw)
+            y = self._vecmat_rows(ct, diags, n, mw, replicate)
         for j in range(int(math.log2(n // mw))):
             y = self.add(y, self.rotate(y, mw << j))
         return y
 
-    def _vecmat_rows(self, ct: Ct, diags: list[Pt], n: int, rows: int) -> Ct:
+    def _vecmat_rows(self, ct: Ct, diags: list[Pt], n: int, rows: int, replicate: bool = True) -> Ct:
         """Replicate an n-vector, then sum_{k < rows} rot(ct, k) * d_k (hoisted), then rescale."""
-        if n < self.slots:
+        if replicate and n < self.slots:
             for st in self.replicate_steps(n):
                 ct = self.add(ct, self.rotate(ct, st))
         digits = self.modup(ct)
@@ -541,10 +543,10 @@ class OracleCKKS:
             acc = t if acc is None else self.add(acc, t)
         return self.rescale(acc)
 
-    def _vecmat_dh_rows(self, ct: Ct, diags_ext: np.ndarray, n: int, rows: int) -> Ct:
+    def _vecmat_dh_rows(self, ct: Ct, diags_ext: np.ndarray, n: int, rows: int, replicate: bool = True) -> Ct:
         """The same with the ModDown once after the sum (orc_vecmat_dh over `rows` diagonals)."""
         level = ct.level
-        if n < self.slots:
+        if replicate and n < self.slots:
             for st in self.replicate_steps(n):
                 ct = self.add(ct, self.rotate(ct, st))
         digits = self.modup(ct)
@@ -673,10 +675,12 @@ class EncodedCNN:
     fc2_ext: np.ndarray | None = None          # [64][L-4][N]
     windows: int = 64
     taps: int = 49
+    rect: bool = False                         # fully connected layers by rectangular diagonals
 
 
-def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64):
-    """Galois steps of the CNN schedule with the level each is used at (key trimming)."""
+def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64, classes=10, rect=False):
+    """Galois steps of the CNN schedule with the level each is used at (key trimming). rect: the fully
+    connected layers by rectangular diagonals (FC2 takes FC1's output as it comes, replicated)."""
     L = o.L
     need = {}
 
@@ -687,12 +691,19 @@ def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64):
                 need[s] = max(need.get(s, 0), level)
 
     use(o.conv_steps(taps, windows), L - 1)
+    if rect:
+        m1w, m2w = o.rect_width(n2), o.rect_width(classes)
+        use(o.replicate_steps(n1) + list(range(1, m1w)), L - 3)
+        use([m1w << j for j in range(int(math.log2(n1 // m1w)))], L - 4)
+        use(list(range(1, m2w)), L - 5)
+        use([m2w << j for j in range(int(math.log2(n2 // m2w)))], L - 6)
+        return need
     use(o.vecmat_steps(n1), L - 3)
     use(o.vecmat_steps(n2), L - 5)
     return need
 
 
-def cnn_encode(o: OracleCKKS, w: CNNWeights, windows=64) -> EncodedCNN:
+def cnn_encode(o: OracleCKKS, w: CNNWeights, windows=64, rect=False) -> EncodedCNN:
     L = o.L
     e = EncodedCNN(windows=windows, taps=w.conv_w.shape[1])
     for k in range(w.conv_w.shape[0]):
@@ -700,6 +711,13 @@ def cnn_encode(o: OracleCKKS, w: CNNWeights, windows=64) -> EncodedCNN:
         mask = np.zeros(o.slots)
         mask[k * windows: (k + 1) * windows] = 1.0
         e.masks.append(o.encode(mask, level=L - 1))
+    if rect:
+        e.fc1 = o.encode_matrix_rect(w.fc1_w.T, L - 3)
+        e.fc2 = o.encode_matrix_rect(w.fc2_w.T, L - 5)
+        e.fc1_ext = o.encode_matrix_rect_ext(w.fc1_w.T, L - 3)
+        e.fc2_ext = o.encode_matrix_rect_ext(w.fc2_w.T, L - 5)
+        e.rect = True
+        return e
     e.fc1 = o.encode_matrix(w.fc1_w.T, L - 3)
     e.fc2 = o.encode_matrix(w.fc2_w.T, L - 5)
     e.fc1_ext = o.encode_matrix_ext(w.fc1_w.T, L - 3)
@@ -713,7 +731,10 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
     four channel outputs with masks -> square -> FC1 (vector x plain matrix) -> square -> FC2.
     Six multiplicative levels; biases are added as plaintexts at the ciphertext's scale and level.
     double_hoist: the two vector x matrix products take the ModDown once after their rotation sums."""
-    def fc(v, diags, diags_ext, n, m):
+    def fc(v, diags, diags_ext, n, m, replicate=True):
+        if enc.rect:
+            return (o.vecmat_rect(v, n, m, diags_ext=diags_ext, replicate=replicate) if double_hoist
+                    else o.vecmat_rect(v, n, m, diags=diags, replicate=replicate))
         return o.vecmat_dh(v, diags_ext, n, m) if double_hoist else o.vecmat(v, diags, n, m)
 
     W = enc.windows
@@ -734,14 +755,18 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
     v = fc(v, enc.fc1, enc.fc1_ext, n1, m1)
     b1 = np.zeros(o.slots)
     b1[:m1] = w.fc1_b
+    if enc.rect:  # FC1's output is replicated with period rect_width(m1): so is its bias
+        b1 = np.resize(b1[:o.rect_width(m1)], o.slots)
     if trace is not None:
         trace["bias_scales"].append(v.scale)
     v = o.add_plain(v, o.encode(b1, scale=v.scale, level=v.level))
     v = o.square(v)
     n2, m2 = w.fc2_w.shape[1], w.fc2_w.shape[0]
-    v = fc(v, enc.fc2, enc.fc2_ext, n2, m2)
+    v = fc(v, enc.fc2, enc.fc2_ext, n2, m2, replicate=not enc.rect)
     b2 = np.zeros(o.slots)
     b2[:m2] = w.fc2_b
+    if enc.rect:
+        b2 = np.resize(b2[:o.rect_width(m2)], o.slots)
     if trace is not None:
         trace["bias_scales"].append(v.scale)
     v = o.add_plain(v, o.encode(b2, scale=v.scale, level=v.level))

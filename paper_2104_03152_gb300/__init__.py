@@ -92,6 +92,10 @@ _SIGS = {
     "tcks_dot": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, _vpp]),
     "tcks_dot_plain": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32, _vpp]),
     "tcks_matrix_encode": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
+    "tcks_matrix_encode_rect": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                                  _vpp]),
+    "tcks_matrix_import_rect": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                                  ctypes.c_double, _vpp]),
     "tcks_matrix_import_ext": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                                  ctypes.c_double, _vpp]),
     "tcks_ctx_set_flags": (ctypes.c_int32, [_vp, ctypes.c_uint32]),
@@ -405,6 +409,20 @@ class Context:
         a = np.ascontiguousarray(diag_limbs, dtype=np.uint64)
         h = _vp()
         check(lib().tcks_matrix_import(self.h, _p(a), rows, cols, a.shape[1], float(scale), ctypes.byref(h)))
+        return Matrix(self, h, rows, cols)
+
+    def matrix_encode_rect(self, M: np.ndarray, level: int = 0) -> "Matrix":
+        """Rectangular (hybrid) diagonals: fewer rotations; slots >= cols of the product hold partial sums."""
+        a = np.ascontiguousarray(M, dtype=np.float64)
+        h = _vp()
+        check(lib().tcks_matrix_encode_rect(self.h, _p(a), a.shape[0], a.shape[1], level, ctypes.byref(h)))
+        return Matrix(self, h, a.shape[0], a.shape[1])
+
+    def matrix_import_rect(self, diag_limbs: np.ndarray, rows: int, cols: int, scale: float) -> "Matrix":
+        """Rectangular-form diagonals over the extended basis [m'][level+1][N]."""
+        a = np.ascontiguousarray(diag_limbs, dtype=np.uint64)
+        h = _vp()
+        check(lib().tcks_matrix_import_rect(self.h, _p(a), rows, cols, a.shape[1] - 1, float(scale), ctypes.byref(h)))
         return Matrix(self, h, rows, cols)
 
     def matrix_import_ext(self, diag_limbs: np.ndarray, rows: int, cols: int, scale: float) -> "Matrix":

@@ -1046,7 +1046,36 @@ tcks_status tcks_matrix_encode(tcks_ctx* c, const double* M, uint32_t rows, uint
     check_cuda(cudaMemcpyAsync(dv.p, diag.data(), (size_t)slots * 8, cudaMemcpyHostToDevice, c->stream), "diag H2D");
     encode_into(c, (const double*)dv.p, slots, c->params.scale, l, d.p + (size_t)k * (l + 1) * c->N, true);
   }
-  *out = new tcks_matrix{c, rows, cols, l, 1, c->params.scale, d.release()};
+  *out = new tcks_matrix{c, rows, cols, l, 1, c->params.scale, d.release(), rows, 0};
+  ctx_retain(c);
+  TCKS_API_END
+}
+
+tcks_status tcks_matrix_encode_rect(tcks_ctx* c, const double* M, uint32_t rows, uint32_t cols, uint32_t level,
+                                   tcks_matrix** out) {
+  TCKS_API_BEGIN
+  if (!c || !M || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  const u32 slots = c->N / 2;
+  if (rows == 0 || cols == 0 || cols > rows || rows > slots || (rows & (rows - 1)) || slots % rows)
+    fail(TCKS_ERR_INVALID_ARG, "need cols <= rows, rows a power of two dividing N/2");
+  const u32 l = level == 0 ? c->L : level;
+  if (l < 2 || l > c->L) fail(TCKS_ERR_INVALID_ARG, "level out of range (needs >= 2 for the rescale)");
+  u32 mw = 1;
+  while (mw < cols) mw <<= 1;
+  // d_k[t] = M[(t' + k) mod n][t' mod m'] with t' = t mod n, zero where t' mod m' >= cols; period n
+  DevBuf d(c, (size_t)mw * (l + 1) * c->N);
+  DevBuf dv(c, slots);
+  std::vector<double> diag(slots);
+  for (u32 k = 0; k < mw; ++k) {
+    for (u32 t = 0; t < slots; ++t) {
+      const u32 tp = t % rows, col = tp % mw;
+      diag[t] = col < cols ? M[(size_t)((tp + k) % rows) * cols + col] : 0.0;
+    }
+    check_cuda(cudaMemcpyAsync(dv.p, diag.data(), (size_t)slots * 8, cudaMemcpyHostToDevice, c->stream), "diag H2D");
+    encode_into(c, (const double*)dv.p, slots, c->params.scale, l, d.p + (size_t)k * (l + 1) * c->N, true);
+  }
+  *out = new tcks_matrix{c, rows, cols, l, 1, c->params.scale, d.release(), mw, 1};
   ctx_retain(c);
   TCKS_API_END
 }
@@ -1064,7 +1093,7 @@ tcks_status tcks_matrix_import(tcks_ctx* c, const uint64_t* diag_limbs, uint32_t
   DevBuf d(c, words);
   check_cuda(cudaMemcpyAsync(d.p, diag_limbs, words * 8, cudaMemcpyHostToDevice, c->stream), "matrix import");
   check_cuda(cudaStreamSynchronize(c->stream), "matrix import");
-  *out = new tcks_matrix{c, rows, cols, level, 0, scale, d.release()};
+  *out = new tcks_matrix{c, rows, cols, level, 0, scale, d.release(), rows, 0};
   ctx_retain(c);
   TCKS_API_END
 }
@@ -1082,7 +1111,27 @@ tcks_status tcks_matrix_import_ext(tcks_ctx* c, const uint64_t* diag_limbs, uint
   DevBuf d(c, words);
   check_cuda(cudaMemcpyAsync(d.p, diag_limbs, words * 8, cudaMemcpyHostToDevice, c->stream), "matrix import");
   check_cuda(cudaStreamSynchronize(c->stream), "matrix import");
-  *out = new tcks_matrix{c, rows, cols, level, 1, scale, d.release()};
+  *out = new tcks_matrix{c, rows, cols, level, 1, scale, d.release(), rows, 0};
+  ctx_retain(c);
+  TCKS_API_END
+}
+
+tcks_status tcks_matrix_import_rect(tcks_ctx* c, const uint64_t* diag_limbs, uint32_t rows, uint32_t cols,
+                                    uint32_t level, double scale, tcks_matrix** out) {
+  TCKS_API_BEGIN
+  if (!c || !diag_limbs || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  const u32 slots = c->N / 2;
+  if (rows == 0 || cols == 0 || cols > rows || rows > slots || (rows & (rows - 1)) || slots % rows)
+    fail(TCKS_ERR_INVALID_ARG, "need cols <= rows, rows a power of two dividing N/2");
+  if (level < 2 || level > c->L) fail(TCKS_ERR_INVALID_ARG, "level out of range");
+  u32 mw = 1;
+  while (mw < cols) mw <<= 1;
+  const size_t words = (size_t)mw * (level + 1) * c->N;
+  DevBuf d(c, words);
+  check_cuda(cudaMemcpyAsync(d.p, diag_limbs, words * 8, cudaMemcpyHostToDevice, c->stream), "matrix import");
+  check_cuda(cudaStreamSynchronize(c->stream), "matrix import");
+  *out = new tcks_matrix{c, rows, cols, level, 1, scale, d.release(), mw, 1};
   ctx_retain(c);
   TCKS_API_END
 }

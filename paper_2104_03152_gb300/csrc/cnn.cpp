@@ -62,7 +62,7 @@ u64 cnn_resident_bytes(const tcks_cnn* m) {
   const u64 n = c->N, L = m->L;
   u64 b = (u64)m->kernels * (L + (L - 1)) * n * 8;          // conv kernels and masks
   b += ((L - 2) + (L - 4) + (L - 6)) * n * 8;                  // biases
-  b += (u64)m->fc1->rows * m->fc1->limbs() * n * 8 + (u64)m->fc2->rows * m->fc2->limbs() * n * 8;
+  b += (u64)m->fc1->diags * m->fc1->limbs() * n * 8 + (u64)m->fc2->diags * m->fc2->limbs() * n * 8;
   return b;
 }
 
@@ -498,7 +498,7 @@ tcks_status tcks_cnn_export_plaintext(const tcks_cnn* m, uint32_t kind, uint32_t
     case 3:
     case 4: {
       const tcks_matrix* M = kind == 3 ? m->fc1 : m->fc2;
-      if (index >= M->rows) fail(TCKS_ERR_INVALID_ARG, "index");
+      if (index >= M->diags) fail(TCKS_ERR_INVALID_ARG, "index");
       src = M->d + (size_t)index * M->limbs() * c->N, lv = M->level, sc = M->scale;
       break;
     }

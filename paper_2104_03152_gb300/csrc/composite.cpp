@@ -35,7 +35,7 @@ void op_sum(tcks_ctx* c, u64* ct, u32 ell) {
 static void op_vecmat_dh(tcks_ctx* c, u64* ct, u64 cw, u32 count, u32 ell, const tcks_matrix* M, const KeyTable* kt,
                          u64* out) {
   const size_t n = c->N;
-  const u32 R = M->rows - 1;
+  const u32 R = M->diags - 1;
   DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
   launch_modup(c->T, ct + (size_t)ell * n, cw, count, ell, coef.p, digits.p, c->stream);
   // chunks of rotations: enough CTAs for a few waves of 256-thread CTAs on every SM
@@ -70,20 +70,27 @@ static void op_vecmat_dh(tcks_ctx* c, u64* ct, u64 cw, u32 count, u32 ell, const
   check_launch("vecmat (double hoisted)");
 }
 
+static void vecmat_single_hoisted(tcks_ctx* c, const u64* ct, u64 cw, u32 count, u32 ell, const tcks_matrix* M,
+                                  const KeyTable* kt, u64* out);
+
 void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell, const tcks_matrix* M, u64* out) {
-  const size_t n = c->N;
   const bool dh = (c->flags & TCKS_DOUBLE_HOIST) != 0;
   if (dh && !M->ext)
     fail(TCKS_ERR_UNSUPPORTED, "double-hoisted vector x matrix needs the diagonals modulo P (tcks_matrix_encode or "
                                "tcks_matrix_import_ext)");
-  const u32 rows = M->rows;
+  const u32 rows = M->rows, diags = M->diags;
   const u32 slots = c->N / 2;
   const u64 cw = ct_words(c, ell);
   std::vector<int32_t> rep;
   for (u32 m = 0; ((u64)rows << m) < slots; ++m) rep.push_back((int32_t)(slots - (rows << m)));
   std::vector<u32> steps;
-  for (u32 k = 1; k < rows; ++k) steps.push_back(k);
+  for (u32 k = 1; k < diags; ++k) steps.push_back(k);
+  // rectangular form: the rotate-and-add chain by diags * 2^j after the rescale
+  std::vector<int32_t> chain;
+  if (M->rect)
+    for (u32 w = diags; w < rows; w <<= 1) chain.push_back((int32_t)w);
   for (int32_t s : rep) galois_key_for(c, s, ell);  // validate before launching anything
+  for (int32_t s : chain) galois_key_for(c, s, ell - 1);
   const KeyTable* kt = steps.empty() ? nullptr : &key_table(c, steps, ell);
   DevBuf ct(c, (size_t)count * cw);
   if (ct_stride == cw || count == 1) {
@@ -94,19 +101,29 @@ void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell,
                  "copy");
   }
   for (int32_t s : rep) op_rotate_add(c, ct.p, cw, count, ell, s);
-  DevBuf acc(c, (size_t)count * cw);
   if (steps.empty()) {
+    DevBuf acc(c, (size_t)count * cw);
     launch_elementwise(c->T, OP_MUL_PLAIN, ct.p, M->d, acc.p, ell, 2 * count, c->stream);
     op_rescale(c, acc.p, ell, out, count);
-    return;
-  }
-  if (dh) {
+  } else if (dh) {
     op_vecmat_dh(c, ct.p, cw, count, ell, M, kt, out);
-    return;
+  } else {
+    vecmat_single_hoisted(c, ct.p, cw, count, ell, M, kt, out);
   }
+  for (int32_t w : chain) op_rotate_add(c, out, ct_words(c, ell - 1), count, ell - 1, w);
+  check_launch("vecmat");
+}
+
+// The sum over rotations with one ModDown per rotation: ModUp once per ciphertext, then per block of
+// rotations the P-limb stage (k_ks_inner_p) and the fused ModDown + multiply-accumulate
+// (k_vecmat_acc), then the k = 0 term and the chunk partials (k_vecmat_reduce), then the rescale.
+static void vecmat_single_hoisted(tcks_ctx* c, const u64* ct, u64 cw, u32 count, u32 ell, const tcks_matrix* M,
+                                  const KeyTable* kt, u64* out) {
+  const size_t n = c->N;
+  DevBuf acc(c, (size_t)count * cw);
   DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
-  launch_modup(c->T, ct.p + (size_t)ell * n, cw, count, ell, coef.p, digits.p, c->stream);
-  const u32 R = rows - 1;
+  launch_modup(c->T, ct + (size_t)ell * n, cw, count, ell, coef.p, digits.p, c->stream);
+  const u32 R = M->diags - 1;
   const u64 per_rot = (u64)count * 2 * n;  // P-limb scratch words per rotation
   u32 RB = (u32)std::max<u64>(1, ((u64)64 << 20) / per_rot);  // 512 MB of scratch per block
   if (RB > R) RB = R;
@@ -141,7 +158,7 @@ void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell,
     v.digits = digits.p;
     v.digits_b = (u64)ell * (ell + 1) * n;
     v.top = top.p;
-    v.ct = ct.p;
+    v.ct = ct;
     v.ct_b = cw;
     v.diag = M->d + (size_t)rb0 * diag_stride;
     v.diag_stride = diag_stride;
@@ -156,7 +173,7 @@ void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell,
     check_launch("vecmat block");
   }
   VecmatPlan red{};
-  red.ct = ct.p;
+  red.ct = ct;
   red.ct_b = cw;
   red.diag = M->d;
   red.partial = partial.p;
@@ -165,7 +182,6 @@ void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell,
   red.chunks = chunks_pb;
   launch_vecmat_reduce(c->T, ell, red, acc.p, c->stream);
   op_rescale(c, acc.p, ell, out, count);
-  check_launch("vecmat");
 }
 
 // One im2col convolution kernel (§3.2): rescale(ct * kernel), then rotate-and-add by windows*2^i.

@@ -99,9 +99,11 @@ struct tcks_pt {
 struct tcks_matrix {
   tcks_ctx* ctx;
   tcks::u32 rows, cols, level;
-  tcks::u32 ext;  // 1: every diagonal also carries its limb modulo the special prime P (last)
+  tcks::u32 ext;    // 1: every diagonal also carries its limb modulo the special prime P (last)
   double scale;
-  tcks::u64* d;  // [rows][level + ext][N] encoded diagonals
+  tcks::u64* d;     // [diags][level + ext][N] encoded diagonals
+  tcks::u32 diags;  // rows (square form) or the rectangular width m' (rectangular form)
+  tcks::u32 rect;   // 1: rectangular (hybrid) diagonals, followed by log2(rows / diags) rotate-and-adds
   tcks::u32 limbs() const { return level + ext; }  // limbs per stored diagonal
 };
 

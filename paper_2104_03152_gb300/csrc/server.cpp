@@ -145,7 +145,7 @@ tcks_status tcks_server_add_vecmat(tcks_server* s, const tcks_matrix* M, uint32_
   if (!s || !M || !lane) fail(TCKS_ERR_INVALID_ARG, "null argument");
   tcks_ctx* c = M->ctx;
   add_context(s, c);
-  s->resident += (u64)M->rows * M->limbs() * c->N * 8;
+  s->resident += (u64)M->diags * M->limbs() * c->N * 8;
   const u64 req = (u64)65 * ct_words(c, M->level) * 8;
   s->lanes.push_back(Lane{false, nullptr, M, c, 1, req, nullptr, false});
   *lane = (u32)s->lanes.size() - 1;

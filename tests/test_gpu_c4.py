@@ -68,3 +68,24 @@ def test_c4_double_hoisted(c4):
         assert err < 1e-3, err
     finally:
         ctx.set_flags(tk.TCKS_AUTO_RELIN)
+
+
+def test_c4_rectangular_double_hoisted():
+    """The rectangular form at full size: 255 hoisted rotations + 4 rotate-and-adds (260 Galois keys
+    instead of 4096); batch equals single and slots < 256 decrypt to v M."""
+    ctx = tk.Context(tk.Params(14, [60, 40, 40, 60], 2.0 ** 40), seed=SEED,
+                     flags=tk.TCKS_AUTO_RELIN | tk.TCKS_DOUBLE_HOIST)
+    steps = [ctx.slots - ROWS] + list(range(1, COLS)) + [COLS << j for j in range(4)]
+    ctx.gen_galois_keys(steps)
+    M = np.random.default_rng(7).normal(0.0, 0.05, size=(ROWS, COLS))
+    mat = ctx.matrix_encode_rect(M, level=3)
+    vs = np.random.default_rng(6).normal(0.0, 1.0, size=(8, ROWS))
+    cts = []
+    for i in range(8):
+        z = np.zeros(ctx.slots)
+        z[:ROWS] = vs[i]
+        cts.append(ctx.encrypt_values(z, 800 + i))
+    outs = mat.vecmat_batch(cts)
+    assert np.array_equal(outs[3].export(), cts[3].vecmat_plain(mat).export())
+    err = max(float(np.max(np.abs(ctx.decrypt_values(outs[i])[:COLS] - vs[i] @ M))) for i in range(8))
+    assert err < 1e-3, err

@@ -98,6 +98,44 @@ def test_vecmat_double_hoisted_parity(n, m):
         g.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE)
 
 
+@pytest.mark.parametrize("n,m", [(16, 4), (64, 10), (256, 64)])
+def test_vecmat_rect_parity(n, m):
+    """Rectangular (hybrid) diagonals: with the oracle's encodings imported, bit-exact against the
+    oracle's rectangular schedule with either key-switch schedule, single and batched. Diagonals
+    encoded on the GPU decrypt to the same v M (their every slot is non-zero, so the FFT and the
+    oracle's direct sum round an encoding coefficient differently at near ties far more often than
+    for the square form, reading A9)."""
+    p = Pair(12, [55, 40, 40, 56], 2.0 ** 40)
+    o, g = p.o, p.g
+    p.add_galois(o.vecmat_rect_steps(n, m))
+    M = inputs.random_matrix(n, m, 9, 0.5)
+    cts = []
+    for i in range(2):
+        v = np.zeros(o.slots)
+        v[:n] = inputs.uniform_slots(n, 80 + i)
+        cts.append((v, o.encrypt_values(v, 510 + i)))
+    level = cts[0][1].level
+    diags = o.encode_matrix_rect(M, level)
+    ext = o.encode_matrix_rect_ext(M, level)
+    gm = g.matrix_import_rect(ext, n, m, o.scale)
+    genc = g.matrix_encode_rect(M, level=level)
+    for flags, kw in ((tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE, {"diags": diags}),
+                      (tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | tk.TCKS_DOUBLE_HOIST, {"diags_ext": ext})):
+        g.set_flags(flags)
+        try:
+            refs = [o.vecmat_rect(ct, n, m, **kw) for _, ct in cts]
+            for (v, ct), ref in zip(cts, refs):
+                got = p.import_ct(ct).vecmat_plain(gm)
+                assert_ct_equal(got, ref, f"vecmat rect {list(kw)}")
+                assert np.max(np.abs(g.decrypt_values(got)[:m] - v[:n] @ M)) < 1e-5
+                own = g.decrypt_values(p.import_ct(ct).vecmat_plain(genc))
+                assert np.max(np.abs(own[:m] - v[:n] @ M)) < 1e-5
+            for got, ref in zip(gm.vecmat_batch([p.import_ct(ct) for _, ct in cts]), refs):
+                assert_ct_equal(got, ref, "vecmat rect batch")
+        finally:
+            g.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE)
+
+
 def test_conv_parity():
     p = Pair(13, [40, 30, 30, 41], 2.0 ** 30)
     o, g = p.o, p.g

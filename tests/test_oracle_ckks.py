@@ -427,3 +427,23 @@ def test_vecmat_rect_decrypts_to_product(n, m):
     assert np.max(np.abs(b[:m] - ref)) < 1e-6
     assert np.max(np.abs(a[:m] - b[:m])) < 1e-7
     assert len(o.vecmat_rect_steps(n, m)) < len(o.vecmat_steps(n))
+
+
+def test_cnn_rect_schedule_matches_fp64():
+    """The CNN with both fully connected layers by rectangular diagonals (FC2 consuming FC1's output
+    as it comes, replicated with period 64) decrypts to the FP64 network as the square schedule does,
+    with far fewer Galois keys."""
+    o = OracleCKKS(13, [31, 26, 26, 26, 26, 26, 26, 31], 2.0 ** 26).keygen()
+    sq, rc = oracle.cnn_galois_steps(o), oracle.cnn_galois_steps(o, rect=True)
+    assert len(rc) < len(sq) // 2
+    for st, lv in rc.items():
+        o.gen_galois_key(st, lv)
+    w = oracle.CNNWeights(**inputs.cnn_weights(4))
+    enc = oracle.cnn_encode(o, w, rect=True)
+    img = inputs.mnist_like_image(3)
+    v, _ = OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+    ct = o.encrypt_values(v, 77)
+    plain = oracle.cnn_plain(img, w)
+    for dh in (False, True):
+        logits = o.decrypt_values(oracle.cnn_forward(o, ct, w, enc, double_hoist=dh), 10)
+        assert np.max(np.abs(logits - plain)) < 5e-3
