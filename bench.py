@@ -34,7 +34,7 @@ METRIC = "encrypted-CNN inferences/s + p99 latency (served vs plain); NTT/keyswi
 LOG_N, BITS, SCALE = 13, [31, 26, 26, 26, 26, 26, 26, 31], 2.0 ** 26
 SEED_IMG, SEED_W, SEED_ENC = 3, 4, 77
 WORKLOAD = ("encrypted MNIST-shaped CNN (conv 4x7x7/3 -> sq -> FC256->64 -> sq -> FC64->10), CKKS N=8192, "
-            "primes [31,26x6|31], scale 2^26, 264 trimmed Galois keys")
+            "primes [31,26x6|31], scale 2^26, Galois keys trimmed to their levels")
 
 
 # ----------------------------------------------------------------------------- distributed --
@@ -162,13 +162,14 @@ def source_digest() -> str:
 
 
 # ---------------------------------------------------------------------------------- GPU arm --
-def gpu_setup(torch, batch, double_hoist):
+def gpu_setup(torch, batch, double_hoist, rect=False):
     import paper_2104_03152_gb300 as tk
     from paper_2104_03152_gb300 import inputs
 
     tk.lib(build_if_missing=True)
     stream = torch.cuda.Stream()
-    flags = tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | (tk.TCKS_DOUBLE_HOIST if double_hoist else 0)
+    flags = (tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | (tk.TCKS_DOUBLE_HOIST if double_hoist else 0)
+             | (tk.TCKS_RECT_DIAG if rect else 0))
     ctx = tk.Context(tk.Params(LOG_N, BITS, SCALE), seed=inputs.SEED_KEYS, flags=flags, stream=stream.cuda_stream)
     w = inputs.cnn_weights(SEED_W)
     model = tk.CNN(ctx, w["conv_w"], w["conv_b"], w["fc1_w"], w["fc1_b"], w["fc2_w"], w["fc2_b"], windows=64)
@@ -197,7 +198,8 @@ def timed(torch, stream, fn, steps):
 def run_gpu(args, world, rank, local):
     torch = dist_init(world, local)
     B = args.batch
-    tk, ctx, model, cts, stream, imgs, w = gpu_setup(torch, B, args.double_hoist)
+    rect = args.fc_form == "rect"
+    tk, ctx, model, cts, stream, imgs, w = gpu_setup(torch, B, args.double_hoist, rect)
     # correctness guard: the decrypted logits of every request must match the FP64 network, and the
     # batched outputs must equal the single-request path bit for bit
     outs = model.forward_batch(cts)
@@ -252,14 +254,26 @@ def run_gpu(args, world, rank, local):
     e2e_s = reduce_max(world, time.perf_counter() - t0)
     # the same batched step with one ModDown per rotation (the schedule bit-identical to rotating
     # each diagonal's ciphertext separately), for comparison
-    single = None
+    single = {}
+    base = tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE
+    dh_flag = tk.TCKS_DOUBLE_HOIST if args.double_hoist else 0
+
+    def time_model(mdl, label):
+        mdl.forward_batch(cts)
+        _, tot = timed(torch, stream, lambda: mdl.forward_batch(cts), 3)
+        single[label] = {"value": B * 3 / (tot / 1e3), "unit": "inferences/s", "ms_per_step": tot / 3}
+    form = "rectangular" if rect else "square"
     if args.double_hoist:
-        ctx.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE)
-        model.forward_batch(cts)
-        t_single, tot_single = timed(torch, stream, lambda: model.forward_batch(cts), 3)
-        single = {"value": B * 3 / (tot_single / 1e3), "unit": "inferences/s", "ms_per_step": tot_single / 3,
-                  "schedule": "one ModDown per rotation"}
-        ctx.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | tk.TCKS_DOUBLE_HOIST)
+        ctx.set_flags(base)
+        time_model(model, f"{form} FC layers, one ModDown per rotation")
+        ctx.set_flags(base | dh_flag)
+    if rect:  # the square-diagonal network on the same context
+        ctx.set_flags(base | dh_flag)
+        sq = tk.CNN(ctx, w["conv_w"], w["conv_b"], w["fc1_w"], w["fc1_b"], w["fc2_w"], w["fc2_b"], windows=64)
+        sq.gen_keys()
+        time_model(sq, "square FC layers" + (", ModDown once after each rotation sum" if args.double_hoist
+                                              else ", one ModDown per rotation"))
+        del sq
     c4 = run_c4(torch, tk, args) if args.c4 else None
     serving = None
     if args.serve_seconds > 0:
@@ -296,7 +310,7 @@ def run_gpu(args, world, rank, local):
     word = 32 if max(ctx.primes) < 2 ** 31 else 64
     bfly_peak = tk.calibrate_butterflies(word)
     primitives = primitives_summary(torch, tk) if args.primitives else None
-    return dict(single=single, c4=c4, primitives=primitives, bfly_peak=bfly_peak, word=word, serving=serving, total_ms=total_ms, per_step=per_step, prof=prof, launches=launches, clocks=clk, e2e_s=e2e_s,
+    return dict(galois_keys=len(model.galois_steps()), single=single, c4=c4, primitives=primitives, bfly_peak=bfly_peak, word=word, serving=serving, total_ms=total_ms, per_step=per_step, prof=prof, launches=launches, clocks=clk, e2e_s=e2e_s,
                 e2e_steps=e2e_steps, h2d=host_in.nbytes, d2h=host_out.nbytes, max_err=max_err,
                 plain_ms=plain_total / plain_steps, plain_times=plain_times)
 
@@ -606,25 +620,26 @@ def primitives_summary(torch, tk):
 
 
 # ------------------------------------------------------------------------------ CPU oracle --
-def oracle_setup():
+def oracle_setup(rect: bool = True):
     import oracle
     from paper_2104_03152_gb300 import inputs
 
     o = oracle.OracleCKKS(LOG_N, BITS, SCALE, key_seed=inputs.SEED_KEYS).keygen()
-    for st, lv in oracle.cnn_galois_steps(o).items():
+    for st, lv in oracle.cnn_galois_steps(o, rect=rect).items():
         o.gen_galois_key(st, lv)
     w = oracle.CNNWeights(**inputs.cnn_weights(SEED_W))
-    enc = oracle.cnn_encode(o, w)
+    enc = oracle.cnn_encode(o, w, rect=rect)
     img = inputs.mnist_like_image(SEED_IMG)
     v, _ = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
     ct = o.encrypt_values(v, SEED_ENC)
     return oracle, o, w, enc, ct
 
 
-def time_oracle(n_steps: int, warmup: int, double_hoist: bool = True, single_thread_steps: int = 0):
+def time_oracle(n_steps: int, warmup: int, double_hoist: bool = True, single_thread_steps: int = 0,
+                rect: bool = True):
     """Oracle CNN inferences on the host cores (same schedule as the GPU arm); optionally also
     single-threaded ones. Returns (times, cores, single-thread times)."""
-    oracle, o, w, enc, ct = oracle_setup()
+    oracle, o, w, enc, ct = oracle_setup(rect)
     for _ in range(warmup):
         oracle.cnn_forward(o, ct, w, enc, double_hoist=double_hoist)
     times = []
@@ -649,7 +664,7 @@ def run_reference(args, world, rank):
         return
     steps, warmup = args.steps, args.warmup
     # bound the run: at most ~3 minutes of oracle inferences
-    times, cores, _ = time_oracle(steps, warmup, bool(args.double_hoist))
+    times, cores, _ = time_oracle(steps, warmup, bool(args.double_hoist), 0, args.fc_form == "rect")
     total = sum(times)
     value = steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": args.gpus,
@@ -681,6 +696,8 @@ def main():
     ap.add_argument("--sweep-ops", default=",".join(SWEEP_OPS), help="ops of the sweep")
     ap.add_argument("--sweep-mixed", type=int, default=1, help="also run the mixed (N, L) batches")
     ap.add_argument("--primitives", type=int, default=1, help="add the NTT / key-switch rates at N=2^16, L=32")
+    ap.add_argument("--fc-form", default="rect", choices=["rect", "square"],
+                    help="diagonal form of the CNN's fully connected layers")
     ap.add_argument("--double-hoist", type=int, default=1,
                     help="vector x matrix products take the ModDown once after the rotation sum (1) or per rotation (0)")
     ap.add_argument("--c4", type=int, default=1, help="time the 4096x256 vector x matrix workload (64 vectors)")
@@ -731,7 +748,7 @@ def main():
     per = sorted(r["per_step"])
     # CPU baseline: the oracle on the host cores, bounded sample
     if args.cpu_sample > 0:
-        times, cores, single = time_oracle(args.cpu_sample, 0, bool(args.double_hoist), 1)
+        times, cores, single = time_oracle(args.cpu_sample, 0, bool(args.double_hoist), 1, args.fc_form == "rect")
         cpu_val = len(times) / sum(times)
     else:
         times, cores, cpu_val, single = [], 0, None, []
@@ -739,9 +756,11 @@ def main():
         "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "batch": B,
+        "config": {"workload": WORKLOAD, "batch": B, "galois_keys": r["galois_keys"],
                    "vecmat_schedule": ("ModDown once after each rotation sum (double hoisting)" if args.double_hoist
                                        else "one ModDown per rotation"),
+                   "fc_form": ("rectangular diagonals: FC1 63 + 2 rotations, FC2 15 + 2 (no replication)"
+                               if args.fc_form == "rect" else "square diagonals: FC1 255 rotations, FC2 63"),
                    "l2": "inputs larger than L2 (Galois keys ~0.75 GB + key-switch scratch streamed per step)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "latency_ms": {"p50": per[len(per) // 2], "p99": per[min(len(per) - 1, int(0.99 * len(per)))],
@@ -760,7 +779,7 @@ def main():
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
         "serving": r["serving"],
         "primitives": r["primitives"],
-        "single_hoisted": r["single"],
+        "compare": r["single"],
         "vecmat_4096x256": r["c4"],
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],

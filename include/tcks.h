@@ -99,7 +99,12 @@ tcks_status tcks_params_primes(const tcks_params* p, uint64_t* primes, uint32_t 
  * method of §3.1 with the same rotations and the same hoisted decomposition; the result decrypts to
  * the same product with less rounding noise, but its limbs differ from the per-rotation schedule).
  * The matrix must carry its diagonals modulo P (tcks_matrix_encode does; see tcks_matrix_import_ext). */
-enum { TCKS_AUTO_RELIN = 1u, TCKS_AUTO_RESCALE = 2u, TCKS_DOUBLE_HOIST = 4u };
+/* TCKS_RECT_DIAG, read by tcks_cnn_create: the network's two fully connected layers use rectangular
+ * diagonals (tcks_matrix_encode_rect): FC1 takes 63 hoisted rotations and 2 rotate-and-adds instead
+ * of 255 rotations, its output comes out replicated with period 64 and feeds FC2 without the
+ * replication rotations, and FC2 takes 15 + 2. The biases are laid out replicated to match; the
+ * network needs the Galois steps tcks_cnn_galois_steps reports for this layout. */
+enum { TCKS_AUTO_RELIN = 1u, TCKS_AUTO_RESCALE = 2u, TCKS_DOUBLE_HOIST = 4u, TCKS_RECT_DIAG = 8u };
 tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32_t flags,
                                 const tcks_allocator* allocator, void* cuda_stream, tcks_ctx** out);
 void tcks_ctx_free(tcks_ctx* ctx);
@@ -108,7 +113,7 @@ tcks_status tcks_ctx_info(const tcks_ctx* ctx, uint32_t* log_n, uint32_t* n_data
 tcks_status tcks_ctx_key_bytes(const tcks_ctx* ctx, uint64_t* bytes);
 /* Wait for all work queued on the context's stream. */
 tcks_status tcks_ctx_synchronize(tcks_ctx* ctx);
-/* Replace the context's flags (TCKS_AUTO_RELIN | TCKS_AUTO_RESCALE | TCKS_DOUBLE_HOIST) for the calls
+/* Replace the context's flags (TCKS_AUTO_RELIN | TCKS_AUTO_RESCALE | TCKS_DOUBLE_HOIST | TCKS_RECT_DIAG) for the calls
  * that follow; work already queued or captured in a graph keeps the flags it was issued with. */
 tcks_status tcks_ctx_set_flags(tcks_ctx* ctx, uint32_t flags);
 
@@ -383,7 +388,9 @@ tcks_status tcks_cnn_graph_create(const tcks_cnn* m, uint32_t count, tcks_cnn_gr
 tcks_status tcks_cnn_graph_run(tcks_cnn_graph* g, const tcks_ct* const* in, tcks_ct** outs);
 void tcks_cnn_graph_free(tcks_cnn_graph* g);
 /* Export one of the model's encoded plaintexts (kind 0 conv kernel, 1 channel mask, 2 bias
- * (index 0..2), 3 FC1 diagonal, 4 FC2 diagonal) to host [level][N]; level / scale are reported. */
+ * (index 0..2), 3 FC1 diagonal, 4 FC2 diagonal, 5 / 6 the FC1 / FC2 diagonal over the extended basis,
+ * its limb modulo P last) to host [level][N] ([level+1][N] for kinds 5, 6); level / scale are
+ * reported (the data level). */
 tcks_status tcks_cnn_export_plaintext(const tcks_cnn* m, uint32_t kind, uint32_t index, uint64_t* host,
                                       size_t n_words, uint32_t* level, double* scale);
 

@@ -676,6 +676,7 @@ class EncodedCNN:
     windows: int = 64
     taps: int = 49
     rect: bool = False                         # fully connected layers by rectangular diagonals
+    biases: list | None = None                 # pre-encoded biases (Pt) in place of encoding them here
 
 
 def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64, classes=10, rect=False):
@@ -749,7 +750,12 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
         bias[k * W: (k + 1) * W] = w.conv_b[k]
     if trace is not None:
         trace["bias_scales"] = [v.scale]
-    v = o.add_plain(v, o.encode(bias, scale=v.scale, level=v.level))
+    def bias_pt(i, values, v):
+        if enc.biases is not None:
+            return enc.biases[i]
+        return o.encode(values, scale=v.scale, level=v.level)
+
+    v = o.add_plain(v, bias_pt(0, bias, v))
     v = o.square(v)
     n1, m1 = w.fc1_w.shape[1], w.fc1_w.shape[0]
     v = fc(v, enc.fc1, enc.fc1_ext, n1, m1)
@@ -759,7 +765,7 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
         b1 = np.resize(b1[:o.rect_width(m1)], o.slots)
     if trace is not None:
         trace["bias_scales"].append(v.scale)
-    v = o.add_plain(v, o.encode(b1, scale=v.scale, level=v.level))
+    v = o.add_plain(v, bias_pt(1, b1, v))
     v = o.square(v)
     n2, m2 = w.fc2_w.shape[1], w.fc2_w.shape[0]
     v = fc(v, enc.fc2, enc.fc2_ext, n2, m2, replicate=not enc.rect)
@@ -769,7 +775,7 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
         b2 = np.resize(b2[:o.rect_width(m2)], o.slots)
     if trace is not None:
         trace["bias_scales"].append(v.scale)
-    v = o.add_plain(v, o.encode(b2, scale=v.scale, level=v.level))
+    v = o.add_plain(v, bias_pt(2, b2, v))
     return v
 
 

@@ -268,8 +268,8 @@ void tcks_ctx::dev_free(void* p) {
   if (!p) return;
   if (has_alloc)
     alloc.free(p, (void*)stream, alloc.user);
-  else
-    cudaFreeAsync(p, stream);
+  else if (cudaFreeAsync(p, stream) != cudaSuccess)
+    cudaGetLastError();  // a release has no caller to report to; keep it out of the next launch check
 }
 
 void tcks_ctx::keys_changed() {
@@ -476,6 +476,7 @@ static void ctx_destroy(tcks_ctx* c) {
   cudaStreamSynchronize(c->stream);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
+  cudaGetLastError();  // clean-up statuses are not reported: leave no error behind for later calls
 }
 
 extern "C" {
@@ -506,7 +507,8 @@ tcks_status tcks_ctx_synchronize(tcks_ctx* c) {
 tcks_status tcks_ctx_set_flags(tcks_ctx* c, uint32_t flags) {
   TCKS_API_BEGIN
   if (!c) fail(TCKS_ERR_INVALID_ARG, "null context");
-  if (flags & ~(u32)(TCKS_AUTO_RELIN | TCKS_AUTO_RESCALE | TCKS_DOUBLE_HOIST)) fail(TCKS_ERR_INVALID_ARG, "unknown flag");
+  if (flags & ~(u32)(TCKS_AUTO_RELIN | TCKS_AUTO_RESCALE | TCKS_DOUBLE_HOIST | TCKS_RECT_DIAG))
+    fail(TCKS_ERR_INVALID_ARG, "unknown flag");
   c->flags = flags;
   TCKS_API_END
 }

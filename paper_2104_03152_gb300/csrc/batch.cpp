@@ -210,6 +210,7 @@ void tcks_batch_graph_free(tcks_batch_graph* g) {
   if (g->graph) cudaGraphDestroy(g->graph);
   for (tcks_ctx* c : g->ctxs) ctx_release(c);
   delete g;
+  cudaGetLastError();  // clean-up statuses are not reported
 }
 
 tcks_status tcks_batch_graph_create(const tcks_batch_job* jobs, uint32_t n_jobs, tcks_batch_graph** out) {

@@ -31,6 +31,7 @@ struct tcks_cnn {
   tcks_matrix* fc1;          // level L-3
   tcks_matrix* fc2;          // level L-5
   double out_scale;
+  bool rect;                 // rectangular FC layers: FC1's output comes replicated and feeds FC2 as is
 };
 
 namespace tcks {
@@ -145,7 +146,7 @@ void cnn_stage(const tcks_cnn* m, u32 stage, const u64* x, u32 count, u64* out) 
       square_stage(c, x, L - 4, count, out);
       break;
     case 4:
-      op_vecmat(c, x, ct_words(c, L - 5), count, L - 5, m->fc2, out);
+      op_vecmat(c, x, ct_words(c, L - 5), count, L - 5, m->fc2, out, m->rect);
       launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[2], out, L - 6, 2 * count, c->stream);
       break;
     default:
@@ -240,6 +241,7 @@ tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* con
   m->classes = classes;
   m->L = L;
   m->in_scale = c->params.scale;
+  m->rect = (c->flags & TCKS_RECT_DIAG) != 0;
   m->bias[0] = m->bias[1] = m->bias[2] = nullptr;
   m->fc1 = m->fc2 = nullptr;
   const double delta = c->params.scale;
@@ -266,9 +268,10 @@ tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* con
     for (u32 o = 0; o < hidden; ++o) M1[(size_t)i * hidden + o] = fc1_w[(size_t)o * n1 + i];
   for (u32 i = 0; i < hidden; ++i)
     for (u32 o = 0; o < classes; ++o) M2[(size_t)i * classes + o] = fc2_w[(size_t)o * hidden + i];
-  tcks_status st = tcks_matrix_encode(c, M1.data(), n1, hidden, L - 3, &m->fc1);
+  auto enc_m = m->rect ? tcks_matrix_encode_rect : tcks_matrix_encode;
+  tcks_status st = enc_m(c, M1.data(), n1, hidden, L - 3, &m->fc1);
   if (st != TCKS_OK) fail(st, tcks_last_error_detail());
-  st = tcks_matrix_encode(c, M2.data(), hidden, classes, L - 5, &m->fc2);
+  st = enc_m(c, M2.data(), hidden, classes, L - 5, &m->fc2);
   if (st != TCKS_OK) fail(st, tcks_last_error_detail());
   double s_pack, s_fc1, s_fc2;
   schedule_scales(m, m->in_scale, delta, &s_pack, &s_fc1, &s_fc2);
@@ -280,11 +283,14 @@ tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* con
   for (u32 k = 0; k < kernels; ++k)
     for (u32 w = 0; w < windows; ++w) lay[(size_t)k * windows + w] = conv_b[k];
   m->bias[0] = encode_host(lay, s_pack, L - 2);
+  // rectangular layers leave their outputs replicated with period m' (hidden, then the power of two
+  // above classes): the biases are laid out the same way
+  const u32 p1 = m->rect ? m->fc1->diags : slots, p2 = m->rect ? m->fc2->diags : slots;
   std::fill(lay.begin(), lay.end(), 0.0);
-  for (u32 o = 0; o < hidden; ++o) lay[o] = fc1_b[o];
+  for (u32 t = 0; t < slots; ++t) lay[t] = t % p1 < hidden && t < (m->rect ? slots : hidden) ? fc1_b[t % p1] : 0.0;
   m->bias[1] = encode_host(lay, s_fc1, L - 4);
   std::fill(lay.begin(), lay.end(), 0.0);
-  for (u32 o = 0; o < classes; ++o) lay[o] = fc2_b[o];
+  for (u32 t = 0; t < slots; ++t) lay[t] = t % p2 < classes && t < (m->rect ? slots : classes) ? fc2_b[t % p2] : 0.0;
   m->bias[2] = encode_host(lay, s_fc2, L - 6);
   *out = m;
   m = nullptr;
@@ -312,9 +318,16 @@ tcks_status tcks_cnn_galois_steps(const tcks_cnn* m, int32_t* steps, uint32_t* l
   for (int i = 0; i < ceil_log2(m->taps); ++i) use(m->windows << i, L - 1);
   const u32 n1 = m->kernels * m->windows, n2 = m->hidden;
   for (u32 r = 0; ((u64)n1 << r) < slots; ++r) use(slots - (n1 << r), L - 3);
-  for (u32 k = 1; k < n1; ++k) use(k, L - 3);
-  for (u32 r = 0; ((u64)n2 << r) < slots; ++r) use(slots - (n2 << r), L - 5);
-  for (u32 k = 1; k < n2; ++k) use(k, L - 5);
+  if (m->rect) {  // m' - 1 rotations, then the rotate-and-add chain after the rescale; FC2 unreplicated
+    for (u32 k = 1; k < m->fc1->diags; ++k) use(k, L - 3);
+    for (u32 w = m->fc1->diags; w < n1; w <<= 1) use(w, L - 4);
+    for (u32 k = 1; k < m->fc2->diags; ++k) use(k, L - 5);
+    for (u32 w = m->fc2->diags; w < n2; w <<= 1) use(w, L - 6);
+  } else {
+    for (u32 k = 1; k < n1; ++k) use(k, L - 3);
+    for (u32 r = 0; ((u64)n2 << r) < slots; ++r) use(slots - (n2 << r), L - 5);
+    for (u32 k = 1; k < n2; ++k) use(k, L - 5);
+  }
   *count = (u32)need.size();
   if (steps && levels) {
     if (cap < need.size()) fail(TCKS_ERR_INVALID_ARG, "capacity too small");
@@ -400,6 +413,7 @@ void tcks_cnn_graph_free(tcks_cnn_graph* g) {
   c->dev_free(g->out);
   delete g;
   ctx_release(c);
+  cudaGetLastError();  // clean-up statuses are not reported
 }
 
 tcks_status tcks_cnn_graph_create(const tcks_cnn* m, uint32_t count, tcks_cnn_graph** out) {
@@ -496,10 +510,12 @@ tcks_status tcks_cnn_export_plaintext(const tcks_cnn* m, uint32_t kind, uint32_t
       src = m->bias[index], lv = m->L - 2 - 2 * index, sc = m->bias_scale[index];
       break;
     case 3:
-    case 4: {
-      const tcks_matrix* M = kind == 3 ? m->fc1 : m->fc2;
+    case 4:
+    case 5:
+    case 6: {
+      const tcks_matrix* M = (kind == 3 || kind == 5) ? m->fc1 : m->fc2;
       if (index >= M->diags) fail(TCKS_ERR_INVALID_ARG, "index");
-      src = M->d + (size_t)index * M->limbs() * c->N, lv = M->level, sc = M->scale;
+      src = M->d + (size_t)index * M->limbs() * c->N, lv = kind >= 5 ? M->limbs() : M->level, sc = M->scale;
       break;
     }
     default: fail(TCKS_ERR_INVALID_ARG, "kind");

@@ -73,7 +73,8 @@ static void op_vecmat_dh(tcks_ctx* c, u64* ct, u64 cw, u32 count, u32 ell, const
 static void vecmat_single_hoisted(tcks_ctx* c, const u64* ct, u64 cw, u32 count, u32 ell, const tcks_matrix* M,
                                   const KeyTable* kt, u64* out);
 
-void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell, const tcks_matrix* M, u64* out) {
+void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell, const tcks_matrix* M, u64* out,
+               bool input_replicated) {
   const bool dh = (c->flags & TCKS_DOUBLE_HOIST) != 0;
   if (dh && !M->ext)
     fail(TCKS_ERR_UNSUPPORTED, "double-hoisted vector x matrix needs the diagonals modulo P (tcks_matrix_encode or "
@@ -82,7 +83,8 @@ void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell,
   const u32 slots = c->N / 2;
   const u64 cw = ct_words(c, ell);
   std::vector<int32_t> rep;
-  for (u32 m = 0; ((u64)rows << m) < slots; ++m) rep.push_back((int32_t)(slots - (rows << m)));
+  if (!input_replicated)
+    for (u32 m = 0; ((u64)rows << m) < slots; ++m) rep.push_back((int32_t)(slots - (rows << m)));
   std::vector<u32> steps;
   for (u32 k = 1; k < diags; ++k) steps.push_back(k);
   // rectangular form: the rotate-and-add chain by diags * 2^j after the rescale

@@ -176,7 +176,9 @@ void encode_into(tcks_ctx* c, const double* d_v, size_t n, double scale, u32 lev
 // composite.cpp
 void op_sum(tcks_ctx* c, u64* ct, u32 ell);  // in place
 // count ciphertexts ct + i * ct_stride at level ell -> out [count][2][ell-1][N]
-void op_vecmat(tcks_ctx* c, const u64* ct, u64 ct_stride, u32 count, u32 ell, const tcks_matrix* M, u64* out);
+// input_replicated: the input already holds the vector replicated with period M->rows (skip replication)
+void op_vecmat(tcks_ctx* c, const u64* ct, u64 ct_stride, u32 count, u32 ell, const tcks_matrix* M, u64* out,
+               bool input_replicated = false);
 void op_conv(tcks_ctx* c, const u64* ct, u32 ell, const u64* kernel_pt, u32 taps, u32 windows, u64* out);
 
 }  // namespace tcks

@@ -868,6 +868,7 @@ extern "C" tcks_status tcks_rescale_noalloc(tcks_ctx* ctx, const uint64_t* d_in,
                           " exceeds the static scratch, which holds two limbs of at most N = 2^14");
   if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
     return abi_record(TCKS_ERR_INVALID_ARG, "rescale_noalloc: device index out of range");
+  drop_stale_cuda_error();  // report only this call's launches
   std::string why;
   u64* scratch = noalloc_setup(ctx->device, &why);
   if (!scratch) return abi_record(TCKS_ERR_CUDA, "rescale_noalloc: " + why);

@@ -124,6 +124,7 @@ void tcks_server_free(tcks_server* s) {
     delete kv.second;
   }
   delete s;
+  cudaGetLastError();  // clean-up statuses are not reported
 }
 
 tcks_status tcks_server_add_cnn(tcks_server* s, const tcks_cnn* m, uint32_t* lane) {

@@ -124,3 +124,59 @@ def test_cnn_double_hoisted_parity(setup):
             assert np.array_equal(b1.export(), s1)
     finally:
         ctx.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE)
+
+
+def _near_tie_agreement(o, got: np.ndarray, ref: np.ndarray, level: int):
+    """Two encodings of the same values agree, or differ in integer coefficients by at most 1 (the
+    FFT and the oracle's direct sum round a near-tie coefficient differently, reading A9)."""
+    if np.array_equal(got, ref):
+        return 0
+    a = np.array(o.crt_compose(o.intt_limbs(got, level), level), dtype=object)
+    b = np.array(o.crt_compose(o.intt_limbs(ref, level), level), dtype=object)
+    d = np.abs(a - b)
+    assert d.max() <= 1
+    return int((d != 0).sum())
+
+
+def test_cnn_rect_parity(setup):
+    """Rectangular fully connected layers (TCKS_RECT_DIAG): the Galois steps, the encodings (equal to
+    the oracle's up to A9 near ties; the dense rectangular diagonals meet far more of them), and, run
+    on the same plaintexts, the forward pass bit-identical to the oracle's schedule with either
+    key-switch schedule, batched and single alike."""
+    o, w, enc, ctx, model, need = setup
+    base = tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE
+    ctx.set_flags(base | tk.TCKS_RECT_DIAG)
+    try:
+        rm = tk.CNN(ctx, w.conv_w, w.conv_b, w.fc1_w, w.fc1_b, w.fc2_w, w.fc2_b, windows=64)
+    finally:
+        ctx.set_flags(base)
+    assert rm.galois_steps() == oracle.cnn_galois_steps(o, rect=True)
+    renc = oracle.cnn_encode(o, w, rect=True)
+    L = o.L
+    # the model's own plaintexts, checked against the oracle's, then fed to the oracle's schedule
+    renc.fc1 = [oracle.Pt(rm.export_plaintext(3, i)[0], L - 3, o.scale) for i in range(64)]
+    renc.fc2 = [oracle.Pt(rm.export_plaintext(4, i)[0], L - 5, o.scale) for i in range(16)]
+    ext1 = np.stack([rm.export_plaintext(5, i)[0] for i in range(64)])
+    ext2 = np.stack([rm.export_plaintext(6, i)[0] for i in range(16)])
+    own1 = o.encode_matrix_rect_ext(w.fc1_w.T, L - 3)
+    ties = sum(_near_tie_agreement(o, ext1[i][:L - 3], own1[i][:L - 3], L - 3) for i in range(0, 64, 9))
+    print(f"rectangular FC1 diagonals: {ties} near-tie coefficients in 8 sampled diagonals")
+    renc.fc1_ext, renc.fc2_ext = ext1, ext2
+    renc.biases = []
+    for i in range(3):
+        data, sc = rm.export_plaintext(2, i)
+        renc.biases.append(oracle.Pt(data, L - 2 - 2 * i, sc))
+    img = inputs.mnist_like_image(5)
+    v, W = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+    ct = o.encrypt_values(v, 79)
+    for dh in (False, True):
+        ctx.set_flags(base | (tk.TCKS_DOUBLE_HOIST if dh else 0))
+        try:
+            ref = oracle.cnn_forward(o, ct, w, renc, double_hoist=dh)
+            got = rm.forward(ctx.ct_import(ct.data, ct.scale))
+            assert_ct_equal(got, ref, f"cnn forward (rectangular, double hoist {dh})")
+            assert float(np.max(np.abs(ctx.decrypt_values(got, 10) - oracle.cnn_plain(img, w)))) < 5e-3
+            b = rm.forward_batch([ctx.ct_import(ct.data, ct.scale)] * 2)
+            assert np.array_equal(b[1].export(), got.export())
+        finally:
+            ctx.set_flags(base)
