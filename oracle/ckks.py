@@ -560,6 +560,42 @@ class OracleCKKS:
                             P(np.ascontiguousarray(diags_ext)), ptrs, P(lv), P(ge), P(out))
         return self.rescale(Ct(out, level, ct.scale * self.scale))
 
+    def rotsum_dh(self, ct: Ct, steps) -> Ct:
+        """ct + sum over `steps` of rot(ct, s), hoisted with one ModDown after the sum: orc_vecmat_dh
+        with every diagonal the constant polynomial 1 (all ones in NTT form over the extended basis),
+        rotation k taking steps[k - 1]. No rescale: the scale is unchanged."""
+        steps = list(steps)
+        level = ct.level
+        rows = len(steps) + 1
+        ones = np.ones((rows, level + 1, self.N), dtype=np.uint64)
+        digits = self.modup(ct)
+        keys = [self._key(st) for st in steps]
+        key_arrs = [np.ascontiguousarray(k.data) for k in keys]
+        ptrs = (_u64p * max(1, len(keys)))(*[P(a) for a in key_arrs])
+        lv = np.array([k.level for k in keys] or [0], dtype=np.uint32)
+        ge = np.array([self.galois_elt(st) for st in steps] or [1], dtype=np.uint32)
+        out = np.zeros((2, level, self.N), dtype=np.uint64)
+        lib().orc_vecmat_dh(self._ctx, P(np.ascontiguousarray(ct.data)), P(digits), level, rows, P(ones), ptrs, P(lv),
+                            P(ge), P(out))
+        return Ct(out, level, ct.scale)
+
+    @staticmethod
+    def conv_bsgs_steps(taps: int, windows: int) -> tuple[list[int], list[int]]:
+        """Baby and giant steps of the hoisted convolution sum: the 2^ceil(log2 taps) tap positions
+        t = b + B g (b < B, g < G) with B = 2^floor(e/2), G = 2^ceil(e/2)."""
+        e = (taps - 1).bit_length()
+        nb, ng = 1 << (e // 2), 1 << (e - e // 2)
+        return [windows * b for b in range(1, nb)], [windows * nb * g for g in range(1, ng)]
+
+    def conv2d_im2col_hoisted(self, ct: Ct, kernel_pt: Pt, taps: int, windows: int) -> Ct:
+        """The im2col convolution with its rotate-and-add chain replaced by two hoisted rotation sums
+        (baby steps, then giant steps), each with one ModDown: rescale(ct * kernel), then
+        x1 = sum_{b < B} rot(x, windows b), x2 = sum_{g < G} rot(x1, windows B g); the same sum over
+        all 2^ceil(log2 taps) taps as the chain."""
+        x = self.rescale(self.mul_plain(ct, kernel_pt))
+        baby, giant = self.conv_bsgs_steps(taps, windows)
+        return self.rotsum_dh(self.rotsum_dh(x, baby), giant)
+
     def encode_matrix_ext(self, M: np.ndarray, level: int) -> np.ndarray:
         """The diagonals over the extended basis: [n][level+1][N]."""
         return np.stack([self.encode_ext(d, level) for d in self.matrix_diagonals(np.asarray(M, dtype=np.float64))])
@@ -677,9 +713,10 @@ class EncodedCNN:
     taps: int = 49
     rect: bool = False                         # fully connected layers by rectangular diagonals
     biases: list | None = None                 # pre-encoded biases (Pt) in place of encoding them here
+    conv_hoist: bool = False                   # convolution sums by hoisted baby-step giant-step rotation sums
 
 
-def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64, classes=10, rect=False):
+def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64, classes=10, rect=False, conv_hoist=False):
     """Galois steps of the CNN schedule with the level each is used at (key trimming). rect: the fully
     connected layers by rectangular diagonals (FC2 takes FC1's output as it comes, replicated)."""
     L = o.L
@@ -691,7 +728,11 @@ def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64, classes=
             if s:
                 need[s] = max(need.get(s, 0), level)
 
-    use(o.conv_steps(taps, windows), L - 1)
+    if conv_hoist:
+        baby, giant = o.conv_bsgs_steps(taps, windows)
+        use(baby + giant, L - 1)
+    else:
+        use(o.conv_steps(taps, windows), L - 1)
     if rect:
         m1w, m2w = o.rect_width(n2), o.rect_width(classes)
         use(o.replicate_steps(n1) + list(range(1, m1w)), L - 3)
@@ -704,9 +745,9 @@ def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64, classes=
     return need
 
 
-def cnn_encode(o: OracleCKKS, w: CNNWeights, windows=64, rect=False) -> EncodedCNN:
+def cnn_encode(o: OracleCKKS, w: CNNWeights, windows=64, rect=False, conv_hoist=False) -> EncodedCNN:
     L = o.L
-    e = EncodedCNN(windows=windows, taps=w.conv_w.shape[1])
+    e = EncodedCNN(windows=windows, taps=w.conv_w.shape[1], conv_hoist=conv_hoist)
     for k in range(w.conv_w.shape[0]):
         e.conv.append(o.encode(o.kernel_slots(w.conv_w[k], windows), level=L))
         mask = np.zeros(o.slots)
@@ -740,7 +781,8 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
 
     W = enc.windows
     K = len(enc.conv)
-    chans = [o.conv2d_im2col_pt(ct, enc.conv[k], enc.taps, W) for k in range(K)]
+    conv = o.conv2d_im2col_hoisted if enc.conv_hoist else o.conv2d_im2col_pt
+    chans = [conv(ct, enc.conv[k], enc.taps, W) for k in range(K)]
     v = None
     for k in range(K):
         t = o.rescale(o.mul_plain(chans[k], enc.masks[k]))

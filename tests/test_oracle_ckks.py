@@ -447,3 +447,41 @@ def test_cnn_rect_schedule_matches_fp64():
     for dh in (False, True):
         logits = o.decrypt_values(oracle.cnn_forward(o, ct, w, enc, double_hoist=dh), 10)
         assert np.max(np.abs(logits - plain)) < 5e-3
+
+
+def test_rotsum_and_hoisted_conv():
+    """A hoisted rotation sum (one ModDown) decrypts to the plain sum of rotations and agrees with the
+    chain of single rotations within the key-switch noise; the baby-step giant-step convolution sums the
+    same 64 tap positions as the rotate-and-add chain."""
+    o = OracleCKKS(12, [55, 40, 40, 56], 2.0 ** 40).keygen()
+    steps = [3, 17, 100, 1000]
+    o.gen_galois_keys(steps)
+    z = inputs.uniform_slots(o.slots, 21)
+    ct = o.encrypt_values(z, 50)
+    got = o.decrypt_values(o.rotsum_dh(ct, steps))
+    ref = z + sum(np.roll(z, -s) for s in steps)
+    assert np.max(np.abs(got - ref)) < 1e-6
+    chain = ct
+    for s in steps:
+        chain = o.add(chain, o.rotate(ct, s))
+    assert np.max(np.abs(o.decrypt_values(chain) - got)) < 1e-7
+    baby, giant = OracleCKKS.conv_bsgs_steps(49, 64)
+    assert baby == [64 * b for b in range(1, 8)] and giant == [512 * g for g in range(1, 8)]
+    sums = sorted(b + g for b in [0] + baby for g in [0] + giant)
+    assert sums == [64 * t for t in range(64)]
+
+
+def test_cnn_hoisted_conv_schedule_matches_fp64():
+    """The CNN with the hoisted baby-step giant-step convolution sums and rectangular FC layers decrypts to
+    the FP64 network."""
+    o = OracleCKKS(13, [31, 26, 26, 26, 26, 26, 26, 31], 2.0 ** 26).keygen()
+    steps = oracle.cnn_galois_steps(o, rect=True, conv_hoist=True)
+    for st, lv in steps.items():
+        o.gen_galois_key(st, lv)
+    w = oracle.CNNWeights(**inputs.cnn_weights(4))
+    enc = oracle.cnn_encode(o, w, rect=True, conv_hoist=True)
+    img = inputs.mnist_like_image(3)
+    v, _ = OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+    ct = o.encrypt_values(v, 77)
+    logits = o.decrypt_values(oracle.cnn_forward(o, ct, w, enc, double_hoist=True), 10)
+    assert np.max(np.abs(logits - oracle.cnn_plain(img, w))) < 5e-3
