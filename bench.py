@@ -162,14 +162,14 @@ def source_digest() -> str:
 
 
 # ---------------------------------------------------------------------------------- GPU arm --
-def gpu_setup(torch, batch, double_hoist, rect=False):
+def gpu_setup(torch, batch, double_hoist, rect=False, conv_hoist=False):
     import paper_2104_03152_gb300 as tk
     from paper_2104_03152_gb300 import inputs
 
     tk.lib(build_if_missing=True)
     stream = torch.cuda.Stream()
     flags = (tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | (tk.TCKS_DOUBLE_HOIST if double_hoist else 0)
-             | (tk.TCKS_RECT_DIAG if rect else 0))
+             | (tk.TCKS_RECT_DIAG if rect else 0) | (tk.TCKS_CONV_HOIST if conv_hoist else 0))
     ctx = tk.Context(tk.Params(LOG_N, BITS, SCALE), seed=inputs.SEED_KEYS, flags=flags, stream=stream.cuda_stream)
     w = inputs.cnn_weights(SEED_W)
     model = tk.CNN(ctx, w["conv_w"], w["conv_b"], w["fc1_w"], w["fc1_b"], w["fc2_w"], w["fc2_b"], windows=64)
@@ -199,7 +199,7 @@ def run_gpu(args, world, rank, local):
     torch = dist_init(world, local)
     B = args.batch
     rect = args.fc_form == "rect"
-    tk, ctx, model, cts, stream, imgs, w = gpu_setup(torch, B, args.double_hoist, rect)
+    tk, ctx, model, cts, stream, imgs, w = gpu_setup(torch, B, args.double_hoist, rect, bool(args.conv_hoist))
     # correctness guard: the decrypted logits of every request must match the FP64 network, and the
     # batched outputs must equal the single-request path bit for bit
     outs = model.forward_batch(cts)
@@ -263,17 +263,22 @@ def run_gpu(args, world, rank, local):
         _, tot = timed(torch, stream, lambda: mdl.forward_batch(cts), 3)
         single[label] = {"value": B * 3 / (tot / 1e3), "unit": "inferences/s", "ms_per_step": tot / 3}
     form = "rectangular" if rect else "square"
+    conv = "hoisted convolution sums" if args.conv_hoist else "rotate-and-add convolution chain"
     if args.double_hoist:
         ctx.set_flags(base)
-        time_model(model, f"{form} FC layers, one ModDown per rotation")
+        time_model(model, f"{form} FC layers, {conv}, one ModDown per FC rotation")
         ctx.set_flags(base | dh_flag)
-    if rect:  # the square-diagonal network on the same context
+
+    def other(flags, label):  # another network layout on the same context
+        ctx.set_flags(base | dh_flag | flags)
+        alt = tk.CNN(ctx, w["conv_w"], w["conv_b"], w["fc1_w"], w["fc1_b"], w["fc2_w"], w["fc2_b"], windows=64)
         ctx.set_flags(base | dh_flag)
-        sq = tk.CNN(ctx, w["conv_w"], w["conv_b"], w["fc1_w"], w["fc1_b"], w["fc2_w"], w["fc2_b"], windows=64)
-        sq.gen_keys()
-        time_model(sq, "square FC layers" + (", ModDown once after each rotation sum" if args.double_hoist
-                                              else ", one ModDown per rotation"))
-        del sq
+        alt.gen_keys()
+        time_model(alt, label)
+    if args.conv_hoist:
+        other(tk.TCKS_RECT_DIAG if rect else 0, f"{form} FC layers, rotate-and-add convolution chain")
+    if rect:
+        other(0, "square FC layers, rotate-and-add convolution chain")
     c4 = run_c4(torch, tk, args) if args.c4 else None
     serving = None
     if args.serve_seconds > 0:
@@ -620,15 +625,15 @@ def primitives_summary(torch, tk):
 
 
 # ------------------------------------------------------------------------------ CPU oracle --
-def oracle_setup(rect: bool = True):
+def oracle_setup(rect: bool = True, conv_hoist: bool = True):
     import oracle
     from paper_2104_03152_gb300 import inputs
 
     o = oracle.OracleCKKS(LOG_N, BITS, SCALE, key_seed=inputs.SEED_KEYS).keygen()
-    for st, lv in oracle.cnn_galois_steps(o, rect=rect).items():
+    for st, lv in oracle.cnn_galois_steps(o, rect=rect, conv_hoist=conv_hoist).items():
         o.gen_galois_key(st, lv)
     w = oracle.CNNWeights(**inputs.cnn_weights(SEED_W))
-    enc = oracle.cnn_encode(o, w, rect=rect)
+    enc = oracle.cnn_encode(o, w, rect=rect, conv_hoist=conv_hoist)
     img = inputs.mnist_like_image(SEED_IMG)
     v, _ = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
     ct = o.encrypt_values(v, SEED_ENC)
@@ -636,10 +641,10 @@ def oracle_setup(rect: bool = True):
 
 
 def time_oracle(n_steps: int, warmup: int, double_hoist: bool = True, single_thread_steps: int = 0,
-                rect: bool = True):
+                rect: bool = True, conv_hoist: bool = True):
     """Oracle CNN inferences on the host cores (same schedule as the GPU arm); optionally also
     single-threaded ones. Returns (times, cores, single-thread times)."""
-    oracle, o, w, enc, ct = oracle_setup(rect)
+    oracle, o, w, enc, ct = oracle_setup(rect, conv_hoist)
     for _ in range(warmup):
         oracle.cnn_forward(o, ct, w, enc, double_hoist=double_hoist)
     times = []
@@ -664,7 +669,8 @@ def run_reference(args, world, rank):
         return
     steps, warmup = args.steps, args.warmup
     # bound the run: at most ~3 minutes of oracle inferences
-    times, cores, _ = time_oracle(steps, warmup, bool(args.double_hoist), 0, args.fc_form == "rect")
+    times, cores, _ = time_oracle(steps, warmup, bool(args.double_hoist), 0, args.fc_form == "rect",
+                                  bool(args.conv_hoist))
     total = sum(times)
     value = steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": args.gpus,
@@ -698,6 +704,8 @@ def main():
     ap.add_argument("--primitives", type=int, default=1, help="add the NTT / key-switch rates at N=2^16, L=32")
     ap.add_argument("--fc-form", default="rect", choices=["rect", "square"],
                     help="diagonal form of the CNN's fully connected layers")
+    ap.add_argument("--conv-hoist", type=int, default=1,
+                    help="the convolution sums as hoisted baby-step giant-step rotation sums (1) or a chain (0)")
     ap.add_argument("--double-hoist", type=int, default=1,
                     help="vector x matrix products take the ModDown once after the rotation sum (1) or per rotation (0)")
     ap.add_argument("--c4", type=int, default=1, help="time the 4096x256 vector x matrix workload (64 vectors)")
@@ -748,7 +756,8 @@ def main():
     per = sorted(r["per_step"])
     # CPU baseline: the oracle on the host cores, bounded sample
     if args.cpu_sample > 0:
-        times, cores, single = time_oracle(args.cpu_sample, 0, bool(args.double_hoist), 1, args.fc_form == "rect")
+        times, cores, single = time_oracle(args.cpu_sample, 0, bool(args.double_hoist), 1, args.fc_form == "rect",
+                                           bool(args.conv_hoist))
         cpu_val = len(times) / sum(times)
     else:
         times, cores, cpu_val, single = [], 0, None, []
@@ -761,6 +770,8 @@ def main():
                                        else "one ModDown per rotation"),
                    "fc_form": ("rectangular diagonals: FC1 63 + 2 rotations, FC2 15 + 2 (no replication)"
                                if args.fc_form == "rect" else "square diagonals: FC1 255 rotations, FC2 63"),
+                   "conv_form": ("two hoisted rotation sums (7 baby + 7 giant steps, one ModDown each)"
+                                 if args.conv_hoist else "rotate-and-add chain (6 key switches)"),
                    "l2": "inputs larger than L2 (Galois keys ~0.75 GB + key-switch scratch streamed per step)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "latency_ms": {"p50": per[len(per) // 2], "p99": per[min(len(per) - 1, int(0.99 * len(per)))],

@@ -104,7 +104,11 @@ tcks_status tcks_params_primes(const tcks_params* p, uint64_t* primes, uint32_t 
  * of 255 rotations, its output comes out replicated with period 64 and feeds FC2 without the
  * replication rotations, and FC2 takes 15 + 2. The biases are laid out replicated to match; the
  * network needs the Galois steps tcks_cnn_galois_steps reports for this layout. */
-enum { TCKS_AUTO_RELIN = 1u, TCKS_AUTO_RESCALE = 2u, TCKS_DOUBLE_HOIST = 4u, TCKS_RECT_DIAG = 8u };
+/* TCKS_CONV_HOIST, read by tcks_cnn_create: the convolution's rotate-and-add chain over the
+ * 2^ceil(log2 taps) tap positions becomes two hoisted rotation sums (tcks_rotate_sum_hoisted), first
+ * over the baby steps windows*b (b < B), then over the giant steps windows*B*g (g < G), B G = 2^e,
+ * B = 2^floor(e/2): 14 key switches with one ModUp and one ModDown per sum instead of 6 full ones. */
+enum { TCKS_AUTO_RELIN = 1u, TCKS_AUTO_RESCALE = 2u, TCKS_DOUBLE_HOIST = 4u, TCKS_RECT_DIAG = 8u, TCKS_CONV_HOIST = 16u };
 tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32_t flags,
                                 const tcks_allocator* allocator, void* cuda_stream, tcks_ctx** out);
 void tcks_ctx_free(tcks_ctx* ctx);
@@ -113,14 +117,15 @@ tcks_status tcks_ctx_info(const tcks_ctx* ctx, uint32_t* log_n, uint32_t* n_data
 tcks_status tcks_ctx_key_bytes(const tcks_ctx* ctx, uint64_t* bytes);
 /* Wait for all work queued on the context's stream. */
 tcks_status tcks_ctx_synchronize(tcks_ctx* ctx);
-/* Replace the context's flags (TCKS_AUTO_RELIN | TCKS_AUTO_RESCALE | TCKS_DOUBLE_HOIST | TCKS_RECT_DIAG) for the calls
+/* Replace the context's flags (any of the TCKS_* flags above) for the calls
  * that follow; work already queued or captured in a graph keeps the flags it was issued with. */
 tcks_status tcks_ctx_set_flags(tcks_ctx* ctx, uint32_t flags);
 
 /* Galois keys for left rotations by `steps` (§2.1, used by rotate / sum / dot / matmul_plain /
  * conv2d_im2col). A step is taken modulo N/2; step 0 needs no key. max_level in [1, L] trims each
- * key to the digits and limbs needed by ciphertexts at levels <= max_level (0 = L). Regenerating a
- * step replaces its key. */
+ * key to the digits and limbs needed by ciphertexts at levels <= max_level (0 = L). A step that already
+ * has a key of at least that level keeps it (a trimmed key holds exactly the first digits and limbs of
+ * the longer one); a shorter existing key is replaced. */
 tcks_status tcks_gen_galois_keys(tcks_ctx* ctx, const int32_t* steps, uint32_t n_steps, uint32_t max_level);
 tcks_status tcks_has_galois_key(const tcks_ctx* ctx, int32_t step, uint32_t* key_level);
 
@@ -224,6 +229,11 @@ tcks_status tcks_rotate(const tcks_ct* a, int32_t step, tcks_ct** out);
 /* Several rotations of one ciphertext sharing one decomposition of c1 (hoisting). outs[i] receives
  * the rotation by steps[i]; results are bit-identical to tcks_rotate. */
 tcks_status tcks_rotate_hoisted(const tcks_ct* a, const int32_t* steps, uint32_t n_steps, tcks_ct** outs);
+
+/* a + sum over steps of rot(a, steps[i]) with the rotations hoisted and the key switch's division by P
+ * taken once, after the sum (one ModUp and one ModDown for all the steps). Every step needs its Galois
+ * key; step 0 is rejected (the identity term is always included). The scale is unchanged. */
+tcks_status tcks_rotate_sum_hoisted(const tcks_ct* a, const int32_t* steps, uint32_t n_steps, tcks_ct** out);
 
 /* ----------------------------------------------------------------- composite ops (§3.1) ---- */
 /* Rotate-and-add over all N/2 slots (slots >= n must be zero): every slot receives the total.

@@ -19,6 +19,7 @@ TCKS_AUTO_RELIN = 1
 TCKS_AUTO_RESCALE = 2
 TCKS_DOUBLE_HOIST = 4
 TCKS_RECT_DIAG = 8
+TCKS_CONV_HOIST = 16
 KEY_SECRET, KEY_PUBLIC, KEY_RELIN, KEY_GALOIS = 0, 1, 2, 3
 
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -136,6 +137,7 @@ _SIGS = {
     "tcks_ct_serialized_size": (ctypes.c_int32, [_vp, _u64p]),
     "tcks_ct_serialize": (ctypes.c_int32, [_vp, ctypes.c_void_p, ctypes.c_uint64, _u64p]),
     "tcks_ct_deserialize": (ctypes.c_int32, [_vp, ctypes.c_void_p, ctypes.c_uint64, _vpp]),
+    "tcks_rotate_sum_hoisted": (ctypes.c_int32, [_vp, _i32p, ctypes.c_uint32, _vpp]),
     "tcks_batch_run": (ctypes.c_int32, [_vp, ctypes.c_uint32]),
     "tcks_batch_graph_create": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vpp]),
     "tcks_batch_graph_run": (ctypes.c_int32, [_vp]),
@@ -578,6 +580,11 @@ class Ciphertext:
 
     def rotate(self, step: int):
         return self._unary(lib().tcks_rotate, step)
+
+    def rotate_sum_hoisted(self, steps):
+        """self + sum of rot(self, s) over steps, one ModUp and one ModDown for all of them."""
+        st = np.ascontiguousarray(list(steps), dtype=np.int32)
+        return self._unary(lib().tcks_rotate_sum_hoisted, _p(st), len(st))
 
     def rotate_hoisted(self, steps) -> list:
         s = np.ascontiguousarray(list(steps), dtype=np.int32)

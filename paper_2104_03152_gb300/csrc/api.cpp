@@ -507,7 +507,7 @@ tcks_status tcks_ctx_synchronize(tcks_ctx* c) {
 tcks_status tcks_ctx_set_flags(tcks_ctx* c, uint32_t flags) {
   TCKS_API_BEGIN
   if (!c) fail(TCKS_ERR_INVALID_ARG, "null context");
-  if (flags & ~(u32)(TCKS_AUTO_RELIN | TCKS_AUTO_RESCALE | TCKS_DOUBLE_HOIST | TCKS_RECT_DIAG))
+  if (flags & ~(u32)(TCKS_AUTO_RELIN | TCKS_AUTO_RESCALE | TCKS_DOUBLE_HOIST | TCKS_RECT_DIAG | TCKS_CONV_HOIST))
     fail(TCKS_ERR_INVALID_ARG, "unknown flag");
   c->flags = flags;
   TCKS_API_END
@@ -524,6 +524,8 @@ tcks_status tcks_gen_galois_keys(tcks_ctx* c, const int32_t* steps, uint32_t n_s
     if (k == 0) continue;
     auto it = c->galois.find(k);
     if (it != c->galois.end()) {
+      // a trimmed key is a prefix of the longer one (same sampler counters): keep the longer key
+      if (it->second.K >= K) continue;
       c->dev_free(it->second.d);
       c->galois.erase(it);
     }
@@ -977,6 +979,27 @@ tcks_status tcks_rotate_hoisted(const tcks_ct* a, const int32_t* steps, uint32_t
 }
 
 // --------------------------------------------------------------------------- composites ----
+tcks_status tcks_rotate_sum_hoisted(const tcks_ct* a, const int32_t* steps, uint32_t n_steps, tcks_ct** out) {
+  TCKS_API_BEGIN
+  if (!a || !out || (n_steps && !steps)) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  tcks_ctx* c = a->ctx;
+  std::vector<int32_t> st(steps, steps + n_steps);
+  for (int32_t s : st) {  // validate before launching anything
+    if (!step_mod(c, s)) fail(TCKS_ERR_INVALID_ARG, "a rotation sum step of 0 (the identity is always included)");
+    galois_key_for(c, s, a->level);
+  }
+  tcks_ct* r = new_ct(c, a->level, a->scale);
+  try {
+    op_rotsum_hoisted(c, a->d, ct_words(c, a->level), 1, a->level, st, r->d);
+  } catch (...) {
+    free_ct(r);
+    throw;
+  }
+  *out = r;
+  TCKS_API_END
+}
+
 tcks_status tcks_sum(const tcks_ct* a, uint32_t n, tcks_ct** out) {
   TCKS_API_BEGIN
   if (!a || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");

@@ -32,6 +32,8 @@ struct tcks_cnn {
   tcks_matrix* fc2;          // level L-5
   double out_scale;
   bool rect;                 // rectangular FC layers: FC1's output comes replicated and feeds FC2 as is
+  bool conv_hoist;           // the convolution sums as two hoisted rotation sums (baby and giant steps)
+  std::vector<int32_t> baby, giant;
 };
 
 namespace tcks {
@@ -122,8 +124,13 @@ void cnn_stage(const tcks_cnn* m, u32 stage, const u64* x, u32 count, u64* out) 
           op_rescale(c, prod.p, L, chans.p + (size_t)k * count * w1, count);
         }
       }
-      const int rsteps = ceil_log2(m->taps);
-      for (int i = 0; i < rsteps; ++i) op_rotate_add(c, chans.p, w1, K * count, L - 1, (int32_t)(m->windows << i));
+      if (m->conv_hoist) {
+        op_rotsum_hoisted(c, chans.p, w1, K * count, L - 1, m->baby, chans.p);
+        op_rotsum_hoisted(c, chans.p, w1, K * count, L - 1, m->giant, chans.p);
+      } else {
+        const int rsteps = ceil_log2(m->taps);
+        for (int i = 0; i < rsteps; ++i) op_rotate_add(c, chans.p, w1, K * count, L - 1, (int32_t)(m->windows << i));
+      }
       // pack [L-2] + bias
       DevBuf prod(c, (size_t)count * w1), t(c, (size_t)count * w2);
       for (u32 k = 0; k < K; ++k) {
@@ -242,6 +249,14 @@ tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* con
   m->L = L;
   m->in_scale = c->params.scale;
   m->rect = (c->flags & TCKS_RECT_DIAG) != 0;
+  m->conv_hoist = (c->flags & TCKS_CONV_HOIST) != 0;
+  {
+    // tap positions t = b + B g over 2^ceil(log2 taps): B = 2^floor(e/2) baby steps, G = 2^ceil(e/2)
+    const int e = ceil_log2(taps);
+    const u32 nb = 1u << (e / 2), ng = 1u << (e - e / 2);
+    for (u32 b = 1; b < nb; ++b) m->baby.push_back((int32_t)(windows * b));
+    for (u32 g = 1; g < ng; ++g) m->giant.push_back((int32_t)(windows * nb * g));
+  }
   m->bias[0] = m->bias[1] = m->bias[2] = nullptr;
   m->fc1 = m->fc2 = nullptr;
   const double delta = c->params.scale;
@@ -315,7 +330,12 @@ tcks_status tcks_cnn_galois_steps(const tcks_cnn* m, int32_t* steps, uint32_t* l
       }
     need.push_back({s, lv});
   };
-  for (int i = 0; i < ceil_log2(m->taps); ++i) use(m->windows << i, L - 1);
+  if (m->conv_hoist) {
+    for (int32_t s : m->baby) use((u32)s, L - 1);
+    for (int32_t s : m->giant) use((u32)s, L - 1);
+  } else {
+    for (int i = 0; i < ceil_log2(m->taps); ++i) use(m->windows << i, L - 1);
+  }
   const u32 n1 = m->kernels * m->windows, n2 = m->hidden;
   for (u32 r = 0; ((u64)n1 << r) < slots; ++r) use(slots - (n1 << r), L - 3);
   if (m->rect) {  // m' - 1 rotations, then the rotate-and-add chain after the rescale; FC2 unreplicated

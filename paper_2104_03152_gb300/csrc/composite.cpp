@@ -73,6 +73,56 @@ static void op_vecmat_dh(tcks_ctx* c, u64* ct, u64 cw, u32 count, u32 ell, const
 static void vecmat_single_hoisted(tcks_ctx* c, const u64* ct, u64 cw, u32 count, u32 ell, const tcks_matrix* M,
                                   const KeyTable* kt, u64* out);
 
+// x + sum over `steps` of rot(x, s) for `count` ciphertexts [count][2][ell][N] (stride cw), with one
+// ModUp and one ModDown per ciphertext: the double-hoisted accumulation with unit diagonals. out may
+// alias x. The scale is unchanged.
+void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const std::vector<int32_t>& steps, u64* out) {
+  const size_t n = c->N;
+  std::vector<u32> ks;
+  for (int32_t s : steps) {
+    const u32 k = step_mod(c, s);
+    if (!k) fail(TCKS_ERR_INVALID_ARG, "a rotation sum step of 0 (the identity is always included)");
+    ks.push_back(k);
+  }
+  if (ks.empty()) {
+    if (out != x)
+      for (u32 i = 0; i < count; ++i)
+        check_cuda(cudaMemcpyAsync(out + i * cw, x + i * cw, ct_words(c, ell) * 8, cudaMemcpyDeviceToDevice, c->stream),
+                   "copy");
+    return;
+  }
+  const KeyTable& kt = key_table(c, ks, ell);
+  const u32 R = (u32)ks.size();
+  DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
+  launch_modup(c->T, x + (size_t)ell * n, cw, count, ell, coef.p, digits.p, c->stream);
+  const u64 base = vecmat_dh_base_ctas(c->params.log_n, ell, count, c->T.narrow), want = 152ull * 8 * 4;
+  u32 chunks = (u32)std::min<u64>(R, std::max<u64>(1, (want + base - 1) / base));
+  const u32 chunk = (R + chunks - 1) / chunks;
+  chunks = (R + chunk - 1) / chunk;
+  DevBuf partial(c, (size_t)count * chunks * 3 * (ell + 1) * n);
+  VecmatDhPlan p{};
+  p.keys = kt.d;
+  p.digits = digits.p;
+  p.digits_b = (u64)ell * (ell + 1) * n;
+  p.ct = x;
+  p.ct_b = cw;
+  p.diag = nullptr;  // unit diagonals
+  p.partial = partial.p;
+  p.R = R;
+  p.B = count;
+  p.chunk = chunk;
+  p.chunks = chunks;
+  launch_vecmat_dh_acc(c->T, ell, p, c->stream);
+  launch_vecmat_dh_fold(c->T, ell, p, c->stream);
+  DevBuf top(c, (size_t)2 * count * n);
+  const u64 per_rq = (u64)chunks * 3 * (ell + 1) * n;
+  for (u32 b = 0; b < 2; ++b)
+    launch_ntt(c->T, true, partial.p + ((u64)b * (ell + 1) + ell) * n, per_rq, top.p + (u64)b * count * n, n, count,
+               c->L, 1, c->stream);
+  launch_vecmat_dh_moddown(c->T, ell, p, top.p, out, cw, c->stream);
+  check_launch("hoisted rotation sum");
+}
+
 void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell, const tcks_matrix* M, u64* out,
                bool input_replicated) {
   const bool dh = (c->flags & TCKS_DOUBLE_HOIST) != 0;

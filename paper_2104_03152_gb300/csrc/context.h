@@ -180,5 +180,6 @@ void op_sum(tcks_ctx* c, u64* ct, u32 ell);  // in place
 void op_vecmat(tcks_ctx* c, const u64* ct, u64 ct_stride, u32 count, u32 ell, const tcks_matrix* M, u64* out,
                bool input_replicated = false);
 void op_conv(tcks_ctx* c, const u64* ct, u32 ell, const u64* kernel_pt, u32 taps, u32 windows, u64* out);
+void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const std::vector<int32_t>& steps, u64* out);
 
 }  // namespace tcks

@@ -32,12 +32,20 @@ template <>
 struct DhAcc<u32> {
   typename Ew<u32>::Acc a;
   __device__ __forceinline__ void mac(u64 x, u64 y) { a.mac(x, y); }
+  __device__ __forceinline__ void add(u64 x) { a.mac(x, 1); }
   __device__ __forceinline__ u64 get(const ModConst& m) const { return a.get(m); }
 };
 template <>
 struct DhAcc<u64> {
   u64 lo = 0, hi = 0;
   u32 top = 0;
+  __device__ __forceinline__ void add(u64 x) {
+    const u64 l = lo + x;
+    const u64 h = hi + (l < x);
+    top += h < hi;
+    lo = l;
+    hi = h;
+  }
   __device__ __forceinline__ void mac(u64 x, u64 y) {
     const u64 plo = x * y, phi = __umul64hi(x, y);
     const u64 l = lo + plo;
@@ -85,10 +93,11 @@ __global__ void __launch_bounds__(kDhThreads) k_vecmat_dh_acc(DevTables T, u32 e
   const u32 base = eb * kDhThreads * EPT + threadIdx.x;
   DhAcc<W> u0[EPT][RPT], u1[EPT][RPT], a0[EPT][RPT];
   const u32 r0 = chunk * p.chunk, r1 = min(p.R, r0 + p.chunk);
+  const bool unit = p.diag == nullptr;  // a hoisted rotation sum: every diagonal is 1
   for (u32 r = r0; r < r1; ++r) {
     const KsKey kk = p.keys[r];
     const u32 key_slot = i < ell ? i : kk.K;
-    const u64* dk = p.diag + (u64)(r + 1) * p.diag_stride + (u64)(i < ell ? i : p.p_limb) * n;
+    const u64* dk = unit ? nullptr : p.diag + (u64)(r + 1) * p.diag_stride + (u64)(i < ell ? i : p.p_limb) * n;
     const u64* k0 = kk.key + (u64)key_slot * n;     // digit j's component b at + (2j + b) (K+1) n
     const u64 kstep = (u64)(kk.K + 1) * n;
 #pragma unroll
@@ -106,12 +115,21 @@ __global__ void __launch_bounds__(kDhThreads) k_vecmat_dh_acc(DevTables T, u32 e
             s1[rr].mac(d, w1);
           }
         }
-        const u64 dv = dk[g];
+        if (unit) {
 #pragma unroll
-        for (int rr = 0; rr < RPT; ++rr) {
-          u0[e][rr].mac(s0[rr].get(m), dv);
-          u1[e][rr].mac(s1[rr].get(m), dv);
-          if (i < ell) a0[e][rr].mac(c0[rr][src], dv);
+          for (int rr = 0; rr < RPT; ++rr) {
+            u0[e][rr].add(s0[rr].get(m));
+            u1[e][rr].add(s1[rr].get(m));
+            if (i < ell) a0[e][rr].add(c0[rr][src]);
+          }
+        } else {
+          const u64 dv = dk[g];
+#pragma unroll
+          for (int rr = 0; rr < RPT; ++rr) {
+            u0[e][rr].mac(s0[rr].get(m), dv);
+            u1[e][rr].mac(s1[rr].get(m), dv);
+            if (i < ell) a0[e][rr].mac(c0[rr][src], dv);
+          }
         }
       }
     }
@@ -172,12 +190,12 @@ __global__ void k_vecmat_dh_moddown(DevTables T, u32 ell, const __grid_constant_
   const u64* U = p.partial + dh_off(rq, 0, p.chunks, b, i, ell, log_n);
   const u64* A = p.partial + dh_off(rq, 0, p.chunks, 2, i, ell, log_n);
   const u64* cb = p.ct + rq * p.ct_b + ((u64)b * ell + i) * n;
-  const u64* d0 = p.diag + (u64)i * n;
+  const u64* d0 = p.diag ? p.diag + (u64)i * n : nullptr;  // unit diagonals: c_b itself
   u64* dst = out + rq * out_b + ((u64)b * ell + i) * n;
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
     const u32 g = sl.off + k;
     u64 v = Ew<W>::shoup_inv(sub_mod(U[g], Ar<W>::fwd_out(s[sw(k)], mi), mi.q), pc, mi);
-    v = add_mod(v, Ew<W>::mul(cb[g], d0[g], mi), mi.q);
+    v = add_mod(v, d0 ? Ew<W>::mul(cb[g], d0[g], mi) : cb[g], mi.q);
     if (b == 0) v = add_mod(v, A[g], mi.q);
     dst[g] = v;
   }
@@ -197,7 +215,8 @@ u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow) {
 void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st) {
   const double n = (double)(1u << T.log_n);
   const double by = 8.0 * n *
-                    ((double)p.B * (ell * (ell + 1.0) + ell) + (double)p.R * (2.0 * ell * (ell + 1.0) + ell + 1.0) +
+                    ((double)p.B * (ell * (ell + 1.0) + ell) +
+                     (double)p.R * (2.0 * ell * (ell + 1.0) + (p.diag ? ell + 1.0 : 0.0)) +
                      (double)p.B * p.chunks * (3.0 * ell + 2.0));
   const double ops = (double)p.B * p.R * n * ((ell + 1.0) * (2.0 * ell + 4.0) + ell);
   Launch L(K_VECMAT_DH, st, by, ops);

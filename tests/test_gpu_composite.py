@@ -136,6 +136,30 @@ def test_vecmat_rect_parity(n, m):
             g.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE)
 
 
+@pytest.mark.parametrize("chain", ["40-bit", "narrow"])
+def test_rotate_sum_hoisted_parity(chain):
+    """The hoisted rotation sum (one ModUp, one ModDown) bit-exact against the oracle, 64-bit and 32-bit
+    words, and within the key-switch noise of the plain sum of rotations."""
+    if chain == "40-bit":
+        p = Pair(12, [55, 40, 40, 56], 2.0 ** 40)
+    else:
+        p = Pair(13, [31, 26, 26, 26, 26, 26, 26, 31], 2.0 ** 26)
+    o, g = p.o, p.g
+    steps = [64 * b for b in range(1, 8)]
+    p.add_galois(steps)
+    z = inputs.uniform_slots(o.slots, 33)
+    ct = o.encrypt_values(z, 90)
+    ref = o.rotsum_dh(ct, steps)
+    got = p.import_ct(ct).rotate_sum_hoisted(steps)
+    assert_ct_equal(got, ref, "rotate_sum_hoisted")
+    plain = z + sum(np.roll(z, -s) for s in steps)
+    # scale 2^40 vs 2^26: the fresh-encryption noise of the 8 summed copies, about 4e-4 per slot each at 2^26
+    assert np.max(np.abs(g.decrypt_values(got) - plain)) < (1e-6 if chain == "40-bit" else 1e-2)
+    with pytest.raises(tk.TcksError) as e:
+        p.import_ct(ct).rotate_sum_hoisted([0])
+    assert e.value.name == "INVALID_ARG"
+
+
 def test_conv_parity():
     p = Pair(13, [40, 30, 30, 41], 2.0 ** 30)
     o, g = p.o, p.g
