@@ -138,26 +138,30 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-def ncu_traffic(kernel: str):
-    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on the current sources."""
+def ncu_traffic(kernel: str, config: dict):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary (profiles/ncu_traffic.json),
+    if it was taken on the current sources of the files that define and launch the kernel and on the
+    same bench configuration; None otherwise."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
     ent = d.get("kernels", {}).get(kernel)
-    if not ent or ent.get("src_sha") != source_digest():
+    if not ent or ent.get("src_sha") != source_digest(ent.get("files", [])):
+        return None
+    if any(config.get(k) != v for k, v in ent.get("config", {}).items()):
         return None
     return ent.get("dram_bytes_per_launch")
 
 
-def source_digest() -> str:
+def source_digest(files) -> str:
+    """sha256 (16 hex digits) over the named files of the library's csrc directory, in order."""
     import hashlib
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_2104_03152_gb300", "csrc")
-    for f in sorted(os.listdir(src)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(f.encode())
-            h.update(open(os.path.join(src, f), "rb").read())
+    for f in files:
+        h.update(f.encode())
+        h.update(open(os.path.join(src, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -246,10 +250,10 @@ def run_gpu(args, world, rank, local):
     t0 = time.perf_counter()
     e2e_steps = max(3, args.steps // 2)
     for _ in range(e2e_steps):
-        cin = [ctx.ct_import(host_in[i], cts[i].scale) for i in range(B)]
+        cin = ctx.ct_import_batch(host_in, cts[0].scale)
         couts = model.forward_batch(cin)
-        for i, co in enumerate(couts):
-            tk.check(tk.lib().tcks_ct_export(co.h, tk._p(host_out[i]), out_words))
+        handles = (tk._vp * B)(*[co.h.value for co in couts])
+        tk.check(tk.lib().tcks_ct_export_batch(handles, B, tk._p(host_out), host_out.size))
     torch.cuda.synchronize()
     e2e_s = reduce_max(world, time.perf_counter() - t0)
     # the same batched step with one ModDown per rotation (the schedule bit-identical to rotating
@@ -738,7 +742,8 @@ def main():
     hbm_ach = by / (ms / 1e3) / 1e9
     alu_ach = ops / (ms / 1e3) / 1e9
     alu_peak = r["bfly_peak"] / 1e9
-    traffic = ncu_traffic(name)
+    traffic = ncu_traffic(name, {"batch": B, "fc_form": args.fc_form, "conv_hoist": args.conv_hoist,
+                                 "double_hoist": args.double_hoist})
     hbm = {"achieved": hbm_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_ach / peaks["hbm_gbs"],
            "peak_source": peaks["source"]}
     alu = {"achieved": alu_ach, "peak": alu_peak, "unit": "Gbfly/s", "frac": alu_ach / alu_peak if alu_peak else None,

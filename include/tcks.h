@@ -161,6 +161,11 @@ tcks_status tcks_decrypt(tcks_ctx* ctx, const tcks_ct* ct, tcks_pt** out);
  * then synchronises so `limbs` may be reused). Export synchronises. */
 tcks_status tcks_ct_import(tcks_ctx* ctx, const uint64_t* limbs, uint32_t level, double scale, tcks_ct** out);
 tcks_status tcks_ct_export(const tcks_ct* ct, uint64_t* limbs, size_t n_words);
+/* The same for a batch: host limbs [count][2][level][N] contiguous; all copies are queued before one
+ * wait (use pinned host memory for overlap). export_batch requires one context and one level. */
+tcks_status tcks_ct_import_batch(tcks_ctx* ctx, const uint64_t* limbs, uint32_t count, uint32_t level, double scale,
+                                 tcks_ct** outs);
+tcks_status tcks_ct_export_batch(const tcks_ct* const* cts, uint32_t count, uint64_t* limbs, size_t n_words);
 /* Wire format (the communication of one encrypted inference, §4): a 16-byte header (b"TCKS",
  * version 1, kind 0, log2 N, level, scale as f64, little-endian) and, for component b = 0, 1 and limb
  * i < level, the N NTT-form residues packed with exactly bit_length(q_i) bits each (residue k in bits

@@ -134,6 +134,8 @@ _SIGS = {
     "tcks_cnn_forward": (ctypes.c_int32, [_vp, _vp, _vpp]),
     "tcks_cnn_forward_batch": (ctypes.c_int32, [_vp, _vpp, ctypes.c_uint32, _vpp]),
     "tcks_vecmat_plain_batch": (ctypes.c_int32, [_vpp, ctypes.c_uint32, _vp, _vpp]),
+    "tcks_ct_import_batch": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double, _vpp]),
+    "tcks_ct_export_batch": (ctypes.c_int32, [_vpp, ctypes.c_uint32, _u64p, ctypes.c_size_t]),
     "tcks_ct_serialized_size": (ctypes.c_int32, [_vp, _u64p]),
     "tcks_ct_serialize": (ctypes.c_int32, [_vp, ctypes.c_void_p, ctypes.c_uint64, _u64p]),
     "tcks_ct_deserialize": (ctypes.c_int32, [_vp, ctypes.c_void_p, ctypes.c_uint64, _vpp]),
@@ -381,6 +383,13 @@ class Context:
         h = _vp()
         check(lib().tcks_ct_import(self.h, _p(a), level, float(scale), ctypes.byref(h)))
         return Ciphertext(self, h)
+
+    def ct_import_batch(self, limbs: np.ndarray, scale: float) -> list:
+        """Ciphertexts from host limbs [count][2][level][N] (one wait for all the copies)."""
+        a = np.ascontiguousarray(limbs, dtype=np.uint64)
+        outs = (_vp * a.shape[0])()
+        check(lib().tcks_ct_import_batch(self.h, _p(a), a.shape[0], a.shape[2], float(scale), outs))
+        return [Ciphertext(self, _vp(outs[i])) for i in range(a.shape[0])]
 
     def ct_deserialize(self, data: bytes) -> "Ciphertext":
         """A ciphertext from the bit-packed wire format (see tcks_ct_serialize)."""

@@ -694,6 +694,47 @@ tcks_status tcks_ct_import(tcks_ctx* c, const uint64_t* limbs, uint32_t level, d
   TCKS_API_END
 }
 
+tcks_status tcks_ct_import_batch(tcks_ctx* c, const uint64_t* limbs, uint32_t count, uint32_t level, double scale,
+                                 tcks_ct** outs) {
+  std::vector<tcks_ct*> made;
+  TCKS_API_BEGIN
+  if (!c || !outs || (count && !limbs)) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  for (u32 i = 0; i < count; ++i) outs[i] = nullptr;
+  if (level < 1 || level > c->L) fail(TCKS_ERR_INVALID_ARG, "level out of range");
+  const u64 w = ct_words(c, level);
+  try {
+    for (u32 i = 0; i < count; ++i) {
+      made.push_back(new_ct(c, level, scale));
+      check_cuda(cudaMemcpyAsync(made.back()->d, limbs + (size_t)i * w, w * 8, cudaMemcpyHostToDevice, c->stream),
+                 "ct import");
+    }
+    check_cuda(cudaStreamSynchronize(c->stream), "ct import");
+  } catch (...) {
+    for (tcks_ct* t : made) free_ct(t);
+    throw;
+  }
+  for (u32 i = 0; i < count; ++i) outs[i] = made[i];
+  TCKS_API_END
+}
+
+tcks_status tcks_ct_export_batch(const tcks_ct* const* cts, uint32_t count, uint64_t* limbs, size_t n_words) {
+  TCKS_API_BEGIN
+  if (!cts || (count && !limbs)) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  if (!count) return TCKS_OK;
+  if (!cts[0]) fail(TCKS_ERR_INVALID_ARG, "null ciphertext");
+  tcks_ctx* c = cts[0]->ctx;
+  const u32 level = cts[0]->level;
+  const u64 w = ct_words(c, level);
+  if (n_words != (size_t)count * w) fail(TCKS_ERR_INVALID_ARG, "n_words does not match [count][2][level][N]");
+  for (u32 i = 0; i < count; ++i)
+    if (!cts[i] || cts[i]->ctx != c || cts[i]->level != level)
+      fail(TCKS_ERR_INVALID_ARG, "the batch must share one context and level");
+  for (u32 i = 0; i < count; ++i)
+    check_cuda(cudaMemcpyAsync(limbs + (size_t)i * w, cts[i]->d, w * 8, cudaMemcpyDeviceToHost, c->stream), "ct export");
+  check_cuda(cudaStreamSynchronize(c->stream), "ct export");
+  TCKS_API_END
+}
+
 tcks_status tcks_ct_export(const tcks_ct* ct, uint64_t* limbs, size_t n_words) {
   TCKS_API_BEGIN
   if (!ct || !limbs) fail(TCKS_ERR_INVALID_ARG, "null argument");

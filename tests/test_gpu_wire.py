@@ -44,3 +44,16 @@ def test_cnn_inference_traffic():
     x = ctx.encrypt_values(inputs.uniform_slots(8, 1), 3)
     y = ctx.ct_import(x.export()[:, :1], x.info()[1])
     assert len(x.serialize()) + len(y.serialize()) == 16 + 382976 + 16 + 63488
+
+
+def test_batch_import_export_roundtrip():
+    ctx = tk.Context(tk.Params(12, [36, 36, 36, 37], 2.0 ** 30), seed=SEED)
+    data = np.stack([np.stack([inputs.random_limbs(ctx.primes[:3], ctx.N, 60 + 2 * i + b, polys=1)[0]
+                               for b in range(2)]) for i in range(5)])
+    cts = ctx.ct_import_batch(data, 2.0 ** 30)
+    for i, c in enumerate(cts):
+        assert np.array_equal(c.export(), data[i]) and c.info() == (3, 2.0 ** 30)
+    out = np.zeros_like(data)
+    handles = (tk._vp * len(cts))(*[c.h.value for c in cts])
+    tk.check(tk.lib().tcks_ct_export_batch(handles, len(cts), tk._p(out), out.size))
+    assert np.array_equal(out, data)
