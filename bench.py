@@ -680,7 +680,12 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": args.gpus,
             "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * total / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": "cpu oracle"},
+            "config": {"workload": WORKLOAD, "parallelism": "cpu oracle",
+                       "vecmat_schedule": ("ModDown once after each rotation sum (double hoisting)"
+                                           if args.double_hoist else "one ModDown per rotation"),
+                       "fc_form": "rectangular diagonals" if args.fc_form == "rect" else "square diagonals",
+                       "conv_form": ("two hoisted rotation sums" if args.conv_hoist
+                                     else "rotate-and-add chain")},
             "cpu_baseline": {"value": value, "unit": "inferences/s", "cores": cores, "kind": "oracle",
                              "sample": f"{steps} full inferences (forward only; keys and weights prepared outside)"},
             "e2e": {"value": value, "unit": "inferences/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
