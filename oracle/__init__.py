@@ -5,5 +5,5 @@ The GPU library never imports, links or executes anything here.
 """
 from .ckks import (  # noqa: F401
     CNNWeights, Ct, EncodedCNN, OracleCKKS, Pt, SwitchKey, cnn_encode, cnn_forward, cnn_galois_steps,
-    cnn_plain, gen_primes, intt, is_prime, lib, min_psi, ntt, ntt_naive, philox4x64,
+    cnn_plain, gen_primes, intt, is_prime, lib, min_psi, ntt, ntt_naive, philox4x64, power_products,
 )

@@ -141,6 +141,33 @@ def intt(a, q: int, psi: int) -> np.ndarray:
     return a
 
 
+def power_products(ks) -> list[tuple[int, int, int]]:
+    """The products (i, a, b), x^i = x^a x^b, of a minimum-depth circuit for x^k, k in ks (§3, power):
+    x^(2m) = (x^m)^2, and for i not a power of two x^i = x^(2^m) x^(i - 2^m) with 2^m the largest power
+    of two below i. Each x^i then has depth ceil(log2 i), the lower bound for a product of i factors.
+    Listed in increasing i, so both operands of a product come before it."""
+    need = set()
+
+    def visit(i):
+        if i == 1 or i in need:
+            return
+        need.add(i)
+        m = 1 << (i.bit_length() - 1)
+        if m == i:
+            visit(i // 2)
+        else:
+            visit(m)
+            visit(i - m)
+
+    for k in ks:
+        visit(int(k))
+    out = []
+    for i in sorted(need):
+        m = 1 << (i.bit_length() - 1)
+        out.append((i, i // 2, i // 2) if m == i else (i, m, i - m))
+    return out
+
+
 # ------------------------------------------------------------------------ ciphertext records --
 
 @dataclass
@@ -383,6 +410,70 @@ class OracleCKKS:
 
     def square(self, a: Ct) -> Ct:
         return self.mul(a, a)
+
+    # ------------------------------------------------------------- power and polyval (§3) ----
+    def const_pt(self, a: float, scale: float, level: int) -> Pt:
+        """The plaintext of the real constant a at `scale`: the constant polynomial c = rint(a * scale)
+        (round half to even of the FP64 product). A constant polynomial evaluates to c at every root, so
+        its canonical embedding is c in every slot and its NTT is c mod q_j at every point."""
+        v = float(a) * float(scale)
+        if not abs(v) < 2.0 ** 62:
+            raise OverflowError("|a * scale| >= 2^62")
+        c = int(np.rint(v))
+        data = np.empty((level, self.N), dtype=np.uint64)
+        for j in range(level):
+            data[j, :] = c % self.q[j]
+        return Pt(data, level, float(scale))
+
+    def power(self, ct: Ct, k: int) -> Ct:
+        """x^k element-wise with the minimum multiplicative depth ceil(log2 k) (§3, power): the products
+        of power_products, each operand pair brought to the lower of their levels by dropping limbs,
+        then multiplied, relinearized and rescaled."""
+        if k < 1:
+            raise ValueError("k must be >= 1")
+        return self._powers(ct, [k])[k]
+
+    def _powers(self, ct: Ct, ks) -> dict:
+        pw = {1: ct}
+        for i, a, b in power_products(ks):
+            A, B = pw[a], pw[b]
+            lvl = min(A.level, B.level)
+            if lvl < 2:
+                raise ValueError("level exhausted")
+            pw[i] = self.mul(self.mod_switch(A, lvl), self.mod_switch(B, lvl))
+        return pw
+
+    def polyval(self, ct: Ct, coeffs) -> Ct:
+        """p(x) = sum_i a_i x^i element-wise (§3, polyval) with the minimum depth ceil(log2 d) + 1.
+
+        The powers with a_i != 0 come from one minimum-depth power table (_powers). With l_min the lowest
+        of their levels, every term is taken to level l_min (limbs dropped), multiplied by the constant
+        a_i encoded at scale t_i = S q / s_i, where S is the context scale, q the prime q_{l_min - 1}
+        that the final rescale divides by and s_i the term's scale, so that every product has the
+        scale S q; the products are added, rescaled once, and the result, whose scale is S, gets a_0
+        encoded at scale S added. Result level l_min - 1."""
+        a = [float(c) for c in coeffs]
+        while a and a[-1] == 0.0:
+            a.pop()
+        ks = [i for i in range(1, len(a)) if a[i] != 0.0]
+        if not ks:
+            raise ValueError("polyval needs a non-zero coefficient of degree >= 1")
+        pw = self._powers(ct, ks)
+        lt = min(pw[i].level for i in ks)
+        if lt < 2:
+            raise ValueError("level exhausted")
+        S, q = self.scale, float(self.q[lt - 1])
+        acc = None
+        for i in ks:
+            t = self.mod_switch(pw[i], lt)
+            u = self.mul_plain(t, self.const_pt(a[i], S * q / t.scale, lt))
+            u = Ct(u.data, lt, S * q)
+            acc = u if acc is None else self.add(acc, u)
+        res = self.rescale(acc)
+        res = Ct(res.data, res.level, S)
+        if a[0] != 0.0:
+            res = self.add_plain(res, self.const_pt(a[0], S, res.level))
+        return res
 
     # ----------------------------------------------------------------------------- rotate ----
     def _key(self, step: int) -> SwitchKey:
