@@ -199,6 +199,29 @@ tcks_status tcks_mul_plain(const tcks_ct* a, const tcks_pt* p, tcks_ct** out);
  * 2-component ciphertext and the call fails with UNSUPPORTED. */
 tcks_status tcks_mul(const tcks_ct* a, const tcks_ct* b, tcks_ct** out);
 tcks_status tcks_square(const tcks_ct* a, tcks_ct** out);
+/* Element-wise power x^k (§3, "power" with a circuit of minimum multiplicative depth), k >= 1:
+ * x^(2m) = (x^m)^2, and for i not a power of two x^i = x^(2^m) x^(i - 2^m) with 2^m the largest power
+ * of two below i. Each product takes both operands to the lower of their levels (limbs dropped),
+ * then tensor product, relinearization and rescale, whatever the context's AUTO flags. Result at
+ * level(x) - ceil(log2 k) with the product of the scales over the dropped primes; k = 1 copies x.
+ * Errors: INVALID_ARG (k = 0, null), LEVEL_EXHAUSTED (level(x) < ceil(log2 k) + 1). The result is a
+ * new ciphertext owned by the caller. */
+tcks_status tcks_power(const tcks_ct* x, uint32_t k, tcks_ct** out);
+/* The same for `count` ciphertexts of one level and scale in batched launches; outs[count]. */
+tcks_status tcks_power_batch(const tcks_ct* const* x, uint32_t count, uint32_t k, tcks_ct** outs);
+/* Element-wise polynomial p(x) = sum_{i < n_coeffs} coeffs[i] x^i (§3, "polyval"; coeffs host,
+ * lowest degree first, trailing zeros ignored, degree d >= 1). The powers with a non-zero
+ * coefficient come from one minimum-depth power table (as tcks_power). With l their lowest level,
+ * S the context scale and q = q_{l-1}: term i is multiplied by the integer rint(a_i S q / s_i) (s_i
+ * its scale, round half to even), the terms are added with rint(a_0 S) q, and one rescale gives
+ * the result at level l - 1 = level(x) - ceil(log2 d) - 1 and scale exactly S. Errors:
+ * INVALID_ARG (no non-zero coefficient of degree >= 1), LEVEL_EXHAUSTED (level(x) < ceil(log2 d) + 2),
+ * VALUE_OVERFLOW (a scaled coefficient of magnitude >= 2^62). */
+tcks_status tcks_polyval(const tcks_ct* x, const double* coeffs, uint32_t n_coeffs, tcks_ct** out);
+/* The same for `count` ciphertexts of one level and scale (LEVEL_MISMATCH / SCALE_MISMATCH
+ * otherwise) in batched launches; outs[count]. */
+tcks_status tcks_polyval_batch(const tcks_ct* const* x, uint32_t count, const double* coeffs, uint32_t n_coeffs,
+                               tcks_ct** outs);
 /* Rescale in place: divide by the last prime with rounding (level - 1, scale / q_last). */
 tcks_status tcks_rescale(tcks_ct* ct);
 /* Drop limbs level..ell-1 in place (scale unchanged). */

@@ -84,6 +84,10 @@ _SIGS = {
     "tcks_mul_plain": (ctypes.c_int32, [_vp, _vp, _vpp]),
     "tcks_mul": (ctypes.c_int32, [_vp, _vp, _vpp]),
     "tcks_square": (ctypes.c_int32, [_vp, _vpp]),
+    "tcks_power": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vpp]),
+    "tcks_power_batch": (ctypes.c_int32, [_vpp, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
+    "tcks_polyval": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32, _vpp]),
+    "tcks_polyval_batch": (ctypes.c_int32, [_vpp, ctypes.c_uint32, _dblp, ctypes.c_uint32, _vpp]),
     "tcks_rescale": (ctypes.c_int32, [_vp]),
     "tcks_mod_switch": (ctypes.c_int32, [_vp, ctypes.c_uint32]),
     "tcks_rescale_noalloc": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, _vp]),
@@ -579,6 +583,15 @@ class Ciphertext:
     def square(self):
         return self._unary(lib().tcks_square)
 
+    def power(self, k: int):
+        """x^k element-wise with the minimum depth ceil(log2 k)."""
+        return self._unary(lib().tcks_power, k)
+
+    def polyval(self, coeffs):
+        """sum_i coeffs[i] x^i element-wise (lowest degree first); result at the context scale."""
+        a = np.ascontiguousarray(coeffs, dtype=np.float64)
+        return self._unary(lib().tcks_polyval, _p(a), len(a))
+
     def rescale_(self):
         check(lib().tcks_rescale(self.h))
         return self
@@ -620,6 +633,29 @@ class Ciphertext:
 
     def conv2d_im2col_pt(self, kernel: Plaintext, taps: int, windows: int):
         return self._unary(lib().tcks_conv2d_im2col_pt, kernel.h, taps, windows)
+
+
+def _handles(cts):
+    return (_vp * len(cts))(*[c.h.value if isinstance(c.h, _vp) else c.h for c in cts])
+
+
+def power_batch(cts, k: int) -> list:
+    """x^k for ciphertexts of one level and scale in batched launches."""
+    if not cts:
+        return []
+    outs = (_vp * len(cts))()
+    check(lib().tcks_power_batch(_handles(cts), len(cts), k, outs))
+    return [Ciphertext(cts[0].ctx, _vp(outs[i])) for i in range(len(cts))]
+
+
+def polyval_batch(cts, coeffs) -> list:
+    """sum_i coeffs[i] x^i for ciphertexts of one level and scale in batched launches."""
+    if not cts:
+        return []
+    a = np.ascontiguousarray(coeffs, dtype=np.float64)
+    outs = (_vp * len(cts))()
+    check(lib().tcks_polyval_batch(_handles(cts), len(cts), _p(a), len(a), outs))
+    return [Ciphertext(cts[0].ctx, _vp(outs[i])) for i in range(len(cts))]
 
 
 class CNN:

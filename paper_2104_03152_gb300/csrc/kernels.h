@@ -9,7 +9,7 @@ namespace tcks {
 // Kernel families for launch accounting and the profiler (profiler.cpp).
 enum KernelId : u32 {
   K_NTT_FWD = 0, K_NTT_INV, K_ELEMENTWISE, K_TENSOR, K_DROP, K_MODUP, K_KS_P, K_KS_MODDOWN, K_MULACC, K_KEYGEN,
-  K_ENCRYPT, K_ENCODE, K_DECODE, K_VECMAT, K_DECRYPT, K_VECMAT_DH, K_COUNT
+  K_ENCRYPT, K_ENCODE, K_DECODE, K_VECMAT, K_DECRYPT, K_VECMAT_DH, K_LINCOMB, K_COUNT
 };
 // Scope around one kernel launch: counts it and, while profiling is on, records CUDA events on the
 // launching stream before and after it together with its algorithmic bytes.
@@ -183,5 +183,20 @@ void launch_crt_compose(const DevTables& T, const u64* coef, u32 ell, const u64*
 // p [N] doubles -> slot values [n_out].
 void launch_decode_slots(const DevTables& T, const FftTables& F, const double* p, double scale, u32 n_out,
                          double* out, cudaStream_t st);
+
+// ---- kern_poly.cu
+// out[count][2][ell][N] = sum_t coef[t][j] * x_t (first ell limbs of [count][2][level[t]][N]) + prev,
+// plus cst[j] on component 0 when has_cst (prev may be null, and may equal out). The constants travel
+// in the launch's parameters (no host-to-device copy, capturable in a graph).
+constexpr u32 kLincombMax = 8, kLincombMaxEll = 32;
+struct LincombArgs {
+  const u64* x[kLincombMax];
+  u32 level[kLincombMax];
+  u64 coef[kLincombMax][kLincombMaxEll];  // residues c_t mod q_j
+  u64 cst[kLincombMaxEll];
+  const u64* prev;
+  u32 terms, ell, count, has_cst;
+};
+void launch_lincomb(const DevTables& T, const LincombArgs& A, u64* out, cudaStream_t st);
 
 }  // namespace tcks
