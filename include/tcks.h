@@ -392,6 +392,58 @@ tcks_status tcks_profile_read(uint32_t idx, const char** name, uint64_t* launche
  * tcks_calibrate_butterflies). */
 tcks_status tcks_profile_read_ops(uint32_t idx, double* algo_ops);
 
+/* ---------------------------------------- ciphertext arrays: CKKSTensor storage (§2.2) ---- */
+/* TenSEAL's CKKSTensor holds an N-dimensional tensor as a tensor of ciphertexts, with optionally one
+ * axis batched into the slots (§2.2). A tcks_cta is the storage of such a tensor: `count`
+ * ciphertexts of one level and scale in one device allocation [count][2][level][N] (ciphertext i at
+ * i * 2 * level * N words), so that each operation below is one batched pass over all of them. The
+ * tensor's shape, broadcasting and axes are the caller's (the Python CKKSTensor). Every array
+ * returned is new and owned by the caller (tcks_cta_free); inputs are not modified except by
+ * tcks_cta_rescale / tcks_cta_mod_switch. Empty arrays are rejected (INVALID_ARG). */
+typedef struct tcks_cta tcks_cta;
+enum { TCKS_CTA_ADD = 0u, TCKS_CTA_SUB = 1u, TCKS_CTA_MUL = 2u };
+void tcks_cta_free(tcks_cta* a);
+tcks_status tcks_cta_info(const tcks_cta* a, uint32_t* count, uint32_t* level, double* scale);
+/* Host [count][2][level][N] limbs (NTT form) in and out; n_words must equal count * 2 * level * N. */
+tcks_status tcks_cta_import(tcks_ctx* ctx, const uint64_t* limbs, uint32_t count, uint32_t level, double scale,
+                            tcks_cta** out);
+tcks_status tcks_cta_export(const tcks_cta* a, uint64_t* limbs, size_t n_words);
+/* Gather ciphertexts of one level and scale into an array (LEVEL_MISMATCH / SCALE_MISMATCH), and copy
+ * ciphertext i out of one. */
+tcks_status tcks_cta_from_cts(const tcks_ct* const* cts, uint32_t count, tcks_cta** out);
+tcks_status tcks_cta_get(const tcks_cta* a, uint32_t i, tcks_ct** out);
+/* Ciphertext i encrypts host values[i*n .. i*n+n) (n <= N/2, the other slots zero) encoded at the
+ * context scale on `level` limbs (0: L), with encryption seed seed + i. */
+tcks_status tcks_cta_encrypt(tcks_ctx* ctx, const double* values, uint32_t count, uint32_t n, uint32_t level,
+                             uint64_t seed, tcks_cta** out);
+/* Slots [0, n) of every ciphertext into host values [count][n]. */
+tcks_status tcks_cta_decrypt(const tcks_cta* a, double* values, uint32_t n);
+/* Element-wise a op b over two arrays of one length and level (add / sub: one scale): one launch;
+ * MUL is tensor product + relinearization (+ rescale under TCKS_AUTO_RESCALE) of all pairs. */
+tcks_status tcks_cta_binary(uint32_t op, const tcks_cta* a, const tcks_cta* b, tcks_cta** out);
+tcks_status tcks_cta_negate(const tcks_cta* a, tcks_cta** out);
+/* a op plain, the plaintext of ciphertext i being host values[i*n .. i*n+n) encoded on a's level at
+ * a's scale (ADD, SUB) or the context scale (MUL, then rescale under TCKS_AUTO_RESCALE). */
+tcks_status tcks_cta_plain(uint32_t op, const tcks_cta* a, const double* values, uint32_t n, tcks_cta** out);
+/* Gathered combination: out[o] = sum_{t < terms} c[o][t] * a[idx[o][t]] for o < outputs (host idx,
+ * w [outputs][terms]). mode 0: c = w, which must be integers of magnitude below 2^53 (gathers,
+ * transposes and sums along tensor axes use w = 1); the scale is a's. mode 1: c = rint(w * S), the
+ * constant polynomial of w at the context scale S (products with a plain matrix, scalars per
+ * ciphertext); the scale is a's times S, then rescale under TCKS_AUTO_RESCALE. One launch.
+ * Errors: INVALID_ARG (index >= count, a non-integer weight in mode 0), VALUE_OVERFLOW (|w S| >= 2^62). */
+tcks_status tcks_cta_combine(const tcks_cta* a, const uint32_t* idx, const double* w, uint32_t outputs,
+                             uint32_t terms, int32_t mode, tcks_cta** out);
+/* Rotate-and-add within every ciphertext by 1, 2, 4, ... below n (n in [1, N/2]): slot 0 then holds the
+ * sum of slots [0, 2^ceil(log2 n)), which is the sum of the first n when the slots from n up to that
+ * power of two are zero. Needs the Galois keys of those steps (NO_GALOIS_KEY before any launch). */
+tcks_status tcks_cta_sum_slots(const tcks_cta* a, uint32_t n, tcks_cta** out);
+/* tcks_power / tcks_polyval on every ciphertext of the array (the same circuits, batched). */
+tcks_status tcks_cta_power(const tcks_cta* a, uint32_t k, tcks_cta** out);
+tcks_status tcks_cta_polyval(const tcks_cta* a, const double* coeffs, uint32_t n_coeffs, tcks_cta** out);
+/* In place: rescale every ciphertext (level - 1, scale / q_last); drop limbs down to `level`. */
+tcks_status tcks_cta_rescale(tcks_cta* a);
+tcks_status tcks_cta_mod_switch(tcks_cta* a, uint32_t level);
+
 /* ------------------------------------------------------------- the encrypted CNN (§4) ---- */
 /* The MNIST-shaped network of the paper's evaluation (§4, Table 2): im2col conv with `kernels`
  * kernels of `taps` taps over `windows` windows (§3.2), square, FC (kernels*windows) -> hidden

@@ -7,3 +7,4 @@ from .ckks import (  # noqa: F401
     CNNWeights, Ct, EncodedCNN, OracleCKKS, Pt, SwitchKey, cnn_encode, cnn_forward, cnn_galois_steps,
     cnn_plain, gen_primes, intt, is_prime, lib, min_psi, ntt, ntt_naive, philox4x64, power_products,
 )
+from .tensor import OracleTensor  # noqa: F401,E402

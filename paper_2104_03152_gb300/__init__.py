@@ -20,6 +20,7 @@ TCKS_AUTO_RESCALE = 2
 TCKS_DOUBLE_HOIST = 4
 TCKS_RECT_DIAG = 8
 TCKS_CONV_HOIST = 16
+TCKS_CTA_ADD, TCKS_CTA_SUB, TCKS_CTA_MUL = 0, 1, 2  # ciphertext-array operations
 KEY_SECRET, KEY_PUBLIC, KEY_RELIN, KEY_GALOIS = 0, 1, 2, 3
 
 _u64p = ctypes.POINTER(ctypes.c_uint64)
@@ -84,6 +85,25 @@ _SIGS = {
     "tcks_mul_plain": (ctypes.c_int32, [_vp, _vp, _vpp]),
     "tcks_mul": (ctypes.c_int32, [_vp, _vp, _vpp]),
     "tcks_square": (ctypes.c_int32, [_vp, _vpp]),
+    "tcks_cta_free": (None, [_vp]),
+    "tcks_cta_info": (ctypes.c_int32, [_vp, _u32p, _u32p, _dblp]),
+    "tcks_cta_import": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double, _vpp]),
+    "tcks_cta_export": (ctypes.c_int32, [_vp, _u64p, ctypes.c_size_t]),
+    "tcks_cta_from_cts": (ctypes.c_int32, [_vpp, ctypes.c_uint32, _vpp]),
+    "tcks_cta_get": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vpp]),
+    "tcks_cta_encrypt": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                          ctypes.c_uint64, _vpp]),
+    "tcks_cta_decrypt": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32]),
+    "tcks_cta_binary": (ctypes.c_int32, [ctypes.c_uint32, _vp, _vp, _vpp]),
+    "tcks_cta_negate": (ctypes.c_int32, [_vp, _vpp]),
+    "tcks_cta_plain": (ctypes.c_int32, [ctypes.c_uint32, _vp, _dblp, ctypes.c_uint32, _vpp]),
+    "tcks_cta_combine": (ctypes.c_int32, [_vp, _u32p, _dblp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int32,
+                                          _vpp]),
+    "tcks_cta_sum_slots": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vpp]),
+    "tcks_cta_power": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vpp]),
+    "tcks_cta_polyval": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32, _vpp]),
+    "tcks_cta_rescale": (ctypes.c_int32, [_vp]),
+    "tcks_cta_mod_switch": (ctypes.c_int32, [_vp, ctypes.c_uint32]),
     "tcks_power": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vpp]),
     "tcks_power_batch": (ctypes.c_int32, [_vpp, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
     "tcks_polyval": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32, _vpp]),
@@ -836,3 +856,5 @@ class Server:
         v = [ctypes.c_uint64() for _ in range(5)]
         check(lib().tcks_server_stats(self.h, *[ctypes.byref(x) for x in v]))
         return dict(zip(["queued", "in_flight", "finished", "bytes_in_use", "bytes_resident"], [x.value for x in v]))
+
+from .tensor import CKKSTensor  # noqa: E402,F401

@@ -107,6 +107,15 @@ struct tcks_matrix {
   tcks::u32 limbs() const { return level + ext; }  // limbs per stored diagonal
 };
 
+// An array of `count` ciphertexts of one level and scale in one device allocation (an encrypted
+// tensor's storage): ciphertext i at d + i * 2 * level * N.
+struct tcks_cta {
+  tcks_ctx* ctx;
+  tcks::u64* d;
+  tcks::u32 count, level;
+  double scale;
+};
+
 namespace tcks {
 
 void ctx_retain(tcks_ctx* c);

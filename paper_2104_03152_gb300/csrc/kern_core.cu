@@ -314,9 +314,10 @@ __device__ __forceinline__ u64 mulq(u64 a, u64 b, const ModConst& m, u32 narrow)
 
 // ------------------------------------------------------------------------ element-wise ops ----
 // Operands laid out [polys][ell][N] (a batch of ciphertexts is [2B][ell][N]); element e belongs to
-// limb (e >> log_n) % ell and component ((e >> log_n) / ell) % 2.
+// limb (e >> log_n) % ell and component ((e >> log_n) / ell) % 2. A plain operand b is shared by every
+// polynomial (b_stride = 0) or is one plaintext per ciphertext, b_stride words apart.
 __global__ void k_elementwise(DevTables T, u32 op, const u64* __restrict__ a, const u64* __restrict__ b,
-                              u64* __restrict__ out, u32 ell, u32 polys) {
+                              u64* __restrict__ out, u32 ell, u32 polys, u64 b_stride) {
   const u32 log_n = T.log_n;
   const u64 n = 1ull << log_n;
   const u64 total2 = ((u64)polys * ell * n) >> 1;
@@ -345,15 +346,17 @@ __global__ void k_elementwise(DevTables T, u32 op, const u64* __restrict__ a, co
         r.x = neg_mod(x.x, m.q);
         r.y = neg_mod(x.y, m.q);
         break;
-      case OP_MUL_PLAIN: {  // b is a plaintext [>= ell][N] shared by every polynomial
-        const ulonglong2 y = reinterpret_cast<const ulonglong2*>(b + (u64)limb * n)[(e & (n - 1)) >> 1];
+      case OP_MUL_PLAIN: {  // b is a plaintext [>= ell][N] (per ciphertext when b_stride != 0)
+        const ulonglong2 y =
+            reinterpret_cast<const ulonglong2*>(b + (poly >> 1) * b_stride + (u64)limb * n)[(e & (n - 1)) >> 1];
         r.x = mulq(x.x, y.x, m, T.narrow);
         r.y = mulq(x.y, y.y, m, T.narrow);
         break;
       }
       default: {  // OP_ADD_PLAIN / OP_SUB_PLAIN: only component 0 of each ciphertext changes
         if ((poly & 1u) == 0) {
-          const ulonglong2 y = reinterpret_cast<const ulonglong2*>(b + (u64)limb * n)[(e & (n - 1)) >> 1];
+          const ulonglong2 y =
+              reinterpret_cast<const ulonglong2*>(b + (poly >> 1) * b_stride + (u64)limb * n)[(e & (n - 1)) >> 1];
           if (op == OP_ADD_PLAIN) {
             r.x = add_mod(x.x, y.x, m.q);
             r.y = add_mod(x.y, y.y, m.q);
@@ -377,14 +380,15 @@ static u32 ew_blocks(u64 elems2) {
 }
 
 void launch_elementwise(const DevTables& T, u32 op, const u64* a, const u64* b, u64* out, u32 ell, u32 polys,
-                        cudaStream_t st) {
+                        cudaStream_t st, u64 b_stride) {
   const u64 e2 = ((u64)polys * ell << T.log_n) >> 1;
   const double limb = 8.0 * ell * (1u << T.log_n);  // bytes of one [ell][N] polynomial
   const double by = op == OP_NEG ? 2.0 * polys * limb
                     : (op == OP_ADD || op == OP_SUB) ? 3.0 * polys * limb
-                                                     : (2.0 * polys + 1.0) * limb;  // shared plaintext operand
+                    : b_stride ? 2.5 * polys * limb                                  // a plaintext per ciphertext
+                               : (2.0 * polys + 1.0) * limb;  // shared plaintext operand
   Launch L(K_ELEMENTWISE, st, by);
-  k_elementwise<<<ew_blocks(e2), 256, 0, st>>>(T, op, a, b, out, ell, polys);
+  k_elementwise<<<ew_blocks(e2), 256, 0, st>>>(T, op, a, b, out, ell, polys, b_stride);
 }
 
 // Tensor product of `count` pairs: (d0, d1, d2) = (a0 b0, a0 b1 + a1 b0, a1 b1); a, b [count][2][ell][N],

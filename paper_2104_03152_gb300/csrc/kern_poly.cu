@@ -1,5 +1,7 @@
-// The combination step of polynomial evaluation (§3, polyval): out = sum_t c_t x^(i_t) (+ prev) with
-// the constant added to component 0, for `count` ciphertexts at once.
+// Linear combinations of ciphertexts with integer constants: the combination step of polynomial
+// evaluation (§3, polyval), out = sum_t c_t x^(i_t) (+ prev) with the constant added to component 0,
+// for `count` ciphertexts at once; and the gathered combination of an encrypted tensor's ciphertexts
+// (gather, sum along an axis, product with a plain matrix), out[o] = sum_t c[o][t] x[idx[o][t]].
 //
 // Each term is a batch of ciphertexts [count][2][level_t][N] at a level >= ell; only its first ell
 // limbs are read, which is the limb drop that brings it to level ell. c_t is an integer constant given
@@ -52,7 +54,50 @@ __global__ void __launch_bounds__(256) k_lincomb(DevTables T, LincombArgs A, u64
   }
 }
 
+// One thread per pair of coefficients of an output row (o, b, j); the terms' rows are read in the
+// same coalesced order, the coefficient of a term is one broadcast load.
+template <typename W>
+__global__ void __launch_bounds__(256) k_combine(DevTables T, const u64* __restrict__ x, u32 level,
+                                                 const u32* __restrict__ idx, const u64* __restrict__ coef,
+                                                 u32 outputs, u32 terms, u64* __restrict__ out) {
+  const u32 log_n = T.log_n;
+  const u64 n = 1ull << log_n;
+  const u64 per_ct = 2ull * level * n;
+  const u64 total2 = (per_ct * outputs) >> 1;
+  for (u64 e2 = (u64)blockIdx.x * blockDim.x + threadIdx.x; e2 < total2; e2 += (u64)gridDim.x * blockDim.x) {
+    const u64 e = e2 << 1;
+    const u64 o = e / per_ct, off = e - o * per_ct;  // output ciphertext, offset inside it
+    const u32 j = (u32)((off >> log_n) % level);
+    const ModConst m = T.mods[j];
+    typename Ew<W>::Acc a0, a1;
+    const u32* it = idx + o * terms;
+    const u64* ct = coef + o * terms * level + j;
+    for (u32 t = 0; t < terms; ++t) {
+      const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(x + (u64)it[t] * per_ct + off);
+      const u64 c = ct[(u64)t * level];
+      a0.mac(v.x, c);
+      a1.mac(v.y, c);
+    }
+    *reinterpret_cast<ulonglong2*>(out + e) = make_ulonglong2(a0.get(m), a1.get(m));
+  }
+}
+
 }  // namespace
+
+void launch_combine(const DevTables& T, const u64* x, u32 level, const u32* idx, const u64* coef, u32 outputs,
+                    u32 terms, u64* out, cudaStream_t st) {
+  const u64 per_ct = (2ull * level) << T.log_n;
+  const u64 e2 = (per_ct * outputs) >> 1;
+  u64 blocks = (e2 + 255) / 256;
+  const u64 cap = 152ull * 8;
+  if (blocks > cap) blocks = cap;
+  if (!blocks) blocks = 1;
+  Launch L(K_COMBINE, st, 8.0 * per_ct * outputs * (terms + 1), (double)per_ct * outputs * terms);
+  if (T.narrow)
+    k_combine<u32><<<(u32)blocks, 256, 0, st>>>(T, x, level, idx, coef, outputs, terms, out);
+  else
+    k_combine<u64><<<(u32)blocks, 256, 0, st>>>(T, x, level, idx, coef, outputs, terms, out);
+}
 
 void launch_lincomb(const DevTables& T, const LincombArgs& A, u64* out, cudaStream_t st) {
   const u64 per_ct = (2ull * A.ell) << T.log_n;

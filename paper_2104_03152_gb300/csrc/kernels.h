@@ -9,7 +9,7 @@ namespace tcks {
 // Kernel families for launch accounting and the profiler (profiler.cpp).
 enum KernelId : u32 {
   K_NTT_FWD = 0, K_NTT_INV, K_ELEMENTWISE, K_TENSOR, K_DROP, K_MODUP, K_KS_P, K_KS_MODDOWN, K_MULACC, K_KEYGEN,
-  K_ENCRYPT, K_ENCODE, K_DECODE, K_VECMAT, K_DECRYPT, K_VECMAT_DH, K_LINCOMB, K_COUNT
+  K_ENCRYPT, K_ENCODE, K_DECODE, K_VECMAT, K_DECRYPT, K_VECMAT_DH, K_LINCOMB, K_COMBINE, K_COUNT
 };
 // Scope around one kernel launch: counts it and, while profiling is on, records CUDA events on the
 // launching stream before and after it together with its algorithmic bytes.
@@ -62,9 +62,10 @@ void launch_unpack(const DevTables& T, const unsigned char* in, u32 level, u64* 
 void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_outer, u64* dst, u64 dst_outer,
                 u32 count, u32 mod_base, u32 per, cudaStream_t st);
 enum : u32 { OP_ADD = 0, OP_SUB = 1, OP_NEG = 2, OP_MUL_PLAIN = 3, OP_ADD_PLAIN = 4, OP_SUB_PLAIN = 5 };
-// [polys][ell][N] operands; plain ops share one plaintext across all polynomials.
+// [polys][ell][N] operands; plain ops share one plaintext across all polynomials (b_stride = 0) or
+// read one plaintext per ciphertext, b_stride words apart.
 void launch_elementwise(const DevTables& T, u32 op, const u64* a, const u64* b, u64* out, u32 ell, u32 polys,
-                        cudaStream_t st);
+                        cudaStream_t st, u64 b_stride = 0);
 // count pairs [count][2][ell][N] -> [count][3][ell][N].
 void launch_tensor(const DevTables& T, const u64* a, const u64* b, u64* out, u32 ell, u32 count, cudaStream_t st);
 void launch_decrypt(const DevTables& T, const u64* ct, const u64* s, u64* pt, u32 ell, cudaStream_t st);
@@ -198,5 +199,11 @@ struct LincombArgs {
   u32 terms, ell, count, has_cst;
 };
 void launch_lincomb(const DevTables& T, const LincombArgs& A, u64* out, cudaStream_t st);
+// Gathered combination over an array of ciphertexts x [count][2][level][N] (ciphertext i at
+// x + i * 2 * level * N): out[o] = sum_{t < terms} coef[o][t][j] * x[idx[o][t]] on limb j, for
+// `outputs` ciphertexts [outputs][2][level][N]. idx [outputs][terms], coef [outputs][terms][level]
+// residues, both on the device.
+void launch_combine(const DevTables& T, const u64* x, u32 level, const u32* idx, const u64* coef, u32 outputs,
+                    u32 terms, u64* out, cudaStream_t st);
 
 }  // namespace tcks

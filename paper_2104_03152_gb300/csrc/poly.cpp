@@ -275,6 +275,30 @@ tcks_status run_batch(const tcks_ct* const* x, u32 count, tcks_ct** outs, F&& fn
   return TCKS_OK;
 }
 
+// The same on a ciphertext array (already one contiguous batch): the result becomes a new array.
+template <typename F>
+tcks_status run_cta(const tcks_cta* a, tcks_cta** out, F&& fn) {
+  try {
+    drop_stale_cuda_error();
+    if (!a || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    tcks_ctx* c = a->ctx;
+    Batch in;
+    in.d = a->d;
+    in.level = a->level;
+    in.scale = a->scale;
+    Batch r = fn(c, in);
+    *out = new tcks_cta{c, r.d, a->count, r.level, r.scale};
+    ctx_retain(c);
+  } catch (const Error& e) {
+    return abi_record(e.code, e.msg);
+  } catch (const std::bad_alloc&) {
+    return abi_record(TCKS_ERR_OUT_OF_MEMORY, "host allocation failed");
+  }
+  abi_clear();
+  return TCKS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -294,6 +318,16 @@ tcks_status tcks_polyval_batch(const tcks_ct* const* x, uint32_t count, const do
 
 tcks_status tcks_polyval(const tcks_ct* x, const double* coeffs, uint32_t n_coeffs, tcks_ct** out) {
   return tcks_polyval_batch(&x, 1, coeffs, n_coeffs, out);
+}
+
+tcks_status tcks_cta_power(const tcks_cta* a, uint32_t k, tcks_cta** out) {
+  return run_cta(a, out, [&](tcks_ctx* c, const Batch& in) { return op_power(c, in, a->count, k); });
+}
+
+tcks_status tcks_cta_polyval(const tcks_cta* a, const double* coeffs, uint32_t n_coeffs, tcks_cta** out) {
+  if (!coeffs && n_coeffs) return abi_record(TCKS_ERR_INVALID_ARG, "null coefficients");
+  std::vector<double> v(coeffs, coeffs + n_coeffs);
+  return run_cta(a, out, [&](tcks_ctx* c, const Batch& in) { return op_polyval(c, in, a->count, v); });
 }
 
 }  // extern "C"

@@ -20,7 +20,7 @@ namespace {
 const char* const kNames[K_COUNT] = {"ntt_fwd",      "ntt_inv",    "elementwise", "tensor",    "drop_combine",
                                      "modup",        "ks_inner_p", "ks_moddown",  "vecmat_reduce", "keygen",
                                      "encrypt",      "encode",     "decode",      "vecmat_acc", "decrypt",
-                                     "vecmat_dh_acc", "lincomb"};
+                                     "vecmat_dh_acc", "lincomb", "combine"};
 
 struct Rec {
   u32 id;
