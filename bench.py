@@ -576,6 +576,71 @@ def primitive_peaks(tk):
             "bfly32_s": tk.calibrate_butterflies(32)}
 
 
+# CPU milliseconds of the paper's unary / binary CKKSVector operation tables (appendix; N = 8192 with a
+# 200-bit modulus, shapes 256 .. 16384, 2x^2 + x for polyval): another machine, context only.
+OPS_SHAPES = (256, 1024, 4096, 8192, 16384)
+PAPER_OPS_MS = {
+    "negate": (0.07, 0.07, 0.07, 0.13, 0.26), "square": (4.29, 4.29, 4.29, 8.49, 17.16),
+    "polyval": (10.55, 10.46, 10.51, 21.32, 42.68), "add": (0.08, 0.08, 0.08, 0.16, 0.31),
+    "multiply": (4.45, 4.34, 4.43, 8.84, 17.75), "sub": (0.08, 0.08, 0.08, 0.15, 0.3),
+    "dot": (20.15, 23.96, 28.11, 55.94, 112.36), "add_plain": (0.8, 0.86, 1.07, 2.13, 4.19),
+    "multiply_plain": (1.75, 1.81, 2.03, 4.02, 7.97), "sub_plain": (0.8, 0.86, 1.08, 2.14, 4.21),
+    "dot_plain": (17.37, 21.36, 25.63, 51.14, 101.82),
+}
+
+
+def run_ops_table(args):
+    """The paper's operation tables on this GPU: each operation on an encrypted tensor of the given
+    length, laid out as ceil(n / 4096) ciphertexts of up to 4096 slots (a batched CKKSTensor), through
+    the public API (plain operands encoded inside the call, as the paper's timings include). Wall time
+    per call with the device synchronized after it, median over --ops-reps calls."""
+    import torch
+
+    import paper_2104_03152_gb300 as tk
+    from paper_2104_03152_gb300 import inputs
+
+    tk.lib(build_if_missing=True)
+    ctx = tk.Context(tk.Params(13, [60, 40, 40, 60], 2.0 ** 40), seed=inputs.SEED_KEYS,
+                     flags=tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE)
+    ctx.gen_galois_keys([1 << m for m in range(12)])
+    rows = {op: [] for op in PAPER_OPS_MS}
+    errs = {op: 0.0 for op in PAPER_OPS_MS}
+    for n in OPS_SHAPES:
+        per, count = min(n, ctx.slots), (n + ctx.slots - 1) // ctx.slots
+        x = np.random.default_rng(n).uniform(-1.0, 1.0, size=(per, count))
+        y = np.random.default_rng(n + 1).uniform(-1.0, 1.0, size=(per, count))
+        A = tk.CKKSTensor.encrypt(ctx, x, batch=True, seed=1)
+        Bt = tk.CKKSTensor.encrypt(ctx, y, batch=True, seed=1 + count)
+        ops = {
+            "negate": (lambda: A.negate(), -x), "square": (lambda: A.square(), x * x),
+            "polyval": (lambda: A.polyval([0.0, 1.0, 2.0]), 2 * x * x + x),
+            "add": (lambda: A.add(Bt), x + y), "multiply": (lambda: A.mul(Bt), x * y),
+            "sub": (lambda: A.sub(Bt), x - y), "dot": (lambda: A.mul(Bt).sum(), np.sum(x * y)),
+            "add_plain": (lambda: A.add(y), x + y), "multiply_plain": (lambda: A.mul(y), x * y),
+            "sub_plain": (lambda: A.sub(y), x - y), "dot_plain": (lambda: A.mul(y).sum(), np.sum(x * y)),
+        }
+        for op, (fn, ref) in ops.items():
+            for _ in range(args.warmup):
+                fn()
+            ctx.synchronize()
+            ts = []
+            for _ in range(args.ops_reps):
+                t0 = time.perf_counter()
+                r = fn()
+                ctx.synchronize()
+                ts.append((time.perf_counter() - t0) * 1e3)
+            rows[op].append(statistics.median(ts))
+            errs[op] = max(errs[op], float(np.max(np.abs(r.decrypt() - ref))))
+        del A, Bt
+        torch.cuda.synchronize()
+    for op, ms in rows.items():
+        print(json.dumps({"table": "ckksvector_ops", "op": op, "shapes": list(OPS_SHAPES), "gpu_ms": ms,
+                          "paper_cpu_ms": list(PAPER_OPS_MS[op]), "max_abs_err": errs[op],
+                          "config": {"log_n": 13, "bits": [60, 40, 40, 60], "scale": "2^40",
+                                     "slots_per_ciphertext": 4096, "reps": args.ops_reps,
+                                     "timing": "wall time of the API call + device synchronize, median"}}))
+
+
 def run_sweep(args):
     import torch
     import paper_2104_03152_gb300 as tk
@@ -705,6 +770,9 @@ def main():
     ap.add_argument("--serve-rate", default="2000,300",
                     help="offered requests/s of the serving traces (comma-separated; one trace each)")
     ap.add_argument("--sweep", action="store_true", help="print the batched primitive sweep (JSON lines) and exit")
+    ap.add_argument("--ops-table", action="store_true",
+                    help="print the paper's CKKSVector operation tables measured here (JSON lines) and exit")
+    ap.add_argument("--ops-reps", type=int, default=20)
     ap.add_argument("--sweep-batches", default="1,8,64,512", help="ciphertexts per batch in the sweep")
     ap.add_argument("--sweep-log-n", default="13,14,15,16", help="log2 N values of the sweep")
     ap.add_argument("--sweep-L", default="4,8,16,32", help="data-prime counts of the sweep")
@@ -728,6 +796,9 @@ def main():
     args = ap.parse_args()
     if args.sweep:
         run_sweep(args)
+        return
+    if args.ops_table:
+        run_ops_table(args)
         return
     world, rank, local = dist_env()
     if args.impl == "reference":
