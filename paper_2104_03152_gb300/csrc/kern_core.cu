@@ -475,8 +475,9 @@ void launch_rescale(const DevTables& T, const u64* ct, u32 ell, u32 polys, u64* 
 
 // ------------------------------------------------------------------------ key switching ----
 // ModUp (one digit per prime) for a batch (y) of inputs: digit j = bal_{q_j}(x_j) lifted to slot i
-// (prime q_i for i < ell, P for i = ell) and NTT'd; digits [batch][ell][ell+1][N]. Slot i == j is
-// x_j itself. x_coef holds the inputs' INTT, [batch][ell][N].
+// (prime q_i for i < ell, P for i = ell) and NTT'd; digits [batch][ell][ell+1][N] of W-sized words
+// (32-bit on chains below 2^31, which halves the bytes every key-switch consumer reads). Slot i == j
+// is x_j itself. x_coef holds the inputs' INTT, [batch][ell][N].
 template <typename W, int LC>
 __global__ void k_modup(DevTables T, const u64* __restrict__ x_ntt, u64 x_stride, const u64* __restrict__ x_coef,
                         u32 ell, u64* __restrict__ digits) {
@@ -484,10 +485,10 @@ __global__ void k_modup(DevTables T, const u64* __restrict__ x_ntt, u64 x_stride
   const Slice sl = slice_of<LC>(T);
   const u64 n = 1ull << T.log_n;
   const u32 j = sl.job / (ell + 1), slot = sl.job % (ell + 1);
-  u64* out = digits + ((sl.y * ell + j) * (ell + 1) + slot) * n + sl.off;
+  W* out = reinterpret_cast<W*>(digits) + ((sl.y * ell + j) * (ell + 1) + slot) * n + sl.off;
   if (slot == j) {
     const u64* in = x_ntt + sl.y * x_stride + (u64)j * n + sl.off;
-    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) out[k] = in[k];
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) out[k] = (W)in[k];
     return;
   }
   const u32 tmod = slot < ell ? slot : T.L;
@@ -498,7 +499,7 @@ __global__ void k_modup(DevTables T, const u64* __restrict__ x_ntt, u64 x_stride
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)lift_balanced(in[k], half_j, qj_mod_t, mt);
   __syncthreads();
   ntt_fwd_slice<W, LC>(s, T, tmod, sl.rank);
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) out[k] = Ar<W>::fwd_out(s[sw(k)], mt);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) out[k] = (W)Ar<W>::fwd_out(s[sw(k)], mt);
 }
 
 static decltype(&k_modup<u64, 0>) const K6_k_modup[6] = TCKS_K6(k_modup);
@@ -507,7 +508,8 @@ void launch_modup(const DevTables& T, const u64* x_ntt, u64 x_stride, u32 count,
                   u64* digits, cudaStream_t st) {
   const u64 n = 1ull << T.log_n;
   launch_ntt(T, true, x_ntt, x_stride, x_coef_tmp, (u64)ell * n, count * ell, 0, ell, st);
-  Launch L(K_MODUP, st, 8.0 * n * count * (2.0 * ell + (double)ell * (ell + 1)),
+  const double wd = T.narrow ? 4.0 : 8.0;  // bytes of a digit word
+  Launch L(K_MODUP, st, n * count * (16.0 * ell + wd * ell * (ell + 1)),
            (double)count * ell * ell * bfly_per_limb(T.log_n));
   launch_limb(K6_k_modup, T.narrow, ell * (ell + 1), count, T.log_n, st, T.limb_threads, T, x_ntt, x_stride, (const u64*)x_coef_tmp, ell, digits);
 }
@@ -515,7 +517,7 @@ void launch_modup(const DevTables& T, const u64* x_ntt, u64 x_stride, u32 count,
 // Inner product of (automorphed) digits with one key component on slot `slot`:
 //   sum_j D_j[slot][src] * key_j[b][key_slot][k], lazy accumulation, one reduction.
 template <typename W>
-__device__ __forceinline__ u64 ks_inner(const u64* __restrict__ digits, u32 ell, u32 slot, const u64* __restrict__ key,
+__device__ __forceinline__ u64 ks_inner(const W* __restrict__ digits, u32 ell, u32 slot, const u64* __restrict__ key,
                                         u32 K, u32 key_slot, u32 b, u32 k, u32 src, u64 n, const ModConst& m) {
   typename Ew<W>::Acc acc;
   for (u32 j = 0; j < ell; ++j) {
@@ -539,7 +541,7 @@ __global__ void k_ks_inner_p(DevTables T, u32 ell, const __grid_constant__ KsPla
   const u32 rq = sl.job % plan.B, r = (u32)sl.y;
   const u64 yy = (u64)r * plan.B + rq;  // entry of the P-limb scratch [R][B][2][N]
   const KsKey kk = plan.keys[r];
-  const u64* digits = plan.digits + rq * plan.digits_b;
+  const W* digits = reinterpret_cast<const W*>(plan.digits) + rq * plan.digits_b;
   const u32 b = sl.job / plan.B;
   const ModConst mp = T.mods[T.L];
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
@@ -565,7 +567,7 @@ __global__ void k_ks_moddown(DevTables T, u32 ell, const __grid_constant__ KsPla
   const u32 rq = sl.job % plan.B, r = (u32)sl.y;
   const u64 yy = (u64)r * plan.B + rq;
   const KsKey kk = plan.keys[r];
-  const u64* digits = plan.digits + rq * plan.digits_b;
+  const W* digits = reinterpret_cast<const W*>(plan.digits) + rq * plan.digits_b;
   const u32 bi = sl.job / plan.B, b = bi / ell, i = bi % ell;
   const ModConst mi = T.mods[i];
   const ModConst mp = T.mods[T.L];
@@ -588,10 +590,10 @@ __global__ void k_ks_moddown(DevTables T, u32 ell, const __grid_constant__ KsPla
 }
 
 // Algorithmic bytes of a plan: distinct digit sets and keys once, scratch and outputs once.
-static void ks_plan_bytes(const KsPlan& p, u32 ell, u32 log_n, double* inner, double* moddown) {
+static void ks_plan_bytes(const KsPlan& p, u32 ell, u32 log_n, bool narrow, double* inner, double* moddown) {
   const double n = (double)(1u << log_n);
   const double jobs = (double)p.B * p.R;
-  const double digit_sets = p.digits_b ? p.B : 1;
+  const double digit_sets = (p.digits_b ? p.B : 1) * (narrow ? 0.5 : 1.0);  // in 8-byte units
   const double key_sets = p.R;  // each rotation index has its own key, shared by the batch
   const double adds = (p.add0 ? (p.add0_b ? p.B : 1) : 0) + (p.add1 ? (p.add1_b ? p.B : 1) : 0);
   *inner = 8.0 * n * (digit_sets * ell + key_sets * 2.0 * ell + 2.0 * jobs);
@@ -605,7 +607,7 @@ void launch_ks_inner_p(const DevTables& T, u32 ell, const KsPlan& plan, cudaStre
   const u64 jobs = (u64)plan.B * plan.R;
   if (!jobs) return;
   double bi, bm;
-  ks_plan_bytes(plan, ell, T.log_n, &bi, &bm);
+  ks_plan_bytes(plan, ell, T.log_n, T.narrow != 0, &bi, &bm);
   Launch L(K_KS_P, st, bi, 2.0 * jobs * ((double)ell * (1u << T.log_n) + bfly_per_limb(T.log_n)));
   launch_limb(K6_k_ks_inner_p, T.narrow, 2 * plan.B, plan.R, T.log_n, st, T.limb_threads, T, ell, plan);
 }
@@ -617,7 +619,7 @@ void launch_keyswitch(const DevTables& T, u32 ell, const KsPlan& plan, cudaStrea
   if (!jobs) return;
   launch_ks_inner_p(T, ell, plan, st);
   double bi, bm;
-  ks_plan_bytes(plan, ell, T.log_n, &bi, &bm);
+  ks_plan_bytes(plan, ell, T.log_n, T.narrow != 0, &bi, &bm);
   Launch L(K_KS_MODDOWN, st, bm,
            2.0 * ell * jobs * ((ell + 1.0) * (1u << T.log_n) + bfly_per_limb(T.log_n)));
   launch_limb(K6_k_ks_moddown, T.narrow, 2 * ell * plan.B, plan.R, T.log_n, st, T.limb_threads, T, ell, plan);
@@ -660,7 +662,7 @@ static u32 vecmat_threads(u32 log_n) {
 
 // The rotated-and-multiplied element g of rotation r: (tau(c0) + ModDown(u_b))[i][g] * d_k[i][g].
 template <typename W>
-__device__ __forceinline__ u64 vecmat_term(const W* s, u32 k, u32 g, const KsKey& kk, const u64* digits, u32 ell, u32 i,
+__device__ __forceinline__ u64 vecmat_term(const W* s, u32 k, u32 g, const KsKey& kk, const W* digits, u32 ell, u32 i,
                                            u32 b, u64 n, u32 log_n, const u64* c0, const u64* dk, const ModConst& mi,
                                            const PairConst& pc) {
   const u32 src = galois_src(g, kk.g, log_n);
@@ -682,7 +684,7 @@ __device__ __forceinline__ void vecmat_acc_body(W* s, const DevTables& T, u32 el
   const ModConst mi = T.mods[i];
   const ModConst mp = T.mods[T.L];
   const PairConst pc = T.pairs[(u64)T.L * T.n_mods + i];
-  const u64* digits = plan.digits + rq * plan.digits_b;
+  const W* digits = reinterpret_cast<const W*>(plan.digits) + rq * plan.digits_b;
   const u64* c0 = plan.ct + rq * plan.ct_b;  // component 0, [ell][N]
   u64* dst = plan.partial + rq * plan.partial_b + (((u64)chunk * 2 + b) * ell + i) * n + sl.off;
   const u32 r0 = chunk * plan.chunk;
@@ -785,8 +787,9 @@ void launch_vecmat_acc(const DevTables& T, u32 ell, const VecmatPlan& plan, cuda
   const double n = (double)(1u << T.log_n);
   // per (request, rotation): the P-limb scratch; per rotation: key limbs and diagonal; per request:
   // digits, c0 and the partial outputs
+  const double wd = T.narrow ? 0.5 : 1.0;  // digit words in 8-byte units
   const double by = 8.0 * n *
-                    ((double)plan.B * plan.R * 2.0 + plan.R * (2.0 * ell * ell + ell) + plan.B * (ell * ell + ell) +
+                    ((double)plan.B * plan.R * 2.0 + plan.R * (2.0 * ell * ell + ell) + plan.B * (wd * ell * ell + ell) +
                      (double)plan.B * plan.chunks * 2.0 * ell * (plan.accumulate ? 2.0 : 1.0));
   Launch L(K_VECMAT, st, by,
            (double)plan.B * plan.R * 2.0 * ell * ((ell + 2.0) * n + bfly_per_limb(T.log_n)));

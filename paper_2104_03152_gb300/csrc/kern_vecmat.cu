@@ -82,12 +82,12 @@ __global__ void __launch_bounds__(kDhThreads) k_vecmat_dh_acc(DevTables T, u32 e
   const u32 chunk = blockIdx.y;
   const u32 mod = i < ell ? i : T.L;
   const ModConst m = T.mods[mod];
-  const u64* digits[RPT];
+  const W* digits[RPT];
   const u64* c0[RPT];
 #pragma unroll
   for (int rr = 0; rr < RPT; ++rr) {
     const u32 rq = min(rg * RPT + rr, p.B - 1);  // a short last group repeats a request, never stored
-    digits[rr] = p.digits + rq * p.digits_b + (u64)i * n;  // digit j at + j * slots * n
+    digits[rr] = reinterpret_cast<const W*>(p.digits) + rq * p.digits_b + (u64)i * n;  // digit j at + j * slots * n
     c0[rr] = p.ct + rq * p.ct_b + (u64)i * n;
   }
   const u32 base = eb * kDhThreads * EPT + threadIdx.x;
@@ -214,8 +214,9 @@ u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow) {
 
 void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st) {
   const double n = (double)(1u << T.log_n);
+  const double wd = T.narrow ? 0.5 : 1.0;  // digit words in 8-byte units
   const double by = 8.0 * n *
-                    ((double)p.B * (ell * (ell + 1.0) + ell) +
+                    ((double)p.B * (wd * ell * (ell + 1.0) + ell) +
                      (double)p.R * (2.0 * ell * (ell + 1.0) + (p.diag ? ell + 1.0 : 0.0)) +
                      (double)p.B * p.chunks * (3.0 * ell + 2.0));
   const double ops = (double)p.B * p.R * n * ((ell + 1.0) * (2.0 * ell + 4.0) + ell);
