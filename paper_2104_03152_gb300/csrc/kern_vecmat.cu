@@ -70,8 +70,12 @@ __device__ __forceinline__ u64 dh_off(u32 rq, u32 chunk, u32 chunks, u32 comp, u
 
 // Thread = EPT elements (stride kDhThreads) x RPT requests of one slot i: the key limbs, the
 // diagonal and the Galois index of a rotation are loaded once for the RPT requests.
-template <typename W, int EPT, int RPT>
-__global__ void __launch_bounds__(kDhThreads) k_vecmat_dh_acc(DevTables T, u32 ell, const __grid_constant__ VecmatDhPlan p) {
+// ELL > 0 fixes the level at compile time (the digit loop unrolls, its offsets become constants);
+// ELL = 0 takes it from the argument.
+template <typename W, int EPT, int RPT, int ELL>
+__global__ void __launch_bounds__(kDhThreads) k_vecmat_dh_acc(DevTables T, u32 ell_arg,
+                                                               const __grid_constant__ VecmatDhPlan p) {
+  const u32 ell = ELL > 0 ? (u32)ELL : ell_arg;
   const u32 log_n = T.log_n;
   const u64 n = 1ull << log_n;
   const u32 slots = ell + 1;
@@ -106,6 +110,7 @@ __global__ void __launch_bounds__(kDhThreads) k_vecmat_dh_acc(DevTables T, u32 e
       if (g < n) {
         const u32 src = galois_src(g, kk.g, log_n);
         typename Ew<W>::Acc s0[RPT], s1[RPT];
+#pragma unroll
         for (u32 j = 0; j < ell; ++j) {
           const u64 w0 = k0[2 * j * kstep + g], w1 = k0[(2 * j + 1) * kstep + g];
 #pragma unroll
@@ -205,6 +210,22 @@ static decltype(&k_vecmat_dh_moddown<u64, 0>) const K6_k_vecmat_dh_moddown[6] = 
 
 }  // namespace
 
+// The level as a template argument up to 8 limbs (every level of the CNN and the 4096x256 product).
+template <typename W, int EPT, int RPT>
+static void dh_acc_launch(dim3 grid, cudaStream_t st, const DevTables& T, u32 ell, const VecmatDhPlan& p) {
+  switch (ell) {
+#define TCKS_DH_CASE(E) \
+  case E:               \
+    k_vecmat_dh_acc<W, EPT, RPT, E><<<grid, kDhThreads, 0, st>>>(T, ell, p); \
+    return;
+    TCKS_DH_CASE(1) TCKS_DH_CASE(2) TCKS_DH_CASE(3) TCKS_DH_CASE(4)
+    TCKS_DH_CASE(5) TCKS_DH_CASE(6) TCKS_DH_CASE(7) TCKS_DH_CASE(8)
+#undef TCKS_DH_CASE
+    default:
+      k_vecmat_dh_acc<W, EPT, RPT, 0><<<grid, kDhThreads, 0, st>>>(T, ell, p);
+  }
+}
+
 u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow) {
   const u64 n = 1ull << log_n;
   const u32 ept = narrow ? kEpt32 : kEpt64, rpt = narrow ? kRpt32 : kRpt64;
@@ -223,9 +244,9 @@ void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cu
   Launch L(K_VECMAT_DH, st, by, ops);
   const dim3 grid(vecmat_dh_base_ctas(T.log_n, ell, p.B, T.narrow), p.chunks);
   if (T.narrow)
-    k_vecmat_dh_acc<u32, kEpt32, kRpt32><<<grid, kDhThreads, 0, st>>>(T, ell, p);
+    dh_acc_launch<u32, kEpt32, kRpt32>(grid, st, T, ell, p);
   else
-    k_vecmat_dh_acc<u64, kEpt64, kRpt64><<<grid, kDhThreads, 0, st>>>(T, ell, p);
+    dh_acc_launch<u64, kEpt64, kRpt64>(grid, st, T, ell, p);
 }
 
 void launch_vecmat_dh_fold(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st) {
