@@ -14,6 +14,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <utility>
 
 #include "context.h"
@@ -514,12 +515,32 @@ void launch_modup(const DevTables& T, const u64* x_ntt, u64 x_stride, u32 count,
   launch_limb(K6_k_modup, T.narrow, ell * (ell + 1), count, T.log_n, st, T.limb_threads, T, x_ntt, x_stride, (const u64*)x_coef_tmp, ell, digits);
 }
 
+// Calls f(std::integral_constant<int, E>) with E = ell for ell <= 8 (E = 0 above), so that a loop over
+// the digits inside f unrolls with constant offsets; ell is uniform across the CTA.
+template <typename F>
+__device__ __forceinline__ void ell_dispatch(u32 ell, F&& f) {
+  switch (ell) {
+    case 1: f(std::integral_constant<int, 1>{}); return;
+    case 2: f(std::integral_constant<int, 2>{}); return;
+    case 3: f(std::integral_constant<int, 3>{}); return;
+    case 4: f(std::integral_constant<int, 4>{}); return;
+    case 5: f(std::integral_constant<int, 5>{}); return;
+    case 6: f(std::integral_constant<int, 6>{}); return;
+    case 7: f(std::integral_constant<int, 7>{}); return;
+    case 8: f(std::integral_constant<int, 8>{}); return;
+    default: f(std::integral_constant<int, 0>{});
+  }
+}
+
 // Inner product of (automorphed) digits with one key component on slot `slot`:
 //   sum_j D_j[slot][src] * key_j[b][key_slot][k], lazy accumulation, one reduction.
-template <typename W>
-__device__ __forceinline__ u64 ks_inner(const W* __restrict__ digits, u32 ell, u32 slot, const u64* __restrict__ key,
+// E > 0: ell == E known at compile time.
+template <typename W, int E = 0>
+__device__ __forceinline__ u64 ks_inner(const W* __restrict__ digits, u32 ell_arg, u32 slot, const u64* __restrict__ key,
                                         u32 K, u32 key_slot, u32 b, u32 k, u32 src, u64 n, const ModConst& m) {
+  const u32 ell = E > 0 ? (u32)E : ell_arg;
   typename Ew<W>::Acc acc;
+#pragma unroll
   for (u32 j = 0; j < ell; ++j) {
     const u64 d = digits[((u64)j * (ell + 1) + slot) * n + src];
     const u64 w = key[(((u64)j * 2 + b) * (K + 1) + key_slot) * n + k];
@@ -544,11 +565,13 @@ __global__ void k_ks_inner_p(DevTables T, u32 ell, const __grid_constant__ KsPla
   const W* digits = reinterpret_cast<const W*>(plan.digits) + rq * plan.digits_b;
   const u32 b = sl.job / plan.B;
   const ModConst mp = T.mods[T.L];
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
-    const u32 g = sl.off + k;
-    const u32 src = kk.g == 1 ? g : galois_src(g, kk.g, log_n);
-    s[sw(k)] = (W)ks_inner<W>(digits, ell, ell, kk.key, kk.K, kk.K, b, g, src, n, mp);
-  }
+  ell_dispatch(ell, [&](auto E) {
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
+      const u32 g = sl.off + k;
+      const u32 src = kk.g == 1 ? g : galois_src(g, kk.g, log_n);
+      s[sw(k)] = (W)ks_inner<W, decltype(E)::value>(digits, ell, ell, kk.key, kk.K, kk.K, b, g, src, n, mp);
+    }
+  });
   __syncthreads();
   ntt_inv_slice<W, LC>(s, T, T.L, sl.rank);
   u64* top = plan.top + (yy * 2 + b) * n + sl.off;
@@ -579,14 +602,16 @@ __global__ void k_ks_moddown(DevTables T, u32 ell, const __grid_constant__ KsPla
   const u64* add = b == 0 ? (plan.add0 ? plan.add0 + rq * plan.add0_b : nullptr)
                           : (plan.add1 ? plan.add1 + rq * plan.add1_b : nullptr);
   u64* dst = plan.out + rq * plan.out_b + r * plan.out_r + ((u64)b * ell + i) * n;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
-    const u32 g = sl.off + k;
-    const u32 src = kk.g == 1 ? g : galois_src(g, kk.g, log_n);
-    const u64 u = ks_inner<W>(digits, ell, i, kk.key, kk.K, i, b, g, src, n, mi);
-    u64 v = Ew<W>::shoup_inv(sub_mod(u, Ar<W>::fwd_out(s[sw(k)], mi), mi.q), pc, mi);
-    if (add) v = add_mod(v, add[(u64)i * n + (plan.add_perm ? src : g)], mi.q);
-    dst[g] = v;
-  }
+  ell_dispatch(ell, [&](auto E) {
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
+      const u32 g = sl.off + k;
+      const u32 src = kk.g == 1 ? g : galois_src(g, kk.g, log_n);
+      const u64 u = ks_inner<W, decltype(E)::value>(digits, ell, i, kk.key, kk.K, i, b, g, src, n, mi);
+      u64 v = Ew<W>::shoup_inv(sub_mod(u, Ar<W>::fwd_out(s[sw(k)], mi), mi.q), pc, mi);
+      if (add) v = add_mod(v, add[(u64)i * n + (plan.add_perm ? src : g)], mi.q);
+      dst[g] = v;
+    }
+  });
 }
 
 // Algorithmic bytes of a plan: distinct digit sets and keys once, scratch and outputs once.
