@@ -12,8 +12,9 @@
 // memory round trip), with a radix-4 or radix-2 round for the remainder.
 //
 // Word types: W = u64 for any prime below 2^62 (Harvey's lazy butterflies: [0, 4q) forward,
-// [0, 2q) inverse, 64-bit Shoup); W = u32 when every prime of the chain is below 2^31 (fully reduced
-// butterflies with 32-bit Shoup companions, half the shared memory). Both give the canonical result.
+// [0, 2q) inverse, 64-bit Shoup); W = u32 when every prime of the chain is below 2^31 (32-bit Shoup
+// companions, half the shared memory): lazy butterflies for primes below 2^30, fully reduced ones for
+// primes in [2^30, 2^31). Both give the canonical result.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -83,9 +84,33 @@ struct Ar<u32> {
   }
 };
 
+// 32-bit words with Harvey's lazy bounds for primes below 2^30 ([0, 4q) forward, [0, 2q) inverse fit
+// in 32 bits): about half the integer operations of the fully reduced butterfly. The slice transforms
+// take this policy for such primes (one uniform branch per CTA) and finish in canonical form.
+struct Ar32Lazy {
+  // X, Y in [0, 4q) -> X + WY, X - WY in [0, 4q).
+  static __device__ __forceinline__ void ct(u32& X, u32& Y, u32 W, u32 Wsh, u32 q) {
+    const u32 two_q = 2 * q;
+    const u32 x = csub32(X, two_q);
+    const u32 t = Y * W - __umulhi(Y, Wsh) * q;  // in [0, 2q)
+    X = x + t;
+    Y = x - t + two_q;
+  }
+  // X, Y in [0, 2q) -> X + Y, (X - Y) W in [0, 2q).
+  static __device__ __forceinline__ void gs(u32& X, u32& Y, u32 W, u32 Wsh, u32 q) {
+    const u32 two_q = 2 * q;
+    const u32 u = csub32(X + Y, two_q);
+    const u32 d = X - Y + two_q;
+    Y = d * W - __umulhi(d, Wsh) * q;
+    X = u;
+  }
+};
+
+
+
 // R = 2^LR elements x[q] = element base + q * stride (stride = the round's smallest butterfly
 // distance) through forward stages st .. st+LR-1; gblk = global index of the block of stage st.
-template <typename W, int LR>
+template <typename W, int LR, typename A = Ar<W>>
 __device__ __forceinline__ void fwd_group(W (&x)[1 << LR], u32 st, u32 gblk, const W* tw, const W* tws, W q) {
   constexpr int R = 1 << LR;
 #pragma unroll
@@ -96,14 +121,14 @@ __device__ __forceinline__ void fwd_group(W (&x)[1 << LR], u32 st, u32 gblk, con
       const u32 idx = ((1u << st) << u) + (gblk << u) + b;
       const W w = tw[idx], wsh = tws[idx];
 #pragma unroll
-      for (int x0 = 0; x0 < h; ++x0) Ar<W>::ct(x[b * 2 * h + x0], x[b * 2 * h + x0 + h], w, wsh, q);
+      for (int x0 = 0; x0 < h; ++x0) A::ct(x[b * 2 * h + x0], x[b * 2 * h + x0 + h], w, wsh, q);
     }
   }
 }
 
 // Inverse stages st .. st+LR-1 on R elements base + q * 2^st; gblk = global block index (at the
 // round's last sub-stage) of the group.
-template <typename W, int LR>
+template <typename W, int LR, typename A = Ar<W>>
 __device__ __forceinline__ void inv_group(W (&x)[1 << LR], u32 log_n, u32 st, u32 gblk, const W* tw, const W* tws,
                                           W q) {
   constexpr int R = 1 << LR;
@@ -116,13 +141,13 @@ __device__ __forceinline__ void inv_group(W (&x)[1 << LR], u32 log_n, u32 st, u3
       const u32 idx = m + (gblk << (LR - u - 1)) + b;
       const W w = tw[idx], wsh = tws[idx];
 #pragma unroll
-      for (int x0 = 0; x0 < h; ++x0) Ar<W>::gs(x[b * 2 * h + x0], x[b * 2 * h + x0 + h], w, wsh, q);
+      for (int x0 = 0; x0 < h; ++x0) A::gs(x[b * 2 * h + x0], x[b * 2 * h + x0 + h], w, wsh, q);
     }
   }
 }
 
 // One local forward round of LR stages starting at stage st over the CTA's slice s[0, ns).
-template <typename W, int LR>
+template <typename W, int LR, typename A = Ar<W>>
 __device__ __forceinline__ void fwd_round(W* s, u32 log_n, u32 log_ns, u32 rank, u32 st, const W* tw, const W* tws,
                                           W q) {
   constexpr int R = 1 << LR;
@@ -136,14 +161,14 @@ __device__ __forceinline__ void fwd_round(W* s, u32 log_n, u32 log_ns, u32 rank,
     W x[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) x[k] = s[sw(base + k * tr)];
-    fwd_group<W, LR>(x, st, gbase + blk, tw, tws, q);
+    fwd_group<W, LR, A>(x, st, gbase + blk, tw, tws, q);
 #pragma unroll
     for (int k = 0; k < R; ++k) s[sw(base + k * tr)] = x[k];
   }
   __syncthreads();
 }
 
-template <typename W, int LR>
+template <typename W, int LR, typename A = Ar<W>>
 __device__ __forceinline__ void inv_round(W* s, u32 log_n, u32 log_ns, u32 rank, u32 st, const W* tw, const W* tws,
                                           W q) {
   constexpr int R = 1 << LR;
@@ -157,7 +182,7 @@ __device__ __forceinline__ void inv_round(W* s, u32 log_n, u32 log_ns, u32 rank,
     W x[R];
 #pragma unroll
     for (int k = 0; k < R; ++k) x[k] = s[sw(base + k * t)];
-    inv_group<W, LR>(x, log_n, st, gbase + blk, tw, tws, q);
+    inv_group<W, LR, A>(x, log_n, st, gbase + blk, tw, tws, q);
 #pragma unroll
     for (int k = 0; k < R; ++k) s[sw(base + k * t)] = x[k];
   }
@@ -167,7 +192,7 @@ __device__ __forceinline__ void inv_round(W* s, u32 log_n, u32 log_ns, u32 rank,
 // Cross-CTA stages (C = 2^LC CTAs): element j of every CTA's slice forms a group of C; each CTA
 // computes the group and keeps its own element. FWD: the first LC forward stages (the slice must be
 // complete in every CTA); otherwise the last LC inverse stages. s is overwritten only after all reads.
-template <typename W, int LC, bool FWD>
+template <typename W, int LC, bool FWD, typename A = Ar<W>>
 __device__ __forceinline__ void cross_stages(W* s, u32 log_n, u32 log_ns, u32 rank, const W* tw, const W* tws, W q) {
   namespace cg = cooperative_groups;
   constexpr int C = 1 << LC;
@@ -188,9 +213,9 @@ __device__ __forceinline__ void cross_stages(W* s, u32 log_n, u32 log_ns, u32 ra
 #pragma unroll
         for (int r = 0; r < C; ++r) x[r] = rem[r][sw(j)];
         if (FWD)
-          fwd_group<W, LC>(x, 0, 0, tw, tws, q);
+          fwd_group<W, LC, A>(x, 0, 0, tw, tws, q);
         else
-          inv_group<W, LC>(x, log_n, log_ns, 0, tw, tws, q);
+          inv_group<W, LC, A>(x, log_n, log_ns, 0, tw, tws, q);
         keep[e] = x[0];
 #pragma unroll
         for (int r = 1; r < C; ++r)
@@ -210,28 +235,28 @@ __device__ __forceinline__ void cross_stages(W* s, u32 log_n, u32 log_ns, u32 ra
 // The stages a slice of 2^log_ns consecutive elements (slice `rank` of the limb) completes on its
 // own: forward stages log_n - log_ns .. log_n - 1 (the earlier ones pair elements of different
 // slices), or inverse stages 0 .. log_ns - 1. Each ends with a barrier.
-template <typename W>
+template <typename W, typename A = Ar<W>>
 __device__ __forceinline__ void ntt_fwd_local_rounds(W* s, u32 log_n, u32 log_ns, u32 rank, const W* tw, const W* tws,
                                                      W q) {
   u32 st = log_n - log_ns;
   const u32 left = log_ns;
   // remainder round first (radix-2 or radix-4), then radix-8 rounds
   if (left % 3 == 1) {
-    fwd_round<W, 1>(s, log_n, log_ns, rank, st, tw, tws, q);
+    fwd_round<W, 1, A>(s, log_n, log_ns, rank, st, tw, tws, q);
     st += 1;
   } else if (left % 3 == 2) {
-    fwd_round<W, 2>(s, log_n, log_ns, rank, st, tw, tws, q);
+    fwd_round<W, 2, A>(s, log_n, log_ns, rank, st, tw, tws, q);
     st += 2;
   }
-  for (; st < log_n; st += 3) fwd_round<W, 3>(s, log_n, log_ns, rank, st, tw, tws, q);
+  for (; st < log_n; st += 3) fwd_round<W, 3, A>(s, log_n, log_ns, rank, st, tw, tws, q);
 }
-template <typename W>
+template <typename W, typename A = Ar<W>>
 __device__ __forceinline__ void ntt_inv_local_rounds(W* s, u32 log_n, u32 log_ns, u32 rank, const W* tw, const W* tws,
                                                      W q) {
   u32 st = 0;
-  for (; st + 3 <= log_ns; st += 3) inv_round<W, 3>(s, log_n, log_ns, rank, st, tw, tws, q);
-  if (log_ns - st == 2) inv_round<W, 2>(s, log_n, log_ns, rank, st, tw, tws, q);
-  if (log_ns - st == 1) inv_round<W, 1>(s, log_n, log_ns, rank, st, tw, tws, q);
+  for (; st + 3 <= log_ns; st += 3) inv_round<W, 3, A>(s, log_n, log_ns, rank, st, tw, tws, q);
+  if (log_ns - st == 2) inv_round<W, 2, A>(s, log_n, log_ns, rank, st, tw, tws, q);
+  if (log_ns - st == 1) inv_round<W, 1, A>(s, log_n, log_ns, rank, st, tw, tws, q);
 }
 
 // Forward transform of the CTA's slice s[0, N/C) of a limb split over C = 2^LC CTAs (LC = 0: the
@@ -243,18 +268,35 @@ __device__ __forceinline__ void ntt_fwd_slice(W* s, const DevTables& T, u32 mod,
   const W q = (W)T.mods[mod].q;
   const W* tw = Ar<W>::tw(T, mod, 0);
   const W* tws = Ar<W>::tw(T, mod, 1);
+  if constexpr (sizeof(W) == 4) {
+    if (q < (1u << 30)) {  // lazy butterflies, then [0, 4q) -> [0, q)
+      if constexpr (LC > 0) cross_stages<W, LC, true, Ar32Lazy>(s, log_n, log_ns, rank, tw, tws, q);
+      ntt_fwd_local_rounds<W, Ar32Lazy>(s, log_n, log_ns, rank, tw, tws, q);
+      for (u32 k = threadIdx.x; k < (1u << log_ns); k += blockDim.x) s[k] = csub32(csub32(s[k], 2 * q), q);
+      __syncthreads();
+      return;
+    }
+  }
   if constexpr (LC > 0) cross_stages<W, LC, true>(s, log_n, log_ns, rank, tw, tws, q);
   ntt_fwd_local_rounds<W>(s, log_n, log_ns, rank, tw, tws, q);
 }
 
-// Inverse transform (without N^-1) of the CTA's slice; input canonical, output in [0, 2q) (u64)
-// or canonical (u32); Ar<W>::inv_out applies N^-1 and gives the canonical value.
+// Inverse transform (without N^-1) of the CTA's slice; input canonical, output in [0, 2q) (u64, and
+// u32 primes below 2^30) or canonical (other u32 primes); Ar<W>::inv_out applies N^-1 and gives the
+// canonical value.
 template <typename W, int LC>
 __device__ __forceinline__ void ntt_inv_slice(W* s, const DevTables& T, u32 mod, u32 rank) {
   const u32 log_n = T.log_n, log_ns = log_n - LC;
   const W q = (W)T.mods[mod].q;
   const W* tw = Ar<W>::tw(T, mod, 2);
   const W* tws = Ar<W>::tw(T, mod, 3);
+  if constexpr (sizeof(W) == 4) {
+    if (q < (1u << 30)) {  // lazy butterflies: output in [0, 2q), which Ar<u32>::inv_out accepts
+      ntt_inv_local_rounds<W, Ar32Lazy>(s, log_n, log_ns, rank, tw, tws, q);
+      if constexpr (LC > 0) cross_stages<W, LC, false, Ar32Lazy>(s, log_n, log_ns, rank, tw, tws, q);
+      return;
+    }
+  }
   ntt_inv_local_rounds<W>(s, log_n, log_ns, rank, tw, tws, q);
   if constexpr (LC > 0) cross_stages<W, LC, false>(s, log_n, log_ns, rank, tw, tws, q);
 }
