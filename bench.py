@@ -3,11 +3,11 @@
 Workload (the paper's evaluation network, §4 / Table 2, with the chain N=8192, primes
 [31,26,26,26,26,26,26,31], scale 2^26): 28x28 seeded uniform image, im2col-encoded and encrypted;
 conv 4x7x7 stride 3 -> square -> FC 256->64 -> square -> FC 64->10 on seeded N(0, 0.1) weights.
-A step is one batch of B encrypted inferences (B requests, default 64) through the whole hot path
+A step is one batch of B encrypted inferences (B requests, default 256) through the whole hot path
 (conv rotations, pack, relinearized squares, two hoisted vector x matrix products) in the batched
 schedule, where every stage runs once for the whole batch; inputs are resident in HBM. Per step the
-kernels stream ~0.75 GB of Galois keys plus ~2 GB of per-request key-switch scratch, more than the
-129 MB L2, so no L2 flush is added. The plain path (one request per step) is timed alongside.
+kernels stream the Galois keys plus several GB of per-request key-switch scratch (~2 GB at B = 64),
+far more than the 129 MB L2, so no L2 flush is added. The plain path (one request per step) is timed alongside.
 `e2e` times the batched step through the C ABI with host buffers: the B input ciphertexts are
 imported from pinned host memory and the B outputs exported back to it inside the timed region.
 
@@ -303,12 +303,12 @@ def run_gpu(args, world, rank, local):
         for rate in [float(x) for x in args.serve_rate.split(",")]:
             arr = poisson_arrivals(rate, args.serve_seconds, 8)
             kinds = np.where(np.random.default_rng(9).uniform(size=len(arr)) < mix, "vm", "cnn")
-            lat_s, kind_s, thr_s = serve_trace(tk, lanes, arr, kinds, args.batch)
+            lat_s, kind_s, thr_s = serve_trace(tk, lanes, arr, kinds, args.serve_batch)
             # the plain path saturates below the offered rate: run it on the start of the same trace
             n_p = min(len(arr), args.plain_requests)
             lat_p, kind_p, thr_p = plain_trace(tk, lanes, arr[:n_p], kinds[:n_p])
             traces.append({"offered_rate": rate, "seconds": args.serve_seconds, "requests": len(arr),
-                           "served": dict(summary(lat_s, kind_s, thr_s), max_batch_per_stage=args.batch,
+                           "served": dict(summary(lat_s, kind_s, thr_s), max_batch_per_stage=args.serve_batch,
                                           max_in_flight=1024, hbm_budget_gb=200),
                            "plain": dict(summary(lat_p, kind_p, thr_p), trace_requests=int(n_p))})
         serving = {"mix": {"cnn": 1.0 - mix, "vm": mix}, "vm_workload": C4_WORKLOAD if c4 else None,
@@ -765,7 +765,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=2, help="oracle inferences timed for cpu_baseline")
-    ap.add_argument("--batch", type=int, default=64, help="requests per step (the batched schedule)")
+    ap.add_argument("--batch", type=int, default=256, help="requests per step (the batched schedule)")
+    ap.add_argument("--serve-batch", type=int, default=64, help="largest batch the serving loop forms per stage")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the Poisson serving trace (0: skip)")
     ap.add_argument("--serve-rate", default="2000,300",
                     help="offered requests/s of the serving traces (comma-separated; one trace each)")
