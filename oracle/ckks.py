@@ -651,6 +651,26 @@ class OracleCKKS:
                             P(np.ascontiguousarray(diags_ext)), ptrs, P(lv), P(ge), P(out))
         return self.rescale(Ct(out, level, ct.scale * self.scale))
 
+    def dh_sum(self, ct: Ct, steps, diags_ext: np.ndarray) -> Ct:
+        """sum_k rot(ct, s_k) * d_k with s_0 = 0 and s_k = steps[k - 1], the diagonals d_k given over
+        the extended basis [len(steps) + 1][level + 1][N], with one ModUp before and one ModDown after
+        the sum (orc_vecmat_dh). The scale is the ciphertext's times the diagonals' (no rescale)."""
+        steps = list(steps)
+        level = ct.level
+        rows = len(steps) + 1
+        if diags_ext.shape != (rows, level + 1, self.N):
+            raise ValueError("diagonals do not match the steps and the level")
+        digits = self.modup(ct)
+        keys = [self._key(st) for st in steps]
+        key_arrs = [np.ascontiguousarray(k.data) for k in keys]
+        ptrs = (_u64p * max(1, len(keys)))(*[P(a) for a in key_arrs])
+        lv = np.array([k.level for k in keys] or [0], dtype=np.uint32)
+        ge = np.array([self.galois_elt(st) for st in steps] or [1], dtype=np.uint32)
+        out = np.zeros((2, level, self.N), dtype=np.uint64)
+        lib().orc_vecmat_dh(self._ctx, P(np.ascontiguousarray(ct.data)), P(digits), level, rows,
+                            P(np.ascontiguousarray(diags_ext)), ptrs, P(lv), P(ge), P(out))
+        return Ct(out, level, ct.scale * self.scale)
+
     def rotsum_dh(self, ct: Ct, steps) -> Ct:
         """ct + sum over `steps` of rot(ct, s), hoisted with one ModDown after the sum: orc_vecmat_dh
         with every diagonal the constant polynomial 1 (all ones in NTT form over the extended basis),
@@ -686,6 +706,22 @@ class OracleCKKS:
         x = self.rescale(self.mul_plain(ct, kernel_pt))
         baby, giant = self.conv_bsgs_steps(taps, windows)
         return self.rotsum_dh(self.rotsum_dh(x, baby), giant)
+
+    def conv_baby_diagonals_ext(self, kernel_slots: np.ndarray, taps: int, windows: int, level: int) -> np.ndarray:
+        """The baby-step diagonals of the shared convolution sum: the kernel's slot vector rotated left
+        by each baby step (0 first), over the extended basis at `level`: [B][level+1][N]."""
+        baby, _ = self.conv_bsgs_steps(taps, windows)
+        return np.stack([self.encode_ext(np.roll(kernel_slots, -s), level) for s in [0] + baby])
+
+    def conv2d_im2col_shared(self, ct: Ct, baby_ext: np.ndarray, taps: int, windows: int) -> Ct:
+        """The hoisted convolution sum with the kernel multiplied after the baby-step rotations:
+        x1 = sum_{b < B} rot(ct * K, windows b) = sum_b rot(ct, windows b) * rot(K, windows b), a
+        diagonal-method sum over the input's own rotations (one ModUp of ct, shared by every kernel of
+        the layer, one ModDown per kernel), rescaled; then the giant steps as before,
+        sum_{g < G} rot(x1, windows B g)."""
+        baby, giant = self.conv_bsgs_steps(taps, windows)
+        x1 = self.rescale(self.dh_sum(ct, baby, baby_ext))
+        return self.rotsum_dh(x1, giant)
 
     def encode_matrix_ext(self, M: np.ndarray, level: int) -> np.ndarray:
         """The diagonals over the extended basis: [n][level+1][N]."""
@@ -805,9 +841,12 @@ class EncodedCNN:
     rect: bool = False                         # fully connected layers by rectangular diagonals
     biases: list | None = None                 # pre-encoded biases (Pt) in place of encoding them here
     conv_hoist: bool = False                   # convolution sums by hoisted baby-step giant-step rotation sums
+    conv_shared: bool = False                  # baby steps on the input's rotations, shared by the kernels
+    conv_baby_ext: list = field(default_factory=list)  # per kernel, its baby-step diagonals [B][L+1][N]
 
 
-def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64, classes=10, rect=False, conv_hoist=False):
+def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64, classes=10, rect=False, conv_hoist=False,
+                     conv_shared=False):
     """Galois steps of the CNN schedule with the level each is used at (key trimming). rect: the fully
     connected layers by rectangular diagonals (FC2 takes FC1's output as it comes, replicated)."""
     L = o.L
@@ -819,7 +858,11 @@ def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64, classes=
             if s:
                 need[s] = max(need.get(s, 0), level)
 
-    if conv_hoist:
+    if conv_shared:  # baby steps rotate the input at level L
+        baby, giant = o.conv_bsgs_steps(taps, windows)
+        use(baby, L)
+        use(giant, L - 1)
+    elif conv_hoist:
         baby, giant = o.conv_bsgs_steps(taps, windows)
         use(baby + giant, L - 1)
     else:
@@ -836,11 +879,15 @@ def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64, classes=
     return need
 
 
-def cnn_encode(o: OracleCKKS, w: CNNWeights, windows=64, rect=False, conv_hoist=False) -> EncodedCNN:
+def cnn_encode(o: OracleCKKS, w: CNNWeights, windows=64, rect=False, conv_hoist=False,
+               conv_shared=False) -> EncodedCNN:
     L = o.L
-    e = EncodedCNN(windows=windows, taps=w.conv_w.shape[1], conv_hoist=conv_hoist)
+    e = EncodedCNN(windows=windows, taps=w.conv_w.shape[1], conv_hoist=conv_hoist, conv_shared=conv_shared)
     for k in range(w.conv_w.shape[0]):
         e.conv.append(o.encode(o.kernel_slots(w.conv_w[k], windows), level=L))
+        if conv_shared:
+            e.conv_baby_ext.append(o.conv_baby_diagonals_ext(o.kernel_slots(w.conv_w[k], windows), e.taps,
+                                                             windows, L))
         mask = np.zeros(o.slots)
         mask[k * windows: (k + 1) * windows] = 1.0
         e.masks.append(o.encode(mask, level=L - 1))
@@ -872,8 +919,11 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
 
     W = enc.windows
     K = len(enc.conv)
-    conv = o.conv2d_im2col_hoisted if enc.conv_hoist else o.conv2d_im2col_pt
-    chans = [conv(ct, enc.conv[k], enc.taps, W) for k in range(K)]
+    if enc.conv_shared:
+        chans = [o.conv2d_im2col_shared(ct, enc.conv_baby_ext[k], enc.taps, W) for k in range(K)]
+    else:
+        conv = o.conv2d_im2col_hoisted if enc.conv_hoist else o.conv2d_im2col_pt
+        chans = [conv(ct, enc.conv[k], enc.taps, W) for k in range(K)]
     v = None
     for k in range(K):
         t = o.rescale(o.mul_plain(chans[k], enc.masks[k]))

@@ -485,3 +485,48 @@ def test_cnn_hoisted_conv_schedule_matches_fp64():
     ct = o.encrypt_values(v, 77)
     logits = o.decrypt_values(oracle.cnn_forward(o, ct, w, enc, double_hoist=True), 10)
     assert np.max(np.abs(logits - oracle.cnn_plain(img, w))) < 5e-3
+
+
+def test_dh_sum_with_diagonals_and_shared_conv():
+    """The double-hoisted sum with arbitrary steps and diagonals decrypts to sum_k rot(z, s_k) * d_k; the
+    shared-baby-step convolution (kernel multiplied after the input's rotations) decrypts to the same
+    tap sums as the hoisted one and as the FP64 convolution."""
+    o = OracleCKKS(13, [55, 40, 40, 40, 56], 2.0 ** 40).keygen()
+    baby, giant = OracleCKKS.conv_bsgs_steps(49, 64)
+    o.gen_galois_keys(baby + giant + [5, 300])
+    z = inputs.uniform_slots(o.slots, 31)
+    ct = o.encrypt_values(z, 60)
+    steps = [5, 300]
+    ds = [inputs.uniform_slots(o.slots, 40 + k) for k in range(3)]
+    ext = np.stack([o.encode_ext(d, ct.level) for d in ds])
+    got = o.decrypt_values(o.rescale(o.dh_sum(ct, steps, ext)))
+    ref = ds[0] * z + sum(np.roll(z, -s) * d for s, d in zip(steps, ds[1:]))
+    assert np.max(np.abs(got - ref)) < 1e-6
+    # the convolution: slot w of the result holds sum_t K[t] x[64 t + w]
+    img = inputs.mnist_like_image(5)
+    x, _ = OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+    kern = np.random.default_rng(8).normal(0.0, 0.1, 49)
+    ks = o.kernel_slots(kern, 64)
+    cx = o.encrypt_values(x, 61)
+    shared = o.conv2d_im2col_shared(cx, o.conv_baby_diagonals_ext(ks, 49, 64, cx.level), 49, 64)
+    hoisted = o.conv2d_im2col_hoisted(cx, o.encode(ks, level=cx.level), 49, 64)
+    assert shared.level == hoisted.level and shared.scale == hoisted.scale
+    a, b = o.decrypt_values(shared, 64), o.decrypt_values(hoisted, 64)
+    conv = np.array([sum(kern[t] * x[64 * t + w] for t in range(49)) for w in range(64)])
+    assert np.max(np.abs(a - conv)) < 1e-6 and np.max(np.abs(a - b)) < 1e-6
+
+
+def test_cnn_shared_conv_schedule_matches_fp64():
+    """The CNN with the shared-baby-step convolution, rectangular FC layers and double hoisting decrypts
+    to the FP64 network."""
+    o = OracleCKKS(13, [31, 26, 26, 26, 26, 26, 26, 31], 2.0 ** 26).keygen()
+    steps = oracle.cnn_galois_steps(o, rect=True, conv_hoist=True, conv_shared=True)
+    for st, lv in steps.items():
+        o.gen_galois_key(st, lv)
+    w = oracle.CNNWeights(**inputs.cnn_weights(4))
+    enc = oracle.cnn_encode(o, w, rect=True, conv_hoist=True, conv_shared=True)
+    img = inputs.mnist_like_image(3)
+    v, _ = OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+    ct = o.encrypt_values(v, 77)
+    logits = o.decrypt_values(oracle.cnn_forward(o, ct, w, enc, double_hoist=True), 10)
+    assert np.max(np.abs(logits - oracle.cnn_plain(img, w))) < 5e-3
