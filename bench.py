@@ -166,14 +166,15 @@ def source_digest(files) -> str:
 
 
 # ---------------------------------------------------------------------------------- GPU arm --
-def gpu_setup(torch, batch, double_hoist, rect=False, conv_hoist=False):
+def gpu_setup(torch, batch, double_hoist, rect=False, conv_hoist=False, conv_shared=False):
     import paper_2104_03152_gb300 as tk
     from paper_2104_03152_gb300 import inputs
 
     tk.lib(build_if_missing=True)
     stream = torch.cuda.Stream()
     flags = (tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | (tk.TCKS_DOUBLE_HOIST if double_hoist else 0)
-             | (tk.TCKS_RECT_DIAG if rect else 0) | (tk.TCKS_CONV_HOIST if conv_hoist else 0))
+             | (tk.TCKS_RECT_DIAG if rect else 0) | (tk.TCKS_CONV_HOIST if conv_hoist else 0)
+             | (tk.TCKS_CONV_SHARED if conv_hoist and conv_shared else 0))
     ctx = tk.Context(tk.Params(LOG_N, BITS, SCALE), seed=inputs.SEED_KEYS, flags=flags, stream=stream.cuda_stream)
     w = inputs.cnn_weights(SEED_W)
     model = tk.CNN(ctx, w["conv_w"], w["conv_b"], w["fc1_w"], w["fc1_b"], w["fc2_w"], w["fc2_b"], windows=64)
@@ -203,7 +204,8 @@ def run_gpu(args, world, rank, local):
     torch = dist_init(world, local)
     B = args.batch
     rect = args.fc_form == "rect"
-    tk, ctx, model, cts, stream, imgs, w = gpu_setup(torch, B, args.double_hoist, rect, bool(args.conv_hoist))
+    tk, ctx, model, cts, stream, imgs, w = gpu_setup(torch, B, args.double_hoist, rect, bool(args.conv_hoist),
+                                                     bool(args.conv_shared))
     # correctness guard: the decrypted logits of every request must match the FP64 network, and the
     # batched outputs must equal the single-request path bit for bit
     outs = model.forward_batch(cts)
@@ -267,7 +269,7 @@ def run_gpu(args, world, rank, local):
         _, tot = timed(torch, stream, lambda: mdl.forward_batch(cts), 3)
         single[label] = {"value": B * 3 / (tot / 1e3), "unit": "inferences/s", "ms_per_step": tot / 3}
     form = "rectangular" if rect else "square"
-    conv = "hoisted convolution sums" if args.conv_hoist else "rotate-and-add convolution chain"
+    conv = CONV_LABEL[conv_form(args)]
     if args.double_hoist:
         ctx.set_flags(base)
         time_model(model, f"{form} FC layers, {conv}, one ModDown per FC rotation")
@@ -279,6 +281,8 @@ def run_gpu(args, world, rank, local):
         ctx.set_flags(base | dh_flag)
         alt.gen_keys()
         time_model(alt, label)
+    if conv_form(args) == "shared":
+        other((tk.TCKS_RECT_DIAG if rect else 0) | tk.TCKS_CONV_HOIST, f"{form} FC layers, {CONV_LABEL['hoist']}")
     if args.conv_hoist:
         other(tk.TCKS_RECT_DIAG if rect else 0, f"{form} FC layers, rotate-and-add convolution chain")
     if rect:
@@ -693,16 +697,28 @@ def primitives_summary(torch, tk):
     return out
 
 
+CONV_LABEL = {
+    "shared": "hoisted sums, baby steps over the input's rotations shared by the 4 kernels (one ModUp per request)",
+    "hoist": "two hoisted rotation sums per kernel (7 baby + 7 giant steps, one ModDown each)",
+    "chain": "rotate-and-add chain (6 key switches)",
+}
+
+
+def conv_form(args) -> str:
+    return ("shared" if args.conv_shared else "hoist") if args.conv_hoist else "chain"
+
+
 # ------------------------------------------------------------------------------ CPU oracle --
-def oracle_setup(rect: bool = True, conv_hoist: bool = True):
+def oracle_setup(rect: bool = True, conv_hoist: bool = True, conv_shared: bool = True):
     import oracle
     from paper_2104_03152_gb300 import inputs
 
     o = oracle.OracleCKKS(LOG_N, BITS, SCALE, key_seed=inputs.SEED_KEYS).keygen()
-    for st, lv in oracle.cnn_galois_steps(o, rect=rect, conv_hoist=conv_hoist).items():
+    shared = conv_hoist and conv_shared
+    for st, lv in oracle.cnn_galois_steps(o, rect=rect, conv_hoist=conv_hoist, conv_shared=shared).items():
         o.gen_galois_key(st, lv)
     w = oracle.CNNWeights(**inputs.cnn_weights(SEED_W))
-    enc = oracle.cnn_encode(o, w, rect=rect, conv_hoist=conv_hoist)
+    enc = oracle.cnn_encode(o, w, rect=rect, conv_hoist=conv_hoist, conv_shared=shared)
     img = inputs.mnist_like_image(SEED_IMG)
     v, _ = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
     ct = o.encrypt_values(v, SEED_ENC)
@@ -710,10 +726,10 @@ def oracle_setup(rect: bool = True, conv_hoist: bool = True):
 
 
 def time_oracle(n_steps: int, warmup: int, double_hoist: bool = True, single_thread_steps: int = 0,
-                rect: bool = True, conv_hoist: bool = True):
+                rect: bool = True, conv_hoist: bool = True, conv_shared: bool = True):
     """Oracle CNN inferences on the host cores (same schedule as the GPU arm); optionally also
     single-threaded ones. Returns (times, cores, single-thread times)."""
-    oracle, o, w, enc, ct = oracle_setup(rect, conv_hoist)
+    oracle, o, w, enc, ct = oracle_setup(rect, conv_hoist, conv_shared)
     for _ in range(warmup):
         oracle.cnn_forward(o, ct, w, enc, double_hoist=double_hoist)
     times = []
@@ -739,7 +755,7 @@ def run_reference(args, world, rank):
     steps, warmup = args.steps, args.warmup
     # bound the run: at most ~3 minutes of oracle inferences
     times, cores, _ = time_oracle(steps, warmup, bool(args.double_hoist), 0, args.fc_form == "rect",
-                                  bool(args.conv_hoist))
+                                  bool(args.conv_hoist), bool(args.conv_shared))
     total = sum(times)
     value = steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": args.gpus,
@@ -749,8 +765,7 @@ def run_reference(args, world, rank):
                        "vecmat_schedule": ("ModDown once after each rotation sum (double hoisting)"
                                            if args.double_hoist else "one ModDown per rotation"),
                        "fc_form": "rectangular diagonals" if args.fc_form == "rect" else "square diagonals",
-                       "conv_form": ("two hoisted rotation sums" if args.conv_hoist
-                                     else "rotate-and-add chain")},
+                       "conv_form": CONV_LABEL[conv_form(args)]},
             "cpu_baseline": {"value": value, "unit": "inferences/s", "cores": cores, "kind": "oracle",
                              "sample": f"{steps} full inferences (forward only; keys and weights prepared outside)"},
             "e2e": {"value": value, "unit": "inferences/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -784,6 +799,8 @@ def main():
                     help="diagonal form of the CNN's fully connected layers")
     ap.add_argument("--conv-hoist", type=int, default=1,
                     help="the convolution sums as hoisted baby-step giant-step rotation sums (1) or a chain (0)")
+    ap.add_argument("--conv-shared", type=int, default=1,
+                    help="with --conv-hoist 1: the baby steps over the input's rotations, shared by the kernels")
     ap.add_argument("--double-hoist", type=int, default=1,
                     help="vector x matrix products take the ModDown once after the rotation sum (1) or per rotation (0)")
     ap.add_argument("--c4", type=int, default=1, help="time the 4096x256 vector x matrix workload (64 vectors)")
@@ -820,6 +837,7 @@ def main():
     alu_ach = ops / (ms / 1e3) / 1e9
     alu_peak = r["bfly_peak"] / 1e9
     traffic = ncu_traffic(name, {"batch": B, "fc_form": args.fc_form, "conv_hoist": args.conv_hoist,
+                                 "conv_shared": args.conv_shared if args.conv_hoist else 0,
                                  "double_hoist": args.double_hoist})
     hbm = {"achieved": hbm_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_ach / peaks["hbm_gbs"],
            "peak_source": peaks["source"]}
@@ -839,7 +857,7 @@ def main():
     # CPU baseline: the oracle on the host cores, bounded sample
     if args.cpu_sample > 0:
         times, cores, single = time_oracle(args.cpu_sample, 0, bool(args.double_hoist), 1, args.fc_form == "rect",
-                                           bool(args.conv_hoist))
+                                           bool(args.conv_hoist), bool(args.conv_shared))
         cpu_val = len(times) / sum(times)
     else:
         times, cores, cpu_val, single = [], 0, None, []
@@ -852,8 +870,7 @@ def main():
                                        else "one ModDown per rotation"),
                    "fc_form": ("rectangular diagonals: FC1 63 + 2 rotations, FC2 15 + 2 (no replication)"
                                if args.fc_form == "rect" else "square diagonals: FC1 255 rotations, FC2 63"),
-                   "conv_form": ("two hoisted rotation sums (7 baby + 7 giant steps, one ModDown each)"
-                                 if args.conv_hoist else "rotate-and-add chain (6 key switches)"),
+                   "conv_form": CONV_LABEL[conv_form(args)],
                    "l2": "inputs larger than L2 (Galois keys ~0.75 GB + key-switch scratch streamed per step)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "latency_ms": {"p50": per[len(per) // 2], "p99": per[min(len(per) - 1, int(0.99 * len(per)))],

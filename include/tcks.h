@@ -107,8 +107,20 @@ tcks_status tcks_params_primes(const tcks_params* p, uint64_t* primes, uint32_t 
 /* TCKS_CONV_HOIST, read by tcks_cnn_create: the convolution's rotate-and-add chain over the
  * 2^ceil(log2 taps) tap positions becomes two hoisted rotation sums (tcks_rotate_sum_hoisted), first
  * over the baby steps windows*b (b < B), then over the giant steps windows*B*g (g < G), B G = 2^e,
- * B = 2^floor(e/2): 14 key switches with one ModUp and one ModDown per sum instead of 6 full ones. */
-enum { TCKS_AUTO_RELIN = 1u, TCKS_AUTO_RESCALE = 2u, TCKS_DOUBLE_HOIST = 4u, TCKS_RECT_DIAG = 8u, TCKS_CONV_HOIST = 16u };
+ * B = 2^floor(e/2): 14 key switches with one ModUp and one ModDown per sum instead of 6 full ones.
+ * TCKS_CONV_SHARED (implies the giant-step sum above): the baby-step sum of every kernel k is taken over
+ * the input's own rotations, sum_b rot(ct, windows*b) * rot(kernel_k, windows*b) (rot(x * K) =
+ * rot(x) * rot(K) slot by slot), with the rotated kernels pre-encoded over the extended basis: one
+ * ModUp per request for all kernels, the key-switch sums formed once per rotation, one ModDown per
+ * kernel, then the rescale; 1 or 4 kernels. The baby-step keys must cover level L. */
+enum {
+  TCKS_AUTO_RELIN = 1u,
+  TCKS_AUTO_RESCALE = 2u,
+  TCKS_DOUBLE_HOIST = 4u,
+  TCKS_RECT_DIAG = 8u,
+  TCKS_CONV_HOIST = 16u,
+  TCKS_CONV_SHARED = 32u
+};
 tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32_t flags,
                                 const tcks_allocator* allocator, void* cuda_stream, tcks_ctx** out);
 void tcks_ctx_free(tcks_ctx* ctx);
@@ -479,8 +491,8 @@ tcks_status tcks_cnn_graph_run(tcks_cnn_graph* g, const tcks_ct* const* in, tcks
 void tcks_cnn_graph_free(tcks_cnn_graph* g);
 /* Export one of the model's encoded plaintexts (kind 0 conv kernel, 1 channel mask, 2 bias
  * (index 0..2), 3 FC1 diagonal, 4 FC2 diagonal, 5 / 6 the FC1 / FC2 diagonal over the extended basis,
- * its limb modulo P last) to host [level][N] ([level+1][N] for kinds 5, 6); level / scale are
- * reported (the data level). */
+ * its limb modulo P last, 7 the baby-step diagonal kernel * B + b of TCKS_CONV_SHARED over the
+ * extended basis) to host [level][N] ([level+1][N] for kinds 5, 6, 7); level / scale are reported. */
 tcks_status tcks_cnn_export_plaintext(const tcks_cnn* m, uint32_t kind, uint32_t index, uint64_t* host,
                                       size_t n_words, uint32_t* level, double* scale);
 

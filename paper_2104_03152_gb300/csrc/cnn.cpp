@@ -5,6 +5,10 @@
 // Schedule (levels in brackets, L = input level):
 //   conv: per kernel k, rescale(ct * kernel_k) [L-1], then log2(taps) left rotate-and-adds by
 //         windows * 2^i — the four channels rotate together, one key-switch launch per step;
+//         (TCKS_CONV_HOIST) the sum as a baby-step and a giant-step hoisted rotation sum;
+//         (TCKS_CONV_SHARED) the baby steps as a diagonal-method sum over the input's own rotations,
+//         sum_b rot(ct, W b) * rot(kernel_k, W b), one ModUp per request for all kernels and one
+//         ModDown per kernel, rescaled [L-1], then the giant steps;
 //   pack: v = sum_k rescale(conv_k * mask_k) [L-2], mask_k = 1 on slots [k*W, (k+1)*W); + conv bias;
 //   square: rescale(relin(v * v)) [L-3];
 //   FC1: vector x plain matrix (replicate, hoisted diagonal method, rescale) [L-4]; + bias;
@@ -33,7 +37,10 @@ struct tcks_cnn {
   double out_scale;
   bool rect;                 // rectangular FC layers: FC1's output comes replicated and feeds FC2 as is
   bool conv_hoist;           // the convolution sums as two hoisted rotation sums (baby and giant steps)
+  bool conv_shared;          // baby steps on the input's own rotations, shared by every kernel
   std::vector<int32_t> baby, giant;
+  u64* baby_ext = nullptr;   // conv_shared: per kernel k and baby step b (0 first), the kernel rotated
+                             // left by windows * b over the extended basis, [kernels][B][L+1][N]
 };
 
 namespace tcks {
@@ -64,6 +71,7 @@ u64 cnn_resident_bytes(const tcks_cnn* m) {
   const tcks_ctx* c = m->ctx;
   const u64 n = c->N, L = m->L;
   u64 b = (u64)m->kernels * (L + (L - 1)) * n * 8;          // conv kernels and masks
+  if (m->baby_ext) b += (u64)m->kernels * (m->baby.size() + 1) * (L + 1) * n * 8;
   b += ((L - 2) + (L - 4) + (L - 6)) * n * 8;                  // biases
   b += (u64)m->fc1->diags * m->fc1->limbs() * n * 8 + (u64)m->fc2->diags * m->fc2->limbs() * n * 8;
   return b;
@@ -117,19 +125,30 @@ void cnn_stage(const tcks_cnn* m, u32 stage, const u64* x, u32 count, u64* out) 
       const u64 w_in = ct_words(c, L), w1 = ct_words(c, L - 1), w2 = ct_words(c, L - 2);
       // conv [L-1]: channel k of request r at chans + (k * count + r) * w1
       DevBuf chans(c, (size_t)K * count * w1);
-      {
-        DevBuf prod(c, (size_t)count * w_in);
-        for (u32 k = 0; k < K; ++k) {
-          launch_elementwise(c->T, OP_MUL_PLAIN, x, m->conv[k], prod.p, L, 2 * count, c->stream);
-          op_rescale(c, prod.p, L, chans.p + (size_t)k * count * w1, count);
-        }
-      }
-      if (m->conv_hoist) {
-        op_rotsum_hoisted(c, chans.p, w1, K * count, L - 1, m->baby, chans.p);
+      if (m->conv_shared) {
+        const u32 nb = (u32)m->baby.size() + 1;
+        DevBuf z(c, (size_t)K * count * w_in);  // [kernel][request][2][L][N] before the rescale
+        const u64 dstride = (u64)(L + 1) * c->N;
+        op_dh_sum_multi(c, x, w_in, count, L, m->baby, m->baby_ext, dstride, dstride * nb, L, K, z.p, w_in,
+                        (u64)count * w_in);
+        op_rescale(c, z.p, L, chans.p, K * count);
         op_rotsum_hoisted(c, chans.p, w1, K * count, L - 1, m->giant, chans.p);
       } else {
-        const int rsteps = ceil_log2(m->taps);
-        for (int i = 0; i < rsteps; ++i) op_rotate_add(c, chans.p, w1, K * count, L - 1, (int32_t)(m->windows << i));
+        {
+          DevBuf prod(c, (size_t)count * w_in);
+          for (u32 k = 0; k < K; ++k) {
+            launch_elementwise(c->T, OP_MUL_PLAIN, x, m->conv[k], prod.p, L, 2 * count, c->stream);
+            op_rescale(c, prod.p, L, chans.p + (size_t)k * count * w1, count);
+          }
+        }
+        if (m->conv_hoist) {
+          op_rotsum_hoisted(c, chans.p, w1, K * count, L - 1, m->baby, chans.p);
+          op_rotsum_hoisted(c, chans.p, w1, K * count, L - 1, m->giant, chans.p);
+        } else {
+          const int rsteps = ceil_log2(m->taps);
+          for (int i = 0; i < rsteps; ++i)
+            op_rotate_add(c, chans.p, w1, K * count, L - 1, (int32_t)(m->windows << i));
+        }
       }
       // pack [L-2] + bias
       DevBuf prod(c, (size_t)count * w1), t(c, (size_t)count * w2);
@@ -213,6 +232,7 @@ void tcks_cnn_free(tcks_cnn* m) {
   for (u64* p : m->conv) c->dev_free(p);
   for (u64* p : m->masks) c->dev_free(p);
   for (u64* p : m->bias) c->dev_free(p);
+  if (m->baby_ext) c->dev_free(m->baby_ext);
   tcks_matrix_free(m->fc1);
   tcks_matrix_free(m->fc2);
   delete m;
@@ -249,7 +269,10 @@ tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* con
   m->L = L;
   m->in_scale = c->params.scale;
   m->rect = (c->flags & TCKS_RECT_DIAG) != 0;
-  m->conv_hoist = (c->flags & TCKS_CONV_HOIST) != 0;
+  m->conv_shared = (c->flags & TCKS_CONV_SHARED) != 0;
+  m->conv_hoist = m->conv_shared || (c->flags & TCKS_CONV_HOIST) != 0;
+  if (m->conv_shared && kernels != 4 && kernels != 1)
+    fail(TCKS_ERR_UNSUPPORTED, "the shared convolution sum takes 1 or 4 kernels");
   {
     // tap positions t = b + B g over 2^ceil(log2 taps): B = 2^floor(e/2) baby steps, G = 2^ceil(e/2)
     const int e = ceil_log2(taps);
@@ -273,6 +296,18 @@ tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* con
     for (u32 t = 0; t < taps; ++t)
       for (u32 w = 0; w < windows; ++w) lay[(size_t)t * windows + w] = conv_w[(size_t)k * taps + t];
     m->conv.push_back(encode_host(lay, delta, L));
+    if (m->conv_shared) {
+      const u32 nb = (u32)m->baby.size() + 1;
+      const u64 per = (u64)(L + 1) * c->N;
+      if (!m->baby_ext) m->baby_ext = (u64*)c->dev_alloc((size_t)kernels * nb * per * 8);
+      std::vector<double> rot(slots);
+      for (u32 b = 0; b < nb; ++b) {
+        const u32 sh = b ? (u32)m->baby[b - 1] : 0;  // left rotation by sh: rot[i] = lay[i + sh]
+        for (u32 i = 0; i < slots; ++i) rot[i] = lay[(i + sh) % slots];
+        check_cuda(cudaMemcpyAsync(dv.p, rot.data(), (size_t)slots * 8, cudaMemcpyHostToDevice, c->stream), "H2D");
+        encode_into(c, (const double*)dv.p, slots, delta, L, m->baby_ext + ((u64)k * nb + b) * per, true);
+      }
+    }
     std::fill(lay.begin(), lay.end(), 0.0);
     for (u32 w = 0; w < windows; ++w) lay[(size_t)k * windows + w] = 1.0;
     m->masks.push_back(encode_host(lay, delta, L - 1));
@@ -330,8 +365,8 @@ tcks_status tcks_cnn_galois_steps(const tcks_cnn* m, int32_t* steps, uint32_t* l
       }
     need.push_back({s, lv});
   };
-  if (m->conv_hoist) {
-    for (int32_t s : m->baby) use((u32)s, L - 1);
+  if (m->conv_hoist) {  // shared: the baby steps rotate the input, at level L
+    for (int32_t s : m->baby) use((u32)s, m->conv_shared ? L : L - 1);
     for (int32_t s : m->giant) use((u32)s, L - 1);
   } else {
     for (int i = 0; i < ceil_log2(m->taps); ++i) use(m->windows << i, L - 1);
@@ -507,7 +542,9 @@ tcks_status tcks_cnn_graph_run(tcks_cnn_graph* g, const tcks_ct* const* in, tcks
 }
 
 // Plaintexts of the model for inspection: kind 0 conv kernel, 1 mask (index = kernel), 2 bias
-// (index 0..2), 3 FC1 diagonal, 4 FC2 diagonal (index = diagonal); host [level][N].
+// (index 0..2), 3 FC1 diagonal, 4 FC2 diagonal (index = diagonal); host [level][N]. Kinds 5, 6: the
+// FC diagonals over the extended basis; 7: baby-step diagonal (index = kernel * B + b) of the shared
+// convolution, [L+1][N].
 tcks_status tcks_cnn_export_plaintext(const tcks_cnn* m, uint32_t kind, uint32_t index, uint64_t* host,
                                       size_t n_words, uint32_t* level, double* scale) {
   CNN_BEGIN
@@ -536,6 +573,12 @@ tcks_status tcks_cnn_export_plaintext(const tcks_cnn* m, uint32_t kind, uint32_t
       const tcks_matrix* M = (kind == 3 || kind == 5) ? m->fc1 : m->fc2;
       if (index >= M->diags) fail(TCKS_ERR_INVALID_ARG, "index");
       src = M->d + (size_t)index * M->limbs() * c->N, lv = kind >= 5 ? M->limbs() : M->level, sc = M->scale;
+      break;
+    }
+    case 7: {
+      const u32 nb = (u32)m->baby.size() + 1;
+      if (!m->baby_ext || index >= m->kernels * nb) fail(TCKS_ERR_INVALID_ARG, "index");
+      src = m->baby_ext + (size_t)index * (m->L + 1) * c->N, lv = m->L + 1, sc = c->params.scale;
       break;
     }
     default: fail(TCKS_ERR_INVALID_ARG, "kind");

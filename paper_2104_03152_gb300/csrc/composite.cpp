@@ -123,6 +123,53 @@ void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const st
   check_launch("hoisted rotation sum");
 }
 
+void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, const std::vector<int32_t>& steps,
+                     const u64* diags, u64 diag_stride, u64 set_stride, u32 p_limb, u32 outs, u64* out, u64 out_b,
+                     u64 out_o) {
+  const size_t n = c->N;
+  std::vector<u32> ks;
+  for (int32_t st : steps) {
+    const u32 k = step_mod(c, st);
+    if (!k) fail(TCKS_ERR_INVALID_ARG, "a double-hoisted sum takes non-zero steps");
+    ks.push_back(k);
+  }
+  const KeyTable& kt = key_table(c, ks, ell);
+  const u32 R = (u32)ks.size();
+  DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
+  launch_modup(c->T, x + (size_t)ell * n, cw, count, ell, coef.p, digits.p, c->stream);
+  const u64 base = vecmat_dh_base_ctas(c->params.log_n, ell, count, c->T.narrow, outs), want = 152ull * 8 * 4;
+  u32 chunks = (u32)std::min<u64>(R, std::max<u64>(1, (want + base - 1) / base));
+  const u32 chunk = (R + chunks - 1) / chunks;
+  chunks = (R + chunk - 1) / chunk;
+  DevBuf partial(c, (size_t)count * outs * chunks * 3 * (ell + 1) * n);
+  VecmatDhPlan p{};
+  p.keys = kt.d;
+  p.digits = digits.p;
+  p.digits_b = (u64)ell * (ell + 1) * n;
+  p.ct = x;
+  p.ct_b = cw;
+  p.diag = diags;
+  p.diag_stride = diag_stride;
+  p.diag_set = set_stride;
+  p.p_limb = p_limb;
+  p.outs = outs;
+  p.partial = partial.p;
+  p.R = R;
+  p.B = count;
+  p.chunk = chunk;
+  p.chunks = chunks;
+  launch_vecmat_dh_acc(c->T, ell, p, c->stream);
+  launch_vecmat_dh_fold(c->T, ell, p, c->stream);
+  const u32 ro = count * outs;
+  DevBuf top(c, (size_t)2 * ro * n);
+  const u64 per_ro = (u64)chunks * 3 * (ell + 1) * n;
+  for (u32 b = 0; b < 2; ++b)
+    launch_ntt(c->T, true, partial.p + ((u64)b * (ell + 1) + ell) * n, per_ro, top.p + (u64)b * ro * n, n, ro, c->L, 1,
+               c->stream);
+  launch_vecmat_dh_moddown(c->T, ell, p, top.p, out, out_b, c->stream, outs > 1 ? out_o : 0);
+  check_launch("double-hoisted sum");
+}
+
 void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell, const tcks_matrix* M, u64* out,
                bool input_replicated) {
   const bool dh = (c->flags & TCKS_DOUBLE_HOIST) != 0;

@@ -190,5 +190,12 @@ void op_vecmat(tcks_ctx* c, const u64* ct, u64 ct_stride, u32 count, u32 ell, co
                bool input_replicated = false);
 void op_conv(tcks_ctx* c, const u64* ct, u32 ell, const u64* kernel_pt, u32 taps, u32 windows, u64* out);
 void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const std::vector<int32_t>& steps, u64* out);
+// sum_k rot(x, s_k) * d_{o,k} (s_0 = 0, s_k = steps[k-1]) for `count` ciphertexts (stride cw) and `outs`
+// (1 or 4) diagonal sets over the extended basis: set o at diags + o * set_stride, diagonal k at
+// + k * diag_stride, its P limb at p_limb. One ModUp per ciphertext, one ModDown per output; output o
+// of ciphertext r at out + r * out_b + o * out_o ([2][ell][N]); scale x's times the diagonals'.
+void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, const std::vector<int32_t>& steps,
+                     const u64* diags, u64 diag_stride, u64 set_stride, u32 p_limb, u32 outs, u64* out, u64 out_b,
+                     u64 out_o);
 
 }  // namespace tcks

@@ -72,7 +72,9 @@ __device__ __forceinline__ u64 dh_off(u32 rq, u32 chunk, u32 chunks, u32 comp, u
 // diagonal and the Galois index of a rotation are loaded once for the RPT requests.
 // ELL > 0 fixes the level at compile time (the digit loop unrolls, its offsets become constants);
 // ELL = 0 takes it from the argument.
-template <typename W, int EPT, int RPT, int ELL>
+// KO outputs per request (KO > 1 with RPT = 1): the key-switch sums of a rotation are formed once
+// and multiplied by each output's diagonal.
+template <typename W, int EPT, int RPT, int ELL, int KO = 1>
 __global__ void __launch_bounds__(kDhThreads) k_vecmat_dh_acc(DevTables T, u32 ell_arg,
                                                                const __grid_constant__ VecmatDhPlan p) {
   const u32 ell = ELL > 0 ? (u32)ELL : ell_arg;
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(kDhThreads) k_vecmat_dh_acc(DevTables T, u32 e
     c0[rr] = p.ct + rq * p.ct_b + (u64)i * n;
   }
   const u32 base = eb * kDhThreads * EPT + threadIdx.x;
-  DhAcc<W> u0[EPT][RPT], u1[EPT][RPT], a0[EPT][RPT];
+  DhAcc<W> u0[EPT][RPT * KO], u1[EPT][RPT * KO], a0[EPT][RPT * KO];
   const u32 r0 = chunk * p.chunk, r1 = min(p.R, r0 + p.chunk);
   const bool unit = p.diag == nullptr;  // a hoisted rotation sum: every diagonal is 1
   for (u32 r = r0; r < r1; ++r) {
@@ -127,13 +129,22 @@ __global__ void __launch_bounds__(kDhThreads) k_vecmat_dh_acc(DevTables T, u32 e
             u1[e][rr].add(s1[rr].get(m));
             if (i < ell) a0[e][rr].add(c0[rr][src]);
           }
-        } else {
+        } else if (KO == 1) {
           const u64 dv = dk[g];
 #pragma unroll
           for (int rr = 0; rr < RPT; ++rr) {
             u0[e][rr].mac(s0[rr].get(m), dv);
             u1[e][rr].mac(s1[rr].get(m), dv);
             if (i < ell) a0[e][rr].mac(c0[rr][src], dv);
+          }
+        } else {
+          const u64 v0 = s0[0].get(m), v1 = s1[0].get(m), x0 = i < ell ? c0[0][src] : 0;
+#pragma unroll
+          for (int o = 0; o < KO; ++o) {
+            const u64 dv = dk[(u64)o * p.diag_set + g];
+            u0[e][o].mac(v0, dv);
+            u1[e][o].mac(v1, dv);
+            if (i < ell) a0[e][o].mac(x0, dv);
           }
         }
       }
@@ -143,12 +154,13 @@ __global__ void __launch_bounds__(kDhThreads) k_vecmat_dh_acc(DevTables T, u32 e
   for (int e = 0; e < EPT; ++e) {
     const u32 g = base + e * kDhThreads;
 #pragma unroll
-    for (int rr = 0; rr < RPT; ++rr) {
-      const u32 rq = rg * RPT + rr;
+    for (int rr = 0; rr < RPT * KO; ++rr) {
+      const u32 rq = KO == 1 ? rg * RPT + rr : rg;  // KO > 1: rr is the output
+      const u32 ro = KO == 1 ? rq : rq * KO + rr;   // index of the partial
       if (g < n && rq < p.B) {
-        p.partial[dh_off(rq, chunk, p.chunks, 0, i, ell, log_n) + g] = u0[e][rr].get(m);
-        p.partial[dh_off(rq, chunk, p.chunks, 1, i, ell, log_n) + g] = u1[e][rr].get(m);
-        if (i < ell) p.partial[dh_off(rq, chunk, p.chunks, 2, i, ell, log_n) + g] = a0[e][rr].get(m);
+        p.partial[dh_off(ro, chunk, p.chunks, 0, i, ell, log_n) + g] = u0[e][rr].get(m);
+        p.partial[dh_off(ro, chunk, p.chunks, 1, i, ell, log_n) + g] = u1[e][rr].get(m);
+        if (i < ell) p.partial[dh_off(ro, chunk, p.chunks, 2, i, ell, log_n) + g] = a0[e][rr].get(m);
       }
     }
   }
@@ -163,7 +175,8 @@ __global__ void k_vecmat_dh_fold(DevTables T, u32 ell, const __grid_constant__ V
   const u64 n = 1ull << log_n;
   const u32 slots = ell + 1;
   const u64 per_rq = 3ull * slots * n;
-  for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < per_rq * p.B; e += (u64)gridDim.x * blockDim.x) {
+  for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < per_rq * p.B * dh_outs(p);
+       e += (u64)gridDim.x * blockDim.x) {
     const u32 rq = (u32)(e / per_rq);
     const u64 o = e - (u64)rq * per_rq;
     const u32 slot = (u32)((o >> log_n) % slots);
@@ -176,27 +189,29 @@ __global__ void k_vecmat_dh_fold(DevTables T, u32 ell, const __grid_constant__ V
 }
 
 // out_b[i] = A_b[i] + c_b[i] d_0[i] + (U_b[i] - NTT_i(bal_P(top_b) mod q_i)) * P^-1.
-// Limb job = (b * ell + i) * B + request; top [2][B][N] holds INTT_P(U_b[P]).
+// Limb job = (b * ell + i) * B * outs + request * outs + output; top [2][B * outs][N] holds INTT_P(U_b[P]).
 template <typename W, int LC>
 __global__ void k_vecmat_dh_moddown(DevTables T, u32 ell, const __grid_constant__ VecmatDhPlan p, const u64* top,
-                                    u64* out, u64 out_b) {
+                                    u64* out, u64 out_b, u64 out_o) {
   TCKS_SMEM(W);
   const Slice sl = slice_of<LC>(T);
   const u32 log_n = T.log_n;
   const u64 n = 1ull << log_n;
-  const u32 rq = sl.job % p.B, bi = sl.job / p.B, b = bi / ell, i = bi % ell;
+  const u32 outs = dh_outs(p), bo = p.B * outs;
+  const u32 ro = sl.job % bo, bi = sl.job / bo, b = bi / ell, i = bi % ell;
+  const u32 rq = ro / outs, o = ro % outs;
   const ModConst mi = T.mods[i];
   const ModConst mp = T.mods[T.L];
   const PairConst pc = T.pairs[(u64)T.L * T.n_mods + i];
-  const u64* t = top + ((u64)b * p.B + rq) * n + sl.off;
+  const u64* t = top + ((u64)b * bo + ro) * n + sl.off;
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)lift_balanced(t[k], mp.half, pc.qa_mod_b, mi);
   __syncthreads();
   ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
-  const u64* U = p.partial + dh_off(rq, 0, p.chunks, b, i, ell, log_n);
-  const u64* A = p.partial + dh_off(rq, 0, p.chunks, 2, i, ell, log_n);
+  const u64* U = p.partial + dh_off(ro, 0, p.chunks, b, i, ell, log_n);
+  const u64* A = p.partial + dh_off(ro, 0, p.chunks, 2, i, ell, log_n);
   const u64* cb = p.ct + rq * p.ct_b + ((u64)b * ell + i) * n;
-  const u64* d0 = p.diag ? p.diag + (u64)i * n : nullptr;  // unit diagonals: c_b itself
-  u64* dst = out + rq * out_b + ((u64)b * ell + i) * n;
+  const u64* d0 = p.diag ? p.diag + (u64)o * p.diag_set + (u64)i * n : nullptr;  // unit diagonals: c_b itself
+  u64* dst = out + (out_o ? rq * out_b + o * out_o : ro * out_b) + ((u64)b * ell + i) * n;
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
     const u32 g = sl.off + k;
     u64 v = Ew<W>::shoup_inv(sub_mod(U[g], Ar<W>::fwd_out(s[sw(k)], mi), mi.q), pc, mi);
@@ -211,24 +226,24 @@ static decltype(&k_vecmat_dh_moddown<u64, 0>) const K6_k_vecmat_dh_moddown[6] = 
 }  // namespace
 
 // The level as a template argument up to 8 limbs (every level of the CNN and the 4096x256 product).
-template <typename W, int EPT, int RPT>
+template <typename W, int EPT, int RPT, int KO>
 static void dh_acc_launch(dim3 grid, cudaStream_t st, const DevTables& T, u32 ell, const VecmatDhPlan& p) {
   switch (ell) {
 #define TCKS_DH_CASE(E) \
   case E:               \
-    k_vecmat_dh_acc<W, EPT, RPT, E><<<grid, kDhThreads, 0, st>>>(T, ell, p); \
+    k_vecmat_dh_acc<W, EPT, RPT, E, KO><<<grid, kDhThreads, 0, st>>>(T, ell, p); \
     return;
     TCKS_DH_CASE(1) TCKS_DH_CASE(2) TCKS_DH_CASE(3) TCKS_DH_CASE(4)
     TCKS_DH_CASE(5) TCKS_DH_CASE(6) TCKS_DH_CASE(7) TCKS_DH_CASE(8)
 #undef TCKS_DH_CASE
     default:
-      k_vecmat_dh_acc<W, EPT, RPT, 0><<<grid, kDhThreads, 0, st>>>(T, ell, p);
+      k_vecmat_dh_acc<W, EPT, RPT, 0, KO><<<grid, kDhThreads, 0, st>>>(T, ell, p);
   }
 }
 
-u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow) {
+u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow, u32 outs) {
   const u64 n = 1ull << log_n;
-  const u32 ept = narrow ? kEpt32 : kEpt64, rpt = narrow ? kRpt32 : kRpt64;
+  const u32 ept = narrow ? kEpt32 : kEpt64, rpt = outs > 1 ? 1 : narrow ? kRpt32 : kRpt64;
   const u64 eblocks = (n + kDhThreads * ept - 1) / (kDhThreads * ept);
   return (u32)(eblocks * (ell + 1) * ((B + rpt - 1) / rpt));
 }
@@ -240,30 +255,40 @@ void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cu
                     ((double)p.B * (wd * ell * (ell + 1.0) + ell) +
                      (double)p.R * (2.0 * ell * (ell + 1.0) + (p.diag ? ell + 1.0 : 0.0)) +
                      (double)p.B * p.chunks * (3.0 * ell + 2.0));
-  const double ops = (double)p.B * p.R * n * ((ell + 1.0) * (2.0 * ell + 4.0) + ell);
-  Launch L(K_VECMAT_DH, st, by, ops);
-  const dim3 grid(vecmat_dh_base_ctas(T.log_n, ell, p.B, T.narrow), p.chunks);
-  if (T.narrow)
-    dh_acc_launch<u32, kEpt32, kRpt32>(grid, st, T, ell, p);
-  else
-    dh_acc_launch<u64, kEpt64, kRpt64>(grid, st, T, ell, p);
+  const u32 outs = dh_outs(p);
+  if ((outs != 1 && outs != 4) || (outs > 1 && !p.diag))
+    fail(TCKS_ERR_UNSUPPORTED, "double-hoisted sums take 1 or 4 outputs per request (4 with diagonals)");
+  // per (request, rotation): the key-switch sums, then per output the diagonal products
+  const double ops = (double)p.B * p.R * n * ((ell + 1.0) * (2.0 * ell + 1.0 + 3.0 * outs) + ell * outs);
+  Launch L(K_VECMAT_DH, st, by + 8.0 * n * (outs - 1.0) * (p.R * (ell + 1.0) + p.B * p.chunks * (3.0 * ell + 2.0)), ops);
+  const dim3 grid(vecmat_dh_base_ctas(T.log_n, ell, p.B, T.narrow, outs), p.chunks);
+  if (outs == 4) {
+    if (T.narrow)
+      dh_acc_launch<u32, 1, 1, 4>(grid, st, T, ell, p);
+    else
+      dh_acc_launch<u64, 1, 1, 4>(grid, st, T, ell, p);
+  } else if (T.narrow) {
+    dh_acc_launch<u32, kEpt32, kRpt32, 1>(grid, st, T, ell, p);
+  } else {
+    dh_acc_launch<u64, kEpt64, kRpt64, 1>(grid, st, T, ell, p);
+  }
 }
 
 void launch_vecmat_dh_fold(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st) {
   if (p.chunks < 2) return;
-  const u64 e = (u64)p.B * 3 * (ell + 1) << T.log_n;
+  const u64 e = (u64)p.B * dh_outs(p) * 3 * (ell + 1) << T.log_n;
   Launch L(K_MULACC, st, 8.0 * (double)e * (p.chunks + 1.0));
   const u32 blocks = (u32)std::min<u64>((e + 255) / 256, 152ull * 16);
   k_vecmat_dh_fold<<<blocks, 256, 0, st>>>(T, ell, p);
 }
 
 void launch_vecmat_dh_moddown(const DevTables& T, u32 ell, const VecmatDhPlan& p, const u64* top, u64* out, u64 out_b,
-                              cudaStream_t st) {
+                              cudaStream_t st, u64 out_o) {
   const double n = (double)(1u << T.log_n);
-  const double jobs = 2.0 * ell * p.B;
-  Launch L(K_KS_MODDOWN, st, 8.0 * n * (jobs * 5.0 + ell), jobs * (0.5 * n * T.log_n + 2.0 * n));
-  launch_limb(K6_k_vecmat_dh_moddown, T.narrow, 2 * ell * p.B, 1, T.log_n, st, T.limb_threads, T, ell, p, top, out,
-              out_b);
+  const double jobs = 2.0 * ell * p.B * dh_outs(p);
+  Launch L(K_KS_MODDOWN, st, 8.0 * n * (jobs * 5.0 + ell * dh_outs(p)), jobs * (0.5 * n * T.log_n + 2.0 * n));
+  launch_limb(K6_k_vecmat_dh_moddown, T.narrow, 2 * ell * p.B * dh_outs(p), 1, T.log_n, st, T.limb_threads, T, ell, p,
+              top, out, out_b, out_o);
 }
 
 }  // namespace tcks

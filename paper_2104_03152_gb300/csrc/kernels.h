@@ -124,7 +124,9 @@ struct VecmatPlan {
 // kern_vecmat.cu): keys[r] = the key of rotation r + 1; digits + rq * digits_b the request's ModUp
 // digits [ell][ell+1][N]; ct + rq * ct_b its (replicated) ciphertext [2][ell][N]; diag + k *
 // diag_stride diagonal k over the extended basis (data limbs from 0, the P limb at p_limb, which is
-// the matrix's level and may exceed ell); partial [B][chunks][3][ell+1][N].
+// the matrix's level and may exceed ell). outs > 1: that many outputs per request from the same
+// rotations, output o with the diagonal set at diag + o * diag_set (outs = 0 means 1). partial
+// [B * outs][chunks][3][ell+1][N], output o of request rq at index rq * outs + o.
 struct VecmatDhPlan {
   const KsKey* keys;
   const u64* digits;
@@ -133,17 +135,23 @@ struct VecmatDhPlan {
   u64 ct_b;
   const u64* diag;
   u64 diag_stride;
+  u64 diag_set;
   u64* partial;
   u32 R, B, chunk, chunks;
-  u32 p_limb, pad;
+  u32 p_limb, outs;
 };
+// Outputs per request of a plan (1 or 4).
+__host__ __device__ inline u32 dh_outs(const VecmatDhPlan& p) { return p.outs > 1 ? p.outs : 1; }
 // CTAs of one chunk of k_vecmat_dh_acc (element blocks x slots x requests).
-u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow);
+u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow, u32 outs = 1);
 void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st);
 void launch_vecmat_dh_fold(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st);
-// top [2][B][N] = INTT_P of the folded U_b[P]; out + rq * out_b receives [2][ell][N] (before the rescale).
+// top [2][B * outs][N] = INTT_P of the folded U_b[P]; out + (rq * outs + o) * out_b receives output o
+// of request rq, [2][ell][N] (before the rescale).
+// out_o: words between consecutive outputs of one request (0: outputs follow each other, out_b apart,
+// request-major); with out_o != 0 output o of request rq goes to out + rq * out_b + o * out_o.
 void launch_vecmat_dh_moddown(const DevTables& T, u32 ell, const VecmatDhPlan& p, const u64* top, u64* out, u64 out_b,
-                              cudaStream_t st);
+                              cudaStream_t st, u64 out_o = 0);
 // Stage 1 of a KsPlan alone (the P-limb inner product and its INTT into plan.top).
 void launch_ks_inner_p(const DevTables& T, u32 ell, const KsPlan& plan, cudaStream_t st);
 // The fused ModDown + multiply-accumulate over the plan's R rotations, chunk rotations per CTA.

@@ -218,3 +218,52 @@ def test_cnn_hoisted_conv_parity(setup):
         assert np.array_equal(b[2].export(), got.export())
     finally:
         ctx.set_flags(base)
+
+
+def test_cnn_shared_conv_parity(setup):
+    """TCKS_CONV_SHARED (+ rectangular FC layers, double hoisting; the bench's network): the baby-step sums
+    of the four kernels over the input's own rotations in one 4-output double-hoisted pass. Galois steps
+    and levels as the oracle's schedule; on the model's own encodings bit-identical to the oracle's
+    forward pass, single and batched, and within 5e-3 of the FP64 network."""
+    o, w, enc, ctx, model, need = setup
+    base = tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE
+    ctx.set_flags(base | tk.TCKS_RECT_DIAG | tk.TCKS_CONV_SHARED | tk.TCKS_DOUBLE_HOIST)
+    try:
+        hm = tk.CNN(ctx, w.conv_w, w.conv_b, w.fc1_w, w.fc1_b, w.fc2_w, w.fc2_b, windows=64)
+        steps = oracle.cnn_galois_steps(o, rect=True, conv_hoist=True, conv_shared=True)
+        assert hm.galois_steps() == steps
+        for st, lv in steps.items():
+            if st not in o.galois or o.galois[st].level < lv:
+                o.gen_galois_key(st, lv)
+        hm.gen_keys()
+        henc = oracle.cnn_encode(o, w, rect=True, conv_hoist=True, conv_shared=True)
+        L = o.L
+        nb = len(o.conv_bsgs_steps(49, 64)[0]) + 1
+        for k in range(4):
+            got_ext = np.stack([hm.export_plaintext(7, k * nb + b)[0] for b in range(nb)])
+            for b in range(nb):  # the data limbs (the P limb follows from the same integers)
+                _near_tie_agreement(o, np.ascontiguousarray(got_ext[b, :L]),
+                                    np.ascontiguousarray(henc.conv_baby_ext[k][b, :L]), L)
+            henc.conv_baby_ext[k] = got_ext
+        henc.fc1 = [oracle.Pt(hm.export_plaintext(3, i)[0], L - 3, o.scale) for i in range(64)]
+        henc.fc2 = [oracle.Pt(hm.export_plaintext(4, i)[0], L - 5, o.scale) for i in range(16)]
+        henc.fc1_ext = np.stack([hm.export_plaintext(5, i)[0] for i in range(64)])
+        henc.fc2_ext = np.stack([hm.export_plaintext(6, i)[0] for i in range(16)])
+        henc.biases = []
+        for i in range(3):
+            data, sc = hm.export_plaintext(2, i)
+            henc.biases.append(oracle.Pt(data, L - 2 - 2 * i, sc))
+        img = inputs.mnist_like_image(7)
+        v, W = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+        ct = o.encrypt_values(v, 83)
+        ref = oracle.cnn_forward(o, ct, w, henc, double_hoist=True)
+        got = hm.forward(ctx.ct_import(ct.data, ct.scale))
+        assert_ct_equal(got, ref, "cnn forward (shared convolution)")
+        assert float(np.max(np.abs(ctx.decrypt_values(got, 10) - oracle.cnn_plain(img, w)))) < 5e-3
+        b = hm.forward_batch([ctx.ct_import(ct.data, ct.scale)] * 3)
+        assert np.array_equal(b[2].export(), got.export())
+        with pytest.raises(tk.TcksError) as e:  # the 4-output pass takes 1 or 4 kernels
+            tk.CNN(ctx, w.conv_w[:3], w.conv_b[:3], w.fc1_w[:, :192], w.fc1_b, w.fc2_w, w.fc2_b, windows=64)
+        assert e.value.name in ("UNSUPPORTED", "INVALID_ARG")
+    finally:
+        ctx.set_flags(base)
