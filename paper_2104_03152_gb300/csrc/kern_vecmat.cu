@@ -75,7 +75,7 @@ __device__ __forceinline__ u64 dh_off(u32 rq, u32 chunk, u32 chunks, u32 comp, u
 // KO outputs per request (KO > 1 with RPT = 1): the key-switch sums of a rotation are formed once
 // and multiplied by each output's diagonal.
 template <typename W, int EPT, int RPT, int ELL, int KO = 1>
-__global__ void __launch_bounds__(kDhThreads) k_vecmat_dh_acc(DevTables T, u32 ell_arg,
+__global__ void __launch_bounds__(kDhThreads, KO > 1 ? 3 : 1) k_vecmat_dh_acc(DevTables T, u32 ell_arg,
                                                                const __grid_constant__ VecmatDhPlan p) {
   const u32 ell = ELL > 0 ? (u32)ELL : ell_arg;
   const u32 log_n = T.log_n;
