@@ -539,9 +539,11 @@ class OracleCKKS:
         pt = self.encode(w, level=a.level)
         return self.sum(self.rescale(self.mul_plain(a, pt)), n)
 
-    def replicate_steps(self, n: int) -> list[int]:
-        """Left-rotation steps that replicate an n-vector over all N/2 slots (§3.1)."""
-        reps = self.slots // n
+    def replicate_steps(self, n: int, period: int | None = None) -> list[int]:
+        """Left-rotation steps that replicate an n-vector over all N/2 slots (§3.1). With `period`, the
+        input already repeats with that period (the vector in [0, n), zeros in [n, period)): only the
+        steps that take the period down to n."""
+        reps = (self.slots if period is None else period) // n
         return [self.slots - n * (1 << m) for m in range(int(math.log2(reps)))]
 
     def matrix_diagonals(self, M: np.ndarray) -> list[np.ndarray]:
@@ -604,27 +606,29 @@ class OracleCKKS:
         return (self.replicate_steps(n) if n < self.slots else []) + list(range(1, mw)) + chain
 
     def vecmat_rect(self, ct: Ct, n: int, m: int, diags: list[Pt] | None = None,
-                    diags_ext: np.ndarray | None = None, replicate: bool = True) -> Ct:
+                    diags_ext: np.ndarray | None = None, replicate: bool = True, period: int | None = None) -> Ct:
         """Vector x plain n x m matrix by the rectangular diagonal method: replicate, y' = sum over
         the m' = rect_width(m) diagonals of rot(ct, k) * d_k (hoisted; with one ModDown per rotation
         when `diags` is given, or once after the sum when `diags_ext` is), rescale, then
         log2(n / m') rotate-and-adds by m' 2^j. Slots s < m hold y_s = sum_i v_i M[i][s]; with the
         input replicated over all slots (period n) every slot s holds the entry s mod m' (zero where
         s mod m' >= m): the product comes out replicated with period m'. replicate=False: the input is
-        already replicated with period n."""
+        already replicated with period n; `period`: the input repeats with that period (see
+        replicate_steps)."""
         mw = self.rect_width(m)
         if diags_ext is not None:
-            y = self._vecmat_dh_rows(ct, diags_ext, n, mw, replicate)
+            y = self._vecmat_dh_rows(ct, diags_ext, n, mw, replicate, period)
         else:
-            y = self._vecmat_rows(ct, diags, n, mw, replicate)
+            y = self._vecmat_rows(ct, diags, n, mw, replicate, period)
         for j in range(int(math.log2(n // mw))):
             y = self.add(y, self.rotate(y, mw << j))
         return y
 
-    def _vecmat_rows(self, ct: Ct, diags: list[Pt], n: int, rows: int, replicate: bool = True) -> Ct:
+    def _vecmat_rows(self, ct: Ct, diags: list[Pt], n: int, rows: int, replicate: bool = True,
+                     period: int | None = None) -> Ct:
         """Replicate an n-vector, then sum_{k < rows} rot(ct, k) * d_k (hoisted), then rescale."""
         if replicate and n < self.slots:
-            for st in self.replicate_steps(n):
+            for st in self.replicate_steps(n, period):
                 ct = self.add(ct, self.rotate(ct, st))
         digits = self.modup(ct)
         acc = None
@@ -634,11 +638,12 @@ class OracleCKKS:
             acc = t if acc is None else self.add(acc, t)
         return self.rescale(acc)
 
-    def _vecmat_dh_rows(self, ct: Ct, diags_ext: np.ndarray, n: int, rows: int, replicate: bool = True) -> Ct:
+    def _vecmat_dh_rows(self, ct: Ct, diags_ext: np.ndarray, n: int, rows: int, replicate: bool = True,
+                        period: int | None = None) -> Ct:
         """The same with the ModDown once after the sum (orc_vecmat_dh over `rows` diagonals)."""
         level = ct.level
         if replicate and n < self.slots:
-            for st in self.replicate_steps(n):
+            for st in self.replicate_steps(n, period):
                 ct = self.add(ct, self.rotate(ct, st))
         digits = self.modup(ct)
         keys = [self._key(k) for k in range(1, rows)]
@@ -731,14 +736,14 @@ class OracleCKKS:
         steps = self.replicate_steps(n) if n < self.slots else []
         return steps + list(range(1, n))
 
-    def vecmat(self, ct: Ct, diags: list[Pt], n: int, m: int) -> Ct:
+    def vecmat(self, ct: Ct, diags: list[Pt], n: int, m: int, period: int | None = None) -> Ct:
         """Encrypted vector (slots [0, n), zeros elsewhere) times a plain n x m matrix given as
         pre-encoded diagonals (§3.1, the diagonal method with left rotations only and a replicated
         input): replicate, then y = sum_k rot(ct, k) * d_k with hoisted rotations, then rescale."""
         if len(diags) != n or m > n:
             raise ValueError("bad matrix shape")
         if n < self.slots:
-            for st in self.replicate_steps(n):
+            for st in self.replicate_steps(n, period):
                 ct = self.add(ct, self.rotate(ct, st))
         digits = self.modup(ct)
         acc = None
@@ -748,7 +753,8 @@ class OracleCKKS:
             acc = t if acc is None else self.add(acc, t)
         return self.rescale(acc)
 
-    def vecmat_dh(self, ct: Ct, diags_ext: np.ndarray, n: int, m: int, scale: float | None = None) -> Ct:
+    def vecmat_dh(self, ct: Ct, diags_ext: np.ndarray, n: int, m: int, scale: float | None = None,
+                  period: int | None = None) -> Ct:
         """The same product with the ModDown taken once after the sum over rotations (double
         hoisting): replicate, ModUp(c1) once, then orc_vecmat_dh (steps 1-3 there), then rescale.
         diags_ext [n][level+1][N] at the ciphertext's level; `scale` is the diagonals' scale."""
@@ -756,7 +762,7 @@ class OracleCKKS:
         if diags_ext.shape != (n, level + 1, self.N) or m > n:
             raise ValueError("bad matrix shape")
         if n < self.slots:
-            for st in self.replicate_steps(n):
+            for st in self.replicate_steps(n, period):
                 ct = self.add(ct, self.rotate(ct, st))
         digits = self.modup(ct)
         keys = [self._key(k) for k in range(1, n)]
@@ -843,10 +849,11 @@ class EncodedCNN:
     conv_hoist: bool = False                   # convolution sums by hoisted baby-step giant-step rotation sums
     conv_shared: bool = False                  # baby steps on the input's rotations, shared by the kernels
     conv_baby_ext: list = field(default_factory=list)  # per kernel, its baby-step diagonals [B][L+1][N]
+    pack_first: bool = False                   # channels packed after the baby steps, one giant-step sum
 
 
 def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64, classes=10, rect=False, conv_hoist=False,
-                     conv_shared=False):
+                     conv_shared=False, pack_first=False):
     """Galois steps of the CNN schedule with the level each is used at (key trimming). rect: the fully
     connected layers by rectangular diagonals (FC2 takes FC1's output as it comes, replicated)."""
     L = o.L
@@ -858,7 +865,13 @@ def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64, classes=
             if s:
                 need[s] = max(need.get(s, 0), level)
 
-    if conv_shared:  # baby steps rotate the input at level L
+    period = None
+    if pack_first:  # the giant steps rotate the packed vector at L - 2, which repeats with period B windows
+        baby, giant = o.conv_bsgs_steps(taps, windows)
+        use(baby, L if conv_shared else L - 1)
+        use(giant, L - 2)
+        period = (len(baby) + 1) * windows
+    elif conv_shared:  # baby steps rotate the input at level L
         baby, giant = o.conv_bsgs_steps(taps, windows)
         use(baby, L)
         use(giant, L - 1)
@@ -869,27 +882,33 @@ def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64, classes=
         use(o.conv_steps(taps, windows), L - 1)
     if rect:
         m1w, m2w = o.rect_width(n2), o.rect_width(classes)
-        use(o.replicate_steps(n1) + list(range(1, m1w)), L - 3)
+        use(o.replicate_steps(n1, period) + list(range(1, m1w)), L - 3)
         use([m1w << j for j in range(int(math.log2(n1 // m1w)))], L - 4)
         use(list(range(1, m2w)), L - 5)
         use([m2w << j for j in range(int(math.log2(n2 // m2w)))], L - 6)
         return need
-    use(o.vecmat_steps(n1), L - 3)
+    use(o.replicate_steps(n1, period) + list(range(1, n1)), L - 3)
     use(o.vecmat_steps(n2), L - 5)
     return need
 
 
 def cnn_encode(o: OracleCKKS, w: CNNWeights, windows=64, rect=False, conv_hoist=False,
-               conv_shared=False) -> EncodedCNN:
+               conv_shared=False, pack_first=False) -> EncodedCNN:
     L = o.L
-    e = EncodedCNN(windows=windows, taps=w.conv_w.shape[1], conv_hoist=conv_hoist, conv_shared=conv_shared)
+    e = EncodedCNN(windows=windows, taps=w.conv_w.shape[1], conv_hoist=conv_hoist, conv_shared=conv_shared,
+                   pack_first=pack_first)
+    nb = len(o.conv_bsgs_steps(e.taps, windows)[0]) + 1
     for k in range(w.conv_w.shape[0]):
         e.conv.append(o.encode(o.kernel_slots(w.conv_w[k], windows), level=L))
         if conv_shared:
             e.conv_baby_ext.append(o.conv_baby_diagonals_ext(o.kernel_slots(w.conv_w[k], windows), e.taps,
                                                              windows, L))
         mask = np.zeros(o.slots)
-        mask[k * windows: (k + 1) * windows] = 1.0
+        if pack_first:  # the windows-blocks k + nb g: what the giant-step sum gathers into block k
+            blk = np.arange(o.slots) // windows
+            mask[blk % nb == k] = 1.0
+        else:
+            mask[k * windows: (k + 1) * windows] = 1.0
         e.masks.append(o.encode(mask, level=L - 1))
     if rect:
         e.fc1 = o.encode_matrix_rect(w.fc1_w.T, L - 3)
@@ -911,26 +930,46 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
     four channel outputs with masks -> square -> FC1 (vector x plain matrix) -> square -> FC2.
     Six multiplicative levels; biases are added as plaintexts at the ciphertext's scale and level.
     double_hoist: the two vector x matrix products take the ModDown once after their rotation sums."""
-    def fc(v, diags, diags_ext, n, m, replicate=True):
+    def fc(v, diags, diags_ext, n, m, replicate=True, period=None):
         if enc.rect:
-            return (o.vecmat_rect(v, n, m, diags_ext=diags_ext, replicate=replicate) if double_hoist
-                    else o.vecmat_rect(v, n, m, diags=diags, replicate=replicate))
-        return o.vecmat_dh(v, diags_ext, n, m) if double_hoist else o.vecmat(v, diags, n, m)
+            return (o.vecmat_rect(v, n, m, diags_ext=diags_ext, replicate=replicate, period=period) if double_hoist
+                    else o.vecmat_rect(v, n, m, diags=diags, replicate=replicate, period=period))
+        return (o.vecmat_dh(v, diags_ext, n, m, period=period) if double_hoist
+                else o.vecmat(v, diags, n, m, period=period))
 
     W = enc.windows
     K = len(enc.conv)
-    if enc.conv_shared:
-        chans = [o.conv2d_im2col_shared(ct, enc.conv_baby_ext[k], enc.taps, W) for k in range(K)]
-    else:
-        conv = o.conv2d_im2col_hoisted if enc.conv_hoist else o.conv2d_im2col_pt
-        chans = [conv(ct, enc.conv[k], enc.taps, W) for k in range(K)]
-    v = None
-    for k in range(K):
-        t = o.rescale(o.mul_plain(chans[k], enc.masks[k]))
-        v = t if v is None else o.add(v, t)
+    period = None
     bias = np.zeros(o.slots)
-    for k in range(K):
-        bias[k * W: (k + 1) * W] = w.conv_b[k]
+    if enc.pack_first:
+        # baby-step sums z_k, masks on the blocks k + B g, the pack, then one giant-step sum: block k of
+        # the result gathers blocks k + B g of z_k, the full tap sum of kernel k (reading A23)
+        baby, giant = o.conv_bsgs_steps(enc.taps, W)
+        if enc.conv_shared:
+            zs = [o.rescale(o.dh_sum(ct, baby, enc.conv_baby_ext[k])) for k in range(K)]
+        else:
+            zs = [o.rotsum_dh(o.rescale(o.mul_plain(ct, enc.conv[k])), baby) for k in range(K)]
+        v = None
+        for k in range(K):
+            t = o.rescale(o.mul_plain(zs[k], enc.masks[k]))
+            v = t if v is None else o.add(v, t)
+        v = o.rotsum_dh(v, giant)
+        period = (len(baby) + 1) * W  # blocks [K, B) are zero, the pattern repeats every B blocks
+        for r in range(o.slots // period):
+            for k in range(K):
+                bias[r * period + k * W: r * period + (k + 1) * W] = w.conv_b[k]
+    else:
+        if enc.conv_shared:
+            chans = [o.conv2d_im2col_shared(ct, enc.conv_baby_ext[k], enc.taps, W) for k in range(K)]
+        else:
+            conv = o.conv2d_im2col_hoisted if enc.conv_hoist else o.conv2d_im2col_pt
+            chans = [conv(ct, enc.conv[k], enc.taps, W) for k in range(K)]
+        v = None
+        for k in range(K):
+            t = o.rescale(o.mul_plain(chans[k], enc.masks[k]))
+            v = t if v is None else o.add(v, t)
+        for k in range(K):
+            bias[k * W: (k + 1) * W] = w.conv_b[k]
     if trace is not None:
         trace["bias_scales"] = [v.scale]
     def bias_pt(i, values, v):
@@ -941,7 +980,7 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
     v = o.add_plain(v, bias_pt(0, bias, v))
     v = o.square(v)
     n1, m1 = w.fc1_w.shape[1], w.fc1_w.shape[0]
-    v = fc(v, enc.fc1, enc.fc1_ext, n1, m1)
+    v = fc(v, enc.fc1, enc.fc1_ext, n1, m1, period=period)
     b1 = np.zeros(o.slots)
     b1[:m1] = w.fc1_b
     if enc.rect:  # FC1's output is replicated with period rect_width(m1): so is its bias

@@ -530,3 +530,22 @@ def test_cnn_shared_conv_schedule_matches_fp64():
     ct = o.encrypt_values(v, 77)
     logits = o.decrypt_values(oracle.cnn_forward(o, ct, w, enc, double_hoist=True), 10)
     assert np.max(np.abs(logits - oracle.cnn_plain(img, w))) < 5e-3
+
+
+@pytest.mark.parametrize("shared", [True, False])
+def test_cnn_pack_first_schedule_matches_fp64(shared):
+    """The CNN with the channels packed after the baby-step sums and one giant-step sum per request
+    (the packed vector repeats every 8 windows-blocks, so FC1 replicates with one rotation) decrypts to
+    the FP64 network, with the shared or the per-kernel baby steps."""
+    o = OracleCKKS(13, [31, 26, 26, 26, 26, 26, 26, 31], 2.0 ** 26).keygen()
+    steps = oracle.cnn_galois_steps(o, rect=True, conv_hoist=True, conv_shared=shared, pack_first=True)
+    assert steps[512] == o.L - 2 and steps[o.slots - 256] == o.L - 3
+    for st, lv in steps.items():
+        o.gen_galois_key(st, lv)
+    w = oracle.CNNWeights(**inputs.cnn_weights(4))
+    enc = oracle.cnn_encode(o, w, rect=True, conv_hoist=True, conv_shared=shared, pack_first=True)
+    img = inputs.mnist_like_image(3)
+    v, _ = OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+    ct = o.encrypt_values(v, 77)
+    logits = o.decrypt_values(oracle.cnn_forward(o, ct, w, enc, double_hoist=True), 10)
+    assert np.max(np.abs(logits - oracle.cnn_plain(img, w))) < 5e-3
