@@ -166,7 +166,7 @@ def source_digest(files) -> str:
 
 
 # ---------------------------------------------------------------------------------- GPU arm --
-def gpu_setup(torch, batch, double_hoist, rect=False, conv_hoist=False, conv_shared=False):
+def gpu_setup(torch, batch, double_hoist, rect=False, conv_hoist=False, conv_shared=False, conv_pack=False):
     import paper_2104_03152_gb300 as tk
     from paper_2104_03152_gb300 import inputs
 
@@ -174,7 +174,8 @@ def gpu_setup(torch, batch, double_hoist, rect=False, conv_hoist=False, conv_sha
     stream = torch.cuda.Stream()
     flags = (tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | (tk.TCKS_DOUBLE_HOIST if double_hoist else 0)
              | (tk.TCKS_RECT_DIAG if rect else 0) | (tk.TCKS_CONV_HOIST if conv_hoist else 0)
-             | (tk.TCKS_CONV_SHARED if conv_hoist and conv_shared else 0))
+             | (tk.TCKS_CONV_SHARED if conv_hoist and conv_shared else 0)
+             | (tk.TCKS_CONV_PACK if conv_hoist and conv_pack else 0))
     ctx = tk.Context(tk.Params(LOG_N, BITS, SCALE), seed=inputs.SEED_KEYS, flags=flags, stream=stream.cuda_stream)
     w = inputs.cnn_weights(SEED_W)
     model = tk.CNN(ctx, w["conv_w"], w["conv_b"], w["fc1_w"], w["fc1_b"], w["fc2_w"], w["fc2_b"], windows=64)
@@ -205,7 +206,7 @@ def run_gpu(args, world, rank, local):
     B = args.batch
     rect = args.fc_form == "rect"
     tk, ctx, model, cts, stream, imgs, w = gpu_setup(torch, B, args.double_hoist, rect, bool(args.conv_hoist),
-                                                     bool(args.conv_shared))
+                                                     bool(args.conv_shared), bool(args.conv_pack))
     # correctness guard: the decrypted logits of every request must match the FP64 network, and the
     # batched outputs must equal the single-request path bit for bit
     outs = model.forward_batch(cts)
@@ -281,7 +282,9 @@ def run_gpu(args, world, rank, local):
         ctx.set_flags(base | dh_flag)
         alt.gen_keys()
         time_model(alt, label)
-    if conv_form(args) == "shared":
+    if conv_form(args) == "shared+pack":
+        other((tk.TCKS_RECT_DIAG if rect else 0) | tk.TCKS_CONV_SHARED, f"{form} FC layers, {CONV_LABEL['shared']}")
+    if conv_form(args).startswith("shared"):
         other((tk.TCKS_RECT_DIAG if rect else 0) | tk.TCKS_CONV_HOIST, f"{form} FC layers, {CONV_LABEL['hoist']}")
     if args.conv_hoist:
         other(tk.TCKS_RECT_DIAG if rect else 0, f"{form} FC layers, rotate-and-add convolution chain")
@@ -698,6 +701,8 @@ def primitives_summary(torch, tk):
 
 
 CONV_LABEL = {
+    "shared+pack": ("hoisted sums, baby steps over the input's rotations shared by the 4 kernels, channels packed "
+                    "before one giant-step sum per request"),
     "shared": "hoisted sums, baby steps over the input's rotations shared by the 4 kernels (one ModUp per request)",
     "hoist": "two hoisted rotation sums per kernel (7 baby + 7 giant steps, one ModDown each)",
     "chain": "rotate-and-add chain (6 key switches)",
@@ -705,20 +710,23 @@ CONV_LABEL = {
 
 
 def conv_form(args) -> str:
-    return ("shared" if args.conv_shared else "hoist") if args.conv_hoist else "chain"
+    if not args.conv_hoist:
+        return "chain"
+    return ("shared+pack" if args.conv_pack else "shared") if args.conv_shared else "hoist"
 
 
 # ------------------------------------------------------------------------------ CPU oracle --
-def oracle_setup(rect: bool = True, conv_hoist: bool = True, conv_shared: bool = True):
+def oracle_setup(rect: bool = True, conv_hoist: bool = True, conv_shared: bool = True, conv_pack: bool = True):
     import oracle
     from paper_2104_03152_gb300 import inputs
 
     o = oracle.OracleCKKS(LOG_N, BITS, SCALE, key_seed=inputs.SEED_KEYS).keygen()
-    shared = conv_hoist and conv_shared
-    for st, lv in oracle.cnn_galois_steps(o, rect=rect, conv_hoist=conv_hoist, conv_shared=shared).items():
+    shared, pack = conv_hoist and conv_shared, conv_hoist and conv_shared and conv_pack
+    for st, lv in oracle.cnn_galois_steps(o, rect=rect, conv_hoist=conv_hoist, conv_shared=shared,
+                                          pack_first=pack).items():
         o.gen_galois_key(st, lv)
     w = oracle.CNNWeights(**inputs.cnn_weights(SEED_W))
-    enc = oracle.cnn_encode(o, w, rect=rect, conv_hoist=conv_hoist, conv_shared=shared)
+    enc = oracle.cnn_encode(o, w, rect=rect, conv_hoist=conv_hoist, conv_shared=shared, pack_first=pack)
     img = inputs.mnist_like_image(SEED_IMG)
     v, _ = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
     ct = o.encrypt_values(v, SEED_ENC)
@@ -726,10 +734,10 @@ def oracle_setup(rect: bool = True, conv_hoist: bool = True, conv_shared: bool =
 
 
 def time_oracle(n_steps: int, warmup: int, double_hoist: bool = True, single_thread_steps: int = 0,
-                rect: bool = True, conv_hoist: bool = True, conv_shared: bool = True):
+                rect: bool = True, conv_hoist: bool = True, conv_shared: bool = True, conv_pack: bool = True):
     """Oracle CNN inferences on the host cores (same schedule as the GPU arm); optionally also
     single-threaded ones. Returns (times, cores, single-thread times)."""
-    oracle, o, w, enc, ct = oracle_setup(rect, conv_hoist, conv_shared)
+    oracle, o, w, enc, ct = oracle_setup(rect, conv_hoist, conv_shared, conv_pack)
     for _ in range(warmup):
         oracle.cnn_forward(o, ct, w, enc, double_hoist=double_hoist)
     times = []
@@ -755,7 +763,7 @@ def run_reference(args, world, rank):
     steps, warmup = args.steps, args.warmup
     # bound the run: at most ~3 minutes of oracle inferences
     times, cores, _ = time_oracle(steps, warmup, bool(args.double_hoist), 0, args.fc_form == "rect",
-                                  bool(args.conv_hoist), bool(args.conv_shared))
+                                  bool(args.conv_hoist), bool(args.conv_shared), bool(args.conv_pack))
     total = sum(times)
     value = steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": args.gpus,
@@ -801,6 +809,8 @@ def main():
                     help="the convolution sums as hoisted baby-step giant-step rotation sums (1) or a chain (0)")
     ap.add_argument("--conv-shared", type=int, default=1,
                     help="with --conv-hoist 1: the baby steps over the input's rotations, shared by the kernels")
+    ap.add_argument("--conv-pack", type=int, default=1,
+                    help="with --conv-shared 1: pack the channels before one giant-step sum per request")
     ap.add_argument("--double-hoist", type=int, default=1,
                     help="vector x matrix products take the ModDown once after the rotation sum (1) or per rotation (0)")
     ap.add_argument("--c4", type=int, default=1, help="time the 4096x256 vector x matrix workload (64 vectors)")
@@ -837,7 +847,7 @@ def main():
     alu_ach = ops / (ms / 1e3) / 1e9
     alu_peak = r["bfly_peak"] / 1e9
     traffic = ncu_traffic(name, {"batch": B, "fc_form": args.fc_form, "conv_hoist": args.conv_hoist,
-                                 "conv_shared": args.conv_shared if args.conv_hoist else 0,
+                                 "conv_form": conv_form(args),
                                  "double_hoist": args.double_hoist})
     hbm = {"achieved": hbm_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_ach / peaks["hbm_gbs"],
            "peak_source": peaks["source"]}
@@ -857,7 +867,7 @@ def main():
     # CPU baseline: the oracle on the host cores, bounded sample
     if args.cpu_sample > 0:
         times, cores, single = time_oracle(args.cpu_sample, 0, bool(args.double_hoist), 1, args.fc_form == "rect",
-                                           bool(args.conv_hoist), bool(args.conv_shared))
+                                           bool(args.conv_hoist), bool(args.conv_shared), bool(args.conv_pack))
         cpu_val = len(times) / sum(times)
     else:
         times, cores, cpu_val, single = [], 0, None, []

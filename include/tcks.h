@@ -112,14 +112,21 @@ tcks_status tcks_params_primes(const tcks_params* p, uint64_t* primes, uint32_t 
  * the input's own rotations, sum_b rot(ct, windows*b) * rot(kernel_k, windows*b) (rot(x * K) =
  * rot(x) * rot(K) slot by slot), with the rotated kernels pre-encoded over the extended basis: one
  * ModUp per request for all kernels, the key-switch sums formed once per rotation, one ModDown per
- * kernel, then the rescale; 1 or 4 kernels. The baby-step keys must cover level L. */
+ * kernel, then the rescale; 1 or 4 kernels. The baby-step keys must cover level L.
+ * TCKS_CONV_PACK (implies the baby/giant split): after the baby-step sums the channels are masked to
+ * the windows-blocks k + B g (g < G) instead of block k, packed into one ciphertext per request, and
+ * one giant-step sum gathers each kernel's full tap sum into its block k: one giant-step sum per
+ * request instead of one per kernel, at level L-2. The packed vector repeats every B windows, so the
+ * first fully connected layer replicates it from that period (one rotation instead of four at the
+ * paper's sizes). Needs kernels <= B and 2^ceil(log2 taps) windows == N/2. */
 enum {
   TCKS_AUTO_RELIN = 1u,
   TCKS_AUTO_RESCALE = 2u,
   TCKS_DOUBLE_HOIST = 4u,
   TCKS_RECT_DIAG = 8u,
   TCKS_CONV_HOIST = 16u,
-  TCKS_CONV_SHARED = 32u
+  TCKS_CONV_SHARED = 32u,
+  TCKS_CONV_PACK = 64u
 };
 tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32_t flags,
                                 const tcks_allocator* allocator, void* cuda_stream, tcks_ctx** out);

@@ -21,6 +21,7 @@ TCKS_DOUBLE_HOIST = 4
 TCKS_RECT_DIAG = 8
 TCKS_CONV_HOIST = 16
 TCKS_CONV_SHARED = 32
+TCKS_CONV_PACK = 64
 TCKS_CTA_ADD, TCKS_CTA_SUB, TCKS_CTA_MUL = 0, 1, 2  # ciphertext-array operations
 KEY_SECRET, KEY_PUBLIC, KEY_RELIN, KEY_GALOIS = 0, 1, 2, 3
 

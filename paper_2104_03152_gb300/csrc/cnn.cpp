@@ -9,6 +9,9 @@
 //         (TCKS_CONV_SHARED) the baby steps as a diagonal-method sum over the input's own rotations,
 //         sum_b rot(ct, W b) * rot(kernel_k, W b), one ModUp per request for all kernels and one
 //         ModDown per kernel, rescaled [L-1], then the giant steps;
+//         (TCKS_CONV_PACK) after the baby steps the channels are masked to the windows-blocks k + B g
+//         and packed [L-2], then one giant-step sum per request gathers block k's full tap sum; the
+//         packed vector repeats every B blocks, so FC1 replicates it from that period;
 //   pack: v = sum_k rescale(conv_k * mask_k) [L-2], mask_k = 1 on slots [k*W, (k+1)*W); + conv bias;
 //   square: rescale(relin(v * v)) [L-3];
 //   FC1: vector x plain matrix (replicate, hoisted diagonal method, rescale) [L-4]; + bias;
@@ -38,6 +41,8 @@ struct tcks_cnn {
   bool rect;                 // rectangular FC layers: FC1's output comes replicated and feeds FC2 as is
   bool conv_hoist;           // the convolution sums as two hoisted rotation sums (baby and giant steps)
   bool conv_shared;          // baby steps on the input's own rotations, shared by every kernel
+  bool pack_first;           // channels packed after the baby steps, one giant-step sum per request
+  u32 period = 0;            // pack_first: the packed vector repeats every B windows (0 otherwise)
   std::vector<int32_t> baby, giant;
   u64* baby_ext = nullptr;   // conv_shared: per kernel k and baby step b (0 first), the kernel rotated
                              // left by windows * b over the extended basis, [kernels][B][L+1][N]
@@ -132,7 +137,7 @@ void cnn_stage(const tcks_cnn* m, u32 stage, const u64* x, u32 count, u64* out) 
         op_dh_sum_multi(c, x, w_in, count, L, m->baby, m->baby_ext, dstride, dstride * nb, L, K, z.p, w_in,
                         (u64)count * w_in);
         op_rescale(c, z.p, L, chans.p, K * count);
-        op_rotsum_hoisted(c, chans.p, w1, K * count, L - 1, m->giant, chans.p);
+        if (!m->pack_first) op_rotsum_hoisted(c, chans.p, w1, K * count, L - 1, m->giant, chans.p);
       } else {
         {
           DevBuf prod(c, (size_t)count * w_in);
@@ -143,7 +148,7 @@ void cnn_stage(const tcks_cnn* m, u32 stage, const u64* x, u32 count, u64* out) 
         }
         if (m->conv_hoist) {
           op_rotsum_hoisted(c, chans.p, w1, K * count, L - 1, m->baby, chans.p);
-          op_rotsum_hoisted(c, chans.p, w1, K * count, L - 1, m->giant, chans.p);
+          if (!m->pack_first) op_rotsum_hoisted(c, chans.p, w1, K * count, L - 1, m->giant, chans.p);
         } else {
           const int rsteps = ceil_log2(m->taps);
           for (int i = 0; i < rsteps; ++i)
@@ -158,6 +163,7 @@ void cnn_stage(const tcks_cnn* m, u32 stage, const u64* x, u32 count, u64* out) 
         op_rescale(c, prod.p, L - 1, k == 0 ? out : t.p, count);
         if (k) launch_elementwise(c->T, OP_ADD, out, t.p, out, L - 2, 2 * count, c->stream);
       }
+      if (m->pack_first) op_rotsum_hoisted(c, out, w2, count, L - 2, m->giant, out);
       launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[0], out, L - 2, 2 * count, c->stream);
       break;
     }
@@ -165,14 +171,14 @@ void cnn_stage(const tcks_cnn* m, u32 stage, const u64* x, u32 count, u64* out) 
       square_stage(c, x, L - 2, count, out);
       break;
     case 2:
-      op_vecmat(c, x, ct_words(c, L - 3), count, L - 3, m->fc1, out);
+      op_vecmat(c, x, ct_words(c, L - 3), count, L - 3, m->fc1, out, m->period);
       launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[1], out, L - 4, 2 * count, c->stream);
       break;
     case 3:
       square_stage(c, x, L - 4, count, out);
       break;
     case 4:
-      op_vecmat(c, x, ct_words(c, L - 5), count, L - 5, m->fc2, out, m->rect);
+      op_vecmat(c, x, ct_words(c, L - 5), count, L - 5, m->fc2, out, m->rect ? m->fc2->rows : 0);
       launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[2], out, L - 6, 2 * count, c->stream);
       break;
     default:
@@ -270,7 +276,8 @@ tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* con
   m->in_scale = c->params.scale;
   m->rect = (c->flags & TCKS_RECT_DIAG) != 0;
   m->conv_shared = (c->flags & TCKS_CONV_SHARED) != 0;
-  m->conv_hoist = m->conv_shared || (c->flags & TCKS_CONV_HOIST) != 0;
+  m->pack_first = (c->flags & TCKS_CONV_PACK) != 0;
+  m->conv_hoist = m->conv_shared || m->pack_first || (c->flags & TCKS_CONV_HOIST) != 0;
   if (m->conv_shared && kernels != 4 && kernels != 1)
     fail(TCKS_ERR_UNSUPPORTED, "the shared convolution sum takes 1 or 4 kernels");
   {
@@ -279,6 +286,13 @@ tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* con
     const u32 nb = 1u << (e / 2), ng = 1u << (e - e / 2);
     for (u32 b = 1; b < nb; ++b) m->baby.push_back((int32_t)(windows * b));
     for (u32 g = 1; g < ng; ++g) m->giant.push_back((int32_t)(windows * nb * g));
+    if (m->pack_first) {
+      // block k of the giant-step sum gathers the blocks k + B g: kernels <= B, and the 2^e tap
+      // positions must wrap around the whole slot vector (as the tap sums themselves do)
+      if (kernels > nb || (u64)nb * ng * windows != slots)
+        fail(TCKS_ERR_UNSUPPORTED, "packing before the giant steps needs kernels <= B and 2^e windows == N/2");
+      m->period = nb * windows;
+    }
   }
   m->bias[0] = m->bias[1] = m->bias[2] = nullptr;
   m->fc1 = m->fc2 = nullptr;
@@ -309,7 +323,11 @@ tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* con
       }
     }
     std::fill(lay.begin(), lay.end(), 0.0);
-    for (u32 w = 0; w < windows; ++w) lay[(size_t)k * windows + w] = 1.0;
+    if (m->pack_first) {  // the windows-blocks k + B g
+      for (u32 i = 0; i < slots; ++i) lay[i] = (i / windows) % (m->period / windows) == k ? 1.0 : 0.0;
+    } else {
+      for (u32 w = 0; w < windows; ++w) lay[(size_t)k * windows + w] = 1.0;
+    }
     m->masks.push_back(encode_host(lay, delta, L - 1));
   }
   // FC weights W [out][in] act as M = W^T [in][out]
@@ -330,8 +348,9 @@ tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* con
   m->bias_scale[2] = s_fc2;
   m->out_scale = s_fc2;
   std::fill(lay.begin(), lay.end(), 0.0);
-  for (u32 k = 0; k < kernels; ++k)
-    for (u32 w = 0; w < windows; ++w) lay[(size_t)k * windows + w] = conv_b[k];
+  for (u32 r = 0; r < (m->period ? slots / m->period : 1); ++r)  // the packed layout's period
+    for (u32 k = 0; k < kernels; ++k)
+      for (u32 w = 0; w < windows; ++w) lay[(size_t)r * m->period + (size_t)k * windows + w] = conv_b[k];
   m->bias[0] = encode_host(lay, s_pack, L - 2);
   // rectangular layers leave their outputs replicated with period m' (hidden, then the power of two
   // above classes): the biases are laid out the same way
@@ -365,14 +384,14 @@ tcks_status tcks_cnn_galois_steps(const tcks_cnn* m, int32_t* steps, uint32_t* l
       }
     need.push_back({s, lv});
   };
-  if (m->conv_hoist) {  // shared: the baby steps rotate the input, at level L
+  if (m->conv_hoist) {  // shared: the baby steps rotate the input, at level L; packed first: giant at L-2
     for (int32_t s : m->baby) use((u32)s, m->conv_shared ? L : L - 1);
-    for (int32_t s : m->giant) use((u32)s, L - 1);
+    for (int32_t s : m->giant) use((u32)s, m->pack_first ? L - 2 : L - 1);
   } else {
     for (int i = 0; i < ceil_log2(m->taps); ++i) use(m->windows << i, L - 1);
   }
   const u32 n1 = m->kernels * m->windows, n2 = m->hidden;
-  for (u32 r = 0; ((u64)n1 << r) < slots; ++r) use(slots - (n1 << r), L - 3);
+  for (u32 r = 0; ((u64)n1 << r) < (m->period ? m->period : slots); ++r) use(slots - (n1 << r), L - 3);
   if (m->rect) {  // m' - 1 rotations, then the rotate-and-add chain after the rescale; FC2 unreplicated
     for (u32 k = 1; k < m->fc1->diags; ++k) use(k, L - 3);
     for (u32 w = m->fc1->diags; w < n1; w <<= 1) use(w, L - 4);

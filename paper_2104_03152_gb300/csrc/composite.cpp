@@ -171,7 +171,7 @@ void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, cons
 }
 
 void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell, const tcks_matrix* M, u64* out,
-               bool input_replicated) {
+               u32 input_period) {
   const bool dh = (c->flags & TCKS_DOUBLE_HOIST) != 0;
   if (dh && !M->ext)
     fail(TCKS_ERR_UNSUPPORTED, "double-hoisted vector x matrix needs the diagonals modulo P (tcks_matrix_encode or "
@@ -180,8 +180,8 @@ void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell,
   const u32 slots = c->N / 2;
   const u64 cw = ct_words(c, ell);
   std::vector<int32_t> rep;
-  if (!input_replicated)
-    for (u32 m = 0; ((u64)rows << m) < slots; ++m) rep.push_back((int32_t)(slots - (rows << m)));
+  const u64 period = input_period ? input_period : slots;
+  for (u32 m = 0; ((u64)rows << m) < period; ++m) rep.push_back((int32_t)(slots - (rows << m)));
   std::vector<u32> steps;
   for (u32 k = 1; k < diags; ++k) steps.push_back(k);
   // rectangular form: the rotate-and-add chain by diags * 2^j after the rescale

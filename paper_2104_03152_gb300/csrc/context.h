@@ -185,9 +185,11 @@ void encode_into(tcks_ctx* c, const double* d_v, size_t n, double scale, u32 lev
 // composite.cpp
 void op_sum(tcks_ctx* c, u64* ct, u32 ell);  // in place
 // count ciphertexts ct + i * ct_stride at level ell -> out [count][2][ell-1][N]
-// input_replicated: the input already holds the vector replicated with period M->rows (skip replication)
+// input_period: 0, the input holds the vector in slots [0, rows) and zeros elsewhere (replicated over
+// all slots first); P, it already repeats with period P (zeros in [rows, P)): replicated from P down
+// to rows only (P = rows: no replication).
 void op_vecmat(tcks_ctx* c, const u64* ct, u64 ct_stride, u32 count, u32 ell, const tcks_matrix* M, u64* out,
-               bool input_replicated = false);
+               u32 input_period = 0);
 void op_conv(tcks_ctx* c, const u64* ct, u32 ell, const u64* kernel_pt, u32 taps, u32 windows, u64* out);
 void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const std::vector<int32_t>& steps, u64* out);
 // sum_k rot(x, s_k) * d_{o,k} (s_0 = 0, s_k = steps[k-1]) for `count` ciphertexts (stride cw) and `outs`

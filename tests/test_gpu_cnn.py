@@ -220,23 +220,26 @@ def test_cnn_hoisted_conv_parity(setup):
         ctx.set_flags(base)
 
 
-def test_cnn_shared_conv_parity(setup):
-    """TCKS_CONV_SHARED (+ rectangular FC layers, double hoisting; the bench's network): the baby-step sums
-    of the four kernels over the input's own rotations in one 4-output double-hoisted pass. Galois steps
+@pytest.mark.parametrize("pack", [False, True], ids=["shared", "shared+pack"])
+def test_cnn_shared_conv_parity(setup, pack):
+    """TCKS_CONV_SHARED (+ rectangular FC layers, double hoisting): the baby-step sums of the four kernels
+    over the input's own rotations in one 4-output double-hoisted pass; with TCKS_CONV_PACK (the bench's
+    network) the channels packed after the baby steps and one giant-step sum per request. Galois steps
     and levels as the oracle's schedule; on the model's own encodings bit-identical to the oracle's
     forward pass, single and batched, and within 5e-3 of the FP64 network."""
     o, w, enc, ctx, model, need = setup
     base = tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE
-    ctx.set_flags(base | tk.TCKS_RECT_DIAG | tk.TCKS_CONV_SHARED | tk.TCKS_DOUBLE_HOIST)
+    ctx.set_flags(base | tk.TCKS_RECT_DIAG | tk.TCKS_CONV_SHARED | tk.TCKS_DOUBLE_HOIST
+                  | (tk.TCKS_CONV_PACK if pack else 0))
     try:
         hm = tk.CNN(ctx, w.conv_w, w.conv_b, w.fc1_w, w.fc1_b, w.fc2_w, w.fc2_b, windows=64)
-        steps = oracle.cnn_galois_steps(o, rect=True, conv_hoist=True, conv_shared=True)
+        steps = oracle.cnn_galois_steps(o, rect=True, conv_hoist=True, conv_shared=True, pack_first=pack)
         assert hm.galois_steps() == steps
         for st, lv in steps.items():
             if st not in o.galois or o.galois[st].level < lv:
                 o.gen_galois_key(st, lv)
         hm.gen_keys()
-        henc = oracle.cnn_encode(o, w, rect=True, conv_hoist=True, conv_shared=True)
+        henc = oracle.cnn_encode(o, w, rect=True, conv_hoist=True, conv_shared=True, pack_first=pack)
         L = o.L
         nb = len(o.conv_bsgs_steps(49, 64)[0]) + 1
         for k in range(4):
@@ -245,6 +248,9 @@ def test_cnn_shared_conv_parity(setup):
                 _near_tie_agreement(o, np.ascontiguousarray(got_ext[b, :L]),
                                     np.ascontiguousarray(henc.conv_baby_ext[k][b, :L]), L)
             henc.conv_baby_ext[k] = got_ext
+            mask = hm.export_plaintext(1, k)[0]
+            _near_tie_agreement(o, mask, henc.masks[k].data, L - 1)
+            henc.masks[k] = oracle.Pt(mask, L - 1, o.scale)
         henc.fc1 = [oracle.Pt(hm.export_plaintext(3, i)[0], L - 3, o.scale) for i in range(64)]
         henc.fc2 = [oracle.Pt(hm.export_plaintext(4, i)[0], L - 5, o.scale) for i in range(16)]
         henc.fc1_ext = np.stack([hm.export_plaintext(5, i)[0] for i in range(64)])
