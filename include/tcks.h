@@ -488,6 +488,12 @@ tcks_status tcks_cnn_forward(const tcks_cnn* m, const tcks_ct* in, tcks_ct** out
  * the whole batch (rotations of all requests share key-switch launches). outs[i] is bit-identical
  * to tcks_cnn_forward(in[i]). */
 tcks_status tcks_cnn_forward_batch(const tcks_cnn* m, const tcks_ct* const* in, uint32_t count, tcks_ct** outs);
+/* The batched forward pass straight from and to host memory: host_in [count][2][L][N] input limbs
+ * (NTT form, level L, the context scale; pinned memory copies fastest), host_out [count][2][L-6][N]
+ * receives the outputs (their scale is the model's output scale, as tcks_cnn_forward reports). One
+ * host-to-device copy, the batched schedule on one contiguous device batch, one device-to-host copy;
+ * returns when host_out is written. */
+tcks_status tcks_cnn_forward_host(const tcks_cnn* m, const uint64_t* host_in, uint32_t count, uint64_t* host_out);
 /* CUDA graph of the batched forward for a fixed batch size (the schedule is captured once with its
  * stream-ordered scratch allocations, then replayed): create captures it (after one eager pass that
  * warms the key tables), run copies the inputs into the graph's staging buffers, replays and returns

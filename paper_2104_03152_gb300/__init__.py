@@ -159,6 +159,7 @@ _SIGS = {
     "tcks_cnn_galois_steps": (ctypes.c_int32, [_vp, _i32p, _u32p, ctypes.c_uint32, _u32p]),
     "tcks_cnn_forward": (ctypes.c_int32, [_vp, _vp, _vpp]),
     "tcks_cnn_forward_batch": (ctypes.c_int32, [_vp, _vpp, ctypes.c_uint32, _vpp]),
+    "tcks_cnn_forward_host": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, _u64p]),
     "tcks_vecmat_plain_batch": (ctypes.c_int32, [_vpp, ctypes.c_uint32, _vp, _vpp]),
     "tcks_ct_import_batch": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double, _vpp]),
     "tcks_ct_export_batch": (ctypes.c_int32, [_vpp, ctypes.c_uint32, _u64p, ctypes.c_size_t]),
@@ -725,6 +726,12 @@ class CNN:
         outs = (_vp * len(cts))()
         check(lib().tcks_cnn_forward_batch(self.h, ins, len(cts), outs))
         return [Ciphertext(self.ctx, _vp(outs[i])) for i in range(len(cts))]
+
+    def forward_host(self, host_in: np.ndarray, host_out: np.ndarray):
+        """The batched forward pass from host limbs [count][2][L][N] into host_out [count][2][L-6][N]."""
+        assert host_in.dtype == np.uint64 and host_out.dtype == np.uint64
+        check(lib().tcks_cnn_forward_host(self.h, _p(host_in), host_in.shape[0], _p(host_out)))
+        return host_out
 
     def graph(self, count: int) -> "CNNGraph":
         return CNNGraph(self, count)

@@ -465,6 +465,20 @@ tcks_status tcks_cnn_forward_batch(const tcks_cnn* m, const tcks_ct* const* in, 
   CNN_END
 }
 
+tcks_status tcks_cnn_forward_host(const tcks_cnn* m, const uint64_t* host_in, uint32_t count, uint64_t* host_out) {
+  CNN_BEGIN
+  if (!m || (count && (!host_in || !host_out))) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  if (!count) return TCKS_OK;
+  tcks_ctx* c = m->ctx;
+  const u64 w_in = ct_words(c, m->L), w_out = ct_words(c, m->L - 6);
+  DevBuf xin(c, (size_t)count * w_in), yout(c, (size_t)count * w_out);
+  check_cuda(cudaMemcpyAsync(xin.p, host_in, (size_t)count * w_in * 8, cudaMemcpyHostToDevice, c->stream), "H2D");
+  cnn_forward_dev(m, xin.p, w_in, count, yout.p);
+  check_cuda(cudaMemcpyAsync(host_out, yout.p, (size_t)count * w_out * 8, cudaMemcpyDeviceToHost, c->stream), "D2H");
+  check_cuda(cudaStreamSynchronize(c->stream), "forward");
+  CNN_END
+}
+
 // -------------------------------------------------------------------------- CUDA graphs ----
 struct tcks_cnn_graph {
   tcks_ctx* ctx;  // retained: the graph's buffers belong to it

@@ -235,26 +235,37 @@ __device__ __forceinline__ void cross_stages(W* s, u32 log_n, u32 log_ns, u32 ra
 // The stages a slice of 2^log_ns consecutive elements (slice `rank` of the limb) completes on its
 // own: forward stages log_n - log_ns .. log_n - 1 (the earlier ones pair elements of different
 // slices), or inverse stages 0 .. log_ns - 1. Each ends with a barrier.
+// Stages per local round (radix-8). Radix-16 rounds for 32-bit words were measured: one shared-memory
+// round trip fewer, but the register pressure they add slowed the fused key-switch kernels more than
+// it sped up the plain transforms.
+constexpr int kRadixBits32 = 3;
+template <typename W>
+struct RadixBits {
+  static constexpr int value = sizeof(W) == 4 ? kRadixBits32 : 3;
+};
+
 template <typename W, typename A = Ar<W>>
 __device__ __forceinline__ void ntt_fwd_local_rounds(W* s, u32 log_n, u32 log_ns, u32 rank, const W* tw, const W* tws,
                                                      W q) {
+  constexpr int RB = RadixBits<W>::value;
   u32 st = log_n - log_ns;
-  const u32 left = log_ns;
-  // remainder round first (radix-2 or radix-4), then radix-8 rounds
-  if (left % 3 == 1) {
-    fwd_round<W, 1, A>(s, log_n, log_ns, rank, st, tw, tws, q);
-    st += 1;
-  } else if (left % 3 == 2) {
-    fwd_round<W, 2, A>(s, log_n, log_ns, rank, st, tw, tws, q);
-    st += 2;
-  }
-  for (; st < log_n; st += 3) fwd_round<W, 3, A>(s, log_n, log_ns, rank, st, tw, tws, q);
+  // remainder round first, then full rounds of RB stages
+  const u32 rem = log_ns % RB;
+  if (rem == 1) fwd_round<W, 1, A>(s, log_n, log_ns, rank, st, tw, tws, q);
+  if (rem == 2) fwd_round<W, 2, A>(s, log_n, log_ns, rank, st, tw, tws, q);
+  if constexpr (RB > 3)
+    if (rem == 3) fwd_round<W, 3, A>(s, log_n, log_ns, rank, st, tw, tws, q);
+  st += rem;
+  for (; st < log_n; st += RB) fwd_round<W, RB, A>(s, log_n, log_ns, rank, st, tw, tws, q);
 }
 template <typename W, typename A = Ar<W>>
 __device__ __forceinline__ void ntt_inv_local_rounds(W* s, u32 log_n, u32 log_ns, u32 rank, const W* tw, const W* tws,
                                                      W q) {
+  constexpr int RB = RadixBits<W>::value;
   u32 st = 0;
-  for (; st + 3 <= log_ns; st += 3) inv_round<W, 3, A>(s, log_n, log_ns, rank, st, tw, tws, q);
+  for (; st + RB <= log_ns; st += RB) inv_round<W, RB, A>(s, log_n, log_ns, rank, st, tw, tws, q);
+  if constexpr (RB > 3)
+    if (log_ns - st == 3) inv_round<W, 3, A>(s, log_n, log_ns, rank, st, tw, tws, q);
   if (log_ns - st == 2) inv_round<W, 2, A>(s, log_n, log_ns, rank, st, tw, tws, q);
   if (log_ns - st == 1) inv_round<W, 1, A>(s, log_n, log_ns, rank, st, tw, tws, q);
 }
