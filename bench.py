@@ -8,8 +8,9 @@ A step is one batch of B encrypted inferences (B requests, default 256) through 
 schedule, where every stage runs once for the whole batch; inputs are resident in HBM. Per step the
 kernels stream the Galois keys plus several GB of per-request key-switch scratch (~2 GB at B = 64),
 far more than the 129 MB L2, so no L2 flush is added. The plain path (one request per step) is timed alongside.
-`e2e` times the batched step through the C ABI with host buffers: the B input ciphertexts are
-imported from pinned host memory and the B outputs exported back to it inside the timed region.
+`e2e` times the batched step through the C ABI with host buffers (tcks_cnn_forward_host): one copy
+of the B input ciphertexts from pinned host memory, the batched schedule, one copy of the B outputs
+back to it, all inside the timed region.
 
 --impl reference times the CPU oracle (the plain CKKS written from the definitions) on the host
 cores, one inference per step.
@@ -215,8 +216,20 @@ def run_gpu(args, world, rank, local):
         logits = ctx.decrypt_values(outs[i], 10)
         max_err = max(max_err, float(np.max(np.abs(logits - plain_cnn(imgs[i], w)))))
         assert np.array_equal(outs[i].export(), model.forward(cts[i]).export()), "batched != single"
+    # the timed step: the whole batch on one contiguous device buffer (inputs resident in HBM)
+    L_in, N_ = cts[0].level, ctx.N
+    d_in = torch.empty((B, 2, L_in, N_), dtype=torch.int64, device="cuda")
+    for i, c in enumerate(cts):
+        d_in[i].copy_(torch.from_numpy(c.export().view(np.int64)))
+    d_out = torch.empty((B, 2, outs[0].level, N_), dtype=torch.int64, device="cuda")
+    d_in_ptr, d_out_ptr = d_in.data_ptr(), d_out.data_ptr()
+    torch.cuda.synchronize()
+    model.forward_device(d_in_ptr, B, d_out_ptr)
+    ctx.synchronize()
+    for i in (0, B - 1):
+        assert np.array_equal(d_out[i].cpu().numpy().view(np.uint64), outs[i].export()), "device batch != batched"
     for _ in range(args.warmup):
-        model.forward_batch(cts)
+        model.forward_device(d_in_ptr, B, d_out_ptr)
     ctx.synchronize()
     # plain path: one request per step
     plain_steps = max(3, min(args.steps, 10))
@@ -230,7 +243,7 @@ def run_gpu(args, world, rank, local):
     n0 = tk.launch_count()
     tk.profile_start()
     torch.cuda.nvtx.range_push("timed")
-    per_step, total_ms = timed(torch, stream, lambda: model.forward_batch(cts), args.steps)
+    per_step, total_ms = timed(torch, stream, lambda: model.forward_device(d_in_ptr, B, d_out_ptr), args.steps)
     torch.cuda.nvtx.range_pop()
     tk.profile_stop()
     launches = tk.launch_count() - n0
@@ -239,7 +252,7 @@ def run_gpu(args, world, rank, local):
     clk = clocks.stop()
     total_ms = reduce_max(world, total_ms)
     prof = tk.profile_read(with_ops=True)
-    # e2e through the C ABI with pinned host buffers: import B inputs, batched forward, export B outputs
+    # e2e through the C ABI with pinned host buffers: B inputs in, batched forward, B outputs out
     L, N = cts[0].level, ctx.N
     host_in = torch.empty(B * 2 * L * N, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
     host_in = host_in.reshape(B, 2, L, N)
@@ -252,11 +265,9 @@ def run_gpu(args, world, rank, local):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_steps = max(3, args.steps // 2)
+    out_view = host_out.reshape(B, 2, outs[0].level, N)
     for _ in range(e2e_steps):
-        cin = ctx.ct_import_batch(host_in, cts[0].scale)
-        couts = model.forward_batch(cin)
-        handles = (tk._vp * B)(*[co.h.value for co in couts])
-        tk.check(tk.lib().tcks_ct_export_batch(handles, B, tk._p(host_out), host_out.size))
+        model.forward_host(host_in, out_view)
     torch.cuda.synchronize()
     e2e_s = reduce_max(world, time.perf_counter() - t0)
     # the same batched step with one ModDown per rotation (the schedule bit-identical to rotating
@@ -266,8 +277,8 @@ def run_gpu(args, world, rank, local):
     dh_flag = tk.TCKS_DOUBLE_HOIST if args.double_hoist else 0
 
     def time_model(mdl, label):
-        mdl.forward_batch(cts)
-        _, tot = timed(torch, stream, lambda: mdl.forward_batch(cts), 3)
+        mdl.forward_device(d_in_ptr, B, d_out_ptr)
+        _, tot = timed(torch, stream, lambda: mdl.forward_device(d_in_ptr, B, d_out_ptr), 3)
         single[label] = {"value": B * 3 / (tot / 1e3), "unit": "inferences/s", "ms_per_step": tot / 3}
     form = "rectangular" if rect else "square"
     conv = CONV_LABEL[conv_form(args)]

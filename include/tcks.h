@@ -488,6 +488,10 @@ tcks_status tcks_cnn_forward(const tcks_cnn* m, const tcks_ct* in, tcks_ct** out
  * the whole batch (rotations of all requests share key-switch launches). outs[i] is bit-identical
  * to tcks_cnn_forward(in[i]). */
 tcks_status tcks_cnn_forward_batch(const tcks_cnn* m, const tcks_ct* const* in, uint32_t count, tcks_ct** outs);
+/* The batched forward pass on device buffers: d_in [count][2][L][N] (level L, the context scale),
+ * d_out [count][2][L-6][N], both contiguous, owned by the caller and not overlapping. Enqueued on the
+ * context's stream; returns without waiting for it. */
+tcks_status tcks_cnn_forward_device(const tcks_cnn* m, const uint64_t* d_in, uint32_t count, uint64_t* d_out);
 /* The batched forward pass straight from and to host memory: host_in [count][2][L][N] input limbs
  * (NTT form, level L, the context scale; pinned memory copies fastest), host_out [count][2][L-6][N]
  * receives the outputs (their scale is the model's output scale, as tcks_cnn_forward reports). One

@@ -160,6 +160,7 @@ _SIGS = {
     "tcks_cnn_forward": (ctypes.c_int32, [_vp, _vp, _vpp]),
     "tcks_cnn_forward_batch": (ctypes.c_int32, [_vp, _vpp, ctypes.c_uint32, _vpp]),
     "tcks_cnn_forward_host": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, _u64p]),
+    "tcks_cnn_forward_device": (ctypes.c_int32, [_vp, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
     "tcks_vecmat_plain_batch": (ctypes.c_int32, [_vpp, ctypes.c_uint32, _vp, _vpp]),
     "tcks_ct_import_batch": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double, _vpp]),
     "tcks_ct_export_batch": (ctypes.c_int32, [_vpp, ctypes.c_uint32, _u64p, ctypes.c_size_t]),
@@ -726,6 +727,11 @@ class CNN:
         outs = (_vp * len(cts))()
         check(lib().tcks_cnn_forward_batch(self.h, ins, len(cts), outs))
         return [Ciphertext(self.ctx, _vp(outs[i])) for i in range(len(cts))]
+
+    def forward_device(self, d_in: int, count: int, d_out: int):
+        """The batched forward pass on device buffers (pointers to [count][2][L][N] and
+        [count][2][L-6][N] words), enqueued on the context's stream."""
+        check(lib().tcks_cnn_forward_device(self.h, d_in, count, d_out))
 
     def forward_host(self, host_in: np.ndarray, host_out: np.ndarray):
         """The batched forward pass from host limbs [count][2][L][N] into host_out [count][2][L-6][N]."""

@@ -465,6 +465,14 @@ tcks_status tcks_cnn_forward_batch(const tcks_cnn* m, const tcks_ct* const* in, 
   CNN_END
 }
 
+tcks_status tcks_cnn_forward_device(const tcks_cnn* m, const uint64_t* d_in, uint32_t count, uint64_t* d_out) {
+  CNN_BEGIN
+  if (!m || (count && (!d_in || !d_out))) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  if (!count) return TCKS_OK;
+  cnn_forward_dev(m, d_in, ct_words(m->ctx, m->L), count, d_out);
+  CNN_END
+}
+
 tcks_status tcks_cnn_forward_host(const tcks_cnn* m, const uint64_t* host_in, uint32_t count, uint64_t* host_out) {
   CNN_BEGIN
   if (!m || (count && (!host_in || !host_out))) fail(TCKS_ERR_INVALID_ARG, "null argument");

@@ -10,6 +10,7 @@ from gpu_common import SEED, assert_ct_equal
 from paper_2104_03152_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
 
 BITS = [31, 26, 26, 26, 26, 26, 26, 31]
 
@@ -273,3 +274,25 @@ def test_cnn_shared_conv_parity(setup, pack):
         assert e.value.name in ("UNSUPPORTED", "INVALID_ARG")
     finally:
         ctx.set_flags(base)
+
+
+def test_cnn_forward_host_equals_batch(setup):
+    """tcks_cnn_forward_host (host limbs in, host limbs out) and tcks_cnn_forward_device (contiguous
+    device buffers) give the batched forward's outputs."""
+    o, w, enc, ctx, model, need = setup
+    img = inputs.mnist_like_image(9)
+    v, W = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+    cts = [o.encrypt_values(v, 90 + i) for i in range(3)]
+    host_in = np.ascontiguousarray(np.stack([c.data for c in cts]))
+    outs = model.forward_batch([ctx.ct_import(c.data, c.scale) for c in cts])
+    lv = outs[0].info()[0]
+    host_out = np.zeros((3, 2, lv, o.N), dtype=np.uint64)
+    model.forward_host(host_in, host_out)
+    for i in range(3):
+        assert np.array_equal(host_out[i], outs[i].export())
+    d_in = torch.from_numpy(host_in.view(np.int64)).cuda()
+    d_out = torch.zeros((3, 2, lv, o.N), dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    model.forward_device(d_in.data_ptr(), 3, d_out.data_ptr())
+    ctx.synchronize()
+    assert np.array_equal(d_out.cpu().numpy().view(np.uint64), host_out)
