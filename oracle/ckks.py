@@ -57,6 +57,8 @@ def lib():
         "orc_decode_sum": (None, [vp, _dblp, ctypes.c_double, u32, _dblp]),
         "orc_encrypt": (None, [vp, _u64p, _u64p, u32, u64, _u64p]),
         "orc_decrypt": (None, [vp, _u64p, _u64p, u32, _u64p]),
+        "orc_sample_sym_a": (None, [vp, u32, u64, _u64p]),
+        "orc_encrypt_symmetric": (None, [vp, _u64p, _u64p, u32, u64, u64, _u64p]),
         "orc_add": (None, [vp, _u64p, _u64p, u32, u32, _u64p]),
         "orc_sub": (None, [vp, _u64p, _u64p, u32, u32, _u64p]),
         "orc_negate": (None, [vp, _u64p, u32, u32, _u64p]),
@@ -316,6 +318,19 @@ class OracleCKKS:
         data = np.ascontiguousarray(pt.data)
         lib().orc_encrypt(self._ctx, P(self.pk), P(data), pt.level, seed, P(ct))
         return Ct(ct, pt.level, pt.scale)
+
+    def encrypt_symmetric(self, pt: Pt, seed_a: int, seed_e: int) -> Ct:
+        """Secret-key encryption (-a s + e + m, a): a uniform from the public seed seed_a, e from the
+        private seed seed_e. The pair travels as c0 and seed_a (wire kind 1)."""
+        ct = np.zeros((2, pt.level, self.N), dtype=np.uint64)
+        lib().orc_encrypt_symmetric(self._ctx, P(self.s), P(np.ascontiguousarray(pt.data)), pt.level, seed_a, seed_e,
+                                    P(ct))
+        return Ct(ct, pt.level, pt.scale)
+
+    def sample_sym_a(self, level: int, seed_a: int) -> np.ndarray:
+        a = np.zeros((level, self.N), dtype=np.uint64)
+        lib().orc_sample_sym_a(self._ctx, level, seed_a, P(a))
+        return a
 
     def decrypt(self, ct: Ct) -> Pt:
         pt = np.zeros((ct.level, self.N), dtype=np.uint64)

@@ -434,6 +434,7 @@ void orc_automorphism_coeff(const OrcCtx* c, const u64* a, u64 q, u32 g, u64* ou
 // ------------------------------------------------------------------------------- keys (O6-O8) ---
 // Stream tags of the sampler (one per sampled polynomial).
 //   1 secret s; 2 public a; 3 public e; 4 encryption u; 5 encryption e0; 6 encryption e1;
+//   7 secret-key encryption a (from the public seed); 8 secret-key encryption e (from the private seed);
 //   switching key for `kind` (0 = relinearization, otherwise the Galois element g), digit j:
 //   a_j: (kind << 32) | 0x80000000 | (2j), e_j: (kind << 32) | 0x80000000 | (2j + 1).
 
@@ -623,6 +624,33 @@ void orc_encrypt(const OrcCtx* c, const u64* pk, const u64* pt, u32 level, u64 s
       c0[i] = addm(addm(mulm(ut[i], p0[i], q), e0t[i], q), ml[i], q);
       c1[i] = addm(mulm(ut[i], p1[i], q), e1t[i], q);
     }
+  }
+}
+
+// The uniform polynomial a of a secret-key encryption, sampled per limb directly in NTT form from the
+// public seed (stream 7): [level][N].
+void orc_sample_sym_a(const OrcCtx* c, u32 level, u64 seed_a, u64* a) {
+  for (u32 l = 0; l < level; ++l)
+    for (u64 i = 0; i < c->n; ++i) limb(a, c->n, l)[i] = sample_uniform(seed_a, 7, i, l, c->q[l]);
+}
+
+// Secret-key encryption: ct = (-a*s + e + m, a), a from the public seed (stream 7), e CBD from the
+// private seed (stream 8). Only c0 and seed_a need to travel: the receiver regenerates a.
+void orc_encrypt_symmetric(const OrcCtx* c, const u64* s, const u64* pt, u32 level, u64 seed_a, u64 seed_e,
+                           u64* ct) {
+  const u64 n = c->n;
+  std::vector<int64_t> e(n);
+  for (u64 i = 0; i < n; ++i) e[i] = sample_cbd(seed_e, 8, i);
+  std::vector<u64> et(n);
+  orc_sample_sym_a(c, level, seed_a, limb(ct, n, level));
+  for (u32 l = 0; l < level; ++l) {
+    const u64 q = c->q[l];
+    signed_to_ntt(c, e.data(), l, et.data());
+    const u64* a = limb(ct, n, level + l);
+    const u64* sl = limb(s, n, l);
+    const u64* ml = limb(pt, n, l);
+    u64* c0 = limb(ct, n, l);
+    for (u64 i = 0; i < n; ++i) c0[i] = addm(addm(negm(mulm(a[i], sl[i], q), q), et[i], q), ml[i], q);
   }
 }
 

@@ -8,6 +8,8 @@ The paper reports the communication of one encrypted inference (encrypted input 
   payload: for component b = 0, 1 and limb i = 0 .. level-1, the N residues of that limb (NTT form),
   residue k in bits [k w_i, (k + 1) w_i) of the limb's segment, w_i = bit_length(q_i), bits numbered
   from the least significant bit of the segment's first byte; each segment is ceil(N w_i / 8) bytes.
+  Kind 1 (a secret-key ciphertext, (-a s + e + m, a) with a the uniform polynomial of a public seed):
+  the header, the seed (u64), then component 0 only, packed the same way.
 """
 from __future__ import annotations
 
@@ -47,6 +49,41 @@ def serialize(data: np.ndarray, level: int, scale: float, log_n: int, primes) ->
         for i in range(level):
             out.append(pack_limb(data[b][i], int(primes[i]).bit_length()))
     return b"".join(out)
+
+
+def size_seeded(n: int, primes, level: int) -> int:
+    return HEADER + 8 + sum(limb_bytes(n, q) for q in primes[:level])
+
+
+def serialize_seeded(c0: np.ndarray, level: int, scale: float, log_n: int, primes, seed_a: int) -> bytes:
+    """Kind 1, a secret-key ciphertext whose c1 is the uniform polynomial of seed_a: header, seed_a
+    (u64, little-endian), then the level limbs of c0 packed as in kind 0. Half the bytes."""
+    out = [MAGIC, struct.pack("<BBBBd", 1, 1, log_n, level, scale), struct.pack("<Q", seed_a)]
+    for i in range(level):
+        out.append(pack_limb(c0[i], int(primes[i]).bit_length()))
+    return b"".join(out)
+
+
+def deserialize_seeded(buf: bytes, primes):
+    """-> (c0 [level][N], seed_a, level, scale, log_n) of a kind-1 buffer; ValueError otherwise."""
+    if len(buf) < HEADER + 8 or buf[:4] != MAGIC:
+        raise ValueError("not a serialized ciphertext")
+    version, kind, log_n, level, scale = struct.unpack("<BBBBd", buf[4:16])
+    if version != 1 or kind != 1 or level < 1 or level > len(primes) - 1:
+        raise ValueError("unsupported header")
+    n = 1 << log_n
+    if len(buf) != size_seeded(n, primes, level):
+        raise ValueError("size mismatch")
+    (seed_a,) = struct.unpack("<Q", buf[16:24])
+    c0 = np.zeros((level, n), dtype=np.uint64)
+    off = HEADER + 8
+    for i in range(level):
+        lb = limb_bytes(n, primes[i])
+        c0[i] = unpack_limb(buf[off:off + lb], n, int(primes[i]).bit_length())
+        if np.any(c0[i] >= np.uint64(primes[i])):
+            raise ValueError("residue out of range")
+        off += lb
+    return c0, seed_a, level, scale, log_n
 
 
 def deserialize(buf: bytes, primes):
