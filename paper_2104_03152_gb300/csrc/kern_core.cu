@@ -539,12 +539,12 @@ template <typename W, int E = 0>
 __device__ __forceinline__ u64 ks_inner(const W* __restrict__ digits, u32 ell_arg, u32 slot, const u64* __restrict__ key,
                                         u32 K, u32 key_slot, u32 b, u32 k, u32 src, u64 n, const ModConst& m) {
   const u32 ell = E > 0 ? (u32)E : ell_arg;
-  typename Ew<W>::Acc acc;
+  KsSum<W, E> acc;
 #pragma unroll
   for (u32 j = 0; j < ell; ++j) {
     const u64 d = digits[((u64)j * (ell + 1) + slot) * n + src];
     const u64 w = key[(((u64)j * 2 + b) * (K + 1) + key_slot) * n + k];
-    acc.mac(d, w);
+    acc.mac(d, w, j);
   }
   return acc.get(m);
 }

@@ -111,15 +111,15 @@ __global__ void __launch_bounds__(kDhThreads, KO > 1 ? 3 : 1) k_vecmat_dh_acc(De
       const u32 g = base + e * kDhThreads;
       if (g < n) {
         const u32 src = galois_src(g, kk.g, log_n);
-        typename Ew<W>::Acc s0[RPT], s1[RPT];
+        KsSum<W, ELL> s0[RPT], s1[RPT];
 #pragma unroll
         for (u32 j = 0; j < ell; ++j) {
           const u64 w0 = k0[2 * j * kstep + g], w1 = k0[(2 * j + 1) * kstep + g];
 #pragma unroll
           for (int rr = 0; rr < RPT; ++rr) {
             const u64 d = digits[rr][(u64)j * slots * n + src];
-            s0[rr].mac(d, w0);
-            s1[rr].mac(d, w1);
+            s0[rr].mac(d, w0, j);
+            s1[rr].mac(d, w1, j);
           }
         }
         if (unit) {

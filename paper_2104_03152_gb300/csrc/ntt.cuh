@@ -349,11 +349,44 @@ struct Ew<u32> {
       lo += p;
       carry += lo < p;
     }
+    // fold a partial sum of products (below 2^64) into the sum
+    __device__ __forceinline__ void add64(u64 p) {
+      lo += p;
+      carry += lo < p;
+    }
     __device__ __forceinline__ u64 get(const ModConst& m) const {
       const u64 v = reduce64(lo, m);
       return carry ? reduce64(v + (u64)carry * m.r64, m) : v;
     }
   };
+};
+
+// Key-switch inner product sum_j d_j w_j over the digits j < E (E = 0: the level is known only at run
+// time), one reduction at the end. 64-bit words: the 128-bit lazy sum. 32-bit words: the products
+// (below 2^62) are summed in plain 64-bit registers in groups of four (4 (2^31 - 1)^2 < 2^64), each
+// group folded into a carry-counted sum, so with E known a product costs one multiply-add.
+template <typename W, int E>
+struct KsSum {
+  typename Ew<W>::Acc acc;
+  __device__ __forceinline__ void mac(u64 d, u64 w, u32) { acc.mac(d, w); }
+  __device__ __forceinline__ u64 get(const ModConst& m) const { return acc.get(m); }
+};
+template <int E>
+struct KsSum<u32, E> {
+  u64 part = 0;
+  typename Ew<u32>::Acc acc;
+  __device__ __forceinline__ void mac(u64 d, u64 w, u32 j) {
+    part += (u64)(u32)d * (u32)w;
+    if ((E == 0 || E > 4) && (j & 3u) == 3u) {
+      acc.add64(part);
+      part = 0;
+    }
+  }
+  __device__ __forceinline__ u64 get(const ModConst& m) {
+    if (E > 0 && E <= 4) return reduce64(part, m);
+    acc.add64(part);
+    return acc.get(m);
+  }
 };
 
 // Launch geometry of a limb transform: cluster size 2^log_c, threads per CTA, shared memory bytes
