@@ -194,7 +194,20 @@ tcks_status tcks_ct_export_batch(const tcks_ct* const* cts, uint32_t count, uint
  * (INVALID_ARG otherwise). */
 tcks_status tcks_ct_serialized_size(const tcks_ct* ct, uint64_t* bytes);
 tcks_status tcks_ct_serialize(const tcks_ct* ct, uint8_t* out, uint64_t cap, uint64_t* written);
+/* deserialize also reads kind 1 (below) and regenerates c1 from the seed on the device. */
 tcks_status tcks_ct_deserialize(tcks_ctx* ctx, const uint8_t* in, uint64_t size, tcks_ct** out);
+/* Secret-key encryption of a plaintext at its level (the client holds the secret key): c1 = a, the
+ * uniform polynomial drawn from the public seed seed_a (sampler stream 7, NTT form), c0 = -a s + e + m
+ * with e drawn from the private seed seed_e (stream 8). seed_e must stay secret; seed_a travels. */
+tcks_status tcks_encrypt_symmetric(tcks_ctx* ctx, const tcks_pt* pt, uint64_t seed_a, uint64_t seed_e,
+                                   tcks_ct** out);
+/* Wire kind 1, the seeded form of such a ciphertext: the header with kind 1, seed_a as a little-endian
+ * u64, then component 0 only, packed as in kind 0 (half the bytes of kind 0 plus 8). serialize_seeded
+ * checks on the device that c1 is the uniform polynomial of seed_a (INVALID_ARG otherwise, so a
+ * ciphertext that has been computed on cannot be sent this way). */
+tcks_status tcks_ct_serialized_size_seeded(const tcks_ct* ct, uint64_t* bytes);
+tcks_status tcks_ct_serialize_seeded(const tcks_ct* ct, uint64_t seed_a, uint8_t* out, uint64_t cap,
+                                     uint64_t* written);
 tcks_status tcks_pt_import(tcks_ctx* ctx, const uint64_t* limbs, uint32_t level, double scale, tcks_pt** out);
 tcks_status tcks_pt_export(const tcks_pt* pt, uint64_t* limbs, size_t n_words);
 tcks_status tcks_ct_info(const tcks_ct* ct, uint32_t* level, double* scale);
@@ -396,6 +409,10 @@ void tcks_batch_graph_free(tcks_batch_graph* g);
  * busy) on the current device for 64-bit (q < 2^62) or 32-bit (q < 2^31) words. A measurement aid
  * with no counterpart in the paper. Synchronous; errors: INVALID_ARG, CUDA. */
 tcks_status tcks_calibrate_butterflies(uint32_t word_bits, double* per_second);
+/* The same for modular multiply-accumulates in the form of the key-switch sums (products summed lazily,
+ * one reduction per eight products; for 32-bit words in plain 64-bit sums of four): product-accumulates
+ * per second, the ceiling of the kernels whose work is sums of products rather than transforms. */
+tcks_status tcks_calibrate_macs(uint32_t word_bits, double* per_second);
 /* Number of kernel launches the library has issued since it was loaded. */
 uint64_t tcks_launch_count(void);
 /* Kernel profiler: while on, every launch is bracketed by CUDA events on its stream and carries its

@@ -142,6 +142,7 @@ _SIGS = {
     "tcks_profile_count": (ctypes.c_uint32, []),
     "tcks_profile_read_ops": (ctypes.c_int32, [ctypes.c_uint32, _dblp]),
     "tcks_calibrate_butterflies": (ctypes.c_int32, [ctypes.c_uint32, _dblp]),
+    "tcks_calibrate_macs": (ctypes.c_int32, [ctypes.c_uint32, _dblp]),
     "tcks_profile_read": (ctypes.c_int32, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_char_p),
                                             ctypes.POINTER(ctypes.c_uint64), _dblp, _dblp]),
     "tcks_server_create": (ctypes.c_int32, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
@@ -167,6 +168,9 @@ _SIGS = {
     "tcks_ct_serialized_size": (ctypes.c_int32, [_vp, _u64p]),
     "tcks_ct_serialize": (ctypes.c_int32, [_vp, ctypes.c_void_p, ctypes.c_uint64, _u64p]),
     "tcks_ct_deserialize": (ctypes.c_int32, [_vp, ctypes.c_void_p, ctypes.c_uint64, _vpp]),
+    "tcks_encrypt_symmetric": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint64, ctypes.c_uint64, _vpp]),
+    "tcks_ct_serialized_size_seeded": (ctypes.c_int32, [_vp, _u64p]),
+    "tcks_ct_serialize_seeded": (ctypes.c_int32, [_vp, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64, _u64p]),
     "tcks_rotate_sum_hoisted": (ctypes.c_int32, [_vp, _i32p, ctypes.c_uint32, _vpp]),
     "tcks_batch_run": (ctypes.c_int32, [_vp, ctypes.c_uint32]),
     "tcks_batch_graph_create": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vpp]),
@@ -243,6 +247,13 @@ def calibrate_butterflies(word_bits: int = 64) -> float:
     """Modular butterflies per second of the integer pipe on the current device (registers only)."""
     v = ctypes.c_double()
     check(lib().tcks_calibrate_butterflies(word_bits, ctypes.byref(v)))
+    return v.value
+
+
+def calibrate_macs(word_bits: int) -> float:
+    """Measured modular multiply-accumulates per second (32- or 64-bit words), registers only."""
+    v = ctypes.c_double()
+    check(lib().tcks_calibrate_macs(word_bits, ctypes.byref(v)))
     return v.value
 
 
@@ -392,6 +403,12 @@ class Context:
     def encrypt(self, pt: "Plaintext", seed: int) -> "Ciphertext":
         h = _vp()
         check(lib().tcks_encrypt(self.h, pt.h, seed, ctypes.byref(h)))
+        return Ciphertext(self, h)
+
+    def encrypt_symmetric(self, pt: "Plaintext", seed_a: int, seed_e: int) -> "Ciphertext":
+        """Secret-key encryption: c1 from the public seed seed_a, the error from the private seed seed_e."""
+        h = _vp()
+        check(lib().tcks_encrypt_symmetric(self.h, pt.h, seed_a, seed_e, ctypes.byref(h)))
         return Ciphertext(self, h)
 
     def decrypt(self, ct: "Ciphertext") -> "Plaintext":
@@ -566,6 +583,15 @@ class Ciphertext:
         buf = ctypes.create_string_buffer(int(size[0]))
         written = np.zeros(1, dtype=np.uint64)
         check(lib().tcks_ct_serialize(self.h, buf, int(size[0]), _p(written)))
+        return buf.raw[: int(written[0])]
+
+    def serialize_seeded(self, seed_a: int) -> bytes:
+        """Wire kind 1 (c0 and the seed of c1) of a fresh secret-key ciphertext."""
+        size = np.zeros(1, dtype=np.uint64)
+        check(lib().tcks_ct_serialized_size_seeded(self.h, _p(size)))
+        buf = ctypes.create_string_buffer(int(size[0]))
+        written = np.zeros(1, dtype=np.uint64)
+        check(lib().tcks_ct_serialize_seeded(self.h, seed_a, buf, int(size[0]), _p(written)))
         return buf.raw[: int(written[0])]
 
     def export(self) -> np.ndarray:

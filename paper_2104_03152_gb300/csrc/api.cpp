@@ -672,6 +672,18 @@ tcks_status tcks_encrypt(tcks_ctx* c, const tcks_pt* pt, uint64_t seed, tcks_ct*
   TCKS_API_END
 }
 
+tcks_status tcks_encrypt_symmetric(tcks_ctx* c, const tcks_pt* pt, uint64_t seed_a, uint64_t seed_e, tcks_ct** out) {
+  TCKS_API_BEGIN
+  if (!c || !pt || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (pt->ctx != c) fail(TCKS_ERR_INVALID_ARG, "plaintext of another context");
+  tcks_ct* ct = new_ct(c, pt->level, pt->scale);
+  launch_encrypt_sym(c->T, seed_a, seed_e, c->sk, pt->d, pt->level, ct->d, c->stream);
+  check_launch("secret-key encrypt");
+  *out = ct;
+  TCKS_API_END
+}
+
 tcks_status tcks_decrypt(tcks_ctx* c, const tcks_ct* ct, tcks_pt** out) {
   TCKS_API_BEGIN
   if (!c || !ct || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
@@ -777,25 +789,68 @@ tcks_status tcks_ct_serialize(const tcks_ct* ct, uint8_t* out, uint64_t cap, uin
   TCKS_API_END
 }
 
+tcks_status tcks_ct_serialized_size_seeded(const tcks_ct* ct, uint64_t* bytes) {
+  TCKS_API_BEGIN
+  if (!ct || !bytes) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *bytes = kWireHeader + 8 + wire_payload_bytes(ct->ctx->T, ct->ctx->host.chain.data(), ct->level) / 2;
+  TCKS_API_END
+}
+
+tcks_status tcks_ct_serialize_seeded(const tcks_ct* ct, uint64_t seed_a, uint8_t* out, uint64_t cap,
+                                     uint64_t* written) {
+  TCKS_API_BEGIN
+  if (!ct || !out || !written) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  tcks_ctx* c = ct->ctx;
+  const u64 payload = wire_payload_bytes(c->T, c->host.chain.data(), ct->level) / 2;
+  if (cap < kWireHeader + 8 + payload) fail(TCKS_ERR_INVALID_ARG, "capacity below the serialized size");
+  // the receiver regenerates c1 from the seed: refuse a ciphertext whose c1 is not that polynomial
+  check_cuda(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "seeded status");
+  launch_sym_a(c->T, seed_a, ct->level, ct->d + (size_t)ct->level * c->N, true, c->d_status, c->stream);
+  DevBuf buf(c, (payload + 7) / 8);
+  launch_pack(c->T, ct->d, ct->level, (unsigned char*)buf.p, c->stream, 1);
+  check_launch("serialize (seeded)");
+  int status = 0;
+  check_cuda(cudaMemcpyAsync(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "seeded status");
+  check_cuda(cudaMemcpyAsync(out + kWireHeader + 8, buf.p, payload, cudaMemcpyDeviceToHost, c->stream), "serialize");
+  check_cuda(cudaStreamSynchronize(c->stream), "serialize");
+  if (status) fail(TCKS_ERR_INVALID_ARG, "c1 is not the uniform polynomial of this seed");
+  std::memcpy(out, kWireMagic, 4);
+  out[4] = 1;  // version
+  out[5] = 1;  // kind: seeded secret-key ciphertext
+  out[6] = (uint8_t)c->params.log_n;
+  out[7] = (uint8_t)ct->level;
+  std::memcpy(out + 8, &ct->scale, 8);
+  for (int b = 0; b < 8; ++b) out[kWireHeader + b] = (uint8_t)(seed_a >> (8 * b));
+  *written = kWireHeader + 8 + payload;
+  TCKS_API_END
+}
+
 tcks_status tcks_ct_deserialize(tcks_ctx* c, const uint8_t* in, uint64_t size, tcks_ct** out) {
   TCKS_API_BEGIN
   if (!c || !in || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   if (size < kWireHeader || std::memcmp(in, kWireMagic, 4) != 0) fail(TCKS_ERR_INVALID_ARG, "not a serialized ciphertext");
-  if (in[4] != 1 || in[5] != 0) fail(TCKS_ERR_INVALID_ARG, "unsupported version or kind");
+  if (in[4] != 1 || in[5] > 1) fail(TCKS_ERR_INVALID_ARG, "unsupported version or kind");
+  const bool seeded = in[5] == 1;
   if (in[6] != c->params.log_n) fail(TCKS_ERR_INVALID_ARG, "ring degree differs from the context's");
   const u32 level = in[7];
   if (level < 1 || level > c->L) fail(TCKS_ERR_INVALID_ARG, "level out of range");
   double scale;
   std::memcpy(&scale, in + 8, 8);
-  const u64 payload = wire_payload_bytes(c->T, c->host.chain.data(), level);
-  if (size != kWireHeader + payload) fail(TCKS_ERR_INVALID_ARG, "size does not match the header");
+  const u64 full = wire_payload_bytes(c->T, c->host.chain.data(), level);
+  const u64 payload = seeded ? full / 2 : full;
+  const u64 head = kWireHeader + (seeded ? 8 : 0);
+  if (size != head + payload) fail(TCKS_ERR_INVALID_ARG, "size does not match the header");
+  u64 seed_a = 0;
+  if (seeded)
+    for (int b = 0; b < 8; ++b) seed_a |= (u64)in[kWireHeader + b] << (8 * b);
   tcks_ct* r = new_ct(c, level, scale);
   try {
     DevBuf buf(c, (payload + 7) / 8);
-    check_cuda(cudaMemcpyAsync(buf.p, in + kWireHeader, payload, cudaMemcpyHostToDevice, c->stream), "deserialize");
+    check_cuda(cudaMemcpyAsync(buf.p, in + head, payload, cudaMemcpyHostToDevice, c->stream), "deserialize");
     check_cuda(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "deserialize status");
-    launch_unpack(c->T, (const unsigned char*)buf.p, level, r->d, c->d_status, c->stream);
+    launch_unpack(c->T, (const unsigned char*)buf.p, level, r->d, c->d_status, c->stream, seeded ? 1 : 2);
+    if (seeded) launch_sym_a(c->T, seed_a, level, r->d + (size_t)level * c->N, false, nullptr, c->stream);
     check_launch("deserialize");
     int status = 0;
     check_cuda(cudaMemcpyAsync(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "deserialize");

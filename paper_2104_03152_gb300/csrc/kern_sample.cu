@@ -3,7 +3,8 @@
 // SC'11) with key = (seed, stream tag) and counter = (coefficient index, chain index of the limb,
 // 0, 0). Draws: uniform residue = (w1:w0) mod q, ternary = (w0 mod 3) - 1, centred binomial
 // error (eta = 21) = popcount(w0 & (2^21-1)) - popcount((w0 >> 21) & (2^21-1)).
-// Stream tags: 1 s, 2 pk.a, 3 pk.e, 4 enc.u, 5 enc.e0, 6 enc.e1; switching key of kind `kind`
+// Stream tags: 1 s, 2 pk.a, 3 pk.e, 4 enc.u, 5 enc.e0, 6 enc.e1, 7 secret-key encryption a (public
+// seed), 8 secret-key encryption e (private seed); switching key of kind `kind`
 // (0 = relinearization, else the Galois element) digit j: a -> (kind<<32)|0x80000000|2j,
 // e -> the same | 1.
 #include <cuda_runtime.h>
@@ -175,17 +176,54 @@ __global__ void k_encrypt(DevTables T, u64 seed, const u64* __restrict__ pk, con
   for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) c1[k] = add_mod(c1[k], Ar<W>::fwd_out(s[sw(k)], m), m.q);
 }
 
+// Secret-key encryption at level ell, limb job = limb: c1 = a, uniform from the public seed (stream 7)
+// drawn directly in NTT form, c0 = -a*s + e + m with e from the private seed (stream 8).
+template <typename W, int LC>
+__global__ void k_encrypt_sym(DevTables T, u64 seed_a, u64 seed_e, const u64* __restrict__ sk,
+                              const u64* __restrict__ pt, u32 ell, u64* __restrict__ out) {
+  TCKS_SMEM(W);
+  const Slice P = slice_of<LC>(T);
+  const u64 n = 1ull << T.log_n;
+  const u32 l = P.job;
+  const ModConst m = T.mods[l];
+  small_ntt<W, LC>(s, T, l, SMALL_CBD, seed_e, 8, P.rank, P.ns);
+  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) {
+    const u32 g = P.off + k;
+    const u64 a = draw_uniform(seed_a, 7, g, l, m);
+    const u64 e = Ar<W>::fwd_out(s[sw(k)], m);
+    out[(u64)l * n + g] =
+        add_mod(add_mod(neg_mod(mulq_s(a, sk[(u64)l * n + g], m, T.narrow), m.q), e, m.q), pt[(u64)l * n + g], m.q);
+    out[((u64)ell + l) * n + g] = a;
+  }
+}
+
+// The uniform polynomial of a public seed over limbs 0..ell-1 ([ell][N], NTT form): with check == 0
+// written to a, otherwise compared with a and any difference flagged in *status.
+__global__ void k_sym_a(DevTables T, u64 seed_a, u32 ell, u64* __restrict__ a, int check, int* __restrict__ status) {
+  const u64 n = 1ull << T.log_n;
+  for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < (u64)ell * n; e += (u64)gridDim.x * blockDim.x) {
+    const u32 l = (u32)(e >> T.log_n);
+    const u64 v = draw_uniform(seed_a, 7, e & (n - 1), l, T.mods[l]);
+    if (!check)
+      a[e] = v;
+    else if (a[e] != v)
+      atomicExch(status, 1);
+  }
+}
+
 static decltype(&k_keygen_secret<u64, 0>) const K6_k_keygen_secret[6] = TCKS_K6(k_keygen_secret);
 static decltype(&k_keygen_public<u64, 0>) const K6_k_keygen_public[6] = TCKS_K6(k_keygen_public);
 static decltype(&k_keygen_switch<u64, 0>) const K6_k_keygen_switch[6] = TCKS_K6(k_keygen_switch);
 static decltype(&k_encrypt<u64, 0>) const K6_k_encrypt[6] = TCKS_K6(k_encrypt);
+static decltype(&k_encrypt_sym<u64, 0>) const K6_k_encrypt_sym[6] = TCKS_K6(k_encrypt_sym);
 
 // Largest CTA size every limb kernel of this file accepts for the word type and cluster split.
 u32 limb_threads_cap_sample(bool narrow, u32 log_c) {
   const u32 i = (narrow ? 3 : 0) + log_c;
   u32 cap = 1024;
-  const void* ks[4] = {(const void*)K6_k_keygen_secret[i], (const void*)K6_k_keygen_public[i],
-                       (const void*)K6_k_keygen_switch[i], (const void*)K6_k_encrypt[i]};
+  const void* ks[5] = {(const void*)K6_k_keygen_secret[i], (const void*)K6_k_keygen_public[i],
+                       (const void*)K6_k_keygen_switch[i], (const void*)K6_k_encrypt[i],
+                       (const void*)K6_k_encrypt_sym[i]};
   for (const void* k : ks) {
     cudaFuncAttributes a{};
     if (cudaFuncGetAttributes(&a, k) != cudaSuccess) return 0;
@@ -212,6 +250,20 @@ void launch_keygen_switch(const DevTables& T, u64 seed, u32 kind, const u64* s, 
 void launch_encrypt(const DevTables& T, u64 seed, const u64* pk, const u64* pt, u32 ell, u64* out, cudaStream_t st) {
   Launch L(K_ENCRYPT, st, 8.0 * 5 * ell * (1u << T.log_n));
   launch_limb(K6_k_encrypt, T.narrow, ell, 1, T.log_n, st, T.limb_threads, T, seed, pk, pt, ell, out);
+}
+
+void launch_encrypt_sym(const DevTables& T, u64 seed_a, u64 seed_e, const u64* sk, const u64* pt, u32 ell, u64* out,
+                        cudaStream_t st) {
+  Launch L(K_ENCRYPT, st, 8.0 * 4 * ell * (1u << T.log_n));
+  launch_limb(K6_k_encrypt_sym, T.narrow, ell, 1, T.log_n, st, T.limb_threads, T, seed_a, seed_e, sk, pt, ell, out);
+}
+
+void launch_sym_a(const DevTables& T, u64 seed_a, u32 ell, u64* a, bool check, int* status, cudaStream_t st) {
+  const u64 e = (u64)ell << T.log_n;
+  Launch L(K_ENCRYPT, st, 8.0 * e);
+  u64 blocks = (e + 255) / 256;
+  if (blocks > 152ull * 8) blocks = 152ull * 8;
+  k_sym_a<<<(u32)blocks, 256, 0, st>>>(T, seed_a, ell, a, check ? 1 : 0, status);
 }
 
 }  // namespace tcks

@@ -258,8 +258,9 @@ void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cu
   const u32 outs = dh_outs(p);
   if ((outs != 1 && outs != 4) || (outs > 1 && !p.diag))
     fail(TCKS_ERR_UNSUPPORTED, "double-hoisted sums take 1 or 4 outputs per request (4 with diagonals)");
-  // per (request, rotation): the key-switch sums, then per output the diagonal products
-  const double ops = (double)p.B * p.R * n * ((ell + 1.0) * (2.0 * ell + 1.0 + 3.0 * outs) + ell * outs);
+  // product-accumulates per (request, rotation, element): the key-switch sums 2 ell (ell + 1), then per
+  // output the two components' and the c0 term's diagonal products (additions for unit diagonals)
+  const double ops = (double)p.B * p.R * n * (2.0 * ell * (ell + 1.0) + outs * (2.0 * (ell + 1.0) + ell));
   Launch L(K_VECMAT_DH, st, by + 8.0 * n * (outs - 1.0) * (p.R * (ell + 1.0) + p.B * p.chunks * (3.0 * ell + 2.0)), ops);
   const dim3 grid(vecmat_dh_base_ctas(T.log_n, ell, p.B, T.narrow, outs), p.chunks);
   if (outs == 4) {

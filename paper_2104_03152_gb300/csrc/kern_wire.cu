@@ -80,17 +80,18 @@ u64 wire_payload_bytes(const DevTables& T, const u64* host_primes, u32 level) {
   return 2 * bytes;
 }
 
-void launch_pack(const DevTables& T, const u64* ct, u32 level, unsigned char* out, cudaStream_t st) {
+void launch_pack(const DevTables& T, const u64* ct, u32 level, unsigned char* out, cudaStream_t st, u32 comps) {
   const u64 n = 1ull << T.log_n;
   const u64 max_seg = (n * 64 + 7) / 8;
-  Launch L(K_ELEMENTWISE, st, 8.0 * 2 * level * n * 1.9);
-  k_pack<<<dim3((unsigned)((max_seg + 255) / 256), level, 2), 256, 0, st>>>(T, ct, level, out);
+  Launch L(K_ELEMENTWISE, st, 8.0 * comps * level * n * 1.9);
+  k_pack<<<dim3((unsigned)((max_seg + 255) / 256), level, comps), 256, 0, st>>>(T, ct, level, out);
 }
 
-void launch_unpack(const DevTables& T, const unsigned char* in, u32 level, u64* ct, int* status, cudaStream_t st) {
+void launch_unpack(const DevTables& T, const unsigned char* in, u32 level, u64* ct, int* status, cudaStream_t st,
+                   u32 comps) {
   const u64 n = 1ull << T.log_n;
-  Launch L(K_ELEMENTWISE, st, 8.0 * 2 * level * n * 1.9);
-  k_unpack<<<dim3((unsigned)((n + 255) / 256), level, 2), 256, 0, st>>>(T, in, level, ct, status);
+  Launch L(K_ELEMENTWISE, st, 8.0 * comps * level * n * 1.9);
+  k_unpack<<<dim3((unsigned)((n + 255) / 256), level, comps), 256, 0, st>>>(T, in, level, ct, status);
 }
 
 }  // namespace tcks

@@ -57,8 +57,10 @@ u32 limb_threads_cap_fft(bool narrow, u32 log_c);
 // Bit-packed wire format of a ciphertext [2][level][N] (kern_wire.cu): payload bytes, pack into
 // `out` (device), unpack with a range check (status set to 1 on a residue >= q_i).
 u64 wire_payload_bytes(const DevTables& T, const u64* host_primes, u32 level);
-void launch_pack(const DevTables& T, const u64* ct, u32 level, unsigned char* out, cudaStream_t st);
-void launch_unpack(const DevTables& T, const unsigned char* in, u32 level, u64* ct, int* status, cudaStream_t st);
+// comps = 2: both components; comps = 1: component 0 only (the seeded format).
+void launch_pack(const DevTables& T, const u64* ct, u32 level, unsigned char* out, cudaStream_t st, u32 comps = 2);
+void launch_unpack(const DevTables& T, const unsigned char* in, u32 level, u64* ct, int* status, cudaStream_t st,
+                   u32 comps = 2);
 void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_outer, u64* dst, u64 dst_outer,
                 u32 count, u32 mod_base, u32 per, cudaStream_t st);
 enum : u32 { OP_ADD = 0, OP_SUB = 1, OP_NEG = 2, OP_MUL_PLAIN = 3, OP_ADD_PLAIN = 4, OP_SUB_PLAIN = 5 };
@@ -171,6 +173,11 @@ void launch_keygen_public(const DevTables& T, u64 seed, const u64* s, u64* pk, c
 void launch_keygen_switch(const DevTables& T, u64 seed, u32 kind, const u64* s, u32 K, u64* ksk, cudaStream_t st);
 // Public-key encryption at level ell: out [2][ell][N]; scratch none.
 void launch_encrypt(const DevTables& T, u64 seed, const u64* pk, const u64* pt, u32 ell, u64* out, cudaStream_t st);
+// Secret-key encryption (c1 = a from the public seed, c0 = -a s + e + m, e from the private seed).
+void launch_encrypt_sym(const DevTables& T, u64 seed_a, u64 seed_e, const u64* sk, const u64* pt, u32 ell, u64* out,
+                        cudaStream_t st);
+// a [ell][N] = the uniform polynomial of seed_a; check: compare instead of writing (status = 1 on a mismatch).
+void launch_sym_a(const DevTables& T, u64 seed_a, u32 ell, u64* a, bool check, int* status, cudaStream_t st);
 
 // ---- kern_fft.cu (FP64 canonical embedding)
 struct FftTables {

@@ -175,3 +175,4 @@ def test_profiler_counts_butterflies_and_calibration(ctxs):
     launches, ms, by, ops = prof["ntt_fwd"]
     assert launches == 1 and by == 16 * o.N * 32 and ops == 32 * (o.N // 2) * o.log_n
     assert tk.calibrate_butterflies(64) > 1e10 and tk.calibrate_butterflies(32) > 1e10
+    assert tk.calibrate_macs(64) > 1e10 and tk.calibrate_macs(32) > tk.calibrate_macs(64)

@@ -6,7 +6,7 @@ import pytest
 import oracle
 from oracle import wire
 import paper_2104_03152_gb300 as tk
-from gpu_common import SEED
+from gpu_common import SEED, Pair
 from paper_2104_03152_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -57,3 +57,27 @@ def test_batch_import_export_roundtrip():
     handles = (tk._vp * len(cts))(*[c.h.value for c in cts])
     tk.check(tk.lib().tcks_ct_export_batch(handles, len(cts), tk._p(out), out.size))
     assert np.array_equal(out, data)
+
+
+@pytest.mark.parametrize("name", ["C1", "C2"])
+def test_secret_key_encryption_and_seeded_wire(name):
+    """tcks_encrypt_symmetric equals the oracle's secret-key encryption bit for bit; its seeded wire form
+    equals the oracle's byte for byte, deserializes to the same ciphertext (c1 regenerated on the
+    device), and a ciphertext that has been computed on is refused."""
+    log_n, bits, scale = {"C1": (12, [36, 36, 36, 37], 2.0 ** 30), "C2": (13, [31, 26, 26, 26, 26, 26, 26, 31], 2.0 ** 26)}[name]
+    p = Pair(log_n, bits, scale)
+    o, g = p.o, p.g
+    pt = o.encode(inputs.uniform_slots(o.slots, 3))
+    ref = o.encrypt_symmetric(pt, 4242, 17)
+    ct = g.encrypt_symmetric(p.import_pt(pt), 4242, 17)
+    assert np.array_equal(ct.export(), ref.data)
+    buf = ct.serialize_seeded(4242)
+    assert buf == wire.serialize_seeded(ref.data[0], ref.level, ref.scale, o.log_n, o.primes, 4242)
+    assert len(buf) == wire.size_seeded(o.N, o.primes, ref.level) == (len(ct.serialize()) - 16) // 2 + 24
+    back = g.ct_deserialize(buf)
+    assert np.array_equal(back.export(), ref.data)
+    with pytest.raises(tk.TcksError) as e:
+        ct.serialize_seeded(4243)  # not the seed of its c1
+    assert e.value.name == "INVALID_ARG"
+    with pytest.raises(tk.TcksError):
+        ct.add(ct).serialize_seeded(4242)
