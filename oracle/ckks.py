@@ -59,6 +59,7 @@ def lib():
         "orc_decrypt": (None, [vp, _u64p, _u64p, u32, _u64p]),
         "orc_sample_sym_a": (None, [vp, u32, u64, _u64p]),
         "orc_encrypt_symmetric": (None, [vp, _u64p, _u64p, u32, u64, u64, _u64p]),
+        "orc_relinearize_rescale": (None, [vp, _u64p, u32, _u64p, u32, _u64p]),
         "orc_add": (None, [vp, _u64p, _u64p, u32, u32, _u64p]),
         "orc_sub": (None, [vp, _u64p, _u64p, u32, u32, _u64p]),
         "orc_negate": (None, [vp, _u64p, u32, u32, _u64p]),
@@ -70,6 +71,7 @@ def lib():
         "orc_modup": (None, [vp, _u64p, u32, _u64p]),
         "orc_encode_ext": (i32, [vp, _dblp, u32, ctypes.c_double, u32, _u64p]),
         "orc_vecmat_dh": (None, [vp, _u64p, _u64p, u32, u32, _u64p, ctypes.POINTER(_u64p), _u32p, _u32p, _u64p]),
+        "orc_vecmat_dh_rs": (None, [vp, _u64p, _u64p, u32, u32, _u64p, ctypes.POINTER(_u64p), _u32p, _u32p, _u64p]),
         "orc_keyswitch_digits": (None, [vp, _u64p, u32, _u64p, u32, u32, _u64p]),
         "orc_keyswitch": (None, [vp, _u64p, u32, _u64p, u32, _u64p]),
         "orc_relinearize": (None, [vp, _u64p, u32, _u64p, u32, _u64p]),
@@ -405,6 +407,13 @@ class OracleCKKS:
         lib().orc_relinearize(self._ctx, P(np.ascontiguousarray(d3)), level, P(self.rlk.data), self.rlk.level, P(out))
         return Ct(out, level, scale)
 
+    def relinearize_rescale(self, d3: np.ndarray, level: int, scale: float) -> Ct:
+        """Relinearization and rescale with one rounding (reading A25): [2][level-1][N]."""
+        out = np.zeros((2, level - 1, self.N), dtype=np.uint64)
+        lib().orc_relinearize_rescale(self._ctx, P(np.ascontiguousarray(d3)), level, P(self.rlk.data), self.rlk.level,
+                                      P(out))
+        return Ct(out, level - 1, scale / float(self.q[level - 1]))
+
     def rescale(self, ct: Ct) -> Ct:
         """Divide by the last prime with rounding (O14)."""
         if ct.level < 2:
@@ -417,9 +426,14 @@ class OracleCKKS:
         """Drop limbs level..ell-1; the scale is unchanged (O19)."""
         return Ct(np.ascontiguousarray(ct.data[:, :level]), level, ct.scale)
 
-    def mul(self, a: Ct, b: Ct, relin: bool = True, rescale: bool = True) -> Ct:
-        """enc x enc multiply with the context's auto relinearize / rescale policy (§2.1)."""
+    def mul(self, a: Ct, b: Ct, relin: bool = True, rescale: bool = True, merged: bool = False) -> Ct:
+        """enc x enc multiply with the context's auto relinearize / rescale policy (§2.1); merged: the
+        relinearization's ModDown and the rescale as one rounding (A25)."""
         d3, level, scale = self.tensor(a, b)
+        if merged and rescale:
+            if level < 2:
+                raise ValueError("level exhausted")
+            return self.relinearize_rescale(d3, level, scale)
         ct = self.relinearize(d3, level, scale)
         return self.rescale(ct) if rescale else ct
 
@@ -621,7 +635,8 @@ class OracleCKKS:
         return (self.replicate_steps(n) if n < self.slots else []) + list(range(1, mw)) + chain
 
     def vecmat_rect(self, ct: Ct, n: int, m: int, diags: list[Pt] | None = None,
-                    diags_ext: np.ndarray | None = None, replicate: bool = True, period: int | None = None) -> Ct:
+                    diags_ext: np.ndarray | None = None, replicate: bool = True, period: int | None = None,
+                    merged: bool = False) -> Ct:
         """Vector x plain n x m matrix by the rectangular diagonal method: replicate, y' = sum over
         the m' = rect_width(m) diagonals of rot(ct, k) * d_k (hoisted; with one ModDown per rotation
         when `diags` is given, or once after the sum when `diags_ext` is), rescale, then
@@ -632,7 +647,7 @@ class OracleCKKS:
         replicate_steps)."""
         mw = self.rect_width(m)
         if diags_ext is not None:
-            y = self._vecmat_dh_rows(ct, diags_ext, n, mw, replicate, period)
+            y = self._vecmat_dh_rows(ct, diags_ext, n, mw, replicate, period, merged)
         else:
             y = self._vecmat_rows(ct, diags, n, mw, replicate, period)
         for j in range(int(math.log2(n // mw))):
@@ -654,8 +669,9 @@ class OracleCKKS:
         return self.rescale(acc)
 
     def _vecmat_dh_rows(self, ct: Ct, diags_ext: np.ndarray, n: int, rows: int, replicate: bool = True,
-                        period: int | None = None) -> Ct:
-        """The same with the ModDown once after the sum (orc_vecmat_dh over `rows` diagonals)."""
+                        period: int | None = None, merged: bool = False) -> Ct:
+        """The same with the ModDown once after the sum (orc_vecmat_dh over `rows` diagonals); merged:
+        the ModDown and the rescale as one rounding (orc_vecmat_dh_rs, A25)."""
         level = ct.level
         if replicate and n < self.slots:
             for st in self.replicate_steps(n, period):
@@ -666,12 +682,17 @@ class OracleCKKS:
         ptrs = (_u64p * max(1, len(keys)))(*[P(a) for a in key_arrs])
         lv = np.array([k.level for k in keys] or [0], dtype=np.uint32)
         ge = np.array([self.galois_elt(k) for k in range(1, rows)] or [1], dtype=np.uint32)
+        if merged:
+            out = np.zeros((2, level - 1, self.N), dtype=np.uint64)
+            lib().orc_vecmat_dh_rs(self._ctx, P(np.ascontiguousarray(ct.data)), P(digits), level, rows,
+                                   P(np.ascontiguousarray(diags_ext)), ptrs, P(lv), P(ge), P(out))
+            return Ct(out, level - 1, ct.scale * self.scale / float(self.q[level - 1]))
         out = np.zeros((2, level, self.N), dtype=np.uint64)
         lib().orc_vecmat_dh(self._ctx, P(np.ascontiguousarray(ct.data)), P(digits), level, rows,
                             P(np.ascontiguousarray(diags_ext)), ptrs, P(lv), P(ge), P(out))
         return self.rescale(Ct(out, level, ct.scale * self.scale))
 
-    def dh_sum(self, ct: Ct, steps, diags_ext: np.ndarray) -> Ct:
+    def dh_sum(self, ct: Ct, steps, diags_ext: np.ndarray, merged: bool = False) -> Ct:
         """sum_k rot(ct, s_k) * d_k with s_0 = 0 and s_k = steps[k - 1], the diagonals d_k given over
         the extended basis [len(steps) + 1][level + 1][N], with one ModUp before and one ModDown after
         the sum (orc_vecmat_dh). The scale is the ciphertext's times the diagonals' (no rescale)."""
@@ -686,6 +707,11 @@ class OracleCKKS:
         ptrs = (_u64p * max(1, len(keys)))(*[P(a) for a in key_arrs])
         lv = np.array([k.level for k in keys] or [0], dtype=np.uint32)
         ge = np.array([self.galois_elt(st) for st in steps] or [1], dtype=np.uint32)
+        if merged:  # with the rescale, one rounding (A25)
+            out = np.zeros((2, level - 1, self.N), dtype=np.uint64)
+            lib().orc_vecmat_dh_rs(self._ctx, P(np.ascontiguousarray(ct.data)), P(digits), level, rows,
+                                   P(np.ascontiguousarray(diags_ext)), ptrs, P(lv), P(ge), P(out))
+            return Ct(out, level - 1, ct.scale * self.scale / float(self.q[level - 1]))
         out = np.zeros((2, level, self.N), dtype=np.uint64)
         lib().orc_vecmat_dh(self._ctx, P(np.ascontiguousarray(ct.data)), P(digits), level, rows,
                             P(np.ascontiguousarray(diags_ext)), ptrs, P(lv), P(ge), P(out))
@@ -769,7 +795,7 @@ class OracleCKKS:
         return self.rescale(acc)
 
     def vecmat_dh(self, ct: Ct, diags_ext: np.ndarray, n: int, m: int, scale: float | None = None,
-                  period: int | None = None) -> Ct:
+                  period: int | None = None, merged: bool = False) -> Ct:
         """The same product with the ModDown taken once after the sum over rotations (double
         hoisting): replicate, ModUp(c1) once, then orc_vecmat_dh (steps 1-3 there), then rescale.
         diags_ext [n][level+1][N] at the ciphertext's level; `scale` is the diagonals' scale."""
@@ -785,10 +811,15 @@ class OracleCKKS:
         ptrs = (_u64p * max(1, len(keys)))(*[P(a) for a in key_arrs])
         lv = np.array([k.level for k in keys] or [0], dtype=np.uint32)
         ge = np.array([self.galois_elt(k) for k in range(1, n)] or [1], dtype=np.uint32)
+        d_scale = self.scale if scale is None else float(scale)
+        if merged:
+            out = np.zeros((2, level - 1, self.N), dtype=np.uint64)
+            lib().orc_vecmat_dh_rs(self._ctx, P(np.ascontiguousarray(ct.data)), P(digits), level, n,
+                                   P(np.ascontiguousarray(diags_ext)), ptrs, P(lv), P(ge), P(out))
+            return Ct(out, level - 1, ct.scale * d_scale / float(self.q[level - 1]))
         out = np.zeros((2, level, self.N), dtype=np.uint64)
         lib().orc_vecmat_dh(self._ctx, P(np.ascontiguousarray(ct.data)), P(digits), level, n,
                             P(np.ascontiguousarray(diags_ext)), ptrs, P(lv), P(ge), P(out))
-        d_scale = self.scale if scale is None else float(scale)
         return self.rescale(Ct(out, level, ct.scale * d_scale))
 
     @staticmethod
@@ -940,16 +971,16 @@ def cnn_encode(o: OracleCKKS, w: CNNWeights, windows=64, rect=False, conv_hoist=
 
 
 def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: dict | None = None,
-                double_hoist: bool = False) -> Ct:
+                double_hoist: bool = False, merged: bool = False) -> Ct:
     """The encrypted CNN schedule (§4): conv (im2col, one multiplication per kernel) -> pack the
     four channel outputs with masks -> square -> FC1 (vector x plain matrix) -> square -> FC2.
     Six multiplicative levels; biases are added as plaintexts at the ciphertext's scale and level.
     double_hoist: the two vector x matrix products take the ModDown once after their rotation sums."""
     def fc(v, diags, diags_ext, n, m, replicate=True, period=None):
         if enc.rect:
-            return (o.vecmat_rect(v, n, m, diags_ext=diags_ext, replicate=replicate, period=period) if double_hoist
-                    else o.vecmat_rect(v, n, m, diags=diags, replicate=replicate, period=period))
-        return (o.vecmat_dh(v, diags_ext, n, m, period=period) if double_hoist
+            return (o.vecmat_rect(v, n, m, diags_ext=diags_ext, replicate=replicate, period=period, merged=merged)
+                    if double_hoist else o.vecmat_rect(v, n, m, diags=diags, replicate=replicate, period=period))
+        return (o.vecmat_dh(v, diags_ext, n, m, period=period, merged=merged) if double_hoist
                 else o.vecmat(v, diags, n, m, period=period))
 
     W = enc.windows
@@ -961,7 +992,8 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
         # the result gathers blocks k + B g of z_k, the full tap sum of kernel k (reading A23)
         baby, giant = o.conv_bsgs_steps(enc.taps, W)
         if enc.conv_shared:
-            zs = [o.rescale(o.dh_sum(ct, baby, enc.conv_baby_ext[k])) for k in range(K)]
+            zs = [o.dh_sum(ct, baby, enc.conv_baby_ext[k], merged=True) if merged
+                  else o.rescale(o.dh_sum(ct, baby, enc.conv_baby_ext[k])) for k in range(K)]
         else:
             zs = [o.rotsum_dh(o.rescale(o.mul_plain(ct, enc.conv[k])), baby) for k in range(K)]
         v = None
@@ -993,7 +1025,7 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
         return o.encode(values, scale=v.scale, level=v.level)
 
     v = o.add_plain(v, bias_pt(0, bias, v))
-    v = o.square(v)
+    v = o.mul(v, v, merged=merged)
     n1, m1 = w.fc1_w.shape[1], w.fc1_w.shape[0]
     v = fc(v, enc.fc1, enc.fc1_ext, n1, m1, period=period)
     b1 = np.zeros(o.slots)
@@ -1003,7 +1035,7 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
     if trace is not None:
         trace["bias_scales"].append(v.scale)
     v = o.add_plain(v, bias_pt(1, b1, v))
-    v = o.square(v)
+    v = o.mul(v, v, merged=merged)
     n2, m2 = w.fc2_w.shape[1], w.fc2_w.shape[0]
     v = fc(v, enc.fc2, enc.fc2_ext, n2, m2, replicate=not enc.rect)
     b2 = np.zeros(o.slots)

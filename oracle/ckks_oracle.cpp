@@ -786,6 +786,78 @@ void orc_modup(const OrcCtx* c, const u64* x, u32 level, u64* digits) {
   }
 }
 
+// ModDown and rescale taken as one rounding (reading A25): for b = 0, 1, the extended-basis value
+// Z = P * A_b + U_b over q_0..q_{level-1} (U_b's P limb alone at P), divided by P q_{level-1} with
+// rounding: out_b[i] = (Z[i] - ([Z]_{P q} mod q_i)) * (P q)^-1 mod q_i, i < level - 1, with [Z]_{P q}
+// the balanced representative of Z modulo P q_{level-1}, composed from its residues modulo P and
+// q_{level-1} (Garner) in 128-bit integers. U [2][level+1][N], A [2][level][N] (NTT form), out
+// [2][level-1][N].
+static void moddown_rescale(const OrcCtx* c, const u64* U, const u64* A, u32 level, u64* out) {
+  const u64 n = c->n;
+  const u32 L = c->L, slots = level + 1, l = level - 1;
+  const u64 P = c->q[L], ql = c->q[l];
+  typedef unsigned __int128 u128;
+  const u128 pq = (u128)P * ql;
+  const u64 pinv_l = invm(P % ql, ql);
+  for (u32 b = 0; b < 2; ++b) {
+    std::vector<u64> z((u64)level * n);
+    for (u32 i = 0; i < level; ++i) {
+      const u64 q = c->q[i];
+      const u64 pm = P % q;
+      for (u64 e = 0; e < n; ++e)
+        z[(u64)i * n + e] = addm(mulm(pm, A[((u64)b * level + i) * n + e], q), U[((u64)b * slots + i) * n + e], q);
+    }
+    std::vector<u64> rp(U + ((u64)b * slots + level) * n, U + ((u64)b * slots + level + 1) * n);
+    std::vector<u64> rl(z.begin() + (u64)l * n, z.begin() + (u64)level * n);
+    intt_mod(c, rp.data(), L);
+    intt_mod(c, rl.data(), l);
+    // v = rp + P * ((rl - rp) P^-1 mod q_l) in [0, P q_l), then balanced
+    std::vector<u128> v(n);
+    std::vector<bool> neg(n);
+    for (u64 e = 0; e < n; ++e) {
+      const u64 t = mulm(subm(rl[e], rp[e] % ql, ql), pinv_l, ql);
+      const u128 x = (u128)rp[e] + (u128)P * t;
+      neg[e] = x > (pq - 1) / 2;
+      v[e] = neg[e] ? pq - x : x;  // magnitude
+    }
+    for (u32 i = 0; i < l; ++i) {
+      const u64 q = c->q[i];
+      std::vector<u64> t(n);
+      for (u64 e = 0; e < n; ++e) {
+        const u64 r = (u64)(v[e] % q);
+        t[e] = neg[e] ? negm(r, q) : r;
+      }
+      ntt_mod(c, t.data(), i);
+      const u64 inv = invm(mulm(P % q, ql % q, q), q);
+      u64* dst = out + ((u64)b * l + i) * n;
+      for (u64 e = 0; e < n; ++e) dst[e] = mulm(subm(z[(u64)i * n + e], t[e], q), inv, q);
+    }
+  }
+}
+
+// Inner products of (optionally automorphed) digits with a switching key over slots i < level and P:
+//   u_b[i] = sum_j tau_g(D_j)[i] * ksk_j[b][i].  u [2][level+1][N].
+static void ks_inner_all(const OrcCtx* c, const u64* digits, u32 level, const u64* ksk, u32 key_level, u32 g, u64* u) {
+  const u64 n = c->n;
+  const u32 L = c->L, slots = level + 1, K = key_level;
+  const std::vector<u32> src = automorphism_index(c, g);
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int b = 0; b < 2; ++b)
+    for (int ii = 0; ii < (int)slots; ++ii) {
+      const u32 i = (u32)ii;
+      const u32 mod_idx = (i < level) ? i : L;
+      const u32 key_slot = (i < level) ? i : K;
+      const u64 q = c->q[mod_idx];
+      u64* acc = u + ((u64)b * slots + i) * n;
+      for (u64 k = 0; k < n; ++k) acc[k] = 0;
+      for (u32 j = 0; j < level; ++j) {
+        const u64* dj = digits + ((u64)j * slots + i) * n;
+        const u64* kj = ksk + (((u64)j * 2 + (u64)b) * (K + 1) + key_slot) * n;
+        for (u64 k = 0; k < n; ++k) acc[k] = addm(acc[k], mulm(dj[src[k]], kj[k], q), q);
+      }
+    }
+}
+
 // Inner product of (optionally automorphed) digits with a switching key, then ModDown:
 //   u_b[i] = sum_j tau_g(D_j)[i] * ksk_j[b][i]  over slots i < level and P,
 //   out_b[i] = (u_b[i] - (bal_P(u_b[P]) mod q_i)) * P^-1 mod q_i.
@@ -845,6 +917,16 @@ void orc_relinearize(const OrcCtx* c, const u64* d, u32 level, const u64* rlk, u
   orc_add(c, d, ks.data(), level, 2, out);
 }
 
+// Relinearization and rescale as one rounding (reading A25): [3][level][N] -> [2][level-1][N],
+// round((P (d0, d1) + sum_j D_j(d2) * rlk_j) / (P q_{level-1})).
+void orc_relinearize_rescale(const OrcCtx* c, const u64* d, u32 level, const u64* rlk, u32 key_level, u64* out) {
+  const u64 n = c->n;
+  std::vector<u64> digits((u64)level * (level + 1) * n), u((u64)2 * (level + 1) * n);
+  orc_modup(c, d + (u64)2 * level * n, level, digits.data());
+  ks_inner_all(c, digits.data(), level, rlk, key_level, 1, u.data());
+  moddown_rescale(c, u.data(), d, level, out);
+}
+
 // Rotation (O18), key switch after the automorphism:
 //   (tau_g(c0) + KS(tau_g(c1))_0, KS(tau_g(c1))_1).
 void orc_rotate(const OrcCtx* c, const u64* ct, u32 level, u32 g, const u64* gk, u32 key_level, u64* out) {
@@ -881,8 +963,25 @@ void orc_rotate_from_digits(const OrcCtx* c, const u64* ct, const u64* digits, u
 //   2. A_0[i] = c0[i] d_0[i] + sum_{k>=1} tau_k(c0)[i] d_k[i],  A_1[i] = c1[i] d_0[i]   (i < level);
 //   3. out_b[i] = A_b[i] + (U_b[i] - (bal_P(U_b[P]) mod q_i)) * P^-1 mod q_i.
 // The caller rescales. out [2][level][N].
+static void vecmat_dh_impl(const OrcCtx* c, const u64* ct, const u64* digits, u32 level, u32 rows,
+                           const u64* diag_ext, const u64* const* keys, const u32* key_levels, const u32* g_elts,
+                           bool merged, u64* out);
+
 void orc_vecmat_dh(const OrcCtx* c, const u64* ct, const u64* digits, u32 level, u32 rows, const u64* diag_ext,
                    const u64* const* keys, const u32* key_levels, const u32* g_elts, u64* out) {
+  vecmat_dh_impl(c, ct, digits, level, rows, diag_ext, keys, key_levels, g_elts, false, out);
+}
+
+// The same sum with its ModDown and the following rescale taken as one rounding (reading A25):
+// out [2][level-1][N].
+void orc_vecmat_dh_rs(const OrcCtx* c, const u64* ct, const u64* digits, u32 level, u32 rows, const u64* diag_ext,
+                      const u64* const* keys, const u32* key_levels, const u32* g_elts, u64* out) {
+  vecmat_dh_impl(c, ct, digits, level, rows, diag_ext, keys, key_levels, g_elts, true, out);
+}
+
+static void vecmat_dh_impl(const OrcCtx* c, const u64* ct, const u64* digits, u32 level, u32 rows,
+                           const u64* diag_ext, const u64* const* keys, const u32* key_levels, const u32* g_elts,
+                           bool merged, u64* out) {
   const u64 n = c->n;
   const u32 L = c->L, slots = level + 1;
   const u64 P = c->q[L];
@@ -919,6 +1018,10 @@ void orc_vecmat_dh(const OrcCtx* c, const u64* ct, const u64* digits, u32 level,
     for (u32 i = 0; i < level; ++i)
       for (u64 e = 0; e < n; ++e)
         A[(u64)i * n + e] = addm(A[(u64)i * n + e], mulm(ct[(u64)i * n + src[e]], dk[(u64)i * n + e], c->q[i]), c->q[i]);
+  }
+  if (merged) {
+    moddown_rescale(c, U.data(), A.data(), level, out);
+    return;
   }
   // step 3
   for (u32 b = 0; b < 2; ++b) {

@@ -162,6 +162,25 @@ def test_tiny_tensor_relin_rescale(tiny):
         assert t.to_int(rs.data[p], idx[:-1]) == t.rescale(t.to_int(rel.data[p], idx), lvl)
 
 
+def test_tiny_merged_relin_rescale(tiny):
+    """A25: relinearization and rescale taken as one rounding equal round((P d + u) / (P q_last)) mod
+    Q_{level-1} in big integers, u the key-switch inner product over Q P before any division."""
+    o, t = tiny
+    lvl = 3
+    a, b = _rand_ct(o, lvl, 5), _rand_ct(o, lvl, 6)
+    d3, _, _ = o.tensor(a, b)
+    idx = list(range(lvl))
+    Q = math.prod(o.q[:lvl])
+    P, ql = t.P, o.q[lvl - 1]
+    d = [t.to_int(d3[p], idx) for p in range(3)]
+    u = t.keyswitch_u(d[2], lvl, o.rlk.data, o.rlk.level)
+    got = o.relinearize_rescale(d3, lvl, 1.0)
+    assert got.level == lvl - 1
+    for p in range(2):
+        ref = [t.round_div((P * x + y) % (Q * P), P * ql) % (Q // ql) for x, y in zip(d[p], u[p])]
+        assert t.to_int(got.data[p], idx[:-1]) == ref
+
+
 def test_tiny_rotation(tiny):
     """P5: rotation = coefficient automorphism, then key switch, in big integers."""
     o, t = tiny
@@ -548,4 +567,54 @@ def test_cnn_pack_first_schedule_matches_fp64(shared):
     v, _ = OracleCKKS.im2col(img, 7, 7, 3, o.slots)
     ct = o.encrypt_values(v, 77)
     logits = o.decrypt_values(oracle.cnn_forward(o, ct, w, enc, double_hoist=True), 10)
+    assert np.max(np.abs(logits - oracle.cnn_plain(img, w))) < 5e-3
+
+
+def _coeff_ints(o, data, level):
+    """Balanced integer coefficients of each component [2][level][N] (exact CRT)."""
+    Q = 1
+    for q in o.primes[:level]:
+        Q *= q
+    out = []
+    for b in range(2):
+        c = o.crt_compose(o.intt_limbs(np.ascontiguousarray(data[b]), level), level)
+        out.append(np.array([x - Q if x > Q // 2 else x for x in c], dtype=object))
+    return out
+
+
+@pytest.mark.parametrize("bits", [[36, 36, 36, 37], [31, 26, 26, 26, 31]])
+def test_merged_moddown_rescale_within_one_of_separate(bits):
+    """One rounding of (P d + U) / (P q_last) against ModDown then rescale, round((d + round(U/P)) / q):
+    the two differ by at most 1 in any integer coefficient, for relinearization and for a double-hoisted
+    sum, and decrypt alike."""
+    o = OracleCKKS(12, bits, 2.0 ** 30 if bits[1] == 36 else 2.0 ** 26).keygen()
+    o.gen_galois_keys([3, 700])
+    L = o.L
+    x, y = inputs.uniform_slots(o.slots, 41), inputs.uniform_slots(o.slots, 42)
+    a, b = o.encrypt_values(x, 1), o.encrypt_values(y, 2)
+    sep, mer = o.mul(a, b), o.mul(a, b, merged=True)
+    assert mer.level == sep.level == L - 1 and mer.scale == sep.scale
+    for u, v in zip(_coeff_ints(o, sep.data, L - 1), _coeff_ints(o, mer.data, L - 1)):
+        assert max(abs(int(t)) for t in (u - v)) <= 1
+    assert np.max(np.abs(o.decrypt_values(mer) - x * y)) < 1e-3
+    ds = np.stack([o.encode_ext(inputs.uniform_slots(o.slots, 50 + k), L) for k in range(3)])
+    sep = o.rescale(o.dh_sum(a, [3, 700], ds))
+    mer = o.dh_sum(a, [3, 700], ds, merged=True)
+    assert mer.level == sep.level and mer.scale == sep.scale
+    for u, v in zip(_coeff_ints(o, sep.data, L - 1), _coeff_ints(o, mer.data, L - 1)):
+        assert max(abs(int(t)) for t in (u - v)) <= 1
+
+
+def test_cnn_merged_rescale_schedule_matches_fp64():
+    """The bench's network (shared baby steps, packed channels, rectangular FC, double hoisting) with every
+    ModDown that precedes a rescale merged into it decrypts to the FP64 network."""
+    o = OracleCKKS(13, [31, 26, 26, 26, 26, 26, 26, 31], 2.0 ** 26).keygen()
+    for st, lv in oracle.cnn_galois_steps(o, rect=True, conv_hoist=True, conv_shared=True, pack_first=True).items():
+        o.gen_galois_key(st, lv)
+    w = oracle.CNNWeights(**inputs.cnn_weights(4))
+    enc = oracle.cnn_encode(o, w, rect=True, conv_hoist=True, conv_shared=True, pack_first=True)
+    img = inputs.mnist_like_image(3)
+    v, _ = OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+    ct = o.encrypt_values(v, 77)
+    logits = o.decrypt_values(oracle.cnn_forward(o, ct, w, enc, double_hoist=True, merged=True), 10)
     assert np.max(np.abs(logits - oracle.cnn_plain(img, w))) < 5e-3
