@@ -167,7 +167,8 @@ def source_digest(files) -> str:
 
 
 # ---------------------------------------------------------------------------------- GPU arm --
-def gpu_setup(torch, batch, double_hoist, rect=False, conv_hoist=False, conv_shared=False, conv_pack=False):
+def gpu_setup(torch, batch, double_hoist, rect=False, conv_hoist=False, conv_shared=False, conv_pack=False,
+              merged=False):
     import paper_2104_03152_gb300 as tk
     from paper_2104_03152_gb300 import inputs
 
@@ -176,7 +177,8 @@ def gpu_setup(torch, batch, double_hoist, rect=False, conv_hoist=False, conv_sha
     flags = (tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | (tk.TCKS_DOUBLE_HOIST if double_hoist else 0)
              | (tk.TCKS_RECT_DIAG if rect else 0) | (tk.TCKS_CONV_HOIST if conv_hoist else 0)
              | (tk.TCKS_CONV_SHARED if conv_hoist and conv_shared else 0)
-             | (tk.TCKS_CONV_PACK if conv_hoist and conv_pack else 0))
+             | (tk.TCKS_CONV_PACK if conv_hoist and conv_pack else 0)
+             | (tk.TCKS_MERGED_RESCALE if merged else 0))
     ctx = tk.Context(tk.Params(LOG_N, BITS, SCALE), seed=inputs.SEED_KEYS, flags=flags, stream=stream.cuda_stream)
     w = inputs.cnn_weights(SEED_W)
     model = tk.CNN(ctx, w["conv_w"], w["conv_b"], w["fc1_w"], w["fc1_b"], w["fc2_w"], w["fc2_b"], windows=64)
@@ -207,7 +209,8 @@ def run_gpu(args, world, rank, local):
     B = args.batch
     rect = args.fc_form == "rect"
     tk, ctx, model, cts, stream, imgs, w = gpu_setup(torch, B, args.double_hoist, rect, bool(args.conv_hoist),
-                                                     bool(args.conv_shared), bool(args.conv_pack))
+                                                     bool(args.conv_shared), bool(args.conv_pack),
+                                                     bool(args.merged_rescale))
     # correctness guard: the decrypted logits of every request must match the FP64 network, and the
     # batched outputs must equal the single-request path bit for bit
     outs = model.forward_batch(cts)
@@ -282,10 +285,15 @@ def run_gpu(args, world, rank, local):
         single[label] = {"value": B * 3 / (tot / 1e3), "unit": "inferences/s", "ms_per_step": tot / 3}
     form = "rectangular" if rect else "square"
     conv = CONV_LABEL[conv_form(args)]
+    run_flags = ctx.flags
+    if args.merged_rescale:  # the same network with the ModDown and the rescale as two roundings
+        ctx.set_flags(run_flags & ~tk.TCKS_MERGED_RESCALE)
+        time_model(model, f"{form} FC layers, {conv}, ModDown and rescale as two roundings")
+        ctx.set_flags(run_flags)
     if args.double_hoist:
         ctx.set_flags(base)
         time_model(model, f"{form} FC layers, {conv}, one ModDown per FC rotation")
-        ctx.set_flags(base | dh_flag)
+        ctx.set_flags(run_flags)
 
     def other(flags, label):  # another network layout on the same context
         ctx.set_flags(base | dh_flag | flags)
@@ -746,16 +754,17 @@ def oracle_setup(rect: bool = True, conv_hoist: bool = True, conv_shared: bool =
 
 
 def time_oracle(n_steps: int, warmup: int, double_hoist: bool = True, single_thread_steps: int = 0,
-                rect: bool = True, conv_hoist: bool = True, conv_shared: bool = True, conv_pack: bool = True):
+                rect: bool = True, conv_hoist: bool = True, conv_shared: bool = True, conv_pack: bool = True,
+                merged: bool = True):
     """Oracle CNN inferences on the host cores (same schedule as the GPU arm); optionally also
     single-threaded ones. Returns (times, cores, single-thread times)."""
     oracle, o, w, enc, ct = oracle_setup(rect, conv_hoist, conv_shared, conv_pack)
     for _ in range(warmup):
-        oracle.cnn_forward(o, ct, w, enc, double_hoist=double_hoist)
+        oracle.cnn_forward(o, ct, w, enc, double_hoist=double_hoist, merged=merged)
     times = []
     for _ in range(n_steps):
         t0 = time.perf_counter()
-        oracle.cnn_forward(o, ct, w, enc, double_hoist=double_hoist)
+        oracle.cnn_forward(o, ct, w, enc, double_hoist=double_hoist, merged=merged)
         times.append(time.perf_counter() - t0)
     cores = oracle.lib().orc_max_threads()
     single = []
@@ -763,7 +772,7 @@ def time_oracle(n_steps: int, warmup: int, double_hoist: bool = True, single_thr
         oracle.lib().orc_set_threads(1)
         for _ in range(single_thread_steps):
             t0 = time.perf_counter()
-            oracle.cnn_forward(o, ct, w, enc, double_hoist=double_hoist)
+            oracle.cnn_forward(o, ct, w, enc, double_hoist=double_hoist, merged=merged)
             single.append(time.perf_counter() - t0)
         oracle.lib().orc_set_threads(cores)
     return times, cores, single
@@ -775,7 +784,8 @@ def run_reference(args, world, rank):
     steps, warmup = args.steps, args.warmup
     # bound the run: at most ~3 minutes of oracle inferences
     times, cores, _ = time_oracle(steps, warmup, bool(args.double_hoist), 0, args.fc_form == "rect",
-                                  bool(args.conv_hoist), bool(args.conv_shared), bool(args.conv_pack))
+                                  bool(args.conv_hoist), bool(args.conv_shared), bool(args.conv_pack),
+                                  bool(args.merged_rescale))
     total = sum(times)
     value = steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": args.gpus,
@@ -823,6 +833,8 @@ def main():
                     help="with --conv-hoist 1: the baby steps over the input's rotations, shared by the kernels")
     ap.add_argument("--conv-pack", type=int, default=1,
                     help="with --conv-shared 1: pack the channels before one giant-step sum per request")
+    ap.add_argument("--merged-rescale", type=int, default=1,
+                    help="take every ModDown that precedes a rescale and the rescale as one rounding")
     ap.add_argument("--double-hoist", type=int, default=1,
                     help="vector x matrix products take the ModDown once after the rotation sum (1) or per rotation (0)")
     ap.add_argument("--c4", type=int, default=1, help="time the 4096x256 vector x matrix workload (64 vectors)")
@@ -862,7 +874,7 @@ def main():
     mac_kernel = name == "vecmat_dh_acc"
     alu_peak = (r["mac_peak"] if mac_kernel else r["bfly_peak"]) / 1e9
     traffic = ncu_traffic(name, {"batch": B, "fc_form": args.fc_form, "conv_hoist": args.conv_hoist,
-                                 "conv_form": conv_form(args),
+                                 "conv_form": conv_form(args), "merged_rescale": args.merged_rescale,
                                  "double_hoist": args.double_hoist})
     hbm = {"achieved": hbm_ach, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_ach / peaks["hbm_gbs"],
            "peak_source": peaks["source"]}
@@ -885,7 +897,8 @@ def main():
     # CPU baseline: the oracle on the host cores, bounded sample
     if args.cpu_sample > 0:
         times, cores, single = time_oracle(args.cpu_sample, 0, bool(args.double_hoist), 1, args.fc_form == "rect",
-                                           bool(args.conv_hoist), bool(args.conv_shared), bool(args.conv_pack))
+                                           bool(args.conv_hoist), bool(args.conv_shared), bool(args.conv_pack),
+                                           bool(args.merged_rescale))
         cpu_val = len(times) / sum(times)
     else:
         times, cores, cpu_val, single = [], 0, None, []

@@ -126,8 +126,16 @@ enum {
   TCKS_RECT_DIAG = 8u,
   TCKS_CONV_HOIST = 16u,
   TCKS_CONV_SHARED = 32u,
-  TCKS_CONV_PACK = 64u
+  TCKS_CONV_PACK = 64u,
+  TCKS_MERGED_RESCALE = 128u
 };
+/* TCKS_MERGED_RESCALE: wherever a key switch's ModDown is followed by a rescale (enc x enc multiply
+ * with AUTO_RESCALE, the double-hoisted vector x matrix products, the CNN's squares, products and
+ * shared convolution sums) the two divisions, by P and by q_last, are one rounding:
+ * round((P d + u) / (P q_last)) with the balanced residue modulo P q_last composed from the two
+ * dropped limbs. About half the transforms of the ModDown + rescale pair; the limbs equal the two
+ * separate roundings' except where those land within 1/q_last of a rounding boundary (a difference of
+ * 1 in that integer coefficient). */
 tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32_t flags,
                                 const tcks_allocator* allocator, void* cuda_stream, tcks_ctx** out);
 void tcks_ctx_free(tcks_ctx* ctx);

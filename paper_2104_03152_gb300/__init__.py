@@ -22,6 +22,7 @@ TCKS_RECT_DIAG = 8
 TCKS_CONV_HOIST = 16
 TCKS_CONV_SHARED = 32
 TCKS_CONV_PACK = 64
+TCKS_MERGED_RESCALE = 128
 TCKS_CTA_ADD, TCKS_CTA_SUB, TCKS_CTA_MUL = 0, 1, 2  # ciphertext-array operations
 KEY_SECRET, KEY_PUBLIC, KEY_RELIN, KEY_GALOIS = 0, 1, 2, 3
 
@@ -334,6 +335,7 @@ class Context:
             self._alloc_keep = (a, keep)
             aptr = ctypes.cast(ctypes.pointer(a), _vp)
         h = _vp()
+        self.flags = flags
         check(lib().tcks_context_create(params.h, seed, flags, aptr, _vp(stream) if stream else None,
                                         ctypes.byref(h)))
         self.h = h
@@ -491,6 +493,7 @@ class Context:
 
     def set_flags(self, flags: int):
         check(lib().tcks_ctx_set_flags(self.h, flags))
+        self.flags = flags
 
 
 def im2col_encode(img: np.ndarray, kh: int, kw: int, stride: int, cap: int):

@@ -160,6 +160,31 @@ void op_relinearize(tcks_ctx* c, const u64* d3, u32 ell, u64* out, u32 count) {
   check_launch("relinearize");
 }
 
+void op_relin_rescale(tcks_ctx* c, const u64* d3, u32 ell, u64* out, u32 count) {
+  if (ell < 2) fail(TCKS_ERR_LEVEL_EXHAUSTED, "rescale needs level >= 2");
+  const size_t n = c->N;
+  const KeyTable& kt = key_table(c, {0u}, ell);
+  DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
+  DevBuf top(c, (size_t)count * 2 * n), top2(c, (size_t)count * 2 * n);
+  const u64 d3_stride = (u64)3 * ell * n;
+  launch_modup(c->T, d3 + (size_t)2 * ell * n, d3_stride, count, ell, coef.p, digits.p, c->stream);
+  KsPlan p{};
+  p.keys = kt.d;
+  p.digits = digits.p;
+  p.digits_b = (u64)ell * (ell + 1) * n;
+  p.top = top.p;
+  p.out = out;
+  p.out_b = (u64)2 * (ell - 1) * n;
+  p.add0 = d3;
+  p.add0_b = d3_stride;
+  p.add1 = d3 + (size_t)ell * n;
+  p.add1_b = d3_stride;
+  p.R = 1;
+  p.B = count;
+  launch_relin_rescale(c->T, c->host, ell, p, top2.p, c->stream);
+  check_launch("relinearize + rescale");
+}
+
 void op_rotate_add(tcks_ctx* c, u64* base, u64 stride, u32 count, u32 ell, int32_t step) {
   const size_t n = c->N;
   const u32 k = step_mod(c, step);
@@ -508,7 +533,7 @@ tcks_status tcks_ctx_set_flags(tcks_ctx* c, uint32_t flags) {
   TCKS_API_BEGIN
   if (!c) fail(TCKS_ERR_INVALID_ARG, "null context");
   if (flags & ~(u32)(TCKS_AUTO_RELIN | TCKS_AUTO_RESCALE | TCKS_DOUBLE_HOIST | TCKS_RECT_DIAG | TCKS_CONV_HOIST |
-                     TCKS_CONV_SHARED | TCKS_CONV_PACK))
+                     TCKS_CONV_SHARED | TCKS_CONV_PACK | TCKS_MERGED_RESCALE))
     fail(TCKS_ERR_INVALID_ARG, "unknown flag");
   c->flags = flags;
   TCKS_API_END
@@ -989,6 +1014,10 @@ tcks_status tcks_mul(const tcks_ct* a, const tcks_ct* b, tcks_ct** out) {
   if (!rescale) {
     tcks_ct* r = new_ct(c, ell, sc);
     op_relinearize(c, d3.p, ell, r->d);
+    *out = r;
+  } else if (c->flags & TCKS_MERGED_RESCALE) {
+    tcks_ct* r = new_ct(c, ell - 1, sc / (double)c->host.chain[ell - 1]);
+    op_relin_rescale(c, d3.p, ell, r->d);
     *out = r;
   } else {
     DevBuf rel(c, ct_words(c, ell));

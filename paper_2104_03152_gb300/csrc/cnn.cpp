@@ -116,8 +116,13 @@ u32 cnn_stage_level(const tcks_cnn* m, u32 stage) {  // input level of a stage (
 
 static void square_stage(tcks_ctx* c, const u64* in, u32 ell, u32 count, u64* out) {
   const size_t n = c->N;
-  DevBuf d3(c, (size_t)count * 3 * ell * n), rel(c, (size_t)count * ct_words(c, ell));
+  DevBuf d3(c, (size_t)count * 3 * ell * n);
   launch_tensor(c->T, in, in, d3.p, ell, count, c->stream);
+  if (c->flags & TCKS_MERGED_RESCALE) {
+    op_relin_rescale(c, d3.p, ell, out, count);
+    return;
+  }
+  DevBuf rel(c, (size_t)count * ct_words(c, ell));
   op_relinearize(c, d3.p, ell, rel.p, count);
   op_rescale(c, rel.p, ell, out, count);
 }
@@ -132,11 +137,16 @@ void cnn_stage(const tcks_cnn* m, u32 stage, const u64* x, u32 count, u64* out) 
       DevBuf chans(c, (size_t)K * count * w1);
       if (m->conv_shared) {
         const u32 nb = (u32)m->baby.size() + 1;
-        DevBuf z(c, (size_t)K * count * w_in);  // [kernel][request][2][L][N] before the rescale
         const u64 dstride = (u64)(L + 1) * c->N;
-        op_dh_sum_multi(c, x, w_in, count, L, m->baby, m->baby_ext, dstride, dstride * nb, L, K, z.p, w_in,
-                        (u64)count * w_in);
-        op_rescale(c, z.p, L, chans.p, K * count);
+        if (c->flags & TCKS_MERGED_RESCALE) {  // ModDown and rescale in one rounding, straight into chans
+          op_dh_sum_multi(c, x, w_in, count, L, m->baby, m->baby_ext, dstride, dstride * nb, L, K, chans.p, w1,
+                          (u64)count * w1, true);
+        } else {
+          DevBuf z(c, (size_t)K * count * w_in);  // [kernel][request][2][L][N] before the rescale
+          op_dh_sum_multi(c, x, w_in, count, L, m->baby, m->baby_ext, dstride, dstride * nb, L, K, z.p, w_in,
+                          (u64)count * w_in);
+          op_rescale(c, z.p, L, chans.p, K * count);
+        }
         if (!m->pack_first) op_rotsum_hoisted(c, chans.p, w1, K * count, L - 1, m->giant, chans.p);
       } else {
         {

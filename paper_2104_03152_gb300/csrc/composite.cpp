@@ -60,13 +60,19 @@ static void op_vecmat_dh(tcks_ctx* c, u64* ct, u64 cw, u32 count, u32 ell, const
   p.chunks = chunks;
   launch_vecmat_dh_acc(c->T, ell, p, c->stream);
   launch_vecmat_dh_fold(c->T, ell, p, c->stream);
-  DevBuf top(c, (size_t)2 * count * n), acc(c, (size_t)count * cw);
+  DevBuf top(c, (size_t)2 * count * n);
   const u64 per_rq = (u64)chunks * 3 * (ell + 1) * n;
   for (u32 b = 0; b < 2; ++b)
     launch_ntt(c->T, true, partial.p + ((u64)b * (ell + 1) + ell) * n, per_rq, top.p + (u64)b * count * n, n, count,
                c->L, 1, c->stream);
-  launch_vecmat_dh_moddown(c->T, ell, p, top.p, acc.p, cw, c->stream);
-  op_rescale(c, acc.p, ell, out, count);
+  if (c->flags & TCKS_MERGED_RESCALE) {  // ModDown and rescale in one rounding
+    DevBuf top2(c, (size_t)2 * count * n);
+    launch_vecmat_dh_moddown_rs(c->T, c->host, ell, p, top.p, top2.p, out, ct_words(c, ell - 1), c->stream);
+  } else {
+    DevBuf acc(c, (size_t)count * cw);
+    launch_vecmat_dh_moddown(c->T, ell, p, top.p, acc.p, cw, c->stream);
+    op_rescale(c, acc.p, ell, out, count);
+  }
   check_launch("vecmat (double hoisted)");
 }
 
@@ -125,7 +131,7 @@ void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const st
 
 void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, const std::vector<int32_t>& steps,
                      const u64* diags, u64 diag_stride, u64 set_stride, u32 p_limb, u32 outs, u64* out, u64 out_b,
-                     u64 out_o) {
+                     u64 out_o, bool merged) {
   const size_t n = c->N;
   std::vector<u32> ks;
   for (int32_t st : steps) {
@@ -166,7 +172,12 @@ void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, cons
   for (u32 b = 0; b < 2; ++b)
     launch_ntt(c->T, true, partial.p + ((u64)b * (ell + 1) + ell) * n, per_ro, top.p + (u64)b * ro * n, n, ro, c->L, 1,
                c->stream);
-  launch_vecmat_dh_moddown(c->T, ell, p, top.p, out, out_b, c->stream, outs > 1 ? out_o : 0);
+  if (merged) {
+    DevBuf top2(c, (size_t)2 * ro * n);
+    launch_vecmat_dh_moddown_rs(c->T, c->host, ell, p, top.p, top2.p, out, out_b, c->stream, outs > 1 ? out_o : 0);
+  } else {
+    launch_vecmat_dh_moddown(c->T, ell, p, top.p, out, out_b, c->stream, outs > 1 ? out_o : 0);
+  }
   check_launch("double-hoisted sum");
 }
 

@@ -173,6 +173,8 @@ void free_ct(tcks_ct* ct);
 void op_rescale(tcks_ctx* c, const u64* in, u32 ell, u64* out, u32 count = 1);
 // Relinearize `count` tensor products [count][3][ell][N] -> [count][2][ell][N].
 void op_relinearize(tcks_ctx* c, const u64* d3, u32 ell, u64* out, u32 count = 1);
+// The same followed by the rescale, both in one rounding -> [count][2][ell-1][N].
+void op_relin_rescale(tcks_ctx* c, const u64* d3, u32 ell, u64* out, u32 count = 1);
 // Rotations of one ciphertext from shared digits: outs[i] = rot(ct, steps[i]) (each [2][ell][N]).
 void op_rotate_hoisted(tcks_ctx* c, const u64* ct, u32 ell, const int32_t* steps, u32 n, u64* const* outs);
 // ct_i <- ct_i + rot(ct_i, step) for count ciphertexts at base + i * stride (words).
@@ -196,8 +198,9 @@ void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const st
 // (1 or 4) diagonal sets over the extended basis: set o at diags + o * set_stride, diagonal k at
 // + k * diag_stride, its P limb at p_limb. One ModUp per ciphertext, one ModDown per output; output o
 // of ciphertext r at out + r * out_b + o * out_o ([2][ell][N]); scale x's times the diagonals'.
+// merged: the ModDown and a rescale by q_{ell-1} in one rounding, outputs [2][ell-1][N].
 void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, const std::vector<int32_t>& steps,
                      const u64* diags, u64 diag_stride, u64 set_stride, u32 p_limb, u32 outs, u64* out, u64 out_b,
-                     u64 out_o);
+                     u64 out_o, bool merged = false);
 
 }  // namespace tcks

@@ -60,6 +60,37 @@ __device__ __forceinline__ u64 lift_balanced(u64 x, u64 half_src, u64 qsrc_mod_t
   return x > half_src ? sub_mod(r, qsrc_mod_t, t.q) : r;
 }
 
+// The balanced integer x, |x| < P q_l / 2, with x = rp (mod P) and x = rl (mod q_l), reduced modulo
+// the target prime t: Garner's x = rp + P ((rl - rp) P^-1 mod q_l), then P q_l subtracted above the
+// half. With every prime below 2^31 (NARROW) P q_l < 2^62 and x fits one 64-bit word (three 64-bit
+// Barrett reductions); otherwise 128-bit words.
+template <bool NARROW>
+__device__ __forceinline__ u64 crt2_lift(u64 rp, u64 rl, const Crt2& k, const ModConst& ml, const ModConst& t) {
+  if constexpr (NARROW) {
+    const u64 a = reduce64(rp, ml);
+    const u64 d = rl >= a ? rl - a : rl + k.ql - a;
+    const u64 u = reduce64(d * k.pinv_l, ml);
+    const u64 x = rp + k.P * u;
+    const bool neg = x > k.half_lo;
+    const u64 r = reduce64(neg ? k.pq_lo - x : x, t);
+    return neg ? (r ? t.q - r : 0) : r;
+  }
+  const u64 a = reduce64(rp, ml);
+  const u64 d = rl >= a ? rl - a : rl + k.ql - a;
+  const u64 u = mul_mod(d, k.pinv_l, ml);
+  u64 lo = k.P * u, hi = __umul64hi(k.P, u);
+  lo += rp;
+  hi += lo < rp;
+  const bool neg = hi > k.half_hi || (hi == k.half_hi && lo > k.half_lo);
+  if (neg) {  // magnitude P q_l - x
+    const u64 nlo = k.pq_lo - lo;
+    hi = k.pq_hi - hi - (k.pq_lo < lo);
+    lo = nlo;
+  }
+  const u64 r = reduce128(hi, lo, t);
+  return neg ? (r ? t.q - r : 0) : r;
+}
+
 // Bit reverse of the low `bits` bits.
 __device__ __forceinline__ u32 brv(u32 x, u32 bits) { return __brev(x) >> (32 - bits); }
 

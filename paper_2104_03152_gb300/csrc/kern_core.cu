@@ -614,6 +614,110 @@ __global__ void k_ks_moddown(DevTables T, u32 ell, const __grid_constant__ KsPla
   });
 }
 
+// Relinearization with its ModDown and the following rescale as one rounding (R = 1, no automorphism).
+// Stage 1: per (request, component b) the coefficient forms of the two limbs the rounding drops:
+// which = 0: u_b[P]; which = 1: u_b[l] + P add_b[l], l = ell - 1. Limb job = ((b B + rq) 2 + which);
+// top [B][2][N] and top2 [B][2][N].
+template <typename W, int LC>
+__global__ void k_ks_top_rs(DevTables T, u32 ell, const __grid_constant__ KsPlan plan, u64* top2) {
+  TCKS_SMEM(W);
+  const Slice sl = slice_of<LC>(T);
+  const u64 n = 1ull << T.log_n;
+  const u32 which = sl.job & 1u, br = sl.job >> 1, b = br / plan.B, rq = br % plan.B;
+  const u32 l = ell - 1;
+  const u32 slot = which ? l : ell, mod = which ? l : T.L;
+  const KsKey kk = plan.keys[0];
+  const W* digits = reinterpret_cast<const W*>(plan.digits) + rq * plan.digits_b;
+  const ModConst m = T.mods[mod];
+  const u64 pm = which ? T.pairs[(u64)T.L * T.n_mods + l].qa_mod_b : 0;  // P mod q_l
+  const u64* add = b == 0 ? plan.add0 + rq * plan.add0_b : plan.add1 + rq * plan.add1_b;
+  ell_dispatch(ell, [&](auto E) {
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
+      const u32 g = sl.off + k;
+      u64 v = ks_inner<W, decltype(E)::value>(digits, ell, slot, kk.key, kk.K, which ? l : kk.K, b, g, g, n, m);
+      if (which) v = add_mod(v, Ew<W>::mul(pm, add[(u64)l * n + g], m), m.q);
+      s[sw(k)] = (W)v;
+    }
+  });
+  __syncthreads();
+  ntt_inv_slice<W, LC>(s, T, mod, sl.rank);
+  u64* dst = (which ? top2 : plan.top) + ((u64)rq * 2 + b) * n + sl.off;
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) dst[k] = Ar<W>::inv_out(s[sw(k)], m);
+}
+
+// Stage 2: out_b[i] = (u_b[i] + P add_b[i] - NTT_i([Z]_{P q_l} mod q_i)) (P q_l)^-1, i < ell - 1.
+// Limb job = (b (ell - 1) + i) B + rq; out + rq out_b receives [2][ell-1][N].
+template <typename W, int LC>
+__global__ void k_ks_moddown_rs(DevTables T, u32 ell, const __grid_constant__ KsPlan plan, const u64* top2, Crt2 k2) {
+  TCKS_SMEM(W);
+  const Slice sl = slice_of<LC>(T);
+  const u32 log_n = T.log_n;
+  const u64 n = 1ull << log_n;
+  const u32 lo = ell - 1;
+  const u32 rq = sl.job % plan.B, bi = sl.job / plan.B, b = bi / lo, i = bi % lo;
+  const KsKey kk = plan.keys[0];
+  const W* digits = reinterpret_cast<const W*>(plan.digits) + rq * plan.digits_b;
+  const ModConst mi = T.mods[i], mp = T.mods[T.L], ml = T.mods[lo];
+  const PairConst pp = T.pairs[(u64)T.L * T.n_mods + i];  // P mod q_i, P^-1 mod q_i
+  const PairConst pl = T.pairs[(u64)lo * T.n_mods + i];   // q_l^-1 mod q_i
+  (void)mp;
+  const u64* tp = plan.top + ((u64)rq * 2 + b) * n + sl.off;
+  const u64* tl = top2 + ((u64)rq * 2 + b) * n + sl.off;
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)crt2_lift<sizeof(W) == 4>(tp[k], tl[k], k2, ml, mi);
+  __syncthreads();
+  ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
+  const u64* add = b == 0 ? plan.add0 + rq * plan.add0_b : plan.add1 + rq * plan.add1_b;
+  u64* dst = plan.out + rq * plan.out_b + ((u64)b * lo + i) * n;
+  ell_dispatch(ell, [&](auto E) {
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
+      const u32 g = sl.off + k;
+      const u64 u = ks_inner<W, decltype(E)::value>(digits, ell, i, kk.key, kk.K, i, b, g, g, n, mi);
+      const u64 z = add_mod(u, Ew<W>::mul(pp.qa_mod_b, add[(u64)i * n + g], mi), mi.q);
+      const u64 v = sub_mod(z, Ar<W>::fwd_out(s[sw(k)], mi), mi.q);
+      dst[g] = Ew<W>::shoup_inv(Ew<W>::shoup_inv(v, pp, mi), pl, mi);
+    }
+  });
+}
+
+static decltype(&k_ks_top_rs<u64, 0>) const K6_k_ks_top_rs[6] = TCKS_K6(k_ks_top_rs);
+static decltype(&k_ks_moddown_rs<u64, 0>) const K6_k_ks_moddown_rs[6] = TCKS_K6(k_ks_moddown_rs);
+
+Crt2 crt2_constants(const HostTables& H, u32 L, u32 l) {
+  using u128 = unsigned __int128;
+  Crt2 k{};
+  k.P = H.chain[L];
+  k.ql = H.chain[l];
+  k.l = l;
+  // P^-1 mod q_l by Fermat
+  u64 base = k.P % k.ql, e = k.ql - 2, r = 1;
+  while (e) {
+    if (e & 1) r = (u64)((u128)r * base % k.ql);
+    base = (u64)((u128)base * base % k.ql);
+    e >>= 1;
+  }
+  k.pinv_l = r;
+  const u128 pq = (u128)k.P * k.ql, half = (pq - 1) / 2;
+  k.pq_lo = (u64)pq;
+  k.pq_hi = (u64)(pq >> 64);
+  k.half_lo = (u64)half;
+  k.half_hi = (u64)(half >> 64);
+  return k;
+}
+
+void launch_relin_rescale(const DevTables& T, const HostTables& H, u32 ell, const KsPlan& plan, u64* top2,
+                          cudaStream_t st) {
+  const u64 n = 1ull << T.log_n;
+  {
+    Launch L(K_KS_P, st, 8.0 * n * (plan.B * 2.0 * (ell + 2.0)), 4.0 * plan.B * ((double)ell * n + bfly_per_limb(T.log_n)));
+    launch_limb(K6_k_ks_top_rs, T.narrow, 4 * plan.B, 1, T.log_n, st, T.limb_threads, T, ell, plan, top2);
+  }
+  const Crt2 k2 = crt2_constants(H, T.L, ell - 1);
+  Launch L(K_KS_MODDOWN, st, 8.0 * n * plan.B * (ell * ell + 2.0 * ell + 4.0 * (ell - 1.0)),
+           2.0 * (ell - 1.0) * plan.B * ((ell + 2.0) * n + bfly_per_limb(T.log_n)));
+  launch_limb(K6_k_ks_moddown_rs, T.narrow, 2 * (ell - 1) * plan.B, 1, T.log_n, st, T.limb_threads, T, ell, plan,
+              (const u64*)top2, k2);
+}
+
 // Algorithmic bytes of a plan: distinct digit sets and keys once, scratch and outputs once.
 static void ks_plan_bytes(const KsPlan& p, u32 ell, u32 log_n, bool narrow, double* inner, double* moddown) {
   const double n = (double)(1u << log_n);
@@ -663,7 +767,8 @@ u32 limb_threads_cap_core(bool narrow, u32 log_c) {
   u32 cap = 1024;
   for (u32 t : {max_threads_of(kNttFwd[i]), max_threads_of(kNttInv[i]), max_threads_of(kNttDescFwd[i]),
                 max_threads_of(kNttDescInv[i]), max_threads_of(K6_k_drop_combine[i]), max_threads_of(K6_k_modup[i]),
-                max_threads_of(K6_k_ks_inner_p[i]), max_threads_of(K6_k_ks_moddown[i])})
+                max_threads_of(K6_k_ks_inner_p[i]), max_threads_of(K6_k_ks_moddown[i]),
+                max_threads_of(K6_k_ks_top_rs[i]), max_threads_of(K6_k_ks_moddown_rs[i])})
     cap = t < cap ? t : cap;
   return cap;
 }

@@ -223,6 +223,75 @@ __global__ void k_vecmat_dh_moddown(DevTables T, u32 ell, const __grid_constant_
 
 static decltype(&k_vecmat_dh_moddown<u64, 0>) const K6_k_vecmat_dh_moddown[6] = TCKS_K6(k_vecmat_dh_moddown);
 
+// The ModDown and the following rescale by q_l (l = ell - 1) as one rounding. Z_b = P (A_b + c_b d_0) +
+// U_b over the data limbs (A_b only for b = 0), Z_b[P] = U_b[P].
+// Stage 1: the coefficient form of Z_b[l], limb job = b * B * outs + request * outs + output; top2
+// [2][B * outs][N].
+template <typename W, int LC>
+__global__ void k_dh_top_l(DevTables T, u32 ell, const __grid_constant__ VecmatDhPlan p, u64* top2) {
+  TCKS_SMEM(W);
+  const Slice sl = slice_of<LC>(T);
+  const u32 log_n = T.log_n;
+  const u64 n = 1ull << log_n;
+  const u32 outs = dh_outs(p), bo = p.B * outs;
+  const u32 ro = sl.job % bo, b = sl.job / bo, rq = ro / outs, o = ro % outs;
+  const u32 l = ell - 1;
+  const ModConst m = T.mods[l];
+  const u64 pm = T.pairs[(u64)T.L * T.n_mods + l].qa_mod_b;
+  const u64* U = p.partial + dh_off(ro, 0, p.chunks, b, l, ell, log_n);
+  const u64* A = p.partial + dh_off(ro, 0, p.chunks, 2, l, ell, log_n);
+  const u64* cb = p.ct + rq * p.ct_b + ((u64)b * ell + l) * n;
+  const u64* d0 = p.diag ? p.diag + (u64)o * p.diag_set + (u64)l * n : nullptr;
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
+    const u32 g = sl.off + k;
+    u64 a = d0 ? Ew<W>::mul(cb[g], d0[g], m) : cb[g];
+    if (b == 0) a = add_mod(a, A[g], m.q);
+    s[sw(k)] = (W)add_mod(U[g], Ew<W>::mul(pm, a, m), m.q);
+  }
+  __syncthreads();
+  ntt_inv_slice<W, LC>(s, T, l, sl.rank);
+  u64* dst = top2 + ((u64)b * bo + ro) * n + sl.off;
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) dst[k] = Ar<W>::inv_out(s[sw(k)], m);
+}
+
+// Stage 2: out_b[i] = (Z_b[i] - NTT_i([Z_b]_{P q_l} mod q_i)) (P q_l)^-1, i < ell - 1; limb job =
+// (b (ell - 1) + i) * B * outs + request * outs + output; top [2][B * outs][N] holds INTT_P(U_b[P]).
+template <typename W, int LC>
+__global__ void k_vecmat_dh_moddown_rs(DevTables T, u32 ell, const __grid_constant__ VecmatDhPlan p, const u64* top,
+                                       const u64* top2, Crt2 k2, u64* out, u64 out_b, u64 out_o) {
+  TCKS_SMEM(W);
+  const Slice sl = slice_of<LC>(T);
+  const u32 log_n = T.log_n;
+  const u64 n = 1ull << log_n;
+  const u32 outs = dh_outs(p), bo = p.B * outs, lo = ell - 1;
+  const u32 ro = sl.job % bo, bi = sl.job / bo, b = bi / lo, i = bi % lo;
+  const u32 rq = ro / outs, o = ro % outs;
+  const ModConst mi = T.mods[i], ml = T.mods[lo];
+  const PairConst pp = T.pairs[(u64)T.L * T.n_mods + i];  // P mod q_i, P^-1 mod q_i
+  const PairConst pl = T.pairs[(u64)lo * T.n_mods + i];   // q_l^-1 mod q_i
+  const u64* tp = top + ((u64)b * bo + ro) * n + sl.off;
+  const u64* tl = top2 + ((u64)b * bo + ro) * n + sl.off;
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)crt2_lift<sizeof(W) == 4>(tp[k], tl[k], k2, ml, mi);
+  __syncthreads();
+  ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
+  const u64* U = p.partial + dh_off(ro, 0, p.chunks, b, i, ell, log_n);
+  const u64* A = p.partial + dh_off(ro, 0, p.chunks, 2, i, ell, log_n);
+  const u64* cb = p.ct + rq * p.ct_b + ((u64)b * ell + i) * n;
+  const u64* d0 = p.diag ? p.diag + (u64)o * p.diag_set + (u64)i * n : nullptr;
+  u64* dst = out + (out_o ? rq * out_b + o * out_o : ro * out_b) + ((u64)b * lo + i) * n;
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
+    const u32 g = sl.off + k;
+    u64 a = d0 ? Ew<W>::mul(cb[g], d0[g], mi) : cb[g];
+    if (b == 0) a = add_mod(a, A[g], mi.q);
+    const u64 z = add_mod(U[g], Ew<W>::mul(pp.qa_mod_b, a, mi), mi.q);
+    const u64 v = sub_mod(z, Ar<W>::fwd_out(s[sw(k)], mi), mi.q);
+    dst[g] = Ew<W>::shoup_inv(Ew<W>::shoup_inv(v, pp, mi), pl, mi);
+  }
+}
+
+static decltype(&k_dh_top_l<u64, 0>) const K6_k_dh_top_l[6] = TCKS_K6(k_dh_top_l);
+static decltype(&k_vecmat_dh_moddown_rs<u64, 0>) const K6_k_vecmat_dh_moddown_rs[6] = TCKS_K6(k_vecmat_dh_moddown_rs);
+
 }  // namespace
 
 // The level as a template argument up to 8 limbs (every level of the CNN and the 4096x256 product).
@@ -281,6 +350,21 @@ void launch_vecmat_dh_fold(const DevTables& T, u32 ell, const VecmatDhPlan& p, c
   Launch L(K_MULACC, st, 8.0 * (double)e * (p.chunks + 1.0));
   const u32 blocks = (u32)std::min<u64>((e + 255) / 256, 152ull * 16);
   k_vecmat_dh_fold<<<blocks, 256, 0, st>>>(T, ell, p);
+}
+
+void launch_vecmat_dh_moddown_rs(const DevTables& T, const HostTables& H, u32 ell, const VecmatDhPlan& p,
+                                 const u64* top, u64* top2, u64* out, u64 out_b, cudaStream_t st, u64 out_o) {
+  const double n = (double)(1u << T.log_n);
+  const double bo = (double)p.B * dh_outs(p);
+  {
+    Launch L(K_KS_MODDOWN, st, 8.0 * n * bo * 2.0 * 5.0, 2.0 * bo * (0.5 * n * T.log_n + 2.0 * n));
+    launch_limb(K6_k_dh_top_l, T.narrow, (u32)(2 * bo), 1, T.log_n, st, T.limb_threads, T, ell, p, top2);
+  }
+  const Crt2 k2 = crt2_constants(H, T.L, ell - 1);
+  const double jobs = 2.0 * (ell - 1) * bo;
+  Launch L(K_KS_MODDOWN, st, 8.0 * n * jobs * 7.0, jobs * (0.5 * n * T.log_n + 4.0 * n));
+  launch_limb(K6_k_vecmat_dh_moddown_rs, T.narrow, (u32)jobs, 1, T.log_n, st, T.limb_threads, T, ell, p,
+              (const u64*)top, (const u64*)top2, k2, out, out_b, out_o);
 }
 
 void launch_vecmat_dh_moddown(const DevTables& T, u32 ell, const VecmatDhPlan& p, const u64* top, u64* out, u64 out_b,

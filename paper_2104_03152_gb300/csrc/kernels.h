@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include "tcks_types.h"
+#include "params.h"
 
 namespace tcks {
 
@@ -102,6 +103,11 @@ struct KsPlan {
   u32 R, B, add_perm, pad;
 };
 void launch_keyswitch(const DevTables& T, u32 ell, const KsPlan& plan, cudaStream_t st);
+// Relinearization of plan.B tensor products (R = 1, addends add0/add1 = d0, d1) with the rescale by
+// q_{ell-1} in the same rounding: out + rq out_b receives [2][ell-1][N]; top2 scratch [B][2][N].
+void launch_relin_rescale(const DevTables& T, const HostTables& H, u32 ell, const KsPlan& plan, u64* top2,
+                          cudaStream_t st);
+Crt2 crt2_constants(const HostTables& H, u32 L, u32 l);
 // Vector x plain matrix after ModUp and the P-limb stage of R = n-1 rotations (steps 1..R):
 // keys[r] = key of step r+1; top [R][B][2][N] from the KsPlan stage 1; ct + rq*ct_b the input
 // ([2][ell][N]); diag + k*diag_stride the diagonal d_k (k = 0..R); partial [B][chunks][2][ell][N]
@@ -154,6 +160,10 @@ void launch_vecmat_dh_fold(const DevTables& T, u32 ell, const VecmatDhPlan& p, c
 // request-major); with out_o != 0 output o of request rq goes to out + rq * out_b + o * out_o.
 void launch_vecmat_dh_moddown(const DevTables& T, u32 ell, const VecmatDhPlan& p, const u64* top, u64* out, u64 out_b,
                               cudaStream_t st, u64 out_o = 0);
+// The same ModDown and the following rescale as one rounding: outputs [2][ell-1][N] (same placement
+// rules); top2 scratch [2][B * outs][N].
+void launch_vecmat_dh_moddown_rs(const DevTables& T, const HostTables& H, u32 ell, const VecmatDhPlan& p,
+                                 const u64* top, u64* top2, u64* out, u64 out_b, cudaStream_t st, u64 out_o = 0);
 // Stage 1 of a KsPlan alone (the P-limb inner product and its INTT into plan.top).
 void launch_ks_inner_p(const DevTables& T, u32 ell, const KsPlan& plan, cudaStream_t st);
 // The fused ModDown + multiply-accumulate over the plan's R rotations, chunk rotations per CTA.

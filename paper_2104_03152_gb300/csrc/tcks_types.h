@@ -29,6 +29,17 @@ struct PairConst {
   u64 inv_qa_sh32;   // floor(inv_qa * 2^32 / q_b) (narrow chains)
 };
 
+// Constants of a two-prime CRT lift (P and q_l = the prime a rescale drops): residues modulo P and q_l
+// -> the balanced integer modulo P q_l (Garner), used when a ModDown and the following rescale are
+// taken as one rounding.
+struct Crt2 {
+  u64 P, ql;
+  u64 pinv_l;          // P^-1 mod q_l
+  u64 pq_lo, pq_hi;    // P q_l
+  u64 half_lo, half_hi;  // (P q_l - 1) / 2
+  u32 l, pad;          // chain index of q_l
+};
+
 // Everything a kernel needs about the modulus chain, passed by value.
 struct DevTables {
   const ModConst* mods;    // [n_mods]

@@ -221,8 +221,9 @@ def test_cnn_hoisted_conv_parity(setup):
         ctx.set_flags(base)
 
 
-@pytest.mark.parametrize("pack", [False, True], ids=["shared", "shared+pack"])
-def test_cnn_shared_conv_parity(setup, pack):
+@pytest.mark.parametrize("pack,merged", [(False, False), (True, False), (True, True)],
+                         ids=["shared", "shared+pack", "shared+pack+merged"])
+def test_cnn_shared_conv_parity(setup, pack, merged):
     """TCKS_CONV_SHARED (+ rectangular FC layers, double hoisting): the baby-step sums of the four kernels
     over the input's own rotations in one 4-output double-hoisted pass; with TCKS_CONV_PACK (the bench's
     network) the channels packed after the baby steps and one giant-step sum per request. Galois steps
@@ -231,7 +232,7 @@ def test_cnn_shared_conv_parity(setup, pack):
     o, w, enc, ctx, model, need = setup
     base = tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE
     ctx.set_flags(base | tk.TCKS_RECT_DIAG | tk.TCKS_CONV_SHARED | tk.TCKS_DOUBLE_HOIST
-                  | (tk.TCKS_CONV_PACK if pack else 0))
+                  | (tk.TCKS_CONV_PACK if pack else 0) | (tk.TCKS_MERGED_RESCALE if merged else 0))
     try:
         hm = tk.CNN(ctx, w.conv_w, w.conv_b, w.fc1_w, w.fc1_b, w.fc2_w, w.fc2_b, windows=64)
         steps = oracle.cnn_galois_steps(o, rect=True, conv_hoist=True, conv_shared=True, pack_first=pack)
@@ -263,7 +264,7 @@ def test_cnn_shared_conv_parity(setup, pack):
         img = inputs.mnist_like_image(7)
         v, W = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
         ct = o.encrypt_values(v, 83)
-        ref = oracle.cnn_forward(o, ct, w, henc, double_hoist=True)
+        ref = oracle.cnn_forward(o, ct, w, henc, double_hoist=True, merged=merged)
         got = hm.forward(ctx.ct_import(ct.data, ct.scale))
         assert_ct_equal(got, ref, "cnn forward (shared convolution)")
         assert float(np.max(np.abs(ctx.decrypt_values(got, 10) - oracle.cnn_plain(img, w)))) < 5e-3

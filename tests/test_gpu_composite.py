@@ -94,6 +94,10 @@ def test_vecmat_double_hoisted_parity(n, m):
         with pytest.raises(tk.TcksError) as e:
             p.import_ct(cts[0][1]).vecmat_plain(plain_only)
         assert e.value.name == "UNSUPPORTED"
+        g.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | tk.TCKS_DOUBLE_HOIST | tk.TCKS_MERGED_RESCALE)
+        for (v, ct) in cts:  # the ModDown and the rescale in one rounding
+            assert_ct_equal(p.import_ct(ct).vecmat_plain(gm), o.vecmat_dh(ct, ext, n, m, merged=True),
+                            "vecmat (double hoisted, merged rescale)")
     finally:
         g.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE)
 
@@ -120,7 +124,9 @@ def test_vecmat_rect_parity(n, m):
     gm = g.matrix_import_rect(ext, n, m, o.scale)
     genc = g.matrix_encode_rect(M, level=level)
     for flags, kw in ((tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE, {"diags": diags}),
-                      (tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | tk.TCKS_DOUBLE_HOIST, {"diags_ext": ext})):
+                      (tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | tk.TCKS_DOUBLE_HOIST, {"diags_ext": ext}),
+                      (tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | tk.TCKS_DOUBLE_HOIST | tk.TCKS_MERGED_RESCALE,
+                       {"diags_ext": ext, "merged": True})):
         g.set_flags(flags)
         try:
             refs = [o.vecmat_rect(ct, n, m, **kw) for _, ct in cts]

@@ -113,6 +113,23 @@ def test_mul_relin_rescale_parity(pair):
         assert_ct_equal(pair.import_ct(c2x).mul(pair.import_ct(c2y)), o.mul(c2x, c2y), "mul level 2")
 
 
+def test_mul_merged_rescale_parity(pair):
+    """TCKS_MERGED_RESCALE: the relinearization's ModDown and the rescale as one rounding, bit-exact
+    against the oracle's merged multiply, at the top level and one level down."""
+    o, g = pair.o, pair.g
+    x, y = inputs.uniform_slots(o.slots, 5), inputs.uniform_slots(o.slots, 6)
+    cx, cy = o.encrypt_values(x, 23), o.encrypt_values(y, 24)
+    g.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | tk.TCKS_MERGED_RESCALE)
+    try:
+        assert_ct_equal(pair.import_ct(cx).mul(pair.import_ct(cy)), o.mul(cx, cy, merged=True), "merged mul")
+        if o.L >= 3:
+            c2x, c2y = o.mod_switch(cx, 2), o.mod_switch(cy, 2)
+            assert_ct_equal(pair.import_ct(c2x).mul(pair.import_ct(c2y)), o.mul(c2x, c2y, merged=True),
+                            "merged mul level 2")
+    finally:
+        g.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE)
+
+
 def test_mul_relin_only_parity():
     log_n, bits, scale = CHAINS["C1"]
     p = Pair(log_n, bits, scale, flags=tk.TCKS_AUTO_RELIN)
