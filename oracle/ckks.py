@@ -970,6 +970,16 @@ def cnn_encode(o: OracleCKKS, w: CNNWeights, windows=64, rect=False, conv_hoist=
     return e
 
 
+def _pack(o: OracleCKKS, chans, masks, merged: bool) -> Ct:
+    """The masked channels summed: each product rescaled, then added; merged (A25): the products added
+    first and rescaled once."""
+    v = None
+    for c, mk in zip(chans, masks):
+        t = o.mul_plain(c, mk) if merged else o.rescale(o.mul_plain(c, mk))
+        v = t if v is None else o.add(v, t)
+    return o.rescale(v) if merged else v
+
+
 def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: dict | None = None,
                 double_hoist: bool = False, merged: bool = False) -> Ct:
     """The encrypted CNN schedule (§4): conv (im2col, one multiplication per kernel) -> pack the
@@ -996,10 +1006,7 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
                   else o.rescale(o.dh_sum(ct, baby, enc.conv_baby_ext[k])) for k in range(K)]
         else:
             zs = [o.rotsum_dh(o.rescale(o.mul_plain(ct, enc.conv[k])), baby) for k in range(K)]
-        v = None
-        for k in range(K):
-            t = o.rescale(o.mul_plain(zs[k], enc.masks[k]))
-            v = t if v is None else o.add(v, t)
+        v = _pack(o, zs, enc.masks, merged)
         v = o.rotsum_dh(v, giant)
         period = (len(baby) + 1) * W  # blocks [K, B) are zero, the pattern repeats every B blocks
         for r in range(o.slots // period):
@@ -1011,10 +1018,7 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
         else:
             conv = o.conv2d_im2col_hoisted if enc.conv_hoist else o.conv2d_im2col_pt
             chans = [conv(ct, enc.conv[k], enc.taps, W) for k in range(K)]
-        v = None
-        for k in range(K):
-            t = o.rescale(o.mul_plain(chans[k], enc.masks[k]))
-            v = t if v is None else o.add(v, t)
+        v = _pack(o, chans, enc.masks, merged)
         for k in range(K):
             bias[k * W: (k + 1) * W] = w.conv_b[k]
     if trace is not None:

@@ -166,12 +166,26 @@ void cnn_stage(const tcks_cnn* m, u32 stage, const u64* x, u32 count, u64* out) 
         }
       }
       // pack [L-2] + bias
-      DevBuf prod(c, (size_t)count * w1), t(c, (size_t)count * w2);
-      for (u32 k = 0; k < K; ++k) {
-        launch_elementwise(c->T, OP_MUL_PLAIN, chans.p + (size_t)k * count * w1, m->masks[k], prod.p, L - 1,
-                           2 * count, c->stream);
-        op_rescale(c, prod.p, L - 1, k == 0 ? out : t.p, count);
-        if (k) launch_elementwise(c->T, OP_ADD, out, t.p, out, L - 2, 2 * count, c->stream);
+      if ((c->flags & TCKS_MERGED_RESCALE) && K <= kLincombMax) {
+        // the masked channels summed before one rescale (one rounding instead of K)
+        MulSumArgs a{};
+        a.x = chans.p;
+        a.x_stride = (u64)count * w1;
+        for (u32 k = 0; k < K; ++k) a.m[k] = m->masks[k];
+        a.terms = K;
+        a.ell = L - 1;
+        a.count = count;
+        DevBuf packed(c, (size_t)count * w1);
+        launch_mulsum(c->T, a, packed.p, c->stream);
+        op_rescale(c, packed.p, L - 1, out, count);
+      } else {
+        DevBuf prod(c, (size_t)count * w1), t(c, (size_t)count * w2);
+        for (u32 k = 0; k < K; ++k) {
+          launch_elementwise(c->T, OP_MUL_PLAIN, chans.p + (size_t)k * count * w1, m->masks[k], prod.p, L - 1,
+                             2 * count, c->stream);
+          op_rescale(c, prod.p, L - 1, k == 0 ? out : t.p, count);
+          if (k) launch_elementwise(c->T, OP_ADD, out, t.p, out, L - 2, 2 * count, c->stream);
+        }
       }
       if (m->pack_first) op_rotsum_hoisted(c, out, w2, count, L - 2, m->giant, out);
       launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[0], out, L - 2, 2 * count, c->stream);

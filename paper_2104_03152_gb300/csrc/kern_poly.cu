@@ -82,7 +82,44 @@ __global__ void __launch_bounds__(256) k_combine(DevTables T, const u64* __restr
   }
 }
 
+// out[r] = sum_t x_t[r] * m_t (slot-wise products with a plaintext each, summed before one rounding)
+// for `count` ciphertexts at level ell: x_t at x + t * x_stride ([count][2][ell][N]), m_t [>= ell][N].
+template <typename W>
+__global__ void __launch_bounds__(256) k_mulsum(DevTables T, MulSumArgs A, u64* __restrict__ out) {
+  const u32 log_n = T.log_n, ell = A.ell;
+  const u64 n = 1ull << log_n;
+  const u64 total2 = ((2ull * ell * A.count) << log_n) >> 1;
+  for (u64 e2 = (u64)blockIdx.x * blockDim.x + threadIdx.x; e2 < total2; e2 += (u64)gridDim.x * blockDim.x) {
+    const u64 e = e2 << 1;
+    const u32 j = (u32)((e >> log_n) % ell);
+    const u64 k = e & (n - 1);
+    const ModConst m = T.mods[j];
+    typename Ew<W>::Acc a0, a1;
+    for (u32 t = 0; t < A.terms; ++t) {
+      const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(A.x + (u64)t * A.x_stride + e);
+      const ulonglong2 w = *reinterpret_cast<const ulonglong2*>(A.m[t] + (u64)j * n + k);
+      a0.mac(v.x, w.x);
+      a1.mac(v.y, w.y);
+    }
+    *reinterpret_cast<ulonglong2*>(out + e) = make_ulonglong2(a0.get(m), a1.get(m));
+  }
+}
+
 }  // namespace
+
+void launch_mulsum(const DevTables& T, const MulSumArgs& A, u64* out, cudaStream_t st) {
+  const u64 per = (2ull * A.ell * A.count) << T.log_n;
+  u64 blocks = (per / 2 + 255) / 256;
+  const u64 cap = 152ull * 8;
+  if (blocks > cap) blocks = cap;
+  if (!blocks) blocks = 1;
+  Launch L(K_ELEMENTWISE, st, 8.0 * per * (A.terms + 1) + 8.0 * A.terms * ((u64)A.ell << T.log_n),
+           (double)per * A.terms);
+  if (T.narrow)
+    k_mulsum<u32><<<(u32)blocks, 256, 0, st>>>(T, A, out);
+  else
+    k_mulsum<u64><<<(u32)blocks, 256, 0, st>>>(T, A, out);
+}
 
 void launch_combine(const DevTables& T, const u64* x, u32 level, const u32* idx, const u64* coef, u32 outputs,
                     u32 terms, u64* out, cudaStream_t st) {

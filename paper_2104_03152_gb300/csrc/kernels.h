@@ -224,6 +224,15 @@ struct LincombArgs {
   u32 terms, ell, count, has_cst;
 };
 void launch_lincomb(const DevTables& T, const LincombArgs& A, u64* out, cudaStream_t st);
+// out [count][2][ell][N] = sum_t x_t * m_t slot-wise: x_t = x + t * x_stride ([count][2][ell][N]),
+// m_t a plaintext [>= ell][N] (one per term, shared by the ciphertexts).
+struct MulSumArgs {
+  const u64* x;
+  u64 x_stride;
+  const u64* m[kLincombMax];
+  u32 terms, ell, count, pad;
+};
+void launch_mulsum(const DevTables& T, const MulSumArgs& A, u64* out, cudaStream_t st);
 // Gathered combination over an array of ciphertexts x [count][2][level][N] (ciphertext i at
 // x + i * 2 * level * N): out[o] = sum_{t < terms} coef[o][t][j] * x[idx[o][t]] on limb j, for
 // `outputs` ciphertexts [outputs][2][level][N]. idx [outputs][terms], coef [outputs][terms][level]
