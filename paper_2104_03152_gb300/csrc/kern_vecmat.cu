@@ -24,16 +24,63 @@ namespace {
 constexpr u32 kDhThreads = 256;
 
 // Lazy sum of products over the whole rotation loop: products of two residues are added without
-// reduction and the sum is reduced once at the end. 32-bit words: products < 2^62 in a 64-bit sum
-// with a carry count; 64-bit words: products < 2^122 in a 128-bit sum with a count of 2^128 carries.
+// reduction and the sum is reduced once at the end. 32-bit words: a 128-bit sum of four 32-bit words
+// fed through the carry flag; it also takes a key-switch sum unreduced (below 2^66) times a diagonal
+// value, so the rotation loop has no reduction at all. 64-bit words: products < 2^122 in a 128-bit
+// sum with a count of 2^128 carries.
 template <typename W>
 struct DhAcc;
 template <>
 struct DhAcc<u32> {
-  typename Ew<u32>::Acc a;
-  __device__ __forceinline__ void mac(u64 x, u64 y) { a.mac(x, y); }
-  __device__ __forceinline__ void add(u64 x) { a.mac(x, 1); }
-  __device__ __forceinline__ u64 get(const ModConst& m) const { return a.get(m); }
+  u32 w0 = 0, w1 = 0, w2 = 0, w3 = 0;
+  // += x y, x, y < 2^32 (below 2^34 such products the sum stays below 2^96: no carry into w3)
+  __device__ __forceinline__ void mac(u64 x, u64 y) {
+    asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "+r"(w0), "+r"(w1), "+r"(w2)
+        : "r"((u32)x), "r"((u32)y));
+  }
+  __device__ __forceinline__ void add(u64 x) {
+    asm("add.cc.u32 %0, %0, %2;\n\t"
+        "addc.u32 %1, %1, 0;"
+        : "+r"(w0), "+r"(w1)
+        : "r"((u32)x));
+  }
+  // += (s + c 2^64) d, d < 2^32; kCarry = false: c is known to be 0
+  template <bool kCarry>
+  __device__ __forceinline__ void mac_wide(u64 s, u32 c, u64 d) {
+    const u32 sl = (u32)s, sh = (u32)(s >> 32), dv = (u32)d;
+    asm("mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
+        "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
+        "addc.u32 %3, %3, 0;\n\t"
+        "mad.lo.cc.u32 %0, %4, %6, %0;\n\t"
+        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
+        "addc.cc.u32 %2, %2, 0;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "+r"(w0), "+r"(w1), "+r"(w2), "+r"(w3)
+        : "r"(sl), "r"(sh), "r"(dv));
+    if (kCarry)
+      asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\t"
+          "madc.hi.u32 %1, %2, %3, %1;"
+          : "+r"(w2), "+r"(w3)
+          : "r"(c), "r"(dv));
+  }
+  // += s + c 2^64
+  __device__ __forceinline__ void add_wide(u64 s, u32 c) {
+    asm("add.cc.u32 %0, %0, %4;\n\t"
+        "addc.cc.u32 %1, %1, %5;\n\t"
+        "addc.cc.u32 %2, %2, %6;\n\t"
+        "addc.u32 %3, %3, 0;"
+        : "+r"(w0), "+r"(w1), "+r"(w2), "+r"(w3)
+        : "r"((u32)s), "r"((u32)(s >> 32)), "r"(c));
+  }
+  // Horner over the words: every step reduces a value below 2^64
+  __device__ __forceinline__ u64 get(const ModConst& m) const {
+    u64 r = reduce64(((u64)w3 << 32) | w2, m);
+    r = reduce64((r << 32) | w1, m);
+    return reduce64((r << 32) | w0, m);
+  }
 };
 template <>
 struct DhAcc<u64> {
@@ -122,19 +169,36 @@ __global__ void __launch_bounds__(kDhThreads, KO > 1 ? 3 : 1) k_vecmat_dh_acc(De
             s1[rr].mac(d, w1, j);
           }
         }
+        constexpr bool kCarry = ELL == 0 || ELL > 4;
         if (unit) {
 #pragma unroll
           for (int rr = 0; rr < RPT; ++rr) {
-            u0[e][rr].add(s0[rr].get(m));
-            u1[e][rr].add(s1[rr].get(m));
+            if constexpr (sizeof(W) == 4) {
+              u32 c;
+              u64 v = s0[rr].raw(c);
+              u0[e][rr].add_wide(v, c);
+              v = s1[rr].raw(c);
+              u1[e][rr].add_wide(v, c);
+            } else {
+              u0[e][rr].add(s0[rr].get(m));
+              u1[e][rr].add(s1[rr].get(m));
+            }
             if (i < ell) a0[e][rr].add(c0[rr][src]);
           }
         } else if (KO == 1) {
           const u64 dv = dk[g];
 #pragma unroll
           for (int rr = 0; rr < RPT; ++rr) {
-            u0[e][rr].mac(s0[rr].get(m), dv);
-            u1[e][rr].mac(s1[rr].get(m), dv);
+            if constexpr (sizeof(W) == 4) {
+              u32 c;
+              u64 v = s0[rr].raw(c);
+              u0[e][rr].template mac_wide<kCarry>(v, c, dv);
+              v = s1[rr].raw(c);
+              u1[e][rr].template mac_wide<kCarry>(v, c, dv);
+            } else {
+              u0[e][rr].mac(s0[rr].get(m), dv);
+              u1[e][rr].mac(s1[rr].get(m), dv);
+            }
             if (i < ell) a0[e][rr].mac(c0[rr][src], dv);
           }
         } else {

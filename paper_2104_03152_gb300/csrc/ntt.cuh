@@ -387,6 +387,16 @@ struct KsSum<u32, E> {
     acc.add64(part);
     return acc.get(m);
   }
+  // The sum unreduced, as lo + c 2^64 (c = 0 when E <= 4); ends the sum like get().
+  __device__ __forceinline__ u64 raw(u32& c) {
+    if (E > 0 && E <= 4) {
+      c = 0;
+      return part;
+    }
+    acc.add64(part);
+    c = acc.carry;
+    return acc.lo;
+  }
 };
 
 // Launch geometry of a limb transform: cluster size 2^log_c, threads per CTA, shared memory bytes
