@@ -53,23 +53,43 @@ __device__ __forceinline__ void mac128(Acc128& acc, u64 a, u64 b) {
   acc.lo = lo;
 }
 
+// x mod q for x < 2^32 and q < 2^31 with mu32 = floor(2^32 / q): the quotient estimate is at most
+// one short, so one conditional subtraction finishes.
+__device__ __forceinline__ u32 reduce32(u32 x, const ModConst& m) {
+  const u32 q = (u32)m.q;
+  const u32 r = x - __umulhi(x, (u32)m.mu32) * q;
+  return r >= q ? r - q : r;
+}
+
 // Lift a residue x in [0, q_src) to the balanced integer bal(x) taken modulo the target prime:
 // bal(x) = x if x <= (q_src - 1)/2, else x - q_src. qsrc_mod_t = q_src mod q_t.
 __device__ __forceinline__ u64 lift_balanced(u64 x, u64 half_src, u64 qsrc_mod_t, const ModConst& t) {
   const u64 r = reduce64(x, t);
   return x > half_src ? sub_mod(r, qsrc_mod_t, t.q) : r;
 }
+// The same for the word type of a limb kernel: with 32-bit words every prime is below 2^31, so the
+// residue fits one word and the reduction is a 32-bit one.
+template <typename W>
+__device__ __forceinline__ W lift_balanced_w(u64 x, u64 half_src, u64 qsrc_mod_t, const ModConst& t) {
+  if constexpr (sizeof(W) == 4) {
+    const u32 r = reduce32((u32)x, t), c = (u32)qsrc_mod_t;
+    return x > half_src ? (r >= c ? r - c : r + (u32)t.q - c) : r;
+  } else {
+    return lift_balanced(x, half_src, qsrc_mod_t, t);
+  }
+}
 
 // The balanced integer x, |x| < P q_l / 2, with x = rp (mod P) and x = rl (mod q_l), reduced modulo
 // the target prime t: Garner's x = rp + P ((rl - rp) P^-1 mod q_l), then P q_l subtracted above the
-// half. With every prime below 2^31 (NARROW) P q_l < 2^62 and x fits one 64-bit word (three 64-bit
-// Barrett reductions); otherwise 128-bit words.
+// half. With every prime below 2^31 (NARROW) P q_l < 2^62 and x fits one 64-bit word (two 32-bit
+// reductions and one 64-bit one); otherwise 128-bit words.
 template <bool NARROW>
 __device__ __forceinline__ u64 crt2_lift(u64 rp, u64 rl, const Crt2& k, const ModConst& ml, const ModConst& t) {
   if constexpr (NARROW) {
-    const u64 a = reduce64(rp, ml);
-    const u64 d = rl >= a ? rl - a : rl + k.ql - a;
-    const u64 u = reduce64(d * k.pinv_l, ml);
+    const u32 a = reduce32((u32)rp, ml), q = (u32)k.ql;
+    const u32 d = (u32)rl >= a ? (u32)rl - a : (u32)rl + q - a;
+    u32 u = d * (u32)k.pinv_l - __umulhi(d, k.pinv_sh32) * q;  // Shoup: d P^-1 mod q_l in [0, 2 q_l)
+    u = u >= q ? u - q : u;
     const u64 x = rp + k.P * u;
     const bool neg = x > k.half_lo;
     const u64 r = reduce64(neg ? k.pq_lo - x : x, t);

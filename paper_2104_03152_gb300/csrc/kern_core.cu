@@ -452,7 +452,7 @@ __global__ void k_drop_combine(DevTables T, const u64* __restrict__ in, u64 in_p
   const ModConst md = T.mods[drop_mod];
   const PairConst pc = T.pairs[(u64)drop_mod * T.n_mods + i];
   const u64* tp = top + (u64)p * n + sl.off;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)lift_balanced(tp[k], md.half, pc.qa_mod_b, mi);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced_w<W>(tp[k], md.half, pc.qa_mod_b, mi);
   __syncthreads();
   ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
   const u64* src = in + (u64)p * in_poly_stride + (u64)i * n + sl.off;
@@ -497,7 +497,7 @@ __global__ void k_modup(DevTables T, const u64* __restrict__ x_ntt, u64 x_stride
   const u64 half_j = T.mods[j].half;
   const u64 qj_mod_t = T.pairs[(u64)j * T.n_mods + tmod].qa_mod_b;
   const u64* in = x_coef + (sl.y * ell + j) * n + sl.off;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)lift_balanced(in[k], half_j, qj_mod_t, mt);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced_w<W>(in[k], half_j, qj_mod_t, mt);
   __syncthreads();
   ntt_fwd_slice<W, LC>(s, T, tmod, sl.rank);
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) out[k] = (W)Ar<W>::fwd_out(s[sw(k)], mt);
@@ -596,7 +596,7 @@ __global__ void k_ks_moddown(DevTables T, u32 ell, const __grid_constant__ KsPla
   const ModConst mp = T.mods[T.L];
   const PairConst pc = T.pairs[(u64)T.L * T.n_mods + i];
   const u64* top = plan.top + (yy * 2 + b) * n + sl.off;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)lift_balanced(top[k], mp.half, pc.qa_mod_b, mi);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced_w<W>(top[k], mp.half, pc.qa_mod_b, mi);
   __syncthreads();
   ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
   const u64* add = b == 0 ? (plan.add0 ? plan.add0 + rq * plan.add0_b : nullptr)
@@ -696,6 +696,7 @@ Crt2 crt2_constants(const HostTables& H, u32 L, u32 l) {
     e >>= 1;
   }
   k.pinv_l = r;
+  k.pinv_sh32 = k.ql < (1ull << 31) ? (u32)(((u128)r << 32) / k.ql) : 0;
   const u128 pq = (u128)k.P * k.ql, half = (pq - 1) / 2;
   k.pq_lo = (u64)pq;
   k.pq_hi = (u64)(pq >> 64);
@@ -829,7 +830,7 @@ __device__ __forceinline__ void vecmat_acc_body(W* s, const DevTables& T, u32 el
   for (u32 r = r0; r < r1; ++r) {
     const KsKey kk = plan.keys[r];
     const u64* top = plan.top + (((u64)r * plan.B + rq) * 2 + b) * n + sl.off;
-    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)lift_balanced(top[k], mp.half, pc.qa_mod_b, mi);
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced_w<W>(top[k], mp.half, pc.qa_mod_b, mi);
     __syncthreads();
     ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
     const u64* dk = plan.diag + (u64)(r + 1) * plan.diag_stride + (u64)i * n;

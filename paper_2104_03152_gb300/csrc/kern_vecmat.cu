@@ -268,7 +268,7 @@ __global__ void k_vecmat_dh_moddown(DevTables T, u32 ell, const __grid_constant_
   const ModConst mp = T.mods[T.L];
   const PairConst pc = T.pairs[(u64)T.L * T.n_mods + i];
   const u64* t = top + ((u64)b * bo + ro) * n + sl.off;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)lift_balanced(t[k], mp.half, pc.qa_mod_b, mi);
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced_w<W>(t[k], mp.half, pc.qa_mod_b, mi);
   __syncthreads();
   ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
   const u64* U = p.partial + dh_off(ro, 0, p.chunks, b, i, ell, log_n);

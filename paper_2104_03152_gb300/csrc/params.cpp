@@ -142,6 +142,7 @@ bool build_tables(u32 log_n, const std::vector<u64>& chain, HostTables& out) {
     m.half = (q - 1) / 2;
     m.r64 = (u64)(((u128)1 << 64) % q);
     m.ninv_sh32 = (u64)(((u128)m.ninv << 32) / q);
+    m.mu32 = q < (1ull << 31) ? (1ull << 32) / q : 0;
     // twiddles: psi^brv(k) and psi^-brv(k) with Shoup companions
     u64* t0 = &out.tw[((size_t)i * 4 + 0) * n];
     u64* t1 = &out.tw[((size_t)i * 4 + 1) * n];

@@ -18,7 +18,7 @@ struct ModConst {
   u64 half;          // (q - 1) / 2
   u64 r64;           // 2^64 mod q
   u64 ninv_sh32;     // floor(ninv * 2^32 / q) (narrow chains, q < 2^31)
-  u64 pad;
+  u64 mu32;          // floor(2^32 / q) (narrow chains, q < 2^31; 0 otherwise)
 };
 
 // Pairwise constants for prime a (source) and prime b (target): [a][b].
@@ -37,7 +37,8 @@ struct Crt2 {
   u64 pinv_l;          // P^-1 mod q_l
   u64 pq_lo, pq_hi;    // P q_l
   u64 half_lo, half_hi;  // (P q_l - 1) / 2
-  u32 l, pad;          // chain index of q_l
+  u32 l;               // chain index of q_l
+  u32 pinv_sh32;       // floor(pinv_l 2^32 / q_l) (narrow chains, q_l < 2^31; 0 otherwise)
 };
 
 // Everything a kernel needs about the modulus chain, passed by value.
