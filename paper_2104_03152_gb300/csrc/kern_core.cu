@@ -629,13 +629,13 @@ __global__ void k_ks_top_rs(DevTables T, u32 ell, const __grid_constant__ KsPlan
   const KsKey kk = plan.keys[0];
   const W* digits = reinterpret_cast<const W*>(plan.digits) + rq * plan.digits_b;
   const ModConst m = T.mods[mod];
-  const u64 pm = which ? T.pairs[(u64)T.L * T.n_mods + l].qa_mod_b : 0;  // P mod q_l
+  const PairConst pm = T.pairs[(u64)T.L * T.n_mods + l];  // P mod q_l
   const u64* add = b == 0 ? plan.add0 + rq * plan.add0_b : plan.add1 + rq * plan.add1_b;
   ell_dispatch(ell, [&](auto E) {
     for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
       const u32 g = sl.off + k;
       u64 v = ks_inner<W, decltype(E)::value>(digits, ell, slot, kk.key, kk.K, which ? l : kk.K, b, g, g, n, m);
-      if (which) v = add_mod(v, Ew<W>::mul(pm, add[(u64)l * n + g], m), m.q);
+      if (which) v = add_mod(v, Ew<W>::mul_pc(add[(u64)l * n + g], pm, m), m.q);
       s[sw(k)] = (W)v;
     }
   });
@@ -672,7 +672,7 @@ __global__ void k_ks_moddown_rs(DevTables T, u32 ell, const __grid_constant__ Ks
     for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
       const u32 g = sl.off + k;
       const u64 u = ks_inner<W, decltype(E)::value>(digits, ell, i, kk.key, kk.K, i, b, g, g, n, mi);
-      const u64 z = add_mod(u, Ew<W>::mul(pp.qa_mod_b, add[(u64)i * n + g], mi), mi.q);
+      const u64 z = add_mod(u, Ew<W>::mul_pc(add[(u64)i * n + g], pp, mi), mi.q);
       const u64 v = sub_mod(z, Ar<W>::fwd_out(s[sw(k)], mi), mi.q);
       dst[g] = Ew<W>::shoup_inv(Ew<W>::shoup_inv(v, pp, mi), pl, mi);
     }

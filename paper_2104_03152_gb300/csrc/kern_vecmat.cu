@@ -301,7 +301,7 @@ __global__ void k_dh_top_l(DevTables T, u32 ell, const __grid_constant__ VecmatD
   const u32 ro = sl.job % bo, b = sl.job / bo, rq = ro / outs, o = ro % outs;
   const u32 l = ell - 1;
   const ModConst m = T.mods[l];
-  const u64 pm = T.pairs[(u64)T.L * T.n_mods + l].qa_mod_b;
+  const PairConst pm = T.pairs[(u64)T.L * T.n_mods + l];  // P mod q_l
   const u64* U = p.partial + dh_off(ro, 0, p.chunks, b, l, ell, log_n);
   const u64* A = p.partial + dh_off(ro, 0, p.chunks, 2, l, ell, log_n);
   const u64* cb = p.ct + rq * p.ct_b + ((u64)b * ell + l) * n;
@@ -310,7 +310,7 @@ __global__ void k_dh_top_l(DevTables T, u32 ell, const __grid_constant__ VecmatD
     const u32 g = sl.off + k;
     u64 a = d0 ? Ew<W>::mul(cb[g], d0[g], m) : cb[g];
     if (b == 0) a = add_mod(a, A[g], m.q);
-    s[sw(k)] = (W)add_mod(U[g], Ew<W>::mul(pm, a, m), m.q);
+    s[sw(k)] = (W)add_mod(U[g], Ew<W>::mul_pc(a, pm, m), m.q);
   }
   __syncthreads();
   ntt_inv_slice<W, LC>(s, T, l, sl.rank);
@@ -347,7 +347,7 @@ __global__ void k_vecmat_dh_moddown_rs(DevTables T, u32 ell, const __grid_consta
     const u32 g = sl.off + k;
     u64 a = d0 ? Ew<W>::mul(cb[g], d0[g], mi) : cb[g];
     if (b == 0) a = add_mod(a, A[g], mi.q);
-    const u64 z = add_mod(U[g], Ew<W>::mul(pp.qa_mod_b, a, mi), mi.q);
+    const u64 z = add_mod(U[g], Ew<W>::mul_pc(a, pp, mi), mi.q);
     const u64 v = sub_mod(z, Ar<W>::fwd_out(s[sw(k)], mi), mi.q);
     dst[g] = Ew<W>::shoup_inv(Ew<W>::shoup_inv(v, pp, mi), pl, mi);
   }

@@ -107,6 +107,19 @@ struct Ar32Lazy {
 };
 
 
+// 32-bit words with primes so small that (2 log N + 4) q < 2^32: the forward butterfly without any
+// conditional subtraction. The Shoup product is in [0, 2q) for any input word, so a value in [0, k q)
+// leaves a stage in [0, (k + 2) q); an input below 4q ends the log N stages below (2 log N + 4) q,
+// still one word, and one 32-bit Barrett reduction per element finishes the transform.
+struct Ar32Grow {
+  static __device__ __forceinline__ void ct(u32& X, u32& Y, u32 W, u32 Wsh, u32 q) {
+    const u32 x = X;
+    const u32 t = Y * W - __umulhi(Y, Wsh) * q;  // in [0, 2q)
+    X = x + t;
+    Y = x - t + 2 * q;
+  }
+  static __device__ __forceinline__ void gs(u32& X, u32& Y, u32 W, u32 Wsh, u32 q) { Ar32Lazy::gs(X, Y, W, Wsh, q); }
+};
 
 // R = 2^LR elements x[q] = element base + q * stride (stride = the round's smallest butterfly
 // distance) through forward stages st .. st+LR-1; gblk = global index of the block of stage st.
@@ -280,6 +293,14 @@ __device__ __forceinline__ void ntt_fwd_slice(W* s, const DevTables& T, u32 mod,
   const W* tw = Ar<W>::tw(T, mod, 0);
   const W* tws = Ar<W>::tw(T, mod, 1);
   if constexpr (sizeof(W) == 4) {
+    if ((u64)q * (2 * log_n + 4) < (1ull << 32)) {  // no subtractions in the stages, one reduction after
+      if constexpr (LC > 0) cross_stages<W, LC, true, Ar32Grow>(s, log_n, log_ns, rank, tw, tws, q);
+      ntt_fwd_local_rounds<W, Ar32Grow>(s, log_n, log_ns, rank, tw, tws, q);
+      const ModConst& m = T.mods[mod];
+      for (u32 k = threadIdx.x; k < (1u << log_ns); k += blockDim.x) s[k] = reduce32(s[k], m);
+      __syncthreads();
+      return;
+    }
     if (q < (1u << 30)) {  // lazy butterflies, then [0, 4q) -> [0, q)
       if constexpr (LC > 0) cross_stages<W, LC, true, Ar32Lazy>(s, log_n, log_ns, rank, tw, tws, q);
       ntt_fwd_local_rounds<W, Ar32Lazy>(s, log_n, log_ns, rank, tw, tws, q);
@@ -324,6 +345,10 @@ struct Ew<u64> {
   static __device__ __forceinline__ u64 shoup_inv(u64 a, const PairConst& p, const ModConst& m) {
     return mul_shoup(a, p.inv_qa, p.inv_qa_sh, m.q);
   }
+  // a (q_a mod q_b)
+  static __device__ __forceinline__ u64 mul_pc(u64 a, const PairConst& p, const ModConst& m) {
+    return mul_mod(a, p.qa_mod_b, m);
+  }
   // sum_j d_j * w_j mod q, 128-bit lazy accumulation
   struct Acc {
     Acc128 a{0, 0};
@@ -339,6 +364,9 @@ struct Ew<u32> {
   }
   static __device__ __forceinline__ u64 shoup_inv(u64 a, const PairConst& p, const ModConst& m) {
     return shoup32((u32)a, (u32)p.inv_qa, (u32)p.inv_qa_sh32, (u32)m.q);
+  }
+  static __device__ __forceinline__ u64 mul_pc(u64 a, const PairConst& p, const ModConst& m) {
+    return shoup32((u32)a, (u32)p.qa_mod_b, (u32)p.qa_mod_b_sh32, (u32)m.q);
   }
   // products of 31-bit residues are below 2^62; a 64-bit sum with a carry count holds any ell
   struct Acc {

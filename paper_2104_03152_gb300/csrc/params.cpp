@@ -176,6 +176,7 @@ bool build_tables(u32 log_n, const std::vector<u64>& chain, HostTables& out) {
       PairConst& p = out.pairs[(size_t)a * nm + b];
       std::memset(&p, 0, sizeof(p));
       p.qa_mod_b = chain[a] % chain[b];
+      if (chain[b] < (1ull << 31)) p.qa_mod_b_sh32 = (u64)(((u128)p.qa_mod_b << 32) / chain[b]);
       if (a != b) {
         p.inv_qa = invmod_h(p.qa_mod_b, chain[b]);
         p.inv_qa_sh = shoup_of(p.inv_qa, chain[b]);

@@ -27,6 +27,7 @@ struct PairConst {
   u64 inv_qa;        // q_a^-1 mod q_b (0 when a == b)
   u64 inv_qa_sh;     // Shoup companion of inv_qa
   u64 inv_qa_sh32;   // floor(inv_qa * 2^32 / q_b) (narrow chains)
+  u64 qa_mod_b_sh32; // floor(qa_mod_b * 2^32 / q_b) (narrow chains)
 };
 
 // Constants of a two-prime CRT lift (P and q_l = the prime a rescale drops): residues modulo P and q_l
