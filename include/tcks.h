@@ -523,6 +523,20 @@ tcks_status tcks_cnn_forward_device(const tcks_cnn* m, const uint64_t* d_in, uin
  * host-to-device copy, the batched schedule on one contiguous device batch, one device-to-host copy;
  * returns when host_out is written. */
 tcks_status tcks_cnn_forward_host(const tcks_cnn* m, const uint64_t* host_in, uint32_t count, uint64_t* host_out);
+/* Sizes of one serialized input of the network (level L; in_full: both components, in_seeded: c0 and
+ * the seed of c1) and of one serialized output (level L-6), in bytes: the wire form of
+ * tcks_ct_serialize / tcks_ct_serialize_seeded. */
+tcks_status tcks_cnn_wire_sizes(const tcks_cnn* m, uint64_t* in_full, uint64_t* in_seeded, uint64_t* out_size);
+/* The batched forward pass on serialized ciphertexts, the client-server exchange of an encrypted
+ * evaluation (§4): host_in holds count inputs back to back, each in_size bytes (in_full or in_seeded of
+ * tcks_cnn_wire_sizes; all of that one kind, level L, the context scale); host_out receives count
+ * serialized outputs, each out_size bytes (kind 0, level L-6, the model's output scale). One
+ * host-to-device copy of the bytes, the residues unpacked and c1 regenerated from its seed on the
+ * device, the batched schedule, the outputs packed on the device, one device-to-host copy; returns when
+ * host_out is written. Errors: INVALID_ARG for a size, header or residue (>= its prime) that does not
+ * fit, SCALE_MISMATCH for an input scale; after a residue error host_out is unspecified. */
+tcks_status tcks_cnn_forward_wire(const tcks_cnn* m, const uint8_t* host_in, uint64_t in_size, uint32_t count,
+                                  uint8_t* host_out, uint64_t out_size);
 /* CUDA graph of the batched forward for a fixed batch size (the schedule is captured once with its
  * stream-ordered scratch allocations, then replayed): create captures it (after one eager pass that
  * warms the key tables), run copies the inputs into the graph's staging buffers, replays and returns

@@ -163,6 +163,9 @@ _SIGS = {
     "tcks_cnn_forward_batch": (ctypes.c_int32, [_vp, _vpp, ctypes.c_uint32, _vpp]),
     "tcks_cnn_forward_host": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, _u64p]),
     "tcks_cnn_forward_device": (ctypes.c_int32, [_vp, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
+    "tcks_cnn_wire_sizes": (ctypes.c_int32, [_vp, _u64p, _u64p, _u64p]),
+    "tcks_cnn_forward_wire": (ctypes.c_int32, [_vp, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                               ctypes.c_void_p, ctypes.c_uint64]),
     "tcks_vecmat_plain_batch": (ctypes.c_int32, [_vpp, ctypes.c_uint32, _vp, _vpp]),
     "tcks_ct_import_batch": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double, _vpp]),
     "tcks_ct_export_batch": (ctypes.c_int32, [_vpp, ctypes.c_uint32, _u64p, ctypes.c_size_t]),
@@ -766,6 +769,22 @@ class CNN:
         """The batched forward pass from host limbs [count][2][L][N] into host_out [count][2][L-6][N]."""
         assert host_in.dtype == np.uint64 and host_out.dtype == np.uint64
         check(lib().tcks_cnn_forward_host(self.h, _p(host_in), host_in.shape[0], _p(host_out)))
+        return host_out
+
+    def wire_sizes(self) -> tuple[int, int, int]:
+        """Bytes of one serialized input (both components), one seeded input, one serialized output."""
+        v = np.zeros(3, dtype=np.uint64)
+        check(lib().tcks_cnn_wire_sizes(self.h, _p(v[0:]), _p(v[1:]), _p(v[2:])))
+        return int(v[0]), int(v[1]), int(v[2])
+
+    def forward_wire(self, host_in: np.ndarray, count: int, host_out: np.ndarray) -> np.ndarray:
+        """The batched forward pass on serialized ciphertexts: host_in = count inputs of one size (uint8,
+        [count][in_size]), host_out [count][out_size] uint8 receives the serialized outputs."""
+        assert host_in.dtype == np.uint8 and host_out.dtype == np.uint8
+        assert host_in.flags.c_contiguous and host_out.flags.c_contiguous
+        in_size, out_size = host_in.size // max(count, 1), host_out.size // max(count, 1)
+        check(lib().tcks_cnn_forward_wire(self.h, host_in.ctypes.data, in_size, count, host_out.ctypes.data,
+                                          out_size))
         return host_out
 
     def graph(self, count: int) -> "CNNGraph":

@@ -783,8 +783,6 @@ tcks_status tcks_ct_export(const tcks_ct* ct, uint64_t* limbs, size_t n_words) {
 }
 
 // ------------------------------------------------------------------------- wire format ----
-static const unsigned char kWireMagic[4] = {'T', 'C', 'K', 'S'};
-static constexpr u64 kWireHeader = 16;
 
 tcks_status tcks_ct_serialized_size(const tcks_ct* ct, uint64_t* bytes) {
   TCKS_API_BEGIN

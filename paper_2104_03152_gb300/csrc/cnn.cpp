@@ -18,7 +18,9 @@
 //   square [L-5]; FC2 [L-6]; + bias. Logits sit in slots [0, classes).
 // Biases are encoded once, at the scales the schedule reaches from an input at the context scale
 // (the same double operations the forward pass performs), so the forward pass needs no encoding.
+#include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -508,6 +510,85 @@ tcks_status tcks_cnn_forward_host(const tcks_cnn* m, const uint64_t* host_in, ui
   cnn_forward_dev(m, xin.p, w_in, count, yout.p);
   check_cuda(cudaMemcpyAsync(host_out, yout.p, (size_t)count * w_out * 8, cudaMemcpyDeviceToHost, c->stream), "D2H");
   check_cuda(cudaStreamSynchronize(c->stream), "forward");
+  CNN_END
+}
+
+tcks_status tcks_cnn_wire_sizes(const tcks_cnn* m, uint64_t* in_full, uint64_t* in_seeded, uint64_t* out_size) {
+  CNN_BEGIN
+  if (!m || !in_full || !in_seeded || !out_size) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  tcks_ctx* c = m->ctx;
+  const u64 pin = wire_payload_bytes(c->T, c->host.chain.data(), m->L);
+  *in_full = kWireHeader + pin;
+  *in_seeded = kWireHeader + 8 + pin / 2;
+  *out_size = kWireHeader + wire_payload_bytes(c->T, c->host.chain.data(), m->L - 6);
+  CNN_END
+}
+
+tcks_status tcks_cnn_forward_wire(const tcks_cnn* m, const uint8_t* host_in, uint64_t in_size, uint32_t count,
+                                  uint8_t* host_out, uint64_t out_size) {
+  CNN_BEGIN
+  if (!m || (count && (!host_in || !host_out))) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  if (!count) return TCKS_OK;
+  tcks_ctx* c = m->ctx;
+  const u32 L = m->L, Lo = m->L - 6;
+  const u64 pin = wire_payload_bytes(c->T, c->host.chain.data(), L);
+  const u64 pout = wire_payload_bytes(c->T, c->host.chain.data(), Lo);
+  const bool seeded = in_size == kWireHeader + 8 + pin / 2;
+  if (!seeded && in_size != kWireHeader + pin) fail(TCKS_ERR_INVALID_ARG, "input size is not a serialized input");
+  if (out_size != kWireHeader + pout) fail(TCKS_ERR_INVALID_ARG, "output size is not the serialized output");
+  // headers on the host: every input of the announced kind, ring, level and scale
+  std::vector<u64> seeds(seeded ? count : 0);
+  for (u32 r = 0; r < count; ++r) {
+    const uint8_t* h = host_in + (u64)r * in_size;
+    double sc;
+    std::memcpy(&sc, h + 8, 8);
+    if (std::memcmp(h, kWireMagic, 4) != 0 || h[4] != 1 || h[5] != (seeded ? 1 : 0) || h[6] != c->params.log_n ||
+        h[7] != L)
+      fail(TCKS_ERR_INVALID_ARG, "an input header does not match the model's input");
+    if (sc != m->in_scale) fail(TCKS_ERR_SCALE_MISMATCH, "the network takes ciphertexts at the context scale");
+    if (seeded)
+      for (int b = 0; b < 8; ++b) seeds[r] |= (u64)h[kWireHeader + b] << (8 * b);
+  }
+  const u64 w_in = ct_words(c, L), w_out = ct_words(c, Lo);
+  DevBuf raw(c, ((u64)count * in_size + 7) / 8), xin(c, (size_t)count * w_in), yout(c, (size_t)count * w_out);
+  DevBuf packed(c, ((u64)count * out_size + 7) / 8), dseeds(c, seeded ? count : 1);
+  unsigned char* rb = (unsigned char*)raw.p;
+  unsigned char* pb = (unsigned char*)packed.p;
+  check_cuda(cudaMemcpyAsync(rb, host_in, (size_t)count * in_size, cudaMemcpyHostToDevice, c->stream), "H2D");
+  if (seeded)
+    check_cuda(cudaMemcpyAsync(dseeds.p, seeds.data(), (size_t)count * 8, cudaMemcpyHostToDevice, c->stream), "H2D");
+  check_cuda(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream), "wire status");
+  const u64 head = kWireHeader + (seeded ? 8 : 0);
+  constexpr u32 kChunk = 16384;  // grid z = requests x components <= 65535
+  for (u32 r0 = 0; r0 < count; r0 += kChunk) {
+    const u32 k = std::min(kChunk, count - r0);
+    launch_unpack_batch(c->T, rb + (u64)r0 * in_size + head, in_size, L, xin.p + (u64)r0 * w_in, w_in, k, c->d_status,
+                        c->stream, seeded ? 1 : 2);
+    if (seeded)
+      launch_sym_a_batch(c->T, dseeds.p + r0, L, xin.p + (u64)r0 * w_in + (u64)L * c->N, w_in, k, c->stream);
+  }
+  check_launch("wire input");
+  cnn_forward_dev(m, xin.p, w_in, count, yout.p);
+  for (u32 r0 = 0; r0 < count; r0 += kChunk) {
+    const u32 k = std::min(kChunk, count - r0);
+    launch_pack_batch(c->T, yout.p + (u64)r0 * w_out, w_out, Lo, pb + (u64)r0 * out_size + kWireHeader, out_size, k,
+                      c->stream);
+  }
+  check_launch("wire output");
+  int status = 0;
+  check_cuda(cudaMemcpyAsync(host_out, pb, (size_t)count * out_size, cudaMemcpyDeviceToHost, c->stream), "D2H");
+  check_cuda(cudaMemcpyAsync(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "wire status");
+  check_cuda(cudaStreamSynchronize(c->stream), "forward");
+  if (status) fail(TCKS_ERR_INVALID_ARG, "an input residue is not below its prime");
+  for (u32 r = 0; r < count; ++r) {
+    uint8_t* h = host_out + (u64)r * out_size;
+    std::memcpy(h, kWireMagic, 4);
+    h[4] = 1;
+    h[5] = 0;
+    h[6] = (uint8_t)c->params.log_n;
+    h[7] = (uint8_t)Lo;
+    std::memcpy(h + 8, &m->out_scale, 8);
+  }
   CNN_END
 }
 

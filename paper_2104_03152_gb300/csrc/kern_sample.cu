@@ -211,6 +211,17 @@ __global__ void k_sym_a(DevTables T, u64 seed_a, u32 ell, u64* __restrict__ a, i
   }
 }
 
+// k_sym_a for count requests: request r's polynomial from seeds[r] at a + r a_stride.
+__global__ void k_sym_a_batch(DevTables T, const u64* __restrict__ seeds, u32 ell, u64* __restrict__ a, u64 a_stride,
+                              u32 count) {
+  const u64 n = 1ull << T.log_n, per = (u64)ell * n;
+  for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < per * count; e += (u64)gridDim.x * blockDim.x) {
+    const u64 r = e / per, x = e - r * per;
+    const u32 l = (u32)(x >> T.log_n);
+    a[r * a_stride + x] = draw_uniform(seeds[r], 7, x & (n - 1), l, T.mods[l]);
+  }
+}
+
 static decltype(&k_keygen_secret<u64, 0>) const K6_k_keygen_secret[6] = TCKS_K6(k_keygen_secret);
 static decltype(&k_keygen_public<u64, 0>) const K6_k_keygen_public[6] = TCKS_K6(k_keygen_public);
 static decltype(&k_keygen_switch<u64, 0>) const K6_k_keygen_switch[6] = TCKS_K6(k_keygen_switch);
@@ -264,6 +275,14 @@ void launch_sym_a(const DevTables& T, u64 seed_a, u32 ell, u64* a, bool check, i
   u64 blocks = (e + 255) / 256;
   if (blocks > 152ull * 8) blocks = 152ull * 8;
   k_sym_a<<<(u32)blocks, 256, 0, st>>>(T, seed_a, ell, a, check ? 1 : 0, status);
+}
+
+void launch_sym_a_batch(const DevTables& T, const u64* seeds, u32 ell, u64* a, u64 a_stride, u32 count, cudaStream_t st) {
+  const u64 e = ((u64)ell << T.log_n) * count;
+  Launch L(K_ENCRYPT, st, 8.0 * e);
+  u64 blocks = (e + 255) / 256;
+  if (blocks > 152ull * 16) blocks = 152ull * 16;
+  k_sym_a_batch<<<(u32)blocks, 256, 0, st>>>(T, seeds, ell, a, a_stride, count);
 }
 
 }  // namespace tcks

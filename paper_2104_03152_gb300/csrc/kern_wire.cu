@@ -26,30 +26,33 @@ __device__ __forceinline__ u64 seg_off(const DevTables& T, u32 level, u32 b, u32
   return (u64)b * per_comp + before;
 }
 
-__global__ void k_pack(DevTables T, const u64* __restrict__ ct, u32 level, unsigned char* __restrict__ out) {
-  const u32 b = blockIdx.z, i = blockIdx.y;
+// blockIdx.z = request * comps + component; request r's ciphertext at ct + r ct_stride (words), its
+// payload at out + r out_stride (bytes)
+__global__ void k_pack(DevTables T, const u64* __restrict__ ct, u64 ct_stride, u32 level, u32 comps,
+                       unsigned char* __restrict__ out, u64 out_stride) {
+  const u32 b = blockIdx.z % comps, r = blockIdx.z / comps, i = blockIdx.y;
   const u64 n = 1ull << T.log_n;
   const u32 w = width_of(T.mods[i].q);
   const u64 seg = (n * w + 7) / 8;
   const u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= seg) return;
-  const u64* x = ct + ((u64)b * level + i) * n;
+  const u64* x = ct + r * ct_stride + ((u64)b * level + i) * n;
   const u64 bit = t * 8;
   const u64 k = bit / w;
   const u32 o = (u32)(bit - k * w);
   u64 v = x[k] >> o;  // the rest of residue k
   if (w - o < 8 && k + 1 < n) v |= x[k + 1] << (w - o);
-  out[seg_off(T, level, b, i) + t] = (unsigned char)v;
+  out[r * out_stride + seg_off(T, level, b, i) + t] = (unsigned char)v;
 }
 
-__global__ void k_unpack(DevTables T, const unsigned char* __restrict__ in, u32 level, u64* __restrict__ ct,
-                         int* __restrict__ status) {
-  const u32 b = blockIdx.z, i = blockIdx.y;
+__global__ void k_unpack(DevTables T, const unsigned char* __restrict__ in, u64 in_stride, u32 level, u32 comps,
+                         u64* __restrict__ ct, u64 ct_stride, int* __restrict__ status) {
+  const u32 b = blockIdx.z % comps, r = blockIdx.z / comps, i = blockIdx.y;
   const u64 n = 1ull << T.log_n;
   const u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const u32 w = width_of(T.mods[i].q);
-  const unsigned char* seg = in + seg_off(T, level, b, i);
+  const unsigned char* seg = in + r * in_stride + seg_off(T, level, b, i);
   const u64 seg_bytes = (n * w + 7) / 8;
   const u64 bit = k * w;
   const u64 byte0 = bit / 8;
@@ -64,7 +67,7 @@ __global__ void k_unpack(DevTables T, const unsigned char* __restrict__ in, u32 
     atomicExch(status, 1);
     v = 0;
   }
-  ct[((u64)b * level + i) * n + k] = v;
+  ct[r * ct_stride + ((u64)b * level + i) * n + k] = v;
 }
 
 }  // namespace
@@ -80,18 +83,30 @@ u64 wire_payload_bytes(const DevTables& T, const u64* host_primes, u32 level) {
   return 2 * bytes;
 }
 
-void launch_pack(const DevTables& T, const u64* ct, u32 level, unsigned char* out, cudaStream_t st, u32 comps) {
+void launch_pack_batch(const DevTables& T, const u64* ct, u64 ct_stride, u32 level, unsigned char* out, u64 out_stride,
+                       u32 count, cudaStream_t st, u32 comps) {
   const u64 n = 1ull << T.log_n;
   const u64 max_seg = (n * 64 + 7) / 8;
-  Launch L(K_ELEMENTWISE, st, 8.0 * comps * level * n * 1.9);
-  k_pack<<<dim3((unsigned)((max_seg + 255) / 256), level, comps), 256, 0, st>>>(T, ct, level, out);
+  Launch L(K_ELEMENTWISE, st, 8.0 * count * comps * level * n * 1.9);
+  k_pack<<<dim3((unsigned)((max_seg + 255) / 256), level, count * comps), 256, 0, st>>>(T, ct, ct_stride, level, comps,
+                                                                                        out, out_stride);
+}
+
+void launch_unpack_batch(const DevTables& T, const unsigned char* in, u64 in_stride, u32 level, u64* ct, u64 ct_stride,
+                         u32 count, int* status, cudaStream_t st, u32 comps) {
+  const u64 n = 1ull << T.log_n;
+  Launch L(K_ELEMENTWISE, st, 8.0 * count * comps * level * n * 1.9);
+  k_unpack<<<dim3((unsigned)((n + 255) / 256), level, count * comps), 256, 0, st>>>(T, in, in_stride, level, comps, ct,
+                                                                                    ct_stride, status);
+}
+
+void launch_pack(const DevTables& T, const u64* ct, u32 level, unsigned char* out, cudaStream_t st, u32 comps) {
+  launch_pack_batch(T, ct, 0, level, out, 0, 1, st, comps);
 }
 
 void launch_unpack(const DevTables& T, const unsigned char* in, u32 level, u64* ct, int* status, cudaStream_t st,
                    u32 comps) {
-  const u64 n = 1ull << T.log_n;
-  Launch L(K_ELEMENTWISE, st, 8.0 * comps * level * n * 1.9);
-  k_unpack<<<dim3((unsigned)((n + 255) / 256), level, comps), 256, 0, st>>>(T, in, level, ct, status);
+  launch_unpack_batch(T, in, 0, level, ct, 0, 1, status, st, comps);
 }
 
 }  // namespace tcks

@@ -57,11 +57,21 @@ u32 limb_threads_cap_sample(bool narrow, u32 log_c);
 u32 limb_threads_cap_fft(bool narrow, u32 log_c);
 // Bit-packed wire format of a ciphertext [2][level][N] (kern_wire.cu): payload bytes, pack into
 // `out` (device), unpack with a range check (status set to 1 on a residue >= q_i).
+// Serialized ciphertext: a 16-byte header (magic "TCKS", version 1, kind 0 = both components or
+// 1 = c0 and the 8-byte seed of c1 right after the header, log N, level, scale as f64), then the payload.
+inline constexpr unsigned char kWireMagic[4] = {'T', 'C', 'K', 'S'};
+inline constexpr u64 kWireHeader = 16;
 u64 wire_payload_bytes(const DevTables& T, const u64* host_primes, u32 level);
 // comps = 2: both components; comps = 1: component 0 only (the seeded format).
 void launch_pack(const DevTables& T, const u64* ct, u32 level, unsigned char* out, cudaStream_t st, u32 comps = 2);
 void launch_unpack(const DevTables& T, const unsigned char* in, u32 level, u64* ct, int* status, cudaStream_t st,
                    u32 comps = 2);
+// count ciphertexts at once: request r's ciphertext at ct + r ct_stride (words), its payload at
+// r out_stride / r in_stride (bytes); count * comps <= 65535
+void launch_pack_batch(const DevTables& T, const u64* ct, u64 ct_stride, u32 level, unsigned char* out, u64 out_stride,
+                       u32 count, cudaStream_t st, u32 comps = 2);
+void launch_unpack_batch(const DevTables& T, const unsigned char* in, u64 in_stride, u32 level, u64* ct, u64 ct_stride,
+                         u32 count, int* status, cudaStream_t st, u32 comps = 2);
 void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_outer, u64* dst, u64 dst_outer,
                 u32 count, u32 mod_base, u32 per, cudaStream_t st);
 enum : u32 { OP_ADD = 0, OP_SUB = 1, OP_NEG = 2, OP_MUL_PLAIN = 3, OP_ADD_PLAIN = 4, OP_SUB_PLAIN = 5 };
@@ -188,6 +198,8 @@ void launch_encrypt_sym(const DevTables& T, u64 seed_a, u64 seed_e, const u64* s
                         cudaStream_t st);
 // a [ell][N] = the uniform polynomial of seed_a; check: compare instead of writing (status = 1 on a mismatch).
 void launch_sym_a(const DevTables& T, u64 seed_a, u32 ell, u64* a, bool check, int* status, cudaStream_t st);
+// c1 of count seeded ciphertexts: a + r a_stride receives the uniform polynomial of seeds[r] (device)
+void launch_sym_a_batch(const DevTables& T, const u64* seeds, u32 ell, u64* a, u64 a_stride, u32 count, cudaStream_t st);
 
 // ---- kern_fft.cu (FP64 canonical embedding)
 struct FftTables {

@@ -297,3 +297,48 @@ def test_cnn_forward_host_equals_batch(setup):
     model.forward_device(d_in.data_ptr(), 3, d_out.data_ptr())
     ctx.synchronize()
     assert np.array_equal(d_out.cpu().numpy().view(np.uint64), host_out)
+
+
+def test_cnn_forward_wire_equals_batch(setup):
+    """tcks_cnn_forward_wire on serialized inputs (the oracle's secret-key ciphertexts in the seeded
+    and the full wire form) returns the batched forward's outputs serialized byte for byte; a bad
+    header, size or residue is refused."""
+    from oracle import wire
+    o, w, enc, ctx, model, need = setup
+    img = inputs.mnist_like_image(11)
+    v, W = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+    pt = o.encode(v)
+    cts = [o.encrypt_symmetric(pt, 700 + i, 70 + i) for i in range(3)]
+    full, seeded, out_size = model.wire_sizes()
+    L = cts[0].level
+    assert seeded == wire.size_seeded(o.N, o.primes, L) and full == wire.size(o.N, o.primes, L)
+    outs = model.forward_batch([ctx.ct_import(c.data, c.scale) for c in cts])
+    lv, sc = outs[0].info()[0], outs[0].info()[1]
+    want = [wire.serialize(x.export(), lv, sc, o.log_n, o.primes) for x in outs]
+    assert out_size == len(want[0])
+    forms = {"seeded": [wire.serialize_seeded(c.data[0], L, c.scale, o.log_n, o.primes, 700 + i)
+                        for i, c in enumerate(cts)],
+             "full": [wire.serialize(c.data, L, c.scale, o.log_n, o.primes) for c in cts]}
+    for name, bufs in forms.items():
+        host_in = np.frombuffer(b"".join(bufs), dtype=np.uint8).copy()
+        host_out = np.zeros(3 * out_size, dtype=np.uint8)
+        model.forward_wire(host_in, 3, host_out)
+        for i in range(3):
+            assert host_out[i * out_size:(i + 1) * out_size].tobytes() == want[i], (name, i)
+    host_in = np.frombuffer(b"".join(forms["seeded"]), dtype=np.uint8).copy()
+    host_out = np.zeros(3 * out_size, dtype=np.uint8)
+    bad = host_in.copy()
+    bad[seeded + 7] = L - 1  # the second input's level
+    with pytest.raises(tk.TcksError) as e:
+        model.forward_wire(bad, 3, host_out)
+    assert e.value.name == "INVALID_ARG"
+    with pytest.raises(tk.TcksError) as e:
+        model.forward_wire(host_in[:-1], 3, host_out)  # sizes that are no serialized input
+    assert e.value.name == "INVALID_ARG"
+    bad = host_in.copy()
+    bad[2 * seeded - 4:2 * seeded] = 0xFF  # the last residue of the second input's c0 above its prime
+    with pytest.raises(tk.TcksError) as e:
+        model.forward_wire(bad, 3, host_out)
+    assert e.value.name == "INVALID_ARG"
+    model.forward_wire(host_in, 3, host_out)  # the context is still usable
+    assert host_out[:out_size].tobytes() == want[0]
