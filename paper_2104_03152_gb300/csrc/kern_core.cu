@@ -497,6 +497,7 @@ __global__ void k_modup(DevTables T, const u64* __restrict__ x_ntt, u64 x_stride
   const u64 half_j = T.mods[j].half;
   const u64 qj_mod_t = T.pairs[(u64)j * T.n_mods + tmod].qa_mod_b;
   const u64* in = x_coef + (sl.y * ell + j) * n + sl.off;
+#pragma unroll 4
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced_w<W>(in[k], half_j, qj_mod_t, mt);
   __syncthreads();
   ntt_fwd_slice<W, LC>(s, T, tmod, sl.rank);

@@ -319,6 +319,8 @@ __global__ void k_dh_top_l(DevTables T, u32 ell, const __grid_constant__ VecmatD
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) dst[k] = Ar<W>::inv_out(s[sw(k)], m);
 }
 
+constexpr u32 kMdBatch = 4;
+
 // Stage 2: out_b[i] = (Z_b[i] - NTT_i([Z_b]_{P q_l} mod q_i)) (P q_l)^-1, i < ell - 1; limb job =
 // (b (ell - 1) + i) * B * outs + request * outs + output; top [2][B * outs][N] holds INTT_P(U_b[P]).
 template <typename W, int LC>
@@ -336,6 +338,7 @@ __global__ void k_vecmat_dh_moddown_rs(DevTables T, u32 ell, const __grid_consta
   const PairConst pl = T.pairs[(u64)lo * T.n_mods + i];   // q_l^-1 mod q_i
   const u64* tp = top + ((u64)b * bo + ro) * n + sl.off;
   const u64* tl = top2 + ((u64)b * bo + ro) * n + sl.off;
+#pragma unroll 4
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)crt2_lift<sizeof(W) == 4>(tp[k], tl[k], k2, ml, mi);
   __syncthreads();
   ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
@@ -344,13 +347,32 @@ __global__ void k_vecmat_dh_moddown_rs(DevTables T, u32 ell, const __grid_consta
   const u64* cb = p.ct + rq * p.ct_b + ((u64)b * ell + i) * n;
   const u64* d0 = p.diag ? p.diag + (u64)o * p.diag_set + (u64)i * n : nullptr;
   u64* dst = out + (out_o ? rq * out_b + o * out_o : ro * out_b) + ((u64)b * lo + i) * n;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
-    const u32 g = sl.off + k;
-    u64 a = d0 ? Ew<W>::mul(cb[g], d0[g], mi) : cb[g];
-    if (b == 0) a = add_mod(a, A[g], mi.q);
-    const u64 z = add_mod(U[g], Ew<W>::mul_pc(a, pp, mi), mi.q);
-    const u64 v = sub_mod(z, Ar<W>::fwd_out(s[sw(k)], mi), mi.q);
-    dst[g] = Ew<W>::shoup_inv(Ew<W>::shoup_inv(v, pp, mi), pl, mi);
+  // the operands of kMdBatch elements are loaded before any of them is finished (the stores could
+  // alias the loads as far as the compiler knows, which would serialise them)
+  for (u32 k0 = threadIdx.x; k0 < sl.ns; k0 += kMdBatch * blockDim.x) {
+    u64 uv[kMdBatch], cv[kMdBatch], dv[kMdBatch], av[kMdBatch];
+#pragma unroll
+    for (u32 t = 0; t < kMdBatch; ++t) {
+      const u32 k = k0 + t * blockDim.x;
+      if (k < sl.ns) {
+        const u32 g = sl.off + k;
+        uv[t] = U[g];
+        cv[t] = cb[g];
+        dv[t] = d0 ? d0[g] : 0;
+        av[t] = b == 0 ? A[g] : 0;
+      }
+    }
+#pragma unroll
+    for (u32 t = 0; t < kMdBatch; ++t) {
+      const u32 k = k0 + t * blockDim.x;
+      if (k < sl.ns) {
+        u64 a = d0 ? Ew<W>::mul(cv[t], dv[t], mi) : cv[t];
+        if (b == 0) a = add_mod(a, av[t], mi.q);
+        const u64 z = add_mod(uv[t], Ew<W>::mul_pc(a, pp, mi), mi.q);
+        const u64 v = sub_mod(z, Ar<W>::fwd_out(s[sw(k)], mi), mi.q);
+        dst[sl.off + k] = Ew<W>::shoup_inv(Ew<W>::shoup_inv(v, pp, mi), pl, mi);
+      }
+    }
   }
 }
 
