@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(kDhThreads, KO > 1 ? 3 : 1) k_vecmat_dh_acc(De
   DhAcc<W> u0[EPT][RPT * KO], u1[EPT][RPT * KO], a0[EPT][RPT * KO];
   const u32 r0 = chunk * p.chunk, r1 = min(p.R, r0 + p.chunk);
   const bool unit = p.diag == nullptr;  // a hoisted rotation sum: every diagonal is 1
-#pragma unroll 2
+  constexpr int kRotUnroll = sizeof(W) == 4 ? 2 : 1;  // two rotations' loads in flight (32-bit words)
+#pragma unroll kRotUnroll
   for (u32 r = r0; r < r1; ++r) {
     const KsKey kk = p.keys[r];
     const u32 key_slot = i < ell ? i : kk.K;

@@ -64,8 +64,10 @@ __device__ __forceinline__ u32 shoup32(u32 a, u32 w, u32 wsh, u32 q) {
 }
 template <>
 struct Ar<u32> {
+  // which = 0, 1: the forward (twiddle, Shoup) pairs; 2, 3: the inverse ones (one table per
+  // direction, read as pairs by the butterfly groups)
   static __device__ __forceinline__ const u32* tw(const DevTables& T, u32 mod, u32 which) {
-    return T.tw32 + ((u64)mod * 4 + which) * (1ull << T.log_n);
+    return T.tw32 + ((u64)mod * 2 + (which >> 1)) * (2ull << T.log_n);
   }
   static __device__ __forceinline__ void ct(u32& X, u32& Y, u32 W, u32 Wsh, u32 q) {
     const u32 t = shoup32(Y, W, Wsh, q);
@@ -121,6 +123,17 @@ struct Ar32Grow {
   static __device__ __forceinline__ void gs(u32& X, u32& Y, u32 W, u32 Wsh, u32 q) { Ar32Lazy::gs(X, Y, W, Wsh, q); }
 };
 
+// Twiddle idx and its Shoup companion: 64-bit words from two tables, 32-bit words as one pair.
+__device__ __forceinline__ void load_tw(const u64* tw, const u64* tws, u32 idx, u64& w, u64& wsh) {
+  w = tw[idx];
+  wsh = tws[idx];
+}
+__device__ __forceinline__ void load_tw(const u32* tw, const u32*, u32 idx, u32& w, u32& wsh) {
+  const uint2 p = reinterpret_cast<const uint2*>(tw)[idx];
+  w = p.x;
+  wsh = p.y;
+}
+
 // R = 2^LR elements x[q] = element base + q * stride (stride = the round's smallest butterfly
 // distance) through forward stages st .. st+LR-1; gblk = global index of the block of stage st.
 template <typename W, int LR, typename A = Ar<W>>
@@ -132,7 +145,8 @@ __device__ __forceinline__ void fwd_group(W (&x)[1 << LR], u32 st, u32 gblk, con
 #pragma unroll
     for (int b = 0; b < (1 << u); ++b) {
       const u32 idx = ((1u << st) << u) + (gblk << u) + b;
-      const W w = tw[idx], wsh = tws[idx];
+      W w, wsh;
+      load_tw(tw, tws, idx, w, wsh);
 #pragma unroll
       for (int x0 = 0; x0 < h; ++x0) A::ct(x[b * 2 * h + x0], x[b * 2 * h + x0 + h], w, wsh, q);
     }
@@ -152,7 +166,8 @@ __device__ __forceinline__ void inv_group(W (&x)[1 << LR], u32 log_n, u32 st, u3
 #pragma unroll
     for (int b = 0; b < (R >> (u + 1)); ++b) {
       const u32 idx = m + (gblk << (LR - u - 1)) + b;
-      const W w = tw[idx], wsh = tws[idx];
+      W w, wsh;
+      load_tw(tw, tws, idx, w, wsh);
 #pragma unroll
       for (int x0 = 0; x0 < h; ++x0) A::gs(x[b * 2 * h + x0], x[b * 2 * h + x0 + h], w, wsh, q);
     }

@@ -163,11 +163,11 @@ bool build_tables(u32 log_n, const std::vector<u64>& chain, HostTables& out) {
       t2[k] = ipw[r];
       t3[k] = shoup_of(ipw[r], q);
       if (out.narrow) {
-        u32* n32 = &out.tw32[(size_t)i * 4 * n];
-        n32[k] = (u32)pw[r];
-        n32[n + k] = (u32)(((u128)pw[r] << 32) / q);
-        n32[2 * n + k] = (u32)ipw[r];
-        n32[3 * n + k] = (u32)(((u128)ipw[r] << 32) / q);
+        u32* n32 = &out.tw32[(size_t)i * 4 * n];  // (twiddle, Shoup) pairs: forward [N][2], inverse [N][2]
+        n32[2 * k] = (u32)pw[r];
+        n32[2 * k + 1] = (u32)(((u128)pw[r] << 32) / q);
+        n32[2 * n + 2 * k] = (u32)ipw[r];
+        n32[2 * n + 2 * k + 1] = (u32)(((u128)ipw[r] << 32) / q);
       }
     }
   }

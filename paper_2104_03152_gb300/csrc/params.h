@@ -14,7 +14,7 @@ struct HostTables {
   std::vector<ModConst> mods;    // per prime
   std::vector<PairConst> pairs;  // [a][b]
   std::vector<u64> tw;           // [prime][4][N]
-  std::vector<u32> tw32;         // [prime][4][N], 32-bit Shoup companions (narrow chains)
+  std::vector<u32> tw32;         // [prime][2][N][2]: forward then inverse (twiddle, 32-bit Shoup) pairs (narrow chains)
   bool narrow = false;           // every prime < 2^31
   std::vector<u32> slot_index;   // slot j -> (5^j mod 2N - 1)/4, j < N/2
   std::vector<double> zeta;      // exp(i pi k / N), k < 2N, interleaved (re, im)

@@ -47,7 +47,7 @@ struct DevTables {
   const ModConst* mods;    // [n_mods]
   const PairConst* pairs;  // [n_mods][n_mods]
   const u64* tw;           // [n_mods][4][N]: psi^brv(k), Shoup, psi^-brv(k), Shoup
-  const u32* tw32;         // the same with 32-bit Shoup companions (narrow chains only)
+  const u32* tw32;         // [n_mods][2][N][2]: forward, inverse (twiddle, 32-bit Shoup) pairs (narrow chains only)
   u32 log_n;
   u32 n_mods;  // L + 1
   u32 L;       // number of data primes; P is chain index L
