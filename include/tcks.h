@@ -276,8 +276,9 @@ tcks_status tcks_mod_switch(tcks_ct* ct, uint32_t level);
  * q_{level-1}, which the caller tracks. Its only scratch (two limbs) is a static device array of
  * 2 x 2^14 u64 words (256 KB), which every GPU that loads the library holds until the process
  * exits; N above 2^14 is rejected with TCKS_ERR_INVALID_ARG. The first call on a device looks up
- * that array's address (and raises the two kernels' shared-memory limit), so make one call on
- * each device before any stream capture. All calls share the one array: calls that can overlap on
+ * that array's address, so make one call on each device before any stream capture. Every call
+ * raises, where needed, the shared-memory limit of its two kernels (a host-side function
+ * attribute that only ever grows; no memory is allocated). All calls share the one array: calls that can overlap on
  * the GPU (different streams, or different contexts on the same device) race on it and must be
  * serialised by the caller. Nothing in the array needs to start at zero. Asynchronous on the
  * context's stream; errors: INVALID_ARG, LEVEL_EXHAUSTED (level < 2), CUDA_ERROR. */

@@ -960,8 +960,10 @@ u64* g_scratch_ptr[kNoAllocMaxDevices];  // device address of g_rescale_scratch 
 bool g_scratch_ready[kNoAllocMaxDevices];
 std::mutex g_scratch_mu;
 
-// Once per device, with that device current: resolve the scratch array's device address and raise
-// the shared-memory limit of the two kernels the rescale launches. Returns nullptr on failure.
+// Once per device, with that device current: resolve the scratch array's device address. Returns
+// nullptr on failure. (The shared-memory limits of the two kernels are raised on every call through
+// ensure_smem, whose registry only ever raises a limit; setting them here behind its back would let a
+// later ordinary launch of the same kernel at a smaller N lower the limit again.)
 u64* noalloc_setup(int device, std::string* why) {
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (g_scratch_ready[device]) return g_scratch_ptr[device];
@@ -975,14 +977,7 @@ u64* noalloc_setup(int device, std::string* why) {
     return nullptr;
   }
   u64* ptr = nullptr;
-  cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_rescale_scratch);
-  const int bytes = (int)(((size_t)8) << kNoAllocMaxLogN);
-  const void* fns[4] = {(const void*)k_ntt<true, u64, 0>, (const void*)k_drop_combine<u64, 0>,
-                        (const void*)k_ntt<true, u32, 0>, (const void*)k_drop_combine<u32, 0>};
-  for (const void* f : fns) {
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  }
+  const cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_rescale_scratch);
   if (prev != device) cudaSetDevice(prev);
   if (e != cudaSuccess) {
     *why = std::string("scratch set-up failed: ") + cudaGetErrorString(e);
@@ -1018,6 +1013,8 @@ extern "C" tcks_status tcks_rescale_noalloc(tcks_ctx* ctx, const uint64_t* d_in,
   const size_t smem = T.narrow ? sh.smem / 2 : sh.smem;
   auto ntt = T.narrow ? k_ntt<true, u32, 0> : k_ntt<true, u64, 0>;
   auto drop = T.narrow ? k_drop_combine<u32, 0> : k_drop_combine<u64, 0>;
+  ensure_smem((const void*)ntt, smem);  // allocates no device memory
+  ensure_smem((const void*)drop, smem);
   count_launch();
   ntt<<<2, sh.threads, smem, ctx->stream>>>(T, d_in + (u64)(level - 1) * n, (u64)level * n, scratch, n, level - 1, 1);
   count_launch();

@@ -32,6 +32,29 @@ def test_rescale_noalloc_matches_rescale_twice(log_n, bits, level):
         assert np.array_equal(got, ref), f"call {call}"
 
 
+def test_rescale_noalloc_after_a_smaller_ordinary_rescale():
+    """The shared-memory limit the first call needs (a 2^14 limb of 64-bit words, 128 KB) must survive an
+    ordinary rescale at N = 2^13 of the same kernels, which needs only 64 KB."""
+    big = tk.Context(tk.Params(14, [60, 40, 40, 60], 2.0 ** 40), seed=inputs.SEED_KEYS)
+    small = tk.Context(tk.Params(13, [50, 40, 40, 50], 2.0 ** 40), seed=inputs.SEED_KEYS)
+    n, level = 1 << 14, 3
+
+    def noalloc_once(seed):
+        limbs = inputs.random_limbs(big.primes[:level], n, seed, polys=2)
+        ref = big.ct_import(limbs, 1.0).rescale_().export()
+        d_in = torch.from_numpy(limbs.view(np.int64).copy()).cuda()
+        d_out = torch.full((2 * (level - 1) * n,), -1, dtype=torch.int64, device="cuda")
+        torch.cuda.synchronize()
+        big.rescale_noalloc(d_in.data_ptr(), level, d_out.data_ptr())
+        big.synchronize()
+        assert np.array_equal(d_out.cpu().numpy().view(np.uint64).reshape(2, level - 1, n), ref), seed
+
+    noalloc_once(600)
+    limbs = inputs.random_limbs(small.primes[:3], 1 << 13, 601, polys=2)
+    small.ct_import(limbs, 1.0).rescale_().export()  # the ordinary path at N = 2^13, 64-bit words
+    noalloc_once(602)
+
+
 def test_rescale_noalloc_rejects_bad_level():
     small = tk.Context(tk.Params(12, [36, 36, 37], 2.0 ** 30), seed=inputs.SEED_KEYS)
     buf = torch.zeros(2 * 2 * (1 << 12), dtype=torch.int64, device="cuda")
