@@ -1,6 +1,6 @@
 """Benchmark: encrypted MNIST-shaped CNN inferences/s on one GB300 (and N replicas under torchrun).
 
-Workload (the paper's evaluation network, §4 / Table 2, with the chain N=8192, primes
+Workload (the paper's evaluation network, §5 / Table 2, with the chain N=8192, primes
 [31,26,26,26,26,26,26,31], scale 2^26): 28x28 seeded uniform image, im2col-encoded and encrypted;
 conv 4x7x7 stride 3 -> square -> FC 256->64 -> square -> FC 64->10 on seeded N(0, 0.1) weights.
 A step is one batch of B encrypted inferences (B requests, default 256) through the whole hot path

@@ -46,7 +46,7 @@ enum {
   TCKS_ERR_OUT_OF_MEMORY = -7,   /* device allocation failed */
   TCKS_ERR_BUDGET_EXCEEDED = -8, /* serving admission: HBM budget would be exceeded */
   TCKS_ERR_CUDA = -9,            /* a CUDA runtime call failed (detail has the CUDA message) */
-  TCKS_ERR_TIMEOUT = -10,        /* a bounded device wait ran out */
+  TCKS_ERR_TIMEOUT = -10,        /* a bounded wait ran out (tcks_batch_wait, the serving loop) */
   TCKS_ERR_VALUE_OVERFLOW = -11, /* encode: |scale * m_i| >= 2^62 */
   TCKS_ERR_UNSUPPORTED = -12,    /* valid request this build does not implement (detail says what) */
   TCKS_ERR_NOT_READY = -13       /* serving: the request has not completed yet */
@@ -71,7 +71,7 @@ typedef struct {
 } tcks_allocator;
 
 /* ---------------------------------------------------------------------------- parameters ---- */
-/* Coefficient-modulus chain (the CKKS parameters of §4 / Tables 4-5: poly degree N = 2^log_n and
+/* Coefficient-modulus chain (the CKKS parameters of §5 and the appendix Tables 4-5: poly degree N = 2^log_n and
  * the bit sizes of the coefficient modulus, last entry = the special prime P). For each bit size
  * in order the prime is the largest c < 2^b, c > 2^(b-1), c == 1 (mod 2N), not chosen before.
  * n_primes >= 2 (at least one data prime plus P), every size in [20, 61]. `scale` is the default
@@ -83,6 +83,21 @@ tcks_status tcks_params_create(uint32_t log_n, const uint32_t* bit_sizes, uint32
  * BAD_PARAMS when a prime fails a condition. */
 tcks_status tcks_params_create_primes(uint32_t log_n, const uint64_t* primes, uint32_t n_primes, double scale,
                                       tcks_params** out);
+/* Parameters for hybrid key switching (the generalisation of the context's relinearization and
+ * Galois keys of §2.1 to fewer, wider digits; the paper has no parameter for it): primes[0..L-1] are
+ * the data primes q_i and the last n_special are the special primes p_k, P their product; a
+ * key-switching digit covers `alpha` consecutive data primes, so a key switch at level ell has
+ * ceil(ell / alpha) digits instead of ell. ModUp lifts each digit's residues to the other data
+ * primes and the special primes by an exact balanced base conversion, D_j = sum_{i in digit j}
+ * bal(x_i (Q_j/q_i)^-1 mod q_i) (Q_j/q_i); ModDown divides by P with the same conversion from the
+ * special primes. Keys of level Kt are [ceil(Kt/alpha)][2][Kt + n_special][N]. n_special and alpha in
+ * [1, 8]; every digit's product must stay below P (BAD_PARAMS otherwise). With n_special = alpha = 1
+ * this is tcks_params_create_primes. On such a context relinearization, rotation (single, hoisted,
+ * batched), sum, dot, power and polyval use the hybrid key switch; the fused vector x matrix
+ * products, hoisted rotation sums, the im2col convolution's fused sums and the CNN return
+ * UNSUPPORTED. */
+tcks_status tcks_params_create_hybrid(uint32_t log_n, const uint64_t* primes, uint32_t n_primes, uint32_t n_special,
+                                      uint32_t alpha, double scale, tcks_params** out);
 void tcks_params_free(tcks_params* p);
 /* Writes the n_primes chosen primes (data primes, then P) to host `primes`. */
 tcks_status tcks_params_primes(const tcks_params* p, uint64_t* primes, uint32_t capacity);
@@ -181,19 +196,27 @@ tcks_status tcks_decode(tcks_ctx* ctx, const tcks_pt* pt, double* out, size_t n)
 /* Public-key encryption at the plaintext's level: c0 = u*pk0 + e0 + m, c1 = u*pk1 + e1 with u
  * ternary and e0, e1 centred-binomial, all drawn from `seed`. */
 tcks_status tcks_encrypt(tcks_ctx* ctx, const tcks_pt* pt, uint64_t seed, tcks_ct** out);
-/* m = c0 + c1*s. */
+/* m = c0 + c1*s; for a three-component ciphertext (an unrelinearized product) m = c0 + c1 s + c2 s^2. */
 tcks_status tcks_decrypt(tcks_ctx* ctx, const tcks_ct* ct, tcks_pt** out);
 
 /* Raw import / export (host u64, layouts above). Import copies host -> device (asynchronously,
  * then synchronises so `limbs` may be reused). Export synchronises. */
 tcks_status tcks_ct_import(tcks_ctx* ctx, const uint64_t* limbs, uint32_t level, double scale, tcks_ct** out);
+/* n_words = size * level * N: the export of a three-component ciphertext is [3][level][N]. */
 tcks_status tcks_ct_export(const tcks_ct* ct, uint64_t* limbs, size_t n_words);
+/* Import of a ciphertext of `size` = 2 or 3 components, host limbs [size][level][N] (NTT form). */
+tcks_status tcks_ct_import_sized(tcks_ctx* ctx, const uint64_t* limbs, uint32_t size, uint32_t level, double scale,
+                                 tcks_ct** out);
+/* Number of components: 2, or 3 for the product of tcks_mul without TCKS_AUTO_RELIN until it is
+ * relinearized (§2.1: relinearization is automatic only when the context asks for it). */
+tcks_status tcks_ct_size(const tcks_ct* ct, uint32_t* size);
 /* The same for a batch: host limbs [count][2][level][N] contiguous; all copies are queued before one
- * wait (use pinned host memory for overlap). export_batch requires one context and one level. */
+ * wait (use pinned host memory for overlap). export_batch requires one context, one level and
+ * two-component ciphertexts. */
 tcks_status tcks_ct_import_batch(tcks_ctx* ctx, const uint64_t* limbs, uint32_t count, uint32_t level, double scale,
                                  tcks_ct** outs);
 tcks_status tcks_ct_export_batch(const tcks_ct* const* cts, uint32_t count, uint64_t* limbs, size_t n_words);
-/* Wire format (the communication of one encrypted inference, §4): a 16-byte header (b"TCKS",
+/* Wire format (the communication of one encrypted inference, §5): a 16-byte header (b"TCKS",
  * version 1, kind 0, log2 N, level, scale as f64, little-endian) and, for component b = 0, 1 and limb
  * i < level, the N NTT-form residues packed with exactly bit_length(q_i) bits each (residue k in bits
  * [k w, (k+1) w) of the limb's ceil(N w / 8)-byte segment, least significant bit first). Packing and
@@ -220,12 +243,17 @@ tcks_status tcks_pt_import(tcks_ctx* ctx, const uint64_t* limbs, uint32_t level,
 tcks_status tcks_pt_export(const tcks_pt* pt, uint64_t* limbs, size_t n_words);
 tcks_status tcks_ct_info(const tcks_ct* ct, uint32_t* level, double* scale);
 tcks_status tcks_pt_info(const tcks_pt* pt, uint32_t* level, double* scale);
-/* Device pointer of the [2][level][N] limbs (valid until the ciphertext is freed). */
+/* Device pointer of the [size][level][N] limbs (valid until the ciphertext is freed). */
 tcks_status tcks_ct_device_ptr(const tcks_ct* ct, uint64_t** d_limbs);
 void tcks_ct_free(tcks_ct* ct);
 void tcks_pt_free(tcks_pt* pt);
 
 /* --------------------------------------------------------- element-wise ops (§3, Table 3) ---- */
+/* These, tcks_decrypt, tcks_rescale, tcks_mod_switch and tcks_ct_export also take three-component
+ * ciphertexts: add / sub give three components when either operand has them (a missing component is
+ * zero), negate and mul_plain act on every component, add_plain / sub_plain on c0 only. Every other
+ * operation (rotations, sums, products, the vector x matrix product, the convolution, the network,
+ * power, polyval, tensors, serving, serialization) refuses them with INVALID_ARG: relinearize first. */
 tcks_status tcks_add(const tcks_ct* a, const tcks_ct* b, tcks_ct** out);
 tcks_status tcks_sub(const tcks_ct* a, const tcks_ct* b, tcks_ct** out);
 tcks_status tcks_negate(const tcks_ct* a, tcks_ct** out);
@@ -234,9 +262,10 @@ tcks_status tcks_negate(const tcks_ct* a, tcks_ct** out);
 tcks_status tcks_add_plain(const tcks_ct* a, const tcks_pt* p, tcks_ct** out);
 tcks_status tcks_sub_plain(const tcks_ct* a, const tcks_pt* p, tcks_ct** out);
 tcks_status tcks_mul_plain(const tcks_ct* a, const tcks_pt* p, tcks_ct** out);
-/* enc x enc: tensor product (d0, d1, d2) = (a0b0, a0b1 + a1b0, a1b1), then relinearize and
- * rescale as the context's AUTO flags say. Without AUTO_RELIN the result cannot be returned as a
- * 2-component ciphertext and the call fails with UNSUPPORTED. */
+/* enc x enc (§3, Table 3 "mul"; both operands two-component): tensor product (d0, d1, d2) = (a0b0,
+ * a0b1 + a1b0, a1b1), then relinearize and rescale as the context's AUTO flags say (§2.1). Without
+ * TCKS_AUTO_RELIN the result is the three-component ciphertext (d0, d1, d2), rescaled component by
+ * component under TCKS_AUTO_RESCALE; tcks_relinearize turns it into the two-component one. */
 tcks_status tcks_mul(const tcks_ct* a, const tcks_ct* b, tcks_ct** out);
 tcks_status tcks_square(const tcks_ct* a, tcks_ct** out);
 /* Element-wise power x^k (§3, "power" with a circuit of minimum multiplicative depth), k >= 1:
@@ -262,9 +291,17 @@ tcks_status tcks_polyval(const tcks_ct* x, const double* coeffs, uint32_t n_coef
  * otherwise) in batched launches; outs[count]. */
 tcks_status tcks_polyval_batch(const tcks_ct* const* x, uint32_t count, const double* coeffs, uint32_t n_coeffs,
                                tcks_ct** outs);
-/* Rescale in place: divide by the last prime with rounding (level - 1, scale / q_last). */
+/* Relinearization in place (§2.1, the relinearization keys; the step TCKS_AUTO_RELIN runs inside
+ * tcks_mul): a three-component ciphertext (c0, c1, c2) becomes (c0, c1) + KS(c2) with the
+ * relinearization key (one ModUp of c2, the inner product with the key's digits, one ModDown by P), the
+ * same result, bit for bit, as tcks_mul with TCKS_AUTO_RELIN and without TCKS_AUTO_RESCALE. A
+ * two-component ciphertext is left as it is. Errors: INVALID_ARG (null), OUT_OF_MEMORY, CUDA_ERROR;
+ * the ciphertext is unchanged on error. */
+tcks_status tcks_relinearize(tcks_ct* ct);
+/* Rescale in place: divide by the last prime with rounding (level - 1, scale / q_last); a
+ * three-component ciphertext is rescaled component by component. */
 tcks_status tcks_rescale(tcks_ct* ct);
-/* Drop limbs level..ell-1 in place (scale unchanged). */
+/* Drop limbs level..ell-1 in place (scale unchanged), of every component. */
 tcks_status tcks_mod_switch(tcks_ct* ct, uint32_t level);
 /* Rescale that allocates no memory, for callers that must not allocate at all while they run: for
  * example a serving loop that reserves all of its device memory when it starts and admits work
@@ -403,6 +440,18 @@ typedef struct {
   uint64_t* d_out;
 } tcks_batch_job;
 tcks_status tcks_batch_run(const tcks_batch_job* jobs, uint32_t n_jobs);
+/* The same batch submitted with a handle to wait on (the paper has no
+ * counterpart): tcks_batch_submit validates and queues the jobs exactly as tcks_batch_run does, then
+ * records a completion point on jobs[0].ctx's stream (after every context's work has joined it) and
+ * returns *out, owned by the caller. tcks_batch_wait waits on the host for that point: TCKS_OK once
+ * every job has completed; TCKS_ERR_TIMEOUT when timeout_ns nanoseconds passed first (0 polls once;
+ * a negative timeout waits without limit) -- the handle stays valid and the work keeps running, so
+ * wait again or free it; TCKS_ERR_CUDA when the device reported an error. tcks_batch_free waits for
+ * the work (without limit) before it releases the handle and the contexts it retains. */
+typedef struct tcks_batch tcks_batch;
+tcks_status tcks_batch_submit(const tcks_batch_job* jobs, uint32_t n_jobs, tcks_batch** out);
+tcks_status tcks_batch_wait(tcks_batch* b, int64_t timeout_ns);
+void tcks_batch_free(tcks_batch* b);
 /* The batch captured once as a CUDA graph (after one eager run that builds the key tables) and
  * replayed by tcks_batch_graph_run on jobs[0].ctx's stream over the same buffers. Every context
  * must use the library's own pool allocator (UNSUPPORTED otherwise). launches: kernels per replay. */
@@ -437,9 +486,9 @@ tcks_status tcks_profile_read(uint32_t idx, const char** name, uint64_t* launche
  * tcks_calibrate_butterflies). */
 tcks_status tcks_profile_read_ops(uint32_t idx, double* algo_ops);
 
-/* ---------------------------------------- ciphertext arrays: CKKSTensor storage (§2.2) ---- */
+/* ---------------------------------------- ciphertext arrays: CKKSTensor storage (§2.3) ---- */
 /* TenSEAL's CKKSTensor holds an N-dimensional tensor as a tensor of ciphertexts, with optionally one
- * axis batched into the slots (§2.2). A tcks_cta is the storage of such a tensor: `count`
+ * axis batched into the slots (§2.3). A tcks_cta is the storage of such a tensor: `count`
  * ciphertexts of one level and scale in one device allocation [count][2][level][N] (ciphertext i at
  * i * 2 * level * N words), so that each operation below is one batched pass over all of them. The
  * tensor's shape, broadcasting and axes are the caller's (the Python CKKSTensor). Every array
@@ -489,15 +538,15 @@ tcks_status tcks_cta_polyval(const tcks_cta* a, const double* coeffs, uint32_t n
 tcks_status tcks_cta_rescale(tcks_cta* a);
 tcks_status tcks_cta_mod_switch(tcks_cta* a, uint32_t level);
 
-/* ------------------------------------------------------------- the encrypted CNN (§4) ---- */
-/* The MNIST-shaped network of the paper's evaluation (§4, Table 2): im2col conv with `kernels`
+/* ------------------------------------------------------------- the encrypted CNN (§5) ---- */
+/* The MNIST-shaped network of the paper's evaluation (§5, Table 2): im2col conv with `kernels`
  * kernels of `taps` taps over `windows` windows (§3.2), square, FC (kernels*windows) -> hidden
  * (§3.1), square, FC hidden -> classes. Weights are host doubles: conv_w [kernels][taps], conv_b
  * [kernels], fc1_w [hidden][kernels*windows], fc1_b [hidden], fc2_w [classes][hidden], fc2_b
  * [classes]. All plaintexts are encoded on the device at creation: kernels at level L, channel
  * masks at L-1, FC1 diagonals at L-3, FC2 diagonals at L-5, biases at the scales the schedule
- * reaches from an input at the context scale. Needs L >= 7 data primes (six levels are consumed:
- * the paper's "6 multiplications"), power-of-two FC sizes, classes <= hidden <= kernels*windows. */
+ * reaches from an input at the context scale. Needs L >= 7 data primes (six levels are consumed,
+ * the six multiplications the paper counts), power-of-two FC sizes, classes <= hidden <= kernels*windows. */
 typedef struct tcks_cnn tcks_cnn;
 tcks_status tcks_cnn_create(tcks_ctx* ctx, const double* conv_w, const double* conv_b, uint32_t kernels,
                             uint32_t taps, uint32_t windows, const double* fc1_w, const double* fc1_b, uint32_t hidden,
@@ -529,7 +578,7 @@ tcks_status tcks_cnn_forward_host(const tcks_cnn* m, const uint64_t* host_in, ui
  * tcks_ct_serialize / tcks_ct_serialize_seeded. */
 tcks_status tcks_cnn_wire_sizes(const tcks_cnn* m, uint64_t* in_full, uint64_t* in_seeded, uint64_t* out_size);
 /* The batched forward pass on serialized ciphertexts, the client-server exchange of an encrypted
- * evaluation (§4): host_in holds count inputs back to back, each in_size bytes (in_full or in_seeded of
+ * evaluation (§5): host_in holds count inputs back to back, each in_size bytes (in_full or in_seeded of
  * tcks_cnn_wire_sizes; all of that one kind, level L, the context scale); host_out receives count
  * serialized outputs, each out_size bytes (kind 0, level L-6, the model's output scale). One
  * host-to-device copy of the bytes, the residues unpacked and c1 regenerated from its seed on the
@@ -554,7 +603,7 @@ tcks_status tcks_cnn_export_plaintext(const tcks_cnn* m, uint32_t kind, uint32_t
                                       size_t n_words, uint32_t* level, double* scale);
 
 /* ------------------------------------------------------------------------------ serving ---- */
-/* A serving loop for encrypted inference requests (the paper's client-server setting, §2 and §4,
+/* A serving loop for encrypted inference requests (the paper's client-server setting, §2 and §5,
  * with requests of several parameter sizes on one GPU). Lanes are models on their contexts: a CNN
  * (five stages) or a vector x plain matrix (one stage). Requests are queued on submit (the server
  * keeps a device copy of the input) and admitted in arrival order while the HBM budget (every

@@ -57,6 +57,7 @@ def lib():
         "orc_decode_sum": (None, [vp, _dblp, ctypes.c_double, u32, _dblp]),
         "orc_encrypt": (None, [vp, _u64p, _u64p, u32, u64, _u64p]),
         "orc_decrypt": (None, [vp, _u64p, _u64p, u32, _u64p]),
+        "orc_decrypt_sized": (None, [vp, _u64p, _u64p, u32, u32, _u64p]),
         "orc_sample_sym_a": (None, [vp, u32, u64, _u64p]),
         "orc_encrypt_symmetric": (None, [vp, _u64p, _u64p, u32, u64, u64, _u64p]),
         "orc_relinearize_rescale": (None, [vp, _u64p, u32, _u64p, u32, _u64p]),
@@ -68,8 +69,10 @@ def lib():
         "orc_mul_plain": (None, [vp, _u64p, _u64p, u32, _u64p]),
         "orc_tensor": (None, [vp, _u64p, _u64p, u32, _u64p]),
         "orc_rescale": (None, [vp, _u64p, u32, _u64p]),
+        "orc_rescale_polys": (None, [vp, _u64p, u32, u32, _u64p]),
+        "orc_mul_plain_polys": (None, [vp, _u64p, _u64p, u32, u32, _u64p]),
         "orc_modup": (None, [vp, _u64p, u32, _u64p]),
-        "orc_encode_ext": (i32, [vp, _dblp, u32, ctypes.c_double, u32, _u64p]),
+        "orc_encode_ext": (i32, [vp, _dblp, u32, ctypes.c_double, u32, _dblp, _u64p]),
         "orc_vecmat_dh": (None, [vp, _u64p, _u64p, u32, u32, _u64p, ctypes.POINTER(_u64p), _u32p, _u32p, _u64p]),
         "orc_vecmat_dh_rs": (None, [vp, _u64p, _u64p, u32, u32, _u64p, ctypes.POINTER(_u64p), _u32p, _u32p, _u64p]),
         "orc_keyswitch_digits": (None, [vp, _u64p, u32, _u64p, u32, u32, _u64p]),
@@ -77,6 +80,16 @@ def lib():
         "orc_relinearize": (None, [vp, _u64p, u32, _u64p, u32, _u64p]),
         "orc_rotate": (None, [vp, _u64p, u32, u32, _u64p, u32, _u64p]),
         "orc_rotate_from_digits": (None, [vp, _u64p, _u64p, u32, u32, _u64p, u32, _u64p]),
+        "orc_ctx_new_hybrid": (vp, [u32, _u64p, u32, u32]),
+        "orc_keygen_switch_hyb": (None, [vp, u64, u64, _u64p, _u64p, u32, u32, _u64p]),
+        "orc_keygen_relin_hyb": (None, [vp, u64, _u64p, u32, u32, _u64p]),
+        "orc_keygen_galois_hyb": (None, [vp, u64, _u64p, u32, u32, u32, _u64p]),
+        "orc_modup_hyb": (None, [vp, _u64p, u32, u32, _u64p]),
+        "orc_keyswitch_digits_hyb": (None, [vp, _u64p, u32, u32, _u64p, u32, u32, _u64p]),
+        "orc_keyswitch_hyb": (None, [vp, _u64p, u32, u32, _u64p, u32, _u64p]),
+        "orc_relinearize_hyb": (None, [vp, _u64p, u32, u32, _u64p, u32, _u64p]),
+        "orc_rotate_hyb": (None, [vp, _u64p, u32, u32, u32, _u64p, u32, _u64p]),
+        "orc_rotate_from_digits_hyb": (None, [vp, _u64p, _u64p, u32, u32, u32, _u64p, u32, _u64p]),
         "orc_max_threads": (i32, []),
         "orc_set_threads": (None, [i32]),
     }
@@ -192,7 +205,8 @@ class Pt:
 
 @dataclass
 class SwitchKey:
-    """A switching key [K][2][K+1][N] of level K (limb K is the special prime)."""
+    """A switching key of level K: [K][2][K+1][N] (limb K is the special prime), or with hybrid key
+    switching [ceil(K/alpha)][2][K+n_special][N] (limbs K.. are the special primes)."""
     data: np.ndarray
     level: int
 
@@ -204,18 +218,27 @@ class OracleCKKS:
     and the context-wide default scale.
     """
 
-    def __init__(self, log_n: int, bits, scale: float, key_seed: int = 0x7E5EA1, primes=None):
+    def __init__(self, log_n: int, bits, scale: float, key_seed: int = 0x7E5EA1, primes=None, n_special: int = 1,
+                 alpha: int = 1):
+        """n_special > 1 or alpha > 1: hybrid key switching (reading A26) with digits of `alpha` data
+        primes and the last `n_special` primes of the chain as the special primes."""
         self.log_n = log_n
         self.N = 1 << log_n
         self.slots = self.N // 2
         self.primes = list(primes) if primes is not None else gen_primes(log_n, bits)
         self.q = self.primes
-        self.L = len(self.primes) - 1
+        self.K = int(n_special)
+        self.alpha = int(alpha)
+        self.hybrid = self.K > 1 or self.alpha > 1
+        self.L = len(self.primes) - self.K
         self.Pspecial = self.primes[-1]
         self.scale = float(scale)
         self.key_seed = key_seed
         arr = np.array(self.primes, dtype=np.uint64)
-        self._ctx = lib().orc_ctx_new(log_n, P(arr), len(self.primes))
+        if self.hybrid:
+            self._ctx = lib().orc_ctx_new_hybrid(log_n, P(arr), len(self.primes), self.K)
+        else:
+            self._ctx = lib().orc_ctx_new(log_n, P(arr), len(self.primes))
         if not self._ctx:
             raise ValueError("a prime of the chain has no primitive 2N-th root")
         self.s = None
@@ -232,15 +255,25 @@ class OracleCKKS:
     def keygen(self, relin_level: int | None = None):
         """Secret, public and relinearization keys from the context seed (§2.1)."""
         N, L = self.N, self.L
-        self.s = np.zeros((L + 1, N), dtype=np.uint64)
+        self.s = np.zeros((len(self.primes), N), dtype=np.uint64)
         lib().orc_keygen_secret(self._ctx, self.key_seed, P(self.s))
         self.pk = np.zeros((2, L, N), dtype=np.uint64)
         lib().orc_keygen_public(self._ctx, self.key_seed, P(self.s), P(self.pk))
         K = L if relin_level is None else relin_level
-        rlk = np.zeros((K, 2, K + 1, N), dtype=np.uint64)
-        lib().orc_keygen_relin(self._ctx, self.key_seed, P(self.s), K, P(rlk))
+        rlk = np.zeros(self.switch_key_shape(K), dtype=np.uint64)
+        if self.hybrid:
+            lib().orc_keygen_relin_hyb(self._ctx, self.key_seed, P(self.s), self.alpha, K, P(rlk))
+        else:
+            lib().orc_keygen_relin(self._ctx, self.key_seed, P(self.s), K, P(rlk))
         self.rlk = SwitchKey(rlk, K)
         return self
+
+    def digits(self, level: int) -> int:
+        """Key-switching digits at `level`: one per data prime, or ceil(level / alpha) (hybrid)."""
+        return -(-level // self.alpha)
+
+    def switch_key_shape(self, key_level: int) -> tuple:
+        return (self.digits(key_level), 2, key_level + self.K, self.N)
 
     def galois_elt(self, step: int) -> int:
         return int(lib().orc_galois_elt(self._ctx, step))
@@ -249,8 +282,11 @@ class OracleCKKS:
         """Galois key for a left rotation by `step` slots, trimmed to `key_level` (default L)."""
         K = self.L if key_level is None else key_level
         g = self.galois_elt(step)
-        gk = np.zeros((K, 2, K + 1, self.N), dtype=np.uint64)
-        lib().orc_keygen_galois(self._ctx, self.key_seed, P(self.s), g, K, P(gk))
+        gk = np.zeros(self.switch_key_shape(K), dtype=np.uint64)
+        if self.hybrid:
+            lib().orc_keygen_galois_hyb(self._ctx, self.key_seed, P(self.s), g, self.alpha, K, P(gk))
+        else:
+            lib().orc_keygen_galois(self._ctx, self.key_seed, P(self.s), g, K, P(gk))
         self.galois[step % self.slots] = SwitchKey(gk, K)
         return self.galois[step % self.slots]
 
@@ -280,6 +316,15 @@ class OracleCKKS:
             row = np.ascontiguousarray(out[l])
             lib().orc_intt_limb(self._ctx, P(row), l)
             out[l] = row
+        return out
+
+    def intt_rows(self, limbs: np.ndarray, chain_idx) -> np.ndarray:
+        """Inverse NTT of rows [k][N], row r modulo the chain's prime chain_idx[r] (P is index L)."""
+        out = np.array(limbs, dtype=np.uint64, copy=True).reshape(len(chain_idx), self.N)
+        for r, l in enumerate(chain_idx):
+            row = np.ascontiguousarray(out[r])
+            lib().orc_intt_limb(self._ctx, P(row), l)
+            out[r] = row
         return out
 
     def crt_compose(self, coeffs: np.ndarray, level: int) -> list[int]:
@@ -335,8 +380,13 @@ class OracleCKKS:
         return a
 
     def decrypt(self, ct: Ct) -> Pt:
+        """m = c0 + c1 s (O11); a three-component ciphertext (an unrelinearized product) adds c2 s^2."""
         pt = np.zeros((ct.level, self.N), dtype=np.uint64)
-        lib().orc_decrypt(self._ctx, P(self.s), P(np.ascontiguousarray(ct.data)), ct.level, P(pt))
+        size = ct.data.shape[0]
+        if size == 2:
+            lib().orc_decrypt(self._ctx, P(self.s), P(np.ascontiguousarray(ct.data)), ct.level, P(pt))
+        else:
+            lib().orc_decrypt_sized(self._ctx, P(self.s), P(np.ascontiguousarray(ct.data)), ct.level, size, P(pt))
         return Pt(pt, ct.level, ct.scale)
 
     def encrypt_values(self, z, seed: int, level: int | None = None) -> Ct:
@@ -353,21 +403,34 @@ class OracleCKKS:
         if a.scale != b.scale:
             raise ValueError("scale mismatch")
 
+    def _same_size(self, a: Ct, b: Ct) -> tuple[np.ndarray, np.ndarray]:
+        """Both operands' components, the shorter one padded with zero polynomials (a missing
+        component of a ciphertext is the zero polynomial: m = sum_k c_k s^k)."""
+        k = max(a.data.shape[0], b.data.shape[0])
+
+        def pad(x):
+            if x.shape[0] == k:
+                return np.ascontiguousarray(x)
+            return np.ascontiguousarray(np.concatenate([x, np.zeros((k - x.shape[0],) + x.shape[1:], np.uint64)]))
+        return pad(a.data), pad(b.data)
+
     def add(self, a: Ct, b: Ct) -> Ct:
         self._check_pair(a, b)
-        out = np.zeros_like(a.data)
-        lib().orc_add(self._ctx, P(a.data), P(b.data), a.level, 2, P(out))
+        x, y = self._same_size(a, b)
+        out = np.zeros_like(x)
+        lib().orc_add(self._ctx, P(x), P(y), a.level, x.shape[0], P(out))
         return Ct(out, a.level, a.scale)
 
     def sub(self, a: Ct, b: Ct) -> Ct:
         self._check_pair(a, b)
-        out = np.zeros_like(a.data)
-        lib().orc_sub(self._ctx, P(a.data), P(b.data), a.level, 2, P(out))
+        x, y = self._same_size(a, b)
+        out = np.zeros_like(x)
+        lib().orc_sub(self._ctx, P(x), P(y), a.level, x.shape[0], P(out))
         return Ct(out, a.level, a.scale)
 
     def negate(self, a: Ct) -> Ct:
         out = np.zeros_like(a.data)
-        lib().orc_negate(self._ctx, P(a.data), a.level, 2, P(out))
+        lib().orc_negate(self._ctx, P(np.ascontiguousarray(a.data)), a.level, a.data.shape[0], P(out))
         return Ct(out, a.level, a.scale)
 
     def _plain_for(self, ct: Ct, pt: Pt) -> np.ndarray:
@@ -378,20 +441,27 @@ class OracleCKKS:
     def add_plain(self, ct: Ct, pt: Pt) -> Ct:
         if pt.scale != ct.scale:
             raise ValueError("scale mismatch")
-        out = np.zeros_like(ct.data)
-        lib().orc_add_plain(self._ctx, P(ct.data), P(self._plain_for(ct, pt)), ct.level, P(out))
+        out = np.array(ct.data, copy=True)  # a third component is unchanged
+        lib().orc_add_plain(self._ctx, P(np.ascontiguousarray(ct.data[:2])), P(self._plain_for(ct, pt)), ct.level,
+                            P(out[:2]))
         return Ct(out, ct.level, ct.scale)
 
     def sub_plain(self, ct: Ct, pt: Pt) -> Ct:
         if pt.scale != ct.scale:
             raise ValueError("scale mismatch")
-        out = np.zeros_like(ct.data)
-        lib().orc_sub_plain(self._ctx, P(ct.data), P(self._plain_for(ct, pt)), ct.level, P(out))
+        out = np.array(ct.data, copy=True)
+        lib().orc_sub_plain(self._ctx, P(np.ascontiguousarray(ct.data[:2])), P(self._plain_for(ct, pt)), ct.level,
+                            P(out[:2]))
         return Ct(out, ct.level, ct.scale)
 
     def mul_plain(self, ct: Ct, pt: Pt) -> Ct:
         out = np.zeros_like(ct.data)
-        lib().orc_mul_plain(self._ctx, P(ct.data), P(self._plain_for(ct, pt)), ct.level, P(out))
+        polys = ct.data.shape[0]
+        if polys == 2:
+            lib().orc_mul_plain(self._ctx, P(ct.data), P(self._plain_for(ct, pt)), ct.level, P(out))
+        else:
+            lib().orc_mul_plain_polys(self._ctx, P(np.ascontiguousarray(ct.data)), P(self._plain_for(ct, pt)), ct.level,
+                                      polys, P(out))
         return Ct(out, ct.level, ct.scale * pt.scale)
 
     def tensor(self, a: Ct, b: Ct) -> tuple[np.ndarray, int, float]:
@@ -404,11 +474,18 @@ class OracleCKKS:
 
     def relinearize(self, d3: np.ndarray, level: int, scale: float) -> Ct:
         out = np.zeros((2, level, self.N), dtype=np.uint64)
-        lib().orc_relinearize(self._ctx, P(np.ascontiguousarray(d3)), level, P(self.rlk.data), self.rlk.level, P(out))
+        if self.hybrid:
+            lib().orc_relinearize_hyb(self._ctx, P(np.ascontiguousarray(d3)), level, self.alpha, P(self.rlk.data),
+                                      self.rlk.level, P(out))
+        else:
+            lib().orc_relinearize(self._ctx, P(np.ascontiguousarray(d3)), level, P(self.rlk.data), self.rlk.level,
+                                  P(out))
         return Ct(out, level, scale)
 
     def relinearize_rescale(self, d3: np.ndarray, level: int, scale: float) -> Ct:
         """Relinearization and rescale with one rounding (reading A25): [2][level-1][N]."""
+        if self.hybrid:
+            raise NotImplementedError("the merged rounding is defined for one special prime and one-prime digits")
         out = np.zeros((2, level - 1, self.N), dtype=np.uint64)
         lib().orc_relinearize_rescale(self._ctx, P(np.ascontiguousarray(d3)), level, P(self.rlk.data), self.rlk.level,
                                       P(out))
@@ -418,8 +495,12 @@ class OracleCKKS:
         """Divide by the last prime with rounding (O14)."""
         if ct.level < 2:
             raise ValueError("level exhausted")
-        out = np.zeros((2, ct.level - 1, self.N), dtype=np.uint64)
-        lib().orc_rescale(self._ctx, P(np.ascontiguousarray(ct.data)), ct.level, P(out))
+        polys = ct.data.shape[0]
+        out = np.zeros((polys, ct.level - 1, self.N), dtype=np.uint64)
+        if polys == 2:
+            lib().orc_rescale(self._ctx, P(np.ascontiguousarray(ct.data)), ct.level, P(out))
+        else:  # every component of a three-component ciphertext on its own
+            lib().orc_rescale_polys(self._ctx, P(np.ascontiguousarray(ct.data)), ct.level, polys, P(out))
         return Ct(out, ct.level - 1, ct.scale / float(self.q[ct.level - 1]))
 
     def mod_switch(self, ct: Ct, level: int) -> Ct:
@@ -430,12 +511,21 @@ class OracleCKKS:
         """enc x enc multiply with the context's auto relinearize / rescale policy (§2.1); merged: the
         relinearization's ModDown and the rescale as one rounding (A25)."""
         d3, level, scale = self.tensor(a, b)
+        if not relin:  # the three-component product, rescaled component by component if asked
+            ct = Ct(d3, level, scale)
+            return self.rescale(ct) if rescale else ct
         if merged and rescale:
             if level < 2:
                 raise ValueError("level exhausted")
             return self.relinearize_rescale(d3, level, scale)
         ct = self.relinearize(d3, level, scale)
         return self.rescale(ct) if rescale else ct
+
+    def relinearize_ct(self, ct: Ct) -> Ct:
+        """A three-component ciphertext relinearized to two (O17); a two-component one is returned as is."""
+        if ct.data.shape[0] == 2:
+            return ct
+        return self.relinearize(ct.data, ct.level, ct.scale)
 
     def square(self, a: Ct) -> Ct:
         return self.mul(a, a)
@@ -517,14 +607,25 @@ class OracleCKKS:
             return Ct(ct.data.copy(), ct.level, ct.scale)
         key = self._key(step)
         out = np.zeros_like(ct.data)
-        lib().orc_rotate(self._ctx, P(ct.data), ct.level, self.galois_elt(step), P(key.data), key.level, P(out))
+        if self.hybrid:
+            lib().orc_rotate_hyb(self._ctx, P(np.ascontiguousarray(ct.data)), ct.level, self.alpha, self.galois_elt(step),
+                                 P(key.data), key.level, P(out))
+        else:
+            lib().orc_rotate(self._ctx, P(ct.data), ct.level, self.galois_elt(step), P(key.data), key.level, P(out))
         return Ct(out, ct.level, ct.scale)
 
     def modup(self, ct: Ct) -> np.ndarray:
-        """Digits of c1 for hoisted rotations: [level][level+1][N]."""
-        d = np.zeros((ct.level, ct.level + 1, self.N), dtype=np.uint64)
-        c1 = np.ascontiguousarray(ct.data[1])
-        lib().orc_modup(self._ctx, P(c1), ct.level, P(d))
+        """Digits of c1 for hoisted rotations: [level][level+1][N], or [ceil(level/alpha)][level+K][N]."""
+        return self.modup_poly(np.ascontiguousarray(ct.data[1]), ct.level)
+
+    def modup_poly(self, x: np.ndarray, level: int) -> np.ndarray:
+        """ModUp (O16) of one NTT-form polynomial [level][N]."""
+        d = np.zeros((self.digits(level), level + self.K, self.N), dtype=np.uint64)
+        x = np.ascontiguousarray(x, dtype=np.uint64)
+        if self.hybrid:
+            lib().orc_modup_hyb(self._ctx, P(x), level, self.alpha, P(d))
+        else:
+            lib().orc_modup(self._ctx, P(x), level, P(d))
         return d
 
     def rotate_from_digits(self, ct: Ct, digits: np.ndarray, step: int) -> Ct:
@@ -532,8 +633,12 @@ class OracleCKKS:
             return Ct(ct.data.copy(), ct.level, ct.scale)
         key = self._key(step)
         out = np.zeros_like(ct.data)
-        lib().orc_rotate_from_digits(self._ctx, P(ct.data), P(digits), ct.level, self.galois_elt(step),
-                                     P(key.data), key.level, P(out))
+        if self.hybrid:
+            lib().orc_rotate_from_digits_hyb(self._ctx, P(np.ascontiguousarray(ct.data)), P(digits), ct.level,
+                                             self.alpha, self.galois_elt(step), P(key.data), key.level, P(out))
+        else:
+            lib().orc_rotate_from_digits(self._ctx, P(ct.data), P(digits), ct.level, self.galois_elt(step),
+                                         P(key.data), key.level, P(out))
         return Ct(out, ct.level, ct.scale)
 
     def rotate_hoisted(self, ct: Ct, steps) -> list[Ct]:
@@ -543,7 +648,22 @@ class OracleCKKS:
 
     def keyswitch(self, x: np.ndarray, level: int, key: SwitchKey) -> np.ndarray:
         out = np.zeros((2, level, self.N), dtype=np.uint64)
-        lib().orc_keyswitch(self._ctx, P(np.ascontiguousarray(x)), level, P(key.data), key.level, P(out))
+        if self.hybrid:
+            lib().orc_keyswitch_hyb(self._ctx, P(np.ascontiguousarray(x)), level, self.alpha, P(key.data), key.level,
+                                    P(out))
+        else:
+            lib().orc_keyswitch(self._ctx, P(np.ascontiguousarray(x)), level, P(key.data), key.level, P(out))
+        return out
+
+    def keyswitch_digits(self, digits: np.ndarray, level: int, key: SwitchKey, g: int = 1) -> np.ndarray:
+        """The inner product of (automorphed) digits with a key and the ModDown: [2][level][N]."""
+        out = np.zeros((2, level, self.N), dtype=np.uint64)
+        if self.hybrid:
+            lib().orc_keyswitch_digits_hyb(self._ctx, P(np.ascontiguousarray(digits)), level, self.alpha,
+                                           P(key.data), key.level, g, P(out))
+        else:
+            lib().orc_keyswitch_digits(self._ctx, P(np.ascontiguousarray(digits)), level, P(key.data), key.level, g,
+                                       P(out))
         return out
 
     # ---------------------------------------------------------------- composite schedules ----
@@ -589,15 +709,17 @@ class OracleCKKS:
     def encode_matrix(self, M: np.ndarray, level: int) -> list[Pt]:
         return [self.encode(d, level=level) for d in self.matrix_diagonals(np.asarray(M, dtype=np.float64))]
 
-    def encode_ext(self, z, level: int, scale: float | None = None) -> np.ndarray:
-        """Encode (O9) over the extended basis: [level+1][N], limbs q_0..q_{level-1} then P."""
+    def encode_ext(self, z, level: int, scale: float | None = None, want_pre: bool = False):
+        """Encode (O9) over the extended basis: [level+1][N], limbs q_0..q_{level-1} then P (and the
+        pre-rounding scale*m_i if asked)."""
         z = np.ascontiguousarray(z, dtype=np.float64)
         scale = self.scale if scale is None else float(scale)
         out = np.zeros((level + 1, self.N), dtype=np.uint64)
-        st = lib().orc_encode_ext(self._ctx, P(z), len(z), scale, level, P(out))
+        pre = np.zeros(self.N, dtype=np.float64)
+        st = lib().orc_encode_ext(self._ctx, P(z), len(z), scale, level, P(pre), P(out))
         if st:
             raise ValueError(f"encode_ext failed ({st})")
-        return out
+        return (out, pre) if want_pre else out
 
     @staticmethod
     def rect_width(m: int) -> int:
@@ -869,7 +991,7 @@ class OracleCKKS:
 
 @dataclass
 class CNNWeights:
-    """Weights of the MNIST-shaped network of §4: conv 4x7x7 stride 3, square, FC 256->64, square,
+    """Weights of the MNIST-shaped network of §5: conv 4x7x7 stride 3, square, FC 256->64, square,
     FC 64->10."""
     conv_w: np.ndarray  # [4][49]
     conv_b: np.ndarray  # [4]
@@ -938,6 +1060,19 @@ def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64, classes=
     return need
 
 
+def cnn_mask_slots(o: OracleCKKS, k: int, windows: int, nb: int, pack_first: bool) -> np.ndarray:
+    """The 0/1 mask that selects kernel k's output for the pack: its own block of windows, or, when the
+    channels are packed before the giant steps, the windows-blocks k + nb g (what the giant-step sum
+    gathers into block k)."""
+    mask = np.zeros(o.slots)
+    if pack_first:
+        blk = np.arange(o.slots) // windows
+        mask[blk % nb == k] = 1.0
+    else:
+        mask[k * windows: (k + 1) * windows] = 1.0
+    return mask
+
+
 def cnn_encode(o: OracleCKKS, w: CNNWeights, windows=64, rect=False, conv_hoist=False,
                conv_shared=False, pack_first=False) -> EncodedCNN:
     L = o.L
@@ -949,13 +1084,7 @@ def cnn_encode(o: OracleCKKS, w: CNNWeights, windows=64, rect=False, conv_hoist=
         if conv_shared:
             e.conv_baby_ext.append(o.conv_baby_diagonals_ext(o.kernel_slots(w.conv_w[k], windows), e.taps,
                                                              windows, L))
-        mask = np.zeros(o.slots)
-        if pack_first:  # the windows-blocks k + nb g: what the giant-step sum gathers into block k
-            blk = np.arange(o.slots) // windows
-            mask[blk % nb == k] = 1.0
-        else:
-            mask[k * windows: (k + 1) * windows] = 1.0
-        e.masks.append(o.encode(mask, level=L - 1))
+        e.masks.append(o.encode(cnn_mask_slots(o, k, windows, nb, pack_first), level=L - 1))
     if rect:
         e.fc1 = o.encode_matrix_rect(w.fc1_w.T, L - 3)
         e.fc2 = o.encode_matrix_rect(w.fc2_w.T, L - 5)
@@ -980,9 +1109,37 @@ def _pack(o: OracleCKKS, chans, masks, merged: bool) -> Ct:
     return o.rescale(v) if merged else v
 
 
+def cnn_bias_slots(o: OracleCKKS, w: CNNWeights, enc: EncodedCNN) -> list[np.ndarray]:
+    """The three bias vectors as slot values, laid out where the schedule's ciphertexts hold the
+    layers' outputs: the conv bias on each kernel's block of windows (repeated with the packed
+    vector's period when the channels are packed before the giant steps), the FC biases in the first
+    m slots (repeated with period rect_width(m) in the rectangular form, whose outputs come out
+    replicated)."""
+    W = enc.windows
+    K = len(w.conv_b)
+    b0 = np.zeros(o.slots)
+    if enc.pack_first:
+        baby, _ = o.conv_bsgs_steps(enc.taps, W)
+        period = (len(baby) + 1) * W
+        for r in range(o.slots // period):
+            for k in range(K):
+                b0[r * period + k * W: r * period + (k + 1) * W] = w.conv_b[k]
+    else:
+        for k in range(K):
+            b0[k * W: (k + 1) * W] = w.conv_b[k]
+    out = [b0]
+    for b in (w.fc1_b, w.fc2_b):
+        v = np.zeros(o.slots)
+        v[:len(b)] = b
+        if enc.rect:
+            v = np.resize(v[:o.rect_width(len(b))], o.slots)
+        out.append(v)
+    return out
+
+
 def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: dict | None = None,
                 double_hoist: bool = False, merged: bool = False) -> Ct:
-    """The encrypted CNN schedule (§4): conv (im2col, one multiplication per kernel) -> pack the
+    """The encrypted CNN schedule (§5): conv (im2col, one multiplication per kernel) -> pack the
     four channel outputs with masks -> square -> FC1 (vector x plain matrix) -> square -> FC2.
     Six multiplicative levels; biases are added as plaintexts at the ciphertext's scale and level.
     double_hoist: the two vector x matrix products take the ModDown once after their rotation sums."""
@@ -996,7 +1153,7 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
     W = enc.windows
     K = len(enc.conv)
     period = None
-    bias = np.zeros(o.slots)
+    bias, b1, b2 = cnn_bias_slots(o, w, enc)
     if enc.pack_first:
         # baby-step sums z_k, masks on the blocks k + B g, the pack, then one giant-step sum: block k of
         # the result gathers blocks k + B g of z_k, the full tap sum of kernel k (reading A23)
@@ -1009,9 +1166,6 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
         v = _pack(o, zs, enc.masks, merged)
         v = o.rotsum_dh(v, giant)
         period = (len(baby) + 1) * W  # blocks [K, B) are zero, the pattern repeats every B blocks
-        for r in range(o.slots // period):
-            for k in range(K):
-                bias[r * period + k * W: r * period + (k + 1) * W] = w.conv_b[k]
     else:
         if enc.conv_shared:
             chans = [o.conv2d_im2col_shared(ct, enc.conv_baby_ext[k], enc.taps, W) for k in range(K)]
@@ -1019,8 +1173,6 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
             conv = o.conv2d_im2col_hoisted if enc.conv_hoist else o.conv2d_im2col_pt
             chans = [conv(ct, enc.conv[k], enc.taps, W) for k in range(K)]
         v = _pack(o, chans, enc.masks, merged)
-        for k in range(K):
-            bias[k * W: (k + 1) * W] = w.conv_b[k]
     if trace is not None:
         trace["bias_scales"] = [v.scale]
     def bias_pt(i, values, v):
@@ -1032,20 +1184,12 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
     v = o.mul(v, v, merged=merged)
     n1, m1 = w.fc1_w.shape[1], w.fc1_w.shape[0]
     v = fc(v, enc.fc1, enc.fc1_ext, n1, m1, period=period)
-    b1 = np.zeros(o.slots)
-    b1[:m1] = w.fc1_b
-    if enc.rect:  # FC1's output is replicated with period rect_width(m1): so is its bias
-        b1 = np.resize(b1[:o.rect_width(m1)], o.slots)
     if trace is not None:
         trace["bias_scales"].append(v.scale)
     v = o.add_plain(v, bias_pt(1, b1, v))
     v = o.mul(v, v, merged=merged)
     n2, m2 = w.fc2_w.shape[1], w.fc2_w.shape[0]
     v = fc(v, enc.fc2, enc.fc2_ext, n2, m2, replicate=not enc.rect)
-    b2 = np.zeros(o.slots)
-    b2[:m2] = w.fc2_b
-    if enc.rect:
-        b2 = np.resize(b2[:o.rect_width(m2)], o.slots)
     if trace is not None:
         trace["bias_scales"].append(v.scale)
     v = o.add_plain(v, bias_pt(2, b2, v))

@@ -324,7 +324,8 @@ struct OrcCtx {
   u32 log_n;
   u64 n;
   u32 L;                 // number of data primes
-  std::vector<u64> q;    // size L + 1; q[L] = P
+  u32 K = 1;             // number of special primes (hybrid key switching: K > 1 allowed)
+  std::vector<u64> q;    // size L + K; q[L] = P when K = 1, else the special primes p_0..p_{K-1}
   std::vector<u64> psi;  // smallest primitive 2N-th root per prime
   std::vector<std::vector<u64>> tw, itw;
 };
@@ -396,6 +397,17 @@ OrcCtx* orc_ctx_new(u32 log_n, const u64* primes, u32 n_primes) {
   return c;
 }
 
+// A chain for hybrid key switching: n_primes - n_special data primes, then the n_special special
+// primes whose product is P.
+OrcCtx* orc_ctx_new_hybrid(u32 log_n, const u64* primes, u32 n_primes, u32 n_special) {
+  if (n_special < 1 || n_primes <= n_special) return nullptr;
+  OrcCtx* c = orc_ctx_new(log_n, primes, n_primes);
+  if (!c) return nullptr;
+  c->L = n_primes - n_special;
+  c->K = n_special;
+  return c;
+}
+
 void orc_ctx_free(OrcCtx* c) { delete c; }
 
 u64 orc_ctx_psi(const OrcCtx* c, u32 mod_idx) { return c->psi[mod_idx]; }
@@ -438,11 +450,11 @@ void orc_automorphism_coeff(const OrcCtx* c, const u64* a, u64 q, u32 g, u64* ou
 //   switching key for `kind` (0 = relinearization, otherwise the Galois element g), digit j:
 //   a_j: (kind << 32) | 0x80000000 | (2j), e_j: (kind << 32) | 0x80000000 | (2j + 1).
 
-// s ternary; stored in NTT form over all L + 1 primes.
+// s ternary; stored in NTT form over every prime of the chain (L + 1, or L + K for hybrid chains).
 void orc_keygen_secret(const OrcCtx* c, u64 seed, u64* s) {
   std::vector<int64_t> v(c->n);
   for (u64 i = 0; i < c->n; ++i) v[i] = sample_ternary(seed, 1, i);
-  for (u32 l = 0; l <= c->L; ++l) signed_to_ntt(c, v.data(), l, limb(s, c->n, l));
+  for (u32 l = 0; l < (u32)c->q.size(); ++l) signed_to_ntt(c, v.data(), l, limb(s, c->n, l));
 }
 
 // pk = (-a*s + e, a) over the data primes; a sampled uniformly per limb directly in NTT form.
@@ -565,11 +577,11 @@ int orc_encode(const OrcCtx* c, const double* z, u32 n_in, double scale, u32 lev
 
 // The same plaintext over the extended basis: limbs q_0..q_{level-1}, then the special prime P
 // (limb `level`) -- the same integer polynomial, as the double-hoisted product needs.
-int orc_encode_ext(const OrcCtx* c, const double* z, u32 n_in, double scale, u32 level, u64* pt) {
+int orc_encode_ext(const OrcCtx* c, const double* z, u32 n_in, double scale, u32 level, double* pre, u64* pt) {
   const u64 n = c->n;
   if (n_in > n / 2 || level < 1 || level > c->L) return -1;
   std::vector<int64_t> p(n);
-  const int status = encode_coeffs(c, z, n_in, scale, nullptr, p.data());
+  const int status = encode_coeffs(c, z, n_in, scale, pre, p.data());
   if (status) return status;
   for (u32 l = 0; l < level; ++l) signed_to_ntt(c, p.data(), l, limb(pt, n, l));
   signed_to_ntt(c, p.data(), c->L, limb(pt, n, level));
@@ -667,6 +679,25 @@ void orc_decrypt(const OrcCtx* c, const u64* s, const u64* ct, u32 level, u64* p
   }
 }
 
+// Decryption of a ciphertext of `size` components (size 3 = an unrelinearized product, whose third
+// component pairs with s^2): m = sum_k c_k s^k, limb by limb in NTT form.
+void orc_decrypt_sized(const OrcCtx* c, const u64* s, const u64* ct, u32 level, u32 size, u64* pt) {
+  const u64 n = c->n;
+  for (u32 l = 0; l < level; ++l) {
+    const u64 q = c->q[l];
+    const u64* sl = limb(s, n, l);
+    u64* m = limb(pt, n, l);
+    for (u64 i = 0; i < n; ++i) {
+      u64 acc = limb(ct, n, l)[i], sk = sl[i];
+      for (u32 k = 1; k < size; ++k) {
+        acc = addm(acc, mulm(limb(ct, n, (u64)k * level + l)[i], sk, q), q);
+        sk = mulm(sk, sl[i], q);
+      }
+      m[i] = acc;
+    }
+  }
+}
+
 // ------------------------------------------------------------- element-wise ops (O12, O13) ---
 // All take n_polys polynomials of `level` limbs laid out back to back.
 
@@ -712,9 +743,15 @@ void orc_sub_plain(const OrcCtx* c, const u64* ct, const u64* pt, u32 level, u64
     for (u64 i = 0; i < n; ++i) out[l * n + i] = subm(ct[l * n + i], pt[l * n + i], c->q[l]);
 }
 
+void orc_mul_plain_polys(const OrcCtx* c, const u64* ct, const u64* pt, u32 level, u32 polys, u64* out);
 void orc_mul_plain(const OrcCtx* c, const u64* ct, const u64* pt, u32 level, u64* out) {
+  orc_mul_plain_polys(c, ct, pt, level, 2, out);
+}
+
+// Every one of `polys` components times the plaintext.
+void orc_mul_plain_polys(const OrcCtx* c, const u64* ct, const u64* pt, u32 level, u32 polys, u64* out) {
   const u64 n = c->n;
-  for (u32 p = 0; p < 2; ++p)
+  for (u32 p = 0; p < polys; ++p)
     for (u32 l = 0; l < level; ++l)
       for (u64 i = 0; i < n; ++i) {
         const u64 k = ((u64)p * level + l) * n + i;
@@ -743,11 +780,15 @@ void orc_tensor(const OrcCtx* c, const u64* a, const u64* b, u32 level, u64* out
 // ----------------------------------------------------------------- rescale (O14) ---------------
 // c'_i = (c_i - (bal(c_{ell-1}) mod q_i)) * q_{ell-1}^-1 mod q_i, i < ell-1, for both components;
 // the correction term is lifted in the coefficient domain and NTT'd per target prime.
-void orc_rescale(const OrcCtx* c, const u64* ct, u32 level, u64* out) {
+void orc_rescale_polys(const OrcCtx* c, const u64* ct, u32 level, u32 polys, u64* out);
+void orc_rescale(const OrcCtx* c, const u64* ct, u32 level, u64* out) { orc_rescale_polys(c, ct, level, 2, out); }
+
+// Rescale (O14) of `polys` polynomials [polys][level][N] -> [polys][level-1][N], each on its own.
+void orc_rescale_polys(const OrcCtx* c, const u64* ct, u32 level, u32 polys, u64* out) {
   const u64 n = c->n;
   const u32 last = level - 1;
   const u64 ql = c->q[last];
-  for (u32 p = 0; p < 2; ++p) {
+  for (u32 p = 0; p < polys; ++p) {
     std::vector<u64> top(limb(ct, n, (u64)p * level + last), limb(ct, n, (u64)p * level + last) + n);
     intt_mod(c, top.data(), last);
 #pragma omp parallel for schedule(static)
@@ -1055,6 +1096,231 @@ void orc_set_threads(int n) {
 #else
   (void)n;
 #endif
+}
+
+
+// ----------------------------------------------------- hybrid key switching (reading A26) ------
+// The generalisation of O16-O18 to digits of alpha data primes and K special primes P = p_0 ...
+// p_{K-1} (the hybrid key switching of Han and Ki, CT-RSA 2020, on the RNS variant of Cheon, Han,
+// Kim, Kim and Song, SAC 2018). Digit j at level ell covers the data primes G_j = {q_i : j alpha <= i
+// < min((j+1) alpha, ell)}, Q_j their product; dnum(ell) = ceil(ell / alpha) digits. Chain layout:
+// q_0..q_{L-1}, then p_0..p_{K-1} (chain indices L..L+K-1). With alpha = 1 and K = 1 every function
+// below computes exactly what its one-prime counterpart above computes.
+//   switching key of level Kt:  [dnum(Kt)][2][Kt + K][N], limb slot t < Kt is q_t, slot Kt + k is p_k;
+//   digits at level ell:        [dnum(ell)][ell + K][N], slot t < ell is q_t, slot ell + k is p_k.
+
+namespace {
+
+u32 hyb_digits(u32 level, u32 alpha) { return (level + alpha - 1) / alpha; }
+
+// Chain index of limb slot t in a layout of `data` data limbs followed by the K special primes.
+u32 hyb_chain(const OrcCtx* c, u32 t, u32 data) { return t < data ? t : c->L + (t - data); }
+
+// The product of the special primes modulo q: P mod q.
+u64 special_product_mod(const OrcCtx* c, u64 q) {
+  u64 r = 1 % q;
+  for (u32 k = 0; k < c->K; ++k) r = mulm(r, c->q[c->L + k] % q, q);
+  return r;
+}
+
+}  // namespace
+
+// Switching key from s' to s (O6 generalised): for digit j < dnum(Kt) and limb slot t,
+//   b_j[t] = -a_j[t] s[t] + e_j[t] + [t is a data prime of G_j] * (P mod q_t) * s'[t],
+// a_j uniform per limb, e_j CBD; the stream tags of O6 (digit index j). s and s' are NTT form over all
+// L + K primes.
+void orc_keygen_switch_hyb(const OrcCtx* c, u64 seed, u64 kind, const u64* s, const u64* s_prime, u32 alpha,
+                           u32 key_level, u64* ksk) {
+  const u32 Kt = key_level, slots = key_level + c->K, dn = hyb_digits(key_level, alpha);
+  const u64 n = c->n;
+#pragma omp parallel for schedule(dynamic)
+  for (int jj = 0; jj < (int)dn; ++jj) {
+    const u32 j = (u32)jj;
+    const u64 tag_a = (kind << 32) | 0x80000000ull | (2ull * j);
+    const u64 tag_e = (kind << 32) | 0x80000000ull | (2ull * j + 1);
+    std::vector<int64_t> e(n);
+    for (u64 i = 0; i < n; ++i) e[i] = sample_cbd(seed, tag_e, i);
+    std::vector<u64> et(n);
+    for (u32 t = 0; t < slots; ++t) {
+      const u32 l = hyb_chain(c, t, Kt);
+      const u64 q = c->q[l];
+      signed_to_ntt(c, e.data(), l, et.data());
+      u64* b0 = ksk + (((u64)j * 2 + 0) * slots + t) * n;
+      u64* b1 = ksk + (((u64)j * 2 + 1) * slots + t) * n;
+      const u64* sl = limb(s, n, l);
+      const u64* spl = limb(s_prime, n, l);
+      const bool in_group = l < c->L && l / alpha == j;
+      const u64 gadget = in_group ? special_product_mod(c, q) : 0;
+      for (u64 i = 0; i < n; ++i) {
+        const u64 a = sample_uniform(seed, tag_a, i, l, q);
+        b1[i] = a;
+        u64 v = addm(negm(mulm(a, sl[i], q), q), et[i], q);
+        if (in_group) v = addm(v, mulm(gadget, spl[i], q), q);
+        b0[i] = v;
+      }
+    }
+  }
+}
+
+void orc_keygen_relin_hyb(const OrcCtx* c, u64 seed, const u64* s, u32 alpha, u32 key_level, u64* ksk) {
+  const u32 nm = (u32)c->q.size();
+  std::vector<u64> s2((u64)nm * c->n);
+  for (u32 l = 0; l < nm; ++l)
+    for (u64 i = 0; i < c->n; ++i) s2[l * c->n + i] = mulm(s[l * c->n + i], s[l * c->n + i], c->q[l]);
+  orc_keygen_switch_hyb(c, seed, 0, s, s2.data(), alpha, key_level, ksk);
+}
+
+void orc_keygen_galois_hyb(const OrcCtx* c, u64 seed, const u64* s, u32 g, u32 alpha, u32 key_level, u64* ksk) {
+  const u32 nm = (u32)c->q.size();
+  std::vector<u64> sg((u64)nm * c->n);
+  orc_automorphism_ntt(c, s, nm, g, sg.data());
+  orc_keygen_switch_hyb(c, seed, g, s, sg.data(), alpha, key_level, ksk);
+}
+
+// ModUp (O16 generalised) of x [level][N] (NTT form): for digit j, with x_i the coefficient form of
+// limb i and i in G_j,
+//   y_i = bal( x_i * [(Q_j / q_i)^-1]_{q_i} mod q_i ),
+//   D_j = sum_{i in G_j} y_i * (Q_j / q_i)                (an integer polynomial, |D_j| <= |G_j| Q_j / 2),
+// the fast base conversion with balanced terms; D_j mod q_t for every slot t outside G_j (the other
+// data primes below `level` and the special primes), NTT form; slot t inside G_j is x_t itself.
+void orc_modup_hyb(const OrcCtx* c, const u64* x, u32 level, u32 alpha, u64* digits) {
+  const u64 n = c->n;
+  const u32 slots = level + c->K, dn = hyb_digits(level, alpha);
+  std::vector<std::vector<u64>> coef(level);
+#pragma omp parallel for schedule(dynamic)
+  for (int ii = 0; ii < (int)level; ++ii) {
+    coef[ii].assign(limb(x, n, ii), limb(x, n, ii) + n);
+    intt_mod(c, coef[ii].data(), (u32)ii);
+  }
+#pragma omp parallel for collapse(2) schedule(dynamic)
+  for (int jj = 0; jj < (int)dn; ++jj)
+    for (int tt = 0; tt < (int)slots; ++tt) {
+      const u32 j = (u32)jj, t = (u32)tt;
+      const u32 g0 = j * alpha, g1 = std::min((j + 1) * alpha, level);
+      u64* out = digits + ((u64)j * slots + t) * n;
+      if (t >= g0 && t < g1) {  // a prime of the digit itself: the input limb
+        std::memcpy(out, limb(x, n, t), sizeof(u64) * n);
+        continue;
+      }
+      const u32 l = hyb_chain(c, t, level);
+      const u64 qt = c->q[l];
+      for (u64 k = 0; k < n; ++k) out[k] = 0;
+      for (u32 i = g0; i < g1; ++i) {
+        const u64 qi = c->q[i];
+        u64 hat_i = 1 % qi, hat_t = 1 % qt;  // Q_j / q_i modulo q_i and modulo q_t
+        for (u32 m = g0; m < g1; ++m)
+          if (m != i) {
+            hat_i = mulm(hat_i, c->q[m] % qi, qi);
+            hat_t = mulm(hat_t, c->q[m] % qt, qt);
+          }
+        const u64 inv_i = invm(hat_i, qi);
+        for (u64 k = 0; k < n; ++k) {
+          const int64_t y = balanced(mulm(coef[i][k], inv_i, qi), qi);
+          out[k] = addm(out[k], mulm(from_signed(y, qt), hat_t, qt), qt);
+        }
+      }
+      ntt_mod(c, out, l);
+    }
+}
+
+// Inner product of (optionally automorphed) digits with a switching key of level key_level >= level,
+// then ModDown by P (O16 generalised): for b = 0, 1 and every slot t < level + K,
+//   u_b[t] = sum_{j < dnum(level)} tau_g(D_j)[t] * ksk_j[b][t'],  t' = t (data) or key_level + k (p_k);
+// then with z_k the coefficient form of u_b[p_k] and
+//   w_k = bal( z_k * [(P / p_k)^-1]_{p_k} mod p_k ),   C_b = sum_k w_k * (P / p_k)   (|C_b| <= K P / 2),
+//   out_b[i] = (u_b[i] - (C_b mod q_i)) * P^-1 mod q_i,  i < level.
+void orc_keyswitch_digits_hyb(const OrcCtx* c, const u64* digits, u32 level, u32 alpha, const u64* ksk,
+                              u32 key_level, u32 g, u64* out) {
+  const u64 n = c->n;
+  const u32 K = c->K, slots = level + K, kslots = key_level + K, dn = hyb_digits(level, alpha);
+  const std::vector<u32> src = automorphism_index(c, g);
+  std::vector<u64> u((u64)2 * slots * n);
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int b = 0; b < 2; ++b)
+    for (int tt = 0; tt < (int)slots; ++tt) {
+      const u32 t = (u32)tt;
+      const u32 l = hyb_chain(c, t, level);
+      const u32 key_slot = t < level ? t : key_level + (t - level);
+      const u64 q = c->q[l];
+      u64* acc = u.data() + ((u64)b * slots + t) * n;
+      for (u64 k = 0; k < n; ++k) acc[k] = 0;
+      for (u32 j = 0; j < dn; ++j) {
+        const u64* dj = digits + ((u64)j * slots + t) * n;
+        const u64* kj = ksk + (((u64)j * 2 + (u64)b) * kslots + key_slot) * n;
+        for (u64 k = 0; k < n; ++k) acc[k] = addm(acc[k], mulm(dj[src[k]], kj[k], q), q);
+      }
+    }
+  for (u32 b = 0; b < 2; ++b) {
+    // w_k for every special prime, as signed coefficients
+    std::vector<std::vector<int64_t>> w(K, std::vector<int64_t>(n));
+    for (u32 k = 0; k < K; ++k) {
+      const u64 pk = c->q[c->L + k];
+      std::vector<u64> z(u.data() + ((u64)b * slots + level + k) * n, u.data() + ((u64)b * slots + level + k + 1) * n);
+      intt_mod(c, z.data(), c->L + k);
+      u64 hat = 1 % pk;  // P / p_k modulo p_k
+      for (u32 m = 0; m < K; ++m)
+        if (m != k) hat = mulm(hat, c->q[c->L + m] % pk, pk);
+      const u64 inv = invm(hat, pk);
+      for (u64 e = 0; e < n; ++e) w[k][e] = balanced(mulm(z[e], inv, pk), pk);
+    }
+#pragma omp parallel for schedule(static)
+    for (int ii = 0; ii < (int)level; ++ii) {
+      const u32 i = (u32)ii;
+      const u64 q = c->q[i];
+      std::vector<u64> t(n, 0);
+      for (u32 k = 0; k < K; ++k) {
+        u64 hat = 1 % q;  // P / p_k modulo q_i
+        for (u32 m = 0; m < K; ++m)
+          if (m != k) hat = mulm(hat, c->q[c->L + m] % q, q);
+        for (u64 e = 0; e < n; ++e) t[e] = addm(t[e], mulm(from_signed(w[k][e], q), hat, q), q);
+      }
+      ntt_mod(c, t.data(), i);
+      const u64 pinv = invm(special_product_mod(c, q), q);
+      const u64* ui = u.data() + ((u64)b * slots + i) * n;
+      u64* dst = out + ((u64)b * level + i) * n;
+      for (u64 e = 0; e < n; ++e) dst[e] = mulm(subm(ui[e], t[e], q), pinv, q);
+    }
+  }
+}
+
+void orc_keyswitch_hyb(const OrcCtx* c, const u64* x, u32 level, u32 alpha, const u64* ksk, u32 key_level, u64* out) {
+  std::vector<u64> digits((u64)hyb_digits(level, alpha) * (level + c->K) * c->n);
+  orc_modup_hyb(c, x, level, alpha, digits.data());
+  orc_keyswitch_digits_hyb(c, digits.data(), level, alpha, ksk, key_level, 1, out);
+}
+
+// Relinearization (O17) with the hybrid key switch: (d0 + KS(d2)_0, d1 + KS(d2)_1).
+void orc_relinearize_hyb(const OrcCtx* c, const u64* d, u32 level, u32 alpha, const u64* rlk, u32 key_level,
+                         u64* out) {
+  const u64 n = c->n;
+  std::vector<u64> ks((u64)2 * level * n);
+  orc_keyswitch_hyb(c, d + (u64)2 * level * n, level, alpha, rlk, key_level, ks.data());
+  orc_add(c, d, ks.data(), level, 2, out);
+}
+
+// Rotation (O18) with the hybrid key switch: (tau_g(c0) + KS(tau_g(c1))_0, KS(tau_g(c1))_1).
+void orc_rotate_hyb(const OrcCtx* c, const u64* ct, u32 level, u32 alpha, u32 g, const u64* gk, u32 key_level,
+                    u64* out) {
+  const u64 n = c->n;
+  std::vector<u64> t((u64)2 * level * n);
+  orc_automorphism_ntt(c, ct, 2 * level, g, t.data());
+  std::vector<u64> ks((u64)2 * level * n);
+  orc_keyswitch_hyb(c, t.data() + (u64)level * n, level, alpha, gk, key_level, ks.data());
+  orc_add(c, t.data(), ks.data(), level, 1, out);
+  std::memcpy(out + (u64)level * n, ks.data() + (u64)level * n, sizeof(u64) * level * n);
+}
+
+// Hoisted rotation: the digits of c1 (orc_modup_hyb) computed once, the automorphism applied to them
+// inside the inner product.
+void orc_rotate_from_digits_hyb(const OrcCtx* c, const u64* ct, const u64* digits, u32 level, u32 alpha, u32 g,
+                                const u64* gk, u32 key_level, u64* out) {
+  const u64 n = c->n;
+  std::vector<u64> ks((u64)2 * level * n);
+  orc_keyswitch_digits_hyb(c, digits, level, alpha, gk, key_level, g, ks.data());
+  std::vector<u64> c0g((u64)level * n);
+  orc_automorphism_ntt(c, ct, level, g, c0g.data());
+  orc_add(c, c0g.data(), ks.data(), level, 1, out);
+  std::memcpy(out + (u64)level * n, ks.data() + (u64)level * n, sizeof(u64) * level * n);
 }
 
 }  // extern "C"

@@ -1,4 +1,4 @@
-"""Oracle of TenSEAL's CKKSTensor (§2.2): an N-dimensional tensor of reals encrypted as a tensor of
+"""Oracle of TenSEAL's CKKSTensor (§2.3): an N-dimensional tensor of reals encrypted as a tensor of
 ciphertexts, with optionally the first axis batched into the slots. Written plainly as loops over the
 per-ciphertext oracle operations of ckks.py, in the order the tensor operations define them.
 

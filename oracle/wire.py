@@ -1,7 +1,7 @@
 """Wire format of a ciphertext (TEST INFRASTRUCTURE ONLY: the oracle of the library's serializer).
 
 The paper reports the communication of one encrypted inference (encrypted input plus encrypted output,
-§4). A ciphertext travels as residues packed with exactly bit_length(q_i) bits each:
+§5). A ciphertext travels as residues packed with exactly bit_length(q_i) bits each:
 
   header (16 bytes, little-endian): b"TCKS", version 1 (u8), kind 0 = ciphertext (u8), log2 N (u8),
   level (u8), scale (f64);

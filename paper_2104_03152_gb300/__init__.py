@@ -54,6 +54,8 @@ _SIGS = {
     "tcks_last_error_detail": (ctypes.c_char_p, []),
     "tcks_params_create": (ctypes.c_int32, [ctypes.c_uint32, _u32p, ctypes.c_uint32, ctypes.c_double, _vpp]),
     "tcks_params_create_primes": (ctypes.c_int32, [ctypes.c_uint32, _u64p, ctypes.c_uint32, ctypes.c_double, _vpp]),
+    "tcks_params_create_hybrid": (ctypes.c_int32, [ctypes.c_uint32, _u64p, ctypes.c_uint32, ctypes.c_uint32,
+                                                   ctypes.c_uint32, ctypes.c_double, _vpp]),
     "tcks_params_free": (None, [_vp]),
     "tcks_params_primes": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32]),
     "tcks_context_create": (ctypes.c_int32, [_vp, ctypes.c_uint64, ctypes.c_uint32, _vp, _vp, _vpp]),
@@ -73,6 +75,9 @@ _SIGS = {
     "tcks_decrypt": (ctypes.c_int32, [_vp, _vp, _vpp]),
     "tcks_ct_import": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, ctypes.c_double, _vpp]),
     "tcks_ct_export": (ctypes.c_int32, [_vp, _u64p, ctypes.c_size_t]),
+    "tcks_ct_import_sized": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_double, _vpp]),
+    "tcks_ct_size": (ctypes.c_int32, [_vp, _u32p]),
+    "tcks_relinearize": (ctypes.c_int32, [_vp]),
     "tcks_pt_import": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, ctypes.c_double, _vpp]),
     "tcks_pt_export": (ctypes.c_int32, [_vp, _u64p, ctypes.c_size_t]),
     "tcks_ct_info": (ctypes.c_int32, [_vp, _u32p, _dblp]),
@@ -177,6 +182,9 @@ _SIGS = {
     "tcks_ct_serialize_seeded": (ctypes.c_int32, [_vp, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64, _u64p]),
     "tcks_rotate_sum_hoisted": (ctypes.c_int32, [_vp, _i32p, ctypes.c_uint32, _vpp]),
     "tcks_batch_run": (ctypes.c_int32, [_vp, ctypes.c_uint32]),
+    "tcks_batch_submit": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vpp]),
+    "tcks_batch_wait": (ctypes.c_int32, [_vp, ctypes.c_int64]),
+    "tcks_batch_free": (None, [_vp]),
     "tcks_batch_graph_create": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vpp]),
     "tcks_batch_graph_run": (ctypes.c_int32, [_vp]),
     "tcks_batch_graph_launches": (ctypes.c_int32, [_vp, _u64p]),
@@ -269,11 +277,22 @@ def _p(a: np.ndarray):
 
 class Params:
     """CKKS parameters: N = 2^log_n and the prime chain (data primes, then P), chosen from bit sizes
-    (`bits`) or given explicitly (`primes`)."""
+    (`bits`) or given explicitly (`primes`). n_special > 1 or alpha > 1: hybrid key switching with the
+    last n_special primes special and digits of alpha data primes (tcks_params_create_hybrid)."""
 
-    def __init__(self, log_n: int, bits=None, scale: float = 2.0 ** 40, primes=None):
+    def __init__(self, log_n: int, bits=None, scale: float = 2.0 ** 40, primes=None, n_special: int = 1,
+                 alpha: int = 1):
         h = _vp()
-        if primes is not None:
+        self.n_special, self.alpha = int(n_special), int(alpha)
+        if self.n_special > 1 or self.alpha > 1:
+            if primes is None:  # the chain from bit sizes, then its primes
+                tmp = Params(log_n, bits, scale)
+                primes = tmp.primes
+            q_in = np.ascontiguousarray([int(x) for x in primes], dtype=np.uint64)
+            check(lib().tcks_params_create_hybrid(log_n, _p(q_in), len(q_in), self.n_special, self.alpha,
+                                                  float(scale), ctypes.byref(h)))
+            bits = [int(x).bit_length() for x in primes]
+        elif primes is not None:
             q_in = np.ascontiguousarray([int(x) for x in primes], dtype=np.uint64)
             check(lib().tcks_params_create_primes(log_n, _p(q_in), len(q_in), float(scale), ctypes.byref(h)))
             bits = [int(x).bit_length() for x in primes]
@@ -329,7 +348,7 @@ class Context:
         self.N = params.N
         self.slots = params.N // 2
         self.primes = params.primes
-        self.L = len(params.primes) - 1
+        self.L = len(params.primes) - params.n_special
         self.stream = stream  # the cudaStream_t handle given by the caller (None: the context's own)
         self._alloc_keep = None
         aptr = None
@@ -370,18 +389,23 @@ class Context:
         st = lib().tcks_has_galois_key(self.h, step, ctypes.byref(v))
         return v.value if st == 0 else None
 
+    def _switch_key_shape(self, K: int):
+        """[digits][2][K + special primes][N] for a switching key of level K."""
+        a, sp = self.params.alpha, self.params.n_special
+        return (-(-K // a), 2, K + sp, self.N)
+
     def _key_shape(self, kind: int, step: int):
         N, L = self.N, self.L
         if kind == KEY_SECRET:
-            return (L + 1, N)
+            return (L + self.params.n_special, N)
         if kind == KEY_PUBLIC:
             return (2, L, N)
         if kind == KEY_RELIN:
-            return (L, 2, L + 1, N)
+            return self._switch_key_shape(L)
         K = self.galois_key_level(step)
         if K is None:
             raise KeyError(step)
-        return (K, 2, K + 1, N)
+        return self._switch_key_shape(K)
 
     def export_key(self, kind: int, step: int = 0) -> np.ndarray:
         a = np.zeros(self._key_shape(kind, step), dtype=np.uint64)
@@ -428,10 +452,14 @@ class Context:
         return self.decode(self.decrypt(ct), n)
 
     def ct_import(self, limbs: np.ndarray, scale: float) -> "Ciphertext":
+        """A ciphertext from host limbs [size][level][N] (size 2, or 3 for an unrelinearized product)."""
         a = np.ascontiguousarray(limbs, dtype=np.uint64)
-        level = a.shape[1]
+        size, level = a.shape[0], a.shape[1]
         h = _vp()
-        check(lib().tcks_ct_import(self.h, _p(a), level, float(scale), ctypes.byref(h)))
+        if size == 2:
+            check(lib().tcks_ct_import(self.h, _p(a), level, float(scale), ctypes.byref(h)))
+        else:
+            check(lib().tcks_ct_import_sized(self.h, _p(a), size, level, float(scale), ctypes.byref(h)))
         return Ciphertext(self, h)
 
     def ct_import_batch(self, limbs: np.ndarray, scale: float) -> list:
@@ -600,8 +628,15 @@ class Ciphertext:
         check(lib().tcks_ct_serialize_seeded(self.h, seed_a, buf, int(size[0]), _p(written)))
         return buf.raw[: int(written[0])]
 
+    @property
+    def size(self) -> int:
+        """Components: 2, or 3 for an enc x enc product taken without automatic relinearization."""
+        v = ctypes.c_uint32()
+        check(lib().tcks_ct_size(self.h, ctypes.byref(v)))
+        return v.value
+
     def export(self) -> np.ndarray:
-        a = np.zeros((2, self.level, self.ctx.N), dtype=np.uint64)
+        a = np.zeros((self.size, self.level, self.ctx.N), dtype=np.uint64)
         check(lib().tcks_ct_export(self.h, _p(a), a.size))
         return a
 
@@ -647,6 +682,11 @@ class Ciphertext:
         """sum_i coeffs[i] x^i element-wise (lowest degree first); result at the context scale."""
         a = np.ascontiguousarray(coeffs, dtype=np.float64)
         return self._unary(lib().tcks_polyval, _p(a), len(a))
+
+    def relinearize_(self):
+        """Relinearize in place (three components -> two); a two-component ciphertext is unchanged."""
+        check(lib().tcks_relinearize(self.h))
+        return self
 
     def rescale_(self):
         check(lib().tcks_rescale(self.h))
@@ -715,7 +755,7 @@ def polyval_batch(cts, coeffs) -> list:
 
 
 class CNN:
-    """The encrypted MNIST-shaped network of §4 (conv -> square -> FC -> square -> FC)."""
+    """The encrypted MNIST-shaped network of §5 (conv -> square -> FC -> square -> FC)."""
 
     def __init__(self, ctx: Context, conv_w, conv_b, fc1_w, fc1_b, fc2_w, fc2_b, windows: int = 64):
         arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (conv_w, conv_b, fc1_w, fc1_b, fc2_w, fc2_b)]
@@ -821,6 +861,26 @@ def batch_run(jobs):
     context stream)."""
     arr = _job_array(jobs)
     check(lib().tcks_batch_run(arr, len(jobs)))
+
+
+class Batch:
+    """A submitted job table with a completion handle (tcks_batch_submit / tcks_batch_wait)."""
+
+    def __init__(self, jobs):
+        self._ctxs = [j[0] for j in jobs]
+        arr = _job_array(jobs)
+        h = _vp()
+        check(lib().tcks_batch_submit(arr, len(jobs), ctypes.byref(h)))
+        self.h = h
+
+    def wait(self, timeout_ns: int = -1):
+        """Waits up to timeout_ns (negative: without limit); raises TcksError TIMEOUT if not done."""
+        check(lib().tcks_batch_wait(self.h, int(timeout_ns)))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().tcks_batch_free(self.h)
+            self.h = None
 
 
 class BatchGraph:

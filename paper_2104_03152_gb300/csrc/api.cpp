@@ -2,6 +2,7 @@
 // kernels into the CKKSVector operations of TenSEAL (§2-§3).
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <vector>
@@ -61,6 +62,50 @@ tcks_ct* new_ct(tcks_ctx* c, u32 level, double scale) {
   return ct;
 }
 
+tcks_ct* new_ct_sized(tcks_ctx* c, u32 size, u32 level, double scale) {
+  DevBuf b(c, (size_t)size * level * c->N);
+  tcks_ct* ct = new tcks_ct{c, b.release(), level, scale, size};
+  ctx_retain(c);
+  return ct;
+}
+
+u64 ksk_words(const tcks_ctx* c, u32 Kt) {
+  if (!c->hyb) return (u64)Kt * 2 * (Kt + 1) * c->N;
+  return (u64)((Kt + c->alpha - 1) / c->alpha) * 2 * (Kt + c->K) * c->N;
+}
+
+u64 ks_digit_words(const tcks_ctx* c, u32 ell) {
+  if (!c->hyb) return (u64)ell * (ell + 1) * c->N;
+  return (u64)((ell + c->alpha - 1) / c->alpha) * (ell + c->K) * c->N;
+}
+
+u64 ks_top_words(const tcks_ctx* c) { return (u64)2 * c->K * c->N; }
+
+void ks_modup(tcks_ctx* c, const u64* x, u64 x_stride, u32 count, u32 ell, u64* coef_tmp, u64* digits) {
+  if (c->hyb)
+    launch_modup_hyb(c->T, c->H, x, x_stride, count, ell, coef_tmp, digits, c->stream);
+  else
+    launch_modup(c->T, x, x_stride, count, ell, coef_tmp, digits, c->stream);
+}
+
+void ks_switch(tcks_ctx* c, u32 ell, const KsPlan& plan) {
+  if (c->hyb)
+    launch_keyswitch_hyb(c->T, c->H, ell, plan, c->stream);
+  else
+    launch_keyswitch(c->T, ell, plan, c->stream);
+}
+
+void need_one_prime_ks(const tcks_ctx* c, const char* what) {
+  if (c && c->hyb)
+    fail(TCKS_ERR_UNSUPPORTED, std::string(what) + " is written for the one-prime key switch (alpha = 1, one special "
+                               "prime); this context uses hybrid key switching");
+}
+
+void need_relinearized(const tcks_ct* ct) {
+  if (ct && ct->size != 2)
+    fail(TCKS_ERR_INVALID_ARG, "a three-component ciphertext must be relinearized first (tcks_relinearize)");
+}
+
 tcks_pt* new_pt(tcks_ctx* c, u32 level, double scale) {
   DevBuf b(c, pt_words(c, level));
   tcks_pt* pt = new tcks_pt{c, b.release(), level, scale};
@@ -97,6 +142,13 @@ const GaloisKey& galois_key_for(tcks_ctx* c, int64_t step, u32 ell) {
     fail(TCKS_ERR_LEVEL_EXHAUSTED, "Galois key for step " + std::to_string(k) + " is trimmed to level " +
                                        std::to_string(it->second.K) + " < " + std::to_string(ell));
   return it->second;
+}
+
+void op_rescale_polys(tcks_ctx* c, const u64* in, u32 ell, u32 polys, u64* out) {
+  if (ell < 2) fail(TCKS_ERR_LEVEL_EXHAUSTED, "rescale needs level >= 2");
+  DevBuf top(c, (size_t)polys * c->N);
+  launch_rescale(c->T, in, ell, polys, top.p, out, c->stream);
+  check_launch("rescale");
 }
 
 void op_rescale(tcks_ctx* c, const u64* in, u32 ell, u64* out, u32 count) {
@@ -138,13 +190,14 @@ const KeyTable& key_table(tcks_ctx* c, const std::vector<u32>& steps, u32 ell) {
 void op_relinearize(tcks_ctx* c, const u64* d3, u32 ell, u64* out, u32 count) {
   const size_t n = c->N;
   const KeyTable& kt = key_table(c, {0u}, ell);
-  DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n), top(c, (size_t)count * 2 * n);
+  const u64 dw = ks_digit_words(c, ell);
+  DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * dw), top(c, (size_t)count * ks_top_words(c));
   const u64 d3_stride = (u64)3 * ell * n;
-  launch_modup(c->T, d3 + (size_t)2 * ell * n, d3_stride, count, ell, coef.p, digits.p, c->stream);
+  ks_modup(c, d3 + (size_t)2 * ell * n, d3_stride, count, ell, coef.p, digits.p);
   KsPlan p{};
   p.keys = kt.d;
   p.digits = digits.p;
-  p.digits_b = (u64)ell * (ell + 1) * n;
+  p.digits_b = dw;
   p.top = top.p;
   p.out = out;
   p.out_b = (u64)2 * ell * n;
@@ -156,13 +209,19 @@ void op_relinearize(tcks_ctx* c, const u64* d3, u32 ell, u64* out, u32 count) {
   p.R = 1;
   p.B = count;
   p.add_perm = 0;
-  launch_keyswitch(c->T, ell, p, c->stream);
+  ks_switch(c, ell, p);
   check_launch("relinearize");
 }
 
 void op_relin_rescale(tcks_ctx* c, const u64* d3, u32 ell, u64* out, u32 count) {
   if (ell < 2) fail(TCKS_ERR_LEVEL_EXHAUSTED, "rescale needs level >= 2");
   const size_t n = c->N;
+  if (c->hyb) {  // the merged rounding is written for one special prime: relinearize, then rescale
+    DevBuf rel(c, (size_t)count * ct_words(c, ell));
+    op_relinearize(c, d3, ell, rel.p, count);
+    op_rescale(c, rel.p, ell, out, count);
+    return;
+  }
   const KeyTable& kt = key_table(c, {0u}, ell);
   DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
   DevBuf top(c, (size_t)count * 2 * n), top2(c, (size_t)count * 2 * n);
@@ -194,13 +253,14 @@ void op_rotate_add(tcks_ctx* c, u64* base, u64 stride, u32 count, u32 ell, int32
     return;
   }
   const KeyTable& kt = key_table(c, {k}, ell);
-  DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
-  DevBuf tmp(c, (size_t)count * ct_words(c, ell)), top(c, (size_t)count * 2 * n);
-  launch_modup(c->T, base + (size_t)ell * n, stride, count, ell, coef.p, digits.p, c->stream);
+  const u64 dw = ks_digit_words(c, ell);
+  DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * dw);
+  DevBuf tmp(c, (size_t)count * ct_words(c, ell)), top(c, (size_t)count * ks_top_words(c));
+  ks_modup(c, base + (size_t)ell * n, stride, count, ell, coef.p, digits.p);
   KsPlan p{};
   p.keys = kt.d;
   p.digits = digits.p;
-  p.digits_b = (u64)ell * (ell + 1) * n;
+  p.digits_b = dw;
   p.top = top.p;
   p.out = tmp.p;
   p.out_b = ct_words(c, ell);
@@ -209,7 +269,7 @@ void op_rotate_add(tcks_ctx* c, u64* base, u64 stride, u32 count, u32 ell, int32
   p.R = 1;
   p.B = count;
   p.add_perm = 1;
-  launch_keyswitch(c->T, ell, p, c->stream);
+  ks_switch(c, ell, p);
   if (stride == ct_words(c, ell)) {
     launch_elementwise(c->T, OP_ADD, base, tmp.p, base, ell, 2 * count, c->stream);
   } else {
@@ -237,9 +297,9 @@ void op_rotate_hoisted(tcks_ctx* c, const u64* ct, u32 ell, const int32_t* steps
   if (ks.empty()) return;
   const KeyTable& kt = key_table(c, ks, ell);
   const u32 R = (u32)ks.size();
-  DevBuf coef(c, (size_t)ell * n), digits(c, (size_t)ell * (ell + 1) * n);
-  DevBuf tmp(c, (size_t)R * ct_words(c, ell)), top(c, (size_t)R * 2 * n);
-  launch_modup(c->T, ct + (size_t)ell * n, 0, 1, ell, coef.p, digits.p, c->stream);
+  DevBuf coef(c, (size_t)ell * n), digits(c, (size_t)ks_digit_words(c, ell));
+  DevBuf tmp(c, (size_t)R * ct_words(c, ell)), top(c, (size_t)R * ks_top_words(c));
+  ks_modup(c, ct + (size_t)ell * n, 0, 1, ell, coef.p, digits.p);
   KsPlan p{};
   p.keys = kt.d;
   p.digits = digits.p;
@@ -250,7 +310,7 @@ void op_rotate_hoisted(tcks_ctx* c, const u64* ct, u32 ell, const int32_t* steps
   p.R = R;
   p.B = 1;
   p.add_perm = 1;
-  launch_keyswitch(c->T, ell, p, c->stream);
+  ks_switch(c, ell, p);
   for (u32 r = 0; r < R; ++r)
     check_cuda(cudaMemcpyAsync(outs[where[r]], tmp.p + (size_t)r * ct_words(c, ell), ct_words(c, ell) * 8,
                                cudaMemcpyDeviceToDevice, c->stream),
@@ -305,8 +365,8 @@ void tcks_ctx::keys_changed() {
 tcks::u64 tcks_ctx::key_bytes() const {
   u64 b = 0;
   const u64 n = N;
-  b += (u64)(L + 1) * n * 8 + (u64)2 * L * n * 8 + (u64)L * 2 * (L + 1) * n * 8;
-  for (const auto& kv : galois) b += (u64)kv.second.K * 2 * (kv.second.K + 1) * n * 8;
+  b += (u64)(L + K) * n * 8 + (u64)2 * L * n * 8 + ksk_words(this, L) * 8;
+  for (const auto& kv : galois) b += ksk_words(this, kv.second.K) * 8;
   return b;
 }
 
@@ -377,6 +437,49 @@ tcks_status tcks_params_create_primes(uint32_t log_n, const uint64_t* primes, ui
   TCKS_API_END
 }
 
+tcks_status tcks_params_create_hybrid(uint32_t log_n, const uint64_t* primes, uint32_t n_primes, uint32_t n_special,
+                                      uint32_t alpha, double scale, tcks_params** out) {
+  TCKS_API_BEGIN
+  if (!out || !primes) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (n_special < 1 || n_special > 8 || alpha < 1 || alpha > 8)
+    fail(TCKS_ERR_BAD_PARAMS, "n_special and alpha must be in [1, 8]");
+  if (n_primes <= n_special || n_primes - n_special > CRT_MAXW - 2)
+    fail(TCKS_ERR_BAD_PARAMS, "need 1..32 data primes before the special primes");
+  tcks_params* p = nullptr;
+  const tcks_status st = tcks_params_create_primes(log_n, primes, n_primes - n_special + 1, scale, &p);
+  if (st != TCKS_OK) return st;
+  std::unique_ptr<tcks_params> guard(p);
+  // the whole chain (the special primes too) must be NTT-friendly primes
+  p->chain.assign(primes, primes + n_primes);
+  p->bits.clear();
+  const u64 two_n = 2ull << log_n;
+  for (u32 i = 0; i < n_primes; ++i) {
+    const u64 q = p->chain[i];
+    if (q >= (1ull << 61) || !is_prime_u64(q) || q % two_n != 1)
+      fail(TCKS_ERR_BAD_PARAMS, "prime " + std::to_string(i) + " is not a prime below 2^61 with q == 1 mod 2N");
+    for (u32 j = 0; j < i; ++j)
+      if (p->chain[j] == q) fail(TCKS_ERR_BAD_PARAMS, "prime " + std::to_string(i) + " repeats an earlier one");
+    u32 b = 0;
+    while (b < 64 && (q >> b)) ++b;
+    p->bits.push_back(b);
+  }
+  // P must exceed the product of every digit's primes, or the key-switch error (D_j e_j / P) grows
+  // with the ratio; compared on bit lengths
+  const u32 L = n_primes - n_special;
+  double logP = 0;
+  for (u32 k = 0; k < n_special; ++k) logP += std::log2((double)p->chain[L + k]);
+  for (u32 j = 0; j * alpha < L; ++j) {
+    double logQ = 0;
+    for (u32 i = j * alpha; i < std::min(L, (j + 1) * alpha); ++i) logQ += std::log2((double)p->chain[i]);
+    if (logQ > logP) fail(TCKS_ERR_BAD_PARAMS, "the special primes' product is below digit " + std::to_string(j));
+  }
+  p->n_special = n_special;
+  p->alpha = alpha;
+  *out = guard.release();
+  TCKS_API_END
+}
+
 void tcks_params_free(tcks_params* p) { delete p; }
 
 tcks_status tcks_params_primes(const tcks_params* p, uint64_t* primes, uint32_t capacity) {
@@ -397,7 +500,10 @@ tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32
   c = new tcks_ctx();
   c->params = *params;
   c->N = 1u << params->log_n;
-  c->L = (u32)params->chain.size() - 1;
+  c->K = params->n_special;
+  c->alpha = params->alpha;
+  c->hyb = c->K > 1 || c->alpha > 1;
+  c->L = (u32)params->chain.size() - c->K;
   c->flags = flags;
   c->seed = seed;
   check_cuda(cudaGetDevice(&c->device), "cudaGetDevice");
@@ -419,7 +525,7 @@ tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32
     check_cuda(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold), "mem pool threshold");
   }
   if (!build_tables(params->log_n, params->chain, c->host)) fail(TCKS_ERR_BAD_PARAMS, "a prime has no 2N-th root");
-  const u32 nm = c->L + 1, n = c->N;
+  const u32 nm = c->L + c->K, n = c->N;
   const HostTables& H = c->host;
   c->d_mods = c->dev_alloc(sizeof(ModConst) * nm);
   c->d_pairs = c->dev_alloc(sizeof(PairConst) * nm * nm);
@@ -468,15 +574,25 @@ tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32
   c->T.log_n = params->log_n;
   c->T.n_mods = nm;
   c->T.L = c->L;
+  if (c->hyb) {  // hybrid key-switching constants
+    const std::vector<u64> hv = hyb_constants(params->chain, c->L, c->K, c->alpha, &c->H);
+    c->d_hyb = (u64*)c->dev_alloc(sizeof(u64) * hv.size());
+    check_cuda(cudaMemcpyAsync(c->d_hyb, hv.data(), sizeof(u64) * hv.size(), cudaMemcpyHostToDevice, s), "H2D");
+    hyb_bind(c->d_hyb, &c->H);
+    c->table_bytes += 8 * hv.size();
+  }
   c->F.slot_index = c->d_slot;
   c->F.zeta = c->d_zeta;
   // keys (§2.1): secret, public, relinearization
   c->sk = (u64*)c->dev_alloc(sizeof(u64) * (size_t)nm * n);
   c->pk = (u64*)c->dev_alloc(sizeof(u64) * (size_t)2 * c->L * n);
-  c->rlk = (u64*)c->dev_alloc(sizeof(u64) * (size_t)c->L * 2 * nm * n);
+  c->rlk = (u64*)c->dev_alloc(sizeof(u64) * ksk_words(c, c->L));
   launch_keygen_secret(c->T, seed, c->sk, s);
   launch_keygen_public(c->T, seed, c->sk, c->pk, s);
-  launch_keygen_switch(c->T, seed, 0, c->sk, c->L, c->rlk, s);
+  if (c->hyb)
+    launch_keygen_switch_hyb(c->T, c->H, seed, 0, c->sk, c->L, c->rlk, s);
+  else
+    launch_keygen_switch(c->T, seed, 0, c->sk, c->L, c->rlk, s);
   check_launch("keygen");
   check_cuda(cudaStreamSynchronize(s), "context create");
   *out = c;
@@ -496,7 +612,7 @@ static void ctx_destroy(tcks_ctx* c) {
   c->keys_changed();
   for (auto& kv : c->galois) c->dev_free(kv.second.d);
   void* bufs[] = {c->d_mods, c->d_pairs, c->d_tw,  c->d_tw32, c->d_slot, c->d_zeta,
-                  c->d_qwords, c->d_status, c->sk, c->pk,   c->rlk};
+                  c->d_qwords, c->d_status, c->sk, c->pk,   c->rlk, c->d_hyb};
   for (void* b : bufs) c->dev_free(b);
   cudaStreamSynchronize(c->stream);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -557,8 +673,12 @@ tcks_status tcks_gen_galois_keys(tcks_ctx* c, const int32_t* steps, uint32_t n_s
     }
     GaloisKey gk;
     gk.K = K;
-    gk.d = (u64*)c->dev_alloc(sizeof(u64) * (size_t)K * 2 * (K + 1) * c->N);
-    launch_keygen_switch(c->T, c->seed, (u32)galois_element(c->params.log_n, k), c->sk, K, gk.d, c->stream);
+    gk.d = (u64*)c->dev_alloc(sizeof(u64) * ksk_words(c, K));
+    const u32 g = (u32)galois_element(c->params.log_n, k);
+    if (c->hyb)
+      launch_keygen_switch_hyb(c->T, c->H, c->seed, g, c->sk, K, gk.d, c->stream);
+    else
+      launch_keygen_switch(c->T, c->seed, g, c->sk, K, gk.d, c->stream);
     check_launch("galois keygen");
     c->galois[k] = gk;
   }
@@ -578,14 +698,14 @@ static u64* key_slot(tcks_ctx* c, uint32_t kind, int32_t step, size_t* words, u3
   const size_t n = c->N;
   const u32 L = c->L;
   switch (kind) {
-    case TCKS_KEY_SECRET: *words = (size_t)(L + 1) * n; return c->sk;
+    case TCKS_KEY_SECRET: *words = (size_t)(L + c->K) * n; return c->sk;
     case TCKS_KEY_PUBLIC: *words = (size_t)2 * L * n; return c->pk;
-    case TCKS_KEY_RELIN: *words = (size_t)L * 2 * (L + 1) * n; return c->rlk;
+    case TCKS_KEY_RELIN: *words = ksk_words(c, L); return c->rlk;
     case TCKS_KEY_GALOIS: {
       auto it = c->galois.find(step_mod(c, step));
       if (it == c->galois.end()) fail(TCKS_ERR_NO_GALOIS_KEY, "no Galois key for this step");
       const u32 K = it->second.K;
-      *words = (size_t)K * 2 * (K + 1) * n;
+      *words = ksk_words(c, K);
       if (K_out) *K_out = K;
       return it->second.d;
     }
@@ -613,7 +733,7 @@ tcks_status tcks_import_key(tcks_ctx* c, uint32_t kind, int32_t step, uint32_t k
     if (k == 0) fail(TCKS_ERR_INVALID_ARG, "step 0 has no key");
     const u32 K = key_level == 0 ? c->L : key_level;
     if (K > c->L) fail(TCKS_ERR_INVALID_ARG, "key_level exceeds L");
-    const size_t words = (size_t)K * 2 * (K + 1) * c->N;
+    const size_t words = ksk_words(c, K);
     if (n_words != words) fail(TCKS_ERR_INVALID_ARG, "n_words does not match the key layout");
     c->keys_changed();
     auto it = c->galois.find(k);
@@ -714,7 +834,7 @@ tcks_status tcks_decrypt(tcks_ctx* c, const tcks_ct* ct, tcks_pt** out) {
   if (!c || !ct || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   tcks_pt* pt = new_pt(c, ct->level, ct->scale);
-  launch_decrypt(c->T, ct->d, c->sk, pt->d, ct->level, c->stream);
+  launch_decrypt(c->T, ct->d, c->sk, pt->d, ct->level, c->stream, ct->size);
   check_launch("decrypt");
   *out = pt;
   TCKS_API_END
@@ -729,6 +849,33 @@ tcks_status tcks_ct_import(tcks_ctx* c, const uint64_t* limbs, uint32_t level, d
   check_cuda(cudaMemcpyAsync(ct->d, limbs, ct_words(c, level) * 8, cudaMemcpyHostToDevice, c->stream), "ct import");
   check_cuda(cudaStreamSynchronize(c->stream), "ct import");
   *out = ct;
+  TCKS_API_END
+}
+
+tcks_status tcks_ct_import_sized(tcks_ctx* c, const uint64_t* limbs, uint32_t size, uint32_t level, double scale,
+                                 tcks_ct** out) {
+  TCKS_API_BEGIN
+  if (!c || !limbs || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (size != 2 && size != 3) fail(TCKS_ERR_INVALID_ARG, "a ciphertext has 2 or 3 components");
+  if (level < 1 || level > c->L) fail(TCKS_ERR_INVALID_ARG, "level out of range");
+  tcks_ct* ct = new_ct_sized(c, size, level, scale);
+  const size_t words = (size_t)size * level * c->N;
+  try {
+    check_cuda(cudaMemcpyAsync(ct->d, limbs, words * 8, cudaMemcpyHostToDevice, c->stream), "ct import");
+    check_cuda(cudaStreamSynchronize(c->stream), "ct import");
+  } catch (...) {
+    free_ct(ct);
+    throw;
+  }
+  *out = ct;
+  TCKS_API_END
+}
+
+tcks_status tcks_ct_size(const tcks_ct* ct, uint32_t* size) {
+  TCKS_API_BEGIN
+  if (!ct || !size) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *size = ct->size;
   TCKS_API_END
 }
 
@@ -764,9 +911,11 @@ tcks_status tcks_ct_export_batch(const tcks_ct* const* cts, uint32_t count, uint
   const u32 level = cts[0]->level;
   const u64 w = ct_words(c, level);
   if (n_words != (size_t)count * w) fail(TCKS_ERR_INVALID_ARG, "n_words does not match [count][2][level][N]");
-  for (u32 i = 0; i < count; ++i)
+  for (u32 i = 0; i < count; ++i) {
     if (!cts[i] || cts[i]->ctx != c || cts[i]->level != level)
       fail(TCKS_ERR_INVALID_ARG, "the batch must share one context and level");
+    need_relinearized(cts[i]);
+  }
   for (u32 i = 0; i < count; ++i)
     check_cuda(cudaMemcpyAsync(limbs + (size_t)i * w, cts[i]->d, w * 8, cudaMemcpyDeviceToHost, c->stream), "ct export");
   check_cuda(cudaStreamSynchronize(c->stream), "ct export");
@@ -776,7 +925,8 @@ tcks_status tcks_ct_export_batch(const tcks_ct* const* cts, uint32_t count, uint
 tcks_status tcks_ct_export(const tcks_ct* ct, uint64_t* limbs, size_t n_words) {
   TCKS_API_BEGIN
   if (!ct || !limbs) fail(TCKS_ERR_INVALID_ARG, "null argument");
-  if (n_words != ct_words(ct->ctx, ct->level)) fail(TCKS_ERR_INVALID_ARG, "n_words does not match [2][level][N]");
+  if (n_words != (size_t)ct->size * ct->level * ct->ctx->N)
+    fail(TCKS_ERR_INVALID_ARG, "n_words does not match [size][level][N]");
   check_cuda(cudaMemcpyAsync(limbs, ct->d, n_words * 8, cudaMemcpyDeviceToHost, ct->ctx->stream), "ct export");
   check_cuda(cudaStreamSynchronize(ct->ctx->stream), "ct export");
   TCKS_API_END
@@ -787,6 +937,7 @@ tcks_status tcks_ct_export(const tcks_ct* ct, uint64_t* limbs, size_t n_words) {
 tcks_status tcks_ct_serialized_size(const tcks_ct* ct, uint64_t* bytes) {
   TCKS_API_BEGIN
   if (!ct || !bytes) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  need_relinearized(ct);
   *bytes = kWireHeader + wire_payload_bytes(ct->ctx->T, ct->ctx->host.chain.data(), ct->level);
   TCKS_API_END
 }
@@ -795,6 +946,7 @@ tcks_status tcks_ct_serialize(const tcks_ct* ct, uint8_t* out, uint64_t cap, uin
   TCKS_API_BEGIN
   if (!ct || !out || !written) fail(TCKS_ERR_INVALID_ARG, "null argument");
   tcks_ctx* c = ct->ctx;
+  need_relinearized(ct);
   const u64 payload = wire_payload_bytes(c->T, c->host.chain.data(), ct->level);
   if (cap < kWireHeader + payload) fail(TCKS_ERR_INVALID_ARG, "capacity below the serialized size");
   DevBuf buf(c, (payload + 7) / 8);
@@ -815,6 +967,7 @@ tcks_status tcks_ct_serialize(const tcks_ct* ct, uint8_t* out, uint64_t cap, uin
 tcks_status tcks_ct_serialized_size_seeded(const tcks_ct* ct, uint64_t* bytes) {
   TCKS_API_BEGIN
   if (!ct || !bytes) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  need_relinearized(ct);
   *bytes = kWireHeader + 8 + wire_payload_bytes(ct->ctx->T, ct->ctx->host.chain.data(), ct->level) / 2;
   TCKS_API_END
 }
@@ -824,6 +977,7 @@ tcks_status tcks_ct_serialize_seeded(const tcks_ct* ct, uint64_t seed_a, uint8_t
   TCKS_API_BEGIN
   if (!ct || !out || !written) fail(TCKS_ERR_INVALID_ARG, "null argument");
   tcks_ctx* c = ct->ctx;
+  need_relinearized(ct);
   const u64 payload = wire_payload_bytes(c->T, c->host.chain.data(), ct->level) / 2;
   if (cap < kWireHeader + 8 + payload) fail(TCKS_ERR_INVALID_ARG, "capacity below the serialized size");
   // the receiver regenerates c1 from the seed: refuse a ciphertext whose c1 is not that polynomial
@@ -949,14 +1103,26 @@ static void check_pair(const tcks_ct* a, const tcks_ct* b, bool need_scale) {
   if (need_scale && a->scale != b->scale) fail(TCKS_ERR_SCALE_MISMATCH, "operands at different scales");
 }
 
+// Sum or difference; with a three-component operand the result has three components, a missing
+// third component being the zero polynomial.
 static tcks_status binary_ct(const tcks_ct* a, const tcks_ct* b, u32 op, tcks_ct** out) {
   TCKS_API_BEGIN
   if (!out) fail(TCKS_ERR_INVALID_ARG, "null output");
   *out = nullptr;
   check_pair(a, b, true);
   tcks_ctx* c = a->ctx;
-  tcks_ct* r = new_ct(c, a->level, a->scale);
-  launch_elementwise(c->T, op, a->d, b->d, r->d, a->level, 2, c->stream);
+  const u32 size = std::max(a->size, b->size), common = std::min(a->size, b->size);
+  tcks_ct* r = new_ct_sized(c, size, a->level, a->scale);
+  const size_t pw = (size_t)a->level * c->N;  // words of one component
+  launch_elementwise(c->T, op, a->d, b->d, r->d, a->level, common, c->stream);
+  if (size > common) {
+    const tcks_ct* big = a->size > b->size ? a : b;
+    if (big == b && op == OP_SUB)
+      launch_elementwise(c->T, OP_NEG, b->d + 2 * pw, nullptr, r->d + 2 * pw, a->level, 1, c->stream);
+    else
+      check_cuda(cudaMemcpyAsync(r->d + 2 * pw, big->d + 2 * pw, pw * 8, cudaMemcpyDeviceToDevice, c->stream),
+                 "third component");
+  }
   check_launch("elementwise");
   *out = r;
   TCKS_API_END
@@ -969,8 +1135,8 @@ tcks_status tcks_negate(const tcks_ct* a, tcks_ct** out) {
   TCKS_API_BEGIN
   if (!a || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
-  tcks_ct* r = new_ct(a->ctx, a->level, a->scale);
-  launch_elementwise(a->ctx->T, OP_NEG, a->d, nullptr, r->d, a->level, 2, a->ctx->stream);
+  tcks_ct* r = new_ct_sized(a->ctx, a->size, a->level, a->scale);
+  launch_elementwise(a->ctx->T, OP_NEG, a->d, nullptr, r->d, a->level, a->size, a->ctx->stream);
   check_launch("negate");
   *out = r;
   TCKS_API_END
@@ -983,8 +1149,14 @@ static tcks_status plain_op(const tcks_ct* a, const tcks_pt* p, u32 op, tcks_ct*
   if (a->ctx != p->ctx) fail(TCKS_ERR_INVALID_ARG, "operands belong to different contexts");
   if (p->level < a->level) fail(TCKS_ERR_LEVEL_MISMATCH, "plaintext level below the ciphertext level");
   if (op != OP_MUL_PLAIN && p->scale != a->scale) fail(TCKS_ERR_SCALE_MISMATCH, "plaintext scale differs");
-  tcks_ct* r = new_ct(a->ctx, a->level, op == OP_MUL_PLAIN ? a->scale * p->scale : a->scale);
-  launch_elementwise(a->ctx->T, op, a->d, p->d, r->d, a->level, 2, a->ctx->stream);
+  tcks_ct* r = new_ct_sized(a->ctx, a->size, a->level, op == OP_MUL_PLAIN ? a->scale * p->scale : a->scale);
+  // add/sub change c0 only: a third component is copied as it is; a product multiplies every component
+  launch_elementwise(a->ctx->T, op, a->d, p->d, r->d, a->level, op == OP_MUL_PLAIN ? a->size : 2, a->ctx->stream);
+  if (op != OP_MUL_PLAIN && a->size == 3) {
+    const size_t pw = (size_t)a->level * a->ctx->N;
+    check_cuda(cudaMemcpyAsync(r->d + 2 * pw, a->d + 2 * pw, pw * 8, cudaMemcpyDeviceToDevice, a->ctx->stream),
+               "third component");
+  }
   check_launch("plain op");
   *out = r;
   TCKS_API_END
@@ -999,16 +1171,36 @@ tcks_status tcks_mul(const tcks_ct* a, const tcks_ct* b, tcks_ct** out) {
   if (!out) fail(TCKS_ERR_INVALID_ARG, "null output");
   *out = nullptr;
   check_pair(a, b, false);
+  need_relinearized(a);
+  need_relinearized(b);
   tcks_ctx* c = a->ctx;
-  if (!(c->flags & TCKS_AUTO_RELIN))
-    fail(TCKS_ERR_UNSUPPORTED, "enc x enc without automatic relinearization has no 2-component result");
   const u32 ell = a->level;
   const bool rescale = (c->flags & TCKS_AUTO_RESCALE) != 0;
   if (rescale && ell < 2) fail(TCKS_ERR_LEVEL_EXHAUSTED, "multiply with auto-rescale needs level >= 2");
+  const double sc = a->scale * b->scale;
+  if (!(c->flags & TCKS_AUTO_RELIN)) {  // the three-component product, rescaled component by component
+    if (!rescale) {
+      tcks_ct* r = new_ct_sized(c, 3, ell, sc);
+      launch_tensor(c->T, a->d, b->d, r->d, ell, 1, c->stream);
+      check_launch("tensor");
+      *out = r;
+      return TCKS_OK;
+    }
+    DevBuf d3(c, (size_t)3 * ell * c->N);
+    launch_tensor(c->T, a->d, b->d, d3.p, ell, 1, c->stream);
+    tcks_ct* r = new_ct_sized(c, 3, ell - 1, sc / (double)c->host.chain[ell - 1]);
+    try {
+      op_rescale_polys(c, d3.p, ell, 3, r->d);
+    } catch (...) {
+      free_ct(r);
+      throw;
+    }
+    *out = r;
+    return TCKS_OK;
+  }
   DevBuf d3(c, (size_t)3 * ell * c->N);
   launch_tensor(c->T, a->d, b->d, d3.p, ell, 1, c->stream);
   check_launch("tensor");
-  const double sc = a->scale * b->scale;
   if (!rescale) {
     tcks_ct* r = new_ct(c, ell, sc);
     op_relinearize(c, d3.p, ell, r->d);
@@ -1029,13 +1221,26 @@ tcks_status tcks_mul(const tcks_ct* a, const tcks_ct* b, tcks_ct** out) {
 
 tcks_status tcks_square(const tcks_ct* a, tcks_ct** out) { return tcks_mul(a, a, out); }
 
+tcks_status tcks_relinearize(tcks_ct* ct) {
+  TCKS_API_BEGIN
+  if (!ct) fail(TCKS_ERR_INVALID_ARG, "null ciphertext");
+  if (ct->size == 2) return TCKS_OK;
+  tcks_ctx* c = ct->ctx;
+  DevBuf nb(c, ct_words(c, ct->level));
+  op_relinearize(c, ct->d, ct->level, nb.p);
+  c->dev_free(ct->d);
+  ct->d = nb.release();
+  ct->size = 2;
+  TCKS_API_END
+}
+
 tcks_status tcks_rescale(tcks_ct* ct) {
   TCKS_API_BEGIN
   if (!ct) fail(TCKS_ERR_INVALID_ARG, "null ciphertext");
   tcks_ctx* c = ct->ctx;
   if (ct->level < 2) fail(TCKS_ERR_LEVEL_EXHAUSTED, "rescale needs level >= 2");
-  DevBuf nb(c, ct_words(c, ct->level - 1));
-  op_rescale(c, ct->d, ct->level, nb.p);
+  DevBuf nb(c, (size_t)ct->size * (ct->level - 1) * c->N);
+  op_rescale_polys(c, ct->d, ct->level, ct->size, nb.p);
   c->dev_free(ct->d);
   ct->d = nb.release();
   ct->scale = ct->scale / (double)c->host.chain[ct->level - 1];
@@ -1049,10 +1254,10 @@ tcks_status tcks_mod_switch(tcks_ct* ct, uint32_t level) {
   if (level < 1 || level > ct->level) fail(TCKS_ERR_INVALID_ARG, "target level out of range");
   if (level == ct->level) return TCKS_OK;
   tcks_ctx* c = ct->ctx;
-  DevBuf nb(c, ct_words(c, level));
+  DevBuf nb(c, (size_t)ct->size * level * c->N);
   const size_t n = c->N;
-  check_cuda(cudaMemcpy2DAsync(nb.p, (size_t)level * n * 8, ct->d, (size_t)ct->level * n * 8, (size_t)level * n * 8, 2,
-                               cudaMemcpyDeviceToDevice, c->stream),
+  check_cuda(cudaMemcpy2DAsync(nb.p, (size_t)level * n * 8, ct->d, (size_t)ct->level * n * 8, (size_t)level * n * 8,
+                               ct->size, cudaMemcpyDeviceToDevice, c->stream),
              "mod switch");
   c->dev_free(ct->d);
   ct->d = nb.release();
@@ -1079,6 +1284,7 @@ tcks_status tcks_rotate_hoisted(const tcks_ct* a, const int32_t* steps, uint32_t
   TCKS_API_BEGIN
   if (!a || !outs || (n_steps && !steps)) fail(TCKS_ERR_INVALID_ARG, "null argument");
   for (u32 i = 0; i < n_steps; ++i) outs[i] = nullptr;
+  need_relinearized(a);
   tcks_ctx* c = a->ctx;
   for (u32 i = 0; i < n_steps; ++i)
     if (step_mod(c, steps[i])) galois_key_for(c, steps[i], a->level);  // validate first
@@ -1107,6 +1313,7 @@ tcks_status tcks_rotate_sum_hoisted(const tcks_ct* a, const int32_t* steps, uint
   TCKS_API_BEGIN
   if (!a || !out || (n_steps && !steps)) fail(TCKS_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
+  need_relinearized(a);
   tcks_ctx* c = a->ctx;
   std::vector<int32_t> st(steps, steps + n_steps);
   for (int32_t s : st) {  // validate before launching anything
@@ -1130,6 +1337,7 @@ tcks_status tcks_sum(const tcks_ct* a, uint32_t n, tcks_ct** out) {
   *out = nullptr;
   tcks_ctx* c = a->ctx;
   if (n > c->N / 2) fail(TCKS_ERR_INVALID_ARG, "n exceeds the slot count");
+  need_relinearized(a);
   for (u32 m = 0; m + 1 < c->params.log_n; ++m) galois_key_for(c, (int32_t)(1u << m), a->level);
   tcks_ct* r = new_ct(c, a->level, a->scale);
   check_cuda(cudaMemcpyAsync(r->d, a->d, ct_words(c, a->level) * 8, cudaMemcpyDeviceToDevice, c->stream), "sum copy");
@@ -1160,6 +1368,7 @@ tcks_status tcks_dot_plain(const tcks_ct* a, const double* w, uint32_t n, tcks_c
   TCKS_API_BEGIN
   if (!a || !w || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
+  need_relinearized(a);
   tcks_pt* p = nullptr;
   tcks_status s = tcks_encode(a->ctx, w, n, 0.0, a->level, &p);
   if (s != TCKS_OK) return s;
@@ -1297,6 +1506,7 @@ tcks_status tcks_vecmat_plain(const tcks_ct* a, const tcks_matrix* M, tcks_ct** 
   TCKS_API_BEGIN
   if (!a || !M || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
+  need_relinearized(a);
   tcks_ctx* c = a->ctx;
   if (M->ctx != c) fail(TCKS_ERR_INVALID_ARG, "matrix belongs to another context");
   if (M->level < a->level) fail(TCKS_ERR_LEVEL_MISMATCH, "matrix encoded below the ciphertext level");
@@ -1322,6 +1532,7 @@ tcks_status tcks_vecmat_plain_batch(const tcks_ct* const* in, uint32_t count, co
   const u32 ell = in[0] ? in[0]->level : 0;
   for (u32 i = 0; i < count; ++i) {
     if (!in[i] || in[i]->ctx != c) fail(TCKS_ERR_INVALID_ARG, "ciphertext missing or of another context");
+    need_relinearized(in[i]);
     if (in[i]->level != ell) fail(TCKS_ERR_LEVEL_MISMATCH, "the batch must share one level");
     if (in[i]->scale != in[0]->scale) fail(TCKS_ERR_SCALE_MISMATCH, "the batch must share one scale");
   }
@@ -1370,6 +1581,7 @@ tcks_status tcks_conv2d_im2col_pt(const tcks_ct* a, const tcks_pt* kernel, uint3
   TCKS_API_BEGIN
   if (!a || !kernel || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
+  need_relinearized(a);
   tcks_ctx* c = a->ctx;
   if (kernel->ctx != c) fail(TCKS_ERR_INVALID_ARG, "kernel belongs to another context");
   if (kernel->level < a->level) fail(TCKS_ERR_LEVEL_MISMATCH, "kernel encoded below the ciphertext level");
@@ -1391,6 +1603,7 @@ tcks_status tcks_conv2d_im2col(const tcks_ct* a, const double* kernel, uint32_t 
   TCKS_API_BEGIN
   if (!a || !kernel || !out) fail(TCKS_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
+  need_relinearized(a);
   tcks_ctx* c = a->ctx;
   const u32 slots = c->N / 2;
   if (taps == 0 || windows == 0 || (u64)windows * taps > slots) fail(TCKS_ERR_INVALID_ARG, "bad conv geometry");

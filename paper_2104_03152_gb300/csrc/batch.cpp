@@ -8,7 +8,10 @@
 //     job's context stream, so that different N overlap on the device.
 // The whole batch can be captured once as a CUDA graph and replayed.
 #include <algorithm>
+#include <chrono>
 #include <map>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "context.h"
@@ -21,8 +24,10 @@ namespace {
 
 constexpr u64 kScratchBound = 4ull << 30;  // bytes of key-switch scratch per sub-batch
 
-// Key-switch scratch words per ciphertext at level ell: coefficients, digits [ell][ell+1], P limbs.
-u64 ks_scratch_words(const tcks_ctx* c, u32 ell) { return ((u64)ell + (u64)ell * (ell + 1) + 2) * c->N; }
+// Key-switch scratch words per ciphertext at level ell: coefficients, digits, P limbs.
+u64 ks_scratch_words(const tcks_ctx* c, u32 ell) {
+  return (u64)ell * c->N + ks_digit_words(c, ell) + ks_top_words(c);
+}
 
 // log2 of the CTAs per limb of the limb kernels (clusters above N = 2^14)
 u32 cluster_log(const tcks_ctx* c) { return c->params.log_n > 14 ? c->params.log_n - 14 : 0; }
@@ -44,15 +49,16 @@ void op_rotate_batch(tcks_ctx* c, const u64* in, u32 count, u32 ell, int32_t ste
   }
   const KeyTable& kt = key_table(c, {k}, ell);
   const u32 sb = sub_batch(c, ell, count);
-  DevBuf coef(c, (size_t)sb * ell * n), digits(c, (size_t)sb * ell * (ell + 1) * n), top(c, (size_t)sb * 2 * n);
+  const u64 dw = ks_digit_words(c, ell);
+  DevBuf coef(c, (size_t)sb * ell * n), digits(c, (size_t)sb * dw), top(c, (size_t)sb * ks_top_words(c));
   for (u32 b0 = 0; b0 < count; b0 += sb) {
     const u32 bn = std::min(sb, count - b0);
     const u64* src = in + (size_t)b0 * cw;
-    launch_modup(c->T, src + (size_t)ell * n, cw, bn, ell, coef.p, digits.p, c->stream);
+    ks_modup(c, src + (size_t)ell * n, cw, bn, ell, coef.p, digits.p);
     KsPlan p{};
     p.keys = kt.d;
     p.digits = digits.p;
-    p.digits_b = (u64)ell * (ell + 1) * n;
+    p.digits_b = dw;
     p.top = top.p;
     p.out = out + (size_t)b0 * cw;
     p.out_b = cw;
@@ -61,7 +67,7 @@ void op_rotate_batch(tcks_ctx* c, const u64* in, u32 count, u32 ell, int32_t ste
     p.R = 1;
     p.B = bn;
     p.add_perm = 1;
-    launch_keyswitch(c->T, ell, p, c->stream);
+    ks_switch(c, ell, p);
   }
   check_launch("rotate batch");
 }
@@ -172,6 +178,11 @@ void run_jobs(const tcks_batch_job* jobs, u32 n_jobs) {
 
 }  // namespace tcks
 
+struct tcks_batch {
+  std::vector<tcks_ctx*> ctxs;  // retained until the handle is freed
+  cudaEvent_t done = nullptr;   // recorded on the origin stream after every job (and join)
+};
+
 struct tcks_batch_graph {
   std::vector<tcks_ctx*> ctxs;  // retained
   cudaStream_t origin = nullptr;
@@ -200,6 +211,61 @@ tcks_status tcks_batch_run(const tcks_batch_job* jobs, uint32_t n_jobs) {
   BATCH_BEGIN
   validate(jobs, n_jobs);
   run_jobs(jobs, n_jobs);
+  BATCH_END
+}
+
+void tcks_batch_free(tcks_batch* b) {
+  if (!b) return;
+  if (b->done) {
+    cudaEventSynchronize(b->done);
+    cudaEventDestroy(b->done);
+  }
+  for (tcks_ctx* c : b->ctxs) ctx_release(c);
+  delete b;
+  cudaGetLastError();  // clean-up statuses are not reported
+}
+
+tcks_status tcks_batch_submit(const tcks_batch_job* jobs, uint32_t n_jobs, tcks_batch** out) {
+  struct Guard {
+    tcks_batch* b = nullptr;
+    ~Guard() { tcks_batch_free(b); }
+  } guard;
+  BATCH_BEGIN
+  if (!out) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  validate(jobs, n_jobs);
+  guard.b = new tcks_batch();
+  for (u32 i = 0; i < n_jobs; ++i) {
+    tcks_ctx* c = jobs[i].ctx;
+    if (std::find(guard.b->ctxs.begin(), guard.b->ctxs.end(), c) == guard.b->ctxs.end()) {
+      ctx_retain(c);
+      guard.b->ctxs.push_back(c);
+    }
+  }
+  check_cuda(cudaEventCreateWithFlags(&guard.b->done, cudaEventDisableTiming), "batch event");
+  run_jobs(jobs, n_jobs);
+  check_cuda(cudaEventRecord(guard.b->done, jobs[0].ctx->stream), "batch event");
+  *out = guard.b;
+  guard.b = nullptr;
+  BATCH_END
+}
+
+tcks_status tcks_batch_wait(tcks_batch* b, int64_t timeout_ns) {
+  BATCH_BEGIN
+  if (!b || !b->done) fail(TCKS_ERR_INVALID_ARG, "null batch");
+  // A host-side wait: the event is polled, with sleeps that grow to 100 us, until it completes or the
+  // deadline passes. Nothing on the device waits.
+  const auto start = std::chrono::steady_clock::now();
+  auto pause = std::chrono::microseconds(2);
+  for (;;) {
+    const cudaError_t e = cudaEventQuery(b->done);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) fail(TCKS_ERR_CUDA, std::string("batch: ") + cudaGetErrorString(e));
+    if (timeout_ns >= 0 && std::chrono::steady_clock::now() - start >= std::chrono::nanoseconds(timeout_ns))
+      fail(TCKS_ERR_TIMEOUT, "the batch has not completed within " + std::to_string(timeout_ns) + " ns");
+    std::this_thread::sleep_for(pause);
+    if (pause < std::chrono::microseconds(100)) pause *= 2;
+  }
   BATCH_END
 }
 

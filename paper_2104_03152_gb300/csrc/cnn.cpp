@@ -1,4 +1,4 @@
-// The encrypted MNIST-shaped CNN of the paper's evaluation (§4, Table 2): conv (4 kernels 7x7,
+// The encrypted MNIST-shaped CNN of the paper's evaluation (§5, Table 2): conv (4 kernels 7x7,
 // stride 3, im2col, §3.2) -> square -> FC 256->64 (§3.1) -> square -> FC 64->10, six multiplicative
 // levels, on one CKKSVector.
 //
@@ -48,6 +48,7 @@ struct tcks_cnn {
   std::vector<int32_t> baby, giant;
   u64* baby_ext = nullptr;   // conv_shared: per kernel k and baby step b (0 first), the kernel rotated
                              // left by windows * b over the extended basis, [kernels][B][L+1][N]
+  int* h_wire_status = nullptr;  // pinned host word: the residue check of tcks_cnn_forward_wire's inputs
 };
 
 namespace tcks {
@@ -265,6 +266,7 @@ void tcks_cnn_free(tcks_cnn* m) {
   for (u64* p : m->masks) c->dev_free(p);
   for (u64* p : m->bias) c->dev_free(p);
   if (m->baby_ext) c->dev_free(m->baby_ext);
+  if (m->h_wire_status) cudaFreeHost(m->h_wire_status);
   tcks_matrix_free(m->fc1);
   tcks_matrix_free(m->fc2);
   delete m;
@@ -284,6 +286,7 @@ tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* con
     fail(TCKS_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   const u32 slots = c->N / 2, L = c->L;
+  need_one_prime_ks(c, "the encrypted network");
   if (L < 7) fail(TCKS_ERR_BAD_PARAMS, "the network needs at least 7 data primes (6 levels + 1)");
   if (!kernels || !taps || !windows || (u64)taps * windows > slots || (u64)kernels * windows > slots)
     fail(TCKS_ERR_INVALID_ARG, "bad conv geometry");
@@ -293,6 +296,7 @@ tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* con
   m = new tcks_cnn();
   m->ctx = c;
   ctx_retain(c);
+  check_cuda(cudaHostAlloc((void**)&m->h_wire_status, sizeof(int), cudaHostAllocDefault), "pinned status word");
   m->kernels = kernels;
   m->taps = taps;
   m->windows = windows;
@@ -445,6 +449,7 @@ tcks_status tcks_cnn_forward(const tcks_cnn* m, const tcks_ct* in, tcks_ct** out
   *out = nullptr;
   tcks_ctx* c = m->ctx;
   if (in->ctx != c) fail(TCKS_ERR_INVALID_ARG, "ciphertext belongs to another context");
+  need_relinearized(in);
   if (in->level != m->L) fail(TCKS_ERR_LEVEL_MISMATCH, "the network takes a ciphertext at the top level");
   if (in->scale != m->in_scale) fail(TCKS_ERR_SCALE_MISMATCH, "the network takes a ciphertext at the context scale");
   tcks_ct* r = new_ct(c, m->L - 6, m->out_scale);
@@ -473,6 +478,7 @@ tcks_status tcks_cnn_forward_batch(const tcks_cnn* m, const tcks_ct* const* in, 
   tcks_ctx* c = m->ctx;
   for (u32 i = 0; i < count; ++i) {
     if (!in[i] || in[i]->ctx != c) fail(TCKS_ERR_INVALID_ARG, "ciphertext missing or of another context");
+    need_relinearized(in[i]);
     if (in[i]->level != m->L) fail(TCKS_ERR_LEVEL_MISMATCH, "the network takes ciphertexts at the top level");
     if (in[i]->scale != m->in_scale) fail(TCKS_ERR_SCALE_MISMATCH, "the network takes ciphertexts at the context scale");
   }
@@ -568,6 +574,19 @@ tcks_status tcks_cnn_forward_wire(const tcks_cnn* m, const uint8_t* host_in, uin
       launch_sym_a_batch(c->T, dseeds.p + r0, L, xin.p + (u64)r0 * w_in + (u64)L * c->N, w_in, k, c->stream);
   }
   check_launch("wire input");
+  // The residue check's verdict travels to a pinned host word right behind the unpacking; the host
+  // reads it while the network runs and only then lets the outputs reach host_out, so a refused batch
+  // leaves the caller's buffer untouched.
+  struct Event {
+    cudaEvent_t e = nullptr;
+    ~Event() {
+      if (e) cudaEventDestroy(e);
+    }
+  } checked;
+  check_cuda(cudaMemcpyAsync(m->h_wire_status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+             "wire status");
+  check_cuda(cudaEventCreateWithFlags(&checked.e, cudaEventDisableTiming), "event");
+  check_cuda(cudaEventRecord(checked.e, c->stream), "event");
   cnn_forward_dev(m, xin.p, w_in, count, yout.p);
   for (u32 r0 = 0; r0 < count; r0 += kChunk) {
     const u32 k = std::min(kChunk, count - r0);
@@ -575,11 +594,13 @@ tcks_status tcks_cnn_forward_wire(const tcks_cnn* m, const uint8_t* host_in, uin
                       c->stream);
   }
   check_launch("wire output");
-  int status = 0;
+  check_cuda(cudaEventSynchronize(checked.e), "wire status");
+  if (*m->h_wire_status) {
+    check_cuda(cudaStreamSynchronize(c->stream), "forward");  // the scratch is released only after the network
+    fail(TCKS_ERR_INVALID_ARG, "an input residue is not below its prime");
+  }
   check_cuda(cudaMemcpyAsync(host_out, pb, (size_t)count * out_size, cudaMemcpyDeviceToHost, c->stream), "D2H");
-  check_cuda(cudaMemcpyAsync(&status, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "wire status");
   check_cuda(cudaStreamSynchronize(c->stream), "forward");
-  if (status) fail(TCKS_ERR_INVALID_ARG, "an input residue is not below its prime");
   for (u32 r = 0; r < count; ++r) {
     uint8_t* h = host_out + (u64)r * out_size;
     std::memcpy(h, kWireMagic, 4);
@@ -669,6 +690,7 @@ tcks_status tcks_cnn_graph_run(tcks_cnn_graph* g, const tcks_ct* const* in, tcks
   for (u32 i = 0; i < g->count; ++i) {
     outs[i] = nullptr;
     if (!in[i] || in[i]->ctx != c) fail(TCKS_ERR_INVALID_ARG, "ciphertext missing or of another context");
+    need_relinearized(in[i]);
     if (in[i]->level != m->L || in[i]->scale != m->in_scale)
       fail(TCKS_ERR_LEVEL_MISMATCH, "the network takes ciphertexts at the top level and the context scale");
   }

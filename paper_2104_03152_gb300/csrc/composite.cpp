@@ -83,6 +83,7 @@ static void vecmat_single_hoisted(tcks_ctx* c, const u64* ct, u64 cw, u32 count,
 // ModUp and one ModDown per ciphertext: the double-hoisted accumulation with unit diagonals. out may
 // alias x. The scale is unchanged.
 void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const std::vector<int32_t>& steps, u64* out) {
+  need_one_prime_ks(c, "the hoisted rotation sum");
   const size_t n = c->N;
   std::vector<u32> ks;
   for (int32_t s : steps) {
@@ -132,6 +133,7 @@ void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const st
 void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, const std::vector<int32_t>& steps,
                      const u64* diags, u64 diag_stride, u64 set_stride, u32 p_limb, u32 outs, u64* out, u64 out_b,
                      u64 out_o, bool merged) {
+  need_one_prime_ks(c, "the double-hoisted rotation sum");
   const size_t n = c->N;
   std::vector<u32> ks;
   for (int32_t st : steps) {
@@ -183,6 +185,7 @@ void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, cons
 
 void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell, const tcks_matrix* M, u64* out,
                u32 input_period) {
+  need_one_prime_ks(c, "the vector x matrix product");
   const bool dh = (c->flags & TCKS_DOUBLE_HOIST) != 0;
   if (dh && !M->ext)
     fail(TCKS_ERR_UNSUPPORTED, "double-hoisted vector x matrix needs the diagonals modulo P (tcks_matrix_encode or "

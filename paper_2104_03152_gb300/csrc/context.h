@@ -14,8 +14,10 @@
 struct tcks_params {
   tcks::u32 log_n;
   std::vector<tcks::u32> bits;
-  std::vector<tcks::u64> chain;  // data primes then P
+  std::vector<tcks::u64> chain;  // data primes, then the n_special special primes (P their product)
   double scale;
+  tcks::u32 n_special = 1;  // hybrid key switching: K > 1 special primes and/or
+  tcks::u32 alpha = 1;      // digits of alpha > 1 data primes
 };
 
 namespace tcks {
@@ -46,6 +48,10 @@ struct tcks_ctx {
   tcks::DevTables T{};
   tcks::FftTables F{};
   tcks::u32 N = 0, L = 0;
+  tcks::u32 K = 1, alpha = 1;    // special primes, data primes per key-switching digit
+  bool hyb = false;              // hybrid key switching (K > 1 or alpha > 1)
+  tcks::HybTables H{};           // its constants (device pointers into d_hyb)
+  tcks::u64* d_hyb = nullptr;
   // device tables
   void* d_mods = nullptr;
   void* d_pairs = nullptr;
@@ -64,9 +70,9 @@ struct tcks_ctx {
   tcks::u64 seed = 0;
   int device = 0;
   // keys
-  tcks::u64* sk = nullptr;   // [L+1][N]
+  tcks::u64* sk = nullptr;   // [L+K][N]
   tcks::u64* pk = nullptr;   // [2][L][N]
-  tcks::u64* rlk = nullptr;  // [L][2][L+1][N]
+  tcks::u64* rlk = nullptr;  // [L][2][L+1][N], or with hybrid key switching [dnum(L)][2][L+K][N]
   std::map<tcks::u32, tcks::GaloisKey> galois;  // step mod N/2 -> key
   std::map<std::vector<tcks::u32>, tcks::KeyTable> key_tables;  // cached device key tables
   tcks::u64 table_bytes = 0;
@@ -84,9 +90,10 @@ struct tcks_ctx {
 
 struct tcks_ct {
   tcks_ctx* ctx;
-  tcks::u64* d;  // [2][level][N]
+  tcks::u64* d;  // [size][level][N]
   tcks::u32 level;
   double scale;
+  tcks::u32 size = 2;  // 3: an unrelinearized enc x enc product (c0, c1, c2), decrypted as c0 + c1 s + c2 s^2
 };
 
 struct tcks_pt {
@@ -165,12 +172,29 @@ inline size_t ct_words(const tcks_ctx* c, u32 level) { return (size_t)2 * level 
 inline size_t pt_words(const tcks_ctx* c, u32 level) { return (size_t)level * c->N; }
 
 tcks_ct* new_ct(tcks_ctx* c, u32 level, double scale);  // uninitialised limbs
+tcks_ct* new_ct_sized(tcks_ctx* c, u32 size, u32 level, double scale);  // [size][level][N], uninitialised
+// Every operation but the element-wise ones, rescale, mod-switch, decrypt and export takes the
+// two-component form: a three-component product has to be relinearized first.
+void need_relinearized(const tcks_ct* ct);
+// Key switching, one-prime or hybrid as the context says: words of a switching key of level Kt, of
+// the digits of one input at level ell, of the P-limb scratch of one (request, rotation); ModUp of
+// `count` inputs; the inner products and ModDown of a plan.
+u64 ksk_words(const tcks_ctx* c, u32 Kt);
+u64 ks_digit_words(const tcks_ctx* c, u32 ell);
+u64 ks_top_words(const tcks_ctx* c);
+void ks_modup(tcks_ctx* c, const u64* x, u64 x_stride, u32 count, u32 ell, u64* coef_tmp, u64* digits);
+void ks_switch(tcks_ctx* c, u32 ell, const KsPlan& plan);
+// The fused schedules (vector x matrix products, hoisted rotation sums, the CNN) are written for the
+// one-prime key switch: UNSUPPORTED on a context with hybrid key switching.
+void need_one_prime_ks(const tcks_ctx* c, const char* what);
 tcks_pt* new_pt(tcks_ctx* c, u32 level, double scale);
 void free_ct(tcks_ct* ct);
 
 // Internal ops on device buffers (results written to caller-provided buffers).
 // Rescale `count` ciphertexts [count][2][ell][N] -> [count][2][ell-1][N].
 void op_rescale(tcks_ctx* c, const u64* in, u32 ell, u64* out, u32 count = 1);
+// Rescale of `polys` polynomials [polys][ell][N] -> [polys][ell-1][N] (a three-component product: 3).
+void op_rescale_polys(tcks_ctx* c, const u64* in, u32 ell, u32 polys, u64* out);
 // Relinearize `count` tensor products [count][3][ell][N] -> [count][2][ell][N].
 void op_relinearize(tcks_ctx* c, const u64* d3, u32 ell, u64* out, u32 count = 1);
 // The same followed by the rescale, both in one rounding -> [count][2][ell-1][N].

@@ -1,4 +1,4 @@
-// Ciphertext arrays: the storage of TenSEAL's CKKSTensor (§2.2: an N-dimensional tensor of real values
+// Ciphertext arrays: the storage of TenSEAL's CKKSTensor (§2.3: an N-dimensional tensor of real values
 // encrypted as a tensor of ciphertexts, optionally with one axis batched into the slots). All of a
 // tensor's ciphertexts live in one device allocation, so that its element-wise operations, its
 // products and its reductions are single batched launches; the tensor's shape, broadcasting and axis
@@ -128,6 +128,7 @@ tcks_status tcks_cta_from_cts(const tcks_ct* const* cts, uint32_t count, tcks_ct
   tcks_ctx* c = cts[0]->ctx;
   for (u32 i = 0; i < count; ++i) {
     if (!cts[i] || cts[i]->ctx != c) fail(TCKS_ERR_INVALID_ARG, "ciphertext missing or of another context");
+    need_relinearized(cts[i]);
     if (cts[i]->level != cts[0]->level) fail(TCKS_ERR_LEVEL_MISMATCH, "ciphertexts at different levels");
     if (cts[i]->scale != cts[0]->scale) fail(TCKS_ERR_SCALE_MISMATCH, "ciphertexts at different scales");
   }

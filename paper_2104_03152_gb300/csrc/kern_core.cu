@@ -420,21 +420,24 @@ void launch_tensor(const DevTables& T, const u64* a, const u64* b, u64* out, u32
   k_tensor<<<ew_blocks(e / 2 + 1), 256, 0, st>>>(T, a, b, out, ell, count);
 }
 
-// Decryption kernel: m = c0 + c1 * s over limbs < ell (s has L+1 limbs, chain order).
+// Decryption kernel: m = c0 + c1 * s (+ c2 * s^2 for a three-component product) over limbs < ell (s
+// has L+1 limbs, chain order).
 __global__ void k_decrypt(DevTables T, const u64* __restrict__ ct, const u64* __restrict__ s, u64* __restrict__ pt,
-                          u32 ell) {
+                          u32 ell, u32 size) {
   const u32 log_n = T.log_n;
   const u64 per_poly = (u64)ell << log_n;
   for (u64 e = (u64)blockIdx.x * blockDim.x + threadIdx.x; e < per_poly; e += (u64)gridDim.x * blockDim.x) {
     const ModConst m = T.mods[e >> log_n];
-    pt[e] = add_mod(ct[e], mulq(ct[per_poly + e], s[e], m, T.narrow), m.q);
+    u64 v = add_mod(ct[e], mulq(ct[per_poly + e], s[e], m, T.narrow), m.q);
+    if (size == 3) v = add_mod(v, mulq(ct[2 * per_poly + e], mulq(s[e], s[e], m, T.narrow), m, T.narrow), m.q);
+    pt[e] = v;
   }
 }
 
-void launch_decrypt(const DevTables& T, const u64* ct, const u64* s, u64* pt, u32 ell, cudaStream_t st) {
+void launch_decrypt(const DevTables& T, const u64* ct, const u64* s, u64* pt, u32 ell, cudaStream_t st, u32 size) {
   const u64 e = (u64)ell << T.log_n;
-  Launch L(K_DECRYPT, st, 4.0 * 8.0 * e);
-  k_decrypt<<<ew_blocks(e / 2 + 1), 256, 0, st>>>(T, ct, s, pt, ell);
+  Launch L(K_DECRYPT, st, (size + 2.0) * 8.0 * e);
+  k_decrypt<<<ew_blocks(e / 2 + 1), 256, 0, st>>>(T, ct, s, pt, ell, size);
 }
 
 // ---------------------------------------------------------------- drop the last prime ----

@@ -86,12 +86,12 @@ __device__ __forceinline__ u32 slot_chain(u32 slot, u32 count, u32 L) { return s
 
 }  // namespace
 
-// s: [L+1][N], one limb job per prime.
+// s: [n_mods][N] (every prime of the chain), one limb job per prime.
 template <typename W, int LC>
 __global__ void k_keygen_secret(DevTables T, u64 seed, u64* __restrict__ s_out) {
   TCKS_SMEM(W);
   const Slice P = slice_of<LC>(T);
-  const u32 mod = P.job;  // 0..L (L is P)
+  const u32 mod = P.job;  // 0..n_mods-1 (the special primes last)
   small_ntt<W, LC>(s, T, mod, SMALL_TERNARY, seed, 1, P.rank, P.ns);
   const u64 q = T.mods[mod].q;
   u64* out = s_out + ((u64)mod << T.log_n) + P.off;
@@ -135,6 +135,41 @@ __global__ void k_keygen_switch(DevTables T, u64 seed, u32 kind, const u64* __re
   const u64* s_l = sk + (u64)l * n;
   u64* b0 = ksk + (((u64)j * 2 + 0) * (K + 1) + slot) * n;
   u64* b1 = ksk + (((u64)j * 2 + 1) * (K + 1) + slot) * n;
+  for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) {
+    const u32 g = P.off + k;
+    const u64 a = draw_uniform(seed, tag_a, g, l, m);
+    u64 v = add_mod(neg_mod(mulq_s(a, s_l[g], m, T.narrow), m.q), Ar<W>::fwd_out(s[sw(k)], m), m.q);
+    if (gadget) {
+      const u64 sp = kind == 0 ? mulq_s(s_l[g], s_l[g], m, T.narrow) : s_l[galois_src(g, kind, log_n)];
+      v = add_mod(v, mulq_s(gadget, sp, m, T.narrow), m.q);
+    }
+    b0[g] = v;
+    b1[g] = a;
+  }
+}
+
+// Switching key of level Kt for hybrid key switching (digits of alpha data primes, K special primes
+// with product P): [dnum(Kt)][2][Kt + K][N], limb job = digit j * (Kt + K) + slot t;
+//   b_j[t] = -a s + e + [t is a data prime of digit j] * (P mod q_t) * s'
+// with the sampler counters of the one-prime key (tags from the digit index, limbs by chain index).
+template <typename W, int LC>
+__global__ void k_keygen_switch_hyb(DevTables T, HybTables H, u64 seed, u32 kind, const u64* __restrict__ sk,
+                                    u32 Kt, u64* __restrict__ ksk) {
+  TCKS_SMEM(W);
+  const Slice P = slice_of<LC>(T);
+  const u32 log_n = T.log_n;
+  const u64 n = 1ull << log_n;
+  const u32 S = Kt + H.K;
+  const u32 j = P.job / S, slot = P.job % S;
+  const u32 l = slot < Kt ? slot : T.L + (slot - Kt);
+  const ModConst m = T.mods[l];
+  const u64 tag_a = ((u64)kind << 32) | 0x80000000ull | (2ull * j);
+  const u64 tag_e = tag_a | 1ull;
+  small_ntt<W, LC>(s, T, l, SMALL_CBD, seed, tag_e, P.rank, P.ns);
+  const u64 gadget = (l < T.L && l / H.alpha == j) ? H.down_P[l] : 0;  // P mod q_l
+  const u64* s_l = sk + (u64)l * n;
+  u64* b0 = ksk + (((u64)j * 2 + 0) * S + slot) * n;
+  u64* b1 = ksk + (((u64)j * 2 + 1) * S + slot) * n;
   for (u32 k = threadIdx.x; k < P.ns; k += blockDim.x) {
     const u32 g = P.off + k;
     const u64 a = draw_uniform(seed, tag_a, g, l, m);
@@ -225,6 +260,7 @@ __global__ void k_sym_a_batch(DevTables T, const u64* __restrict__ seeds, u32 el
 static decltype(&k_keygen_secret<u64, 0>) const K6_k_keygen_secret[6] = TCKS_K6(k_keygen_secret);
 static decltype(&k_keygen_public<u64, 0>) const K6_k_keygen_public[6] = TCKS_K6(k_keygen_public);
 static decltype(&k_keygen_switch<u64, 0>) const K6_k_keygen_switch[6] = TCKS_K6(k_keygen_switch);
+static decltype(&k_keygen_switch_hyb<u64, 0>) const K6_k_keygen_switch_hyb[6] = TCKS_K6(k_keygen_switch_hyb);
 static decltype(&k_encrypt<u64, 0>) const K6_k_encrypt[6] = TCKS_K6(k_encrypt);
 static decltype(&k_encrypt_sym<u64, 0>) const K6_k_encrypt_sym[6] = TCKS_K6(k_encrypt_sym);
 
@@ -244,8 +280,15 @@ u32 limb_threads_cap_sample(bool narrow, u32 log_c) {
 }
 
 void launch_keygen_secret(const DevTables& T, u64 seed, u64* s, cudaStream_t st) {
-  Launch L(K_KEYGEN, st, 8.0 * (T.L + 1) * (1u << T.log_n));
-  launch_limb(K6_k_keygen_secret, T.narrow, T.L + 1, 1, T.log_n, st, T.limb_threads, T, seed, s);
+  Launch L(K_KEYGEN, st, 8.0 * T.n_mods * (1u << T.log_n));
+  launch_limb(K6_k_keygen_secret, T.narrow, T.n_mods, 1, T.log_n, st, T.limb_threads, T, seed, s);
+}
+
+void launch_keygen_switch_hyb(const DevTables& T, const HybTables& H, u64 seed, u32 kind, const u64* s, u32 Kt,
+                              u64* ksk, cudaStream_t st) {
+  const u32 dn = (Kt + H.alpha - 1) / H.alpha, S = Kt + H.K;
+  Launch L(K_KEYGEN, st, 8.0 * 2 * dn * S * (1u << T.log_n));
+  launch_limb(K6_k_keygen_switch_hyb, T.narrow, dn * S, 1, T.log_n, st, T.limb_threads, T, H, seed, kind, s, Kt, ksk);
 }
 
 void launch_keygen_public(const DevTables& T, u64 seed, const u64* s, u64* pk, cudaStream_t st) {

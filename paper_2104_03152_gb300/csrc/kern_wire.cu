@@ -1,4 +1,4 @@
-// Bit-packed ciphertext wire format (the communication of §4's encrypted inference): every residue of
+// Bit-packed ciphertext wire format (the communication of §5's encrypted inference): every residue of
 // limb i travels in exactly w_i = bit_length(q_i) bits. A limb's segment is ceil(N w_i / 8) bytes,
 // residue k in bits [k w_i, (k + 1) w_i), least significant bit first. One thread per output byte
 // packs (a byte touches at most two residues, w_i >= 8); one thread per residue unpacks and checks

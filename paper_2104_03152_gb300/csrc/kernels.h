@@ -81,7 +81,7 @@ void launch_elementwise(const DevTables& T, u32 op, const u64* a, const u64* b, 
                         cudaStream_t st, u64 b_stride = 0);
 // count pairs [count][2][ell][N] -> [count][3][ell][N].
 void launch_tensor(const DevTables& T, const u64* a, const u64* b, u64* out, u32 ell, u32 count, cudaStream_t st);
-void launch_decrypt(const DevTables& T, const u64* ct, const u64* s, u64* pt, u32 ell, cudaStream_t st);
+void launch_decrypt(const DevTables& T, const u64* ct, const u64* s, u64* pt, u32 ell, cudaStream_t st, u32 size = 2);
 // polys polynomials [polys][ell][N] -> [polys][ell-1][N]; top_tmp: [polys][N] scratch.
 void launch_rescale(const DevTables& T, const u64* ct, u32 ell, u32 polys, u64* top_tmp, u64* out, cudaStream_t st);
 // count inputs x_ntt + c * x_stride ([ell][N] each) -> digits [count][ell][ell+1][N];
@@ -113,6 +113,17 @@ struct KsPlan {
   u32 R, B, add_perm, pad;
 };
 void launch_keyswitch(const DevTables& T, u32 ell, const KsPlan& plan, cudaStream_t st);
+// ---- kern_hybrid.cu: hybrid key switching (digits of H.alpha data primes, H.K special primes).
+// ModUp of count inputs x_ntt + c x_stride ([ell][N]) -> digits [count][dnum][ell + K][N] (W words);
+// y_coef_tmp: [count][ell][N] scratch.
+void launch_modup_hyb(const DevTables& T, const HybTables& H, const u64* x_ntt, u64 x_stride, u32 count, u32 ell,
+                      u64* y_coef_tmp, u64* digits, cudaStream_t st);
+// The inner products and the ModDown of a plan over hybrid digits (digits_b = dnum (ell + K) N words
+// per request); plan.top is [R][B][2][K][N] scratch.
+void launch_keyswitch_hyb(const DevTables& T, const HybTables& H, u32 ell, const KsPlan& plan, cudaStream_t st);
+// Switching key of level Kt: [dnum(Kt)][2][Kt + K][N] (kern_sample.cu).
+void launch_keygen_switch_hyb(const DevTables& T, const HybTables& H, u64 seed, u32 kind, const u64* s, u32 Kt,
+                              u64* ksk, cudaStream_t st);
 // Relinearization of plan.B tensor products (R = 1, addends add0/add1 = d0, d1) with the rescale by
 // q_{ell-1} in the same rounding: out + rq out_b receives [2][ell-1][N]; top2 scratch [B][2][N].
 void launch_relin_rescale(const DevTables& T, const HostTables& H, u32 ell, const KsPlan& plan, u64* top2,

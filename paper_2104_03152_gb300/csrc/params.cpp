@@ -201,6 +201,86 @@ bool build_tables(u32 log_n, const std::vector<u64>& chain, HostTables& out) {
   return true;
 }
 
+std::vector<u64> hyb_constants(const std::vector<u64>& chain, u32 L, u32 K, u32 alpha, HybTables* H) {
+  const u32 nm = L + K, dn = (L + alpha - 1) / alpha, V = dn * alpha;
+  std::vector<u64> v;
+  auto section = [&](size_t words) {
+    const size_t off = v.size();
+    v.resize(off + words, 0);
+    return off;
+  };
+  const size_t o_inv = section((size_t)V * alpha * 2), o_conv = section((size_t)V * alpha * nm),
+               o_qg = section((size_t)V * nm), o_dinv = section((size_t)K * 2), o_dconv = section((size_t)K * nm),
+               o_dP = section(nm), o_pinv = section((size_t)L * 2);
+  // ModUp: digit j holding r primes q_{j alpha + m}, m < r
+  for (u32 j = 0; j < dn; ++j)
+    for (u32 r = 1; r <= alpha; ++r) {
+      if (j * alpha + r > L) break;
+      const u32 var = j * alpha + (r - 1);
+      for (u32 m = 0; m < r; ++m) {
+        const u64 qi = chain[j * alpha + m];
+        u64 hat = 1;  // (Q_v / q_i) mod q_i
+        for (u32 m2 = 0; m2 < r; ++m2)
+          if (m2 != m) hat = mulmod_h(hat, chain[j * alpha + m2] % qi, qi);
+        const u64 inv = invmod_h(hat, qi);
+        v[o_inv + ((size_t)var * alpha + m) * 2] = inv;
+        v[o_inv + ((size_t)var * alpha + m) * 2 + 1] = shoup_of(inv, qi);
+        for (u32 t = 0; t < nm; ++t) {
+          const u64 qt = chain[t];
+          u64 c = 1 % qt;  // (Q_v / q_i) mod q_t
+          for (u32 m2 = 0; m2 < r; ++m2)
+            if (m2 != m) c = mulmod_h(c, chain[j * alpha + m2] % qt, qt);
+          v[o_conv + ((size_t)var * alpha + m) * nm + t] = c;
+        }
+      }
+      for (u32 t = 0; t < nm; ++t) {
+        const u64 qt = chain[t];
+        u64 c = 1 % qt;  // Q_v mod q_t
+        for (u32 m = 0; m < r; ++m) c = mulmod_h(c, chain[j * alpha + m] % qt, qt);
+        v[o_qg + (size_t)var * nm + t] = c;
+      }
+    }
+  // ModDown: P = p_0 ... p_{K-1}
+  for (u32 k = 0; k < K; ++k) {
+    const u64 pk = chain[L + k];
+    u64 hat = 1 % pk;
+    for (u32 k2 = 0; k2 < K; ++k2)
+      if (k2 != k) hat = mulmod_h(hat, chain[L + k2] % pk, pk);
+    const u64 inv = invmod_h(hat, pk);
+    v[o_dinv + 2 * k] = inv;
+    v[o_dinv + 2 * k + 1] = shoup_of(inv, pk);
+    for (u32 t = 0; t < nm; ++t) {
+      const u64 qt = chain[t];
+      u64 c = 1 % qt;
+      for (u32 k2 = 0; k2 < K; ++k2)
+        if (k2 != k) c = mulmod_h(c, chain[L + k2] % qt, qt);
+      v[o_dconv + (size_t)k * nm + t] = c;
+    }
+  }
+  for (u32 t = 0; t < nm; ++t) {
+    const u64 qt = chain[t];
+    u64 c = 1 % qt;
+    for (u32 k = 0; k < K; ++k) c = mulmod_h(c, chain[L + k] % qt, qt);
+    v[o_dP + t] = c;
+    if (t < L) {
+      const u64 inv = invmod_h(c, qt);
+      v[o_pinv + 2 * t] = inv;
+      v[o_pinv + 2 * t + 1] = shoup_of(inv, qt);
+    }
+  }
+  H->alpha = alpha;
+  H->K = K;
+  const size_t offs[7] = {o_inv, o_conv, o_qg, o_dinv, o_dconv, o_dP, o_pinv};
+  const u64** fields[7] = {&H->up_inv, &H->up_conv, &H->up_qg, &H->down_inv, &H->down_conv, &H->down_P, &H->pinv};
+  for (int f = 0; f < 7; ++f) *fields[f] = reinterpret_cast<const u64*>(offs[f]);
+  return v;
+}
+
+void hyb_bind(const u64* d_base, HybTables* H) {
+  const u64** fields[7] = {&H->up_inv, &H->up_conv, &H->up_qg, &H->down_inv, &H->down_conv, &H->down_P, &H->pinv};
+  for (int f = 0; f < 7; ++f) *fields[f] = d_base + reinterpret_cast<size_t>(*fields[f]);
+}
+
 u64 galois_element(u32 log_n, int64_t step) {
   const int64_t half = (int64_t)1 << (log_n - 1);
   int64_t k = step % half;

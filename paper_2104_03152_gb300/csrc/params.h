@@ -26,6 +26,11 @@ u64 smallest_psi(u64 q, u32 log_n);
 u64 invmod_h(u64 a, u64 q);
 u64 shoup_of(u64 w, u64 q);
 bool build_tables(u32 log_n, const std::vector<u64>& chain, HostTables& out);
+// Constants of hybrid key switching for the chain (L data primes, then K special primes): one flat
+// array (layout of HybTables, sections in its field order); H receives alpha, K and every section's
+// offset into the array, which hyb_bind turns into device pointers once the array is on the device.
+std::vector<u64> hyb_constants(const std::vector<u64>& chain, u32 L, u32 K, u32 alpha, HybTables* H);
+void hyb_bind(const u64* d_base, HybTables* H);
 // 5^step mod 2N with step taken modulo N/2 (left rotation by `step` slots).
 u64 galois_element(u32 log_n, int64_t step);
 

@@ -230,6 +230,7 @@ tcks_status run_batch(const tcks_ct* const* x, u32 count, tcks_ct** outs, F&& fn
     tcks_ctx* c = x[0]->ctx;
     for (u32 i = 0; i < count; ++i) {
       if (!x[i] || x[i]->ctx != c) fail(TCKS_ERR_INVALID_ARG, "ciphertext missing or of another context");
+      need_relinearized(x[i]);
       if (x[i]->level != x[0]->level) fail(TCKS_ERR_LEVEL_MISMATCH, "the batch's ciphertexts differ in level");
       if (x[i]->scale != x[0]->scale) fail(TCKS_ERR_SCALE_MISMATCH, "the batch's ciphertexts differ in scale");
     }

@@ -159,6 +159,7 @@ tcks_status tcks_server_submit(tcks_server* s, uint32_t lane, const tcks_ct* in,
   if (lane >= s->lanes.size()) fail(TCKS_ERR_INVALID_ARG, "no such lane");
   const Lane& L = s->lanes[lane];
   if (in->ctx != L.ctx) fail(TCKS_ERR_INVALID_ARG, "ciphertext belongs to another context");
+  need_relinearized(in);
   const u32 want = L.is_cnn ? cnn_stage_level(L.cnn, 0) : L.M->level;
   if (in->level != want) fail(TCKS_ERR_LEVEL_MISMATCH, "request ciphertext at the wrong level for this lane");
   if (s->resident + L.req_bytes > s->budget)

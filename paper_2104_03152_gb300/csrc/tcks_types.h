@@ -42,6 +42,21 @@ struct Crt2 {
   u32 pinv_sh32;       // floor(pinv_l 2^32 / q_l) (narrow chains, q_l < 2^31; 0 otherwise)
 };
 
+// Constants of hybrid key switching (digits of alpha data primes, K special primes with product P),
+// device pointers. A "group variant" v = j alpha + (r - 1) is digit j holding r primes (the last
+// digit of a level holds fewer than alpha); its members are q_{j alpha + m}, m < r, and Q_v their
+// product.
+struct HybTables {
+  const u64* up_inv;     // [variant][alpha][2]: (Q_v / q_i)^-1 mod q_i and its Shoup companion
+  const u64* up_conv;    // [variant][alpha][n_mods]: (Q_v / q_i) mod t
+  const u64* up_qg;      // [variant][n_mods]: Q_v mod t
+  const u64* down_inv;   // [K][2]: (P / p_k)^-1 mod p_k and its Shoup companion
+  const u64* down_conv;  // [K][n_mods]: (P / p_k) mod t
+  const u64* down_P;     // [n_mods]: P mod t
+  const u64* pinv;       // [L][2]: P^-1 mod q_i and its Shoup companion
+  u32 alpha, K;
+};
+
 // Everything a kernel needs about the modulus chain, passed by value.
 struct DevTables {
   const ModConst* mods;    // [n_mods]
@@ -49,8 +64,8 @@ struct DevTables {
   const u64* tw;           // [n_mods][4][N]: psi^brv(k), Shoup, psi^-brv(k), Shoup
   const u32* tw32;         // [n_mods][2][N][2]: forward, inverse (twiddle, 32-bit Shoup) pairs (narrow chains only)
   u32 log_n;
-  u32 n_mods;  // L + 1
-  u32 L;       // number of data primes; P is chain index L
+  u32 n_mods;  // L + K (L + 1 with the one-prime key switch)
+  u32 L;       // number of data primes; the special primes (P) follow at chain index L ...
   u32 narrow;  // every prime < 2^31: kernels use 32-bit arithmetic
   u32 limb_threads;  // threads per CTA of the limb kernels (0 = the default for N), set by the autotuner
   u32 pad2;

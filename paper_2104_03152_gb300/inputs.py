@@ -1,7 +1,7 @@
 """Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
 
 This module holds no CKKS arithmetic: it only draws numbers (numpy's default_rng) in the shapes of the
-paper's workloads (§4: a 28x28 MNIST-sized image in [0, 1], conv 4x7x7 stride 3, FC 256->64, FC
+paper's workloads (§5: a 28x28 MNIST-sized image in [0, 1], conv 4x7x7 stride 3, FC 256->64, FC
 64->10) and of the primitive sweeps. The MNIST set and trained weights are not available, so seeded
 uniform images and N(0, 0.1) weights stand in for them.
 """

@@ -1,4 +1,4 @@
-"""CKKSTensor (§2.2): an N-dimensional tensor of reals encrypted as a tensor of ciphertexts, with
+"""CKKSTensor (§2.3): an N-dimensional tensor of reals encrypted as a tensor of ciphertexts, with
 optionally the first axis batched into the slots, on the GPU.
 
 The ciphertexts are the elements of the grid (the shape without the batched axis) in C order, all in

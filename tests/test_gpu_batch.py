@@ -176,3 +176,34 @@ def test_profiler_counts_butterflies_and_calibration(ctxs):
     assert launches == 1 and by == 16 * o.N * 32 and ops == 32 * (o.N // 2) * o.log_n
     assert tk.calibrate_butterflies(64) > 1e10 and tk.calibrate_butterflies(32) > 1e10
     assert tk.calibrate_macs(64) > 1e10 and tk.calibrate_macs(32) > tk.calibrate_macs(64)
+
+
+def test_batch_submit_wait_and_timeout(ctxs):
+    """tcks_batch_submit queues a job table and returns a handle; tcks_batch_wait reports TIMEOUT while
+    the work cannot have finished (the context's stream is held by a bounded GPU sleep of about a
+    second queued before it), then OK, with the results of the single calls."""
+    if not hasattr(torch.cuda, "_sleep"):
+        pytest.skip("torch.cuda._sleep is not available")
+    o, _ = ctxs[13]
+    st = torch.cuda.Stream()
+    g = tk.Context(tk.Params(13, primes=o.primes, scale=2.0 ** 50), seed=SEED, flags=tk.TCKS_AUTO_RELIN,
+                   stream=st.cuda_stream)
+    x = inputs.random_limbs(o.primes[:8], o.N, 41, polys=4)
+    d = _dev(x)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(st):
+        torch.cuda._sleep(2_000_000_000)  # ~1 s at 2 GHz, ends by itself
+    b = tk.Batch([(g, tk.JOB_NTT, 0, 4, 8, d.data_ptr(), d.data_ptr())])
+    with pytest.raises(tk.TcksError) as e:
+        b.wait(1_000_000)
+    assert e.value.name == "TIMEOUT"
+    b.wait(60_000_000_000)
+    b.wait(0)  # completed work polls as done
+    single = _dev(x)
+    g.ntt_inplace(single.data_ptr(), 4, 8, inverse=False)
+    g.synchronize()
+    assert np.array_equal(_host(d, x.shape), _host(single, x.shape))
+    del b
+    with pytest.raises(tk.TcksError) as e:  # validation fails before anything is queued
+        tk.Batch([(g, 7, 0, 1, 8, d.data_ptr(), d.data_ptr())])
+    assert e.value.name == "INVALID_ARG"

@@ -1,4 +1,4 @@
-"""The encrypted MNIST-shaped CNN of §4 (config C2: N=8192, [31,26x6|31], scale 2^26) on the GPU versus
+"""The encrypted MNIST-shaped CNN of §5 (config C2: N=8192, [31,26x6|31], scale 2^26) on the GPU versus
 the oracle: identical encoded weights, identical Galois steps, bit-identical output ciphertext, and
 the decrypted logits against the FP64 network."""
 import numpy as np
@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import paper_2104_03152_gb300 as tk
-from gpu_common import SEED, assert_ct_equal
+from gpu_common import SEED, assert_ct_equal, assert_encoding_agrees
 from paper_2104_03152_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -37,15 +37,77 @@ def test_cnn_steps_and_keys(setup):
         assert np.array_equal(ctx.export_key(tk.KEY_GALOIS, st), o.galois[st].data)
 
 
+def model_plaintexts(o, w, m, *, rect, conv_hoist=False, conv_shared=False, pack_first=False, windows=64):
+    """Every plaintext the GPU model holds except the biases, each checked against the oracle's own
+    encoding of the same slot values (assert_encoding_agrees: equal integers, or one apart where the
+    oracle's value before rounding lies within the FP64 bound of a .5 tie): the conv kernels, the pack
+    masks, the shared convolution's baby-step diagonals (extended basis), and every diagonal of both
+    fully connected layers in the basis the model keeps (extended when it holds the P limb; the
+    normal-basis export must be its prefix). Returns the oracle EncodedCNN made of those checked
+    plaintexts and the number of near-tie coefficients met."""
+    L = o.L
+    K, taps = w.conv_w.shape
+    baby, _ = o.conv_bsgs_steps(taps, windows)
+    nb = len(baby) + 1
+    enc = oracle.EncodedCNN(windows=windows, taps=taps, rect=rect, conv_hoist=conv_hoist, conv_shared=conv_shared,
+                            pack_first=pack_first)
+    ties = 0
+    for k in range(K):
+        ks = o.kernel_slots(w.conv_w[k], windows)
+        data, sc = m.export_plaintext(0, k)
+        assert sc == o.scale
+        ties += assert_encoding_agrees(o, data, ks, sc, L, f"conv kernel {k}")
+        enc.conv.append(oracle.Pt(data, L, sc))
+        data, sc = m.export_plaintext(1, k)
+        assert sc == o.scale
+        ties += assert_encoding_agrees(o, data, oracle.cnn_mask_slots(o, k, windows, nb, pack_first), sc, L - 1,
+                                       f"mask {k}")
+        enc.masks.append(oracle.Pt(data, L - 1, sc))
+        if conv_shared:
+            got = np.stack([m.export_plaintext(7, k * nb + b)[0] for b in range(nb)])
+            for b, st in enumerate([0] + baby):
+                ties += assert_encoding_agrees(o, got[b], np.roll(ks, -st), o.scale, L, f"baby diagonal {k}/{b}")
+            enc.conv_baby_ext.append(got)
+    for name, Wm, lv, kn, ke in (("fc1", w.fc1_w, L - 3, 3, 5), ("fc2", w.fc2_w, L - 5, 4, 6)):
+        diags = o.matrix_diagonals_rect(Wm.T) if rect else o.matrix_diagonals(Wm.T)
+        ext = np.stack([m.export_plaintext(ke, i)[0] for i in range(len(diags))])
+        pts = []
+        for i, d in enumerate(diags):
+            data, sc = m.export_plaintext(kn, i)
+            assert sc == o.scale and np.array_equal(data, ext[i][:lv]), f"{name} diagonal {i}: normal basis"
+            ties += assert_encoding_agrees(o, ext[i], d, sc, lv, f"{name} diagonal {i}")
+            pts.append(oracle.Pt(np.ascontiguousarray(ext[i][:lv]), lv, sc))
+        setattr(enc, name, pts)
+        setattr(enc, name + "_ext", ext if ext.shape[1] == lv + 1 else None)
+    return enc, ties
+
+
+def model_biases(o, w, m, enc):
+    """The model's three biases as oracle plaintexts (levels L-2, L-4, L-6 at the scales the model
+    computed for them); check_biases compares them with the oracle after its forward pass has traced
+    the schedule's scales."""
+    enc.biases = []
+    for i in range(3):
+        data, sc = m.export_plaintext(2, i)
+        enc.biases.append(oracle.Pt(data, o.L - 2 - 2 * i, sc))
+    return enc
+
+
+def check_biases(o, w, enc, trace):
+    """Each bias at exactly the scale the oracle's schedule reaches where it is added, and its
+    encoding against the oracle's own encoding of the bias slot vector at that scale."""
+    ties = 0
+    for i, (pt, want, sc) in enumerate(zip(enc.biases, oracle.cnn_bias_slots(o, w, enc), trace["bias_scales"])):
+        assert pt.scale == sc, f"bias {i}: scale {pt.scale!r} != {sc!r}"
+        ties += assert_encoding_agrees(o, pt.data, want, sc, pt.level, f"bias {i}")
+    return ties
+
+
 def test_cnn_plaintexts_match_oracle(setup):
+    """The default (square-diagonal) model: every plaintext it holds against the oracle's encoding."""
     o, w, enc, ctx, model, need = setup
-    for k in range(4):
-        assert np.array_equal(model.export_plaintext(0, k)[0], enc.conv[k].data)
-        assert np.array_equal(model.export_plaintext(1, k)[0], enc.masks[k].data)
-    for i in range(0, 256, 17):
-        assert np.array_equal(model.export_plaintext(3, i)[0], enc.fc1[i].data)
-    for i in range(0, 64, 7):
-        assert np.array_equal(model.export_plaintext(4, i)[0], enc.fc2[i].data)
+    got, ties = model_plaintexts(o, w, model, rect=False)
+    print(f"square model: {ties} near-tie coefficients")
 
 
 def test_cnn_forward_parity(setup):
@@ -55,10 +117,8 @@ def test_cnn_forward_parity(setup):
     ct = o.encrypt_values(v, 77)
     trace = {}
     ref = oracle.cnn_forward(o, ct, w, enc, trace)
-    # the model's biases sit at the scales the oracle's schedule reaches
-    for i, sc in enumerate(trace["bias_scales"]):
-        data, gsc = model.export_plaintext(2, i)
-        assert gsc == sc
+    # the model's biases sit at the scales the oracle's schedule reaches, with the oracle's encodings
+    check_biases(o, w, model_biases(o, w, model, oracle.EncodedCNN()), trace)
     got = model.forward(ctx.ct_import(ct.data, ct.scale))
     assert_ct_equal(got, ref, "cnn forward")
     logits = ctx.decrypt_values(got, 10)
@@ -127,23 +187,11 @@ def test_cnn_double_hoisted_parity(setup):
         ctx.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE)
 
 
-def _near_tie_agreement(o, got: np.ndarray, ref: np.ndarray, level: int):
-    """Two encodings of the same values agree, or differ in integer coefficients by at most 1 (the
-    FFT and the oracle's direct sum round a near-tie coefficient differently, reading A9)."""
-    if np.array_equal(got, ref):
-        return 0
-    a = np.array(o.crt_compose(o.intt_limbs(got, level), level), dtype=object)
-    b = np.array(o.crt_compose(o.intt_limbs(ref, level), level), dtype=object)
-    d = np.abs(a - b)
-    assert d.max() <= 1
-    return int((d != 0).sum())
-
-
 def test_cnn_rect_parity(setup):
-    """Rectangular fully connected layers (TCKS_RECT_DIAG): the Galois steps, the encodings (equal to
-    the oracle's up to A9 near ties; the dense rectangular diagonals meet far more of them), and, run
-    on the same plaintexts, the forward pass bit-identical to the oracle's schedule with either
-    key-switch schedule, batched and single alike."""
+    """Rectangular fully connected layers (TCKS_RECT_DIAG): the Galois steps, every plaintext of the
+    model against the oracle's own encodings (equal up to A9 near ties, which the dense rectangular
+    diagonals meet far more often), and, run on those checked plaintexts, the forward pass
+    bit-identical to the oracle's schedule with either key-switch schedule, batched and single alike."""
     o, w, enc, ctx, model, need = setup
     base = tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE
     ctx.set_flags(base | tk.TCKS_RECT_DIAG)
@@ -152,28 +200,17 @@ def test_cnn_rect_parity(setup):
     finally:
         ctx.set_flags(base)
     assert rm.galois_steps() == oracle.cnn_galois_steps(o, rect=True)
-    renc = oracle.cnn_encode(o, w, rect=True)
-    L = o.L
-    # the model's own plaintexts, checked against the oracle's, then fed to the oracle's schedule
-    renc.fc1 = [oracle.Pt(rm.export_plaintext(3, i)[0], L - 3, o.scale) for i in range(64)]
-    renc.fc2 = [oracle.Pt(rm.export_plaintext(4, i)[0], L - 5, o.scale) for i in range(16)]
-    ext1 = np.stack([rm.export_plaintext(5, i)[0] for i in range(64)])
-    ext2 = np.stack([rm.export_plaintext(6, i)[0] for i in range(16)])
-    own1 = o.encode_matrix_rect_ext(w.fc1_w.T, L - 3)
-    ties = sum(_near_tie_agreement(o, ext1[i][:L - 3], own1[i][:L - 3], L - 3) for i in range(0, 64, 9))
-    print(f"rectangular FC1 diagonals: {ties} near-tie coefficients in 8 sampled diagonals")
-    renc.fc1_ext, renc.fc2_ext = ext1, ext2
-    renc.biases = []
-    for i in range(3):
-        data, sc = rm.export_plaintext(2, i)
-        renc.biases.append(oracle.Pt(data, L - 2 - 2 * i, sc))
+    renc, ties = model_plaintexts(o, w, rm, rect=True)
+    model_biases(o, w, rm, renc)
     img = inputs.mnist_like_image(5)
     v, W = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
     ct = o.encrypt_values(v, 79)
     for dh in (False, True):
         ctx.set_flags(base | (tk.TCKS_DOUBLE_HOIST if dh else 0))
         try:
-            ref = oracle.cnn_forward(o, ct, w, renc, double_hoist=dh)
+            trace = {}
+            ref = oracle.cnn_forward(o, ct, w, renc, trace, double_hoist=dh)
+            ties += check_biases(o, w, renc, trace)
             got = rm.forward(ctx.ct_import(ct.data, ct.scale))
             assert_ct_equal(got, ref, f"cnn forward (rectangular, double hoist {dh})")
             assert float(np.max(np.abs(ctx.decrypt_values(got, 10) - oracle.cnn_plain(img, w)))) < 5e-3
@@ -181,12 +218,14 @@ def test_cnn_rect_parity(setup):
             assert np.array_equal(b[1].export(), got.export())
         finally:
             ctx.set_flags(base)
+    print(f"rectangular model: {ties} near-tie coefficients")
 
 
 def test_cnn_hoisted_conv_parity(setup):
-    """TCKS_CONV_HOIST + TCKS_RECT_DIAG + double hoisting (the bench's network): the convolution sums as
-    two hoisted rotation sums; Galois steps as the oracle's schedule, and on the model's own encodings
-    the forward pass bit-identical to the oracle's, single and batched."""
+    """TCKS_CONV_HOIST + TCKS_RECT_DIAG + double hoisting: the convolution sums as two hoisted rotation
+    sums; Galois steps as the oracle's schedule, every plaintext of the model against the oracle's
+    encodings, and on those plaintexts the forward pass bit-identical to the oracle's, single and
+    batched."""
     o, w, enc, ctx, model, need = setup
     base = tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE
     ctx.set_flags(base | tk.TCKS_RECT_DIAG | tk.TCKS_CONV_HOIST | tk.TCKS_DOUBLE_HOIST)
@@ -198,25 +237,20 @@ def test_cnn_hoisted_conv_parity(setup):
             if st not in o.galois or o.galois[st].level < lv:
                 o.gen_galois_key(st, lv)
         hm.gen_keys()
-        henc = oracle.cnn_encode(o, w, rect=True, conv_hoist=True)
-        L = o.L
-        henc.fc1 = [oracle.Pt(hm.export_plaintext(3, i)[0], L - 3, o.scale) for i in range(64)]
-        henc.fc2 = [oracle.Pt(hm.export_plaintext(4, i)[0], L - 5, o.scale) for i in range(16)]
-        henc.fc1_ext = np.stack([hm.export_plaintext(5, i)[0] for i in range(64)])
-        henc.fc2_ext = np.stack([hm.export_plaintext(6, i)[0] for i in range(16)])
-        henc.biases = []
-        for i in range(3):
-            data, sc = hm.export_plaintext(2, i)
-            henc.biases.append(oracle.Pt(data, L - 2 - 2 * i, sc))
+        henc, ties = model_plaintexts(o, w, hm, rect=True, conv_hoist=True)
+        model_biases(o, w, hm, henc)
         img = inputs.mnist_like_image(6)
         v, W = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
         ct = o.encrypt_values(v, 81)
-        ref = oracle.cnn_forward(o, ct, w, henc, double_hoist=True)
+        trace = {}
+        ref = oracle.cnn_forward(o, ct, w, henc, trace, double_hoist=True)
+        ties += check_biases(o, w, henc, trace)
         got = hm.forward(ctx.ct_import(ct.data, ct.scale))
         assert_ct_equal(got, ref, "cnn forward (hoisted convolution)")
         assert float(np.max(np.abs(ctx.decrypt_values(got, 10) - oracle.cnn_plain(img, w)))) < 5e-3
         b = hm.forward_batch([ctx.ct_import(ct.data, ct.scale)] * 3)
         assert np.array_equal(b[2].export(), got.export())
+        print(f"hoisted-convolution model: {ties} near-tie coefficients")
     finally:
         ctx.set_flags(base)
 
@@ -241,30 +275,15 @@ def test_cnn_shared_conv_parity(setup, pack, merged):
             if st not in o.galois or o.galois[st].level < lv:
                 o.gen_galois_key(st, lv)
         hm.gen_keys()
-        henc = oracle.cnn_encode(o, w, rect=True, conv_hoist=True, conv_shared=True, pack_first=pack)
-        L = o.L
-        nb = len(o.conv_bsgs_steps(49, 64)[0]) + 1
-        for k in range(4):
-            got_ext = np.stack([hm.export_plaintext(7, k * nb + b)[0] for b in range(nb)])
-            for b in range(nb):  # the data limbs (the P limb follows from the same integers)
-                _near_tie_agreement(o, np.ascontiguousarray(got_ext[b, :L]),
-                                    np.ascontiguousarray(henc.conv_baby_ext[k][b, :L]), L)
-            henc.conv_baby_ext[k] = got_ext
-            mask = hm.export_plaintext(1, k)[0]
-            _near_tie_agreement(o, mask, henc.masks[k].data, L - 1)
-            henc.masks[k] = oracle.Pt(mask, L - 1, o.scale)
-        henc.fc1 = [oracle.Pt(hm.export_plaintext(3, i)[0], L - 3, o.scale) for i in range(64)]
-        henc.fc2 = [oracle.Pt(hm.export_plaintext(4, i)[0], L - 5, o.scale) for i in range(16)]
-        henc.fc1_ext = np.stack([hm.export_plaintext(5, i)[0] for i in range(64)])
-        henc.fc2_ext = np.stack([hm.export_plaintext(6, i)[0] for i in range(16)])
-        henc.biases = []
-        for i in range(3):
-            data, sc = hm.export_plaintext(2, i)
-            henc.biases.append(oracle.Pt(data, L - 2 - 2 * i, sc))
+        henc, ties = model_plaintexts(o, w, hm, rect=True, conv_hoist=True, conv_shared=True, pack_first=pack)
+        model_biases(o, w, hm, henc)
         img = inputs.mnist_like_image(7)
         v, W = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
         ct = o.encrypt_values(v, 83)
-        ref = oracle.cnn_forward(o, ct, w, henc, double_hoist=True, merged=merged)
+        trace = {}
+        ref = oracle.cnn_forward(o, ct, w, henc, trace, double_hoist=True, merged=merged)
+        ties += check_biases(o, w, henc, trace)
+        print(f"shared-convolution model (pack {pack}, merged {merged}): {ties} near-tie coefficients")
         got = hm.forward(ctx.ct_import(ct.data, ct.scale))
         assert_ct_equal(got, ref, "cnn forward (shared convolution)")
         assert float(np.max(np.abs(ctx.decrypt_values(got, 10) - oracle.cnn_plain(img, w)))) < 5e-3
@@ -337,8 +356,10 @@ def test_cnn_forward_wire_equals_batch(setup):
     assert e.value.name == "INVALID_ARG"
     bad = host_in.copy()
     bad[2 * seeded - 4:2 * seeded] = 0xFF  # the last residue of the second input's c0 above its prime
+    host_out[:] = 0xAB
     with pytest.raises(tk.TcksError) as e:
         model.forward_wire(bad, 3, host_out)
     assert e.value.name == "INVALID_ARG"
+    assert np.all(host_out == 0xAB), "a refused batch wrote into the output buffer"
     model.forward_wire(host_in, 3, host_out)  # the context is still usable
     assert host_out[:out_size].tobytes() == want[0]

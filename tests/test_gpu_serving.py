@@ -46,7 +46,40 @@ def vm():
     return ctx, mat, reqs, singles
 
 
-def test_continuous_batching_mix_is_bit_identical(cnn, vm):
+BENCH_CNN_FLAGS = (tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | tk.TCKS_RECT_DIAG | tk.TCKS_CONV_HOIST
+                   | tk.TCKS_CONV_SHARED | tk.TCKS_CONV_PACK | tk.TCKS_MERGED_RESCALE | tk.TCKS_DOUBLE_HOIST)
+
+
+@pytest.fixture(scope="module")
+def bench_lanes():
+    """The lanes in the layout the benchmark serves: the CNN with rectangular FC layers, shared baby
+    steps, channels packed before the giant steps, ModDown and rescale merged and double hoisting; the
+    vector x matrix product in rectangular form, double hoisted."""
+    ctx = tk.Context(tk.Params(13, BITS, 2.0 ** 26), seed=SEED, flags=BENCH_CNN_FLAGS)
+    w = inputs.cnn_weights(4)
+    model = tk.CNN(ctx, w["conv_w"], w["conv_b"], w["fc1_w"], w["fc1_b"], w["fc2_w"], w["fc2_b"], windows=64)
+    model.gen_keys()
+    reqs = []
+    for i in range(8):
+        v, _ = tk.im2col_encode(inputs.mnist_like_image(320 + i), 7, 7, 3, ctx.slots)
+        reqs.append(ctx.encrypt_values(v, 920 + i))
+    singles = [model.forward(c).export() for c in reqs]
+    vctx = tk.Context(tk.Params(12, [55, 40, 40, 56], 2.0 ** 40), seed=SEED,
+                      flags=tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | tk.TCKS_DOUBLE_HOIST)
+    n, m = 64, 10
+    o = oracle.OracleCKKS(12, [55, 40, 40, 56], 2.0 ** 40)
+    vctx.gen_galois_keys(o.vecmat_rect_steps(n, m))
+    mat = vctx.matrix_encode_rect(inputs.random_matrix(n, m, 8, 0.5), level=3)
+    vreqs = []
+    for i in range(3):
+        v = np.zeros(vctx.slots)
+        v[:n] = inputs.uniform_slots(n, 60 + i)
+        vreqs.append(vctx.encrypt_values(v, 760 + i))
+    vsingles = [c.vecmat_plain(mat).export() for c in vreqs]
+    return (ctx, model, reqs, singles), (vctx, mat, vreqs, vsingles)
+
+
+def _mix_is_bit_identical(cnn, vm):
     ctx, model, reqs, singles = cnn
     vctx, mat, vreqs, vsingles = vm
     srv = tk.Server(hbm_budget_bytes=200 << 30, max_in_flight=64, max_batch=4)
@@ -76,6 +109,15 @@ def test_continuous_batching_mix_is_bit_identical(cnn, vm):
         kind, i = ids[rid]
         ref = singles[i] if kind == "cnn" else vsingles[i]
         assert np.array_equal(out, ref), (kind, i)
+
+
+def test_continuous_batching_mix_is_bit_identical(cnn, vm):
+    _mix_is_bit_identical(cnn, vm)
+
+
+def test_continuous_batching_mix_bench_layout(bench_lanes):
+    """The same alone-versus-mix identity for the layout the benchmark's served trace uses."""
+    _mix_is_bit_identical(*bench_lanes)
 
 
 def test_budget_admission(cnn):

@@ -1,4 +1,4 @@
-"""CKKSTensor (§2.2) on the GPU through the C ABI (ciphertext arrays) versus the oracle's tensor,
+"""CKKSTensor (§2.3) on the GPU through the C ABI (ciphertext arrays) versus the oracle's tensor,
 bit-exact ciphertext by ciphertext after every operation, on a 64-bit chain and on C2's 32-bit chain;
 plus the array ABI's argument errors."""
 import ctypes

@@ -1,5 +1,5 @@
 """The bit-packed wire format on the GPU: byte-identical to the oracle's serializer, round trips, the
-range and header checks, and the size of one encrypted CNN inference's traffic (§4)."""
+range and header checks, and the size of one encrypted CNN inference's traffic (§5)."""
 import numpy as np
 import pytest
 

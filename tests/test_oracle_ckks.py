@@ -197,6 +197,69 @@ def test_tiny_rotation(tiny):
         assert t.to_int(r.data[1], idx) == k1
 
 
+def test_tiny_three_component_ciphertext(tiny):
+    """An unrelinearized product (c0, c1, c2): decryption c0 + c1 s + c2 s^2, the rescale of every
+    component, mul_plain and the mixed-size sum, each against the big-integer definitions."""
+    o, t = tiny
+    from tiny_ckks import negacyclic_mul
+    lvl = 3
+    idx = list(range(lvl))
+    Q = math.prod(o.q[:lvl])
+    c3 = oracle.Ct(np.ascontiguousarray(inputs.random_limbs(o.q[:lvl], o.N, 31, polys=3)), lvl, 1.0)
+    C = [t.to_int(c3.data[p], idx) for p in range(3)]
+    S = t.to_int(o.s[:lvl], idx)
+    S2 = negacyclic_mul(S, S, Q)
+    c1s, c2s2 = negacyclic_mul(C[1], S, Q), negacyclic_mul(C[2], S2, Q)
+    want = [(a + b + c) % Q for a, b, c in zip(C[0], c1s, c2s2)]
+    assert t.to_int(o.decrypt(c3).data, idx) == want
+    rs = o.rescale(c3)
+    assert rs.data.shape[0] == 3
+    for p in range(3):
+        assert t.to_int(rs.data[p], idx[:-1]) == t.rescale(C[p], lvl)
+    pt = oracle.Pt(np.ascontiguousarray(inputs.random_limbs(o.q[:lvl], o.N, 32, polys=1)[0]), lvl, 1.0)
+    Pt_ = t.to_int(pt.data, idx)
+    mp = o.mul_plain(c3, pt)
+    for p in range(3):
+        assert t.to_int(mp.data[p], idx) == negacyclic_mul(C[p], Pt_, Q)
+    ap = o.add_plain(c3, pt)
+    assert t.to_int(ap.data[0], idx) == [(a + b) % Q for a, b in zip(C[0], Pt_)]
+    assert np.array_equal(ap.data[1:], c3.data[1:])
+    c2 = _rand_ct(o, lvl, 33)
+    D = [t.to_int(c2.data[p], idx) for p in range(2)]
+    sm = o.sub(c2, c3)  # a missing third component is zero
+    assert sm.data.shape[0] == 3
+    for p in range(3):
+        other = D[p] if p < 2 else [0] * o.N
+        assert t.to_int(sm.data[p], idx) == [(a - b) % Q for a, b in zip(other, C[p])]
+
+
+def test_three_component_product():
+    """The product without relinearization: its decryption is the product of the operands'
+    decryptions, limb by limb in NTT form (exactly: (a0 + a1 s)(b0 + b1 s) = d0 + d1 s + d2 s^2);
+    relinearizing it gives the relinearized product bit for bit; rescaled before relinearization it
+    still decrypts to x y. (The rescale's rounding error in c2 is multiplied by s^2 at decryption, so
+    the chain's primes match the scale here, 40-bit primes at 2^40, as a user of this order would
+    choose them.)"""
+    o = OracleCKKS(12, [60, 40, 40, 60], 2.0 ** 40).keygen()
+    x, y = inputs.uniform_slots(o.slots, 41), inputs.uniform_slots(o.slots, 42)
+    a, b = o.encrypt_values(x, 43), o.encrypt_values(y, 44)
+    d3 = o.mul(a, b, relin=False, rescale=False)
+    assert d3.data.shape == (3, o.L, o.N) and d3.scale == a.scale * b.scale
+    ma, mb, m3 = o.decrypt(a).data, o.decrypt(b).data, o.decrypt(d3).data
+    for l in range(o.L):
+        q = o.q[l]
+        want = [int(u) * int(v) % q for u, v in zip(ma[l], mb[l])]
+        assert np.array_equal(m3[l], np.array(want, dtype=np.uint64)), l
+    rel = o.relinearize_ct(d3)
+    assert np.array_equal(rel.data, o.mul(a, b, relin=True, rescale=False).data)
+    tol = 1e-3  # the products' noise at scale 2^30, as for the relinearized product
+    assert np.max(np.abs(o.decrypt_values(d3) - x * y)) < tol
+    r3 = o.mul(a, b, relin=False, rescale=True)
+    assert r3.data.shape == (3, o.L - 1, o.N)
+    assert np.max(np.abs(o.decrypt_values(r3) - x * y)) < tol
+    assert np.max(np.abs(o.decrypt_values(o.relinearize_ct(r3)) - x * y)) < tol
+
+
 # --------------------------------------------------------------------- exact invariants ----
 
 def test_automorphism_ntt_equals_coefficient_map(c1):

@@ -1,4 +1,4 @@
-"""Pins of the oracle's CKKSTensor (§2.2): every tensor operation decrypts to numpy's result on the
+"""Pins of the oracle's CKKSTensor (§2.3): every tensor operation decrypts to numpy's result on the
 same values (broadcasting, axes, reductions and products as numpy defines them), batched and not."""
 import numpy as np
 import pytest

@@ -16,7 +16,7 @@ def test_pack_worked_example():
 
 
 def test_cnn_traffic_closed_form():
-    """C2 chain: the encrypted input at level 7 and the output at level 1 (§4's 427 KB figure, with
+    """C2 chain: the encrypted input at level 7 and the output at level 1 (§5's 427 KB figure, with
     the configs' 218-bit chain instead of the paper's 206-bit one)."""
     primes = oracle.gen_primes(13, [31, 26, 26, 26, 26, 26, 26, 31])
     n = 8192
