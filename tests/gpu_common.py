@@ -12,9 +12,12 @@ SEED = 0x7E5EA1
 class Pair:
     """An oracle context and a GPU context with the same chain, scale and key seed."""
 
-    def __init__(self, log_n, bits, scale, flags=tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE, galois=(), key_level=None):
-        self.o = oracle.OracleCKKS(log_n, bits, scale, key_seed=SEED).keygen()
-        self.params = tk.Params(log_n, bits, scale)
+    def __init__(self, log_n, bits, scale, flags=tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE, galois=(), key_level=None,
+                 primes=None, n_special=1, alpha=1):
+        self.o = oracle.OracleCKKS(log_n, bits, scale, key_seed=SEED, primes=primes, n_special=n_special,
+                                   alpha=alpha).keygen()
+        self.params = tk.Params(log_n, bits, scale, primes=self.o.primes if (primes or n_special > 1 or alpha > 1)
+                                else None, n_special=n_special, alpha=alpha)
         assert self.params.primes == self.o.primes
         self.g = tk.Context(self.params, seed=SEED, flags=flags)
         self.steps = []
