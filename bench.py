@@ -236,6 +236,17 @@ def run_gpu(args, world, rank, local):
     for _ in range(args.warmup):
         model.forward_device(d_in_ptr, B, d_out_ptr)
     ctx.synchronize()
+    # launch shape: the hand-tuned default, then the autotuner's choice (kept for the timed region)
+    _, hand_ms = timed(torch, stream, lambda: model.forward_device(d_in_ptr, B, d_out_ptr), 3)
+    tune_cache = os.path.join(tempfile.gettempdir(), "tcks_autotune.json")
+    tuned = model.autotune(B, tune_cache if args.tune_cache else None)
+    for _ in range(2):
+        model.forward_device(d_in_ptr, B, d_out_ptr)
+    _, tuned_ms = timed(torch, stream, lambda: model.forward_device(d_in_ptr, B, d_out_ptr), 3)
+    tune = {"limb_threads": tuned[0], "accumulation_requests_per_thread": tuned[1],
+            "hand_tuned_ms_per_step": hand_ms / 3, "autotuned_ms_per_step": tuned_ms / 3,
+            "searched": "limb-kernel CTA size {N/64, N/32, N/16 per slice} x accumulation requests per thread {1, 2}"}
+    ctx.synchronize()
     # plain path: one request per step
     plain_steps = max(3, min(args.steps, 10))
     for _ in range(2):
@@ -251,6 +262,7 @@ def run_gpu(args, world, rank, local):
     per_step, total_ms = timed(torch, stream, lambda: model.forward_device(d_in_ptr, B, d_out_ptr), args.steps)
     torch.cuda.nvtx.range_pop()
     tk.profile_stop()
+    dh_records = tk.profile_records("vecmat_dh_acc")
     launches = tk.launch_count() - n0
     barrier(world)
     torch.cuda.synchronize()
@@ -338,10 +350,8 @@ def run_gpu(args, world, rank, local):
     c4 = run_c4(torch, tk, args) if args.c4 else None
     serving = None
     if args.serve_seconds > 0:
-        lanes = {"cnn": (ctx, model, cts)}
         mix = args.serve_mix if c4 else 0.0
-        if c4:
-            lanes["vm"] = (c4["ctx"], c4["mat"], c4["cts"])
+        clients = serving_clients(torch, tk, args, (ctx, model, cts), (c4["ctx"], c4["mat"], c4["cts"]) if c4 else None)
         pct = lambda a, p: float(np.percentile(a, p) * 1e3) if len(a) else None
 
         def summary(lat, kind, thr):
@@ -352,27 +362,37 @@ def run_gpu(args, world, rank, local):
                     d[k] = {"requests": len(sel), "p50_ms": pct(sel, 50), "p99_ms": pct(sel, 99)}
             return d
         traces = []
+        total_s = args.serve_warmup + args.serve_seconds
         for rate in [float(x) for x in args.serve_rate.split(",")]:
-            arr = poisson_arrivals(rate, args.serve_seconds, 8)
-            kinds = np.where(np.random.default_rng(9).uniform(size=len(arr)) < mix, "vm", "cnn")
-            lat_s, kind_s, thr_s = serve_trace(tk, lanes, arr, kinds, args.serve_batch)
-            # the plain path saturates below the offered rate: run it on the start of the same trace
-            n_p = min(len(arr), args.plain_requests)
-            lat_p, kind_p, thr_p = plain_trace(tk, lanes, arr[:n_p], kinds[:n_p])
-            traces.append({"offered_rate": rate, "seconds": args.serve_seconds, "requests": len(arr),
+            arr = poisson_arrivals(rate, total_s, 8)
+            rng = np.random.default_rng(9)
+            kinds = np.where(rng.uniform(size=len(arr)) < mix, "vm", "cnn")
+            who = np.array([rng.integers(len(clients[k])) for k in kinds])
+            lat_s, kind_s, thr_s, st = serve_trace(tk, clients, arr, kinds, who, args.serve_batch, args.serve_warmup)
+            n_p = len(arr) if args.plain_requests <= 0 else min(len(arr), args.plain_requests)
+            lat_p, kind_p, thr_p = plain_trace(tk, clients, arr[:n_p], kinds[:n_p], who[:n_p], args.serve_warmup)
+            traces.append({"offered_rate": rate, "seconds": args.serve_seconds, "warmup_seconds": args.serve_warmup,
+                           "requests": int(np.sum(arr >= args.serve_warmup)),
                            "served": dict(summary(lat_s, kind_s, thr_s), max_batch_per_stage=args.serve_batch,
-                                          max_in_flight=1024, hbm_budget_gb=200),
-                           "plain": dict(summary(lat_p, kind_p, thr_p), trace_requests=int(n_p))})
+                                          max_in_flight=1024, hbm_budget_gb=200,
+                                          hbm_resident_gb=st["bytes_resident"] / 1e9),
+                           "plain": dict(summary(lat_p, kind_p, thr_p),
+                                         trace_requests=int(np.sum(arr[:n_p] >= args.serve_warmup)))})
         serving = {"mix": {"cnn": 1.0 - mix, "vm": mix}, "vm_workload": C4_WORKLOAD if c4 else None,
+                   "clients": {"cnn": len(clients["cnn"]), "vm": len(clients["vm"]),
+                               "key_sets": "one context (own secret, relinearization and Galois keys) per client"},
                    "latency": "arrival -> result exported to the host", "traces": traces}
+        del clients
     if c4:
         for k in ("ctx", "mat", "cts"):
             c4.pop(k)
     word = 32 if max(ctx.primes) < 2 ** 31 else 64
     bfly_peak = tk.calibrate_butterflies(word)
     mac_peak = tk.calibrate_macs(word)
+    dh_peaks = {ell: tk.calibrate_dh_macs(ell) for ell in sorted({t & 0xFF for t, _, _ in dh_records})}
     primitives = primitives_summary(torch, tk) if args.primitives else None
-    return dict(galois_keys=len(model.galois_steps()), single=single, c4=c4, primitives=primitives, bfly_peak=bfly_peak, mac_peak=mac_peak, word=word, serving=serving, total_ms=total_ms, per_step=per_step, prof=prof, launches=launches, clocks=clk, e2e_s=e2e_s,
+    return dict(galois_keys=len(model.galois_steps()), single=single, c4=c4, primitives=primitives, bfly_peak=bfly_peak,
+                mac_peak=mac_peak, dh_records=dh_records, dh_peaks=dh_peaks, word=word, tune=tune, serving=serving, total_ms=total_ms, per_step=per_step, prof=prof, launches=launches, clocks=clk, e2e_s=e2e_s,
                 e2e_steps=e2e_steps, h2d=host_in.nbytes, d2h=host_out.nbytes, max_err=max_err, wire_s=wire_s,
                 wire_h2d=wire_in.nbytes + 8 * B, wire_d2h=wire_out.nbytes + 4, wire_sizes=(seeded_sz, out_sz),
                 plain_ms=plain_total / plain_steps, plain_times=plain_times)
@@ -388,32 +408,73 @@ def poisson_arrivals(rate: float, seconds: float, seed: int) -> np.ndarray:
         out.append(t)
 
 
-def _finish(tk, lanes, kind, ct, hosts):
+def _finish(tk, ctx, ct, hosts):
     """Export a result to the host (the end of a request's latency)."""
-    if kind not in hosts:
-        level = ct.info()[0]
-        hosts[kind] = np.zeros((2, level, lanes[kind][0].N), dtype=np.uint64)
-    h = hosts[kind]
+    key = (ctx.N, ct.info()[0])
+    if key not in hosts:
+        hosts[key] = np.zeros((2, key[1], ctx.N), dtype=np.uint64)
+    h = hosts[key]
     tk.check(tk.lib().tcks_ct_export(ct.h, tk._p(h), h.size))
 
 
-def serve_trace(tk, lanes, arrivals, kinds, max_batch):
-    """Continuous batching over the lanes (CNN; vector x matrix): requests are submitted when their
-    arrival time passes and join their lane at its next launch; latency = arrival -> result exported
-    to the host."""
+def serving_clients(torch, tk, args, cnn0, vm0):
+    """The client population of the serving trace: args.cnn_clients CNN clients and args.vm_clients
+    vector x matrix clients, each with its own key set (its own context, key seed SEED_KEYS + client),
+    model or matrix, and a pool of its own encrypted inputs. cnn0 / vm0 are client 0 of each kind."""
+    from paper_2104_03152_gb300 import inputs
+    out = {"cnn": [cnn0], "vm": [vm0] if vm0 else []}
+    w = inputs.cnn_weights(SEED_W)
+    ctx0 = cnn0[0]
+    for c in range(1, args.cnn_clients):
+        st = torch.cuda.Stream()
+        ctx = tk.Context(tk.Params(LOG_N, BITS, SCALE), seed=inputs.SEED_KEYS + c, flags=ctx0.flags,
+                         stream=st.cuda_stream)
+        ctx._torch_stream = st
+        model = tk.CNN(ctx, w["conv_w"], w["conv_b"], w["fc1_w"], w["fc1_b"], w["fc2_w"], w["fc2_b"], windows=64)
+        model.gen_keys()
+        pool = []
+        for i in range(4):
+            v, _ = tk.im2col_encode(inputs.mnist_like_image(SEED_IMG + 100 * c + i), 7, 7, 3, ctx.slots)
+            pool.append(ctx.encrypt_values(v, SEED_ENC + 100 * c + i))
+        out["cnn"].append((ctx, model, pool))
+    if vm0:
+        vctx0 = vm0[0]
+        for c in range(1, args.vm_clients):
+            st = torch.cuda.Stream()
+            ctx = tk.Context(tk.Params(14, [60, 40, 40, 60], 2.0 ** 40), seed=inputs.SEED_KEYS + 1000 + c,
+                             flags=vctx0.flags, stream=st.cuda_stream)
+            ctx._torch_stream = st
+            ctx.gen_galois_keys([ctx.slots - C4_ROWS] + list(range(1, C4_COLS)) + [C4_COLS << j for j in range(4)])
+            mat = ctx.matrix_encode_rect(inputs.random_matrix(C4_ROWS, C4_COLS, 7, 0.05), level=3)
+            pool = []
+            for i in range(4):
+                z = np.zeros(ctx.slots)
+                z[:C4_ROWS] = inputs.normal_slots(C4_ROWS, 6 + 1000 * (100 * c + i))
+                pool.append(ctx.encrypt_values(z, 600 + 100 * c + i))
+            out["vm"].append((ctx, mat, pool))
+    torch.cuda.synchronize()
+    return out
+
+
+def serve_trace(tk, clients, arrivals, kinds, who, max_batch, warmup_s):
+    """Continuous batching over one lane per client (a CNN or a vector x matrix product on the client's
+    own key set), all under one HBM budget: requests are submitted when their arrival time passes and
+    join their lane at its next launch; latency = arrival -> result exported to the host. Requests
+    arriving in the first warmup_s seconds are served but not counted."""
     srv = tk.Server(hbm_budget_bytes=200 << 30, max_in_flight=1024, max_batch=max_batch)
-    lane_id = {"cnn": srv.add_cnn(lanes["cnn"][1])}
-    if "vm" in lanes:
-        lane_id["vm"] = srv.add_vecmat(lanes["vm"][1])
+    lane_of = {}
+    for kind, lst in clients.items():
+        for c, (ctx, model, pool) in enumerate(lst):
+            lane_of[(kind, c)] = srv.add_cnn(model) if kind == "cnn" else srv.add_vecmat(model)
     hosts, pending, lat, lat_kind = {}, {}, [], []
-    i, total = 0, len(arrivals)
+    i, total, finished = 0, len(arrivals), 0
     t0 = time.perf_counter()
-    while len(lat) < total:
+    while finished < total:
         now = time.perf_counter() - t0
         while i < total and arrivals[i] <= now:
-            k = kinds[i]
-            pool = lanes[k][2]
-            pending[srv.submit(lane_id[k], pool[i % len(pool)])] = (arrivals[i], k)
+            k, c = kinds[i], who[i]
+            pool = clients[k][c][2]
+            pending[srv.submit(lane_of[(k, c)], pool[i % len(pool)])] = (arrivals[i], k, c)
             i += 1
         st = srv.stats()
         if st["queued"] + st["in_flight"] == 0:
@@ -421,30 +482,36 @@ def serve_trace(tk, lanes, arrivals, kinds, max_batch):
             continue
         srv.step()
         for rid in srv.poll():
-            a, k = pending.pop(rid)
-            _finish(tk, lanes, k, srv.take(rid, lanes[k][0]), hosts)
-            lat.append(time.perf_counter() - t0 - a)
-            lat_kind.append(k)
-    span = time.perf_counter() - t0 - arrivals[0]
-    return np.array(lat), np.array(lat_kind), total / span
+            a, k, c = pending.pop(rid)
+            _finish(tk, clients[k][c][0], srv.take(rid, clients[k][c][0]), hosts)
+            finished += 1
+            if a >= warmup_s:
+                lat.append(time.perf_counter() - t0 - a)
+                lat_kind.append(k)
+    span = time.perf_counter() - t0 - warmup_s
+    stats = srv.stats()
+    return np.array(lat), np.array(lat_kind), len(lat) / span, stats
 
 
-def plain_trace(tk, lanes, arrivals, kinds):
-    """The plain path on the same trace: one request at a time in arrival order."""
-    hosts, lat = {}, []
+def plain_trace(tk, clients, arrivals, kinds, who, warmup_s):
+    """The plain path on the same trace: one request at a time in arrival order, each on its client's
+    key set; latencies counted after the warm-up as in serve_trace."""
+    hosts, lat, lat_kind = {}, [], []
     t0 = time.perf_counter()
     for i, a in enumerate(arrivals):
         now = time.perf_counter() - t0
         if now < a:
             time.sleep(a - now)
-        k = kinds[i]
-        ctx, model, pool = lanes[k]
+        k, c = kinds[i], who[i]
+        ctx, model, pool = clients[k][c]
         x = pool[i % len(pool)]
         out = model.forward(x) if k == "cnn" else x.vecmat_plain(model)
-        _finish(tk, lanes, k, out, hosts)
-        lat.append(time.perf_counter() - t0 - a)
-    span = time.perf_counter() - t0 - arrivals[0] if len(arrivals) else 1.0
-    return np.array(lat), np.array(kinds), len(arrivals) / span
+        _finish(tk, ctx, out, hosts)
+        if a >= warmup_s:
+            lat.append(time.perf_counter() - t0 - a)
+            lat_kind.append(k)
+    span = time.perf_counter() - t0 - warmup_s
+    return np.array(lat), np.array(lat_kind), len(lat) / span if span > 0 else 0.0
 
 
 # ------------------------------------------------------ vector x plain matrix at full size --
@@ -601,7 +668,7 @@ def time_graph(torch, ctx_stream, graph, reps):
     return sorted(evs[k].elapsed_time(evs[k + 1]) for k in range(reps))
 
 
-def sweep_point(torch, tk, ctxs, entries, op, peaks, gen, reps=20):
+def sweep_point(torch, tk, ctxs, entries, op, peaks, gen, reps=20, work=None):
     """entries: [(log_n, level, count)] forming one batch; returns a result dict."""
     jobs, keep, by, ops = [], [], 0.0, 0.0
     for log_n, level, count in entries:
@@ -609,7 +676,7 @@ def sweep_point(torch, tk, ctxs, entries, op, peaks, gen, reps=20):
         x, y = sweep_buffers(torch, c, op, level, count, gen)
         keep += [x, y]
         jobs.append(sweep_job(tk, c, op, level, count, x, y))
-        b, o = sweep_work(op, log_n, level, count)
+        b, o = (work or sweep_work)(op, log_n, level, count)
         by, ops = by + b, ops + o
     graph = tk.BatchGraph(jobs)
     first = time_graph(torch, jobs[0][0].stream, graph, 1)[0]
@@ -732,17 +799,64 @@ def run_sweep(args):
         torch.cuda.empty_cache()
 
 
+HYB_SPECIAL, HYB_ALPHA = 8, 8  # hybrid key switching at the sweep's largest shape: 4 digits of 8 primes, 8 special
+
+
+def ks_transforms(level: int, alpha: int = 1, special: int = 1) -> int:
+    """Length-N transforms of one key switch at `level`: the INTT of the input, the NTT of every converted
+    digit limb, the INTT of the special limbs and the NTT of the ModDown's conversions (2 components)."""
+    dn = -(-level // alpha)
+    return level + (dn * (level + special) - level) + 2 * special + 2 * level
+
+
+def hybrid_contexts(torch, tk, log_n: int, special: int, alpha: int):
+    from paper_2104_03152_gb300 import inputs
+    bits = SWEEP_BITS[:-1] + [60] * special
+    primes = tk.Params(log_n, bits, 2.0 ** 50).primes
+    st = torch.cuda.Stream()
+    c = tk.Context(tk.Params(log_n, primes=primes, scale=2.0 ** 50, n_special=special, alpha=alpha),
+                   seed=inputs.SEED_KEYS, flags=tk.TCKS_AUTO_RELIN, stream=st.cuda_stream)
+    c._torch_stream = st
+    c.gen_galois_keys([1])
+    return {log_n: c}
+
+
+def sweep_work_hybrid(op, log_n, level, count, special, alpha):
+    """(algorithmic bytes, algorithmic integer ops) of one hybrid job: inputs and outputs once, the key
+    (dnum digits x 2 x (level + K) limbs) once; transforms plus conversion and inner-product products."""
+    n, l = 1 << log_n, level
+    bf = 0.5 * n * log_n
+    dn = -(-l // alpha)
+    key = 8.0 * n * dn * 2 * (l + special)
+    per_ct_in = (3 if op == "relin" else 2) * l * n * 8.0
+    conv = (dn * (l + special) - l) * alpha + 2 * l * special  # base-conversion products per coefficient
+    inner = 2 * dn * (l + special)  # inner-product products per coefficient
+    ops = count * (ks_transforms(l, alpha, special) * bf + (conv + inner + 2 * l) * n)
+    return count * (per_ct_in + 2 * l * n * 8.0) + key, ops
+
+
 def primitives_summary(torch, tk):
-    """NTT and key-switch rates at the largest sweep shape (N = 2^16, L = 32, 64 ciphertexts)."""
+    """NTT and key-switch rates at the largest sweep shape (N = 2^16, L = 32, 64 ciphertexts), with the
+    one-prime key switch and with hybrid key switching (4 digits of 8 primes, 8 special primes)."""
     peaks = primitive_peaks(tk)
     ctxs = sweep_contexts(torch, tk, [16])
     gen = torch.Generator(device="cuda")
     gen.manual_seed(5)
     out = {"shape": "N=2^16, L=32 data primes (50-60-bit), 64 ciphertexts per batch, CUDA-graph replay",
-           "peaks": {"hbm_gbs": peaks["hbm_gbs"], "bfly64_per_s": peaks["bfly64_s"], "bfly32_per_s": peaks["bfly32_s"]}}
+           "peaks": {"hbm_gbs": peaks["hbm_gbs"], "bfly64_per_s": peaks["bfly64_s"], "bfly32_per_s": peaks["bfly32_s"]},
+           "transforms_per_key_switch": {"one_prime": ks_transforms(32),
+                                         "hybrid": ks_transforms(32, HYB_ALPHA, HYB_SPECIAL)}}
     for op in SWEEP_OPS:
         out[op] = sweep_point(torch, tk, ctxs, [(16, 32, 64)], op, peaks, gen)
     del ctxs
+    torch.cuda.empty_cache()
+    hyb = hybrid_contexts(torch, tk, 16, HYB_SPECIAL, HYB_ALPHA)
+    for op in ("relin", "rotate"):
+        r = sweep_point(torch, tk, hyb, [(16, 32, 64)], op, peaks, gen,
+                        work=lambda o, ln, lv, cnt: sweep_work_hybrid(o, ln, lv, cnt, HYB_SPECIAL, HYB_ALPHA))
+        r["key_switching"] = f"hybrid: {-(-32 // HYB_ALPHA)} digits of {HYB_ALPHA} primes, {HYB_SPECIAL} special primes"
+        out[op + "_hybrid"] = r
+    del hyb
     torch.cuda.empty_cache()
     return out
 
@@ -830,6 +944,76 @@ def run_reference(args, world, rank):
 
 
 # ------------------------------------------------------------------------------------ main --
+PROFILE_CASES = {
+    # name: (log_n, data primes, op, ciphertexts, special primes, alpha)
+    "ntt-n16-l32": (16, 32, "ntt", 8, 1, 1),
+    "intt-n16-l32": (16, 32, "intt", 8, 1, 1),
+    "relin-n16-l32": (16, 32, "relin", 2, 1, 1),
+    "rotate-n16-l32": (16, 32, "rotate", 2, 1, 1),
+    "relin-hyb-n16-l32": (16, 32, "relin", 2, HYB_SPECIAL, HYB_ALPHA),
+    "rotate-hyb-n16-l32": (16, 32, "rotate", 2, HYB_SPECIAL, HYB_ALPHA),
+}
+
+
+def run_profile_case(args):
+    """One small case for a profiler: a primitive job at the sweep's largest shape (PROFILE_CASES), or
+    'cnn-b<B>' (the bench's CNN layout on B requests), run --warmup times, then --steps times inside
+    the NVTX range 'case', eagerly (no graph), so that `ncu --nvtx --nvtx-include case/ -k ...` takes
+    exactly the launches of the case."""
+    import torch
+
+    import paper_2104_03152_gb300 as tk
+    tk.lib(build_if_missing=True)
+    torch.cuda.set_device(0)
+    name = args.profile_case
+    if name.startswith("cnn-b"):
+        B = int(name[5:])
+        tk_, ctx, model, cts, stream, imgs, w = gpu_setup(torch, B, True, True, True, True, True, True)
+        d_in = torch.empty((B, 2, cts[0].level, ctx.N), dtype=torch.int64, device="cuda")
+        for i, c in enumerate(cts):
+            d_in[i].copy_(torch.from_numpy(c.export().view(np.int64)))
+        d_out = torch.empty((B, 2, cts[0].level - 6, ctx.N), dtype=torch.int64, device="cuda")
+        torch.cuda.synchronize()
+        step = lambda: model.forward_device(d_in.data_ptr(), B, d_out.data_ptr())
+        sync = ctx.synchronize
+    else:
+        log_n, L, op, count, special, alpha = PROFILE_CASES[name]
+        from paper_2104_03152_gb300 import inputs
+        bits = SWEEP_BITS[:L] + [60] * special
+        primes = tk.Params(log_n, bits, 2.0 ** 50).primes
+        ctx = tk.Context(tk.Params(log_n, primes=primes, scale=2.0 ** 50, n_special=special, alpha=alpha),
+                         seed=inputs.SEED_KEYS, flags=tk.TCKS_AUTO_RELIN)
+        ctx.gen_galois_keys([1])
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(5)
+        x, y = sweep_buffers(torch, ctx, op, L, count, gen)
+        job = sweep_job(tk, ctx, op, L, count, x, y)
+        step = lambda: tk.batch_run([job])
+        sync = ctx.synchronize
+    for _ in range(args.warmup):
+        step()
+    sync()
+    torch.cuda.nvtx.range_push("case")
+    for _ in range(args.steps):
+        step()
+    sync()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_case": name, "steps": args.steps, "warmup": args.warmup}))
+
+
+def served_vs_plain(serving):
+    """The first trace's served and plain throughput and p99 latency, side by side."""
+    if not serving or not serving.get("traces"):
+        return None
+    t = serving["traces"][0]
+    sv, pl = t["served"], t["plain"]
+    return {"offered_rate": t["offered_rate"], "served_throughput": sv["throughput"], "served_p50_ms": sv["p50_ms"],
+            "served_p99_ms": sv["p99_ms"], "plain_throughput": pl["throughput"], "plain_p50_ms": pl["p50_ms"],
+            "plain_p99_ms": pl["p99_ms"], "unit": "requests/s, ms (arrival -> result on the host)",
+            "measured_seconds": t["seconds"], "requests": t["requests"],
+            "plain_requests": pl.get("trace_requests")}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -839,13 +1023,23 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=2, help="oracle inferences timed for cpu_baseline")
     ap.add_argument("--batch", type=int, default=256, help="requests per step (the batched schedule)")
     ap.add_argument("--serve-batch", type=int, default=64, help="largest batch the serving loop forms per stage")
-    ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the Poisson serving trace (0: skip)")
-    ap.add_argument("--serve-rate", default="2000,300",
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="measured length of the Poisson serving trace (0: skip)")
+    ap.add_argument("--serve-warmup", type=float, default=1.0,
+                    help="seconds of trace served before the measured part (not counted)")
+    ap.add_argument("--serve-rate", default="2000",
                     help="offered requests/s of the serving traces (comma-separated; one trace each)")
+    ap.add_argument("--cnn-clients", type=int, default=8, help="CNN clients of the trace, each with its own keys")
+    ap.add_argument("--vm-clients", type=int, default=2,
+                    help="vector x matrix clients of the trace, each with its own keys")
     ap.add_argument("--sweep", action="store_true", help="print the batched primitive sweep (JSON lines) and exit")
     ap.add_argument("--ops-table", action="store_true",
                     help="print the paper's CKKSVector operation tables measured here (JSON lines) and exit")
     ap.add_argument("--ops-reps", type=int, default=20)
+    ap.add_argument("--tune-cache", type=int, default=0,
+                    help="reuse / record the network autotuner's choice in a JSON file in the temp directory")
+    ap.add_argument("--profile-case", default="",
+                    help="run one small case for a profiler (" + ", ".join(PROFILE_CASES) + ", cnn-b<B>) and exit")
     ap.add_argument("--sweep-batches", default="1,8,64,512", help="ciphertexts per batch in the sweep")
     ap.add_argument("--sweep-log-n", default="13,14,15,16", help="log2 N values of the sweep")
     ap.add_argument("--sweep-L", default="4,8,16,32", help="data-prime counts of the sweep")
@@ -870,14 +1064,17 @@ def main():
                     help="diagonal form of the 4096x256 matrix (rect: 260 rotations, square: 4096)")
     ap.add_argument("--c4-steps", type=int, default=3)
     ap.add_argument("--serve-mix", type=float, default=0.3, help="share of vector x matrix requests in the trace")
-    ap.add_argument("--plain-requests", type=int, default=300,
-                    help="requests at the start of each trace replayed through the plain path")
+    ap.add_argument("--plain-requests", type=int, default=0,
+                    help="requests at the start of each trace replayed through the plain path (0: the whole trace)")
     args = ap.parse_args()
     if args.sweep:
         run_sweep(args)
         return
     if args.ops_table:
         run_ops_table(args)
+        return
+    if args.profile_case:
+        run_profile_case(args)
         return
     world, rank, local = dist_env()
     if args.impl == "reference":
@@ -896,10 +1093,26 @@ def main():
     name, (nl, ms, by, ops) = dom
     hbm_ach = by / (ms / 1e3) / 1e9
     alu_ach = ops / (ms / 1e3) / 1e9
-    # sums of products (the double-hoisted accumulation) against the measured multiply-accumulate rate,
-    # transforms against the measured butterfly rate
+    # sums of products (the double-hoisted accumulation) against the rate of the kernel's own form at each
+    # launch's level (tcks_calibrate_dh_macs), transforms against the measured butterfly rate
     mac_kernel = name == "vecmat_dh_acc"
-    alu_peak = (r["mac_peak"] if mac_kernel else r["bfly_peak"]) / 1e9
+    shapes = None
+    if mac_kernel and r["dh_records"]:
+        t_min, shapes = 0.0, {}
+        for tag, rms, rops in r["dh_records"]:
+            ell, outs, unit = tag & 0xFF, (tag >> 8) & 0xFF, (tag >> 16) & 1
+            t_min += rops / r["dh_peaks"][ell]
+            key = f"level {ell}, {outs} output{'s' if outs > 1 else ''}{', unit diagonals' if unit else ''}"
+            sh = shapes.setdefault(key, {"launches": 0, "ms": 0.0, "ops": 0.0, "ceiling_gmacs": r["dh_peaks"][ell] / 1e9})
+            sh["launches"] += 1
+            sh["ms"] += rms
+            sh["ops"] += rops
+        for sh in shapes.values():
+            sh["achieved_gmacs"] = sh["ops"] / (sh["ms"] / 1e3) / 1e9
+            sh["frac"] = sh["achieved_gmacs"] / sh["ceiling_gmacs"]
+        alu_peak = ops / t_min / 1e9  # the work-weighted ceiling of the family's launches
+    else:
+        alu_peak = (r["mac_peak"] if mac_kernel else r["bfly_peak"]) / 1e9
     traffic = ncu_traffic(name, {"batch": B, "fc_form": args.fc_form, "conv_hoist": args.conv_hoist,
                                  "conv_form": conv_form(args), "merged_rescale": args.merged_rescale,
                                  "double_hoist": args.double_hoist})
@@ -907,8 +1120,13 @@ def main():
            "peak_source": peaks["source"]}
     alu = {"achieved": alu_ach, "peak": alu_peak, "unit": "Gmac/s" if mac_kernel else "Gbfly/s",
            "frac": alu_ach / alu_peak if alu_peak else None,
-           "peak_source": (f"measured: tcks_calibrate_{'macs' if mac_kernel else 'butterflies'}({r['word']}) on this "
-                           "GPU, registers only")}
+           "peak_source": ("measured: tcks_calibrate_dh_macs(level) on this GPU -- the kernel's own form (unreduced "
+                           "key-switch sums, carry-chain diagonal products, one logic op per load) from registers, "
+                           "at each launch's level, weighted by each launch's work" if shapes else
+                           f"measured: tcks_calibrate_{'macs' if mac_kernel else 'butterflies'}({r['word']}) on this "
+                           "GPU, registers only"),
+           "per_shape": shapes,
+           "generic_mac_peak_gmacs": r["mac_peak"] / 1e9 if mac_kernel else None}
     bound = "alu" if alu["frac"] and alu["frac"] > hbm["frac"] else "hbm"
     top = alu if bound == "alu" else hbm
     roofline = {"kernel": name, "bound": bound, "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
@@ -932,7 +1150,9 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "vs_baseline": None, "dtype": f"u{r['word']}", "data": "synthetic",
+        "dtype_note": ("exact residues modulo primes below 2^31 held in 32-bit words" if r["word"] == 32
+                       else "exact residues in 64-bit words"),
         "config": {"workload": WORKLOAD, "batch": B, "galois_keys": r["galois_keys"],
                    "vecmat_schedule": ("ModDown once after each rotation sum (double hoisting)" if args.double_hoist
                                        else "one ModDown per rotation"),
@@ -940,6 +1160,7 @@ def main():
                                if args.fc_form == "rect" else "square diagonals: FC1 255 rotations, FC2 63"),
                    "conv_form": CONV_LABEL[conv_form(args)],
                    "l2": "inputs larger than L2 (Galois keys ~0.75 GB + key-switch scratch streamed per step)",
+                   "launch_shape": r["tune"],
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "latency_ms": {"p50": per[len(per) // 2], "p99": per[min(len(per) - 1, int(0.99 * len(per)))],
                        "mode": f"batched step of {B} requests (each request completes with its batch)"},
@@ -962,6 +1183,7 @@ def main():
         "e2e_limbs": {"value": world * B * r["e2e_steps"] / r["e2e_s"], "unit": "inferences/s",
                       "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],
                       "api": "tcks_cnn_forward_host: 64-bit limbs in and out"},
+        "served_vs_plain": served_vs_plain(r["serving"]),
         "serving": r["serving"],
         "primitives": r["primitives"],
         "compare": r["single"],

@@ -407,6 +407,15 @@ tcks_status tcks_conv2d_im2col_pt(const tcks_ct* a, const tcks_pt* kernel, uint3
  * word size) a stored choice is reused and a new one recorded. Results are unchanged (bit-exact);
  * only the launch shape moves. *chosen_threads may be NULL. */
 tcks_status tcks_autotune(tcks_ctx* ctx, const char* cache_path, uint32_t* chosen_threads);
+/* Autotuner of the batched encrypted network (declared here, takes the model of tcks_cnn_create): times
+ * a whole batched forward pass of `batch` requests for every pair of limb-kernel CTA size (N/64, N/32,
+ * N/16 threads per slice) and double-hoisted accumulation shape (1 or 2 requests per thread, 32-bit
+ * words), keeps the fastest on the model's context and, with a cache_path, records it under the GPU
+ * name, log N, word size and batch (a later call reads it back). Results are bit-identical for every
+ * shape. chosen_threads / chosen_rpt may be NULL. Synchronises. */
+typedef struct tcks_cnn tcks_cnn;
+tcks_status tcks_cnn_autotune(const tcks_cnn* m, uint32_t batch, const char* cache_path, uint32_t* chosen_threads,
+                              uint32_t* chosen_rpt);
 
 /* --------------------------------------------------- batched launches (descriptor table) ---- */
 /* A batch of independent jobs over raw device buffers, possibly of several contexts (different N)
@@ -471,6 +480,12 @@ tcks_status tcks_calibrate_butterflies(uint32_t word_bits, double* per_second);
  * one reduction per eight products; for 32-bit words in plain 64-bit sums of four): product-accumulates
  * per second, the ceiling of the kernels whose work is sums of products rather than transforms. */
 tcks_status tcks_calibrate_macs(uint32_t word_bits, double* per_second);
+/* The product-accumulate rate of the double-hoisted vector x matrix accumulation in its own form at
+ * level ell (1..8; 32-bit words, two requests per thread): the unreduced key-switch sums over ell
+ * digits, their carry-chain products with the diagonal and the c0 product, from registers, each of
+ * the kernel's loads replaced by one logic op. The measured ceiling of that kernel's roofline, in the
+ * unit it counts (one modular product-accumulate). Uses the current device; a measurement aid. */
+tcks_status tcks_calibrate_dh_macs(uint32_t ell, double* per_second);
 /* Number of kernel launches the library has issued since it was loaded. */
 uint64_t tcks_launch_count(void);
 /* Kernel profiler: while on, every launch is bracketed by CUDA events on its stream and carries its
@@ -485,6 +500,11 @@ tcks_status tcks_profile_read(uint32_t idx, const char** name, uint64_t* launche
  * transforms plus its modular multiplies and multiply-accumulates, one unit each (the unit of
  * tcks_calibrate_butterflies). */
 tcks_status tcks_profile_read_ops(uint32_t idx, double* algo_ops);
+/* The profiled launches of family idx one by one, in launch order: up to `capacity` records of
+ * (shape tag, device ms, algorithmic ops); *count receives the number of launches. The double-hoisted
+ * accumulation tags a launch with its level | outputs << 8 | (unit diagonals) << 16. */
+tcks_status tcks_profile_records(uint32_t idx, uint32_t capacity, uint32_t* tags, double* ms, double* algo_ops,
+                                 uint32_t* count);
 
 /* ---------------------------------------- ciphertext arrays: CKKSTensor storage (§2.3) ---- */
 /* TenSEAL's CKKSTensor holds an N-dimensional tensor as a tensor of ciphertexts, with optionally one

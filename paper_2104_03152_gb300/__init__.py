@@ -142,6 +142,7 @@ _SIGS = {
     "tcks_conv2d_im2col": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
     "tcks_conv2d_im2col_pt": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
     "tcks_autotune": (ctypes.c_int32, [_vp, ctypes.c_char_p, _u32p]),
+    "tcks_cnn_autotune": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_char_p, _u32p, _u32p]),
     "tcks_launch_count": (ctypes.c_uint64, []),
     "tcks_profile_start": (ctypes.c_int32, []),
     "tcks_profile_stop": (ctypes.c_int32, []),
@@ -149,6 +150,8 @@ _SIGS = {
     "tcks_profile_read_ops": (ctypes.c_int32, [ctypes.c_uint32, _dblp]),
     "tcks_calibrate_butterflies": (ctypes.c_int32, [ctypes.c_uint32, _dblp]),
     "tcks_calibrate_macs": (ctypes.c_int32, [ctypes.c_uint32, _dblp]),
+    "tcks_calibrate_dh_macs": (ctypes.c_int32, [ctypes.c_uint32, _dblp]),
+    "tcks_profile_records": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_uint32, _u32p, _dblp, _dblp, _u32p]),
     "tcks_profile_read": (ctypes.c_int32, [ctypes.c_uint32, ctypes.POINTER(ctypes.c_char_p),
                                             ctypes.POINTER(ctypes.c_uint64), _dblp, _dblp]),
     "tcks_server_create": (ctypes.c_int32, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
@@ -255,6 +258,24 @@ def profile_read(with_ops: bool = False) -> dict:
     return out
 
 
+def profile_records(family: str) -> list:
+    """[(shape tag, device ms, algorithmic ops)] of the profiled launches of one kernel family, in order."""
+    L = lib()
+    for i in range(L.tcks_profile_count()):
+        name = ctypes.c_char_p()
+        check(L.tcks_profile_read(i, ctypes.byref(name), None, None, None))
+        if name.value.decode() != family:
+            continue
+        n = ctypes.c_uint32()
+        check(L.tcks_profile_records(i, 0, None, None, None, ctypes.byref(n)))
+        tags = np.zeros(n.value, dtype=np.uint32)
+        ms = np.zeros(n.value, dtype=np.float64)
+        ops = np.zeros(n.value, dtype=np.float64)
+        check(L.tcks_profile_records(i, n.value, _p(tags), _p(ms), _p(ops), ctypes.byref(n)))
+        return [(int(t), float(m), float(o)) for t, m, o in zip(tags, ms, ops)]
+    return []
+
+
 def calibrate_butterflies(word_bits: int = 64) -> float:
     """Modular butterflies per second of the integer pipe on the current device (registers only)."""
     v = ctypes.c_double()
@@ -266,6 +287,13 @@ def calibrate_macs(word_bits: int) -> float:
     """Measured modular multiply-accumulates per second (32- or 64-bit words), registers only."""
     v = ctypes.c_double()
     check(lib().tcks_calibrate_macs(word_bits, ctypes.byref(v)))
+    return v.value
+
+
+def calibrate_dh_macs(ell: int) -> float:
+    """Product-accumulates per second of the double-hoisted accumulation's own form at level ell."""
+    v = ctypes.c_double()
+    check(lib().tcks_calibrate_dh_macs(ell, ctypes.byref(v)))
     return v.value
 
 
@@ -810,6 +838,14 @@ class CNN:
         assert host_in.dtype == np.uint64 and host_out.dtype == np.uint64
         check(lib().tcks_cnn_forward_host(self.h, _p(host_in), host_in.shape[0], _p(host_out)))
         return host_out
+
+    def autotune(self, batch: int, cache_path: str | None = None) -> tuple[int, int]:
+        """Times the batched forward pass at `batch` requests over the launch shapes and keeps the fastest
+        (CTA size of the limb kernels, requests per thread of the accumulation); returns that pair."""
+        t, r = ctypes.c_uint32(), ctypes.c_uint32()
+        check(lib().tcks_cnn_autotune(self.h, batch, cache_path.encode() if cache_path else None, ctypes.byref(t),
+                                      ctypes.byref(r)))
+        return t.value, r.value
 
     def wire_sizes(self) -> tuple[int, int, int]:
         """Bytes of one serialized input (both components), one seeded input, one serialized output."""

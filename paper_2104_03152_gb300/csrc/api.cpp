@@ -26,6 +26,7 @@ static void ctx_destroy(tcks_ctx* c);
 
 #define TCKS_API_BEGIN \
   try {                 \
+    tcks::NvtxRange tcks_nvtx_range_(__func__); \
     tcks::drop_stale_cuda_error();
 #define TCKS_API_END                                                   \
   }                                                                    \
@@ -402,7 +403,7 @@ tcks_status tcks_params_create(uint32_t log_n, const uint32_t* bit_sizes, uint32
   if (!out || !bit_sizes) fail(TCKS_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   if (log_n < 3 || log_n > 16) fail(TCKS_ERR_BAD_PARAMS, "log_n must be in [3, 16]");
-  if (n_primes < 2 || n_primes > CRT_MAXW - 1) fail(TCKS_ERR_BAD_PARAMS, "need 2..33 primes (data primes + P)");
+  if (n_primes < 2 || n_primes > 64) fail(TCKS_ERR_BAD_PARAMS, "need 2..64 primes (data primes + special primes)");
   if (!(scale > 0) || !std::isfinite(scale)) fail(TCKS_ERR_BAD_PARAMS, "scale must be positive");
   std::vector<u64> chain;
   if (!find_chain(log_n, bit_sizes, n_primes, chain))
@@ -418,7 +419,7 @@ tcks_status tcks_params_create_primes(uint32_t log_n, const uint64_t* primes, ui
   if (!out || !primes) fail(TCKS_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
   if (log_n < 3 || log_n > 16) fail(TCKS_ERR_BAD_PARAMS, "log_n must be in [3, 16]");
-  if (n_primes < 2 || n_primes > CRT_MAXW - 1) fail(TCKS_ERR_BAD_PARAMS, "need 2..33 primes (data primes + P)");
+  if (n_primes < 2 || n_primes > 64) fail(TCKS_ERR_BAD_PARAMS, "need 2..64 primes (data primes + special primes)");
   if (!(scale > 0) || !std::isfinite(scale)) fail(TCKS_ERR_BAD_PARAMS, "scale must be positive");
   std::vector<u64> chain(primes, primes + n_primes);
   std::vector<u32> bits;
@@ -504,6 +505,8 @@ tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32
   c->alpha = params->alpha;
   c->hyb = c->K > 1 || c->alpha > 1;
   c->L = (u32)params->chain.size() - c->K;
+  if (c->L < 1 || c->L > CRT_MAXW - 2)
+    fail(TCKS_ERR_BAD_PARAMS, "a context takes 1.." + std::to_string(CRT_MAXW - 2) + " data primes");
   c->flags = flags;
   c->seed = seed;
   check_cuda(cudaGetDevice(&c->device), "cudaGetDevice");

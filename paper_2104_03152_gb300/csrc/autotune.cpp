@@ -1,4 +1,5 @@
-// Autotuner for the limb kernels' CTA size.
+// Autotuners: the limb kernels' CTA size (tcks_autotune), and the launch shape of the batched
+// encrypted network (tcks_cnn_autotune).
 //
 // Every limb kernel (transforms with their fused prologues and epilogues) strides its work over
 // the CTA's threads, so any multiple of 32 up to the slice size is correct; the best size depends
@@ -61,6 +62,96 @@ void write_cache(const std::string& path, const std::map<std::string, u32>& c) {
 }
 
 }  // namespace
+
+namespace tcks {
+void cnn_forward_dev(const tcks_cnn* m, const u64* x, u64 x_stride, u32 count, u64* out);
+tcks_ctx* cnn_context(const tcks_cnn* m);
+u32 cnn_input_level(const tcks_cnn* m);
+}  // namespace tcks
+
+// The batched network's launch shape: the limb kernels' CTA size (N/64, N/32, N/16 threads per slice)
+// times the double-hoisted accumulation's requests per thread (1 or 2, 32-bit words), each timed on a
+// whole batched forward pass of `batch` requests (the median of three after one warm-up); the fastest
+// pair is kept on the context and recorded under "<GPU>|cnn|<log N>|<word bits>|<batch>" (threads *
+// 10 + requests per thread). Results are bit-identical for every shape.
+extern "C" tcks_status tcks_cnn_autotune(const tcks_cnn* m, uint32_t batch, const char* cache_path,
+                                         uint32_t* chosen_threads, uint32_t* chosen_rpt) {
+  try {
+    tcks::NvtxRange nvtx(__func__);
+    drop_stale_cuda_error();
+    if (!m || !batch) fail(TCKS_ERR_INVALID_ARG, "null model or empty batch");
+    tcks_ctx* c = cnn_context(m);
+    cudaDeviceProp prop;
+    check_cuda(cudaGetDeviceProperties(&prop, c->device), "device properties");
+    const u32 log_n = c->params.log_n, log_c = log_n > 14 ? log_n - 14 : 0, ns = 1u << (log_n - log_c);
+    const std::string key = std::string(prop.name) + "|cnn|" + std::to_string(log_n) + "|" +
+                            (c->T.narrow ? "32" : "64") + "|" + std::to_string(batch);
+    std::map<std::string, u32> cache;
+    if (cache_path && *cache_path) cache = read_cache(cache_path);
+    u32 cap = 1024;
+    for (u32 t : {limb_threads_cap_core(c->T.narrow, log_c), limb_threads_cap_sample(c->T.narrow, log_c),
+                  limb_threads_cap_fft(c->T.narrow, log_c)})
+      cap = std::min(cap, t);
+    cap &= ~31u;
+    u32 best_t = 0, best_r = 0;
+    auto it = cache.find(key);
+    if (it != cache.end() && it->second / 10 >= 32 && it->second / 10 <= cap && (it->second % 10 == 1 || it->second % 10 == 2)) {
+      best_t = it->second / 10;
+      best_r = it->second % 10;
+    } else {
+      std::vector<u32> threads;
+      for (u32 div : {64u, 32u, 16u}) {
+        u32 t = std::max<u32>(32, std::min(cap, ns / div));
+        if (std::find(threads.begin(), threads.end(), t) == threads.end()) threads.push_back(t);
+      }
+      const std::vector<u32> rpts = c->T.narrow ? std::vector<u32>{2, 1} : std::vector<u32>{0};
+      const u32 L = cnn_input_level(m);
+      const u64 win = ct_words(c, L), wout = ct_words(c, L - 6);
+      DevBuf x(c, (size_t)batch * win), y(c, (size_t)batch * wout);
+      check_cuda(cudaMemsetAsync(x.p, 0, (size_t)batch * win * 8, c->stream), "tune input");
+      cudaEvent_t ev[4];
+      for (cudaEvent_t& e : ev) check_cuda(cudaEventCreate(&e), "event");
+      const u32 saved_t = c->T.limb_threads, saved_r = c->T.dh_rpt;
+      float best_ms = 1e30f;
+      for (u32 t : threads)
+        for (u32 r : rpts) {
+          c->T.limb_threads = t;
+          c->T.dh_rpt = r;
+          cnn_forward_dev(m, x.p, win, batch, y.p);  // warm-up
+          float ms[3];
+          for (int k = 0; k < 3; ++k) {
+            check_cuda(cudaEventRecord(ev[0], c->stream), "event");
+            cnn_forward_dev(m, x.p, win, batch, y.p);
+            check_cuda(cudaEventRecord(ev[1], c->stream), "event");
+            check_cuda(cudaEventSynchronize(ev[1]), "tune");
+            cudaEventElapsedTime(&ms[k], ev[0], ev[1]);
+          }
+          std::sort(ms, ms + 3);
+          if (ms[1] < best_ms) {
+            best_ms = ms[1];
+            best_t = t;
+            best_r = r;
+          }
+        }
+      c->T.limb_threads = saved_t;
+      c->T.dh_rpt = saved_r;
+      for (cudaEvent_t& e : ev) cudaEventDestroy(e);
+      check_launch("cnn autotune");
+      if (cache_path && *cache_path) {
+        cache[key] = best_t * 10 + best_r;
+        write_cache(cache_path, cache);
+      }
+    }
+    c->T.limb_threads = best_t;
+    c->T.dh_rpt = best_r;
+    if (chosen_threads) *chosen_threads = best_t;
+    if (chosen_rpt) *chosen_rpt = best_r;
+  } catch (const tcks::Error& e) {
+    return abi_record(e.code, e.msg);
+  }
+  abi_clear();
+  return TCKS_OK;
+}
 
 extern "C" tcks_status tcks_autotune(tcks_ctx* c, const char* cache_path, uint32_t* chosen_threads) {
   try {

@@ -1,7 +1,8 @@
 // Batched launches over a descriptor table of independent jobs (several contexts, N and levels):
 // the device-side replacement for the CPU thread pool that runs TenSEAL's per-ciphertext work.
-//   * NTT / INTT jobs of one context: one launch of k_ntt_desc over all of them (mixed levels and
-//     buffers), split only when the table holds more than kNttDescMax batches;
+//   * NTT / INTT jobs: with several contexts of N in [2^13, 2^16] and one word type, one columns launch
+//     and one slices launch per direction for all of them (mixed N, levels and buffers); otherwise per
+//     context, one launch of k_ntt_desc over its jobs, split only past kNttDescMax batches;
 //   * relinearize / rotate jobs: the batched key-switch sequence (ModUp, inner product, ModDown)
 //     per job, in sub-batches whose scratch stays under a fixed bound;
 //   * each context's work is queued on its own stream, forked from and joined back into the first
@@ -149,6 +150,33 @@ void run_jobs(const tcks_batch_job* jobs, u32 n_jobs) {
     events.push_back(e);
     return e;
   };
+  // The NTT / INTT jobs of every context (N >= 2^13, one word type) as one columns launch and one
+  // slices launch per direction on the first job's stream; otherwise per context, below.
+  bool multi_done = false;
+  if (order.size() > 1) {
+    std::vector<MultiNttBatch> fwd_b, inv_b;
+    for (u32 i = 0; i < n_jobs; ++i) {
+      const tcks_batch_job& j = jobs[i];
+      if (!j.count || (j.op != TCKS_JOB_NTT && j.op != TCKS_JOB_INTT)) continue;
+      (j.op == TCKS_JOB_NTT ? fwd_b : inv_b).push_back(MultiNttBatch{&j.ctx->T, j.d_in, j.d_out, j.count, j.level});
+    }
+    auto fits = [](const std::vector<MultiNttBatch>& b) {
+      if (b.empty()) return true;
+      if (b.size() > kMultiDescMax) return false;
+      std::vector<const void*> ctxs;
+      for (const MultiNttBatch& x : b) {
+        if (x.T->log_n < 13 || x.T->log_n > 16 || x.T->narrow != b[0].T->narrow) return false;
+        if (std::find(ctxs.begin(), ctxs.end(), (const void*)x.T->mods) == ctxs.end()) ctxs.push_back(x.T->mods);
+      }
+      return ctxs.size() <= kMultiCtxMax;
+    };
+    if (fits(fwd_b) && fits(inv_b) && (!fwd_b.empty() || !inv_b.empty())) {
+      if (!fwd_b.empty()) launch_ntt_multi(false, fwd_b.data(), (u32)fwd_b.size(), origin);
+      if (!inv_b.empty()) launch_ntt_multi(true, inv_b.data(), (u32)inv_b.size(), origin);
+      check_launch("batched NTT over contexts");
+      multi_done = true;
+    }
+  }
   cudaEvent_t fork = new_event();
   check_cuda(cudaEventRecord(fork, origin), "fork");
   for (tcks_ctx* c : order) {
@@ -159,8 +187,8 @@ void run_jobs(const tcks_batch_job* jobs, u32 n_jobs) {
       if (j->op == TCKS_JOB_NTT) fwd.push_back(j);
       if (j->op == TCKS_JOB_INTT) inv.push_back(j);
     }
-    if (!fwd.empty()) run_ctx_ntt(c, fwd, false);
-    if (!inv.empty()) run_ctx_ntt(c, inv, true);
+    if (!multi_done && !fwd.empty()) run_ctx_ntt(c, fwd, false);
+    if (!multi_done && !inv.empty()) run_ctx_ntt(c, inv, true);
     for (const tcks_batch_job* j : js) {
       if (!j->count) continue;
       if (j->op == TCKS_JOB_RELIN) op_relin_batch(c, j->d_in, j->count, j->level, j->d_out);
@@ -193,6 +221,7 @@ struct tcks_batch_graph {
 
 #define BATCH_BEGIN \
   try {                 \
+    tcks::NvtxRange tcks_nvtx_range_(__func__); \
     tcks::drop_stale_cuda_error();
 #define BATCH_END                                                    \
   }                                                                  \

@@ -216,7 +216,9 @@ void cnn_stage(const tcks_cnn* m, u32 stage, const u64* x, u32 count, u64* out) 
 
 // Forward pass of `count` requests at once: inputs in + r * in_stride ([2][L][N] each), outputs
 // out [count][2][L-6][N].
-static void cnn_forward_dev(const tcks_cnn* m, const u64* in, u64 in_stride, u32 count, u64* out) {
+u32 cnn_input_level(const tcks_cnn* m) { return m->L; }
+
+void cnn_forward_dev(const tcks_cnn* m, const u64* in, u64 in_stride, u32 count, u64* out) {
   tcks_ctx* c = m->ctx;
   const u64 w_in = ct_words(c, m->L);
   DevBuf xin;
@@ -245,6 +247,7 @@ static void cnn_forward_dev(const tcks_cnn* m, const u64* in, u64 in_stride, u32
 
 #define CNN_BEGIN \
   try {                 \
+    tcks::NvtxRange tcks_nvtx_range_(__func__); \
     tcks::drop_stale_cuda_error();
 #define CNN_END                                                       \
   }                                                                   \

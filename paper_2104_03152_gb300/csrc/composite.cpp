@@ -39,7 +39,7 @@ static void op_vecmat_dh(tcks_ctx* c, u64* ct, u64 cw, u32 count, u32 ell, const
   DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
   launch_modup(c->T, ct + (size_t)ell * n, cw, count, ell, coef.p, digits.p, c->stream);
   // chunks of rotations: enough CTAs for a few waves of 256-thread CTAs on every SM
-  const u64 base = vecmat_dh_base_ctas(c->params.log_n, ell, count, c->T.narrow), want = 152ull * 8 * 4;
+  const u64 base = vecmat_dh_base_ctas(c->params.log_n, ell, count, c->T.narrow, 1, c->T.dh_rpt), want = 152ull * 8 * 4;
   u32 chunks = (u32)std::min<u64>(R, std::max<u64>(1, (want + base - 1) / base));
   const u32 chunk = (R + chunks - 1) / chunks;
   chunks = (R + chunk - 1) / chunk;
@@ -102,7 +102,7 @@ void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const st
   const u32 R = (u32)ks.size();
   DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
   launch_modup(c->T, x + (size_t)ell * n, cw, count, ell, coef.p, digits.p, c->stream);
-  const u64 base = vecmat_dh_base_ctas(c->params.log_n, ell, count, c->T.narrow), want = 152ull * 8 * 4;
+  const u64 base = vecmat_dh_base_ctas(c->params.log_n, ell, count, c->T.narrow, 1, c->T.dh_rpt), want = 152ull * 8 * 4;
   u32 chunks = (u32)std::min<u64>(R, std::max<u64>(1, (want + base - 1) / base));
   const u32 chunk = (R + chunks - 1) / chunks;
   chunks = (R + chunk - 1) / chunk;
@@ -145,7 +145,7 @@ void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, cons
   const u32 R = (u32)ks.size();
   DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
   launch_modup(c->T, x + (size_t)ell * n, cw, count, ell, coef.p, digits.p, c->stream);
-  const u64 base = vecmat_dh_base_ctas(c->params.log_n, ell, count, c->T.narrow, outs), want = 152ull * 8 * 4;
+  const u64 base = vecmat_dh_base_ctas(c->params.log_n, ell, count, c->T.narrow, outs, c->T.dh_rpt), want = 152ull * 8 * 4;
   u32 chunks = (u32)std::min<u64>(R, std::max<u64>(1, (want + base - 1) / base));
   const u32 chunk = (R + chunks - 1) / chunks;
   chunks = (R + chunk - 1) / chunk;

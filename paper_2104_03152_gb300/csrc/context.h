@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/tcks.h"
 #include "kernels.h"
 #include "params.h"
@@ -32,6 +34,15 @@ struct KeyTable {
   KsKey* d = nullptr;
   u32 n = 0;
   u32 min_K = 0;  // smallest key level in the table
+};
+
+// A profiler range around one ABI call (or one stage of a served request group), visible in Nsight
+// Systems / Compute timelines; the header-only NVTX calls cost a few nanoseconds when no tool listens.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // Status with message, raised by internal helpers and turned into a return code at the ABI.

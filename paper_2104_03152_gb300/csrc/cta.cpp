@@ -15,6 +15,7 @@ namespace {
 
 #define CTA_BEGIN \
   try {           \
+    tcks::NvtxRange tcks_nvtx_range_(__func__); \
     tcks::drop_stale_cuda_error();
 #define CTA_END                                                                  \
   }                                                                              \

@@ -232,6 +232,180 @@ static void launch_ntt_split(const DevTables& T, bool inverse, const Jobs& jobs,
   }
 }
 
+// ------------------------------------------- NTT over several contexts (mixed N and level) ----
+// Every N = 2^(13 + k), k = 0..3, is the k column stages (columns of 2^k elements 2^13 apart) plus the
+// other 13 stages on 2^k slices of 8192 elements, so batches of different contexts share one columns
+// launch (batches with k > 0) and one slices launch: each CTA / item finds its batch in the table
+// (binary search on the first job, then a forward walk in the grid-stride loop) and takes that
+// batch's context tables. The butterflies and their order are those of the single-context
+// transforms, so the results are identical.
+__device__ __forceinline__ u32 multi_desc_slice(const MultiNttTable& tab, u64 job) {
+  u32 lo = 0, hi = tab.n;
+  while (hi - lo > 1) {
+    const u32 mid = (lo + hi) >> 1;
+    if (tab.d[mid].first <= job) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+template <bool INVERSE, typename W>
+__global__ void k_ntt_slices_multi(const __grid_constant__ MultiNttTable tab) {
+  TCKS_SMEM(W);
+  const MultiNttDesc& d = tab.d[multi_desc_slice(tab, blockIdx.x)];
+  const DevTables& T = tab.T[d.ctx];
+  const u32 log_n = T.log_n, log_k = log_n - kSplitLogNs;
+  const u64 local = blockIdx.x - d.first;
+  const u64 limb = local >> log_k;
+  const u32 rank = (u32)(local & ((1u << log_k) - 1)), mod = (u32)(limb % d.level);
+  const ModConst m = T.mods[mod];
+  const W q = (W)m.q;
+  const u32 ns = 1u << kSplitLogNs;
+  const u64 off = (limb << log_n) + ((u64)rank << kSplitLogNs);
+  const u64* from = (INVERSE || log_k == 0 ? d.src : d.dst) + off;
+  u64* to = d.dst + off;
+  for (u32 k = 2 * threadIdx.x; k < ns; k += 2 * blockDim.x) {
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(from + k);
+    s[sw(k)] = (W)v.x;
+    s[sw(k + 1)] = (W)v.y;
+  }
+  __syncthreads();
+  if (INVERSE) {
+    ntt_inv_local_rounds<W>(s, log_n, kSplitLogNs, rank, Ar<W>::tw(T, mod, 2), Ar<W>::tw(T, mod, 3), q);
+    for (u32 k = 2 * threadIdx.x; k < ns; k += 2 * blockDim.x) {  // without columns the N^-1 is taken here
+      const u64 a = log_k ? (u64)s[sw(k)] : Ar<W>::inv_out(s[sw(k)], m);
+      const u64 b = log_k ? (u64)s[sw(k + 1)] : Ar<W>::inv_out(s[sw(k + 1)], m);
+      *reinterpret_cast<ulonglong2*>(to + k) = make_ulonglong2(a, b);
+    }
+  } else {
+    ntt_fwd_local_rounds<W>(s, log_n, kSplitLogNs, rank, Ar<W>::tw(T, mod, 0), Ar<W>::tw(T, mod, 1), q);
+    for (u32 k = 2 * threadIdx.x; k < ns; k += 2 * blockDim.x)
+      *reinterpret_cast<ulonglong2*>(to + k) = make_ulonglong2(Ar<W>::fwd_out(s[sw(k)], m), Ar<W>::fwd_out(s[sw(k + 1)], m));
+  }
+}
+
+template <bool INVERSE, typename W, int K>
+__device__ __forceinline__ void multi_column(const DevTables& T, const MultiNttDesc& d, u64 local) {
+  const u32 log_n = T.log_n;
+  const u64 job = local >> kSplitLogNs;
+  const u32 j = (u32)(local & ((1u << kSplitLogNs) - 1)), mod = (u32)(job % d.level);
+  const ModConst m = T.mods[mod];
+  const W q = (W)m.q;
+  const u64* in = d.src + (job << log_n);
+  u64* out = d.dst + (job << log_n);
+  W x[1 << K];
+  const u64* from = INVERSE ? out : in;
+#pragma unroll
+  for (int c = 0; c < (1 << K); ++c) x[c] = (W)from[j + ((u64)c << kSplitLogNs)];
+  if (INVERSE) {
+    inv_group<W, K>(x, log_n, kSplitLogNs, 0, Ar<W>::tw(T, mod, 2), Ar<W>::tw(T, mod, 3), q);
+#pragma unroll
+    for (int c = 0; c < (1 << K); ++c) out[j + ((u64)c << kSplitLogNs)] = Ar<W>::inv_out(x[c], m);
+  } else {
+    fwd_group<W, K>(x, 0, 0, Ar<W>::tw(T, mod, 0), Ar<W>::tw(T, mod, 1), q);
+#pragma unroll
+    for (int c = 0; c < (1 << K); ++c) out[j + ((u64)c << kSplitLogNs)] = (u64)x[c];
+  }
+}
+
+template <bool INVERSE, typename W>
+__global__ void k_ntt_columns_multi(const __grid_constant__ MultiNttTable tab) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  u64 it = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= tab.col_items) return;
+  u32 di = 0;
+  {  // the batch of the first item, then walk forward (items only grow)
+    u32 lo = 0, hi = tab.n;
+    while (hi - lo > 1) {
+      const u32 mid = (lo + hi) >> 1;
+      if (tab.d[mid].col_first <= it) lo = mid; else hi = mid;
+    }
+    di = lo;
+  }
+  for (; it < tab.col_items; it += stride) {
+    while (di + 1 < tab.n && tab.d[di + 1].col_first <= it) ++di;
+    const MultiNttDesc& d = tab.d[di];
+    const DevTables& T = tab.T[d.ctx];
+    const u64 local = it - d.col_first;
+    switch (T.log_n - kSplitLogNs) {
+      case 1: multi_column<INVERSE, W, 1>(T, d, local); break;
+      case 2: multi_column<INVERSE, W, 2>(T, d, local); break;
+      case 3: multi_column<INVERSE, W, 3>(T, d, local); break;
+      default: break;  // N = 2^13 batches have no columns (and no items)
+    }
+  }
+}
+
+u32 launch_ntt_multi(bool inverse, const MultiNttBatch* batches, u32 n, cudaStream_t st) {
+  if (!n || n > kMultiDescMax) return 0;
+  MultiNttTable tab{};
+  const bool narrow = batches[0].T->narrow != 0;
+  double bytes = 0, slice_ops = 0, col_ops = 0;
+  for (u32 i = 0; i < n; ++i) {
+    const MultiNttBatch& b = batches[i];
+    if (b.T->log_n < kSplitLogNs || b.T->log_n > kSplitLogNs + 3 || (b.T->narrow != 0) != narrow) return 0;
+    u32 c = 0;
+    while (c < tab.n_ctx && tab.T[c].mods != b.T->mods) ++c;  // contexts told apart by their tables
+    if (c == tab.n_ctx) {
+      if (tab.n_ctx == kMultiCtxMax) return 0;
+      tab.T[tab.n_ctx++] = *b.T;
+    }
+    const u64 limbs = (u64)b.polys * b.level;
+    const u32 log_k = b.T->log_n - kSplitLogNs;
+    MultiNttDesc& d = tab.d[tab.n];
+    d.src = b.src;
+    d.dst = b.dst;
+    d.level = b.level;
+    d.limbs = (u32)limbs;
+    d.ctx = c;
+    d.first = tab.slice_jobs;
+    d.col_first = tab.col_items;
+    ++tab.n;
+    tab.slice_jobs += limbs << log_k;
+    if (log_k) tab.col_items += limbs << kSplitLogNs;
+    const double nn = (double)(1u << b.T->log_n);
+    bytes += 16.0 * nn * limbs;
+    slice_ops += limbs * 0.5 * nn * kSplitLogNs;
+    col_ops += limbs * 0.5 * nn * log_k;
+  }
+  if (!tab.slice_jobs || tab.slice_jobs > 0x7fffffffull) return 0;
+  const KernelId id = inverse ? K_NTT_INV : K_NTT_FWD;
+  const size_t smem = (narrow ? 4 : 8) << kSplitLogNs;
+  auto slices = [&]() {
+    Launch L(id, st, bytes, slice_ops);
+    const void* k = narrow ? (inverse ? (const void*)k_ntt_slices_multi<true, u32> : (const void*)k_ntt_slices_multi<false, u32>)
+                           : (inverse ? (const void*)k_ntt_slices_multi<true, u64> : (const void*)k_ntt_slices_multi<false, u64>);
+    ensure_smem(k, smem);
+    const u32 grid = (u32)tab.slice_jobs;
+    if (narrow) {
+      if (inverse) k_ntt_slices_multi<true, u32><<<grid, 256, smem, st>>>(tab);
+      else k_ntt_slices_multi<false, u32><<<grid, 256, smem, st>>>(tab);
+    } else {
+      if (inverse) k_ntt_slices_multi<true, u64><<<grid, 256, smem, st>>>(tab);
+      else k_ntt_slices_multi<false, u64><<<grid, 256, smem, st>>>(tab);
+    }
+  };
+  auto columns = [&]() {
+    if (!tab.col_items) return;
+    Launch L(id, st, 0.0, col_ops);
+    const u32 blocks = (u32)std::min<u64>((tab.col_items + 255) / 256, 152ull * 16);
+    if (narrow) {
+      if (inverse) k_ntt_columns_multi<true, u32><<<blocks, 256, 0, st>>>(tab);
+      else k_ntt_columns_multi<false, u32><<<blocks, 256, 0, st>>>(tab);
+    } else {
+      if (inverse) k_ntt_columns_multi<true, u64><<<blocks, 256, 0, st>>>(tab);
+      else k_ntt_columns_multi<false, u64><<<blocks, 256, 0, st>>>(tab);
+    }
+  };
+  if (inverse) {
+    slices();
+    columns();
+  } else {
+    columns();
+    slices();
+  }
+  return tab.col_items ? 2 : 1;
+}
+
 // ------------------------------------------------------- NTT over a descriptor table ----
 // One launch over several polynomial batches of the same N and chain but their own levels and
 // buffers: CTA job j belongs to the last descriptor whose first job is <= j, and is limb

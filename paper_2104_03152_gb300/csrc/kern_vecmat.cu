@@ -8,10 +8,12 @@
 // k_vecmat_dh_acc is element-wise (no transform inside the rotation loop): one thread owns a few
 // elements of one (request, slot i) and walks a chunk of rotations, reading the digits through the
 // Galois permutation and each key limb, diagonal and c0 limb once; the grid orders requests fastest
-// so that the CTAs sharing a key limb run together. k_vecmat_dh_fold sums the chunk partials;
+// so that the CTAs sharing a key limb run together, and the slots slowest so that one slot's digits
+// stay in the L2 while its element blocks run. k_vecmat_dh_fold sums the chunk partials;
 // k_vecmat_dh_moddown finishes (one limb job per request, component and prime).
 #include <cuda_runtime.h>
 
+#include "../../include/tcks.h"
 #include "context.h"
 #include "kernels.h"
 #include "limb_launch.cuh"
@@ -129,9 +131,14 @@ __global__ void __launch_bounds__(kDhThreads, KO > 1 ? 3 : 1) k_vecmat_dh_acc(De
   const u64 n = 1ull << log_n;
   const u32 slots = ell + 1;
   const u32 groups = (p.B + RPT - 1) / RPT;
+  const u32 eblocks = (u32)((n + kDhThreads * EPT - 1) / (kDhThreads * EPT));
+  // Requests fastest (the CTAs sharing a key block run together), then element blocks, then the slot:
+  // while the CTAs of slot i run, the working set is that slot's digits of every request and its key
+  // limbs, which fits the L2, so each digit limb is read from DRAM once although every element block
+  // reads it through a different permutation at every rotation.
   const u32 rg = blockIdx.x % groups;
   const u32 rest = blockIdx.x / groups;
-  const u32 i = rest % slots, eb = rest / slots;
+  const u32 eb = rest % eblocks, i = rest / eblocks;
   const u32 chunk = blockIdx.y;
   const u32 mod = i < ell ? i : T.L;
   const ModConst m = T.mods[mod];
@@ -234,6 +241,61 @@ __global__ void __launch_bounds__(kDhThreads, KO > 1 ? 3 : 1) k_vecmat_dh_acc(De
 
 // Launch shape per word type: elements and requests per thread.
 constexpr int kEpt32 = 1, kRpt32 = 2, kEpt64 = 1, kRpt64 = 1;
+
+// Calibration in the accumulation's own form (32-bit words, RPT = 2 requests per thread, level ELL,
+// one output): per iteration, for both requests, the two key-switch sums over ELL digits (KsSum, no
+// reduction), their unreduced products with the diagonal value into the 128-bit carry-chain sums
+// (DhAcc::mac_wide) and the c0 product (DhAcc::mac), all from registers. Each of the kernel's loads (a
+// digit, two key words, the diagonal, c0) becomes one XOR with the iteration count, so the operands
+// change every iteration and the instruction mix matches the kernel's arithmetic plus one issue slot
+// per load. One op = one product-accumulate, counted as in the kernel: 2 (2 ELL + 3) per iteration.
+template <int ELL>
+__global__ void __launch_bounds__(kDhThreads, 1) k_dh_peak(ModConst m, u32 iters, u64* __restrict__ sink) {
+  const u64 tid = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  const u32 mask = 0x7FFFFFFFu;
+  u32 d[2][ELL], w0[ELL], w1[ELL], x[2];
+  u32 dv = (u32)(tid * 5 + 3) & mask;
+#pragma unroll
+  for (int j = 0; j < ELL; ++j) {
+    w0[j] = (u32)(tid * 11 + j) & mask;
+    w1[j] = (u32)(tid * 17 + j + 5) & mask;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) d[r][j] = (u32)(tid * 7 + 3 * j + r) & mask;
+  }
+  x[0] = (u32)(tid * 13) & mask;
+  x[1] = (u32)(tid * 19 + 1) & mask;
+  DhAcc<u32> u0[2], u1[2], a0[2];
+  constexpr bool kCarry = ELL > 4;
+  for (u32 it = 0; it < iters; ++it) {
+    dv ^= it;
+    KsSum<u32, ELL> s0[2], s1[2];
+#pragma unroll
+    for (int j = 0; j < ELL; ++j) {
+      w0[j] ^= it;
+      w1[j] ^= it;
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        d[r][j] ^= it;
+        s0[r].mac(d[r][j], w0[j], (u32)j);
+        s1[r].mac(d[r][j], w1[j], (u32)j);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      u32 c;
+      u64 v = s0[r].raw(c);
+      u0[r].template mac_wide<kCarry>(v, c, dv);
+      v = s1[r].raw(c);
+      u1[r].template mac_wide<kCarry>(v, c, dv);
+      x[r] ^= it;
+      a0[r].mac(x[r], dv);
+    }
+  }
+  u64 h = 0;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) h ^= u0[r].get(m) ^ u1[r].get(m) ^ a0[r].get(m);
+  sink[tid] = h;
+}
 
 // Sum of the chunk partials into chunk 0 (in place), every (request, component, slot).
 __global__ void k_vecmat_dh_fold(DevTables T, u32 ell, const __grid_constant__ VecmatDhPlan p) {
@@ -398,9 +460,16 @@ static void dh_acc_launch(dim3 grid, cudaStream_t st, const DevTables& T, u32 el
   }
 }
 
-u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow, u32 outs) {
+// Requests per thread of a launch: 1 with several outputs, else the tuned value (32-bit words) or the default.
+static u32 dh_rpt_of(bool narrow, u32 outs, u32 tuned) {
+  if (outs > 1) return 1;
+  if (!narrow) return kRpt64;
+  return tuned == 1 || tuned == 2 ? tuned : kRpt32;
+}
+
+u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow, u32 outs, u32 rpt_tuned) {
   const u64 n = 1ull << log_n;
-  const u32 ept = narrow ? kEpt32 : kEpt64, rpt = outs > 1 ? 1 : narrow ? kRpt32 : kRpt64;
+  const u32 ept = narrow ? kEpt32 : kEpt64, rpt = dh_rpt_of(narrow, outs, rpt_tuned);
   const u64 eblocks = (n + kDhThreads * ept - 1) / (kDhThreads * ept);
   return (u32)(eblocks * (ell + 1) * ((B + rpt - 1) / rpt));
 }
@@ -418,15 +487,19 @@ void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cu
   // product-accumulates per (request, rotation, element): the key-switch sums 2 ell (ell + 1), then per
   // output the two components' and the c0 term's diagonal products (additions for unit diagonals)
   const double ops = (double)p.B * p.R * n * (2.0 * ell * (ell + 1.0) + outs * (2.0 * (ell + 1.0) + ell));
-  Launch L(K_VECMAT_DH, st, by + 8.0 * n * (outs - 1.0) * (p.R * (ell + 1.0) + p.B * p.chunks * (3.0 * ell + 2.0)), ops);
-  const dim3 grid(vecmat_dh_base_ctas(T.log_n, ell, p.B, T.narrow, outs), p.chunks);
+  Launch L(K_VECMAT_DH, st, by + 8.0 * n * (outs - 1.0) * (p.R * (ell + 1.0) + p.B * p.chunks * (3.0 * ell + 2.0)), ops,
+           ell | (outs << 8) | ((p.diag ? 0u : 1u) << 16));
+  const dim3 grid(vecmat_dh_base_ctas(T.log_n, ell, p.B, T.narrow, outs, T.dh_rpt), p.chunks);
   if (outs == 4) {
     if (T.narrow)
       dh_acc_launch<u32, 1, 1, 4>(grid, st, T, ell, p);
     else
       dh_acc_launch<u64, 1, 1, 4>(grid, st, T, ell, p);
   } else if (T.narrow) {
-    dh_acc_launch<u32, kEpt32, kRpt32, 1>(grid, st, T, ell, p);
+    if (dh_rpt_of(true, 1, T.dh_rpt) == 1)
+      dh_acc_launch<u32, kEpt32, 1, 1>(grid, st, T, ell, p);
+    else
+      dh_acc_launch<u32, kEpt32, kRpt32, 1>(grid, st, T, ell, p);
   } else {
     dh_acc_launch<u64, kEpt64, kRpt64, 1>(grid, st, T, ell, p);
   }
@@ -465,3 +538,56 @@ void launch_vecmat_dh_moddown(const DevTables& T, u32 ell, const VecmatDhPlan& p
 }
 
 }  // namespace tcks
+
+// The product-accumulate rate of the double-hoisted accumulation's own form (k_dh_peak) at level
+// `ell` (1..8) on the current device, every SM busy: the ceiling its roofline is read against.
+extern "C" tcks_status tcks_calibrate_dh_macs(uint32_t ell, double* per_second) {
+  using namespace tcks;
+  if (!per_second || ell < 1 || ell > 8) return TCKS_ERR_INVALID_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return TCKS_ERR_CUDA;
+  const u32 blocks = (u32)sms * 8, iters = 2048;
+  const u64 total = (u64)kDhThreads * blocks;
+  const u64 q = 1073479681ull;  // a 30-bit prime
+  ModConst m{};
+  m.q = q;
+  m.mu64 = ~0ull / q;
+  const unsigned __int128 mu = ~(unsigned __int128)0 / q;
+  m.mu_hi = (u64)(mu >> 64);
+  m.mu_lo = (u64)mu;
+  m.r64 = (u64)(((unsigned __int128)1 << 64) % q);
+  m.mu32 = (1ull << 32) / q;
+  u64* sink = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  double best = 0;
+  tcks_status st = TCKS_OK;
+  if (cudaMalloc(&sink, total * 8) != cudaSuccess || cudaEventCreate(&a) != cudaSuccess ||
+      cudaEventCreate(&b) != cudaSuccess) {
+    st = TCKS_ERR_CUDA;
+  } else {
+    for (int rep = 0; rep < 4 && st == TCKS_OK; ++rep) {
+      cudaEventRecord(a, 0);
+      switch (ell) {
+#define TCKS_DHP(E) \
+  case E: k_dh_peak<E><<<blocks, kDhThreads>>>(m, iters, sink); break;
+        TCKS_DHP(1) TCKS_DHP(2) TCKS_DHP(3) TCKS_DHP(4) TCKS_DHP(5) TCKS_DHP(6) TCKS_DHP(7) TCKS_DHP(8)
+#undef TCKS_DHP
+      }
+      cudaEventRecord(b, 0);
+      if (cudaEventSynchronize(b) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        st = TCKS_ERR_CUDA;
+        break;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, a, b);
+      if (rep > 0 && ms > 0) best = std::max(best, (double)total * iters * 2.0 * (2.0 * ell + 3.0) / (ms * 1e-3));
+    }
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (sink) cudaFree(sink);
+  *per_second = best;
+  return st;
+}
+

@@ -17,7 +17,8 @@ enum KernelId : u32 {
 class Launch {
  public:
   // algo_ops: modular butterflies plus modular multiplies / multiply-accumulates of the launch
-  Launch(KernelId id, cudaStream_t st, double algo_bytes, double algo_ops = 0.0);
+  // tag: a launch-shape label the profiler keeps per record (0 = none)
+  Launch(KernelId id, cudaStream_t st, double algo_bytes, double algo_ops = 0.0, u32 tag = 0);
   ~Launch();
   Launch(const Launch&) = delete;
   Launch& operator=(const Launch&) = delete;
@@ -27,6 +28,7 @@ class Launch {
   cudaStream_t st_;
   double bytes_;
   double ops_;
+  u32 tag_;
   void* a_ = nullptr;
   bool active_ = false;
 };
@@ -51,6 +53,32 @@ struct NttDescTable {
   u32 pad;
 };
 void launch_ntt_desc(const DevTables& T, bool inverse, const NttDescTable& tab, u32 total_jobs, cudaStream_t st);
+// Polynomial batches of several contexts (N in [2^13, 2^16], one word type) transformed by one
+// columns launch and one launch over 8192-element slices: batch i is [polys][level][N] of context
+// ctx, from src to dst (equal pointers: in place).
+constexpr u32 kMultiCtxMax = 8, kMultiDescMax = 48;
+struct MultiNttDesc {
+  const u64* src;
+  u64* dst;
+  u64 first;      // first slice job of the batch in the slices launch
+  u64 col_first;  // first column item of the batch in the columns launch
+  u32 level, limbs, ctx, pad;
+};
+struct MultiNttTable {
+  DevTables T[kMultiCtxMax];
+  MultiNttDesc d[kMultiDescMax];
+  u32 n, n_ctx;
+  u64 slice_jobs, col_items;
+};
+struct MultiNttBatch {
+  const DevTables* T;
+  const u64* src;
+  u64* dst;
+  u32 polys, level;
+};
+// True when the batches fit one launch pair (at most kMultiCtxMax contexts and kMultiDescMax batches,
+// every N >= 2^13, one word type). Returns the number of launches made (0 when they do not fit).
+u32 launch_ntt_multi(bool inverse, const MultiNttBatch* batches, u32 n, cudaStream_t st);
 // Largest CTA size the limb kernels of each file accept (0 when the query fails).
 u32 limb_threads_cap_core(bool narrow, u32 log_c);
 u32 limb_threads_cap_sample(bool narrow, u32 log_c);
@@ -172,7 +200,7 @@ struct VecmatDhPlan {
 // Outputs per request of a plan (1 or 4).
 __host__ __device__ inline u32 dh_outs(const VecmatDhPlan& p) { return p.outs > 1 ? p.outs : 1; }
 // CTAs of one chunk of k_vecmat_dh_acc (element blocks x slots x requests).
-u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow, u32 outs = 1);
+u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow, u32 outs = 1, u32 rpt = 0);
 void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st);
 void launch_vecmat_dh_fold(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st);
 // top [2][B * outs][N] = INTT_P of the folded U_b[P]; out + (rq * outs + o) * out_b receives output o

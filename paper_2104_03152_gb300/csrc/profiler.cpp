@@ -26,6 +26,7 @@ struct Rec {
   u32 id;
   cudaEvent_t a, b;
   double bytes, ops;
+  u32 tag;
 };
 
 struct Prof {
@@ -58,8 +59,8 @@ std::atomic<bool> g_on{false};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_launches(u64 n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
-Launch::Launch(KernelId id, cudaStream_t st, double algo_bytes, double algo_ops)
-    : id_(id), st_(st), bytes_(algo_bytes), ops_(algo_ops) {
+Launch::Launch(KernelId id, cudaStream_t st, double algo_bytes, double algo_ops, u32 tag)
+    : id_(id), st_(st), bytes_(algo_bytes), ops_(algo_ops), tag_(tag) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (!g_on.load(std::memory_order_relaxed)) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -77,7 +78,7 @@ Launch::~Launch() {
   std::lock_guard<std::mutex> lock(p.mu);
   cudaEvent_t b = p.get();
   cudaEventRecord(b, st_);
-  p.recs.push_back(Rec{(u32)id_, (cudaEvent_t)a_, b, bytes_, ops_});
+  p.recs.push_back(Rec{(u32)id_, (cudaEvent_t)a_, b, bytes_, ops_, tag_});
 }
 
 }  // namespace tcks
@@ -139,6 +140,28 @@ tcks_status tcks_profile_read_ops(uint32_t idx, double* algo_ops) {
   for (const Rec& r : p.recs)
     if (r.id == idx) ops += r.ops;
   *algo_ops = ops;
+  return TCKS_OK;
+}
+
+tcks_status tcks_profile_records(uint32_t idx, uint32_t capacity, uint32_t* tags, double* ms, double* algo_ops,
+                                 uint32_t* count) {
+  if (idx >= K_COUNT || !count) return TCKS_ERR_INVALID_ARG;
+  Prof& p = prof();
+  std::lock_guard<std::mutex> lock(p.mu);
+  uint32_t n = 0;
+  for (const Rec& r : p.recs) {
+    if (r.id != idx) continue;
+    if (n < capacity) {
+      if (cudaEventSynchronize(r.b) != cudaSuccess) return TCKS_ERR_CUDA;
+      float e = 0;
+      if (cudaEventElapsedTime(&e, r.a, r.b) != cudaSuccess) return TCKS_ERR_CUDA;
+      if (tags) tags[n] = r.tag;
+      if (ms) ms[n] = e;
+      if (algo_ops) algo_ops[n] = r.ops;
+    }
+    ++n;
+  }
+  *count = n;
   return TCKS_OK;
 }
 

@@ -75,6 +75,7 @@ struct tcks_server {
 
 #define SRV_BEGIN \
   try {                 \
+    tcks::NvtxRange tcks_nvtx_range_(__func__); \
     tcks::drop_stale_cuda_error();
 #define SRV_END                                                        \
   }                                                                    \
@@ -208,6 +209,10 @@ static u32 harvest(tcks_server* s) {
 static void run_group(tcks_server* s, Lane& L, u32 stage, std::vector<Req*>& g) {
   tcks_ctx* c = L.ctx;
   const u32 count = (u32)g.size();
+  const std::string range = "lane " + std::to_string(&L - s->lanes.data()) + " stage " + std::to_string(stage) +
+                            " requests " + std::to_string(g.front()->id) + ".." + std::to_string(g.back()->id) +
+                            " (" + std::to_string(count) + ")";
+  NvtxRange nvtx(range.c_str());
   const u32 lin = g[0]->ct->level;
   const u32 lout = L.is_cnn ? cnn_stage_level(L.cnn, stage + 1) : lin - 1;
   const u64 win = ct_words(c, lin), wout = ct_words(c, lout);

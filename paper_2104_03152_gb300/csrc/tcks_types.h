@@ -68,7 +68,7 @@ struct DevTables {
   u32 L;       // number of data primes; the special primes (P) follow at chain index L ...
   u32 narrow;  // every prime < 2^31: kernels use 32-bit arithmetic
   u32 limb_threads;  // threads per CTA of the limb kernels (0 = the default for N), set by the autotuner
-  u32 pad2;
+  u32 dh_rpt;        // requests per thread of the double-hoisted accumulation, 32-bit words (0 = default 2)
 };
 
 }  // namespace tcks

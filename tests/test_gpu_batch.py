@@ -207,3 +207,33 @@ def test_batch_submit_wait_and_timeout(ctxs):
     with pytest.raises(tk.TcksError) as e:  # validation fails before anything is queued
         tk.Batch([(g, 7, 0, 1, 8, d.data_ptr(), d.data_ptr())])
     assert e.value.name == "INVALID_ARG"
+
+
+def test_ntt_jobs_of_four_ring_sizes_in_one_launch_pair(ctxs):
+    """NTT and INTT jobs of contexts with N = 2^13, 2^14, 2^15 and 2^16 go out as one columns launch and one
+    slices launch per direction (4 launches for the whole table), bit-identical to the single calls."""
+    o13 = ctxs[13][0]
+    gs = {13: ctxs[13][1], 15: ctxs[15][1]}
+    for ln in (14, 16):
+        gs[ln] = tk.Context(tk.Params(ln, primes=o13.primes[:5] + [o13.primes[-1]], scale=2.0 ** 50), seed=SEED,
+                            flags=tk.TCKS_AUTO_RELIN)
+    jobs, bufs = [], []
+    for k, (ln, g) in enumerate(sorted(gs.items())):
+        n = 1 << ln
+        for op, level, count in ((tk.JOB_NTT, 3, 2), (tk.JOB_INTT, 2, 3)):
+            x = inputs.random_limbs(g.primes[:level], n, 200 + 10 * k + op, polys=count)
+            d_in = _dev(x)
+            d_out = torch.empty_like(d_in)
+            bufs.append((g, op, count, level, x, d_out))
+            jobs.append((g, op, 0, count, level, d_in.data_ptr(), d_out.data_ptr()))
+    torch.cuda.synchronize()
+    before = tk.launch_count()
+    tk.batch_run(jobs)
+    for g in gs.values():
+        g.synchronize()
+    assert tk.launch_count() - before == 4
+    for g, op, count, level, x, d_out in bufs:
+        single = _dev(x)
+        g.ntt_inplace(single.data_ptr(), count, level, inverse=(op == tk.JOB_INTT))
+        g.synchronize()
+        assert np.array_equal(_host(d_out, x.shape), _host(single, x.shape)), (g.N, op)

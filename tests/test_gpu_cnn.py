@@ -363,3 +363,27 @@ def test_cnn_forward_wire_equals_batch(setup):
     assert np.all(host_out == 0xAB), "a refused batch wrote into the output buffer"
     model.forward_wire(host_in, 3, host_out)  # the context is still usable
     assert host_out[:out_size].tobytes() == want[0]
+
+
+def test_cnn_autotune_is_bit_identical(setup, tmp_path):
+    """The network autotuner (limb-kernel CTA size x accumulation requests per thread, timed on the
+    batched forward pass) changes only the launch shape: the batch's outputs are bit-identical before
+    and after, and a second call reads the recorded choice back from the cache."""
+    o, w, enc, ctx, model, need = setup
+    ctx.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | tk.TCKS_DOUBLE_HOIST)
+    try:
+        cts = []
+        for seed in range(3):
+            v, _ = oracle.OracleCKKS.im2col(inputs.mnist_like_image(400 + seed), 7, 7, 3, o.slots)
+            cts.append(ctx.encrypt_values(v, 800 + seed))
+        before = [x.export() for x in model.forward_batch(cts)]
+        cache = str(tmp_path / "tune.json")
+        t, r = model.autotune(3, cache)
+        assert t in (128, 256, 512) and r in (1, 2)
+        after = [x.export() for x in model.forward_batch(cts)]
+        for a, b in zip(before, after):
+            assert np.array_equal(a, b)
+        assert model.autotune(3, cache) == (t, r)
+        assert "|cnn|13|32|3" in open(cache).read()
+    finally:
+        ctx.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE)
