@@ -462,13 +462,44 @@ tcks_status tcks_batch_submit(const tcks_batch_job* jobs, uint32_t n_jobs, tcks_
 tcks_status tcks_batch_wait(tcks_batch* b, int64_t timeout_ns);
 void tcks_batch_free(tcks_batch* b);
 /* The batch captured once as a CUDA graph (after one eager run that builds the key tables) and
- * replayed by tcks_batch_graph_run on jobs[0].ctx's stream over the same buffers. Every context
- * must use the library's own pool allocator (UNSUPPORTED otherwise). launches: kernels per replay. */
+ * replayed by tcks_batch_graph_run on jobs[0].ctx's stream over the same buffers. With the library's
+ * pool allocator the graph holds stream-ordered allocation nodes; a context with a caller allocator
+ * (whose callbacks cannot run inside a capture) gets one scratch block from its allocator, sized by a
+ * second uncaptured pass, which the graph holds until tcks_batch_graph_free. launches: kernels per
+ * replay. */
 typedef struct tcks_batch_graph tcks_batch_graph;
 tcks_status tcks_batch_graph_create(const tcks_batch_job* jobs, uint32_t n_jobs, tcks_batch_graph** out);
 tcks_status tcks_batch_graph_run(tcks_batch_graph* g);
 tcks_status tcks_batch_graph_launches(const tcks_batch_graph* g, uint64_t* launches);
 void tcks_batch_graph_free(tcks_batch_graph* g);
+
+/* -------------------------------------------- persistent executor (device work queue) ---- */
+/* A kernel that stays resident and takes NTT / INTT work from a queue instead of one launch per job
+ * (for streams of small transforms, such as a serving loop's, where a launch costs as much as the
+ * work; the paper has no counterpart). tcks_executor_start launches it on a stream of its own (one CTA
+ * per SM; N <= 2^13, one CTA per limb) with a ring of `capacity` one-limb tasks in pinned, mapped host
+ * memory. tcks_executor_post queues a job: polys polynomials [polys][level][N] from d_in to d_out
+ * (device buffers of the executor's context that stay valid until the ticket completes; limb l of
+ * each polynomial modulo q_l; forward: natural order in, bit-reversed out; results equal
+ * tcks_ntt_inplace), and returns a ticket. tcks_executor_wait waits on the host for the ticket (a
+ * negative timeout waits without limit; TCKS_ERR_TIMEOUT when timeout_ns passes first). Every wait
+ * inside the kernel is bounded: when no task is published for idle_timeout_ns (the GPU's global timer,
+ * with an iteration cap as well), the kernel writes TCKS_ERR_TIMEOUT to its status word and every CTA
+ * leaves; later posts and waits then return that status. tcks_executor_close stops the kernel (and
+ * waits, bounded, for it to leave) and returns the status word (0, or TCKS_ERR_TIMEOUT);
+ * tcks_executor_free closes if needed and releases everything. While the kernel is resident, a
+ * device-wide synchronize (cudaDeviceSynchronize, and calls that imply one such as cudaFree) waits
+ * for it to leave, i.e. until close or the idle limit: synchronize streams instead, and have d_in
+ * written (its stream synchronized) before the post. Errors: INVALID_ARG, UNSUPPORTED (N > 2^13),
+ * TIMEOUT, CUDA_ERROR. */
+typedef struct tcks_executor tcks_executor;
+enum { TCKS_EXEC_NTT = 0, TCKS_EXEC_INTT = 1 };
+tcks_status tcks_executor_start(tcks_ctx* ctx, uint32_t capacity, int64_t idle_timeout_ns, tcks_executor** out);
+tcks_status tcks_executor_post(tcks_executor* e, uint32_t op, const uint64_t* d_in, uint64_t* d_out, uint32_t polys,
+                               uint32_t level, uint64_t* ticket);
+tcks_status tcks_executor_wait(tcks_executor* e, uint64_t ticket, int64_t timeout_ns);
+tcks_status tcks_executor_close(tcks_executor* e, int32_t* device_status);
+void tcks_executor_free(tcks_executor* e);
 
 /* ------------------------------------------------------------------ launch accounting ---- */
 /* Integer-pipe ceiling for the roofline of the ALU-bound kernels: modular butterflies per second
@@ -610,7 +641,8 @@ tcks_status tcks_cnn_forward_wire(const tcks_cnn* m, const uint8_t* host_in, uin
 /* CUDA graph of the batched forward for a fixed batch size (the schedule is captured once with its
  * stream-ordered scratch allocations, then replayed): create captures it (after one eager pass that
  * warms the key tables), run copies the inputs into the graph's staging buffers, replays and returns
- * new output ciphertexts, bit-identical to tcks_cnn_forward. Needs the library's own allocator. */
+ * new output ciphertexts, bit-identical to tcks_cnn_forward. With a caller allocator the scratch
+ * is one block from it, sized by a second uncaptured pass and held by the graph. */
 typedef struct tcks_cnn_graph tcks_cnn_graph;
 tcks_status tcks_cnn_graph_create(const tcks_cnn* m, uint32_t count, tcks_cnn_graph** out);
 tcks_status tcks_cnn_graph_run(tcks_cnn_graph* g, const tcks_ct* const* in, tcks_ct** outs);

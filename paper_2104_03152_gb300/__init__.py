@@ -185,6 +185,11 @@ _SIGS = {
     "tcks_ct_serialize_seeded": (ctypes.c_int32, [_vp, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64, _u64p]),
     "tcks_rotate_sum_hoisted": (ctypes.c_int32, [_vp, _i32p, ctypes.c_uint32, _vpp]),
     "tcks_batch_run": (ctypes.c_int32, [_vp, ctypes.c_uint32]),
+    "tcks_executor_start": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_int64, _vpp]),
+    "tcks_executor_post": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vp, _vp, ctypes.c_uint32, ctypes.c_uint32, _u64p]),
+    "tcks_executor_wait": (ctypes.c_int32, [_vp, ctypes.c_uint64, ctypes.c_int64]),
+    "tcks_executor_close": (ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int32)]),
+    "tcks_executor_free": (None, [_vp]),
     "tcks_batch_submit": (ctypes.c_int32, [_vp, ctypes.c_uint32, _vpp]),
     "tcks_batch_wait": (ctypes.c_int32, [_vp, ctypes.c_int64]),
     "tcks_batch_free": (None, [_vp]),
@@ -897,6 +902,39 @@ def batch_run(jobs):
     context stream)."""
     arr = _job_array(jobs)
     check(lib().tcks_batch_run(arr, len(jobs)))
+
+
+EXEC_NTT, EXEC_INTT = 0, 1
+
+
+class Executor:
+    """A persistent kernel taking NTT / INTT jobs from a queue (tcks_executor_*); every wait inside it is
+    bounded by idle_timeout_ns."""
+
+    def __init__(self, ctx: "Context", capacity: int = 4096, idle_timeout_ns: int = 1_000_000_000):
+        self.ctx = ctx
+        h = _vp()
+        check(lib().tcks_executor_start(ctx.h, capacity, int(idle_timeout_ns), ctypes.byref(h)))
+        self.h = h
+
+    def post(self, op: int, d_in: int, d_out: int, polys: int, level: int) -> int:
+        t = np.zeros(1, dtype=np.uint64)
+        check(lib().tcks_executor_post(self.h, op, _vp(d_in), _vp(d_out), polys, level, _p(t)))
+        return int(t[0])
+
+    def wait(self, ticket: int, timeout_ns: int = -1):
+        check(lib().tcks_executor_wait(self.h, ticket, int(timeout_ns)))
+
+    def close(self) -> int:
+        """Stops the kernel; returns its status word (0, or the TIMEOUT code)."""
+        st = ctypes.c_int32()
+        check(lib().tcks_executor_close(self.h, ctypes.byref(st)))
+        return st.value
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().tcks_executor_free(self.h)
+            self.h = None
 
 
 class Batch:
