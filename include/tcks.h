@@ -49,7 +49,8 @@ enum {
   TCKS_ERR_TIMEOUT = -10,        /* a bounded wait ran out (tcks_batch_wait, the serving loop) */
   TCKS_ERR_VALUE_OVERFLOW = -11, /* encode: |scale * m_i| >= 2^62 */
   TCKS_ERR_UNSUPPORTED = -12,    /* valid request this build does not implement (detail says what) */
-  TCKS_ERR_NOT_READY = -13       /* serving: the request has not completed yet */
+  TCKS_ERR_NOT_READY = -13,      /* serving: the request has not completed yet */
+  TCKS_ERR_DEBUG_CHECK = -14     /* debug build: a descriptor index or bound check failed (detail says which) */
 };
 
 const char* tcks_status_string(tcks_status s);
@@ -486,8 +487,8 @@ void tcks_batch_graph_free(tcks_batch_graph* g);
  * inside the kernel is bounded: when no task is published for idle_timeout_ns (the GPU's global timer,
  * with an iteration cap as well), the kernel writes TCKS_ERR_TIMEOUT to its status word and every CTA
  * leaves; later posts and waits then return that status. tcks_executor_close stops the kernel (and
- * waits, bounded, for it to leave) and returns the status word (0, or TCKS_ERR_TIMEOUT);
- * tcks_executor_free closes if needed and releases everything. While the kernel is resident, a
+ * waits, bounded, for it to leave) and returns the status word (0, TCKS_ERR_TIMEOUT, or in a debug
+ * build TCKS_ERR_DEBUG_CHECK for a task that failed its range check); tcks_executor_free closes if needed and releases everything. While the kernel is resident, a
  * device-wide synchronize (cudaDeviceSynchronize, and calls that imply one such as cudaFree) waits
  * for it to leave, i.e. until close or the idle limit: synchronize streams instead, and have d_in
  * written (its stream synchronized) before the post. Errors: INVALID_ARG, UNSUPPORTED (N > 2^13),
@@ -519,6 +520,22 @@ tcks_status tcks_calibrate_macs(uint32_t word_bits, double* per_second);
 tcks_status tcks_calibrate_dh_macs(uint32_t ell, double* per_second);
 /* Number of kernel launches the library has issued since it was loaded. */
 uint64_t tcks_launch_count(void);
+/* Debug build (compiled with TCKS_DEBUG_CHECKS): 1, else 0. A debug build asserts the invariants of
+ * every descriptor table a batched launch builds and of the job list it comes from (no job's buffer
+ * overlapping another job's output), and its descriptor-driven kernels check each index they take
+ * from a descriptor (context, limb within the descriptor's declared range, prime within the chain)
+ * before using it: a failed check sets a bit of the context's error word and skips that work item
+ * (no trap). Batch runs, graph replays and batch waits then synchronize, read the word of every
+ * context involved and return TCKS_ERR_DEBUG_CHECK when a bit is set (clearing it). */
+int32_t tcks_debug_checks(void);
+/* Debug builds' self-test of the device range checks: transforms (forward NTT, in place) the
+ * device buffer d_buf [polys][level][N] of ctx (N in [2^13, 2^16]) through the multi-context
+ * descriptor launch with the descriptor declaring `understate` limbs fewer than the grid covers, so
+ * that the kernels must skip the last `understate` limbs (left as they were) and report them;
+ * *word receives the error word's bits (then cleared). UNSUPPORTED in the default build or for N
+ * outside the range. */
+tcks_status tcks_debug_selftest(tcks_ctx* ctx, uint64_t* d_buf, uint32_t polys, uint32_t level, uint32_t understate,
+                                uint32_t* word);
 /* Kernel profiler: while on, every launch is bracketed by CUDA events on its stream and carries its
  * algorithmic bytes (each operand read once, each result written once, each distinct key once).
  * start clears earlier records. read() reports, for kernel family idx < tcks_profile_count(), its

@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libtcks.so")
+# TCKS_DEBUG_CHECKS=1 in the environment selects the debug build (descriptor and range checks).
+DEBUG_BUILD = os.environ.get("TCKS_DEBUG_CHECKS", "") == "1"
+LIB_PATH = os.path.join(HERE, "_build_debug" if DEBUG_BUILD else "_build", "libtcks.so")
 
 TCKS_AUTO_RELIN = 1
 TCKS_AUTO_RESCALE = 2
@@ -144,6 +146,9 @@ _SIGS = {
     "tcks_autotune": (ctypes.c_int32, [_vp, ctypes.c_char_p, _u32p]),
     "tcks_cnn_autotune": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_char_p, _u32p, _u32p]),
     "tcks_launch_count": (ctypes.c_uint64, []),
+    "tcks_debug_checks": (ctypes.c_int32, []),
+    "tcks_debug_selftest": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
+                                             ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     "tcks_profile_start": (ctypes.c_int32, []),
     "tcks_profile_stop": (ctypes.c_int32, []),
     "tcks_profile_count": (ctypes.c_uint32, []),
@@ -215,7 +220,7 @@ def lib(build_if_missing: bool = False):
     if not os.path.exists(LIB_PATH):
         if build_if_missing:
             from .build import build
-            build()
+            build(debug=DEBUG_BUILD)
         else:
             raise RuntimeError(f"libtcks.so is not built ({LIB_PATH}); run paper_2104_03152_gb300.build.build()")
     L = ctypes.CDLL(LIB_PATH)
@@ -235,6 +240,19 @@ def check(status: int):
 
 def launch_count() -> int:
     return int(lib().tcks_launch_count())
+
+
+def debug_checks() -> bool:
+    """True when the loaded library is the debug build (descriptor and device range checks)."""
+    return bool(lib().tcks_debug_checks())
+
+
+def debug_selftest(ctx: "Context", d_ptr: int, polys: int, level: int, understate: int) -> int:
+    """Forward NTT in place through the multi-context descriptor launch with the descriptor declaring
+    `understate` limbs fewer than the grid covers; returns the error word the range checks set."""
+    w = ctypes.c_uint32()
+    check(lib().tcks_debug_selftest(ctx.h, _vp(d_ptr), polys, level, understate, ctypes.byref(w)))
+    return w.value
 
 
 def profile_start():

@@ -16,6 +16,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtcks.so")
+# The debug build (index and bounds checks on descriptor tables, device range checks writing an error
+# word; see csrc/debug_checks.cuh) goes to its own folder; the package loads it when the environment
+# sets TCKS_DEBUG_CHECKS=1.
+OUT_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(OUT_DEBUG, "libtcks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -45,28 +50,30 @@ def _compile(nvcc: str, src: str, obj: str, extra: list[str]) -> str:
     return r.stderr
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, debug: bool = False) -> str:
+    out, lib = (OUT_DEBUG, LIB_DEBUG) if debug else (OUT, LIB)
+    extra = list(extra or []) + (["-DTCKS_DEBUG_CHECKS"] if debug else [])
+    os.makedirs(out, exist_ok=True)
     srcs = sources()
     newest = max(os.path.getmtime(p) for p in srcs + _headers() + [__file__])
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
-        return LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= newest:
+        return lib
     nvcc = _nvcc()
-    objs = [os.path.join(OUT, os.path.basename(s) + ".o") for s in srcs]
+    objs = [os.path.join(out, os.path.basename(s) + ".o") for s in srcs]
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        futs = [ex.submit(_compile, nvcc, s, o, extra or []) for s, o in zip(srcs, objs)]
+        futs = [ex.submit(_compile, nvcc, s, o, extra) for s, o in zip(srcs, objs)]
         for f in futs:
             msg = f.result()
             if verbose and msg:
                 print(msg, file=sys.stderr)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

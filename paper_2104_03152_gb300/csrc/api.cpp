@@ -1,6 +1,7 @@
 // C ABI of the library (include/tcks.h): handle management, argument checks, and the composition of
 // kernels into the CKKSVector operations of TenSEAL (§2-§3).
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -176,6 +177,8 @@ const KeyTable& key_table(tcks_ctx* c, const std::vector<u32>& steps, u32 ell) {
     KeyTable t;
     t.n = (u32)h.size();
     t.min_K = min_K;
+    t.aligned16 = true;
+    for (const KsKey& k : h) t.aligned16 = t.aligned16 && ((uintptr_t)k.key & 15) == 0;
     t.d = (KsKey*)c->dev_alloc(sizeof(KsKey) * h.size());
     check_cuda(cudaMemcpyAsync(t.d, h.data(), sizeof(KsKey) * h.size(), cudaMemcpyHostToDevice, c->stream),
                "key table");
@@ -337,6 +340,16 @@ void encode_into(tcks_ctx* c, const double* d_v, size_t n, double scale, u32 lev
 void* tcks_ctx::dev_alloc(size_t bytes) {
   if (bytes == 0) bytes = 8;
   void* p = nullptr;
+  const size_t rounded = (bytes + 255) & ~(size_t)255;
+  if (arena.mode == ARENA_SERVE) {
+    if (arena.used + rounded > arena.size)
+      fail(TCKS_ERR_OUT_OF_MEMORY, "the captured pass allocated more than the recorded pass (" +
+                                       std::to_string(arena.used + rounded) + " > " + std::to_string(arena.size) + " bytes)");
+    p = arena.base + arena.used;
+    arena.used += rounded;
+    return p;
+  }
+  if (arena.mode == ARENA_RECORD) arena.recorded += rounded;
   if (has_alloc) {
     p = alloc.alloc(bytes, (void*)stream, alloc.user);
     if (!p) fail(TCKS_ERR_OUT_OF_MEMORY, "allocator callback returned NULL for " + std::to_string(bytes) + " bytes");
@@ -352,11 +365,63 @@ void* tcks_ctx::dev_alloc(size_t bytes) {
 
 void tcks_ctx::dev_free(void* p) {
   if (!p) return;
+  for (const auto& b : graph_blocks)
+    if ((char*)p >= b.first && (char*)p < b.first + b.second) return;  // a graph's block: released with the graph
+  if (arena.mode == ARENA_SERVE && (char*)p >= arena.base && (char*)p < arena.base + arena.size) return;
   if (has_alloc)
     alloc.free(p, (void*)stream, alloc.user);
   else if (cudaFreeAsync(p, stream) != cudaSuccess)
     cudaGetLastError();  // a release has no caller to report to; keep it out of the next launch check
 }
+
+namespace tcks {
+
+void arena_record(const std::vector<tcks_ctx*>& ctxs) {
+  for (tcks_ctx* c : ctxs)
+    if (c->has_alloc) c->arena = tcks_ctx::CaptureArena{tcks_ctx::ARENA_RECORD, 0, nullptr, 0, 0};
+}
+
+void arena_serve(const std::vector<tcks_ctx*>& ctxs, std::vector<std::pair<tcks_ctx*, char*>>& held) {
+  for (tcks_ctx* c : ctxs) {
+    if (!c->has_alloc || c->arena.mode != tcks_ctx::ARENA_RECORD) continue;
+    const size_t size = c->arena.recorded ? c->arena.recorded : 256;
+    c->arena.mode = tcks_ctx::ARENA_OFF;
+    char* base = (char*)c->dev_alloc(size);
+    c->graph_blocks.push_back({base, size});
+    held.push_back({c, base});
+    c->arena = tcks_ctx::CaptureArena{tcks_ctx::ARENA_SERVE, 0, base, 0, size};
+  }
+}
+
+void debug_word_check(const std::vector<tcks_ctx*>& ctxs, const char* where) {
+  for (tcks_ctx* c : ctxs) {
+    u32 w = 0;
+    check_cuda(cudaStreamSynchronize(c->stream), where);
+    check_cuda(cudaMemcpy(&w, c->T.dbg, sizeof(u32), cudaMemcpyDeviceToHost), "debug word");
+    if (!w) continue;
+    check_cuda(cudaMemset(c->T.dbg, 0, sizeof(u32)), "debug word");
+    char bits[16];
+    std::snprintf(bits, sizeof bits, "0x%x", w);
+    fail(TCKS_ERR_DEBUG_CHECK, std::string(where) + ": a device range check failed (error bits " + bits +
+                                   ": 1 context index, 2 limb range, 4 prime index, 8 null pointer)");
+  }
+}
+
+void arena_off(const std::vector<tcks_ctx*>& ctxs) {
+  for (tcks_ctx* c : ctxs) c->arena = tcks_ctx::CaptureArena{};
+}
+
+void arena_release(tcks_ctx* c, char* block) {
+  cudaStreamSynchronize(c->stream);
+  for (size_t i = 0; i < c->graph_blocks.size(); ++i)
+    if (c->graph_blocks[i].first == block) {
+      c->graph_blocks.erase(c->graph_blocks.begin() + (long)i);
+      c->dev_free(block);
+      return;
+    }
+}
+
+}  // namespace tcks
 
 void tcks_ctx::keys_changed() {
   for (auto& kv : key_tables) dev_free(kv.second.d);
@@ -390,6 +455,7 @@ const char* tcks_status_string(tcks_status s) {
     case TCKS_ERR_VALUE_OVERFLOW: return "VALUE_OVERFLOW";
     case TCKS_ERR_UNSUPPORTED: return "UNSUPPORTED";
     case TCKS_ERR_NOT_READY: return "NOT_READY";
+    case TCKS_ERR_DEBUG_CHECK: return "DEBUG_CHECK";
     default: return "UNKNOWN";
   }
 }
@@ -536,7 +602,8 @@ tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32
   if (H.narrow) c->d_tw32 = (u32*)c->dev_alloc(sizeof(u32) * H.tw32.size());
   c->d_slot = (u32*)c->dev_alloc(sizeof(u32) * H.slot_index.size());
   c->d_zeta = (double*)c->dev_alloc(sizeof(double) * H.zeta.size());
-  c->d_status = (int*)c->dev_alloc(sizeof(int) * 4);
+  c->d_status = (int*)c->dev_alloc(sizeof(int) * 4);  // [0] kernel status words, [2] debug error word
+  check_cuda(cudaMemsetAsync(c->d_status, 0, sizeof(int) * 4, c->stream), "status words");
   // CRT words per level: Q_l and (Q_l - 1)/2
   std::vector<u64> qw((size_t)2 * c->L * CRT_MAXW, 0);
   for (u32 l = 1; l <= c->L; ++l) {
@@ -577,6 +644,8 @@ tcks_status tcks_context_create(const tcks_params* params, uint64_t seed, uint32
   c->T.log_n = params->log_n;
   c->T.n_mods = nm;
   c->T.L = c->L;
+  c->T.dbg = (u32*)(c->d_status + 2);
+  c->T.kerr = (u32*)(c->d_status + 3);
   if (c->hyb) {  // hybrid key-switching constants
     const std::vector<u64> hv = hyb_constants(params->chain, c->L, c->K, c->alpha, &c->H);
     c->d_hyb = (u64*)c->dev_alloc(sizeof(u64) * hv.size());

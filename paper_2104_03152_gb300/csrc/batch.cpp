@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "context.h"
+#include "debug_checks.cuh"
 
 using namespace tcks;
 
@@ -107,12 +108,40 @@ void validate(const tcks_batch_job* jobs, u32 n_jobs) {
         fail(TCKS_ERR_INVALID_ARG, "job " + std::to_string(i) + ": unknown op");
     }
   }
+  if (kDebugChecks) {  // jobs of one batch may run concurrently: no job writes what another touches
+    auto extent = [](const tcks_batch_job& j, bool out) -> u64 {
+      const u64 limb = (u64)j.ctx->N * 8;
+      const u32 polys = j.op == TCKS_JOB_NTT || j.op == TCKS_JOB_INTT ? 1 : (j.op == TCKS_JOB_RELIN && !out ? 3 : 2);
+      return (u64)j.count * polys * j.level * limb;
+    };
+    auto overlap = [](const void* a, u64 na, const void* b, u64 nb) {
+      const char *x = (const char*)a, *y = (const char*)b;
+      return na && nb && x < y + nb && y < x + na;
+    };
+    for (u32 i = 0; i < n_jobs; ++i)
+      for (u32 k = 0; k < n_jobs; ++k) {
+        if (i == k) continue;
+        const tcks_batch_job &a = jobs[i], &b = jobs[k];
+        if (overlap(a.d_out, extent(a, true), b.d_out, extent(b, true)) ||
+            overlap(a.d_out, extent(a, true), b.d_in, extent(b, false)))
+          fail(TCKS_ERR_DEBUG_CHECK, "job " + std::to_string(i) + " writes memory that job " + std::to_string(k) + " uses");
+      }
+  }
 }
 
 void run_ctx_ntt(tcks_ctx* c, const std::vector<const tcks_batch_job*>& js, bool inverse) {
   NttDescTable tab{};
   u32 total = 0;
   auto flush = [&]() {
+    if (kDebugChecks) {  // offsets from 0, monotone, adding up to the launch
+      u32 at = 0;
+      for (u32 i = 0; i < tab.n; ++i) {
+        if (tab.d[i].first != at || !tab.d[i].level || tab.d[i].limbs % tab.d[i].level)
+          fail(TCKS_ERR_DEBUG_CHECK, "NTT descriptor " + std::to_string(i) + " out of order or range");
+        at += tab.d[i].limbs;
+      }
+      if (at != total) fail(TCKS_ERR_DEBUG_CHECK, "NTT descriptors do not add up to the launch");
+    }
     launch_ntt_desc(c->T, inverse, tab, total, c->stream);
     tab.n = 0;
     total = 0;
@@ -121,7 +150,7 @@ void run_ctx_ntt(tcks_ctx* c, const std::vector<const tcks_batch_job*>& js, bool
     if (!j->count) continue;
     const u64 limbs = (u64)j->count * j->level;
     if (tab.n == kNttDescMax || total + limbs > (0x7fffffffull >> cluster_log(c))) flush();
-    tab.d[tab.n++] = NttDesc{j->d_in, j->d_out, total, j->level};
+    tab.d[tab.n++] = NttDesc{j->d_in, j->d_out, total, j->level, (u32)limbs, 0};
     total += (u32)limbs;
   }
   flush();
@@ -217,6 +246,7 @@ struct tcks_batch_graph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   u64 launches = 0;
+  std::vector<std::pair<tcks_ctx*, char*>> blocks;  // capture arenas of contexts with a caller allocator
 };
 
 #define BATCH_BEGIN \
@@ -236,10 +266,20 @@ struct tcks_batch_graph {
 
 extern "C" {
 
+namespace {
+std::vector<tcks_ctx*> contexts_of(const tcks_batch_job* jobs, u32 n_jobs) {
+  std::vector<tcks_ctx*> v;
+  for (u32 i = 0; i < n_jobs; ++i)
+    if (std::find(v.begin(), v.end(), jobs[i].ctx) == v.end()) v.push_back(jobs[i].ctx);
+  return v;
+}
+}  // namespace
+
 tcks_status tcks_batch_run(const tcks_batch_job* jobs, uint32_t n_jobs) {
   BATCH_BEGIN
   validate(jobs, n_jobs);
   run_jobs(jobs, n_jobs);
+  if (kDebugChecks) debug_word_check(contexts_of(jobs, n_jobs), "batch run");
   BATCH_END
 }
 
@@ -295,6 +335,7 @@ tcks_status tcks_batch_wait(tcks_batch* b, int64_t timeout_ns) {
     std::this_thread::sleep_for(pause);
     if (pause < std::chrono::microseconds(100)) pause *= 2;
   }
+  if (kDebugChecks) debug_word_check(b->ctxs, "batch wait");
   BATCH_END
 }
 
@@ -303,6 +344,7 @@ void tcks_batch_graph_free(tcks_batch_graph* g) {
   if (g->origin) cudaStreamSynchronize(g->origin);
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
+  for (const auto& b : g->blocks) arena_release(b.first, b.second);
   for (tcks_ctx* c : g->ctxs) ctx_release(c);
   delete g;
   cudaGetLastError();  // clean-up statuses are not reported
@@ -321,7 +363,6 @@ tcks_status tcks_batch_graph_create(const tcks_batch_job* jobs, uint32_t n_jobs,
   tcks_batch_graph* g = guard.g;
   for (u32 i = 0; i < n_jobs; ++i) {
     tcks_ctx* c = jobs[i].ctx;
-    if (c->has_alloc) fail(TCKS_ERR_UNSUPPORTED, "graph capture needs the library's own stream-ordered pool allocator");
     if (std::find(g->ctxs.begin(), g->ctxs.end(), c) == g->ctxs.end()) {
       ctx_retain(c);
       g->ctxs.push_back(c);
@@ -331,6 +372,19 @@ tcks_status tcks_batch_graph_create(const tcks_batch_job* jobs, uint32_t n_jobs,
   // one eager pass builds every cached key table (their host copies cannot run inside a capture)
   run_jobs(jobs, n_jobs);
   for (tcks_ctx* c : g->ctxs) check_cuda(cudaStreamSynchronize(c->stream), "graph warm-up");
+  // contexts with a caller allocator: a second uncaptured pass measures the scratch the capture takes
+  struct ArenaGuard {
+    const std::vector<tcks_ctx*>& ctxs;
+    ~ArenaGuard() { arena_off(ctxs); }
+  } arena_guard{g->ctxs};
+  bool any_caller_alloc = false;
+  for (tcks_ctx* c : g->ctxs) any_caller_alloc |= c->has_alloc;
+  if (any_caller_alloc) {
+    arena_record(g->ctxs);
+    run_jobs(jobs, n_jobs);
+    for (tcks_ctx* c : g->ctxs) check_cuda(cudaStreamSynchronize(c->stream), "graph scratch pass");
+    arena_serve(g->ctxs, g->blocks);
+  }
   const u64 n0 = tcks_launch_count();
   check_cuda(cudaStreamBeginCapture(g->origin, cudaStreamCaptureModeThreadLocal), "begin capture");
   try {
@@ -342,6 +396,7 @@ tcks_status tcks_batch_graph_create(const tcks_batch_job* jobs, uint32_t n_jobs,
     throw;
   }
   check_cuda(cudaStreamEndCapture(g->origin, &g->graph), "end capture");
+  arena_off(g->ctxs);
   g->launches = tcks_launch_count() - n0;
   check_cuda(cudaGraphInstantiate(&g->exec, g->graph, 0), "graph instantiate");
   *out = g;
@@ -354,6 +409,29 @@ tcks_status tcks_batch_graph_run(tcks_batch_graph* g) {
   if (!g) fail(TCKS_ERR_INVALID_ARG, "null graph");
   check_cuda(cudaGraphLaunch(g->exec, g->origin), "graph launch");
   count_launches(g->launches);
+  if (kDebugChecks) debug_word_check(g->ctxs, "graph replay");
+  BATCH_END
+}
+
+int32_t tcks_debug_checks(void) { return kDebugChecks ? 1 : 0; }
+
+tcks_status tcks_debug_selftest(tcks_ctx* c, uint64_t* d_buf, uint32_t polys, uint32_t level, uint32_t understate,
+                                uint32_t* word) {
+  BATCH_BEGIN
+  if (!c || !d_buf || !word) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *word = 0;
+  if (!kDebugChecks) fail(TCKS_ERR_UNSUPPORTED, "the device range checks are compiled into debug builds only");
+  if (c->params.log_n < 13 || c->params.log_n > 16) fail(TCKS_ERR_UNSUPPORTED, "the self-test takes N in [2^13, 2^16]");
+  if (!polys || level < 1 || level > c->L + c->K) fail(TCKS_ERR_INVALID_ARG, "level out of range");
+  if (understate > (u64)polys * level) fail(TCKS_ERR_INVALID_ARG, "understate exceeds the limbs");
+  const MultiNttBatch b{&c->T, d_buf, d_buf, polys, level};
+  if (!launch_ntt_multi(false, &b, 1, c->stream, understate)) fail(TCKS_ERR_UNSUPPORTED, "the launch does not fit");
+  check_launch("debug self-test");
+  check_cuda(cudaStreamSynchronize(c->stream), "debug self-test");
+  u32 w = 0;
+  check_cuda(cudaMemcpy(&w, c->T.dbg, sizeof(u32), cudaMemcpyDeviceToHost), "debug word");
+  check_cuda(cudaMemset(c->T.dbg, 0, sizeof(u32)), "debug word");
+  *word = w;
   BATCH_END
 }
 

@@ -626,6 +626,7 @@ struct tcks_cnn_graph {
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   u64 launches;  // kernel launches in one replay
+  std::vector<std::pair<tcks_ctx*, char*>> blocks;  // the capture arena with a caller allocator
 };
 
 void tcks_cnn_graph_free(tcks_cnn_graph* g) {
@@ -634,6 +635,7 @@ void tcks_cnn_graph_free(tcks_cnn_graph* g) {
   cudaStreamSynchronize(c->stream);
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
+  for (const auto& b : g->blocks) arena_release(b.first, b.second);
   c->dev_free(g->in);
   c->dev_free(g->out);
   delete g;
@@ -650,7 +652,6 @@ tcks_status tcks_cnn_graph_create(const tcks_cnn* m, uint32_t count, tcks_cnn_gr
   if (!m || !out || !count) fail(TCKS_ERR_INVALID_ARG, "null argument or zero batch");
   *out = nullptr;
   tcks_ctx* c = m->ctx;
-  if (c->has_alloc) fail(TCKS_ERR_UNSUPPORTED, "graph capture needs the library's own stream-ordered pool allocator");
   const u64 w_in = ct_words(c, m->L), w_out = ct_words(c, m->L - 6);
   guard.g = new tcks_cnn_graph{c, m, count, nullptr, nullptr, nullptr, nullptr, 0};
   ctx_retain(c);
@@ -661,6 +662,18 @@ tcks_status tcks_cnn_graph_create(const tcks_cnn* m, uint32_t count, tcks_cnn_gr
   // one eager pass builds every cached key table (their host copies cannot run inside a capture)
   cnn_forward_dev(m, g->in, w_in, count, g->out);
   check_cuda(cudaStreamSynchronize(c->stream), "graph warm-up");
+  // a caller allocator: a second uncaptured pass measures the scratch the capture takes
+  const std::vector<tcks_ctx*> ctxs{c};
+  struct ArenaGuard {
+    const std::vector<tcks_ctx*>& ctxs;
+    ~ArenaGuard() { arena_off(ctxs); }
+  } arena_guard{ctxs};
+  if (c->has_alloc) {
+    arena_record(ctxs);
+    cnn_forward_dev(m, g->in, w_in, count, g->out);
+    check_cuda(cudaStreamSynchronize(c->stream), "graph scratch pass");
+    arena_serve(ctxs, g->blocks);
+  }
   const u64 n0 = tcks_launch_count();
   check_cuda(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
   try {
@@ -672,6 +685,7 @@ tcks_status tcks_cnn_graph_create(const tcks_cnn* m, uint32_t count, tcks_cnn_gr
     throw;
   }
   check_cuda(cudaStreamEndCapture(c->stream, &g->graph), "end capture");
+  arena_off(ctxs);
   g->launches = tcks_launch_count() - n0;
   check_cuda(cudaGraphInstantiate(&g->exec, g->graph, 0), "graph instantiate");
   *out = g;

@@ -46,6 +46,7 @@ static void op_vecmat_dh(tcks_ctx* c, u64* ct, u64 cw, u32 count, u32 ell, const
   DevBuf partial(c, (size_t)count * chunks * 3 * (ell + 1) * n);
   VecmatDhPlan p{};
   p.keys = kt->d;
+  p.keys_aligned = kt->aligned16;
   p.digits = digits.p;
   p.digits_b = (u64)ell * (ell + 1) * n;
   p.ct = ct;
@@ -109,6 +110,7 @@ void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const st
   DevBuf partial(c, (size_t)count * chunks * 3 * (ell + 1) * n);
   VecmatDhPlan p{};
   p.keys = kt.d;
+  p.keys_aligned = kt.aligned16;
   p.digits = digits.p;
   p.digits_b = (u64)ell * (ell + 1) * n;
   p.ct = x;
@@ -152,6 +154,7 @@ void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, cons
   DevBuf partial(c, (size_t)count * outs * chunks * 3 * (ell + 1) * n);
   VecmatDhPlan p{};
   p.keys = kt.d;
+  p.keys_aligned = kt.aligned16;
   p.digits = digits.p;
   p.digits_b = (u64)ell * (ell + 1) * n;
   p.ct = x;

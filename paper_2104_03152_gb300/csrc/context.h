@@ -34,6 +34,7 @@ struct KeyTable {
   KsKey* d = nullptr;
   u32 n = 0;
   u32 min_K = 0;  // smallest key level in the table
+  bool aligned16 = false;  // every key starts on a 16-byte boundary
 };
 
 // A profiler range around one ABI call (or one stage of a served request group), visible in Nsight
@@ -90,6 +91,20 @@ struct tcks_ctx {
   // References: the caller's handle plus every object made from the context (ciphertexts,
   // plaintexts, matrices, models, graphs). The context is destroyed when the last one goes.
   std::atomic<int> refs{1};
+
+  // Graph capture with a caller allocator, whose callbacks cannot run inside a capture: an uncaptured
+  // pass counts the bytes the work allocates (mode RECORD), one block of that size comes from the
+  // allocator, and the captured pass takes its allocations from the block in order (mode SERVE; no
+  // region is reused, since forked streams would race on it). Blocks that graphs hold are never passed
+  // to the allocator's free by dev_free.
+  enum ArenaMode { ARENA_OFF = 0, ARENA_RECORD = 1, ARENA_SERVE = 2 };
+  struct CaptureArena {
+    ArenaMode mode = ARENA_OFF;
+    size_t recorded = 0;  // RECORD: bytes requested, each rounded up to 256
+    char* base = nullptr;  // SERVE: the block and how much of it is handed out
+    size_t used = 0, size = 0;
+  } arena;
+  std::vector<std::pair<char*, size_t>> graph_blocks;  // blocks held by live graphs
 
   // Galois keys changed: drop every cached key table.
   void keys_changed();
@@ -184,6 +199,16 @@ inline size_t pt_words(const tcks_ctx* c, u32 level) { return (size_t)level * c-
 
 tcks_ct* new_ct(tcks_ctx* c, u32 level, double scale);  // uninitialised limbs
 tcks_ct* new_ct_sized(tcks_ctx* c, u32 size, u32 level, double scale);  // [size][level][N], uninitialised
+// Capture arenas (see tcks_ctx::CaptureArena): arena_record before the uncaptured pass, arena_serve
+// after it (one block per context with a caller allocator, recorded in `held`), arena_off after the
+// capture; arena_release frees a graph's block when the graph goes.
+void arena_record(const std::vector<tcks_ctx*>& ctxs);
+void arena_serve(const std::vector<tcks_ctx*>& ctxs, std::vector<std::pair<tcks_ctx*, char*>>& held);
+void arena_off(const std::vector<tcks_ctx*>& ctxs);
+void arena_release(tcks_ctx* c, char* block);
+// Debug builds: synchronize each context's stream, read its error word and fail with
+// TCKS_ERR_DEBUG_CHECK (the word cleared) when a range check has set a bit.
+void debug_word_check(const std::vector<tcks_ctx*>& ctxs, const char* where);
 // Every operation but the element-wise ones, rescale, mod-switch, decrypt and export takes the
 // two-component form: a three-component product has to be relinearized first.
 void need_relinearized(const tcks_ct* ct);

@@ -19,6 +19,7 @@
 #include <thread>
 
 #include "context.h"
+#include "debug_checks.cuh"
 #include "limb_launch.cuh"
 #include "ntt.cuh"
 
@@ -93,6 +94,10 @@ __global__ void k_executor(DevTables T, ExecQueue* q, unsigned long long* head, 
         task.dst = (u64*)v->dst;
         task.mod = v->mod;
         task.inverse = v->inverse;
+        if (dbg_fail(T.dbg, task.mod < T.n_mods, DBG_MOD_INDEX) | dbg_fail(T.dbg, task.src && task.dst, DBG_NULL)) {
+          status.store(TCKS_ERR_DEBUG_CHECK, cuda::memory_order_relaxed);  // debug builds: stop on a bad task
+          stop = 1;
+        }
       }
     }
     __syncthreads();
@@ -226,7 +231,9 @@ tcks_status tcks_executor_post(tcks_executor* e, uint32_t op, const uint64_t* d_
   tcks_ctx* c = e->ctx;
   if (level < 1 || level > c->L + c->K) fail(TCKS_ERR_INVALID_ARG, "level out of range");
   const int st = host_load_int(&e->hq->status);
-  if (st) fail((tcks_status)st, "the executor has stopped: no task was published within its idle limit");
+  if (st)
+    fail((tcks_status)st, st == TCKS_ERR_TIMEOUT ? "the executor has stopped: no task was published within its idle limit"
+                                                 : "the executor has stopped on a task that failed a debug range check");
   if (e->hq->closed) fail(TCKS_ERR_INVALID_ARG, "the executor is closed");
   const unsigned long long count = (unsigned long long)polys * level;
   if (count > e->capacity) fail(TCKS_ERR_INVALID_ARG, "more tasks than the queue holds");

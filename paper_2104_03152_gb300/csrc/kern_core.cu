@@ -20,6 +20,7 @@
 #include "context.h"
 #include "kernels.h"
 #include "limb_launch.cuh"
+#include "debug_checks.cuh"
 #include "ntt.cuh"
 
 namespace tcks {
@@ -252,11 +253,14 @@ template <bool INVERSE, typename W>
 __global__ void k_ntt_slices_multi(const __grid_constant__ MultiNttTable tab) {
   TCKS_SMEM(W);
   const MultiNttDesc& d = tab.d[multi_desc_slice(tab, blockIdx.x)];
+  if (dbg_fail(tab.T[0].dbg, d.ctx < tab.n_ctx, DBG_CTX_INDEX)) return;
   const DevTables& T = tab.T[d.ctx];
   const u32 log_n = T.log_n, log_k = log_n - kSplitLogNs;
   const u64 local = blockIdx.x - d.first;
   const u64 limb = local >> log_k;
+  if (dbg_fail(T.dbg, limb < d.limbs && d.level > 0, DBG_LIMB_RANGE)) return;  // uniform over the CTA
   const u32 rank = (u32)(local & ((1u << log_k) - 1)), mod = (u32)(limb % d.level);
+  if (dbg_fail(T.dbg, mod < T.n_mods, DBG_MOD_INDEX) || dbg_fail(T.dbg, d.src && d.dst, DBG_NULL)) return;
   const ModConst m = T.mods[mod];
   const W q = (W)m.q;
   const u32 ns = 1u << kSplitLogNs;
@@ -324,8 +328,13 @@ __global__ void k_ntt_columns_multi(const __grid_constant__ MultiNttTable tab) {
   for (; it < tab.col_items; it += stride) {
     while (di + 1 < tab.n && tab.d[di + 1].col_first <= it) ++di;
     const MultiNttDesc& d = tab.d[di];
+    if (dbg_fail(tab.T[0].dbg, d.ctx < tab.n_ctx, DBG_CTX_INDEX)) continue;
     const DevTables& T = tab.T[d.ctx];
     const u64 local = it - d.col_first;
+    if (dbg_fail(T.dbg, (local >> kSplitLogNs) < d.limbs && d.level > 0, DBG_LIMB_RANGE) ||
+        dbg_fail(T.dbg, (u32)((local >> kSplitLogNs) % d.level) < T.n_mods, DBG_MOD_INDEX) ||
+        dbg_fail(T.dbg, d.src && d.dst, DBG_NULL))
+      continue;
     switch (T.log_n - kSplitLogNs) {
       case 1: multi_column<INVERSE, W, 1>(T, d, local); break;
       case 2: multi_column<INVERSE, W, 2>(T, d, local); break;
@@ -335,7 +344,7 @@ __global__ void k_ntt_columns_multi(const __grid_constant__ MultiNttTable tab) {
   }
 }
 
-u32 launch_ntt_multi(bool inverse, const MultiNttBatch* batches, u32 n, cudaStream_t st) {
+u32 launch_ntt_multi(bool inverse, const MultiNttBatch* batches, u32 n, cudaStream_t st, u32 understate) {
   if (!n || n > kMultiDescMax) return 0;
   MultiNttTable tab{};
   const bool narrow = batches[0].T->narrow != 0;
@@ -368,6 +377,20 @@ u32 launch_ntt_multi(bool inverse, const MultiNttBatch* batches, u32 n, cudaStre
     col_ops += limbs * 0.5 * nn * log_k;
   }
   if (!tab.slice_jobs || tab.slice_jobs > 0x7fffffffull) return 0;
+  if (kDebugChecks) {  // the table's invariants: offsets from 0, monotone, adding up to the launch
+    u64 slices = 0, cols = 0;
+    for (u32 i = 0; i < tab.n; ++i) {
+      const MultiNttDesc& d = tab.d[i];
+      const u32 log_k = tab.T[d.ctx].log_n - kSplitLogNs;
+      if (d.ctx >= tab.n_ctx || d.first != slices || d.col_first != cols || !d.level || d.limbs % d.level)
+        fail(TCKS_ERR_DEBUG_CHECK, "multi-context NTT table: descriptor " + std::to_string(i) + " out of order or range");
+      slices += (u64)d.limbs << log_k;
+      if (log_k) cols += (u64)d.limbs << kSplitLogNs;
+    }
+    if (slices != tab.slice_jobs || cols != tab.col_items)
+      fail(TCKS_ERR_DEBUG_CHECK, "multi-context NTT table: descriptors do not add up to the launch");
+    if (understate) tab.d[tab.n - 1].limbs -= std::min(understate, tab.d[tab.n - 1].limbs);
+  }
   const KernelId id = inverse ? K_NTT_INV : K_NTT_FWD;
   const size_t smem = (narrow ? 4 : 8) << kSplitLogNs;
   auto slices = [&]() {
@@ -424,7 +447,10 @@ __global__ void k_ntt_desc(DevTables T, const __grid_constant__ NttDescTable tab
   }
   const NttDesc& d = tab.d[lo];
   const u32 local = sl.job - d.first;
+  // the same for every CTA of the limb (cluster), so a skip reaches no barrier
+  if (dbg_fail(T.dbg, local < d.limbs && d.level > 0, DBG_LIMB_RANGE)) return;
   const u32 mod = local % d.level;
+  if (dbg_fail(T.dbg, mod < T.n_mods, DBG_MOD_INDEX) || dbg_fail(T.dbg, d.src && d.dst, DBG_NULL)) return;
   const ModConst m = T.mods[mod];
   const u64* in = d.src + ((u64)local << T.log_n) + sl.off;
   u64* out = d.dst + ((u64)local << T.log_n) + sl.off;

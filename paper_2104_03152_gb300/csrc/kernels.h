@@ -45,6 +45,8 @@ struct NttDesc {
   u64* dst;        // [polys][level][N] (may equal src)
   u32 first;       // index of the batch's first limb job in the launch
   u32 level;
+  u32 limbs;       // limb jobs of the batch (polys x level)
+  u32 pad;
 };
 constexpr u32 kNttDescMax = 96;
 struct NttDescTable {
@@ -78,7 +80,9 @@ struct MultiNttBatch {
 };
 // True when the batches fit one launch pair (at most kMultiCtxMax contexts and kMultiDescMax batches,
 // every N >= 2^13, one word type). Returns the number of launches made (0 when they do not fit).
-u32 launch_ntt_multi(bool inverse, const MultiNttBatch* batches, u32 n, cudaStream_t st);
+// understate (debug builds' self-test only, 0 otherwise): declare the last batch `understate` limbs
+// shorter than the grid covers, so that its range check has to skip them.
+u32 launch_ntt_multi(bool inverse, const MultiNttBatch* batches, u32 n, cudaStream_t st, u32 understate = 0);
 // Largest CTA size the limb kernels of each file accept (0 when the query fails).
 u32 limb_threads_cap_core(bool narrow, u32 log_c);
 u32 limb_threads_cap_sample(bool narrow, u32 log_c);
@@ -196,6 +200,8 @@ struct VecmatDhPlan {
   u64* partial;
   u32 R, B, chunk, chunks;
   u32 p_limb, outs;
+  u32 keys_aligned;  // every key of `keys` starts on a 16-byte boundary (bulk copies may read it)
+  u32 pad;
 };
 // Outputs per request of a plan (1 or 4).
 __host__ __device__ inline u32 dh_outs(const VecmatDhPlan& p) { return p.outs > 1 ? p.outs : 1; }

@@ -69,6 +69,11 @@ struct DevTables {
   u32 narrow;  // every prime < 2^31: kernels use 32-bit arithmetic
   u32 limb_threads;  // threads per CTA of the limb kernels (0 = the default for N), set by the autotuner
   u32 dh_rpt;        // requests per thread of the double-hoisted accumulation, 32-bit words (0 = default 2)
+  u32* dbg;          // error word of the debug build's device range checks (debug_checks.cuh)
+  u32* kerr;         // error word of bounded device waits that gave up and of refused bulk copies
+  u32 dh_form;       // double-hoisted accumulation: 0 = operands staged by bulk copies where possible,
+                     // 1 = per-thread loads only (set by the autotuner)
+  u32 pad3;
 };
 
 }  // namespace tcks

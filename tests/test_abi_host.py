@@ -3,6 +3,7 @@ its host-only logic (prime chain, argument checks, client-side im2col) agrees wi
 import os
 import re
 import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -96,3 +97,19 @@ def test_im2col_matches_oracle(built):
     assert np.array_equal(v, ref)
     with pytest.raises(tk.TcksError):
         tk.im2col_encode(img, 7, 7, 3, 1000)
+
+
+@pytest.mark.slow
+def test_debug_build_compiles_and_reports_itself(built):
+    """The debug build (TCKS_DEBUG_CHECKS: descriptor-table asserts, device range checks) compiles,
+    exports the same symbols, and reports itself; the default build does not."""
+    dbg = tkbuild.build(debug=True)
+    assert dbg != built
+    out = subprocess.run(["nm", "-D", "--defined-only", dbg], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(tcks_\w+)", out))
+    assert not [n for n in declared_functions() if n not in exported]
+    code = "import paper_2104_03152_gb300 as tk; print(int(tk.debug_checks()))"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT,
+                       env=dict(os.environ, TCKS_DEBUG_CHECKS="1"), check=True)
+    assert r.stdout.strip() == "1"
+    assert tk.debug_checks() is False

@@ -88,10 +88,13 @@ def _ks_specs(ctxs):
             (13, tk.JOB_ROTATE, 2, 32, 24), (15, tk.JOB_ROTATE, 1, 4, 25)]
 
 
-def _ks_batch(ctxs):
+def _ks_batch(ctxs, contexts=None):
+    """The relinearize / rotate batch of _ks_specs; `contexts` (N -> GPU context) replaces the fixture's
+    GPU contexts, with the same inputs."""
     jobs, bufs = [], []
     for log_n, op, count, level, seed in _ks_specs(ctxs):
         o, g = ctxs[log_n]
+        g = contexts[log_n] if contexts else g
         polys = 3 if op == tk.JOB_RELIN else 2
         x = np.stack([inputs.random_limbs(o.primes[:level], o.N, seed * 100 + i, polys=polys) for i in range(count)])
         d_in = _dev(x)
@@ -137,6 +140,34 @@ def test_batch_graph_replay_is_bit_identical(ctxs):
         assert tk.launch_count() - before == graph.launches
         for ref, (_, _, d_out) in zip(eager, bufs):
             assert np.array_equal(_host(d_out, ref.shape), ref)
+
+
+def test_batch_graph_with_caller_allocator(ctxs):
+    """Contexts whose memory comes from PyTorch's caching allocator (callbacks that cannot run inside a
+    capture): the graph takes its scratch from one block of that allocator, sized by an uncaptured
+    pass, and replays to the same bits as the fixture's pool-allocator contexts run eagerly."""
+    jobs, bufs = _ks_batch(ctxs)
+    tk.batch_run(jobs)
+    ctxs[13][1].synchronize()
+    eager = [_host(d_out, tuple(d_out.shape)).copy() for _, _, d_out in bufs]
+    mine = {}
+    for log_n, n_data in ((13, L_SMALL), (15, L_LARGE)):
+        primes = ctxs[log_n][0].primes
+        g = tk.Context(tk.Params(log_n, primes=primes, scale=2.0 ** 50), seed=SEED, flags=tk.TCKS_AUTO_RELIN,
+                       allocator="torch")
+        g.gen_galois_keys([1])
+        mine[log_n] = g
+    jobs, bufs = _ks_batch(ctxs, mine)
+    graph = tk.BatchGraph(jobs)
+    for _ in range(2):
+        for _, _, d_out in bufs:
+            d_out.zero_()
+        torch.cuda.synchronize()
+        graph.run()
+        mine[13].synchronize()
+        for ref, (_, _, d_out) in zip(eager, bufs):
+            assert np.array_equal(_host(d_out, ref.shape), ref)
+    del graph
 
 
 def test_batch_validation_launches_nothing(ctxs):

@@ -158,6 +158,23 @@ def test_cnn_graph_equals_single(setup):
             assert np.array_equal(b1.export(), s1)
 
 
+def test_cnn_graph_with_caller_allocator(setup):
+    """A model on a context whose memory comes from PyTorch's caching allocator captures to a graph
+    (its scratch one block of that allocator) that replays to the single forward's bits."""
+    o, w, enc, ctx, model, need = setup
+    tctx = tk.Context(tk.Params(13, BITS, 2.0 ** 26), seed=SEED, allocator="torch")
+    tm = tk.CNN(tctx, w.conv_w, w.conv_b, w.fc1_w, w.fc1_b, w.fc2_w, w.fc2_b, windows=64)
+    tm.gen_keys()
+    img = inputs.mnist_like_image(210)
+    v, W = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+    ct = tctx.encrypt_values(v, 610)
+    single = model.forward(ctx.encrypt_values(v, 610)).export()
+    g = tm.graph(1)
+    for _ in range(2):
+        assert np.array_equal(g.run([ct])[0].export(), single)
+    del g
+
+
 def test_cnn_double_hoisted_parity(setup):
     """With TCKS_DOUBLE_HOIST the two fully connected layers take the ModDown once after their
     rotation sums: bit-identical to the oracle's double-hoisted schedule, batched and graph-captured
