@@ -244,8 +244,13 @@ def run_gpu(args, world, rank, local):
         model.forward_device(d_in_ptr, B, d_out_ptr)
     _, tuned_ms = timed(torch, stream, lambda: model.forward_device(d_in_ptr, B, d_out_ptr), 3)
     tune = {"limb_threads": tuned[0], "accumulation_requests_per_thread": tuned[1],
+            "accumulation_form": "per-thread loads" if tuned[2] == 0 else
+            "operands staged in shared memory by bulk copies, %d elements per CTA x %d stages"
+            % {1: (256, 2), 2: (256, 3), 3: (128, 3), 4: (128, 4)}[tuned[2]],
             "hand_tuned_ms_per_step": hand_ms / 3, "autotuned_ms_per_step": tuned_ms / 3,
-            "searched": "limb-kernel CTA size {N/64, N/32, N/16 per slice} x accumulation requests per thread {1, 2}"}
+            "searched": "limb-kernel CTA size {N/64, N/32, N/16 per slice} x accumulation requests per thread "
+                        "{1, 2} x accumulation form {per-thread loads, staged by bulk copies: 256 x 2, "
+                        "256 x 3, 128 x 3, 128 x 4 elements per CTA x stages}"}
     ctx.synchronize()
     # plain path: one request per step
     plain_steps = max(3, min(args.steps, 10))

@@ -158,8 +158,19 @@ void tcks_ctx_free(tcks_ctx* ctx);
 tcks_status tcks_ctx_info(const tcks_ctx* ctx, uint32_t* log_n, uint32_t* n_data_primes, double* scale);
 /* Device bytes held by the context's keys and tables. */
 tcks_status tcks_ctx_key_bytes(const tcks_ctx* ctx, uint64_t* bytes);
-/* Wait for all work queued on the context's stream. */
+/* Wait for all work queued on the context's stream. A kernel whose bounded wait for its staged
+ * operands ran out (results invalid) is reported here, and by tcks_ct_export, as TCKS_ERR_TIMEOUT. */
 tcks_status tcks_ctx_synchronize(tcks_ctx* ctx);
+/* Launch shape of the context's kernels (results are bit-identical for every shape): limb_threads =
+ * threads per CTA of the limb kernels (0: the default for N; else a multiple of 32 the kernels
+ * accept), accum_rpt = requests per thread of the double-hoisted accumulation with 32-bit words (0:
+ * default 2; 1 or 2), accum_form = 0 (default): that accumulation loads its operands thread by
+ * thread; 1, 2, 3, 4: it stages each rotation's operands in shared memory with bulk copies where the
+ * layout allows (32-bit words, level <= 8, 16-byte aligned operands), with 256 x 2, 256 x 3, 128 x 3
+ * or 128 x 4 elements per CTA x stages. Set by the autotuners; get reads it back. */
+tcks_status tcks_ctx_set_launch_shape(tcks_ctx* ctx, uint32_t limb_threads, uint32_t accum_rpt, uint32_t accum_form);
+tcks_status tcks_ctx_get_launch_shape(const tcks_ctx* ctx, uint32_t* limb_threads, uint32_t* accum_rpt,
+                                      uint32_t* accum_form);
 /* Replace the context's flags (any of the TCKS_* flags above) for the calls
  * that follow; work already queued or captured in a graph keeps the flags it was issued with. */
 tcks_status tcks_ctx_set_flags(tcks_ctx* ctx, uint32_t flags);
@@ -409,14 +420,15 @@ tcks_status tcks_conv2d_im2col_pt(const tcks_ct* a, const tcks_pt* kernel, uint3
  * only the launch shape moves. *chosen_threads may be NULL. */
 tcks_status tcks_autotune(tcks_ctx* ctx, const char* cache_path, uint32_t* chosen_threads);
 /* Autotuner of the batched encrypted network (declared here, takes the model of tcks_cnn_create): times
- * a whole batched forward pass of `batch` requests for every pair of limb-kernel CTA size (N/64, N/32,
- * N/16 threads per slice) and double-hoisted accumulation shape (1 or 2 requests per thread, 32-bit
- * words), keeps the fastest on the model's context and, with a cache_path, records it under the GPU
- * name, log N, word size and batch (a later call reads it back). Results are bit-identical for every
- * shape. chosen_threads / chosen_rpt may be NULL. Synchronises. */
+ * a whole batched forward pass of `batch` requests for every combination of limb-kernel CTA size
+ * (N/64, N/32, N/16 threads per slice), double-hoisted accumulation requests per thread (1 or 2) and
+ * accumulation form (per-thread loads, or operands staged by bulk copies in one of four shapes; see
+ * tcks_ctx_set_launch_shape; the last two for 32-bit words), keeps the fastest on the model's context (tcks_ctx_set_launch_shape) and, with a cache_path,
+ * records it under the GPU name, log N, word size and batch (a later call reads it back). Results are
+ * bit-identical for every shape. The chosen_* pointers may be NULL. Synchronises. */
 typedef struct tcks_cnn tcks_cnn;
 tcks_status tcks_cnn_autotune(const tcks_cnn* m, uint32_t batch, const char* cache_path, uint32_t* chosen_threads,
-                              uint32_t* chosen_rpt);
+                              uint32_t* chosen_rpt, uint32_t* chosen_form);
 
 /* --------------------------------------------------- batched launches (descriptor table) ---- */
 /* A batch of independent jobs over raw device buffers, possibly of several contexts (different N)

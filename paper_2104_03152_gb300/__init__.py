@@ -144,9 +144,12 @@ _SIGS = {
     "tcks_conv2d_im2col": (ctypes.c_int32, [_vp, _dblp, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
     "tcks_conv2d_im2col_pt": (ctypes.c_int32, [_vp, _vp, ctypes.c_uint32, ctypes.c_uint32, _vpp]),
     "tcks_autotune": (ctypes.c_int32, [_vp, ctypes.c_char_p, _u32p]),
-    "tcks_cnn_autotune": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_char_p, _u32p, _u32p]),
+    "tcks_cnn_autotune": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_char_p, _u32p, _u32p, _u32p]),
     "tcks_launch_count": (ctypes.c_uint64, []),
     "tcks_debug_checks": (ctypes.c_int32, []),
+    "tcks_ctx_set_launch_shape": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]),
+    "tcks_ctx_get_launch_shape": (ctypes.c_int32, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32),
+                                                   ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)]),
     "tcks_debug_selftest": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32,
                                              ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)]),
     "tcks_profile_start": (ctypes.c_int32, []),
@@ -420,6 +423,16 @@ class Context:
 
     def synchronize(self):
         check(lib().tcks_ctx_synchronize(self.h))
+
+    def set_launch_shape(self, limb_threads: int = 0, accum_rpt: int = 0, accum_form: int = 0):
+        """Launch shape of the context's kernels (bit-identical results for every shape); accum_form 0 (the
+        default) loads the accumulation's operands thread by thread, 1..4 stage them with bulk copies."""
+        check(lib().tcks_ctx_set_launch_shape(self.h, limb_threads, accum_rpt, accum_form))
+
+    def launch_shape(self) -> tuple:
+        a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        check(lib().tcks_ctx_get_launch_shape(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
 
     def autotune(self, cache_path: str | None = None) -> int:
         t = ctypes.c_uint32()
@@ -862,13 +875,14 @@ class CNN:
         check(lib().tcks_cnn_forward_host(self.h, _p(host_in), host_in.shape[0], _p(host_out)))
         return host_out
 
-    def autotune(self, batch: int, cache_path: str | None = None) -> tuple[int, int]:
+    def autotune(self, batch: int, cache_path: str | None = None) -> tuple[int, int, int]:
         """Times the batched forward pass at `batch` requests over the launch shapes and keeps the fastest
-        (CTA size of the limb kernels, requests per thread of the accumulation); returns that pair."""
-        t, r = ctypes.c_uint32(), ctypes.c_uint32()
+        (CTA size of the limb kernels, requests per thread of the accumulation, its form: 0 per-thread
+        loads, 1..4 staged by bulk copies); returns that triple."""
+        t, r, f = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
         check(lib().tcks_cnn_autotune(self.h, batch, cache_path.encode() if cache_path else None, ctypes.byref(t),
-                                      ctypes.byref(r)))
-        return t.value, r.value
+                                      ctypes.byref(r), ctypes.byref(f)))
+        return t.value, r.value, f.value
 
     def wire_sizes(self) -> tuple[int, int, int]:
         """Bytes of one serialized input (both components), one seeded input, one serialized output."""

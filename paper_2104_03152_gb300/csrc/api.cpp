@@ -396,15 +396,25 @@ void arena_serve(const std::vector<tcks_ctx*>& ctxs, std::vector<std::pair<tcks_
 void debug_word_check(const std::vector<tcks_ctx*>& ctxs, const char* where) {
   for (tcks_ctx* c : ctxs) {
     u32 w = 0;
+    check_cuda(cudaMemcpyAsync(&w, c->T.dbg, sizeof(u32), cudaMemcpyDeviceToHost, c->stream), "debug word");
     check_cuda(cudaStreamSynchronize(c->stream), where);
-    check_cuda(cudaMemcpy(&w, c->T.dbg, sizeof(u32), cudaMemcpyDeviceToHost), "debug word");
     if (!w) continue;
-    check_cuda(cudaMemset(c->T.dbg, 0, sizeof(u32)), "debug word");
+    check_cuda(cudaMemsetAsync(c->T.dbg, 0, sizeof(u32), c->stream), "debug word");
     char bits[16];
     std::snprintf(bits, sizeof bits, "0x%x", w);
     fail(TCKS_ERR_DEBUG_CHECK, std::string(where) + ": a device range check failed (error bits " + bits +
                                    ": 1 context index, 2 limb range, 4 prime index, 8 null pointer)");
   }
+}
+
+void kernel_error_check(tcks_ctx* c) {
+  u32 w = 0;
+  check_cuda(cudaMemcpyAsync(&w, c->T.kerr, sizeof(u32), cudaMemcpyDeviceToHost, c->stream), "kernel error word");
+  check_cuda(cudaStreamSynchronize(c->stream), "kernel error word");
+  if (!w) return;
+  check_cuda(cudaMemsetAsync(c->T.kerr, 0, sizeof(u32), c->stream), "kernel error word");
+  if (w & 1u) fail(TCKS_ERR_TIMEOUT, "a kernel's bounded wait for its staged operands ran out; its results are invalid");
+  fail(TCKS_ERR_CUDA, "a kernel refused a bulk copy from a source off its 16-byte alignment; its results are invalid");
 }
 
 void arena_off(const std::vector<tcks_ctx*>& ctxs) {
@@ -714,6 +724,28 @@ tcks_status tcks_ctx_synchronize(tcks_ctx* c) {
   TCKS_API_BEGIN
   if (!c) fail(TCKS_ERR_INVALID_ARG, "null context");
   check_cuda(cudaStreamSynchronize(c->stream), "synchronize");
+  kernel_error_check(c);
+  TCKS_API_END
+}
+
+tcks_status tcks_ctx_set_launch_shape(tcks_ctx* c, uint32_t limb_threads, uint32_t accum_rpt, uint32_t accum_form) {
+  TCKS_API_BEGIN
+  if (!c) fail(TCKS_ERR_INVALID_ARG, "null context");
+  if (limb_threads && (limb_threads % 32 || limb_threads > 1024)) fail(TCKS_ERR_INVALID_ARG, "limb_threads: 0 or a multiple of 32 up to 1024");
+  if (accum_rpt > 2) fail(TCKS_ERR_INVALID_ARG, "accum_rpt: 0 (default), 1 or 2");
+  if (accum_form > 4) fail(TCKS_ERR_INVALID_ARG, "accum_form: 0 (per-thread loads) or 1..4 (staged where possible)");
+  c->T.limb_threads = limb_threads;
+  c->T.dh_rpt = accum_rpt;
+  c->T.dh_form = accum_form;
+  TCKS_API_END
+}
+
+tcks_status tcks_ctx_get_launch_shape(const tcks_ctx* c, uint32_t* limb_threads, uint32_t* accum_rpt, uint32_t* accum_form) {
+  TCKS_API_BEGIN
+  if (!c || !limb_threads || !accum_rpt || !accum_form) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  *limb_threads = c->T.limb_threads;
+  *accum_rpt = c->T.dh_rpt;
+  *accum_form = c->T.dh_form;
   TCKS_API_END
 }
 
@@ -1001,6 +1033,7 @@ tcks_status tcks_ct_export(const tcks_ct* ct, uint64_t* limbs, size_t n_words) {
     fail(TCKS_ERR_INVALID_ARG, "n_words does not match [size][level][N]");
   check_cuda(cudaMemcpyAsync(limbs, ct->d, n_words * 8, cudaMemcpyDeviceToHost, ct->ctx->stream), "ct export");
   check_cuda(cudaStreamSynchronize(ct->ctx->stream), "ct export");
+  kernel_error_check(ct->ctx);
   TCKS_API_END
 }
 

@@ -70,12 +70,14 @@ u32 cnn_input_level(const tcks_cnn* m);
 }  // namespace tcks
 
 // The batched network's launch shape: the limb kernels' CTA size (N/64, N/32, N/16 threads per slice)
-// times the double-hoisted accumulation's requests per thread (1 or 2, 32-bit words), each timed on a
-// whole batched forward pass of `batch` requests (the median of three after one warm-up); the fastest
-// pair is kept on the context and recorded under "<GPU>|cnn|<log N>|<word bits>|<batch>" (threads *
-// 10 + requests per thread). Results are bit-identical for every shape.
+// times the double-hoisted accumulation's requests per thread (1 or 2) times its form (0 per-thread
+// loads, or 1..4 operands staged by bulk copies with 256 x 2, 256 x 3, 128 x 3 or 128 x 4 elements per
+// CTA x stages; 32-bit words), each timed on a whole batched forward pass of
+// `batch` requests (the median of three after one warm-up); the fastest shape is kept on the context
+// and recorded under "<GPU>|cnn2|<log N>|<word bits>|<batch>" (threads * 100 + form * 10 + requests
+// per thread). Results are bit-identical for every shape.
 extern "C" tcks_status tcks_cnn_autotune(const tcks_cnn* m, uint32_t batch, const char* cache_path,
-                                         uint32_t* chosen_threads, uint32_t* chosen_rpt) {
+                                         uint32_t* chosen_threads, uint32_t* chosen_rpt, uint32_t* chosen_form) {
   try {
     tcks::NvtxRange nvtx(__func__);
     drop_stale_cuda_error();
@@ -84,7 +86,7 @@ extern "C" tcks_status tcks_cnn_autotune(const tcks_cnn* m, uint32_t batch, cons
     cudaDeviceProp prop;
     check_cuda(cudaGetDeviceProperties(&prop, c->device), "device properties");
     const u32 log_n = c->params.log_n, log_c = log_n > 14 ? log_n - 14 : 0, ns = 1u << (log_n - log_c);
-    const std::string key = std::string(prop.name) + "|cnn|" + std::to_string(log_n) + "|" +
+    const std::string key = std::string(prop.name) + "|cnn2|" + std::to_string(log_n) + "|" +
                             (c->T.narrow ? "32" : "64") + "|" + std::to_string(batch);
     std::map<std::string, u32> cache;
     if (cache_path && *cache_path) cache = read_cache(cache_path);
@@ -93,11 +95,13 @@ extern "C" tcks_status tcks_cnn_autotune(const tcks_cnn* m, uint32_t batch, cons
                   limb_threads_cap_fft(c->T.narrow, log_c)})
       cap = std::min(cap, t);
     cap &= ~31u;
-    u32 best_t = 0, best_r = 0;
+    u32 best_t = 0, best_r = 0, best_f = 0;
     auto it = cache.find(key);
-    if (it != cache.end() && it->second / 10 >= 32 && it->second / 10 <= cap && (it->second % 10 == 1 || it->second % 10 == 2)) {
-      best_t = it->second / 10;
-      best_r = it->second % 10;
+    const u32 cv = it != cache.end() ? it->second : 0;
+    if (cv / 100 >= 32 && cv / 100 <= cap && (cv / 10) % 10 <= 4 && cv % 10 <= 2) {
+      best_t = cv / 100;
+      best_f = (cv / 10) % 10;
+      best_r = cv % 10;
     } else {
       std::vector<u32> threads;
       for (u32 div : {64u, 32u, 16u}) {
@@ -105,18 +109,21 @@ extern "C" tcks_status tcks_cnn_autotune(const tcks_cnn* m, uint32_t batch, cons
         if (std::find(threads.begin(), threads.end(), t) == threads.end()) threads.push_back(t);
       }
       const std::vector<u32> rpts = c->T.narrow ? std::vector<u32>{2, 1} : std::vector<u32>{0};
+      const std::vector<u32> forms = c->T.narrow ? std::vector<u32>{0, 1, 2, 3, 4} : std::vector<u32>{0};
       const u32 L = cnn_input_level(m);
       const u64 win = ct_words(c, L), wout = ct_words(c, L - 6);
       DevBuf x(c, (size_t)batch * win), y(c, (size_t)batch * wout);
       check_cuda(cudaMemsetAsync(x.p, 0, (size_t)batch * win * 8, c->stream), "tune input");
       cudaEvent_t ev[4];
       for (cudaEvent_t& e : ev) check_cuda(cudaEventCreate(&e), "event");
-      const u32 saved_t = c->T.limb_threads, saved_r = c->T.dh_rpt;
+      const u32 saved_t = c->T.limb_threads, saved_r = c->T.dh_rpt, saved_f = c->T.dh_form;
       float best_ms = 1e30f;
       for (u32 t : threads)
-        for (u32 r : rpts) {
+        for (u32 r : rpts)
+          for (u32 f : forms) {
           c->T.limb_threads = t;
           c->T.dh_rpt = r;
+          c->T.dh_form = f;
           cnn_forward_dev(m, x.p, win, batch, y.p);  // warm-up
           float ms[3];
           for (int k = 0; k < 3; ++k) {
@@ -131,21 +138,25 @@ extern "C" tcks_status tcks_cnn_autotune(const tcks_cnn* m, uint32_t batch, cons
             best_ms = ms[1];
             best_t = t;
             best_r = r;
+            best_f = f;
           }
         }
       c->T.limb_threads = saved_t;
       c->T.dh_rpt = saved_r;
+      c->T.dh_form = saved_f;
       for (cudaEvent_t& e : ev) cudaEventDestroy(e);
       check_launch("cnn autotune");
       if (cache_path && *cache_path) {
-        cache[key] = best_t * 10 + best_r;
+        cache[key] = best_t * 100 + best_f * 10 + best_r;
         write_cache(cache_path, cache);
       }
     }
     c->T.limb_threads = best_t;
     c->T.dh_rpt = best_r;
+    c->T.dh_form = best_f;
     if (chosen_threads) *chosen_threads = best_t;
     if (chosen_rpt) *chosen_rpt = best_r;
+    if (chosen_form) *chosen_form = best_f;
   } catch (const tcks::Error& e) {
     return abi_record(e.code, e.msg);
   }

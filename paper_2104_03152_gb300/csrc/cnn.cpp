@@ -519,6 +519,7 @@ tcks_status tcks_cnn_forward_host(const tcks_cnn* m, const uint64_t* host_in, ui
   cnn_forward_dev(m, xin.p, w_in, count, yout.p);
   check_cuda(cudaMemcpyAsync(host_out, yout.p, (size_t)count * w_out * 8, cudaMemcpyDeviceToHost, c->stream), "D2H");
   check_cuda(cudaStreamSynchronize(c->stream), "forward");
+  kernel_error_check(c);
   CNN_END
 }
 
@@ -604,6 +605,7 @@ tcks_status tcks_cnn_forward_wire(const tcks_cnn* m, const uint8_t* host_in, uin
   }
   check_cuda(cudaMemcpyAsync(host_out, pb, (size_t)count * out_size, cudaMemcpyDeviceToHost, c->stream), "D2H");
   check_cuda(cudaStreamSynchronize(c->stream), "forward");
+  kernel_error_check(c);
   for (u32 r = 0; r < count; ++r) {
     uint8_t* h = host_out + (u64)r * out_size;
     std::memcpy(h, kWireMagic, 4);

@@ -209,6 +209,9 @@ void arena_release(tcks_ctx* c, char* block);
 // Debug builds: synchronize each context's stream, read its error word and fail with
 // TCKS_ERR_DEBUG_CHECK (the word cleared) when a range check has set a bit.
 void debug_word_check(const std::vector<tcks_ctx*>& ctxs, const char* where);
+// After the caller synchronized the context's stream: fail when a kernel recorded a bounded wait that
+// gave up (TCKS_ERR_TIMEOUT) or a refused bulk copy (TCKS_ERR_CUDA) in the kernel error word (cleared).
+void kernel_error_check(tcks_ctx* c);
 // Every operation but the element-wise ones, rescale, mod-switch, decrypt and export takes the
 // two-component form: a three-component product has to be relinearized first.
 void need_relinearized(const tcks_ct* ct);

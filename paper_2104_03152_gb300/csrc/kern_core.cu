@@ -34,10 +34,19 @@ void ensure_smem(const void* kernel, size_t bytes) {
   auto it = granted.find(kernel);
   if (it == granted.end()) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    it = granted.emplace(kernel, (size_t)48 * 1024).first;
+    // the default dynamic allowance is 48 KB less the kernel's static shared memory
+    cudaFuncAttributes fa{};
+    const size_t start = cudaFuncGetAttributes(&fa, kernel) == cudaSuccess ? (size_t)fa.maxDynamicSharedSizeBytes : 0;
+    cudaGetLastError();
+    it = granted.emplace(kernel, start).first;
   }
   if (bytes > it->second) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      fail(TCKS_ERR_CUDA, "raising a kernel's dynamic shared memory to " + std::to_string(bytes) +
+                              " bytes failed: " + cudaGetErrorString(e));
+    }
     it->second = bytes;
   }
 }
@@ -655,13 +664,17 @@ __global__ void k_drop_combine(DevTables T, const u64* __restrict__ in, u64 in_p
   const ModConst md = T.mods[drop_mod];
   const PairConst pc = T.pairs[(u64)drop_mod * T.n_mods + i];
   const u64* tp = top + (u64)p * n + sl.off;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced_w<W>(tp[k], md.half, pc.qa_mod_b, mi);
-  __syncthreads();
-  ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
+  if constexpr (LC == 0) {
+    ntt_fwd_limb_load<W>(s, T, i, [&](u32 k) { return lift_balanced_w<W>(tp[k], md.half, pc.qa_mod_b, mi); });
+  } else {
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced_w<W>(tp[k], md.half, pc.qa_mod_b, mi);
+    __syncthreads();
+    ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
+  }
   const u64* src = in + (u64)p * in_poly_stride + (u64)i * n + sl.off;
   u64* dst = out + ((u64)p * n_out + i) * n + sl.off;
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
-    const u64 c = sub_mod(src[k], Ar<W>::fwd_out(s[sw(k)], mi), mi.q);
+    const u64 c = sub_mod(src[k], fwd_fin(s[sw(k)], mi), mi.q);
     dst[k] = Ew<W>::shoup_inv(c, pc, mi);
   }
 }
@@ -700,11 +713,15 @@ __global__ void k_modup(DevTables T, const u64* __restrict__ x_ntt, u64 x_stride
   const u64 half_j = T.mods[j].half;
   const u64 qj_mod_t = T.pairs[(u64)j * T.n_mods + tmod].qa_mod_b;
   const u64* in = x_coef + (sl.y * ell + j) * n + sl.off;
+  if constexpr (LC == 0) {  // the lift feeds the first butterfly round directly
+    ntt_fwd_limb_load<W>(s, T, tmod, [&](u32 k) { return lift_balanced_w<W>(in[k], half_j, qj_mod_t, mt); });
+  } else {
 #pragma unroll 4
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced_w<W>(in[k], half_j, qj_mod_t, mt);
-  __syncthreads();
-  ntt_fwd_slice<W, LC>(s, T, tmod, sl.rank);
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) out[k] = (W)Ar<W>::fwd_out(s[sw(k)], mt);
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced_w<W>(in[k], half_j, qj_mod_t, mt);
+    __syncthreads();
+    ntt_fwd_slice<W, LC>(s, T, tmod, sl.rank);
+  }
+  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) out[k] = (W)fwd_fin(s[sw(k)], mt);
 }
 
 static decltype(&k_modup<u64, 0>) const K6_k_modup[6] = TCKS_K6(k_modup);
@@ -800,9 +817,13 @@ __global__ void k_ks_moddown(DevTables T, u32 ell, const __grid_constant__ KsPla
   const ModConst mp = T.mods[T.L];
   const PairConst pc = T.pairs[(u64)T.L * T.n_mods + i];
   const u64* top = plan.top + (yy * 2 + b) * n + sl.off;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced_w<W>(top[k], mp.half, pc.qa_mod_b, mi);
-  __syncthreads();
-  ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
+  if constexpr (LC == 0) {
+    ntt_fwd_limb_load<W>(s, T, i, [&](u32 k) { return lift_balanced_w<W>(top[k], mp.half, pc.qa_mod_b, mi); });
+  } else {
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced_w<W>(top[k], mp.half, pc.qa_mod_b, mi);
+    __syncthreads();
+    ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
+  }
   const u64* add = b == 0 ? (plan.add0 ? plan.add0 + rq * plan.add0_b : nullptr)
                           : (plan.add1 ? plan.add1 + rq * plan.add1_b : nullptr);
   u64* dst = plan.out + rq * plan.out_b + r * plan.out_r + ((u64)b * ell + i) * n;
@@ -811,7 +832,7 @@ __global__ void k_ks_moddown(DevTables T, u32 ell, const __grid_constant__ KsPla
       const u32 g = sl.off + k;
       const u32 src = kk.g == 1 ? g : galois_src(g, kk.g, log_n);
       const u64 u = ks_inner<W, decltype(E)::value>(digits, ell, i, kk.key, kk.K, i, b, g, src, n, mi);
-      u64 v = Ew<W>::shoup_inv(sub_mod(u, Ar<W>::fwd_out(s[sw(k)], mi), mi.q), pc, mi);
+      u64 v = Ew<W>::shoup_inv(sub_mod(u, fwd_fin(s[sw(k)], mi), mi.q), pc, mi);
       if (add) v = add_mod(v, add[(u64)i * n + (plan.add_perm ? src : g)], mi.q);
       dst[g] = v;
     }
@@ -867,9 +888,13 @@ __global__ void k_ks_moddown_rs(DevTables T, u32 ell, const __grid_constant__ Ks
   (void)mp;
   const u64* tp = plan.top + ((u64)rq * 2 + b) * n + sl.off;
   const u64* tl = top2 + ((u64)rq * 2 + b) * n + sl.off;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)crt2_lift<sizeof(W) == 4>(tp[k], tl[k], k2, ml, mi);
-  __syncthreads();
-  ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
+  if constexpr (LC == 0) {
+    ntt_fwd_limb_load<W>(s, T, i, [&](u32 k) { return crt2_lift<sizeof(W) == 4>(tp[k], tl[k], k2, ml, mi); });
+  } else {
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)crt2_lift<sizeof(W) == 4>(tp[k], tl[k], k2, ml, mi);
+    __syncthreads();
+    ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
+  }
   const u64* add = b == 0 ? plan.add0 + rq * plan.add0_b : plan.add1 + rq * plan.add1_b;
   u64* dst = plan.out + rq * plan.out_b + ((u64)b * lo + i) * n;
   ell_dispatch(ell, [&](auto E) {
@@ -877,7 +902,7 @@ __global__ void k_ks_moddown_rs(DevTables T, u32 ell, const __grid_constant__ Ks
       const u32 g = sl.off + k;
       const u64 u = ks_inner<W, decltype(E)::value>(digits, ell, i, kk.key, kk.K, i, b, g, g, n, mi);
       const u64 z = add_mod(u, Ew<W>::mul_pc(add[(u64)i * n + g], pp, mi), mi.q);
-      const u64 v = sub_mod(z, Ar<W>::fwd_out(s[sw(k)], mi), mi.q);
+      const u64 v = sub_mod(z, fwd_fin(s[sw(k)], mi), mi.q);
       dst[g] = Ew<W>::shoup_inv(Ew<W>::shoup_inv(v, pp, mi), pl, mi);
     }
   });

@@ -16,6 +16,7 @@
 #include "../../include/tcks.h"
 #include "context.h"
 #include "kernels.h"
+#include "dh_acc.cuh"
 #include "limb_launch.cuh"
 #include "ntt.cuh"
 
@@ -25,97 +26,6 @@ namespace {
 
 constexpr u32 kDhThreads = 256;
 
-// Lazy sum of products over the whole rotation loop: products of two residues are added without
-// reduction and the sum is reduced once at the end. 32-bit words: a 128-bit sum of four 32-bit words
-// fed through the carry flag; it also takes a key-switch sum unreduced (below 2^66) times a diagonal
-// value, so the rotation loop has no reduction at all. 64-bit words: products < 2^122 in a 128-bit
-// sum with a count of 2^128 carries.
-template <typename W>
-struct DhAcc;
-template <>
-struct DhAcc<u32> {
-  u32 w0 = 0, w1 = 0, w2 = 0, w3 = 0;
-  // += x y, x, y < 2^32 (below 2^34 such products the sum stays below 2^96: no carry into w3)
-  __device__ __forceinline__ void mac(u64 x, u64 y) {
-    asm("mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
-        "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
-        "addc.u32 %2, %2, 0;"
-        : "+r"(w0), "+r"(w1), "+r"(w2)
-        : "r"((u32)x), "r"((u32)y));
-  }
-  __device__ __forceinline__ void add(u64 x) {
-    asm("add.cc.u32 %0, %0, %2;\n\t"
-        "addc.u32 %1, %1, 0;"
-        : "+r"(w0), "+r"(w1)
-        : "r"((u32)x));
-  }
-  // += (s + c 2^64) d, d < 2^32; kCarry = false: c is known to be 0
-  template <bool kCarry>
-  __device__ __forceinline__ void mac_wide(u64 s, u32 c, u64 d) {
-    const u32 sl = (u32)s, sh = (u32)(s >> 32), dv = (u32)d;
-    asm("mad.lo.cc.u32 %1, %5, %6, %1;\n\t"
-        "madc.hi.cc.u32 %2, %5, %6, %2;\n\t"
-        "addc.u32 %3, %3, 0;\n\t"
-        "mad.lo.cc.u32 %0, %4, %6, %0;\n\t"
-        "madc.hi.cc.u32 %1, %4, %6, %1;\n\t"
-        "addc.cc.u32 %2, %2, 0;\n\t"
-        "addc.u32 %3, %3, 0;"
-        : "+r"(w0), "+r"(w1), "+r"(w2), "+r"(w3)
-        : "r"(sl), "r"(sh), "r"(dv));
-    if (kCarry)
-      asm("mad.lo.cc.u32 %0, %2, %3, %0;\n\t"
-          "madc.hi.u32 %1, %2, %3, %1;"
-          : "+r"(w2), "+r"(w3)
-          : "r"(c), "r"(dv));
-  }
-  // += s + c 2^64
-  __device__ __forceinline__ void add_wide(u64 s, u32 c) {
-    asm("add.cc.u32 %0, %0, %4;\n\t"
-        "addc.cc.u32 %1, %1, %5;\n\t"
-        "addc.cc.u32 %2, %2, %6;\n\t"
-        "addc.u32 %3, %3, 0;"
-        : "+r"(w0), "+r"(w1), "+r"(w2), "+r"(w3)
-        : "r"((u32)s), "r"((u32)(s >> 32)), "r"(c));
-  }
-  // Horner over the words: every step reduces a value below 2^64
-  __device__ __forceinline__ u64 get(const ModConst& m) const {
-    u64 r = reduce64(((u64)w3 << 32) | w2, m);
-    r = reduce64((r << 32) | w1, m);
-    return reduce64((r << 32) | w0, m);
-  }
-};
-template <>
-struct DhAcc<u64> {
-  u64 lo = 0, hi = 0;
-  u32 top = 0;
-  __device__ __forceinline__ void add(u64 x) {
-    const u64 l = lo + x;
-    const u64 h = hi + (l < x);
-    top += h < hi;
-    lo = l;
-    hi = h;
-  }
-  __device__ __forceinline__ void mac(u64 x, u64 y) {
-    const u64 plo = x * y, phi = __umul64hi(x, y);
-    const u64 l = lo + plo;
-    const u64 h1 = hi + phi;
-    top += h1 < phi;
-    const u64 h2 = h1 + (l < plo);
-    top += h2 < h1;
-    lo = l;
-    hi = h2;
-  }
-  __device__ __forceinline__ u64 get(const ModConst& m) const {
-    u64 r = reduce128(hi, lo, m);
-    if (top) r = add_mod(r, mul_mod(mul_mod(m.r64, m.r64, m), top, m), m.q);  // top * 2^128 mod q
-    return r;
-  }
-};
-
-// partial layout: [B][chunks][3][ell+1][N] with component 2 = A_0 (slot ell unused)
-__device__ __forceinline__ u64 dh_off(u32 rq, u32 chunk, u32 chunks, u32 comp, u32 slot, u32 ell, u32 log_n) {
-  return ((((u64)rq * chunks + chunk) * 3 + comp) * (ell + 1) + slot) << log_n;
-}
 
 // Thread = EPT elements (stride kDhThreads) x RPT requests of one slot i: the key limbs, the
 // diagonal and the Galois index of a rotation are loaded once for the RPT requests.
@@ -332,9 +242,13 @@ __global__ void k_vecmat_dh_moddown(DevTables T, u32 ell, const __grid_constant_
   const ModConst mp = T.mods[T.L];
   const PairConst pc = T.pairs[(u64)T.L * T.n_mods + i];
   const u64* t = top + ((u64)b * bo + ro) * n + sl.off;
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced_w<W>(t[k], mp.half, pc.qa_mod_b, mi);
-  __syncthreads();
-  ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
+  if constexpr (LC == 0) {  // the lift feeds the first butterfly round directly
+    ntt_fwd_limb_load<W>(s, T, i, [&](u32 k) { return lift_balanced_w<W>(t[k], mp.half, pc.qa_mod_b, mi); });
+  } else {
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced_w<W>(t[k], mp.half, pc.qa_mod_b, mi);
+    __syncthreads();
+    ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
+  }
   const u64* U = p.partial + dh_off(ro, 0, p.chunks, b, i, ell, log_n);
   const u64* A = p.partial + dh_off(ro, 0, p.chunks, 2, i, ell, log_n);
   const u64* cb = p.ct + rq * p.ct_b + ((u64)b * ell + i) * n;
@@ -342,7 +256,7 @@ __global__ void k_vecmat_dh_moddown(DevTables T, u32 ell, const __grid_constant_
   u64* dst = out + (out_o ? rq * out_b + o * out_o : ro * out_b) + ((u64)b * ell + i) * n;
   for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
     const u32 g = sl.off + k;
-    u64 v = Ew<W>::shoup_inv(sub_mod(U[g], Ar<W>::fwd_out(s[sw(k)], mi), mi.q), pc, mi);
+    u64 v = Ew<W>::shoup_inv(sub_mod(U[g], fwd_fin(s[sw(k)], mi), mi.q), pc, mi);
     v = add_mod(v, d0 ? Ew<W>::mul(cb[g], d0[g], mi) : cb[g], mi.q);
     if (b == 0) v = add_mod(v, A[g], mi.q);
     dst[g] = v;
@@ -401,10 +315,14 @@ __global__ void k_vecmat_dh_moddown_rs(DevTables T, u32 ell, const __grid_consta
   const PairConst pl = T.pairs[(u64)lo * T.n_mods + i];   // q_l^-1 mod q_i
   const u64* tp = top + ((u64)b * bo + ro) * n + sl.off;
   const u64* tl = top2 + ((u64)b * bo + ro) * n + sl.off;
+  if constexpr (LC == 0) {
+    ntt_fwd_limb_load<W>(s, T, i, [&](u32 k) { return crt2_lift<sizeof(W) == 4>(tp[k], tl[k], k2, ml, mi); });
+  } else {
 #pragma unroll 4
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)crt2_lift<sizeof(W) == 4>(tp[k], tl[k], k2, ml, mi);
-  __syncthreads();
-  ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = (W)crt2_lift<sizeof(W) == 4>(tp[k], tl[k], k2, ml, mi);
+    __syncthreads();
+    ntt_fwd_slice<W, LC>(s, T, i, sl.rank);
+  }
   const u64* U = p.partial + dh_off(ro, 0, p.chunks, b, i, ell, log_n);
   const u64* A = p.partial + dh_off(ro, 0, p.chunks, 2, i, ell, log_n);
   const u64* cb = p.ct + rq * p.ct_b + ((u64)b * ell + i) * n;
@@ -432,7 +350,7 @@ __global__ void k_vecmat_dh_moddown_rs(DevTables T, u32 ell, const __grid_consta
         u64 a = d0 ? Ew<W>::mul(cv[t], dv[t], mi) : cv[t];
         if (b == 0) a = add_mod(a, av[t], mi.q);
         const u64 z = add_mod(uv[t], Ew<W>::mul_pc(a, pp, mi), mi.q);
-        const u64 v = sub_mod(z, Ar<W>::fwd_out(s[sw(k)], mi), mi.q);
+        const u64 v = sub_mod(z, fwd_fin(s[sw(k)], mi), mi.q);
         dst[sl.off + k] = Ew<W>::shoup_inv(Ew<W>::shoup_inv(v, pp, mi), pl, mi);
       }
     }
@@ -487,9 +405,15 @@ void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cu
   // product-accumulates per (request, rotation, element): the key-switch sums 2 ell (ell + 1), then per
   // output the two components' and the c0 term's diagonal products (additions for unit diagonals)
   const double ops = (double)p.B * p.R * n * (2.0 * ell * (ell + 1.0) + outs * (2.0 * (ell + 1.0) + ell));
+  const bool bulk = dh_bulk_applies(T, ell, p);
+  // profiler tag: level, outputs, unit diagonals (bit 16), staged operands (bit 17)
   Launch L(K_VECMAT_DH, st, by + 8.0 * n * (outs - 1.0) * (p.R * (ell + 1.0) + p.B * p.chunks * (3.0 * ell + 2.0)), ops,
-           ell | (outs << 8) | ((p.diag ? 0u : 1u) << 16));
+           ell | (outs << 8) | ((p.diag ? 0u : 1u) << 16) | ((bulk ? 1u : 0u) << 17));
   const dim3 grid(vecmat_dh_base_ctas(T.log_n, ell, p.B, T.narrow, outs, T.dh_rpt), p.chunks);
+  if (bulk) {
+    launch_vecmat_dh_acc_bulk(T, ell, p, dh_rpt_of(true, outs, T.dh_rpt), st);
+    return;
+  }
   if (outs == 4) {
     if (T.narrow)
       dh_acc_launch<u32, 1, 1, 4>(grid, st, T, ell, p);

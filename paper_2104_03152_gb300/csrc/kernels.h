@@ -208,6 +208,12 @@ __host__ __device__ inline u32 dh_outs(const VecmatDhPlan& p) { return p.outs > 
 // CTAs of one chunk of k_vecmat_dh_acc (element blocks x slots x requests).
 u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow, u32 outs = 1, u32 rpt = 0);
 void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st);
+// The same accumulation with each rotation's operands staged in shared memory by bulk copies
+// (kern_dh_bulk.cu): whether it applies to a plan (T.dh_form 1..4, 32-bit words, level 1..8, 16-byte
+// aligned operands), and its launch (rpt requests per thread; the elements per CTA and stages of
+// T.dh_form: 1 = 256 x 2, 2 = 256 x 3, 3 = 128 x 3, 4 = 128 x 4).
+bool dh_bulk_applies(const DevTables& T, u32 ell, const VecmatDhPlan& p);
+void launch_vecmat_dh_acc_bulk(const DevTables& T, u32 ell, const VecmatDhPlan& p, u32 rpt, cudaStream_t st);
 void launch_vecmat_dh_fold(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st);
 // top [2][B * outs][N] = INTT_P of the folded U_b[P]; out + (rq * outs + o) * out_b receives output o
 // of request rq, [2][ell][N] (before the rescale).

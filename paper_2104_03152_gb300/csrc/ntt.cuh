@@ -348,6 +348,66 @@ __device__ __forceinline__ void ntt_inv_slice(W* s, const DevTables& T, u32 mod,
   if constexpr (LC > 0) cross_stages<W, LC, false>(s, log_n, log_ns, rank, tw, tws, q);
 }
 
+// ---------------------------------------- forward transform fed by its producer, relaxed output ----
+// fwd_round at stage 0 of a whole limb with the groups' inputs taken from load(index) instead of the
+// shared slice: the first round of a transform whose input is computed on the fly (a lift from
+// another prime), which saves the staging pass through shared memory and its barrier.
+template <typename W, int LR, typename A, typename F>
+__device__ __forceinline__ void fwd_round_load(W* s, u32 log_n, const W* tw, const W* tws, W q, F&& load) {
+  constexpr int R = 1 << LR;
+  const u32 tr = 1u << (log_n - LR);  // the first stage's distance is N / 2; N / R groups
+  for (u32 g = threadIdx.x; g < tr; g += blockDim.x) {
+    W x[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = (W)load(g + k * tr);
+    fwd_group<W, LR, A>(x, 0, 0, tw, tws, q);
+#pragma unroll
+    for (int k = 0; k < R; ++k) s[sw(g + k * tr)] = x[k];
+  }
+  __syncthreads();
+}
+
+// Forward transform of a whole limb (one CTA) whose input element k is load(k) (canonical), the first
+// round reading it directly. The butterflies and their order are ntt_fwd_slice's; the output is left
+// as its rounds leave it (64-bit words: [0, 4q); 32-bit words: below 2^32, without the final
+// canonicalisation pass), and fwd_fin gives the canonical value. Ends with a barrier.
+template <typename W, typename F>
+__device__ __forceinline__ void ntt_fwd_limb_load(W* s, const DevTables& T, u32 mod, F&& load) {
+  constexpr int RB = RadixBits<W>::value;
+  static_assert(RB == 3, "the first round below covers remainders of radix-8 rounds");
+  const u32 log_n = T.log_n;
+  const W q = (W)T.mods[mod].q;
+  const W* tw = Ar<W>::tw(T, mod, 0);
+  const W* tws = Ar<W>::tw(T, mod, 1);
+  auto run = [&](auto policy) {
+    using A = decltype(policy);
+    const u32 first = log_n % RB ? log_n % RB : RB;
+    if (first == 1)
+      fwd_round_load<W, 1, A>(s, log_n, tw, tws, q, load);
+    else if (first == 2)
+      fwd_round_load<W, 2, A>(s, log_n, tw, tws, q, load);
+    else
+      fwd_round_load<W, 3, A>(s, log_n, tw, tws, q, load);
+    for (u32 st = first; st < log_n; st += RB) fwd_round<W, RB, A>(s, log_n, log_n, 0, st, tw, tws, q);
+  };
+  if constexpr (sizeof(W) == 4) {
+    if ((u64)q * (2 * log_n + 4) < (1ull << 32)) {
+      run(Ar32Grow{});
+      return;
+    }
+    if (q < (1u << 30)) {
+      run(Ar32Lazy{});
+      return;
+    }
+  }
+  run(Ar<W>{});
+}
+
+// The canonical value of a forward output left relaxed by ntt_fwd_limb_load (or a canonical one): a
+// 32-bit Barrett reduction is exact for any word below 2^32 when q < 2^31.
+__device__ __forceinline__ u64 fwd_fin(u32 x, const ModConst& m) { return reduce32(x, m); }
+__device__ __forceinline__ u64 fwd_fin(u64 x, const ModConst& m) { return Ar<u64>::fwd_out(x, m); }
+
 // ------------------------------------------------------------ word-typed element arithmetic ----
 // Helpers for the kernels' prologues and epilogues: a W-typed multiply, Shoup multiply by a pair
 // constant, and the key-switch inner product.

@@ -71,8 +71,9 @@ struct DevTables {
   u32 dh_rpt;        // requests per thread of the double-hoisted accumulation, 32-bit words (0 = default 2)
   u32* dbg;          // error word of the debug build's device range checks (debug_checks.cuh)
   u32* kerr;         // error word of bounded device waits that gave up and of refused bulk copies
-  u32 dh_form;       // double-hoisted accumulation: 0 = operands staged by bulk copies where possible,
-                     // 1 = per-thread loads only (set by the autotuner)
+  u32 dh_form;       // double-hoisted accumulation: 0 = per-thread loads; 1, 2, 3, 4 = operands staged
+                     // by bulk copies where possible, with 256 x 2, 256 x 3, 128 x 3, 128 x 4 elements
+                     // per CTA x stages (set by the autotuner)
   u32 pad3;
 };
 

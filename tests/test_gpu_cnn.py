@@ -158,6 +158,44 @@ def test_cnn_graph_equals_single(setup):
             assert np.array_equal(b1.export(), s1)
 
 
+def test_cnn_accumulation_forms_identical(setup):
+    """The double-hoisted accumulation with its operands staged in shared memory by bulk copies (every
+    staged shape: 256 or 128 elements per CTA, 2 to 4 stages) and with per-thread loads, at one and two
+    requests per thread, give the same bits on the bench's layout; the profiler's tags show which form
+    ran."""
+    o, w, enc, ctx, model, need = setup
+    base = ctx.flags
+    shape = ctx.launch_shape()
+    try:
+        ctx.set_flags(base | tk.TCKS_RECT_DIAG | tk.TCKS_DOUBLE_HOIST | tk.TCKS_CONV_SHARED | tk.TCKS_CONV_PACK |
+                      tk.TCKS_MERGED_RESCALE)
+        m = tk.CNN(ctx, w.conv_w, w.conv_b, w.fc1_w, w.fc1_b, w.fc2_w, w.fc2_b, windows=64)
+        m.gen_keys()
+        cts = []
+        for seed in range(5):
+            img = inputs.mnist_like_image(300 + seed)
+            v, W = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+            cts.append(ctx.encrypt_values(v, 700 + seed))
+        results = {}
+        for form in (0, 1, 2, 3, 4):
+            for rpt in (1, 2):
+                ctx.set_launch_shape(0, rpt, form)
+                tk.profile_start()
+                outs = m.forward_batch(cts)
+                ctx.synchronize()
+                tk.profile_stop()
+                staged = {(tag >> 17) & 1 for tag, _, _ in tk.profile_records("vecmat_dh_acc")}
+                assert staged == {0 if form == 0 else 1}, (form, rpt, staged)
+                results[(form, rpt)] = [c.export() for c in outs]
+        ref = results[(0, 2)]
+        for key, got in results.items():
+            for a, b in zip(got, ref):
+                assert np.array_equal(a, b), key
+    finally:
+        ctx.set_launch_shape(*shape)
+        ctx.set_flags(base)
+
+
 def test_cnn_graph_with_caller_allocator(setup):
     """A model on a context whose memory comes from PyTorch's caching allocator captures to a graph
     (its scratch one block of that allocator) that replays to the single forward's bits."""
@@ -395,12 +433,15 @@ def test_cnn_autotune_is_bit_identical(setup, tmp_path):
             cts.append(ctx.encrypt_values(v, 800 + seed))
         before = [x.export() for x in model.forward_batch(cts)]
         cache = str(tmp_path / "tune.json")
-        t, r = model.autotune(3, cache)
-        assert t in (128, 256, 512) and r in (1, 2)
+        shape = ctx.launch_shape()
+        t, r, f = model.autotune(3, cache)
+        assert t in (128, 256, 512) and r in (1, 2) and f in (0, 1, 2, 3, 4)
+        assert ctx.launch_shape() == (t, r, f)
         after = [x.export() for x in model.forward_batch(cts)]
         for a, b in zip(before, after):
             assert np.array_equal(a, b)
-        assert model.autotune(3, cache) == (t, r)
-        assert "|cnn|13|32|3" in open(cache).read()
+        assert model.autotune(3, cache) == (t, r, f)
+        assert "|cnn2|13|32|3" in open(cache).read()
     finally:
+        ctx.set_launch_shape(*shape)
         ctx.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE)
