@@ -177,6 +177,7 @@ const KeyTable& key_table(tcks_ctx* c, const std::vector<u32>& steps, u32 ell) {
     KeyTable t;
     t.n = (u32)h.size();
     t.min_K = min_K;
+    for (const KsKey& k : h) t.max_K = k.K > t.max_K ? k.K : t.max_K;
     t.aligned16 = true;
     for (const KsKey& k : h) t.aligned16 = t.aligned16 && ((uintptr_t)k.key & 15) == 0;
     t.d = (KsKey*)c->dev_alloc(sizeof(KsKey) * h.size());

@@ -34,6 +34,7 @@ struct KeyTable {
   KsKey* d = nullptr;
   u32 n = 0;
   u32 min_K = 0;  // smallest key level in the table
+  u32 max_K = 0;  // largest key level in the table
   bool aligned16 = false;  // every key starts on a 16-byte boundary
 };
 

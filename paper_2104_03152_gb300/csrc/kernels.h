@@ -201,7 +201,7 @@ struct VecmatDhPlan {
   u32 R, B, chunk, chunks;
   u32 p_limb, outs;
   u32 keys_aligned;  // every key of `keys` starts on a 16-byte boundary (bulk copies may read it)
-  u32 pad;
+  u32 keys_K;        // the level of every key of `keys` when they share one, else 0
 };
 // Outputs per request of a plan (1 or 4).
 __host__ __device__ inline u32 dh_outs(const VecmatDhPlan& p) { return p.outs > 1 ? p.outs : 1; }
