@@ -284,6 +284,7 @@ __device__ __forceinline__ void ntt_fwd_local_rounds(W* s, u32 log_n, u32 log_ns
   if constexpr (RB > 3)
     if (rem == 3) fwd_round<W, 3, A>(s, log_n, log_ns, rank, st, tw, tws, q);
   st += rem;
+#pragma unroll
   for (; st < log_n; st += RB) fwd_round<W, RB, A>(s, log_n, log_ns, rank, st, tw, tws, q);
 }
 template <typename W, typename A = Ar<W>>
@@ -291,6 +292,7 @@ __device__ __forceinline__ void ntt_inv_local_rounds(W* s, u32 log_n, u32 log_ns
                                                      W q) {
   constexpr int RB = RadixBits<W>::value;
   u32 st = 0;
+#pragma unroll
   for (; st + RB <= log_ns; st += RB) inv_round<W, RB, A>(s, log_n, log_ns, rank, st, tw, tws, q);
   if constexpr (RB > 3)
     if (log_ns - st == 3) inv_round<W, 3, A>(s, log_n, log_ns, rank, st, tw, tws, q);
@@ -301,9 +303,9 @@ __device__ __forceinline__ void ntt_inv_local_rounds(W* s, u32 log_n, u32 log_ns
 // Forward transform of the CTA's slice s[0, N/C) of a limb split over C = 2^LC CTAs (LC = 0: the
 // whole limb). Input canonical (or in [0, 4q) for W = u64); output in [0, 4q) (u64) or canonical
 // (u32); Ar<W>::fwd_out gives the canonical value. Ends with a barrier.
-template <typename W, int LC>
-__device__ __forceinline__ void ntt_fwd_slice(W* s, const DevTables& T, u32 mod, u32 rank) {
-  const u32 log_n = T.log_n, log_ns = log_n - LC;
+template <typename W, int LC, int LOGN>
+__device__ __forceinline__ void ntt_fwd_slice_n(W* s, const DevTables& T, u32 mod, u32 rank) {
+  const u32 log_n = LOGN > 0 ? (u32)LOGN : T.log_n, log_ns = log_n - LC;
   const W q = (W)T.mods[mod].q;
   const W* tw = Ar<W>::tw(T, mod, 0);
   const W* tws = Ar<W>::tw(T, mod, 1);
@@ -327,13 +329,23 @@ __device__ __forceinline__ void ntt_fwd_slice(W* s, const DevTables& T, u32 mod,
   if constexpr (LC > 0) cross_stages<W, LC, true>(s, log_n, log_ns, rank, tw, tws, q);
   ntt_fwd_local_rounds<W>(s, log_n, log_ns, rank, tw, tws, q);
 }
+template <typename W, int LC>
+__device__ __forceinline__ void ntt_fwd_slice(W* s, const DevTables& T, u32 mod, u32 rank) {
+  if constexpr (LC == 0) {
+    if (T.log_n == 13) {  // the encrypted network's ring: the size fixed at compile time
+      ntt_fwd_slice_n<W, 0, 13>(s, T, mod, rank);
+      return;
+    }
+  }
+  ntt_fwd_slice_n<W, LC, 0>(s, T, mod, rank);
+}
 
 // Inverse transform (without N^-1) of the CTA's slice; input canonical, output in [0, 2q) (u64, and
 // u32 primes below 2^30) or canonical (other u32 primes); Ar<W>::inv_out applies N^-1 and gives the
 // canonical value.
-template <typename W, int LC>
-__device__ __forceinline__ void ntt_inv_slice(W* s, const DevTables& T, u32 mod, u32 rank) {
-  const u32 log_n = T.log_n, log_ns = log_n - LC;
+template <typename W, int LC, int LOGN>
+__device__ __forceinline__ void ntt_inv_slice_n(W* s, const DevTables& T, u32 mod, u32 rank) {
+  const u32 log_n = LOGN > 0 ? (u32)LOGN : T.log_n, log_ns = log_n - LC;
   const W q = (W)T.mods[mod].q;
   const W* tw = Ar<W>::tw(T, mod, 2);
   const W* tws = Ar<W>::tw(T, mod, 3);
@@ -346,6 +358,16 @@ __device__ __forceinline__ void ntt_inv_slice(W* s, const DevTables& T, u32 mod,
   }
   ntt_inv_local_rounds<W>(s, log_n, log_ns, rank, tw, tws, q);
   if constexpr (LC > 0) cross_stages<W, LC, false>(s, log_n, log_ns, rank, tw, tws, q);
+}
+template <typename W, int LC>
+__device__ __forceinline__ void ntt_inv_slice(W* s, const DevTables& T, u32 mod, u32 rank) {
+  if constexpr (LC == 0) {
+    if (T.log_n == 13) {
+      ntt_inv_slice_n<W, 0, 13>(s, T, mod, rank);
+      return;
+    }
+  }
+  ntt_inv_slice_n<W, LC, 0>(s, T, mod, rank);
 }
 
 // ---------------------------------------- forward transform fed by its producer, relaxed output ----
@@ -371,11 +393,13 @@ __device__ __forceinline__ void fwd_round_load(W* s, u32 log_n, const W* tw, con
 // round reading it directly. The butterflies and their order are ntt_fwd_slice's; the output is left
 // as its rounds leave it (64-bit words: [0, 4q); 32-bit words: below 2^32, without the final
 // canonicalisation pass), and fwd_fin gives the canonical value. Ends with a barrier.
-template <typename W, typename F>
-__device__ __forceinline__ void ntt_fwd_limb_load(W* s, const DevTables& T, u32 mod, F&& load) {
+// LOGN > 0 fixes the ring size at compile time: the rounds unroll and their strides, swizzled offsets
+// and twiddle indices fold into constants.
+template <typename W, int LOGN, typename F>
+__device__ __forceinline__ void ntt_fwd_limb_load_n(W* s, const DevTables& T, u32 mod, F&& load) {
   constexpr int RB = RadixBits<W>::value;
   static_assert(RB == 3, "the first round below covers remainders of radix-8 rounds");
-  const u32 log_n = T.log_n;
+  const u32 log_n = LOGN > 0 ? (u32)LOGN : T.log_n;
   const W q = (W)T.mods[mod].q;
   const W* tw = Ar<W>::tw(T, mod, 0);
   const W* tws = Ar<W>::tw(T, mod, 1);
@@ -388,6 +412,7 @@ __device__ __forceinline__ void ntt_fwd_limb_load(W* s, const DevTables& T, u32 
       fwd_round_load<W, 2, A>(s, log_n, tw, tws, q, load);
     else
       fwd_round_load<W, 3, A>(s, log_n, tw, tws, q, load);
+#pragma unroll
     for (u32 st = first; st < log_n; st += RB) fwd_round<W, RB, A>(s, log_n, log_n, 0, st, tw, tws, q);
   };
   if constexpr (sizeof(W) == 4) {
@@ -401,6 +426,15 @@ __device__ __forceinline__ void ntt_fwd_limb_load(W* s, const DevTables& T, u32 
     }
   }
   run(Ar<W>{});
+}
+
+// The entry point: N = 2^13 (the encrypted network's ring) with the size fixed, any other size as is.
+template <typename W, typename F>
+__device__ __forceinline__ void ntt_fwd_limb_load(W* s, const DevTables& T, u32 mod, F&& load) {
+  if (T.log_n == 13)
+    ntt_fwd_limb_load_n<W, 13>(s, T, mod, load);
+  else
+    ntt_fwd_limb_load_n<W, 0>(s, T, mod, load);
 }
 
 // The canonical value of a forward output left relaxed by ntt_fwd_limb_load (or a canonical one): a
