@@ -170,7 +170,7 @@ def source_digest(files) -> str:
 
 # ---------------------------------------------------------------------------------- GPU arm --
 def gpu_setup(torch, batch, double_hoist, rect=False, conv_hoist=False, conv_shared=False, conv_pack=False,
-              merged=False):
+              merged=False, fold=False):
     import paper_2104_03152_gb300 as tk
     from paper_2104_03152_gb300 import inputs
 
@@ -180,6 +180,7 @@ def gpu_setup(torch, batch, double_hoist, rect=False, conv_hoist=False, conv_sha
              | (tk.TCKS_RECT_DIAG if rect else 0) | (tk.TCKS_CONV_HOIST if conv_hoist else 0)
              | (tk.TCKS_CONV_SHARED if conv_hoist and conv_shared else 0)
              | (tk.TCKS_CONV_PACK if conv_hoist and conv_pack else 0)
+             | (tk.TCKS_CONV_FOLD if conv_hoist and conv_shared and conv_pack and fold else 0)
              | (tk.TCKS_MERGED_RESCALE if merged else 0))
     ctx = tk.Context(tk.Params(LOG_N, BITS, SCALE), seed=inputs.SEED_KEYS, flags=flags, stream=stream.cuda_stream)
     w = inputs.cnn_weights(SEED_W)
@@ -212,7 +213,7 @@ def run_gpu(args, world, rank, local):
     rect = args.fc_form == "rect"
     tk, ctx, model, cts, stream, imgs, w = gpu_setup(torch, B, args.double_hoist, rect, bool(args.conv_hoist),
                                                      bool(args.conv_shared), bool(args.conv_pack),
-                                                     bool(args.merged_rescale))
+                                                     bool(args.merged_rescale), bool(args.conv_fold))
     # correctness guard: the decrypted logits of every request must match the FP64 network, and the
     # batched outputs must equal the single-request path bit for bit
     outs = model.forward_batch(cts)
@@ -344,7 +345,10 @@ def run_gpu(args, world, rank, local):
         ctx.set_flags(base | dh_flag)
         alt.gen_keys()
         time_model(alt, label)
-    if conv_form(args) == "shared+pack":
+    if conv_form(args) == "shared+pack+fold":
+        other((tk.TCKS_RECT_DIAG if rect else 0) | tk.TCKS_CONV_SHARED | tk.TCKS_CONV_PACK,
+              f"{form} FC layers, {CONV_LABEL['shared+pack']}")
+    if conv_form(args).startswith("shared+pack"):
         other((tk.TCKS_RECT_DIAG if rect else 0) | tk.TCKS_CONV_SHARED, f"{form} FC layers, {CONV_LABEL['shared']}")
     if conv_form(args).startswith("shared"):
         other((tk.TCKS_RECT_DIAG if rect else 0) | tk.TCKS_CONV_HOIST, f"{form} FC layers, {CONV_LABEL['hoist']}")
@@ -867,6 +871,9 @@ def primitives_summary(torch, tk):
 
 
 CONV_LABEL = {
+    "shared+pack+fold": ("hoisted sums, the pack masks folded into the baby-step diagonals over the input's "
+                         "rotations (one diagonal-method sum and one ModDown per request for the 4 kernels), one "
+                         "giant-step sum per request"),
     "shared+pack": ("hoisted sums, baby steps over the input's rotations shared by the 4 kernels, channels packed "
                     "before one giant-step sum per request"),
     "shared": "hoisted sums, baby steps over the input's rotations shared by the 4 kernels (one ModUp per request)",
@@ -878,11 +885,16 @@ CONV_LABEL = {
 def conv_form(args) -> str:
     if not args.conv_hoist:
         return "chain"
-    return ("shared+pack" if args.conv_pack else "shared") if args.conv_shared else "hoist"
+    if not args.conv_shared:
+        return "hoist"
+    if not args.conv_pack:
+        return "shared"
+    return "shared+pack+fold" if args.conv_fold else "shared+pack"
 
 
 # ------------------------------------------------------------------------------ CPU oracle --
-def oracle_setup(rect: bool = True, conv_hoist: bool = True, conv_shared: bool = True, conv_pack: bool = True):
+def oracle_setup(rect: bool = True, conv_hoist: bool = True, conv_shared: bool = True, conv_pack: bool = True,
+                 fold: bool = True):
     import oracle
     from paper_2104_03152_gb300 import inputs
 
@@ -892,7 +904,8 @@ def oracle_setup(rect: bool = True, conv_hoist: bool = True, conv_shared: bool =
                                           pack_first=pack).items():
         o.gen_galois_key(st, lv)
     w = oracle.CNNWeights(**inputs.cnn_weights(SEED_W))
-    enc = oracle.cnn_encode(o, w, rect=rect, conv_hoist=conv_hoist, conv_shared=shared, pack_first=pack)
+    enc = oracle.cnn_encode(o, w, rect=rect, conv_hoist=conv_hoist, conv_shared=shared, pack_first=pack,
+                            fold=pack and fold)
     img = inputs.mnist_like_image(SEED_IMG)
     v, _ = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
     ct = o.encrypt_values(v, SEED_ENC)
@@ -901,10 +914,10 @@ def oracle_setup(rect: bool = True, conv_hoist: bool = True, conv_shared: bool =
 
 def time_oracle(n_steps: int, warmup: int, double_hoist: bool = True, single_thread_steps: int = 0,
                 rect: bool = True, conv_hoist: bool = True, conv_shared: bool = True, conv_pack: bool = True,
-                merged: bool = True):
+                merged: bool = True, fold: bool = True):
     """Oracle CNN inferences on the host cores (same schedule as the GPU arm); optionally also
     single-threaded ones. Returns (times, cores, single-thread times)."""
-    oracle, o, w, enc, ct = oracle_setup(rect, conv_hoist, conv_shared, conv_pack)
+    oracle, o, w, enc, ct = oracle_setup(rect, conv_hoist, conv_shared, conv_pack, fold)
     for _ in range(warmup):
         oracle.cnn_forward(o, ct, w, enc, double_hoist=double_hoist, merged=merged)
     times = []
@@ -931,7 +944,7 @@ def run_reference(args, world, rank):
     # bound the run: at most ~3 minutes of oracle inferences
     times, cores, _ = time_oracle(steps, warmup, bool(args.double_hoist), 0, args.fc_form == "rect",
                                   bool(args.conv_hoist), bool(args.conv_shared), bool(args.conv_pack),
-                                  bool(args.merged_rescale))
+                                  bool(args.merged_rescale), bool(args.conv_fold))
     total = sum(times)
     value = steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "inferences/s", "n_gpus": args.gpus,
@@ -973,7 +986,7 @@ def run_profile_case(args):
     name = args.profile_case
     if name.startswith("cnn-b"):
         B = int(name[5:])
-        tk_, ctx, model, cts, stream, imgs, w = gpu_setup(torch, B, True, True, True, True, True, True)
+        tk_, ctx, model, cts, stream, imgs, w = gpu_setup(torch, B, True, True, True, True, True, True, True)
         d_in = torch.empty((B, 2, cts[0].level, ctx.N), dtype=torch.int64, device="cuda")
         for i, c in enumerate(cts):
             d_in[i].copy_(torch.from_numpy(c.export().view(np.int64)))
@@ -1059,6 +1072,8 @@ def main():
                     help="with --conv-hoist 1: the baby steps over the input's rotations, shared by the kernels")
     ap.add_argument("--conv-pack", type=int, default=1,
                     help="with --conv-shared 1: pack the channels before one giant-step sum per request")
+    ap.add_argument("--conv-fold", type=int, default=1,
+                    help="fold the pack masks into the shared baby-step diagonals (one sum per request)")
     ap.add_argument("--merged-rescale", type=int, default=1,
                     help="take every ModDown that precedes a rescale and the rescale as one rounding")
     ap.add_argument("--double-hoist", type=int, default=1,
@@ -1148,7 +1163,7 @@ def main():
     if args.cpu_sample > 0:
         times, cores, single = time_oracle(args.cpu_sample, 0, bool(args.double_hoist), 1, args.fc_form == "rect",
                                            bool(args.conv_hoist), bool(args.conv_shared), bool(args.conv_pack),
-                                           bool(args.merged_rescale))
+                                           bool(args.merged_rescale), bool(args.conv_fold))
         cpu_val = len(times) / sum(times)
     else:
         times, cores, cpu_val, single = [], 0, None, []

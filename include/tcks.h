@@ -143,8 +143,16 @@ enum {
   TCKS_CONV_HOIST = 16u,
   TCKS_CONV_SHARED = 32u,
   TCKS_CONV_PACK = 64u,
-  TCKS_MERGED_RESCALE = 128u
+  TCKS_MERGED_RESCALE = 128u,
+  TCKS_CONV_FOLD = 256u
 };
+/* TCKS_CONV_FOLD (with TCKS_CONV_SHARED and TCKS_CONV_PACK): the network's pack masks are folded into
+ * the shared baby-step diagonals. A slot-wise mask commutes with the slot-wise diagonal products, so
+ * sum_k mask_k * sum_b rot(x, W b) * d_kb = sum_b rot(x, W b) * (sum_k mask_k * d_kb): one
+ * diagonal-method sum per request (one ModUp, one ModDown) gives the packed vector, without the
+ * per-kernel sums, the masks' products or the pack's rescale; a modulus switch then drops the limb
+ * that rescale would have dropped, so every later level and key is unchanged (§5 network; a reading
+ * of this library, not the paper's schedule). UNSUPPORTED at model creation without the other two. */
 /* TCKS_MERGED_RESCALE: wherever a key switch's ModDown is followed by a rescale (enc x enc multiply
  * with AUTO_RESCALE, the double-hoisted vector x matrix products, the CNN's squares, products and
  * shared convolution sums) the two divisions, by P and by q_last, are one rounding:
@@ -679,7 +687,8 @@ void tcks_cnn_graph_free(tcks_cnn_graph* g);
 /* Export one of the model's encoded plaintexts (kind 0 conv kernel, 1 channel mask, 2 bias
  * (index 0..2), 3 FC1 diagonal, 4 FC2 diagonal, 5 / 6 the FC1 / FC2 diagonal over the extended basis,
  * its limb modulo P last, 7 the baby-step diagonal kernel * B + b of TCKS_CONV_SHARED over the
- * extended basis) to host [level][N] ([level+1][N] for kinds 5, 6, 7); level / scale are reported. */
+ * extended basis, 8 the folded baby-step diagonal b of TCKS_CONV_FOLD over the extended basis) to
+ * host [level][N] ([level+1][N] for kinds 5 to 8); level / scale are reported. */
 tcks_status tcks_cnn_export_plaintext(const tcks_cnn* m, uint32_t kind, uint32_t index, uint64_t* host,
                                       size_t n_words, uint32_t* level, double* scale);
 

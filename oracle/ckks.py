@@ -1018,6 +1018,8 @@ class EncodedCNN:
     conv_shared: bool = False                  # baby steps on the input's rotations, shared by the kernels
     conv_baby_ext: list = field(default_factory=list)  # per kernel, its baby-step diagonals [B][L+1][N]
     pack_first: bool = False                   # channels packed after the baby steps, one giant-step sum
+    fold: bool = False                         # the masks folded into the shared baby-step diagonals
+    conv_baby_fold_ext: np.ndarray | None = None  # sum_k mask_k * (kernel k's baby diagonal b): [B][L+1][N]
 
 
 def cnn_galois_steps(o: OracleCKKS, windows=64, taps=49, n1=256, n2=64, classes=10, rect=False, conv_hoist=False,
@@ -1074,11 +1076,21 @@ def cnn_mask_slots(o: OracleCKKS, k: int, windows: int, nb: int, pack_first: boo
 
 
 def cnn_encode(o: OracleCKKS, w: CNNWeights, windows=64, rect=False, conv_hoist=False,
-               conv_shared=False, pack_first=False) -> EncodedCNN:
+               conv_shared=False, pack_first=False, fold=False) -> EncodedCNN:
     L = o.L
+    if fold and not (conv_shared and pack_first):
+        raise ValueError("folding the masks needs the shared baby steps and the pack before the giant steps")
     e = EncodedCNN(windows=windows, taps=w.conv_w.shape[1], conv_hoist=conv_hoist, conv_shared=conv_shared,
-                   pack_first=pack_first)
+                   pack_first=pack_first, fold=fold)
     nb = len(o.conv_bsgs_steps(e.taps, windows)[0]) + 1
+    if fold:
+        # reading A27: mask_k * sum_b rot(x, s_b) * d_kb summed over k is sum_b rot(x, s_b) * (sum_k mask_k * d_kb)
+        # slot by slot, so one diagonal-method sum over the folded diagonals gives the packed vector
+        baby, _ = o.conv_bsgs_steps(e.taps, windows)
+        kern = [o.kernel_slots(w.conv_w[k], windows) for k in range(w.conv_w.shape[0])]
+        masks = [cnn_mask_slots(o, k, windows, nb, True) for k in range(w.conv_w.shape[0])]
+        e.conv_baby_fold_ext = np.stack([
+            o.encode_ext(sum(masks[k] * np.roll(kern[k], -s) for k in range(len(kern))), L) for s in [0] + baby])
     for k in range(w.conv_w.shape[0]):
         e.conv.append(o.encode(o.kernel_slots(w.conv_w[k], windows), level=L))
         if conv_shared:
@@ -1158,12 +1170,19 @@ def cnn_forward(o: OracleCKKS, ct: Ct, w: CNNWeights, enc: EncodedCNN, trace: di
         # baby-step sums z_k, masks on the blocks k + B g, the pack, then one giant-step sum: block k of
         # the result gathers blocks k + B g of z_k, the full tap sum of kernel k (reading A23)
         baby, giant = o.conv_bsgs_steps(enc.taps, W)
-        if enc.conv_shared:
-            zs = [o.dh_sum(ct, baby, enc.conv_baby_ext[k], merged=True) if merged
-                  else o.rescale(o.dh_sum(ct, baby, enc.conv_baby_ext[k])) for k in range(K)]
+        if enc.fold:
+            # one sum over the folded diagonals is the packed vector at level L - 1; the limb the pack's
+            # rescale would have dropped is dropped by a modulus switch, so every later level is unchanged
+            v = (o.dh_sum(ct, baby, enc.conv_baby_fold_ext, merged=True) if merged
+                 else o.rescale(o.dh_sum(ct, baby, enc.conv_baby_fold_ext)))
+            v = o.mod_switch(v, v.level - 1)
         else:
-            zs = [o.rotsum_dh(o.rescale(o.mul_plain(ct, enc.conv[k])), baby) for k in range(K)]
-        v = _pack(o, zs, enc.masks, merged)
+            if enc.conv_shared:
+                zs = [o.dh_sum(ct, baby, enc.conv_baby_ext[k], merged=True) if merged
+                      else o.rescale(o.dh_sum(ct, baby, enc.conv_baby_ext[k])) for k in range(K)]
+            else:
+                zs = [o.rotsum_dh(o.rescale(o.mul_plain(ct, enc.conv[k])), baby) for k in range(K)]
+            v = _pack(o, zs, enc.masks, merged)
         v = o.rotsum_dh(v, giant)
         period = (len(baby) + 1) * W  # blocks [K, B) are zero, the pattern repeats every B blocks
     else:

@@ -25,6 +25,7 @@ TCKS_CONV_HOIST = 16
 TCKS_CONV_SHARED = 32
 TCKS_CONV_PACK = 64
 TCKS_MERGED_RESCALE = 128
+TCKS_CONV_FOLD = 256
 TCKS_CTA_ADD, TCKS_CTA_SUB, TCKS_CTA_MUL = 0, 1, 2  # ciphertext-array operations
 KEY_SECRET, KEY_PUBLIC, KEY_RELIN, KEY_GALOIS = 0, 1, 2, 3
 
@@ -905,7 +906,7 @@ class CNN:
 
     def export_plaintext(self, kind: int, index: int):
         lv = {0: self.ctx.L, 1: self.ctx.L - 1, 2: self.ctx.L - 2 - 2 * index, 3: self.ctx.L - 3,
-              4: self.ctx.L - 5, 5: self.ctx.L - 2, 6: self.ctx.L - 4, 7: self.ctx.L + 1}[kind]
+              4: self.ctx.L - 5, 5: self.ctx.L - 2, 6: self.ctx.L - 4, 7: self.ctx.L + 1, 8: self.ctx.L + 1}[kind]
         a = np.zeros((lv, self.ctx.N), dtype=np.uint64)
         l, sc = ctypes.c_uint32(), ctypes.c_double()
         check(lib().tcks_cnn_export_plaintext(self.h, kind, index, _p(a), a.size, ctypes.byref(l), ctypes.byref(sc)))

@@ -754,7 +754,7 @@ tcks_status tcks_ctx_set_flags(tcks_ctx* c, uint32_t flags) {
   TCKS_API_BEGIN
   if (!c) fail(TCKS_ERR_INVALID_ARG, "null context");
   if (flags & ~(u32)(TCKS_AUTO_RELIN | TCKS_AUTO_RESCALE | TCKS_DOUBLE_HOIST | TCKS_RECT_DIAG | TCKS_CONV_HOIST |
-                     TCKS_CONV_SHARED | TCKS_CONV_PACK | TCKS_MERGED_RESCALE))
+                     TCKS_CONV_SHARED | TCKS_CONV_PACK | TCKS_MERGED_RESCALE | TCKS_CONV_FOLD))
     fail(TCKS_ERR_INVALID_ARG, "unknown flag");
   c->flags = flags;
   TCKS_API_END

@@ -12,6 +12,10 @@
 //         (TCKS_CONV_PACK) after the baby steps the channels are masked to the windows-blocks k + B g
 //         and packed [L-2], then one giant-step sum per request gathers block k's full tap sum; the
 //         packed vector repeats every B blocks, so FC1 replicates it from that period;
+//         (TCKS_CONV_FOLD) the masks folded into the shared baby-step diagonals, sum_k mask_k * rot(
+//         kernel_k, W b): one diagonal-method sum per request gives the packed vector [L-1] (one ModUp,
+//         one ModDown, no pack), and a modulus switch drops the limb the pack's rescale would have
+//         dropped [L-2], so every later level is the same;
 //   pack: v = sum_k rescale(conv_k * mask_k) [L-2], mask_k = 1 on slots [k*W, (k+1)*W); + conv bias;
 //   square: rescale(relin(v * v)) [L-3];
 //   FC1: vector x plain matrix (replicate, hoisted diagonal method, rescale) [L-4]; + bias;
@@ -48,6 +52,9 @@ struct tcks_cnn {
   std::vector<int32_t> baby, giant;
   u64* baby_ext = nullptr;   // conv_shared: per kernel k and baby step b (0 first), the kernel rotated
                              // left by windows * b over the extended basis, [kernels][B][L+1][N]
+  bool fold = false;         // the masks folded into the baby-step diagonals (one sum, no pack)
+  u64* fold_ext = nullptr;   // fold: per baby step b, sum_k mask_k * (kernel k rotated left by windows * b)
+                             // over the extended basis, [B][L+1][N]
   int* h_wire_status = nullptr;  // pinned host word: the residue check of tcks_cnn_forward_wire's inputs
 };
 
@@ -65,7 +72,7 @@ static void schedule_scales(const tcks_cnn* m, double s_in, double delta, double
   const std::vector<u64>& q = m->ctx->host.chain;
   const u32 L = m->L;
   double s = s_in * delta / (double)q[L - 1];  // conv: mul_plain + rescale
-  s = s * delta / (double)q[L - 2];             // pack: mul_plain(mask) + rescale
+  if (!m->fold) s = s * delta / (double)q[L - 2];  // pack: mul_plain(mask) + rescale (folded: a modulus switch)
   *s_pack = s;
   s = s * s / (double)q[L - 3];                 // square
   s = s * m->fc1->scale / (double)q[L - 4];     // FC1
@@ -80,6 +87,7 @@ u64 cnn_resident_bytes(const tcks_cnn* m) {
   const u64 n = c->N, L = m->L;
   u64 b = (u64)m->kernels * (L + (L - 1)) * n * 8;          // conv kernels and masks
   if (m->baby_ext) b += (u64)m->kernels * (m->baby.size() + 1) * (L + 1) * n * 8;
+  if (m->fold_ext) b += (u64)(m->baby.size() + 1) * (L + 1) * n * 8;
   b += ((L - 2) + (L - 4) + (L - 6)) * n * 8;                  // biases
   b += (u64)m->fc1->diags * m->fc1->limbs() * n * 8 + (u64)m->fc2->diags * m->fc2->limbs() * n * 8;
   return b;
@@ -95,7 +103,7 @@ double cnn_out_scale(const tcks_cnn* m, u32 stage, double s) {
   switch (stage) {
     case 0:
       s = s * delta / (double)q[L - 1];
-      return s * delta / (double)q[L - 2];
+      return m->fold ? s : s * delta / (double)q[L - 2];  // folded masks: no pack, a modulus switch
     case 1: return s * s / (double)q[L - 3];
     case 2: return s * m->fc1->scale / (double)q[L - 4];
     case 3: return s * s / (double)q[L - 5];
@@ -136,6 +144,28 @@ void cnn_stage(const tcks_cnn* m, u32 stage, const u64* x, u32 count, u64* out) 
   switch (stage) {
     case 0: {
       const u64 w_in = ct_words(c, L), w1 = ct_words(c, L - 1), w2 = ct_words(c, L - 2);
+      if (m->fold) {  // one sum over the folded diagonals is the packed vector [L-1]
+        const u32 nb = (u32)m->baby.size() + 1;
+        const u64 dstride = (u64)(L + 1) * c->N;
+        DevBuf z(c, (size_t)count * w1);
+        if (c->flags & TCKS_MERGED_RESCALE) {
+          op_dh_sum_multi(c, x, w_in, count, L, m->baby, m->fold_ext, dstride, dstride * nb, L, 1, z.p, w1,
+                          (u64)count * w1, true);
+        } else {
+          DevBuf zz(c, (size_t)count * w_in);
+          op_dh_sum_multi(c, x, w_in, count, L, m->baby, m->fold_ext, dstride, dstride * nb, L, 1, zz.p, w_in,
+                          (u64)count * w_in);
+          op_rescale(c, zz.p, L, z.p, count);
+        }
+        // modulus switch [L-2]: each polynomial keeps its first L-2 limbs
+        const size_t limb = (size_t)c->N * 8;
+        check_cuda(cudaMemcpy2DAsync(out, (L - 2) * limb, z.p, (L - 1) * limb, (L - 2) * limb, 2 * (size_t)count,
+                                     cudaMemcpyDeviceToDevice, c->stream),
+                   "modulus switch");
+        op_rotsum_hoisted(c, out, w2, count, L - 2, m->giant, out);
+        launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[0], out, L - 2, 2 * count, c->stream);
+        break;
+      }
       // conv [L-1]: channel k of request r at chans + (k * count + r) * w1
       DevBuf chans(c, (size_t)K * count * w1);
       if (m->conv_shared) {
@@ -269,6 +299,7 @@ void tcks_cnn_free(tcks_cnn* m) {
   for (u64* p : m->masks) c->dev_free(p);
   for (u64* p : m->bias) c->dev_free(p);
   if (m->baby_ext) c->dev_free(m->baby_ext);
+  if (m->fold_ext) c->dev_free(m->fold_ext);
   if (m->h_wire_status) cudaFreeHost(m->h_wire_status);
   tcks_matrix_free(m->fc1);
   tcks_matrix_free(m->fc2);
@@ -311,6 +342,9 @@ tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* con
   m->conv_shared = (c->flags & TCKS_CONV_SHARED) != 0;
   m->pack_first = (c->flags & TCKS_CONV_PACK) != 0;
   m->conv_hoist = m->conv_shared || m->pack_first || (c->flags & TCKS_CONV_HOIST) != 0;
+  m->fold = (c->flags & TCKS_CONV_FOLD) != 0;
+  if (m->fold && !(m->conv_shared && m->pack_first))
+    fail(TCKS_ERR_UNSUPPORTED, "folding the masks needs TCKS_CONV_SHARED and TCKS_CONV_PACK");
   if (m->conv_shared && kernels != 4 && kernels != 1)
     fail(TCKS_ERR_UNSUPPORTED, "the shared convolution sum takes 1 or 4 kernels");
   {
@@ -338,10 +372,12 @@ tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* con
     encode_into(c, (const double*)dv.p, slots, scale, level, p.p);
     return p.release();
   };
+  std::vector<std::vector<double>> kern_lay, mask_lay;  // slot layouts, kept for the folded diagonals
   for (u32 k = 0; k < kernels; ++k) {
     std::fill(lay.begin(), lay.end(), 0.0);
     for (u32 t = 0; t < taps; ++t)
       for (u32 w = 0; w < windows; ++w) lay[(size_t)t * windows + w] = conv_w[(size_t)k * taps + t];
+    if (m->fold) kern_lay.push_back(lay);
     m->conv.push_back(encode_host(lay, delta, L));
     if (m->conv_shared) {
       const u32 nb = (u32)m->baby.size() + 1;
@@ -362,6 +398,23 @@ tcks_status tcks_cnn_create(tcks_ctx* c, const double* conv_w, const double* con
       for (u32 w = 0; w < windows; ++w) lay[(size_t)k * windows + w] = 1.0;
     }
     m->masks.push_back(encode_host(lay, delta, L - 1));
+    if (m->fold) mask_lay.push_back(lay);
+  }
+  if (m->fold) {  // reading A27: sum_k mask_k * rot(kernel_k, W b), slot by slot
+    const u32 nb = (u32)m->baby.size() + 1;
+    const u64 per = (u64)(L + 1) * c->N;
+    m->fold_ext = (u64*)c->dev_alloc((size_t)nb * per * 8);
+    std::vector<double> f(slots);
+    for (u32 b = 0; b < nb; ++b) {
+      const u32 sh = b ? (u32)m->baby[b - 1] : 0;
+      for (u32 i = 0; i < slots; ++i) {
+        double v = 0.0;
+        for (u32 k = 0; k < kernels; ++k) v += mask_lay[k][i] * kern_lay[k][(i + sh) % slots];
+        f[i] = v;
+      }
+      check_cuda(cudaMemcpyAsync(dv.p, f.data(), (size_t)slots * 8, cudaMemcpyHostToDevice, c->stream), "H2D");
+      encode_into(c, (const double*)dv.p, slots, delta, L, m->fold_ext + (u64)b * per, true);
+    }
   }
   // FC weights W [out][in] act as M = W^T [in][out]
   std::vector<double> M1((size_t)n1 * hidden), M2((size_t)hidden * classes);
@@ -731,7 +784,7 @@ tcks_status tcks_cnn_graph_run(tcks_cnn_graph* g, const tcks_ct* const* in, tcks
 // Plaintexts of the model for inspection: kind 0 conv kernel, 1 mask (index = kernel), 2 bias
 // (index 0..2), 3 FC1 diagonal, 4 FC2 diagonal (index = diagonal); host [level][N]. Kinds 5, 6: the
 // FC diagonals over the extended basis; 7: baby-step diagonal (index = kernel * B + b) of the shared
-// convolution, [L+1][N].
+// convolution, [L+1][N]; 8: folded baby-step diagonal b (TCKS_CONV_FOLD), [L+1][N].
 tcks_status tcks_cnn_export_plaintext(const tcks_cnn* m, uint32_t kind, uint32_t index, uint64_t* host,
                                       size_t n_words, uint32_t* level, double* scale) {
   CNN_BEGIN
@@ -766,6 +819,12 @@ tcks_status tcks_cnn_export_plaintext(const tcks_cnn* m, uint32_t kind, uint32_t
       const u32 nb = (u32)m->baby.size() + 1;
       if (!m->baby_ext || index >= m->kernels * nb) fail(TCKS_ERR_INVALID_ARG, "index");
       src = m->baby_ext + (size_t)index * (m->L + 1) * c->N, lv = m->L + 1, sc = c->params.scale;
+      break;
+    }
+    case 8: {
+      const u32 nb = (u32)m->baby.size() + 1;
+      if (!m->fold_ext || index >= nb) fail(TCKS_ERR_INVALID_ARG, "index");
+      src = m->fold_ext + (size_t)index * (m->L + 1) * c->N, lv = m->L + 1, sc = c->params.scale;
       break;
     }
     default: fail(TCKS_ERR_INVALID_ARG, "kind");

@@ -37,11 +37,13 @@ def test_cnn_steps_and_keys(setup):
         assert np.array_equal(ctx.export_key(tk.KEY_GALOIS, st), o.galois[st].data)
 
 
-def model_plaintexts(o, w, m, *, rect, conv_hoist=False, conv_shared=False, pack_first=False, windows=64):
+def model_plaintexts(o, w, m, *, rect, conv_hoist=False, conv_shared=False, pack_first=False, fold=False,
+                     windows=64):
     """Every plaintext the GPU model holds except the biases, each checked against the oracle's own
     encoding of the same slot values (assert_encoding_agrees: equal integers, or one apart where the
     oracle's value before rounding lies within the FP64 bound of a .5 tie): the conv kernels, the pack
-    masks, the shared convolution's baby-step diagonals (extended basis), and every diagonal of both
+    masks, the shared convolution's baby-step diagonals (extended basis), the folded baby-step
+    diagonals sum_k mask_k * d_kb (TCKS_CONV_FOLD, extended basis), and every diagonal of both
     fully connected layers in the basis the model keeps (extended when it holds the P limb; the
     normal-basis export must be its prefix). Returns the oracle EncodedCNN made of those checked
     plaintexts and the number of near-tie coefficients met."""
@@ -50,8 +52,16 @@ def model_plaintexts(o, w, m, *, rect, conv_hoist=False, conv_shared=False, pack
     baby, _ = o.conv_bsgs_steps(taps, windows)
     nb = len(baby) + 1
     enc = oracle.EncodedCNN(windows=windows, taps=taps, rect=rect, conv_hoist=conv_hoist, conv_shared=conv_shared,
-                            pack_first=pack_first)
+                            pack_first=pack_first, fold=fold)
     ties = 0
+    if fold:
+        kern = [o.kernel_slots(w.conv_w[k], windows) for k in range(K)]
+        masks = [oracle.cnn_mask_slots(o, k, windows, nb, True) for k in range(K)]
+        got = np.stack([m.export_plaintext(8, b)[0] for b in range(nb)])
+        for b, st in enumerate([0] + baby):
+            want = sum(masks[k] * np.roll(kern[k], -st) for k in range(K))
+            ties += assert_encoding_agrees(o, got[b], want, o.scale, L, f"folded baby diagonal {b}")
+        enc.conv_baby_fold_ext = got
     for k in range(K):
         ks = o.kernel_slots(w.conv_w[k], windows)
         data, sc = m.export_plaintext(0, k)
@@ -310,18 +320,22 @@ def test_cnn_hoisted_conv_parity(setup):
         ctx.set_flags(base)
 
 
-@pytest.mark.parametrize("pack,merged", [(False, False), (True, False), (True, True)],
-                         ids=["shared", "shared+pack", "shared+pack+merged"])
-def test_cnn_shared_conv_parity(setup, pack, merged):
+@pytest.mark.parametrize("pack,merged,fold", [(False, False, False), (True, False, False), (True, True, False),
+                                               (True, False, True), (True, True, True)],
+                         ids=["shared", "shared+pack", "shared+pack+merged", "shared+pack+fold",
+                              "shared+pack+merged+fold"])
+def test_cnn_shared_conv_parity(setup, pack, merged, fold):
     """TCKS_CONV_SHARED (+ rectangular FC layers, double hoisting): the baby-step sums of the four kernels
     over the input's own rotations in one 4-output double-hoisted pass; with TCKS_CONV_PACK (the bench's
-    network) the channels packed after the baby steps and one giant-step sum per request. Galois steps
+    network) the channels packed after the baby steps and one giant-step sum per request; with
+    TCKS_CONV_FOLD the masks folded into the baby-step diagonals (one sum per request). Galois steps
     and levels as the oracle's schedule; on the model's own encodings bit-identical to the oracle's
     forward pass, single and batched, and within 5e-3 of the FP64 network."""
     o, w, enc, ctx, model, need = setup
     base = tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE
     ctx.set_flags(base | tk.TCKS_RECT_DIAG | tk.TCKS_CONV_SHARED | tk.TCKS_DOUBLE_HOIST
-                  | (tk.TCKS_CONV_PACK if pack else 0) | (tk.TCKS_MERGED_RESCALE if merged else 0))
+                  | (tk.TCKS_CONV_PACK if pack else 0) | (tk.TCKS_MERGED_RESCALE if merged else 0)
+                  | (tk.TCKS_CONV_FOLD if fold else 0))
     try:
         hm = tk.CNN(ctx, w.conv_w, w.conv_b, w.fc1_w, w.fc1_b, w.fc2_w, w.fc2_b, windows=64)
         steps = oracle.cnn_galois_steps(o, rect=True, conv_hoist=True, conv_shared=True, pack_first=pack)
@@ -330,7 +344,8 @@ def test_cnn_shared_conv_parity(setup, pack, merged):
             if st not in o.galois or o.galois[st].level < lv:
                 o.gen_galois_key(st, lv)
         hm.gen_keys()
-        henc, ties = model_plaintexts(o, w, hm, rect=True, conv_hoist=True, conv_shared=True, pack_first=pack)
+        henc, ties = model_plaintexts(o, w, hm, rect=True, conv_hoist=True, conv_shared=True, pack_first=pack,
+                                      fold=fold)
         model_biases(o, w, hm, henc)
         img = inputs.mnist_like_image(7)
         v, W = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
@@ -338,7 +353,7 @@ def test_cnn_shared_conv_parity(setup, pack, merged):
         trace = {}
         ref = oracle.cnn_forward(o, ct, w, henc, trace, double_hoist=True, merged=merged)
         ties += check_biases(o, w, henc, trace)
-        print(f"shared-convolution model (pack {pack}, merged {merged}): {ties} near-tie coefficients")
+        print(f"shared-convolution model (pack {pack}, merged {merged}, fold {fold}): {ties} near-tie coefficients")
         got = hm.forward(ctx.ct_import(ct.data, ct.scale))
         assert_ct_equal(got, ref, "cnn forward (shared convolution)")
         assert float(np.max(np.abs(ctx.decrypt_values(got, 10) - oracle.cnn_plain(img, w)))) < 5e-3
@@ -347,6 +362,11 @@ def test_cnn_shared_conv_parity(setup, pack, merged):
         with pytest.raises(tk.TcksError) as e:  # the 4-output pass takes 1 or 4 kernels
             tk.CNN(ctx, w.conv_w[:3], w.conv_b[:3], w.fc1_w[:, :192], w.fc1_b, w.fc2_w, w.fc2_b, windows=64)
         assert e.value.name in ("UNSUPPORTED", "INVALID_ARG")
+        if fold:  # the fold needs the shared baby steps and the pack before the giant steps
+            ctx.set_flags(base | tk.TCKS_CONV_SHARED | tk.TCKS_CONV_FOLD)
+            with pytest.raises(tk.TcksError) as e:
+                tk.CNN(ctx, w.conv_w, w.conv_b, w.fc1_w, w.fc1_b, w.fc2_w, w.fc2_b, windows=64)
+            assert e.value.name == "UNSUPPORTED"
     finally:
         ctx.set_flags(base)
 

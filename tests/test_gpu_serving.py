@@ -47,13 +47,14 @@ def vm():
 
 
 BENCH_CNN_FLAGS = (tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE | tk.TCKS_RECT_DIAG | tk.TCKS_CONV_HOIST
-                   | tk.TCKS_CONV_SHARED | tk.TCKS_CONV_PACK | tk.TCKS_MERGED_RESCALE | tk.TCKS_DOUBLE_HOIST)
+                   | tk.TCKS_CONV_SHARED | tk.TCKS_CONV_PACK | tk.TCKS_CONV_FOLD | tk.TCKS_MERGED_RESCALE
+                   | tk.TCKS_DOUBLE_HOIST)
 
 
 @pytest.fixture(scope="module")
 def bench_lanes():
     """The lanes in the layout the benchmark serves: the CNN with rectangular FC layers, shared baby
-    steps, channels packed before the giant steps, ModDown and rescale merged and double hoisting; the
+    steps with the pack masks folded into their diagonals, ModDown and rescale merged and double hoisting; the
     vector x matrix product in rectangular form, double hoisted."""
     ctx = tk.Context(tk.Params(13, BITS, 2.0 ** 26), seed=SEED, flags=BENCH_CNN_FLAGS)
     w = inputs.cnn_weights(4)

@@ -681,3 +681,35 @@ def test_cnn_merged_rescale_schedule_matches_fp64():
     ct = o.encrypt_values(v, 77)
     logits = o.decrypt_values(oracle.cnn_forward(o, ct, w, enc, double_hoist=True, merged=True), 10)
     assert np.max(np.abs(logits - oracle.cnn_plain(img, w))) < 5e-3
+
+
+@pytest.mark.parametrize("merged", [True, False])
+def test_cnn_folded_masks_match_the_pack_and_fp64(merged):
+    """Masks folded into the shared baby-step diagonals (reading A27): one diagonal-method sum over
+    sum_k mask_k * d_kb, then a modulus switch, gives the packed vector the per-kernel sums, masks and
+    pack give (same level, same slot values up to rounding noise), and the whole network decrypts to the
+    FP64 network."""
+    o = OracleCKKS(13, [31, 26, 26, 26, 26, 26, 26, 31], 2.0 ** 26).keygen()
+    for st, lv in oracle.cnn_galois_steps(o, rect=True, conv_hoist=True, conv_shared=True, pack_first=True).items():
+        o.gen_galois_key(st, lv)
+    w = oracle.CNNWeights(**inputs.cnn_weights(4))
+    enc = oracle.cnn_encode(o, w, rect=True, conv_hoist=True, conv_shared=True, pack_first=True)
+    encf = oracle.cnn_encode(o, w, rect=True, conv_hoist=True, conv_shared=True, pack_first=True, fold=True)
+    with pytest.raises(ValueError):
+        oracle.cnn_encode(o, w, rect=True, conv_hoist=True, conv_shared=True, fold=True)
+    img = inputs.mnist_like_image(5)
+    v, _ = OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+    ct = o.encrypt_values(v, 78)
+    baby, _ = o.conv_bsgs_steps(enc.taps, enc.windows)
+    zs = [o.dh_sum(ct, baby, enc.conv_baby_ext[k], merged=True) if merged
+          else o.rescale(o.dh_sum(ct, baby, enc.conv_baby_ext[k])) for k in range(4)]
+    packed = oracle.ckks._pack(o, zs, enc.masks, merged)
+    folded = (o.dh_sum(ct, baby, encf.conv_baby_fold_ext, merged=True) if merged
+              else o.rescale(o.dh_sum(ct, baby, encf.conv_baby_fold_ext)))
+    folded = o.mod_switch(folded, folded.level - 1)
+    assert folded.level == packed.level == o.L - 2
+    a, b = o.decrypt_values(folded), o.decrypt_values(packed)
+    assert np.max(np.abs(a - b)) < 1e-3 * max(1.0, float(np.max(np.abs(b))))
+    assert np.max(np.abs(b)) > 0.1  # the comparison is not between two empty vectors
+    logits = o.decrypt_values(oracle.cnn_forward(o, ct, w, encf, double_hoist=True, merged=merged), 10)
+    assert np.max(np.abs(logits - oracle.cnn_plain(img, w))) < 5e-3
