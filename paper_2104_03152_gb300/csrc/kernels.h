@@ -85,6 +85,7 @@ struct MultiNttBatch {
 u32 launch_ntt_multi(bool inverse, const MultiNttBatch* batches, u32 n, cudaStream_t st, u32 understate = 0);
 // Largest CTA size the limb kernels of each file accept (0 when the query fails).
 u32 limb_threads_cap_core(bool narrow, u32 log_c);
+u32 limb_threads_cap_keyswitch(bool narrow, u32 log_c);  // the key-switching file's kernels (in the core cap)
 u32 limb_threads_cap_sample(bool narrow, u32 log_c);
 u32 limb_threads_cap_fft(bool narrow, u32 log_c);
 // Bit-packed wire format of a ciphertext [2][level][N] (kern_wire.cu): payload bytes, pack into
