@@ -35,8 +35,10 @@ constexpr u32 kDhThreads = 256;
 // and multiplied by each output's diagonal.
 // LOGN > 0 (with ELL > 0) fixes the ring size too, for plans whose keys all sit at level ELL: every key
 // and digit stride is then a compile-time constant, so each load is a base plus an immediate offset.
-template <typename W, int EPT, int RPT, int ELL, int KO = 1, int LOGN = 0>
-__global__ void __launch_bounds__(kDhThreads, KO > 1 ? 3 : 1) k_vecmat_dh_acc(DevTables T, u32 ell_arg,
+// KEYS_AT = false: the keys share one level above ELL (p.keys_K), a run-time value uniform over the
+// launch, so only the key strides are computed.
+template <typename W, int EPT, int RPT, int ELL, int KO = 1, int LOGN = 0, bool KEYS_AT = true>
+__global__ void __launch_bounds__(kDhThreads, (KO > 1 || LOGN > 0) ? 3 : 1) k_vecmat_dh_acc(DevTables T, u32 ell_arg,
                                                                const __grid_constant__ VecmatDhPlan p) {
   static_assert(LOGN == 0 || ELL > 0, "a fixed ring size needs a fixed level");
   const u32 ell = ELL > 0 ? (u32)ELL : ell_arg;
@@ -71,7 +73,8 @@ __global__ void __launch_bounds__(kDhThreads, KO > 1 ? 3 : 1) k_vecmat_dh_acc(De
 #pragma unroll kRotUnroll
   for (u32 r = r0; r < r1; ++r) {
     const KsKey kk = p.keys[r];
-    const u32 kK = LOGN > 0 ? (u32)ELL : kk.K;  // LOGN > 0: every key is at level ELL (checked by the host)
+    // LOGN > 0: every key at level ELL, or (KEYS_AT = false) at the plan's shared level (checked by the host)
+    const u32 kK = LOGN > 0 ? (KEYS_AT ? (u32)ELL : p.keys_K) : kk.K;
     const u32 key_slot = i < ell ? i : kK;
     const u64* dk = unit ? nullptr : p.diag + (u64)(r + 1) * p.diag_stride + (u64)(i < ell ? i : p.p_limb) * n;
     const u64* k0 = kk.key + (u64)key_slot * n;     // digit j's component b at + (2j + b) (K+1) n
@@ -367,19 +370,27 @@ static decltype(&k_vecmat_dh_moddown_rs<u64, 0>) const K6_k_vecmat_dh_moddown_rs
 }  // namespace
 
 // The level as a template argument up to 8 limbs (every level of the CNN and the 4096x256 product).
-// With 32-bit words at N = 2^13 and every key at the plan's level, the ring size is fixed as well.
+// With 32-bit words at N = 2^13 and every key at the plan's level, the ring size is fixed as well; with
+// the keys sharing a level above the plan's (two requests per thread, one output), the ring size alone.
 static bool dh_fixed_ring(const DevTables& T, u32 ell, const VecmatDhPlan& p) {
   return T.narrow && T.log_n == 13 && p.keys_K == ell && ell >= 1 && ell <= 8;
+}
+static bool dh_fixed_ring_keys_above(const DevTables& T, u32 ell, const VecmatDhPlan& p, u32 rpt, u32 outs) {
+  return T.narrow && T.log_n == 13 && p.keys_K > ell && ell >= 1 && ell <= 8 && rpt == 2 && outs == 1;
 }
 
 template <typename W, int EPT, int RPT, int KO>
 static void dh_acc_launch(dim3 grid, cudaStream_t st, const DevTables& T, u32 ell, const VecmatDhPlan& p) {
   const bool fixed = sizeof(W) == 4 && dh_fixed_ring(T, ell, p);
+  constexpr bool kAbove = sizeof(W) == 4 && RPT == 2 && KO == 1;  // the shape with a keys-above form
+  const bool above = kAbove && dh_fixed_ring_keys_above(T, ell, p, RPT, KO);
   switch (ell) {
 #define TCKS_DH_CASE(E)                                                                          \
   case E:                                                                                        \
     if (fixed)                                                                                   \
       k_vecmat_dh_acc<W, EPT, RPT, E, KO, sizeof(W) == 4 ? 13 : 0><<<grid, kDhThreads, 0, st>>>(T, ell, p); \
+    else if (above)                                                                              \
+      k_vecmat_dh_acc<W, EPT, RPT, E, KO, kAbove ? 13 : 0, !kAbove><<<grid, kDhThreads, 0, st>>>(T, ell, p); \
     else                                                                                         \
       k_vecmat_dh_acc<W, EPT, RPT, E, KO><<<grid, kDhThreads, 0, st>>>(T, ell, p);             \
     return;
@@ -420,9 +431,11 @@ void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cu
   const double ops = (double)p.B * p.R * n * (2.0 * ell * (ell + 1.0) + outs * (2.0 * (ell + 1.0) + ell));
   const bool bulk = dh_bulk_applies(T, ell, p);
   // profiler tag: level, outputs, unit diagonals (bit 16), staged operands (bit 17), fixed ring size (bit 18)
+  const bool fixed_ring = dh_fixed_ring(T, ell, p) ||
+                          dh_fixed_ring_keys_above(T, ell, p, dh_rpt_of(T.narrow, outs, T.dh_rpt), outs);
   Launch L(K_VECMAT_DH, st, by + 8.0 * n * (outs - 1.0) * (p.R * (ell + 1.0) + p.B * p.chunks * (3.0 * ell + 2.0)), ops,
            ell | (outs << 8) | ((p.diag ? 0u : 1u) << 16) | ((bulk ? 1u : 0u) << 17) |
-               ((!bulk && dh_fixed_ring(T, ell, p) ? 1u : 0u) << 18));
+               ((!bulk && fixed_ring ? 1u : 0u) << 18));
   const dim3 grid(vecmat_dh_base_ctas(T.log_n, ell, p.B, T.narrow, outs, T.dh_rpt), p.chunks);
   if (bulk) {
     launch_vecmat_dh_acc_bulk(T, ell, p, dh_rpt_of(true, outs, T.dh_rpt), st);
