@@ -49,15 +49,31 @@ __global__ void k_modup(DevTables T, const u64* __restrict__ x_ntt, u64 x_stride
   const u64 half_j = T.mods[j].half;
   const u64 qj_mod_t = T.pairs[(u64)j * T.n_mods + tmod].qa_mod_b;
   const u64* in = x_coef + (sl.y * ell + j) * n + sl.off;
-  if constexpr (LC == 0) {  // the lift feeds the first butterfly round directly
-    ntt_fwd_limb_load<W>(s, T, tmod, [&](u32 k) { return lift_balanced_w<W>(in[k], half_j, qj_mod_t, mt); });
+  if constexpr (LC == 0) {
+    // the lift feeds the first butterfly round and the last round writes the digit out directly
+    ntt_fwd_limb_load_store<W>(
+        s, T, tmod, [&](u32 k) { return lift_balanced_w<W>(in[k], half_j, qj_mod_t, mt); },
+        [&](u32 base, const W(&x)[8]) {
+          W v[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) v[k] = (W)fwd_fin(x[k], mt);
+          if constexpr (sizeof(W) == 4) {
+            uint4* o = reinterpret_cast<uint4*>(out + base);
+            o[0] = make_uint4(v[0], v[1], v[2], v[3]);
+            o[1] = make_uint4(v[4], v[5], v[6], v[7]);
+          } else {
+            ulonglong2* o = reinterpret_cast<ulonglong2*>(out + base);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[k] = make_ulonglong2(v[2 * k], v[2 * k + 1]);
+          }
+        });
   } else {
 #pragma unroll 4
     for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) s[sw(k)] = lift_balanced_w<W>(in[k], half_j, qj_mod_t, mt);
     __syncthreads();
     ntt_fwd_slice<W, LC>(s, T, tmod, sl.rank);
+    for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) out[k] = (W)fwd_fin(s[sw(k)], mt);
   }
-  for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) out[k] = (W)fwd_fin(s[sw(k)], mt);
 }
 
 static decltype(&k_modup<u64, 0>) const K6_k_modup[6] = TCKS_K6(k_modup);

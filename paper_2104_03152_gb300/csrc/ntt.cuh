@@ -428,6 +428,80 @@ __device__ __forceinline__ void ntt_fwd_limb_load_n(W* s, const DevTables& T, u3
   run(Ar<W>{});
 }
 
+// The last forward round of a whole limb (its smallest distance is 1): group g holds the outputs
+// 8g .. 8g + 7 in registers, which go to store(8g, x) instead of back to shared memory.
+template <typename W, typename A, typename G>
+__device__ __forceinline__ void fwd_round_store(u32 log_n, u32 st, const W* s, const W* tw, const W* tws, W q, G&& store) {
+  constexpr int LR = 3, R = 1 << LR;
+  const u32 groups = (1u << log_n) >> LR;
+  for (u32 g = threadIdx.x; g < groups; g += blockDim.x) {
+    const u32 base = g << LR;
+    W x[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) x[k] = s[sw(base + k)];
+    fwd_group<W, LR, A>(x, st, g, tw, tws, q);
+    store(base, x);
+  }
+}
+
+// ntt_fwd_limb_load whose last round hands each thread's 8 consecutive outputs (relaxed as
+// ntt_fwd_limb_load leaves them; fwd_fin gives the canonical values) to store(first index, x[8])
+// instead of writing them back: one shared-memory pass and a barrier fewer for a caller that only
+// writes the transform out. Shared memory is left partly stale; no barrier at the end.
+template <typename W, int LOGN, typename F, typename G>
+__device__ __forceinline__ void ntt_fwd_limb_load_store_n(W* s, const DevTables& T, u32 mod, F&& load, G&& store) {
+  constexpr int RB = RadixBits<W>::value;
+  static_assert(RB == 3, "the rounds below are radix-8");
+  const u32 log_n = LOGN > 0 ? (u32)LOGN : T.log_n;
+  const W q = (W)T.mods[mod].q;
+  const W* tw = Ar<W>::tw(T, mod, 0);
+  const W* tws = Ar<W>::tw(T, mod, 1);
+  auto run = [&](auto policy) {
+    using A = decltype(policy);
+    const u32 first = log_n % RB ? log_n % RB : RB;
+    if (first == 1)
+      fwd_round_load<W, 1, A>(s, log_n, tw, tws, q, load);
+    else if (first == 2)
+      fwd_round_load<W, 2, A>(s, log_n, tw, tws, q, load);
+    else
+      fwd_round_load<W, 3, A>(s, log_n, tw, tws, q, load);
+#pragma unroll
+    for (u32 st = first; st + RB < log_n; st += RB) fwd_round<W, RB, A>(s, log_n, log_n, 0, st, tw, tws, q);
+    fwd_round_store<W, A>(log_n, log_n - RB, s, tw, tws, q, store);
+  };
+  if constexpr (sizeof(W) == 4) {
+    if ((u64)q * (2 * log_n + 4) < (1ull << 32)) {
+      run(Ar32Grow{});
+      return;
+    }
+    if (q < (1u << 30)) {
+      run(Ar32Lazy{});
+      return;
+    }
+  }
+  run(Ar<W>{});
+}
+
+template <typename W, typename F>
+__device__ __forceinline__ void ntt_fwd_limb_load(W* s, const DevTables& T, u32 mod, F&& load);
+
+template <typename W, typename F, typename G>
+__device__ __forceinline__ void ntt_fwd_limb_load_store(W* s, const DevTables& T, u32 mod, F&& load, G&& store) {
+  if (T.log_n == 13) {
+    ntt_fwd_limb_load_store_n<W, 13>(s, T, mod, load, store);
+  } else if (T.log_n > 3) {
+    ntt_fwd_limb_load_store_n<W, 0>(s, T, mod, load, store);
+  } else {  // N = 8: the first round is the last; transform in shared memory, then hand the words out
+    ntt_fwd_limb_load<W>(s, T, mod, load);
+    W x[8];
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = s[sw(k)];
+      store(0u, x);
+    }
+  }
+}
+
 // The entry point: N = 2^13 (the encrypted network's ring) with the size fixed, any other size as is.
 template <typename W, typename F>
 __device__ __forceinline__ void ntt_fwd_limb_load(W* s, const DevTables& T, u32 mod, F&& load) {
