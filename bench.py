@@ -321,7 +321,25 @@ def run_gpu(args, world, rank, local):
     for _ in range(e2e_steps):
         model.forward_wire(wire_in, B, wire_out)
     torch.cuda.synchronize()
+    wire_sync_s = reduce_max(world, time.perf_counter() - t0)
+    # the same exchange pipelined (tcks_cnn_pipe_*): batch k's input copy overlaps batch k-1's network;
+    # every batch still copies its serialized inputs in and its serialized outputs out
+    pipe = model.pipe(B, seeded_sz)
+    wire_outs = [wire_out, torch.empty(B * out_sz, dtype=torch.uint8, pin_memory=True).numpy()]
+    pipe.wait(pipe.submit(wire_in, wire_outs[1]))
+    assert np.array_equal(wire_outs[1], wire_out), "pipelined output != forward_wire output"
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tickets = []
+    for k in range(e2e_steps):
+        tickets.append(pipe.submit(wire_in, wire_outs[k % 2]))
+        if k >= 1:
+            pipe.wait(tickets[k - 1])
+    pipe.wait(tickets[-1])
+    torch.cuda.synchronize()
     wire_s = reduce_max(world, time.perf_counter() - t0)
+    del pipe
     # the same batched step with one ModDown per rotation (the schedule bit-identical to rotating
     # each diagonal's ciphertext separately), for comparison
     single = {}
@@ -408,6 +426,7 @@ def run_gpu(args, world, rank, local):
     return dict(galois_keys=len(model.galois_steps()), single=single, c4=c4, primitives=primitives, bfly_peak=bfly_peak,
                 mac_peak=mac_peak, dh_records=dh_records, dh_peaks=dh_peaks, word=word, tune=tune, serving=serving, total_ms=total_ms, per_step=per_step, prof=prof, launches=launches, clocks=clk, e2e_s=e2e_s,
                 e2e_steps=e2e_steps, h2d=host_in.nbytes, d2h=host_out.nbytes, max_err=max_err, wire_s=wire_s,
+                wire_sync_s=wire_sync_s,
                 wire_h2d=wire_in.nbytes + 8 * B, wire_d2h=wire_out.nbytes + 4, wire_sizes=(seeded_sz, out_sz),
                 plain_ms=plain_total / plain_steps, plain_times=plain_times)
 
@@ -1201,10 +1220,14 @@ def main():
                                            "sample": f"{len(single)} inference(s)"}},
         "e2e": {"value": world * B * r["e2e_steps"] / r["wire_s"], "unit": "inferences/s",
                 "h2d_bytes_per_step": r["wire_h2d"], "d2h_bytes_per_step": r["wire_d2h"],
-                "api": "tcks_cnn_forward_wire: seeded serialized inputs in (%d bytes each, c0 bit-packed + the "
+                "api": "tcks_cnn_pipe_submit / tcks_cnn_pipe_wait (the pipelined tcks_cnn_forward_wire, two "
+                       "batches in flight): seeded serialized inputs in (%d bytes each, c0 bit-packed + the "
                        "seed of c1, plus its 8-byte seed copied to the device), serialized outputs out (%d bytes "
                        "each); unpacking, c1 from its seed and packing on the device, inside the timed region"
                        % r["wire_sizes"]},
+        "e2e_unpipelined": {"value": world * B * r["e2e_steps"] / r["wire_sync_s"], "unit": "inferences/s",
+                            "h2d_bytes_per_step": r["wire_h2d"], "d2h_bytes_per_step": r["wire_d2h"],
+                            "api": "tcks_cnn_forward_wire, one synchronous call per batch"},
         "e2e_limbs": {"value": world * B * r["e2e_steps"] / r["e2e_s"], "unit": "inferences/s",
                       "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"],
                       "api": "tcks_cnn_forward_host: 64-bit limbs in and out"},

@@ -675,6 +675,24 @@ tcks_status tcks_cnn_wire_sizes(const tcks_cnn* m, uint64_t* in_full, uint64_t* 
  * fit, SCALE_MISMATCH for an input scale; after a residue error host_out is unspecified. */
 tcks_status tcks_cnn_forward_wire(const tcks_cnn* m, const uint8_t* host_in, uint64_t in_size, uint32_t count,
                                   uint8_t* host_out, uint64_t out_size);
+/* The same exchange for a stream of batches, pipelined (§5's client-server evaluation served batch
+ * after batch; the paper has no pipeline): a pipe holds two slots of device buffers for batches of
+ * `count` serialized inputs of in_size bytes (in_full or in_seeded). submit checks the headers,
+ * queues the batch and returns a ticket without waiting. The input copy runs on the pipe's own copy
+ * stream as soon as the batch's slot is free; the unpacking, the network and the packing run on the
+ * model's stream after it. So the input copy of one batch overlaps the network of the one before.
+ * wait(ticket) returns when that batch's outputs are in its host_out (serialized as in
+ * tcks_cnn_forward_wire). host_in and host_out must stay valid (and host_in unchanged) until the
+ * batch completes; pinned memory lets the copies run asynchronously. A submit first completes the
+ * batch two submits earlier, whose slot it takes. A batch's errors (INVALID_ARG for a residue >= its
+ * prime: its host_out is then not written; TIMEOUT or CUDA_ERROR for a kernel error) are reported by
+ * the call that completes it: its wait, or that later submit. wait on a ticket already completed
+ * returns OK. free waits for the work in flight. */
+typedef struct tcks_cnn_pipe tcks_cnn_pipe;
+tcks_status tcks_cnn_pipe_create(const tcks_cnn* m, uint32_t count, uint64_t in_size, tcks_cnn_pipe** out);
+tcks_status tcks_cnn_pipe_submit(tcks_cnn_pipe* p, const uint8_t* host_in, uint8_t* host_out, uint64_t* ticket);
+tcks_status tcks_cnn_pipe_wait(tcks_cnn_pipe* p, uint64_t ticket);
+void tcks_cnn_pipe_free(tcks_cnn_pipe* p);
 /* CUDA graph of the batched forward for a fixed batch size (the schedule is captured once with its
  * stream-ordered scratch allocations, then replayed): create captures it (after one eager pass that
  * warms the key tables), run copies the inputs into the graph's staging buffers, replays and returns

@@ -181,6 +181,10 @@ _SIGS = {
     "tcks_cnn_forward_host": (ctypes.c_int32, [_vp, _u64p, ctypes.c_uint32, _u64p]),
     "tcks_cnn_forward_device": (ctypes.c_int32, [_vp, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p]),
     "tcks_cnn_wire_sizes": (ctypes.c_int32, [_vp, _u64p, _u64p, _u64p]),
+    "tcks_cnn_pipe_create": (ctypes.c_int32, [_vp, ctypes.c_uint32, ctypes.c_uint64, _vpp]),
+    "tcks_cnn_pipe_submit": (ctypes.c_int32, [_vp, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint64)]),
+    "tcks_cnn_pipe_wait": (ctypes.c_int32, [_vp, ctypes.c_uint64]),
+    "tcks_cnn_pipe_free": (None, [_vp]),
     "tcks_cnn_forward_wire": (ctypes.c_int32, [_vp, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
                                                ctypes.c_void_p, ctypes.c_uint64]),
     "tcks_vecmat_plain_batch": (ctypes.c_int32, [_vpp, ctypes.c_uint32, _vp, _vpp]),
@@ -904,6 +908,9 @@ class CNN:
     def graph(self, count: int) -> "CNNGraph":
         return CNNGraph(self, count)
 
+    def pipe(self, count: int, in_size: int) -> "CNNPipe":
+        return CNNPipe(self, count, in_size)
+
     def export_plaintext(self, kind: int, index: int):
         lv = {0: self.ctx.L, 1: self.ctx.L - 1, 2: self.ctx.L - 2 - 2 * index, 3: self.ctx.L - 3,
               4: self.ctx.L - 5, 5: self.ctx.L - 2, 6: self.ctx.L - 4, 7: self.ctx.L + 1, 8: self.ctx.L + 1}[kind]
@@ -1009,6 +1016,39 @@ class BatchGraph:
     def __del__(self):
         if getattr(self, "h", None):
             lib().tcks_batch_graph_free(self.h)
+            self.h = None
+
+
+class CNNPipe:
+    """Pipelined serialized batches (tcks_cnn_pipe_*): submit queues a batch of `count` inputs of
+    in_size bytes and returns a ticket; wait(ticket) returns once its outputs are in its host_out. The
+    arrays must stay alive and unchanged until their batch completes (pinned memory lets the copies
+    run asynchronously)."""
+
+    def __init__(self, model: "CNN", count: int, in_size: int):
+        h = _vp()
+        check(lib().tcks_cnn_pipe_create(model.h, count, in_size, ctypes.byref(h)))
+        self.model, self.count, self.in_size, self.h = model, count, in_size, h
+        self._held = {}
+
+    def submit(self, host_in: np.ndarray, host_out: np.ndarray) -> int:
+        assert host_in.dtype == np.uint8 and host_out.dtype == np.uint8
+        assert host_in.flags.c_contiguous and host_out.flags.c_contiguous
+        assert host_in.size == self.count * self.in_size
+        t = ctypes.c_uint64()
+        check(lib().tcks_cnn_pipe_submit(self.h, host_in.ctypes.data, host_out.ctypes.data, ctypes.byref(t)))
+        self._held[t.value] = (host_in, host_out)
+        for k in [k for k in self._held if k + 2 <= t.value]:  # completed by this submit
+            del self._held[k]
+        return t.value
+
+    def wait(self, ticket: int):
+        check(lib().tcks_cnn_pipe_wait(self.h, ticket))
+        self._held.pop(ticket, None)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().tcks_cnn_pipe_free(self.h)
             self.h = None
 
 

@@ -671,6 +671,228 @@ tcks_status tcks_cnn_forward_wire(const tcks_cnn* m, const uint8_t* host_in, uin
   CNN_END
 }
 
+// ------------------------------------------------------------- pipelined serialized batches ----
+// Two slots of device buffers for batches of `count` serialized inputs of one size. A batch's input copy
+// runs on the pipe's copy stream as soon as its slot is free, and its unpacking, network and packing on
+// the model's stream after that copy; its output copy waits for the residue check on the host (in
+// wait), so a refused batch never reaches its output buffer. With two batches in flight the next
+// batch's input copy overlaps the current batch's network.
+struct tcks_cnn_pipe {
+  const tcks_cnn* m = nullptr;
+  tcks_ctx* c = nullptr;  // retained
+  u32 count = 0;
+  u64 in_size = 0, out_size = 0;
+  bool seeded = false;
+  cudaStream_t copy = nullptr;
+  struct Slot {
+    unsigned char* raw = nullptr;  // [count][in_size]
+    u64* seeds = nullptr;          // [count] (seeded inputs)
+    u64* xin = nullptr;            // [count][2][L][N]
+    u64* yout = nullptr;           // [count][2][L-6][N]
+    unsigned char* packed = nullptr;  // [count][out_size]
+    int* d_status = nullptr;
+    int* h_status = nullptr;          // pinned
+    u32* h_kerr = nullptr;            // pinned: the context's kernel error word after the batch
+    u64* h_seeds = nullptr;           // pinned staging of the seeds
+    cudaEvent_t in_copied = nullptr, checked = nullptr, packed_ev = nullptr, out_copied = nullptr, consumed = nullptr;
+    uint8_t* host_out = nullptr;      // the batch in flight, or null
+    u64 ticket = 0;
+    bool used = false;                // out_copied has been recorded once
+  } slot[2];
+  u64 next = 1;  // ticket of the next submit
+};
+
+namespace {
+
+void pipe_release(tcks_cnn_pipe* p) {
+  if (!p) return;
+  tcks_ctx* c = p->c;
+  if (c) cudaStreamSynchronize(c->stream);
+  if (p->copy) {
+    cudaStreamSynchronize(p->copy);
+    cudaStreamDestroy(p->copy);
+  }
+  for (auto& s : p->slot) {
+    if (c) {
+      c->dev_free(s.raw);
+      c->dev_free(s.seeds);
+      c->dev_free(s.xin);
+      c->dev_free(s.yout);
+      c->dev_free(s.packed);
+      c->dev_free(s.d_status);
+    }
+    if (s.h_status) cudaFreeHost(s.h_status);
+    if (s.h_kerr) cudaFreeHost(s.h_kerr);
+    if (s.h_seeds) cudaFreeHost(s.h_seeds);
+    for (cudaEvent_t e : {s.in_copied, s.checked, s.packed_ev, s.out_copied, s.consumed})
+      if (e) cudaEventDestroy(e);
+  }
+  if (c) {
+    cudaStreamSynchronize(c->stream);
+    ctx_release(c);
+  }
+  delete p;
+  cudaGetLastError();  // clean-up statuses are not reported
+}
+
+// Wait for slot s's batch: its residue check, then (if it passed) its output copy; the slot is free after.
+void pipe_finish(tcks_cnn_pipe* p, tcks_cnn_pipe::Slot& s) {
+  if (!s.host_out) return;
+  tcks_ctx* c = p->c;
+  uint8_t* host_out = s.host_out;
+  s.host_out = nullptr;
+  check_cuda(cudaEventSynchronize(s.checked), "pipe residue check");
+  if (*s.h_status) {
+    check_cuda(cudaEventSynchronize(s.packed_ev), "pipe");
+    fail(TCKS_ERR_INVALID_ARG, "an input residue is not below its prime");
+  }
+  check_cuda(cudaStreamWaitEvent(p->copy, s.packed_ev, 0), "pipe");
+  check_cuda(cudaMemcpyAsync(host_out, s.packed, (size_t)p->count * p->out_size, cudaMemcpyDeviceToHost, p->copy),
+             "D2H");
+  check_cuda(cudaEventRecord(s.out_copied, p->copy), "pipe");
+  s.used = true;
+  check_cuda(cudaEventSynchronize(s.out_copied), "pipe output");
+  if (*s.h_kerr) {  // a kernel's bounded wait gave up (or refused a copy): the results are invalid
+    check_cuda(cudaMemsetAsync(c->T.kerr, 0, sizeof(u32), c->stream), "kernel error word");
+    fail((*s.h_kerr & 1u) ? TCKS_ERR_TIMEOUT : TCKS_ERR_CUDA, "a kernel of this batch recorded an error");
+  }
+  const u32 Lo = p->m->L - 6;
+  for (u32 r = 0; r < p->count; ++r) {
+    uint8_t* h = host_out + (u64)r * p->out_size;
+    std::memcpy(h, kWireMagic, 4);
+    h[4] = 1;
+    h[5] = 0;
+    h[6] = (uint8_t)c->params.log_n;
+    h[7] = (uint8_t)Lo;
+    std::memcpy(h + 8, &p->m->out_scale, 8);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+tcks_status tcks_cnn_pipe_create(const tcks_cnn* m, uint32_t count, uint64_t in_size, tcks_cnn_pipe** out) {
+  struct Guard {
+    tcks_cnn_pipe* p = nullptr;
+    ~Guard() { pipe_release(p); }
+  } guard;
+  CNN_BEGIN
+  if (!m || !out || !count) fail(TCKS_ERR_INVALID_ARG, "null argument or empty batch");
+  *out = nullptr;
+  tcks_ctx* c = m->ctx;
+  const u32 L = m->L, Lo = m->L - 6;
+  const u64 pin = wire_payload_bytes(c->T, c->host.chain.data(), L);
+  const u64 pout = wire_payload_bytes(c->T, c->host.chain.data(), Lo);
+  const bool seeded = in_size == kWireHeader + 8 + pin / 2;
+  if (!seeded && in_size != kWireHeader + pin) fail(TCKS_ERR_INVALID_ARG, "input size is not a serialized input");
+  guard.p = new tcks_cnn_pipe();
+  tcks_cnn_pipe* p = guard.p;
+  p->m = m;
+  p->c = c;
+  ctx_retain(c);
+  p->count = count;
+  p->in_size = in_size;
+  p->out_size = kWireHeader + pout;
+  p->seeded = seeded;
+  check_cuda(cudaStreamCreateWithFlags(&p->copy, cudaStreamNonBlocking), "pipe copy stream");
+  const u64 w_in = ct_words(c, L), w_out = ct_words(c, Lo);
+  for (auto& s : p->slot) {
+    s.raw = (unsigned char*)c->dev_alloc((size_t)count * in_size);
+    s.seeds = (u64*)c->dev_alloc((size_t)count * 8);
+    s.xin = (u64*)c->dev_alloc((size_t)count * w_in * 8);
+    s.yout = (u64*)c->dev_alloc((size_t)count * w_out * 8);
+    s.packed = (unsigned char*)c->dev_alloc((size_t)count * p->out_size);
+    s.d_status = (int*)c->dev_alloc(sizeof(int));
+    check_cuda(cudaHostAlloc((void**)&s.h_status, sizeof(int), cudaHostAllocDefault), "pinned status word");
+    check_cuda(cudaHostAlloc((void**)&s.h_kerr, sizeof(u32), cudaHostAllocDefault), "pinned status word");
+    check_cuda(cudaHostAlloc((void**)&s.h_seeds, (size_t)count * 8, cudaHostAllocDefault), "pinned seeds");
+    for (cudaEvent_t* e : {&s.in_copied, &s.checked, &s.packed_ev, &s.out_copied, &s.consumed})
+      check_cuda(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "pipe event");
+  }
+  // the buffers come from the model stream's pool: ready before the copy stream touches them
+  check_cuda(cudaStreamSynchronize(c->stream), "pipe buffers");
+  *out = p;
+  guard.p = nullptr;
+  CNN_END
+}
+
+tcks_status tcks_cnn_pipe_submit(tcks_cnn_pipe* p, const uint8_t* host_in, uint8_t* host_out, uint64_t* ticket) {
+  CNN_BEGIN
+  if (!p || !host_in || !host_out || !ticket) fail(TCKS_ERR_INVALID_ARG, "null argument");
+  const tcks_cnn* m = p->m;
+  tcks_ctx* c = p->c;
+  const u32 L = m->L, Lo = m->L - 6, count = p->count;
+  const u64 in_size = p->in_size;
+  tcks_cnn_pipe::Slot& s = p->slot[p->next & 1];
+  pipe_finish(p, s);  // the slot's previous batch (two submits ago) completes first
+  for (u32 r = 0; r < count; ++r) {
+    const uint8_t* h = host_in + (u64)r * in_size;
+    double sc;
+    std::memcpy(&sc, h + 8, 8);
+    if (std::memcmp(h, kWireMagic, 4) != 0 || h[4] != 1 || h[5] != (p->seeded ? 1 : 0) || h[6] != c->params.log_n ||
+        h[7] != L)
+      fail(TCKS_ERR_INVALID_ARG, "an input header does not match the model's input");
+    if (sc != m->in_scale) fail(TCKS_ERR_SCALE_MISMATCH, "the network takes ciphertexts at the context scale");
+  }
+  // the input copy may start once the slot's previous batch has been unpacked
+  if (s.used) check_cuda(cudaStreamWaitEvent(p->copy, s.consumed, 0), "pipe");
+  check_cuda(cudaMemcpyAsync(s.raw, host_in, (size_t)count * in_size, cudaMemcpyHostToDevice, p->copy), "H2D");
+  if (p->seeded) {
+    for (u32 r = 0; r < count; ++r) {
+      u64 v = 0;
+      for (int b = 0; b < 8; ++b) v |= (u64)host_in[(u64)r * in_size + kWireHeader + b] << (8 * b);
+      s.h_seeds[r] = v;
+    }
+    check_cuda(cudaMemcpyAsync(s.seeds, s.h_seeds, (size_t)count * 8, cudaMemcpyHostToDevice, p->copy), "H2D");
+  }
+  check_cuda(cudaEventRecord(s.in_copied, p->copy), "pipe");
+  // the model's stream: unpack after the copy, the network, then pack once the slot's last output copy is done
+  const u64 w_in = ct_words(c, L), w_out = ct_words(c, Lo);
+  check_cuda(cudaStreamWaitEvent(c->stream, s.in_copied, 0), "pipe");
+  check_cuda(cudaMemsetAsync(s.d_status, 0, sizeof(int), c->stream), "pipe status");
+  const u64 head = kWireHeader + (p->seeded ? 8 : 0);
+  constexpr u32 kChunk = 16384;  // grid z = requests x components <= 65535
+  for (u32 r0 = 0; r0 < count; r0 += kChunk) {
+    const u32 k = std::min(kChunk, count - r0);
+    launch_unpack_batch(c->T, s.raw + (u64)r0 * in_size + head, in_size, L, s.xin + (u64)r0 * w_in, w_in, k,
+                        s.d_status, c->stream, p->seeded ? 1 : 2);
+    if (p->seeded) launch_sym_a_batch(c->T, s.seeds + r0, L, s.xin + (u64)r0 * w_in + (u64)L * c->N, w_in, k, c->stream);
+  }
+  check_launch("pipe input");
+  check_cuda(cudaEventRecord(s.consumed, c->stream), "pipe");
+  check_cuda(cudaMemcpyAsync(s.h_status, s.d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "pipe status");
+  check_cuda(cudaEventRecord(s.checked, c->stream), "pipe");
+  cnn_forward_dev(m, s.xin, w_in, count, s.yout);
+  if (s.used) check_cuda(cudaStreamWaitEvent(c->stream, s.out_copied, 0), "pipe");
+  for (u32 r0 = 0; r0 < count; r0 += kChunk) {
+    const u32 k = std::min(kChunk, count - r0);
+    launch_pack_batch(c->T, s.yout + (u64)r0 * w_out, w_out, Lo, s.packed + (u64)r0 * p->out_size + kWireHeader,
+                      p->out_size, k, c->stream);
+  }
+  check_launch("pipe output");
+  check_cuda(cudaMemcpyAsync(s.h_kerr, c->T.kerr, sizeof(u32), cudaMemcpyDeviceToHost, c->stream), "pipe status");
+  check_cuda(cudaEventRecord(s.packed_ev, c->stream), "pipe");
+  s.host_out = host_out;
+  s.ticket = p->next++;
+  *ticket = s.ticket;
+  CNN_END
+}
+
+tcks_status tcks_cnn_pipe_wait(tcks_cnn_pipe* p, uint64_t ticket) {
+  CNN_BEGIN
+  if (!p) fail(TCKS_ERR_INVALID_ARG, "null pipe");
+  tcks_cnn_pipe::Slot& s = p->slot[ticket & 1];
+  if (ticket == 0 || ticket >= p->next) fail(TCKS_ERR_INVALID_ARG, "unknown ticket");
+  if (s.ticket != ticket) return TCKS_OK;  // completed and reported already (its slot holds a later batch)
+  pipe_finish(p, s);
+  CNN_END
+}
+
+void tcks_cnn_pipe_free(tcks_cnn_pipe* p) { pipe_release(p); }
+
+}  // extern "C"
+
 // -------------------------------------------------------------------------- CUDA graphs ----
 struct tcks_cnn_graph {
   tcks_ctx* ctx;  // retained: the graph's buffers belong to it

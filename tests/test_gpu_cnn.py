@@ -440,6 +440,54 @@ def test_cnn_forward_wire_equals_batch(setup):
     assert host_out[:out_size].tobytes() == want[0]
 
 
+def test_cnn_pipe_equals_forward_wire(setup):
+    """tcks_cnn_pipe_*: five batches of serialized inputs submitted two ahead of their waits (each
+    slot reused, submits completing earlier batches) give tcks_cnn_forward_wire's bytes for each batch;
+    a batch with a residue above its prime is refused by the call that completes it and leaves its
+    output buffer untouched, and the pipe goes on."""
+    from oracle import wire
+    o, w, enc, ctx, model, need = setup
+    full, seeded, out_size = model.wire_sizes()
+    L = o.L
+    batches = []
+    for b in range(5):
+        img = inputs.mnist_like_image(20 + b)
+        v, W = oracle.OracleCKKS.im2col(img, 7, 7, 3, o.slots)
+        pt = o.encode(v)
+        bufs = [wire.serialize_seeded(o.encrypt_symmetric(pt, 800 + 10 * b + i, 90 + i).data[0], L, o.scale, o.log_n,
+                                      o.primes, 800 + 10 * b + i) for i in range(2)]
+        host_in = torch.from_numpy(np.frombuffer(b"".join(bufs), dtype=np.uint8).copy()).pin_memory().numpy()
+        want = np.zeros(2 * out_size, dtype=np.uint8)
+        model.forward_wire(host_in, 2, want)
+        batches.append((host_in, want))
+    pipe = model.pipe(2, seeded)
+    outs = [torch.zeros(2 * out_size, dtype=torch.uint8).pin_memory().numpy() for _ in batches]
+    tickets = []
+    for b, (host_in, _) in enumerate(batches):
+        tickets.append(pipe.submit(host_in, outs[b]))
+        if b >= 1:
+            pipe.wait(tickets[b - 1])
+    pipe.wait(tickets[-1])
+    for b, (_, want) in enumerate(batches):
+        assert np.array_equal(outs[b], want), b
+    pipe.wait(tickets[0])  # long completed
+    bad = batches[1][0].copy()
+    bad[2 * seeded - 4:2 * seeded] = 0xFF  # the last residue of the second input's c0 above its prime
+    bad = torch.from_numpy(bad).pin_memory().numpy()
+    dirty = torch.full((2 * out_size,), 0xAB, dtype=torch.uint8).pin_memory().numpy()
+    t = pipe.submit(bad, dirty)
+    with pytest.raises(tk.TcksError) as e:
+        pipe.wait(t)
+    assert e.value.name == "INVALID_ARG"
+    assert np.all(dirty == 0xAB), "a refused batch wrote into its output buffer"
+    again = np.zeros(2 * out_size, dtype=np.uint8)
+    pipe.wait(pipe.submit(batches[2][0], again))
+    assert np.array_equal(again, batches[2][1])
+    with pytest.raises(tk.TcksError):
+        model.pipe(2, seeded - 1)  # no serialized input size
+    del pipe
+
+
 def test_cnn_autotune_is_bit_identical(setup, tmp_path):
     """The network autotuner (limb-kernel CTA size x accumulation requests per thread, timed on the
     batched forward pass) changes only the launch shape: the batch's outputs are bit-identical before
