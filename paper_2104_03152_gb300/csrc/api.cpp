@@ -170,7 +170,18 @@ const KeyTable& key_table(tcks_ctx* c, const std::vector<u32>& steps, u32 ell) {
         h[i] = KsKey{c->rlk, c->L, 1u};
       } else {
         const GaloisKey& gk = galois_key_for(c, steps[i], 1);
-        h[i] = KsKey{gk.d, gk.K, (u32)galois_element(c->params.log_n, steps[i])};
+        h[i] = KsKey{gk.d, gk.K, (u32)galois_element(c->params.log_n, steps[i]), nullptr};
+        if (c->T.narrow) {  // the double-hoisted accumulation reads the key's 32-bit copy
+          auto nk = c->narrow_keys.find(gk.d);
+          if (nk == c->narrow_keys.end()) {
+            const u64 words = ksk_words(c, gk.K);
+            u32* d32 = (u32*)c->dev_alloc(words * 4);
+            launch_narrow_copy(gk.d, d32, words, c->stream);
+            check_launch("32-bit key copy");
+            nk = c->narrow_keys.emplace(gk.d, std::make_pair(d32, words)).first;
+          }
+          h[i].key32 = nk->second.first;
+        }
       }
       min_K = h[i].K < min_K ? h[i].K : min_K;
     }
@@ -178,6 +189,8 @@ const KeyTable& key_table(tcks_ctx* c, const std::vector<u32>& steps, u32 ell) {
     t.n = (u32)h.size();
     t.min_K = min_K;
     for (const KsKey& k : h) t.max_K = k.K > t.max_K ? k.K : t.max_K;
+    t.keys32 = true;
+    for (const KsKey& k : h) t.keys32 = t.keys32 && k.key32 != nullptr;
     t.aligned16 = true;
     for (const KsKey& k : h) t.aligned16 = t.aligned16 && ((uintptr_t)k.key & 15) == 0;
     t.d = (KsKey*)c->dev_alloc(sizeof(KsKey) * h.size());
@@ -437,13 +450,16 @@ void arena_release(tcks_ctx* c, char* block) {
 void tcks_ctx::keys_changed() {
   for (auto& kv : key_tables) dev_free(kv.second.d);
   key_tables.clear();
+  for (auto& kv : narrow_keys) dev_free(kv.second.first);
+  narrow_keys.clear();
 }
 
 tcks::u64 tcks_ctx::key_bytes() const {
   u64 b = 0;
   const u64 n = N;
   b += (u64)(L + K) * n * 8 + (u64)2 * L * n * 8 + ksk_words(this, L) * 8;
-  for (const auto& kv : galois) b += ksk_words(this, kv.second.K) * 8;
+  // with 32-bit chains each Galois key may also hold its 32-bit copy (made with the key tables)
+  for (const auto& kv : galois) b += ksk_words(this, kv.second.K) * (T.narrow ? 12 : 8);
   return b;
 }
 

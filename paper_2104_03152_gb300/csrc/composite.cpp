@@ -48,6 +48,7 @@ static void op_vecmat_dh(tcks_ctx* c, u64* ct, u64 cw, u32 count, u32 ell, const
   p.keys = kt->d;
   p.keys_aligned = kt->aligned16;
   p.keys_K = kt->min_K == kt->max_K ? kt->min_K : 0;
+  p.keys32 = kt->keys32;
   p.digits = digits.p;
   p.digits_b = (u64)ell * (ell + 1) * n;
   p.ct = ct;
@@ -113,6 +114,7 @@ void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const st
   p.keys = kt.d;
   p.keys_aligned = kt.aligned16;
   p.keys_K = kt.min_K == kt.max_K ? kt.min_K : 0;
+  p.keys32 = kt.keys32;
   p.digits = digits.p;
   p.digits_b = (u64)ell * (ell + 1) * n;
   p.ct = x;
@@ -158,6 +160,7 @@ void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, cons
   p.keys = kt.d;
   p.keys_aligned = kt.aligned16;
   p.keys_K = kt.min_K == kt.max_K ? kt.min_K : 0;
+  p.keys32 = kt.keys32;
   p.digits = digits.p;
   p.digits_b = (u64)ell * (ell + 1) * n;
   p.ct = x;

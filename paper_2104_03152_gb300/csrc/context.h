@@ -36,6 +36,7 @@ struct KeyTable {
   u32 min_K = 0;  // smallest key level in the table
   u32 max_K = 0;  // largest key level in the table
   bool aligned16 = false;  // every key starts on a 16-byte boundary
+  bool keys32 = false;     // every key has a 32-bit copy (32-bit chains)
 };
 
 // A profiler range around one ABI call (or one stage of a served request group), visible in Nsight
@@ -88,6 +89,9 @@ struct tcks_ctx {
   tcks::u64* rlk = nullptr;  // [L][2][L+1][N], or with hybrid key switching [dnum(L)][2][L+K][N]
   std::map<tcks::u32, tcks::GaloisKey> galois;  // step mod N/2 -> key
   std::map<std::vector<tcks::u32>, tcks::KeyTable> key_tables;  // cached device key tables
+  // 32-bit copies of Galois keys (chains of primes below 2^31), made with the key tables that use them
+  // and dropped with them: key -> (copy, words)
+  std::map<const tcks::u64*, std::pair<tcks::u32*, tcks::u64>> narrow_keys;
   tcks::u64 table_bytes = 0;
   // References: the caller's handle plus every object made from the context (ciphertexts,
   // plaintexts, matrices, models, graphs). The context is destroyed when the last one goes.

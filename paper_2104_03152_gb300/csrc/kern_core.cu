@@ -10,6 +10,7 @@
 // rotations), so one launch carries a whole batch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -519,6 +520,20 @@ void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_outer,
 // a * b mod q: the 64-bit Barrett of the product when every prime is below 2^31, else the 128-bit one
 __device__ __forceinline__ u64 mulq(u64 a, u64 b, const ModConst& m, u32 narrow) {
   return narrow ? reduce64(a * b, m) : mul_mod(a, b, m);
+}
+
+// ------------------------------------------------------------------ 32-bit copies of keys ----
+void count_launch();
+
+__global__ void k_narrow_copy(const u64* __restrict__ src, u32* __restrict__ dst, u64 n) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) dst[i] = (u32)src[i];
+}
+
+void launch_narrow_copy(const u64* src, u32* dst, u64 n, cudaStream_t st) {
+  if (!n) return;
+  const u64 blocks = std::min<u64>((n + 255) / 256, 152ull * 16);
+  count_launch();
+  k_narrow_copy<<<(u32)blocks, 256, 0, st>>>(src, dst, n);
 }
 
 // ------------------------------------------------------------------------ element-wise ops ----

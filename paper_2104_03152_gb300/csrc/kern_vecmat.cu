@@ -78,6 +78,8 @@ __global__ void __launch_bounds__(kDhThreads, (KO > 1 || LOGN > 0) ? 3 : 1) k_ve
     const u32 key_slot = i < ell ? i : kK;
     const u64* dk = unit ? nullptr : p.diag + (u64)(r + 1) * p.diag_stride + (u64)(i < ell ? i : p.p_limb) * n;
     const u64* k0 = kk.key + (u64)key_slot * n;     // digit j's component b at + (2j + b) (K+1) n
+    // LOGN > 0 (32-bit words): the key's 32-bit copy, half the bytes (the host checked it exists)
+    const u32* k32 = LOGN > 0 ? kk.key32 + (u64)key_slot * n : nullptr;
     const u64 kstep = (u64)(kK + 1) * n;
 #pragma unroll
     for (int e = 0; e < EPT; ++e) {
@@ -87,7 +89,14 @@ __global__ void __launch_bounds__(kDhThreads, (KO > 1 || LOGN > 0) ? 3 : 1) k_ve
         KsSum<W, ELL> s0[RPT], s1[RPT];
 #pragma unroll
         for (u32 j = 0; j < ell; ++j) {
-          const u64 w0 = k0[2 * j * kstep + g], w1 = k0[(2 * j + 1) * kstep + g];
+          u64 w0, w1;
+          if constexpr (LOGN > 0) {
+            w0 = k32[2 * j * kstep + g];
+            w1 = k32[(2 * j + 1) * kstep + g];
+          } else {
+            w0 = k0[2 * j * kstep + g];
+            w1 = k0[(2 * j + 1) * kstep + g];
+          }
 #pragma unroll
           for (int rr = 0; rr < RPT; ++rr) {
             const u64 d = digits[rr][(u64)j * slots * n + src];
@@ -373,10 +382,10 @@ static decltype(&k_vecmat_dh_moddown_rs<u64, 0>) const K6_k_vecmat_dh_moddown_rs
 // With 32-bit words at N = 2^13 and every key at the plan's level, the ring size is fixed as well; with
 // the keys sharing a level above the plan's (two requests per thread, one output), the ring size alone.
 static bool dh_fixed_ring(const DevTables& T, u32 ell, const VecmatDhPlan& p) {
-  return T.narrow && T.log_n == 13 && p.keys_K == ell && ell >= 1 && ell <= 8;
+  return T.narrow && T.log_n == 13 && p.keys_K == ell && p.keys32 && ell >= 1 && ell <= 8;
 }
 static bool dh_fixed_ring_keys_above(const DevTables& T, u32 ell, const VecmatDhPlan& p, u32 rpt, u32 outs) {
-  return T.narrow && T.log_n == 13 && p.keys_K > ell && ell >= 1 && ell <= 8 && rpt == 2 && outs == 1;
+  return T.narrow && T.log_n == 13 && p.keys_K > ell && p.keys32 && ell >= 1 && ell <= 8 && rpt == 2 && outs == 1;
 }
 
 template <typename W, int EPT, int RPT, int KO>
@@ -419,20 +428,21 @@ u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow, u32 outs, u32 rp
 void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st) {
   const double n = (double)(1u << T.log_n);
   const double wd = T.narrow ? 0.5 : 1.0;  // digit words in 8-byte units
+  const u32 outs = dh_outs(p);
+  const bool bulk = dh_bulk_applies(T, ell, p);
+  const bool fixed_ring = dh_fixed_ring(T, ell, p) ||
+                          dh_fixed_ring_keys_above(T, ell, p, dh_rpt_of(T.narrow, outs, T.dh_rpt), outs);
+  const double kw = !bulk && fixed_ring ? 0.5 : 1.0;  // the fixed-ring forms read the keys' 32-bit copies
   const double by = 8.0 * n *
                     ((double)p.B * (wd * ell * (ell + 1.0) + ell) +
-                     (double)p.R * (2.0 * ell * (ell + 1.0) + (p.diag ? ell + 1.0 : 0.0)) +
+                     (double)p.R * (kw * 2.0 * ell * (ell + 1.0) + (p.diag ? ell + 1.0 : 0.0)) +
                      (double)p.B * p.chunks * (3.0 * ell + 2.0));
-  const u32 outs = dh_outs(p);
   if ((outs != 1 && outs != 4) || (outs > 1 && !p.diag))
     fail(TCKS_ERR_UNSUPPORTED, "double-hoisted sums take 1 or 4 outputs per request (4 with diagonals)");
   // product-accumulates per (request, rotation, element): the key-switch sums 2 ell (ell + 1), then per
   // output the two components' and the c0 term's diagonal products (additions for unit diagonals)
   const double ops = (double)p.B * p.R * n * (2.0 * ell * (ell + 1.0) + outs * (2.0 * (ell + 1.0) + ell));
-  const bool bulk = dh_bulk_applies(T, ell, p);
   // profiler tag: level, outputs, unit diagonals (bit 16), staged operands (bit 17), fixed ring size (bit 18)
-  const bool fixed_ring = dh_fixed_ring(T, ell, p) ||
-                          dh_fixed_ring_keys_above(T, ell, p, dh_rpt_of(T.narrow, outs, T.dh_rpt), outs);
   Launch L(K_VECMAT_DH, st, by + 8.0 * n * (outs - 1.0) * (p.R * (ell + 1.0) + p.B * p.chunks * (3.0 * ell + 2.0)), ops,
            ell | (outs << 8) | ((p.diag ? 0u : 1u) << 16) | ((bulk ? 1u : 0u) << 17) |
                ((!bulk && fixed_ring ? 1u : 0u) << 18));

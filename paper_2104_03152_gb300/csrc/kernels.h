@@ -127,7 +127,10 @@ struct KsKey {
   const u64* key;
   u32 K;
   u32 g;
+  const u32* key32;  // the same key's words as 32-bit words (32-bit chains, made with the key table), or null
 };
+// 32-bit copy of n 64-bit words whose values fit 32 bits (keys of a chain of primes below 2^31).
+void launch_narrow_copy(const u64* src, u32* dst, u64 n, cudaStream_t st);
 // B requests x R key switches of hoisted digits. Request rq, rotation r: digits + rq*digits_b,
 // key keys[r] (device array), P-limb scratch top [R][B][2][N], output out + rq*out_b + r*out_r
 // ([2][ell][N]), addends add0 + rq*add0_b / add1 + rq*add1_b ([ell][N], read through the
@@ -203,6 +206,8 @@ struct VecmatDhPlan {
   u32 p_limb, outs;
   u32 keys_aligned;  // every key of `keys` starts on a 16-byte boundary (bulk copies may read it)
   u32 keys_K;        // the level of every key of `keys` when they share one, else 0
+  u32 keys32;        // every key of `keys` has its 32-bit copy (key32)
+  u32 pad;
 };
 // Outputs per request of a plan (1 or 4).
 __host__ __device__ inline u32 dh_outs(const VecmatDhPlan& p) { return p.outs > 1 ? p.outs : 1; }
