@@ -298,6 +298,46 @@ void op_rotate_add(tcks_ctx* c, u64* base, u64 stride, u32 count, u32 ell, int32
   check_launch("rotate-add");
 }
 
+void op_rotate_add_to(tcks_ctx* c, const u64* in, u64 in_stride, u32 count, u32 ell, int32_t step, u64* out,
+                      u64 out_stride, const u64* bias) {
+  need_one_prime_ks(c, "the fused rotate-and-add");
+  const size_t n = c->N;
+  const u64 w = ct_words(c, ell);
+  if (count > 1 && (in_stride < w || out_stride < w)) fail(TCKS_ERR_INVALID_ARG, "rotate-add: overlapping batch entries");
+  const u64 in_end = (count - 1) * in_stride + w, out_end = (count - 1) * out_stride + w;
+  if (out < in + in_end && in < out + out_end) fail(TCKS_ERR_INVALID_ARG, "rotate-add: out overlaps in");
+  const u32 k = step_mod(c, step);
+  if (k == 0) {  // rot by 0 is the identity: out = 2 in (+ bias)
+    for (u32 i = 0; i < count; ++i) {
+      launch_elementwise(c->T, OP_ADD, in + i * in_stride, in + i * in_stride, out + i * out_stride, ell, 2, c->stream);
+      if (bias) launch_elementwise(c->T, OP_ADD_PLAIN, out + i * out_stride, bias, out + i * out_stride, ell, 2, c->stream);
+    }
+    return;
+  }
+  const KeyTable& kt = key_table(c, {k}, ell);
+  const u64 dw = ks_digit_words(c, ell);
+  DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * dw);
+  DevBuf top(c, (size_t)count * ks_top_words(c));
+  ks_modup(c, in + (size_t)ell * n, in_stride, count, ell, coef.p, digits.p);
+  KsPlan p{};
+  p.keys = kt.d;
+  p.digits = digits.p;
+  p.digits_b = dw;
+  p.top = top.p;
+  p.out = out;
+  p.out_b = out_stride;
+  p.add0 = in;  // the automorphed c0 of in
+  p.add0_b = in_stride;
+  p.add_perm = 1;
+  p.addx = in;  // in itself, both components
+  p.addx_b = in_stride;
+  p.addp = bias;
+  p.R = 1;
+  p.B = count;
+  launch_keyswitch(c->T, ell, p, c->stream);
+  check_launch("rotate-add");
+}
+
 void op_rotate_hoisted(tcks_ctx* c, const u64* ct, u32 ell, const int32_t* steps, u32 n_steps, u64* const* outs) {
   const size_t n = c->N;
   std::vector<u32> ks;

@@ -147,23 +147,23 @@ void cnn_stage(const tcks_cnn* m, u32 stage, const u64* x, u32 count, u64* out) 
       if (m->fold) {  // one sum over the folded diagonals is the packed vector [L-1]
         const u32 nb = (u32)m->baby.size() + 1;
         const u64 dstride = (u64)(L + 1) * c->N;
-        DevBuf z(c, (size_t)count * w1);
         if (c->flags & TCKS_MERGED_RESCALE) {
-          op_dh_sum_multi(c, x, w_in, count, L, m->baby, m->fold_ext, dstride, dstride * nb, L, 1, z.p, w1,
-                          (u64)count * w1, true);
+          // the ModDown, the rescale and the modulus switch [L-2] in one pass: the limb the switch
+          // drops is never formed
+          op_dh_sum_multi(c, x, w_in, count, L, m->baby, m->fold_ext, dstride, dstride * nb, L, 1, out, w2,
+                          (u64)count * w2, true, L - 2);
         } else {
-          DevBuf zz(c, (size_t)count * w_in);
+          DevBuf z(c, (size_t)count * w1), zz(c, (size_t)count * w_in);
           op_dh_sum_multi(c, x, w_in, count, L, m->baby, m->fold_ext, dstride, dstride * nb, L, 1, zz.p, w_in,
                           (u64)count * w_in);
           op_rescale(c, zz.p, L, z.p, count);
+          // modulus switch [L-2]: each polynomial keeps its first L-2 limbs
+          const size_t limb = (size_t)c->N * 8;
+          check_cuda(cudaMemcpy2DAsync(out, (L - 2) * limb, z.p, (L - 1) * limb, (L - 2) * limb, 2 * (size_t)count,
+                                       cudaMemcpyDeviceToDevice, c->stream),
+                     "modulus switch");
         }
-        // modulus switch [L-2]: each polynomial keeps its first L-2 limbs
-        const size_t limb = (size_t)c->N * 8;
-        check_cuda(cudaMemcpy2DAsync(out, (L - 2) * limb, z.p, (L - 1) * limb, (L - 2) * limb, 2 * (size_t)count,
-                                     cudaMemcpyDeviceToDevice, c->stream),
-                   "modulus switch");
-        op_rotsum_hoisted(c, out, w2, count, L - 2, m->giant, out);
-        launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[0], out, L - 2, 2 * count, c->stream);
+        op_rotsum_hoisted(c, out, w2, count, L - 2, m->giant, out, m->bias[0]);  // + bias in the ModDown
         break;
       }
       // conv [L-1]: channel k of request r at chans + (k * count + r) * w1
@@ -220,23 +220,23 @@ void cnn_stage(const tcks_cnn* m, u32 stage, const u64* x, u32 count, u64* out) 
           if (k) launch_elementwise(c->T, OP_ADD, out, t.p, out, L - 2, 2 * count, c->stream);
         }
       }
-      if (m->pack_first) op_rotsum_hoisted(c, out, w2, count, L - 2, m->giant, out);
-      launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[0], out, L - 2, 2 * count, c->stream);
+      if (m->pack_first)
+        op_rotsum_hoisted(c, out, w2, count, L - 2, m->giant, out, m->bias[0]);
+      else
+        launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[0], out, L - 2, 2 * count, c->stream);
       break;
     }
     case 1:
       square_stage(c, x, L - 2, count, out);
       break;
     case 2:
-      op_vecmat(c, x, ct_words(c, L - 3), count, L - 3, m->fc1, out, m->period);
-      launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[1], out, L - 4, 2 * count, c->stream);
+      op_vecmat(c, x, ct_words(c, L - 3), count, L - 3, m->fc1, out, m->period, m->bias[1]);
       break;
     case 3:
       square_stage(c, x, L - 4, count, out);
       break;
     case 4:
-      op_vecmat(c, x, ct_words(c, L - 5), count, L - 5, m->fc2, out, m->rect ? m->fc2->rows : 0);
-      launch_elementwise(c->T, OP_ADD_PLAIN, out, m->bias[2], out, L - 6, 2 * count, c->stream);
+      op_vecmat(c, x, ct_words(c, L - 5), count, L - 5, m->fc2, out, m->rect ? m->fc2->rows : 0, m->bias[2]);
       break;
     default:
       fail(TCKS_ERR_INVALID_ARG, "no such stage");

@@ -32,7 +32,7 @@ void op_sum(tcks_ctx* c, u64* ct, u32 ell) {
 // key-switch inner products times the extended-basis diagonals (k_vecmat_dh_acc), the fold of its
 // chunk partials, INTT of the P limbs, one ModDown per (request, component, prime) with the k = 0
 // term and tau(c0) part added (k_vecmat_dh_moddown), and the rescale. No transform runs per rotation.
-static void op_vecmat_dh(tcks_ctx* c, u64* ct, u64 cw, u32 count, u32 ell, const tcks_matrix* M, const KeyTable* kt,
+static void op_vecmat_dh(tcks_ctx* c, const u64* ct, u64 cw, u32 count, u32 ell, const tcks_matrix* M, const KeyTable* kt,
                          u64* out) {
   const size_t n = c->N;
   const u32 R = M->diags - 1;
@@ -65,9 +65,9 @@ static void op_vecmat_dh(tcks_ctx* c, u64* ct, u64 cw, u32 count, u32 ell, const
   launch_vecmat_dh_fold(c->T, ell, p, c->stream);
   DevBuf top(c, (size_t)2 * count * n);
   const u64 per_rq = (u64)chunks * 3 * (ell + 1) * n;
-  for (u32 b = 0; b < 2; ++b)
-    launch_ntt(c->T, true, partial.p + ((u64)b * (ell + 1) + ell) * n, per_rq, top.p + (u64)b * count * n, n, count,
-               c->L, 1, c->stream);
+  // the P limb of both components, one launch
+  launch_ntt(c->T, true, partial.p + (u64)ell * n, per_rq, top.p, n, count, c->L, 1, c->stream, 2, (u64)(ell + 1) * n,
+             (u64)count * n);
   if (c->flags & TCKS_MERGED_RESCALE) {  // ModDown and rescale in one rounding
     DevBuf top2(c, (size_t)2 * count * n);
     launch_vecmat_dh_moddown_rs(c->T, c->host, ell, p, top.p, top2.p, out, ct_words(c, ell - 1), c->stream);
@@ -85,7 +85,8 @@ static void vecmat_single_hoisted(tcks_ctx* c, const u64* ct, u64 cw, u32 count,
 // x + sum over `steps` of rot(x, s) for `count` ciphertexts [count][2][ell][N] (stride cw), with one
 // ModUp and one ModDown per ciphertext: the double-hoisted accumulation with unit diagonals. out may
 // alias x. The scale is unchanged.
-void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const std::vector<int32_t>& steps, u64* out) {
+void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const std::vector<int32_t>& steps, u64* out,
+                       const u64* bias) {
   need_one_prime_ks(c, "the hoisted rotation sum");
   const size_t n = c->N;
   std::vector<u32> ks;
@@ -99,6 +100,9 @@ void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const st
       for (u32 i = 0; i < count; ++i)
         check_cuda(cudaMemcpyAsync(out + i * cw, x + i * cw, ct_words(c, ell) * 8, cudaMemcpyDeviceToDevice, c->stream),
                    "copy");
+    if (bias)
+      for (u32 i = 0; i < count; ++i)
+        launch_elementwise(c->T, OP_ADD_PLAIN, out + i * cw, bias, out + i * cw, ell, 2, c->stream);
     return;
   }
   const KeyTable& kt = key_table(c, ks, ell);
@@ -120,6 +124,7 @@ void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const st
   p.ct = x;
   p.ct_b = cw;
   p.diag = nullptr;  // unit diagonals
+  p.addp = bias;
   p.partial = partial.p;
   p.R = R;
   p.B = count;
@@ -129,17 +134,18 @@ void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const st
   launch_vecmat_dh_fold(c->T, ell, p, c->stream);
   DevBuf top(c, (size_t)2 * count * n);
   const u64 per_rq = (u64)chunks * 3 * (ell + 1) * n;
-  for (u32 b = 0; b < 2; ++b)
-    launch_ntt(c->T, true, partial.p + ((u64)b * (ell + 1) + ell) * n, per_rq, top.p + (u64)b * count * n, n, count,
-               c->L, 1, c->stream);
+  // the P limb of both components, one launch
+  launch_ntt(c->T, true, partial.p + (u64)ell * n, per_rq, top.p, n, count, c->L, 1, c->stream, 2, (u64)(ell + 1) * n,
+             (u64)count * n);
   launch_vecmat_dh_moddown(c->T, ell, p, top.p, out, cw, c->stream);
   check_launch("hoisted rotation sum");
 }
 
 void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, const std::vector<int32_t>& steps,
                      const u64* diags, u64 diag_stride, u64 set_stride, u32 p_limb, u32 outs, u64* out, u64 out_b,
-                     u64 out_o, bool merged) {
+                     u64 out_o, bool merged, u32 keep) {
   need_one_prime_ks(c, "the double-hoisted rotation sum");
+  if (keep && (!merged || keep > ell - 1)) fail(TCKS_ERR_INVALID_ARG, "keep: a merged rescale to at most ell - 1 limbs");
   const size_t n = c->N;
   std::vector<u32> ks;
   for (int32_t st : steps) {
@@ -170,6 +176,7 @@ void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, cons
   p.diag_set = set_stride;
   p.p_limb = p_limb;
   p.outs = outs;
+  p.keep = keep;
   p.partial = partial.p;
   p.R = R;
   p.B = count;
@@ -180,9 +187,8 @@ void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, cons
   const u32 ro = count * outs;
   DevBuf top(c, (size_t)2 * ro * n);
   const u64 per_ro = (u64)chunks * 3 * (ell + 1) * n;
-  for (u32 b = 0; b < 2; ++b)
-    launch_ntt(c->T, true, partial.p + ((u64)b * (ell + 1) + ell) * n, per_ro, top.p + (u64)b * ro * n, n, ro, c->L, 1,
-               c->stream);
+  launch_ntt(c->T, true, partial.p + (u64)ell * n, per_ro, top.p, n, ro, c->L, 1, c->stream, 2, (u64)(ell + 1) * n,
+             (u64)ro * n);
   if (merged) {
     DevBuf top2(c, (size_t)2 * ro * n);
     launch_vecmat_dh_moddown_rs(c->T, c->host, ell, p, top.p, top2.p, out, out_b, c->stream, outs > 1 ? out_o : 0);
@@ -193,7 +199,7 @@ void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, cons
 }
 
 void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell, const tcks_matrix* M, u64* out,
-               u32 input_period) {
+               u32 input_period, const u64* bias) {
   need_one_prime_ks(c, "the vector x matrix product");
   const bool dh = (c->flags & TCKS_DOUBLE_HOIST) != 0;
   if (dh && !M->ext)
@@ -214,25 +220,54 @@ void op_vecmat(tcks_ctx* c, const u64* ct_in, u64 ct_stride, u32 count, u32 ell,
   for (int32_t s : rep) galois_key_for(c, s, ell);  // validate before launching anything
   for (int32_t s : chain) galois_key_for(c, s, ell - 1);
   const KeyTable* kt = steps.empty() ? nullptr : &key_table(c, steps, ell);
-  DevBuf ct(c, (size_t)count * cw);
-  if (ct_stride == cw || count == 1) {
-    check_cuda(cudaMemcpyAsync(ct.p, ct_in, (size_t)count * cw * 8, cudaMemcpyDeviceToDevice, c->stream), "copy");
-  } else {
-    for (u32 i = 0; i < count; ++i)
-      check_cuda(cudaMemcpyAsync(ct.p + i * cw, ct_in + i * ct_stride, cw * 8, cudaMemcpyDeviceToDevice, c->stream),
-                 "copy");
+  const u64 out_w = ct_words(c, ell - 1);
+  const u64 in_s = count > 1 ? ct_stride : cw;
+  // The sums read x: the input itself when nothing replicates it and it is laid out as the sums need
+  // (the input is read-only there), else its replica. The first rotate-and-add of the replication
+  // reads the input and writes the replica.
+  DevBuf ct;
+  const u64* x = ct_in;
+  const bool overlap = out < ct_in + (count - 1) * in_s + cw && ct_in < out + (count - 1) * out_w + out_w;
+  if (!rep.empty() && in_s >= cw) {
+    ct = DevBuf(c, (size_t)count * cw);
+    op_rotate_add_to(c, ct_in, in_s, count, ell, rep[0], ct.p, cw);
+    for (size_t k = 1; k < rep.size(); ++k) op_rotate_add(c, ct.p, cw, count, ell, rep[k]);
+    x = ct.p;
+  } else if (!rep.empty() || steps.empty() || overlap || in_s != cw) {
+    ct = DevBuf(c, (size_t)count * cw);
+    if (in_s == cw) {
+      check_cuda(cudaMemcpyAsync(ct.p, ct_in, (size_t)count * cw * 8, cudaMemcpyDeviceToDevice, c->stream), "copy");
+    } else {
+      for (u32 i = 0; i < count; ++i)
+        check_cuda(cudaMemcpyAsync(ct.p + i * cw, ct_in + i * in_s, cw * 8, cudaMemcpyDeviceToDevice, c->stream),
+                   "copy");
+    }
+    for (int32_t s : rep) op_rotate_add(c, ct.p, cw, count, ell, s);
+    x = ct.p;
   }
-  for (int32_t s : rep) op_rotate_add(c, ct.p, cw, count, ell, s);
   if (steps.empty()) {
     DevBuf acc(c, (size_t)count * cw);
-    launch_elementwise(c->T, OP_MUL_PLAIN, ct.p, M->d, acc.p, ell, 2 * count, c->stream);
+    launch_elementwise(c->T, OP_MUL_PLAIN, x, M->d, acc.p, ell, 2 * count, c->stream);
     op_rescale(c, acc.p, ell, out, count);
   } else if (dh) {
-    op_vecmat_dh(c, ct.p, cw, count, ell, M, kt, out);
+    op_vecmat_dh(c, x, cw, count, ell, M, kt, out);
   } else {
-    vecmat_single_hoisted(c, ct.p, cw, count, ell, M, kt, out);
+    vecmat_single_hoisted(c, x, cw, count, ell, M, kt, out);
   }
-  for (int32_t w : chain) op_rotate_add(c, out, ct_words(c, ell - 1), count, ell - 1, w);
+  // The rotate-and-add chain alternates between out and a scratch so that its last step writes out
+  // (adding the bias in the same epilogue); an odd chain takes its first step in place.
+  size_t k = 0;
+  if (chain.size() % 2) op_rotate_add(c, out, out_w, count, ell - 1, chain[k++]);
+  if (k < chain.size()) {
+    DevBuf tmp(c, (size_t)count * out_w);
+    for (; k < chain.size(); k += 2) {
+      op_rotate_add_to(c, out, out_w, count, ell - 1, chain[k], tmp.p, out_w);
+      op_rotate_add_to(c, tmp.p, out_w, count, ell - 1, chain[k + 1], out, out_w,
+                       k + 2 == chain.size() ? bias : nullptr);
+    }
+  } else if (bias) {
+    launch_elementwise(c->T, OP_ADD_PLAIN, out, bias, out, ell - 1, 2 * count, c->stream);
+  }
   check_launch("vecmat");
 }
 

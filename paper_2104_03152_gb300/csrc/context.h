@@ -247,6 +247,11 @@ void op_relin_rescale(tcks_ctx* c, const u64* d3, u32 ell, u64* out, u32 count =
 void op_rotate_hoisted(tcks_ctx* c, const u64* ct, u32 ell, const int32_t* steps, u32 n, u64* const* outs);
 // ct_i <- ct_i + rot(ct_i, step) for count ciphertexts at base + i * stride (words).
 void op_rotate_add(tcks_ctx* c, u64* base, u64 stride, u32 count, u32 ell, int32_t step);
+// out_i = in_i + rot(in_i, step) (+ the plaintext bias [ell][N] on component 0, if given) for count
+// ciphertexts in + i in_stride -> out + i out_stride; out must not overlap in. One-prime key switch:
+// the additions ride in the ModDown's epilogue.
+void op_rotate_add_to(tcks_ctx* c, const u64* in, u64 in_stride, u32 count, u32 ell, int32_t step, u64* out,
+                      u64 out_stride, const u64* bias = nullptr);
 const GaloisKey& galois_key_for(tcks_ctx* c, int64_t step, u32 ell);
 // Device key table for `steps` (0 = relinearization key); every key must cover level ell.
 const KeyTable& key_table(tcks_ctx* c, const std::vector<u32>& steps, u32 ell);
@@ -258,17 +263,21 @@ void op_sum(tcks_ctx* c, u64* ct, u32 ell);  // in place
 // input_period: 0, the input holds the vector in slots [0, rows) and zeros elsewhere (replicated over
 // all slots first); P, it already repeats with period P (zeros in [rows, P)): replicated from P down
 // to rows only (P = rows: no replication).
+// bias: a plaintext [ell-1][N] added to component 0 of every output, or null.
 void op_vecmat(tcks_ctx* c, const u64* ct, u64 ct_stride, u32 count, u32 ell, const tcks_matrix* M, u64* out,
-               u32 input_period = 0);
+               u32 input_period = 0, const u64* bias = nullptr);
 void op_conv(tcks_ctx* c, const u64* ct, u32 ell, const u64* kernel_pt, u32 taps, u32 windows, u64* out);
-void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const std::vector<int32_t>& steps, u64* out);
+// x + sum over steps of rot(x, s) (+ the plaintext bias [ell][N] on component 0, if given); out may alias x.
+void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const std::vector<int32_t>& steps, u64* out,
+                       const u64* bias = nullptr);
 // sum_k rot(x, s_k) * d_{o,k} (s_0 = 0, s_k = steps[k-1]) for `count` ciphertexts (stride cw) and `outs`
 // (1 or 4) diagonal sets over the extended basis: set o at diags + o * set_stride, diagonal k at
 // + k * diag_stride, its P limb at p_limb. One ModUp per ciphertext, one ModDown per output; output o
 // of ciphertext r at out + r * out_b + o * out_o ([2][ell][N]); scale x's times the diagonals'.
-// merged: the ModDown and a rescale by q_{ell-1} in one rounding, outputs [2][ell-1][N].
+// merged: the ModDown and a rescale by q_{ell-1} in one rounding, outputs [2][ell-1][N]; keep > 0
+// (merged only): each output component keeps its first `keep` limbs, [2][keep][N] (a modulus switch).
 void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, const std::vector<int32_t>& steps,
                      const u64* diags, u64 diag_stride, u64 set_stride, u32 p_limb, u32 outs, u64* out, u64 out_b,
-                     u64 out_o, bool merged = false);
+                     u64 out_o, bool merged = false, u32 keep = 0);
 
 }  // namespace tcks

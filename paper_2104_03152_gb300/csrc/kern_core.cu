@@ -60,15 +60,15 @@ static double bfly_per_limb(u32 log_n) { return 0.5 * (double)(1u << log_n) * lo
 // Job j: limb (j % per) of entry (j / per): src + (j/per)*src_outer + (j%per)*N, prime mod_base + j%per.
 template <bool INVERSE, typename W, int LC>
 __global__ void k_ntt(DevTables T, const u64* __restrict__ src, u64 src_outer, u64* __restrict__ dst, u64 dst_outer,
-                      u32 mod_base, u32 per) {
+                      u32 mod_base, u32 per, u64 src_y, u64 dst_y) {
   TCKS_SMEM(W);
   const Slice sl = slice_of<LC>(T);
   const u64 n = 1ull << T.log_n;
   const u32 jo = sl.job / per, ji = sl.job % per;
   const u32 mod = mod_base + ji;
   const ModConst m = T.mods[mod];
-  const u64* in = src + jo * src_outer + ji * n + sl.off;
-  u64* out = dst + jo * dst_outer + ji * n + sl.off;
+  const u64* in = src + sl.y * src_y + jo * src_outer + ji * n + sl.off;
+  u64* out = dst + sl.y * dst_y + jo * dst_outer + ji * n + sl.off;
   for (u32 k = 2 * threadIdx.x; k < sl.ns; k += 2 * blockDim.x) {
     const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(in + k);
     s[sw(k)] = (W)v.x;
@@ -86,10 +86,10 @@ __global__ void k_ntt(DevTables T, const u64* __restrict__ src, u64 src_outer, u
   }
 }
 
-static void (*const kNttInv[6])(DevTables, const u64*, u64, u64*, u64, u32, u32) = {
+static void (*const kNttInv[6])(DevTables, const u64*, u64, u64*, u64, u32, u32, u64, u64) = {
     k_ntt<true, u64, 0>, k_ntt<true, u64, 1>, k_ntt<true, u64, 2>,
     k_ntt<true, u32, 0>, k_ntt<true, u32, 1>, k_ntt<true, u32, 2>};
-static void (*const kNttFwd[6])(DevTables, const u64*, u64, u64*, u64, u32, u32) = {
+static void (*const kNttFwd[6])(DevTables, const u64*, u64, u64*, u64, u32, u32, u64, u64) = {
     k_ntt<false, u64, 0>, k_ntt<false, u64, 1>, k_ntt<false, u64, 2>,
     k_ntt<false, u32, 0>, k_ntt<false, u32, 1>, k_ntt<false, u32, 2>};
 
@@ -503,18 +503,23 @@ void launch_ntt_desc(const DevTables& T, bool inverse, const NttDescTable& tab, 
 }
 
 void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_outer, u64* dst, u64 dst_outer, u32 count,
-                u32 mod_base, u32 per, cudaStream_t st) {
-  if (!count) return;
+                u32 mod_base, u32 per, cudaStream_t st, u32 ny, u64 src_y, u64 dst_y) {
+  if (!count || !ny) return;
   if (T.log_n > kSplitLogNs) {
-    const NttJobsStrided jobs{src, dst, src_outer, dst_outer, mod_base, per};
-    launch_ntt_split(T, inverse, jobs, count, st);
+    for (u32 y = 0; y < ny; ++y) {
+      const NttJobsStrided jobs{src + y * src_y, dst + y * dst_y, src_outer, dst_outer, mod_base, per};
+      launch_ntt_split(T, inverse, jobs, count, st);
+    }
     return;
   }
-  Launch L(inverse ? K_NTT_INV : K_NTT_FWD, st, 16.0 * count * (1u << T.log_n), count * bfly_per_limb(T.log_n));
+  const double jobs = (double)count * ny;
+  Launch L(inverse ? K_NTT_INV : K_NTT_FWD, st, 16.0 * jobs * (1u << T.log_n), jobs * bfly_per_limb(T.log_n));
   if (inverse)
-    launch_limb(kNttInv, T.narrow, count, 1, T.log_n, st, T.limb_threads, T, src, src_outer, dst, dst_outer, mod_base, per);
+    launch_limb(kNttInv, T.narrow, count, ny, T.log_n, st, T.limb_threads, T, src, src_outer, dst, dst_outer, mod_base, per,
+                src_y, dst_y);
   else
-    launch_limb(kNttFwd, T.narrow, count, 1, T.log_n, st, T.limb_threads, T, src, src_outer, dst, dst_outer, mod_base, per);
+    launch_limb(kNttFwd, T.narrow, count, ny, T.log_n, st, T.limb_threads, T, src, src_outer, dst, dst_outer, mod_base, per,
+                src_y, dst_y);
 }
 
 // a * b mod q: the 64-bit Barrett of the product when every prime is below 2^31, else the 128-bit one
@@ -798,7 +803,8 @@ extern "C" tcks_status tcks_rescale_noalloc(tcks_ctx* ctx, const uint64_t* d_in,
   ensure_smem((const void*)ntt, smem);  // allocates no device memory
   ensure_smem((const void*)drop, smem);
   count_launch();
-  ntt<<<2, sh.threads, smem, ctx->stream>>>(T, d_in + (u64)(level - 1) * n, (u64)level * n, scratch, n, level - 1, 1);
+  ntt<<<2, sh.threads, smem, ctx->stream>>>(T, d_in + (u64)(level - 1) * n, (u64)level * n, scratch, n, level - 1, 1,
+                                            0, 0);
   count_launch();
   drop<<<2 * (level - 1), sh.threads, smem, ctx->stream>>>(T, d_in, (u64)level * n, scratch, level - 1, level - 1,
                                                              d_out);

@@ -178,6 +178,8 @@ __global__ void k_ks_moddown(DevTables T, u32 ell, const __grid_constant__ KsPla
   }
   const u64* add = b == 0 ? (plan.add0 ? plan.add0 + rq * plan.add0_b : nullptr)
                           : (plan.add1 ? plan.add1 + rq * plan.add1_b : nullptr);
+  const u64* addx = plan.addx ? plan.addx + rq * plan.addx_b + ((u64)b * ell + i) * n : nullptr;
+  const u64* addp = b == 0 && plan.addp ? plan.addp + (u64)i * n : nullptr;
   u64* dst = plan.out + rq * plan.out_b + r * plan.out_r + ((u64)b * ell + i) * n;
   ell_dispatch(ell, [&](auto E) {
     for (u32 k = threadIdx.x; k < sl.ns; k += blockDim.x) {
@@ -186,6 +188,8 @@ __global__ void k_ks_moddown(DevTables T, u32 ell, const __grid_constant__ KsPla
       const u64 u = ks_inner<W, decltype(E)::value>(digits, ell, i, kk.key, kk.K, i, b, g, src, n, mi);
       u64 v = Ew<W>::shoup_inv(sub_mod(u, fwd_fin(s[sw(k)], mi), mi.q), pc, mi);
       if (add) v = add_mod(v, add[(u64)i * n + (plan.add_perm ? src : g)], mi.q);
+      if (addx) v = add_mod(v, addx[g], mi.q);
+      if (addp) v = add_mod(v, addp[g], mi.q);
       dst[g] = v;
     }
   });

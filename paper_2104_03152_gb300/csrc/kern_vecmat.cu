@@ -26,6 +26,19 @@ namespace {
 
 constexpr u32 kDhThreads = 256;
 
+// CTAs per SM the accumulation is compiled for, and rotations whose loads it keeps in flight (32-bit
+// words). The fixed-ring form holds two rotations' operands in registers: from level 6 on that needs
+// more than the 80 registers of three CTAs per SM (it spilled), so those levels take two CTAs per SM;
+// at level 5 one rotation at a time at three CTAs per SM measured faster than either.
+template <int ELL, int KO, int LOGN>
+__host__ __device__ constexpr int dh_min_ctas() {
+  return KO > 1 ? 3 : LOGN > 0 ? (ELL >= 6 ? 2 : 3) : 1;
+}
+template <typename W, int ELL, int LOGN>
+__host__ __device__ constexpr int dh_rot_unroll() {
+  return sizeof(W) == 4 && !(LOGN > 0 && ELL == 5) ? 2 : 1;
+}
+
 
 // Thread = EPT elements (stride kDhThreads) x RPT requests of one slot i: the key limbs, the
 // diagonal and the Galois index of a rotation are loaded once for the RPT requests.
@@ -38,7 +51,7 @@ constexpr u32 kDhThreads = 256;
 // KEYS_AT = false: the keys share one level above ELL (p.keys_K), a run-time value uniform over the
 // launch, so only the key strides are computed.
 template <typename W, int EPT, int RPT, int ELL, int KO = 1, int LOGN = 0, bool KEYS_AT = true>
-__global__ void __launch_bounds__(kDhThreads, (KO > 1 || LOGN > 0) ? 3 : 1) k_vecmat_dh_acc(DevTables T, u32 ell_arg,
+__global__ void __launch_bounds__(kDhThreads, dh_min_ctas<ELL, KO, LOGN>()) k_vecmat_dh_acc(DevTables T, u32 ell_arg,
                                                                const __grid_constant__ VecmatDhPlan p) {
   static_assert(LOGN == 0 || ELL > 0, "a fixed ring size needs a fixed level");
   const u32 ell = ELL > 0 ? (u32)ELL : ell_arg;
@@ -69,7 +82,7 @@ __global__ void __launch_bounds__(kDhThreads, (KO > 1 || LOGN > 0) ? 3 : 1) k_ve
   DhAcc<W> u0[EPT][RPT * KO], u1[EPT][RPT * KO], a0[EPT][RPT * KO];
   const u32 r0 = chunk * p.chunk, r1 = min(p.R, r0 + p.chunk);
   const bool unit = p.diag == nullptr;  // a hoisted rotation sum: every diagonal is 1
-  constexpr int kRotUnroll = sizeof(W) == 4 ? 2 : 1;  // two rotations' loads in flight (32-bit words)
+  constexpr int kRotUnroll = dh_rot_unroll<W, ELL, LOGN>();
 #pragma unroll kRotUnroll
   for (u32 r = r0; r < r1; ++r) {
     const KsKey kk = p.keys[r];
@@ -275,6 +288,7 @@ __global__ void k_vecmat_dh_moddown(DevTables T, u32 ell, const __grid_constant_
     u64 v = Ew<W>::shoup_inv(sub_mod(U[g], fwd_fin(s[sw(k)], mi), mi.q), pc, mi);
     v = add_mod(v, d0 ? Ew<W>::mul(cb[g], d0[g], mi) : cb[g], mi.q);
     if (b == 0) v = add_mod(v, A[g], mi.q);
+    if (b == 0 && p.addp) v = add_mod(v, p.addp[(u64)i * n + g], mi.q);
     dst[g] = v;
   }
 }
@@ -314,8 +328,8 @@ __global__ void k_dh_top_l(DevTables T, u32 ell, const __grid_constant__ VecmatD
 
 constexpr u32 kMdBatch = 4;
 
-// Stage 2: out_b[i] = (Z_b[i] - NTT_i([Z_b]_{P q_l} mod q_i)) (P q_l)^-1, i < ell - 1; limb job =
-// (b (ell - 1) + i) * B * outs + request * outs + output; top [2][B * outs][N] holds INTT_P(U_b[P]).
+// Stage 2: out_b[i] = (Z_b[i] - NTT_i([Z_b]_{P q_l} mod q_i)) (P q_l)^-1, i < kp (kp = p.keep, else ell - 1);
+// limb job = (b kp + i) * B * outs + request * outs + output; top [2][B * outs][N] holds INTT_P(U_b[P]).
 template <typename W, int LC>
 __global__ void k_vecmat_dh_moddown_rs(DevTables T, u32 ell, const __grid_constant__ VecmatDhPlan p, const u64* top,
                                        const u64* top2, Crt2 k2, u64* out, u64 out_b, u64 out_o) {
@@ -323,8 +337,8 @@ __global__ void k_vecmat_dh_moddown_rs(DevTables T, u32 ell, const __grid_consta
   const Slice sl = slice_of<LC>(T);
   const u32 log_n = T.log_n;
   const u64 n = 1ull << log_n;
-  const u32 outs = dh_outs(p), bo = p.B * outs, lo = ell - 1;
-  const u32 ro = sl.job % bo, bi = sl.job / bo, b = bi / lo, i = bi % lo;
+  const u32 outs = dh_outs(p), bo = p.B * outs, lo = ell - 1, kp = p.keep ? p.keep : lo;
+  const u32 ro = sl.job % bo, bi = sl.job / bo, b = bi / kp, i = bi % kp;
   const u32 rq = ro / outs, o = ro % outs;
   const ModConst mi = T.mods[i], ml = T.mods[lo];
   const PairConst pp = T.pairs[(u64)T.L * T.n_mods + i];  // P mod q_i, P^-1 mod q_i
@@ -343,7 +357,7 @@ __global__ void k_vecmat_dh_moddown_rs(DevTables T, u32 ell, const __grid_consta
   const u64* A = p.partial + dh_off(ro, 0, p.chunks, 2, i, ell, log_n);
   const u64* cb = p.ct + rq * p.ct_b + ((u64)b * ell + i) * n;
   const u64* d0 = p.diag ? p.diag + (u64)o * p.diag_set + (u64)i * n : nullptr;
-  u64* dst = out + (out_o ? rq * out_b + o * out_o : ro * out_b) + ((u64)b * lo + i) * n;
+  u64* dst = out + (out_o ? rq * out_b + o * out_o : ro * out_b) + ((u64)b * kp + i) * n;
   // the operands of kMdBatch elements are loaded before any of them is finished (the stores could
   // alias the loads as far as the compiler knows, which would serialise them)
   for (u32 k0 = threadIdx.x; k0 < sl.ns; k0 += kMdBatch * blockDim.x) {
@@ -483,7 +497,7 @@ void launch_vecmat_dh_moddown_rs(const DevTables& T, const HostTables& H, u32 el
     launch_limb(K6_k_dh_top_l, T.narrow, (u32)(2 * bo), 1, T.log_n, st, T.limb_threads, T, ell, p, top2);
   }
   const Crt2 k2 = crt2_constants(H, T.L, ell - 1);
-  const double jobs = 2.0 * (ell - 1) * bo;
+  const double jobs = 2.0 * (p.keep ? p.keep : ell - 1) * bo;
   Launch L(K_KS_MODDOWN, st, 8.0 * n * jobs * 7.0, jobs * (0.5 * n * T.log_n + 4.0 * n));
   launch_limb(K6_k_vecmat_dh_moddown_rs, T.narrow, (u32)jobs, 1, T.log_n, st, T.limb_threads, T, ell, p,
               (const u64*)top, (const u64*)top2, k2, out, out_b, out_o);

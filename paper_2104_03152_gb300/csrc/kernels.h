@@ -105,8 +105,10 @@ void launch_pack_batch(const DevTables& T, const u64* ct, u64 ct_stride, u32 lev
                        u32 count, cudaStream_t st, u32 comps = 2);
 void launch_unpack_batch(const DevTables& T, const unsigned char* in, u64 in_stride, u32 level, u64* ct, u64 ct_stride,
                          u32 count, int* status, cudaStream_t st, u32 comps = 2);
+// count limb jobs (job k: limb k % per of batch entry k / per, prime mod_base + k % per), repeated for
+// ny entries of a second index y (src + y src_y, dst + y dst_y; one launch on one-CTA limbs).
 void launch_ntt(const DevTables& T, bool inverse, const u64* src, u64 src_outer, u64* dst, u64 dst_outer,
-                u32 count, u32 mod_base, u32 per, cudaStream_t st);
+                u32 count, u32 mod_base, u32 per, cudaStream_t st, u32 ny = 1, u64 src_y = 0, u64 dst_y = 0);
 enum : u32 { OP_ADD = 0, OP_SUB = 1, OP_NEG = 2, OP_MUL_PLAIN = 3, OP_ADD_PLAIN = 4, OP_SUB_PLAIN = 5 };
 // [polys][ell][N] operands; plain ops share one plaintext across all polynomials (b_stride = 0) or
 // read one plaintext per ciphertext, b_stride words apart.
@@ -147,6 +149,11 @@ struct KsPlan {
   const u64* add1;
   u64 add1_b;
   u32 R, B, add_perm, pad;
+  // one-prime ModDown only (k_ks_moddown): addx + rq addx_b ([2][ell][N], unpermuted) added to both
+  // components, and the plaintext addp ([ell][N], shared by the requests) to component 0
+  const u64* addx;
+  u64 addx_b;
+  const u64* addp;
 };
 void launch_keyswitch(const DevTables& T, u32 ell, const KsPlan& plan, cudaStream_t st);
 // ---- kern_hybrid.cu: hybrid key switching (digits of H.alpha data primes, H.K special primes).
@@ -207,7 +214,9 @@ struct VecmatDhPlan {
   u32 keys_aligned;  // every key of `keys` starts on a 16-byte boundary (bulk copies may read it)
   u32 keys_K;        // the level of every key of `keys` when they share one, else 0
   u32 keys32;        // every key of `keys` has its 32-bit copy (key32)
-  u32 pad;
+  u32 keep;          // k_vecmat_dh_moddown_rs: limbs kept per output component (0: all ell - 1; fewer: a
+                     // modulus switch down to `keep` limbs in the same pass, the dropped limbs never formed)
+  const u64* addp;   // k_vecmat_dh_moddown: a plaintext [ell][N] added to component 0 of every output, or null
 };
 // Outputs per request of a plan (1 or 4).
 __host__ __device__ inline u32 dh_outs(const VecmatDhPlan& p) { return p.outs > 1 ? p.outs : 1; }
@@ -222,13 +231,13 @@ bool dh_bulk_applies(const DevTables& T, u32 ell, const VecmatDhPlan& p);
 void launch_vecmat_dh_acc_bulk(const DevTables& T, u32 ell, const VecmatDhPlan& p, u32 rpt, cudaStream_t st);
 void launch_vecmat_dh_fold(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st);
 // top [2][B * outs][N] = INTT_P of the folded U_b[P]; out + (rq * outs + o) * out_b receives output o
-// of request rq, [2][ell][N] (before the rescale).
+// of request rq, [2][ell][N] (before the rescale), plus p.addp on component 0 when given.
 // out_o: words between consecutive outputs of one request (0: outputs follow each other, out_b apart,
 // request-major); with out_o != 0 output o of request rq goes to out + rq * out_b + o * out_o.
 void launch_vecmat_dh_moddown(const DevTables& T, u32 ell, const VecmatDhPlan& p, const u64* top, u64* out, u64 out_b,
                               cudaStream_t st, u64 out_o = 0);
 // The same ModDown and the following rescale as one rounding: outputs [2][ell-1][N] (same placement
-// rules); top2 scratch [2][B * outs][N].
+// rules), or [2][p.keep][N] when p.keep > 0; top2 scratch [2][B * outs][N].
 void launch_vecmat_dh_moddown_rs(const DevTables& T, const HostTables& H, u32 ell, const VecmatDhPlan& p,
                                  const u64* top, u64* top2, u64* out, u64 out_b, cudaStream_t st, u64 out_o = 0);
 // Stage 1 of a KsPlan alone (the P-limb inner product and its INTT into plan.top).
