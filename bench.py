@@ -249,13 +249,15 @@ def run_gpu(args, world, rank, local):
     for _ in range(2):
         model.forward_device(d_in_ptr, B, d_out_ptr)
     _, tuned_ms = timed(torch, stream, lambda: model.forward_device(d_in_ptr, B, d_out_ptr), 3)
-    tune = {"limb_threads": tuned[0], "accumulation_requests_per_thread": tuned[1],
+    tune = {"limb_threads": tuned[0],
+            "accumulation_requests_per_thread": tuned[1] if tuned[1] else
+            "default: 4 where a plan's keys sit at its level 4 or 5, else 2",
             "accumulation_form": "per-thread loads" if tuned[2] == 0 else
             "operands staged in shared memory by bulk copies, %d elements per CTA x %d stages"
             % {1: (256, 2), 2: (256, 3), 3: (128, 3), 4: (128, 4)}[tuned[2]],
             "hand_tuned_ms_per_step": hand_ms / 3, "autotuned_ms_per_step": tuned_ms / 3,
             "searched": "limb-kernel CTA size {N/64, N/32, N/16 per slice} x accumulation requests per thread "
-                        "{1, 2} x accumulation form {per-thread loads, staged by bulk copies: 256 x 2, "
+                        "{default, 2, 4, 1} x accumulation form {per-thread loads, staged by bulk copies: 256 x 2, "
                         "256 x 3, 128 x 3, 128 x 4 elements per CTA x stages}"}
     ctx.synchronize()
     # plain path: one request per step

@@ -171,8 +171,11 @@ tcks_status tcks_ctx_key_bytes(const tcks_ctx* ctx, uint64_t* bytes);
 tcks_status tcks_ctx_synchronize(tcks_ctx* ctx);
 /* Launch shape of the context's kernels (results are bit-identical for every shape): limb_threads =
  * threads per CTA of the limb kernels (0: the default for N; else a multiple of 32 the kernels
- * accept), accum_rpt = requests per thread of the double-hoisted accumulation with 32-bit words (0:
- * default 2; 1 or 2), accum_form = 0 (default): that accumulation loads its operands thread by
+ * accept), accum_rpt = requests per thread of the double-hoisted accumulation with 32-bit words (1 or
+ * 2: that many everywhere; 0 (default): 4 where every key of a plan sits at its level 4 or 5 at N = 2^13
+ * (each key word then serves four requests), 2 elsewhere; 4: 4 wherever every key of a plan sits at its
+ * level (levels 1..8, N = 2^13), 2 elsewhere), accum_form = 0 (default): that accumulation loads its
+ * operands thread by
  * thread; 1, 2, 3, 4: it stages each rotation's operands in shared memory with bulk copies where the
  * layout allows (32-bit words, level <= 8, 16-byte aligned operands), with 256 x 2, 256 x 3, 128 x 3
  * or 128 x 4 elements per CTA x stages. Set by the autotuners; get reads it back. */
@@ -429,7 +432,7 @@ tcks_status tcks_conv2d_im2col_pt(const tcks_ct* a, const tcks_pt* kernel, uint3
 tcks_status tcks_autotune(tcks_ctx* ctx, const char* cache_path, uint32_t* chosen_threads);
 /* Autotuner of the batched encrypted network (declared here, takes the model of tcks_cnn_create): times
  * a whole batched forward pass of `batch` requests for every combination of limb-kernel CTA size
- * (N/64, N/32, N/16 threads per slice), double-hoisted accumulation requests per thread (1 or 2) and
+ * (N/64, N/32, N/16 threads per slice), double-hoisted accumulation requests per thread (0, 2, 4 or 1) and
  * accumulation form (per-thread loads, or operands staged by bulk copies in one of four shapes; see
  * tcks_ctx_set_launch_shape; the last two for 32-bit words), keeps the fastest on the model's context (tcks_ctx_set_launch_shape) and, with a cache_path,
  * records it under the GPU name, log N, word size and batch (a later call reads it back). Results are

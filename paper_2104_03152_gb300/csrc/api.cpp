@@ -789,7 +789,7 @@ tcks_status tcks_ctx_set_launch_shape(tcks_ctx* c, uint32_t limb_threads, uint32
   TCKS_API_BEGIN
   if (!c) fail(TCKS_ERR_INVALID_ARG, "null context");
   if (limb_threads && (limb_threads % 32 || limb_threads > 1024)) fail(TCKS_ERR_INVALID_ARG, "limb_threads: 0 or a multiple of 32 up to 1024");
-  if (accum_rpt > 2) fail(TCKS_ERR_INVALID_ARG, "accum_rpt: 0 (default), 1 or 2");
+  if (accum_rpt > 2 && accum_rpt != 4) fail(TCKS_ERR_INVALID_ARG, "accum_rpt: 0 (default), 1, 2 or 4");
   if (accum_form > 4) fail(TCKS_ERR_INVALID_ARG, "accum_form: 0 (per-thread loads) or 1..4 (staged where possible)");
   c->T.limb_threads = limb_threads;
   c->T.dh_rpt = accum_rpt;

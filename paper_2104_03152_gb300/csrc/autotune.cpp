@@ -86,7 +86,7 @@ extern "C" tcks_status tcks_cnn_autotune(const tcks_cnn* m, uint32_t batch, cons
     cudaDeviceProp prop;
     check_cuda(cudaGetDeviceProperties(&prop, c->device), "device properties");
     const u32 log_n = c->params.log_n, log_c = log_n > 14 ? log_n - 14 : 0, ns = 1u << (log_n - log_c);
-    const std::string key = std::string(prop.name) + "|cnn2|" + std::to_string(log_n) + "|" +
+    const std::string key = std::string(prop.name) + "|cnn3|" + std::to_string(log_n) + "|" +
                             (c->T.narrow ? "32" : "64") + "|" + std::to_string(batch);
     std::map<std::string, u32> cache;
     if (cache_path && *cache_path) cache = read_cache(cache_path);
@@ -98,7 +98,7 @@ extern "C" tcks_status tcks_cnn_autotune(const tcks_cnn* m, uint32_t batch, cons
     u32 best_t = 0, best_r = 0, best_f = 0;
     auto it = cache.find(key);
     const u32 cv = it != cache.end() ? it->second : 0;
-    if (cv / 100 >= 32 && cv / 100 <= cap && (cv / 10) % 10 <= 4 && cv % 10 <= 2) {
+    if (cv / 100 >= 32 && cv / 100 <= cap && (cv / 10) % 10 <= 4 && (cv % 10 <= 2 || cv % 10 == 4)) {
       best_t = cv / 100;
       best_f = (cv / 10) % 10;
       best_r = cv % 10;
@@ -108,7 +108,7 @@ extern "C" tcks_status tcks_cnn_autotune(const tcks_cnn* m, uint32_t batch, cons
         u32 t = std::max<u32>(32, std::min(cap, ns / div));
         if (std::find(threads.begin(), threads.end(), t) == threads.end()) threads.push_back(t);
       }
-      const std::vector<u32> rpts = c->T.narrow ? std::vector<u32>{2, 1} : std::vector<u32>{0};
+      const std::vector<u32> rpts = c->T.narrow ? std::vector<u32>{0, 2, 4, 1} : std::vector<u32>{0};
       const std::vector<u32> forms = c->T.narrow ? std::vector<u32>{0, 1, 2, 3, 4} : std::vector<u32>{0};
       const u32 L = cnn_input_level(m);
       const u64 win = ct_words(c, L), wout = ct_words(c, L - 6);

@@ -38,12 +38,6 @@ static void op_vecmat_dh(tcks_ctx* c, const u64* ct, u64 cw, u32 count, u32 ell,
   const u32 R = M->diags - 1;
   DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
   launch_modup(c->T, ct + (size_t)ell * n, cw, count, ell, coef.p, digits.p, c->stream);
-  // chunks of rotations: enough CTAs for a few waves of 256-thread CTAs on every SM
-  const u64 base = vecmat_dh_base_ctas(c->params.log_n, ell, count, c->T.narrow, 1, c->T.dh_rpt), want = 152ull * 8 * 4;
-  u32 chunks = (u32)std::min<u64>(R, std::max<u64>(1, (want + base - 1) / base));
-  const u32 chunk = (R + chunks - 1) / chunks;
-  chunks = (R + chunk - 1) / chunk;
-  DevBuf partial(c, (size_t)count * chunks * 3 * (ell + 1) * n);
   VecmatDhPlan p{};
   p.keys = kt->d;
   p.keys_aligned = kt->aligned16;
@@ -56,9 +50,15 @@ static void op_vecmat_dh(tcks_ctx* c, const u64* ct, u64 cw, u32 count, u32 ell,
   p.diag = M->d;
   p.diag_stride = (u64)M->limbs() * n;
   p.p_limb = M->level;
-  p.partial = partial.p;
   p.R = R;
   p.B = count;
+  // chunks of rotations: enough CTAs for a few waves of 256-thread CTAs on every SM
+  const u64 base = vecmat_dh_base_ctas(c->T, ell, p), want = 152ull * 8 * 4;
+  u32 chunks = (u32)std::min<u64>(R, std::max<u64>(1, (want + base - 1) / base));
+  const u32 chunk = (R + chunks - 1) / chunks;
+  chunks = (R + chunk - 1) / chunk;
+  DevBuf partial(c, (size_t)count * chunks * 3 * (ell + 1) * n);
+  p.partial = partial.p;
   p.chunk = chunk;
   p.chunks = chunks;
   launch_vecmat_dh_acc(c->T, ell, p, c->stream);
@@ -109,11 +109,6 @@ void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const st
   const u32 R = (u32)ks.size();
   DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
   launch_modup(c->T, x + (size_t)ell * n, cw, count, ell, coef.p, digits.p, c->stream);
-  const u64 base = vecmat_dh_base_ctas(c->params.log_n, ell, count, c->T.narrow, 1, c->T.dh_rpt), want = 152ull * 8 * 4;
-  u32 chunks = (u32)std::min<u64>(R, std::max<u64>(1, (want + base - 1) / base));
-  const u32 chunk = (R + chunks - 1) / chunks;
-  chunks = (R + chunk - 1) / chunk;
-  DevBuf partial(c, (size_t)count * chunks * 3 * (ell + 1) * n);
   VecmatDhPlan p{};
   p.keys = kt.d;
   p.keys_aligned = kt.aligned16;
@@ -125,9 +120,15 @@ void op_rotsum_hoisted(tcks_ctx* c, u64* x, u64 cw, u32 count, u32 ell, const st
   p.ct_b = cw;
   p.diag = nullptr;  // unit diagonals
   p.addp = bias;
-  p.partial = partial.p;
   p.R = R;
   p.B = count;
+  // chunks of rotations: enough CTAs for a few waves of 256-thread CTAs on every SM
+  const u64 base = vecmat_dh_base_ctas(c->T, ell, p), want = 152ull * 8 * 4;
+  u32 chunks = (u32)std::min<u64>(R, std::max<u64>(1, (want + base - 1) / base));
+  const u32 chunk = (R + chunks - 1) / chunks;
+  chunks = (R + chunk - 1) / chunk;
+  DevBuf partial(c, (size_t)count * chunks * 3 * (ell + 1) * n);
+  p.partial = partial.p;
   p.chunk = chunk;
   p.chunks = chunks;
   launch_vecmat_dh_acc(c->T, ell, p, c->stream);
@@ -157,11 +158,6 @@ void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, cons
   const u32 R = (u32)ks.size();
   DevBuf coef(c, (size_t)count * ell * n), digits(c, (size_t)count * ell * (ell + 1) * n);
   launch_modup(c->T, x + (size_t)ell * n, cw, count, ell, coef.p, digits.p, c->stream);
-  const u64 base = vecmat_dh_base_ctas(c->params.log_n, ell, count, c->T.narrow, outs, c->T.dh_rpt), want = 152ull * 8 * 4;
-  u32 chunks = (u32)std::min<u64>(R, std::max<u64>(1, (want + base - 1) / base));
-  const u32 chunk = (R + chunks - 1) / chunks;
-  chunks = (R + chunk - 1) / chunk;
-  DevBuf partial(c, (size_t)count * outs * chunks * 3 * (ell + 1) * n);
   VecmatDhPlan p{};
   p.keys = kt.d;
   p.keys_aligned = kt.aligned16;
@@ -177,9 +173,15 @@ void op_dh_sum_multi(tcks_ctx* c, const u64* x, u64 cw, u32 count, u32 ell, cons
   p.p_limb = p_limb;
   p.outs = outs;
   p.keep = keep;
-  p.partial = partial.p;
   p.R = R;
   p.B = count;
+  // chunks of rotations: enough CTAs for a few waves of 256-thread CTAs on every SM
+  const u64 base = vecmat_dh_base_ctas(c->T, ell, p), want = 152ull * 8 * 4;
+  u32 chunks = (u32)std::min<u64>(R, std::max<u64>(1, (want + base - 1) / base));
+  const u32 chunk = (R + chunks - 1) / chunks;
+  chunks = (R + chunk - 1) / chunk;
+  DevBuf partial(c, (size_t)count * outs * chunks * 3 * (ell + 1) * n);
+  p.partial = partial.p;
   p.chunk = chunk;
   p.chunks = chunks;
   launch_vecmat_dh_acc(c->T, ell, p, c->stream);

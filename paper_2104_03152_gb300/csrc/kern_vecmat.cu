@@ -29,10 +29,11 @@ constexpr u32 kDhThreads = 256;
 // CTAs per SM the accumulation is compiled for, and rotations whose loads it keeps in flight (32-bit
 // words). The fixed-ring form holds two rotations' operands in registers: from level 6 on that needs
 // more than the 80 registers of three CTAs per SM (it spilled), so those levels take two CTAs per SM;
-// at level 5 one rotation at a time at three CTAs per SM measured faster than either.
-template <int ELL, int KO, int LOGN>
+// at level 5 one rotation at a time at three CTAs per SM measured faster than either. Four requests
+// per thread take two CTAs per SM.
+template <int ELL, int KO, int LOGN, int RPT>
 __host__ __device__ constexpr int dh_min_ctas() {
-  return KO > 1 ? 3 : LOGN > 0 ? (ELL >= 6 ? 2 : 3) : 1;
+  return KO > 1 ? 3 : LOGN > 0 ? (ELL >= 6 || RPT == 4 ? 2 : 3) : 1;
 }
 template <typename W, int ELL, int LOGN>
 __host__ __device__ constexpr int dh_rot_unroll() {
@@ -51,7 +52,7 @@ __host__ __device__ constexpr int dh_rot_unroll() {
 // KEYS_AT = false: the keys share one level above ELL (p.keys_K), a run-time value uniform over the
 // launch, so only the key strides are computed.
 template <typename W, int EPT, int RPT, int ELL, int KO = 1, int LOGN = 0, bool KEYS_AT = true>
-__global__ void __launch_bounds__(kDhThreads, dh_min_ctas<ELL, KO, LOGN>()) k_vecmat_dh_acc(DevTables T, u32 ell_arg,
+__global__ void __launch_bounds__(kDhThreads, dh_min_ctas<ELL, KO, LOGN, RPT>()) k_vecmat_dh_acc(DevTables T, u32 ell_arg,
                                                                const __grid_constant__ VecmatDhPlan p) {
   static_assert(LOGN == 0 || ELL > 0, "a fixed ring size needs a fixed level");
   const u32 ell = ELL > 0 ? (u32)ELL : ell_arg;
@@ -408,35 +409,44 @@ static void dh_acc_launch(dim3 grid, cudaStream_t st, const DevTables& T, u32 el
   constexpr bool kAbove = sizeof(W) == 4 && RPT == 2 && KO == 1;  // the shape with a keys-above form
   const bool above = kAbove && dh_fixed_ring_keys_above(T, ell, p, RPT, KO);
   switch (ell) {
+// RPT = 4 exists in the fixed-ring form only (dh_rpt never picks it elsewhere).
 #define TCKS_DH_CASE(E)                                                                          \
   case E:                                                                                        \
     if (fixed)                                                                                   \
       k_vecmat_dh_acc<W, EPT, RPT, E, KO, sizeof(W) == 4 ? 13 : 0><<<grid, kDhThreads, 0, st>>>(T, ell, p); \
-    else if (above)                                                                              \
-      k_vecmat_dh_acc<W, EPT, RPT, E, KO, kAbove ? 13 : 0, !kAbove><<<grid, kDhThreads, 0, st>>>(T, ell, p); \
-    else                                                                                         \
-      k_vecmat_dh_acc<W, EPT, RPT, E, KO><<<grid, kDhThreads, 0, st>>>(T, ell, p);             \
+    else if constexpr (RPT != 4) {                                                               \
+      if (above)                                                                                 \
+        k_vecmat_dh_acc<W, EPT, RPT, E, KO, kAbove ? 13 : 0, !kAbove><<<grid, kDhThreads, 0, st>>>(T, ell, p); \
+      else                                                                                       \
+        k_vecmat_dh_acc<W, EPT, RPT, E, KO><<<grid, kDhThreads, 0, st>>>(T, ell, p);           \
+    }                                                                                            \
     return;
     TCKS_DH_CASE(1) TCKS_DH_CASE(2) TCKS_DH_CASE(3) TCKS_DH_CASE(4)
     TCKS_DH_CASE(5) TCKS_DH_CASE(6) TCKS_DH_CASE(7) TCKS_DH_CASE(8)
 #undef TCKS_DH_CASE
     default:
-      k_vecmat_dh_acc<W, EPT, RPT, 0, KO><<<grid, kDhThreads, 0, st>>>(T, ell, p);
+      if constexpr (RPT != 4) k_vecmat_dh_acc<W, EPT, RPT, 0, KO><<<grid, kDhThreads, 0, st>>>(T, ell, p);
   }
 }
 
-// Requests per thread of a launch: 1 with several outputs, else the tuned value (32-bit words) or the default.
-static u32 dh_rpt_of(bool narrow, u32 outs, u32 tuned) {
-  if (outs > 1) return 1;
-  if (!narrow) return kRpt64;
-  return tuned == 1 || tuned == 2 ? tuned : kRpt32;
+// Requests per thread of a plan's launch: 1 with several outputs; with 32-bit words the tuned value 1 or
+// 2 everywhere, or else four in the fixed-ring form at the plan's own level (each key word and diagonal
+// then serves four requests; two CTAs per SM) -- at levels 4 and 5 by default (tuned 0), at every level
+// with tuned 4 -- and two elsewhere (and in the staged form).
+static u32 dh_rpt(const DevTables& T, u32 ell, const VecmatDhPlan& p) {
+  if (dh_outs(p) > 1) return 1;
+  if (!T.narrow) return kRpt64;
+  const u32 t = T.dh_rpt;
+  if (t == 1 || t == 2) return t;
+  if (!dh_bulk_applies(T, ell, p) && dh_fixed_ring(T, ell, p) && (t == 4 || ell == 4 || ell == 5)) return 4;
+  return kRpt32;
 }
 
-u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow, u32 outs, u32 rpt_tuned) {
-  const u64 n = 1ull << log_n;
-  const u32 ept = narrow ? kEpt32 : kEpt64, rpt = dh_rpt_of(narrow, outs, rpt_tuned);
+u32 vecmat_dh_base_ctas(const DevTables& T, u32 ell, const VecmatDhPlan& p) {
+  const u64 n = 1ull << T.log_n;
+  const u32 ept = T.narrow ? kEpt32 : kEpt64, rpt = dh_rpt(T, ell, p);
   const u64 eblocks = (n + kDhThreads * ept - 1) / (kDhThreads * ept);
-  return (u32)(eblocks * (ell + 1) * ((B + rpt - 1) / rpt));
+  return (u32)(eblocks * (ell + 1) * ((p.B + rpt - 1) / rpt));
 }
 
 void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st) {
@@ -444,8 +454,8 @@ void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cu
   const double wd = T.narrow ? 0.5 : 1.0;  // digit words in 8-byte units
   const u32 outs = dh_outs(p);
   const bool bulk = dh_bulk_applies(T, ell, p);
-  const bool fixed_ring = dh_fixed_ring(T, ell, p) ||
-                          dh_fixed_ring_keys_above(T, ell, p, dh_rpt_of(T.narrow, outs, T.dh_rpt), outs);
+  const u32 rpt = dh_rpt(T, ell, p);
+  const bool fixed_ring = dh_fixed_ring(T, ell, p) || dh_fixed_ring_keys_above(T, ell, p, rpt, outs);
   const double kw = !bulk && fixed_ring ? 0.5 : 1.0;  // the fixed-ring forms read the keys' 32-bit copies
   const double by = 8.0 * n *
                     ((double)p.B * (wd * ell * (ell + 1.0) + ell) +
@@ -456,13 +466,14 @@ void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cu
   // product-accumulates per (request, rotation, element): the key-switch sums 2 ell (ell + 1), then per
   // output the two components' and the c0 term's diagonal products (additions for unit diagonals)
   const double ops = (double)p.B * p.R * n * (2.0 * ell * (ell + 1.0) + outs * (2.0 * (ell + 1.0) + ell));
-  // profiler tag: level, outputs, unit diagonals (bit 16), staged operands (bit 17), fixed ring size (bit 18)
+  // profiler tag: level, outputs, unit diagonals (bit 16), staged operands (bit 17), fixed ring size (bit 18),
+  // four requests per thread (bit 19)
   Launch L(K_VECMAT_DH, st, by + 8.0 * n * (outs - 1.0) * (p.R * (ell + 1.0) + p.B * p.chunks * (3.0 * ell + 2.0)), ops,
            ell | (outs << 8) | ((p.diag ? 0u : 1u) << 16) | ((bulk ? 1u : 0u) << 17) |
-               ((!bulk && fixed_ring ? 1u : 0u) << 18));
-  const dim3 grid(vecmat_dh_base_ctas(T.log_n, ell, p.B, T.narrow, outs, T.dh_rpt), p.chunks);
+               ((!bulk && fixed_ring ? 1u : 0u) << 18) | ((rpt == 4 ? 1u : 0u) << 19));
+  const dim3 grid(vecmat_dh_base_ctas(T, ell, p), p.chunks);
   if (bulk) {
-    launch_vecmat_dh_acc_bulk(T, ell, p, dh_rpt_of(true, outs, T.dh_rpt), st);
+    launch_vecmat_dh_acc_bulk(T, ell, p, rpt, st);
     return;
   }
   if (outs == 4) {
@@ -471,7 +482,9 @@ void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cu
     else
       dh_acc_launch<u64, 1, 1, 4>(grid, st, T, ell, p);
   } else if (T.narrow) {
-    if (dh_rpt_of(true, 1, T.dh_rpt) == 1)
+    if (rpt == 4)
+      dh_acc_launch<u32, kEpt32, 4, 1>(grid, st, T, ell, p);
+    else if (rpt == 1)
       dh_acc_launch<u32, kEpt32, 1, 1>(grid, st, T, ell, p);
     else
       dh_acc_launch<u32, kEpt32, kRpt32, 1>(grid, st, T, ell, p);

@@ -221,7 +221,7 @@ struct VecmatDhPlan {
 // Outputs per request of a plan (1 or 4).
 __host__ __device__ inline u32 dh_outs(const VecmatDhPlan& p) { return p.outs > 1 ? p.outs : 1; }
 // CTAs of one chunk of k_vecmat_dh_acc (element blocks x slots x requests).
-u32 vecmat_dh_base_ctas(u32 log_n, u32 ell, u32 B, bool narrow, u32 outs = 1, u32 rpt = 0);
+u32 vecmat_dh_base_ctas(const DevTables& T, u32 ell, const VecmatDhPlan& p);
 void launch_vecmat_dh_acc(const DevTables& T, u32 ell, const VecmatDhPlan& p, cudaStream_t st);
 // The same accumulation with each rotation's operands staged in shared memory by bulk copies
 // (kern_dh_bulk.cu): whether it applies to a plan (T.dh_form 1..4, 32-bit words, level 1..8, 16-byte

@@ -170,9 +170,10 @@ def test_cnn_graph_equals_single(setup):
 
 def test_cnn_accumulation_forms_identical(setup):
     """The double-hoisted accumulation with its operands staged in shared memory by bulk copies (every
-    staged shape: 256 or 128 elements per CTA, 2 to 4 stages) and with per-thread loads, at one and two
-    requests per thread, give the same bits on the bench's layout; the profiler's tags show which form
-    ran."""
+    staged shape: 256 or 128 elements per CTA, 2 to 4 stages) and with per-thread loads, at one, two
+    and four requests per thread (0: four at levels 4 and 5 in the fixed-ring form; 4: four at every
+    level there), give the same bits on the bench's layout, five requests (a ragged last group); the
+    profiler's tags show which form and how many requests per thread ran."""
     o, w, enc, ctx, model, need = setup
     base = ctx.flags
     shape = ctx.launch_shape()
@@ -188,14 +189,19 @@ def test_cnn_accumulation_forms_identical(setup):
             cts.append(ctx.encrypt_values(v, 700 + seed))
         results = {}
         for form in (0, 1, 2, 3, 4):
-            for rpt in (1, 2):
+            for rpt in (0, 1, 2, 4):
                 ctx.set_launch_shape(0, rpt, form)
                 tk.profile_start()
                 outs = m.forward_batch(cts)
                 ctx.synchronize()
                 tk.profile_stop()
-                staged = {(tag >> 17) & 1 for tag, _, _ in tk.profile_records("vecmat_dh_acc")}
+                tags = [tag for tag, _, _ in tk.profile_records("vecmat_dh_acc")]
+                staged = {(tag >> 17) & 1 for tag in tags}
                 assert staged == {0 if form == 0 else 1}, (form, rpt, staged)
+                # levels that ran four requests per thread: the giant steps (5) and FC1 (4), whose keys
+                # sit at their own level; the conv sum has four outputs and FC2's keys sit above it
+                four = {tag & 0xFF for tag in tags if (tag >> 19) & 1}
+                assert four == (set() if form or rpt in (1, 2) else {4, 5}), (form, rpt, four)
                 results[(form, rpt)] = [c.export() for c in outs]
         ref = results[(0, 2)]
         for key, got in results.items():
@@ -503,13 +509,13 @@ def test_cnn_autotune_is_bit_identical(setup, tmp_path):
         cache = str(tmp_path / "tune.json")
         shape = ctx.launch_shape()
         t, r, f = model.autotune(3, cache)
-        assert t in (128, 256, 512) and r in (1, 2) and f in (0, 1, 2, 3, 4)
+        assert t in (128, 256, 512) and r in (0, 1, 2, 4) and f in (0, 1, 2, 3, 4)
         assert ctx.launch_shape() == (t, r, f)
         after = [x.export() for x in model.forward_batch(cts)]
         for a, b in zip(before, after):
             assert np.array_equal(a, b)
         assert model.autotune(3, cache) == (t, r, f)
-        assert "|cnn2|13|32|3" in open(cache).read()
+        assert "|cnn3|13|32|3" in open(cache).read()
     finally:
         ctx.set_launch_shape(*shape)
         ctx.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE)

@@ -102,10 +102,12 @@ def test_vecmat_double_hoisted_parity(n, m):
         g.set_flags(tk.TCKS_AUTO_RELIN | tk.TCKS_AUTO_RESCALE)
 
 
-@pytest.mark.parametrize("n,m", [(16, 4), (64, 10), (256, 64)])
+@pytest.mark.parametrize("n,m", [(16, 4), (64, 10), (256, 64), (32, 4), (16, 8)])
 def test_vecmat_rect_parity(n, m):
     """Rectangular (hybrid) diagonals: with the oracle's encodings imported, bit-exact against the
-    oracle's rectangular schedule with either key-switch schedule, single and batched. Diagonals
+    oracle's rectangular schedule with either key-switch schedule, single and batched; the
+    rotate-and-add chains after the sum have two, three and one steps (the steps alternate between
+    the output and a scratch, an odd chain takes its first in place). Diagonals
     encoded on the GPU decrypt to the same v M (their every slot is non-zero, so the FFT and the
     oracle's direct sum round an encoding coefficient differently at near ties far more often than
     for the square form, reading A9)."""
