@@ -198,10 +198,16 @@ def test_cnn_accumulation_forms_identical(setup):
                 tags = [tag for tag, _, _ in tk.profile_records("vecmat_dh_acc")]
                 staged = {(tag >> 17) & 1 for tag in tags}
                 assert staged == {0 if form == 0 else 1}, (form, rpt, staged)
-                # levels that ran four requests per thread: the giant steps (5) and FC1 (4), whose keys
-                # sit at their own level; the conv sum has four outputs and FC2's keys sit above it
+                # levels that ran four requests per thread: only the fixed-ring form (tag bit 18), by
+                # default at levels 4 and 5 only; FC1 (level 4) has its keys at its own level
                 four = {tag & 0xFF for tag in tags if (tag >> 19) & 1}
-                assert four == (set() if form or rpt in (1, 2) else {4, 5}), (form, rpt, four)
+                fixed = {tag & 0xFF for tag in tags if (tag >> 18) & 1}
+                if form or rpt in (1, 2):
+                    assert not four, (form, rpt, four)
+                else:
+                    assert 4 in four and four <= fixed, (form, rpt, four, fixed)
+                    if rpt == 0:
+                        assert four <= {4, 5}, four
                 results[(form, rpt)] = [c.export() for c in outs]
         ref = results[(0, 2)]
         for key, got in results.items():
