@@ -70,13 +70,21 @@ def barrier(world):
 
 
 def reduce_max(world, x: float) -> float:
+    """The largest x over the ranks (the slowest rank's time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(world: int, batch: int, steps: int, total_ms: float) -> float:
+    """Whole-job inferences/s: every rank runs `steps` batches of `batch` independent requests (replicas,
+    no exchange), over the slowest rank's time (total_ms, already the max over ranks)."""
+    return world * batch * steps / (total_ms / 1e3)
 
 
 # ------------------------------------------------------------------------------------ clocks --
@@ -1132,7 +1140,7 @@ def main():
     peaks = measured_peaks()
     B = args.batch
     ms_per_step = r["total_ms"] / args.steps
-    value = world * B * args.steps / (r["total_ms"] / 1e3)
+    value = job_value(world, B, args.steps, r["total_ms"])
     # dominant kernel family by device time
     prof = r["prof"]
     dom = max(prof.items(), key=lambda kv: kv[1][1])
